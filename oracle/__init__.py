@@ -1,0 +1,292 @@
+"""Python binding of the FP64 CPU oracle (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package. It shares no code with the CUDA library
+in ``paper_2408_01361_gb300``; the two meet only through the seeded inputs of
+``paper_2408_01361_gb300.inputs`` (which holds none of the method's arithmetic).
+
+Arrays are numpy float64 of shape (8, N3, N2, N1), ghosts included and not
+padded, slot order (rho, u, u~1, u~2, u~3, B1, B2, B3).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_SRC = [os.path.join(_HERE, f) for f in ("harm_oracle.cpp", "harm_oracle.hpp", "dual.hpp")]
+
+KIND = {"minkowski": 0, "ks": 1, "mks": 2, "fmks": 3}
+BC = {"periodic": 0, "outflow": 1, "polar": 2, "dirichlet": 3}
+RECON = {"mc": 0, "weno5": 1}
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so in place (plain g++, OpenMP, no CPU-specific flags)."""
+    newest = max(os.path.getmtime(p) for p in _SRC)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
+        cmd = ["g++", "-std=c++17", "-O3", "-fopenmp", "-fPIC", "-shared", "-o", _LIB_PATH,
+               os.path.join(_HERE, "harm_oracle.cpp")]
+        subprocess.run(cmd, check=True)
+    return _LIB_PATH
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("kind", C.c_int), ("n1", C.c_int), ("n2", C.c_int), ("n3", C.c_int), ("ng", C.c_int),
+        ("recon", C.c_int), ("bc", C.c_int * 6),
+        ("a", C.c_double), ("gam", C.c_double),
+        ("x1min", C.c_double), ("x1max", C.c_double), ("x2min", C.c_double),
+        ("x2max", C.c_double), ("x3min", C.c_double), ("x3max", C.c_double),
+        ("hslope", C.c_double), ("poly_xt", C.c_double), ("poly_alpha", C.c_double),
+        ("mks_smooth", C.c_double), ("cfl", C.c_double),
+        ("rho_min", C.c_double), ("u_min", C.c_double), ("bsq_rho_max", C.c_double),
+        ("bsq_u_max", C.c_double), ("u_rho_max", C.c_double), ("gamma_max", C.c_double),
+    ]
+
+
+def params(cfg: dict) -> Params:
+    """ctypes parameter block from a problem configuration dict."""
+    p = Params()
+    p.kind = KIND[cfg["coords"]]
+    p.n1, p.n2, p.n3 = cfg["n1"], cfg["n2"], cfg["n3"]
+    p.ng = cfg.get("ng", 3)
+    p.recon = RECON[cfg["recon"]]
+    for q, b in enumerate(cfg["bc"]):
+        p.bc[q] = BC[b]
+    p.a = cfg.get("a", 0.0)
+    p.gam = cfg["gam"]
+    (p.x1min, p.x1max), (p.x2min, p.x2max), (p.x3min, p.x3max) = cfg["x1"], cfg["x2"], cfg["x3"]
+    p.hslope = cfg.get("hslope", 0.3)
+    p.poly_xt = cfg.get("poly_xt", 0.82)
+    p.poly_alpha = cfg.get("poly_alpha", 14.0)
+    p.mks_smooth = cfg.get("mks_smooth", 0.5)
+    p.cfl = cfg.get("cfl", 0.9)
+    fl = cfg.get("floors", {})
+    p.rho_min = fl.get("rho_min", 1e-20)
+    p.u_min = fl.get("u_min", 1e-20)
+    p.bsq_rho_max = fl.get("bsq_rho_max", 1e300)
+    p.bsq_u_max = fl.get("bsq_u_max", 1e300)
+    p.u_rho_max = fl.get("u_rho_max", 1e300)
+    p.gamma_max = fl.get("gamma_max", 1e300)
+    return p
+
+
+_lib = None
+_dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        L = _lib
+        PP = C.POINTER(Params)
+        L.or_set_threads.argtypes = [C.c_int]
+        L.or_get_threads.restype = C.c_int
+        L.or_geometry.argtypes = [PP, C.c_int, _dp, _dp, _dp, _dp]
+        L.or_connection.argtypes = [PP, _dp]
+        L.or_metric_points.argtypes = [PP, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
+        L.or_native_to_ks.argtypes = [PP, C.c_int, _dp, _dp, _dp, _dp]
+        L.or_prim_to_cons.argtypes = [PP, _dp, _dp]
+        L.or_cons_to_prim.argtypes = [PP, _dp, _dp, C.c_void_p]
+        L.or_cons_to_prim.restype = C.c_long
+        L.or_apply_bc.argtypes = [PP, _dp, C.c_void_p, C.c_void_p]
+        L.or_fluxes.argtypes = [PP, _dp] + [C.c_void_p] * 6
+        L.or_cfl_dt.argtypes = [PP, _dp, C.c_void_p, C.c_void_p]
+        L.or_cfl_dt.restype = C.c_double
+        L.or_step.argtypes = [PP, _dp, _dp, C.c_double, C.c_void_p, C.c_void_p, C.POINTER(C.c_long)]
+        L.or_step.restype = C.c_double
+        L.or_evolve.argtypes = [PP, _dp, _dp, C.c_int, C.c_double, C.c_double, C.c_void_p, C.c_void_p,
+                                C.POINTER(C.c_long)]
+        L.or_evolve.restype = C.c_double
+        L.or_divb.argtypes = [PP, _dp, _dp, C.c_void_p]
+        L.or_point_flux.argtypes = [C.c_double, _dp, _dp, C.c_int, _dp]
+        L.or_point_state.argtypes = [_dp, _dp, _dp]
+        L.or_point_speeds.argtypes = [C.c_double, _dp, _dp, C.c_int, C.POINTER(C.c_double),
+                                      C.POINTER(C.c_double)]
+        L.or_point_llf.argtypes = [C.c_double, _dp, _dp, _dp, C.c_int, _dp, C.POINTER(C.c_double)]
+        L.or_point_c2p.argtypes = [C.c_double, _dp, _dp, _dp]
+        L.or_point_c2p.restype = C.c_int
+        L.or_point_jacobians.argtypes = [C.c_double, _dp, _dp, C.c_int, _dp, _dp]
+        L.or_point_source.argtypes = [PP, C.c_double, C.c_double, _dp, _dp]
+        L.or_recon.argtypes = [C.c_int, C.c_int, _dp, _dp, _dp]
+    return _lib
+
+
+def set_threads(n: int) -> None:
+    lib().or_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return lib().or_get_threads()
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def shape(cfg: dict):
+    ng = cfg.get("ng", 3)
+    n3 = cfg["n3"]
+    return (8, n3 + 2 * ng if n3 > 1 else 1, cfg["n2"] + 2 * ng, cfg["n1"] + 2 * ng)
+
+
+def geometry(cfg: dict, loc: int = 0):
+    """(gcov, gcon, gdet, alpha) over the (N2, N1) ghosted grid at a location
+    (0 centre, 1 x1 face, 2 x2 face, 3 x3 face, 4 corner)."""
+    _, _, N2, N1 = shape(cfg)
+    gcov = np.zeros((N2, N1, 4, 4)); gcon = np.zeros((N2, N1, 4, 4))
+    gdet = np.zeros((N2, N1)); alpha = np.zeros((N2, N1))
+    lib().or_geometry(C.byref(params(cfg)), loc, gcov, gcon, gdet, alpha)
+    return gcov, gcon, gdet, alpha
+
+
+def connection(cfg: dict):
+    _, _, N2, N1 = shape(cfg)
+    out = np.zeros((N2, N1, 4, 4, 4))
+    lib().or_connection(C.byref(params(cfg)), out)
+    return out
+
+
+def metric_points(cfg: dict, x1, x2):
+    x1 = np.ascontiguousarray(x1, dtype=np.float64); x2 = np.ascontiguousarray(x2, dtype=np.float64)
+    n = x1.size
+    gcov = np.zeros((n, 4, 4)); gcon = np.zeros((n, 4, 4)); gdet = np.zeros(n); conn = np.zeros((n, 4, 4, 4))
+    lib().or_metric_points(C.byref(params(cfg)), n, x1, x2, gcov, gcon, gdet, conn)
+    return gcov, gcon, gdet, conn
+
+
+def native_to_ks(cfg: dict, x1, x2):
+    x1 = np.ascontiguousarray(x1, dtype=np.float64); x2 = np.ascontiguousarray(x2, dtype=np.float64)
+    r = np.zeros(x1.size); th = np.zeros(x1.size)
+    lib().or_native_to_ks(C.byref(params(cfg)), x1.size, x1, x2, r, th)
+    return r, th
+
+
+def prim_to_cons(cfg: dict, P):
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    U = np.zeros_like(P)
+    lib().or_prim_to_cons(C.byref(params(cfg)), P, U)
+    return U
+
+
+def cons_to_prim(cfg: dict, U, P_guess):
+    """Returns (P, pflag, nfail); P keeps the guess where the inversion failed."""
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    P = np.array(P_guess, dtype=np.float64, order="C", copy=True)
+    pflag = np.zeros(P.shape[1:], dtype=np.int32)
+    nfail = lib().or_cons_to_prim(C.byref(params(cfg)), U, P, _ptr(pflag))
+    return P, pflag, int(nfail)
+
+
+def apply_bc(cfg: dict, P, dirichlet=None):
+    P = np.array(P, dtype=np.float64, order="C", copy=True)
+    lo, hi = (dirichlet or (None, None))
+    lib().or_apply_bc(C.byref(params(cfg)), P, _ptr(lo), _ptr(hi))
+    return P
+
+
+def fluxes(cfg: dict, P):
+    """Fluxes after polar zeroing and Flux-CT from P (ghosts must be filled)."""
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    F = [np.zeros_like(P) for _ in range(3)]
+    ct = [np.zeros(P.shape[1:]) for _ in range(3)]
+    lib().or_fluxes(C.byref(params(cfg)), P, *[_ptr(f) for f in F], *[_ptr(c) for c in ct])
+    return F, ct
+
+
+def cfl_dt(cfg: dict, P, dirichlet=None) -> float:
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    lo, hi = (dirichlet or (None, None))
+    return lib().or_cfl_dt(C.byref(params(cfg)), P, _ptr(lo), _ptr(hi))
+
+
+def step(cfg: dict, U, P, dt: float, dirichlet=None):
+    """One two-stage step. Returns (U, P, dt_next, stats[nfail, nfloor, nunfixed])."""
+    U = np.array(U, dtype=np.float64, order="C", copy=True)
+    P = np.array(P, dtype=np.float64, order="C", copy=True)
+    lo, hi = (dirichlet or (None, None))
+    st = (C.c_long * 3)()
+    dtn = lib().or_step(C.byref(params(cfg)), U, P, float(dt), _ptr(lo), _ptr(hi), st)
+    return U, P, dtn, list(st)
+
+
+def evolve(cfg: dict, U, P, nsteps: int, dt: float, t_end: float = 0.0, dirichlet=None):
+    """nsteps steps (or until t_end); dt > 0 fixed, dt < 0: first step -dt, then CFL.
+    Returns (U, P, t, stats)."""
+    U = np.array(U, dtype=np.float64, order="C", copy=True)
+    P = np.array(P, dtype=np.float64, order="C", copy=True)
+    lo, hi = (dirichlet or (None, None))
+    st = (C.c_long * 3)()
+    t = lib().or_evolve(C.byref(params(cfg)), U, P, int(nsteps), float(dt), float(t_end), _ptr(lo), _ptr(hi), st)
+    return U, P, t, list(st)
+
+
+def divb(cfg: dict, P, field: bool = False):
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    out = np.zeros(2)
+    div = np.zeros(P.shape[1:]) if field else None
+    lib().or_divb(C.byref(params(cfg)), P, out, _ptr(div))
+    return (out[0], out[1], div) if field else (out[0], out[1])
+
+
+# ---- point-level helpers -------------------------------------------------
+def _g16(gcov):
+    return np.ascontiguousarray(np.asarray(gcov, dtype=np.float64).reshape(16))
+
+
+def point_flux(gam, gcov, P, d):
+    F = np.zeros(8)
+    lib().or_point_flux(float(gam), _g16(gcov), np.ascontiguousarray(P, dtype=np.float64), int(d), F)
+    return F
+
+
+def point_state(gcov, P):
+    out = np.zeros(9)
+    lib().or_point_state(_g16(gcov), np.ascontiguousarray(P, dtype=np.float64), out)
+    return out[:4], out[4:8], out[8]
+
+
+def point_speeds(gam, gcov, P, d):
+    cmax = C.c_double(); cmin = C.c_double()
+    lib().or_point_speeds(float(gam), _g16(gcov), np.ascontiguousarray(P, dtype=np.float64), int(d),
+                          C.byref(cmax), C.byref(cmin))
+    return cmax.value, cmin.value
+
+
+def point_llf(gam, gcov, PL, PR, d):
+    F = np.zeros(8); ct = C.c_double()
+    lib().or_point_llf(float(gam), _g16(gcov), np.ascontiguousarray(PL, dtype=np.float64),
+                       np.ascontiguousarray(PR, dtype=np.float64), int(d), F, C.byref(ct))
+    return F, ct.value
+
+
+def point_c2p(gam, gcov, U, P_guess):
+    P = np.array(P_guess, dtype=np.float64, copy=True)
+    flag = lib().or_point_c2p(float(gam), _g16(gcov), np.ascontiguousarray(U, dtype=np.float64), P)
+    return P, flag
+
+
+def point_jacobians(gam, gcov, P, d):
+    dF = np.zeros((8, 8)); dU = np.zeros((8, 8))
+    lib().or_point_jacobians(float(gam), _g16(gcov), np.ascontiguousarray(P, dtype=np.float64), int(d), dF, dU)
+    return dF, dU
+
+
+def point_source(cfg, x1, x2, P):
+    S = np.zeros(8)
+    lib().or_point_source(C.byref(params(cfg)), float(x1), float(x2), np.ascontiguousarray(P, dtype=np.float64), S)
+    return S
+
+
+def recon(kind: str, q):
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    lo = np.full_like(q, np.nan); hi = np.full_like(q, np.nan)
+    lib().or_recon(RECON[kind], q.size, q, lo, hi)
+    return lo, hi

@@ -1,0 +1,795 @@
+// Grid-level oracle: boundaries, fluxes with Flux-CT, sources, the two-stage
+// update, primitive recovery, floors, fixup, the CFL time step and divB.
+//
+// TEST INFRASTRUCTURE ONLY (see harm_oracle.hpp). Exposed to Python through a
+// plain C API (prefix or_) for the parity tests, the pin tests and the CPU
+// baseline of the benchmark.
+//
+// Array layout used by every or_ entry point: double[8][N3][N2][N1] with
+// ghosts included and no padding (N1 = n1 + 2 ng, N2 = n2 + 2 ng,
+// N3 = n3 + 2 ng or 1 for a 2-D problem), slot order rho, u, u~1..3, B1..3.
+#include <omp.h>
+
+#include <cstdio>
+#include <cstring>
+#include <limits>
+
+#include "harm_oracle.hpp"
+
+using namespace oracle;
+
+namespace {
+
+struct Grid {
+  Params c;
+  GridInfo g;
+  // Geometry cache over (j, i) of the ghosted grid, per location (the metric
+  // depends only on x1 and x2).
+  std::vector<Geo> geo[5];
+  std::vector<double> conn;  // [N2][N1][4][4][4] at cell centres
+
+  size_t idx(int v, int k, int j, int i) const {
+    return ((static_cast<size_t>(v) * g.N3 + k) * g.N2 + j) * g.N1 + i;
+  }
+  size_t cells() const { return static_cast<size_t>(g.N1) * g.N2 * g.N3; }
+  const Geo& G(int loc, int j, int i) const { return geo[loc][static_cast<size_t>(j) * g.N1 + i]; }
+  const double (*C(int j, int i) const)[4][4] {
+    return reinterpret_cast<const double(*)[4][4]>(&conn[(static_cast<size_t>(j) * g.N1 + i) * 64]);
+  }
+  // Interior index ranges [s, e) per direction.
+  int s1() const { return g.ng; }
+  int e1() const { return g.ng + g.n1; }
+  int s2() const { return g.ng; }
+  int e2() const { return g.ng + g.n2; }
+  int s3() const { return g.ng3; }
+  int e3() const { return g.ng3 + g.n3; }
+};
+
+void build_grid(const Params& c, Grid& gr) {
+  gr.c = c;
+  gr.g = grid_info(c);
+  const GridInfo& g = gr.g;
+  for (int loc = 0; loc < 5; ++loc) {
+    gr.geo[loc].resize(static_cast<size_t>(g.N1) * g.N2);
+    for (int j = 0; j < g.N2; ++j)
+      for (int i = 0; i < g.N1; ++i) {
+        // x3 faces share the cell-centre metric (no x3 dependence).
+        int l = (loc == LOC_FACE3) ? LOC_CENT : loc;
+        double x1, x2;
+        loc_coords(c, g, l, i, j, x1, x2);
+        gr.geo[loc][static_cast<size_t>(j) * g.N1 + i] = geo_at(c, x1, x2);
+      }
+  }
+  gr.conn.assign(static_cast<size_t>(g.N1) * g.N2 * 64, 0.0);
+  for (int j = 0; j < g.N2; ++j)
+    for (int i = 0; i < g.N1; ++i) {
+      double x1, x2;
+      loc_coords(c, g, LOC_CENT, i, j, x1, x2);
+      double cn[4][4][4];
+      connection_at(c, x1, x2, cn);
+      std::memcpy(&gr.conn[(static_cast<size_t>(j) * g.N1 + i) * 64], cn, sizeof(cn));
+    }
+}
+
+// Boyer-Lindquist-independent radius of a cell centre (used only by the floors):
+// r for KS-family coordinates, 1 for Minkowski (floors are then constants).
+double radius_at(const Grid& gr, int j, int i) {
+  if (gr.c.kind == MINKOWSKI) return 1.0;
+  double x1, x2, r, th;
+  loc_coords(gr.c, gr.g, LOC_CENT, i, j, x1, x2);
+  native_to_ks<double>(gr.c, x1, x2, r, th);
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// Boundary conditions on the primitives (all 8 slots). x1 ghosts are filled
+// over interior (j, k); x2 ghosts over all i and interior k; x3 ghosts over all
+// i and j, so edge and corner ghosts are compositions of the face rules.
+//   periodic: copy from the opposite side;
+//   outflow:  copy the last interior zone; x1 faces forbid inflow by clamping
+//             u~1 (<= 0 at the inner face, >= 0 at the outer face);
+//   polar:    reflect across the face, flipping the sign of u~2 and B2;
+//   dirichlet: copy caller-supplied ghost values (x1 faces only).
+// ---------------------------------------------------------------------------
+void apply_bc(const Grid& gr, double* P, const double* dir_lo, const double* dir_hi) {
+  const GridInfo& g = gr.g;
+  const int ng = g.ng;
+  // x1
+  for (int k = gr.s3(); k < gr.e3(); ++k)
+    for (int j = gr.s2(); j < gr.e2(); ++j)
+      for (int m = 0; m < ng; ++m) {
+        int ilo = ng - 1 - m, ihi = ng + g.n1 + m;
+        for (int side = 0; side < 2; ++side) {
+          int bc = gr.c.bc[side];
+          int ig = side == 0 ? ilo : ihi;
+          for (int v = 0; v < NVAR; ++v) {
+            double val = 0.0;
+            if (bc == BC_PERIODIC) {
+              int src = side == 0 ? ig + g.n1 : ig - g.n1;
+              val = P[gr.idx(v, k, j, src)];
+            } else if (bc == BC_OUTFLOW) {
+              int src = side == 0 ? ng : ng + g.n1 - 1;
+              val = P[gr.idx(v, k, j, src)];
+            } else if (bc == BC_DIRICHLET) {
+              const double* D = side == 0 ? dir_lo : dir_hi;
+              int ii = side == 0 ? ig : ig - (ng + g.n1);  // 0..ng-1
+              val = D[((static_cast<size_t>(v) * g.N3 + k) * g.N2 + j) * ng + ii];
+            } else {  // polar reflection across an x1 face is not meaningful; copy
+              int src = side == 0 ? 2 * ng - 1 - ig : 2 * (ng + g.n1) - 1 - ig;
+              val = P[gr.idx(v, k, j, src)];
+            }
+            P[gr.idx(v, k, j, ig)] = val;
+          }
+          if (bc == BC_OUTFLOW) {
+            double& u1 = P[gr.idx(U1, k, j, ig)];
+            if (side == 0 && u1 > 0.0) u1 = 0.0;
+            if (side == 1 && u1 < 0.0) u1 = 0.0;
+          }
+        }
+      }
+  // x2
+  for (int k = gr.s3(); k < gr.e3(); ++k)
+    for (int i = 0; i < g.N1; ++i)
+      for (int m = 0; m < ng; ++m) {
+        int jlo = ng - 1 - m, jhi = ng + g.n2 + m;
+        for (int side = 0; side < 2; ++side) {
+          int bc = gr.c.bc[2 + side];
+          int jg = side == 0 ? jlo : jhi;
+          int src;
+          if (bc == BC_PERIODIC)
+            src = side == 0 ? jg + g.n2 : jg - g.n2;
+          else if (bc == BC_OUTFLOW)
+            src = side == 0 ? ng : ng + g.n2 - 1;
+          else  // polar
+            src = side == 0 ? 2 * ng - 1 - jg : 2 * (ng + g.n2) - 1 - jg;
+          for (int v = 0; v < NVAR; ++v) {
+            double val = P[gr.idx(v, k, src, i)];
+            if (bc == BC_POLAR && (v == U2 || v == B2)) val = -val;
+            P[gr.idx(v, k, jg, i)] = val;
+          }
+        }
+      }
+  // x3
+  if (g.ndim == 3) {
+    for (int j = 0; j < g.N2; ++j)
+      for (int i = 0; i < g.N1; ++i)
+        for (int m = 0; m < g.ng3; ++m) {
+          int klo = g.ng3 - 1 - m, khi = g.ng3 + g.n3 + m;
+          for (int side = 0; side < 2; ++side) {
+            int bc = gr.c.bc[4 + side];
+            int kg = side == 0 ? klo : khi;
+            int src;
+            if (bc == BC_PERIODIC)
+              src = side == 0 ? kg + g.n3 : kg - g.n3;
+            else
+              src = side == 0 ? g.ng3 : g.ng3 + g.n3 - 1;
+            for (int v = 0; v < NVAR; ++v) P[gr.idx(v, kg, j, i)] = P[gr.idx(v, src, j, i)];
+          }
+        }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Fluxes: reconstruction + LLF at every face needed by the update and by
+// Flux-CT (one transverse row beyond the interior), polar zeroing, Flux-CT.
+// F[d] has the cell layout; F[d] at (k,j,i) is the flux through the lower
+// x^d face of cell (k,j,i). ctop[d] likewise.
+// ---------------------------------------------------------------------------
+struct Fluxes {
+  std::vector<double> F[3];
+  std::vector<double> ctop[3];
+};
+
+void face_range(const Grid& gr, int d, int lo[3], int hi[3]) {
+  // inclusive ranges in (i, j, k) order
+  int s[3] = {gr.s1(), gr.s2(), gr.s3()};
+  int e[3] = {gr.e1(), gr.e2(), gr.e3()};
+  for (int a = 0; a < 3; ++a) {
+    bool active = (a < 2) || gr.g.ndim == 3;
+    if (!active) { lo[a] = 0; hi[a] = 0; continue; }
+    if (a == d) { lo[a] = s[a]; hi[a] = e[a]; }
+    else { lo[a] = s[a] - 1; hi[a] = e[a]; }
+  }
+}
+
+void compute_fluxes(const Grid& gr, const double* P, Fluxes& fx) {
+  const GridInfo& g = gr.g;
+  const size_t n = gr.cells();
+  for (int d = 0; d < 3; ++d) {
+    fx.F[d].assign(NVAR * n, 0.0);
+    fx.ctop[d].assign(n, 0.0);
+  }
+  for (int d = 0; d < g.ndim; ++d) {
+    int lo[3], hi[3];
+    face_range(gr, d, lo, hi);
+    const int loc = LOC_FACE1 + d;
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int k = lo[2]; k <= hi[2]; ++k)
+      for (int j = lo[1]; j <= hi[1]; ++j)
+        for (int i = lo[0]; i <= hi[0]; ++i) {
+          double PL[NVAR], PR[NVAR];
+          for (int v = 0; v < NVAR; ++v) {
+            // stencil of the cell below the face (c = -1) and above it (c = 0)
+            double qm[5], qp[5];
+            for (int s = 0; s < 5; ++s) {
+              int o1 = (d == 0) ? s - 3 : 0, o2 = (d == 1) ? s - 3 : 0, o3 = (d == 2) ? s - 3 : 0;
+              qm[s] = P[gr.idx(v, k + o3, j + o2, i + o1)];
+              int p1 = (d == 0) ? s - 2 : 0, p2 = (d == 1) ? s - 2 : 0, p3 = (d == 2) ? s - 2 : 0;
+              qp[s] = P[gr.idx(v, k + p3, j + p2, i + p1)];
+            }
+            double lo_m, hi_m, lo_p, hi_p;
+            recon_cell(gr.c.recon, qm, lo_m, hi_m);
+            recon_cell(gr.c.recon, qp, lo_p, hi_p);
+            PL[v] = hi_m;
+            PR[v] = lo_p;
+          }
+          double F[NVAR], ct;
+          llf_flux<double>(PL, PR, gr.G(loc, j, i), gr.c.gam, d + 1, F, ct);
+          for (int v = 0; v < NVAR; ++v) fx.F[d][gr.idx(v, k, j, i)] = F[v];
+          fx.ctop[d][gr.idx(0, k, j, i)] = ct;
+        }
+  }
+  // Polar axis: no flux of anything through an x2 face lying on the axis.
+  {
+    int lo[3], hi[3];
+    face_range(gr, 1, lo, hi);
+    for (int side = 0; side < 2; ++side) {
+      if (gr.c.bc[2 + side] != BC_POLAR) continue;
+      int j = side == 0 ? gr.s2() : gr.e2();
+      for (int k = lo[2]; k <= hi[2]; ++k)
+        for (int i = lo[0]; i <= hi[0]; ++i)
+          for (int v = 0; v < NVAR; ++v) fx.F[1][gr.idx(v, k, j, i)] = 0.0;
+    }
+  }
+  // Flux-CT (Toth 2000): corner EMFs as averages of the four adjacent face
+  // fluxes of the field, then field fluxes as averages of the edge EMFs.
+  std::vector<double>& F1 = fx.F[0];
+  std::vector<double>& F2 = fx.F[1];
+  std::vector<double>& F3 = fx.F[2];
+  std::vector<double> e1(n, 0.0), e2(n, 0.0), e3(n, 0.0);
+  auto I = [&](int k, int j, int i) { return gr.idx(0, k, j, i); };
+  auto V = [&](int v, int k, int j, int i) { return gr.idx(v, k, j, i); };
+  if (g.ndim == 2) {
+    const int k = 0;
+    for (int j = gr.s2(); j <= gr.e2(); ++j)
+      for (int i = gr.s1(); i <= gr.e1(); ++i)
+        e3[I(k, j, i)] = 0.25 * (F1[V(B2, k, j, i)] + F1[V(B2, k, j - 1, i)] - F2[V(B1, k, j, i)] - F2[V(B1, k, j, i - 1)]);
+    for (int j = gr.s2(); j < gr.e2(); ++j)
+      for (int i = gr.s1(); i <= gr.e1(); ++i) {
+        F1[V(B1, k, j, i)] = 0.0;
+        F1[V(B2, k, j, i)] = 0.5 * (e3[I(k, j, i)] + e3[I(k, j + 1, i)]);
+      }
+    for (int j = gr.s2(); j <= gr.e2(); ++j)
+      for (int i = gr.s1(); i < gr.e1(); ++i) {
+        F2[V(B1, k, j, i)] = -0.5 * (e3[I(k, j, i)] + e3[I(k, j, i + 1)]);
+        F2[V(B2, k, j, i)] = 0.0;
+      }
+    return;
+  }
+  for (int k = gr.s3(); k <= gr.e3(); ++k)
+    for (int j = gr.s2(); j <= gr.e2(); ++j)
+      for (int i = gr.s1(); i <= gr.e1(); ++i) {
+        // emf3 on the x3-edge at (i-1/2, j-1/2, k)
+        if (k < gr.e3())
+          e3[I(k, j, i)] = 0.25 * (F1[V(B2, k, j, i)] + F1[V(B2, k, j - 1, i)] - F2[V(B1, k, j, i)] - F2[V(B1, k, j, i - 1)]);
+        // emf1 on the x1-edge at (i, j-1/2, k-1/2)
+        if (i < gr.e1())
+          e1[I(k, j, i)] = 0.25 * (F2[V(B3, k, j, i)] + F2[V(B3, k - 1, j, i)] - F3[V(B2, k, j, i)] - F3[V(B2, k, j - 1, i)]);
+        // emf2 on the x2-edge at (i-1/2, j, k-1/2)
+        if (j < gr.e2())
+          e2[I(k, j, i)] = 0.25 * (F3[V(B1, k, j, i)] + F3[V(B1, k, j, i - 1)] - F1[V(B3, k, j, i)] - F1[V(B3, k - 1, j, i)]);
+      }
+  for (int k = gr.s3(); k < gr.e3(); ++k)
+    for (int j = gr.s2(); j < gr.e2(); ++j)
+      for (int i = gr.s1(); i <= gr.e1(); ++i) {
+        F1[V(B1, k, j, i)] = 0.0;
+        F1[V(B2, k, j, i)] = 0.5 * (e3[I(k, j, i)] + e3[I(k, j + 1, i)]);
+        F1[V(B3, k, j, i)] = -0.5 * (e2[I(k, j, i)] + e2[I(k + 1, j, i)]);
+      }
+  for (int k = gr.s3(); k < gr.e3(); ++k)
+    for (int j = gr.s2(); j <= gr.e2(); ++j)
+      for (int i = gr.s1(); i < gr.e1(); ++i) {
+        F2[V(B1, k, j, i)] = -0.5 * (e3[I(k, j, i)] + e3[I(k, j, i + 1)]);
+        F2[V(B2, k, j, i)] = 0.0;
+        F2[V(B3, k, j, i)] = 0.5 * (e1[I(k, j, i)] + e1[I(k + 1, j, i)]);
+      }
+  for (int k = gr.s3(); k <= gr.e3(); ++k)
+    for (int j = gr.s2(); j < gr.e2(); ++j)
+      for (int i = gr.s1(); i < gr.e1(); ++i) {
+        F3[V(B1, k, j, i)] = 0.5 * (e2[I(k, j, i)] + e2[I(k, j, i + 1)]);
+        F3[V(B2, k, j, i)] = -0.5 * (e1[I(k, j, i)] + e1[I(k, j + 1, i)]);
+        F3[V(B3, k, j, i)] = 0.0;
+      }
+}
+
+// ---------------------------------------------------------------------------
+// Floors (applied after each successful inversion and after each fixup).
+//   rho >= max(rho_min r^-3/2, 1e-20, b^2 / bsq_rho_max)
+//   u   >= max(u_min r^-5/2, 1e-20, b^2 / bsq_u_max)
+//   u   <= u_rho_max rho
+//   gamma <= gamma_max (u~ rescaled so that gamma = gamma_max)
+// Returns a bit mask: 1 density/energy floor, 2 temperature ceiling, 4 gamma.
+// ---------------------------------------------------------------------------
+int apply_floors(const Params& c, const Geo& G, double r, double P[NVAR]) {
+  FluidState<double> S;
+  fluid_state(P, G, S);
+  double rho_fl = std::max(c.rho_min * std::pow(r, -1.5), 1e-20);
+  double u_fl = std::max(c.u_min * std::pow(r, -2.5), 1e-20);
+  rho_fl = std::max(rho_fl, S.bsq / c.bsq_rho_max);
+  u_fl = std::max(u_fl, S.bsq / c.bsq_u_max);
+  int flag = 0;
+  if (P[RHO] < rho_fl) { P[RHO] = rho_fl; flag |= 1; }
+  if (P[UU] < u_fl) { P[UU] = u_fl; flag |= 1; }
+  if (P[UU] > c.u_rho_max * P[RHO]) { P[UU] = c.u_rho_max * P[RHO]; flag |= 2; }
+  double qsq = 0.0;
+  for (int i = 1; i < 4; ++i)
+    for (int j = 1; j < 4; ++j) qsq += G.gcov[i][j] * P[U1 + i - 1] * P[U1 + j - 1];
+  double gamma = std::sqrt(1.0 + qsq);
+  if (gamma > c.gamma_max) {
+    double f = std::sqrt((c.gamma_max * c.gamma_max - 1.0) / (gamma * gamma - 1.0));
+    for (int i = 0; i < 3; ++i) P[U1 + i] *= f;
+    flag |= 4;
+  }
+  return flag;
+}
+
+void p2c_point(const Params& c, const Geo& G, const double P[NVAR], double U[NVAR]) {
+  FluidState<double> S;
+  fluid_state(P, G, S);
+  prim_to_flux<double>(P, S, G, c.gam, 0, U);
+}
+
+struct StageStats {
+  long nfail = 0, nfloor = 0, nunfixed = 0;
+};
+
+// One stage: Pin (ghosts filled) -> fluxes -> Uout = U0 + cdt (-div F + S(Pin))
+// -> inversion (guess Pin) -> floors -> fixup. Writes Pout (interior) and Uout
+// (interior; consistent with Pout wherever floors or fixups changed Pout).
+void stage(const Grid& gr, const double* U0, const double* Pin, double cdt, double* Uout, double* Pout,
+           Fluxes& fx, StageStats& st, std::vector<int>* pflag_out) {
+  const GridInfo& g = gr.g;
+  compute_fluxes(gr, Pin, fx);
+  std::vector<int> pflag(gr.cells(), 0), fflag(gr.cells(), 0);
+  const double dx[3] = {g.dx1, g.dx2, g.dx3};
+#pragma omp parallel for collapse(2) schedule(static)
+  for (int k = gr.s3(); k < gr.e3(); ++k)
+    for (int j = gr.s2(); j < gr.e2(); ++j)
+      for (int i = gr.s1(); i < gr.e1(); ++i) {
+        const Geo& G = gr.G(LOC_CENT, j, i);
+        double P[NVAR], S[NVAR], U[NVAR];
+        for (int v = 0; v < NVAR; ++v) P[v] = Pin[gr.idx(v, k, j, i)];
+        source_terms<double>(P, G, gr.C(j, i), gr.c.gam, S);
+        for (int v = 0; v < NVAR; ++v) {
+          double div = 0.0;
+          for (int d = 0; d < g.ndim; ++d) {
+            int o1 = d == 0, o2 = d == 1, o3 = d == 2;
+            div += (fx.F[d][gr.idx(v, k + o3, j + o2, i + o1)] - fx.F[d][gr.idx(v, k, j, i)]) / dx[d];
+          }
+          U[v] = U0[gr.idx(v, k, j, i)] + cdt * (-div + S[v]);
+        }
+        // guess = stage input
+        int flag = cons_to_prim_point(U, G, gr.c.gam, P);
+        size_t c = gr.idx(0, k, j, i);
+        pflag[c] = flag;
+        if (flag == 0) {
+          fflag[c] = apply_floors(gr.c, G, radius_at(gr, j, i), P);
+          if (fflag[c]) p2c_point(gr.c, G, P, U);
+        } else {
+          for (int v = 0; v < 5; ++v) P[v] = Pin[gr.idx(v, k, j, i)];  // provisional, replaced by fixup
+        }
+        for (int v = 0; v < NVAR; ++v) {
+          Pout[gr.idx(v, k, j, i)] = P[v];
+          Uout[gr.idx(v, k, j, i)] = U[v];
+        }
+      }
+  // Fixup: each failed zone takes the equal-weight mean of its non-failed
+  // neighbours in the 3x3(x3) block, interior zones only; then floors; then U
+  // is recomputed from the repaired primitives.
+  std::vector<double> fixed;
+  std::vector<size_t> where;
+  for (int k = gr.s3(); k < gr.e3(); ++k)
+    for (int j = gr.s2(); j < gr.e2(); ++j)
+      for (int i = gr.s1(); i < gr.e1(); ++i) {
+        size_t c = gr.idx(0, k, j, i);
+        if (pflag[c] == 0) continue;
+        st.nfail++;
+        double sum[5] = {0, 0, 0, 0, 0};
+        int cnt = 0;
+        int kl = g.ndim == 3 ? -1 : 0, kh = g.ndim == 3 ? 1 : 0;
+        for (int dk = kl; dk <= kh; ++dk)
+          for (int dj = -1; dj <= 1; ++dj)
+            for (int di = -1; di <= 1; ++di) {
+              if (!dk && !dj && !di) continue;
+              int kk = k + dk, jj = j + dj, ii = i + di;
+              if (kk < gr.s3() || kk >= gr.e3() || jj < gr.s2() || jj >= gr.e2() || ii < gr.s1() || ii >= gr.e1())
+                continue;
+              if (pflag[gr.idx(0, kk, jj, ii)] != 0) continue;
+              for (int v = 0; v < 5; ++v) sum[v] += Pout[gr.idx(v, kk, jj, ii)];
+              ++cnt;
+            }
+        double P[NVAR];
+        for (int v = 0; v < NVAR; ++v) P[v] = Pout[gr.idx(v, k, j, i)];
+        if (cnt > 0)
+          for (int v = 0; v < 5; ++v) P[v] = sum[v] / cnt;
+        else
+          st.nunfixed++;
+        const Geo& G = gr.G(LOC_CENT, j, i);
+        fflag[c] = apply_floors(gr.c, G, radius_at(gr, j, i), P);
+        double U[NVAR];
+        p2c_point(gr.c, G, P, U);
+        for (int v = 0; v < NVAR; ++v) {
+          fixed.push_back(P[v]);
+          fixed.push_back(U[v]);
+        }
+        where.push_back(c);
+      }
+  for (size_t w = 0; w < where.size(); ++w) {
+    size_t c = where[w];
+    for (int v = 0; v < NVAR; ++v) {
+      Pout[c + static_cast<size_t>(v) * gr.cells()] = fixed[w * 16 + 2 * v];
+      Uout[c + static_cast<size_t>(v) * gr.cells()] = fixed[w * 16 + 2 * v + 1];
+    }
+  }
+  for (size_t c = 0; c < gr.cells(); ++c)
+    if (fflag[c]) st.nfloor++;
+  if (pflag_out) *pflag_out = pflag;
+}
+
+// CFL time step from the stage fluxes' signal speeds:
+// dt = cfl * min_zones 1 / sum_d (ctop_d / dx_d), ctop_d = max over the zone's two x^d faces.
+double cfl_dt(const Grid& gr, const Fluxes& fx) {
+  const GridInfo& g = gr.g;
+  const double dx[3] = {g.dx1, g.dx2, g.dx3};
+  double best = std::numeric_limits<double>::infinity();
+  for (int k = gr.s3(); k < gr.e3(); ++k)
+    for (int j = gr.s2(); j < gr.e2(); ++j)
+      for (int i = gr.s1(); i < gr.e1(); ++i) {
+        double inv = 0.0;
+        for (int d = 0; d < g.ndim; ++d) {
+          int o1 = d == 0, o2 = d == 1, o3 = d == 2;
+          double c = std::max(fx.ctop[d][gr.idx(0, k, j, i)], fx.ctop[d][gr.idx(0, k + o3, j + o2, i + o1)]);
+          inv += c / dx[d];
+        }
+        double dtz = gr.c.cfl / inv;
+        if (dtz < best) best = dtz;
+      }
+  return best;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C API
+// ---------------------------------------------------------------------------
+extern "C" {
+
+typedef Params or_params;
+
+void or_set_threads(int n) { omp_set_num_threads(n > 0 ? n : 1); }
+int or_get_threads(void) { return omp_get_max_threads(); }
+
+// Geometry at one location over the (N2, N1) grid: gcov, gcon [N2][N1][4][4],
+// gdet, alpha [N2][N1].
+void or_geometry(const or_params* c, int loc, double* gcov, double* gcon, double* gdet, double* alpha) {
+  Grid gr;
+  build_grid(*c, gr);
+  const GridInfo& g = gr.g;
+  for (int j = 0; j < g.N2; ++j)
+    for (int i = 0; i < g.N1; ++i) {
+      const Geo& G = gr.G(loc, j, i);
+      size_t p = static_cast<size_t>(j) * g.N1 + i;
+      for (int m = 0; m < 4; ++m)
+        for (int n = 0; n < 4; ++n) {
+          gcov[p * 16 + m * 4 + n] = G.gcov[m][n];
+          gcon[p * 16 + m * 4 + n] = G.gcon[m][n];
+        }
+      gdet[p] = G.gdet;
+      alpha[p] = G.alpha;
+    }
+}
+
+// Connection Gamma^l_{mn} at cell centres: [N2][N1][4][4][4].
+void or_connection(const or_params* c, double* conn) {
+  Grid gr;
+  build_grid(*c, gr);
+  std::memcpy(conn, gr.conn.data(), gr.conn.size() * sizeof(double));
+}
+
+// Metric and connection at arbitrary native points (n points).
+void or_metric_points(const or_params* c, int n, const double* x1, const double* x2, double* gcov, double* gcon,
+                      double* gdet, double* conn) {
+  for (int p = 0; p < n; ++p) {
+    Geo G = geo_at(*c, x1[p], x2[p]);
+    for (int m = 0; m < 4; ++m)
+      for (int q = 0; q < 4; ++q) {
+        gcov[p * 16 + m * 4 + q] = G.gcov[m][q];
+        gcon[p * 16 + m * 4 + q] = G.gcon[m][q];
+      }
+    gdet[p] = G.gdet;
+    double cn[4][4][4];
+    connection_at(*c, x1[p], x2[p], cn);
+    std::memcpy(conn + static_cast<size_t>(p) * 64, cn, sizeof(cn));
+  }
+}
+
+// Native -> Kerr-Schild (r, theta) at n points.
+void or_native_to_ks(const or_params* c, int n, const double* x1, const double* x2, double* r, double* th) {
+  for (int p = 0; p < n; ++p) native_to_ks<double>(*c, x1[p], x2[p], r[p], th[p]);
+}
+
+// P -> U at every cell (ghosts included), cell-centre metric.
+void or_prim_to_cons(const or_params* c, const double* P, double* U) {
+  Grid gr;
+  build_grid(*c, gr);
+  const GridInfo& g = gr.g;
+#pragma omp parallel for collapse(2)
+  for (int k = 0; k < g.N3; ++k)
+    for (int j = 0; j < g.N2; ++j)
+      for (int i = 0; i < g.N1; ++i) {
+        double p[NVAR], u[NVAR];
+        for (int v = 0; v < NVAR; ++v) p[v] = P[gr.idx(v, k, j, i)];
+        p2c_point(*c, gr.G(LOC_CENT, j, i), p, u);
+        for (int v = 0; v < NVAR; ++v) U[gr.idx(v, k, j, i)] = u[v];
+      }
+}
+
+// U -> P at every cell (ghosts included). P holds the guess on entry. No floors
+// and no fixup. pflag (nullable) receives the C2P_* code per cell; returns the
+// number of failed cells.
+long or_cons_to_prim(const or_params* c, const double* U, double* P, int* pflag) {
+  Grid gr;
+  build_grid(*c, gr);
+  const GridInfo& g = gr.g;
+  long nfail = 0;
+#pragma omp parallel for collapse(2) reduction(+ : nfail)
+  for (int k = 0; k < g.N3; ++k)
+    for (int j = 0; j < g.N2; ++j)
+      for (int i = 0; i < g.N1; ++i) {
+        double p[NVAR], u[NVAR];
+        for (int v = 0; v < NVAR; ++v) {
+          p[v] = P[gr.idx(v, k, j, i)];
+          u[v] = U[gr.idx(v, k, j, i)];
+        }
+        int f = cons_to_prim_point(u, gr.G(LOC_CENT, j, i), c->gam, p);
+        if (f) ++nfail;
+        if (pflag) pflag[gr.idx(0, k, j, i)] = f;
+        if (f == 0)
+          for (int v = 0; v < NVAR; ++v) P[gr.idx(v, k, j, i)] = p[v];
+      }
+  return nfail;
+}
+
+// Boundary fill of P in place. dir_lo/dir_hi: x1 Dirichlet ghosts
+// [8][N3][N2][ng] (nullable unless the matching face is Dirichlet).
+void or_apply_bc(const or_params* c, double* P, const double* dir_lo, const double* dir_hi) {
+  Grid gr;
+  build_grid(*c, gr);
+  apply_bc(gr, P, dir_lo, dir_hi);
+}
+
+// Fluxes (after polar zeroing and Flux-CT) from P with ghosts already filled.
+// F1, F2, F3: cell layout [8][N3][N2][N1]; ctop1..3: [N3][N2][N1]. Entries
+// outside the computed face ranges are zero.
+void or_fluxes(const or_params* c, const double* P, double* F1, double* F2, double* F3, double* ct1, double* ct2,
+               double* ct3) {
+  Grid gr;
+  build_grid(*c, gr);
+  Fluxes fx;
+  compute_fluxes(gr, P, fx);
+  double* Fo[3] = {F1, F2, F3};
+  double* Co[3] = {ct1, ct2, ct3};
+  for (int d = 0; d < 3; ++d) {
+    if (Fo[d]) std::memcpy(Fo[d], fx.F[d].data(), fx.F[d].size() * sizeof(double));
+    if (Co[d]) std::memcpy(Co[d], fx.ctop[d].data(), fx.ctop[d].size() * sizeof(double));
+  }
+}
+
+// CFL dt of a state P (ghosts are filled here on a copy), from LLF signal
+// speeds at every face of the interior zones.
+double or_cfl_dt(const or_params* c, const double* P, const double* dir_lo, const double* dir_hi) {
+  Grid gr;
+  build_grid(*c, gr);
+  std::vector<double> Pc(P, P + gr.cells() * NVAR);
+  apply_bc(gr, Pc.data(), dir_lo, dir_hi);
+  Fluxes fx;
+  compute_fluxes(gr, Pc.data(), fx);
+  return cfl_dt(gr, fx);
+}
+
+// One full two-stage step (conserved-synchronised). U (interior) is advanced in
+// place; P holds P^n on entry (the stage-1 input and inversion guess) and
+// P^{n+1} in the interior on exit. stats[0..2] = failed inversions, floored
+// zones, unfixed zones (summed over both stages). Returns the next CFL dt.
+double or_step(const or_params* c, double* U, double* P, double dt, const double* dir_lo, const double* dir_hi,
+               long* stats) {
+  Grid gr;
+  build_grid(*c, gr);
+  const size_t n = gr.cells() * NVAR;
+  std::vector<double> Pn(P, P + n), U0(U, U + n), Ps(Pn), Us(U0), Pnew, Unew;
+  Fluxes fx;
+  StageStats st;
+  apply_bc(gr, Pn.data(), dir_lo, dir_hi);
+  stage(gr, U0.data(), Pn.data(), 0.5 * dt, Us.data(), Ps.data(), fx, st, nullptr);
+  // ghosts of P* start from those of P^n, then get refilled
+  apply_bc(gr, Ps.data(), dir_lo, dir_hi);
+  Pnew = Ps;
+  Unew = U0;
+  stage(gr, U0.data(), Ps.data(), dt, Unew.data(), Pnew.data(), fx, st, nullptr);
+  double dtn = cfl_dt(gr, fx);
+  const GridInfo& g = gr.g;
+  for (int v = 0; v < NVAR; ++v)
+    for (int k = gr.s3(); k < gr.e3(); ++k)
+      for (int j = gr.s2(); j < gr.e2(); ++j)
+        for (int i = gr.s1(); i < gr.e1(); ++i) {
+          size_t q = gr.idx(v, k, j, i);
+          U[q] = Unew[q];
+          P[q] = Pnew[q];
+        }
+  (void)g;
+  if (stats) {
+    stats[0] = st.nfail;
+    stats[1] = st.nfloor;
+    stats[2] = st.nunfixed;
+  }
+  return dtn;
+}
+
+// Run nsteps steps with a fixed dt (dt > 0) or with the CFL dt of the previous
+// step (dt <= 0: the first step uses -dt, or the CFL dt of P if dt == 0),
+// stopping at time t_end when t_end > 0 (the last step is clipped to land on it).
+// Returns the time advanced. stats as or_step, accumulated.
+double or_evolve(const or_params* c, double* U, double* P, int nsteps, double dt, double t_end, const double* dir_lo,
+                 const double* dir_hi, long* stats) {
+  double t = 0.0;
+  double dtc = dt > 0.0 ? dt : -dt;
+  long acc[3] = {0, 0, 0};
+  for (int s = 0; s < nsteps || (t_end > 0.0 && nsteps <= 0); ++s) {
+    double step_dt = dtc;
+    if (t_end > 0.0) {
+      if (t >= t_end * (1.0 - 1e-14)) break;
+      if (t + step_dt > t_end) step_dt = t_end - t;
+    }
+    long st[3];
+    double next = or_step(c, U, P, step_dt, dir_lo, dir_hi, st);
+    for (int q = 0; q < 3; ++q) acc[q] += st[q];
+    t += step_dt;
+    if (dt <= 0.0) dtc = next;
+  }
+  if (stats)
+    for (int q = 0; q < 3; ++q) stats[q] = acc[q];
+  return t;
+}
+
+// divB of sqrt(-g) B at the corners whose adjacent cells are all interior
+// (Flux-CT's conserved corner divergence). out[0] = max |divB|, out[1] = mean
+// |divB|; optional field div (cell layout [N3][N2][N1], corner (i-1/2,j-1/2,
+// k-1/2) stored at (k,j,i), zero elsewhere).
+void or_divb(const or_params* c, const double* P, double* out, double* div) {
+  Grid gr;
+  build_grid(*c, gr);
+  const GridInfo& g = gr.g;
+  const double dx[3] = {g.dx1, g.dx2, g.dx3};
+  auto gB = [&](int d, int k, int j, int i) { return gr.G(LOC_CENT, j, i).gdet * P[gr.idx(B1 + d, k, j, i)]; };
+  double mx = 0.0, sum = 0.0;
+  long cnt = 0;
+  if (div) std::memset(div, 0, gr.cells() * sizeof(double));
+  int kl = g.ndim == 3 ? gr.s3() + 1 : 0, kh = g.ndim == 3 ? gr.e3() - 1 : 0;
+  for (int k = kl; k <= kh; ++k)
+    for (int j = gr.s2() + 1; j <= gr.e2() - 1; ++j)
+      for (int i = gr.s1() + 1; i <= gr.e1() - 1; ++i) {
+        double dv = 0.0;
+        if (g.ndim == 2) {
+          dv += (gB(0, k, j, i) + gB(0, k, j - 1, i) - gB(0, k, j, i - 1) - gB(0, k, j - 1, i - 1)) / (2.0 * dx[0]);
+          dv += (gB(1, k, j, i) + gB(1, k, j, i - 1) - gB(1, k, j - 1, i) - gB(1, k, j - 1, i - 1)) / (2.0 * dx[1]);
+        } else {
+          double s1p = gB(0, k, j, i) + gB(0, k, j - 1, i) + gB(0, k - 1, j, i) + gB(0, k - 1, j - 1, i);
+          double s1m = gB(0, k, j, i - 1) + gB(0, k, j - 1, i - 1) + gB(0, k - 1, j, i - 1) + gB(0, k - 1, j - 1, i - 1);
+          double s2p = gB(1, k, j, i) + gB(1, k, j, i - 1) + gB(1, k - 1, j, i) + gB(1, k - 1, j, i - 1);
+          double s2m = gB(1, k, j - 1, i) + gB(1, k, j - 1, i - 1) + gB(1, k - 1, j - 1, i) + gB(1, k - 1, j - 1, i - 1);
+          double s3p = gB(2, k, j, i) + gB(2, k, j, i - 1) + gB(2, k, j - 1, i) + gB(2, k, j - 1, i - 1);
+          double s3m = gB(2, k - 1, j, i) + gB(2, k - 1, j, i - 1) + gB(2, k - 1, j - 1, i) + gB(2, k - 1, j - 1, i - 1);
+          dv = (s1p - s1m) / (4.0 * dx[0]) + (s2p - s2m) / (4.0 * dx[1]) + (s3p - s3m) / (4.0 * dx[2]);
+        }
+        if (div) div[gr.idx(0, k, j, i)] = dv;
+        mx = std::max(mx, std::fabs(dv));
+        sum += std::fabs(dv);
+        ++cnt;
+      }
+  out[0] = mx;
+  out[1] = cnt ? sum / cnt : 0.0;
+}
+
+// ---- point-level entry points for the pin tests ----
+
+// Conserved U and the flux F^dir of one state at a given covariant metric.
+void or_point_flux(double gam, const double* gcov16, const double* P, int dir, double* F) {
+  Geo G;
+  for (int m = 0; m < 4; ++m)
+    for (int n = 0; n < 4; ++n) G.gcov[m][n] = gcov16[m * 4 + n];
+  geo_from_gcov(G);
+  FluidState<double> S;
+  fluid_state(P, G, S);
+  prim_to_flux<double>(P, S, G, gam, dir, F);
+}
+
+// u^mu, b^mu, b^2 of one state: out[0..3] ucon, out[4..7] bcon, out[8] bsq.
+void or_point_state(const double* gcov16, const double* P, double* out) {
+  Geo G;
+  for (int m = 0; m < 4; ++m)
+    for (int n = 0; n < 4; ++n) G.gcov[m][n] = gcov16[m * 4 + n];
+  geo_from_gcov(G);
+  FluidState<double> S;
+  fluid_state(P, G, S);
+  for (int m = 0; m < 4; ++m) {
+    out[m] = S.ucon[m];
+    out[4 + m] = S.bcon[m];
+  }
+  out[8] = S.bsq;
+}
+
+void or_point_speeds(double gam, const double* gcov16, const double* P, int dir, double* cmax, double* cmin) {
+  Geo G;
+  for (int m = 0; m < 4; ++m)
+    for (int n = 0; n < 4; ++n) G.gcov[m][n] = gcov16[m * 4 + n];
+  geo_from_gcov(G);
+  FluidState<double> S;
+  fluid_state(P, G, S);
+  signal_speeds<double>(P, S, G, gam, dir, *cmax, *cmin);
+}
+
+void or_point_llf(double gam, const double* gcov16, const double* PL, const double* PR, int dir, double* F,
+                  double* ctop) {
+  Geo G;
+  for (int m = 0; m < 4; ++m)
+    for (int n = 0; n < 4; ++n) G.gcov[m][n] = gcov16[m * 4 + n];
+  geo_from_gcov(G);
+  llf_flux<double>(PL, PR, G, gam, dir, F, *ctop);
+}
+
+// Single-point inversion at a given metric; P: guess in, result out.
+int or_point_c2p(double gam, const double* gcov16, const double* U, double* P) {
+  Geo G;
+  for (int m = 0; m < 4; ++m)
+    for (int n = 0; n < 4; ++n) G.gcov[m][n] = gcov16[m * 4 + n];
+  geo_from_gcov(G);
+  return cons_to_prim_point(U, G, gam, P);
+}
+
+// Jacobians dF^dir/dP and dU/dP (8x8, row = output slot, column = primitive)
+// of one state, by forward-mode differentiation.
+void or_point_jacobians(double gam, const double* gcov16, const double* P, int dir, double* dF, double* dU) {
+  Geo G;
+  for (int m = 0; m < 4; ++m)
+    for (int n = 0; n < 4; ++n) G.gcov[m][n] = gcov16[m * 4 + n];
+  geo_from_gcov(G);
+  for (int col = 0; col < NVAR; ++col) {
+    Dual<double> Pd[NVAR];
+    for (int v = 0; v < NVAR; ++v) Pd[v] = mk<double>(P[v], v == col ? 1.0 : 0.0);
+    FluidState<Dual<double>> S;
+    fluid_state(Pd, G, S);
+    Dual<double> F[NVAR], U[NVAR];
+    prim_to_flux(Pd, S, G, gam, dir, F);
+    prim_to_flux(Pd, S, G, gam, 0, U);
+    for (int r = 0; r < NVAR; ++r) {
+      dF[r * NVAR + col] = F[r].d;
+      dU[r * NVAR + col] = U[r].d;
+    }
+  }
+}
+
+// Source terms of one state at a cell centre of the grid (j, i).
+void or_point_source(const or_params* c, double x1, double x2, const double* P, double* S) {
+  Geo G = geo_at(*c, x1, x2);
+  double cn[4][4][4];
+  connection_at(*c, x1, x2, cn);
+  source_terms<double>(P, G, cn, c->gam, S);
+}
+
+// 1-D reconstruction of q[0..n-1]: lo[i], hi[i] = lower/upper face values of
+// cell i for 2 <= i < n-2 (others untouched).
+void or_recon(int recon, int n, const double* q, double* lo, double* hi) {
+  for (int i = 2; i < n - 2; ++i) recon_cell(recon, q + i - 2, lo[i], hi[i]);
+}
+
+}  // extern "C"

@@ -1,0 +1,512 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests, the oracle's tests
+and the benchmark.
+
+This module computes INITIAL DATA only. It holds none of the finite-volume
+step's arithmetic (no reconstruction, flux, EMF, source, update, inversion or
+floor). To express analytic solutions in the native coordinates it carries its
+own few Kerr-Schild metric components and its own coordinate map, written
+separately from both the CUDA library and the oracle.
+
+Problems (the paper's test and performance workloads; every input is
+synthetic):
+  * linear MHD slow mode in a periodic Minkowski box (regression tests,
+    "Readiness and Testing" section);
+  * Bondi accretion on Schwarzschild in MKS coordinates (same section;
+    Michel's transonic polytrope solution);
+  * Fishbone-Moncrief torus with a single-loop poloidal field on Kerr in funky
+    MKS (the torus workload of the "Performance" section).
+
+Arrays are numpy float64 of shape (8, N3, N2, N1), ghosts included, slot
+order (rho, u, u~1, u~2, u~3, B1, B2, B3).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+NG = 3
+
+# ---------------------------------------------------------------------------
+# Counter-based noise: splitmix64 (Steele, Lea & Flood 2014) of
+# seed XOR global interior zone index, top 53 bits scaled to [0, 1).
+# ---------------------------------------------------------------------------
+_M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+def splitmix64(x: np.ndarray) -> np.ndarray:
+    z = (np.asarray(x, dtype=np.uint64) + np.uint64(0x9E3779B97F4A7C15)) & _M64
+    with np.errstate(over="ignore"):
+        z = ((z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)) & _M64
+        z = ((z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)) & _M64
+    return z ^ (z >> np.uint64(31))
+
+
+def uniform01(seed: int, index: np.ndarray) -> np.ndarray:
+    z = splitmix64(np.uint64(seed) ^ np.asarray(index, dtype=np.uint64))
+    return (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def interior_index(cfg: dict) -> np.ndarray:
+    """Global interior zone index (k n2 + j) n1 + i over the interior, shape (n3, n2, n1)."""
+    n1, n2, n3 = cfg["n1"], cfg["n2"], cfg["n3"]
+    k, j, i = np.meshgrid(np.arange(n3), np.arange(n2), np.arange(n1), indexing="ij")
+    return ((k * n2 + j) * n1 + i).astype(np.uint64)
+
+
+# ---------------------------------------------------------------------------
+# Grid helpers
+# ---------------------------------------------------------------------------
+def shape(cfg: dict):
+    ng = cfg.get("ng", NG)
+    n3 = cfg["n3"]
+    return (8, n3 + 2 * ng if n3 > 1 else 1, cfg["n2"] + 2 * ng, cfg["n1"] + 2 * ng)
+
+
+def interior(cfg: dict):
+    """Slices selecting the interior of a (…, N3, N2, N1) array."""
+    ng = cfg.get("ng", NG)
+    g3 = ng if cfg["n3"] > 1 else 0
+    return (slice(g3, g3 + cfg["n3"]), slice(ng, ng + cfg["n2"]), slice(ng, ng + cfg["n1"]))
+
+
+def centers(cfg: dict, axis: int, face: bool = False) -> np.ndarray:
+    """Native coordinates of cell centres (or lower faces) along an axis, ghosts included."""
+    ng = cfg.get("ng", NG)
+    n = cfg[("n1", "n2", "n3")[axis]]
+    lo, hi = cfg[("x1", "x2", "x3")[axis]]
+    d = (hi - lo) / n
+    g = ng if (axis < 2 or cfg["n3"] > 1) else 0
+    idx = np.arange(n + 2 * g)
+    return lo + (idx - g + (0.0 if face else 0.5)) * d
+
+
+# ---------------------------------------------------------------------------
+# Problem configurations
+# ---------------------------------------------------------------------------
+def linear_mode_cfg(n: int, ndim: int = 3, recon: str = "mc") -> dict:
+    """Slow-mode box: Minkowski, [0,1]^3 periodic, gamma = 4/3, MC, CFL 0.9."""
+    return dict(
+        name=f"linear slow mode {n}^{ndim}", coords="minkowski", n1=n, n2=n, n3=n if ndim == 3 else 1,
+        recon=recon, bc=["periodic"] * 6, a=0.0, gam=4.0 / 3.0,
+        x1=(0.0, 1.0), x2=(0.0, 1.0), x3=(0.0, 1.0), cfl=0.9, floors={},
+    )
+
+
+def bondi_cfg(n1: int = 128, n2: int = 128, recon: str = "mc") -> dict:
+    """Bondi: a = 0, MKS h = 0.3, r in [1.8, 50], gamma = 4/3."""
+    return dict(
+        name=f"bondi mks {n1}x{n2}", coords="mks", n1=n1, n2=n2, n3=1, recon=recon,
+        bc=["outflow", "dirichlet", "polar", "polar", "periodic", "periodic"], a=0.0, gam=4.0 / 3.0,
+        x1=(math.log(1.8), math.log(50.0)), x2=(0.0, 1.0), x3=(0.0, 2.0 * math.pi), hslope=0.3, cfl=0.9,
+        floors=dict(rho_min=1e-6, u_min=1e-8, bsq_rho_max=100.0, bsq_u_max=5000.0, u_rho_max=100.0,
+                    gamma_max=50.0),
+        r_sonic=8.0,
+    )
+
+
+def torus_cfg(n1: int = 192, n2: int = 96, n3: int = 96, a: float = 0.9375, recon: str = "weno5",
+              r_out: float = 1000.0) -> dict:
+    """FM torus: funky MKS, spin a, r_out = 1000, 5.5 zones inside the horizon."""
+    rh = 1.0 + math.sqrt(1.0 - a * a)
+    x1in = (n1 * math.log(rh) - 5.5 * math.log(r_out)) / (n1 - 5.5)
+    return dict(
+        name=f"fm torus fmks {n1}x{n2}x{n3}", coords="fmks", n1=n1, n2=n2, n3=n3, recon=recon,
+        bc=["outflow", "outflow", "polar", "polar", "periodic", "periodic"], a=a, gam=13.0 / 9.0,
+        x1=(x1in, math.log(r_out)), x2=(0.0, 1.0), x3=(0.0, 2.0 * math.pi), hslope=0.3, poly_xt=0.82,
+        poly_alpha=14.0, mks_smooth=0.5, cfl=0.9,
+        floors=dict(rho_min=1e-6, u_min=1e-8, bsq_rho_max=100.0, bsq_u_max=5000.0, u_rho_max=100.0,
+                    gamma_max=50.0),
+        r_in=6.0, r_max=12.0, beta=100.0,
+    )
+
+
+# ---------------------------------------------------------------------------
+# Initial-data geometry (this module's own): native (x1, x2) -> (r, theta),
+# the theta derivatives by complex-step differentiation, and the few
+# Kerr-Schild quantities needed to express a 4-velocity as u~^i.
+# ---------------------------------------------------------------------------
+def _theta(cfg: dict, x1, x2):
+    if cfg["coords"] == "ks":
+        return x2
+    h = cfg.get("hslope", 0.3)
+    thg = np.pi * x2 + 0.5 * (1.0 - h) * np.sin(2.0 * np.pi * x2)
+    if cfg["coords"] == "mks":
+        return thg
+    xt, al, s = cfg["poly_xt"], cfg["poly_alpha"], cfg["mks_smooth"]
+    # continued past the poles by reflection: theta(-x2) = -theta(x2), theta(2 - x2) = 2 pi - theta(x2)
+    x2r = np.real(x2)
+    if np.any(x2r < 0.0) or np.any(x2r > 1.0):
+        lo = x2r < 0.0
+        hi = x2r > 1.0
+        mid = ~(lo | hi)
+        x2m = np.where(lo, -x2, np.where(hi, 2.0 - x2, x2))
+        t = _theta(cfg, x1, x2m)
+        return np.where(mid, t, np.where(lo, -t, 2.0 * np.pi - t))
+    y = 2.0 * x2 - 1.0
+    nrm = 0.5 * np.pi / (1.0 + xt ** (-al) / (al + 1.0))
+    thj = 0.5 * np.pi + nrm * y * (1.0 + (y / xt) ** int(al) / (al + 1.0))
+    return thg + np.exp(s * (cfg["x1"][0] - x1)) * (thj - thg)
+
+
+def embed(cfg: dict, x1, x2):
+    """(r, theta, dtheta/dx1, dtheta/dx2) at native points (MKS family: r = e^x1)."""
+    x1 = np.asarray(x1, dtype=np.float64)
+    x2 = np.asarray(x2, dtype=np.float64)
+    hstep = 1e-30
+    r = np.exp(x1) if cfg["coords"] != "ks" else x1
+    th = _theta(cfg, x1, x2)
+    th1 = np.imag(_theta(cfg, x1 + 1j * hstep, x2)) / hstep
+    th2 = np.imag(_theta(cfg, x1, x2 + 1j * hstep)) / hstep
+    return r, th, th1, th2
+
+
+def _ks_lapse_gtr(a, r, th):
+    sig = r * r + a * a * np.cos(th) ** 2
+    alpha = 1.0 / np.sqrt(1.0 + 2.0 * r / sig)
+    gtr = 2.0 * r / sig  # g^{tr} of Kerr-Schild
+    return alpha, gtr, sig
+
+
+def utilde_from_ks(cfg: dict, x1, x2, ut, ur, uth, uph):
+    """Native u~^i from Kerr-Schild u^mu at native points (MKS family).
+
+    u^i_native = (d x^i / d x^a) u^a and u~^i = u^i + gamma alpha g^{0i}, with
+    gamma = alpha u^t and g^{0i}_native = g^{tr}_KS d x^i / d r (Kerr-Schild has
+    g^{t theta} = g^{t phi} = 0)."""
+    a = cfg.get("a", 0.0)
+    r, th, th1, th2 = embed(cfg, x1, x2)
+    alpha, gtr, _ = _ks_lapse_gtr(a, r, th)
+    dx1_dr = 1.0 / r
+    dx2_dr = -th1 / (th2 * r)
+    dx2_dth = 1.0 / th2
+    u1 = dx1_dr * ur
+    u2 = dx2_dr * ur + dx2_dth * uth
+    u3 = uph
+    gamma = alpha * ut
+    return (u1 + gamma * alpha * gtr * dx1_dr, u2 + gamma * alpha * gtr * dx2_dr, u3)
+
+
+def gdet_native(cfg: dict, x1, x2):
+    """sqrt(-g) of Kerr in native MKS-family coordinates: Sigma |sin theta| r dtheta/dx2."""
+    a = cfg.get("a", 0.0)
+    r, th, th1, th2 = embed(cfg, x1, x2)
+    sig = r * r + a * a * np.cos(th) ** 2
+    return sig * np.abs(np.sin(th)) * r * th2
+
+
+# ---------------------------------------------------------------------------
+# Linear slow mode: P = P0 + amp * dP cos(k.x); the eigenvector (dP, omega) is
+# supplied by the caller (it is derived from the oracle's flux Jacobians and
+# stored as a text fixture).
+# ---------------------------------------------------------------------------
+LINEAR_BACKGROUND = np.array([1.0, 1.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0])
+LINEAR_K = (2.0 * np.pi, 2.0 * np.pi, 0.0)
+
+
+def linear_mode_state(cfg: dict, dP: np.ndarray, omega: float, t: float = 0.0, amp: float = 1e-4) -> np.ndarray:
+    """Analytic mode at time t sampled at cell centres (ghosts included)."""
+    x1 = centers(cfg, 0)
+    x2 = centers(cfg, 1)
+    x3 = centers(cfg, 2)
+    X3, X2, X1 = np.meshgrid(x3, x2, x1, indexing="ij")
+    phase = LINEAR_K[0] * X1 + LINEAR_K[1] * X2 + LINEAR_K[2] * X3 - omega * t
+    P = np.empty(shape(cfg))
+    for v in range(8):
+        P[v] = LINEAR_BACKGROUND[v] + amp * dP[v] * np.cos(phase)
+    return P
+
+
+def load_eigvec(path: str):
+    """(dP[8], omega) from a fixture written by tests/golden/make_linear_mode.py."""
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            key, val = line.split("=")
+            vals[key.strip()] = val.strip()
+    dP = np.array([float(x) for x in vals["dP"].split()])
+    return dP, float(vals["omega"])
+
+
+# ---------------------------------------------------------------------------
+# Bondi accretion (Michel 1972 transonic polytrope, M = 1, a = 0):
+#   p = K rho^Gamma, n = 1/(Gamma-1), T = p/rho;
+#   C1 = r^2 T^n u^r, C2 = (1 + (1+n) T)^2 (1 - 2/r + (u^r)^2);
+#   sonic point r_s: u_s^2 = 1/(2 r_s), V_s^2 = u_s^2 / (1 - 3 u_s^2),
+#   T_s = n V_s^2 / ((1+n)(1 - n V_s^2)); K such that mdot = 4 pi r^2 rho |u^r| = 1.
+# ---------------------------------------------------------------------------
+def bondi_constants(gam: float, r_s: float):
+    n = 1.0 / (gam - 1.0)
+    us = math.sqrt(1.0 / (2.0 * r_s))
+    Vs2 = us * us / (1.0 - 3.0 * us * us)
+    Ts = n * Vs2 / ((1.0 + n) * (1.0 - n * Vs2))
+    C1 = us * r_s * r_s * Ts ** n
+    C2 = (1.0 + (1.0 + n) * Ts) ** 2 * (1.0 - 2.0 / r_s + us * us)
+    K = (4.0 * math.pi * C1) ** (1.0 / n)
+    return n, C1, C2, K, Ts
+
+
+def bondi_T(r: np.ndarray, gam: float, r_s: float) -> np.ndarray:
+    """Temperature T(r) on the accreting branch (subsonic outside r_s, supersonic inside)."""
+    n, C1, C2, K, Ts = bondi_constants(gam, r_s)
+    r = np.asarray(r, dtype=np.float64)
+
+    def F(T):
+        ur = C1 / (r * r * T ** n)
+        return (1.0 + (1.0 + n) * T) ** 2 * (1.0 - 2.0 / r + ur * ur) - C2
+
+    # F is convex-like in log T with one minimum; locate it by golden section on log T.
+    lo = np.full_like(r, math.log(1e-12))
+    hi = np.full_like(r, math.log(1e3))
+    g = (math.sqrt(5.0) - 1.0) / 2.0
+    for _ in range(200):
+        m1 = hi - g * (hi - lo)
+        m2 = lo + g * (hi - lo)
+        f1 = F(np.exp(m1))
+        f2 = F(np.exp(m2))
+        left = f1 < f2
+        hi = np.where(left, m2, hi)
+        lo = np.where(left, lo, m1)
+    tmin = np.exp(0.5 * (lo + hi))
+    # subsonic (larger-T) root outside r_s, supersonic (smaller-T) root inside
+    outside = r >= r_s
+    a_ = np.where(outside, tmin, np.full_like(r, 1e-12))
+    b_ = np.where(outside, np.full_like(r, 1e3), tmin)
+    fa = F(a_)
+    for _ in range(400):
+        m = 0.5 * (a_ + b_)
+        fm = F(m)
+        same = np.sign(fm) == np.sign(fa)
+        a_ = np.where(same, m, a_)
+        fa = np.where(same, fm, fa)
+        b_ = np.where(same, b_, m)
+    return 0.5 * (a_ + b_)
+
+
+def bondi_fluid(r: np.ndarray, gam: float, r_s: float):
+    """(rho, u, u^r, u^t_KS) of the Bondi solution at radii r."""
+    n, C1, C2, K, Ts = bondi_constants(gam, r_s)
+    T = bondi_T(r, gam, r_s)
+    ur = -C1 / (r * r * T ** n)
+    rho = (T / K) ** n
+    uint = n * rho * T
+    X = 1.0 - 2.0 / r + ur * ur
+    # u^t in Kerr-Schild (a = 0), written without the 0/0 at r = 2:
+    ut = (r + ur * ur * (r + 2.0)) / (r * np.sqrt(X) - 2.0 * ur)
+    return rho, uint, ur, ut
+
+
+def bondi_prims(cfg: dict, x1, x2):
+    r, th, _, _ = embed(cfg, x1, x2)
+    rho, uint, ur, ut = bondi_fluid(r, cfg["gam"], cfg["r_sonic"])
+    u1, u2, u3 = utilde_from_ks(cfg, x1, x2, ut, ur, 0.0 * ur, 0.0 * ur)
+    return rho, uint, u1, u2, u3
+
+
+def bondi_state(cfg: dict, seed: int = 1, noise: float = 1e-3):
+    """(P, dirichlet) for the Bondi problem: analytic solution everywhere, the
+    interior's u multiplied by 1 + noise (xi - 1/2), xi = uniform01(seed, zone);
+    dirichlet = (None, ghosts of the outer x1 face [8][N3][N2][ng])."""
+    ng = cfg.get("ng", NG)
+    x1 = centers(cfg, 0)
+    x2 = centers(cfg, 1)
+    X2, X1 = np.meshgrid(x2, x1, indexing="ij")
+    rho, uint, u1, u2, u3 = bondi_prims(cfg, X1, X2)
+    P = np.zeros(shape(cfg))
+    for v, q in enumerate((rho, uint, u1, u2, u3)):
+        P[v] = q[None, :, :]
+    if noise:
+        sl = interior(cfg)
+        xi = uniform01(seed, interior_index(cfg))
+        P[1][sl] = P[1][sl] * (1.0 + noise * (xi - 0.5))
+    hi = np.ascontiguousarray(P[:, :, :, ng + cfg["n1"]:])
+    # the analytic (noise-free) values in the outer ghosts
+    for v, q in enumerate((rho, uint, u1, u2, u3)):
+        hi[v] = q[None, :, ng + cfg["n1"]:]
+    return P, (None, hi)
+
+
+def bondi_analytic(cfg: dict) -> np.ndarray:
+    P, _ = bondi_state(cfg, noise=0.0)
+    return P
+
+
+# ---------------------------------------------------------------------------
+# Fishbone & Moncrief (1976) torus, constant l = u^t u_phi, on Kerr (M = 1).
+# ---------------------------------------------------------------------------
+def _bl_metric_eq(a, r, th):
+    """Boyer-Lindquist g_tt, g_tphi, g_phiphi."""
+    sig = r * r + a * a * np.cos(th) ** 2
+    s2 = np.sin(th) ** 2
+    gtt = -(1.0 - 2.0 * r / sig)
+    gtp = -2.0 * a * r * s2 / sig
+    gpp = s2 * (r * r + a * a + 2.0 * a * a * r * s2 / sig)
+    return gtt, gtp, gpp
+
+
+def fm_angular_momentum(a: float, r_max: float) -> float:
+    """l = u^t u_phi of the prograde circular equatorial orbit at r_max
+    (Omega = 1 / (r^{3/2} + a))."""
+    gtt, gtp, gpp = _bl_metric_eq(a, r_max, 0.5 * math.pi)
+    om = 1.0 / (r_max ** 1.5 + a)
+    ut = 1.0 / math.sqrt(-(gtt + 2.0 * om * gtp + om * om * gpp))
+    uphi_cov = ut * (gtp + om * gpp)
+    return ut * uphi_cov
+
+
+def fm_lnh(a: float, l: float, r, th):
+    """ln h of the FM solution, not yet offset by its value at the inner edge
+    (NaN inside the horizon, where the torus does not exist)."""
+    with np.errstate(invalid="ignore", divide="ignore"):
+        return _fm_lnh(a, l, r, th)
+
+
+def _fm_lnh(a, l, r, th):
+    sth = np.sin(th)
+    cth = np.cos(th)
+    sig = r * r + a * a * cth * cth
+    dl = r * r - 2.0 * r + a * a
+    A = (r * r + a * a) ** 2 - dl * a * a * sth * sth
+    q = np.sqrt(1.0 + 4.0 * l * l * sig * sig * dl / (A * A * sth * sth))
+    return 0.5 * np.log((1.0 + q) / (sig * dl / A)) - 0.5 * q - 2.0 * a * r * l / A
+
+
+def fm_velocity(a: float, l: float, r, th):
+    """(u^t, u^phi) in Boyer-Lindquist with u^r = u^theta = 0 and u^t u_phi = l:
+    with D = g_tphi^2 - g_tt g_phiphi, (u^t)^2 = (g_phiphi + sqrt(g_phiphi^2 + 4 D l^2)) / (2 D)
+    and u^phi = (l/u^t - g_tphi u^t) / g_phiphi."""
+    gtt, gtp, gpp = _bl_metric_eq(a, r, th)
+    D = gtp * gtp - gtt * gpp
+    with np.errstate(invalid="ignore", divide="ignore"):
+        ut = np.sqrt((gpp + np.sqrt(gpp * gpp + 4.0 * D * l * l)) / (2.0 * D))
+        uph = (l / ut - gtp * ut) / gpp
+    return ut, uph
+
+
+def fm_density(cfg: dict, r, th, kappa: float = 1e-3):
+    """(rho, u, inside) of the unnormalised torus (ln h > 0 and r > r_in)."""
+    a, gam = cfg["a"], cfg["gam"]
+    l = fm_angular_momentum(a, cfg["r_max"])
+    lnh = fm_lnh(a, l, r, th) - fm_lnh(a, l, cfg["r_in"], 0.5 * np.pi)
+    inside = (lnh > 0.0) & (r > cfg["r_in"])
+    h = np.exp(np.where(inside, lnh, 0.0))
+    rho = np.where(inside, ((h - 1.0) * (gam - 1.0) / (kappa * gam)) ** (1.0 / (gam - 1.0)), 0.0)
+    uint = kappa * rho ** gam / (gam - 1.0)
+    return rho, uint, inside
+
+
+def torus_state(cfg: dict, seed: int = 2, noise: float = 4e-2, kappa: float = 1e-3, field: bool = True):
+    """FM torus (rho_max = 1) in an atmosphere at the floors, single poloidal
+    loop from A_phi = max(rho/rho_max - 0.2, 0) at corners normalised to
+    beta = max(p_gas) / max(p_mag) (p_mag = g_ij B^i B^j / 2), multiplicative
+    u noise inside the torus. Returns P with ghosts filled by value (the
+    boundary rules refill them)."""
+    a = cfg["a"]
+    fl = cfg["floors"]
+    x1 = centers(cfg, 0)
+    x2 = centers(cfg, 1)
+    X2, X1 = np.meshgrid(x2, x1, indexing="ij")
+    r, th, th1, th2 = embed(cfg, X1, X2)
+    rho, uint, inside = fm_density(cfg, r, th, kappa)
+    ut_bl, uph = fm_velocity(cfg["a"], fm_angular_momentum(a, cfg["r_max"]), r, th)
+    # BL -> KS with u^r = 0: u^t and u^phi are unchanged.
+    u1, u2, u3 = utilde_from_ks(cfg, X1, X2, ut_bl, 0.0 * r, 0.0 * r, uph)
+    rho_max = rho.max()
+    rho = rho / rho_max
+    uint = uint / rho_max
+    rho_atm = np.maximum(fl["rho_min"] * r ** -1.5, 1e-20)
+    u_atm = np.maximum(fl["u_min"] * r ** -2.5, 1e-20)
+    P2 = np.zeros((8,) + r.shape)
+    P2[0] = np.where(inside, rho, rho_atm)
+    P2[1] = np.where(inside, uint, u_atm)
+    P2[2] = np.where(inside, u1, 0.0)
+    P2[3] = np.where(inside, u2, 0.0)
+    P2[4] = np.where(inside, u3, 0.0)
+    P2[0] = np.maximum(P2[0], rho_atm)
+    P2[1] = np.maximum(P2[1], u_atm)
+    if field:
+        # corner vector potential from the analytic density at the corners
+        x1f = centers(cfg, 0, face=True)
+        x2f = centers(cfg, 1, face=True)
+        Y2, Y1 = np.meshgrid(x2f, x1f, indexing="ij")
+        rc, thc, _, _ = embed(cfg, Y1, Y2)
+        rhoc, _, insc = fm_density(cfg, rc, thc, kappa)
+        Aphi = np.maximum(np.where(insc, rhoc / rho_max, 0.0) - 0.2, 0.0)
+        dx1 = x1[1] - x1[0]
+        dx2 = x2[1] - x2[0]
+        gd = gdet_native(cfg, X1, X2)
+        B1 = np.zeros_like(r)
+        B2 = np.zeros_like(r)
+        # cell (j, i) has corners (j, i), (j, i+1), (j+1, i), (j+1, i+1)
+        d2A = (Aphi[1:, :-1] + Aphi[1:, 1:] - Aphi[:-1, :-1] - Aphi[:-1, 1:]) / (2.0 * dx2)
+        d1A = (Aphi[:-1, 1:] + Aphi[1:, 1:] - Aphi[:-1, :-1] - Aphi[1:, :-1]) / (2.0 * dx1)
+        B1[:-1, :-1] = d2A / gd[:-1, :-1]
+        B2[:-1, :-1] = -d1A / gd[:-1, :-1]
+        # native spatial metric for the magnetic-pressure proxy (B^3 = 0)
+        sig = r * r + a * a * np.cos(th) ** 2
+        g_rr = 1.0 + 2.0 * r / sig
+        g11 = r * r * g_rr + th1 * th1 * sig
+        g12 = th1 * th2 * sig
+        g22 = th2 * th2 * sig
+        pmag = 0.5 * (g11 * B1 * B1 + 2.0 * g12 * B1 * B2 + g22 * B2 * B2)
+        pgas = (cfg["gam"] - 1.0) * P2[1]
+        sl = interior(cfg)
+        norm = math.sqrt((pgas[sl[1], sl[2]].max() / pmag[sl[1], sl[2]].max()) / cfg["beta"])
+        P2[5] = B1 * norm
+        P2[6] = B2 * norm
+    P = np.zeros(shape(cfg))
+    P[:] = P2[:, None, :, :]
+    if noise:
+        sl = interior(cfg)
+        xi = uniform01(seed, interior_index(cfg))
+        ins3 = np.broadcast_to(inside[None, sl[1], sl[2]], xi.shape)
+        fac = np.where(ins3, 1.0 + noise * (xi - 0.5), 1.0)
+        P[1][sl] = P[1][sl] * fac
+    return P
+
+
+# ---------------------------------------------------------------------------
+# Random physical states for single-kernel parity (p2c / c2p).
+# ---------------------------------------------------------------------------
+def random_prims(cfg: dict, seed: int, rho_range=(1e-4, 1.0), u_range=(1e-6, 1.0), ut_scale=(1.0, 1.0, 1.0),
+                 b_scale=(1.0, 1.0, 1.0), b_sqrt_rho: bool = True) -> np.ndarray:
+    """Log-uniform rho and u, uniform u~^i in [-s_i, s_i], uniform B^i in
+    [-b_i, b_i] (times sqrt(rho) when b_sqrt_rho, so that b^2/rho stays of
+    order sum b_i^2), every cell (ghosts included) from the counter-based stream."""
+    shp = shape(cfg)
+    n = int(np.prod(shp[1:]))
+    base = np.arange(n, dtype=np.uint64)
+    P = np.zeros(shp)
+
+    def draw(slot):
+        return uniform01(seed * 16 + slot, base).reshape(shp[1:])
+
+    # in curved coordinates scale u~^i and B^i by 1/sqrt(g_ii) so that the
+    # ranges are orthonormal-frame magnitudes
+    if cfg["coords"] != "minkowski":
+        x1 = centers(cfg, 0)
+        x2 = centers(cfg, 1)
+        X2, X1 = np.meshgrid(x2, x1, indexing="ij")
+        a = cfg.get("a", 0.0)
+        r, th, th1, th2 = embed(cfg, X1, X2)
+        sig = r * r + a * a * np.cos(th) ** 2
+        s2 = np.sin(th) ** 2
+        z = 2.0 * r / sig
+        diag = [np.sqrt(r * r * (1.0 + z) + th1 * th1 * sig), np.sqrt(th2 * th2 * sig),
+                np.sqrt(s2 * (sig + a * a * s2 * (1.0 + z)))]
+        diag = [np.broadcast_to(dd[None], shp[1:]) for dd in diag]
+    else:
+        diag = [1.0, 1.0, 1.0]
+    lr = np.log(rho_range)
+    lu = np.log(u_range)
+    P[0] = np.exp(lr[0] + (lr[1] - lr[0]) * draw(0))
+    P[1] = np.exp(lu[0] + (lu[1] - lu[0]) * draw(1))
+    for q in range(3):
+        P[2 + q] = ut_scale[q] * (2.0 * draw(2 + q) - 1.0) / diag[q]
+        P[5 + q] = b_scale[q] * (2.0 * draw(5 + q) - 1.0) / diag[q]
+        if b_sqrt_rho:
+            P[5 + q] *= np.sqrt(P[0])
+    return P

@@ -1,0 +1,102 @@
+"""Pins for the oracle's primitive recovery and reconstruction."""
+import numpy as np
+import pytest
+
+from paper_2408_01361_gb300 import inputs
+
+
+def _rel(a, b, scale):
+    return np.abs(a - b) / scale
+
+
+@pytest.mark.parametrize("which", ["minkowski", "fmks"])
+def test_round_trip(orc, which):
+    """P -> U -> P over seeded physical states (rho in [1e-4,1], u in [1e-6,1],
+    Lorentz factors up to ~10, sigma = b^2/rho up to ~50); the oracle's
+    root must also leave a residual |p2c(P) - U| / |U| at round-off level
+    (< 5e-12 everywhere, < 1e-14 in the median: bisection stops where the
+    energy residual's own rounding noise decides the sign)."""
+    if which == "minkowski":
+        cfg = inputs.linear_mode_cfg(12, ndim=2)
+        P = inputs.random_prims(cfg, seed=7, ut_scale=(6.0, 6.0, 6.0), b_scale=(4.0, 4.0, 4.0))
+    else:
+        cfg = inputs.torus_cfg(12, 12, 1)
+        cfg["x1"] = (np.log(1.2), np.log(50.0))  # keep the ghosts away from the ring singularity
+        P = inputs.random_prims(cfg, seed=8, ut_scale=(6.0, 6.0, 6.0), b_scale=(4.0, 4.0, 4.0))
+    U = orc.prim_to_cons(cfg, P)
+    guess = P * (1 + 0.05 * (inputs.uniform01(99, np.arange(P.size)).reshape(P.shape) - 0.5))
+    Pr, pflag, nfail = orc.cons_to_prim(cfg, U, guess)
+    assert nfail == 0
+    Ur = orc.prim_to_cons(cfg, Pr)
+    res = np.abs(Ur - U).max(axis=0) / np.abs(U).max(axis=0)
+    assert res.max() < 5e-12 and np.median(res) < 1e-14
+    # primitives: relative to the state's own scale (u~ and B relative to |u~|, |B| + 1)
+    assert _rel(Pr[0], P[0], P[0]).max() < 1e-10
+    # u is recovered from w - rho: its error is bounded by eps * (rho gamma^2) / u
+    assert np.median(_rel(Pr[1], P[1], P[1])) < 1e-12
+    assert _rel(Pr[1], P[1], P[1] + P[0]).max() < 1e-9
+    vs = np.abs(P[2:5]).max(axis=0) + 1.0
+    assert (np.abs(Pr[2:5] - P[2:5]) / vs).max() < 1e-9
+    assert np.array_equal(Pr[5:8], U[5:8] / orc.geometry(cfg, 0)[2][None])
+
+
+def test_inversion_failure_codes(orc):
+    eta = np.diag([-1.0, 1.0, 1.0, 1.0])
+    P = np.array([1.0, 1.0, 0.5, 0, 0, 0.3, 0, 0])
+    U = orc.point_flux(4 / 3, eta, P, 0)
+    # momentum larger than energy allows: no solution with v^2 < 1
+    Ubad = U.copy()
+    Ubad[2] = 50.0 * abs(U[1])
+    _, flag = orc.point_c2p(4 / 3, eta, Ubad, P)
+    assert flag != 0
+    _, flag = orc.point_c2p(4 / 3, eta, U, P)
+    assert flag == 0
+
+
+def test_mc_exact_on_linear(orc):
+    q = 0.3 + 1.7 * np.arange(12.0)
+    lo, hi = orc.recon("mc", q)
+    assert np.allclose(lo[2:-2], q[2:-2] - 0.85, rtol=0, atol=1e-14)
+    assert np.allclose(hi[2:-2], q[2:-2] + 0.85, rtol=0, atol=1e-14)
+
+
+def test_mc_tvd_at_step(orc):
+    q = np.where(np.arange(16) < 8, 1.0, 0.1) + 0.01 * np.sin(np.arange(16.0))
+    lo, hi = orc.recon("mc", q)
+    for i in range(2, 14):
+        mn, mx = min(q[i - 1:i + 2]), max(q[i - 1:i + 2])
+        assert mn - 1e-15 <= lo[i] <= mx + 1e-15 and mn - 1e-15 <= hi[i] <= mx + 1e-15
+    # local extremum -> zero slope
+    q2 = np.array([0, 1, 2, 3, 2, 1, 0.0, 1, 2])
+    lo, hi = orc.recon("mc", q2)
+    assert lo[3] == hi[3] == 3.0
+
+
+def test_weno5_exact_on_quadratics(orc):
+    """Every candidate interpolates a quadratic exactly, so any convex weighting
+    returns q(x_face) for point values of a quadratic."""
+    x = np.arange(14.0)
+    q = 0.7 * x ** 2 - 3.1 * x + 2.0
+    lo, hi = orc.recon("weno5", q)
+    f = lambda y: 0.7 * y ** 2 - 3.1 * y + 2.0
+    assert np.abs(hi[2:-2] - f(x[2:-2] + 0.5)).max() < 1e-12
+    assert np.abs(lo[2:-2] - f(x[2:-2] - 0.5)).max() < 1e-12
+
+
+def test_weno5_fifth_order(orc):
+    errs = []
+    for n in (20, 40, 80, 160):
+        h = 1.0 / n
+        x = (np.arange(n + 4) - 2 + 0.5) * h
+        q = np.sin(2 * np.pi * x) + 2.0
+        lo, hi = orc.recon("weno5", q)
+        ex = np.sin(2 * np.pi * (x + 0.5 * h)) + 2.0
+        errs.append(np.abs(hi[2:-2] - ex[2:-2]).max())
+    slopes = np.diff(np.log(errs)) / np.log(0.5)
+    assert slopes[-1] > 4.5, slopes
+
+
+def test_weno5_no_large_overshoot(orc):
+    q = np.where(np.arange(20) < 10, 1.0, 0.0)
+    lo, hi = orc.recon("weno5", q)
+    assert np.nanmax(hi[2:-2]) < 1.0 + 1e-3 and np.nanmin(lo[2:-2]) > -1e-3

@@ -1,0 +1,176 @@
+"""Pins for the oracle's full step: the paper's convergence band for linear
+modes, exact conservation and uniform-state invariance in a periodic box,
+Flux-CT's divB invariance, determinism, and the Bondi steady state."""
+import os
+
+import numpy as np
+import pytest
+
+from conftest import GOLDEN
+from paper_2408_01361_gb300 import inputs
+
+
+@pytest.fixture(scope="module")
+def eig():
+    return inputs.load_eigvec(os.path.join(GOLDEN, "linear_slow_mode.txt"))
+
+
+def _run_mode(orc, eig, n, ndim=2):
+    dP, om = eig
+    cfg = inputs.linear_mode_cfg(n, ndim=ndim)
+    P = inputs.linear_mode_state(cfg, dP, om)
+    U = orc.prim_to_cons(cfg, P)
+    T = 2 * np.pi / om
+    U2, P2, t, st = orc.evolve(cfg, U, P, 0, -orc.cfl_dt(cfg, P), T)
+    assert abs(t - T) < 1e-12 and st == [0, 0, 0]
+    Pex = inputs.linear_mode_state(cfg, dP, om, t=t)
+    sl = inputs.interior(cfg)
+    return np.array([np.abs(P2[v][sl] - Pex[v][sl]).mean() for v in range(8)])
+
+
+@pytest.mark.slow
+def test_linear_mode_convergence_band(orc, eig):
+    """L1 error of each perturbed primitive after one period scales as N^p with
+    p in [-2.1, -1.9] ("Readiness and Testing" section); least-squares slope
+    over N = 32, 64, 128 (2-D: k = (2 pi, 2 pi, 0) has no x3 dependence)."""
+    ns = np.array([32, 64, 128])
+    errs = np.array([_run_mode(orc, eig, n) for n in ns])
+    dP, _ = eig
+    for v in range(8):
+        if abs(dP[v]) < 1e-12:
+            assert errs[:, v].max() < 1e-15
+            continue
+        p = np.polyfit(np.log(ns), np.log(errs[:, v]), 1)[0]
+        assert -2.1 <= p <= -1.9, (v, p, errs[:, v])
+
+
+def test_eigvec_fixture_speed_closed_form(eig):
+    """The stored slow speed solves the rest-frame magnetosonic relation for
+    rho = 1, u = 1, B = (1,0,0), gamma = 4/3, angle 45 degrees."""
+    _, om = eig
+    v2 = (om / (2 * np.pi * np.sqrt(2))) ** 2
+    w, b2, cs2, s2, c2 = 7 / 3, 1.0, 4 / 21, 0.5, 0.5
+    lhs = (v2 * (w + b2 * s2) - cs2 * w - b2 * s2) * (v2 * (w + b2 * c2) - b2 * c2)
+    assert abs(lhs - b2 * b2 * s2 * c2 * (1 - v2) ** 2) < 1e-14
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_uniform_state_invariant(orc, ndim):
+    cfg = inputs.linear_mode_cfg(8, ndim=ndim)
+    P = np.zeros(inputs.shape(cfg))
+    P[:] = np.array([0.8, 0.5, 0.3, -0.2, 0.1, 0.4, 0.7, -0.3])[:, None, None, None]
+    U = orc.prim_to_cons(cfg, P)
+    U2, P2, dtn, st = orc.step(cfg, U, P, 0.01)
+    sl = (slice(None),) + inputs.interior(cfg)
+    assert np.array_equal(U2[sl], U[sl])
+    assert np.abs(P2[sl] - P[sl]).max() < 1e-14
+
+
+def _smooth_field_state(cfg, seed):
+    """Smooth periodic flow plus a field from a periodic vector potential
+    sampled at corners, so the initial corner divB vanishes to round-off."""
+    rng = np.random.default_rng(seed)
+    P = np.zeros(inputs.shape(cfg))
+    x1, x2, x3 = (inputs.centers(cfg, a) for a in range(3))
+    X3, X2, X1 = np.meshgrid(x3, x2, x1, indexing="ij")
+    tp = 2 * np.pi
+    P[0] = 1.0 + 0.3 * np.sin(tp * X1 + 0.4) * np.cos(tp * X2)
+    P[1] = 0.7 + 0.2 * np.cos(tp * X2 + 1.0) * (1 + 0.3 * np.sin(tp * X3))
+    P[2] = 0.3 * np.sin(tp * X2) * np.cos(tp * X3)
+    P[3] = 0.2 * np.cos(tp * X1)
+    P[4] = 0.25 * np.sin(tp * (X1 + X2))
+    f1, f2, f3 = (inputs.centers(cfg, a, face=True) for a in range(3))
+    d = [(cfg[k][1] - cfg[k][0]) / cfg[n] for k, n in (("x1", "n1"), ("x2", "n2"), ("x3", "n3"))]
+    c = rng.uniform(0.02, 0.05, 4)
+    if cfg["n3"] == 1:
+        Y2, Y1 = np.meshgrid(f2, f1, indexing="ij")
+        A = c[0] * np.sin(tp * Y1) * np.sin(tp * Y2) + c[1] * np.cos(tp * (Y1 - Y2))
+        P[5, 0, :-1, :-1] = (A[1:, :-1] + A[1:, 1:] - A[:-1, :-1] - A[:-1, 1:]) / (2 * d[1])
+        P[6, 0, :-1, :-1] = -(A[:-1, 1:] + A[1:, 1:] - A[:-1, :-1] - A[1:, :-1]) / (2 * d[0])
+        P[7] = 0.1
+    else:
+        # B = curl A with A_3 only plus a uniform field: divergence-free at corners
+        Y3, Y2, Y1 = np.meshgrid(f3, f2, f1, indexing="ij")
+        A = c[0] * np.sin(tp * Y1) * np.sin(tp * Y2) + c[1] * np.cos(tp * (Y1 - Y2))
+        # average over the two x3 corners of the cell
+        Ak = 0.5 * (A[1:, :, :] + A[:-1, :, :])
+        P[5, :-1, :-1, :-1] = (Ak[:, 1:, :-1] + Ak[:, 1:, 1:] - Ak[:, :-1, :-1] - Ak[:, :-1, 1:]) / (2 * d[1])
+        P[6, :-1, :-1, :-1] = -(Ak[:, :-1, 1:] + Ak[:, 1:, 1:] - Ak[:, :-1, :-1] - Ak[:, 1:, :-1]) / (2 * d[0])
+        P[5] += 0.1
+        P[7] = 0.1
+    return orc_bc(cfg, P)
+
+
+def orc_bc(cfg, P):
+    import oracle
+    return oracle.apply_bc(cfg, P)
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_conservation_and_divb(orc, ndim):
+    cfg = inputs.linear_mode_cfg(16, ndim=ndim)
+    P = _smooth_field_state(cfg, 4)
+    U = orc.prim_to_cons(cfg, P)
+    sl = (slice(None),) + inputs.interior(cfg)
+    tot0 = U[sl].sum(axis=(1, 2, 3))
+    dmax0, _, div0 = orc.divb(cfg, P, field=True)
+    bscale = np.abs(P[5:8]).max() / (1 / 16)
+    assert dmax0 < 1e-12 * bscale
+    dt = 0.5 * orc.cfl_dt(cfg, P)
+    for _ in range(5):
+        U, P, dtn, st = orc.step(cfg, U, P, dt)
+        assert st == [0, 0, 0]
+    tot = U[sl].sum(axis=(1, 2, 3))
+    scale = np.abs(U[sl]).sum(axis=(1, 2, 3))
+    assert (np.abs(tot - tot0) / scale).max() < 1e-13
+    P = orc.apply_bc(cfg, P)
+    _, _, div = orc.divb(cfg, P, field=True)
+    assert np.abs(div - div0).max() < 1e-12 * bscale
+
+
+def test_determinism(orc):
+    cfg = inputs.linear_mode_cfg(12, ndim=3)
+    P = _smooth_field_state(cfg, 9)
+    U = orc.prim_to_cons(cfg, P)
+    outs = []
+    for threads in (1, 4):
+        orc.set_threads(threads)
+        outs.append(orc.evolve(cfg, U, P, 3, 0.004))
+    orc.set_threads(min(8, os.cpu_count() or 1))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+def test_divb_invariant_in_curved_coords(orc):
+    """Flux-CT in FMKS Kerr with polar and outflow boundaries: corner divB of
+    sqrt(-g) B at interior corners is unchanged to round-off."""
+    cfg = inputs.torus_cfg(32, 24, 1, r_out=40.0)
+    P = inputs.torus_state(cfg, seed=2)
+    P = orc.apply_bc(cfg, P)
+    U = orc.prim_to_cons(cfg, P)
+    _, _, div0 = orc.divb(cfg, P, field=True)
+    gdet = orc.geometry(cfg, 0)[2]
+    scale = np.abs(gdet[None, None] * P[5:7]).max() / ((cfg["x1"][1] - cfg["x1"][0]) / 32)
+    dt = 0.5 * orc.cfl_dt(cfg, P)
+    for _ in range(3):
+        U, P, dtn, st = orc.step(cfg, U, P, dt)
+    P = orc.apply_bc(cfg, P)
+    _, _, div = orc.divb(cfg, P, field=True)
+    assert np.abs(div - div0).max() < 1e-12 * scale
+
+
+def test_bondi_steady_state_converges(orc):
+    """The analytic Bondi flow is a steady state of the scheme up to truncation
+    error: after t = 10 M the L1 deviation of rho from the analytic solution
+    falls by ~4x per doubling (second order)."""
+    errs = []
+    for n in (32, 64):
+        cfg = inputs.bondi_cfg(n, n)
+        P, dirich = inputs.bondi_state(cfg, noise=0.0)
+        Pa = P.copy()
+        U = orc.prim_to_cons(cfg, P)
+        U2, P2, t, st = orc.evolve(cfg, U, P, 0, -orc.cfl_dt(cfg, P, dirich), 10.0, dirichlet=dirich)
+        assert st[0] == 0
+        sl = inputs.interior(cfg)
+        errs.append(np.abs(P2[0][sl] - Pa[0][sl]).mean())
+    ratio = errs[0] / errs[1]
+    assert 3.0 < ratio < 6.0, errs
