@@ -1,0 +1,184 @@
+/*
+ * kharma_gb300.h -- C ABI of the GB300 (sm_103a) implementation of the HARM
+ * finite-volume step for ideal GRMHD on a stationary Kerr spacetime
+ * (arXiv 2408.01361, "KHARMA": "Algorithm" section for the scheme, "Extended
+ * GRMHD" section for the ideal-MHD stress-energy tensor, "Requirements"
+ * section for the funky-MKS coordinates, "Performance" section for the
+ * zone-cycles/s metric).
+ *
+ * Memory: every array argument is a DEVICE pointer owned by the caller,
+ * double precision, structure of arrays [var][n3s][n2s][n1s] with ghost
+ * zones included; (n1s, n2s, n3s, ng) come from kh_shape(). Interior zone
+ * (i, j, k) (0-based) lives at (ng + i, ng + j, ng3 + k) where ng3 = ng for
+ * 3-D problems and 0 when n3 == 1. The row length n1s is n1 + 2 ng rounded
+ * up to a multiple of 16 elements; the padding is never read or written.
+ *   P: 5 fluid primitives rho, u, u~1, u~2, u~3 (u~ = velocity relative to the
+ *      normal observer, McKinney & Gammie 2004);
+ *   B: 3 cell-centred field components B^1..B^3;
+ *   U: 8 conserved variables sqrt(-g) (rho u^t, T^t_t + rho u^t, T^t_i, B^i).
+ * The library owns its geometry cache, scratch fluxes and reductions; it
+ * allocates them in kh_geometry_init and frees them in kh_destroy.
+ *
+ * Streams: all calls are ordered on the context's stream (kh_set_stream;
+ * default stream 0). A context is not thread-safe.
+ *
+ * Errors: 0 on success; negative KH_E* codes on failure (kh_strerror). A
+ * positive return from kh_step / kh_cons_to_prim means "completed, with that
+ * many zones whose inversion failed" (they were repaired by the fixup). No
+ * call traps or asserts on the device; every device loop is bounded.
+ */
+#ifndef KHARMA_GB300_H
+#define KHARMA_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { KH_MINKOWSKI = 0, KH_KS = 1, KH_MKS = 2, KH_FMKS = 3 };
+enum { KH_BC_PERIODIC = 0, KH_BC_OUTFLOW = 1, KH_BC_POLAR = 2, KH_BC_DIRICHLET = 3 };
+enum { KH_RECON_MC = 0, KH_RECON_WENO5 = 1 };
+enum { KH_FP64 = 0, KH_MIXED = 1 };
+enum {
+  KH_OK = 0,
+  KH_EINVAL = -1,   /* bad argument or unsupported combination */
+  KH_ECUDA = -2,    /* a CUDA runtime call failed */
+  KH_ENOMEM = -3,   /* device allocation failed */
+  KH_ETIMEOUT = -4, /* a bounded device wait gave up */
+  KH_ENAN = -5      /* non-finite time step */
+};
+
+/* Problem description (coordinates, grid, boundaries, scheme options). */
+typedef struct {
+  int kind;               /* KH_MINKOWSKI | KH_KS | KH_MKS | KH_FMKS */
+  int n1, n2, n3;         /* interior zones; n3 == 1 => 2-D (x1, x2) problem */
+  int recon;              /* KH_RECON_MC | KH_RECON_WENO5 */
+  int precision;          /* KH_FP64 (KH_MIXED reserved) */
+  int bc[6];              /* x1 in, x1 out, x2 in, x2 out, x3 in, x3 out: KH_BC_* */
+  double x1min, x1max, x2min, x2max, x3min, x3max; /* native coordinate box */
+  double hslope;          /* MKS / FMKS theta concentration h */
+  double poly_xt, poly_alpha, mks_smooth; /* FMKS parameters (alpha: even integer) */
+  double cfl;             /* Courant number of the returned dt */
+  double rho_min, u_min;  /* floor coefficients of r^-3/2 and r^-5/2 (>= 1e-20 each) */
+  double bsq_rho_max, bsq_u_max; /* magnetisation ceilings b^2/rho, b^2/u */
+  double u_rho_max;       /* temperature ceiling u/rho */
+  double gamma_max;       /* Lorentz-factor ceiling */
+  int newton_max_iter;    /* inversion iteration cap (<= 0: 30) */
+  double newton_tol;      /* inversion tolerance on |dW/W| + |dv^2| (<= 0: 1e-14) */
+} kh_coords;
+
+/* Counters of the last kh_step (both stages summed). */
+typedef struct {
+  int64_t nfail;    /* zones whose inversion failed (repaired by the fixup) */
+  int64_t nfloor;   /* zones where a floor or ceiling was applied */
+  int64_t nunfixed; /* failed zones with no good neighbour (kept the stage input) */
+  double dt_cfl;    /* CFL time step for the next step */
+} kh_stats;
+
+typedef struct kh_ctx kh_ctx;
+
+/* Create a context: validates c, allocates the library's device buffers and
+ * fills the FP64 geometry cache (metric, inverse, sqrt(-g), lapse at cell
+ * centres and x1/x2 faces; connection at cell centres) for Kerr spin a and
+ * the ideal-gas adiabatic index gamma ("Code Structure": GRCoordinates).
+ * Geometry: Kerr-Schild (t, r, theta, phi); MKS r = e^x1, theta = pi x2 +
+ * (1-h)/2 sin(2 pi x2); FMKS adds the polynomial theta of Wong et al. 2022
+ * blended by exp(mks_smooth (x1min - x1)); theta is continued past the poles
+ * by reflection. Requires n1, n2 >= 4, n3 >= 1, ng = 3 ghost zones.
+ * Returns KH_EINVAL, KH_ENOMEM or KH_ECUDA on failure (*out untouched). */
+int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out);
+
+/* Allocation shape of every array: [var][*n3s][*n2s][*n1s], *ng ghosts. */
+int kh_shape(const kh_ctx* ctx, int* n1s, int* n2s, int* n3s, int* ng);
+
+/* Order all later calls on this cudaStream_t (NULL = legacy default stream). */
+int kh_set_stream(kh_ctx* ctx, void* cuda_stream);
+
+/* Ghost values for a KH_BC_DIRICHLET face (face 0: x1 inner, 1: x1 outer).
+ * PB: device pointer, [8][n3s][n2s][ng] (P slots then B slots; ghost index
+ * 0 is the ghost nearest the inner face of the array, i.e. cell ng - 3 for
+ * face 0 and cell ng + n1 for face 1). Copied into the context. */
+int kh_set_dirichlet(kh_ctx* ctx, int face, const double* PB);
+
+/* U = sqrt(-g) (rho u^t, T^t_t + rho u^t, T^t_i, B^i) at every cell
+ * (ghosts included), T^mu_nu the ideal-MHD stress-energy tensor. */
+int kh_prim_to_cons(kh_ctx* ctx, const double* P, const double* B, double* U);
+
+/* Primitive recovery at every cell (ghosts included) by the Noble et al.
+ * (2006) two-unknown Newton iteration on (W, v^2), FP64. P holds the initial
+ * guess on entry and the result on exit (unchanged where the inversion
+ * failed); B = U_B / sqrt(-g). No floors, no fixup. pflag (device int8,
+ * nullable): 0 ok, 1 no convergence, 2 v^2 >= 1, 3 W <= 0, 4 rho <= 0,
+ * 5 u < 0. *nfail (host, nullable) = number of failed cells (synchronises). */
+int kh_cons_to_prim(kh_ctx* ctx, const double* U, double* P, double* B, int8_t* pflag, int64_t* nfail);
+
+/* One two-stage predictor-corrector step of length dt ("Algorithm" section;
+ * conserved-synchronised). On entry U is U^n (authoritative) and (P, B) is
+ * the matching P^n (stage-1 input and inversion guess). Stage 1: ghost fill,
+ * fluxes from P^n (reconstruction, LLF, polar zeroing, Flux-CT), sources,
+ * U* = U^n + dt/2 (-div F + S), inversion, floors, fixup -> P*. Stage 2: the
+ * same from P* with dt applied to U^n -> U^{n+1}, P^{n+1}. Interior zones of
+ * U, P, B are overwritten; ghost zones of P, B hold the stage-1 fill.
+ * dt_cfl (host, nullable): if given, the stream is synchronised and the CFL
+ * dt of the new state (from stage-2 signal speeds) is written; otherwise no
+ * host synchronisation happens and the value is kept for kh_get_stats.
+ * Returns the number of failed inversions (>= 0) when dt_cfl is given, 0
+ * otherwise, or a negative KH_E* code. */
+int kh_step(kh_ctx* ctx, double* U, double* P, double* B, double dt, double* dt_cfl);
+
+/* CFL dt of a state (P, B): ghost fill on a scratch copy, fluxes, then
+ * dt = cfl min_zones 1 / sum_d (ctop_d / dx_d). Synchronises. */
+int kh_cfl_dt(kh_ctx* ctx, const double* P, const double* B, double* dt_cfl);
+
+/* Corner divergence of sqrt(-g) B at corners whose adjacent cells are all
+ * interior (the quantity Flux-CT conserves): *max_abs = max |divB|, *l1 =
+ * mean |divB| over those corners (host pointers; synchronises). */
+int kh_divb(kh_ctx* ctx, const double* B, double* max_abs, double* l1);
+
+/* Diagnostics: the fluxes kh_step uses, from (P, B) with ghosts filled by the
+ * caller: F1, F2, F3 (device, [8][n3s][n2s][n1s], the flux through the lower
+ * face of each cell, after polar zeroing and Flux-CT; F3 unused when
+ * n3 == 1). Entries outside the computed face ranges are left untouched. */
+int kh_fluxes(kh_ctx* ctx, const double* P, const double* B, double* F1, double* F2, double* F3);
+
+/* Ghost fill of (P, B) in place with the context's boundary rules. */
+int kh_fill_ghosts(kh_ctx* ctx, double* P, double* B);
+
+/* Counters of the last kh_step (synchronises). */
+int kh_get_stats(kh_ctx* ctx, kh_stats* out);
+
+/* Per-kernel-group timing. Groups: */
+enum {
+  KH_T_BC = 0,     /* ghost fill (3 kernels in 3-D) */
+  KH_T_FLUX1 = 1,  /* reconstruction + LLF through x1 faces */
+  KH_T_FLUX2 = 2,  /* ... x2 faces */
+  KH_T_FLUX3 = 3,  /* ... x3 faces */
+  KH_T_CT = 4,     /* Flux-CT EMFs and field fluxes (2 kernels) */
+  KH_T_UPDATE = 5, /* sources + update + inversion + floors */
+  KH_T_FIXUP = 6,  /* neighbour-average repair of failed zones */
+  KH_T_CFL = 7,    /* CFL reduction (2 kernels) */
+  KH_NTIMERS = 8
+};
+/* enable != 0: record CUDA events on the context stream around each group of
+ * every later kh_step (each step then synchronises its stream) and reset the
+ * accumulators; enable == 0 stops and resets. */
+int kh_profile(kh_ctx* ctx, int enable);
+/* Accumulated milliseconds and timed intervals per group (host arrays of
+ * KH_NTIMERS entries; either may be NULL). One interval per stage. */
+int kh_profile_read(const kh_ctx* ctx, double* ms, int64_t* count);
+
+/* Number of kernel launches issued by this context since creation. */
+int64_t kh_launch_count(const kh_ctx* ctx);
+
+/* Free the context and its device buffers (synchronises its stream). */
+int kh_destroy(kh_ctx* ctx);
+
+/* Static description of an error code. */
+const char* kh_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KHARMA_GB300_H */

@@ -1,0 +1,437 @@
+// C ABI of the library (declared in include/kharma_gb300.h): context,
+// device buffers, the step driver and the diagnostics.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "kh_internal.h"
+
+using namespace kh;
+
+extern "C" int kh_get_stats(kh_ctx* x, kh_stats* out);
+
+struct kh_ctx {
+  kh_coords c;
+  double a, gam;
+  Layout L;
+  Scheme S;
+  CoordParams cp;
+  cudaStream_t stream;
+  double* geo;
+  double* conn;
+  double* rad;
+  double* pstar;   // 8 planes: stage-1 output
+  double* F[3];    // 8 planes each
+  double* ctop[3];
+  double* emf[3];
+  int8_t* pflag;
+  double* partial;
+  int npartial;
+  double* dscalar;              // [0] dt, [1..2] divb max/sum
+  unsigned long long* counters; // NCNT
+  double* dirichlet[2];
+  long long launches;
+  kh_stats last;
+  // optional per-kernel-group timing (CUDA events on the context stream)
+  int profiling;
+  cudaEvent_t ev[KH_NTIMERS][2][2];  // [group][stage][start, stop]
+  int ev_used[KH_NTIMERS][2];
+  double prof_ms[KH_NTIMERS];
+  long long prof_n[KH_NTIMERS];
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e) {
+  if (e == cudaSuccess) return KH_OK;
+  return e == cudaErrorMemoryAllocation ? KH_ENOMEM : KH_ECUDA;
+}
+
+#define KH_TRY(call)                      \
+  do {                                    \
+    int _rc = cuda_fail(call);            \
+    if (_rc != KH_OK) return _rc;         \
+  } while (0)
+
+DevGeom devgeom(const kh_ctx* x) { return DevGeom{x->geo, x->conn, x->rad}; }
+
+Vars vars_of(const kh_ctx* x, double* P, double* B) {
+  Vars v;
+  for (int q = 0; q < 5; ++q) v.v[q] = P + q * x->L.plane;
+  for (int q = 0; q < 3; ++q) v.v[5 + q] = B + q * x->L.plane;
+  return v;
+}
+
+CVars cvars_of(const kh_ctx* x, const double* P, const double* B) {
+  CVars v;
+  for (int q = 0; q < 5; ++q) v.v[q] = P + q * x->L.plane;
+  for (int q = 0; q < 3; ++q) v.v[5 + q] = B + q * x->L.plane;
+  return v;
+}
+
+CVars cview(const Vars& v) {
+  CVars c;
+  for (int q = 0; q < NV; ++q) c.v[q] = v.v[q];
+  return c;
+}
+
+void mark(kh_ctx* x, int group, int stage, int which) {
+  if (!x->profiling) return;
+  cudaEventRecord(x->ev[group][stage][which], x->stream);
+  if (which == 1) x->ev_used[group][stage] = 1;
+}
+
+// Accumulate the recorded intervals (the stream must be synchronised).
+void harvest(kh_ctx* x) {
+  if (!x->profiling) return;
+  for (int g = 0; g < KH_NTIMERS; ++g)
+    for (int st = 0; st < 2; ++st)
+      if (x->ev_used[g][st]) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, x->ev[g][st][0], x->ev[g][st][1]) == cudaSuccess) {
+          x->prof_ms[g] += ms;
+          x->prof_n[g] += 1;
+        }
+        x->ev_used[g][st] = 0;
+      }
+}
+
+int check_launch(kh_ctx* x, int n) {
+  x->launches += n;
+  return cuda_fail(cudaGetLastError());
+}
+
+void free_all(kh_ctx* x) {
+  void* ptrs[] = {x->geo, x->conn, x->rad, x->pstar, x->F[0], x->F[1], x->F[2], x->ctop[0], x->ctop[1],
+                  x->ctop[2], x->emf[0], x->emf[1], x->emf[2], x->pflag, x->partial, x->dscalar,
+                  x->counters, x->dirichlet[0], x->dirichlet[1]};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+// One stage: ghost fill, fluxes per direction, Flux-CT, update, fixup.
+int run_stage(kh_ctx* x, int st, const double* U0, const Vars& Pin, const Vars& Pout, double* Uout, double cdt) {
+  const Layout& L = x->L;
+  const DevGeom G = devgeom(x);
+  cudaStream_t s = x->stream;
+  int n = 0;
+  mark(x, KH_T_BC, st, 0);
+  n += launch_bc(Pin, L, x->S, x->dirichlet[0], x->dirichlet[1], s);
+  mark(x, KH_T_BC, st, 1);
+  for (int d = 1; d <= L.ndim; ++d) {
+    mark(x, KH_T_FLUX1 + d - 1, st, 0);
+    n += launch_flux_dir(d, cview(Pin), L, G, x->S, x->F[d - 1], x->ctop[d - 1], s);
+    mark(x, KH_T_FLUX1 + d - 1, st, 1);
+  }
+  mark(x, KH_T_CT, st, 0);
+  n += launch_ct(x->F, x->emf, L, s);
+  mark(x, KH_T_CT, st, 1);
+  mark(x, KH_T_UPDATE, st, 0);
+  n += launch_update(U0, cview(Pin), Pout, Uout, x->F, L, G, x->S, cdt, x->pflag, x->counters, s);
+  mark(x, KH_T_UPDATE, st, 1);
+  mark(x, KH_T_FIXUP, st, 0);
+  n += launch_fixup(Pout, Uout, x->pflag, L, G, x->S, x->counters, s);
+  mark(x, KH_T_FIXUP, st, 1);
+  return n;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* kh_strerror(int code) {
+  switch (code) {
+    case KH_OK: return "success";
+    case KH_EINVAL: return "invalid argument";
+    case KH_ECUDA: return "CUDA runtime error";
+    case KH_ENOMEM: return "device allocation failed";
+    case KH_ETIMEOUT: return "bounded device wait timed out";
+    case KH_ENAN: return "non-finite time step";
+    default: return code > 0 ? "completed with failed inversions (repaired)" : "unknown error";
+  }
+}
+
+int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
+  if (!c || !out) return KH_EINVAL;
+  if (c->kind < KH_MINKOWSKI || c->kind > KH_FMKS) return KH_EINVAL;
+  if (c->n1 < 4 || c->n2 < 4 || c->n3 < 1) return KH_EINVAL;
+  if (c->recon != KH_RECON_MC && c->recon != KH_RECON_WENO5) return KH_EINVAL;
+  if (c->precision != KH_FP64) return KH_EINVAL;
+  if (!(gamma > 1.0) || !(c->cfl > 0.0) || !(fabs(a) < 1.0)) return KH_EINVAL;
+  if (!(c->x1max > c->x1min) || !(c->x2max > c->x2min) || !(c->x3max > c->x3min)) return KH_EINVAL;
+  for (int q = 0; q < 6; ++q) {
+    const int b = c->bc[q];
+    if (b < KH_BC_PERIODIC || b > KH_BC_DIRICHLET) return KH_EINVAL;
+    if (b == KH_BC_DIRICHLET && q >= 2) return KH_EINVAL;
+    if (b == KH_BC_POLAR && (q < 2 || q >= 4)) return KH_EINVAL;
+  }
+  if (c->kind == KH_FMKS && (c->poly_alpha != floor(c->poly_alpha) || !(c->poly_xt > 0.0))) return KH_EINVAL;
+  if (c->kind == KH_MKS || c->kind == KH_FMKS) {
+    if (c->x2min < -1e-12 || c->x2max > 1.0 + 1e-12) return KH_EINVAL;
+  }
+
+  kh_ctx* x = (kh_ctx*)calloc(1, sizeof(kh_ctx));
+  if (!x) return KH_ENOMEM;
+  x->c = *c;
+  x->a = a;
+  x->gam = gamma;
+  x->stream = 0;
+  Layout& L = x->L;
+  L.n1 = c->n1; L.n2 = c->n2; L.n3 = c->n3;
+  L.ng = NGHOST;
+  L.ndim = c->n3 > 1 ? 3 : 2;
+  L.ng3 = L.ndim == 3 ? NGHOST : 0;
+  L.N1 = L.n1 + 2 * L.ng;
+  L.N2 = L.n2 + 2 * L.ng;
+  L.N3 = L.n3 + 2 * L.ng3;
+  L.n1s = (L.N1 + 15) / 16 * 16;
+  L.n2s = L.N2;
+  L.n3s = L.N3;
+  L.gplane = (long long)L.n1s * L.n2s;
+  L.plane = L.gplane * L.n3s;
+  L.dx[0] = (c->x1max - c->x1min) / c->n1;
+  L.dx[1] = (c->x2max - c->x2min) / c->n2;
+  L.dx[2] = (c->x3max - c->x3min) / c->n3;
+  L.s[0] = L.ng; L.e[0] = L.ng + L.n1;
+  L.s[1] = L.ng; L.e[1] = L.ng + L.n2;
+  L.s[2] = L.ng3; L.e[2] = L.ng3 + L.n3;
+
+  Scheme& S = x->S;
+  S.gam = gamma;
+  S.cfl = c->cfl;
+  S.recon = c->recon;
+  for (int q = 0; q < 6; ++q) S.bc[q] = c->bc[q];
+  S.fl.rho_min = c->rho_min;
+  S.fl.u_min = c->u_min;
+  S.fl.bsq_rho_max = c->bsq_rho_max;
+  S.fl.bsq_u_max = c->bsq_u_max;
+  S.fl.u_rho_max = c->u_rho_max;
+  S.fl.gamma_max = c->gamma_max;
+  S.c2p.max_iter = c->newton_max_iter > 0 ? c->newton_max_iter : 30;
+  S.c2p.tol = c->newton_tol > 0.0 ? c->newton_tol : 1e-14;
+
+  x->cp = CoordParams{c->kind, a, c->x1min, c->hslope, c->poly_xt, c->poly_alpha, c->mks_smooth};
+
+  const size_t pl = (size_t)L.plane * sizeof(double);
+  const size_t gp = (size_t)L.gplane * sizeof(double);
+  x->npartial = reduction_blocks(L);
+  int rc = KH_OK;
+#define KH_ALLOC(ptr, bytes)                                          \
+  if (rc == KH_OK) {                                                  \
+    rc = cuda_fail(cudaMalloc((void**)&(ptr), (bytes)));              \
+  }
+  KH_ALLOC(x->geo, 3 * NGEO * gp);
+  KH_ALLOC(x->conn, NCONN * gp);
+  KH_ALLOC(x->rad, gp);
+  KH_ALLOC(x->pstar, NV * pl);
+  for (int d = 0; d < L.ndim; ++d) {
+    KH_ALLOC(x->F[d], NV * pl);
+    KH_ALLOC(x->ctop[d], pl);
+  }
+  KH_ALLOC(x->emf[2], pl);
+  if (L.ndim == 3) {
+    KH_ALLOC(x->emf[0], pl);
+    KH_ALLOC(x->emf[1], pl);
+  }
+  KH_ALLOC(x->pflag, (size_t)L.plane);
+  KH_ALLOC(x->partial, 2 * (size_t)x->npartial * sizeof(double));
+  KH_ALLOC(x->dscalar, 4 * sizeof(double));
+  KH_ALLOC(x->counters, NCNT * sizeof(unsigned long long));
+  for (int f = 0; f < 2; ++f)
+    if (c->bc[f] == KH_BC_DIRICHLET) KH_ALLOC(x->dirichlet[f], (size_t)NV * L.n3s * L.n2s * L.ng * sizeof(double));
+#undef KH_ALLOC
+  if (rc == KH_OK) {
+    // zero-initialise scratch so that never-written face entries are finite
+    for (int d = 0; d < L.ndim && rc == KH_OK; ++d) {
+      rc = cuda_fail(cudaMemset(x->F[d], 0, NV * pl));
+      if (rc == KH_OK) rc = cuda_fail(cudaMemset(x->ctop[d], 0, pl));
+    }
+    for (int d = 0; d < 3 && rc == KH_OK; ++d)
+      if (x->emf[d]) rc = cuda_fail(cudaMemset(x->emf[d], 0, pl));
+    if (rc == KH_OK) rc = cuda_fail(cudaMemset(x->pstar, 0, NV * pl));
+  }
+  if (rc == KH_OK) {
+    x->launches += launch_geometry(x->cp, c->x2min, L, x->geo, x->conn, x->rad, 0);
+    rc = cuda_fail(cudaGetLastError());
+    if (rc == KH_OK) rc = cuda_fail(cudaDeviceSynchronize());
+  }
+  if (rc != KH_OK) {
+    free_all(x);
+    free(x);
+    return rc;
+  }
+  *out = x;
+  return KH_OK;
+}
+
+int kh_shape(const kh_ctx* x, int* n1s, int* n2s, int* n3s, int* ng) {
+  if (!x) return KH_EINVAL;
+  if (n1s) *n1s = x->L.n1s;
+  if (n2s) *n2s = x->L.n2s;
+  if (n3s) *n3s = x->L.n3s;
+  if (ng) *ng = x->L.ng;
+  return KH_OK;
+}
+
+int kh_set_stream(kh_ctx* x, void* s) {
+  if (!x) return KH_EINVAL;
+  x->stream = (cudaStream_t)s;
+  return KH_OK;
+}
+
+int kh_set_dirichlet(kh_ctx* x, int face, const double* PB) {
+  if (!x || face < 0 || face > 1 || !PB || !x->dirichlet[face]) return KH_EINVAL;
+  const size_t bytes = (size_t)NV * x->L.n3s * x->L.n2s * x->L.ng * sizeof(double);
+  KH_TRY(cudaMemcpyAsync(x->dirichlet[face], PB, bytes, cudaMemcpyDeviceToDevice, x->stream));
+  return KH_OK;
+}
+
+int kh_prim_to_cons(kh_ctx* x, const double* P, const double* B, double* U) {
+  if (!x || !P || !B || !U) return KH_EINVAL;
+  return check_launch(x, launch_p2c(cvars_of(x, P, B), U, x->L, devgeom(x), x->S, x->stream));
+}
+
+int kh_cons_to_prim(kh_ctx* x, const double* U, double* P, double* B, int8_t* pflag, int64_t* nfail) {
+  if (!x || !U || !P || !B) return KH_EINVAL;
+  KH_TRY(cudaMemsetAsync(x->counters, 0, NCNT * sizeof(unsigned long long), x->stream));
+  int rc = check_launch(x, launch_c2p(U, vars_of(x, P, B), pflag, x->L, devgeom(x), x->S, x->counters, x->stream));
+  if (rc != KH_OK) return rc;
+  if (nfail) {
+    unsigned long long h[NCNT];
+    KH_TRY(cudaMemcpyAsync(h, x->counters, sizeof(h), cudaMemcpyDeviceToHost, x->stream));
+    KH_TRY(cudaStreamSynchronize(x->stream));
+    *nfail = (int64_t)h[CNT_FAIL];
+    return (int)(h[CNT_FAIL] > 0x7fffffffULL ? 0x7fffffff : h[CNT_FAIL]);
+  }
+  return KH_OK;
+}
+
+int kh_fill_ghosts(kh_ctx* x, double* P, double* B) {
+  if (!x || !P || !B) return KH_EINVAL;
+  return check_launch(x, launch_bc(vars_of(x, P, B), x->L, x->S, x->dirichlet[0], x->dirichlet[1], x->stream));
+}
+
+int kh_fluxes(kh_ctx* x, const double* P, const double* B, double* F1, double* F2, double* F3) {
+  if (!x || !P || !B || !F1 || !F2 || (x->L.ndim == 3 && !F3)) return KH_EINVAL;
+  double* const F[3] = {F1, F2, x->L.ndim == 3 ? F3 : x->F[2]};
+  return check_launch(x, launch_fluxes(cvars_of(x, P, B), x->L, devgeom(x), x->S, F, x->ctop, x->emf, x->stream));
+}
+
+int kh_step(kh_ctx* x, double* U, double* P, double* B, double dt, double* dt_cfl) {
+  if (!x || !U || !P || !B || !(dt > 0.0) || !isfinite(dt)) return KH_EINVAL;
+  const Layout& L = x->L;
+  cudaStream_t s = x->stream;
+  KH_TRY(cudaMemsetAsync(x->counters, 0, NCNT * sizeof(unsigned long long), s));
+  Vars Pn = vars_of(x, P, B);
+  Vars Ps;
+  for (int q = 0; q < NV; ++q) Ps.v[q] = x->pstar + q * L.plane;
+  int n = 0;
+  // stage 1: P^n -> P* (U* is not stored); stage 2: P* -> P^{n+1}, U^{n+1} in place
+  n += run_stage(x, 0, U, Pn, Ps, nullptr, 0.5 * dt);
+  n += run_stage(x, 1, U, Ps, Pn, U, dt);
+  mark(x, KH_T_CFL, 1, 0);
+  n += launch_cfl(x->ctop, L, x->S.cfl, x->partial, x->npartial, x->dscalar, s);
+  mark(x, KH_T_CFL, 1, 1);
+  int rc = check_launch(x, n);
+  if (rc != KH_OK) return rc;
+  if (!dt_cfl && !x->profiling) return KH_OK;
+  kh_stats st;
+  rc = kh_get_stats(x, &st);
+  if (rc != KH_OK) return rc;
+  harvest(x);
+  if (!dt_cfl) return KH_OK;
+  *dt_cfl = st.dt_cfl;
+  if (!isfinite(st.dt_cfl)) return KH_ENAN;
+  return (int)(st.nfail > 0x7fffffffLL ? 0x7fffffff : st.nfail);
+}
+
+int kh_profile(kh_ctx* x, int enable) {
+  if (!x) return KH_EINVAL;
+  if (enable && !x->profiling) {
+    for (int g = 0; g < KH_NTIMERS; ++g)
+      for (int st = 0; st < 2; ++st)
+        for (int w = 0; w < 2; ++w) KH_TRY(cudaEventCreate(&x->ev[g][st][w]));
+  }
+  if (!enable && x->profiling) {
+    for (int g = 0; g < KH_NTIMERS; ++g)
+      for (int st = 0; st < 2; ++st)
+        for (int w = 0; w < 2; ++w) cudaEventDestroy(x->ev[g][st][w]);
+  }
+  x->profiling = enable ? 1 : 0;
+  for (int g = 0; g < KH_NTIMERS; ++g) {
+    x->prof_ms[g] = 0.0;
+    x->prof_n[g] = 0;
+    x->ev_used[g][0] = x->ev_used[g][1] = 0;
+  }
+  return KH_OK;
+}
+
+int kh_profile_read(const kh_ctx* x, double* ms, int64_t* count) {
+  if (!x) return KH_EINVAL;
+  for (int g = 0; g < KH_NTIMERS; ++g) {
+    if (ms) ms[g] = x->prof_ms[g];
+    if (count) count[g] = x->prof_n[g];
+  }
+  return KH_OK;
+}
+
+int kh_get_stats(kh_ctx* x, kh_stats* out) {
+  if (!x || !out) return KH_EINVAL;
+  unsigned long long h[NCNT];
+  double dt;
+  KH_TRY(cudaMemcpyAsync(h, x->counters, sizeof(h), cudaMemcpyDeviceToHost, x->stream));
+  KH_TRY(cudaMemcpyAsync(&dt, x->dscalar, sizeof(double), cudaMemcpyDeviceToHost, x->stream));
+  KH_TRY(cudaStreamSynchronize(x->stream));
+  out->nfail = (int64_t)h[CNT_FAIL];
+  out->nfloor = (int64_t)h[CNT_FLOOR];
+  out->nunfixed = (int64_t)h[CNT_UNFIXED];
+  out->dt_cfl = dt;
+  x->last = *out;
+  return KH_OK;
+}
+
+int kh_cfl_dt(kh_ctx* x, const double* P, const double* B, double* dt_cfl) {
+  if (!x || !P || !B || !dt_cfl) return KH_EINVAL;
+  const Layout& L = x->L;
+  cudaStream_t s = x->stream;
+  const size_t pl = (size_t)L.plane * sizeof(double);
+  KH_TRY(cudaMemcpyAsync(x->pstar, P, 5 * pl, cudaMemcpyDeviceToDevice, s));
+  KH_TRY(cudaMemcpyAsync(x->pstar + 5 * L.plane, B, 3 * pl, cudaMemcpyDeviceToDevice, s));
+  Vars Ps;
+  for (int q = 0; q < NV; ++q) Ps.v[q] = x->pstar + q * L.plane;
+  int n = launch_bc(Ps, L, x->S, x->dirichlet[0], x->dirichlet[1], s);
+  n += launch_fluxes(cview(Ps), L, devgeom(x), x->S, x->F, x->ctop, x->emf, s);
+  n += launch_cfl(x->ctop, L, x->S.cfl, x->partial, x->npartial, x->dscalar, s);
+  int rc = check_launch(x, n);
+  if (rc != KH_OK) return rc;
+  KH_TRY(cudaMemcpyAsync(dt_cfl, x->dscalar, sizeof(double), cudaMemcpyDeviceToHost, s));
+  KH_TRY(cudaStreamSynchronize(s));
+  return isfinite(*dt_cfl) ? KH_OK : KH_ENAN;
+}
+
+int kh_divb(kh_ctx* x, const double* B, double* max_abs, double* l1) {
+  if (!x || !B) return KH_EINVAL;
+  const Layout& L = x->L;
+  const double* Bp[3] = {B, B + L.plane, B + 2 * L.plane};
+  int rc = check_launch(x, launch_divb(Bp, L, devgeom(x), x->partial, x->npartial, x->dscalar + 1, x->stream));
+  if (rc != KH_OK) return rc;
+  double h[2];
+  KH_TRY(cudaMemcpyAsync(h, x->dscalar + 1, sizeof(h), cudaMemcpyDeviceToHost, x->stream));
+  KH_TRY(cudaStreamSynchronize(x->stream));
+  long long ncorner = (long long)(L.n1 - 1) * (L.n2 - 1) * (L.ndim == 3 ? (L.n3 - 1) : 1);
+  if (max_abs) *max_abs = h[0];
+  if (l1) *l1 = ncorner > 0 ? h[1] / (double)ncorner : 0.0;
+  return KH_OK;
+}
+
+int64_t kh_launch_count(const kh_ctx* x) { return x ? (int64_t)x->launches : 0; }
+
+int kh_destroy(kh_ctx* x) {
+  if (!x) return KH_EINVAL;
+  cudaStreamSynchronize(x->stream);
+  free_all(x);
+  free(x);
+  return KH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,84 @@
+// Internal declarations shared by the CUDA translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kh_physics.cuh"
+#include "kharma_gb300.h"
+
+namespace kh {
+
+constexpr int NGHOST = 3;
+constexpr int NGEO = 22;  // per location: gcov (10 symmetric), gcon (10), gdet, alpha
+constexpr int NCONN = 40; // Gamma^l_{mn}: 4 x 10 symmetric pairs
+enum { LOC_CENT = 0, LOC_F1 = 1, LOC_F2 = 2 };
+
+// Symmetric-pair index of (m, n), m <= n: 00 01 02 03 11 12 13 22 23 33.
+KH_HD int sym_index(int m, int n) {
+  if (m > n) { int t = m; m = n; n = t; }
+  return m == 0 ? n : (m == 1 ? 3 + n : (m == 2 ? 5 + n : 9));
+}
+
+struct Layout {
+  int n1, n2, n3, ng, ng3, ndim;
+  int n1s, n2s, n3s;  // allocation extents
+  int N1, N2, N3;     // ghosted extents (N1 <= n1s)
+  long long plane;    // n1s * n2s * n3s
+  long long gplane;   // n1s * n2s
+  double dx[3];
+  int s[3], e[3];     // interior [s, e) per direction (i, j, k)
+  KH_HD long long at(int k, int j, int i) const { return ((long long)k * n2s + j) * n1s + i; }
+};
+
+struct Vars {
+  double* v[NV];
+};
+struct CVars {
+  const double* v[NV];
+};
+
+struct DevGeom {
+  const double* g;     // [3][NGEO][n2s][n1s]
+  const double* conn;  // [NCONN][n2s][n1s]
+  const double* rad;   // [n2s][n1s], r at cell centres (1 for Minkowski)
+};
+
+struct Scheme {
+  double gam;
+  double cfl;
+  int recon;
+  int bc[6];
+  FloorParams fl;
+  C2POpts c2p;
+};
+
+// Counters kept on the device for one step.
+enum { CNT_FAIL = 0, CNT_FLOOR = 1, CNT_UNFIXED = 2, NCNT = 3 };
+
+// ---- launchers (kh_kernels.cu); all return the number of kernels launched ----
+int launch_geometry(const CoordParams& cp, double x2min, const Layout& L, double* geo, double* conn, double* rad, cudaStream_t s);
+int launch_bc(const Vars& P, const Layout& L, const Scheme& S, const double* dlo, const double* dhi, cudaStream_t s);
+int launch_fluxes(const CVars& P, const Layout& L, const DevGeom& G, const Scheme& S, double* const F[3],
+                  double* const ctop[3], double* const emf[3], cudaStream_t s);
+int launch_flux_dir(int D, const CVars& P, const Layout& L, const DevGeom& G, const Scheme& S, double* F,
+                    double* ctop, cudaStream_t s);
+int launch_ct(double* const F[3], double* const emf[3], const Layout& L, cudaStream_t s);
+int launch_update(const double* U0, const CVars& Pin, const Vars& Pout, double* Uout, double* const F[3],
+                  const Layout& L, const DevGeom& G, const Scheme& S, double cdt, int8_t* pflag,
+                  unsigned long long* cnt, cudaStream_t s);
+int launch_fixup(const Vars& P, double* Uout, const int8_t* pflag, const Layout& L, const DevGeom& G,
+                 const Scheme& S, unsigned long long* cnt, cudaStream_t s);
+int launch_cfl(double* const ctop[3], const Layout& L, double cfl, double* partial, int npartial, double* dt_out,
+               cudaStream_t s);
+int launch_divb(const double* const B[3], const Layout& L, const DevGeom& G, double* partial, int npartial,
+                double* out2, cudaStream_t s);
+int launch_p2c(const CVars& P, double* U, const Layout& L, const DevGeom& G, const Scheme& S, cudaStream_t s);
+int launch_c2p(const double* U, const Vars& P, int8_t* pflag, const Layout& L, const DevGeom& G, const Scheme& S,
+               unsigned long long* cnt, cudaStream_t s);
+
+// Blocks used by the reductions (partial buffers hold 2 doubles per block).
+constexpr int RED_THREADS = 256;
+int reduction_blocks(const Layout& L);
+
+}  // namespace kh

@@ -1,0 +1,680 @@
+// Kernels of the FP64 HARM step on sm_103a (arXiv 2408.01361, "Algorithm"
+// section) and their host launchers:
+//   geometry cache, ghost fill, reconstruction + LLF fluxes, Flux-CT EMFs,
+//   update + sources + Noble-2D inversion + floors, fixup, CFL reduction,
+//   corner divB, and the stand-alone prim->cons / cons->prim kernels.
+//
+// Layout: structure of arrays [var][k][j][i] with padded rows; the thread
+// index runs fastest along i so a warp reads consecutive doubles of a row.
+// Every device loop has a fixed bound; no kernel waits on another.
+#include "kh_internal.h"
+
+namespace kh {
+
+namespace {
+
+constexpr int TPB = 128;
+
+inline int nblocks(long long n, int tpb) { return (int)((n + tpb - 1) / tpb); }
+
+__device__ __forceinline__ Met<double> load_met(const DevGeom& G, long long gplane, int loc, long long p) {
+  const double* b = G.g + (long long)loc * NGEO * gplane + p;
+  Met<double> m;
+  double c[10], u[10];
+#pragma unroll
+  for (int q = 0; q < 10; ++q) {
+    c[q] = __ldg(b + q * gplane);
+    u[q] = __ldg(b + (10 + q) * gplane);
+  }
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu)
+#pragma unroll
+    for (int nu = 0; nu < 4; ++nu) {
+      m.gcov[mu][nu] = c[sym_index(mu, nu)];
+      m.gcon[mu][nu] = u[sym_index(mu, nu)];
+    }
+  m.gdet = __ldg(b + 20 * gplane);
+  m.alpha = __ldg(b + 21 * gplane);
+  return m;
+}
+
+// ---------------------------------------------------------------------------
+// Geometry cache: one thread per (j, i) of the allocation. Metric, inverse,
+// sqrt(-g), lapse at CENT, x1 face and x2 face; connection and r at CENT.
+// ---------------------------------------------------------------------------
+__global__ void k_geometry(CoordParams cp, double x2min, Layout L, double* geo, double* conn, double* rad) {
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= L.gplane) return;
+  const int i = (int)(p % L.n1s), j = (int)(p / L.n1s);
+  const double x1c = cp.x1min + (i - L.ng + 0.5) * L.dx[0];
+  const double x1f = cp.x1min + (i - L.ng) * L.dx[0];
+  const double x2c = x2min + (j - L.ng + 0.5) * L.dx[1];
+  const double x2f = x2min + (j - L.ng) * L.dx[1];
+  for (int loc = 0; loc < 3; ++loc) {
+    const double x1 = (loc == LOC_F1) ? x1f : x1c;
+    const double x2 = (loc == LOC_F2) ? x2f : x2c;
+    double g[4][4], gi[4][4], dg[4][4][4];
+    native_metric(cp, x1, x2, g, loc == LOC_CENT ? dg : nullptr);
+    const double det = inverse4_cofactor(g, gi);
+    double* b = geo + (long long)loc * NGEO * L.gplane + p;
+    for (int m = 0; m < 4; ++m)
+      for (int n = m; n < 4; ++n) {
+        b[sym_index(m, n) * L.gplane] = g[m][n];
+        b[(10 + sym_index(m, n)) * L.gplane] = gi[m][n];
+      }
+    b[20 * L.gplane] = sqrt(fabs(det));
+    b[21 * L.gplane] = 1.0 / sqrt(-gi[0][0]);
+    if (loc == LOC_CENT) {
+      double G[4][4][4];
+      connection_from(gi, dg, G);
+      for (int l = 0; l < 4; ++l)
+        for (int m = 0; m < 4; ++m)
+          for (int n = m; n < 4; ++n) conn[(l * 10 + sym_index(m, n)) * L.gplane + p] = G[l][m][n];
+      rad[p] = (cp.kind == COORD_MINKOWSKI) ? 1.0 : coord_map(cp, x1c, x2c).r;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Ghost fill of the 8 primitive slots. x1 ghosts over interior (j, k); x2
+// ghosts over all i and interior k; x3 ghosts over all (i, j): edges and
+// corners are compositions of the face rules (three launches, in order).
+// ---------------------------------------------------------------------------
+__global__ void k_bc_x1(Vars P, Layout L, Scheme S, const double* dlo, const double* dhi) {
+  const int nj = L.e[1] - L.s[1], nk = L.e[2] - L.s[2];
+  const long long tot = (long long)nj * nk * L.ng * 2;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= tot) return;
+  const int side = (int)(t % 2);
+  const int m = (int)((t / 2) % L.ng);
+  const int j = L.s[1] + (int)((t / (2 * L.ng)) % nj);
+  const int k = L.s[2] + (int)(t / (2LL * L.ng * nj));
+  const int ig = side == 0 ? L.ng - 1 - m : L.ng + L.n1 + m;
+  const int bc = S.bc[side];
+  const long long dst = L.at(k, j, ig);
+  if (bc == KH_BC_DIRICHLET) {
+    const double* D = side == 0 ? dlo : dhi;
+    const int ii = side == 0 ? ig : ig - (L.ng + L.n1);
+    for (int v = 0; v < NV; ++v) P.v[v][dst] = D[(((long long)v * L.n3s + k) * L.n2s + j) * L.ng + ii];
+    return;
+  }
+  int src;
+  if (bc == KH_BC_PERIODIC)
+    src = side == 0 ? ig + L.n1 : ig - L.n1;
+  else if (bc == KH_BC_OUTFLOW)
+    src = side == 0 ? L.ng : L.ng + L.n1 - 1;
+  else  // reflection (not used on x1 faces by the supported problems)
+    src = side == 0 ? 2 * L.ng - 1 - ig : 2 * (L.ng + L.n1) - 1 - ig;
+  const long long s = L.at(k, j, src);
+  for (int v = 0; v < NV; ++v) P.v[v][dst] = P.v[v][s];
+  if (bc == KH_BC_OUTFLOW) {
+    double u1 = P.v[V_U1][dst];
+    if (side == 0 && u1 > 0.0) u1 = 0.0;
+    if (side == 1 && u1 < 0.0) u1 = 0.0;
+    P.v[V_U1][dst] = u1;
+  }
+}
+
+__global__ void k_bc_x2(Vars P, Layout L, Scheme S) {
+  const int nk = L.e[2] - L.s[2];
+  const long long tot = (long long)L.N1 * nk * L.ng * 2;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= tot) return;
+  const int i = (int)(t % L.N1);
+  const int side = (int)((t / L.N1) % 2);
+  const int m = (int)((t / (2LL * L.N1)) % L.ng);
+  const int k = L.s[2] + (int)(t / (2LL * L.N1 * L.ng));
+  const int jg = side == 0 ? L.ng - 1 - m : L.ng + L.n2 + m;
+  const int bc = S.bc[2 + side];
+  int src;
+  if (bc == KH_BC_PERIODIC)
+    src = side == 0 ? jg + L.n2 : jg - L.n2;
+  else if (bc == KH_BC_OUTFLOW)
+    src = side == 0 ? L.ng : L.ng + L.n2 - 1;
+  else
+    src = side == 0 ? 2 * L.ng - 1 - jg : 2 * (L.ng + L.n2) - 1 - jg;
+  const long long s = L.at(k, src, i), d = L.at(k, jg, i);
+  const bool flip = (bc == KH_BC_POLAR);
+  for (int v = 0; v < NV; ++v) {
+    const double x = P.v[v][s];
+    P.v[v][d] = (flip && (v == V_U2 || v == V_B2)) ? -x : x;
+  }
+}
+
+__global__ void k_bc_x3(Vars P, Layout L, Scheme S) {
+  const long long tot = (long long)L.N1 * L.N2 * L.ng3 * 2;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= tot) return;
+  const int i = (int)(t % L.N1);
+  const int j = (int)((t / L.N1) % L.N2);
+  const int side = (int)((t / ((long long)L.N1 * L.N2)) % 2);
+  const int m = (int)(t / (2LL * L.N1 * L.N2));
+  const int kg = side == 0 ? L.ng3 - 1 - m : L.ng3 + L.n3 + m;
+  const int bc = S.bc[4 + side];
+  const int src = (bc == KH_BC_PERIODIC) ? (side == 0 ? kg + L.n3 : kg - L.n3)
+                                          : (side == 0 ? L.ng3 : L.ng3 + L.n3 - 1);
+  const long long s = L.at(src, j, i), d = L.at(kg, j, i);
+  for (int v = 0; v < NV; ++v) P.v[v][d] = P.v[v][s];
+}
+
+// ---------------------------------------------------------------------------
+// Reconstruction + LLF flux through the lower x^D face of cell (k, j, i),
+// over the interior faces plus one transverse row on each side (Flux-CT).
+// ---------------------------------------------------------------------------
+struct FaceBox {
+  int lo[3];
+  int n[3];
+};
+
+template <int D, int RECON>
+__global__ void __launch_bounds__(TPB) k_flux(CVars P, Layout L, DevGeom G, Scheme S, FaceBox box, double* F,
+                                             double* ctop, int polar_lo, int polar_hi) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long tot = (long long)box.n[0] * box.n[1] * box.n[2];
+  if (t >= tot) return;
+  const int i = box.lo[0] + (int)(t % box.n[0]);
+  const int j = box.lo[1] + (int)((t / box.n[0]) % box.n[1]);
+  const int k = box.lo[2] + (int)(t / ((long long)box.n[0] * box.n[1]));
+  const long long c = L.at(k, j, i);
+  const long long st = (D == 1) ? 1 : (D == 2 ? (long long)L.n1s : (long long)L.n1s * L.n2s);
+  double PL[NV], PR[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const double* q = P.v[v] + c;
+    if (RECON == KH_RECON_MC) {
+      const double qm2 = __ldg(q - 2 * st), qm1 = __ldg(q - st), q0 = __ldg(q), qp1 = __ldg(q + st);
+      double lo, hi;
+      recon_mc(qm2, qm1, q0, lo, hi);
+      PL[v] = hi;
+      recon_mc(qm1, q0, qp1, lo, hi);
+      PR[v] = lo;
+    } else {
+      const double qm3 = __ldg(q - 3 * st), qm2 = __ldg(q - 2 * st), qm1 = __ldg(q - st), q0 = __ldg(q);
+      const double qp1 = __ldg(q + st), qp2 = __ldg(q + 2 * st);
+      PL[v] = weno5_plus(qm3, qm2, qm1, q0, qp1);
+      PR[v] = weno5_plus(qp2, qp1, q0, qm1, qm2);
+    }
+  }
+  const Met<double> m = load_met(G, L.gplane, D == 3 ? LOC_CENT : D, (long long)j * L.n1s + i);
+  FState<double> sL, sR;
+  fluid_state(PL, m, sL);
+  fluid_state(PR, m, sR);
+  double FL[NV], UL[NV], FR[NV], UR[NV];
+  flux_cons(PL, sL, m, S.gam, D, FL, UL);
+  flux_cons(PR, sR, m, S.gam, D, FR, UR);
+  double cmaxL, cminL, cmaxR, cminR;
+  signal_speeds(PL, sL, m, S.gam, D, cmaxL, cminL);
+  signal_speeds(PR, sR, m, S.gam, D, cmaxR, cminR);
+  double cm = fmax(0.0, fmax(cmaxL, cmaxR));
+  double cn = fmax(0.0, fmax(-cminL, -cminR));
+  const double ct = fmax(cm, cn);
+  const bool axis = (D == 2) && ((polar_lo && j == L.s[1]) || (polar_hi && j == L.e[1]));
+#pragma unroll
+  for (int v = 0; v < NV; ++v)
+    F[v * L.plane + c] = axis ? 0.0 : 0.5 * (FL[v] + FR[v]) - 0.5 * ct * (UR[v] - UL[v]);
+  ctop[c] = ct;
+}
+
+// Corner EMFs of Flux-CT (Toth 2000) from the LLF field fluxes:
+//   e3(i-1/2, j-1/2) = (F1_B2(j) + F1_B2(j-1) - F2_B1(i) - F2_B1(i-1)) / 4 and
+//   cyclic e1 (x1-edges), e2 (x2-edges) in 3-D.
+__global__ void k_emf(const double* F1, const double* F2, const double* F3, double* e1, double* e2, double* e3,
+                      Layout L) {
+  const int n0 = L.e[0] - L.s[0] + 1, n1 = L.e[1] - L.s[1] + 1, n2 = (L.ndim == 3) ? L.e[2] - L.s[2] + 1 : 1;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)n0 * n1 * n2) return;
+  const int i = L.s[0] + (int)(t % n0);
+  const int j = L.s[1] + (int)((t / n0) % n1);
+  const int k = (L.ndim == 3 ? L.s[2] : 0) + (int)(t / ((long long)n0 * n1));
+  const long long c = L.at(k, j, i);
+  const long long P = L.plane, sj = L.n1s, sk = (long long)L.n1s * L.n2s;
+  const double* F1B2 = F1 + V_B2 * P;
+  const double* F2B1 = F2 + V_B1 * P;
+  if (L.ndim == 2) {
+    e3[c] = 0.25 * (F1B2[c] + F1B2[c - sj] - F2B1[c] - F2B1[c - 1]);
+    return;
+  }
+  if (k < L.e[2]) e3[c] = 0.25 * (F1B2[c] + F1B2[c - sj] - F2B1[c] - F2B1[c - 1]);
+  if (i < L.e[0]) {
+    const double* F2B3 = F2 + V_B3 * P;
+    const double* F3B2 = F3 + V_B2 * P;
+    e1[c] = 0.25 * (F2B3[c] + F2B3[c - sk] - F3B2[c] - F3B2[c - sj]);
+  }
+  if (j < L.e[1]) {
+    const double* F3B1 = F3 + V_B1 * P;
+    const double* F1B3 = F1 + V_B3 * P;
+    e2[c] = 0.25 * (F3B1[c] + F3B1[c - 1] - F1B3[c] - F1B3[c - sk]);
+  }
+}
+
+// Field fluxes from edge EMFs (the other slots keep their LLF values):
+//   F1 = (0, (e3 + e3(j+1))/2, -(e2 + e2(k+1))/2), F2 = (-(e3 + e3(i+1))/2, 0, (e1 + e1(k+1))/2),
+//   F3 = ((e2 + e2(i+1))/2, -(e1 + e1(j+1))/2, 0); in 2-D only e3 and the B1, B2 slots.
+__global__ void k_apply_ct(double* F1, double* F2, double* F3, const double* e1, const double* e2,
+                           const double* e3, Layout L) {
+  const int n0 = L.e[0] - L.s[0] + 1, n1 = L.e[1] - L.s[1] + 1, n2 = (L.ndim == 3) ? L.e[2] - L.s[2] + 1 : 1;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)n0 * n1 * n2) return;
+  const int i = L.s[0] + (int)(t % n0);
+  const int j = L.s[1] + (int)((t / n0) % n1);
+  const int k = (L.ndim == 3 ? L.s[2] : 0) + (int)(t / ((long long)n0 * n1));
+  const long long c = L.at(k, j, i);
+  const long long P = L.plane, sj = L.n1s, sk = (long long)L.n1s * L.n2s;
+  const bool in_i = i < L.e[0], in_j = j < L.e[1];
+  const bool in_k = (L.ndim == 2) || k < L.e[2];
+  if (in_j && in_k) {  // x1 faces
+    F1[V_B1 * P + c] = 0.0;
+    F1[V_B2 * P + c] = 0.5 * (e3[c] + e3[c + sj]);
+    if (L.ndim == 3) F1[V_B3 * P + c] = -0.5 * (e2[c] + e2[c + sk]);
+  }
+  if (in_i && in_k) {  // x2 faces
+    F2[V_B1 * P + c] = -0.5 * (e3[c] + e3[c + 1]);
+    F2[V_B2 * P + c] = 0.0;
+    if (L.ndim == 3) F2[V_B3 * P + c] = 0.5 * (e1[c] + e1[c + sk]);
+  }
+  if (L.ndim == 3 && in_i && in_j) {  // x3 faces
+    F3[V_B1 * P + c] = 0.5 * (e2[c] + e2[c + 1]);
+    F3[V_B2 * P + c] = -0.5 * (e1[c] + e1[c + sj]);
+    F3[V_B3 * P + c] = 0.0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Update of one interior zone: U = U0 + cdt (-div F + S(Pin)), inversion with
+// Pin as the guess, floors; writes Pout, pflag and (stage 2) U.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void zone_ijk(const Layout& L, long long t, int& i, int& j, int& k) {
+  const int n0 = L.e[0] - L.s[0], n1 = L.e[1] - L.s[1];
+  i = L.s[0] + (int)(t % n0);
+  j = L.s[1] + (int)((t / n0) % n1);
+  k = L.s[2] + (int)(t / ((long long)n0 * n1));
+}
+
+__device__ __forceinline__ long long nzones(const Layout& L) {
+  return (long long)(L.e[0] - L.s[0]) * (L.e[1] - L.s[1]) * (L.e[2] - L.s[2]);
+}
+
+__device__ __forceinline__ void source_terms(const double* P, const Met<double>& m, const DevGeom& G,
+                                             long long gplane, long long p, double gam, double* S) {
+  FState<double> s;
+  fluid_state(P, m, s);
+  const double pg = (gam - 1.0) * P[V_U];
+  const double eta = P[V_RHO] + P[V_U] + pg + s.bsq;
+  const double ptot = pg + 0.5 * s.bsq;
+  double T[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) T[a][b] = eta * s.ucon[a] * s.ucov[b] - s.bcon[a] * s.bcov[b] + (a == b ? ptot : 0.0);
+  // S_nu = sqrt(-g) T^k_l Gamma^l_{nu k}
+#pragma unroll
+  for (int nu = 0; nu < 4; ++nu) {
+    double acc = 0.0;
+#pragma unroll
+    for (int l = 0; l < 4; ++l)
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) acc += T[kk][l] * __ldg(G.conn + (l * 10 + sym_index(nu, kk)) * gplane + p);
+    S[V_U + nu] = m.gdet * acc;
+  }
+}
+
+__global__ void __launch_bounds__(TPB) k_update(const double* U0, CVars Pin, Vars Pout, double* Uout,
+                                               const double* F1, const double* F2, const double* F3, Layout L,
+                                               DevGeom G, Scheme S, double cdt, int8_t* pflag,
+                                               unsigned long long* cnt) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= nzones(L)) return;
+  int i, j, k;
+  zone_ijk(L, t, i, j, k);
+  const long long c = L.at(k, j, i);
+  const long long p = (long long)j * L.n1s + i;
+  const long long sj = L.n1s, sk = (long long)L.n1s * L.n2s;
+  const Met<double> m = load_met(G, L.gplane, LOC_CENT, p);
+  double P[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) P[v] = Pin.v[v][c];
+  double Sv[NV] = {0, 0, 0, 0, 0, 0, 0, 0};
+  source_terms(P, m, G, L.gplane, p, S.gam, Sv);
+  double U[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const long long o = v * L.plane + c;
+    double div = (F1[o + 1] - F1[o]) / L.dx[0] + (F2[o + sj] - F2[o]) / L.dx[1];
+    if (L.ndim == 3) div += (F3[o + sk] - F3[o]) / L.dx[2];
+    U[v] = U0[o] + cdt * (-div + Sv[v]);
+  }
+  double Pn[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Pn[v] = P[v];
+  const int flag = noble2d(U, m, S.gam, S.c2p, Pn);
+  const double ig = 1.0 / m.gdet;
+  Pn[V_B1] = U[V_B1] * ig;
+  Pn[V_B2] = U[V_B2] * ig;
+  Pn[V_B3] = U[V_B3] * ig;
+  int fmask = 0;
+  if (flag == 0) {
+    fmask = apply_floors(S.fl, m, __ldg(G.rad + p), Pn);
+    if (fmask && Uout) {
+      FState<double> s;
+      fluid_state(Pn, m, s);
+      cons_only(Pn, s, m, S.gam, U);
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Pout.v[v][c] = Pn[v];
+  if (Uout) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Uout[v * L.plane + c] = U[v];
+  }
+  pflag[c] = (int8_t)flag;
+  if (flag) atomicAdd(cnt + CNT_FAIL, 1ULL);
+  if (fmask) atomicAdd(cnt + CNT_FLOOR, 1ULL);
+}
+
+// Fixup: a zone whose inversion failed takes the equal-weight mean of the
+// fluid primitives of its non-failed interior neighbours (3x3x3, or 3x3 in
+// 2-D); with none it keeps the stage input. Then floors; U recomputed.
+__global__ void __launch_bounds__(TPB) k_fixup(Vars P, double* Uout, const int8_t* pflag, Layout L, DevGeom G,
+                                              Scheme S, unsigned long long* cnt) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= nzones(L)) return;
+  int i, j, k;
+  zone_ijk(L, t, i, j, k);
+  const long long c = L.at(k, j, i);
+  if (pflag[c] == 0) return;
+  double sum[5] = {0, 0, 0, 0, 0};
+  int n = 0;
+  const int kl = L.ndim == 3 ? -1 : 0, kh = L.ndim == 3 ? 1 : 0;
+  for (int dk = kl; dk <= kh; ++dk)
+    for (int dj = -1; dj <= 1; ++dj)
+      for (int di = -1; di <= 1; ++di) {
+        if (dk == 0 && dj == 0 && di == 0) continue;
+        const int ii = i + di, jj = j + dj, kk = k + dk;
+        if (ii < L.s[0] || ii >= L.e[0] || jj < L.s[1] || jj >= L.e[1] || kk < L.s[2] || kk >= L.e[2]) continue;
+        const long long q = L.at(kk, jj, ii);
+        if (pflag[q] != 0) continue;
+        for (int v = 0; v < 5; ++v) sum[v] += P.v[v][q];
+        ++n;
+      }
+  double Pn[NV];
+  for (int v = 0; v < NV; ++v) Pn[v] = P.v[v][c];
+  if (n > 0) {
+    for (int v = 0; v < 5; ++v) Pn[v] = sum[v] / n;
+  } else {
+    atomicAdd(cnt + CNT_UNFIXED, 1ULL);
+  }
+  const long long p = (long long)j * L.n1s + i;
+  const Met<double> m = load_met(G, L.gplane, LOC_CENT, p);
+  const int fmask = apply_floors(S.fl, m, __ldg(G.rad + p), Pn);
+  if (fmask) atomicAdd(cnt + CNT_FLOOR, 1ULL);
+  for (int v = 0; v < 5; ++v) P.v[v][c] = Pn[v];
+  if (Uout) {
+    FState<double> s;
+    fluid_state(Pn, m, s);
+    double U[NV];
+    cons_only(Pn, s, m, S.gam, U);
+    for (int v = 0; v < NV; ++v) Uout[v * L.plane + c] = U[v];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Reductions: warp shuffles, then shared memory, then one block over partials.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_max(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+  return x;
+}
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// Block-wide (max a, sum b) with RED_THREADS threads.
+__device__ __forceinline__ void block_max_sum(double& a, double& b) {
+  __shared__ double sa[RED_THREADS / 32], sb[RED_THREADS / 32];
+  a = warp_max(a);
+  b = warp_sum(b);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) { sa[w] = a; sb[w] = b; }
+  __syncthreads();
+  if (w == 0) {
+    a = (l < RED_THREADS / 32) ? sa[l] : 0.0;
+    b = (l < RED_THREADS / 32) ? sb[l] : 0.0;
+    a = warp_max(a);
+    b = warp_sum(b);
+  }
+}
+
+// CFL: inv = sum_d max(ctop_d(lower face), ctop_d(upper face)) / dx_d per zone;
+// the grid-wide maximum gives dt = cfl / max(inv) = min over zones of cfl / inv.
+__global__ void __launch_bounds__(RED_THREADS) k_cfl(const double* c1, const double* c2, const double* c3,
+                                                    Layout L, double* partial) {
+  const long long nz = nzones(L);
+  const long long sj = L.n1s, sk = (long long)L.n1s * L.n2s;
+  double mx = 0.0, dummy = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nz; t += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    zone_ijk(L, t, i, j, k);
+    const long long c = L.at(k, j, i);
+    double inv = fmax(c1[c], c1[c + 1]) / L.dx[0] + fmax(c2[c], c2[c + sj]) / L.dx[1];
+    if (L.ndim == 3) inv += fmax(c3[c], c3[c + sk]) / L.dx[2];
+    mx = fmax(mx, inv);
+  }
+  block_max_sum(mx, dummy);
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = mx;
+    partial[2 * blockIdx.x + 1] = 0.0;
+  }
+}
+
+__global__ void k_finish(const double* partial, int n, double cfl, int mode, double* out) {
+  double a = 0.0, b = 0.0;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    a = fmax(a, partial[2 * q]);
+    b += partial[2 * q + 1];
+  }
+  block_max_sum(a, b);
+  if (threadIdx.x == 0) {
+    if (mode == 0) {
+      out[0] = cfl / a;
+    } else {
+      out[0] = a;
+      out[1] = b;
+    }
+  }
+}
+
+// Corner divB of sqrt(-g) B at corners whose adjacent cells are all interior.
+__global__ void __launch_bounds__(RED_THREADS) k_divb(const double* B1, const double* B2, const double* B3,
+                                                     Layout L, DevGeom G, double* partial) {
+  const int n0 = L.e[0] - L.s[0] - 1, n1 = L.e[1] - L.s[1] - 1;
+  const int n2 = L.ndim == 3 ? L.e[2] - L.s[2] - 1 : 1;
+  const long long tot = (long long)(n0 > 0 ? n0 : 0) * (n1 > 0 ? n1 : 0) * (n2 > 0 ? n2 : 0);
+  const double* gd = G.g + (long long)LOC_CENT * NGEO * L.gplane + 20 * L.gplane;
+  double mx = 0.0, sm = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const int i = L.s[0] + 1 + (int)(t % n0);
+    const int j = L.s[1] + 1 + (int)((t / n0) % n1);
+    const int k = (L.ndim == 3 ? L.s[2] + 1 : 0) + (int)(t / ((long long)n0 * n1));
+    auto gB = [&](const double* B, int kk, int jj, int ii) { return gd[(long long)jj * L.n1s + ii] * B[L.at(kk, jj, ii)]; };
+    double dv;
+    if (L.ndim == 2) {
+      dv = (gB(B1, k, j, i) + gB(B1, k, j - 1, i) - gB(B1, k, j, i - 1) - gB(B1, k, j - 1, i - 1)) / (2.0 * L.dx[0]) +
+           (gB(B2, k, j, i) + gB(B2, k, j, i - 1) - gB(B2, k, j - 1, i) - gB(B2, k, j - 1, i - 1)) / (2.0 * L.dx[1]);
+    } else {
+      const double a1 = gB(B1, k, j, i) + gB(B1, k, j - 1, i) + gB(B1, k - 1, j, i) + gB(B1, k - 1, j - 1, i);
+      const double b1 = gB(B1, k, j, i - 1) + gB(B1, k, j - 1, i - 1) + gB(B1, k - 1, j, i - 1) + gB(B1, k - 1, j - 1, i - 1);
+      const double a2 = gB(B2, k, j, i) + gB(B2, k, j, i - 1) + gB(B2, k - 1, j, i) + gB(B2, k - 1, j, i - 1);
+      const double b2 = gB(B2, k, j - 1, i) + gB(B2, k, j - 1, i - 1) + gB(B2, k - 1, j - 1, i) + gB(B2, k - 1, j - 1, i - 1);
+      const double a3 = gB(B3, k, j, i) + gB(B3, k, j, i - 1) + gB(B3, k, j - 1, i) + gB(B3, k, j - 1, i - 1);
+      const double b3 = gB(B3, k - 1, j, i) + gB(B3, k - 1, j, i - 1) + gB(B3, k - 1, j - 1, i) + gB(B3, k - 1, j - 1, i - 1);
+      dv = (a1 - b1) / (4.0 * L.dx[0]) + (a2 - b2) / (4.0 * L.dx[1]) + (a3 - b3) / (4.0 * L.dx[2]);
+    }
+    mx = fmax(mx, fabs(dv));
+    sm += fabs(dv);
+  }
+  block_max_sum(mx, sm);
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = mx;
+    partial[2 * blockIdx.x + 1] = sm;
+  }
+}
+
+// Stand-alone P -> U and U -> P over every cell of the allocation's ghosted box.
+__global__ void __launch_bounds__(TPB) k_p2c(CVars P, double* U, Layout L, DevGeom G, Scheme S) {
+  const long long tot = (long long)L.N1 * L.N2 * L.N3;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= tot) return;
+  const int i = (int)(t % L.N1), j = (int)((t / L.N1) % L.N2), k = (int)(t / ((long long)L.N1 * L.N2));
+  const long long c = L.at(k, j, i);
+  const Met<double> m = load_met(G, L.gplane, LOC_CENT, (long long)j * L.n1s + i);
+  double p[NV], u[NV];
+  for (int v = 0; v < NV; ++v) p[v] = P.v[v][c];
+  FState<double> s;
+  fluid_state(p, m, s);
+  cons_only(p, s, m, S.gam, u);
+  for (int v = 0; v < NV; ++v) U[v * L.plane + c] = u[v];
+}
+
+__global__ void __launch_bounds__(TPB) k_c2p(const double* U, Vars P, int8_t* pflag, Layout L, DevGeom G, Scheme S,
+                                            unsigned long long* cnt) {
+  const long long tot = (long long)L.N1 * L.N2 * L.N3;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= tot) return;
+  const int i = (int)(t % L.N1), j = (int)((t / L.N1) % L.N2), k = (int)(t / ((long long)L.N1 * L.N2));
+  const long long c = L.at(k, j, i);
+  const Met<double> m = load_met(G, L.gplane, LOC_CENT, (long long)j * L.n1s + i);
+  double u[NV], p[NV];
+  for (int v = 0; v < NV; ++v) {
+    u[v] = U[v * L.plane + c];
+    p[v] = P.v[v][c];
+  }
+  const int flag = noble2d(u, m, S.gam, S.c2p, p);
+  const double ig = 1.0 / m.gdet;
+  p[V_B1] = u[V_B1] * ig;
+  p[V_B2] = u[V_B2] * ig;
+  p[V_B3] = u[V_B3] * ig;
+  for (int v = 0; v < NV; ++v) P.v[v][c] = p[v];
+  if (pflag) pflag[c] = (int8_t)flag;
+  if (flag) atomicAdd(cnt + CNT_FAIL, 1ULL);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+int reduction_blocks(const Layout& L) {
+  long long nz = (long long)L.n1 * L.n2 * L.n3;
+  long long b = (nz + RED_THREADS - 1) / RED_THREADS;
+  if (b > 152 * 8) b = 152 * 8;
+  return b < 1 ? 1 : (int)b;
+}
+
+int launch_geometry(const CoordParams& cp, double x2min, const Layout& L, double* geo, double* conn, double* rad,
+                     cudaStream_t s) {
+  k_geometry<<<nblocks(L.gplane, TPB), TPB, 0, s>>>(cp, x2min, L, geo, conn, rad);
+  return 1;
+}
+
+int launch_bc(const Vars& P, const Layout& L, const Scheme& S, const double* dlo, const double* dhi, cudaStream_t s) {
+  int n = 0;
+  long long t1 = (long long)(L.e[1] - L.s[1]) * (L.e[2] - L.s[2]) * L.ng * 2;
+  k_bc_x1<<<nblocks(t1, TPB), TPB, 0, s>>>(P, L, S, dlo, dhi);
+  ++n;
+  long long t2 = (long long)L.N1 * (L.e[2] - L.s[2]) * L.ng * 2;
+  k_bc_x2<<<nblocks(t2, TPB), TPB, 0, s>>>(P, L, S);
+  ++n;
+  if (L.ndim == 3) {
+    long long t3 = (long long)L.N1 * L.N2 * L.ng3 * 2;
+    k_bc_x3<<<nblocks(t3, TPB), TPB, 0, s>>>(P, L, S);
+    ++n;
+  }
+  return n;
+}
+
+template <int D>
+static int launch_flux_d(const CVars& P, const Layout& L, const DevGeom& G, const Scheme& S, double* F, double* ctop,
+                         cudaStream_t s) {
+  FaceBox b;
+  for (int a = 0; a < 3; ++a) {
+    const bool active = a < 2 || L.ndim == 3;
+    if (!active) { b.lo[a] = 0; b.n[a] = 1; continue; }
+    if (a == D - 1) { b.lo[a] = L.s[a]; b.n[a] = L.e[a] - L.s[a] + 1; }
+    else { b.lo[a] = L.s[a] - 1; b.n[a] = L.e[a] - L.s[a] + 2; }
+  }
+  const long long tot = (long long)b.n[0] * b.n[1] * b.n[2];
+  const int plo = S.bc[2] == KH_BC_POLAR, phi = S.bc[3] == KH_BC_POLAR;
+  if (S.recon == KH_RECON_MC)
+    k_flux<D, KH_RECON_MC><<<nblocks(tot, TPB), TPB, 0, s>>>(P, L, G, S, b, F, ctop, plo, phi);
+  else
+    k_flux<D, KH_RECON_WENO5><<<nblocks(tot, TPB), TPB, 0, s>>>(P, L, G, S, b, F, ctop, plo, phi);
+  return 1;
+}
+
+int launch_flux_dir(int D, const CVars& P, const Layout& L, const DevGeom& G, const Scheme& S, double* F,
+                    double* ctop, cudaStream_t s) {
+  if (D == 1) return launch_flux_d<1>(P, L, G, S, F, ctop, s);
+  if (D == 2) return launch_flux_d<2>(P, L, G, S, F, ctop, s);
+  return launch_flux_d<3>(P, L, G, S, F, ctop, s);
+}
+
+int launch_ct(double* const F[3], double* const emf[3], const Layout& L, cudaStream_t s) {
+  const long long tot = (long long)(L.e[0] - L.s[0] + 1) * (L.e[1] - L.s[1] + 1) * (L.ndim == 3 ? L.e[2] - L.s[2] + 1 : 1);
+  k_emf<<<nblocks(tot, TPB), TPB, 0, s>>>(F[0], F[1], F[2], emf[0], emf[1], emf[2], L);
+  k_apply_ct<<<nblocks(tot, TPB), TPB, 0, s>>>(F[0], F[1], F[2], emf[0], emf[1], emf[2], L);
+  return 2;
+}
+
+int launch_fluxes(const CVars& P, const Layout& L, const DevGeom& G, const Scheme& S, double* const F[3],
+                  double* const ctop[3], double* const emf[3], cudaStream_t s) {
+  int n = 0;
+  for (int d = 1; d <= L.ndim; ++d) n += launch_flux_dir(d, P, L, G, S, F[d - 1], ctop[d - 1], s);
+  return n + launch_ct(F, emf, L, s);
+}
+
+int launch_update(const double* U0, const CVars& Pin, const Vars& Pout, double* Uout, double* const F[3],
+                  const Layout& L, const DevGeom& G, const Scheme& S, double cdt, int8_t* pflag,
+                  unsigned long long* cnt, cudaStream_t s) {
+  const long long nz = (long long)L.n1 * L.n2 * L.n3;
+  k_update<<<nblocks(nz, TPB), TPB, 0, s>>>(U0, Pin, Pout, Uout, F[0], F[1], F[2], L, G, S, cdt, pflag, cnt);
+  return 1;
+}
+
+int launch_fixup(const Vars& P, double* Uout, const int8_t* pflag, const Layout& L, const DevGeom& G,
+                 const Scheme& S, unsigned long long* cnt, cudaStream_t s) {
+  const long long nz = (long long)L.n1 * L.n2 * L.n3;
+  k_fixup<<<nblocks(nz, TPB), TPB, 0, s>>>(P, Uout, pflag, L, G, S, cnt);
+  return 1;
+}
+
+int launch_cfl(double* const ctop[3], const Layout& L, double cfl, double* partial, int npartial, double* dt_out,
+               cudaStream_t s) {
+  k_cfl<<<npartial, RED_THREADS, 0, s>>>(ctop[0], ctop[1], ctop[2], L, partial);
+  k_finish<<<1, RED_THREADS, 0, s>>>(partial, npartial, cfl, 0, dt_out);
+  return 2;
+}
+
+int launch_divb(const double* const B[3], const Layout& L, const DevGeom& G, double* partial, int npartial,
+                double* out2, cudaStream_t s) {
+  k_divb<<<npartial, RED_THREADS, 0, s>>>(B[0], B[1], B[2], L, G, partial);
+  k_finish<<<1, RED_THREADS, 0, s>>>(partial, npartial, 0.0, 1, out2);
+  return 2;
+}
+
+int launch_p2c(const CVars& P, double* U, const Layout& L, const DevGeom& G, const Scheme& S, cudaStream_t s) {
+  const long long tot = (long long)L.N1 * L.N2 * L.N3;
+  k_p2c<<<nblocks(tot, TPB), TPB, 0, s>>>(P, U, L, G, S);
+  return 1;
+}
+
+int launch_c2p(const double* U, const Vars& P, int8_t* pflag, const Layout& L, const DevGeom& G, const Scheme& S,
+               unsigned long long* cnt, cudaStream_t s) {
+  const long long tot = (long long)L.N1 * L.N2 * L.N3;
+  k_c2p<<<nblocks(tot, TPB), TPB, 0, s>>>(U, P, pflag, L, G, S, cnt);
+  return 1;
+}
+
+}  // namespace kh

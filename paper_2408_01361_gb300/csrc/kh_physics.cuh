@@ -1,0 +1,317 @@
+// Per-point physics of the CUDA path (host+device), templated on the
+// arithmetic type R so the same formulas serve the FP64 path.
+//
+// arXiv 2408.01361: the ideal-MHD stress-energy tensor
+// T^{mu nu} = (rho + u + P + b^2) u^mu u^nu + (P + b^2/2) g^{mu nu} - b^mu b^nu
+// ("Extended GRMHD" section); HARM's conserved variables, fluxes, signal
+// speeds and the LLF flux ("Algorithm" section, Gammie et al. 2003); the
+// normal-observer primitive velocity (McKinney & Gammie 2004); the Noble et
+// al. (2006) two-unknown (W, v^2) Newton inversion; MC (van Leer 1977) and
+// WENO5 (Liu et al. 1994) reconstruction; floors ("Algorithm" section).
+#pragma once
+
+#include "kh_geom_math.h"
+
+namespace kh {
+
+enum { V_RHO = 0, V_U = 1, V_U1 = 2, V_U2 = 3, V_U3 = 4, V_B1 = 5, V_B2 = 6, V_B3 = 7, NV = 8 };
+
+// Metric at one point: full 4x4 covariant and contravariant, sqrt(-g), lapse.
+template <class R> struct Met {
+  R gcov[4][4];
+  R gcon[4][4];
+  R gdet;
+  R alpha;
+};
+
+// Fluid 4-vectors at one point.
+template <class R> struct FState {
+  R ucon[4], ucov[4], bcon[4], bcov[4], bsq;
+};
+
+// u^t = gamma / alpha, u^i = u~^i - gamma alpha g^{ti}, gamma^2 = 1 + g_ij u~^i u~^j;
+// b^t = B^i u_i, b^i = (B^i + b^t u^i) / u^t.
+template <class R> KH_HD void fluid_state(const R* P, const Met<R>& m, FState<R>& s) {
+  const R v1 = P[V_U1], v2 = P[V_U2], v3 = P[V_U3];
+  const R q = m.gcov[1][1] * v1 * v1 + m.gcov[2][2] * v2 * v2 + m.gcov[3][3] * v3 * v3 +
+              R(2) * (m.gcov[1][2] * v1 * v2 + m.gcov[1][3] * v1 * v3 + m.gcov[2][3] * v2 * v3);
+  const R gam = sqrt(R(1) + q);
+  const R ga = gam * m.alpha;
+  s.ucon[0] = gam / m.alpha;
+  s.ucon[1] = v1 - ga * m.gcon[0][1];
+  s.ucon[2] = v2 - ga * m.gcon[0][2];
+  s.ucon[3] = v3 - ga * m.gcon[0][3];
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu)
+    s.ucov[mu] = m.gcov[mu][0] * s.ucon[0] + m.gcov[mu][1] * s.ucon[1] + m.gcov[mu][2] * s.ucon[2] +
+                 m.gcov[mu][3] * s.ucon[3];
+  const R bt = P[V_B1] * s.ucov[1] + P[V_B2] * s.ucov[2] + P[V_B3] * s.ucov[3];
+  s.bcon[0] = bt;
+  const R iut = R(1) / s.ucon[0];
+  s.bcon[1] = (P[V_B1] + bt * s.ucon[1]) * iut;
+  s.bcon[2] = (P[V_B2] + bt * s.ucon[2]) * iut;
+  s.bcon[3] = (P[V_B3] + bt * s.ucon[3]) * iut;
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu)
+    s.bcov[mu] = m.gcov[mu][0] * s.bcon[0] + m.gcov[mu][1] * s.bcon[1] + m.gcov[mu][2] * s.bcon[2] +
+                 m.gcov[mu][3] * s.bcon[3];
+  s.bsq = s.bcon[0] * s.bcov[0] + s.bcon[1] * s.bcov[1] + s.bcon[2] * s.bcov[2] + s.bcon[3] * s.bcov[3];
+}
+
+// Flux through an x^d face (d = 1..3) and the conserved vector of one state:
+// F = sqrt(-g) (rho u^d, T^d_t + rho u^d, T^d_i, b^i u^d - b^d u^i),
+// U = sqrt(-g) (rho u^t, T^t_t + rho u^t, T^t_i, B^i).
+template <class R>
+KH_HD void flux_cons(const R* P, const FState<R>& s, const Met<R>& m, R gam, int d, R* F, R* U) {
+  const R p = (gam - R(1)) * P[V_U];
+  const R eta = P[V_RHO] + P[V_U] + p + s.bsq;
+  const R ptot = p + R(0.5) * s.bsq;
+  const R g = m.gdet;
+  const R ud = s.ucon[d], bd = s.bcon[d];
+  const R mf = P[V_RHO] * ud;
+  F[V_RHO] = g * mf;
+  F[V_U] = g * (eta * ud * s.ucov[0] - bd * s.bcov[0] + mf);
+#pragma unroll
+  for (int i = 1; i < 4; ++i) {
+    R t = eta * ud * s.ucov[i] - bd * s.bcov[i];
+    if (i == d) t += ptot;
+    F[V_U1 + i - 1] = g * t;
+    F[V_B1 + i - 1] = g * (s.bcon[i] * ud - bd * s.ucon[i]);
+  }
+  const R ut = s.ucon[0], bt = s.bcon[0];
+  const R mt = P[V_RHO] * ut;
+  U[V_RHO] = g * mt;
+  U[V_U] = g * (eta * ut * s.ucov[0] - bt * s.bcov[0] + ptot + mt);
+#pragma unroll
+  for (int i = 1; i < 4; ++i) {
+    U[V_U1 + i - 1] = g * (eta * ut * s.ucov[i] - bt * s.bcov[i]);
+    U[V_B1 + i - 1] = g * P[V_B1 + i - 1];
+  }
+}
+
+// Conserved vector only.
+template <class R> KH_HD void cons_only(const R* P, const FState<R>& s, const Met<R>& m, R gam, R* U) {
+  const R p = (gam - R(1)) * P[V_U];
+  const R eta = P[V_RHO] + P[V_U] + p + s.bsq;
+  const R ptot = p + R(0.5) * s.bsq;
+  const R g = m.gdet;
+  const R ut = s.ucon[0], bt = s.bcon[0];
+  const R mt = P[V_RHO] * ut;
+  U[V_RHO] = g * mt;
+  U[V_U] = g * (eta * ut * s.ucov[0] - bt * s.bcov[0] + ptot + mt);
+#pragma unroll
+  for (int i = 1; i < 4; ++i) {
+    U[V_U1 + i - 1] = g * (eta * ut * s.ucov[i] - bt * s.bcov[i]);
+    U[V_B1 + i - 1] = g * P[V_B1 + i - 1];
+  }
+}
+
+// Signal speeds dx^d/dt: with c_ms^2 = c_s^2 + v_A^2 - c_s^2 v_A^2 (clamped to
+// [0, 1]) a covariant wave vector (-v, delta^d) obeys
+// (k_mu u^mu)^2 = c_ms^2 (k_mu k^mu + (k_mu u^mu)^2), i.e. A v^2 - Bq v + C = 0.
+template <class R>
+KH_HD void signal_speeds(const R* P, const FState<R>& s, const Met<R>& m, R gam, int d, R& cmax, R& cmin) {
+  const R p = (gam - R(1)) * P[V_U];
+  const R w = P[V_RHO] + P[V_U] + p;
+  const R cs2 = gam * p / w;
+  const R va2 = s.bsq / (s.bsq + w);
+  R cms2 = cs2 + va2 - cs2 * va2;
+  cms2 = cms2 < R(0) ? R(0) : (cms2 > R(1) ? R(1) : cms2);
+  const R Au = s.ucon[d], Bu = s.ucon[0];
+  const R A = Bu * Bu - (m.gcon[0][0] + Bu * Bu) * cms2;
+  const R Bq = R(2) * (Au * Bu - (m.gcon[0][d] + Au * Bu) * cms2);
+  const R C = Au * Au - (m.gcon[d][d] + Au * Au) * cms2;
+  R disc = Bq * Bq - R(4) * A * C;
+  disc = disc < R(0) ? R(0) : disc;
+  const R sd = sqrt(disc);
+  const R i2a = R(1) / (R(2) * A);
+  const R vp = (Bq + sd) * i2a;
+  const R vm = (Bq - sd) * i2a;
+  cmax = vp > vm ? vp : vm;
+  cmin = vp > vm ? vm : vp;
+}
+
+// ---------------------------------------------------------------------------
+// Reconstruction of one variable.
+// ---------------------------------------------------------------------------
+// Monotonized central: zero slope unless both one-sided differences share a
+// sign; otherwise the smallest-magnitude of 2 dL, 2 dR, (dL + dR)/2.
+template <class R> KH_HD void recon_mc(R qm, R q0, R qp, R& lo, R& hi) {
+  const R dl = q0 - qm, dr = qp - q0;
+  R s = R(0);
+  if (dl * dr > R(0)) {
+    const R a = R(2) * dl, b = R(2) * dr, c = R(0.5) * (dl + dr);
+    s = a;
+    if (fabs(b) < fabs(s)) s = b;
+    if (fabs(c) < fabs(s)) s = c;
+  }
+  lo = q0 - R(0.5) * s;
+  hi = q0 + R(0.5) * s;
+}
+
+// WENO5 point value at x = +1/2 of the centre cell of (a, b, c, d, e).
+template <class R> KH_HD R weno5_plus(R a, R b, R c, R d, R e) {
+  const R eps = R(1e-26);
+  const R p0 = R(0.375) * a - R(1.25) * b + R(1.875) * c;
+  const R p1 = R(-0.125) * b + R(0.75) * c + R(0.375) * d;
+  const R p2 = R(0.375) * c + R(0.75) * d - R(0.125) * e;
+  const R k = R(13.0 / 12.0);
+  const R t0 = a - R(2) * b + c, u0 = a - R(4) * b + R(3) * c;
+  const R t1 = b - R(2) * c + d, u1 = b - d;
+  const R t2 = c - R(2) * d + e, u2 = R(3) * c - R(4) * d + e;
+  const R s0 = k * t0 * t0 + R(0.25) * u0 * u0 + eps;
+  const R s1 = k * t1 * t1 + R(0.25) * u1 * u1 + eps;
+  const R s2 = k * t2 * t2 + R(0.25) * u2 * u2 + eps;
+  const R w0 = R(0.0625) / (s0 * s0);
+  const R w1 = R(0.625) / (s1 * s1);
+  const R w2 = R(0.3125) / (s2 * s2);
+  return (w0 * p0 + w1 * p1 + w2 * p2) / (w0 + w1 + w2);
+}
+
+// ---------------------------------------------------------------------------
+// Noble et al. (2006) 2-unknown inversion, FP64.
+//   D = alpha rho u^t; Q_mu = alpha T^t_mu; B^mu = alpha (0, B^i);
+//   n_mu = (-alpha, 0, 0, 0); Q~^mu = Q^mu + n^mu (Q.n).
+// Unknowns W = (rho + u + p) gamma^2 and v^2 = 1 - 1/gamma^2:
+//   f1 = Q~^2 - v^2 (B^2 + W)^2 + (Q.B)^2 (B^2 + 2W) / W^2 = 0
+//   f2 = Q.n + W - p(W, v^2) + B^2 (1 + v^2)/2 - (Q.B)^2 / (2 W^2) = 0
+//   p = (gam - 1)/gam (W (1 - v^2) - D sqrt(1 - v^2)).
+// Returns 0 or a failure code (1 no convergence, 2 v^2 >= 1, 3 W <= 0,
+// 4 rho <= 0, 5 u < 0); P (fluid slots) is written only on success.
+// ---------------------------------------------------------------------------
+struct C2POpts {
+  int max_iter;
+  double tol;
+};
+
+KH_HD int noble2d(const double* U, const Met<double>& m, double gam, const C2POpts& o, double* P) {
+  const double ig = 1.0 / m.gdet;
+  const double a = m.alpha;
+  const double D = a * U[V_RHO] * ig;
+  const double Qc[4] = {a * (U[V_U] - U[V_RHO]) * ig, a * U[V_U1] * ig, a * U[V_U2] * ig, a * U[V_U3] * ig};
+  double Qu[4];
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu)
+    Qu[mu] = m.gcon[mu][0] * Qc[0] + m.gcon[mu][1] * Qc[1] + m.gcon[mu][2] * Qc[2] + m.gcon[mu][3] * Qc[3];
+  // n^mu = -alpha g^{mu t}
+  const double nu[4] = {-a * m.gcon[0][0], -a * m.gcon[1][0], -a * m.gcon[2][0], -a * m.gcon[3][0]};
+  const double Qdn = Qc[0] * nu[0] + Qc[1] * nu[1] + Qc[2] * nu[2] + Qc[3] * nu[3];
+  const double Qsq = Qc[0] * Qu[0] + Qc[1] * Qu[1] + Qc[2] * Qu[2] + Qc[3] * Qu[3];
+  const double Qtsq = Qsq + Qdn * Qdn;
+  const double Bc1 = a * U[V_B1] * ig, Bc2 = a * U[V_B2] * ig, Bc3 = a * U[V_B3] * ig;
+  const double Bsq = m.gcov[1][1] * Bc1 * Bc1 + m.gcov[2][2] * Bc2 * Bc2 + m.gcov[3][3] * Bc3 * Bc3 +
+                     2.0 * (m.gcov[1][2] * Bc1 * Bc2 + m.gcov[1][3] * Bc1 * Bc3 + m.gcov[2][3] * Bc2 * Bc3);
+  const double QdB = Qc[1] * Bc1 + Qc[2] * Bc2 + Qc[3] * Bc3;
+  const double QdB2 = QdB * QdB;
+  const double gf = (gam - 1.0) / gam;
+
+  // initial guess from the stage-input primitives at this metric
+  double W, vsq;
+  {
+    const double v1 = P[V_U1], v2 = P[V_U2], v3 = P[V_U3];
+    const double q = m.gcov[1][1] * v1 * v1 + m.gcov[2][2] * v2 * v2 + m.gcov[3][3] * v3 * v3 +
+                     2.0 * (m.gcov[1][2] * v1 * v2 + m.gcov[1][3] * v1 * v3 + m.gcov[2][3] * v2 * v3);
+    const double g2 = 1.0 + q;
+    W = (P[V_RHO] + gam * P[V_U]) * g2;
+    vsq = q / g2;
+  }
+  if (!(W > 0.0) || !isfinite(W)) W = fabs(Qdn) + 1e-300;
+  const double vmax = 1.0 - 1e-16;
+  if (!(vsq >= 0.0)) vsq = 0.0;
+  if (vsq > vmax) vsq = vmax;
+
+  bool conv = false;
+  double err = 1.0;
+  for (int it = 0; it < o.max_iter; ++it) {
+    const double g2i = 1.0 - vsq;
+    const double sg = sqrt(g2i);
+    const double p = gf * (W * g2i - D * sg);
+    const double BW = Bsq + W;
+    const double W2 = W * W;
+    const double iW2 = 1.0 / W2;
+    const double f1 = Qtsq - vsq * BW * BW + QdB2 * (Bsq + 2.0 * W) * iW2;
+    const double f2 = Qdn + W - p + 0.5 * Bsq * (1.0 + vsq) - 0.5 * QdB2 * iW2;
+    const double dpdW = gf * g2i;
+    const double dpdv = gf * (-W + 0.5 * D / sg);
+    const double j11 = -2.0 * vsq * BW - 2.0 * QdB2 * BW * iW2 / W;
+    const double j12 = -BW * BW;
+    const double j21 = 1.0 - dpdW + QdB2 * iW2 / W;
+    const double j22 = 0.5 * Bsq - dpdv;
+    const double det = j11 * j22 - j12 * j21;
+    const double dW = -(j22 * f1 - j12 * f2) / det;
+    const double dv = -(-j21 * f1 + j11 * f2) / det;
+    double Wn = W + dW;
+    double vn = vsq + dv;
+    // keep the iterate admissible
+    if (!(Wn > 0.0)) Wn = 0.5 * W;
+    if (vn < 0.0) vn = 0.0;
+    if (vn > vmax) vn = vmax;
+    err = fabs(Wn - W) / Wn + fabs(vn - vsq);
+    W = Wn;
+    vsq = vn;
+    if (!isfinite(W) || !isfinite(vsq)) return 1;
+    if (err < o.tol) {
+      conv = true;
+      break;
+    }
+  }
+  if (!conv && !(err < 1e-9)) return 1;
+  if (!(W > 0.0)) return 3;
+  if (!(vsq < 1.0) || vsq < 0.0) return 2;
+  const double gamma = 1.0 / sqrt(1.0 - vsq);
+  const double rho = D / gamma;
+  const double uint = (W * (1.0 - vsq) - rho) / gam;
+  if (!(rho > 0.0)) return 4;
+  if (!(uint >= 0.0)) return 5;
+  P[V_RHO] = rho;
+  P[V_U] = uint;
+  const double f = gamma / (W + Bsq);
+  const double iW = 1.0 / W;
+  P[V_U1] = f * (Qu[1] + nu[1] * Qdn + QdB * Bc1 * iW);
+  P[V_U2] = f * (Qu[2] + nu[2] * Qdn + QdB * Bc2 * iW);
+  P[V_U3] = f * (Qu[3] + nu[3] * Qdn + QdB * Bc3 * iW);
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Floors (after a successful inversion or a fixup):
+//   rho >= max(rho_min r^-3/2, 1e-20, b^2/bsq_rho_max)
+//   u   >= max(u_min r^-5/2, 1e-20, b^2/bsq_u_max)
+//   u   <= u_rho_max rho
+//   gamma <= gamma_max (u~ scaled down)
+// Mass and energy are injected by raising rho and u at fixed u~ (normal-
+// observer frame); the caller recomputes U where the mask is non-zero.
+// ---------------------------------------------------------------------------
+struct FloorParams {
+  double rho_min, u_min, bsq_rho_max, bsq_u_max, u_rho_max, gamma_max;
+};
+
+KH_HD int apply_floors(const FloorParams& f, const Met<double>& m, double r, double* P) {
+  FState<double> s;
+  fluid_state(P, m, s);
+  double rf = f.rho_min * pow(r, -1.5);
+  double uf = f.u_min * pow(r, -2.5);
+  rf = rf > 1e-20 ? rf : 1e-20;
+  uf = uf > 1e-20 ? uf : 1e-20;
+  const double rb = s.bsq / f.bsq_rho_max, ub = s.bsq / f.bsq_u_max;
+  rf = rf > rb ? rf : rb;
+  uf = uf > ub ? uf : ub;
+  int mask = 0;
+  if (P[V_RHO] < rf) { P[V_RHO] = rf; mask |= 1; }
+  if (P[V_U] < uf) { P[V_U] = uf; mask |= 1; }
+  if (P[V_U] > f.u_rho_max * P[V_RHO]) { P[V_U] = f.u_rho_max * P[V_RHO]; mask |= 2; }
+  const double v1 = P[V_U1], v2 = P[V_U2], v3 = P[V_U3];
+  const double q = m.gcov[1][1] * v1 * v1 + m.gcov[2][2] * v2 * v2 + m.gcov[3][3] * v3 * v3 +
+                   2.0 * (m.gcov[1][2] * v1 * v2 + m.gcov[1][3] * v1 * v3 + m.gcov[2][3] * v2 * v3);
+  const double gamma = sqrt(1.0 + q);
+  if (gamma > f.gamma_max) {
+    const double sc = sqrt((f.gamma_max * f.gamma_max - 1.0) / (gamma * gamma - 1.0));
+    P[V_U1] *= sc;
+    P[V_U2] *= sc;
+    P[V_U3] *= sc;
+    mask |= 4;
+  }
+  return mask;
+}
+
+}  // namespace kh

@@ -1,0 +1,236 @@
+"""Thin Python binding of the C ABI in include/kharma_gb300.h.
+
+Argument marshalling only: every step of the method runs in the CUDA library
+(libkharma_gb300.so, built in place by ``build.py``). PyTorch supplies device
+memory and the stream. There is no CPU fallback: if the library or a GPU is
+missing, the calls raise.
+
+Arrays handed to the library are torch float64 CUDA tensors in the library
+layout [var][n3s][n2s][n1s] (see ``Context.shape``); ``to_device`` /
+``to_host`` convert from/to the unpadded (8, N3, N2, N1) numpy layout used by
+the input generators (slots rho, u, u~1..3, B1..3).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = os.path.join(_HERE, "libkharma_gb300.so")
+
+MINKOWSKI, KS, MKS, FMKS = 0, 1, 2, 3
+KIND = {"minkowski": MINKOWSKI, "ks": KS, "mks": MKS, "fmks": FMKS}
+BC = {"periodic": 0, "outflow": 1, "polar": 2, "dirichlet": 3}
+RECON = {"mc": 0, "weno5": 1}
+ERRORS = {0: "KH_OK", -1: "KH_EINVAL", -2: "KH_ECUDA", -3: "KH_ENOMEM", -4: "KH_ETIMEOUT", -5: "KH_ENAN"}
+
+
+class KHError(RuntimeError):
+    pass
+
+
+class Coords(C.Structure):
+    _fields_ = [
+        ("kind", C.c_int), ("n1", C.c_int), ("n2", C.c_int), ("n3", C.c_int), ("recon", C.c_int),
+        ("precision", C.c_int), ("bc", C.c_int * 6),
+        ("x1min", C.c_double), ("x1max", C.c_double), ("x2min", C.c_double), ("x2max", C.c_double),
+        ("x3min", C.c_double), ("x3max", C.c_double),
+        ("hslope", C.c_double), ("poly_xt", C.c_double), ("poly_alpha", C.c_double), ("mks_smooth", C.c_double),
+        ("cfl", C.c_double), ("rho_min", C.c_double), ("u_min", C.c_double), ("bsq_rho_max", C.c_double),
+        ("bsq_u_max", C.c_double), ("u_rho_max", C.c_double), ("gamma_max", C.c_double),
+        ("newton_max_iter", C.c_int), ("newton_tol", C.c_double),
+    ]
+
+
+class Stats(C.Structure):
+    _fields_ = [("nfail", C.c_int64), ("nfloor", C.c_int64), ("nunfixed", C.c_int64), ("dt_cfl", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libkharma_gb300.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB):
+            raise KHError(f"CUDA library not built: {_LIB} (run __graft_entry__.build())")
+        L = C.CDLL(_LIB)
+        vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int)
+        L.kh_geometry_init.argtypes = [C.c_double, C.POINTER(Coords), C.c_double, C.POINTER(C.c_void_p)]
+        L.kh_shape.argtypes = [vp, ip, ip, ip, ip]
+        L.kh_set_stream.argtypes = [vp, vp]
+        L.kh_set_dirichlet.argtypes = [vp, C.c_int, vp]
+        L.kh_prim_to_cons.argtypes = [vp, vp, vp, vp]
+        L.kh_cons_to_prim.argtypes = [vp, vp, vp, vp, vp, C.POINTER(C.c_int64)]
+        L.kh_step.argtypes = [vp, vp, vp, vp, C.c_double, dp]
+        L.kh_cfl_dt.argtypes = [vp, vp, vp, dp]
+        L.kh_divb.argtypes = [vp, vp, dp, dp]
+        L.kh_fluxes.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.kh_fill_ghosts.argtypes = [vp, vp, vp]
+        L.kh_get_stats.argtypes = [vp, C.POINTER(Stats)]
+        L.kh_profile.argtypes = [vp, C.c_int]
+        L.kh_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+        L.kh_launch_count.argtypes = [vp]
+        L.kh_launch_count.restype = C.c_int64
+        L.kh_destroy.argtypes = [vp]
+        L.kh_strerror.argtypes = [C.c_int]
+        L.kh_strerror.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, what: str) -> int:
+    if rc < 0:
+        raise KHError(f"{what}: {ERRORS.get(rc, rc)} ({lib().kh_strerror(rc).decode()})")
+    return rc
+
+
+def coords_from_cfg(cfg: dict) -> Coords:
+    c = Coords()
+    c.kind = KIND[cfg["coords"]]
+    c.n1, c.n2, c.n3 = cfg["n1"], cfg["n2"], cfg["n3"]
+    c.recon = RECON[cfg["recon"]]
+    c.precision = 0
+    for q, b in enumerate(cfg["bc"]):
+        c.bc[q] = BC[b]
+    (c.x1min, c.x1max), (c.x2min, c.x2max), (c.x3min, c.x3max) = cfg["x1"], cfg["x2"], cfg["x3"]
+    c.hslope = cfg.get("hslope", 0.3)
+    c.poly_xt = cfg.get("poly_xt", 0.82)
+    c.poly_alpha = cfg.get("poly_alpha", 14.0)
+    c.mks_smooth = cfg.get("mks_smooth", 0.5)
+    c.cfl = cfg.get("cfl", 0.9)
+    fl = cfg.get("floors", {})
+    c.rho_min = fl.get("rho_min", 1e-20)
+    c.u_min = fl.get("u_min", 1e-20)
+    c.bsq_rho_max = fl.get("bsq_rho_max", 1e300)
+    c.bsq_u_max = fl.get("bsq_u_max", 1e300)
+    c.u_rho_max = fl.get("u_rho_max", 1e300)
+    c.gamma_max = fl.get("gamma_max", 1e300)
+    c.newton_max_iter = cfg.get("newton_max_iter", 30)
+    c.newton_tol = cfg.get("newton_tol", 1e-14)
+    return c
+
+
+def _ptr(t) -> C.c_void_p:
+    return C.c_void_p(0 if t is None else t.data_ptr())
+
+
+class Context:
+    """One kh_ctx: geometry cache + scratch for one problem on the current GPU."""
+
+    def __init__(self, cfg: dict, device=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise KHError("no CUDA device: the GB300 path has no CPU fallback")
+        self.torch = torch
+        self.device = torch.device(device or "cuda:0")
+        torch.cuda.set_device(self.device)
+        self.cfg = cfg
+        self._c = coords_from_cfg(cfg)
+        h = C.c_void_p()
+        _check(lib().kh_geometry_init(float(cfg.get("a", 0.0)), C.byref(self._c), float(cfg["gam"]), C.byref(h)),
+               "kh_geometry_init")
+        self._h = h
+        a, b, c, d = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        _check(lib().kh_shape(h, C.byref(a), C.byref(b), C.byref(c), C.byref(d)), "kh_shape")
+        self.n1s, self.n2s, self.n3s, self.ng = a.value, b.value, c.value, d.value
+        self.stream = None
+
+    # ---- lifetime ----
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().kh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        self.stream = stream
+        _check(lib().kh_set_stream(self._h, C.c_void_p(stream.cuda_stream if stream is not None else 0)),
+               "kh_set_stream")
+
+    # ---- layout helpers ----
+    def shape(self, nvar: int):
+        return (nvar, self.n3s, self.n2s, self.n1s)
+
+    def empty(self, nvar: int):
+        return self.torch.zeros(self.shape(nvar), dtype=self.torch.float64, device=self.device)
+
+    def to_device(self, A: np.ndarray, pinned_src=None):
+        """(nvar, N3, N2, N1) numpy -> padded device tensor."""
+        t = self.empty(A.shape[0])
+        src = self.torch.from_numpy(np.ascontiguousarray(A))
+        t[:, :, :, : A.shape[3]].copy_(src)
+        return t
+
+    def to_host(self, t, N1: int) -> np.ndarray:
+        return t[:, :, :, :N1].cpu().numpy()
+
+    def split(self, PB):
+        """Device (8, ...) tensor -> (P view of 5 slots, B view of 3 slots), both contiguous."""
+        return PB[:5], PB[5:]
+
+    # ---- the C ABI ----
+    def set_dirichlet(self, face: int, PB_ghost):
+        _check(lib().kh_set_dirichlet(self._h, face, _ptr(PB_ghost)), "kh_set_dirichlet")
+
+    def prim_to_cons(self, P, B, U):
+        _check(lib().kh_prim_to_cons(self._h, _ptr(P), _ptr(B), _ptr(U)), "kh_prim_to_cons")
+
+    def cons_to_prim(self, U, P, B, pflag=None) -> int:
+        n = C.c_int64()
+        _check(lib().kh_cons_to_prim(self._h, _ptr(U), _ptr(P), _ptr(B), _ptr(pflag), C.byref(n)),
+               "kh_cons_to_prim")
+        return n.value
+
+    def step(self, U, P, B, dt: float, sync: bool = True):
+        """One step; returns (dt_cfl, nfail) when sync, else (None, None)."""
+        if sync:
+            d = C.c_double()
+            rc = _check(lib().kh_step(self._h, _ptr(U), _ptr(P), _ptr(B), float(dt), C.byref(d)), "kh_step")
+            return d.value, rc
+        _check(lib().kh_step(self._h, _ptr(U), _ptr(P), _ptr(B), float(dt), None), "kh_step")
+        return None, None
+
+    def cfl_dt(self, P, B) -> float:
+        d = C.c_double()
+        _check(lib().kh_cfl_dt(self._h, _ptr(P), _ptr(B), C.byref(d)), "kh_cfl_dt")
+        return d.value
+
+    def divb(self, B):
+        mx, l1 = C.c_double(), C.c_double()
+        _check(lib().kh_divb(self._h, _ptr(B), C.byref(mx), C.byref(l1)), "kh_divb")
+        return mx.value, l1.value
+
+    def fluxes(self, P, B, F1, F2, F3=None):
+        _check(lib().kh_fluxes(self._h, _ptr(P), _ptr(B), _ptr(F1), _ptr(F2), _ptr(F3)), "kh_fluxes")
+
+    def fill_ghosts(self, P, B):
+        _check(lib().kh_fill_ghosts(self._h, _ptr(P), _ptr(B)), "kh_fill_ghosts")
+
+    def stats(self) -> Stats:
+        s = Stats()
+        _check(lib().kh_get_stats(self._h, C.byref(s)), "kh_get_stats")
+        return s
+
+    TIMERS = ("bc", "flux_x1", "flux_x2", "flux_x3", "flux_ct", "update", "fixup", "cfl")
+
+    def profile(self, enable: bool):
+        _check(lib().kh_profile(self._h, 1 if enable else 0), "kh_profile")
+
+    def profile_read(self) -> dict:
+        ms = (C.c_double * 8)()
+        n = (C.c_int64 * 8)()
+        _check(lib().kh_profile_read(self._h, ms, n), "kh_profile_read")
+        return {name: (ms[q], n[q]) for q, name in enumerate(self.TIMERS)}
+
+    def launches(self) -> int:
+        return int(lib().kh_launch_count(self._h))
