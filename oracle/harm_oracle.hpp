@@ -523,7 +523,9 @@ inline int cons_to_prim_point(const double U[NVAR], const Geo& G, double gam, do
     Qsq += Qcov[m] * Qcon[m];
   }
   in.Qdotn = Qn;
-  in.Qtsq = Qsq + Qn * Qn;
+  // Q~^2 is the square of a spacelike vector (>= 0 by definition); for a fluid
+  // at rest in the normal frame rounding can leave it slightly negative.
+  in.Qtsq = std::max(Qsq + Qn * Qn, 0.0);
   for (int m = 0; m < 4; ++m) in.Qt[m] = Qcon[m] + ncon[m] * Qn;
   in.Bcal[0] = 0.0;
   for (int i = 1; i < 4; ++i) in.Bcal[i] = a * u[B1 + i - 1];

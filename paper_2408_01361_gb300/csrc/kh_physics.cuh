@@ -197,7 +197,9 @@ KH_HD int noble2d(const double* U, const Met<double>& m, double gam, const C2POp
   const double nu[4] = {-a * m.gcon[0][0], -a * m.gcon[1][0], -a * m.gcon[2][0], -a * m.gcon[3][0]};
   const double Qdn = Qc[0] * nu[0] + Qc[1] * nu[1] + Qc[2] * nu[2] + Qc[3] * nu[3];
   const double Qsq = Qc[0] * Qu[0] + Qc[1] * Qu[1] + Qc[2] * Qu[2] + Qc[3] * Qu[3];
-  const double Qtsq = Qsq + Qdn * Qdn;
+  // square of the spacelike projected momentum: >= 0 (rounding can make the
+  // difference slightly negative for a fluid at rest in the normal frame)
+  const double Qtsq = fmax(Qsq + Qdn * Qdn, 0.0);
   const double Bc1 = a * U[V_B1] * ig, Bc2 = a * U[V_B2] * ig, Bc3 = a * U[V_B3] * ig;
   const double Bsq = m.gcov[1][1] * Bc1 * Bc1 + m.gcov[2][2] * Bc2 * Bc2 + m.gcov[3][3] * Bc3 * Bc3 +
                      2.0 * (m.gcov[1][2] * Bc1 * Bc2 + m.gcov[1][3] * Bc1 * Bc3 + m.gcov[2][3] * Bc2 * Bc3);

@@ -194,3 +194,104 @@ def test_linear_mode_one_period_gpu(kh, orc):
     eg = np.array([np.abs(Pg[v][sl] - Pex[v][sl]).mean() for v in range(8)])
     eo = np.array([np.abs(Po2[v][sl] - Pex[v][sl]).mean() for v in range(8)])
     assert np.all(np.abs(eg - eo) <= 1e-6 * eo + 1e-18), (eg, eo)
+
+
+def test_full_size_torus_one_step(kh, orc):
+    """The benchmark workload (192x96x96 FMKS torus, WENO5) at full size, in the
+    launch configuration the benchmark times: one step vs the oracle."""
+    cfg = inputs.torus_cfg(192, 96, 96)
+    P = inputs.torus_state(cfg, seed=2)
+    Uo = orc.prim_to_cons(cfg, P)
+    dt = 0.5 * orc.cfl_dt(cfg, P)
+    Uo2, Po2, dto, st = orc.step(cfg, Uo, P, dt)
+    ctx = kh.Context(cfg)
+    g = GpuRun(ctx, cfg, P, U=Uo)
+    dtg, nfail = ctx.step(g.U, g.P, g.B, dt)
+    assert nfail == st[0]
+    Ug, Pg = g.host()
+    eu = rel_l1(interior(cfg, Ug), interior(cfg, Uo2))
+    ep = rel_l1(interior(cfg, Pg), interior(cfg, Po2))
+    assert eu.max() < TOL and ep.max() < TOL, (eu, ep)
+    assert abs(dtg - dto) <= 1e-10 * dto
+
+
+def test_full_size_bondi_10_steps(kh, orc):
+    """The 128x128 MKS Bondi problem at full size, 10 steps (smooth flow)."""
+    cfg = inputs.bondi_cfg(128, 128)
+    P, dirich = inputs.bondi_state(cfg, seed=1)
+    Uo = orc.prim_to_cons(cfg, P)
+    dt = orc.cfl_dt(cfg, P, dirich)
+    Uc, Pc = Uo, P
+    ctx = kh.Context(cfg)
+    g = GpuRun(ctx, cfg, P, U=Uo, dirichlet=dirich)
+    dtg = dt
+    for _ in range(10):
+        Uc, Pc, dt, st = orc.step(cfg, Uc, Pc, dt, dirich)
+        dtg2, nfail = ctx.step(g.U, g.P, g.B, dtg)
+        dtg = dtg2
+    Ug, Pg = g.host()
+    eu = rel_l1(interior(cfg, Ug), interior(cfg, Uc))
+    ep = rel_l1(interior(cfg, Pg), interior(cfg, Pc))
+    assert eu.max() < TOL and ep.max() < TOL, (eu, ep)
+
+
+def test_ragged_and_minimum_sizes(kh, orc):
+    """Row length not a multiple of the 16-element padding, odd sizes, and the
+    minimum grid (4 zones per direction)."""
+    for n1, n2, n3 in ((37, 23, 11), (4, 4, 4), (5, 7, 1)):
+        cfg = inputs.linear_mode_cfg(8, ndim=3)
+        cfg.update(n1=n1, n2=n2, n3=n3)
+        P = inputs.random_prims(cfg, seed=3, rho_range=(0.5, 1.0), u_range=(0.3, 1.0), ut_scale=(0.3, 0.3, 0.3),
+                                b_scale=(0.3, 0.3, 0.3))
+        P = orc.apply_bc(cfg, P)
+        Uo = orc.prim_to_cons(cfg, P)
+        dt = 0.3 * orc.cfl_dt(cfg, P)
+        Uo2, Po2, _, st = orc.step(cfg, Uo, P, dt)
+        ctx = kh.Context(cfg)
+        g = GpuRun(ctx, cfg, P, U=Uo)
+        _, nfail = ctx.step(g.U, g.P, g.B, dt)
+        assert nfail == st[0]
+        Ug, Pg = g.host()
+        assert rel_l1(interior(cfg, Ug), interior(cfg, Uo2)).max() < TOL
+        assert rel_l1(interior(cfg, Pg), interior(cfg, Po2)).max() < TOL
+
+
+def test_failed_inversion_fixup_parity(kh, orc):
+    """Zones whose conserved state has no physical inversion (momentum beyond
+    what the energy allows) fail in both stages; the neighbour-average fixup
+    and the re-synchronised U must match the oracle's."""
+    cfg = inputs.linear_mode_cfg(12, ndim=3)
+    P = inputs.random_prims(cfg, seed=5, rho_range=(0.5, 1.0), u_range=(0.3, 1.0), ut_scale=(0.2, 0.2, 0.2),
+                            b_scale=(0.2, 0.2, 0.2))
+    P = orc.apply_bc(cfg, P)
+    Uo = orc.prim_to_cons(cfg, P)
+    for (k, j, i) in ((5, 5, 5), (6, 9, 4), (10, 3, 12)):
+        Uo[2, k, j, i] = 40.0 * abs(Uo[1, k, j, i]) + 40.0
+    dt = 0.2 * orc.cfl_dt(cfg, P)
+    Uo2, Po2, _, st = orc.step(cfg, Uo, P, dt)
+    assert st[0] >= 6
+    ctx = kh.Context(cfg)
+    g = GpuRun(ctx, cfg, P, U=Uo)
+    _, nfail = ctx.step(g.U, g.P, g.B, dt)
+    assert nfail == st[0]
+    Ug, Pg = g.host()
+    assert rel_l1(interior(cfg, Ug), interior(cfg, Uo2)).max() < TOL
+    assert rel_l1(interior(cfg, Pg), interior(cfg, Po2)).max() < TOL
+
+
+def test_inversion_failure_codes_match(kh, orc):
+    """Crafted unphysical U: both inverters report failure at the same cells."""
+    cfg = inputs.linear_mode_cfg(8, ndim=2)
+    P = inputs.random_prims(cfg, seed=9, ut_scale=(1.0, 1.0, 1.0), b_scale=(1.0, 1.0, 1.0))
+    Uo = orc.prim_to_cons(cfg, P)
+    bad = np.zeros(Uo.shape[1:], dtype=bool)
+    bad[0, 2:5, 3:9] = True
+    Uo[2][bad] = 100.0 * np.abs(Uo[1][bad]) + 100.0
+    Po, pflag_o, nfail_o = orc.cons_to_prim(cfg, Uo, P)
+    ctx = kh.Context(cfg)
+    g = GpuRun(ctx, cfg, P, U=Uo)
+    pflag = ctx.torch.zeros(ctx.shape(1)[1:], dtype=ctx.torch.int8, device=ctx.device)
+    nfail = ctx.cons_to_prim(g.U, g.P, g.B, pflag)
+    pf = pflag.cpu().numpy()[:, :, :P.shape[3]]
+    assert nfail == nfail_o == int(bad.sum())
+    assert np.array_equal(pf != 0, pflag_o != 0)

@@ -100,3 +100,21 @@ def test_weno5_no_large_overshoot(orc):
     q = np.where(np.arange(20) < 10, 1.0, 0.0)
     lo, hi = orc.recon("weno5", q)
     assert np.nanmax(hi[2:-2]) < 1.0 + 1e-3 and np.nanmin(lo[2:-2]) > -1e-3
+
+
+def test_inversion_of_fluid_at_rest_in_normal_frame(orc):
+    """u~ = 0 (at rest relative to the normal observer) gives Q~^2 = 0 exactly;
+    rounding must not turn it into a failure. Tenuous atmosphere-like states
+    (rho ~ 1e-11, u ~ 1e-15) at many FMKS points, including near the axis."""
+    cfg = inputs.torus_cfg(192, 96, 8)
+    P = np.zeros(inputs.shape(cfg))
+    x1 = inputs.centers(cfg, 0)
+    r = np.exp(x1)[None, None, :]
+    P[0] = 1e-6 * r ** -1.5
+    P[1] = 1e-8 * r ** -2.5
+    U = orc.prim_to_cons(cfg, P)
+    Pr, pflag, nfail = orc.cons_to_prim(cfg, U, P)
+    assert nfail == 0
+    sl = inputs.interior(cfg)
+    assert np.abs(Pr[0][sl] / P[0][sl] - 1).max() < 1e-10
+    assert np.abs(Pr[2:5][(slice(None),) + sl]).max() < 1e-12
