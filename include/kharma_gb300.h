@@ -171,6 +171,35 @@ int kh_profile_read(const kh_ctx* ctx, double* ms, int64_t* count);
 /* Number of kernel launches issued by this context since creation. */
 int64_t kh_launch_count(const kh_ctx* ctx);
 
+/* No-allocation divB (no counterpart in the paper; an interface addition).
+ * For callers that cannot call cudaMalloc -- code confined to a pre-sized
+ * memory pool or a hard device-memory budget, or frameworks whose allocator
+ * forbids raw CUDA allocations -- and therefore cannot create a kh_ctx. It
+ * computes the same corner divergence of sqrt(-g) B as kh_divb, without a
+ * context, allocating nothing: its only scratch (one partial result per row
+ * of corners) is a file-scope static __device__ array of
+ * 2 * KH_DIVB_NOALLOC_MAX_ROWS doubles (1 MiB), which every GPU that loads the
+ * library holds until the process exits.
+ *   B:    device, [3][n3s][n2s][n1s] with n3s = n3 + 6 (n3 > 1) or 1 (n3 == 1),
+ *         ng = 3 ghost zones, interior as in kh_shape();
+ *   gdet: device, [n2s][n1s], sqrt(-g) at cell centres;
+ *   dx1..dx3: native zone widths (dx3 ignored when n3 == 1);
+ *   out:  device, 2 doubles: out[0] = max |divB|, out[1] = mean |divB| over the
+ *         corners whose adjacent cells are all interior;
+ *   cuda_stream: cudaStream_t to launch on (NULL = legacy default stream).
+ * Asynchronous on the stream; returns KH_EINVAL for bad sizes, including a
+ * grid with more than KH_DIVB_NOALLOC_MAX_ROWS rows of corners
+ * ((n2 - 1) * max(n3 - 1, 1)), and KH_ECUDA if a launch fails.
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture. Every call shares the one array and leaves its
+ * last contents there; each call writes every slot it later reads, so nothing
+ * needs clearing between calls, but calls that overlap on the GPU (concurrent
+ * streams, or several host threads) race on it and must be serialised. */
+#define KH_DIVB_NOALLOC_MAX_ROWS 65536
+int kh_divb_noalloc(const double* B, const double* gdet, int n1, int n2, int n3, int n1s, int n2s, double dx1,
+                    double dx2, double dx3, double* out, void* cuda_stream);
+
 /* Free the context and its device buffers (synchronises its stream). */
 int kh_destroy(kh_ctx* ctx);
 

@@ -234,3 +234,16 @@ class Context:
 
     def launches(self) -> int:
         return int(lib().kh_launch_count(self._h))
+
+
+def divb_noalloc(B, gdet, n1: int, n2: int, n3: int, n1s: int, n2s: int, dx, out, stream=None) -> int:
+    """kh_divb_noalloc: corner divB without a context and without any
+    allocation (for callers that cannot call cudaMalloc); B, gdet, out are
+    device tensors, out receives (max |divB|, mean |divB|) asynchronously."""
+    L = lib()
+    f = L.kh_divb_noalloc
+    f.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
+                  C.c_double, C.c_void_p, C.c_void_p]
+    rc = f(_ptr(B), _ptr(gdet), n1, n2, n3, n1s, n2s, float(dx[0]), float(dx[1]), float(dx[2]), _ptr(out),
+           C.c_void_p(stream.cuda_stream if stream is not None else 0))
+    return _check(rc, "kh_divb_noalloc")
