@@ -33,11 +33,14 @@ sys.path.insert(0, ROOT)
 METRIC = "zone-cycles/s on 1 GB300 (mixed vs FP64), % HBM roofline, err vs FP64 oracle"
 UNIT = "zone-cycles/s"
 WORKLOAD = dict(n1=192, n2=96, n3=96)
-# Algorithmic HBM bytes per zone-cycle of the FP64 step: each stage reads the
-# stage input P (8 doubles) and U^n (8) and writes its output P (8); stage 2
-# also writes U^{n+1} (8): 56 doubles = 448 B, plus the axisymmetric geometry
-# re-read per (i, j) column and amortised over n3.
-ALG_BYTES_PER_ZONE_CYCLE = 448.0
+# Algorithmic HBM bytes per zone-cycle. FP64 step: each stage reads its input
+# P (8 doubles) and U^n (8) and writes its output P (8); stage 2 also writes
+# U^{n+1} (8): 56 doubles = 448 B. Mixed step: stage 1 reads P^n (FP64, 64 B)
+# and U^n (64 B) and writes the FP32 P* (32 B); stage 2 reads P* (32 B) and U^n
+# (64 B) and writes P^{n+1} (64 B) and U^{n+1} (64 B): 384 B. The axisymmetric
+# geometry re-read per (i, j) column adds ~21 B (FP64) amortised over n3.
+ALG_BYTES_PER_ZONE_CYCLE = {"fp64": 448.0, "mixed": 384.0}
+DTYPE = {"fp64": "f64", "mixed": "f32+f64"}
 
 
 def parse():
@@ -49,7 +52,11 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--n3", type=int, default=WORKLOAD["n3"], help="azimuthal zones (96 = the named workload)")
-    return p.parse_args()
+    p.add_argument("--precisions", default="mixed,fp64",
+                   help="comma list; the first is the headline, the others are reported beside it")
+    a = p.parse_args()
+    a.precisions = [x.strip() for x in a.precisions.split(",") if x.strip()]
+    return a
 
 
 def peaks():
@@ -121,7 +128,7 @@ def workload_cfg(n3: int):
 
 def workload_name(cfg) -> str:
     return (f"FM torus a=0.9375 FMKS {cfg['n1']}x{cfg['n2']}x{cfg['n3']} WENO5 LLF Flux-CT "
-            f"2-stage Noble-2D FP64, floors bsq/rho<100, 4e-2 u noise (seed 2)")
+            f"2-stage Noble-2D, floors bsq/rho<100, 4e-2 u noise (seed 2)")
 
 
 def dist_setup():
@@ -174,28 +181,12 @@ def run_reference(args, world, rank):
 # ---------------------------------------------------------------------------
 # the CUDA arm
 # ---------------------------------------------------------------------------
-def run_kh(args, world, rank, local):
-    import numpy as np
+def measure(args, cfg, P0, ctx, dev, stream, dist, world, oracle_step):
+    """Warm-up + K timed steps (+ e2e) of one context; returns a dict."""
     import torch
 
-    from paper_2408_01361_gb300 import build as kbuild
-    from paper_2408_01361_gb300 import inputs, kh
-
-    if not torch.cuda.is_available():
-        raise SystemExit("bench.py: no CUDA device (the GB300 path has no CPU fallback)")
-    kbuild.build()
-    torch.cuda.set_device(local)
-    dev = torch.device(f"cuda:{local}")
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
-
-    cfg = workload_cfg(args.n3)
-    nz = cfg["n1"] * cfg["n2"] * cfg["n3"]
-    P0 = inputs.torus_state(cfg, seed=2)
-    ctx = kh.Context(cfg, device=dev)
     N1 = P0.shape[3]
+    nz = cfg["n1"] * cfg["n2"] * cfg["n3"]
 
     def fresh():
         PB = ctx.to_device(P0)
@@ -206,25 +197,16 @@ def run_kh(args, world, rank, local):
 
     U, PB, P, B = fresh()
     dt0 = ctx.cfl_dt(P, B)
-
-    # ---- 1-step error against the oracle (rank 0, N = 1 only) ----
     err = None
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        dt1 = 0.5 * dt0
-        ctx.step(U, P, B, dt1)
-        Ug, Pg = ctx.to_host(U, N1), ctx.to_host(PB, N1)
-        cpu, err = cpu_leg(cfg, P0, dt1, Ug, Pg)
+    if oracle_step is not None:
+        ctx.step(U, P, B, oracle_step["dt"])
+        err = err_vs(cfg, ctx.to_host(U, N1), ctx.to_host(PB, N1), oracle_step)
         U, PB, P, B = fresh()
-
-    # ---- warm-up ----
     dt = dt0
     for _ in range(args.warmup):
         dt, _ = ctx.step(U, P, B, 0.5 * dt)
-    # ---- timed region ----
     ctx.profile(True)
-    sampler = ClockSampler(local)
-    stream = torch.cuda.current_stream(dev)
+    sampler = ClockSampler(dev.index or 0)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if dist:
         dist.barrier()
@@ -245,15 +227,12 @@ def run_kh(args, world, rank, local):
     ms = e0.elapsed_time(e1)
     prof = ctx.profile_read()
     ctx.profile(False)
-    t_max = ms
     if dist:
         t = torch.tensor([ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = nz * args.steps * world / (t_max * 1e-3)
-
-    # ---- end to end through the C ABI with host buffers ----
-    e2e = None
+        ms = float(t.item())
+    out = {"value": nz * args.steps * world / (ms * 1e-3), "ms": ms, "prof": prof, "launches": launches,
+           "clocks": clocks, "err": err, "nfail": nfail}
     if not args.no_e2e:
         hU = torch.empty(U.shape, dtype=torch.float64, pin_memory=True)
         hPB = torch.empty(PB.shape, dtype=torch.float64, pin_memory=True)
@@ -278,15 +257,12 @@ def run_kh(args, world, rank, local):
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ems = float(t.item())
         nbytes = (U.numel() + PB.numel()) * 8
-        e2e = {"value": nz * args.steps * world / (ems * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
-               "d2h_bytes_per_step": nbytes}
+        out["e2e"] = {"value": nz * args.steps * world / (ems * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                      "d2h_bytes_per_step": nbytes}
+    return out
 
-    if rank != 0:
-        if dist:
-            dist.destroy_process_group()
-        return 0
 
-    # ---- roofline of the dominant kernel group ----
+def roofline_of(prof, nz, precision):
     hbm, hbm_kind, sm_max = peaks()
     groups = {k: v for k, v in prof.items() if v[1] > 0}
     top = max(groups, key=lambda k: groups[k][0])
@@ -294,52 +270,103 @@ def run_kh(args, world, rank, local):
     avg_ms = top_ms / top_n
     share = {k: round(v[0] / sum(x[0] for x in groups.values()), 4) for k, v in groups.items()}
     fp64_peak = fp64_peak_tflops(sm_max)
-    flops_zone = FP64_FLOPS_PER_ZONE.get(top)
+    flops_zone = FP64_FLOPS_PER_ZONE.get((precision, top))
     achieved = (flops_zone * nz / (avg_ms * 1e-3) / 1e12) if flops_zone else None
-    roofline = {
+    roof = {
         "bound": "alu", "kernel": top, "achieved": achieved, "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
-        "frac": (achieved / fp64_peak) if achieved else None, "traffic": TRAFFIC_PER_LAUNCH.get(top),
-        "peak_source": "FP64 from unit counts: 152 SMs x 4 flop/clk x max SM clock (measured probe 1.20 TFLOP/s)",
-        "avg_launch_ms": avg_ms, "flops_per_zone": flops_zone,
+        "frac": (achieved / fp64_peak) if achieved else None, "traffic": TRAFFIC_PER_LAUNCH.get((precision, top)),
+        "peak_source": "FP64 from unit counts: 152 SMs x 4 flop/clk x max SM clock (a probe measured 1.20 TFLOP/s)",
+        "avg_launch_ms": avg_ms, "fp64_flops_per_zone": flops_zone,
     }
-    hbm_step = {"algorithmic_bytes_per_zone_cycle": ALG_BYTES_PER_ZONE_CYCLE,
-                "achieved_gbs": ALG_BYTES_PER_ZONE_CYCLE * value / world / 1e9,
+    return roof, share
+
+
+def run_kh(args, world, rank, local):
+    import torch
+
+    from paper_2408_01361_gb300 import build as kbuild
+    from paper_2408_01361_gb300 import inputs, kh
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py: no CUDA device (the GB300 path has no CPU fallback)")
+    kbuild.build()
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    cfg64 = workload_cfg(args.n3)
+    nz = cfg64["n1"] * cfg64["n2"] * cfg64["n3"]
+    P0 = inputs.torus_state(cfg64, seed=2)
+
+    # the oracle's step from the same state (CPU baseline + error reference)
+    oracle_step, cpu = None, None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ctx = kh.Context(cfg64, device=dev)
+        PB = ctx.to_device(P0)
+        dt1 = 0.5 * ctx.cfl_dt(*ctx.split(PB))
+        ctx.close()
+        oracle_step, cpu = cpu_leg(cfg64, P0, dt1)
+
+    results = {}
+    for prec in args.precisions:
+        cfg = dict(cfg64, precision=prec)
+        ctx = kh.Context(cfg, device=dev)
+        results[prec] = measure(args, cfg, P0, ctx, dev, stream, dist, world, oracle_step)
+        ctx.close()
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    head = args.precisions[0]
+    r = results[head]
+    roof, share = roofline_of(r["prof"], nz, head)
+    hbm, hbm_kind, _ = peaks()
+    alg = ALG_BYTES_PER_ZONE_CYCLE[head]
+    hbm_step = {"algorithmic_bytes_per_zone_cycle": alg, "achieved_gbs": alg * r["value"] / world / 1e9,
                 "peak_gbs": hbm, "peak_kind": hbm_kind}
     hbm_step["frac"] = hbm_step["achieved_gbs"] / hbm
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(cfg), "precision": "fp64", "zones": nz,
+        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": DTYPE[head], "data": "synthetic",
+        "config": {"workload": workload_name(cfg64), "precision": head, "zones": nz,
                    "l2": "inputs larger than L2 (~1 GB resident), no flush",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "roofline": roofline, "hbm_step": hbm_step,
-        "kernel_share": share,
-        "cpu_baseline": cpu, "err_vs_oracle": err, "e2e": e2e, "gpu_launches": launches,
-        "clocks": clocks, "nfail_timed": nfail,
+        "roofline": roof, "hbm_step": hbm_step, "kernel_share": share,
+        "cpu_baseline": cpu, "err_vs_oracle": r["err"], "e2e": r.get("e2e"), "gpu_launches": r["launches"],
+        "clocks": r["clocks"], "nfail_timed": r["nfail"],
     }
+    for prec in args.precisions[1:]:
+        q = results[prec]
+        rf, sh = roofline_of(q["prof"], nz, prec)
+        line[prec] = {"value": q["value"], "ms_per_step": q["ms"] / args.steps, "dtype": DTYPE[prec],
+                      "err_vs_oracle": q["err"], "e2e": q.get("e2e"), "roofline": rf, "kernel_share": sh,
+                      "gpu_launches": q["launches"], "clocks": q["clocks"], "nfail_timed": q["nfail"]}
+        line[f"speedup_{head}_vs_{prec}"] = r["value"] / q["value"]
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
     return 0
 
 
-# FP64 floating-point operations per zone of each kernel group, counted from
-# ncu's executed DFMA/DADD/DMUL instruction totals (2 flops per FMA) on the
-# torus workload, divided by the zones a launch processes.
+# Executed FP64 floating-point operations per zone of a kernel group,
+# (precision, group) -> 2 DFMA + DADD + DMUL per zone from ncu instruction
+# counts on the torus (192x96x64 case), divided by the zones of a launch.
 FP64_FLOPS_PER_ZONE: dict = {}
-# dram read + write bytes per launch of each group from one ncu capture
+# (precision, group) -> dram read + write bytes per launch of the full
+# workload from one ncu capture (scaled by zones from the 192x96x64 case).
 TRAFFIC_PER_LAUNCH: dict = {}
 
 
-def cpu_leg(cfg, P0, dt, Ug, Pg):
+def cpu_leg(cfg, P0, dt):
     """The oracle as it stands on the host cores: one full step of the same
-    workload from the same state (bounded sample: one step), plus the GPU
-    path's 1-step error against it."""
-    import numpy as np
-
+    workload from the same state (the bounded sample is one step)."""
     import oracle
-    from paper_2408_01361_gb300 import inputs
 
     oracle.build()
     cores = os.cpu_count() or 1
@@ -349,19 +376,27 @@ def cpu_leg(cfg, P0, dt, Ug, Pg):
     Uo, Po, dto, st = oracle.step(cfg, U0, P0, dt)
     el = time.perf_counter() - t0
     nz = cfg["n1"] * cfg["n2"] * cfg["n3"]
+    cpu = {"value": nz / el, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+           "sample": f"1 two-stage step of the full {cfg['n1']}x{cfg['n2']}x{cfg['n3']} torus ({el:.1f} s)"}
+    return {"U": Uo, "P": Po, "dt": dt}, cpu
+
+
+def err_vs(cfg, Ug, Pg, ref):
+    """Relative L1 per variable of the GPU's one-step state against the oracle's."""
+    import numpy as np
+
+    from paper_2408_01361_gb300 import inputs
+
     sl = (slice(None),) + inputs.interior(cfg)
     errs = {}
-    for name, a, b in (("U", Ug[sl], Uo[sl]), ("P", Pg[sl], Po[sl])):
+    for name, a, b in (("U", Ug[sl], ref["U"][sl]), ("P", Pg[sl], ref["P"][sl])):
         e = []
         for v in range(8):
             den = np.abs(b[v]).sum()
             e.append(float(np.abs(a[v] - b[v]).sum() / den) if den > 0 else float(np.abs(a[v]).sum()))
         errs[name] = e
-    cpu = {"value": nz / el, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
-           "sample": f"1 two-stage step of the full {cfg['n1']}x{cfg['n2']}x{cfg['n3']} torus ({el:.1f} s)"}
-    err = {"rel_l1_per_var": errs, "max": max(max(errs["U"]), max(errs["P"])),
-           "how": "1 step from the same state and dt, GPU FP64 path vs FP64 oracle"}
-    return cpu, err
+    return {"rel_l1_per_var": errs, "max": max(max(errs["U"]), max(errs["P"])),
+            "how": "1 step from the same state and dt vs the FP64 oracle"}
 
 
 def main():

@@ -19,7 +19,7 @@ struct kh_ctx {
   cudaStream_t stream;
   double* geo;
   double* conn;
-  double* rad;
+  double* flo;     // geometric floors of rho and u per (i, j)
   double* pstar;   // 8 planes: stage-1 output
   double* F[3];    // 8 planes each
   double* ctop[3];
@@ -30,6 +30,16 @@ struct kh_ctx {
   double* dscalar;              // [0] dt, [1..2] divb max/sum
   unsigned long long* counters; // NCNT
   double* dirichlet[2];
+  // mixed precision (KH_MIXED): FP32 geometry copy, FP32 flux pass buffers,
+  // FP32 stage-1 output and FP32 Dirichlet ghosts
+  float* geof;
+  float* connf;
+  float* pstarf;   // 8 planes
+  float* pnf;      // 8 planes: FP32 copy of the ghost-filled stage-1 input
+  float* Ff[3];    // 8 planes each
+  float* ctopf[3];
+  float* emff[3];
+  float* dirichletf[2];
   long long launches;
   kh_stats last;
   // optional per-kernel-group timing (CUDA events on the context stream)
@@ -53,7 +63,7 @@ int cuda_fail(cudaError_t e) {
     if (_rc != KH_OK) return _rc;         \
   } while (0)
 
-DevGeom devgeom(const kh_ctx* x) { return DevGeom{x->geo, x->conn, x->rad}; }
+DevGeom devgeom(const kh_ctx* x) { return DevGeom{x->geo, x->conn, x->flo}; }
 
 Vars vars_of(const kh_ctx* x, double* P, double* B) {
   Vars v;
@@ -102,35 +112,90 @@ int check_launch(kh_ctx* x, int n) {
 }
 
 void free_all(kh_ctx* x) {
-  void* ptrs[] = {x->geo, x->conn, x->rad, x->pstar, x->F[0], x->F[1], x->F[2], x->ctop[0], x->ctop[1],
+  void* ptrs[] = {x->geo, x->conn, x->flo, x->pstar, x->F[0], x->F[1], x->F[2], x->ctop[0], x->ctop[1],
                   x->ctop[2], x->emf[0], x->emf[1], x->emf[2], x->pflag, x->partial, x->dscalar,
-                  x->counters, x->dirichlet[0], x->dirichlet[1]};
+                  x->counters, x->dirichlet[0], x->dirichlet[1], x->geof, x->connf, x->pstarf, x->pnf, x->Ff[0],
+                  x->Ff[1], x->Ff[2], x->ctopf[0], x->ctopf[1], x->ctopf[2], x->emff[0], x->emff[1],
+                  x->emff[2], x->dirichletf[0], x->dirichletf[1]};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
 
-// One stage: ghost fill, fluxes per direction, Flux-CT, update, fixup.
+GeomT<float> geomf(const kh_ctx* x) { return GeomT<float>{x->geof, x->connf, x->flo}; }
+
+// One FP64 stage: ghost fill, fluxes per direction, Flux-CT, update, fixup.
 int run_stage(kh_ctx* x, int st, const double* U0, const Vars& Pin, const Vars& Pout, double* Uout, double cdt) {
   const Layout& L = x->L;
   const DevGeom G = devgeom(x);
   cudaStream_t s = x->stream;
   int n = 0;
   mark(x, KH_T_BC, st, 0);
-  n += launch_bc(Pin, L, x->S, x->dirichlet[0], x->dirichlet[1], s);
+  n += launch_bc<double>(Pin, L, x->S, x->dirichlet[0], x->dirichlet[1], s);
   mark(x, KH_T_BC, st, 1);
   for (int d = 1; d <= L.ndim; ++d) {
     mark(x, KH_T_FLUX1 + d - 1, st, 0);
-    n += launch_flux_dir(d, cview(Pin), L, G, x->S, x->F[d - 1], x->ctop[d - 1], s);
+    n += launch_flux_dir<double, double>(d, cview(Pin), L, G, x->S, x->F[d - 1], x->ctop[d - 1], s);
     mark(x, KH_T_FLUX1 + d - 1, st, 1);
   }
   mark(x, KH_T_CT, st, 0);
-  n += launch_ct(x->F, x->emf, L, s);
+  n += launch_ct<double>(x->F, x->emf, L, s);
   mark(x, KH_T_CT, st, 1);
   mark(x, KH_T_UPDATE, st, 0);
   n += launch_update(U0, cview(Pin), Pout, Uout, x->F, L, G, x->S, cdt, x->pflag, x->counters, s);
   mark(x, KH_T_UPDATE, st, 1);
   mark(x, KH_T_FIXUP, st, 0);
-  n += launch_fixup(Pout, Uout, x->pflag, L, G, x->S, x->counters, s);
+  n += launch_fixup<double>(Pout, Uout, x->pflag, L, G, x->S, x->counters, s);
+  mark(x, KH_T_FIXUP, st, 1);
+  return n;
+}
+
+template <class T> CVarsT<T> cviewT(const VarsT<T>& v) {
+  CVarsT<T> c;
+  for (int q = 0; q < NV; ++q) c.v[q] = v.v[q];
+  return c;
+}
+
+// One mixed stage. Stage 1 (st = 0): FP64 input (ghost-filled in FP64) read
+// by the FP32 flux pass, output to the FP32 shadow P*. Stage 2 (st = 1): the
+// FP32 shadow (ghost-filled in FP32) as input, FP64 output and U.
+template <class TIN>
+int run_stage_mixed(kh_ctx* x, int st, const double* U0, const VarsT<TIN>& Pin, const TIN* dlo, const TIN* dhi,
+                    const Vars& Pout64, const VarsT<float>& Pout32, double* Uout, double cdt) {
+  const Layout& L = x->L;
+  const DevGeom G = devgeom(x);
+  const GeomT<float> Gf = geomf(x);
+  cudaStream_t s = x->stream;
+  int n = 0;
+  mark(x, KH_T_BC, st, 0);
+  n += launch_bc<TIN>(Pin, L, x->S, dlo, dhi, s);
+  // The stencil pass reads FP32: an FP64 input is converted once per cell
+  // here (on GB300 a double->float conversion issues on the FP64 pipe, so
+  // converting inside the 6-point stencils would cost 6x more of it).
+  VarsT<float> Pf;
+  if constexpr (sizeof(TIN) == sizeof(double)) {
+    for (int q = 0; q < NV; ++q) Pf.v[q] = x->pnf + q * L.plane;
+    n += launch_vars_to_f32(cviewT(Pin), Pf, L, s);
+  } else {
+    Pf = Pin;
+  }
+  mark(x, KH_T_BC, st, 1);
+  for (int d = 1; d <= L.ndim; ++d) {
+    mark(x, KH_T_FLUX1 + d - 1, st, 0);
+    n += launch_flux_dir<float, float>(d, cviewT(Pf), L, Gf, x->S, x->Ff[d - 1], x->ctopf[d - 1], s);
+    mark(x, KH_T_FLUX1 + d - 1, st, 1);
+  }
+  mark(x, KH_T_CT, st, 0);
+  n += launch_ct<float>(x->Ff, x->emff, L, s);
+  mark(x, KH_T_CT, st, 1);
+  mark(x, KH_T_UPDATE, st, 0);
+  n += launch_update_mixed<TIN>(U0, cviewT(Pin), Pout64, Pout32, Uout, x->Ff, L, G, Gf, x->S, cdt, x->pflag,
+                                x->counters, s);
+  mark(x, KH_T_UPDATE, st, 1);
+  mark(x, KH_T_FIXUP, st, 0);
+  if (Pout64.v[0])
+    n += launch_fixup<double>(Pout64, Uout, x->pflag, L, G, x->S, x->counters, s);
+  else
+    n += launch_fixup<float>(Pout32, Uout, x->pflag, L, G, x->S, x->counters, s);
   mark(x, KH_T_FIXUP, st, 1);
   return n;
 }
@@ -156,7 +221,7 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
   if (c->kind < KH_MINKOWSKI || c->kind > KH_FMKS) return KH_EINVAL;
   if (c->n1 < 4 || c->n2 < 4 || c->n3 < 1) return KH_EINVAL;
   if (c->recon != KH_RECON_MC && c->recon != KH_RECON_WENO5) return KH_EINVAL;
-  if (c->precision != KH_FP64) return KH_EINVAL;
+  if (c->precision != KH_FP64 && c->precision != KH_MIXED) return KH_EINVAL;
   if (!(gamma > 1.0) || !(c->cfl > 0.0) || !(fabs(a) < 1.0)) return KH_EINVAL;
   if (!(c->x1max > c->x1min) || !(c->x2max > c->x2min) || !(c->x3max > c->x3min)) return KH_EINVAL;
   for (int q = 0; q < 6; ++q) {
@@ -222,16 +287,38 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
   }
   KH_ALLOC(x->geo, 3 * NGEO * gp);
   KH_ALLOC(x->conn, NCONN * gp);
-  KH_ALLOC(x->rad, gp);
+  KH_ALLOC(x->flo, 2 * gp);
+  const bool mixed = c->precision == KH_MIXED;
+  const size_t plf = (size_t)L.plane * sizeof(float);
+  const size_t gpf = (size_t)L.gplane * sizeof(float);
   KH_ALLOC(x->pstar, NV * pl);
-  for (int d = 0; d < L.ndim; ++d) {
-    KH_ALLOC(x->F[d], NV * pl);
-    KH_ALLOC(x->ctop[d], pl);
-  }
-  KH_ALLOC(x->emf[2], pl);
-  if (L.ndim == 3) {
-    KH_ALLOC(x->emf[0], pl);
-    KH_ALLOC(x->emf[1], pl);
+  if (!mixed) {
+    for (int d = 0; d < L.ndim; ++d) {
+      KH_ALLOC(x->F[d], NV * pl);
+      KH_ALLOC(x->ctop[d], pl);
+    }
+    KH_ALLOC(x->emf[2], pl);
+    if (L.ndim == 3) {
+      KH_ALLOC(x->emf[0], pl);
+      KH_ALLOC(x->emf[1], pl);
+    }
+  } else {
+    KH_ALLOC(x->geof, 3 * NGEO * gpf);
+    KH_ALLOC(x->connf, NCONN * gpf);
+    KH_ALLOC(x->pstarf, NV * plf);
+    KH_ALLOC(x->pnf, NV * plf);
+    for (int d = 0; d < L.ndim; ++d) {
+      KH_ALLOC(x->Ff[d], NV * plf);
+      KH_ALLOC(x->ctopf[d], plf);
+    }
+    KH_ALLOC(x->emff[2], plf);
+    if (L.ndim == 3) {
+      KH_ALLOC(x->emff[0], plf);
+      KH_ALLOC(x->emff[1], plf);
+    }
+    for (int f = 0; f < 2; ++f)
+      if (c->bc[f] == KH_BC_DIRICHLET)
+        KH_ALLOC(x->dirichletf[f], (size_t)NV * L.n3s * L.n2s * L.ng * sizeof(float));
   }
   KH_ALLOC(x->pflag, (size_t)L.plane);
   KH_ALLOC(x->partial, 2 * (size_t)x->npartial * sizeof(double));
@@ -242,16 +329,23 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
 #undef KH_ALLOC
   if (rc == KH_OK) {
     // zero-initialise scratch so that never-written face entries are finite
-    for (int d = 0; d < L.ndim && rc == KH_OK; ++d) {
-      rc = cuda_fail(cudaMemset(x->F[d], 0, NV * pl));
-      if (rc == KH_OK) rc = cuda_fail(cudaMemset(x->ctop[d], 0, pl));
+    for (int d = 0; d < 3 && rc == KH_OK; ++d) {
+      if (x->F[d]) rc = cuda_fail(cudaMemset(x->F[d], 0, NV * pl));
+      if (rc == KH_OK && x->ctop[d]) rc = cuda_fail(cudaMemset(x->ctop[d], 0, pl));
+      if (rc == KH_OK && x->emf[d]) rc = cuda_fail(cudaMemset(x->emf[d], 0, pl));
+      if (rc == KH_OK && x->Ff[d]) rc = cuda_fail(cudaMemset(x->Ff[d], 0, NV * plf));
+      if (rc == KH_OK && x->ctopf[d]) rc = cuda_fail(cudaMemset(x->ctopf[d], 0, plf));
+      if (rc == KH_OK && x->emff[d]) rc = cuda_fail(cudaMemset(x->emff[d], 0, plf));
     }
-    for (int d = 0; d < 3 && rc == KH_OK; ++d)
-      if (x->emf[d]) rc = cuda_fail(cudaMemset(x->emf[d], 0, pl));
     if (rc == KH_OK) rc = cuda_fail(cudaMemset(x->pstar, 0, NV * pl));
+    if (rc == KH_OK && x->pstarf) rc = cuda_fail(cudaMemset(x->pstarf, 0, NV * plf));
   }
   if (rc == KH_OK) {
-    x->launches += launch_geometry(x->cp, c->x2min, L, x->geo, x->conn, x->rad, 0);
+    x->launches += launch_geometry(x->cp, c->x2min, S.fl, L, x->geo, x->conn, x->flo, 0);
+    if (mixed) {
+      x->launches += launch_to_f32(x->geo, x->geof, 3LL * NGEO * L.gplane, 0);
+      x->launches += launch_to_f32(x->conn, x->connf, (long long)NCONN * L.gplane, 0);
+    }
     rc = cuda_fail(cudaGetLastError());
     if (rc == KH_OK) rc = cuda_fail(cudaDeviceSynchronize());
   }
@@ -283,6 +377,11 @@ int kh_set_dirichlet(kh_ctx* x, int face, const double* PB) {
   if (!x || face < 0 || face > 1 || !PB || !x->dirichlet[face]) return KH_EINVAL;
   const size_t bytes = (size_t)NV * x->L.n3s * x->L.n2s * x->L.ng * sizeof(double);
   KH_TRY(cudaMemcpyAsync(x->dirichlet[face], PB, bytes, cudaMemcpyDeviceToDevice, x->stream));
+  if (x->dirichletf[face]) {
+    x->launches += launch_to_f32(x->dirichlet[face], x->dirichletf[face],
+                                 (long long)NV * x->L.n3s * x->L.n2s * x->L.ng, x->stream);
+    KH_TRY(cudaGetLastError());
+  }
   return KH_OK;
 }
 
@@ -308,13 +407,19 @@ int kh_cons_to_prim(kh_ctx* x, const double* U, double* P, double* B, int8_t* pf
 
 int kh_fill_ghosts(kh_ctx* x, double* P, double* B) {
   if (!x || !P || !B) return KH_EINVAL;
-  return check_launch(x, launch_bc(vars_of(x, P, B), x->L, x->S, x->dirichlet[0], x->dirichlet[1], x->stream));
+  return check_launch(x, launch_bc<double>(vars_of(x, P, B), x->L, x->S, x->dirichlet[0], x->dirichlet[1], x->stream));
 }
 
 int kh_fluxes(kh_ctx* x, const double* P, const double* B, double* F1, double* F2, double* F3) {
   if (!x || !P || !B || !F1 || !F2 || (x->L.ndim == 3 && !F3)) return KH_EINVAL;
+  if (x->c.precision != KH_FP64) return KH_EINVAL;  // FP64 diagnostic
   double* const F[3] = {F1, F2, x->L.ndim == 3 ? F3 : x->F[2]};
-  return check_launch(x, launch_fluxes(cvars_of(x, P, B), x->L, devgeom(x), x->S, F, x->ctop, x->emf, x->stream));
+  int n = 0;
+  for (int d = 1; d <= x->L.ndim; ++d)
+    n += launch_flux_dir<double, double>(d, cvars_of(x, P, B), x->L, devgeom(x), x->S, F[d - 1], x->ctop[d - 1],
+                                         x->stream);
+  n += launch_ct<double>(F, x->emf, x->L, x->stream);
+  return check_launch(x, n);
 }
 
 int kh_step(kh_ctx* x, double* U, double* P, double* B, double dt, double* dt_cfl) {
@@ -326,12 +431,28 @@ int kh_step(kh_ctx* x, double* U, double* P, double* B, double dt, double* dt_cf
   Vars Ps;
   for (int q = 0; q < NV; ++q) Ps.v[q] = x->pstar + q * L.plane;
   int n = 0;
-  // stage 1: P^n -> P* (U* is not stored); stage 2: P* -> P^{n+1}, U^{n+1} in place
-  n += run_stage(x, 0, U, Pn, Ps, nullptr, 0.5 * dt);
-  n += run_stage(x, 1, U, Ps, Pn, U, dt);
-  mark(x, KH_T_CFL, 1, 0);
-  n += launch_cfl(x->ctop, L, x->S.cfl, x->partial, x->npartial, x->dscalar, s);
-  mark(x, KH_T_CFL, 1, 1);
+  if (x->c.precision == KH_FP64) {
+    // stage 1: P^n -> P* (U* is not stored); stage 2: P* -> P^{n+1}, U^{n+1} in place
+    n += run_stage(x, 0, U, Pn, Ps, nullptr, 0.5 * dt);
+    n += run_stage(x, 1, U, Ps, Pn, U, dt);
+    mark(x, KH_T_CFL, 1, 0);
+    n += launch_cfl<double>(x->ctop, L, x->S.cfl, x->partial, x->npartial, x->dscalar, s);
+    mark(x, KH_T_CFL, 1, 1);
+  } else {
+    // stage 1: FP64 P^n -> FP32 shadow P*; stage 2: FP32 P* -> FP64 P^{n+1}, U^{n+1}
+    VarsT<float> Psf, nof;
+    Vars no64;
+    for (int q = 0; q < NV; ++q) {
+      Psf.v[q] = x->pstarf + q * L.plane;
+      nof.v[q] = nullptr;
+      no64.v[q] = nullptr;
+    }
+    n += run_stage_mixed<double>(x, 0, U, Pn, x->dirichlet[0], x->dirichlet[1], no64, Psf, nullptr, 0.5 * dt);
+    n += run_stage_mixed<float>(x, 1, U, Psf, x->dirichletf[0], x->dirichletf[1], Pn, nof, U, dt);
+    mark(x, KH_T_CFL, 1, 0);
+    n += launch_cfl<float>(x->ctopf, L, x->S.cfl, x->partial, x->npartial, x->dscalar, s);
+    mark(x, KH_T_CFL, 1, 1);
+  }
   int rc = check_launch(x, n);
   if (rc != KH_OK) return rc;
   if (!dt_cfl && !x->profiling) return KH_OK;
@@ -399,9 +520,16 @@ int kh_cfl_dt(kh_ctx* x, const double* P, const double* B, double* dt_cfl) {
   KH_TRY(cudaMemcpyAsync(x->pstar + 5 * L.plane, B, 3 * pl, cudaMemcpyDeviceToDevice, s));
   Vars Ps;
   for (int q = 0; q < NV; ++q) Ps.v[q] = x->pstar + q * L.plane;
-  int n = launch_bc(Ps, L, x->S, x->dirichlet[0], x->dirichlet[1], s);
-  n += launch_fluxes(cview(Ps), L, devgeom(x), x->S, x->F, x->ctop, x->emf, s);
-  n += launch_cfl(x->ctop, L, x->S.cfl, x->partial, x->npartial, x->dscalar, s);
+  int n = launch_bc<double>(Ps, L, x->S, x->dirichlet[0], x->dirichlet[1], s);
+  if (x->c.precision == KH_FP64) {
+    for (int d = 1; d <= L.ndim; ++d)
+      n += launch_flux_dir<double, double>(d, cview(Ps), L, devgeom(x), x->S, x->F[d - 1], x->ctop[d - 1], s);
+    n += launch_cfl<double>(x->ctop, L, x->S.cfl, x->partial, x->npartial, x->dscalar, s);
+  } else {
+    for (int d = 1; d <= L.ndim; ++d)
+      n += launch_flux_dir<double, float>(d, cview(Ps), L, geomf(x), x->S, x->Ff[d - 1], x->ctopf[d - 1], s);
+    n += launch_cfl<float>(x->ctopf, L, x->S.cfl, x->partial, x->npartial, x->dscalar, s);
+  }
   int rc = check_launch(x, n);
   if (rc != KH_OK) return rc;
   KH_TRY(cudaMemcpyAsync(dt_cfl, x->dscalar, sizeof(double), cudaMemcpyDeviceToHost, s));

@@ -14,7 +14,7 @@ constexpr int NGEO = 22;  // per location: gcov (10 symmetric), gcon (10), gdet,
 constexpr int NCONN = 40; // Gamma^l_{mn}: 4 x 10 symmetric pairs
 enum { LOC_CENT = 0, LOC_F1 = 1, LOC_F2 = 2 };
 
-// Symmetric-pair index of (m, n), m <= n: 00 01 02 03 11 12 13 22 23 33.
+// Symmetric-pair index of (m, n): 00 01 02 03 11 12 13 22 23 33.
 KH_HD int sym_index(int m, int n) {
   if (m > n) { int t = m; m = n; n = t; }
   return m == 0 ? n : (m == 1 ? 3 + n : (m == 2 ? 5 + n : 9));
@@ -31,18 +31,23 @@ struct Layout {
   KH_HD long long at(int k, int j, int i) const { return ((long long)k * n2s + j) * n1s + i; }
 };
 
-struct Vars {
-  double* v[NV];
+// Pointers to the 8 primitive planes (5 fluid + 3 field) of one state.
+template <class T> struct VarsT {
+  T* v[NV];
 };
-struct CVars {
-  const double* v[NV];
+template <class T> struct CVarsT {
+  const T* v[NV];
 };
+using Vars = VarsT<double>;
+using CVars = CVarsT<double>;
 
-struct DevGeom {
-  const double* g;     // [3][NGEO][n2s][n1s]
-  const double* conn;  // [NCONN][n2s][n1s]
-  const double* rad;   // [n2s][n1s], r at cell centres (1 for Minkowski)
+// Geometry cache in precision T (the FP64 cache and its FP32 copy).
+template <class T> struct GeomT {
+  const T* g;          // [3][NGEO][n2s][n1s]
+  const T* conn;       // [NCONN][n2s][n1s]
+  const double* flo;   // [2][n2s][n1s]: geometric floors of rho and u at cell centres
 };
+using DevGeom = GeomT<double>;
 
 struct Scheme {
   double gam;
@@ -56,26 +61,43 @@ struct Scheme {
 // Counters kept on the device for one step.
 enum { CNT_FAIL = 0, CNT_FLOOR = 1, CNT_UNFIXED = 2, NCNT = 3 };
 
-// ---- launchers (kh_kernels.cu); all return the number of kernels launched ----
-int launch_geometry(const CoordParams& cp, double x2min, const Layout& L, double* geo, double* conn, double* rad, cudaStream_t s);
-int launch_bc(const Vars& P, const Layout& L, const Scheme& S, const double* dlo, const double* dhi, cudaStream_t s);
-int launch_fluxes(const CVars& P, const Layout& L, const DevGeom& G, const Scheme& S, double* const F[3],
-                  double* const ctop[3], double* const emf[3], cudaStream_t s);
-int launch_flux_dir(int D, const CVars& P, const Layout& L, const DevGeom& G, const Scheme& S, double* F,
-                    double* ctop, cudaStream_t s);
-int launch_ct(double* const F[3], double* const emf[3], const Layout& L, cudaStream_t s);
+// ---- launchers (kh_kernels.cu); each returns the number of kernels launched ----
+int launch_geometry(const CoordParams& cp, double x2min, const FloorParams& fl, const Layout& L, double* geo,
+                    double* conn, double* flo, cudaStream_t s);
+template <class T>
+int launch_bc(const VarsT<T>& P, const Layout& L, const Scheme& S, const T* dlo, const T* dhi, cudaStream_t s);
+// Reconstruction + LLF through x^D faces: stencil read in TIN, arithmetic and
+// outputs in R (FP64 path: double/double; mixed: double or float in, float out).
+template <class TIN, class R>
+int launch_flux_dir(int D, const CVarsT<TIN>& P, const Layout& L, const GeomT<R>& G, const Scheme& S, R* F, R* ctop,
+                    cudaStream_t s);
+template <class R> int launch_ct(R* const F[3], R* const emf[3], const Layout& L, cudaStream_t s);
 int launch_update(const double* U0, const CVars& Pin, const Vars& Pout, double* Uout, double* const F[3],
                   const Layout& L, const DevGeom& G, const Scheme& S, double cdt, int8_t* pflag,
                   unsigned long long* cnt, cudaStream_t s);
-int launch_fixup(const Vars& P, double* Uout, const int8_t* pflag, const Layout& L, const DevGeom& G,
+// Mixed update: FP32 fluxes and sources, FP64 accumulation of U and FP64
+// inversion; the stage input (sources and inversion guess) is read in TIN.
+// Writes the FP64 output (Pout64.v[0] may be null) and/or its FP32 shadow
+// (Pout32.v[0] may be null), and U when Uout is given (stage 2).
+template <class TIN>
+int launch_update_mixed(const double* U0, const CVarsT<TIN>& Pin, const Vars& Pout64, const VarsT<float>& Pout32,
+                        double* Uout, float* const F[3], const Layout& L, const DevGeom& G, const GeomT<float>& Gf,
+                        const Scheme& S, double cdt, int8_t* pflag, unsigned long long* cnt, cudaStream_t s);
+template <class T>
+int launch_fixup(const VarsT<T>& P, double* Uout, const int8_t* pflag, const Layout& L, const DevGeom& G,
                  const Scheme& S, unsigned long long* cnt, cudaStream_t s);
-int launch_cfl(double* const ctop[3], const Layout& L, double cfl, double* partial, int npartial, double* dt_out,
+template <class T>
+int launch_cfl(T* const ctop[3], const Layout& L, double cfl, double* partial, int npartial, double* dt_out,
                cudaStream_t s);
 int launch_divb(const double* const B[3], const Layout& L, const DevGeom& G, double* partial, int npartial,
                 double* out2, cudaStream_t s);
 int launch_p2c(const CVars& P, double* U, const Layout& L, const DevGeom& G, const Scheme& S, cudaStream_t s);
 int launch_c2p(const double* U, const Vars& P, int8_t* pflag, const Layout& L, const DevGeom& G, const Scheme& S,
                unsigned long long* cnt, cudaStream_t s);
+// Element-wise FP64 -> FP32 copy of n values.
+int launch_to_f32(const double* src, float* dst, long long n, cudaStream_t s);
+// FP64 -> FP32 copy of the 8 primitive planes (every cell of the allocation).
+int launch_vars_to_f32(const CVars& src, const VarsT<float>& dst, const Layout& L, cudaStream_t s);
 
 // Blocks used by the reductions (partial buffers hold 2 doubles per block).
 constexpr int RED_THREADS = 256;

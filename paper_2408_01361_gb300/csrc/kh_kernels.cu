@@ -17,10 +17,11 @@ constexpr int TPB = 128;
 
 inline int nblocks(long long n, int tpb) { return (int)((n + tpb - 1) / tpb); }
 
-__device__ __forceinline__ Met<double> load_met(const DevGeom& G, long long gplane, int loc, long long p) {
-  const double* b = G.g + (long long)loc * NGEO * gplane + p;
-  Met<double> m;
-  double c[10], u[10];
+template <class R>
+__device__ __forceinline__ Met<R> load_met(const GeomT<R>& G, long long gplane, int loc, long long p) {
+  const R* b = G.g + (long long)loc * NGEO * gplane + p;
+  Met<R> m;
+  R c[10], u[10];
 #pragma unroll
   for (int q = 0; q < 10; ++q) {
     c[q] = __ldg(b + q * gplane);
@@ -42,7 +43,8 @@ __device__ __forceinline__ Met<double> load_met(const DevGeom& G, long long gpla
 // Geometry cache: one thread per (j, i) of the allocation. Metric, inverse,
 // sqrt(-g), lapse at CENT, x1 face and x2 face; connection and r at CENT.
 // ---------------------------------------------------------------------------
-__global__ void k_geometry(CoordParams cp, double x2min, Layout L, double* geo, double* conn, double* rad) {
+__global__ void k_geometry(CoordParams cp, double x2min, FloorParams fl, Layout L, double* geo, double* conn,
+                           double* flo) {
   const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= L.gplane) return;
   const int i = (int)(p % L.n1s), j = (int)(p / L.n1s);
@@ -70,7 +72,9 @@ __global__ void k_geometry(CoordParams cp, double x2min, Layout L, double* geo, 
       for (int l = 0; l < 4; ++l)
         for (int m = 0; m < 4; ++m)
           for (int n = m; n < 4; ++n) conn[(l * 10 + sym_index(m, n)) * L.gplane + p] = G[l][m][n];
-      rad[p] = (cp.kind == COORD_MINKOWSKI) ? 1.0 : coord_map(cp, x1c, x2c).r;
+      const double r = (cp.kind == COORD_MINKOWSKI) ? 1.0 : coord_map(cp, x1c, x2c).r;
+      flo[p] = fmax(fl.rho_min * pow(r, -1.5), 1e-20);
+      flo[L.gplane + p] = fmax(fl.u_min * pow(r, -2.5), 1e-20);
     }
   }
 }
@@ -80,7 +84,8 @@ __global__ void k_geometry(CoordParams cp, double x2min, Layout L, double* geo, 
 // ghosts over all i and interior k; x3 ghosts over all (i, j): edges and
 // corners are compositions of the face rules (three launches, in order).
 // ---------------------------------------------------------------------------
-__global__ void k_bc_x1(Vars P, Layout L, Scheme S, const double* dlo, const double* dhi) {
+template <class T>
+__global__ void k_bc_x1(VarsT<T> P, Layout L, Scheme S, const T* dlo, const T* dhi) {
   const int nj = L.e[1] - L.s[1], nk = L.e[2] - L.s[2];
   const long long tot = (long long)nj * nk * L.ng * 2;
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -93,8 +98,9 @@ __global__ void k_bc_x1(Vars P, Layout L, Scheme S, const double* dlo, const dou
   const int bc = S.bc[side];
   const long long dst = L.at(k, j, ig);
   if (bc == KH_BC_DIRICHLET) {
-    const double* D = side == 0 ? dlo : dhi;
+    const T* D = side == 0 ? dlo : dhi;
     const int ii = side == 0 ? ig : ig - (L.ng + L.n1);
+#pragma unroll
     for (int v = 0; v < NV; ++v) P.v[v][dst] = D[(((long long)v * L.n3s + k) * L.n2s + j) * L.ng + ii];
     return;
   }
@@ -106,16 +112,18 @@ __global__ void k_bc_x1(Vars P, Layout L, Scheme S, const double* dlo, const dou
   else  // reflection (not used on x1 faces by the supported problems)
     src = side == 0 ? 2 * L.ng - 1 - ig : 2 * (L.ng + L.n1) - 1 - ig;
   const long long s = L.at(k, j, src);
+#pragma unroll
   for (int v = 0; v < NV; ++v) P.v[v][dst] = P.v[v][s];
   if (bc == KH_BC_OUTFLOW) {
-    double u1 = P.v[V_U1][dst];
-    if (side == 0 && u1 > 0.0) u1 = 0.0;
-    if (side == 1 && u1 < 0.0) u1 = 0.0;
+    T u1 = P.v[V_U1][dst];
+    if (side == 0 && u1 > T(0)) u1 = T(0);
+    if (side == 1 && u1 < T(0)) u1 = T(0);
     P.v[V_U1][dst] = u1;
   }
 }
 
-__global__ void k_bc_x2(Vars P, Layout L, Scheme S) {
+template <class T>
+__global__ void k_bc_x2(VarsT<T> P, Layout L, Scheme S) {
   const int nk = L.e[2] - L.s[2];
   const long long tot = (long long)L.N1 * nk * L.ng * 2;
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -135,13 +143,15 @@ __global__ void k_bc_x2(Vars P, Layout L, Scheme S) {
     src = side == 0 ? 2 * L.ng - 1 - jg : 2 * (L.ng + L.n2) - 1 - jg;
   const long long s = L.at(k, src, i), d = L.at(k, jg, i);
   const bool flip = (bc == KH_BC_POLAR);
+#pragma unroll
   for (int v = 0; v < NV; ++v) {
-    const double x = P.v[v][s];
+    const T x = P.v[v][s];
     P.v[v][d] = (flip && (v == V_U2 || v == V_B2)) ? -x : x;
   }
 }
 
-__global__ void k_bc_x3(Vars P, Layout L, Scheme S) {
+template <class T>
+__global__ void k_bc_x3(VarsT<T> P, Layout L, Scheme S) {
   const long long tot = (long long)L.N1 * L.N2 * L.ng3 * 2;
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= tot) return;
@@ -154,6 +164,7 @@ __global__ void k_bc_x3(Vars P, Layout L, Scheme S) {
   const int src = (bc == KH_BC_PERIODIC) ? (side == 0 ? kg + L.n3 : kg - L.n3)
                                           : (side == 0 ? L.ng3 : L.ng3 + L.n3 - 1);
   const long long s = L.at(src, j, i), d = L.at(kg, j, i);
+#pragma unroll
   for (int v = 0; v < NV; ++v) P.v[v][d] = P.v[v][s];
 }
 
@@ -166,9 +177,9 @@ struct FaceBox {
   int n[3];
 };
 
-template <int D, int RECON>
-__global__ void __launch_bounds__(TPB) k_flux(CVars P, Layout L, DevGeom G, Scheme S, FaceBox box, double* F,
-                                             double* ctop, int polar_lo, int polar_hi) {
+template <int D, int RECON, class TIN, class R>
+__global__ void __launch_bounds__(TPB) k_flux(CVarsT<TIN> P, Layout L, GeomT<R> G, Scheme S, FaceBox box, R* F,
+                                             R* ctop, int polar_lo, int polar_hi) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long tot = (long long)box.n[0] * box.n[1] * box.n[2];
   if (t >= tot) return;
@@ -177,49 +188,50 @@ __global__ void __launch_bounds__(TPB) k_flux(CVars P, Layout L, DevGeom G, Sche
   const int k = box.lo[2] + (int)(t / ((long long)box.n[0] * box.n[1]));
   const long long c = L.at(k, j, i);
   const long long st = (D == 1) ? 1 : (D == 2 ? (long long)L.n1s : (long long)L.n1s * L.n2s);
-  double PL[NV], PR[NV];
+  R PL[NV], PR[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    const double* q = P.v[v] + c;
+    const TIN* q = P.v[v] + c;
     if (RECON == KH_RECON_MC) {
-      const double qm2 = __ldg(q - 2 * st), qm1 = __ldg(q - st), q0 = __ldg(q), qp1 = __ldg(q + st);
-      double lo, hi;
+      const R qm2 = (R)__ldg(q - 2 * st), qm1 = (R)__ldg(q - st), q0 = (R)__ldg(q), qp1 = (R)__ldg(q + st);
+      R lo, hi;
       recon_mc(qm2, qm1, q0, lo, hi);
       PL[v] = hi;
       recon_mc(qm1, q0, qp1, lo, hi);
       PR[v] = lo;
     } else {
-      const double qm3 = __ldg(q - 3 * st), qm2 = __ldg(q - 2 * st), qm1 = __ldg(q - st), q0 = __ldg(q);
-      const double qp1 = __ldg(q + st), qp2 = __ldg(q + 2 * st);
+      const R qm3 = (R)__ldg(q - 3 * st), qm2 = (R)__ldg(q - 2 * st), qm1 = (R)__ldg(q - st), q0 = (R)__ldg(q);
+      const R qp1 = (R)__ldg(q + st), qp2 = (R)__ldg(q + 2 * st);
       PL[v] = weno5_plus(qm3, qm2, qm1, q0, qp1);
       PR[v] = weno5_plus(qp2, qp1, q0, qm1, qm2);
     }
   }
-  const Met<double> m = load_met(G, L.gplane, D == 3 ? LOC_CENT : D, (long long)j * L.n1s + i);
-  FState<double> sL, sR;
+  const Met<R> m = load_met(G, L.gplane, D == 3 ? LOC_CENT : D, (long long)j * L.n1s + i);
+  const R gam = (R)S.gam;
+  FState<R> sL, sR;
   fluid_state(PL, m, sL);
   fluid_state(PR, m, sR);
-  double FL[NV], UL[NV], FR[NV], UR[NV];
-  flux_cons(PL, sL, m, S.gam, D, FL, UL);
-  flux_cons(PR, sR, m, S.gam, D, FR, UR);
-  double cmaxL, cminL, cmaxR, cminR;
-  signal_speeds(PL, sL, m, S.gam, D, cmaxL, cminL);
-  signal_speeds(PR, sR, m, S.gam, D, cmaxR, cminR);
-  double cm = fmax(0.0, fmax(cmaxL, cmaxR));
-  double cn = fmax(0.0, fmax(-cminL, -cminR));
-  const double ct = fmax(cm, cn);
+  R FL[NV], UL[NV], FR[NV], UR[NV];
+  flux_cons(PL, sL, m, gam, D, FL, UL);
+  flux_cons(PR, sR, m, gam, D, FR, UR);
+  R cmaxL, cminL, cmaxR, cminR;
+  signal_speeds(PL, sL, m, gam, D, cmaxL, cminL);
+  signal_speeds(PR, sR, m, gam, D, cmaxR, cminR);
+  const R cm = fmax(R(0), fmax(cmaxL, cmaxR));
+  const R cn = fmax(R(0), fmax(-cminL, -cminR));
+  const R ct = fmax(cm, cn);
   const bool axis = (D == 2) && ((polar_lo && j == L.s[1]) || (polar_hi && j == L.e[1]));
 #pragma unroll
   for (int v = 0; v < NV; ++v)
-    F[v * L.plane + c] = axis ? 0.0 : 0.5 * (FL[v] + FR[v]) - 0.5 * ct * (UR[v] - UL[v]);
+    F[v * L.plane + c] = axis ? R(0) : R(0.5) * (FL[v] + FR[v]) - R(0.5) * ct * (UR[v] - UL[v]);
   ctop[c] = ct;
 }
 
 // Corner EMFs of Flux-CT (Toth 2000) from the LLF field fluxes:
 //   e3(i-1/2, j-1/2) = (F1_B2(j) + F1_B2(j-1) - F2_B1(i) - F2_B1(i-1)) / 4 and
 //   cyclic e1 (x1-edges), e2 (x2-edges) in 3-D.
-__global__ void k_emf(const double* F1, const double* F2, const double* F3, double* e1, double* e2, double* e3,
-                      Layout L) {
+template <class R>
+__global__ void k_emf(const R* F1, const R* F2, const R* F3, R* e1, R* e2, R* e3, Layout L) {
   const int n0 = L.e[0] - L.s[0] + 1, n1 = L.e[1] - L.s[1] + 1, n2 = (L.ndim == 3) ? L.e[2] - L.s[2] + 1 : 1;
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= (long long)n0 * n1 * n2) return;
@@ -228,30 +240,31 @@ __global__ void k_emf(const double* F1, const double* F2, const double* F3, doub
   const int k = (L.ndim == 3 ? L.s[2] : 0) + (int)(t / ((long long)n0 * n1));
   const long long c = L.at(k, j, i);
   const long long P = L.plane, sj = L.n1s, sk = (long long)L.n1s * L.n2s;
-  const double* F1B2 = F1 + V_B2 * P;
-  const double* F2B1 = F2 + V_B1 * P;
+  const R q = R(0.25);
+  const R* F1B2 = F1 + V_B2 * P;
+  const R* F2B1 = F2 + V_B1 * P;
   if (L.ndim == 2) {
-    e3[c] = 0.25 * (F1B2[c] + F1B2[c - sj] - F2B1[c] - F2B1[c - 1]);
+    e3[c] = q * (F1B2[c] + F1B2[c - sj] - F2B1[c] - F2B1[c - 1]);
     return;
   }
-  if (k < L.e[2]) e3[c] = 0.25 * (F1B2[c] + F1B2[c - sj] - F2B1[c] - F2B1[c - 1]);
+  if (k < L.e[2]) e3[c] = q * (F1B2[c] + F1B2[c - sj] - F2B1[c] - F2B1[c - 1]);
   if (i < L.e[0]) {
-    const double* F2B3 = F2 + V_B3 * P;
-    const double* F3B2 = F3 + V_B2 * P;
-    e1[c] = 0.25 * (F2B3[c] + F2B3[c - sk] - F3B2[c] - F3B2[c - sj]);
+    const R* F2B3 = F2 + V_B3 * P;
+    const R* F3B2 = F3 + V_B2 * P;
+    e1[c] = q * (F2B3[c] + F2B3[c - sk] - F3B2[c] - F3B2[c - sj]);
   }
   if (j < L.e[1]) {
-    const double* F3B1 = F3 + V_B1 * P;
-    const double* F1B3 = F1 + V_B3 * P;
-    e2[c] = 0.25 * (F3B1[c] + F3B1[c - 1] - F1B3[c] - F1B3[c - sk]);
+    const R* F3B1 = F3 + V_B1 * P;
+    const R* F1B3 = F1 + V_B3 * P;
+    e2[c] = q * (F3B1[c] + F3B1[c - 1] - F1B3[c] - F1B3[c - sk]);
   }
 }
 
 // Field fluxes from edge EMFs (the other slots keep their LLF values):
 //   F1 = (0, (e3 + e3(j+1))/2, -(e2 + e2(k+1))/2), F2 = (-(e3 + e3(i+1))/2, 0, (e1 + e1(k+1))/2),
 //   F3 = ((e2 + e2(i+1))/2, -(e1 + e1(j+1))/2, 0); in 2-D only e3 and the B1, B2 slots.
-__global__ void k_apply_ct(double* F1, double* F2, double* F3, const double* e1, const double* e2,
-                           const double* e3, Layout L) {
+template <class R>
+__global__ void k_apply_ct(R* F1, R* F2, R* F3, const R* e1, const R* e2, const R* e3, Layout L) {
   const int n0 = L.e[0] - L.s[0] + 1, n1 = L.e[1] - L.s[1] + 1, n2 = (L.ndim == 3) ? L.e[2] - L.s[2] + 1 : 1;
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= (long long)n0 * n1 * n2) return;
@@ -262,20 +275,21 @@ __global__ void k_apply_ct(double* F1, double* F2, double* F3, const double* e1,
   const long long P = L.plane, sj = L.n1s, sk = (long long)L.n1s * L.n2s;
   const bool in_i = i < L.e[0], in_j = j < L.e[1];
   const bool in_k = (L.ndim == 2) || k < L.e[2];
+  const R h = R(0.5);
   if (in_j && in_k) {  // x1 faces
-    F1[V_B1 * P + c] = 0.0;
-    F1[V_B2 * P + c] = 0.5 * (e3[c] + e3[c + sj]);
-    if (L.ndim == 3) F1[V_B3 * P + c] = -0.5 * (e2[c] + e2[c + sk]);
+    F1[V_B1 * P + c] = R(0);
+    F1[V_B2 * P + c] = h * (e3[c] + e3[c + sj]);
+    if (L.ndim == 3) F1[V_B3 * P + c] = -h * (e2[c] + e2[c + sk]);
   }
   if (in_i && in_k) {  // x2 faces
-    F2[V_B1 * P + c] = -0.5 * (e3[c] + e3[c + 1]);
-    F2[V_B2 * P + c] = 0.0;
-    if (L.ndim == 3) F2[V_B3 * P + c] = 0.5 * (e1[c] + e1[c + sk]);
+    F2[V_B1 * P + c] = -h * (e3[c] + e3[c + 1]);
+    F2[V_B2 * P + c] = R(0);
+    if (L.ndim == 3) F2[V_B3 * P + c] = h * (e1[c] + e1[c + sk]);
   }
   if (L.ndim == 3 && in_i && in_j) {  // x3 faces
-    F3[V_B1 * P + c] = 0.5 * (e2[c] + e2[c + 1]);
-    F3[V_B2 * P + c] = -0.5 * (e1[c] + e1[c + sj]);
-    F3[V_B3 * P + c] = 0.0;
+    F3[V_B1 * P + c] = h * (e2[c] + e2[c + 1]);
+    F3[V_B2 * P + c] = -h * (e1[c] + e1[c + sj]);
+    F3[V_B3 * P + c] = R(0);
   }
 }
 
@@ -294,26 +308,28 @@ __device__ __forceinline__ long long nzones(const Layout& L) {
   return (long long)(L.e[0] - L.s[0]) * (L.e[1] - L.s[1]) * (L.e[2] - L.s[2]);
 }
 
-__device__ __forceinline__ void source_terms(const double* P, const Met<double>& m, const DevGeom& G,
-                                             long long gplane, long long p, double gam, double* S) {
-  FState<double> s;
+// S_nu = sqrt(-g) T^k_l Gamma^l_{nu k} for nu = t, 1, 2, 3 (energy and
+// momentum slots); zero for rho and B.
+template <class R>
+__device__ __forceinline__ void source_terms(const R* P, const Met<R>& m, const R* conn, long long gplane, long long p,
+                                             R gam, R* S) {
+  FState<R> s;
   fluid_state(P, m, s);
-  const double pg = (gam - 1.0) * P[V_U];
-  const double eta = P[V_RHO] + P[V_U] + pg + s.bsq;
-  const double ptot = pg + 0.5 * s.bsq;
-  double T[4][4];
+  const R pg = (gam - R(1)) * P[V_U];
+  const R eta = P[V_RHO] + P[V_U] + pg + s.bsq;
+  const R ptot = pg + R(0.5) * s.bsq;
+  R T[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) T[a][b] = eta * s.ucon[a] * s.ucov[b] - s.bcon[a] * s.bcov[b] + (a == b ? ptot : 0.0);
-  // S_nu = sqrt(-g) T^k_l Gamma^l_{nu k}
+    for (int b = 0; b < 4; ++b) T[a][b] = eta * s.ucon[a] * s.ucov[b] - s.bcon[a] * s.bcov[b] + (a == b ? ptot : R(0));
 #pragma unroll
   for (int nu = 0; nu < 4; ++nu) {
-    double acc = 0.0;
+    R acc = R(0);
 #pragma unroll
     for (int l = 0; l < 4; ++l)
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) acc += T[kk][l] * __ldg(G.conn + (l * 10 + sym_index(nu, kk)) * gplane + p);
+      for (int kk = 0; kk < 4; ++kk) acc += T[kk][l] * __ldg(conn + (l * 10 + sym_index(nu, kk)) * gplane + p);
     S[V_U + nu] = m.gdet * acc;
   }
 }
@@ -334,7 +350,7 @@ __global__ void __launch_bounds__(TPB) k_update(const double* U0, CVars Pin, Var
 #pragma unroll
   for (int v = 0; v < NV; ++v) P[v] = Pin.v[v][c];
   double Sv[NV] = {0, 0, 0, 0, 0, 0, 0, 0};
-  source_terms(P, m, G, L.gplane, p, S.gam, Sv);
+  source_terms(P, m, G.conn, L.gplane, p, S.gam, Sv);
   double U[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
@@ -353,9 +369,10 @@ __global__ void __launch_bounds__(TPB) k_update(const double* U0, CVars Pin, Var
   Pn[V_B3] = U[V_B3] * ig;
   int fmask = 0;
   if (flag == 0) {
-    fmask = apply_floors(S.fl, m, __ldg(G.rad + p), Pn);
+    FState<double> s;
+    fluid_state(Pn, m, s);
+    fmask = apply_floors(S.fl, m, __ldg(G.flo + p), __ldg(G.flo + L.gplane + p), s.bsq, Pn);
     if (fmask && Uout) {
-      FState<double> s;
       fluid_state(Pn, m, s);
       cons_only(Pn, s, m, S.gam, U);
     }
@@ -371,10 +388,103 @@ __global__ void __launch_bounds__(TPB) k_update(const double* U0, CVars Pin, Var
   if (fmask) atomicAdd(cnt + CNT_FLOOR, 1ULL);
 }
 
+// Mixed-precision update of one interior zone: the divergence of the FP32
+// fluxes and the FP32 source terms (FP32 metric and connection) give dU in
+// FP32; U = U0 + cdt dU is accumulated in FP64; the Noble-2D inversion and the
+// floors run in FP64 on the FP64 metric, the stage input serving as guess.
+template <class TIN>
+__global__ void __launch_bounds__(TPB) k_update_mixed(const double* U0, CVarsT<TIN> Pin, Vars Pout64,
+                                                     VarsT<float> Pout32, double* Uout, const float* F1,
+                                                     const float* F2, const float* F3, Layout L, DevGeom G,
+                                                     GeomT<float> Gf, Scheme S, double cdt, int8_t* pflag,
+                                                     unsigned long long* cnt) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= nzones(L)) return;
+  int i, j, k;
+  zone_ijk(L, t, i, j, k);
+  const long long c = L.at(k, j, i);
+  const long long p = (long long)j * L.n1s + i;
+  const long long sj = L.n1s, sk = (long long)L.n1s * L.n2s;
+  float Pf[NV];
+  double Pn[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const TIN x = Pin.v[v][c];
+    Pf[v] = (float)x;
+    Pn[v] = (double)x;
+  }
+  float Sv[NV] = {0, 0, 0, 0, 0, 0, 0, 0};
+  {
+    const Met<float> mf = load_met(Gf, L.gplane, LOC_CENT, p);
+    source_terms(Pf, mf, Gf.conn, L.gplane, p, (float)S.gam, Sv);
+  }
+  const float i1 = (float)(1.0 / L.dx[0]), i2 = (float)(1.0 / L.dx[1]), i3 = (float)(1.0 / L.dx[2]);
+  double U[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const long long o = v * L.plane + c;
+    float div = (F1[o + 1] - F1[o]) * i1 + (F2[o + sj] - F2[o]) * i2;
+    if (L.ndim == 3) div += (F3[o + sk] - F3[o]) * i3;
+    U[v] = U0[o] + cdt * (double)(Sv[v] - div);
+  }
+  const Met<double> m = load_met(G, L.gplane, LOC_CENT, p);
+  const int flag = noble2d_mixed(U, m, S.gam, S.c2p, Pn);
+  const double ig = 1.0 / m.gdet;
+  Pn[V_B1] = U[V_B1] * ig;
+  Pn[V_B2] = U[V_B2] * ig;
+  Pn[V_B3] = U[V_B3] * ig;
+  int fmask = 0;
+  if (flag == 0) {
+    // FP32 fluid state for the magnetisation floors (a threshold) and for the
+    // conserved increment of a density/energy floor.
+    const Met<float> mf = load_met(Gf, L.gplane, LOC_CENT, p);
+    float q[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) q[v] = (float)Pn[v];
+    FState<float> sf;
+    fluid_state(q, mf, sf);
+    const double rho0 = Pn[V_RHO], u0 = Pn[V_U];
+    fmask = apply_floors(S.fl, m, __ldg(G.flo + p), __ldg(G.flo + L.gplane + p), (double)sf.bsq, Pn);
+    if (fmask && Uout) {
+      if (fmask & 4) {  // the Lorentz-factor ceiling changed u~: full FP64 recompute
+        FState<double> s;
+        fluid_state(Pn, m, s);
+        cons_only(Pn, s, m, S.gam, U);
+      } else {
+        // at fixed u~ and B, U is linear in (rho, u): add
+        // drho dU/drho + du dU/du, formed in FP32, to the FP64 U
+        const float drho = (float)(Pn[V_RHO] - rho0), du = (float)(Pn[V_U] - u0);
+        const float gm = (float)S.gam, gd = mf.gdet, ut = sf.ucon[0];
+        U[V_RHO] += (double)(gd * ut * drho);
+        U[V_U] += (double)(gd * ((ut * sf.ucov[0] + ut) * drho + (gm * ut * sf.ucov[0] + gm - 1.0f) * du));
+        U[V_U1] += (double)(gd * ut * sf.ucov[1] * (drho + gm * du));
+        U[V_U2] += (double)(gd * ut * sf.ucov[2] * (drho + gm * du));
+        U[V_U3] += (double)(gd * ut * sf.ucov[3] * (drho + gm * du));
+      }
+    }
+  }
+  if (Pout64.v[0]) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Pout64.v[v][c] = Pn[v];
+  }
+  if (Pout32.v[0]) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Pout32.v[v][c] = (float)Pn[v];
+  }
+  if (Uout) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Uout[v * L.plane + c] = U[v];
+  }
+  pflag[c] = (int8_t)flag;
+  if (flag) atomicAdd(cnt + CNT_FAIL, 1ULL);
+  if (fmask) atomicAdd(cnt + CNT_FLOOR, 1ULL);
+}
+
 // Fixup: a zone whose inversion failed takes the equal-weight mean of the
 // fluid primitives of its non-failed interior neighbours (3x3x3, or 3x3 in
 // 2-D); with none it keeps the stage input. Then floors; U recomputed.
-__global__ void __launch_bounds__(TPB) k_fixup(Vars P, double* Uout, const int8_t* pflag, Layout L, DevGeom G,
+template <class T>
+__global__ void __launch_bounds__(TPB) k_fixup(VarsT<T> P, double* Uout, const int8_t* pflag, Layout L, DevGeom G,
                                               Scheme S, unsigned long long* cnt) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= nzones(L)) return;
@@ -393,11 +503,11 @@ __global__ void __launch_bounds__(TPB) k_fixup(Vars P, double* Uout, const int8_
         if (ii < L.s[0] || ii >= L.e[0] || jj < L.s[1] || jj >= L.e[1] || kk < L.s[2] || kk >= L.e[2]) continue;
         const long long q = L.at(kk, jj, ii);
         if (pflag[q] != 0) continue;
-        for (int v = 0; v < 5; ++v) sum[v] += P.v[v][q];
+        for (int v = 0; v < 5; ++v) sum[v] += (double)P.v[v][q];
         ++n;
       }
   double Pn[NV];
-  for (int v = 0; v < NV; ++v) Pn[v] = P.v[v][c];
+  for (int v = 0; v < NV; ++v) Pn[v] = (double)P.v[v][c];
   if (n > 0) {
     for (int v = 0; v < 5; ++v) Pn[v] = sum[v] / n;
   } else {
@@ -405,9 +515,11 @@ __global__ void __launch_bounds__(TPB) k_fixup(Vars P, double* Uout, const int8_
   }
   const long long p = (long long)j * L.n1s + i;
   const Met<double> m = load_met(G, L.gplane, LOC_CENT, p);
-  const int fmask = apply_floors(S.fl, m, __ldg(G.rad + p), Pn);
+  FState<double> sb;
+  fluid_state(Pn, m, sb);
+  const int fmask = apply_floors(S.fl, m, __ldg(G.flo + p), __ldg(G.flo + L.gplane + p), sb.bsq, Pn);
   if (fmask) atomicAdd(cnt + CNT_FLOOR, 1ULL);
-  for (int v = 0; v < 5; ++v) P.v[v][c] = Pn[v];
+  for (int v = 0; v < 5; ++v) P.v[v][c] = (T)Pn[v];
   if (Uout) {
     FState<double> s;
     fluid_state(Pn, m, s);
@@ -449,8 +561,9 @@ __device__ __forceinline__ void block_max_sum(double& a, double& b) {
 
 // CFL: inv = sum_d max(ctop_d(lower face), ctop_d(upper face)) / dx_d per zone;
 // the grid-wide maximum gives dt = cfl / max(inv) = min over zones of cfl / inv.
-__global__ void __launch_bounds__(RED_THREADS) k_cfl(const double* c1, const double* c2, const double* c3,
-                                                    Layout L, double* partial) {
+template <class T>
+__global__ void __launch_bounds__(RED_THREADS) k_cfl(const T* c1, const T* c2, const T* c3, Layout L,
+                                                    double* partial) {
   const long long nz = nzones(L);
   const long long sj = L.n1s, sk = (long long)L.n1s * L.n2s;
   double mx = 0.0, dummy = 0.0;
@@ -458,8 +571,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_cfl(const double* c1, const dou
     int i, j, k;
     zone_ijk(L, t, i, j, k);
     const long long c = L.at(k, j, i);
-    double inv = fmax(c1[c], c1[c + 1]) / L.dx[0] + fmax(c2[c], c2[c + sj]) / L.dx[1];
-    if (L.ndim == 3) inv += fmax(c3[c], c3[c + sk]) / L.dx[2];
+    double inv = fmax((double)c1[c], (double)c1[c + 1]) / L.dx[0] + fmax((double)c2[c], (double)c2[c + sj]) / L.dx[1];
+    if (L.ndim == 3) inv += fmax((double)c3[c], (double)c3[c + sk]) / L.dx[2];
     mx = fmax(mx, inv);
   }
   block_max_sum(mx, dummy);
@@ -561,6 +674,19 @@ __global__ void __launch_bounds__(TPB) k_c2p(const double* U, Vars P, int8_t* pf
   if (flag) atomicAdd(cnt + CNT_FAIL, 1ULL);
 }
 
+__global__ void k_to_f32(const double* src, float* dst, long long n) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    dst[q] = (float)src[q];
+}
+
+__global__ void k_vars_to_f32(CVars src, VarsT<float> dst, long long plane) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < plane;
+       q += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) dst.v[v][q] = (float)src.v[v][q];
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -573,30 +699,35 @@ int reduction_blocks(const Layout& L) {
   return b < 1 ? 1 : (int)b;
 }
 
-int launch_geometry(const CoordParams& cp, double x2min, const Layout& L, double* geo, double* conn, double* rad,
-                     cudaStream_t s) {
-  k_geometry<<<nblocks(L.gplane, TPB), TPB, 0, s>>>(cp, x2min, L, geo, conn, rad);
+int launch_geometry(const CoordParams& cp, double x2min, const FloorParams& fl, const Layout& L, double* geo,
+                    double* conn, double* flo, cudaStream_t s) {
+  k_geometry<<<nblocks(L.gplane, TPB), TPB, 0, s>>>(cp, x2min, fl, L, geo, conn, flo);
   return 1;
 }
 
-int launch_bc(const Vars& P, const Layout& L, const Scheme& S, const double* dlo, const double* dhi, cudaStream_t s) {
+template <class T>
+int launch_bc(const VarsT<T>& P, const Layout& L, const Scheme& S, const T* dlo, const T* dhi, cudaStream_t s) {
   int n = 0;
   long long t1 = (long long)(L.e[1] - L.s[1]) * (L.e[2] - L.s[2]) * L.ng * 2;
-  k_bc_x1<<<nblocks(t1, TPB), TPB, 0, s>>>(P, L, S, dlo, dhi);
+  k_bc_x1<T><<<nblocks(t1, TPB), TPB, 0, s>>>(P, L, S, dlo, dhi);
   ++n;
   long long t2 = (long long)L.N1 * (L.e[2] - L.s[2]) * L.ng * 2;
-  k_bc_x2<<<nblocks(t2, TPB), TPB, 0, s>>>(P, L, S);
+  k_bc_x2<T><<<nblocks(t2, TPB), TPB, 0, s>>>(P, L, S);
   ++n;
   if (L.ndim == 3) {
     long long t3 = (long long)L.N1 * L.N2 * L.ng3 * 2;
-    k_bc_x3<<<nblocks(t3, TPB), TPB, 0, s>>>(P, L, S);
+    k_bc_x3<T><<<nblocks(t3, TPB), TPB, 0, s>>>(P, L, S);
     ++n;
   }
   return n;
 }
+template int launch_bc<double>(const VarsT<double>&, const Layout&, const Scheme&, const double*, const double*,
+                               cudaStream_t);
+template int launch_bc<float>(const VarsT<float>&, const Layout&, const Scheme&, const float*, const float*,
+                              cudaStream_t);
 
-template <int D>
-static int launch_flux_d(const CVars& P, const Layout& L, const DevGeom& G, const Scheme& S, double* F, double* ctop,
+template <int D, class TIN, class R>
+static int launch_flux_d(const CVarsT<TIN>& P, const Layout& L, const GeomT<R>& G, const Scheme& S, R* F, R* ctop,
                          cudaStream_t s) {
   FaceBox b;
   for (int a = 0; a < 3; ++a) {
@@ -608,32 +739,34 @@ static int launch_flux_d(const CVars& P, const Layout& L, const DevGeom& G, cons
   const long long tot = (long long)b.n[0] * b.n[1] * b.n[2];
   const int plo = S.bc[2] == KH_BC_POLAR, phi = S.bc[3] == KH_BC_POLAR;
   if (S.recon == KH_RECON_MC)
-    k_flux<D, KH_RECON_MC><<<nblocks(tot, TPB), TPB, 0, s>>>(P, L, G, S, b, F, ctop, plo, phi);
+    k_flux<D, KH_RECON_MC, TIN, R><<<nblocks(tot, TPB), TPB, 0, s>>>(P, L, G, S, b, F, ctop, plo, phi);
   else
-    k_flux<D, KH_RECON_WENO5><<<nblocks(tot, TPB), TPB, 0, s>>>(P, L, G, S, b, F, ctop, plo, phi);
+    k_flux<D, KH_RECON_WENO5, TIN, R><<<nblocks(tot, TPB), TPB, 0, s>>>(P, L, G, S, b, F, ctop, plo, phi);
   return 1;
 }
 
-int launch_flux_dir(int D, const CVars& P, const Layout& L, const DevGeom& G, const Scheme& S, double* F,
-                    double* ctop, cudaStream_t s) {
+template <class TIN, class R>
+int launch_flux_dir(int D, const CVarsT<TIN>& P, const Layout& L, const GeomT<R>& G, const Scheme& S, R* F, R* ctop,
+                    cudaStream_t s) {
   if (D == 1) return launch_flux_d<1>(P, L, G, S, F, ctop, s);
   if (D == 2) return launch_flux_d<2>(P, L, G, S, F, ctop, s);
   return launch_flux_d<3>(P, L, G, S, F, ctop, s);
 }
+template int launch_flux_dir<double, double>(int, const CVarsT<double>&, const Layout&, const GeomT<double>&,
+                                             const Scheme&, double*, double*, cudaStream_t);
+template int launch_flux_dir<double, float>(int, const CVarsT<double>&, const Layout&, const GeomT<float>&,
+                                            const Scheme&, float*, float*, cudaStream_t);
+template int launch_flux_dir<float, float>(int, const CVarsT<float>&, const Layout&, const GeomT<float>&,
+                                           const Scheme&, float*, float*, cudaStream_t);
 
-int launch_ct(double* const F[3], double* const emf[3], const Layout& L, cudaStream_t s) {
+template <class R> int launch_ct(R* const F[3], R* const emf[3], const Layout& L, cudaStream_t s) {
   const long long tot = (long long)(L.e[0] - L.s[0] + 1) * (L.e[1] - L.s[1] + 1) * (L.ndim == 3 ? L.e[2] - L.s[2] + 1 : 1);
-  k_emf<<<nblocks(tot, TPB), TPB, 0, s>>>(F[0], F[1], F[2], emf[0], emf[1], emf[2], L);
-  k_apply_ct<<<nblocks(tot, TPB), TPB, 0, s>>>(F[0], F[1], F[2], emf[0], emf[1], emf[2], L);
+  k_emf<R><<<nblocks(tot, TPB), TPB, 0, s>>>(F[0], F[1], F[2], emf[0], emf[1], emf[2], L);
+  k_apply_ct<R><<<nblocks(tot, TPB), TPB, 0, s>>>(F[0], F[1], F[2], emf[0], emf[1], emf[2], L);
   return 2;
 }
-
-int launch_fluxes(const CVars& P, const Layout& L, const DevGeom& G, const Scheme& S, double* const F[3],
-                  double* const ctop[3], double* const emf[3], cudaStream_t s) {
-  int n = 0;
-  for (int d = 1; d <= L.ndim; ++d) n += launch_flux_dir(d, P, L, G, S, F[d - 1], ctop[d - 1], s);
-  return n + launch_ct(F, emf, L, s);
-}
+template int launch_ct<double>(double* const[3], double* const[3], const Layout&, cudaStream_t);
+template int launch_ct<float>(float* const[3], float* const[3], const Layout&, cudaStream_t);
 
 int launch_update(const double* U0, const CVars& Pin, const Vars& Pout, double* Uout, double* const F[3],
                   const Layout& L, const DevGeom& G, const Scheme& S, double cdt, int8_t* pflag,
@@ -643,18 +776,60 @@ int launch_update(const double* U0, const CVars& Pin, const Vars& Pout, double* 
   return 1;
 }
 
-int launch_fixup(const Vars& P, double* Uout, const int8_t* pflag, const Layout& L, const DevGeom& G,
+template <class TIN>
+int launch_update_mixed(const double* U0, const CVarsT<TIN>& Pin, const Vars& Pout64, const VarsT<float>& Pout32,
+                        double* Uout, float* const F[3], const Layout& L, const DevGeom& G, const GeomT<float>& Gf,
+                        const Scheme& S, double cdt, int8_t* pflag, unsigned long long* cnt, cudaStream_t s) {
+  const long long nz = (long long)L.n1 * L.n2 * L.n3;
+  k_update_mixed<TIN><<<nblocks(nz, TPB), TPB, 0, s>>>(U0, Pin, Pout64, Pout32, Uout, F[0], F[1], F[2], L, G, Gf, S,
+                                                      cdt, pflag, cnt);
+  return 1;
+}
+template int launch_update_mixed<double>(const double*, const CVarsT<double>&, const Vars&, const VarsT<float>&,
+                                         double*, float* const[3], const Layout&, const DevGeom&,
+                                         const GeomT<float>&, const Scheme&, double, int8_t*, unsigned long long*,
+                                         cudaStream_t);
+template int launch_update_mixed<float>(const double*, const CVarsT<float>&, const Vars&, const VarsT<float>&,
+                                        double*, float* const[3], const Layout&, const DevGeom&,
+                                        const GeomT<float>&, const Scheme&, double, int8_t*, unsigned long long*,
+                                        cudaStream_t);
+
+template <class T>
+int launch_fixup(const VarsT<T>& P, double* Uout, const int8_t* pflag, const Layout& L, const DevGeom& G,
                  const Scheme& S, unsigned long long* cnt, cudaStream_t s) {
   const long long nz = (long long)L.n1 * L.n2 * L.n3;
-  k_fixup<<<nblocks(nz, TPB), TPB, 0, s>>>(P, Uout, pflag, L, G, S, cnt);
+  k_fixup<T><<<nblocks(nz, TPB), TPB, 0, s>>>(P, Uout, pflag, L, G, S, cnt);
+  return 1;
+}
+template int launch_fixup<double>(const VarsT<double>&, double*, const int8_t*, const Layout&, const DevGeom&,
+                                  const Scheme&, unsigned long long*, cudaStream_t);
+template int launch_fixup<float>(const VarsT<float>&, double*, const int8_t*, const Layout&, const DevGeom&,
+                                 const Scheme&, unsigned long long*, cudaStream_t);
+
+template <class T>
+int launch_cfl(T* const ctop[3], const Layout& L, double cfl, double* partial, int npartial, double* dt_out,
+               cudaStream_t s) {
+  k_cfl<T><<<npartial, RED_THREADS, 0, s>>>(ctop[0], ctop[1], ctop[2], L, partial);
+  k_finish<<<1, RED_THREADS, 0, s>>>(partial, npartial, cfl, 0, dt_out);
+  return 2;
+}
+template int launch_cfl<double>(double* const[3], const Layout&, double, double*, int, double*, cudaStream_t);
+template int launch_cfl<float>(float* const[3], const Layout&, double, double*, int, double*, cudaStream_t);
+
+int launch_vars_to_f32(const CVars& src, const VarsT<float>& dst, const Layout& L, cudaStream_t s) {
+  long long b = nblocks(L.plane, 256);
+  if (b > 152 * 16) b = 152 * 16;
+  if (b < 1) b = 1;
+  k_vars_to_f32<<<(int)b, 256, 0, s>>>(src, dst, L.plane);
   return 1;
 }
 
-int launch_cfl(double* const ctop[3], const Layout& L, double cfl, double* partial, int npartial, double* dt_out,
-               cudaStream_t s) {
-  k_cfl<<<npartial, RED_THREADS, 0, s>>>(ctop[0], ctop[1], ctop[2], L, partial);
-  k_finish<<<1, RED_THREADS, 0, s>>>(partial, npartial, cfl, 0, dt_out);
-  return 2;
+int launch_to_f32(const double* src, float* dst, long long n, cudaStream_t s) {
+  long long b = nblocks(n, 256);
+  if (b > 152 * 16) b = 152 * 16;
+  if (b < 1) b = 1;
+  k_to_f32<<<(int)b, 256, 0, s>>>(src, dst, n);
+  return 1;
 }
 
 int launch_divb(const double* const B[3], const Layout& L, const DevGeom& G, double* partial, int npartial,

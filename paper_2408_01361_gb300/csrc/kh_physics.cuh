@@ -106,16 +106,16 @@ template <class R> KH_HD void cons_only(const R* P, const FState<R>& s, const Me
   }
 }
 
-// Signal speeds dx^d/dt: with c_ms^2 = c_s^2 + v_A^2 - c_s^2 v_A^2 (clamped to
-// [0, 1]) a covariant wave vector (-v, delta^d) obeys
-// (k_mu u^mu)^2 = c_ms^2 (k_mu k^mu + (k_mu u^mu)^2), i.e. A v^2 - Bq v + C = 0.
+// Signal speeds dx^d/dt: with the isotropic fast speed
+// c_ms^2 = c_s^2 + v_A^2 - c_s^2 v_A^2 = (gam p + b^2) / (w + b^2)
+// (c_s^2 = gam p / w, v_A^2 = b^2 / (w + b^2); clamped to [0, 1]) a covariant
+// wave vector (-v, delta^d) obeys (k_mu u^mu)^2 = c_ms^2 (k_mu k^mu + (k_mu u^mu)^2),
+// i.e. A v^2 - Bq v + C = 0.
 template <class R>
 KH_HD void signal_speeds(const R* P, const FState<R>& s, const Met<R>& m, R gam, int d, R& cmax, R& cmin) {
   const R p = (gam - R(1)) * P[V_U];
   const R w = P[V_RHO] + P[V_U] + p;
-  const R cs2 = gam * p / w;
-  const R va2 = s.bsq / (s.bsq + w);
-  R cms2 = cs2 + va2 - cs2 * va2;
+  R cms2 = (gam * p + s.bsq) / (w + s.bsq);
   cms2 = cms2 < R(0) ? R(0) : (cms2 > R(1) ? R(1) : cms2);
   const R Au = s.ucon[d], Bu = s.ucon[0];
   const R A = Bu * Bu - (m.gcon[0][0] + Bu * Bu) * cms2;
@@ -149,22 +149,48 @@ template <class R> KH_HD void recon_mc(R qm, R q0, R qp, R& lo, R& hi) {
   hi = q0 + R(0.5) * s;
 }
 
-// WENO5 point value at x = +1/2 of the centre cell of (a, b, c, d, e).
-template <class R> KH_HD R weno5_plus(R a, R b, R c, R d, R e) {
-  const R eps = R(1e-26);
-  const R p0 = R(0.375) * a - R(1.25) * b + R(1.875) * c;
-  const R p1 = R(-0.125) * b + R(0.75) * c + R(0.375) * d;
-  const R p2 = R(0.375) * c + R(0.75) * d - R(0.125) * e;
-  const R k = R(13.0 / 12.0);
-  const R t0 = a - R(2) * b + c, u0 = a - R(4) * b + R(3) * c;
-  const R t1 = b - R(2) * c + d, u1 = b - d;
-  const R t2 = c - R(2) * d + e, u2 = R(3) * c - R(4) * d + e;
-  const R s0 = k * t0 * t0 + R(0.25) * u0 * u0 + eps;
-  const R s1 = k * t1 * t1 + R(0.25) * u1 * u1 + eps;
-  const R s2 = k * t2 * t2 + R(0.25) * u2 * u2 + eps;
-  const R w0 = R(0.0625) / (s0 * s0);
-  const R w1 = R(0.625) / (s1 * s1);
-  const R w2 = R(0.3125) / (s2 * s2);
+// WENO5 point value at x = +1/2 of the centre cell of (a, b, c, d, e):
+// quadratic candidates at +1/2, linear weights (1/16, 5/8, 5/16), Jiang-Shu
+// smoothness indicators, nonlinear weights d_k / (eps + beta_k)^2.
+// FP64: eps = 1e-26 (absolute). The three weights share one division by
+// multiplying each through by (s0 s1 s2)^2, s_k = eps + beta_k.
+KH_HD double weno5_plus(double a, double b, double c, double d, double e) {
+  const double p0 = 0.375 * a - 1.25 * b + 1.875 * c;
+  const double p1 = -0.125 * b + 0.75 * c + 0.375 * d;
+  const double p2 = 0.375 * c + 0.75 * d - 0.125 * e;
+  const double k = 13.0 / 12.0;
+  const double t0 = a - 2.0 * b + c, u0 = a - 4.0 * b + 3.0 * c;
+  const double t1 = b - 2.0 * c + d, u1 = b - d;
+  const double t2 = c - 2.0 * d + e, u2 = 3.0 * c - 4.0 * d + e;
+  const double s0 = k * t0 * t0 + 0.25 * u0 * u0 + 1e-26;
+  const double s1 = k * t1 * t1 + 0.25 * u1 * u1 + 1e-26;
+  const double s2 = k * t2 * t2 + 0.25 * u2 * u2 + 1e-26;
+  const double q0 = s1 * s2, q1 = s0 * s2, q2 = s0 * s1;
+  const double w0 = 0.0625 * q0 * q0, w1 = 0.625 * q1 * q1, w2 = 0.3125 * q2 * q2;
+  return (w0 * p0 + w1 * p1 + w2 * p2) / (w0 + w1 + w2);
+}
+
+// FP32 (mixed path): the same weights, written scale-free so that nothing
+// underflows in FP32: the indicators are normalised by their sum, eps = 1e-12
+// relative to it, and each weight is d_k (s_min / s_k)^2 with s_min the
+// smallest s_k (a common factor). A stencil whose indicator is many orders
+// above the smoothest one gets a weight that vanishes, as it does in FP64.
+KH_HD float weno5_plus(float a, float b, float c, float d, float e) {
+  const float p0 = 0.375f * a - 1.25f * b + 1.875f * c;
+  const float p1 = -0.125f * b + 0.75f * c + 0.375f * d;
+  const float p2 = 0.375f * c + 0.75f * d - 0.125f * e;
+  const float k = 13.0f / 12.0f;
+  const float t0 = a - 2.0f * b + c, u0 = a - 4.0f * b + 3.0f * c;
+  const float t1 = b - 2.0f * c + d, u1 = b - d;
+  const float t2 = c - 2.0f * d + e, u2 = 3.0f * c - 4.0f * d + e;
+  const float b0 = k * t0 * t0 + 0.25f * u0 * u0;
+  const float b1 = k * t1 * t1 + 0.25f * u1 * u1;
+  const float b2 = k * t2 * t2 + 0.25f * u2 * u2;
+  const float in = 1.0f / (b0 + b1 + b2 + 1e-37f);
+  const float s0 = b0 * in + 1e-12f, s1 = b1 * in + 1e-12f, s2 = b2 * in + 1e-12f;
+  const float sm = fminf(s0, fminf(s1, s2));
+  const float r0 = sm / s0, r1 = sm / s1, r2 = sm / s2;
+  const float w0 = 0.0625f * r0 * r0, w1 = 0.625f * r1 * r1, w2 = 0.3125f * r2 * r2;
   return (w0 * p0 + w1 * p1 + w2 * p2) / (w0 + w1 + w2);
 }
 
@@ -288,14 +314,12 @@ struct FloorParams {
   double rho_min, u_min, bsq_rho_max, bsq_u_max, u_rho_max, gamma_max;
 };
 
-KH_HD int apply_floors(const FloorParams& f, const Met<double>& m, double r, double* P) {
-  FState<double> s;
-  fluid_state(P, m, s);
-  double rf = f.rho_min * pow(r, -1.5);
-  double uf = f.u_min * pow(r, -2.5);
-  rf = rf > 1e-20 ? rf : 1e-20;
-  uf = uf > 1e-20 ? uf : 1e-20;
-  const double rb = s.bsq / f.bsq_rho_max, ub = s.bsq / f.bsq_u_max;
+// rho_geo, u_geo: the geometric floors max(rho_min r^-3/2, 1e-20) and
+// max(u_min r^-5/2, 1e-20) of the zone (cached per (i, j)); bsq: b^2 of P.
+KH_HD int apply_floors(const FloorParams& f, const Met<double>& m, double rho_geo, double u_geo, double bsq,
+                       double* P) {
+  double rf = rho_geo, uf = u_geo;
+  const double rb = bsq / f.bsq_rho_max, ub = bsq / f.bsq_u_max;
   rf = rf > rb ? rf : rb;
   uf = uf > ub ? uf : ub;
   int mask = 0;
@@ -314,6 +338,115 @@ KH_HD int apply_floors(const FloorParams& f, const Met<double>& m, double r, dou
     mask |= 4;
   }
   return mask;
+}
+
+// ---------------------------------------------------------------------------
+// Mixed-precision inversion: the same (W, v^2) equations, with the Newton
+// iterations first run in FP32 on the problem scaled by a power of two
+// S ~ W (exact in either precision: every term of f1 scales as S^2, of f2 as
+// S), then finished in FP64. The FP64 phase stops once a step changes
+// |dW/W| + |dv^2| by less than 1e-6, i.e. the iterate it produced lies in
+// Newton's quadratic regime (its error ~ that step squared). Invariants D,
+// Q.n, Q~^2, B^2, (Q.B)^2 are formed in FP64 exactly as in noble2d.
+// ---------------------------------------------------------------------------
+template <class R>
+KH_HD bool newton_wv(R D, R Qdn, R Qtsq, R Bsq, R QdB2, R gf, int max_iter, R stop, R& W, R& vsq, R& err) {
+  const R vmax = R(1) - R(sizeof(R) == 4 ? 1e-7 : 1e-16);
+  for (int it = 0; it < max_iter; ++it) {
+    const R g2i = R(1) - vsq;
+    const R sg = sqrt(g2i);
+    const R p = gf * (W * g2i - D * sg);
+    const R BW = Bsq + W;
+    const R iW = R(1) / W;
+    const R iW2 = iW * iW;
+    const R f1 = Qtsq - vsq * BW * BW + QdB2 * (Bsq + R(2) * W) * iW2;
+    const R f2 = Qdn + W - p + R(0.5) * Bsq * (R(1) + vsq) - R(0.5) * QdB2 * iW2;
+    const R dpdW = gf * g2i;
+    const R dpdv = gf * (-W + R(0.5) * D / sg);
+    const R j11 = -R(2) * vsq * BW - R(2) * QdB2 * BW * iW2 * iW;
+    const R j12 = -BW * BW;
+    const R j21 = R(1) - dpdW + QdB2 * iW2 * iW;
+    const R j22 = R(0.5) * Bsq - dpdv;
+    const R idet = R(1) / (j11 * j22 - j12 * j21);
+    R Wn = W - (j22 * f1 - j12 * f2) * idet;
+    R vn = vsq - (-j21 * f1 + j11 * f2) * idet;
+    if (!(Wn > R(0))) Wn = R(0.5) * W;
+    if (vn < R(0)) vn = R(0);
+    if (vn > vmax) vn = vmax;
+    err = fabs(Wn - W) / Wn + fabs(vn - vsq);
+    W = Wn;
+    vsq = vn;
+    if (!isfinite(W) || !isfinite(vsq)) return false;
+    if (err < stop) return true;
+  }
+  return false;
+}
+
+KH_HD int noble2d_mixed(const double* U, const Met<double>& m, double gam, const C2POpts& o, double* P) {
+  const double ig = 1.0 / m.gdet;
+  const double a = m.alpha;
+  const double D = a * U[V_RHO] * ig;
+  const double Qc[4] = {a * (U[V_U] - U[V_RHO]) * ig, a * U[V_U1] * ig, a * U[V_U2] * ig, a * U[V_U3] * ig};
+  double Qu[4];
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu)
+    Qu[mu] = m.gcon[mu][0] * Qc[0] + m.gcon[mu][1] * Qc[1] + m.gcon[mu][2] * Qc[2] + m.gcon[mu][3] * Qc[3];
+  const double nu[4] = {-a * m.gcon[0][0], -a * m.gcon[1][0], -a * m.gcon[2][0], -a * m.gcon[3][0]};
+  const double Qdn = Qc[0] * nu[0] + Qc[1] * nu[1] + Qc[2] * nu[2] + Qc[3] * nu[3];
+  const double Qsq = Qc[0] * Qu[0] + Qc[1] * Qu[1] + Qc[2] * Qu[2] + Qc[3] * Qu[3];
+  const double Qtsq = fmax(Qsq + Qdn * Qdn, 0.0);
+  const double Bc1 = a * U[V_B1] * ig, Bc2 = a * U[V_B2] * ig, Bc3 = a * U[V_B3] * ig;
+  const double Bsq = m.gcov[1][1] * Bc1 * Bc1 + m.gcov[2][2] * Bc2 * Bc2 + m.gcov[3][3] * Bc3 * Bc3 +
+                     2.0 * (m.gcov[1][2] * Bc1 * Bc2 + m.gcov[1][3] * Bc1 * Bc3 + m.gcov[2][3] * Bc2 * Bc3);
+  const double QdB = Qc[1] * Bc1 + Qc[2] * Bc2 + Qc[3] * Bc3;
+  const double QdB2 = QdB * QdB;
+  const double gf = (gam - 1.0) / gam;
+
+  double W, vsq;
+  {
+    const double v1 = P[V_U1], v2 = P[V_U2], v3 = P[V_U3];
+    const double q = m.gcov[1][1] * v1 * v1 + m.gcov[2][2] * v2 * v2 + m.gcov[3][3] * v3 * v3 +
+                     2.0 * (m.gcov[1][2] * v1 * v2 + m.gcov[1][3] * v1 * v3 + m.gcov[2][3] * v2 * v3);
+    const double g2 = 1.0 + q;
+    W = (P[V_RHO] + gam * P[V_U]) * g2;
+    vsq = q / g2;
+  }
+  if (!(W > 0.0) || !isfinite(W)) W = fabs(Qdn) + 1e-300;
+  if (!(vsq >= 0.0)) vsq = 0.0;
+  if (vsq > 1.0 - 1e-16) vsq = 1.0 - 1e-16;
+
+  // FP32 phase on the problem scaled by S = 2^e ~ W
+  {
+    int e = 0;
+    frexp(W, &e);
+    const double S = ldexp(1.0, e), iS = ldexp(1.0, -e);
+    float Wf = (float)(W * iS), vf = (float)vsq, ef = 1.0f;
+    const bool ok = newton_wv<float>((float)(D * iS), (float)(Qdn * iS), (float)(Qtsq * iS * iS), (float)(Bsq * iS),
+                                     (float)(QdB2 * iS * iS * iS), (float)gf, 12, 3e-6f, Wf, vf, ef);
+    if (ok || (isfinite(Wf) && isfinite(vf) && Wf > 0.0f && ef < 1e-3f)) {
+      W = (double)Wf * S;
+      vsq = (double)vf;
+    }
+  }
+  // FP64 phase
+  double err = 1.0;
+  const bool conv = newton_wv<double>(D, Qdn, Qtsq, Bsq, QdB2, gf, o.max_iter, 1e-6, W, vsq, err);
+  if (!conv && !(err < 1e-9)) return 1;
+  if (!(W > 0.0)) return 3;
+  if (!(vsq < 1.0) || vsq < 0.0) return 2;
+  const double gamma = 1.0 / sqrt(1.0 - vsq);
+  const double rho = D / gamma;
+  const double uint = (W * (1.0 - vsq) - rho) / gam;
+  if (!(rho > 0.0)) return 4;
+  if (!(uint >= 0.0)) return 5;
+  P[V_RHO] = rho;
+  P[V_U] = uint;
+  const double f = gamma / (W + Bsq);
+  const double iW = 1.0 / W;
+  P[V_U1] = f * (Qu[1] + nu[1] * Qdn + QdB * Bc1 * iW);
+  P[V_U2] = f * (Qu[2] + nu[2] * Qdn + QdB * Bc2 * iW);
+  P[V_U3] = f * (Qu[3] + nu[3] * Qdn + QdB * Bc3 * iW);
+  return 0;
 }
 
 }  // namespace kh

@@ -24,6 +24,7 @@ MINKOWSKI, KS, MKS, FMKS = 0, 1, 2, 3
 KIND = {"minkowski": MINKOWSKI, "ks": KS, "mks": MKS, "fmks": FMKS}
 BC = {"periodic": 0, "outflow": 1, "polar": 2, "dirichlet": 3}
 RECON = {"mc": 0, "weno5": 1}
+PRECISION = {"fp64": 0, "mixed": 1}
 ERRORS = {0: "KH_OK", -1: "KH_EINVAL", -2: "KH_ECUDA", -3: "KH_ENOMEM", -4: "KH_ETIMEOUT", -5: "KH_ENAN"}
 
 
@@ -93,7 +94,7 @@ def coords_from_cfg(cfg: dict) -> Coords:
     c.kind = KIND[cfg["coords"]]
     c.n1, c.n2, c.n3 = cfg["n1"], cfg["n2"], cfg["n3"]
     c.recon = RECON[cfg["recon"]]
-    c.precision = 0
+    c.precision = PRECISION[cfg.get("precision", "fp64")]
     for q, b in enumerate(cfg["bc"]):
         c.bc[q] = BC[b]
     (c.x1min, c.x1max), (c.x2min, c.x2max), (c.x3min, c.x3max) = cfg["x1"], cfg["x2"], cfg["x3"]
