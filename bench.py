@@ -197,6 +197,7 @@ def measure(args, cfg, P0, ctx, dev, stream, dist, world, oracle_step):
 
     U, PB, P, B = fresh()
     dt0 = ctx.cfl_dt(P, B)
+    tuned = ctx.autotune(U, P, B, 0.5 * dt0)
     err = None
     if oracle_step is not None:
         ctx.step(U, P, B, oracle_step["dt"])
@@ -232,7 +233,22 @@ def measure(args, cfg, P0, ctx, dev, stream, dist, world, oracle_step):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     out = {"value": nz * args.steps * world / (ms * 1e-3), "ms": ms, "prof": prof, "launches": launches,
-           "clocks": clocks, "err": err, "nfail": nfail}
+           "clocks": clocks, "err": err, "nfail": nfail, "launch": {"tpb_flux": tuned[0], "tpb_update": tuned[1]}}
+    # the same K steps replayed as a CUDA graph (no per-kernel events)
+    ctx.set_graph(True)
+    dt, _ = ctx.step(U, P, B, 0.5 * dt)
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    g0.record(stream)
+    for _ in range(args.steps):
+        dt, _ = ctx.step(U, P, B, 0.5 * dt)
+    g1.record(stream)
+    torch.cuda.synchronize(dev)
+    gms = g0.elapsed_time(g1)
+    ctx.set_graph(False)
+    out["graph"] = {"value": nz * args.steps * world / (gms * 1e-3), "ms_per_step": gms / args.steps}
     if not args.no_e2e:
         hU = torch.empty(U.shape, dtype=torch.float64, pin_memory=True)
         hPB = torch.empty(PB.shape, dtype=torch.float64, pin_memory=True)
@@ -339,14 +355,15 @@ def run_kh(args, world, rank, local):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": roof, "hbm_step": hbm_step, "kernel_share": share,
         "cpu_baseline": cpu, "err_vs_oracle": r["err"], "e2e": r.get("e2e"), "gpu_launches": r["launches"],
-        "clocks": r["clocks"], "nfail_timed": r["nfail"],
+        "clocks": r["clocks"], "nfail_timed": r["nfail"], "launch_config": r["launch"], "graph_replay": r["graph"],
     }
     for prec in args.precisions[1:]:
         q = results[prec]
         rf, sh = roofline_of(q["prof"], nz, prec)
         line[prec] = {"value": q["value"], "ms_per_step": q["ms"] / args.steps, "dtype": DTYPE[prec],
                       "err_vs_oracle": q["err"], "e2e": q.get("e2e"), "roofline": rf, "kernel_share": sh,
-                      "gpu_launches": q["launches"], "clocks": q["clocks"], "nfail_timed": q["nfail"]}
+                      "gpu_launches": q["launches"], "clocks": q["clocks"], "nfail_timed": q["nfail"],
+                      "launch_config": q["launch"], "graph_replay": q["graph"]}
         line[f"speedup_{head}_vs_{prec}"] = r["value"] / q["value"]
     print(json.dumps(line), flush=True)
     if dist:

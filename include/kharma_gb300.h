@@ -148,6 +148,28 @@ int kh_fill_ghosts(kh_ctx* ctx, double* P, double* B);
 /* Counters of the last kh_step (synchronises). */
 int kh_get_stats(kh_ctx* ctx, kh_stats* out);
 
+/* CUDA-graph replay: enable != 0 captures the launches of one kh_step into a
+ * graph (on a private capture stream) the first time kh_step is called with a
+ * given (U, P, B) triple and replays it on the context stream afterwards;
+ * dt reaches the captured update kernels through device memory, so every
+ * call may use a new dt. New pointers or launch settings re-capture.
+ * Profiling (kh_profile) bypasses the graph. enable == 0 frees it. */
+int kh_set_graph(kh_ctx* ctx, int enable);
+
+/* Threads per block of the stencil (reconstruction + LLF) kernels and of the
+ * update kernels: each one of 32, 64, 128, 256 (default 128, 128). */
+int kh_set_launch(kh_ctx* ctx, int tpb_flux, int tpb_update);
+int kh_get_launch(const kh_ctx* ctx, int* tpb_flux, int* tpb_update);
+
+/* Autotuner: times kh_step of the state (U, P, B) with step dt (on scratch
+ * copies; the inputs are not modified) for every pair of threads per block in
+ * {64, 128, 256} x {64, 128, 256}, keeps the fastest in the context and in a
+ * process-wide cache keyed by (n1, n2, n3, coordinates, reconstruction,
+ * precision), and writes the choice to the host pointers (nullable). The
+ * scratch copies are allocated and freed inside the call. Synchronises. */
+int kh_autotune(kh_ctx* ctx, const double* U, const double* P, const double* B, double dt, int* tpb_flux,
+                int* tpb_update);
+
 /* Per-kernel-group timing. Groups: */
 enum {
   KH_T_BC = 0,     /* ghost fill (3 kernels in 3-D) */

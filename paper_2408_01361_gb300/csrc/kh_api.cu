@@ -4,6 +4,10 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "kh_internal.h"
 
 using namespace kh;
@@ -27,7 +31,7 @@ struct kh_ctx {
   int8_t* pflag;
   double* partial;
   int npartial;
-  double* dscalar;              // [0] dt, [1..2] divb max/sum
+  double* dscalar;              // [0] dt_cfl out, [1..2] divb max/sum, [3] dt in
   unsigned long long* counters; // NCNT
   double* dirichlet[2];
   // mixed precision (KH_MIXED): FP32 geometry copy, FP32 flux pass buffers,
@@ -42,6 +46,14 @@ struct kh_ctx {
   float* dirichletf[2];
   long long launches;
   kh_stats last;
+  // launch configuration (threads per block of the stencil and update kernels)
+  int tpb_flux, tpb_update;
+  // CUDA-graph replay of the step, keyed by the (U, P, B) pointers captured
+  int graph_on;
+  cudaStream_t cap_stream;
+  cudaGraphExec_t gexec;
+  const void* gkey[3];
+  int graph_launches;
   // optional per-kernel-group timing (CUDA events on the context stream)
   int profiling;
   cudaEvent_t ev[KH_NTIMERS][2][2];  // [group][stage][start, stop]
@@ -124,7 +136,7 @@ void free_all(kh_ctx* x) {
 GeomT<float> geomf(const kh_ctx* x) { return GeomT<float>{x->geof, x->connf, x->flo}; }
 
 // One FP64 stage: ghost fill, fluxes per direction, Flux-CT, update, fixup.
-int run_stage(kh_ctx* x, int st, const double* U0, const Vars& Pin, const Vars& Pout, double* Uout, double cdt) {
+int run_stage(kh_ctx* x, int st, const double* U0, const Vars& Pin, const Vars& Pout, double* Uout, double coef) {
   const Layout& L = x->L;
   const DevGeom G = devgeom(x);
   cudaStream_t s = x->stream;
@@ -134,14 +146,15 @@ int run_stage(kh_ctx* x, int st, const double* U0, const Vars& Pin, const Vars& 
   mark(x, KH_T_BC, st, 1);
   for (int d = 1; d <= L.ndim; ++d) {
     mark(x, KH_T_FLUX1 + d - 1, st, 0);
-    n += launch_flux_dir<double, double>(d, cview(Pin), L, G, x->S, x->F[d - 1], x->ctop[d - 1], s);
+    n += launch_flux_dir<double, double>(d, cview(Pin), L, G, x->S, x->F[d - 1], x->ctop[d - 1], x->tpb_flux, s);
     mark(x, KH_T_FLUX1 + d - 1, st, 1);
   }
   mark(x, KH_T_CT, st, 0);
   n += launch_ct<double>(x->F, x->emf, L, s);
   mark(x, KH_T_CT, st, 1);
   mark(x, KH_T_UPDATE, st, 0);
-  n += launch_update(U0, cview(Pin), Pout, Uout, x->F, L, G, x->S, cdt, x->pflag, x->counters, s);
+  n += launch_update(U0, cview(Pin), Pout, Uout, x->F, L, G, x->S, x->dscalar + 3, coef, x->pflag, x->counters,
+                     x->tpb_update, s);
   mark(x, KH_T_UPDATE, st, 1);
   mark(x, KH_T_FIXUP, st, 0);
   n += launch_fixup<double>(Pout, Uout, x->pflag, L, G, x->S, x->counters, s);
@@ -160,7 +173,7 @@ template <class T> CVarsT<T> cviewT(const VarsT<T>& v) {
 // FP32 shadow (ghost-filled in FP32) as input, FP64 output and U.
 template <class TIN>
 int run_stage_mixed(kh_ctx* x, int st, const double* U0, const VarsT<TIN>& Pin, const TIN* dlo, const TIN* dhi,
-                    const Vars& Pout64, const VarsT<float>& Pout32, double* Uout, double cdt) {
+                    const Vars& Pout64, const VarsT<float>& Pout32, double* Uout, double coef) {
   const Layout& L = x->L;
   const DevGeom G = devgeom(x);
   const GeomT<float> Gf = geomf(x);
@@ -181,15 +194,15 @@ int run_stage_mixed(kh_ctx* x, int st, const double* U0, const VarsT<TIN>& Pin, 
   mark(x, KH_T_BC, st, 1);
   for (int d = 1; d <= L.ndim; ++d) {
     mark(x, KH_T_FLUX1 + d - 1, st, 0);
-    n += launch_flux_dir<float, float>(d, cviewT(Pf), L, Gf, x->S, x->Ff[d - 1], x->ctopf[d - 1], s);
+    n += launch_flux_dir<float, float>(d, cviewT(Pf), L, Gf, x->S, x->Ff[d - 1], x->ctopf[d - 1], x->tpb_flux, s);
     mark(x, KH_T_FLUX1 + d - 1, st, 1);
   }
   mark(x, KH_T_CT, st, 0);
   n += launch_ct<float>(x->Ff, x->emff, L, s);
   mark(x, KH_T_CT, st, 1);
   mark(x, KH_T_UPDATE, st, 0);
-  n += launch_update_mixed<TIN>(U0, cviewT(Pin), Pout64, Pout32, Uout, x->Ff, L, G, Gf, x->S, cdt, x->pflag,
-                                x->counters, s);
+  n += launch_update_mixed<TIN>(U0, cviewT(Pin), Pout64, Pout32, Uout, x->Ff, L, G, Gf, x->S, x->dscalar + 3, coef,
+                                x->pflag, x->counters, x->tpb_update, s);
   mark(x, KH_T_UPDATE, st, 1);
   mark(x, KH_T_FIXUP, st, 0);
   if (Pout64.v[0])
@@ -254,6 +267,12 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
   L.n3s = L.N3;
   L.gplane = (long long)L.n1s * L.n2s;
   L.plane = L.gplane * L.n3s;
+  if (L.plane >= (1LL << 31)) {  // kernels index cells with 32-bit arithmetic
+    free(x);
+    return KH_EINVAL;
+  }
+  x->tpb_flux = 128;
+  x->tpb_update = 128;
   L.dx[0] = (c->x1max - c->x1min) / c->n1;
   L.dx[1] = (c->x2max - c->x2min) / c->n2;
   L.dx[2] = (c->x3max - c->x3min) / c->n3;
@@ -417,24 +436,29 @@ int kh_fluxes(kh_ctx* x, const double* P, const double* B, double* F1, double* F
   int n = 0;
   for (int d = 1; d <= x->L.ndim; ++d)
     n += launch_flux_dir<double, double>(d, cvars_of(x, P, B), x->L, devgeom(x), x->S, F[d - 1], x->ctop[d - 1],
-                                         x->stream);
+                                         x->tpb_flux, x->stream);
   n += launch_ct<double>(F, x->emf, x->L, x->stream);
   return check_launch(x, n);
 }
 
-int kh_step(kh_ctx* x, double* U, double* P, double* B, double dt, double* dt_cfl) {
-  if (!x || !U || !P || !B || !(dt > 0.0) || !isfinite(dt)) return KH_EINVAL;
+}  // extern "C"
+
+namespace {
+
+// Issue the launches of one full step on x->stream (dt is read from
+// x->dscalar[3] by the update kernels).
+int issue_step(kh_ctx* x, double* U, double* P, double* B) {
   const Layout& L = x->L;
   cudaStream_t s = x->stream;
-  KH_TRY(cudaMemsetAsync(x->counters, 0, NCNT * sizeof(unsigned long long), s));
+  if (cudaMemsetAsync(x->counters, 0, NCNT * sizeof(unsigned long long), s) != cudaSuccess) return -1;
   Vars Pn = vars_of(x, P, B);
   Vars Ps;
   for (int q = 0; q < NV; ++q) Ps.v[q] = x->pstar + q * L.plane;
   int n = 0;
   if (x->c.precision == KH_FP64) {
     // stage 1: P^n -> P* (U* is not stored); stage 2: P* -> P^{n+1}, U^{n+1} in place
-    n += run_stage(x, 0, U, Pn, Ps, nullptr, 0.5 * dt);
-    n += run_stage(x, 1, U, Ps, Pn, U, dt);
+    n += run_stage(x, 0, U, Pn, Ps, nullptr, 0.5);
+    n += run_stage(x, 1, U, Ps, Pn, U, 1.0);
     mark(x, KH_T_CFL, 1, 0);
     n += launch_cfl<double>(x->ctop, L, x->S.cfl, x->partial, x->npartial, x->dscalar, s);
     mark(x, KH_T_CFL, 1, 1);
@@ -447,13 +471,76 @@ int kh_step(kh_ctx* x, double* U, double* P, double* B, double dt, double* dt_cf
       nof.v[q] = nullptr;
       no64.v[q] = nullptr;
     }
-    n += run_stage_mixed<double>(x, 0, U, Pn, x->dirichlet[0], x->dirichlet[1], no64, Psf, nullptr, 0.5 * dt);
-    n += run_stage_mixed<float>(x, 1, U, Psf, x->dirichletf[0], x->dirichletf[1], Pn, nof, U, dt);
+    n += run_stage_mixed<double>(x, 0, U, Pn, x->dirichlet[0], x->dirichlet[1], no64, Psf, nullptr, 0.5);
+    n += run_stage_mixed<float>(x, 1, U, Psf, x->dirichletf[0], x->dirichletf[1], Pn, nof, U, 1.0);
     mark(x, KH_T_CFL, 1, 0);
     n += launch_cfl<float>(x->ctopf, L, x->S.cfl, x->partial, x->npartial, x->dscalar, s);
     mark(x, KH_T_CFL, 1, 1);
   }
-  int rc = check_launch(x, n);
+  return n;
+}
+
+void drop_graph(kh_ctx* x) {
+  if (x->gexec) cudaGraphExecDestroy(x->gexec);
+  x->gexec = nullptr;
+  x->gkey[0] = x->gkey[1] = x->gkey[2] = nullptr;
+}
+
+// Capture the step for these pointers (once) and replay it.
+int step_graph(kh_ctx* x, double* U, double* P, double* B) {
+  if (!(x->gexec && x->gkey[0] == U && x->gkey[1] == P && x->gkey[2] == B)) {
+    drop_graph(x);
+    if (!x->cap_stream && cudaStreamCreateWithFlags(&x->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return KH_ECUDA;
+    cudaStream_t user = x->stream;
+    x->stream = x->cap_stream;
+    if (cudaStreamBeginCapture(x->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      x->stream = user;
+      return KH_ECUDA;
+    }
+    const int n = issue_step(x, U, P, B);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(x->cap_stream, &g);
+    x->stream = user;
+    if (n < 0 || e != cudaSuccess || !g) {
+      if (g) cudaGraphDestroy(g);
+      return KH_ECUDA;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&x->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      x->gexec = nullptr;
+      return KH_ECUDA;
+    }
+    x->gkey[0] = U;
+    x->gkey[1] = P;
+    x->gkey[2] = B;
+    x->graph_launches = n;
+  }
+  if (cudaGraphLaunch(x->gexec, x->stream) != cudaSuccess) return KH_ECUDA;
+  x->launches += x->graph_launches;
+  return KH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int kh_step(kh_ctx* x, double* U, double* P, double* B, double dt, double* dt_cfl) {
+  if (!x || !U || !P || !B || !(dt > 0.0) || !isfinite(dt)) return KH_EINVAL;
+  // dt enters through device memory (a pageable copy: the host value may be
+  // reused as soon as the call returns)
+  KH_TRY(cudaMemcpyAsync(x->dscalar + 3, &dt, sizeof(double), cudaMemcpyHostToDevice, x->stream));
+  int rc;
+  if (x->graph_on && !x->profiling) {
+    rc = step_graph(x, U, P, B);
+    if (rc != KH_OK) return rc;
+    rc = cuda_fail(cudaGetLastError());
+  } else {
+    const int n = issue_step(x, U, P, B);
+    if (n < 0) return KH_ECUDA;
+    rc = check_launch(x, n);
+  }
   if (rc != KH_OK) return rc;
   if (!dt_cfl && !x->profiling) return KH_OK;
   kh_stats st;
@@ -464,6 +551,113 @@ int kh_step(kh_ctx* x, double* U, double* P, double* B, double dt, double* dt_cf
   *dt_cfl = st.dt_cfl;
   if (!isfinite(st.dt_cfl)) return KH_ENAN;
   return (int)(st.nfail > 0x7fffffffLL ? 0x7fffffff : st.nfail);
+}
+
+int kh_set_graph(kh_ctx* x, int enable) {
+  if (!x) return KH_EINVAL;
+  if (!enable) drop_graph(x);
+  x->graph_on = enable ? 1 : 0;
+  return KH_OK;
+}
+
+int kh_set_launch(kh_ctx* x, int tpb_flux, int tpb_update) {
+  if (!x) return KH_EINVAL;
+  const int ok[4] = {32, 64, 128, 256};
+  bool f = false, u = false;
+  for (int q = 0; q < 4; ++q) {
+    f = f || tpb_flux == ok[q];
+    u = u || tpb_update == ok[q];
+  }
+  if (!f || !u) return KH_EINVAL;
+  x->tpb_flux = tpb_flux;
+  x->tpb_update = tpb_update;
+  drop_graph(x);
+  return KH_OK;
+}
+
+int kh_get_launch(const kh_ctx* x, int* tpb_flux, int* tpb_update) {
+  if (!x) return KH_EINVAL;
+  if (tpb_flux) *tpb_flux = x->tpb_flux;
+  if (tpb_update) *tpb_update = x->tpb_update;
+  return KH_OK;
+}
+
+int kh_autotune(kh_ctx* x, const double* U, const double* P, const double* B, double dt, int* tpb_flux,
+                int* tpb_update) {
+  if (!x || !U || !P || !B || !(dt > 0.0)) return KH_EINVAL;
+  // process-wide cache: one search per (grid, coordinates, reconstruction, precision)
+  static std::mutex lock;
+  static std::map<std::tuple<int, int, int, int, int, int>, std::pair<int, int>> cache;
+  const auto key = std::make_tuple(x->L.n1, x->L.n2, x->L.n3, x->c.kind, x->c.recon, x->c.precision);
+  {
+    std::lock_guard<std::mutex> g(lock);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      const int rc = kh_set_launch(x, it->second.first, it->second.second);
+      if (tpb_flux) *tpb_flux = x->tpb_flux;
+      if (tpb_update) *tpb_update = x->tpb_update;
+      return rc;
+    }
+  }
+  const Layout& L = x->L;
+  const size_t pl = (size_t)L.plane * sizeof(double);
+  double *Us = nullptr, *Ps = nullptr, *Bs = nullptr;
+  int rc = cuda_fail(cudaMalloc((void**)&Us, 8 * pl));
+  if (rc == KH_OK) rc = cuda_fail(cudaMalloc((void**)&Ps, 5 * pl));
+  if (rc == KH_OK) rc = cuda_fail(cudaMalloc((void**)&Bs, 3 * pl));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (rc == KH_OK) rc = cuda_fail(cudaEventCreate(&e0));
+  if (rc == KH_OK) rc = cuda_fail(cudaEventCreate(&e1));
+  const int graph = x->graph_on, prof = x->profiling;
+  x->graph_on = 0;
+  x->profiling = 0;
+  const int cand[3] = {64, 128, 256};
+  float best = 1e30f;
+  int bf = x->tpb_flux, bu = x->tpb_update;
+  for (int a = 0; a < 3 && rc == KH_OK; ++a)
+    for (int b = 0; b < 3 && rc == KH_OK; ++b) {
+      x->tpb_flux = cand[a];
+      x->tpb_update = cand[b];
+      float ms = 0.0f;
+      // one untimed step, then two timed steps, each from the caller's state
+      for (int rep = 0; rep < 3 && rc == KH_OK; ++rep) {
+        rc = cuda_fail(cudaMemcpyAsync(Us, U, 8 * pl, cudaMemcpyDeviceToDevice, x->stream));
+        if (rc == KH_OK) rc = cuda_fail(cudaMemcpyAsync(Ps, P, 5 * pl, cudaMemcpyDeviceToDevice, x->stream));
+        if (rc == KH_OK) rc = cuda_fail(cudaMemcpyAsync(Bs, B, 3 * pl, cudaMemcpyDeviceToDevice, x->stream));
+        if (rc == KH_OK) rc = cuda_fail(cudaEventRecord(e0, x->stream));
+        if (rc == KH_OK) {
+          const int r = kh_step(x, Us, Ps, Bs, dt, nullptr);
+          rc = r < 0 ? r : KH_OK;
+        }
+        if (rc == KH_OK) rc = cuda_fail(cudaEventRecord(e1, x->stream));
+        if (rc == KH_OK) rc = cuda_fail(cudaEventSynchronize(e1));
+        float t = 0.0f;
+        if (rc == KH_OK && rep > 0 && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess) ms += t;
+      }
+      if (rc == KH_OK && ms < best) {
+        best = ms;
+        bf = cand[a];
+        bu = cand[b];
+      }
+    }
+  x->tpb_flux = bf;
+  x->tpb_update = bu;
+  x->graph_on = graph;
+  x->profiling = prof;
+  drop_graph(x);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (Us) cudaFree(Us);
+  if (Ps) cudaFree(Ps);
+  if (Bs) cudaFree(Bs);
+  if (rc != KH_OK) return rc;
+  {
+    std::lock_guard<std::mutex> g(lock);
+    cache[key] = std::make_pair(bf, bu);
+  }
+  if (tpb_flux) *tpb_flux = bf;
+  if (tpb_update) *tpb_update = bu;
+  return KH_OK;
 }
 
 int kh_profile(kh_ctx* x, int enable) {
@@ -523,11 +717,13 @@ int kh_cfl_dt(kh_ctx* x, const double* P, const double* B, double* dt_cfl) {
   int n = launch_bc<double>(Ps, L, x->S, x->dirichlet[0], x->dirichlet[1], s);
   if (x->c.precision == KH_FP64) {
     for (int d = 1; d <= L.ndim; ++d)
-      n += launch_flux_dir<double, double>(d, cview(Ps), L, devgeom(x), x->S, x->F[d - 1], x->ctop[d - 1], s);
+      n += launch_flux_dir<double, double>(d, cview(Ps), L, devgeom(x), x->S, x->F[d - 1], x->ctop[d - 1],
+                                           x->tpb_flux, s);
     n += launch_cfl<double>(x->ctop, L, x->S.cfl, x->partial, x->npartial, x->dscalar, s);
   } else {
     for (int d = 1; d <= L.ndim; ++d)
-      n += launch_flux_dir<double, float>(d, cview(Ps), L, geomf(x), x->S, x->Ff[d - 1], x->ctopf[d - 1], s);
+      n += launch_flux_dir<double, float>(d, cview(Ps), L, geomf(x), x->S, x->Ff[d - 1], x->ctopf[d - 1],
+                                          x->tpb_flux, s);
     n += launch_cfl<float>(x->ctopf, L, x->S.cfl, x->partial, x->npartial, x->dscalar, s);
   }
   int rc = check_launch(x, n);
@@ -557,6 +753,9 @@ int64_t kh_launch_count(const kh_ctx* x) { return x ? (int64_t)x->launches : 0; 
 int kh_destroy(kh_ctx* x) {
   if (!x) return KH_EINVAL;
   cudaStreamSynchronize(x->stream);
+  drop_graph(x);
+  if (x->cap_stream) cudaStreamDestroy(x->cap_stream);
+  if (x->profiling) kh_profile(x, 0);
   free_all(x);
   free(x);
   return KH_OK;

@@ -70,11 +70,13 @@ int launch_bc(const VarsT<T>& P, const Layout& L, const Scheme& S, const T* dlo,
 // outputs in R (FP64 path: double/double; mixed: double or float in, float out).
 template <class TIN, class R>
 int launch_flux_dir(int D, const CVarsT<TIN>& P, const Layout& L, const GeomT<R>& G, const Scheme& S, R* F, R* ctop,
-                    cudaStream_t s);
+                    int tpb, cudaStream_t s);
 template <class R> int launch_ct(R* const F[3], R* const emf[3], const Layout& L, cudaStream_t s);
+// The update reads its time increment as coef * dtp[0] (device memory), so a
+// captured step keeps working when dt changes.
 int launch_update(const double* U0, const CVars& Pin, const Vars& Pout, double* Uout, double* const F[3],
-                  const Layout& L, const DevGeom& G, const Scheme& S, double cdt, int8_t* pflag,
-                  unsigned long long* cnt, cudaStream_t s);
+                  const Layout& L, const DevGeom& G, const Scheme& S, const double* dtp, double coef, int8_t* pflag,
+                  unsigned long long* cnt, int tpb, cudaStream_t s);
 // Mixed update: FP32 fluxes and sources, FP64 accumulation of U and FP64
 // inversion; the stage input (sources and inversion guess) is read in TIN.
 // Writes the FP64 output (Pout64.v[0] may be null) and/or its FP32 shadow
@@ -82,7 +84,8 @@ int launch_update(const double* U0, const CVars& Pin, const Vars& Pout, double* 
 template <class TIN>
 int launch_update_mixed(const double* U0, const CVarsT<TIN>& Pin, const Vars& Pout64, const VarsT<float>& Pout32,
                         double* Uout, float* const F[3], const Layout& L, const DevGeom& G, const GeomT<float>& Gf,
-                        const Scheme& S, double cdt, int8_t* pflag, unsigned long long* cnt, cudaStream_t s);
+                        const Scheme& S, const double* dtp, double coef, int8_t* pflag, unsigned long long* cnt,
+                        int tpb, cudaStream_t s);
 template <class T>
 int launch_fixup(const VarsT<T>& P, double* Uout, const int8_t* pflag, const Layout& L, const DevGeom& G,
                  const Scheme& S, unsigned long long* cnt, cudaStream_t s);

@@ -13,7 +13,18 @@ namespace kh {
 
 namespace {
 
-constexpr int TPB = 128;
+constexpr int TPB = 128;    // default threads per block
+constexpr int TPB_MAX = 256;
+
+// t -> (a, b, c) with t = a + n0 (b + n1 c), in 32-bit arithmetic (every
+// allocation holds fewer than 2^31 cells).
+__device__ __forceinline__ void split3(unsigned t, unsigned n0, unsigned n1, int& a, int& b, int& c) {
+  const unsigned q = t / n0;
+  a = (int)(t - q * n0);
+  const unsigned r = q / n1;
+  b = (int)(q - r * n1);
+  c = (int)r;
+}
 
 inline int nblocks(long long n, int tpb) { return (int)((n + tpb - 1) / tpb); }
 
@@ -178,14 +189,16 @@ struct FaceBox {
 };
 
 template <int D, int RECON, class TIN, class R>
-__global__ void __launch_bounds__(TPB) k_flux(CVarsT<TIN> P, Layout L, GeomT<R> G, Scheme S, FaceBox box, R* F,
-                                             R* ctop, int polar_lo, int polar_hi) {
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const long long tot = (long long)box.n[0] * box.n[1] * box.n[2];
+__global__ void __launch_bounds__(TPB_MAX) k_flux(CVarsT<TIN> P, Layout L, GeomT<R> G, Scheme S, FaceBox box, R* F,
+                                                 R* ctop, int polar_lo, int polar_hi) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned tot = (unsigned)box.n[0] * box.n[1] * box.n[2];
   if (t >= tot) return;
-  const int i = box.lo[0] + (int)(t % box.n[0]);
-  const int j = box.lo[1] + (int)((t / box.n[0]) % box.n[1]);
-  const int k = box.lo[2] + (int)(t / ((long long)box.n[0] * box.n[1]));
+  int i, j, k;
+  split3(t, box.n[0], box.n[1], i, j, k);
+  i += box.lo[0];
+  j += box.lo[1];
+  k += box.lo[2];
   const long long c = L.at(k, j, i);
   const long long st = (D == 1) ? 1 : (D == 2 ? (long long)L.n1s : (long long)L.n1s * L.n2s);
   R PL[NV], PR[NV];
@@ -233,11 +246,13 @@ __global__ void __launch_bounds__(TPB) k_flux(CVarsT<TIN> P, Layout L, GeomT<R> 
 template <class R>
 __global__ void k_emf(const R* F1, const R* F2, const R* F3, R* e1, R* e2, R* e3, Layout L) {
   const int n0 = L.e[0] - L.s[0] + 1, n1 = L.e[1] - L.s[1] + 1, n2 = (L.ndim == 3) ? L.e[2] - L.s[2] + 1 : 1;
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= (long long)n0 * n1 * n2) return;
-  const int i = L.s[0] + (int)(t % n0);
-  const int j = L.s[1] + (int)((t / n0) % n1);
-  const int k = (L.ndim == 3 ? L.s[2] : 0) + (int)(t / ((long long)n0 * n1));
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (unsigned)n0 * n1 * n2) return;
+  int i, j, k;
+  split3(t, n0, n1, i, j, k);
+  i += L.s[0];
+  j += L.s[1];
+  k += (L.ndim == 3 ? L.s[2] : 0);
   const long long c = L.at(k, j, i);
   const long long P = L.plane, sj = L.n1s, sk = (long long)L.n1s * L.n2s;
   const R q = R(0.25);
@@ -266,11 +281,13 @@ __global__ void k_emf(const R* F1, const R* F2, const R* F3, R* e1, R* e2, R* e3
 template <class R>
 __global__ void k_apply_ct(R* F1, R* F2, R* F3, const R* e1, const R* e2, const R* e3, Layout L) {
   const int n0 = L.e[0] - L.s[0] + 1, n1 = L.e[1] - L.s[1] + 1, n2 = (L.ndim == 3) ? L.e[2] - L.s[2] + 1 : 1;
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= (long long)n0 * n1 * n2) return;
-  const int i = L.s[0] + (int)(t % n0);
-  const int j = L.s[1] + (int)((t / n0) % n1);
-  const int k = (L.ndim == 3 ? L.s[2] : 0) + (int)(t / ((long long)n0 * n1));
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (unsigned)n0 * n1 * n2) return;
+  int i, j, k;
+  split3(t, n0, n1, i, j, k);
+  i += L.s[0];
+  j += L.s[1];
+  k += (L.ndim == 3 ? L.s[2] : 0);
   const long long c = L.at(k, j, i);
   const long long P = L.plane, sj = L.n1s, sk = (long long)L.n1s * L.n2s;
   const bool in_i = i < L.e[0], in_j = j < L.e[1];
@@ -297,15 +314,15 @@ __global__ void k_apply_ct(R* F1, R* F2, R* F3, const R* e1, const R* e2, const 
 // Update of one interior zone: U = U0 + cdt (-div F + S(Pin)), inversion with
 // Pin as the guess, floors; writes Pout, pflag and (stage 2) U.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void zone_ijk(const Layout& L, long long t, int& i, int& j, int& k) {
-  const int n0 = L.e[0] - L.s[0], n1 = L.e[1] - L.s[1];
-  i = L.s[0] + (int)(t % n0);
-  j = L.s[1] + (int)((t / n0) % n1);
-  k = L.s[2] + (int)(t / ((long long)n0 * n1));
+__device__ __forceinline__ void zone_ijk(const Layout& L, unsigned t, int& i, int& j, int& k) {
+  split3(t, L.e[0] - L.s[0], L.e[1] - L.s[1], i, j, k);
+  i += L.s[0];
+  j += L.s[1];
+  k += L.s[2];
 }
 
-__device__ __forceinline__ long long nzones(const Layout& L) {
-  return (long long)(L.e[0] - L.s[0]) * (L.e[1] - L.s[1]) * (L.e[2] - L.s[2]);
+__device__ __forceinline__ unsigned nzones(const Layout& L) {
+  return (unsigned)(L.e[0] - L.s[0]) * (L.e[1] - L.s[1]) * (L.e[2] - L.s[2]);
 }
 
 // S_nu = sqrt(-g) T^k_l Gamma^l_{nu k} for nu = t, 1, 2, 3 (energy and
@@ -334,14 +351,15 @@ __device__ __forceinline__ void source_terms(const R* P, const Met<R>& m, const 
   }
 }
 
-__global__ void __launch_bounds__(TPB) k_update(const double* U0, CVars Pin, Vars Pout, double* Uout,
+__global__ void __launch_bounds__(TPB_MAX) k_update(const double* U0, CVars Pin, Vars Pout, double* Uout,
                                                const double* F1, const double* F2, const double* F3, Layout L,
-                                               DevGeom G, Scheme S, double cdt, int8_t* pflag,
+                                               DevGeom G, Scheme S, const double* dtp, double coef, int8_t* pflag,
                                                unsigned long long* cnt) {
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nzones(L)) return;
   int i, j, k;
   zone_ijk(L, t, i, j, k);
+  const double cdt = coef * __ldg(dtp);
   const long long c = L.at(k, j, i);
   const long long p = (long long)j * L.n1s + i;
   const long long sj = L.n1s, sk = (long long)L.n1s * L.n2s;
@@ -393,15 +411,16 @@ __global__ void __launch_bounds__(TPB) k_update(const double* U0, CVars Pin, Var
 // FP32; U = U0 + cdt dU is accumulated in FP64; the Noble-2D inversion and the
 // floors run in FP64 on the FP64 metric, the stage input serving as guess.
 template <class TIN>
-__global__ void __launch_bounds__(TPB) k_update_mixed(const double* U0, CVarsT<TIN> Pin, Vars Pout64,
+__global__ void __launch_bounds__(TPB_MAX) k_update_mixed(const double* U0, CVarsT<TIN> Pin, Vars Pout64,
                                                      VarsT<float> Pout32, double* Uout, const float* F1,
                                                      const float* F2, const float* F3, Layout L, DevGeom G,
-                                                     GeomT<float> Gf, Scheme S, double cdt, int8_t* pflag,
-                                                     unsigned long long* cnt) {
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+                                                     GeomT<float> Gf, Scheme S, const double* dtp, double coef,
+                                                     int8_t* pflag, unsigned long long* cnt) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nzones(L)) return;
   int i, j, k;
   zone_ijk(L, t, i, j, k);
+  const double cdt = coef * __ldg(dtp);
   const long long c = L.at(k, j, i);
   const long long p = (long long)j * L.n1s + i;
   const long long sj = L.n1s, sk = (long long)L.n1s * L.n2s;
@@ -486,7 +505,7 @@ __global__ void __launch_bounds__(TPB) k_update_mixed(const double* U0, CVarsT<T
 template <class T>
 __global__ void __launch_bounds__(TPB) k_fixup(VarsT<T> P, double* Uout, const int8_t* pflag, Layout L, DevGeom G,
                                               Scheme S, unsigned long long* cnt) {
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nzones(L)) return;
   int i, j, k;
   zone_ijk(L, t, i, j, k);
@@ -564,10 +583,10 @@ __device__ __forceinline__ void block_max_sum(double& a, double& b) {
 template <class T>
 __global__ void __launch_bounds__(RED_THREADS) k_cfl(const T* c1, const T* c2, const T* c3, Layout L,
                                                     double* partial) {
-  const long long nz = nzones(L);
+  const unsigned nz = nzones(L);
   const long long sj = L.n1s, sk = (long long)L.n1s * L.n2s;
   double mx = 0.0, dummy = 0.0;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nz; t += (long long)gridDim.x * blockDim.x) {
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < nz; t += gridDim.x * blockDim.x) {
     int i, j, k;
     zone_ijk(L, t, i, j, k);
     const long long c = L.at(k, j, i);
@@ -728,7 +747,7 @@ template int launch_bc<float>(const VarsT<float>&, const Layout&, const Scheme&,
 
 template <int D, class TIN, class R>
 static int launch_flux_d(const CVarsT<TIN>& P, const Layout& L, const GeomT<R>& G, const Scheme& S, R* F, R* ctop,
-                         cudaStream_t s) {
+                         int tpb, cudaStream_t s) {
   FaceBox b;
   for (int a = 0; a < 3; ++a) {
     const bool active = a < 2 || L.ndim == 3;
@@ -739,25 +758,25 @@ static int launch_flux_d(const CVarsT<TIN>& P, const Layout& L, const GeomT<R>& 
   const long long tot = (long long)b.n[0] * b.n[1] * b.n[2];
   const int plo = S.bc[2] == KH_BC_POLAR, phi = S.bc[3] == KH_BC_POLAR;
   if (S.recon == KH_RECON_MC)
-    k_flux<D, KH_RECON_MC, TIN, R><<<nblocks(tot, TPB), TPB, 0, s>>>(P, L, G, S, b, F, ctop, plo, phi);
+    k_flux<D, KH_RECON_MC, TIN, R><<<nblocks(tot, tpb), tpb, 0, s>>>(P, L, G, S, b, F, ctop, plo, phi);
   else
-    k_flux<D, KH_RECON_WENO5, TIN, R><<<nblocks(tot, TPB), TPB, 0, s>>>(P, L, G, S, b, F, ctop, plo, phi);
+    k_flux<D, KH_RECON_WENO5, TIN, R><<<nblocks(tot, tpb), tpb, 0, s>>>(P, L, G, S, b, F, ctop, plo, phi);
   return 1;
 }
 
 template <class TIN, class R>
 int launch_flux_dir(int D, const CVarsT<TIN>& P, const Layout& L, const GeomT<R>& G, const Scheme& S, R* F, R* ctop,
-                    cudaStream_t s) {
-  if (D == 1) return launch_flux_d<1>(P, L, G, S, F, ctop, s);
-  if (D == 2) return launch_flux_d<2>(P, L, G, S, F, ctop, s);
-  return launch_flux_d<3>(P, L, G, S, F, ctop, s);
+                    int tpb, cudaStream_t s) {
+  if (D == 1) return launch_flux_d<1>(P, L, G, S, F, ctop, tpb, s);
+  if (D == 2) return launch_flux_d<2>(P, L, G, S, F, ctop, tpb, s);
+  return launch_flux_d<3>(P, L, G, S, F, ctop, tpb, s);
 }
 template int launch_flux_dir<double, double>(int, const CVarsT<double>&, const Layout&, const GeomT<double>&,
-                                             const Scheme&, double*, double*, cudaStream_t);
+                                             const Scheme&, double*, double*, int, cudaStream_t);
 template int launch_flux_dir<double, float>(int, const CVarsT<double>&, const Layout&, const GeomT<float>&,
-                                            const Scheme&, float*, float*, cudaStream_t);
+                                            const Scheme&, float*, float*, int, cudaStream_t);
 template int launch_flux_dir<float, float>(int, const CVarsT<float>&, const Layout&, const GeomT<float>&,
-                                           const Scheme&, float*, float*, cudaStream_t);
+                                           const Scheme&, float*, float*, int, cudaStream_t);
 
 template <class R> int launch_ct(R* const F[3], R* const emf[3], const Layout& L, cudaStream_t s) {
   const long long tot = (long long)(L.e[0] - L.s[0] + 1) * (L.e[1] - L.s[1] + 1) * (L.ndim == 3 ? L.e[2] - L.s[2] + 1 : 1);
@@ -769,30 +788,31 @@ template int launch_ct<double>(double* const[3], double* const[3], const Layout&
 template int launch_ct<float>(float* const[3], float* const[3], const Layout&, cudaStream_t);
 
 int launch_update(const double* U0, const CVars& Pin, const Vars& Pout, double* Uout, double* const F[3],
-                  const Layout& L, const DevGeom& G, const Scheme& S, double cdt, int8_t* pflag,
-                  unsigned long long* cnt, cudaStream_t s) {
+                  const Layout& L, const DevGeom& G, const Scheme& S, const double* dtp, double coef, int8_t* pflag,
+                  unsigned long long* cnt, int tpb, cudaStream_t s) {
   const long long nz = (long long)L.n1 * L.n2 * L.n3;
-  k_update<<<nblocks(nz, TPB), TPB, 0, s>>>(U0, Pin, Pout, Uout, F[0], F[1], F[2], L, G, S, cdt, pflag, cnt);
+  k_update<<<nblocks(nz, tpb), tpb, 0, s>>>(U0, Pin, Pout, Uout, F[0], F[1], F[2], L, G, S, dtp, coef, pflag, cnt);
   return 1;
 }
 
 template <class TIN>
 int launch_update_mixed(const double* U0, const CVarsT<TIN>& Pin, const Vars& Pout64, const VarsT<float>& Pout32,
                         double* Uout, float* const F[3], const Layout& L, const DevGeom& G, const GeomT<float>& Gf,
-                        const Scheme& S, double cdt, int8_t* pflag, unsigned long long* cnt, cudaStream_t s) {
+                        const Scheme& S, const double* dtp, double coef, int8_t* pflag, unsigned long long* cnt,
+                        int tpb, cudaStream_t s) {
   const long long nz = (long long)L.n1 * L.n2 * L.n3;
-  k_update_mixed<TIN><<<nblocks(nz, TPB), TPB, 0, s>>>(U0, Pin, Pout64, Pout32, Uout, F[0], F[1], F[2], L, G, Gf, S,
-                                                      cdt, pflag, cnt);
+  k_update_mixed<TIN><<<nblocks(nz, tpb), tpb, 0, s>>>(U0, Pin, Pout64, Pout32, Uout, F[0], F[1], F[2], L, G, Gf, S,
+                                                      dtp, coef, pflag, cnt);
   return 1;
 }
-template int launch_update_mixed<double>(const double*, const CVarsT<double>&, const Vars&, const VarsT<float>&,
-                                         double*, float* const[3], const Layout&, const DevGeom&,
-                                         const GeomT<float>&, const Scheme&, double, int8_t*, unsigned long long*,
-                                         cudaStream_t);
-template int launch_update_mixed<float>(const double*, const CVarsT<float>&, const Vars&, const VarsT<float>&,
-                                        double*, float* const[3], const Layout&, const DevGeom&,
-                                        const GeomT<float>&, const Scheme&, double, int8_t*, unsigned long long*,
-                                        cudaStream_t);
+template int launch_update_mixed<double>(const double*, const CVarsT<double>&, const Vars&, const VarsT<float>&, double*,
+                                      float* const[3], const Layout&, const DevGeom&, const GeomT<float>&,
+                                      const Scheme&, const double*, double, int8_t*, unsigned long long*, int,
+                                      cudaStream_t);
+template int launch_update_mixed<float>(const double*, const CVarsT<float>&, const Vars&, const VarsT<float>&, double*,
+                                      float* const[3], const Layout&, const DevGeom&, const GeomT<float>&,
+                                      const Scheme&, const double*, double, int8_t*, unsigned long long*, int,
+                                      cudaStream_t);
 
 template <class T>
 int launch_fixup(const VarsT<T>& P, double* Uout, const int8_t* pflag, const Layout& L, const DevGeom& G,

@@ -73,6 +73,10 @@ def lib():
         L.kh_fill_ghosts.argtypes = [vp, vp, vp]
         L.kh_get_stats.argtypes = [vp, C.POINTER(Stats)]
         L.kh_profile.argtypes = [vp, C.c_int]
+        L.kh_set_graph.argtypes = [vp, C.c_int]
+        L.kh_set_launch.argtypes = [vp, C.c_int, C.c_int]
+        L.kh_get_launch.argtypes = [vp, ip, ip]
+        L.kh_autotune.argtypes = [vp, vp, vp, vp, C.c_double, ip, ip]
         L.kh_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
         L.kh_launch_count.argtypes = [vp]
         L.kh_launch_count.restype = C.c_int64
@@ -221,6 +225,23 @@ class Context:
         s = Stats()
         _check(lib().kh_get_stats(self._h, C.byref(s)), "kh_get_stats")
         return s
+
+    def set_graph(self, enable: bool):
+        _check(lib().kh_set_graph(self._h, 1 if enable else 0), "kh_set_graph")
+
+    def set_launch(self, tpb_flux: int, tpb_update: int):
+        _check(lib().kh_set_launch(self._h, int(tpb_flux), int(tpb_update)), "kh_set_launch")
+
+    def get_launch(self):
+        a, b = C.c_int(), C.c_int()
+        _check(lib().kh_get_launch(self._h, C.byref(a), C.byref(b)), "kh_get_launch")
+        return a.value, b.value
+
+    def autotune(self, U, P, B, dt: float):
+        a, b = C.c_int(), C.c_int()
+        _check(lib().kh_autotune(self._h, _ptr(U), _ptr(P), _ptr(B), float(dt), C.byref(a), C.byref(b)),
+               "kh_autotune")
+        return a.value, b.value
 
     TIMERS = ("bc", "flux_x1", "flux_x2", "flux_x3", "flux_ct", "update", "fixup", "cfl")
 

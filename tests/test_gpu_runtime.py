@@ -1,0 +1,79 @@
+"""Runtime features of the step: CUDA-graph replay, launch configuration and
+the autotuner leave the arithmetic unchanged (bitwise), on both precisions."""
+import numpy as np
+import pytest
+
+from gpu_helpers import GpuRun
+from paper_2408_01361_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kh():
+    from paper_2408_01361_gb300 import kh as _kh
+    return _kh
+
+
+def _run(kh, cfg, P, nsteps, graph=False, launch=None, autotune=False):
+    ctx = kh.Context(cfg)
+    g = GpuRun(ctx, cfg, P)
+    dt = 0.5 * ctx.cfl_dt(g.P, g.B)
+    if launch:
+        ctx.set_launch(*launch)
+    if autotune:
+        tf, tu = ctx.autotune(g.U, g.P, g.B, dt)
+        assert tf in (64, 128, 256) and tu in (64, 128, 256)
+        assert ctx.get_launch() == (tf, tu)
+    ctx.set_graph(graph)
+    dts = []
+    for _ in range(nsteps):
+        d, _ = ctx.step(g.U, g.P, g.B, dt)
+        dts.append(d)
+        dt = 0.5 * d
+    return g.host(), dts
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_graph_replay_is_bitwise(kh, precision):
+    cfg = inputs.torus_cfg(40, 24, 12, r_out=60.0)
+    cfg["precision"] = precision
+    P = inputs.torus_state(cfg, seed=2)
+    (U0, P0), d0 = _run(kh, cfg, P, 4)
+    (U1, P1), d1 = _run(kh, cfg, P, 4, graph=True)
+    assert np.array_equal(U0, U1) and np.array_equal(P0, P1) and d0 == d1
+
+
+def test_launch_config_and_autotune_are_bitwise(kh):
+    cfg = inputs.torus_cfg(40, 24, 12, r_out=60.0)
+    cfg["precision"] = "mixed"
+    P = inputs.torus_state(cfg, seed=2)
+    (U0, P0), _ = _run(kh, cfg, P, 2)
+    (U1, P1), _ = _run(kh, cfg, P, 2, launch=(64, 256))
+    (U2, P2), _ = _run(kh, cfg, P, 2, autotune=True, graph=True)
+    for A, B in ((U0, U1), (P0, P1), (U0, U2), (P0, P2)):
+        assert np.array_equal(A, B)
+
+
+def test_graph_follows_new_pointers(kh):
+    """Two states (different tensors) stepped alternately with graph replay
+    match the same sequence without graphs: a new pointer triple re-captures
+    instead of replaying stale pointers."""
+    cfg = inputs.linear_mode_cfg(12, ndim=3)
+    P = inputs.random_prims(cfg, seed=3, rho_range=(0.5, 1), u_range=(0.3, 1), ut_scale=(0.2, 0.2, 0.2),
+                            b_scale=(0.2, 0.2, 0.2))
+    out = []
+    for graph in (True, False):
+        ctx = kh.Context(cfg)
+        ctx.set_graph(graph)
+        a = GpuRun(ctx, cfg, P)
+        b = GpuRun(ctx, cfg, P)
+        ctx.step(a.U, a.P, a.B, 1e-3)
+        ctx.step(b.U, b.P, b.B, 1e-3)
+        ctx.step(b.U, b.P, b.B, 2e-3)
+        ctx.step(a.U, a.P, a.B, 1e-3)
+        out.append((a.host(), b.host()))
+    (ga, gb), (na, nb) = out
+    assert np.array_equal(ga[0], na[0]) and np.array_equal(gb[0], nb[0])
+    assert np.array_equal(ga[1], na[1]) and np.array_equal(gb[1], nb[1])
+    assert not np.array_equal(ga[0], gb[0])
