@@ -276,6 +276,7 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
   L.dx[0] = (c->x1max - c->x1min) / c->n1;
   L.dx[1] = (c->x2max - c->x2min) / c->n2;
   L.dx[2] = (c->x3max - c->x3min) / c->n3;
+  for (int q = 0; q < 3; ++q) L.idx[q] = 1.0 / L.dx[q];
   L.s[0] = L.ng; L.e[0] = L.ng + L.n1;
   L.s[1] = L.ng; L.e[1] = L.ng + L.n2;
   L.s[2] = L.ng3; L.e[2] = L.ng3 + L.n3;

@@ -27,6 +27,7 @@ struct Layout {
   long long plane;    // n1s * n2s * n3s
   long long gplane;   // n1s * n2s
   double dx[3];
+  double idx[3];      // 1 / dx
   int s[3], e[3];     // interior [s, e) per direction (i, j, k)
   KH_HD long long at(int k, int j, int i) const { return ((long long)k * n2s + j) * n1s + i; }
 };

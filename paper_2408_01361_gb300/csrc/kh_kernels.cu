@@ -590,8 +590,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_cfl(const T* c1, const T* c2, c
     int i, j, k;
     zone_ijk(L, t, i, j, k);
     const long long c = L.at(k, j, i);
-    double inv = fmax((double)c1[c], (double)c1[c + 1]) / L.dx[0] + fmax((double)c2[c], (double)c2[c + sj]) / L.dx[1];
-    if (L.ndim == 3) inv += fmax((double)c3[c], (double)c3[c + sk]) / L.dx[2];
+    double inv = fmax((double)c1[c], (double)c1[c + 1]) * L.idx[0] + fmax((double)c2[c], (double)c2[c + sj]) * L.idx[1];
+    if (L.ndim == 3) inv += fmax((double)c3[c], (double)c3[c + sk]) * L.idx[2];
     mx = fmax(mx, inv);
   }
   block_max_sum(mx, dummy);
