@@ -52,6 +52,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--n3", type=int, default=WORKLOAD["n3"], help="azimuthal zones (96 = the named workload)")
+    p.add_argument("--no-smr", action="store_true", help="skip the statically refined torus leg")
+    p.add_argument("--smr-only", action="store_true", help="run only the statically refined torus leg")
     p.add_argument("--precisions", default="mixed,fp64",
                    help="comma list; the first is the headline, the others are reported beside it")
     a = p.parse_args()
@@ -278,6 +280,54 @@ def measure(args, cfg, P0, ctx, dev, stream, dist, world, oracle_step):
     return out
 
 
+def measure_smr(args, dev, stream, precision):
+    """The statically refined torus (3 levels, 592 uneven blocks, 5.57 M zones)
+    stepped as one mesh: every kernel covers all blocks, ghost zones of every
+    block are filled by one gather, the step is replayed as a CUDA graph."""
+    import torch
+
+    from paper_2408_01361_gb300 import inputs, kh
+
+    base, blocks = inputs.smr_torus_layout()
+    norms = inputs.torus_norms(base)
+    Ps = [inputs.torus_state(inputs.block_cfg(base, b), seed=2, norms=norms) for b in blocks]
+    m = kh.Mesh(dict(base, precision=precision), blocks, device=dev)
+    P, B = m.to_device(Ps)
+    del Ps
+    U = m.empty(8)
+    m.prim_to_cons(P, B, U)
+    dt = m.cfl_dt(P, B)
+    m.set_graph(True)
+    for _ in range(args.warmup):
+        dt, _ = m.step(U, P, B, 0.5 * dt)
+    sampler = ClockSampler(dev.index or 0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    l0 = m.launches()
+    nfail = 0
+    e0.record(stream)
+    for _ in range(args.steps):
+        dt, nf = m.step(U, P, B, 0.5 * dt)
+        nfail += nf
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    from collections import Counter
+    shapes = Counter(f"L{b['level']}:{b['n1']}x{b['n2']}x{b['n3']}" for b in blocks)
+    out = {
+        "workload": "FM torus (as above) on 3 static refinement levels: level 2 over the disc, level 1 around "
+                    f"it, level 0 at the poles and outer radii; base {base['n1']}x{base['n2']}x{base['n3']}",
+        "precision": precision, "dtype": DTYPE[precision], "blocks": len(blocks), "block_shapes": dict(shapes),
+        "zones": m.zones, "ghost_cells": m.ghost_cells, "value": m.zones * args.steps / (ms * 1e-3), "unit": UNIT,
+        "ms_per_step": ms / args.steps, "graph": True, "gpu_launches": m.launches() - l0, "clocks": clocks,
+        "nfail_timed": nfail,
+    }
+    m.close()
+    return out
+
+
 def roofline_of(prof, nz, precision):
     hbm, hbm_kind, sm_max = peaks()
     groups = {k: v for k, v in prof.items() if v[1] > 0}
@@ -313,6 +363,11 @@ def run_kh(args, world, rank, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     stream = torch.cuda.current_stream(dev)
+
+    if args.smr_only:
+        out = {p: measure_smr(args, dev, stream, p) for p in args.precisions}
+        print(json.dumps({"smr": out}), flush=True)
+        return 0
 
     cfg64 = workload_cfg(args.n3)
     nz = cfg64["n1"] * cfg64["n2"] * cfg64["n3"]
@@ -365,6 +420,8 @@ def run_kh(args, world, rank, local):
                       "gpu_launches": q["launches"], "clocks": q["clocks"], "nfail_timed": q["nfail"],
                       "launch_config": q["launch"], "graph_replay": q["graph"]}
         line[f"speedup_{head}_vs_{prec}"] = r["value"] / q["value"]
+    if not args.no_smr and world == 1:
+        line["smr"] = {p: measure_smr(args, dev, stream, p) for p in args.precisions}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

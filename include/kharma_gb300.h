@@ -193,6 +193,60 @@ int kh_profile_read(const kh_ctx* ctx, double* ms, int64_t* count);
 /* Number of kernel launches issued by this context since creation. */
 int64_t kh_launch_count(const kh_ctx* ctx);
 
+/* ---------------------------------------------------------------------------
+ * Static mesh refinement: many blocks at several levels stepped together
+ * ("Requirements" section: refinement against the polar time-step limit;
+ * "Code Structure" section: SMR through the mesh framework).
+ *
+ * The domain and scheme come from a kh_coords whose n1, n2, n3 give the
+ * level-0 grid; level l is 2^l times finer in every direction (x1 and x2 only
+ * when n3 == 1). A block covers the level-l index box [i0, i0+n1) x [j0, j0+n2)
+ * x [k0, k0+n3); blocks must tile the domain exactly, blocks above level 0
+ * must start and end on even indices, and blocks whose ghost zones meet must
+ * be at most one level apart. Boundaries: periodic, outflow, polar.
+ *
+ * Arrays are arenas of all blocks in order: block b's U occupies
+ * U + 8 * off_b with 8 planes of its own padded shape (kh_mesh_block_shape),
+ * its P (5 planes) P + 5 * off_b, its B (3 planes) B + 3 * off_b, where off_b
+ * is the block's cell offset. Ghost cells are filled from other blocks: a
+ * same-level copy, an MC-limited linear prolongation from a coarser block,
+ * or the average of the 2x2(x2) cells of a finer block. A prolongation slope
+ * takes the coarse-level values on both sides of the coarse cell (a cell of
+ * a block at that level, or the mean of a finer block's cells there) and is
+ * zero where one is missing (past a non-periodic domain edge, or inside a
+ * still coarser block). Every block takes the same dt (no sub-cycling);
+ * fluxes at level interfaces are not corrected (no refluxing) and Flux-CT
+ * keeps divB only inside blocks.
+ *
+ * kh_mesh_init returns KH_EINVAL for blocks that overlap, leave a hole, are
+ * smaller than 4 cells a side (n3 == 1 in 2-D), are misaligned, meet a block
+ * more than one level away, or for more than 5 levels or 2^31 cells; it
+ * copies the block list, so the caller may free it on return. */
+typedef struct {
+  int level;
+  int i0, j0, k0;  /* first interior cell in level-l indices */
+  int n1, n2, n3;  /* interior cells */
+} kh_block;
+
+typedef struct kh_mesh kh_mesh;
+
+int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const kh_block* blocks, kh_mesh** out);
+int kh_mesh_block_shape(const kh_mesh* mesh, int b, int* n1s, int* n2s, int* n3s, int64_t* cell_offset);
+int64_t kh_mesh_cells(const kh_mesh* mesh);       /* sum of the blocks' allocation planes */
+int64_t kh_mesh_zones(const kh_mesh* mesh);       /* interior zones of all blocks */
+int64_t kh_mesh_ghost_cells(const kh_mesh* mesh); /* entries of the ghost map */
+int kh_mesh_set_stream(kh_mesh* mesh, void* cuda_stream);
+int kh_mesh_prim_to_cons(kh_mesh* mesh, const double* P, const double* B, double* U);
+int kh_mesh_fill_ghosts(kh_mesh* mesh, double* P, double* B);
+/* Same contract as kh_cfl_dt / kh_step, over all blocks; one kernel launch
+ * per step phase covers every block. */
+int kh_mesh_cfl_dt(kh_mesh* mesh, const double* P, const double* B, double* dt_cfl);
+int kh_mesh_step(kh_mesh* mesh, double* U, double* P, double* B, double dt, double* dt_cfl);
+int kh_mesh_set_graph(kh_mesh* mesh, int enable);
+int kh_mesh_get_stats(kh_mesh* mesh, kh_stats* out);
+int64_t kh_mesh_launch_count(const kh_mesh* mesh);
+int kh_mesh_destroy(kh_mesh* mesh);
+
 /* No-allocation divB (no counterpart in the paper; an interface addition).
  * For callers that cannot call cudaMalloc -- code confined to a pre-sized
  * memory pool or a hard device-memory budget, or frameworks whose allocator

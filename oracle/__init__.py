@@ -46,6 +46,7 @@ class Params(C.Structure):
         ("mks_smooth", C.c_double), ("cfl", C.c_double),
         ("rho_min", C.c_double), ("u_min", C.c_double), ("bsq_rho_max", C.c_double),
         ("bsq_u_max", C.c_double), ("u_rho_max", C.c_double), ("gamma_max", C.c_double),
+        ("x1ref", C.c_double),
     ]
 
 
@@ -73,6 +74,7 @@ def params(cfg: dict) -> Params:
     p.bsq_u_max = fl.get("bsq_u_max", 1e300)
     p.u_rho_max = fl.get("u_rho_max", 1e300)
     p.gamma_max = fl.get("gamma_max", 1e300)
+    p.x1ref = cfg.get("x1ref", cfg["x1"][0])
     return p
 
 
@@ -106,6 +108,8 @@ def lib():
                                 C.POINTER(C.c_long)]
         L.or_evolve.restype = C.c_double
         L.or_divb.argtypes = [PP, _dp, _dp, C.c_void_p]
+        L.or_stage.argtypes = [PP, _dp, _dp, C.c_double, _dp, _dp, C.c_void_p, C.c_void_p, C.c_void_p,
+                               C.POINTER(C.c_long)]
         L.or_point_flux.argtypes = [C.c_double, _dp, _dp, C.c_int, _dp]
         L.or_point_state.argtypes = [_dp, _dp, _dp]
         L.or_point_speeds.argtypes = [C.c_double, _dp, _dp, C.c_int, C.POINTER(C.c_double),
@@ -290,3 +294,14 @@ def recon(kind: str, q):
     lo = np.full_like(q, np.nan); hi = np.full_like(q, np.nan)
     lib().or_recon(RECON[kind], q.size, q, lo, hi)
     return lo, hi
+
+
+def stage(cfg: dict, U0, Pin, cdt: float, Uout, Pout):
+    """One stage on a grid with caller-filled ghosts; Uout/Pout updated in place
+    (interior). Returns (ctop[3] arrays, stats)."""
+    U0 = np.ascontiguousarray(U0, dtype=np.float64)
+    Pin = np.ascontiguousarray(Pin, dtype=np.float64)
+    ct = [np.zeros(Pin.shape[1:]) for _ in range(3)]
+    st = (C.c_long * 3)()
+    lib().or_stage(C.byref(params(cfg)), U0, Pin, float(cdt), Uout, Pout, *[_ptr(c) for c in ct], st)
+    return ct, list(st)

@@ -597,6 +597,28 @@ double or_cfl_dt(const or_params* c, const double* P, const double* dir_lo, cons
   return cfl_dt(gr, fx);
 }
 
+// One stage on a grid whose ghost zones the caller has filled (a block of a
+// multi-block mesh): fluxes from Pin, Uout = U0 + cdt (-div F + S(Pin)),
+// inversion, floors, fixup (interior neighbours only). Uout and Pout: full
+// arrays, interior written. ctop1..3 (nullable): signal speeds per face.
+// stats[0..2] as or_step (this stage only).
+void or_stage(const or_params* c, const double* U0, const double* Pin, double cdt, double* Uout, double* Pout,
+              double* ct1, double* ct2, double* ct3, long* stats) {
+  Grid gr;
+  build_grid(*c, gr);
+  Fluxes fx;
+  StageStats st;
+  stage(gr, U0, Pin, cdt, Uout, Pout, fx, st, nullptr);
+  double* Co[3] = {ct1, ct2, ct3};
+  for (int d = 0; d < 3; ++d)
+    if (Co[d]) std::memcpy(Co[d], fx.ctop[d].data(), fx.ctop[d].size() * sizeof(double));
+  if (stats) {
+    stats[0] = st.nfail;
+    stats[1] = st.nfloor;
+    stats[2] = st.nunfixed;
+  }
+}
+
 // One full two-stage step (conserved-synchronised). U (interior) is advanced in
 // place; P holds P^n on entry (the stage-1 input and inversion guess) and
 // P^{n+1} in the interior on exit. stats[0..2] = failed inversions, floored

@@ -51,6 +51,7 @@ struct Params {
   double bsq_rho_max, bsq_u_max;  // magnetisation floors
   double u_rho_max;               // temperature ceiling u/rho
   double gamma_max;               // Lorentz-factor ceiling
+  double x1ref;                   // FMKS blending reference: the x1 start of the whole domain
 };
 
 // Geometry of one point.
@@ -72,7 +73,8 @@ struct Geo {
 //   FMKS: r = exp(x1); theta_G = MKS theta; y = 2 x2 - 1;
 //         theta_J = pi/2 + N y (1 + (y/x_t)^alpha / (alpha + 1)),  N such that
 //         theta_J(x2=0) = 0 and theta_J(x2=1) = pi;
-//         theta = theta_G + exp(s (x1min - x1)) (theta_J - theta_G),
+//         theta = theta_G + exp(s (x1ref - x1)) (theta_J - theta_G), x1ref the
+//         x1 start of the whole domain,
 //         continued past the poles by reflection (below).
 template <class R>
 void native_to_ks(const Params& c, const R& x1, const R& x2, R& r, R& th) {
@@ -107,7 +109,7 @@ void native_to_ks(const Params& c, const R& x1, const R& x2, R& r, R& th) {
   R y = 2.0 * x2 - 1.0;
   double norm = 0.5 * pi / (1.0 + std::pow(c.poly_xt, -c.poly_alpha) / (c.poly_alpha + 1.0));
   R thJ = 0.5 * pi + norm * y * (1.0 + pow(y / c.poly_xt, c.poly_alpha) / (c.poly_alpha + 1.0));
-  th = thG + exp(c.mks_smooth * (c.x1min - x1)) * (thJ - thG);
+  th = thG + exp(c.mks_smooth * (c.x1ref - x1)) * (thJ - thG);
 }
 
 // Kerr metric in spherical Kerr-Schild coordinates (t, r, theta, phi), M = 1.

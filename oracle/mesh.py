@@ -1,0 +1,252 @@
+"""Statically refined mesh on the oracle (test infrastructure only).
+
+A mesh is a base configuration (its n1, n2, n3 the level-0 grid) plus blocks
+(level, first interior cell i0, j0, k0 in level indices, sizes n1, n2, n3);
+level l is 2^l times finer (x3 only when the problem is 3-D). Each block is a
+grid of its own, stepped by the oracle's single-stage routine after its
+ghost zones are filled here, cell by cell, from the block that owns the
+ghost cell's centre:
+
+* the centre is first carried through the physical boundaries: outflow in x1
+  moves it to the centre of the first (last) interior cell of its level and
+  forbids inflow through u~1; polar x2 reflects it across the axis and flips
+  u~2 and B2; periodic directions wrap;
+* the owner at the same level gives its cell's value; a coarser owner gives
+  its cell's value plus MC-limited slopes times the +-1/4 offset of the fine
+  centre; a finer owner gives the mean of its 2x2(x2) cells covering the
+  ghost cell;
+* a slope in one direction takes the coarse-level values at the centres one
+  coarse cell below and above: the value of the cell there if a block at the
+  coarse level owns it, the mean of the covering cells if a block one level
+  finer owns it; the slope is zero if either centre lies past a non-periodic
+  edge of the domain or inside a still coarser block.
+
+Every block takes the same dt; there is no flux correction at level
+interfaces. Written from positions in floating point, independently of the
+CUDA library's integer map.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import stage
+
+NV = 8
+
+
+def _mc(qm, q0, qp):
+    dm, dp = q0 - qm, qp - q0
+    if dm * dp <= 0.0:
+        return 0.0
+    cand = (2.0 * dm, 2.0 * dp, 0.5 * (dm + dp))
+    s = cand[0]
+    for c in cand[1:]:
+        if abs(c) < abs(s):
+            s = c
+    return s
+
+
+class OracleMesh:
+    def __init__(self, base: dict, blocks: list, block_cfg):
+        self.base = base
+        self.blocks = blocks
+        self.cfgs = [block_cfg(base, b) for b in blocks]
+        self.ng = base.get("ng", 3)
+        self.ndim = 3 if base["n3"] > 1 else 2
+        self.dom = [base["x1"], base["x2"], base["x3"]]
+
+    # ---- geometry of a block ----
+    def _dx(self, b):
+        c = self.cfgs[b]
+        return [(c[k][1] - c[k][0]) / c[n] for k, n in (("x1", "n1"), ("x2", "n2"), ("x3", "n3"))]
+
+    def _origin(self, b):
+        c = self.cfgs[b]
+        return [c["x1"][0], c["x2"][0], c["x3"][0]]
+
+    def _ng(self, d):
+        return self.ng if (d < 2 or self.ndim == 3) else 0
+
+    def _owner(self, x):
+        for b, c in enumerate(self.cfgs):
+            ok = True
+            for d, key in enumerate(("x1", "x2", "x3")):
+                if d == 2 and self.ndim == 2:
+                    continue
+                lo, hi = c[key]
+                if not (lo < x[d] < hi):
+                    ok = False
+                    break
+            if ok:
+                return b
+        raise ValueError(f"no block owns {x}")
+
+    def _cell(self, b, x):
+        """(local array index per direction) of block b's cell containing x."""
+        o, dx = self._origin(b), self._dx(b)
+        return [int(math.floor((x[d] - o[d]) / dx[d])) + self._ng(d) if (d < 2 or self.ndim == 3) else 0
+                for d in range(3)]
+
+    def _transform(self, b, x):
+        bc = self.base["bc"]
+        dx = self._dx(b)
+        flip = False
+        clamp = 0
+        (a1, b1), (a2, b2), (a3, b3) = self.dom
+        if x[0] < a1:
+            if bc[0] == "periodic":
+                x[0] += b1 - a1
+            else:
+                x[0], clamp = a1 + 0.5 * dx[0], 1
+        elif x[0] > b1:
+            if bc[1] == "periodic":
+                x[0] -= b1 - a1
+            else:
+                x[0], clamp = b1 - 0.5 * dx[0], 2
+        if x[1] < a2:
+            if bc[2] == "polar":
+                x[1], flip = 2 * a2 - x[1], not flip
+            elif bc[2] == "periodic":
+                x[1] += b2 - a2
+            else:
+                x[1] = a2 + 0.5 * dx[1]
+        elif x[1] > b2:
+            if bc[3] == "polar":
+                x[1], flip = 2 * b2 - x[1], not flip
+            elif bc[3] == "periodic":
+                x[1] -= b2 - a2
+            else:
+                x[1] = b2 - 0.5 * dx[1]
+        if self.ndim == 3:
+            if x[2] < a3:
+                x[2] = x[2] + (b3 - a3) if bc[4] == "periodic" else a3 + 0.5 * dx[2]
+            elif x[2] > b3:
+                x[2] = x[2] - (b3 - a3) if bc[5] == "periodic" else b3 - 0.5 * dx[2]
+        return x, flip, clamp
+
+    def _mean_fine(self, s, x, Ps):
+        """Mean of block s's cells covering the cell twice their size centred at x."""
+        dxs = self._dx(s)
+        acc = np.zeros(NV)
+        cnt = 0
+        for a3 in ((-0.5, 0.5) if self.ndim == 3 else (0.0,)):
+            for a2 in (-0.5, 0.5):
+                for a1 in (-0.5, 0.5):
+                    y = [x[0] + a1 * dxs[0], x[1] + a2 * dxs[1], x[2] + a3 * dxs[2]]
+                    ci = self._cell(s, y)
+                    acc += Ps[s][:, ci[2], ci[1], ci[0]]
+                    cnt += 1
+        return acc / cnt
+
+    def _coarse_value(self, level, cc, d, step, Ps):
+        """Level-`level` value at the centre cc shifted by `step` along d, or None."""
+        y = list(cc)
+        y[d] += step
+        lo, hi = self.dom[d]
+        if not (lo < y[d] < hi):
+            if self.base["bc"][2 * d + (0 if y[d] < lo else 1)] != "periodic":
+                return None
+            y[d] += (hi - lo) if y[d] < lo else -(hi - lo)
+        w = self._owner(y)
+        lw = self.blocks[w]["level"]
+        if lw == level:
+            ci = self._cell(w, y)
+            return Ps[w][:, ci[2], ci[1], ci[0]]
+        if lw == level + 1:
+            return self._mean_fine(w, y, Ps)
+        return None
+
+    def fill_ghosts(self, Ps):
+        """Fill every block's ghost cells in place (Ps: list of (8, N3, N2, N1))."""
+        lev = [blk["level"] for blk in self.blocks]
+        for b, P in enumerate(Ps):
+            N3, N2, N1 = P.shape[1:]
+            o, dx = self._origin(b), self._dx(b)
+            g = [self._ng(0), self._ng(1), self._ng(2)]
+            n = [self.cfgs[b]["n1"], self.cfgs[b]["n2"], self.cfgs[b]["n3"]]
+            for k in range(N3):
+                for j in range(N2):
+                    for i in range(N1):
+                        idx = (i, j, k)
+                        if all(g[d] <= idx[d] < g[d] + n[d] for d in range(3)):
+                            continue
+                        x = [o[d] + (idx[d] - g[d] + 0.5) * dx[d] for d in range(3)]
+                        if self.ndim == 2:
+                            x[2] = 0.5 * sum(self.dom[2])
+                        x, flip, clamp = self._transform(b, x)
+                        s = self._owner(x)
+                        Q = Ps[s]
+                        dl = lev[s] - lev[b]
+                        if dl == 0:
+                            ci = self._cell(s, x)
+                            val = Q[:, ci[2], ci[1], ci[0]].copy()
+                        elif dl == -1:
+                            ci = self._cell(s, x)
+                            os_, dxs = self._origin(s), self._dx(s)
+                            gs = [self._ng(0), self._ng(1), self._ng(2)]
+                            q0 = Q[:, ci[2], ci[1], ci[0]]
+                            val = q0.copy()
+                            cc = [os_[d] + (ci[d] - gs[d] + 0.5) * dxs[d] for d in range(3)]
+                            for d in range(self.ndim):
+                                sgn = 1.0 if x[d] > cc[d] else -1.0
+                                qm = self._coarse_value(lev[s], cc, d, -dxs[d], Ps)
+                                qp = self._coarse_value(lev[s], cc, d, +dxs[d], Ps)
+                                if qm is None or qp is None:
+                                    continue
+                                for v in range(NV):
+                                    val[v] += 0.25 * sgn * _mc(qm[v], q0[v], qp[v])
+                        elif dl == 1:
+                            val = self._mean_fine(s, x, Ps)
+                        else:
+                            raise ValueError("blocks more than one level apart")
+                        if flip:
+                            val[3] = -val[3]
+                            val[6] = -val[6]
+                        if clamp == 1 and val[2] > 0.0:
+                            val[2] = 0.0
+                        if clamp == 2 and val[2] < 0.0:
+                            val[2] = 0.0
+                        P[:, k, j, i] = val
+
+    def cfl_dt(self, cts):
+        """cfl / max over all blocks' zones of sum_d max(ctop faces)/dx_d."""
+        mx = 0.0
+        for b, ct in enumerate(cts):
+            c = self.cfgs[b]
+            g = [self._ng(0), self._ng(1), self._ng(2)]
+            n = [c["n1"], c["n2"], c["n3"]]
+            dx = self._dx(b)
+            sl = (slice(g[2], g[2] + n[2]), slice(g[1], g[1] + n[1]), slice(g[0], g[0] + n[0]))
+            inv = np.zeros((n[2], n[1], n[0]))
+            for d in range(self.ndim):
+                lo = ct[d][sl]
+                shift = [0, 0, 0]
+                shift[d] = 1
+                sh = tuple(slice(s_.start + shift[2 - q], s_.stop + shift[2 - q]) for q, s_ in enumerate(sl))
+                hi = ct[d][sh]
+                inv += np.maximum(lo, hi) / dx[d]
+            mx = max(mx, inv.max())
+        return self.base.get("cfl", 0.9) / mx
+
+    def step(self, Us, Ps, dt):
+        """One two-stage step of every block; returns (Us, Ps, dt_cfl, stats)."""
+        Pn = [np.array(P, copy=True) for P in Ps]
+        U0 = [np.array(U, copy=True) for U in Us]
+        self.fill_ghosts(Pn)
+        Ps_ = [np.array(P, copy=True) for P in Pn]
+        Us_ = [np.array(U, copy=True) for U in U0]
+        tot = [0, 0, 0]
+        for b in range(len(Pn)):
+            _, st = stage(self.cfgs[b], U0[b], Pn[b], 0.5 * dt, Us_[b], Ps_[b])
+            tot = [a + c for a, c in zip(tot, st)]
+        self.fill_ghosts(Ps_)
+        Pout = [np.array(P, copy=True) for P in Pn]
+        Uout = [np.array(U, copy=True) for U in U0]
+        cts = []
+        for b in range(len(Pn)):
+            ct, st = stage(self.cfgs[b], U0[b], Ps_[b], dt, Uout[b], Pout[b])
+            cts.append(ct)
+            tot = [a + c for a, c in zip(tot, st)]
+        return Uout, Pout, self.cfl_dt(cts), tot

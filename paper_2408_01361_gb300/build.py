@@ -16,8 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libkharma_gb300.so")
-SOURCES = ["kh_kernels.cu", "kh_api.cu", "kh_noalloc.cu"]
-HEADERS = ["kh_internal.h", "kh_physics.cuh", "kh_geom_math.h"]
+SOURCES = ["kh_kernels.cu", "kh_api.cu", "kh_noalloc.cu", "kh_mesh.cu"]
+HEADERS = ["kh_internal.h", "kh_physics.cuh", "kh_geom_math.h", "kh_zone.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -361,7 +361,7 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
     if (rc == KH_OK && x->pstarf) rc = cuda_fail(cudaMemset(x->pstarf, 0, NV * plf));
   }
   if (rc == KH_OK) {
-    x->launches += launch_geometry(x->cp, c->x2min, S.fl, L, x->geo, x->conn, x->flo, 0);
+    x->launches += launch_geometry(x->cp, c->x1min, c->x2min, S.fl, L, x->geo, x->conn, x->flo, 0);
     if (mixed) {
       x->launches += launch_to_f32(x->geo, x->geof, 3LL * NGEO * L.gplane, 0);
       x->launches += launch_to_f32(x->conn, x->connf, (long long)NCONN * L.gplane, 0);

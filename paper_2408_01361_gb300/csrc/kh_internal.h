@@ -63,7 +63,9 @@ struct Scheme {
 enum { CNT_FAIL = 0, CNT_FLOOR = 1, CNT_UNFIXED = 2, NCNT = 3 };
 
 // ---- launchers (kh_kernels.cu); each returns the number of kernels launched ----
-int launch_geometry(const CoordParams& cp, double x2min, const FloorParams& fl, const Layout& L, double* geo,
+// Geometry of a grid whose first interior cell starts at native (x1o, x2o);
+// cp.x1min is the FMKS blending reference (the x1 start of the whole domain).
+int launch_geometry(const CoordParams& cp, double x1o, double x2o, const FloorParams& fl, const Layout& L, double* geo,
                     double* conn, double* flo, cudaStream_t s);
 template <class T>
 int launch_bc(const VarsT<T>& P, const Layout& L, const Scheme& S, const T* dlo, const T* dhi, cudaStream_t s);

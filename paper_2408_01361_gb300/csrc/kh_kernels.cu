@@ -7,7 +7,7 @@
 // Layout: structure of arrays [var][k][j][i] with padded rows; the thread
 // index runs fastest along i so a warp reads consecutive doubles of a row.
 // Every device loop has a fixed bound; no kernel waits on another.
-#include "kh_internal.h"
+#include "kh_zone.cuh"
 
 namespace kh {
 
@@ -16,53 +16,22 @@ namespace {
 constexpr int TPB = 128;    // default threads per block
 constexpr int TPB_MAX = 256;
 
-// t -> (a, b, c) with t = a + n0 (b + n1 c), in 32-bit arithmetic (every
-// allocation holds fewer than 2^31 cells).
-__device__ __forceinline__ void split3(unsigned t, unsigned n0, unsigned n1, int& a, int& b, int& c) {
-  const unsigned q = t / n0;
-  a = (int)(t - q * n0);
-  const unsigned r = q / n1;
-  b = (int)(q - r * n1);
-  c = (int)r;
-}
 
 inline int nblocks(long long n, int tpb) { return (int)((n + tpb - 1) / tpb); }
-
-template <class R>
-__device__ __forceinline__ Met<R> load_met(const GeomT<R>& G, long long gplane, int loc, long long p) {
-  const R* b = G.g + (long long)loc * NGEO * gplane + p;
-  Met<R> m;
-  R c[10], u[10];
-#pragma unroll
-  for (int q = 0; q < 10; ++q) {
-    c[q] = __ldg(b + q * gplane);
-    u[q] = __ldg(b + (10 + q) * gplane);
-  }
-#pragma unroll
-  for (int mu = 0; mu < 4; ++mu)
-#pragma unroll
-    for (int nu = 0; nu < 4; ++nu) {
-      m.gcov[mu][nu] = c[sym_index(mu, nu)];
-      m.gcon[mu][nu] = u[sym_index(mu, nu)];
-    }
-  m.gdet = __ldg(b + 20 * gplane);
-  m.alpha = __ldg(b + 21 * gplane);
-  return m;
-}
 
 // ---------------------------------------------------------------------------
 // Geometry cache: one thread per (j, i) of the allocation. Metric, inverse,
 // sqrt(-g), lapse at CENT, x1 face and x2 face; connection and r at CENT.
 // ---------------------------------------------------------------------------
-__global__ void k_geometry(CoordParams cp, double x2min, FloorParams fl, Layout L, double* geo, double* conn,
-                           double* flo) {
+__global__ void k_geometry(CoordParams cp, double x1o, double x2o, FloorParams fl, Layout L, double* geo,
+                           double* conn, double* flo) {
   const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= L.gplane) return;
   const int i = (int)(p % L.n1s), j = (int)(p / L.n1s);
-  const double x1c = cp.x1min + (i - L.ng + 0.5) * L.dx[0];
-  const double x1f = cp.x1min + (i - L.ng) * L.dx[0];
-  const double x2c = x2min + (j - L.ng + 0.5) * L.dx[1];
-  const double x2f = x2min + (j - L.ng) * L.dx[1];
+  const double x1c = x1o + (i - L.ng + 0.5) * L.dx[0];
+  const double x1f = x1o + (i - L.ng) * L.dx[0];
+  const double x2c = x2o + (j - L.ng + 0.5) * L.dx[1];
+  const double x2f = x2o + (j - L.ng) * L.dx[1];
   for (int loc = 0; loc < 3; ++loc) {
     const double x1 = (loc == LOC_F1) ? x1f : x1c;
     const double x2 = (loc == LOC_F2) ? x2f : x2c;
@@ -183,11 +152,6 @@ __global__ void k_bc_x3(VarsT<T> P, Layout L, Scheme S) {
 // Reconstruction + LLF flux through the lower x^D face of cell (k, j, i),
 // over the interior faces plus one transverse row on each side (Flux-CT).
 // ---------------------------------------------------------------------------
-struct FaceBox {
-  int lo[3];
-  int n[3];
-};
-
 template <int D, int RECON, class TIN, class R>
 __global__ void __launch_bounds__(TPB_MAX) k_flux(CVarsT<TIN> P, Layout L, GeomT<R> G, Scheme S, FaceBox box, R* F,
                                                  R* ctop, int polar_lo, int polar_hi) {
@@ -196,48 +160,7 @@ __global__ void __launch_bounds__(TPB_MAX) k_flux(CVarsT<TIN> P, Layout L, GeomT
   if (t >= tot) return;
   int i, j, k;
   split3(t, box.n[0], box.n[1], i, j, k);
-  i += box.lo[0];
-  j += box.lo[1];
-  k += box.lo[2];
-  const long long c = L.at(k, j, i);
-  const long long st = (D == 1) ? 1 : (D == 2 ? (long long)L.n1s : (long long)L.n1s * L.n2s);
-  R PL[NV], PR[NV];
-#pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    const TIN* q = P.v[v] + c;
-    if (RECON == KH_RECON_MC) {
-      const R qm2 = (R)__ldg(q - 2 * st), qm1 = (R)__ldg(q - st), q0 = (R)__ldg(q), qp1 = (R)__ldg(q + st);
-      R lo, hi;
-      recon_mc(qm2, qm1, q0, lo, hi);
-      PL[v] = hi;
-      recon_mc(qm1, q0, qp1, lo, hi);
-      PR[v] = lo;
-    } else {
-      const R qm3 = (R)__ldg(q - 3 * st), qm2 = (R)__ldg(q - 2 * st), qm1 = (R)__ldg(q - st), q0 = (R)__ldg(q);
-      const R qp1 = (R)__ldg(q + st), qp2 = (R)__ldg(q + 2 * st);
-      PL[v] = weno5_plus(qm3, qm2, qm1, q0, qp1);
-      PR[v] = weno5_plus(qp2, qp1, q0, qm1, qm2);
-    }
-  }
-  const Met<R> m = load_met(G, L.gplane, D == 3 ? LOC_CENT : D, (long long)j * L.n1s + i);
-  const R gam = (R)S.gam;
-  FState<R> sL, sR;
-  fluid_state(PL, m, sL);
-  fluid_state(PR, m, sR);
-  R FL[NV], UL[NV], FR[NV], UR[NV];
-  flux_cons(PL, sL, m, gam, D, FL, UL);
-  flux_cons(PR, sR, m, gam, D, FR, UR);
-  R cmaxL, cminL, cmaxR, cminR;
-  signal_speeds(PL, sL, m, gam, D, cmaxL, cminL);
-  signal_speeds(PR, sR, m, gam, D, cmaxR, cminR);
-  const R cm = fmax(R(0), fmax(cmaxL, cmaxR));
-  const R cn = fmax(R(0), fmax(-cminL, -cminR));
-  const R ct = fmax(cm, cn);
-  const bool axis = (D == 2) && ((polar_lo && j == L.s[1]) || (polar_hi && j == L.e[1]));
-#pragma unroll
-  for (int v = 0; v < NV; ++v)
-    F[v * L.plane + c] = axis ? R(0) : R(0.5) * (FL[v] + FR[v]) - R(0.5) * ct * (UR[v] - UL[v]);
-  ctop[c] = ct;
+  flux_face<D, RECON, TIN, R>(P, L, G, S, i + box.lo[0], j + box.lo[1], k + box.lo[2], F, ctop, polar_lo, polar_hi);
 }
 
 // Corner EMFs of Flux-CT (Toth 2000) from the LLF field fluxes:
@@ -250,34 +173,9 @@ __global__ void k_emf(const R* F1, const R* F2, const R* F3, R* e1, R* e2, R* e3
   if (t >= (unsigned)n0 * n1 * n2) return;
   int i, j, k;
   split3(t, n0, n1, i, j, k);
-  i += L.s[0];
-  j += L.s[1];
-  k += (L.ndim == 3 ? L.s[2] : 0);
-  const long long c = L.at(k, j, i);
-  const long long P = L.plane, sj = L.n1s, sk = (long long)L.n1s * L.n2s;
-  const R q = R(0.25);
-  const R* F1B2 = F1 + V_B2 * P;
-  const R* F2B1 = F2 + V_B1 * P;
-  if (L.ndim == 2) {
-    e3[c] = q * (F1B2[c] + F1B2[c - sj] - F2B1[c] - F2B1[c - 1]);
-    return;
-  }
-  if (k < L.e[2]) e3[c] = q * (F1B2[c] + F1B2[c - sj] - F2B1[c] - F2B1[c - 1]);
-  if (i < L.e[0]) {
-    const R* F2B3 = F2 + V_B3 * P;
-    const R* F3B2 = F3 + V_B2 * P;
-    e1[c] = q * (F2B3[c] + F2B3[c - sk] - F3B2[c] - F3B2[c - sj]);
-  }
-  if (j < L.e[1]) {
-    const R* F3B1 = F3 + V_B1 * P;
-    const R* F1B3 = F1 + V_B3 * P;
-    e2[c] = q * (F3B1[c] + F3B1[c - 1] - F1B3[c] - F1B3[c - sk]);
-  }
+  emf_at<R>(F1, F2, F3, e1, e2, e3, L, i + L.s[0], j + L.s[1], k + (L.ndim == 3 ? L.s[2] : 0));
 }
 
-// Field fluxes from edge EMFs (the other slots keep their LLF values):
-//   F1 = (0, (e3 + e3(j+1))/2, -(e2 + e2(k+1))/2), F2 = (-(e3 + e3(i+1))/2, 0, (e1 + e1(k+1))/2),
-//   F3 = ((e2 + e2(i+1))/2, -(e1 + e1(j+1))/2, 0); in 2-D only e3 and the B1, B2 slots.
 template <class R>
 __global__ void k_apply_ct(R* F1, R* F2, R* F3, const R* e1, const R* e2, const R* e3, Layout L) {
   const int n0 = L.e[0] - L.s[0] + 1, n1 = L.e[1] - L.s[1] + 1, n2 = (L.ndim == 3) ? L.e[2] - L.s[2] + 1 : 1;
@@ -285,223 +183,39 @@ __global__ void k_apply_ct(R* F1, R* F2, R* F3, const R* e1, const R* e2, const 
   if (t >= (unsigned)n0 * n1 * n2) return;
   int i, j, k;
   split3(t, n0, n1, i, j, k);
-  i += L.s[0];
-  j += L.s[1];
-  k += (L.ndim == 3 ? L.s[2] : 0);
-  const long long c = L.at(k, j, i);
-  const long long P = L.plane, sj = L.n1s, sk = (long long)L.n1s * L.n2s;
-  const bool in_i = i < L.e[0], in_j = j < L.e[1];
-  const bool in_k = (L.ndim == 2) || k < L.e[2];
-  const R h = R(0.5);
-  if (in_j && in_k) {  // x1 faces
-    F1[V_B1 * P + c] = R(0);
-    F1[V_B2 * P + c] = h * (e3[c] + e3[c + sj]);
-    if (L.ndim == 3) F1[V_B3 * P + c] = -h * (e2[c] + e2[c + sk]);
-  }
-  if (in_i && in_k) {  // x2 faces
-    F2[V_B1 * P + c] = -h * (e3[c] + e3[c + 1]);
-    F2[V_B2 * P + c] = R(0);
-    if (L.ndim == 3) F2[V_B3 * P + c] = h * (e1[c] + e1[c + sk]);
-  }
-  if (L.ndim == 3 && in_i && in_j) {  // x3 faces
-    F3[V_B1 * P + c] = h * (e2[c] + e2[c + 1]);
-    F3[V_B2 * P + c] = -h * (e1[c] + e1[c + sj]);
-    F3[V_B3 * P + c] = R(0);
-  }
+  apply_ct_at<R>(F1, F2, F3, e1, e2, e3, L, i + L.s[0], j + L.s[1], k + (L.ndim == 3 ? L.s[2] : 0));
 }
 
 // ---------------------------------------------------------------------------
 // Update of one interior zone: U = U0 + cdt (-div F + S(Pin)), inversion with
 // Pin as the guess, floors; writes Pout, pflag and (stage 2) U.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void zone_ijk(const Layout& L, unsigned t, int& i, int& j, int& k) {
-  split3(t, L.e[0] - L.s[0], L.e[1] - L.s[1], i, j, k);
-  i += L.s[0];
-  j += L.s[1];
-  k += L.s[2];
-}
-
-__device__ __forceinline__ unsigned nzones(const Layout& L) {
-  return (unsigned)(L.e[0] - L.s[0]) * (L.e[1] - L.s[1]) * (L.e[2] - L.s[2]);
-}
-
-// S_nu = sqrt(-g) T^k_l Gamma^l_{nu k} for nu = t, 1, 2, 3 (energy and
-// momentum slots); zero for rho and B.
-template <class R>
-__device__ __forceinline__ void source_terms(const R* P, const Met<R>& m, const R* conn, long long gplane, long long p,
-                                             R gam, R* S) {
-  FState<R> s;
-  fluid_state(P, m, s);
-  const R pg = (gam - R(1)) * P[V_U];
-  const R eta = P[V_RHO] + P[V_U] + pg + s.bsq;
-  const R ptot = pg + R(0.5) * s.bsq;
-  R T[4][4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) T[a][b] = eta * s.ucon[a] * s.ucov[b] - s.bcon[a] * s.bcov[b] + (a == b ? ptot : R(0));
-#pragma unroll
-  for (int nu = 0; nu < 4; ++nu) {
-    R acc = R(0);
-#pragma unroll
-    for (int l = 0; l < 4; ++l)
-#pragma unroll
-      for (int kk = 0; kk < 4; ++kk) acc += T[kk][l] * __ldg(conn + (l * 10 + sym_index(nu, kk)) * gplane + p);
-    S[V_U + nu] = m.gdet * acc;
-  }
-}
 
 __global__ void __launch_bounds__(TPB_MAX) k_update(const double* U0, CVars Pin, Vars Pout, double* Uout,
-                                               const double* F1, const double* F2, const double* F3, Layout L,
-                                               DevGeom G, Scheme S, const double* dtp, double coef, int8_t* pflag,
-                                               unsigned long long* cnt) {
+                                                   const double* F1, const double* F2, const double* F3, Layout L,
+                                                   DevGeom G, Scheme S, const double* dtp, double coef, int8_t* pflag,
+                                                   unsigned long long* cnt) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nzones(L)) return;
   int i, j, k;
   zone_ijk(L, t, i, j, k);
-  const double cdt = coef * __ldg(dtp);
-  const long long c = L.at(k, j, i);
-  const long long p = (long long)j * L.n1s + i;
-  const long long sj = L.n1s, sk = (long long)L.n1s * L.n2s;
-  const Met<double> m = load_met(G, L.gplane, LOC_CENT, p);
-  double P[NV];
-#pragma unroll
-  for (int v = 0; v < NV; ++v) P[v] = Pin.v[v][c];
-  double Sv[NV] = {0, 0, 0, 0, 0, 0, 0, 0};
-  source_terms(P, m, G.conn, L.gplane, p, S.gam, Sv);
-  double U[NV];
-#pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    const long long o = v * L.plane + c;
-    double div = (F1[o + 1] - F1[o]) / L.dx[0] + (F2[o + sj] - F2[o]) / L.dx[1];
-    if (L.ndim == 3) div += (F3[o + sk] - F3[o]) / L.dx[2];
-    U[v] = U0[o] + cdt * (-div + Sv[v]);
-  }
-  double Pn[NV];
-#pragma unroll
-  for (int v = 0; v < NV; ++v) Pn[v] = P[v];
-  const int flag = noble2d(U, m, S.gam, S.c2p, Pn);
-  const double ig = 1.0 / m.gdet;
-  Pn[V_B1] = U[V_B1] * ig;
-  Pn[V_B2] = U[V_B2] * ig;
-  Pn[V_B3] = U[V_B3] * ig;
-  int fmask = 0;
-  if (flag == 0) {
-    FState<double> s;
-    fluid_state(Pn, m, s);
-    fmask = apply_floors(S.fl, m, __ldg(G.flo + p), __ldg(G.flo + L.gplane + p), s.bsq, Pn);
-    if (fmask && Uout) {
-      fluid_state(Pn, m, s);
-      cons_only(Pn, s, m, S.gam, U);
-    }
-  }
-#pragma unroll
-  for (int v = 0; v < NV; ++v) Pout.v[v][c] = Pn[v];
-  if (Uout) {
-#pragma unroll
-    for (int v = 0; v < NV; ++v) Uout[v * L.plane + c] = U[v];
-  }
-  pflag[c] = (int8_t)flag;
-  if (flag) atomicAdd(cnt + CNT_FAIL, 1ULL);
-  if (fmask) atomicAdd(cnt + CNT_FLOOR, 1ULL);
+  update_zone(U0, Pin, Pout, Uout, F1, F2, F3, L, G, S, coef * __ldg(dtp), pflag, cnt, i, j, k);
 }
 
-// Mixed-precision update of one interior zone: the divergence of the FP32
-// fluxes and the FP32 source terms (FP32 metric and connection) give dU in
-// FP32; U = U0 + cdt dU is accumulated in FP64; the Noble-2D inversion and the
-// floors run in FP64 on the FP64 metric, the stage input serving as guess.
 template <class TIN>
 __global__ void __launch_bounds__(TPB_MAX) k_update_mixed(const double* U0, CVarsT<TIN> Pin, Vars Pout64,
-                                                     VarsT<float> Pout32, double* Uout, const float* F1,
-                                                     const float* F2, const float* F3, Layout L, DevGeom G,
-                                                     GeomT<float> Gf, Scheme S, const double* dtp, double coef,
-                                                     int8_t* pflag, unsigned long long* cnt) {
+                                                         VarsT<float> Pout32, double* Uout, const float* F1,
+                                                         const float* F2, const float* F3, Layout L, DevGeom G,
+                                                         GeomT<float> Gf, Scheme S, const double* dtp, double coef,
+                                                         int8_t* pflag, unsigned long long* cnt) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nzones(L)) return;
   int i, j, k;
   zone_ijk(L, t, i, j, k);
-  const double cdt = coef * __ldg(dtp);
-  const long long c = L.at(k, j, i);
-  const long long p = (long long)j * L.n1s + i;
-  const long long sj = L.n1s, sk = (long long)L.n1s * L.n2s;
-  float Pf[NV];
-  double Pn[NV];
-#pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    const TIN x = Pin.v[v][c];
-    Pf[v] = (float)x;
-    Pn[v] = (double)x;
-  }
-  float Sv[NV] = {0, 0, 0, 0, 0, 0, 0, 0};
-  {
-    const Met<float> mf = load_met(Gf, L.gplane, LOC_CENT, p);
-    source_terms(Pf, mf, Gf.conn, L.gplane, p, (float)S.gam, Sv);
-  }
-  const float i1 = (float)(1.0 / L.dx[0]), i2 = (float)(1.0 / L.dx[1]), i3 = (float)(1.0 / L.dx[2]);
-  double U[NV];
-#pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    const long long o = v * L.plane + c;
-    float div = (F1[o + 1] - F1[o]) * i1 + (F2[o + sj] - F2[o]) * i2;
-    if (L.ndim == 3) div += (F3[o + sk] - F3[o]) * i3;
-    U[v] = U0[o] + cdt * (double)(Sv[v] - div);
-  }
-  const Met<double> m = load_met(G, L.gplane, LOC_CENT, p);
-  const int flag = noble2d_mixed(U, m, S.gam, S.c2p, Pn);
-  const double ig = 1.0 / m.gdet;
-  Pn[V_B1] = U[V_B1] * ig;
-  Pn[V_B2] = U[V_B2] * ig;
-  Pn[V_B3] = U[V_B3] * ig;
-  int fmask = 0;
-  if (flag == 0) {
-    // FP32 fluid state for the magnetisation floors (a threshold) and for the
-    // conserved increment of a density/energy floor.
-    const Met<float> mf = load_met(Gf, L.gplane, LOC_CENT, p);
-    float q[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) q[v] = (float)Pn[v];
-    FState<float> sf;
-    fluid_state(q, mf, sf);
-    const double rho0 = Pn[V_RHO], u0 = Pn[V_U];
-    fmask = apply_floors(S.fl, m, __ldg(G.flo + p), __ldg(G.flo + L.gplane + p), (double)sf.bsq, Pn);
-    if (fmask && Uout) {
-      if (fmask & 4) {  // the Lorentz-factor ceiling changed u~: full FP64 recompute
-        FState<double> s;
-        fluid_state(Pn, m, s);
-        cons_only(Pn, s, m, S.gam, U);
-      } else {
-        // at fixed u~ and B, U is linear in (rho, u): add
-        // drho dU/drho + du dU/du, formed in FP32, to the FP64 U
-        const float drho = (float)(Pn[V_RHO] - rho0), du = (float)(Pn[V_U] - u0);
-        const float gm = (float)S.gam, gd = mf.gdet, ut = sf.ucon[0];
-        U[V_RHO] += (double)(gd * ut * drho);
-        U[V_U] += (double)(gd * ((ut * sf.ucov[0] + ut) * drho + (gm * ut * sf.ucov[0] + gm - 1.0f) * du));
-        U[V_U1] += (double)(gd * ut * sf.ucov[1] * (drho + gm * du));
-        U[V_U2] += (double)(gd * ut * sf.ucov[2] * (drho + gm * du));
-        U[V_U3] += (double)(gd * ut * sf.ucov[3] * (drho + gm * du));
-      }
-    }
-  }
-  if (Pout64.v[0]) {
-#pragma unroll
-    for (int v = 0; v < NV; ++v) Pout64.v[v][c] = Pn[v];
-  }
-  if (Pout32.v[0]) {
-#pragma unroll
-    for (int v = 0; v < NV; ++v) Pout32.v[v][c] = (float)Pn[v];
-  }
-  if (Uout) {
-#pragma unroll
-    for (int v = 0; v < NV; ++v) Uout[v * L.plane + c] = U[v];
-  }
-  pflag[c] = (int8_t)flag;
-  if (flag) atomicAdd(cnt + CNT_FAIL, 1ULL);
-  if (fmask) atomicAdd(cnt + CNT_FLOOR, 1ULL);
+  update_mixed_zone<TIN>(U0, Pin, Pout64, Pout32, Uout, F1, F2, F3, L, G, Gf, S, coef * __ldg(dtp), pflag, cnt, i,
+                         j, k);
 }
 
-// Fixup: a zone whose inversion failed takes the equal-weight mean of the
-// fluid primitives of its non-failed interior neighbours (3x3x3, or 3x3 in
-// 2-D); with none it keeps the stage input. Then floors; U recomputed.
 template <class T>
 __global__ void __launch_bounds__(TPB) k_fixup(VarsT<T> P, double* Uout, const int8_t* pflag, Layout L, DevGeom G,
                                               Scheme S, unsigned long long* cnt) {
@@ -509,43 +223,7 @@ __global__ void __launch_bounds__(TPB) k_fixup(VarsT<T> P, double* Uout, const i
   if (t >= nzones(L)) return;
   int i, j, k;
   zone_ijk(L, t, i, j, k);
-  const long long c = L.at(k, j, i);
-  if (pflag[c] == 0) return;
-  double sum[5] = {0, 0, 0, 0, 0};
-  int n = 0;
-  const int kl = L.ndim == 3 ? -1 : 0, kh = L.ndim == 3 ? 1 : 0;
-  for (int dk = kl; dk <= kh; ++dk)
-    for (int dj = -1; dj <= 1; ++dj)
-      for (int di = -1; di <= 1; ++di) {
-        if (dk == 0 && dj == 0 && di == 0) continue;
-        const int ii = i + di, jj = j + dj, kk = k + dk;
-        if (ii < L.s[0] || ii >= L.e[0] || jj < L.s[1] || jj >= L.e[1] || kk < L.s[2] || kk >= L.e[2]) continue;
-        const long long q = L.at(kk, jj, ii);
-        if (pflag[q] != 0) continue;
-        for (int v = 0; v < 5; ++v) sum[v] += (double)P.v[v][q];
-        ++n;
-      }
-  double Pn[NV];
-  for (int v = 0; v < NV; ++v) Pn[v] = (double)P.v[v][c];
-  if (n > 0) {
-    for (int v = 0; v < 5; ++v) Pn[v] = sum[v] / n;
-  } else {
-    atomicAdd(cnt + CNT_UNFIXED, 1ULL);
-  }
-  const long long p = (long long)j * L.n1s + i;
-  const Met<double> m = load_met(G, L.gplane, LOC_CENT, p);
-  FState<double> sb;
-  fluid_state(Pn, m, sb);
-  const int fmask = apply_floors(S.fl, m, __ldg(G.flo + p), __ldg(G.flo + L.gplane + p), sb.bsq, Pn);
-  if (fmask) atomicAdd(cnt + CNT_FLOOR, 1ULL);
-  for (int v = 0; v < 5; ++v) P.v[v][c] = (T)Pn[v];
-  if (Uout) {
-    FState<double> s;
-    fluid_state(Pn, m, s);
-    double U[NV];
-    cons_only(Pn, s, m, S.gam, U);
-    for (int v = 0; v < NV; ++v) Uout[v * L.plane + c] = U[v];
-  }
+  fixup_zone<T>(P, Uout, pflag, L, G, S, cnt, i, j, k);
 }
 
 // ---------------------------------------------------------------------------
@@ -584,15 +262,11 @@ template <class T>
 __global__ void __launch_bounds__(RED_THREADS) k_cfl(const T* c1, const T* c2, const T* c3, Layout L,
                                                     double* partial) {
   const unsigned nz = nzones(L);
-  const long long sj = L.n1s, sk = (long long)L.n1s * L.n2s;
   double mx = 0.0, dummy = 0.0;
   for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < nz; t += gridDim.x * blockDim.x) {
     int i, j, k;
     zone_ijk(L, t, i, j, k);
-    const long long c = L.at(k, j, i);
-    double inv = fmax((double)c1[c], (double)c1[c + 1]) * L.idx[0] + fmax((double)c2[c], (double)c2[c + sj]) * L.idx[1];
-    if (L.ndim == 3) inv += fmax((double)c3[c], (double)c3[c + sk]) * L.idx[2];
-    mx = fmax(mx, inv);
+    mx = fmax(mx, cfl_inv_zone(c1, c2, c3, L, i, j, k));
   }
   block_max_sum(mx, dummy);
   if (threadIdx.x == 0) {
@@ -718,9 +392,9 @@ int reduction_blocks(const Layout& L) {
   return b < 1 ? 1 : (int)b;
 }
 
-int launch_geometry(const CoordParams& cp, double x2min, const FloorParams& fl, const Layout& L, double* geo,
+int launch_geometry(const CoordParams& cp, double x1o, double x2o, const FloorParams& fl, const Layout& L, double* geo,
                     double* conn, double* flo, cudaStream_t s) {
-  k_geometry<<<nblocks(L.gplane, TPB), TPB, 0, s>>>(cp, x2min, fl, L, geo, conn, flo);
+  k_geometry<<<nblocks(L.gplane, TPB), TPB, 0, s>>>(cp, x1o, x2o, fl, L, geo, conn, flo);
   return 1;
 }
 
@@ -748,13 +422,7 @@ template int launch_bc<float>(const VarsT<float>&, const Layout&, const Scheme&,
 template <int D, class TIN, class R>
 static int launch_flux_d(const CVarsT<TIN>& P, const Layout& L, const GeomT<R>& G, const Scheme& S, R* F, R* ctop,
                          int tpb, cudaStream_t s) {
-  FaceBox b;
-  for (int a = 0; a < 3; ++a) {
-    const bool active = a < 2 || L.ndim == 3;
-    if (!active) { b.lo[a] = 0; b.n[a] = 1; continue; }
-    if (a == D - 1) { b.lo[a] = L.s[a]; b.n[a] = L.e[a] - L.s[a] + 1; }
-    else { b.lo[a] = L.s[a] - 1; b.n[a] = L.e[a] - L.s[a] + 2; }
-  }
+  const FaceBox b = face_box(L, D);
   const long long tot = (long long)b.n[0] * b.n[1] * b.n[2];
   const int plo = S.bc[2] == KH_BC_POLAR, phi = S.bc[3] == KH_BC_POLAR;
   if (S.recon == KH_RECON_MC)

@@ -1,0 +1,1046 @@
+// Static mesh refinement on one GPU: many uneven blocks at several levels
+// stepped by one launch per kernel over all blocks (arXiv 2408.01361,
+// "Requirements": refinement of the grid away from where the polar zones
+// limit the time step; "Code Structure": SMR/AMR through Parthenon).
+//
+// Every kernel of the step runs over the concatenation of all blocks' items
+// (faces, edges, zones, ghost cells): a thread finds its block by binary
+// search over a per-kernel prefix sum of item counts, then runs the same
+// per-item device function as the single-grid kernels with that block's
+// layout, geometry and arena offsets. Ghost cells of every block are filled
+// by ONE gather kernel from a map built on the host at set-up: each ghost
+// cell's centre is carried through the physical boundary rules (outflow
+// clamps to the first interior cell, polar reflection, periodic wrap), the
+// leaf block owning that point is found, and the ghost cell copies the
+// owner's cell (same level), prolongs from the owner's coarse cell with
+// MC-limited slopes (coarser owner), or averages the owner's 2x2(x2) fine
+// cells (finer owner). The slopes take the coarse-level values beside the
+// coarse cell: a cell of a block at that level, or the mean of a finer
+// block's cells there; where neither exists (past a non-periodic domain edge,
+// or inside a still coarser block) the slope in that direction is zero.
+// Every source is an interior cell, so the fill has no ordering between
+// ghost cells.
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "kh_zone.cuh"
+
+using namespace kh;
+
+namespace {
+
+constexpr int MTPB = 128;
+
+struct MBlock {
+  Layout L;
+  long long off;   // cell offset of the block in cell-concatenated arenas
+  long long goff;  // (j, i) offset in the geometry arenas
+  FaceBox fb[3];
+  int polar_lo, polar_hi;
+  int level;
+  int i0, j0, k0;
+};
+
+enum { G_COPY = 0, G_PROLONG = 1, G_RESTRICT = 2 };
+enum { G_FLIP2 = 1, G_CLAMP_IN = 2, G_CLAMP_OUT = 4 };
+
+struct GhostOp {
+  int dst_block, dst_cell;
+  int src_block, src_cell;
+  int nbi;             // prolongation: index of the coarse cell's neighbour record
+  signed char off[3];  // prolongation: sign of the fine-cell offset from the coarse centre per direction
+  unsigned char mode, flags, pad;
+};
+
+// Coarse-level values on either side of a prolonged coarse cell, per
+// direction: [d][0] below, [d][1] above. mode G_COPY: a cell of a block at
+// the coarse level; G_RESTRICT: the mean of a finer block's 2x2(x2) cells
+// starting at that cell; NB_NONE: no value (beyond a non-periodic edge of
+// the domain, or inside a still coarser block), the slope is then zero.
+enum { NB_NONE = 3 };
+struct ProlongNb {
+  int block[3][2];
+  int cell[3][2];
+  unsigned char mode[3][2];
+  unsigned char pad[2];
+};
+
+// Arena of 8 primitive slots: slots [0, na) at a + na * off + v * plane,
+// slots [na, 8) at b + (8 - na) * off + (v - na) * plane.
+template <class T> struct Arena {
+  T* a;
+  T* b;
+  int na;
+};
+
+template <class T> __device__ __forceinline__ VarsT<T> vars_at(const Arena<T>& A, const MBlock& m) {
+  VarsT<T> V;
+#pragma unroll
+  for (int v = 0; v < NV; ++v)
+    V.v[v] = v < A.na ? A.a + A.na * m.off + v * m.L.plane : A.b + (NV - A.na) * m.off + (v - A.na) * m.L.plane;
+  return V;
+}
+template <class T> __device__ __forceinline__ CVarsT<T> cvars_at(const Arena<T>& A, const MBlock& m) {
+  const VarsT<T> V = vars_at(A, m);
+  CVarsT<T> C;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) C.v[v] = V.v[v];
+  return C;
+}
+
+struct GeoArena {
+  const double* g;
+  const double* conn;
+  const double* flo;
+  const float* gf;
+  const float* connf;
+};
+__device__ __forceinline__ DevGeom geo64(const GeoArena& A, const MBlock& m) {
+  return DevGeom{A.g + 3LL * NGEO * m.goff, A.conn + (long long)NCONN * m.goff, A.flo + 2 * m.goff};
+}
+__device__ __forceinline__ GeomT<float> geo32(const GeoArena& A, const MBlock& m) {
+  return GeomT<float>{A.gf + 3LL * NGEO * m.goff, A.connf + (long long)NCONN * m.goff, A.flo + 2 * m.goff};
+}
+
+// Largest b with pre[b] <= t (pre has nb + 1 entries, pre[0] = 0).
+__device__ __forceinline__ int find_block(const unsigned* pre, int nb, unsigned t) {
+  int lo = 0, hi = nb;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(pre + mid) <= t) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+template <int D, int RECON, class TIN, class R>
+__global__ void __launch_bounds__(256) km_flux(const MBlock* blk, const unsigned* pre, int nb, Arena<TIN> Pin,
+                                              GeoArena GA, Scheme S, R* F, R* ctop) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= __ldg(pre + nb)) return;
+  const int b = find_block(pre, nb, t);
+  const MBlock& m = blk[b];
+  int i, j, k;
+  const FaceBox& fb = m.fb[D - 1];
+  split3(t - __ldg(pre + b), fb.n[0], fb.n[1], i, j, k);
+  GeomT<R> G;
+  if constexpr (sizeof(R) == sizeof(double)) G = geo64(GA, m); else G = geo32(GA, m);
+  flux_face<D, RECON, TIN, R>(cvars_at(Pin, m), m.L, G, S, i + fb.lo[0], j + fb.lo[1], k + fb.lo[2],
+                              F + NV * m.off, ctop + m.off, m.polar_lo, m.polar_hi);
+}
+
+template <class R>
+__global__ void km_ct(const MBlock* blk, const unsigned* pre, int nb, R* F1, R* F2, R* F3, R* e1, R* e2, R* e3,
+                      int phase) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= __ldg(pre + nb)) return;
+  const int b = find_block(pre, nb, t);
+  const MBlock& m = blk[b];
+  const Layout& L = m.L;
+  int i, j, k;
+  split3(t - __ldg(pre + b), L.e[0] - L.s[0] + 1, L.e[1] - L.s[1] + 1, i, j, k);
+  i += L.s[0];
+  j += L.s[1];
+  k += (L.ndim == 3 ? L.s[2] : 0);
+  const long long o8 = NV * m.off, o1 = m.off;
+  R* f3 = L.ndim == 3 ? F3 + o8 : nullptr;
+  R* ee1 = L.ndim == 3 ? e1 + o1 : nullptr;
+  R* ee2 = L.ndim == 3 ? e2 + o1 : nullptr;
+  if (phase == 0)
+    emf_at<R>(F1 + o8, F2 + o8, f3, ee1, ee2, e3 + o1, L, i, j, k);
+  else
+    apply_ct_at<R>(F1 + o8, F2 + o8, f3, ee1, ee2, e3 + o1, L, i, j, k);
+}
+
+__global__ void __launch_bounds__(256) km_update(const MBlock* blk, const unsigned* pre, int nb, const double* U0,
+                                                Arena<double> Pin, Arena<double> Pout, double* Uout,
+                                                const double* F1, const double* F2, const double* F3, GeoArena GA,
+                                                Scheme S, const double* dtp, double coef, int8_t* pflag,
+                                                unsigned long long* cnt) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= __ldg(pre + nb)) return;
+  const int b = find_block(pre, nb, t);
+  const MBlock& m = blk[b];
+  int i, j, k;
+  zone_ijk(m.L, t - __ldg(pre + b), i, j, k);
+  const long long o8 = NV * m.off;
+  update_zone(U0 + o8, cvars_at(Pin, m), vars_at(Pout, m), Uout ? Uout + o8 : nullptr, F1 + o8, F2 + o8,
+              m.L.ndim == 3 ? F3 + o8 : nullptr, m.L, geo64(GA, m), S, coef * __ldg(dtp), pflag + m.off, cnt, i, j,
+              k);
+}
+
+template <class TIN>
+__global__ void __launch_bounds__(256) km_update_mixed(const MBlock* blk, const unsigned* pre, int nb,
+                                                      const double* U0, Arena<TIN> Pin, Arena<double> Pout64,
+                                                      Arena<float> Pout32, double* Uout, const float* F1,
+                                                      const float* F2, const float* F3, GeoArena GA, Scheme S,
+                                                      const double* dtp, double coef, int8_t* pflag,
+                                                      unsigned long long* cnt) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= __ldg(pre + nb)) return;
+  const int b = find_block(pre, nb, t);
+  const MBlock& m = blk[b];
+  int i, j, k;
+  zone_ijk(m.L, t - __ldg(pre + b), i, j, k);
+  const long long o8 = NV * m.off;
+  Vars P64;
+  VarsT<float> P32;
+  if (Pout64.a) P64 = vars_at(Pout64, m); else for (int v = 0; v < NV; ++v) P64.v[v] = nullptr;
+  if (Pout32.a) P32 = vars_at(Pout32, m); else for (int v = 0; v < NV; ++v) P32.v[v] = nullptr;
+  update_mixed_zone<TIN>(U0 + o8, cvars_at(Pin, m), P64, P32, Uout ? Uout + o8 : nullptr, F1 + o8, F2 + o8,
+                         m.L.ndim == 3 ? F3 + o8 : nullptr, m.L, geo64(GA, m), geo32(GA, m), S, coef * __ldg(dtp),
+                         pflag + m.off, cnt, i, j, k);
+}
+
+template <class T>
+__global__ void km_fixup(const MBlock* blk, const unsigned* pre, int nb, Arena<T> P, double* Uout,
+                         const int8_t* pflag, GeoArena GA, Scheme S, unsigned long long* cnt) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= __ldg(pre + nb)) return;
+  const int b = find_block(pre, nb, t);
+  const MBlock& m = blk[b];
+  int i, j, k;
+  zone_ijk(m.L, t - __ldg(pre + b), i, j, k);
+  if (pflag[m.off + m.L.at(k, j, i)] == 0) return;
+  fixup_zone<T>(vars_at(P, m), Uout ? Uout + NV * m.off : nullptr, pflag + m.off, m.L, geo64(GA, m), S, cnt, i, j,
+                k);
+}
+
+__device__ __forceinline__ double wmax(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+  return x;
+}
+
+template <class T>
+__global__ void __launch_bounds__(RED_THREADS) km_cfl(const MBlock* blk, const unsigned* pre, int nb, const T* c1,
+                                                     const T* c2, const T* c3, double cfl, double* partial) {
+  double mx = 0.0;
+  const unsigned nz = __ldg(pre + nb);
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < nz; t += gridDim.x * blockDim.x) {
+    const int b = find_block(pre, nb, t);
+    const MBlock& m = blk[b];
+    int i, j, k;
+    zone_ijk(m.L, t - __ldg(pre + b), i, j, k);
+    mx = fmax(mx, cfl_inv_zone(c1 + m.off, c2 + m.off, m.L.ndim == 3 ? c3 + m.off : c3, m.L, i, j, k));
+  }
+  __shared__ double sm[RED_THREADS / 32];
+  mx = wmax(mx);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    mx = threadIdx.x < RED_THREADS / 32 ? sm[threadIdx.x] : 0.0;
+    mx = wmax(mx);
+    if (threadIdx.x == 0) partial[blockIdx.x] = mx;
+  }
+}
+
+__global__ void km_cfl_finish(const double* partial, int n, double cfl, double* out) {
+  __shared__ double sm[RED_THREADS / 32];
+  double mx = 0.0;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) mx = fmax(mx, partial[q]);
+  mx = wmax(mx);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    mx = threadIdx.x < RED_THREADS / 32 ? sm[threadIdx.x] : 0.0;
+    mx = wmax(mx);
+    if (threadIdx.x == 0) out[0] = cfl / mx;
+  }
+}
+
+// Mean of variable v over the 2x2(x2) cells of block m starting at cell c
+// (a restriction to the next coarser level), summed i fastest, then j, k.
+template <class T>
+__device__ __forceinline__ double restrict_at(const Arena<T>& P, const MBlock& m, int v, long long c) {
+  const Layout& L = m.L;
+  const T* q = vars_at(P, m).v[v];
+  const long long sj = L.n1s, sk = (long long)L.n1s * L.n2s;
+  const int nk = L.ndim == 3 ? 2 : 1;
+  double acc = 0.0;
+  for (int dk = 0; dk < nk; ++dk)
+    for (int dj = 0; dj < 2; ++dj)
+      for (int di = 0; di < 2; ++di) acc += (double)q[c + di + dj * sj + dk * sk];
+  return (L.ndim == 3 ? 0.125 : 0.25) * acc;
+}
+
+// The ghost-fill gather: one thread per ghost cell of any block.
+template <class T>
+__global__ void km_ghost(const MBlock* blk, const GhostOp* ops, long long nops, const ProlongNb* nbs, Arena<T> P) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= nops) return;
+  const GhostOp op = ops[t];
+  const MBlock& md = blk[op.dst_block];
+  const MBlock& ms = blk[op.src_block];
+  const VarsT<T> D = vars_at(P, md);
+  const VarsT<T> Sv = vars_at(P, ms);
+  const long long c = op.src_cell;
+  T val[NV];
+  if (op.mode == G_COPY) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) val[v] = Sv.v[v][c];
+  } else if (op.mode == G_RESTRICT) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) val[v] = (T)restrict_at(P, ms, v, c);
+  } else {  // prolongation from the coarse cell c with MC slopes over coarse-level neighbours
+    const ProlongNb& nb = nbs[op.nbi];
+    const int nd = ms.L.ndim;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const double q0 = (double)Sv.v[v][c];
+      double out = q0;
+      for (int d = 0; d < nd; ++d) {
+        if (op.off[d] == 0 || nb.mode[d][0] == NB_NONE || nb.mode[d][1] == NB_NONE) continue;
+        double q[2];
+        for (int side = 0; side < 2; ++side) {
+          const MBlock& mn = blk[nb.block[d][side]];
+          const long long cn = nb.cell[d][side];
+          q[side] = nb.mode[d][side] == G_COPY ? (double)vars_at(P, mn).v[v][cn] : restrict_at(P, mn, v, cn);
+        }
+        out += 0.25 * op.off[d] * mc_slope(q[0], q0, q[1]);
+      }
+      val[v] = (T)out;
+    }
+  }
+  if (op.flags & G_FLIP2) {
+    val[V_U2] = -val[V_U2];
+    val[V_B2] = -val[V_B2];
+  }
+  if ((op.flags & G_CLAMP_IN) && val[V_U1] > T(0)) val[V_U1] = T(0);
+  if ((op.flags & G_CLAMP_OUT) && val[V_U1] < T(0)) val[V_U1] = T(0);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) D.v[v][op.dst_cell] = val[v];
+}
+
+// FP64 -> FP32 copy of the 8 slots of every cell of every block.
+__global__ void km_to_f32(const MBlock* blk, const unsigned* pre, int nb, Arena<double> src, Arena<float> dst) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= __ldg(pre + nb)) return;
+  const int b = find_block(pre, nb, t);
+  const MBlock& m = blk[b];
+  const long long c = t - __ldg(pre + b);
+  const CVars S = cvars_at(src, m);
+  const VarsT<float> D = vars_at(dst, m);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) D.v[v][c] = (float)S.v[v][c];
+}
+
+__global__ void km_p2c(const MBlock* blk, const unsigned* pre, int nb, Arena<double> P, double* U, GeoArena GA,
+                       Scheme S) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= __ldg(pre + nb)) return;
+  const int b = find_block(pre, nb, t);
+  const MBlock& m = blk[b];
+  const Layout& L = m.L;
+  int i, j, k;
+  split3(t - __ldg(pre + b), L.N1, L.N2, i, j, k);
+  const long long c = L.at(k, j, i);
+  const CVars Pv = cvars_at(P, m);
+  double p[NV], u[NV];
+  for (int v = 0; v < NV; ++v) p[v] = Pv.v[v][c];
+  const DevGeom G = geo64(GA, m);
+  const Met<double> met = load_met(G, L.gplane, LOC_CENT, (long long)j * L.n1s + i);
+  FState<double> s;
+  fluid_state(p, met, s);
+  cons_only(p, s, met, S.gam, u);
+  for (int v = 0; v < NV; ++v) U[NV * m.off + v * L.plane + c] = u[v];
+}
+
+inline int nblk(long long n, int tpb) { return (int)((n + tpb - 1) / tpb); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// The mesh context
+// ---------------------------------------------------------------------------
+struct kh_mesh {
+  kh_coords c;
+  Scheme S;
+  CoordParams cp;
+  int nb, ndim, lmax;
+  int N0[3];  // level-0 grid
+  std::vector<MBlock> hb;
+  std::vector<unsigned> pre_face[3], pre_zone, pre_ct, pre_alloc, pre_all;
+  long long cells;     // sum of allocation planes
+  long long gcells;    // sum of (j, i) planes
+  long long zones;     // interior zones
+  cudaStream_t stream;
+  MBlock* dblk;
+  unsigned* dpre[7];   // face1..3, zone, ct, alloc cells (km_to_f32), all-cells (p2c)
+  GhostOp* dops;
+  long long nops;
+  ProlongNb* dnbs;
+  long long nnbs;
+  double *geo, *conn, *flo;
+  float *geof, *connf;
+  double* pstar;
+  float *pstarf, *pnf;
+  double* F[3];
+  double* ctop[3];
+  double* emf[3];
+  float* Ff[3];
+  float* ctopf[3];
+  float* emff[3];
+  int8_t* pflag;
+  double* partial;
+  int npartial;
+  double* dscalar;  // [0] dt out, [3] dt in
+  unsigned long long* counters;
+  long long launches;
+  int graph_on;
+  cudaStream_t cap_stream;
+  cudaGraphExec_t gexec;
+  const void* gkey[3];
+  int graph_launches;
+};
+
+namespace {
+
+int cuda_rc(cudaError_t e) { return e == cudaSuccess ? KH_OK : (e == cudaErrorMemoryAllocation ? KH_ENOMEM : KH_ECUDA); }
+
+// Doubled finest-level index coordinates of cell centres (exact integers):
+// the centre of level-l cell g along a direction refined by ratio r is
+// (2 g + 1) * r^(lmax - l).
+struct Locator {
+  int lmax, ndim;
+  long long nf[3];  // finest-level cells per direction
+  std::vector<int> owner;
+  long long ratio_pow(int d, int l) const {
+    long long r = 1;
+    const int rr = (d == 2 && ndim == 2) ? 1 : 2;
+    for (int q = 0; q < lmax - l; ++q) r *= rr;
+    return r;
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+int kh_mesh_destroy(kh_mesh* x);
+
+int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const kh_block* blocks, kh_mesh** out) {
+  if (!c || !blocks || !out || nblocks < 1) return KH_EINVAL;
+  if (c->kind < KH_MINKOWSKI || c->kind > KH_FMKS || c->n1 < 2 || c->n2 < 2 || c->n3 < 1) return KH_EINVAL;
+  if (c->precision != KH_FP64 && c->precision != KH_MIXED) return KH_EINVAL;
+  if (c->recon != KH_RECON_MC && c->recon != KH_RECON_WENO5) return KH_EINVAL;
+  if (!(gamma > 1.0) || !(c->cfl > 0.0) || !(fabs(a) < 1.0)) return KH_EINVAL;
+  for (int q = 0; q < 6; ++q) {
+    const int b = c->bc[q];
+    if (b != KH_BC_PERIODIC && b != KH_BC_OUTFLOW && b != KH_BC_POLAR) return KH_EINVAL;
+    if (b == KH_BC_POLAR && (q < 2 || q >= 4)) return KH_EINVAL;
+  }
+  kh_mesh* x = new kh_mesh();
+  x->c = *c;
+  x->nb = nblocks;
+  x->ndim = c->n3 > 1 ? 3 : 2;
+  x->N0[0] = c->n1;
+  x->N0[1] = c->n2;
+  x->N0[2] = c->n3;
+  x->stream = 0;
+  Scheme& S = x->S;
+  S.gam = gamma;
+  S.cfl = c->cfl;
+  S.recon = c->recon;
+  for (int q = 0; q < 6; ++q) S.bc[q] = c->bc[q];
+  S.fl = FloorParams{c->rho_min, c->u_min, c->bsq_rho_max, c->bsq_u_max, c->u_rho_max, c->gamma_max};
+  S.c2p.max_iter = c->newton_max_iter > 0 ? c->newton_max_iter : 30;
+  S.c2p.tol = c->newton_tol > 0.0 ? c->newton_tol : 1e-14;
+  x->cp = CoordParams{c->kind, a, c->x1min, c->hslope, c->poly_xt, c->poly_alpha, c->mks_smooth};
+
+  // ---- validate the blocks and rasterise ownership at the finest level ----
+  int lmax = 0;
+  for (int b = 0; b < nblocks; ++b) lmax = std::max(lmax, blocks[b].level);
+  if (lmax > 4) { delete x; return KH_EINVAL; }
+  x->lmax = lmax;
+  Locator loc;
+  loc.lmax = lmax;
+  loc.ndim = x->ndim;
+  for (int d = 0; d < 3; ++d) loc.nf[d] = (long long)x->N0[d] * loc.ratio_pow(d, 0);
+  const long long nfin = loc.nf[0] * loc.nf[1] * loc.nf[2];
+  if (nfin > (1LL << 31)) { delete x; return KH_EINVAL; }
+  loc.owner.assign((size_t)nfin, -1);
+  const double dx0[3] = {(c->x1max - c->x1min) / c->n1, (c->x2max - c->x2min) / c->n2,
+                         (c->x3max - c->x3min) / c->n3};
+  long long cells = 0, gcells = 0, zones = 0;
+  x->hb.resize(nblocks);
+  for (int b = 0; b < nblocks; ++b) {
+    const kh_block& B = blocks[b];
+    const int n[3] = {B.n1, B.n2, B.n3};
+    const int o[3] = {B.i0, B.j0, B.k0};
+    if (B.level < 0 || B.n1 < 4 || B.n2 < 4 || B.n3 < 1) { delete x; return KH_EINVAL; }
+    if (x->ndim == 2 && (B.n3 != 1 || B.k0 != 0)) { delete x; return KH_EINVAL; }
+    if (x->ndim == 3 && B.n3 < 4) { delete x; return KH_EINVAL; }
+    for (int d = 0; d < 3; ++d) {
+      const long long rl = loc.ratio_pow(d, 0) / loc.ratio_pow(d, B.level);  // level-l cells per level-0 cell
+      const long long nl = (long long)x->N0[d] * rl;
+      if (o[d] < 0 || o[d] + n[d] > nl) { delete x; return KH_EINVAL; }
+      const bool refined_dir = !(d == 2 && x->ndim == 2);
+      if (B.level > 0 && refined_dir && ((o[d] & 1) || (n[d] & 1))) { delete x; return KH_EINVAL; }
+    }
+    MBlock& m = x->hb[b];
+    m.level = B.level;
+    m.i0 = B.i0;
+    m.j0 = B.j0;
+    m.k0 = B.k0;
+    Layout& L = m.L;
+    L.n1 = B.n1; L.n2 = B.n2; L.n3 = B.n3;
+    L.ng = NGHOST;
+    L.ndim = x->ndim;
+    L.ng3 = L.ndim == 3 ? NGHOST : 0;
+    L.N1 = L.n1 + 2 * L.ng;
+    L.N2 = L.n2 + 2 * L.ng;
+    L.N3 = L.n3 + 2 * L.ng3;
+    L.n1s = (L.N1 + 15) / 16 * 16;
+    L.n2s = L.N2;
+    L.n3s = L.N3;
+    L.gplane = (long long)L.n1s * L.n2s;
+    L.plane = L.gplane * L.n3s;
+    for (int d = 0; d < 3; ++d) {
+      const double rr = (double)(loc.ratio_pow(d, 0) / loc.ratio_pow(d, B.level));
+      L.dx[d] = dx0[d] / rr;
+      L.idx[d] = 1.0 / L.dx[d];
+    }
+    L.s[0] = L.ng; L.e[0] = L.ng + L.n1;
+    L.s[1] = L.ng; L.e[1] = L.ng + L.n2;
+    L.s[2] = L.ng3; L.e[2] = L.ng3 + L.n3;
+    for (int d = 1; d <= 3; ++d) m.fb[d - 1] = face_box(L, d);
+    const long long nl2 = (long long)x->N0[1] * (loc.ratio_pow(1, 0) / loc.ratio_pow(1, B.level));
+    m.polar_lo = c->bc[2] == KH_BC_POLAR && B.j0 == 0;
+    m.polar_hi = c->bc[3] == KH_BC_POLAR && B.j0 + B.n2 == nl2;
+    m.off = cells;
+    m.goff = gcells;
+    cells += L.plane;
+    gcells += L.gplane;
+    zones += (long long)L.n1 * L.n2 * L.n3;
+    // ownership raster
+    long long sc[3];
+    for (int d = 0; d < 3; ++d) sc[d] = loc.ratio_pow(d, B.level);
+    for (long long kf = o[2] * sc[2]; kf < (o[2] + n[2]) * sc[2]; ++kf)
+      for (long long jf = o[1] * sc[1]; jf < (o[1] + n[1]) * sc[1]; ++jf)
+        for (long long ifn = o[0] * sc[0]; ifn < (o[0] + n[0]) * sc[0]; ++ifn) {
+          int& w = loc.owner[(size_t)((kf * loc.nf[1] + jf) * loc.nf[0] + ifn)];
+          if (w != -1) { delete x; return KH_EINVAL; }  // overlap
+          w = b;
+        }
+  }
+  for (long long q = 0; q < nfin; ++q)
+    if (loc.owner[(size_t)q] < 0) { delete x; return KH_EINVAL; }  // hole
+  if (cells >= (1LL << 31)) { delete x; return KH_EINVAL; }
+  x->cells = cells;
+  x->gcells = gcells;
+  x->zones = zones;
+
+  // ---- ghost map ----
+  std::vector<GhostOp> ops;
+  std::vector<ProlongNb> nbs;
+  const long long two_nf[3] = {2 * loc.nf[0], 2 * loc.nf[1], 2 * loc.nf[2]};
+  for (int b = 0; b < nblocks && true; ++b) {
+    const MBlock& m = x->hb[b];
+    const Layout& L = m.L;
+    const long long rp[3] = {loc.ratio_pow(0, m.level), loc.ratio_pow(1, m.level), loc.ratio_pow(2, m.level)};
+    for (int k = 0; k < L.N3; ++k)
+      for (int j = 0; j < L.N2; ++j)
+        for (int i = 0; i < L.N1; ++i) {
+          const bool inside = i >= L.s[0] && i < L.e[0] && j >= L.s[1] && j < L.e[1] && k >= L.s[2] && k < L.e[2];
+          if (inside) continue;
+          const int gi[3] = {m.i0 + i - L.ng, m.j0 + j - L.ng, m.k0 + k - L.ng3};
+          long long X[3];
+          for (int d = 0; d < 3; ++d) X[d] = (2LL * gi[d] + 1) * rp[d];
+          unsigned char flags = 0;
+          // x1: outflow clamps to the first/last interior cell at this level; periodic wraps
+          if (X[0] < 0) {
+            if (c->bc[0] == KH_BC_PERIODIC) X[0] += two_nf[0];
+            else { X[0] = rp[0]; flags |= G_CLAMP_IN; }
+          } else if (X[0] > two_nf[0]) {
+            if (c->bc[1] == KH_BC_PERIODIC) X[0] -= two_nf[0];
+            else { X[0] = two_nf[0] - rp[0]; flags |= G_CLAMP_OUT; }
+          }
+          // x2: polar reflection, periodic wrap or outflow clamp
+          if (X[1] < 0) {
+            if (c->bc[2] == KH_BC_POLAR) { X[1] = -X[1]; flags ^= G_FLIP2; }
+            else if (c->bc[2] == KH_BC_PERIODIC) X[1] += two_nf[1];
+            else X[1] = rp[1];
+          } else if (X[1] > two_nf[1]) {
+            if (c->bc[3] == KH_BC_POLAR) { X[1] = 2 * two_nf[1] - X[1]; flags ^= G_FLIP2; }
+            else if (c->bc[3] == KH_BC_PERIODIC) X[1] -= two_nf[1];
+            else X[1] = two_nf[1] - rp[1];
+          }
+          if (x->ndim == 3) {
+            if (X[2] < 0) {
+              if (c->bc[4] == KH_BC_PERIODIC) X[2] += two_nf[2]; else X[2] = rp[2];
+            } else if (X[2] > two_nf[2]) {
+              if (c->bc[5] == KH_BC_PERIODIC) X[2] -= two_nf[2]; else X[2] = two_nf[2] - rp[2];
+            }
+          } else {
+            X[2] = 1;
+          }
+          const long long fi[3] = {X[0] / 2, X[1] / 2, X[2] / 2};
+          const int s = loc.owner[(size_t)((fi[2] * loc.nf[1] + fi[1]) * loc.nf[0] + fi[0])];
+          const MBlock& ms = x->hb[s];
+          const Layout& Ls = ms.L;
+          const int dl = ms.level - m.level;
+          GhostOp op;
+          op.dst_block = b;
+          op.dst_cell = (int)L.at(k, j, i);
+          op.src_block = s;
+          op.flags = flags;
+          op.pad = 0;
+          op.off[0] = op.off[1] = op.off[2] = 0;
+          const long long rs[3] = {loc.ratio_pow(0, ms.level), loc.ratio_pow(1, ms.level),
+                                   loc.ratio_pow(2, ms.level)};
+          const int so[3] = {ms.i0, ms.j0, ms.k0};
+          const int sg[3] = {Ls.ng, Ls.ng, Ls.ng3};
+          int li[3];
+          op.nbi = -1;
+          if (dl == 0 || dl == -1) {
+            // the owner's cell containing the point
+            for (int d = 0; d < 3; ++d) li[d] = (int)(X[d] / (2 * rs[d])) - so[d] + sg[d];
+            op.mode = dl == 0 ? G_COPY : G_PROLONG;
+            if (dl == -1) {
+              long long gc[3];
+              for (int d = 0; d < 3; ++d) {
+                gc[d] = X[d] / (2 * rs[d]);  // the coarse cell's index at its own level
+                const long long cc = (2LL * gc[d] + 1) * rs[d];
+                op.off[d] = (signed char)(X[d] > cc ? 1 : (X[d] < cc ? -1 : 0));
+              }
+              ProlongNb nb{};
+              for (int d = 0; d < 3; ++d)
+                for (int side = 0; side < 2; ++side) {
+                  nb.mode[d][side] = NB_NONE;
+                  nb.block[d][side] = 0;
+                  nb.cell[d][side] = 0;
+                  if (d >= x->ndim) continue;
+                  long long nc[3] = {gc[0], gc[1], gc[2]};
+                  nc[d] += side ? 1 : -1;
+                  const long long ncl = loc.nf[d] / rs[d];  // coarse-level cells across the domain
+                  if (nc[d] < 0 || nc[d] >= ncl) {
+                    if (c->bc[2 * d + (nc[d] < 0 ? 0 : 1)] != KH_BC_PERIODIC) continue;
+                    nc[d] = (nc[d] + ncl) % ncl;
+                  }
+                  long long Y[3];
+                  for (int q = 0; q < 3; ++q) Y[q] = x->ndim == 2 && q == 2 ? 1 : (2 * nc[q] + 1) * rs[q];
+                  const int w = loc.owner[(size_t)(((Y[2] / 2) * loc.nf[1] + Y[1] / 2) * loc.nf[0] + Y[0] / 2)];
+                  const MBlock& mw = x->hb[w];
+                  const int wo[3] = {mw.i0, mw.j0, mw.k0};
+                  const int wg[3] = {mw.L.ng, mw.L.ng, mw.L.ng3};
+                  int lw[3];
+                  if (mw.level == ms.level) {
+                    for (int q = 0; q < 3; ++q) lw[q] = (int)(nc[q] - wo[q] + wg[q]);
+                    nb.mode[d][side] = G_COPY;
+                  } else if (mw.level == ms.level + 1) {
+                    for (int q = 0; q < 3; ++q) {
+                      const bool refined_dir = !(q == 2 && x->ndim == 2);
+                      lw[q] = (int)((refined_dir ? 2 * nc[q] : nc[q]) - wo[q] + wg[q]);
+                    }
+                    nb.mode[d][side] = G_RESTRICT;
+                  } else {
+                    continue;  // inside a coarser block: no slope in this direction
+                  }
+                  nb.block[d][side] = w;
+                  nb.cell[d][side] = (int)mw.L.at(lw[2], lw[1], lw[0]);
+                }
+              op.nbi = (int)nbs.size();
+              nbs.push_back(nb);
+            }
+          } else if (dl == 1) {
+            // the owner's 2x2(x2) fine cells covering this coarse cell
+            for (int d = 0; d < 3; ++d) {
+              const bool refined_dir = !(d == 2 && x->ndim == 2);
+              const long long gcell = X[d] / (2 * rp[d]);  // this level's cell index
+              li[d] = (int)((refined_dir ? 2 * gcell : gcell) - so[d] + sg[d]);
+            }
+            op.mode = G_RESTRICT;
+          } else {
+            kh_mesh_destroy(x);
+            return KH_EINVAL;  // neighbours more than one level apart
+          }
+          op.src_cell = (int)Ls.at(li[2], li[1], li[0]);
+          ops.push_back(op);
+        }
+  }
+  x->nops = (long long)ops.size();
+  x->nnbs = (long long)nbs.size();
+
+  // ---- prefix sums per kernel ----
+  for (int d = 0; d < 3; ++d) x->pre_face[d].assign(1, 0u);
+  x->pre_zone.assign(1, 0u);
+  x->pre_ct.assign(1, 0u);
+  x->pre_alloc.assign(1, 0u);
+  x->pre_all.assign(1, 0u);
+  for (int b = 0; b < nblocks; ++b) {
+    const MBlock& m = x->hb[b];
+    const Layout& L = m.L;
+    for (int d = 0; d < 3; ++d) {
+      const FaceBox& f = m.fb[d];
+      x->pre_face[d].push_back(x->pre_face[d].back() + (unsigned)(f.n[0] * f.n[1] * f.n[2]));
+    }
+    x->pre_zone.push_back(x->pre_zone.back() + (unsigned)(L.n1 * L.n2 * L.n3));
+    x->pre_ct.push_back(x->pre_ct.back() +
+                        (unsigned)((L.e[0] - L.s[0] + 1) * (L.e[1] - L.s[1] + 1) * (L.ndim == 3 ? L.e[2] - L.s[2] + 1 : 1)));
+    x->pre_alloc.push_back(x->pre_alloc.back() + (unsigned)L.plane);
+    x->pre_all.push_back(x->pre_all.back() + (unsigned)(L.N1 * L.N2 * L.N3));
+  }
+
+  // ---- device buffers ----
+  int rc = KH_OK;
+#define KM_ALLOC(ptr, bytes) \
+  if (rc == KH_OK) rc = cuda_rc(cudaMalloc((void**)&(ptr), (bytes)));
+  const bool mixed = c->precision == KH_MIXED;
+  const size_t pl = (size_t)cells * sizeof(double), plf = (size_t)cells * sizeof(float);
+  const size_t gp = (size_t)gcells * sizeof(double), gpf = (size_t)gcells * sizeof(float);
+  KM_ALLOC(x->dblk, sizeof(MBlock) * nblocks);
+  for (int q = 0; q < 7; ++q) KM_ALLOC(x->dpre[q], sizeof(unsigned) * (nblocks + 1));
+  KM_ALLOC(x->dops, sizeof(GhostOp) * std::max<long long>(x->nops, 1));
+  KM_ALLOC(x->dnbs, sizeof(ProlongNb) * std::max<long long>(x->nnbs, 1));
+  KM_ALLOC(x->geo, 3 * NGEO * gp);
+  KM_ALLOC(x->conn, NCONN * gp);
+  KM_ALLOC(x->flo, 2 * gp);
+  KM_ALLOC(x->pstar, NV * pl);
+  KM_ALLOC(x->pflag, (size_t)cells);
+  if (!mixed) {
+    for (int d = 0; d < x->ndim; ++d) {
+      KM_ALLOC(x->F[d], NV * pl);
+      KM_ALLOC(x->ctop[d], pl);
+    }
+    KM_ALLOC(x->emf[2], pl);
+    if (x->ndim == 3) {
+      KM_ALLOC(x->emf[0], pl);
+      KM_ALLOC(x->emf[1], pl);
+    }
+  } else {
+    KM_ALLOC(x->geof, 3 * NGEO * gpf);
+    KM_ALLOC(x->connf, NCONN * gpf);
+    KM_ALLOC(x->pstarf, NV * plf);
+    KM_ALLOC(x->pnf, NV * plf);
+    for (int d = 0; d < x->ndim; ++d) {
+      KM_ALLOC(x->Ff[d], NV * plf);
+      KM_ALLOC(x->ctopf[d], plf);
+    }
+    KM_ALLOC(x->emff[2], plf);
+    if (x->ndim == 3) {
+      KM_ALLOC(x->emff[0], plf);
+      KM_ALLOC(x->emff[1], plf);
+    }
+  }
+  x->npartial = 152 * 4;
+  KM_ALLOC(x->partial, sizeof(double) * x->npartial);
+  KM_ALLOC(x->dscalar, 4 * sizeof(double));
+  KM_ALLOC(x->counters, NCNT * sizeof(unsigned long long));
+#undef KM_ALLOC
+  if (rc == KH_OK) rc = cuda_rc(cudaMemcpy(x->dblk, x->hb.data(), sizeof(MBlock) * nblocks, cudaMemcpyHostToDevice));
+  const std::vector<unsigned>* pres[7] = {&x->pre_face[0], &x->pre_face[1], &x->pre_face[2], &x->pre_zone,
+                                          &x->pre_ct, &x->pre_alloc, &x->pre_all};
+  for (int q = 0; q < 7 && rc == KH_OK; ++q)
+    rc = cuda_rc(cudaMemcpy(x->dpre[q], pres[q]->data(), sizeof(unsigned) * (nblocks + 1), cudaMemcpyHostToDevice));
+  if (rc == KH_OK && x->nops)
+    rc = cuda_rc(cudaMemcpy(x->dops, ops.data(), sizeof(GhostOp) * x->nops, cudaMemcpyHostToDevice));
+  if (rc == KH_OK && x->nnbs)
+    rc = cuda_rc(cudaMemcpy(x->dnbs, nbs.data(), sizeof(ProlongNb) * x->nnbs, cudaMemcpyHostToDevice));
+  // zero scratch so never-written entries stay finite
+  for (int d = 0; d < 3 && rc == KH_OK; ++d) {
+    if (x->F[d]) rc = cuda_rc(cudaMemset(x->F[d], 0, NV * pl));
+    if (rc == KH_OK && x->ctop[d]) rc = cuda_rc(cudaMemset(x->ctop[d], 0, pl));
+    if (rc == KH_OK && x->emf[d]) rc = cuda_rc(cudaMemset(x->emf[d], 0, pl));
+    if (rc == KH_OK && x->Ff[d]) rc = cuda_rc(cudaMemset(x->Ff[d], 0, NV * plf));
+    if (rc == KH_OK && x->ctopf[d]) rc = cuda_rc(cudaMemset(x->ctopf[d], 0, plf));
+    if (rc == KH_OK && x->emff[d]) rc = cuda_rc(cudaMemset(x->emff[d], 0, plf));
+  }
+  if (rc == KH_OK) rc = cuda_rc(cudaMemset(x->pstar, 0, NV * pl));
+  if (rc == KH_OK && x->pstarf) rc = cuda_rc(cudaMemset(x->pstarf, 0, NV * plf));
+  if (rc == KH_OK && x->pnf) rc = cuda_rc(cudaMemset(x->pnf, 0, NV * plf));
+  // geometry of every block
+  for (int b = 0; b < nblocks && rc == KH_OK; ++b) {
+    const MBlock& m = x->hb[b];
+    const double x1o = c->x1min + m.i0 * m.L.dx[0];
+    const double x2o = c->x2min + m.j0 * m.L.dx[1];
+    x->launches += launch_geometry(x->cp, x1o, x2o, S.fl, m.L, x->geo + 3LL * NGEO * m.goff,
+                                   x->conn + (long long)NCONN * m.goff, x->flo + 2 * m.goff, 0);
+    rc = cuda_rc(cudaGetLastError());
+  }
+  if (rc == KH_OK && mixed) {
+    x->launches += launch_to_f32(x->geo, x->geof, 3LL * NGEO * gcells, 0);
+    x->launches += launch_to_f32(x->conn, x->connf, (long long)NCONN * gcells, 0);
+    rc = cuda_rc(cudaGetLastError());
+  }
+  if (rc == KH_OK) rc = cuda_rc(cudaDeviceSynchronize());
+  if (rc != KH_OK) {
+    kh_mesh_destroy(x);
+    return rc;
+  }
+  *out = x;
+  return KH_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+GeoArena garena(const kh_mesh* x) { return GeoArena{x->geo, x->conn, x->flo, x->geof, x->connf}; }
+
+template <class T> Arena<T> arena8(T* p) { return Arena<T>{p, nullptr, NV}; }
+Arena<double> arena_pb(double* P, double* B) { return Arena<double>{P, B, 5}; }
+
+template <class T> int fill_ghosts(kh_mesh* x, const Arena<T>& P) {
+  if (!x->nops) return 0;
+  km_ghost<T><<<nblk(x->nops, MTPB), MTPB, 0, x->stream>>>(x->dblk, x->dops, x->nops, x->dnbs, P);
+  return 1;
+}
+
+template <class TIN, class R>
+int flux_pass(kh_mesh* x, const Arena<TIN>& P, R* const F[3], R* const ct[3], R* const emf[3]) {
+  int n = 0;
+  const GeoArena GA = garena(x);
+  for (int d = 1; d <= x->ndim; ++d) {
+    const unsigned tot = x->pre_face[d - 1].back();
+    const int g = nblk(tot, MTPB);
+#define KM_FLUX(DD)                                                                                              \
+  if (x->S.recon == KH_RECON_MC)                                                                                 \
+    km_flux<DD, KH_RECON_MC, TIN, R><<<g, MTPB, 0, x->stream>>>(x->dblk, x->dpre[DD - 1], x->nb, P, GA, x->S,    \
+                                                                F[DD - 1], ct[DD - 1]);                          \
+  else                                                                                                           \
+    km_flux<DD, KH_RECON_WENO5, TIN, R><<<g, MTPB, 0, x->stream>>>(x->dblk, x->dpre[DD - 1], x->nb, P, GA, x->S, \
+                                                                   F[DD - 1], ct[DD - 1]);
+    if (d == 1) { KM_FLUX(1) } else if (d == 2) { KM_FLUX(2) } else { KM_FLUX(3) }
+#undef KM_FLUX
+    ++n;
+  }
+  const unsigned tot = x->pre_ct.back();
+  for (int phase = 0; phase < 2; ++phase) {
+    km_ct<R><<<nblk(tot, MTPB), MTPB, 0, x->stream>>>(x->dblk, x->dpre[4], x->nb, F[0], F[1], F[2], emf[0], emf[1],
+                                                      emf[2], phase);
+    ++n;
+  }
+  return n;
+}
+
+template <class T> int cfl_pass(kh_mesh* x, T* const ct[3]) {
+  km_cfl<T><<<x->npartial, RED_THREADS, 0, x->stream>>>(x->dblk, x->dpre[3], x->nb, ct[0], ct[1], ct[2], x->S.cfl,
+                                                        x->partial);
+  km_cfl_finish<<<1, RED_THREADS, 0, x->stream>>>(x->partial, x->npartial, x->S.cfl, x->dscalar);
+  return 2;
+}
+
+int issue_mesh_step(kh_mesh* x, double* U, double* P, double* B) {
+  cudaStream_t s = x->stream;
+  if (cudaMemsetAsync(x->counters, 0, NCNT * sizeof(unsigned long long), s) != cudaSuccess) return -1;
+  const GeoArena GA = garena(x);
+  const unsigned nz = x->pre_zone.back();
+  const int gz = nblk(nz, MTPB);
+  const Arena<double> Pn = arena_pb(P, B);
+  int n = 0;
+  if (x->c.precision == KH_FP64) {
+    const Arena<double> Ps = arena8(x->pstar);
+    // stage 1: P^n -> P*
+    n += fill_ghosts(x, Pn);
+    n += flux_pass<double, double>(x, Pn, x->F, x->ctop, x->emf);
+    km_update<<<gz, MTPB, 0, s>>>(x->dblk, x->dpre[3], x->nb, U, Pn, Ps, nullptr, x->F[0], x->F[1], x->F[2], GA,
+                                  x->S, x->dscalar + 3, 0.5, x->pflag, x->counters);
+    km_fixup<double><<<gz, MTPB, 0, s>>>(x->dblk, x->dpre[3], x->nb, Ps, nullptr, x->pflag, GA, x->S, x->counters);
+    n += 2;
+    // stage 2: P* -> P^{n+1}, U^{n+1}
+    n += fill_ghosts(x, Ps);
+    n += flux_pass<double, double>(x, Ps, x->F, x->ctop, x->emf);
+    km_update<<<gz, MTPB, 0, s>>>(x->dblk, x->dpre[3], x->nb, U, Ps, Pn, U, x->F[0], x->F[1], x->F[2], GA, x->S,
+                                  x->dscalar + 3, 1.0, x->pflag, x->counters);
+    km_fixup<double><<<gz, MTPB, 0, s>>>(x->dblk, x->dpre[3], x->nb, Pn, U, x->pflag, GA, x->S, x->counters);
+    n += 2;
+    n += cfl_pass<double>(x, x->ctop);
+  } else {
+    const Arena<float> Psf = arena8(x->pstarf), Pnf = arena8(x->pnf);
+    const Arena<double> none64{nullptr, nullptr, NV};
+    const Arena<float> none32{nullptr, nullptr, NV};
+    // stage 1: FP64 P^n (ghost-filled in FP64, converted once) -> FP32 P*
+    n += fill_ghosts(x, Pn);
+    km_to_f32<<<nblk(x->pre_alloc.back(), 256), 256, 0, s>>>(x->dblk, x->dpre[5], x->nb, Pn, Pnf);
+    ++n;
+    n += flux_pass<float, float>(x, Pnf, x->Ff, x->ctopf, x->emff);
+    km_update_mixed<double><<<gz, MTPB, 0, s>>>(x->dblk, x->dpre[3], x->nb, U, Pn, none64, Psf, nullptr, x->Ff[0],
+                                                x->Ff[1], x->Ff[2], GA, x->S, x->dscalar + 3, 0.5, x->pflag,
+                                                x->counters);
+    km_fixup<float><<<gz, MTPB, 0, s>>>(x->dblk, x->dpre[3], x->nb, Psf, nullptr, x->pflag, GA, x->S, x->counters);
+    n += 2;
+    // stage 2: FP32 P* -> FP64 P^{n+1}, U^{n+1}
+    n += fill_ghosts(x, Psf);
+    n += flux_pass<float, float>(x, Psf, x->Ff, x->ctopf, x->emff);
+    km_update_mixed<float><<<gz, MTPB, 0, s>>>(x->dblk, x->dpre[3], x->nb, U, Psf, Pn, none32, U, x->Ff[0], x->Ff[1],
+                                               x->Ff[2], GA, x->S, x->dscalar + 3, 1.0, x->pflag, x->counters);
+    km_fixup<double><<<gz, MTPB, 0, s>>>(x->dblk, x->dpre[3], x->nb, Pn, U, x->pflag, GA, x->S, x->counters);
+    n += 2;
+    n += cfl_pass<float>(x, x->ctopf);
+  }
+  return n;
+}
+
+void drop_mesh_graph(kh_mesh* x) {
+  if (x->gexec) cudaGraphExecDestroy(x->gexec);
+  x->gexec = nullptr;
+  x->gkey[0] = x->gkey[1] = x->gkey[2] = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+int kh_mesh_block_shape(const kh_mesh* x, int b, int* n1s, int* n2s, int* n3s, int64_t* cell_offset) {
+  if (!x || b < 0 || b >= x->nb) return KH_EINVAL;
+  const Layout& L = x->hb[b].L;
+  if (n1s) *n1s = L.n1s;
+  if (n2s) *n2s = L.n2s;
+  if (n3s) *n3s = L.n3s;
+  if (cell_offset) *cell_offset = x->hb[b].off;
+  return KH_OK;
+}
+
+int64_t kh_mesh_cells(const kh_mesh* x) { return x ? (int64_t)x->cells : 0; }
+int64_t kh_mesh_zones(const kh_mesh* x) { return x ? (int64_t)x->zones : 0; }
+int64_t kh_mesh_ghost_cells(const kh_mesh* x) { return x ? (int64_t)x->nops : 0; }
+int64_t kh_mesh_launch_count(const kh_mesh* x) { return x ? (int64_t)x->launches : 0; }
+
+int kh_mesh_set_stream(kh_mesh* x, void* s) {
+  if (!x) return KH_EINVAL;
+  x->stream = (cudaStream_t)s;
+  drop_mesh_graph(x);
+  return KH_OK;
+}
+
+int kh_mesh_prim_to_cons(kh_mesh* x, const double* P, const double* B, double* U) {
+  if (!x || !P || !B || !U) return KH_EINVAL;
+  const unsigned tot = x->pre_all.back();
+  km_p2c<<<nblk(tot, MTPB), MTPB, 0, x->stream>>>(x->dblk, x->dpre[6], x->nb,
+                                                  arena_pb(const_cast<double*>(P), const_cast<double*>(B)), U,
+                                                  garena(x), x->S);
+  x->launches += 1;
+  return cuda_rc(cudaGetLastError());
+}
+
+int kh_mesh_fill_ghosts(kh_mesh* x, double* P, double* B) {
+  if (!x || !P || !B) return KH_EINVAL;
+  x->launches += fill_ghosts(x, arena_pb(P, B));
+  return cuda_rc(cudaGetLastError());
+}
+
+int kh_mesh_cfl_dt(kh_mesh* x, const double* P, const double* B, double* dt_cfl) {
+  if (!x || !P || !B || !dt_cfl) return KH_EINVAL;
+  cudaStream_t s = x->stream;
+  // ghost-fill a scratch copy (block by block: P is a [block][5][plane], B a [block][3][plane] arena)
+  for (int b = 0; b < x->nb; ++b) {
+    const MBlock& m = x->hb[b];
+    const size_t pl = (size_t)m.L.plane * sizeof(double);
+    int rc = cuda_rc(cudaMemcpyAsync(x->pstar + NV * m.off, P + 5 * m.off, 5 * pl, cudaMemcpyDeviceToDevice, s));
+    if (rc == KH_OK)
+      rc = cuda_rc(cudaMemcpyAsync(x->pstar + NV * m.off + 5 * m.L.plane, B + 3 * m.off, 3 * pl,
+                                   cudaMemcpyDeviceToDevice, s));
+    if (rc != KH_OK) return rc;
+  }
+  const Arena<double> Ps = arena8(x->pstar);
+  int n = fill_ghosts(x, Ps);
+  if (x->c.precision == KH_FP64) {
+    n += flux_pass<double, double>(x, Ps, x->F, x->ctop, x->emf);
+    n += cfl_pass<double>(x, x->ctop);
+  } else {
+    km_to_f32<<<nblk(x->pre_alloc.back(), 256), 256, 0, s>>>(x->dblk, x->dpre[5], x->nb, Ps, arena8(x->pnf));
+    n += 1;
+    n += flux_pass<float, float>(x, arena8(x->pnf), x->Ff, x->ctopf, x->emff);
+    n += cfl_pass<float>(x, x->ctopf);
+  }
+  x->launches += n;
+  int rc = cuda_rc(cudaGetLastError());
+  if (rc != KH_OK) return rc;
+  rc = cuda_rc(cudaMemcpyAsync(dt_cfl, x->dscalar, sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (rc == KH_OK) rc = cuda_rc(cudaStreamSynchronize(s));
+  if (rc != KH_OK) return rc;
+  return isfinite(*dt_cfl) ? KH_OK : KH_ENAN;
+}
+
+int kh_mesh_get_stats(kh_mesh* x, kh_stats* out) {
+  if (!x || !out) return KH_EINVAL;
+  unsigned long long h[NCNT];
+  double dt;
+  int rc = cuda_rc(cudaMemcpyAsync(h, x->counters, sizeof(h), cudaMemcpyDeviceToHost, x->stream));
+  if (rc == KH_OK) rc = cuda_rc(cudaMemcpyAsync(&dt, x->dscalar, sizeof(double), cudaMemcpyDeviceToHost, x->stream));
+  if (rc == KH_OK) rc = cuda_rc(cudaStreamSynchronize(x->stream));
+  if (rc != KH_OK) return rc;
+  out->nfail = (int64_t)h[CNT_FAIL];
+  out->nfloor = (int64_t)h[CNT_FLOOR];
+  out->nunfixed = (int64_t)h[CNT_UNFIXED];
+  out->dt_cfl = dt;
+  return KH_OK;
+}
+
+int kh_mesh_step(kh_mesh* x, double* U, double* P, double* B, double dt, double* dt_cfl) {
+  if (!x || !U || !P || !B || !(dt > 0.0) || !isfinite(dt)) return KH_EINVAL;
+  int rc = cuda_rc(cudaMemcpyAsync(x->dscalar + 3, &dt, sizeof(double), cudaMemcpyHostToDevice, x->stream));
+  if (rc != KH_OK) return rc;
+  if (x->graph_on) {
+    if (!(x->gexec && x->gkey[0] == U && x->gkey[1] == P && x->gkey[2] == B)) {
+      drop_mesh_graph(x);
+      if (!x->cap_stream && cudaStreamCreateWithFlags(&x->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return KH_ECUDA;
+      cudaStream_t user = x->stream;
+      x->stream = x->cap_stream;
+      if (cudaStreamBeginCapture(x->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        x->stream = user;
+        return KH_ECUDA;
+      }
+      const int n = issue_mesh_step(x, U, P, B);
+      cudaGraph_t g = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(x->cap_stream, &g);
+      x->stream = user;
+      if (n < 0 || e != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        return KH_ECUDA;
+      }
+      const cudaError_t ei = cudaGraphInstantiate(&x->gexec, g, 0);
+      cudaGraphDestroy(g);
+      if (ei != cudaSuccess) {
+        x->gexec = nullptr;
+        return KH_ECUDA;
+      }
+      x->gkey[0] = U;
+      x->gkey[1] = P;
+      x->gkey[2] = B;
+      x->graph_launches = n;
+    }
+    if (cudaGraphLaunch(x->gexec, x->stream) != cudaSuccess) return KH_ECUDA;
+    x->launches += x->graph_launches;
+  } else {
+    const int n = issue_mesh_step(x, U, P, B);
+    if (n < 0) return KH_ECUDA;
+    x->launches += n;
+  }
+  rc = cuda_rc(cudaGetLastError());
+  if (rc != KH_OK || !dt_cfl) return rc;
+  kh_stats st;
+  rc = kh_mesh_get_stats(x, &st);
+  if (rc != KH_OK) return rc;
+  *dt_cfl = st.dt_cfl;
+  if (!isfinite(st.dt_cfl)) return KH_ENAN;
+  return (int)(st.nfail > 0x7fffffffLL ? 0x7fffffff : st.nfail);
+}
+
+int kh_mesh_set_graph(kh_mesh* x, int enable) {
+  if (!x) return KH_EINVAL;
+  if (!enable) drop_mesh_graph(x);
+  x->graph_on = enable ? 1 : 0;
+  return KH_OK;
+}
+
+int kh_mesh_destroy(kh_mesh* x) {
+  if (!x) return KH_EINVAL;
+  cudaStreamSynchronize(x->stream);
+  drop_mesh_graph(x);
+  if (x->cap_stream) cudaStreamDestroy(x->cap_stream);
+  void* ptrs[] = {x->dblk, x->dops, x->dnbs, x->geo, x->conn, x->flo, x->geof, x->connf, x->pstar, x->pstarf, x->pnf,
+                  x->pflag, x->partial, x->dscalar, x->counters, x->F[0], x->F[1], x->F[2], x->ctop[0],
+                  x->ctop[1], x->ctop[2], x->emf[0], x->emf[1], x->emf[2], x->Ff[0], x->Ff[1], x->Ff[2],
+                  x->ctopf[0], x->ctopf[1], x->ctopf[2], x->emff[0], x->emff[1], x->emff[2]};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (int q = 0; q < 7; ++q)
+    if (x->dpre[q]) cudaFree(x->dpre[q]);
+  delete x;
+  return KH_OK;
+}
+
+}  // extern "C"

@@ -48,9 +48,14 @@ def uniform01(seed: int, index: np.ndarray) -> np.ndarray:
 
 
 def interior_index(cfg: dict) -> np.ndarray:
-    """Global interior zone index (k n2 + j) n1 + i over the interior, shape (n3, n2, n1)."""
+    """Global interior zone index (k n2 + j) n1 + i over the interior, shape (n3, n2, n1).
+    For a block of a refined mesh (cfg["block"] = (level, i0, j0, k0, N1l, N2l)),
+    the index of the zone in its level's grid, offset by level * 2^40."""
     n1, n2, n3 = cfg["n1"], cfg["n2"], cfg["n3"]
     k, j, i = np.meshgrid(np.arange(n3), np.arange(n2), np.arange(n1), indexing="ij")
+    if "block" in cfg:
+        lev, i0, j0, k0, N1l, N2l = cfg["block"]
+        return (((k + k0) * N2l + (j + j0)) * N1l + (i + i0) + lev * (1 << 40)).astype(np.uint64)
     return ((k * n2 + j) * n1 + i).astype(np.uint64)
 
 
@@ -146,7 +151,7 @@ def _theta(cfg: dict, x1, x2):
     y = 2.0 * x2 - 1.0
     nrm = 0.5 * np.pi / (1.0 + xt ** (-al) / (al + 1.0))
     thj = 0.5 * np.pi + nrm * y * (1.0 + (y / xt) ** int(al) / (al + 1.0))
-    return thg + np.exp(s * (cfg["x1"][0] - x1)) * (thj - thg)
+    return thg + np.exp(s * (cfg.get("x1ref", cfg["x1"][0]) - x1)) * (thj - thg)
 
 
 def embed(cfg: dict, x1, x2):
@@ -398,7 +403,14 @@ def fm_density(cfg: dict, r, th, kappa: float = 1e-3):
     return rho, uint, inside
 
 
-def torus_state(cfg: dict, seed: int = 2, noise: float = 4e-2, kappa: float = 1e-3, field: bool = True):
+def torus_norms(cfg: dict, kappa: float = 1e-3):
+    """(rho_max, field normalisation) of the torus on the grid of cfg."""
+    _, info = torus_state(cfg, noise=0.0, kappa=kappa, return_norms=True)
+    return info
+
+
+def torus_state(cfg: dict, seed: int = 2, noise: float = 4e-2, kappa: float = 1e-3, field: bool = True,
+                norms=None, return_norms: bool = False):
     """FM torus (rho_max = 1) in an atmosphere at the floors, single poloidal
     loop from A_phi = max(rho/rho_max - 0.2, 0) at corners normalised to
     beta = max(p_gas) / max(p_mag) (p_mag = g_ij B^i B^j / 2), multiplicative
@@ -414,11 +426,12 @@ def torus_state(cfg: dict, seed: int = 2, noise: float = 4e-2, kappa: float = 1e
     ut_bl, uph = fm_velocity(cfg["a"], fm_angular_momentum(a, cfg["r_max"]), r, th)
     # BL -> KS with u^r = 0: u^t and u^phi are unchanged.
     u1, u2, u3 = utilde_from_ks(cfg, X1, X2, ut_bl, 0.0 * r, 0.0 * r, uph)
-    rho_max = rho.max()
+    rho_max = rho.max() if norms is None else norms[0]
     rho = rho / rho_max
     uint = uint / rho_max
     rho_atm = np.maximum(fl["rho_min"] * r ** -1.5, 1e-20)
     u_atm = np.maximum(fl["u_min"] * r ** -2.5, 1e-20)
+    norm = 0.0
     P2 = np.zeros((8,) + r.shape)
     P2[0] = np.where(inside, rho, rho_atm)
     P2[1] = np.where(inside, uint, u_atm)
@@ -454,7 +467,10 @@ def torus_state(cfg: dict, seed: int = 2, noise: float = 4e-2, kappa: float = 1e
         pmag = 0.5 * (g11 * B1 * B1 + 2.0 * g12 * B1 * B2 + g22 * B2 * B2)
         pgas = (cfg["gam"] - 1.0) * P2[1]
         sl = interior(cfg)
-        norm = math.sqrt((pgas[sl[1], sl[2]].max() / pmag[sl[1], sl[2]].max()) / cfg["beta"])
+        if norms is None:
+            norm = math.sqrt((pgas[sl[1], sl[2]].max() / pmag[sl[1], sl[2]].max()) / cfg["beta"])
+        else:
+            norm = norms[1]
         P2[5] = B1 * norm
         P2[6] = B2 * norm
     P = np.zeros(shape(cfg))
@@ -465,6 +481,8 @@ def torus_state(cfg: dict, seed: int = 2, noise: float = 4e-2, kappa: float = 1e
         ins3 = np.broadcast_to(inside[None, sl[1], sl[2]], xi.shape)
         fac = np.where(ins3, 1.0 + noise * (xi - 0.5), 1.0)
         P[1][sl] = P[1][sl] * fac
+    if return_norms:
+        return P, (rho_max, norm if field else 0.0)
     return P
 
 
@@ -510,3 +528,63 @@ def random_prims(cfg: dict, seed: int, rho_range=(1e-4, 1.0), u_range=(1e-6, 1.0
         if b_sqrt_rho:
             P[5 + q] *= np.sqrt(P[0])
     return P
+
+
+# ---------------------------------------------------------------------------
+# Statically refined meshes: per-block problem configurations.
+# ---------------------------------------------------------------------------
+def block_cfg(base: dict, blk: dict) -> dict:
+    """Configuration of one block (level l, interior box [i0, i0+n1) x ... in
+    level-l indices) of a mesh whose level-0 grid is base: same coordinates and
+    scheme, the block's box as the native extent, base's x1 start as the FMKS
+    reference, boundaries that are physical only where the block touches them."""
+    lev = blk["level"]
+    r3 = 2 if base["n3"] > 1 else 1
+    rr = (2 ** lev, 2 ** lev, r3 ** lev)
+    cfg = dict(base)
+    ext = []
+    for d, key, nk, ok in ((0, "x1", "n1", "i0"), (1, "x2", "n2", "j0"), (2, "x3", "n3", "k0")):
+        lo, hi = base[key]
+        dx = (hi - lo) / (base[nk] * rr[d])
+        ext.append((lo + blk[ok] * dx, lo + (blk[ok] + blk[nk]) * dx))
+        cfg[nk] = blk[nk]
+    cfg["x1"], cfg["x2"], cfg["x3"] = ext
+    cfg["x1ref"] = base["x1"][0]
+    bc = list(base["bc"])
+    nl = [base["n1"] * rr[0], base["n2"] * rr[1], base["n3"] * rr[2]]
+    for d, ok, nk in ((0, "i0", "n1"), (1, "j0", "n2"), (2, "k0", "n3")):
+        if blk[ok] != 0:
+            bc[2 * d] = "outflow" if bc[2 * d] == "polar" else bc[2 * d]
+        if blk[ok] + blk[nk] != nl[d]:
+            bc[2 * d + 1] = "outflow" if bc[2 * d + 1] == "polar" else bc[2 * d + 1]
+    cfg["bc"] = bc
+    cfg["block"] = (lev, blk["i0"], blk["j0"], blk["k0"], nl[0], nl[1])
+    return cfg
+
+
+def _tile(level, box, size):
+    """Blocks of `size` (n1, n2, n3) tiling the level-`level` index box
+    ((i0, i1), (j0, j1), (k0, k1)); every extent must divide evenly."""
+    (i0, i1), (j0, j1), (k0, k1) = box
+    s1, s2, s3 = size
+    assert (i1 - i0) % s1 == 0 and (j1 - j0) % s2 == 0 and (k1 - k0) % s3 == 0
+    return [dict(level=level, i0=i, j0=j, k0=k, n1=s1, n2=s2, n3=s3)
+            for k in range(k0, k1, s3) for j in range(j0, j1, s2) for i in range(i0, i1, s1)]
+
+
+def smr_torus_layout(n1: int = 128, n2: int = 64, n3: int = 64):
+    """Three-level static refinement of the torus grid (base n1 x n2 x n3 at
+    level 0): level 2 over the inner half in x1 and the middle quarter in x2
+    (the disc), level 1 around it (the inner three quarters in x1, the middle
+    half in x2), level 0 elsewhere (the polar caps and the outer x1 quarter).
+    Blocks: 16x16x32 at level 2; 16x32x32 and 32x16x32 at level 1; 32^3 and
+    32x16x32 at level 0. At the default size: 592 blocks, 5,570,560 zones."""
+    q1, q2 = n1 // 4, n2 // 8
+    L2 = _tile(2, ((0, 8 * q1), (4 * 3 * q2, 4 * 5 * q2), (0, 4 * n3)), (16, 16, 32))
+    L1 = (_tile(1, ((2 * 2 * q1, 2 * 3 * q1), (2 * 2 * q2, 2 * 6 * q2), (0, 2 * n3)), (16, 32, 32))
+          + _tile(1, ((0, 2 * 2 * q1), (2 * 2 * q2, 2 * 3 * q2), (0, 2 * n3)), (32, 16, 32))
+          + _tile(1, ((0, 2 * 2 * q1), (2 * 5 * q2, 2 * 6 * q2), (0, 2 * n3)), (32, 16, 32)))
+    L0 = (_tile(0, ((3 * q1, n1), (0, n2), (0, n3)), (32, 32, 32))
+          + _tile(0, ((0, 3 * q1), (0, 2 * q2), (0, n3)), (32, 16, 32))
+          + _tile(0, ((0, 3 * q1), (6 * q2, n2), (0, n3)), (32, 16, 32)))
+    return torus_cfg(n1, n2, n3), L0 + L1 + L2

@@ -49,6 +49,11 @@ class Stats(C.Structure):
     _fields_ = [("nfail", C.c_int64), ("nfloor", C.c_int64), ("nunfixed", C.c_int64), ("dt_cfl", C.c_double)]
 
 
+class Block(C.Structure):
+    _fields_ = [("level", C.c_int), ("i0", C.c_int), ("j0", C.c_int), ("k0", C.c_int),
+                ("n1", C.c_int), ("n2", C.c_int), ("n3", C.c_int)]
+
+
 _lib = None
 
 
@@ -83,6 +88,20 @@ def lib():
         L.kh_destroy.argtypes = [vp]
         L.kh_strerror.argtypes = [C.c_int]
         L.kh_strerror.restype = C.c_char_p
+        L.kh_mesh_init.argtypes = [C.c_double, C.POINTER(Coords), C.c_double, C.c_int, C.POINTER(Block),
+                                   C.POINTER(C.c_void_p)]
+        L.kh_mesh_block_shape.argtypes = [vp, C.c_int, ip, ip, ip, C.POINTER(C.c_int64)]
+        for f in ("kh_mesh_cells", "kh_mesh_zones", "kh_mesh_ghost_cells", "kh_mesh_launch_count"):
+            getattr(L, f).argtypes = [vp]
+            getattr(L, f).restype = C.c_int64
+        L.kh_mesh_set_stream.argtypes = [vp, vp]
+        L.kh_mesh_prim_to_cons.argtypes = [vp, vp, vp, vp]
+        L.kh_mesh_fill_ghosts.argtypes = [vp, vp, vp]
+        L.kh_mesh_cfl_dt.argtypes = [vp, vp, vp, dp]
+        L.kh_mesh_step.argtypes = [vp, vp, vp, vp, C.c_double, dp]
+        L.kh_mesh_set_graph.argtypes = [vp, C.c_int]
+        L.kh_mesh_get_stats.argtypes = [vp, C.POINTER(Stats)]
+        L.kh_mesh_destroy.argtypes = [vp]
         _lib = L
     return _lib
 
@@ -269,3 +288,131 @@ def divb_noalloc(B, gdet, n1: int, n2: int, n3: int, n1s: int, n2s: int, dx, out
     rc = f(_ptr(B), _ptr(gdet), n1, n2, n3, n1s, n2s, float(dx[0]), float(dx[1]), float(dx[2]), _ptr(out),
            C.c_void_p(stream.cuda_stream if stream is not None else 0))
     return _check(rc, "kh_divb_noalloc")
+
+
+class Mesh:
+    """One kh_mesh: statically refined blocks stepped together.
+
+    ``blocks`` is a list of dicts {level, i0, j0, k0, n1, n2, n3} (first
+    interior cell and interior size in level-``level`` indices; level l is
+    2^l times finer than the base grid of ``cfg``). State lives in three flat
+    arenas (U: 8 slots, P: 5, B: 3 per cell of every block); ``views`` gives
+    each block's (nvar, n3s, n2s, n1s) window into an arena.
+    """
+
+    def __init__(self, cfg: dict, blocks: list, device=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise KHError("no CUDA device: the GB300 path has no CPU fallback")
+        self.torch = torch
+        self.device = torch.device(device or "cuda:0")
+        torch.cuda.set_device(self.device)
+        self.cfg = cfg
+        self.blocks = blocks
+        self._c = coords_from_cfg(cfg)
+        arr = (Block * len(blocks))()
+        for q, b in enumerate(blocks):
+            arr[q] = Block(b["level"], b["i0"], b["j0"], b.get("k0", 0), b["n1"], b["n2"], b.get("n3", 1))
+        h = C.c_void_p()
+        _check(lib().kh_mesh_init(float(cfg.get("a", 0.0)), C.byref(self._c), float(cfg["gam"]), len(blocks), arr,
+                                  C.byref(h)), "kh_mesh_init")
+        self._h = h
+        self.shapes, self.offsets = [], []
+        for q in range(len(blocks)):
+            a, b, c, o = C.c_int(), C.c_int(), C.c_int(), C.c_int64()
+            _check(lib().kh_mesh_block_shape(h, q, C.byref(a), C.byref(b), C.byref(c), C.byref(o)),
+                   "kh_mesh_block_shape")
+            self.shapes.append((c.value, b.value, a.value))
+            self.offsets.append(o.value)
+        self.cells = int(lib().kh_mesh_cells(h))
+        self.zones = int(lib().kh_mesh_zones(h))
+        self.ghost_cells = int(lib().kh_mesh_ghost_cells(h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().kh_mesh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        _check(lib().kh_mesh_set_stream(self._h, C.c_void_p(stream.cuda_stream if stream is not None else 0)),
+               "kh_mesh_set_stream")
+
+    # ---- arenas ----
+    def empty(self, nvar: int):
+        return self.torch.zeros(nvar * self.cells, dtype=self.torch.float64, device=self.device)
+
+    def views(self, arena, nvar: int):
+        out = []
+        for (n3s, n2s, n1s), off in zip(self.shapes, self.offsets):
+            pl = n3s * n2s * n1s
+            out.append(arena[nvar * off: nvar * off + nvar * pl].view(nvar, n3s, n2s, n1s))
+        return out
+
+    def to_device(self, PBs):
+        """List of per-block (8, N3, N2, N1) numpy arrays -> (P arena, B arena)."""
+        P, B = self.empty(5), self.empty(3)
+        for A, vp, vb in zip(PBs, self.views(P, 5), self.views(B, 3)):
+            src = self.torch.from_numpy(np.ascontiguousarray(A))
+            vp[:, :, :, : A.shape[3]].copy_(src[:5])
+            vb[:, :, :, : A.shape[3]].copy_(src[5:])
+        return P, B
+
+    def to_host(self, P, B):
+        """(P, B) arenas -> list of per-block (8, N3, N2, N1) numpy arrays."""
+        out = []
+        for blk, vp, vb in zip(self.blocks, self.views(P, 5), self.views(B, 3)):
+            N1 = blk["n1"] + 2 * 3
+            out.append(np.concatenate([vp[:, :, :, :N1].cpu().numpy(), vb[:, :, :, :N1].cpu().numpy()]))
+        return out
+
+    def cons_to_device(self, Us):
+        """List of per-block (8, N3, N2, N1) numpy conserved arrays -> U arena."""
+        U = self.empty(8)
+        for A, vu in zip(Us, self.views(U, 8)):
+            vu[:, :, :, : A.shape[3]].copy_(self.torch.from_numpy(np.ascontiguousarray(A)))
+        return U
+
+    def cons_to_host(self, U):
+        out = []
+        for blk, vu in zip(self.blocks, self.views(U, 8)):
+            out.append(vu[:, :, :, : blk["n1"] + 2 * 3].cpu().numpy())
+        return out
+
+    # ---- the C ABI ----
+    def prim_to_cons(self, P, B, U):
+        _check(lib().kh_mesh_prim_to_cons(self._h, _ptr(P), _ptr(B), _ptr(U)), "kh_mesh_prim_to_cons")
+
+    def fill_ghosts(self, P, B):
+        _check(lib().kh_mesh_fill_ghosts(self._h, _ptr(P), _ptr(B)), "kh_mesh_fill_ghosts")
+
+    def cfl_dt(self, P, B) -> float:
+        d = C.c_double()
+        _check(lib().kh_mesh_cfl_dt(self._h, _ptr(P), _ptr(B), C.byref(d)), "kh_mesh_cfl_dt")
+        return d.value
+
+    def step(self, U, P, B, dt: float, sync: bool = True):
+        if sync:
+            d = C.c_double()
+            rc = _check(lib().kh_mesh_step(self._h, _ptr(U), _ptr(P), _ptr(B), float(dt), C.byref(d)),
+                        "kh_mesh_step")
+            return d.value, rc
+        _check(lib().kh_mesh_step(self._h, _ptr(U), _ptr(P), _ptr(B), float(dt), None), "kh_mesh_step")
+        return None, None
+
+    def set_graph(self, enable: bool):
+        _check(lib().kh_mesh_set_graph(self._h, 1 if enable else 0), "kh_mesh_set_graph")
+
+    def stats(self) -> Stats:
+        s = Stats()
+        _check(lib().kh_mesh_get_stats(self._h, C.byref(s)), "kh_mesh_get_stats")
+        return s
+
+    def launches(self) -> int:
+        return int(lib().kh_mesh_launch_count(self._h))
