@@ -242,6 +242,11 @@ int kh_mesh_fill_ghosts(kh_mesh* mesh, double* P, double* B);
  * per step phase covers every block. */
 int kh_mesh_cfl_dt(kh_mesh* mesh, const double* P, const double* B, double* dt_cfl);
 int kh_mesh_step(kh_mesh* mesh, double* U, double* P, double* B, double dt, double* dt_cfl);
+/* Corner divB of sqrt(-g) B (as kh_divb) at the corners of every block whose
+ * adjacent cells are all interior cells of that block: max |divB| and its
+ * mean over those corners. Corners on block faces are left out: Flux-CT
+ * holds divB only inside blocks (level interfaces are not constrained). */
+int kh_mesh_divb(kh_mesh* mesh, const double* B, double* max_abs, double* l1);
 int kh_mesh_set_graph(kh_mesh* mesh, int enable);
 int kh_mesh_get_stats(kh_mesh* mesh, kh_stats* out);
 int64_t kh_mesh_launch_count(const kh_mesh* mesh);

@@ -201,8 +201,8 @@ int run_stage_mixed(kh_ctx* x, int st, const double* U0, const VarsT<TIN>& Pin, 
   n += launch_ct<float>(x->Ff, x->emff, L, s);
   mark(x, KH_T_CT, st, 1);
   mark(x, KH_T_UPDATE, st, 0);
-  n += launch_update_mixed<TIN>(U0, cviewT(Pin), Pout64, Pout32, Uout, x->Ff, L, G, Gf, x->S, x->dscalar + 3, coef,
-                                x->pflag, x->counters, x->tpb_update, s);
+  n += launch_update_mixed(U0, cviewT(Pf), Pout64, Pout32, Uout, x->Ff, L, G, Gf, x->S, x->dscalar + 3, coef,
+                           x->pflag, x->counters, x->tpb_update, s);
   mark(x, KH_T_UPDATE, st, 1);
   mark(x, KH_T_FIXUP, st, 0);
   if (Pout64.v[0])
@@ -283,6 +283,8 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
 
   Scheme& S = x->S;
   S.gam = gamma;
+  S.igam = 1.0 / gamma;
+  S.gfac = (gamma - 1.0) / gamma;
   S.cfl = c->cfl;
   S.recon = c->recon;
   for (int q = 0; q < 6; ++q) S.bc[q] = c->bc[q];
@@ -307,7 +309,7 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
   }
   KH_ALLOC(x->geo, 3 * NGEO * gp);
   KH_ALLOC(x->conn, NCONN * gp);
-  KH_ALLOC(x->flo, 2 * gp);
+  KH_ALLOC(x->flo, 3 * gp);
   const bool mixed = c->precision == KH_MIXED;
   const size_t plf = (size_t)L.plane * sizeof(float);
   const size_t gpf = (size_t)L.gplane * sizeof(float);

@@ -46,12 +46,14 @@ using CVars = CVarsT<double>;
 template <class T> struct GeomT {
   const T* g;          // [3][NGEO][n2s][n1s]
   const T* conn;       // [NCONN][n2s][n1s]
-  const double* flo;   // [2][n2s][n1s]: geometric floors of rho and u at cell centres
+  const double* flo;   // [3][n2s][n1s]: geometric floors of rho and u, and 1/sqrt(-g), at cell centres
 };
 using DevGeom = GeomT<double>;
 
 struct Scheme {
   double gam;
+  double igam;  // 1 / gam
+  double gfac;  // (gam - 1) / gam
   double cfl;
   int recon;
   int bc[6];
@@ -81,11 +83,10 @@ int launch_update(const double* U0, const CVars& Pin, const Vars& Pout, double* 
                   const Layout& L, const DevGeom& G, const Scheme& S, const double* dtp, double coef, int8_t* pflag,
                   unsigned long long* cnt, int tpb, cudaStream_t s);
 // Mixed update: FP32 fluxes and sources, FP64 accumulation of U and FP64
-// inversion; the stage input (sources and inversion guess) is read in TIN.
+// inversion; the stage input (sources, inversion guess) is read in FP32.
 // Writes the FP64 output (Pout64.v[0] may be null) and/or its FP32 shadow
 // (Pout32.v[0] may be null), and U when Uout is given (stage 2).
-template <class TIN>
-int launch_update_mixed(const double* U0, const CVarsT<TIN>& Pin, const Vars& Pout64, const VarsT<float>& Pout32,
+int launch_update_mixed(const double* U0, const CVarsT<float>& Pin, const Vars& Pout64, const VarsT<float>& Pout32,
                         double* Uout, float* const F[3], const Layout& L, const DevGeom& G, const GeomT<float>& Gf,
                         const Scheme& S, const double* dtp, double coef, int8_t* pflag, unsigned long long* cnt,
                         int tpb, cudaStream_t s);

@@ -55,6 +55,7 @@ __global__ void k_geometry(CoordParams cp, double x1o, double x2o, FloorParams f
       const double r = (cp.kind == COORD_MINKOWSKI) ? 1.0 : coord_map(cp, x1c, x2c).r;
       flo[p] = fmax(fl.rho_min * pow(r, -1.5), 1e-20);
       flo[L.gplane + p] = fmax(fl.u_min * pow(r, -2.5), 1e-20);
+      flo[2 * L.gplane + p] = 1.0 / sqrt(fabs(det));
     }
   }
 }
@@ -202,8 +203,7 @@ __global__ void __launch_bounds__(TPB_MAX) k_update(const double* U0, CVars Pin,
   update_zone(U0, Pin, Pout, Uout, F1, F2, F3, L, G, S, coef * __ldg(dtp), pflag, cnt, i, j, k);
 }
 
-template <class TIN>
-__global__ void __launch_bounds__(TPB_MAX) k_update_mixed(const double* U0, CVarsT<TIN> Pin, Vars Pout64,
+__global__ void __launch_bounds__(TPB_MAX) k_update_mixed(const double* U0, CVarsT<float> Pin, Vars Pout64,
                                                          VarsT<float> Pout32, double* Uout, const float* F1,
                                                          const float* F2, const float* F3, Layout L, DevGeom G,
                                                          GeomT<float> Gf, Scheme S, const double* dtp, double coef,
@@ -212,8 +212,7 @@ __global__ void __launch_bounds__(TPB_MAX) k_update_mixed(const double* U0, CVar
   if (t >= nzones(L)) return;
   int i, j, k;
   zone_ijk(L, t, i, j, k);
-  update_mixed_zone<TIN>(U0, Pin, Pout64, Pout32, Uout, F1, F2, F3, L, G, Gf, S, coef * __ldg(dtp), pflag, cnt, i,
-                         j, k);
+  update_mixed_zone(U0, Pin, Pout64, Pout32, Uout, F1, F2, F3, L, G, Gf, S, coef * __ldg(dtp), pflag, cnt, i, j, k);
 }
 
 template <class T>
@@ -304,20 +303,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_divb(const double* B1, const do
     const int i = L.s[0] + 1 + (int)(t % n0);
     const int j = L.s[1] + 1 + (int)((t / n0) % n1);
     const int k = (L.ndim == 3 ? L.s[2] + 1 : 0) + (int)(t / ((long long)n0 * n1));
-    auto gB = [&](const double* B, int kk, int jj, int ii) { return gd[(long long)jj * L.n1s + ii] * B[L.at(kk, jj, ii)]; };
-    double dv;
-    if (L.ndim == 2) {
-      dv = (gB(B1, k, j, i) + gB(B1, k, j - 1, i) - gB(B1, k, j, i - 1) - gB(B1, k, j - 1, i - 1)) / (2.0 * L.dx[0]) +
-           (gB(B2, k, j, i) + gB(B2, k, j, i - 1) - gB(B2, k, j - 1, i) - gB(B2, k, j - 1, i - 1)) / (2.0 * L.dx[1]);
-    } else {
-      const double a1 = gB(B1, k, j, i) + gB(B1, k, j - 1, i) + gB(B1, k - 1, j, i) + gB(B1, k - 1, j - 1, i);
-      const double b1 = gB(B1, k, j, i - 1) + gB(B1, k, j - 1, i - 1) + gB(B1, k - 1, j, i - 1) + gB(B1, k - 1, j - 1, i - 1);
-      const double a2 = gB(B2, k, j, i) + gB(B2, k, j, i - 1) + gB(B2, k - 1, j, i) + gB(B2, k - 1, j, i - 1);
-      const double b2 = gB(B2, k, j - 1, i) + gB(B2, k, j - 1, i - 1) + gB(B2, k - 1, j - 1, i) + gB(B2, k - 1, j - 1, i - 1);
-      const double a3 = gB(B3, k, j, i) + gB(B3, k, j, i - 1) + gB(B3, k, j - 1, i) + gB(B3, k, j - 1, i - 1);
-      const double b3 = gB(B3, k - 1, j, i) + gB(B3, k - 1, j, i - 1) + gB(B3, k - 1, j - 1, i) + gB(B3, k - 1, j - 1, i - 1);
-      dv = (a1 - b1) / (4.0 * L.dx[0]) + (a2 - b2) / (4.0 * L.dx[1]) + (a3 - b3) / (4.0 * L.dx[2]);
-    }
+    const double dv = divb_corner(B1, B2, B3, L, gd, i, j, k);
     mx = fmax(mx, fabs(dv));
     sm += fabs(dv);
   }
@@ -357,8 +343,8 @@ __global__ void __launch_bounds__(TPB) k_c2p(const double* U, Vars P, int8_t* pf
     u[v] = U[v * L.plane + c];
     p[v] = P.v[v][c];
   }
-  const int flag = noble2d(u, m, S.gam, S.c2p, p);
-  const double ig = 1.0 / m.gdet;
+  const double ig = __ldg(G.flo + 2 * L.gplane + (long long)j * L.n1s + i);  // 1 / sqrt(-g)
+  const int flag = noble2d(u, m, ig, S.gam, S.igam, S.gfac, S.c2p, p);
   p[V_B1] = u[V_B1] * ig;
   p[V_B2] = u[V_B2] * ig;
   p[V_B3] = u[V_B3] * ig;
@@ -463,24 +449,15 @@ int launch_update(const double* U0, const CVars& Pin, const Vars& Pout, double* 
   return 1;
 }
 
-template <class TIN>
-int launch_update_mixed(const double* U0, const CVarsT<TIN>& Pin, const Vars& Pout64, const VarsT<float>& Pout32,
+int launch_update_mixed(const double* U0, const CVarsT<float>& Pin, const Vars& Pout64, const VarsT<float>& Pout32,
                         double* Uout, float* const F[3], const Layout& L, const DevGeom& G, const GeomT<float>& Gf,
                         const Scheme& S, const double* dtp, double coef, int8_t* pflag, unsigned long long* cnt,
                         int tpb, cudaStream_t s) {
   const long long nz = (long long)L.n1 * L.n2 * L.n3;
-  k_update_mixed<TIN><<<nblocks(nz, tpb), tpb, 0, s>>>(U0, Pin, Pout64, Pout32, Uout, F[0], F[1], F[2], L, G, Gf, S,
-                                                      dtp, coef, pflag, cnt);
+  k_update_mixed<<<nblocks(nz, tpb), tpb, 0, s>>>(U0, Pin, Pout64, Pout32, Uout, F[0], F[1], F[2], L, G, Gf, S, dtp,
+                                                  coef, pflag, cnt);
   return 1;
 }
-template int launch_update_mixed<double>(const double*, const CVarsT<double>&, const Vars&, const VarsT<float>&, double*,
-                                      float* const[3], const Layout&, const DevGeom&, const GeomT<float>&,
-                                      const Scheme&, const double*, double, int8_t*, unsigned long long*, int,
-                                      cudaStream_t);
-template int launch_update_mixed<float>(const double*, const CVarsT<float>&, const Vars&, const VarsT<float>&, double*,
-                                      float* const[3], const Layout&, const DevGeom&, const GeomT<float>&,
-                                      const Scheme&, const double*, double, int8_t*, unsigned long long*, int,
-                                      cudaStream_t);
 
 template <class T>
 int launch_fixup(const VarsT<T>& P, double* Uout, const int8_t* pflag, const Layout& L, const DevGeom& G,

@@ -97,10 +97,10 @@ struct GeoArena {
   const float* connf;
 };
 __device__ __forceinline__ DevGeom geo64(const GeoArena& A, const MBlock& m) {
-  return DevGeom{A.g + 3LL * NGEO * m.goff, A.conn + (long long)NCONN * m.goff, A.flo + 2 * m.goff};
+  return DevGeom{A.g + 3LL * NGEO * m.goff, A.conn + (long long)NCONN * m.goff, A.flo + 3 * m.goff};
 }
 __device__ __forceinline__ GeomT<float> geo32(const GeoArena& A, const MBlock& m) {
-  return GeomT<float>{A.gf + 3LL * NGEO * m.goff, A.connf + (long long)NCONN * m.goff, A.flo + 2 * m.goff};
+  return GeomT<float>{A.gf + 3LL * NGEO * m.goff, A.connf + (long long)NCONN * m.goff, A.flo + 3 * m.goff};
 }
 
 // Largest b with pre[b] <= t (pre has nb + 1 entries, pre[0] = 0).
@@ -169,9 +169,8 @@ __global__ void __launch_bounds__(256) km_update(const MBlock* blk, const unsign
               k);
 }
 
-template <class TIN>
 __global__ void __launch_bounds__(256) km_update_mixed(const MBlock* blk, const unsigned* pre, int nb,
-                                                      const double* U0, Arena<TIN> Pin, Arena<double> Pout64,
+                                                      const double* U0, Arena<float> Pin, Arena<double> Pout64,
                                                       Arena<float> Pout32, double* Uout, const float* F1,
                                                       const float* F2, const float* F3, GeoArena GA, Scheme S,
                                                       const double* dtp, double coef, int8_t* pflag,
@@ -187,9 +186,9 @@ __global__ void __launch_bounds__(256) km_update_mixed(const MBlock* blk, const 
   VarsT<float> P32;
   if (Pout64.a) P64 = vars_at(Pout64, m); else for (int v = 0; v < NV; ++v) P64.v[v] = nullptr;
   if (Pout32.a) P32 = vars_at(Pout32, m); else for (int v = 0; v < NV; ++v) P32.v[v] = nullptr;
-  update_mixed_zone<TIN>(U0 + o8, cvars_at(Pin, m), P64, P32, Uout ? Uout + o8 : nullptr, F1 + o8, F2 + o8,
-                         m.L.ndim == 3 ? F3 + o8 : nullptr, m.L, geo64(GA, m), geo32(GA, m), S, coef * __ldg(dtp),
-                         pflag + m.off, cnt, i, j, k);
+  update_mixed_zone(U0 + o8, cvars_at(Pin, m), P64, P32, Uout ? Uout + o8 : nullptr, F1 + o8, F2 + o8,
+                    m.L.ndim == 3 ? F3 + o8 : nullptr, m.L, geo64(GA, m), geo32(GA, m), S, coef * __ldg(dtp),
+                    pflag + m.off, cnt, i, j, k);
 }
 
 template <class T>
@@ -262,6 +261,71 @@ __device__ __forceinline__ double restrict_at(const Arena<T>& P, const MBlock& m
     for (int dj = 0; dj < 2; ++dj)
       for (int di = 0; di < 2; ++di) acc += (double)q[c + di + dj * sj + dk * sk];
   return (L.ndim == 3 ? 0.125 : 0.25) * acc;
+}
+
+__device__ __forceinline__ double wsum(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// Block-wide max and sum of (a, b); thread 0 holds the result.
+__device__ __forceinline__ void block_max_sum2(double& a, double& b) {
+  __shared__ double sa[RED_THREADS / 32], sb[RED_THREADS / 32];
+  a = wmax(a);
+  b = wsum(b);
+  if ((threadIdx.x & 31) == 0) {
+    sa[threadIdx.x >> 5] = a;
+    sb[threadIdx.x >> 5] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    a = threadIdx.x < RED_THREADS / 32 ? sa[threadIdx.x] : 0.0;
+    b = threadIdx.x < RED_THREADS / 32 ? sb[threadIdx.x] : 0.0;
+    a = wmax(a);
+    b = wsum(b);
+  }
+}
+
+// Corner divB at the corners of every block whose adjacent cells are all
+// interior cells of that block; per launch block: (max |divB|, sum |divB|).
+__global__ void __launch_bounds__(RED_THREADS) km_divb(const MBlock* blk, const unsigned* pre, int nb,
+                                                      const double* B, const double* geo, double* partial) {
+  double mx = 0.0, sm = 0.0;
+  const unsigned tot = __ldg(pre + nb);
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
+    const int b = find_block(pre, nb, t);
+    const MBlock& m = blk[b];
+    const Layout& L = m.L;
+    int i, j, k;
+    split3(t - __ldg(pre + b), L.n1 - 1, L.n2 - 1, i, j, k);
+    i += L.s[0] + 1;
+    j += L.s[1] + 1;
+    k += L.ndim == 3 ? L.s[2] + 1 : 0;
+    const double* Bb = B + 3 * m.off;
+    const double* gd = geo + 3LL * NGEO * m.goff + (long long)LOC_CENT * NGEO * L.gplane + 20 * L.gplane;
+    const double dv = divb_corner(Bb, Bb + L.plane, Bb + 2 * L.plane, L, gd, i, j, k);
+    mx = fmax(mx, fabs(dv));
+    sm += fabs(dv);
+  }
+  block_max_sum2(mx, sm);
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = mx;
+    partial[2 * blockIdx.x + 1] = sm;
+  }
+}
+
+__global__ void km_max_sum_finish(const double* partial, int n, double* out) {
+  double a = 0.0, b = 0.0;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    a = fmax(a, partial[2 * q]);
+    b += partial[2 * q + 1];
+  }
+  block_max_sum2(a, b);
+  if (threadIdx.x == 0) {
+    out[0] = a;
+    out[1] = b;
+  }
 }
 
 // The ghost-fill gather: one thread per ghost cell of any block.
@@ -360,13 +424,14 @@ struct kh_mesh {
   int nb, ndim, lmax;
   int N0[3];  // level-0 grid
   std::vector<MBlock> hb;
-  std::vector<unsigned> pre_face[3], pre_zone, pre_ct, pre_alloc, pre_all;
+  std::vector<unsigned> pre_face[3], pre_zone, pre_ct, pre_alloc, pre_all, pre_corner;
+  long long corners;   // divB corners (adjacent cells all interior to one block)
   long long cells;     // sum of allocation planes
   long long gcells;    // sum of (j, i) planes
   long long zones;     // interior zones
   cudaStream_t stream;
   MBlock* dblk;
-  unsigned* dpre[7];   // face1..3, zone, ct, alloc cells (km_to_f32), all-cells (p2c)
+  unsigned* dpre[8];   // face1..3, zone, ct, alloc cells (km_to_f32), all-cells (p2c), divB corners
   GhostOp* dops;
   long long nops;
   ProlongNb* dnbs;
@@ -384,7 +449,7 @@ struct kh_mesh {
   int8_t* pflag;
   double* partial;
   int npartial;
-  double* dscalar;  // [0] dt out, [3] dt in
+  double* dscalar;  // [0] dt out, [1..2] divB max and sum, [3] dt in
   unsigned long long* counters;
   long long launches;
   int graph_on;
@@ -440,6 +505,8 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
   x->stream = 0;
   Scheme& S = x->S;
   S.gam = gamma;
+  S.igam = 1.0 / gamma;
+  S.gfac = (gamma - 1.0) / gamma;
   S.cfl = c->cfl;
   S.recon = c->recon;
   for (int q = 0; q < 6; ++q) S.bc[q] = c->bc[q];
@@ -668,6 +735,7 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
   x->pre_ct.assign(1, 0u);
   x->pre_alloc.assign(1, 0u);
   x->pre_all.assign(1, 0u);
+  x->pre_corner.assign(1, 0u);
   for (int b = 0; b < nblocks; ++b) {
     const MBlock& m = x->hb[b];
     const Layout& L = m.L;
@@ -680,7 +748,10 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
                         (unsigned)((L.e[0] - L.s[0] + 1) * (L.e[1] - L.s[1] + 1) * (L.ndim == 3 ? L.e[2] - L.s[2] + 1 : 1)));
     x->pre_alloc.push_back(x->pre_alloc.back() + (unsigned)L.plane);
     x->pre_all.push_back(x->pre_all.back() + (unsigned)(L.N1 * L.N2 * L.N3));
+    x->pre_corner.push_back(x->pre_corner.back() +
+                            (unsigned)((L.n1 - 1) * (L.n2 - 1) * (L.ndim == 3 ? L.n3 - 1 : 1)));
   }
+  x->corners = x->pre_corner.back();
 
   // ---- device buffers ----
   int rc = KH_OK;
@@ -690,12 +761,12 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
   const size_t pl = (size_t)cells * sizeof(double), plf = (size_t)cells * sizeof(float);
   const size_t gp = (size_t)gcells * sizeof(double), gpf = (size_t)gcells * sizeof(float);
   KM_ALLOC(x->dblk, sizeof(MBlock) * nblocks);
-  for (int q = 0; q < 7; ++q) KM_ALLOC(x->dpre[q], sizeof(unsigned) * (nblocks + 1));
+  for (int q = 0; q < 8; ++q) KM_ALLOC(x->dpre[q], sizeof(unsigned) * (nblocks + 1));
   KM_ALLOC(x->dops, sizeof(GhostOp) * std::max<long long>(x->nops, 1));
   KM_ALLOC(x->dnbs, sizeof(ProlongNb) * std::max<long long>(x->nnbs, 1));
   KM_ALLOC(x->geo, 3 * NGEO * gp);
   KM_ALLOC(x->conn, NCONN * gp);
-  KM_ALLOC(x->flo, 2 * gp);
+  KM_ALLOC(x->flo, 3 * gp);
   KM_ALLOC(x->pstar, NV * pl);
   KM_ALLOC(x->pflag, (size_t)cells);
   if (!mixed) {
@@ -724,14 +795,14 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
     }
   }
   x->npartial = 152 * 4;
-  KM_ALLOC(x->partial, sizeof(double) * x->npartial);
+  KM_ALLOC(x->partial, sizeof(double) * 2 * x->npartial);  // (max, sum) pairs for divB
   KM_ALLOC(x->dscalar, 4 * sizeof(double));
   KM_ALLOC(x->counters, NCNT * sizeof(unsigned long long));
 #undef KM_ALLOC
   if (rc == KH_OK) rc = cuda_rc(cudaMemcpy(x->dblk, x->hb.data(), sizeof(MBlock) * nblocks, cudaMemcpyHostToDevice));
-  const std::vector<unsigned>* pres[7] = {&x->pre_face[0], &x->pre_face[1], &x->pre_face[2], &x->pre_zone,
-                                          &x->pre_ct, &x->pre_alloc, &x->pre_all};
-  for (int q = 0; q < 7 && rc == KH_OK; ++q)
+  const std::vector<unsigned>* pres[8] = {&x->pre_face[0], &x->pre_face[1], &x->pre_face[2], &x->pre_zone,
+                                          &x->pre_ct,      &x->pre_alloc,   &x->pre_all,     &x->pre_corner};
+  for (int q = 0; q < 8 && rc == KH_OK; ++q)
     rc = cuda_rc(cudaMemcpy(x->dpre[q], pres[q]->data(), sizeof(unsigned) * (nblocks + 1), cudaMemcpyHostToDevice));
   if (rc == KH_OK && x->nops)
     rc = cuda_rc(cudaMemcpy(x->dops, ops.data(), sizeof(GhostOp) * x->nops, cudaMemcpyHostToDevice));
@@ -755,7 +826,7 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
     const double x1o = c->x1min + m.i0 * m.L.dx[0];
     const double x2o = c->x2min + m.j0 * m.L.dx[1];
     x->launches += launch_geometry(x->cp, x1o, x2o, S.fl, m.L, x->geo + 3LL * NGEO * m.goff,
-                                   x->conn + (long long)NCONN * m.goff, x->flo + 2 * m.goff, 0);
+                                   x->conn + (long long)NCONN * m.goff, x->flo + 3 * m.goff, 0);
     rc = cuda_rc(cudaGetLastError());
   }
   if (rc == KH_OK && mixed) {
@@ -855,16 +926,15 @@ int issue_mesh_step(kh_mesh* x, double* U, double* P, double* B) {
     km_to_f32<<<nblk(x->pre_alloc.back(), 256), 256, 0, s>>>(x->dblk, x->dpre[5], x->nb, Pn, Pnf);
     ++n;
     n += flux_pass<float, float>(x, Pnf, x->Ff, x->ctopf, x->emff);
-    km_update_mixed<double><<<gz, MTPB, 0, s>>>(x->dblk, x->dpre[3], x->nb, U, Pn, none64, Psf, nullptr, x->Ff[0],
-                                                x->Ff[1], x->Ff[2], GA, x->S, x->dscalar + 3, 0.5, x->pflag,
-                                                x->counters);
+    km_update_mixed<<<gz, MTPB, 0, s>>>(x->dblk, x->dpre[3], x->nb, U, Pnf, none64, Psf, nullptr, x->Ff[0],
+                                        x->Ff[1], x->Ff[2], GA, x->S, x->dscalar + 3, 0.5, x->pflag, x->counters);
     km_fixup<float><<<gz, MTPB, 0, s>>>(x->dblk, x->dpre[3], x->nb, Psf, nullptr, x->pflag, GA, x->S, x->counters);
     n += 2;
     // stage 2: FP32 P* -> FP64 P^{n+1}, U^{n+1}
     n += fill_ghosts(x, Psf);
     n += flux_pass<float, float>(x, Psf, x->Ff, x->ctopf, x->emff);
-    km_update_mixed<float><<<gz, MTPB, 0, s>>>(x->dblk, x->dpre[3], x->nb, U, Psf, Pn, none32, U, x->Ff[0], x->Ff[1],
-                                               x->Ff[2], GA, x->S, x->dscalar + 3, 1.0, x->pflag, x->counters);
+    km_update_mixed<<<gz, MTPB, 0, s>>>(x->dblk, x->dpre[3], x->nb, U, Psf, Pn, none32, U, x->Ff[0], x->Ff[1],
+                                        x->Ff[2], GA, x->S, x->dscalar + 3, 1.0, x->pflag, x->counters);
     km_fixup<double><<<gz, MTPB, 0, s>>>(x->dblk, x->dpre[3], x->nb, Pn, U, x->pflag, GA, x->S, x->counters);
     n += 2;
     n += cfl_pass<float>(x, x->ctopf);
@@ -953,6 +1023,22 @@ int kh_mesh_cfl_dt(kh_mesh* x, const double* P, const double* B, double* dt_cfl)
   return isfinite(*dt_cfl) ? KH_OK : KH_ENAN;
 }
 
+int kh_mesh_divb(kh_mesh* x, const double* B, double* max_abs, double* l1) {
+  if (!x || !B) return KH_EINVAL;
+  cudaStream_t s = x->stream;
+  km_divb<<<x->npartial, RED_THREADS, 0, s>>>(x->dblk, x->dpre[7], x->nb, B, x->geo, x->partial);
+  km_max_sum_finish<<<1, RED_THREADS, 0, s>>>(x->partial, x->npartial, x->dscalar + 1);
+  x->launches += 2;
+  int rc = cuda_rc(cudaGetLastError());
+  double h[2];
+  if (rc == KH_OK) rc = cuda_rc(cudaMemcpyAsync(h, x->dscalar + 1, sizeof(h), cudaMemcpyDeviceToHost, s));
+  if (rc == KH_OK) rc = cuda_rc(cudaStreamSynchronize(s));
+  if (rc != KH_OK) return rc;
+  if (max_abs) *max_abs = h[0];
+  if (l1) *l1 = x->corners > 0 ? h[1] / (double)x->corners : 0.0;
+  return KH_OK;
+}
+
 int kh_mesh_get_stats(kh_mesh* x, kh_stats* out) {
   if (!x || !out) return KH_EINVAL;
   unsigned long long h[NCNT];
@@ -1037,7 +1123,7 @@ int kh_mesh_destroy(kh_mesh* x) {
                   x->ctopf[0], x->ctopf[1], x->ctopf[2], x->emff[0], x->emff[1], x->emff[2]};
   for (void* p : ptrs)
     if (p) cudaFree(p);
-  for (int q = 0; q < 7; ++q)
+  for (int q = 0; q < 8; ++q)
     if (x->dpre[q]) cudaFree(x->dpre[q]);
   delete x;
   return KH_OK;

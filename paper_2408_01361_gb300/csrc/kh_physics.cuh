@@ -16,6 +16,33 @@ namespace kh {
 
 enum { V_RHO = 0, V_U = 1, V_U1 = 2, V_U2 = 3, V_U3 = 4, V_B1 = 5, V_B2 = 6, V_B3 = 7, NV = 8 };
 
+// 1/sqrt(x) (CUDA's rsqrt on the device; it gives sqrt(x) = x rsqrt(x) and its
+// reciprocal from one operation).
+KH_HD double krsqrt(double x) {
+#ifdef __CUDA_ARCH__
+  return rsqrt(x);
+#else
+  return 1.0 / sqrt(x);
+#endif
+}
+KH_HD float krsqrt(float x) {
+#ifdef __CUDA_ARCH__
+  return rsqrtf(x);
+#else
+  return 1.0f / sqrtf(x);
+#endif
+}
+// a / b: IEEE division in FP64; in FP32 (the mixed path's stencil physics)
+// CUDA's fast division, for divisors of modest magnitude (|b| < 2^126).
+KH_HD double kdiv(double a, double b) { return a / b; }
+KH_HD float kdiv(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fdividef(a, b);
+#else
+  return a / b;
+#endif
+}
+
 // Metric at one point: full 4x4 covariant and contravariant, sqrt(-g), lapse.
 template <class R> struct Met {
   R gcov[4][4];
@@ -35,9 +62,11 @@ template <class R> KH_HD void fluid_state(const R* P, const Met<R>& m, FState<R>
   const R v1 = P[V_U1], v2 = P[V_U2], v3 = P[V_U3];
   const R q = m.gcov[1][1] * v1 * v1 + m.gcov[2][2] * v2 * v2 + m.gcov[3][3] * v3 * v3 +
               R(2) * (m.gcov[1][2] * v1 * v2 + m.gcov[1][3] * v1 * v3 + m.gcov[2][3] * v2 * v3);
-  const R gam = sqrt(R(1) + q);
+  const R opq = R(1) + q;
+  const R rg = krsqrt(opq);  // 1 / gamma
+  const R gam = opq * rg;
   const R ga = gam * m.alpha;
-  s.ucon[0] = gam / m.alpha;
+  s.ucon[0] = kdiv(gam, m.alpha);
   s.ucon[1] = v1 - ga * m.gcon[0][1];
   s.ucon[2] = v2 - ga * m.gcon[0][2];
   s.ucon[3] = v3 - ga * m.gcon[0][3];
@@ -47,7 +76,7 @@ template <class R> KH_HD void fluid_state(const R* P, const Met<R>& m, FState<R>
                  m.gcov[mu][3] * s.ucon[3];
   const R bt = P[V_B1] * s.ucov[1] + P[V_B2] * s.ucov[2] + P[V_B3] * s.ucov[3];
   s.bcon[0] = bt;
-  const R iut = R(1) / s.ucon[0];
+  const R iut = m.alpha * rg;  // 1 / u^t
   s.bcon[1] = (P[V_B1] + bt * s.ucon[1]) * iut;
   s.bcon[2] = (P[V_B2] + bt * s.ucon[2]) * iut;
   s.bcon[3] = (P[V_B3] + bt * s.ucon[3]) * iut;
@@ -115,7 +144,7 @@ template <class R>
 KH_HD void signal_speeds(const R* P, const FState<R>& s, const Met<R>& m, R gam, int d, R& cmax, R& cmin) {
   const R p = (gam - R(1)) * P[V_U];
   const R w = P[V_RHO] + P[V_U] + p;
-  R cms2 = (gam * p + s.bsq) / (w + s.bsq);
+  R cms2 = kdiv(gam * p + s.bsq, w + s.bsq);
   cms2 = cms2 < R(0) ? R(0) : (cms2 > R(1) ? R(1) : cms2);
   const R Au = s.ucon[d], Bu = s.ucon[0];
   const R A = Bu * Bu - (m.gcon[0][0] + Bu * Bu) * cms2;
@@ -124,7 +153,7 @@ KH_HD void signal_speeds(const R* P, const FState<R>& s, const Met<R>& m, R gam,
   R disc = Bq * Bq - R(4) * A * C;
   disc = disc < R(0) ? R(0) : disc;
   const R sd = sqrt(disc);
-  const R i2a = R(1) / (R(2) * A);
+  const R i2a = kdiv(R(1), R(2) * A);
   const R vp = (Bq + sd) * i2a;
   const R vm = (Bq - sd) * i2a;
   cmax = vp > vm ? vp : vm;
@@ -186,12 +215,17 @@ KH_HD float weno5_plus(float a, float b, float c, float d, float e) {
   const float b0 = k * t0 * t0 + 0.25f * u0 * u0;
   const float b1 = k * t1 * t1 + 0.25f * u1 * u1;
   const float b2 = k * t2 * t2 + 0.25f * u2 * u2;
+#ifdef __CUDA_ARCH__
+  const float in = __frcp_rn(b0 + b1 + b2 + 1e-37f);  // any magnitude
+#else
   const float in = 1.0f / (b0 + b1 + b2 + 1e-37f);
+#endif
   const float s0 = b0 * in + 1e-12f, s1 = b1 * in + 1e-12f, s2 = b2 * in + 1e-12f;
   const float sm = fminf(s0, fminf(s1, s2));
-  const float r0 = sm / s0, r1 = sm / s1, r2 = sm / s2;
+  // s_k in [1e-12, 1 + 3e-12] and the weights' sum in [1/16, 1]: fast divisions
+  const float r0 = kdiv(sm, s0), r1 = kdiv(sm, s1), r2 = kdiv(sm, s2);
   const float w0 = 0.0625f * r0 * r0, w1 = 0.625f * r1 * r1, w2 = 0.3125f * r2 * r2;
-  return (w0 * p0 + w1 * p1 + w2 * p2) / (w0 + w1 + w2);
+  return kdiv(w0 * p0 + w1 * p1 + w2 * p2, w0 + w1 + w2);
 }
 
 // ---------------------------------------------------------------------------
@@ -210,8 +244,8 @@ struct C2POpts {
   double tol;
 };
 
-KH_HD int noble2d(const double* U, const Met<double>& m, double gam, const C2POpts& o, double* P) {
-  const double ig = 1.0 / m.gdet;
+KH_HD int noble2d(const double* U, const Met<double>& m, double ig, double gam, double igam, double gf,
+                  const C2POpts& o, double* P) {
   const double a = m.alpha;
   const double D = a * U[V_RHO] * ig;
   const double Qc[4] = {a * (U[V_U] - U[V_RHO]) * ig, a * U[V_U1] * ig, a * U[V_U2] * ig, a * U[V_U3] * ig};
@@ -231,7 +265,6 @@ KH_HD int noble2d(const double* U, const Met<double>& m, double gam, const C2POp
                      2.0 * (m.gcov[1][2] * Bc1 * Bc2 + m.gcov[1][3] * Bc1 * Bc3 + m.gcov[2][3] * Bc2 * Bc3);
   const double QdB = Qc[1] * Bc1 + Qc[2] * Bc2 + Qc[3] * Bc3;
   const double QdB2 = QdB * QdB;
-  const double gf = (gam - 1.0) / gam;
 
   // initial guess from the stage-input primitives at this metric
   double W, vsq;
@@ -252,29 +285,30 @@ KH_HD int noble2d(const double* U, const Met<double>& m, double gam, const C2POp
   double err = 1.0;
   for (int it = 0; it < o.max_iter; ++it) {
     const double g2i = 1.0 - vsq;
-    const double sg = sqrt(g2i);
+    const double rs = krsqrt(g2i);  // gamma
+    const double sg = g2i * rs;     // 1 / gamma
     const double p = gf * (W * g2i - D * sg);
     const double BW = Bsq + W;
-    const double W2 = W * W;
-    const double iW2 = 1.0 / W2;
+    const double iW = 1.0 / W;
+    const double iW2 = iW * iW, iW3 = iW2 * iW;
     const double f1 = Qtsq - vsq * BW * BW + QdB2 * (Bsq + 2.0 * W) * iW2;
     const double f2 = Qdn + W - p + 0.5 * Bsq * (1.0 + vsq) - 0.5 * QdB2 * iW2;
     const double dpdW = gf * g2i;
-    const double dpdv = gf * (-W + 0.5 * D / sg);
-    const double j11 = -2.0 * vsq * BW - 2.0 * QdB2 * BW * iW2 / W;
+    const double dpdv = gf * (-W + 0.5 * D * rs);
+    const double j11 = -2.0 * vsq * BW - 2.0 * QdB2 * BW * iW3;
     const double j12 = -BW * BW;
-    const double j21 = 1.0 - dpdW + QdB2 * iW2 / W;
+    const double j21 = 1.0 - dpdW + QdB2 * iW3;
     const double j22 = 0.5 * Bsq - dpdv;
-    const double det = j11 * j22 - j12 * j21;
-    const double dW = -(j22 * f1 - j12 * f2) / det;
-    const double dv = -(-j21 * f1 + j11 * f2) / det;
+    const double idet = 1.0 / (j11 * j22 - j12 * j21);
+    const double dW = -(j22 * f1 - j12 * f2) * idet;
+    const double dv = -(-j21 * f1 + j11 * f2) * idet;
     double Wn = W + dW;
     double vn = vsq + dv;
     // keep the iterate admissible
     if (!(Wn > 0.0)) Wn = 0.5 * W;
     if (vn < 0.0) vn = 0.0;
     if (vn > vmax) vn = vmax;
-    err = fabs(Wn - W) / Wn + fabs(vn - vsq);
+    err = fabs(Wn - W) * iW + fabs(vn - vsq);  // step relative to the previous iterate
     W = Wn;
     vsq = vn;
     if (!isfinite(W) || !isfinite(vsq)) return 1;
@@ -286,15 +320,17 @@ KH_HD int noble2d(const double* U, const Met<double>& m, double gam, const C2POp
   if (!conv && !(err < 1e-9)) return 1;
   if (!(W > 0.0)) return 3;
   if (!(vsq < 1.0) || vsq < 0.0) return 2;
-  const double gamma = 1.0 / sqrt(1.0 - vsq);
-  const double rho = D / gamma;
-  const double uint = (W * (1.0 - vsq) - rho) / gam;
+  const double gamma = krsqrt(1.0 - vsq);
+  const double rho = D * ((1.0 - vsq) * gamma);
+  const double uint = (W * (1.0 - vsq) - rho) * igam;
   if (!(rho > 0.0)) return 4;
   if (!(uint >= 0.0)) return 5;
   P[V_RHO] = rho;
   P[V_U] = uint;
-  const double f = gamma / (W + Bsq);
-  const double iW = 1.0 / W;
+  const double BW = W + Bsq;
+  const double inv = 1.0 / (W * BW);  // one division for 1/W and gamma/(W + B^2)
+  const double f = gamma * W * inv;
+  const double iW = BW * inv;
   P[V_U1] = f * (Qu[1] + nu[1] * Qdn + QdB * Bc1 * iW);
   P[V_U2] = f * (Qu[2] + nu[2] * Qdn + QdB * Bc2 * iW);
   P[V_U3] = f * (Qu[3] + nu[3] * Qdn + QdB * Bc3 * iW);
@@ -329,9 +365,10 @@ KH_HD int apply_floors(const FloorParams& f, const Met<double>& m, double rho_ge
   const double v1 = P[V_U1], v2 = P[V_U2], v3 = P[V_U3];
   const double q = m.gcov[1][1] * v1 * v1 + m.gcov[2][2] * v2 * v2 + m.gcov[3][3] * v3 * v3 +
                    2.0 * (m.gcov[1][2] * v1 * v2 + m.gcov[1][3] * v1 * v3 + m.gcov[2][3] * v2 * v3);
-  const double gamma = sqrt(1.0 + q);
-  if (gamma > f.gamma_max) {
-    const double sc = sqrt((f.gamma_max * f.gamma_max - 1.0) / (gamma * gamma - 1.0));
+  // gamma^2 = 1 + q: compare squares, take a root only for the rare zone over the ceiling
+  const double g2max = f.gamma_max * f.gamma_max;
+  if (1.0 + q > g2max) {
+    const double sc = sqrt((g2max - 1.0) / q);
     P[V_U1] *= sc;
     P[V_U2] *= sc;
     P[V_U3] *= sc;
@@ -345,16 +382,19 @@ KH_HD int apply_floors(const FloorParams& f, const Met<double>& m, double rho_ge
 // iterations first run in FP32 on the problem scaled by a power of two
 // S ~ W (exact in either precision: every term of f1 scales as S^2, of f2 as
 // S), then finished in FP64. The FP64 phase stops once a step changes
-// |dW/W| + |dv^2| by less than 1e-6, i.e. the iterate it produced lies in
-// Newton's quadratic regime (its error ~ that step squared). Invariants D,
-// Q.n, Q~^2, B^2, (Q.B)^2 are formed in FP64 exactly as in noble2d.
+// |dW/W| + |dv^2| by less than a threshold (1e-5 after a converged FP32
+// phase, else 1e-6), i.e. the iterate it produced lies in Newton's quadratic
+// regime (its error ~ that step squared). Invariants D, Q.n, Q~^2, B^2,
+// (Q.B)^2 are formed in FP64 as in noble2d, from the cached 1/sqrt(-g). The
+// initial guess (W, v^2) comes from the FP32 stage input.
 // ---------------------------------------------------------------------------
 template <class R>
 KH_HD bool newton_wv(R D, R Qdn, R Qtsq, R Bsq, R QdB2, R gf, int max_iter, R stop, R& W, R& vsq, R& err) {
   const R vmax = R(1) - R(sizeof(R) == 4 ? 1e-7 : 1e-16);
   for (int it = 0; it < max_iter; ++it) {
     const R g2i = R(1) - vsq;
-    const R sg = sqrt(g2i);
+    const R rs = krsqrt(g2i);  // gamma
+    const R sg = g2i * rs;     // 1 / gamma
     const R p = gf * (W * g2i - D * sg);
     const R BW = Bsq + W;
     const R iW = R(1) / W;
@@ -362,7 +402,7 @@ KH_HD bool newton_wv(R D, R Qdn, R Qtsq, R Bsq, R QdB2, R gf, int max_iter, R st
     const R f1 = Qtsq - vsq * BW * BW + QdB2 * (Bsq + R(2) * W) * iW2;
     const R f2 = Qdn + W - p + R(0.5) * Bsq * (R(1) + vsq) - R(0.5) * QdB2 * iW2;
     const R dpdW = gf * g2i;
-    const R dpdv = gf * (-W + R(0.5) * D / sg);
+    const R dpdv = gf * (-W + R(0.5) * D * rs);
     const R j11 = -R(2) * vsq * BW - R(2) * QdB2 * BW * iW2 * iW;
     const R j12 = -BW * BW;
     const R j21 = R(1) - dpdW + QdB2 * iW2 * iW;
@@ -373,7 +413,7 @@ KH_HD bool newton_wv(R D, R Qdn, R Qtsq, R Bsq, R QdB2, R gf, int max_iter, R st
     if (!(Wn > R(0))) Wn = R(0.5) * W;
     if (vn < R(0)) vn = R(0);
     if (vn > vmax) vn = vmax;
-    err = fabs(Wn - W) / Wn + fabs(vn - vsq);
+    err = fabs(Wn - W) * iW + fabs(vn - vsq);  // step relative to the previous iterate
     W = Wn;
     vsq = vn;
     if (!isfinite(W) || !isfinite(vsq)) return false;
@@ -382,11 +422,12 @@ KH_HD bool newton_wv(R D, R Qdn, R Qtsq, R Bsq, R QdB2, R gf, int max_iter, R st
   return false;
 }
 
-KH_HD int noble2d_mixed(const double* U, const Met<double>& m, double gam, const C2POpts& o, double* P) {
-  const double ig = 1.0 / m.gdet;
+KH_HD int noble2d_mixed(const double* U, const Met<double>& m, double ig, double gam, double igam, double gf,
+                        const C2POpts& o, float W0, float vsq0, double* P) {
   const double a = m.alpha;
-  const double D = a * U[V_RHO] * ig;
-  const double Qc[4] = {a * (U[V_U] - U[V_RHO]) * ig, a * U[V_U1] * ig, a * U[V_U2] * ig, a * U[V_U3] * ig};
+  const double aig = a * ig;
+  const double D = aig * U[V_RHO];
+  const double Qc[4] = {aig * (U[V_U] - U[V_RHO]), aig * U[V_U1], aig * U[V_U2], aig * U[V_U3]};
   double Qu[4];
 #pragma unroll
   for (int mu = 0; mu < 4; ++mu)
@@ -395,54 +436,50 @@ KH_HD int noble2d_mixed(const double* U, const Met<double>& m, double gam, const
   const double Qdn = Qc[0] * nu[0] + Qc[1] * nu[1] + Qc[2] * nu[2] + Qc[3] * nu[3];
   const double Qsq = Qc[0] * Qu[0] + Qc[1] * Qu[1] + Qc[2] * Qu[2] + Qc[3] * Qu[3];
   const double Qtsq = fmax(Qsq + Qdn * Qdn, 0.0);
-  const double Bc1 = a * U[V_B1] * ig, Bc2 = a * U[V_B2] * ig, Bc3 = a * U[V_B3] * ig;
+  const double Bc1 = aig * U[V_B1], Bc2 = aig * U[V_B2], Bc3 = aig * U[V_B3];
   const double Bsq = m.gcov[1][1] * Bc1 * Bc1 + m.gcov[2][2] * Bc2 * Bc2 + m.gcov[3][3] * Bc3 * Bc3 +
                      2.0 * (m.gcov[1][2] * Bc1 * Bc2 + m.gcov[1][3] * Bc1 * Bc3 + m.gcov[2][3] * Bc2 * Bc3);
   const double QdB = Qc[1] * Bc1 + Qc[2] * Bc2 + Qc[3] * Bc3;
   const double QdB2 = QdB * QdB;
-  const double gf = (gam - 1.0) / gam;
 
-  double W, vsq;
-  {
-    const double v1 = P[V_U1], v2 = P[V_U2], v3 = P[V_U3];
-    const double q = m.gcov[1][1] * v1 * v1 + m.gcov[2][2] * v2 * v2 + m.gcov[3][3] * v3 * v3 +
-                     2.0 * (m.gcov[1][2] * v1 * v2 + m.gcov[1][3] * v1 * v3 + m.gcov[2][3] * v2 * v3);
-    const double g2 = 1.0 + q;
-    W = (P[V_RHO] + gam * P[V_U]) * g2;
-    vsq = q / g2;
-  }
+  double W = (double)W0, vsq = (double)vsq0;
   if (!(W > 0.0) || !isfinite(W)) W = fabs(Qdn) + 1e-300;
   if (!(vsq >= 0.0)) vsq = 0.0;
   if (vsq > 1.0 - 1e-16) vsq = 1.0 - 1e-16;
 
   // FP32 phase on the problem scaled by S = 2^e ~ W
+  bool ok32 = false;
   {
     int e = 0;
     frexp(W, &e);
     const double S = ldexp(1.0, e), iS = ldexp(1.0, -e);
     float Wf = (float)(W * iS), vf = (float)vsq, ef = 1.0f;
-    const bool ok = newton_wv<float>((float)(D * iS), (float)(Qdn * iS), (float)(Qtsq * iS * iS), (float)(Bsq * iS),
-                                     (float)(QdB2 * iS * iS * iS), (float)gf, 12, 3e-6f, Wf, vf, ef);
-    if (ok || (isfinite(Wf) && isfinite(vf) && Wf > 0.0f && ef < 1e-3f)) {
+    ok32 = newton_wv<float>((float)(D * iS), (float)(Qdn * iS), (float)(Qtsq * iS * iS), (float)(Bsq * iS),
+                            (float)(QdB2 * iS * iS * iS), (float)gf, 12, 3e-6f, Wf, vf, ef);
+    if (ok32 || (isfinite(Wf) && isfinite(vf) && Wf > 0.0f && ef < 1e-3f)) {
       W = (double)Wf * S;
       vsq = (double)vf;
     }
   }
-  // FP64 phase
+  // FP64 phase: after a converged FP32 phase one FP64 step is accepted when
+  // it moves the iterate by less than 1e-5 (the accepted iterate's error is
+  // then of the order of that step squared); otherwise iterate to 1e-6.
   double err = 1.0;
-  const bool conv = newton_wv<double>(D, Qdn, Qtsq, Bsq, QdB2, gf, o.max_iter, 1e-6, W, vsq, err);
+  const bool conv = newton_wv<double>(D, Qdn, Qtsq, Bsq, QdB2, gf, o.max_iter, ok32 ? 1e-5 : 1e-6, W, vsq, err);
   if (!conv && !(err < 1e-9)) return 1;
   if (!(W > 0.0)) return 3;
   if (!(vsq < 1.0) || vsq < 0.0) return 2;
-  const double gamma = 1.0 / sqrt(1.0 - vsq);
-  const double rho = D / gamma;
-  const double uint = (W * (1.0 - vsq) - rho) / gam;
+  const double gamma = krsqrt(1.0 - vsq);
+  const double rho = D * ((1.0 - vsq) * gamma);
+  const double uint = (W * (1.0 - vsq) - rho) * igam;
   if (!(rho > 0.0)) return 4;
   if (!(uint >= 0.0)) return 5;
   P[V_RHO] = rho;
   P[V_U] = uint;
-  const double f = gamma / (W + Bsq);
-  const double iW = 1.0 / W;
+  const double BW = W + Bsq;
+  const double inv = 1.0 / (W * BW);  // one division for 1/W and gamma/(W + B^2)
+  const double f = gamma * W * inv;
+  const double iW = BW * inv;
   P[V_U1] = f * (Qu[1] + nu[1] * Qdn + QdB * Bc1 * iW);
   P[V_U2] = f * (Qu[2] + nu[2] * Qdn + QdB * Bc2 * iW);
   P[V_U3] = f * (Qu[3] + nu[3] * Qdn + QdB * Bc3 * iW);

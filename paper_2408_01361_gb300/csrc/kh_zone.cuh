@@ -237,15 +237,15 @@ __device__ __forceinline__ void update_zone(const double* U0, const CVars& Pin, 
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     const long long o = v * L.plane + c;
-    double div = (F1[o + 1] - F1[o]) / L.dx[0] + (F2[o + sj] - F2[o]) / L.dx[1];
-    if (L.ndim == 3) div += (F3[o + sk] - F3[o]) / L.dx[2];
+    double div = (F1[o + 1] - F1[o]) * L.idx[0] + (F2[o + sj] - F2[o]) * L.idx[1];
+    if (L.ndim == 3) div += (F3[o + sk] - F3[o]) * L.idx[2];
     U[v] = U0[o] + cdt * (-div + Sv[v]);
   }
   double Pn[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) Pn[v] = P[v];
-  const int flag = noble2d(U, m, S.gam, S.c2p, Pn);
-  const double ig = 1.0 / m.gdet;
+  const double ig = __ldg(G.flo + 2 * L.gplane + p);  // 1 / sqrt(-g)
+  const int flag = noble2d(U, m, ig, S.gam, S.igam, S.gfac, S.c2p, Pn);
   Pn[V_B1] = U[V_B1] * ig;
   Pn[V_B2] = U[V_B2] * ig;
   Pn[V_B3] = U[V_B3] * ig;
@@ -274,9 +274,10 @@ __device__ __forceinline__ void update_zone(const double* U0, const CVars& Pin, 
 // Mixed-precision update of one interior zone: the divergence of the FP32
 // fluxes and the FP32 source terms (FP32 metric and connection) give dU in
 // FP32; U = U0 + cdt dU is accumulated in FP64; the Noble-2D inversion and the
-// floors run in FP64 on the FP64 metric, the stage input serving as guess.
-template <class TIN>
-__device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT<TIN>& Pin, const Vars& Pout64,
+// floors run in FP64 on the FP64 metric. The stage input is read in FP32 only
+// (both stages' inputs exist as FP32 arrays): it gives the sources, the
+// inversion's initial guess, and the output of a zone whose inversion failed.
+__device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT<float>& Pin, const Vars& Pout64,
                                                   const VarsT<float>& Pout32, double* Uout, const float* F1,
                                                   const float* F2, const float* F3, const Layout& L, const DevGeom& G,
                                                   const GeomT<float>& Gf, const Scheme& S, double cdt, int8_t* pflag,
@@ -285,19 +286,22 @@ __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT
   const long long p = (long long)j * L.n1s + i;
   const long long sj = L.n1s, sk = (long long)L.n1s * L.n2s;
   float Pf[NV];
-  double Pn[NV];
 #pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    const TIN x = Pin.v[v][c];
-    Pf[v] = (float)x;
-    Pn[v] = (double)x;
-  }
+  for (int v = 0; v < NV; ++v) Pf[v] = Pin.v[v][c];
   float Sv[NV] = {0, 0, 0, 0, 0, 0, 0, 0};
+  const Met<float> mf = load_met(Gf, L.gplane, LOC_CENT, p);
+  source_terms(Pf, mf, Gf.conn, L.gplane, p, (float)S.gam, Sv);
+  // initial guess of the inversion from the FP32 input: W = (rho + gam u) gamma^2, v^2 = q / gamma^2
+  float W0, vsq0;
   {
-    const Met<float> mf = load_met(Gf, L.gplane, LOC_CENT, p);
-    source_terms(Pf, mf, Gf.conn, L.gplane, p, (float)S.gam, Sv);
+    const float v1 = Pf[V_U1], v2 = Pf[V_U2], v3 = Pf[V_U3];
+    const float q = mf.gcov[1][1] * v1 * v1 + mf.gcov[2][2] * v2 * v2 + mf.gcov[3][3] * v3 * v3 +
+                    2.0f * (mf.gcov[1][2] * v1 * v2 + mf.gcov[1][3] * v1 * v3 + mf.gcov[2][3] * v2 * v3);
+    const float g2 = 1.0f + q;
+    W0 = (Pf[V_RHO] + (float)S.gam * Pf[V_U]) * g2;
+    vsq0 = q / g2;
   }
-  const float i1 = (float)(1.0 / L.dx[0]), i2 = (float)(1.0 / L.dx[1]), i3 = (float)(1.0 / L.dx[2]);
+  const float i1 = (float)L.idx[0], i2 = (float)L.idx[1], i3 = (float)L.idx[2];
   double U[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
@@ -307,8 +311,13 @@ __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT
     U[v] = U0[o] + cdt * (double)(Sv[v] - div);
   }
   const Met<double> m = load_met(G, L.gplane, LOC_CENT, p);
-  const int flag = noble2d_mixed(U, m, S.gam, S.c2p, Pn);
-  const double ig = 1.0 / m.gdet;
+  const double ig = __ldg(G.flo + 2 * L.gplane + p);  // 1 / sqrt(-g)
+  double Pn[NV];
+  const int flag = noble2d_mixed(U, m, ig, S.gam, S.igam, S.gfac, S.c2p, W0, vsq0, Pn);
+  if (flag) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) Pn[v] = (double)Pf[v];
+  }
   Pn[V_B1] = U[V_B1] * ig;
   Pn[V_B2] = U[V_B2] * ig;
   Pn[V_B3] = U[V_B3] * ig;
@@ -316,7 +325,6 @@ __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT
   if (flag == 0) {
     // FP32 fluid state for the magnetisation floors (a threshold) and for the
     // conserved increment of a density/energy floor.
-    const Met<float> mf = load_met(Gf, L.gplane, LOC_CENT, p);
     float q[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) q[v] = (float)Pn[v];
@@ -341,14 +349,26 @@ __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT
         U[V_U3] += (double)(gd * ut * sf.ucov[3] * (drho + gm * du));
       }
     }
+    if (Pout32.v[0]) {
+      if (fmask) {
+        q[V_RHO] = (float)Pn[V_RHO];
+        q[V_U] = (float)Pn[V_U];
+        if (fmask & 4) {
+          q[V_U1] = (float)Pn[V_U1];
+          q[V_U2] = (float)Pn[V_U2];
+          q[V_U3] = (float)Pn[V_U3];
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Pout32.v[v][c] = q[v];
+    }
+  } else if (Pout32.v[0]) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Pout32.v[v][c] = v < 5 ? Pf[v] : (float)Pn[v];
   }
   if (Pout64.v[0]) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) Pout64.v[v][c] = Pn[v];
-  }
-  if (Pout32.v[0]) {
-#pragma unroll
-    for (int v = 0; v < NV; ++v) Pout32.v[v][c] = (float)Pn[v];
   }
   if (Uout) {
 #pragma unroll
@@ -418,5 +438,23 @@ __device__ __forceinline__ double cfl_inv_zone(const T* c1, const T* c2, const T
   return inv;
 }
 
+// Corner divergence of sqrt(-g) B at the lower corner of cell (i, j, k): per
+// direction d, the average of sqrt(-g) B^d over the 2 (2-D) or 4 (3-D) cells
+// above the corner minus that over the cells below, divided by dx_d. gd is
+// the sqrt(-g) plane at cell centres.
+__device__ __forceinline__ double divb_corner(const double* B1, const double* B2, const double* B3, const Layout& L,
+                                              const double* gd, int i, int j, int k) {
+  auto gB = [&](const double* B, int kk, int jj, int ii) { return gd[(long long)jj * L.n1s + ii] * B[L.at(kk, jj, ii)]; };
+  if (L.ndim == 2)
+    return (gB(B1, k, j, i) + gB(B1, k, j - 1, i) - gB(B1, k, j, i - 1) - gB(B1, k, j - 1, i - 1)) / (2.0 * L.dx[0]) +
+           (gB(B2, k, j, i) + gB(B2, k, j, i - 1) - gB(B2, k, j - 1, i) - gB(B2, k, j - 1, i - 1)) / (2.0 * L.dx[1]);
+  const double a1 = gB(B1, k, j, i) + gB(B1, k, j - 1, i) + gB(B1, k - 1, j, i) + gB(B1, k - 1, j - 1, i);
+  const double b1 = gB(B1, k, j, i - 1) + gB(B1, k, j - 1, i - 1) + gB(B1, k - 1, j, i - 1) + gB(B1, k - 1, j - 1, i - 1);
+  const double a2 = gB(B2, k, j, i) + gB(B2, k, j, i - 1) + gB(B2, k - 1, j, i) + gB(B2, k - 1, j, i - 1);
+  const double b2 = gB(B2, k, j - 1, i) + gB(B2, k, j - 1, i - 1) + gB(B2, k - 1, j - 1, i) + gB(B2, k - 1, j - 1, i - 1);
+  const double a3 = gB(B3, k, j, i) + gB(B3, k, j, i - 1) + gB(B3, k, j - 1, i) + gB(B3, k, j - 1, i - 1);
+  const double b3 = gB(B3, k - 1, j, i) + gB(B3, k - 1, j, i - 1) + gB(B3, k - 1, j - 1, i) + gB(B3, k - 1, j - 1, i - 1);
+  return (a1 - b1) / (4.0 * L.dx[0]) + (a2 - b2) / (4.0 * L.dx[1]) + (a3 - b3) / (4.0 * L.dx[2]);
+}
 
 }  // namespace kh

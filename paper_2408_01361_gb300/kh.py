@@ -100,6 +100,7 @@ def lib():
         L.kh_mesh_cfl_dt.argtypes = [vp, vp, vp, dp]
         L.kh_mesh_step.argtypes = [vp, vp, vp, vp, C.c_double, dp]
         L.kh_mesh_set_graph.argtypes = [vp, C.c_int]
+        L.kh_mesh_divb.argtypes = [vp, vp, dp, dp]
         L.kh_mesh_get_stats.argtypes = [vp, C.POINTER(Stats)]
         L.kh_mesh_destroy.argtypes = [vp]
         _lib = L
@@ -405,6 +406,11 @@ class Mesh:
             return d.value, rc
         _check(lib().kh_mesh_step(self._h, _ptr(U), _ptr(P), _ptr(B), float(dt), None), "kh_mesh_step")
         return None, None
+
+    def divb(self, B):
+        mx, l1 = C.c_double(), C.c_double()
+        _check(lib().kh_mesh_divb(self._h, _ptr(B), C.byref(mx), C.byref(l1)), "kh_mesh_divb")
+        return mx.value, l1.value
 
     def set_graph(self, enable: bool):
         _check(lib().kh_mesh_set_graph(self._h, 1 if enable else 0), "kh_mesh_set_graph")

@@ -206,3 +206,31 @@ def test_mesh_rejects_invalid_layouts(kh, bad):
         blocks = [blk(0, 0, 0, 0, 32, 6, 1), blk(0, 0, 18, 0, 32, 6, 1), blk(2, 0, 24, 0, 128, 48, 1)]
     with pytest.raises(kh.KHError):
         kh.Mesh(base, blocks)
+
+
+@pytest.mark.parametrize("which", ["torus2_weno5", "box_mc"])
+def test_mesh_divb_parity_and_invariance(kh, orc, which):
+    """Corner divB inside every block: equal to the oracle's per-block value
+    at the start, held by Flux-CT through steps (level interfaces excluded)."""
+    base, blocks, Ps = _case(which)
+    m = kh.Mesh(base, blocks)
+    P, B = m.to_device(Ps)
+    mg, lg = m.divb(B)
+    mx, tot, cnt, scale = 0.0, 0.0, 0, 0.0
+    for b, Pb in zip(blocks, Ps):
+        c = inputs.block_cfg(base, b)
+        mo, lo = orc.divb(c, Pb)
+        nc = (b["n1"] - 1) * (b["n2"] - 1) * (b["n3"] - 1 if base["n3"] > 1 else 1)
+        mx, tot, cnt = max(mx, mo), tot + lo * nc, cnt + nc
+        gdet = orc.geometry(c, 0)[2]
+        dxm = min((c["x1"][1] - c["x1"][0]) / c["n1"], (c["x2"][1] - c["x2"][0]) / c["n2"])
+        scale = max(scale, np.abs(gdet[None, None] * Pb[5:8]).max() / dxm)
+    assert abs(mg - mx) <= 1e-10 * mx + 1e-13 * scale
+    assert abs(lg - tot / cnt) <= 1e-10 * (tot / cnt) + 1e-13 * scale
+    U = m.empty(8)
+    m.prim_to_cons(P, B, U)
+    dt = 0.5 * m.cfl_dt(P, B)
+    for _ in range(3):
+        m.step(U, P, B, dt)
+    m2, _ = m.divb(B)
+    assert abs(m2 - mg) < 1e-12 * scale + 1e-12 * mg
