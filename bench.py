@@ -297,6 +297,7 @@ def measure_smr(args, dev, stream, precision):
     U = m.empty(8)
     m.prim_to_cons(P, B, U)
     dt = m.cfl_dt(P, B)
+    tuned = m.autotune(U, P, B, 0.5 * dt)
     m.set_graph(True)
     for _ in range(args.warmup):
         dt, _ = m.step(U, P, B, 0.5 * dt)
@@ -322,28 +323,47 @@ def measure_smr(args, dev, stream, precision):
         "precision": precision, "dtype": DTYPE[precision], "blocks": len(blocks), "block_shapes": dict(shapes),
         "zones": m.zones, "ghost_cells": m.ghost_cells, "value": m.zones * args.steps / (ms * 1e-3), "unit": UNIT,
         "ms_per_step": ms / args.steps, "graph": True, "gpu_launches": m.launches() - l0, "clocks": clocks,
-        "nfail_timed": nfail,
+        "nfail_timed": nfail, "launch_config": {"tpb_flux": tuned[0], "tpb_update": tuned[1]},
     }
     m.close()
     return out
 
 
 def roofline_of(prof, nz, precision):
+    """Roofline of the kernel group with the largest share of the profiled
+    step time: FP64-ALU bound (the update on both paths, the FP64 flux) with
+    the executed FP64 flops per zone; the FP32 flux of the mixed path beside
+    it against the FP32 peak."""
     hbm, hbm_kind, sm_max = peaks()
     groups = {k: v for k, v in prof.items() if v[1] > 0}
     top = max(groups, key=lambda k: groups[k][0])
-    top_ms, top_n = groups[top]
-    avg_ms = top_ms / top_n
     share = {k: round(v[0] / sum(x[0] for x in groups.values()), 4) for k, v in groups.items()}
-    fp64_peak = fp64_peak_tflops(sm_max)
-    flops_zone = FP64_FLOPS_PER_ZONE.get((precision, top))
-    achieved = (flops_zone * nz / (avg_ms * 1e-3) / 1e12) if flops_zone else None
-    roof = {
-        "bound": "alu", "kernel": top, "achieved": achieved, "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
-        "frac": (achieved / fp64_peak) if achieved else None, "traffic": TRAFFIC_PER_LAUNCH.get((precision, top)),
-        "peak_source": "FP64 from unit counts: 152 SMs x 4 flop/clk x max SM clock (a probe measured 1.20 TFLOP/s)",
-        "avg_launch_ms": avg_ms, "fp64_flops_per_zone": flops_zone,
-    }
+
+    def one(group):
+        ms, n = groups[group]
+        avg = ms / n
+        f64 = FP64_FLOPS_PER_ZONE.get((precision, group))
+        f32 = FP32_FLOPS_PER_ZONE.get((precision, group))
+        byt = DRAM_BYTES_PER_ZONE.get((precision, group))
+        if f64:
+            peak, flops, bound, unit = fp64_peak_tflops(sm_max), f64, "alu", "TFLOP/s"
+            src = "FP64 from unit counts: 152 SMs x 4 flop/clk x max SM clock (a probe measured 1.20 TFLOP/s)"
+        elif f32:
+            peak, flops, bound, unit = fp32_peak_tflops(sm_max), f32, "alu", "TFLOP/s"
+            src = "FP32 from unit counts: 152 SMs x 256 flop/clk x max SM clock (a probe measured 74.7 TFLOP/s)"
+        else:
+            return {"kernel": group, "avg_launch_ms": avg}
+        achieved = flops * nz / (avg * 1e-3) / 1e12
+        return {
+            "bound": bound, "kernel": group, "achieved": achieved, "peak": round(peak, 4), "unit": unit,
+            "frac": achieved / peak, "traffic": byt * nz if byt else None, "peak_source": src,
+            "avg_launch_ms": avg, "flops_per_zone": flops, "fp_type": "f64" if f64 else "f32",
+            "dram_gbs": (byt * nz / (avg * 1e-3) / 1e9) if byt else None, "hbm_peak_gbs": hbm,
+        }
+
+    roof = one(top)
+    others = [g for g in ("flux_x1", "flux_x2", "flux_x3", "update") if g in groups and g != top]
+    roof["others"] = [one(g) for g in others]
     return roof, share
 
 
@@ -428,13 +448,29 @@ def run_kh(args, world, rank, local):
     return 0
 
 
-# Executed FP64 floating-point operations per zone of a kernel group,
-# (precision, group) -> 2 DFMA + DADD + DMUL per zone from ncu instruction
-# counts on the torus (192x96x64 case), divided by the zones of a launch.
-FP64_FLOPS_PER_ZONE: dict = {}
-# (precision, group) -> dram read + write bytes per launch of the full
-# workload from one ncu capture (scaled by zones from the 192x96x64 case).
-TRAFFIC_PER_LAUNCH: dict = {}
+# Per-zone figures of each kernel group from one ncu capture of the same
+# kernels on the 192x96x64 torus (1 step, mixed and FP64; see profiles/):
+# executed floating-point operations per zone and per launch (a DFMA or FFMA
+# counts 2, DADD/DMUL/FADD/FMUL 1), and DRAM bytes (read + write) per zone
+# per launch. Launch totals at the bench size scale by the zone count.
+FP64_FLOPS_PER_ZONE: dict = {
+    ("mixed", "update"): 346.2,
+    ("fp64", "update"): 1000.5,
+    ("fp64", "flux_x1"): 2102.3, ("fp64", "flux_x2"): 2091.0, ("fp64", "flux_x3"): 2083.5,
+}
+FP32_FLOPS_PER_ZONE: dict = {
+    ("mixed", "flux_x1"): 1770.4, ("mixed", "flux_x2"): 1760.5, ("mixed", "flux_x3"): 1752.6,
+}
+DRAM_BYTES_PER_ZONE: dict = {
+    ("mixed", "update"): 282.6,  # mean of stage 1 (245.6) and stage 2 (319.5)
+    ("mixed", "flux_x1"): 42.4, ("mixed", "flux_x2"): 46.9, ("mixed", "flux_x3"): 48.4,
+    ("fp64", "update"): 419.0,  # stage 1
+    ("fp64", "flux_x1"): 118.1, ("fp64", "flux_x2"): 125.3, ("fp64", "flux_x3"): 127.7,
+}
+# FP32 peak from unit counts: 152 SMs x 128 lanes x 2 flop/clk x max SM clock
+# (a probe measured 74.7 TFLOP/s at 2070 MHz).
+def fp32_peak_tflops(sm_mhz: float) -> float:
+    return 152 * 256 * sm_mhz * 1e6 / 1e12
 
 
 def cpu_leg(cfg, P0, dt):

@@ -248,6 +248,16 @@ int kh_mesh_step(kh_mesh* mesh, double* U, double* P, double* B, double dt, doub
  * holds divB only inside blocks (level interfaces are not constrained). */
 int kh_mesh_divb(kh_mesh* mesh, const double* B, double* max_abs, double* l1);
 int kh_mesh_set_graph(kh_mesh* mesh, int enable);
+/* Threads per block of the face kernels and of the update kernel over all
+ * blocks (multiples of 32 in [32, 256]; KH_EINVAL otherwise), and the
+ * autotuner: times the pairs {64, 128, 256}^2 on scratch copies of (U, P, B)
+ * (allocated for the search and freed), keeps the fastest and caches it for
+ * the process per (block shapes with their counts, coordinates,
+ * reconstruction, precision). Results are bitwise independent of the choice. */
+int kh_mesh_set_launch(kh_mesh* mesh, int tpb_flux, int tpb_update);
+int kh_mesh_get_launch(const kh_mesh* mesh, int* tpb_flux, int* tpb_update);
+int kh_mesh_autotune(kh_mesh* mesh, const double* U, const double* P, const double* B, double dt, int* tpb_flux,
+                     int* tpb_update);
 int kh_mesh_get_stats(kh_mesh* mesh, kh_stats* out);
 int64_t kh_mesh_launch_count(const kh_mesh* mesh);
 int kh_mesh_destroy(kh_mesh* mesh);

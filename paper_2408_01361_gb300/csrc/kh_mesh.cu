@@ -21,7 +21,10 @@
 // Every source is an interior cell, so the fill has no ordering between
 // ghost cells.
 #include <algorithm>
+#include <map>
 #include <mutex>
+#include <string>
+#include <tuple>
 #include <vector>
 
 #include "kh_zone.cuh"
@@ -453,6 +456,7 @@ struct kh_mesh {
   unsigned long long* counters;
   long long launches;
   int graph_on;
+  int tpb_flux, tpb_update;  // threads per block of the face and update kernels
   cudaStream_t cap_stream;
   cudaGraphExec_t gexec;
   const void* gkey[3];
@@ -503,6 +507,7 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
   x->N0[1] = c->n2;
   x->N0[2] = c->n3;
   x->stream = 0;
+  x->tpb_flux = x->tpb_update = MTPB;
   Scheme& S = x->S;
   S.gam = gamma;
   S.igam = 1.0 / gamma;
@@ -864,14 +869,15 @@ int flux_pass(kh_mesh* x, const Arena<TIN>& P, R* const F[3], R* const ct[3], R*
   const GeoArena GA = garena(x);
   for (int d = 1; d <= x->ndim; ++d) {
     const unsigned tot = x->pre_face[d - 1].back();
-    const int g = nblk(tot, MTPB);
-#define KM_FLUX(DD)                                                                                              \
-  if (x->S.recon == KH_RECON_MC)                                                                                 \
-    km_flux<DD, KH_RECON_MC, TIN, R><<<g, MTPB, 0, x->stream>>>(x->dblk, x->dpre[DD - 1], x->nb, P, GA, x->S,    \
-                                                                F[DD - 1], ct[DD - 1]);                          \
-  else                                                                                                           \
-    km_flux<DD, KH_RECON_WENO5, TIN, R><<<g, MTPB, 0, x->stream>>>(x->dblk, x->dpre[DD - 1], x->nb, P, GA, x->S, \
-                                                                   F[DD - 1], ct[DD - 1]);
+    const int tpb = x->tpb_flux;
+    const int g = nblk(tot, tpb);
+#define KM_FLUX(DD)                                                                                             \
+  if (x->S.recon == KH_RECON_MC)                                                                                \
+    km_flux<DD, KH_RECON_MC, TIN, R><<<g, tpb, 0, x->stream>>>(x->dblk, x->dpre[DD - 1], x->nb, P, GA, x->S,    \
+                                                               F[DD - 1], ct[DD - 1]);                          \
+  else                                                                                                          \
+    km_flux<DD, KH_RECON_WENO5, TIN, R><<<g, tpb, 0, x->stream>>>(x->dblk, x->dpre[DD - 1], x->nb, P, GA, x->S, \
+                                                                  F[DD - 1], ct[DD - 1]);
     if (d == 1) { KM_FLUX(1) } else if (d == 2) { KM_FLUX(2) } else { KM_FLUX(3) }
 #undef KM_FLUX
     ++n;
@@ -898,6 +904,7 @@ int issue_mesh_step(kh_mesh* x, double* U, double* P, double* B) {
   const GeoArena GA = garena(x);
   const unsigned nz = x->pre_zone.back();
   const int gz = nblk(nz, MTPB);
+  const int tu = x->tpb_update, gu = nblk(nz, tu);
   const Arena<double> Pn = arena_pb(P, B);
   int n = 0;
   if (x->c.precision == KH_FP64) {
@@ -905,14 +912,14 @@ int issue_mesh_step(kh_mesh* x, double* U, double* P, double* B) {
     // stage 1: P^n -> P*
     n += fill_ghosts(x, Pn);
     n += flux_pass<double, double>(x, Pn, x->F, x->ctop, x->emf);
-    km_update<<<gz, MTPB, 0, s>>>(x->dblk, x->dpre[3], x->nb, U, Pn, Ps, nullptr, x->F[0], x->F[1], x->F[2], GA,
+    km_update<<<gu, tu, 0, s>>>(x->dblk, x->dpre[3], x->nb, U, Pn, Ps, nullptr, x->F[0], x->F[1], x->F[2], GA,
                                   x->S, x->dscalar + 3, 0.5, x->pflag, x->counters);
     km_fixup<double><<<gz, MTPB, 0, s>>>(x->dblk, x->dpre[3], x->nb, Ps, nullptr, x->pflag, GA, x->S, x->counters);
     n += 2;
     // stage 2: P* -> P^{n+1}, U^{n+1}
     n += fill_ghosts(x, Ps);
     n += flux_pass<double, double>(x, Ps, x->F, x->ctop, x->emf);
-    km_update<<<gz, MTPB, 0, s>>>(x->dblk, x->dpre[3], x->nb, U, Ps, Pn, U, x->F[0], x->F[1], x->F[2], GA, x->S,
+    km_update<<<gu, tu, 0, s>>>(x->dblk, x->dpre[3], x->nb, U, Ps, Pn, U, x->F[0], x->F[1], x->F[2], GA, x->S,
                                   x->dscalar + 3, 1.0, x->pflag, x->counters);
     km_fixup<double><<<gz, MTPB, 0, s>>>(x->dblk, x->dpre[3], x->nb, Pn, U, x->pflag, GA, x->S, x->counters);
     n += 2;
@@ -926,14 +933,14 @@ int issue_mesh_step(kh_mesh* x, double* U, double* P, double* B) {
     km_to_f32<<<nblk(x->pre_alloc.back(), 256), 256, 0, s>>>(x->dblk, x->dpre[5], x->nb, Pn, Pnf);
     ++n;
     n += flux_pass<float, float>(x, Pnf, x->Ff, x->ctopf, x->emff);
-    km_update_mixed<<<gz, MTPB, 0, s>>>(x->dblk, x->dpre[3], x->nb, U, Pnf, none64, Psf, nullptr, x->Ff[0],
+    km_update_mixed<<<gu, tu, 0, s>>>(x->dblk, x->dpre[3], x->nb, U, Pnf, none64, Psf, nullptr, x->Ff[0],
                                         x->Ff[1], x->Ff[2], GA, x->S, x->dscalar + 3, 0.5, x->pflag, x->counters);
     km_fixup<float><<<gz, MTPB, 0, s>>>(x->dblk, x->dpre[3], x->nb, Psf, nullptr, x->pflag, GA, x->S, x->counters);
     n += 2;
     // stage 2: FP32 P* -> FP64 P^{n+1}, U^{n+1}
     n += fill_ghosts(x, Psf);
     n += flux_pass<float, float>(x, Psf, x->Ff, x->ctopf, x->emff);
-    km_update_mixed<<<gz, MTPB, 0, s>>>(x->dblk, x->dpre[3], x->nb, U, Psf, Pn, none32, U, x->Ff[0], x->Ff[1],
+    km_update_mixed<<<gu, tu, 0, s>>>(x->dblk, x->dpre[3], x->nb, U, Psf, Pn, none32, U, x->Ff[0], x->Ff[1],
                                         x->Ff[2], GA, x->S, x->dscalar + 3, 1.0, x->pflag, x->counters);
     km_fixup<double><<<gz, MTPB, 0, s>>>(x->dblk, x->dpre[3], x->nb, Pn, U, x->pflag, GA, x->S, x->counters);
     n += 2;
@@ -1103,6 +1110,106 @@ int kh_mesh_step(kh_mesh* x, double* U, double* P, double* B, double dt, double*
   *dt_cfl = st.dt_cfl;
   if (!isfinite(st.dt_cfl)) return KH_ENAN;
   return (int)(st.nfail > 0x7fffffffLL ? 0x7fffffff : st.nfail);
+}
+
+int kh_mesh_set_launch(kh_mesh* x, int tpb_flux, int tpb_update) {
+  if (!x) return KH_EINVAL;
+  auto ok = [](int t) { return t >= 32 && t <= 256 && t % 32 == 0; };
+  if (!ok(tpb_flux) || !ok(tpb_update)) return KH_EINVAL;
+  x->tpb_flux = tpb_flux;
+  x->tpb_update = tpb_update;
+  drop_mesh_graph(x);
+  return KH_OK;
+}
+
+int kh_mesh_get_launch(const kh_mesh* x, int* tpb_flux, int* tpb_update) {
+  if (!x) return KH_EINVAL;
+  if (tpb_flux) *tpb_flux = x->tpb_flux;
+  if (tpb_update) *tpb_update = x->tpb_update;
+  return KH_OK;
+}
+
+int kh_mesh_autotune(kh_mesh* x, const double* U, const double* P, const double* B, double dt, int* tpb_flux,
+                     int* tpb_update) {
+  if (!x || !U || !P || !B || !(dt > 0.0)) return KH_EINVAL;
+  // process-wide cache keyed by the block shapes (with counts), coordinates,
+  // reconstruction and precision
+  static std::mutex lock;
+  static std::map<std::string, std::pair<int, int>> cache;
+  std::map<std::tuple<int, int, int, int>, int> shapes;
+  for (const MBlock& m : x->hb) ++shapes[std::make_tuple(m.level, m.L.n1, m.L.n2, m.L.n3)];
+  std::string key = std::to_string(x->c.kind) + "/" + std::to_string(x->c.recon) + "/" +
+                    std::to_string(x->c.precision);
+  for (const auto& kv : shapes)
+    key += "/" + std::to_string(std::get<1>(kv.first)) + "x" + std::to_string(std::get<2>(kv.first)) + "x" +
+           std::to_string(std::get<3>(kv.first)) + "L" + std::to_string(std::get<0>(kv.first)) + ":" +
+           std::to_string(kv.second);
+  {
+    std::lock_guard<std::mutex> g(lock);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      const int rc = kh_mesh_set_launch(x, it->second.first, it->second.second);
+      if (tpb_flux) *tpb_flux = x->tpb_flux;
+      if (tpb_update) *tpb_update = x->tpb_update;
+      return rc;
+    }
+  }
+  const size_t pl = (size_t)x->cells * sizeof(double);
+  double *Us = nullptr, *Ps = nullptr, *Bs = nullptr;
+  int rc = cuda_rc(cudaMalloc((void**)&Us, 8 * pl));
+  if (rc == KH_OK) rc = cuda_rc(cudaMalloc((void**)&Ps, 5 * pl));
+  if (rc == KH_OK) rc = cuda_rc(cudaMalloc((void**)&Bs, 3 * pl));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (rc == KH_OK) rc = cuda_rc(cudaEventCreate(&e0));
+  if (rc == KH_OK) rc = cuda_rc(cudaEventCreate(&e1));
+  const int graph = x->graph_on;
+  x->graph_on = 0;
+  const int cand[3] = {64, 128, 256};
+  float best = 1e30f;
+  int bf = x->tpb_flux, bu = x->tpb_update;
+  for (int a = 0; a < 3 && rc == KH_OK; ++a)
+    for (int b = 0; b < 3 && rc == KH_OK; ++b) {
+      x->tpb_flux = cand[a];
+      x->tpb_update = cand[b];
+      float ms = 0.0f;
+      // one untimed step, then two timed steps, each from the caller's state
+      for (int rep = 0; rep < 3 && rc == KH_OK; ++rep) {
+        rc = cuda_rc(cudaMemcpyAsync(Us, U, 8 * pl, cudaMemcpyDeviceToDevice, x->stream));
+        if (rc == KH_OK) rc = cuda_rc(cudaMemcpyAsync(Ps, P, 5 * pl, cudaMemcpyDeviceToDevice, x->stream));
+        if (rc == KH_OK) rc = cuda_rc(cudaMemcpyAsync(Bs, B, 3 * pl, cudaMemcpyDeviceToDevice, x->stream));
+        if (rc == KH_OK) rc = cuda_rc(cudaEventRecord(e0, x->stream));
+        if (rc == KH_OK) {
+          const int r = kh_mesh_step(x, Us, Ps, Bs, dt, nullptr);
+          rc = r < 0 ? r : KH_OK;
+        }
+        if (rc == KH_OK) rc = cuda_rc(cudaEventRecord(e1, x->stream));
+        if (rc == KH_OK) rc = cuda_rc(cudaEventSynchronize(e1));
+        float t = 0.0f;
+        if (rc == KH_OK && rep > 0 && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess) ms += t;
+      }
+      if (rc == KH_OK && ms < best) {
+        best = ms;
+        bf = cand[a];
+        bu = cand[b];
+      }
+    }
+  x->tpb_flux = bf;
+  x->tpb_update = bu;
+  x->graph_on = graph;
+  drop_mesh_graph(x);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (Us) cudaFree(Us);
+  if (Ps) cudaFree(Ps);
+  if (Bs) cudaFree(Bs);
+  if (rc != KH_OK) return rc;
+  {
+    std::lock_guard<std::mutex> g(lock);
+    cache[key] = std::make_pair(bf, bu);
+  }
+  if (tpb_flux) *tpb_flux = bf;
+  if (tpb_update) *tpb_update = bu;
+  return KH_OK;
 }
 
 int kh_mesh_set_graph(kh_mesh* x, int enable) {

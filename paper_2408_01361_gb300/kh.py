@@ -101,6 +101,9 @@ def lib():
         L.kh_mesh_step.argtypes = [vp, vp, vp, vp, C.c_double, dp]
         L.kh_mesh_set_graph.argtypes = [vp, C.c_int]
         L.kh_mesh_divb.argtypes = [vp, vp, dp, dp]
+        L.kh_mesh_set_launch.argtypes = [vp, C.c_int, C.c_int]
+        L.kh_mesh_get_launch.argtypes = [vp, ip, ip]
+        L.kh_mesh_autotune.argtypes = [vp, vp, vp, vp, C.c_double, ip, ip]
         L.kh_mesh_get_stats.argtypes = [vp, C.POINTER(Stats)]
         L.kh_mesh_destroy.argtypes = [vp]
         _lib = L
@@ -411,6 +414,20 @@ class Mesh:
         mx, l1 = C.c_double(), C.c_double()
         _check(lib().kh_mesh_divb(self._h, _ptr(B), C.byref(mx), C.byref(l1)), "kh_mesh_divb")
         return mx.value, l1.value
+
+    def set_launch(self, tpb_flux: int, tpb_update: int):
+        _check(lib().kh_mesh_set_launch(self._h, int(tpb_flux), int(tpb_update)), "kh_mesh_set_launch")
+
+    def get_launch(self):
+        a, b = C.c_int(), C.c_int()
+        _check(lib().kh_mesh_get_launch(self._h, C.byref(a), C.byref(b)), "kh_mesh_get_launch")
+        return a.value, b.value
+
+    def autotune(self, U, P, B, dt: float):
+        a, b = C.c_int(), C.c_int()
+        _check(lib().kh_mesh_autotune(self._h, _ptr(U), _ptr(P), _ptr(B), float(dt), C.byref(a), C.byref(b)),
+               "kh_mesh_autotune")
+        return a.value, b.value
 
     def set_graph(self, enable: bool):
         _check(lib().kh_mesh_set_graph(self._h, 1 if enable else 0), "kh_mesh_set_graph")

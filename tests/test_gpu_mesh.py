@@ -234,3 +234,32 @@ def test_mesh_divb_parity_and_invariance(kh, orc, which):
         m.step(U, P, B, dt)
     m2, _ = m.divb(B)
     assert abs(m2 - mg) < 1e-12 * scale + 1e-12 * mg
+
+
+def test_mesh_launch_settings_and_autotune_bitwise(kh):
+    """Threads per block change nothing in the result; the autotuner picks
+    one of its candidates and caches it."""
+    base, blocks, Ps = _case("torus2_weno5")
+    res = []
+    for cfg in ((64, 256), (256, 64), None):
+        m = kh.Mesh(base, blocks)
+        P, B = m.to_device(Ps)
+        U = m.empty(8)
+        m.prim_to_cons(P, B, U)
+        dt = 0.5 * m.cfl_dt(P, B)
+        if cfg is None:
+            got = m.autotune(U, P, B, dt)
+            assert got[0] in (64, 128, 256) and got[1] in (64, 128, 256)
+            assert m.get_launch() == got
+            assert m.autotune(U, P, B, dt) == got  # cached
+        else:
+            m.set_launch(*cfg)
+            assert m.get_launch() == cfg
+        for _ in range(2):
+            m.step(U, P, B, dt)
+        res.append((U.cpu().numpy(), P.cpu().numpy(), B.cpu().numpy()))
+    for r in res[1:]:
+        for a, b in zip(res[0], r):
+            assert np.array_equal(a, b)
+    with pytest.raises(kh.KHError):
+        m.set_launch(48, 128)
