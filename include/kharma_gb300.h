@@ -194,6 +194,42 @@ int kh_profile_read(const kh_ctx* ctx, double* ms, int64_t* count);
 int64_t kh_launch_count(const kh_ctx* ctx);
 
 /* ---------------------------------------------------------------------------
+ * Adjoint of one step (FP64 contexts). Given the gradient of an objective
+ * with respect to the outputs of kh_step(U, P, B, dt) -- gU (8 planes), gP
+ * (5), gB (3), each nullable (= 0), and gF1, nullable, the gradient with
+ * respect to the stage-2 x1 face fluxes (8 planes, the flux through the lower
+ * x1 face of each cell, after Flux-CT) -- writes the gradient with respect to
+ * the step's inputs U (gU_in, 8 planes), P (gP_in, 5) and B (gB_in, 3), and
+ * with respect to the adiabatic index (*g_gamma). Interior cells carry the
+ * gradient; ghost cells are written as 0. U, P, B are the step's input
+ * (the checkpoint; read only): the step is re-run from it to record the
+ * stage states, then reversed (see the reverse rules below). All arrays are
+ * device pointers in the kh_shape layout; the call synchronises the context
+ * stream. Scratch (~83 planes of doubles) is allocated on the first call and
+ * kept until kh_destroy. KH_EINVAL for a mixed-precision context or bad
+ * arguments.
+ *
+ * Reverse rules (NS pattern 3): limiter and max branches as taken by the
+ * forward (ties: the first argument), LLF with ctop differentiated through
+ * its active speed, Flux-CT and the ghost fill transposed exactly, the
+ * inversion by the implicit-function theorem (a 5x5 FP64 solve per zone),
+ * floored components and fixed-up zones frozen (zero derivative upstream).
+ * The initial guess of the inversion carries no derivative. */
+int kh_step_adjoint(kh_ctx* ctx, const double* U, const double* P, const double* B, double dt, const double* gU,
+                    const double* gP, const double* gB, const double* gF1, double* gU_in, double* gP_in,
+                    double* gB_in, double* g_gamma);
+
+/* Gradient of U = kh_prim_to_cons(P, B) at interior cells: gP (5 planes), gB
+ * (3 planes) = (dU/dP)^T gU, and the gamma derivative; ghosts written as 0.
+ * FP64 contexts; synchronises the stream. */
+int kh_prim_to_cons_adjoint(kh_ctx* ctx, const double* P, const double* B, const double* gU, double* gP, double* gB,
+                            double* g_gamma);
+/* The fluxes through the lower x^dir faces (dir 1..3; 8 planes, after
+ * Flux-CT) of the last stage the context ran -- after kh_step, its second
+ * stage. Copied on the context stream (asynchronous). FP64 contexts. */
+int kh_get_stage_flux(kh_ctx* ctx, int dir, double* F);
+
+/* ---------------------------------------------------------------------------
  * Static mesh refinement: many blocks at several levels stepped together
  * ("Requirements" section: refinement against the polar time-step limit;
  * "Code Structure" section: SMR through the mesh framework).

@@ -16,8 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libkharma_gb300.so")
-SOURCES = ["kh_kernels.cu", "kh_api.cu", "kh_noalloc.cu", "kh_mesh.cu"]
-HEADERS = ["kh_internal.h", "kh_physics.cuh", "kh_geom_math.h", "kh_zone.cuh"]
+SOURCES = ["kh_kernels.cu", "kh_api.cu", "kh_noalloc.cu", "kh_mesh.cu", "kh_adjoint.cu"]
+HEADERS = ["kh_internal.h", "kh_physics.cuh", "kh_geom_math.h", "kh_zone.cuh", "kh_ctx.h", "kh_dual.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -8,59 +8,12 @@
 #include <mutex>
 #include <tuple>
 
-#include "kh_internal.h"
+#include "kh_ctx.h"
 
 using namespace kh;
 
 extern "C" int kh_get_stats(kh_ctx* x, kh_stats* out);
 
-struct kh_ctx {
-  kh_coords c;
-  double a, gam;
-  Layout L;
-  Scheme S;
-  CoordParams cp;
-  cudaStream_t stream;
-  double* geo;
-  double* conn;
-  double* flo;     // geometric floors of rho and u per (i, j)
-  double* pstar;   // 8 planes: stage-1 output
-  double* F[3];    // 8 planes each
-  double* ctop[3];
-  double* emf[3];
-  int8_t* pflag;
-  double* partial;
-  int npartial;
-  double* dscalar;              // [0] dt_cfl out, [1..2] divb max/sum, [3] dt in
-  unsigned long long* counters; // NCNT
-  double* dirichlet[2];
-  // mixed precision (KH_MIXED): FP32 geometry copy, FP32 flux pass buffers,
-  // FP32 stage-1 output and FP32 Dirichlet ghosts
-  float* geof;
-  float* connf;
-  float* pstarf;   // 8 planes
-  float* pnf;      // 8 planes: FP32 copy of the ghost-filled stage-1 input
-  float* Ff[3];    // 8 planes each
-  float* ctopf[3];
-  float* emff[3];
-  float* dirichletf[2];
-  long long launches;
-  kh_stats last;
-  // launch configuration (threads per block of the stencil and update kernels)
-  int tpb_flux, tpb_update;
-  // CUDA-graph replay of the step, keyed by the (U, P, B) pointers captured
-  int graph_on;
-  cudaStream_t cap_stream;
-  cudaGraphExec_t gexec;
-  const void* gkey[3];
-  int graph_launches;
-  // optional per-kernel-group timing (CUDA events on the context stream)
-  int profiling;
-  cudaEvent_t ev[KH_NTIMERS][2][2];  // [group][stage][start, stop]
-  int ev_used[KH_NTIMERS][2];
-  double prof_ms[KH_NTIMERS];
-  long long prof_n[KH_NTIMERS];
-};
 
 namespace {
 
@@ -128,7 +81,7 @@ void free_all(kh_ctx* x) {
                   x->ctop[2], x->emf[0], x->emf[1], x->emf[2], x->pflag, x->partial, x->dscalar,
                   x->counters, x->dirichlet[0], x->dirichlet[1], x->geof, x->connf, x->pstarf, x->pnf, x->Ff[0],
                   x->Ff[1], x->Ff[2], x->ctopf[0], x->ctopf[1], x->ctopf[2], x->emff[0], x->emff[1],
-                  x->emff[2], x->dirichletf[0], x->dirichletf[1]};
+                  x->emff[2], x->dirichletf[0], x->dirichletf[1], x->adj, x->adj_i8, x->adj_red};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }

@@ -58,7 +58,7 @@ template <class R> struct FState {
 
 // u^t = gamma / alpha, u^i = u~^i - gamma alpha g^{ti}, gamma^2 = 1 + g_ij u~^i u~^j;
 // b^t = B^i u_i, b^i = (B^i + b^t u^i) / u^t.
-template <class R> KH_HD void fluid_state(const R* P, const Met<R>& m, FState<R>& s) {
+template <class R, class M> KH_HD void fluid_state(const R* P, const Met<M>& m, FState<R>& s) {
   const R v1 = P[V_U1], v2 = P[V_U2], v3 = P[V_U3];
   const R q = m.gcov[1][1] * v1 * v1 + m.gcov[2][2] * v2 * v2 + m.gcov[3][3] * v3 * v3 +
               R(2) * (m.gcov[1][2] * v1 * v2 + m.gcov[1][3] * v1 * v3 + m.gcov[2][3] * v2 * v3);
@@ -90,8 +90,8 @@ template <class R> KH_HD void fluid_state(const R* P, const Met<R>& m, FState<R>
 // Flux through an x^d face (d = 1..3) and the conserved vector of one state:
 // F = sqrt(-g) (rho u^d, T^d_t + rho u^d, T^d_i, b^i u^d - b^d u^i),
 // U = sqrt(-g) (rho u^t, T^t_t + rho u^t, T^t_i, B^i).
-template <class R>
-KH_HD void flux_cons(const R* P, const FState<R>& s, const Met<R>& m, R gam, int d, R* F, R* U) {
+template <class R, class M>
+KH_HD void flux_cons(const R* P, const FState<R>& s, const Met<M>& m, R gam, int d, R* F, R* U) {
   const R p = (gam - R(1)) * P[V_U];
   const R eta = P[V_RHO] + P[V_U] + p + s.bsq;
   const R ptot = p + R(0.5) * s.bsq;
@@ -119,7 +119,7 @@ KH_HD void flux_cons(const R* P, const FState<R>& s, const Met<R>& m, R gam, int
 }
 
 // Conserved vector only.
-template <class R> KH_HD void cons_only(const R* P, const FState<R>& s, const Met<R>& m, R gam, R* U) {
+template <class R, class M> KH_HD void cons_only(const R* P, const FState<R>& s, const Met<M>& m, R gam, R* U) {
   const R p = (gam - R(1)) * P[V_U];
   const R eta = P[V_RHO] + P[V_U] + p + s.bsq;
   const R ptot = p + R(0.5) * s.bsq;
@@ -140,8 +140,8 @@ template <class R> KH_HD void cons_only(const R* P, const FState<R>& s, const Me
 // (c_s^2 = gam p / w, v_A^2 = b^2 / (w + b^2); clamped to [0, 1]) a covariant
 // wave vector (-v, delta^d) obeys (k_mu u^mu)^2 = c_ms^2 (k_mu k^mu + (k_mu u^mu)^2),
 // i.e. A v^2 - Bq v + C = 0.
-template <class R>
-KH_HD void signal_speeds(const R* P, const FState<R>& s, const Met<R>& m, R gam, int d, R& cmax, R& cmin) {
+template <class R, class M>
+KH_HD void signal_speeds(const R* P, const FState<R>& s, const Met<M>& m, R gam, int d, R& cmax, R& cmin) {
   const R p = (gam - R(1)) * P[V_U];
   const R w = P[V_RHO] + P[V_U] + p;
   R cms2 = kdiv(gam * p + s.bsq, w + s.bsq);
@@ -183,21 +183,24 @@ template <class R> KH_HD void recon_mc(R qm, R q0, R qp, R& lo, R& hi) {
 // smoothness indicators, nonlinear weights d_k / (eps + beta_k)^2.
 // FP64: eps = 1e-26 (absolute). The three weights share one division by
 // multiplying each through by (s0 s1 s2)^2, s_k = eps + beta_k.
-KH_HD double weno5_plus(double a, double b, double c, double d, double e) {
-  const double p0 = 0.375 * a - 1.25 * b + 1.875 * c;
-  const double p1 = -0.125 * b + 0.75 * c + 0.375 * d;
-  const double p2 = 0.375 * c + 0.75 * d - 0.125 * e;
+// (Templated for the adjoint's dual numbers; the double instance is the FP64
+// path's.)
+template <class R> KH_HD R weno5_plus_t(R a, R b, R c, R d, R e) {
+  const R p0 = 0.375 * a - 1.25 * b + 1.875 * c;
+  const R p1 = -0.125 * b + 0.75 * c + 0.375 * d;
+  const R p2 = 0.375 * c + 0.75 * d - 0.125 * e;
   const double k = 13.0 / 12.0;
-  const double t0 = a - 2.0 * b + c, u0 = a - 4.0 * b + 3.0 * c;
-  const double t1 = b - 2.0 * c + d, u1 = b - d;
-  const double t2 = c - 2.0 * d + e, u2 = 3.0 * c - 4.0 * d + e;
-  const double s0 = k * t0 * t0 + 0.25 * u0 * u0 + 1e-26;
-  const double s1 = k * t1 * t1 + 0.25 * u1 * u1 + 1e-26;
-  const double s2 = k * t2 * t2 + 0.25 * u2 * u2 + 1e-26;
-  const double q0 = s1 * s2, q1 = s0 * s2, q2 = s0 * s1;
-  const double w0 = 0.0625 * q0 * q0, w1 = 0.625 * q1 * q1, w2 = 0.3125 * q2 * q2;
+  const R t0 = a - 2.0 * b + c, u0 = a - 4.0 * b + 3.0 * c;
+  const R t1 = b - 2.0 * c + d, u1 = b - d;
+  const R t2 = c - 2.0 * d + e, u2 = 3.0 * c - 4.0 * d + e;
+  const R s0 = k * t0 * t0 + 0.25 * u0 * u0 + 1e-26;
+  const R s1 = k * t1 * t1 + 0.25 * u1 * u1 + 1e-26;
+  const R s2 = k * t2 * t2 + 0.25 * u2 * u2 + 1e-26;
+  const R q0 = s1 * s2, q1 = s0 * s2, q2 = s0 * s1;
+  const R w0 = 0.0625 * q0 * q0, w1 = 0.625 * q1 * q1, w2 = 0.3125 * q2 * q2;
   return (w0 * p0 + w1 * p1 + w2 * p2) / (w0 + w1 + w2);
 }
+KH_HD double weno5_plus(double a, double b, double c, double d, double e) { return weno5_plus_t<double>(a, b, c, d, e); }
 
 // FP32 (mixed path): the same weights, written scale-free so that nothing
 // underflows in FP32: the indicators are normalised by their sum, eps = 1e-12

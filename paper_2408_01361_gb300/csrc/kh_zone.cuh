@@ -192,8 +192,8 @@ __device__ __forceinline__ void apply_ct_at(R* F1, R* F2, R* F3, const R* e1, co
 
 // S_nu = sqrt(-g) T^k_l Gamma^l_{nu k} for nu = t, 1, 2, 3 (energy and
 // momentum slots); zero for rho and B.
-template <class R>
-__device__ __forceinline__ void source_terms(const R* P, const Met<R>& m, const R* conn, long long gplane, long long p,
+template <class R, class M>
+__device__ __forceinline__ void source_terms(const R* P, const Met<M>& m, const M* conn, long long gplane, long long p,
                                              R gam, R* S) {
   FState<R> s;
   fluid_state(P, m, s);
@@ -223,7 +223,7 @@ __device__ __forceinline__ void source_terms(const R* P, const Met<R>& m, const 
 __device__ __forceinline__ void update_zone(const double* U0, const CVars& Pin, const Vars& Pout, double* Uout,
                                             const double* F1, const double* F2, const double* F3, const Layout& L,
                                             const DevGeom& G, const Scheme& S, double cdt, int8_t* pflag,
-                                            unsigned long long* cnt, int i, int j, int k) {
+                                            unsigned long long* cnt, int i, int j, int k, double* Praw = nullptr) {
   const long long c = L.at(k, j, i);
   const long long p = (long long)j * L.n1s + i;
   const long long sj = L.n1s, sk = (long long)L.n1s * L.n2s;
@@ -249,6 +249,10 @@ __device__ __forceinline__ void update_zone(const double* U0, const CVars& Pin, 
   Pn[V_B1] = U[V_B1] * ig;
   Pn[V_B2] = U[V_B2] * ig;
   Pn[V_B3] = U[V_B3] * ig;
+  if (Praw) {  // the adjoint's record of the inversion result before floors
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Praw[v * L.plane + c] = Pn[v];
+  }
   int fmask = 0;
   if (flag == 0) {
     FState<double> s;

@@ -88,6 +88,9 @@ def lib():
         L.kh_destroy.argtypes = [vp]
         L.kh_strerror.argtypes = [C.c_int]
         L.kh_strerror.restype = C.c_char_p
+        L.kh_step_adjoint.argtypes = [vp, vp, vp, vp, C.c_double, vp, vp, vp, vp, vp, vp, vp, dp]
+        L.kh_prim_to_cons_adjoint.argtypes = [vp, vp, vp, vp, vp, vp, dp]
+        L.kh_get_stage_flux.argtypes = [vp, C.c_int, vp]
         L.kh_mesh_init.argtypes = [C.c_double, C.POINTER(Coords), C.c_double, C.c_int, C.POINTER(Block),
                                    C.POINTER(C.c_void_p)]
         L.kh_mesh_block_shape.argtypes = [vp, C.c_int, ip, ip, ip, C.POINTER(C.c_int64)]
@@ -265,6 +268,30 @@ class Context:
         _check(lib().kh_autotune(self._h, _ptr(U), _ptr(P), _ptr(B), float(dt), C.byref(a), C.byref(b)),
                "kh_autotune")
         return a.value, b.value
+
+    def step_adjoint(self, U, P, B, dt: float, gU=None, gP=None, gB=None, gF1=None):
+        """Gradient through one step (kh_step_adjoint) at the checkpoint
+        (U, P, B): returns (gU_in, gP_in, gB_in, g_gamma) as new tensors."""
+        gU_in, gP_in, gB_in = self.empty(8), self.empty(5), self.empty(3)
+        gg = C.c_double()
+        _check(lib().kh_step_adjoint(self._h, _ptr(U), _ptr(P), _ptr(B), float(dt), _ptr(gU), _ptr(gP), _ptr(gB),
+                                     _ptr(gF1), _ptr(gU_in), _ptr(gP_in), _ptr(gB_in), C.byref(gg)),
+               "kh_step_adjoint")
+        return gU_in, gP_in, gB_in, gg.value
+
+    def prim_to_cons_adjoint(self, P, B, gU):
+        """(dU/dP)^T gU at interior cells: returns (gP, gB, g_gamma)."""
+        gP, gB = self.empty(5), self.empty(3)
+        gg = C.c_double()
+        _check(lib().kh_prim_to_cons_adjoint(self._h, _ptr(P), _ptr(B), _ptr(gU), _ptr(gP), _ptr(gB), C.byref(gg)),
+               "kh_prim_to_cons_adjoint")
+        return gP, gB, gg.value
+
+    def stage_flux(self, d: int = 1):
+        """Fluxes through the lower x^d faces from the last stage run (8 planes)."""
+        F = self.empty(8)
+        _check(lib().kh_get_stage_flux(self._h, int(d), _ptr(F)), "kh_get_stage_flux")
+        return F
 
     TIMERS = ("bc", "flux_x1", "flux_x2", "flux_x3", "flux_ct", "update", "fixup", "cfl")
 

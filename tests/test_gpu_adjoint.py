@@ -1,0 +1,366 @@
+"""Adjoint of the step (kh_step_adjoint, kh_prim_to_cons_adjoint and the
+torch.autograd wrappers) against central finite differences of the forward
+(the CUDA step, and independently the FP64 oracle), and against the exact
+conservation of total energy in a periodic Minkowski box: d E_final / d P0
+equals d E(P0) / d P0 because E_final = E_initial for every P0 and gamma.
+
+The step is only piecewise smooth (MC's branches, the max in the LLF speed,
+WENO5's weights have an eps of 1e-26), so a difference quotient measures the
+derivative only where no branch flips inside the step h: the checks perturb
+one zone at a time (few branch evaluations see the change) on rough states
+(no component uniform), and a probe whose quotients at h and h/2 disagree
+(a flip) is reported and left out, as are runs that fixed up a zone. The
+bar is 1e-6 of the largest derivative of each component."""
+import os
+
+import numpy as np
+import pytest
+
+from conftest import GOLDEN
+from gpu_helpers import GpuRun, interior
+from paper_2408_01361_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kh():
+    from paper_2408_01361_gb300 import kh as _kh
+    return _kh
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as _t
+    return _t
+
+
+# A directional derivative is only defined where the step is differentiable:
+# MC is not at dq- dq+ = 0, and WENO5's weights are smooth only on the scale
+# of their eps (1e-26) around uniform data. Every component of the test
+# states therefore carries seeded additive roughness (no component is
+# uniform, e.g. the slow mode's u~3 and B3, or the torus's u~1, u~2), far
+# above the finite-difference step.
+
+
+def _rough(P, seed, amp, where=None):
+    xi = inputs.uniform01(seed, np.arange(P.size)).reshape(P.shape) - 0.5
+    sc = np.maximum(np.abs(P).reshape(P.shape[0], -1).max(axis=1), 1e-2)[:, None, None, None]
+    d = amp * sc * xi
+    if where is not None:
+        d = d * where
+    return P + d
+
+
+def _box(n=12, recon="mc", amp=0.05, seed=11):
+    cfg = inputs.linear_mode_cfg(n, ndim=3, recon=recon)
+    dP, om = inputs.load_eigvec(os.path.join(GOLDEN, "linear_slow_mode.txt"))
+    P = inputs.linear_mode_state(cfg, dP, om, amp=amp)
+    return cfg, _rough(P, seed, 0.02)
+
+
+def _torus(n1=48, n2=32, recon="mc"):
+    cfg = inputs.torus_cfg(n1, n2, 1, r_out=60.0, recon=recon)
+    P = inputs.torus_state(cfg, seed=2)
+    body = (P[0:1] > 1e-2).astype(float)
+    Pr = _rough(P, 13, 1e-3, body)
+    Pr[0:2] = P[0:2]  # keep rho and u (noise already in u)
+    return cfg, Pr
+
+
+def _weights(cfg, seed):
+    rng = np.random.default_rng(seed)
+    shp = inputs.shape(cfg)
+    wU = np.zeros(shp)
+    wP = np.zeros(shp)
+    sl = (slice(None),) + inputs.interior(cfg)
+    wU[sl] = rng.normal(size=wU[sl].shape)
+    wP[sl] = rng.normal(size=wP[sl].shape)
+    return wU, wP
+
+
+def _forward(kh, cfg, U0, P0, nsteps, dt, gam=None):
+    c = dict(cfg)
+    if gam is not None:
+        c["gam"] = gam
+    ctx = kh.Context(c)
+    g = GpuRun(ctx, c, P0, U=U0)
+    for _ in range(nsteps):
+        ctx.step(g.U, g.P, g.B, dt)
+    return g.host()
+
+
+def _J(cfg, U, P, wU, wP):
+    sl = (slice(None),) + inputs.interior(cfg)
+    return float((wU[sl] * U[sl]).sum() + (wP[sl] * P[sl]).sum())
+
+
+def _adjoint_one_step(kh, torch, cfg, U0, P0, dt, wU, wP):
+    ctx = kh.Context(cfg)
+    g = GpuRun(ctx, cfg, P0, U=U0)
+    gU = ctx.to_device(wU)
+    gPB = ctx.to_device(wP)
+    gUi, gPi, gBi, gg = ctx.step_adjoint(g.U, g.P, g.B, dt, gU, gPB[:5].contiguous(), gPB[5:].contiguous())
+    N1 = P0.shape[3]
+    return (ctx.to_host(gUi, N1), np.concatenate([ctx.to_host(gPi, N1), ctx.to_host(gBi, N1)]), gg)
+
+
+def _direction(cfg, P0, seed, mask=None):
+    rng = np.random.default_rng(seed)
+    sl = (slice(None),) + inputs.interior(cfg)
+    vU = np.zeros(P0.shape)
+    vP = np.zeros(P0.shape)
+    vU[sl] = rng.normal(size=vU[sl].shape)
+    vP[sl] = rng.normal(size=vP[sl].shape)
+    if mask is not None:
+        vU *= mask
+        vP *= mask
+    return vU, vP
+
+
+def _random_state(cfg, seed, b_amp=0.5):
+    """Rough, non-degenerate state: every primitive varies from cell to cell."""
+    rng = np.random.default_rng(seed)
+    P = np.zeros(inputs.shape(cfg))
+    P[0] = 1.0 + 0.1 * rng.random(P[0].shape)
+    P[1] = 1.0 + 0.1 * rng.random(P[1].shape)
+    P[2:5] = 0.1 * rng.normal(size=P[2:5].shape)
+    P[5:] = b_amp * rng.normal(size=P[5:].shape)
+    return P
+
+
+def _probes(kh, cfg, U0, P0, dt, wU, wP, gU, gP, zones, comps=range(16)):
+    """Single-zone central differences of J at the given interior zones."""
+    ctx = kh.Context(cfg)
+
+    def J(U, P):
+        g = GpuRun(ctx, cfg, P, U=U)
+        ctx.step(g.U, g.P, g.B, dt)
+        assert ctx.stats().nfail == 0
+        u, p = g.host()
+        return _J(cfg, u, p, wU, wP)
+
+    res = {}  # component -> list of (adjoint, fd)
+    flips = []
+    sl = (slice(None),) + inputs.interior(cfg)
+    # rounding of J between two runs: ~1e-15 of the sum of its terms' magnitudes
+    noise = 1e-15 * (np.abs(wU[sl] * U0[sl]).sum() + np.abs(wP[sl] * P0[sl]).sum())
+    for q in comps:
+        which, comp = ("P", q) if q < 8 else ("U", q - 8)
+        # step: 1e-5 of the value at the zone (at least 1e-3 of the
+        # component's largest magnitude)
+        big = max(np.abs((P0 if which == "P" else U0)[sl][comp]).max(), 1e-2)
+        for z in zones:
+            e = np.zeros(P0.shape)
+            e[(comp,) + z] = 1.0
+            sc = max(abs((P0 if which == "P" else U0)[(comp,) + z]), 1e-3 * big)
+            fds = []
+            for h in (1e-5 * sc, 0.5e-5 * sc):
+                if which == "P":
+                    fds.append((J(U0, P0 + h * e) - J(U0, P0 - h * e)) / (2 * h))
+                else:
+                    fds.append((J(U0 + h * e, P0) - J(U0 - h * e, P0)) / (2 * h))
+            tol_noise = 4.0 * noise / (0.5e-5 * sc)
+            if abs(fds[0] - fds[1]) > 1e-6 * abs(fds[1]) + tol_noise:
+                flips.append((q, z, fds))
+                continue
+            adj = (gP if which == "P" else gU)[(comp,) + z]
+            res.setdefault(q, []).append((adj, fds[1], tol_noise))
+    return res, flips
+
+
+def _check_probes(res, flips, total):
+    assert len(flips) <= 0.05 * total, (len(flips), flips[:6])
+    for q, trip in res.items():
+        a = np.array(trip)
+        sc = np.abs(a[:, 1]).max()
+        err = np.abs(a[:, 0] - a[:, 1]) - a[:, 2]
+        assert err.max() <= 1e-6 * sc, (q, err.max() / max(sc, 1e-300), sc)
+
+
+@pytest.mark.parametrize("recon", ["mc", "weno5"])
+def test_step_adjoint_single_zone_probes_box(kh, torch, orc, recon):
+    """3-D periodic Minkowski box: every component of dJ/dU^n and dJ/dP^n at
+    every zone of a 4^3 grid (fluxes in three directions, Flux-CT in 3-D,
+    periodic ghost fill)."""
+    cfg = inputs.linear_mode_cfg(4, ndim=3, recon=recon)
+    P0 = orc.apply_bc(cfg, _random_state(cfg, 3))
+    U0 = orc.prim_to_cons(cfg, P0)
+    dt = 0.5 * orc.cfl_dt(cfg, P0)
+    wU, wP = _weights(cfg, 5)
+    gU, gP, gg = _adjoint_one_step(kh, torch, cfg, U0, P0, dt, wU, wP)
+    zones = [(k, j, i) for k in range(3, 7) for j in range(3, 7) for i in range(3, 7)]
+    res, flips = _probes(kh, cfg, U0, P0, dt, wU, wP, gU, gP, zones)
+    _check_probes(res, flips, 16 * len(zones))
+    # gamma
+    hg = 1e-6 * cfg["gam"]
+    fdg = (_J(cfg, *_forward(kh, cfg, U0, P0, 1, dt, gam=cfg["gam"] + hg), wU, wP)
+           - _J(cfg, *_forward(kh, cfg, U0, P0, 1, dt, gam=cfg["gam"] - hg), wU, wP)) / (2 * hg)
+    assert abs(gg - fdg) <= 1e-6 * abs(fdg), (gg, fdg)
+
+
+def test_step_adjoint_single_zone_probes_fmks(kh, torch, orc):
+    """2-D funky MKS Kerr grid (metric, connection sources, polar reflection
+    with zero axis fluxes, outflow with no inflow), floors out of reach:
+    probes at zones along both poles, both x1 edges and inside."""
+    cfg = inputs.torus_cfg(12, 12, 1, r_out=60.0, recon="weno5")
+    cfg["floors"] = dict(rho_min=1e-30, u_min=1e-30, bsq_rho_max=1e300, bsq_u_max=1e300, u_rho_max=1e300,
+                         gamma_max=1e300)
+    cfg["x1"] = (np.log(2.5), np.log(20.0))
+    P0 = inputs.random_prims(cfg, 4, rho_range=(0.5, 1.0), u_range=(0.5, 1.0), ut_scale=(0.1, 0.1, 0.1),
+                             b_scale=(0.3, 0.3, 0.3))
+    P0 = orc.apply_bc(cfg, P0)
+    U0 = orc.prim_to_cons(cfg, P0)
+    dt = 0.3 * orc.cfl_dt(cfg, P0)
+    wU, wP = _weights(cfg, 6)
+    gU, gP, gg = _adjoint_one_step(kh, torch, cfg, U0, P0, dt, wU, wP)
+    zones = [(0, j, i) for j in (3, 4, 9, 14) for i in (3, 4, 8, 13, 14)]
+    res, flips = _probes(kh, cfg, U0, P0, dt, wU, wP, gU, gP, zones)
+    _check_probes(res, flips, 16 * len(zones))
+
+
+def test_prim_to_cons_adjoint_matches_central_differences(kh, orc):
+    cfg, P0 = _torus(40, 24)
+    P0 = orc.apply_bc(cfg, P0)
+    ctx = kh.Context(cfg)
+    g = GpuRun(ctx, cfg, P0)
+    wU, _ = _weights(cfg, 7)
+    gP, gB, gg = ctx.prim_to_cons_adjoint(g.P, g.B, ctx.to_device(wU))
+    N1 = P0.shape[3]
+    gPB = np.concatenate([ctx.to_host(gP, N1), ctx.to_host(gB, N1)])
+    _, vP = _direction(cfg, P0, 8)
+    vP *= np.abs(P0).reshape(8, -1).max(axis=1)[:, None, None, None] + 1e-3
+    adj = float((gPB * vP).sum())
+    h = 1e-6
+    sl = (slice(None),) + inputs.interior(cfg)
+    Jp = float((wU[sl] * orc.prim_to_cons(cfg, P0 + h * vP)[sl]).sum())
+    Jm = float((wU[sl] * orc.prim_to_cons(cfg, P0 - h * vP)[sl]).sum())
+    fd = (Jp - Jm) / (2 * h)
+    assert abs(adj - fd) <= 1e-7 * abs(fd), (adj, fd)
+
+
+def _rollout_grad(kh, torch, cfg, P0, nsteps, dt, objective):
+    from paper_2408_01361_gb300 import autograd as kga
+    ctx = kh.Context(cfg)
+    PB = ctx.to_device(P0)
+    P = PB[:5].clone().requires_grad_(True)
+    B = PB[5:].clone().requires_grad_(True)
+    gam = torch.tensor(cfg["gam"], dtype=torch.float64, device=ctx.device, requires_grad=True)
+    U = kga.prim_to_cons(ctx, P, B, gam)
+    Uc, Pc, Bc = U, P, B
+    F1 = None
+    for q in range(nsteps):
+        if q == nsteps - 1:
+            Uc, Pc, Bc, F1 = kga.step(ctx, Uc, Pc, Bc, gam, dt, with_flux=True)
+        else:
+            Uc, Pc, Bc = kga.step(ctx, Uc, Pc, Bc, gam, dt)
+    J = objective(ctx, U, Uc, Pc, Bc, F1)
+    J.backward()
+    N1 = P0.shape[3]
+    gPB = np.concatenate([ctx.to_host(P.grad, N1), ctx.to_host(B.grad, N1)])
+    return float(J), gPB, float(gam.grad)
+
+
+def _energy(cfg, torch):
+    """E = -sum (U_energy - U_rho) dV over the interior (total energy)."""
+    n1, n2, n3 = cfg["n1"], cfg["n2"], cfg["n3"]
+    dV = np.prod([(cfg[k][1] - cfg[k][0]) / cfg[n] for k, n in (("x1", "n1"), ("x2", "n2"), ("x3", "n3"))])
+    sl = inputs.interior(cfg)
+
+    def E(ctx, U0, U, P, B, F1):
+        return -(U[1][sl[0], sl[1], sl[2]] - U[0][sl[0], sl[1], sl[2]]).sum() * dV
+    return E
+
+
+@pytest.mark.parametrize("recon", ["mc", "weno5"])
+def test_energy_gradient_through_20_steps_equals_initial(kh, torch, recon):
+    """Periodic Minkowski box: E is conserved by the step exactly (up to
+    round-off), so its gradient through 20 steps must equal its gradient at
+    t = 0 -- every transpose of the reverse pass (divergence, Flux-CT,
+    ghost fill, reconstruction, LLF, inversion) has to telescope."""
+    cfg, P0 = _box(16, recon)
+    E = _energy(cfg, torch)
+    dt = 0.2 / 16
+    J20, g20, gg20 = _rollout_grad(kh, torch, cfg, P0, 20, dt, E)
+    J0, g0, gg0 = _rollout_grad(kh, torch, cfg, P0, 0, dt, lambda ctx, U0, U, P, B, F1: E(ctx, U0, U0, P, B, F1))
+    assert abs(J20 - J0) < 1e-12 * abs(J0)
+    sc = np.abs(g0).max()
+    assert np.abs(g20 - g0).max() < 1e-9 * sc, np.abs(g20 - g0).max() / sc
+    assert abs(gg20 - gg0) < 1e-9 * abs(gg0)
+
+
+def test_rollout_directional_derivative_vs_oracle(kh, torch, orc):
+    """3 steps of a rough WENO5 box: the adjoint's <dJ/dP0, v> for v on a few
+    zones, and dJ/dgamma, against central differences of the FP64 oracle
+    (independent code); a direction whose quotients at h and h/2 disagree
+    (a branch flip) is replaced by the next seed."""
+    cfg = inputs.linear_mode_cfg(6, ndim=3, recon="weno5")
+    P0 = orc.apply_bc(cfg, _random_state(cfg, 8))
+    dt = 0.3 / 6
+    wU, wP = _weights(cfg, 9)
+    sl = (slice(None),) + inputs.interior(cfg)
+
+    def obj(ctx, U0, U, P, B, F1):
+        tU = ctx.to_device(wU)
+        tP = ctx.to_device(wP)
+        return (tU * U).sum() + (tP[:5] * P).sum() + (tP[5:] * B).sum()
+
+    J, gPB, gg = _rollout_grad(kh, torch, cfg, P0, 3, dt, obj)
+
+    def Jor(P, gam):
+        c = dict(cfg, gam=gam)
+        U = orc.prim_to_cons(c, P)
+        for _ in range(3):
+            U, P, _, _ = orc.step(c, U, P, dt)
+        return float((wU[sl] * U[sl]).sum() + (wP[sl] * P[sl]).sum())
+
+    checked = 0
+    for seed in range(20, 28):
+        rng = np.random.default_rng(seed)
+        v = np.zeros(P0.shape)
+        for _ in range(3):
+            z = tuple(rng.integers(3, 9, size=3))
+            v[(slice(None),) + z] = rng.normal(size=8)
+        adj = float((gPB * v).sum())
+        fds = [(Jor(P0 + h * v, cfg["gam"]) - Jor(P0 - h * v, cfg["gam"])) / (2 * h) for h in (1e-6, 0.5e-6)]
+        if abs(fds[0] - fds[1]) > 1e-7 * abs(fds[1]):
+            continue
+        assert abs(adj - fds[1]) <= 1e-6 * abs(fds[1]), (seed, adj, fds)
+        checked += 1
+    assert checked >= 4
+    hg = 1e-6 * cfg["gam"]
+    fdg = (Jor(P0, cfg["gam"] + hg) - Jor(P0, cfg["gam"] - hg)) / (2 * hg)
+    assert abs(gg - fdg) <= 1e-6 * abs(fdg), (gg, fdg)
+
+
+def test_face_flux_seed_gradient(kh, torch):
+    """The gradient of the mass flux through one x1 face plane on the last
+    step's second stage (the form of the horizon mass-flux objective) over 3
+    steps of the rough box: adjoint with the flux seed against central
+    differences of the CUDA forward."""
+    cfg, P0 = _box(12, "weno5")
+    dt = 0.3 / 12
+    ng = 3
+    i_f = ng + cfg["n1"] // 2
+    n2, n3 = cfg["n2"], cfg["n3"]
+
+    def mdot(ctx, U0, U, P, B, F1):
+        return -(F1[0, ng:ng + n3, ng:ng + n2, i_f]).sum()
+
+    J, gPB, gg = _rollout_grad(kh, torch, cfg, P0, 3, dt, mdot)
+    _, vP = _direction(cfg, P0, 12)
+    vP *= np.abs(P0).reshape(8, -1).max(axis=1)[:, None, None, None]
+    adj = float((gPB * vP).sum())
+
+    def Jgpu(P):
+        ctx = kh.Context(cfg)
+        g = GpuRun(ctx, cfg, P)
+        for _ in range(3):
+            ctx.step(g.U, g.P, g.B, dt)
+        F1 = ctx.stage_flux(1).cpu().numpy()
+        return float(-(F1[0, ng:ng + n3, ng:ng + n2, i_f]).sum())
+
+    h = 1e-6
+    fd = (Jgpu(P0 + h * vP) - Jgpu(P0 - h * vP)) / (2 * h)
+    assert abs(J - Jgpu(P0)) <= 1e-12 * abs(J)
+    assert abs(adj - fd) <= 1e-6 * abs(fd), (adj, fd)
