@@ -53,6 +53,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--n3", type=int, default=WORKLOAD["n3"], help="azimuthal zones (96 = the named workload)")
     p.add_argument("--no-smr", action="store_true", help="skip the statically refined torus leg")
+    p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-cost leg")
     p.add_argument("--smr-only", action="store_true", help="run only the statically refined torus leg")
     p.add_argument("--precisions", default="mixed,fp64",
                    help="comma list; the first is the headline, the others are reported beside it")
@@ -329,6 +330,60 @@ def measure_smr(args, dev, stream, precision):
     return out
 
 
+def measure_adjoint(args, dev, stream, nsteps: int = 20):
+    """Adjoint cost (C5 shapes): 20 FP64 steps forward keeping per-step
+    checkpoints, then the 20 adjoint steps in reverse (kh_step_adjoint),
+    each timed with CUDA events; the objective's seed is the gradient of the
+    total energy."""
+    import numpy as np
+    import torch
+
+    from paper_2408_01361_gb300 import inputs, kh
+
+    dP = np.zeros(8)
+    dP[0] = 1.0  # a density mode: the state only has to be representative
+    out = {}
+    for name, cfg in (("linear-mode box 64^3", inputs.linear_mode_cfg(64, ndim=3)),
+                      ("FM torus 128x64x1 (2-D)", inputs.torus_cfg(128, 64, 1))):
+        if cfg["coords"] == "minkowski":
+            P0 = inputs.linear_mode_state(cfg, dP, 1.0, amp=1e-4)
+        else:
+            P0 = inputs.torus_state(cfg, seed=2)
+        ctx = kh.Context(cfg, device=dev)
+        PB = ctx.to_device(P0)
+        P, B = PB[:5].clone(), PB[5:].clone()
+        U = ctx.empty(8)
+        ctx.prim_to_cons(P, B, U)
+        dt = 0.5 * ctx.cfl_dt(P, B)
+        ckpt = []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(nsteps):
+            ckpt.append((U.clone(), P.clone(), B.clone()))
+            ctx.step(U, P, B, dt, sync=False)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        fwd = e0.elapsed_time(e1)
+        gU = torch.zeros_like(U)
+        gU[0] = 1.0
+        gU[1] = -1.0
+        gP, gB = None, None
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for (Uc, Pc, Bc) in reversed(ckpt):
+            gU, gP, gB, _ = ctx.step_adjoint(Uc, Pc, Bc, dt, gU, gP, gB)
+        a1.record(stream)
+        torch.cuda.synchronize(dev)
+        adj = a0.elapsed_time(a1)
+        nz = cfg["n1"] * cfg["n2"] * cfg["n3"]
+        out[name] = {"steps": nsteps, "forward_ms_per_step": fwd / nsteps, "adjoint_ms_per_step": adj / nsteps,
+                     "adjoint_over_forward": adj / fwd, "zones": nz, "precision": "f64",
+                     "finite": bool(torch.isfinite(gP).all() and torch.isfinite(gB).all())}
+        ctx.close()
+    return out
+
+
 def roofline_of(prof, nz, precision):
     """Roofline of the kernel group with the largest share of the profiled
     step time: FP64-ALU bound (the update on both paths, the FP64 flux) with
@@ -442,6 +497,8 @@ def run_kh(args, world, rank, local):
         line[f"speedup_{head}_vs_{prec}"] = r["value"] / q["value"]
     if not args.no_smr and world == 1:
         line["smr"] = {p: measure_smr(args, dev, stream, p) for p in args.precisions}
+    if not args.no_adjoint and world == 1:
+        line["adjoint"] = measure_adjoint(args, dev, stream)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
