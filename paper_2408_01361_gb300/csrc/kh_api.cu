@@ -247,6 +247,8 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
   S.fl.bsq_u_max = c->bsq_u_max;
   S.fl.u_rho_max = c->u_rho_max;
   S.fl.gamma_max = c->gamma_max;
+  S.fl.ibsq_rho_max = 1.0 / c->bsq_rho_max;
+  S.fl.ibsq_u_max = 1.0 / c->bsq_u_max;
   S.c2p.max_iter = c->newton_max_iter > 0 ? c->newton_max_iter : 30;
   S.c2p.tol = c->newton_tol > 0.0 ? c->newton_tol : 1e-14;
 

@@ -515,7 +515,8 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
   S.cfl = c->cfl;
   S.recon = c->recon;
   for (int q = 0; q < 6; ++q) S.bc[q] = c->bc[q];
-  S.fl = FloorParams{c->rho_min, c->u_min, c->bsq_rho_max, c->bsq_u_max, c->u_rho_max, c->gamma_max};
+  S.fl = FloorParams{c->rho_min,       c->u_min,           c->bsq_rho_max,         c->bsq_u_max,
+                     c->u_rho_max,      c->gamma_max,       1.0 / c->bsq_rho_max,   1.0 / c->bsq_u_max};
   S.c2p.max_iter = c->newton_max_iter > 0 ? c->newton_max_iter : 30;
   S.c2p.tol = c->newton_tol > 0.0 ? c->newton_tol : 1e-14;
   x->cp = CoordParams{c->kind, a, c->x1min, c->hslope, c->poly_xt, c->poly_alpha, c->mks_smooth};

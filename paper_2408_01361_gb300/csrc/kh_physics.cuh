@@ -351,26 +351,35 @@ KH_HD int noble2d(const double* U, const Met<double>& m, double ig, double gam, 
 // ---------------------------------------------------------------------------
 struct FloorParams {
   double rho_min, u_min, bsq_rho_max, bsq_u_max, u_rho_max, gamma_max;
+  double ibsq_rho_max, ibsq_u_max;  // 1 / bsq_rho_max, 1 / bsq_u_max (set with them)
 };
 
 // rho_geo, u_geo: the geometric floors max(rho_min r^-3/2, 1e-20) and
 // max(u_min r^-5/2, 1e-20) of the zone (cached per (i, j)); bsq: b^2 of P.
+// q_est >= 0: an estimate of g_ij u~^i u~^j (= gamma^2 - 1) that only decides
+// whether the Lorentz-factor ceiling applies (the exact FP64 value is then
+// formed for the rescaling); q_est < 0: formed in FP64 here.
 KH_HD int apply_floors(const FloorParams& f, const Met<double>& m, double rho_geo, double u_geo, double bsq,
-                       double* P) {
+                       double* P, double q_est = -1.0) {
   double rf = rho_geo, uf = u_geo;
-  const double rb = bsq / f.bsq_rho_max, ub = bsq / f.bsq_u_max;
+  const double rb = bsq * f.ibsq_rho_max, ub = bsq * f.ibsq_u_max;
   rf = rf > rb ? rf : rb;
   uf = uf > ub ? uf : ub;
   int mask = 0;
   if (P[V_RHO] < rf) { P[V_RHO] = rf; mask |= 1; }
   if (P[V_U] < uf) { P[V_U] = uf; mask |= 1; }
   if (P[V_U] > f.u_rho_max * P[V_RHO]) { P[V_U] = f.u_rho_max * P[V_RHO]; mask |= 2; }
-  const double v1 = P[V_U1], v2 = P[V_U2], v3 = P[V_U3];
-  const double q = m.gcov[1][1] * v1 * v1 + m.gcov[2][2] * v2 * v2 + m.gcov[3][3] * v3 * v3 +
-                   2.0 * (m.gcov[1][2] * v1 * v2 + m.gcov[1][3] * v1 * v3 + m.gcov[2][3] * v2 * v3);
   // gamma^2 = 1 + q: compare squares, take a root only for the rare zone over the ceiling
   const double g2max = f.gamma_max * f.gamma_max;
-  if (1.0 + q > g2max) {
+  auto qexact = [&]() {
+    const double v1 = P[V_U1], v2 = P[V_U2], v3 = P[V_U3];
+    return m.gcov[1][1] * v1 * v1 + m.gcov[2][2] * v2 * v2 + m.gcov[3][3] * v3 * v3 +
+           2.0 * (m.gcov[1][2] * v1 * v2 + m.gcov[1][3] * v1 * v3 + m.gcov[2][3] * v2 * v3);
+  };
+  const double qt = q_est >= 0.0 ? q_est : qexact();
+  if (1.0 + qt > g2max * (q_est >= 0.0 ? 0.999 : 1.0)) {
+    const double q = q_est >= 0.0 ? qexact() : qt;
+    if (!(1.0 + q > g2max)) return mask;
     const double sc = sqrt((g2max - 1.0) / q);
     P[V_U1] *= sc;
     P[V_U2] *= sc;
@@ -435,8 +444,9 @@ KH_HD int noble2d_mixed(const double* U, const Met<double>& m, double ig, double
 #pragma unroll
   for (int mu = 0; mu < 4; ++mu)
     Qu[mu] = m.gcon[mu][0] * Qc[0] + m.gcon[mu][1] * Qc[1] + m.gcon[mu][2] * Qc[2] + m.gcon[mu][3] * Qc[3];
-  const double nu[4] = {-a * m.gcon[0][0], -a * m.gcon[1][0], -a * m.gcon[2][0], -a * m.gcon[3][0]};
-  const double Qdn = Qc[0] * nu[0] + Qc[1] * nu[1] + Qc[2] * nu[2] + Qc[3] * nu[3];
+  // n^mu = -alpha g^{mu t}, so Q.n = -alpha Q^t
+  const double nu[4] = {0.0, -a * m.gcon[1][0], -a * m.gcon[2][0], -a * m.gcon[3][0]};
+  const double Qdn = -a * Qu[0];
   const double Qsq = Qc[0] * Qu[0] + Qc[1] * Qu[1] + Qc[2] * Qu[2] + Qc[3] * Qu[3];
   const double Qtsq = fmax(Qsq + Qdn * Qdn, 0.0);
   const double Bc1 = aig * U[V_B1], Bc2 = aig * U[V_B2], Bc3 = aig * U[V_B3];

@@ -335,7 +335,9 @@ __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT
     FState<float> sf;
     fluid_state(q, mf, sf);
     const double rho0 = Pn[V_RHO], u0 = Pn[V_U];
-    fmask = apply_floors(S.fl, m, __ldg(G.flo + p), __ldg(G.flo + L.gplane + p), (double)sf.bsq, Pn);
+    const float gq = mf.alpha * sf.ucon[0];  // Lorentz factor: the FP32 estimate of gamma^2 - 1 gates the ceiling
+    fmask = apply_floors(S.fl, m, __ldg(G.flo + p), __ldg(G.flo + L.gplane + p), (double)sf.bsq, Pn,
+                         (double)fmaxf(gq * gq - 1.0f, 0.0f));
     if (fmask && Uout) {
       if (fmask & 4) {  // the Lorentz-factor ceiling changed u~: full FP64 recompute
         FState<double> s;
