@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libkharma_gb300.so")
-SOURCES = ["kh_kernels.cu", "kh_api.cu", "kh_noalloc.cu", "kh_mesh.cu", "kh_adjoint.cu"]
+SOURCES = ["kh_kernels.cu", "kh_api.cu", "kh_noalloc.cu", "kh_mesh.cu", "kh_adjoint.cu", "kh_flux_tma.cu"]
 HEADERS = ["kh_internal.h", "kh_physics.cuh", "kh_geom_math.h", "kh_zone.cuh", "kh_ctx.h", "kh_dual.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

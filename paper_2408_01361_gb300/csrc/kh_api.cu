@@ -147,7 +147,12 @@ int run_stage_mixed(kh_ctx* x, int st, const double* U0, const VarsT<TIN>& Pin, 
   mark(x, KH_T_BC, st, 1);
   for (int d = 1; d <= L.ndim; ++d) {
     mark(x, KH_T_FLUX1 + d - 1, st, 0);
-    n += launch_flux_dir<float, float>(d, cviewT(Pf), L, Gf, x->S, x->Ff[d - 1], x->ctopf[d - 1], x->tpb_flux, s);
+    // the stage input's 8 FP32 planes are contiguous (pnf or pstarf); a grid
+    // too small for the tile's tensor box takes the per-face kernel
+    int r = launch_flux_dir_tma(d, Pf.v[0], L, Gf, x->S, x->Ff[d - 1], x->ctopf[d - 1], x->counters, s);
+    if (r < 0)
+      r = launch_flux_dir<float, float>(d, cviewT(Pf), L, Gf, x->S, x->Ff[d - 1], x->ctopf[d - 1], x->tpb_flux, s);
+    n += r;
     mark(x, KH_T_FLUX1 + d - 1, st, 1);
   }
   mark(x, KH_T_CT, st, 0);
@@ -660,7 +665,7 @@ int kh_get_stats(kh_ctx* x, kh_stats* out) {
   out->nunfixed = (int64_t)h[CNT_UNFIXED];
   out->dt_cfl = dt;
   x->last = *out;
-  return KH_OK;
+  return h[CNT_TIMEOUT] ? KH_ETIMEOUT : KH_OK;
 }
 
 int kh_cfl_dt(kh_ctx* x, const double* P, const double* B, double* dt_cfl) {

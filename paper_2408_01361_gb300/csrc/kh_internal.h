@@ -62,7 +62,7 @@ struct Scheme {
 };
 
 // Counters kept on the device for one step.
-enum { CNT_FAIL = 0, CNT_FLOOR = 1, CNT_UNFIXED = 2, NCNT = 3 };
+enum { CNT_FAIL = 0, CNT_FLOOR = 1, CNT_UNFIXED = 2, CNT_TIMEOUT = 3, NCNT = 4 };
 
 // ---- launchers (kh_kernels.cu); each returns the number of kernels launched ----
 // Geometry of a grid whose first interior cell starts at native (x1o, x2o);
@@ -73,6 +73,11 @@ template <class T>
 int launch_bc(const VarsT<T>& P, const Layout& L, const Scheme& S, const T* dlo, const T* dhi, cudaStream_t s);
 // Reconstruction + LLF through x^D faces: stencil read in TIN, arithmetic and
 // outputs in R (FP64 path: double/double; mixed: double or float in, float out).
+// FP32 face fluxes from TMA-staged shared-memory tiles (kh_flux_tma.cu): P8
+// is the 8-plane FP32 stage input; returns -1 if the tensor map cannot be
+// encoded.
+int launch_flux_dir_tma(int D, const float* P8, const Layout& L, const GeomT<float>& G, const Scheme& S, float* F,
+                        float* ctop, unsigned long long* cnt, cudaStream_t s);
 template <class TIN, class R>
 int launch_flux_dir(int D, const CVarsT<TIN>& P, const Layout& L, const GeomT<R>& G, const Scheme& S, R* F, R* ctop,
                     int tpb, cudaStream_t s);
