@@ -434,6 +434,21 @@ KH_HD bool newton_wv(R D, R Qdn, R Qtsq, R Bsq, R QdB2, R gf, int max_iter, R st
   return false;
 }
 
+// FP64 values refined from FP32 seeds by one Newton step each (Newton's
+// iteration for the square root, s <- s + (x - s^2) / (2 s), and for the
+// reciprocal, r <- r + r (1 - y r)): the seed's relative error e (~6e-8)
+// becomes ~e^2, well below the mixed path's FP32 flux error. x and y must lie
+// in FP32's normal range (the callers scale them by powers of two).
+KH_HD double sqrt_from_f32(double x) {
+  const float sf = sqrtf((float)x);
+  const double s = (double)sf;
+  return s + (x - s * s) * (0.5 * (double)(1.0f / sf));
+}
+KH_HD double rcp_from_f32(double y) {
+  const double r = (double)(1.0f / (float)y);
+  return r + r * (1.0 - y * r);
+}
+
 KH_HD int noble2d_mixed(const double* U, const Met<double>& m, double ig, double gam, double igam, double gf,
                         const C2POpts& o, float W0, float vsq0, double* P) {
   const double a = m.alpha;
@@ -461,36 +476,74 @@ KH_HD int noble2d_mixed(const double* U, const Met<double>& m, double ig, double
   if (vsq > 1.0 - 1e-16) vsq = 1.0 - 1e-16;
 
   // FP32 phase on the problem scaled by S = 2^e ~ W
-  bool ok32 = false;
+  bool done = false;
+  double S = 1.0, iS = 1.0;
   {
     int e = 0;
     frexp(W, &e);
-    const double S = ldexp(1.0, e), iS = ldexp(1.0, -e);
+    S = ldexp(1.0, e);
+    iS = ldexp(1.0, -e);
+    const float Df = (float)(D * iS), Qnf = (float)(Qdn * iS), Qtf = (float)(Qtsq * iS * iS), Bf = (float)(Bsq * iS);
+    const float QBf = (float)(QdB2 * iS * iS * iS), gff = (float)gf;
     float Wf = (float)(W * iS), vf = (float)vsq, ef = 1.0f;
-    ok32 = newton_wv<float>((float)(D * iS), (float)(Qdn * iS), (float)(Qtsq * iS * iS), (float)(Bsq * iS),
-                            (float)(QdB2 * iS * iS * iS), (float)gf, 12, 3e-6f, Wf, vf, ef);
+    const bool ok32 = newton_wv<float>(Df, Qnf, Qtf, Bf, QBf, gff, 12, 3e-6f, Wf, vf, ef);
     if (ok32 || (isfinite(Wf) && isfinite(vf) && Wf > 0.0f && ef < 1e-3f)) {
       W = (double)Wf * S;
       vsq = (double)vf;
     }
+    if (ok32 && vf < 1.0f - 1e-6f) {
+      // One refinement: the residuals (f1, f2) in FP64 at the FP32 root,
+      // the correction through the FP32 Jacobian of the scaled system (f1
+      // scales as S^2, f2 as S): the Jacobian's FP32 error multiplies a
+      // step of ~1e-7, so the refined iterate is as good as an FP64 Newton
+      // step's. Accepted when the step is below 1e-5; else the FP64 loop.
+      const double x = 1.0 - vsq;
+      const double sg = sqrt_from_f32(x);
+      const double iW = rcp_from_f32(W * iS) * iS;
+      const double p = gf * (W * x - D * sg);
+      const double BW = Bsq + W;
+      const double iW2 = iW * iW;
+      const double f1 = Qtsq - vsq * BW * BW + QdB2 * (Bsq + 2.0 * W) * iW2;
+      const double f2 = Qdn + W - p + 0.5 * Bsq * (1.0 + vsq) - 0.5 * QdB2 * iW2;
+      // scaled FP32 Jacobian at (Wf, vf)
+      const float xg = 1.0f - vf, sgf = sqrtf(xg), BWf = Bf + Wf, iWf = 1.0f / Wf, iW3f = iWf * iWf * iWf;
+      const float j11 = -2.0f * vf * BWf - 2.0f * QBf * BWf * iW3f;
+      const float j12 = -BWf * BWf;
+      const float j21 = 1.0f - gff * xg + QBf * iW3f;
+      const float j22 = 0.5f * Bf - gff * (-Wf + 0.5f * Df / sgf);
+      const float idet = 1.0f / (j11 * j22 - j12 * j21);
+      const float g1 = (float)(f1 * iS * iS), g2 = (float)(f2 * iS);
+      const double dW = (double)((j22 * g1 - j12 * g2) * idet) * S;
+      const double dv = (double)((-j21 * g1 + j11 * g2) * idet);
+      const double Wn = W - dW, vn = vsq - dv;
+      if (Wn > 0.0 && vn >= 0.0 && vn < 1.0 - 1e-16) {
+        const double err = fabs(dW) * iW + fabs(dv);
+        W = Wn;
+        vsq = vn;
+        done = err < 1e-5;
+      }
+    }
   }
-  // FP64 phase: after a converged FP32 phase one FP64 step is accepted when
-  // it moves the iterate by less than 1e-5 (the accepted iterate's error is
-  // then of the order of that step squared); otherwise iterate to 1e-6.
-  double err = 1.0;
-  const bool conv = newton_wv<double>(D, Qdn, Qtsq, Bsq, QdB2, gf, o.max_iter, ok32 ? 1e-5 : 1e-6, W, vsq, err);
-  if (!conv && !(err < 1e-9)) return 1;
+  if (!done) {
+    double err = 1.0;
+    const bool conv = newton_wv<double>(D, Qdn, Qtsq, Bsq, QdB2, gf, o.max_iter, 1e-6, W, vsq, err);
+    if (!conv && !(err < 1e-9)) return 1;
+  }
   if (!(W > 0.0)) return 3;
   if (!(vsq < 1.0) || vsq < 0.0) return 2;
-  const double gamma = krsqrt(1.0 - vsq);
-  const double rho = D * ((1.0 - vsq) * gamma);
-  const double uint = (W * (1.0 - vsq) - rho) * igam;
+  // primitives from (W, v^2); roots and reciprocals refined from FP32 seeds
+  // (1 - v^2 >= 1e-16 and the scaled W (W + B^2) are in FP32's normal range)
+  const double x = 1.0 - vsq;
+  const double sg = sqrt_from_f32(x);  // 1 / Lorentz factor
+  const double gamma = rcp_from_f32(sg);
+  const double rho = D * sg;
+  const double uint = (W * x - rho) * igam;
   if (!(rho > 0.0)) return 4;
   if (!(uint >= 0.0)) return 5;
   P[V_RHO] = rho;
   P[V_U] = uint;
   const double BW = W + Bsq;
-  const double inv = 1.0 / (W * BW);  // one division for 1/W and gamma/(W + B^2)
+  const double inv = rcp_from_f32(W * BW * iS * iS) * iS * iS;  // 1 / (W (W + B^2))
   const double f = gamma * W * inv;
   const double iW = BW * inv;
   P[V_U1] = f * (Qu[1] + nu[1] * Qdn + QdB * Bc1 * iW);
