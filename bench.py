@@ -511,18 +511,18 @@ def run_kh(args, world, rank, local):
 # counts 2, DADD/DMUL/FADD/FMUL 1), and DRAM bytes (read + write) per zone
 # per launch. Launch totals at the bench size scale by the zone count.
 FP64_FLOPS_PER_ZONE: dict = {
-    ("mixed", "update"): 346.2,
-    ("fp64", "update"): 1000.5,
+    ("mixed", "update"): 215.0,  # stages 1 and 2 (214, 216)
+    ("fp64", "update"): 947.0,
     ("fp64", "flux_x1"): 2102.3, ("fp64", "flux_x2"): 2091.0, ("fp64", "flux_x3"): 2083.5,
 }
 FP32_FLOPS_PER_ZONE: dict = {
-    ("mixed", "flux_x1"): 1770.4, ("mixed", "flux_x2"): 1760.5, ("mixed", "flux_x3"): 1752.6,
+    ("mixed", "flux_x1"): 1530.0, ("mixed", "flux_x2"): 1611.0, ("mixed", "flux_x3"): 1677.0,
 }
 DRAM_BYTES_PER_ZONE: dict = {
-    ("mixed", "update"): 282.6,  # mean of stage 1 (245.6) and stage 2 (319.5)
-    ("mixed", "flux_x1"): 42.4, ("mixed", "flux_x2"): 46.9, ("mixed", "flux_x3"): 48.4,
-    ("fp64", "update"): 419.0,  # stage 1
-    ("fp64", "flux_x1"): 118.1, ("fp64", "flux_x2"): 125.3, ("fp64", "flux_x3"): 127.7,
+    ("mixed", "update"): 282.6,  # mean of stage 1 (245.4) and stage 2 (319.5)
+    ("mixed", "flux_x1"): 44.4, ("mixed", "flux_x2"): 46.0, ("mixed", "flux_x3"): 47.7,
+    ("fp64", "update"): 419.1,  # stage 1
+    ("fp64", "flux_x1"): 118.0, ("fp64", "flux_x2"): 126.1, ("fp64", "flux_x3"): 128.3,
 }
 # FP32 peak from unit counts: 152 SMs x 128 lanes x 2 flop/clk x max SM clock
 # (a probe measured 74.7 TFLOP/s at 2070 MHz).
