@@ -24,6 +24,7 @@
 
 #include "kh_ctx.h"
 #include "kh_dual.cuh"
+#include "kh_face_vjp.cuh"
 #include "kh_zone.cuh"
 
 using namespace kh;
@@ -188,7 +189,7 @@ __global__ void __launch_bounds__(ATPB) k_adj_out(CVars gP, const double* gU, co
 // ---- reverse of the update's base and sources: gU_in += lu; sources ----
 __global__ void __launch_bounds__(ATPB) k_adj_src(const double* lu, CVars Ph, Layout L, DevGeom G, Scheme S,
                                                  const double* dtp, double coef, double* gU_in, double* lp,
-                                                 double* gsum) {
+                                                 double* gsum, int has_sources) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   double dg = 0.0;
   if (t < nzones(L)) {
@@ -206,7 +207,7 @@ __global__ void __launch_bounds__(ATPB) k_adj_src(const double* lu, CVars Ph, La
       ls[v] = cdt * x;
       any |= (v >= V_U && v <= V_U3 && x != 0.0);
     }
-    if (any) {
+    if (any && has_sources) {
       D9 Pd[NV], Sd[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
@@ -373,31 +374,9 @@ __global__ void k_adj_ctf(double* lf, const double* le1, const double* le2, cons
 }
 
 // ---- reverse of reconstruction + LLF at one face ----
-// Gradient of g(P_side, gamma) = sum_v lam_v (F_side_v / 2 +- ct U_side_v / 2)
-// (+ lam_ct * the active speed if it belongs to this side), ct held fixed.
-template <int D>
-__device__ __forceinline__ void side_grad(const double* Pside, const Met<double>& m, double gam, const double* lam,
-                                         double ct, double sgn, int active, double lct, double* g) {
-  D9 Pd[NV];
-#pragma unroll
-  for (int v = 0; v < NV; ++v) Pd[v] = D9::var(Pside[v], v);
-  const D9 gd = D9::var(gam, 8);
-  FState<D9> s;
-  fluid_state(Pd, m, s);
-  D9 F[NV], U[NV];
-  flux_cons(Pd, s, m, gd, D, F, U);
-  D9 acc(0.0);
-#pragma unroll
-  for (int v = 0; v < NV; ++v) acc += lam[v] * (0.5 * F[v] + (0.5 * sgn * ct) * U[v]);
-  if (active) {
-    D9 cmax, cmin;
-    signal_speeds(Pd, s, m, gd, D, cmax, cmin);
-    acc += lct * (active > 0 ? cmax : -cmin);
-  }
-#pragma unroll
-  for (int q = 0; q < 9; ++q) g[q] = acc.d[q];
-}
-
+// Each side's gradient comes from side_grad_rev (kh_face_vjp.cuh, written
+// reverse mode); side_grad_dual there is the dual-number evaluation of the
+// same quantity that a host test compares it with.
 template <int D, int RECON>
 __global__ void __launch_bounds__(AFPB) k_adj_face(CVars Ph, const double* lf, Layout L, DevGeom G, Scheme S,
                                                   FaceBox box, int polar_lo, int polar_hi, double* lp, double* gsum) {
@@ -405,7 +384,14 @@ __global__ void __launch_bounds__(AFPB) k_adj_face(CVars Ph, const double* lf, L
   double dg = 0.0;
   if (t < (unsigned)box.n[0] * box.n[1] * box.n[2]) {
     int i, j, k;
-    split3(t, box.n[0], box.n[1], i, j, k);
+    // x1 faces run with x2 fastest, so that the lanes of a warp scatter into
+    // different cells (with x1 fastest, neighbouring lanes' 6-cell stencils
+    // overlap and their atomics serialise)
+    if (D == 1) {
+      split3(t, box.n[1], box.n[0], j, i, k);
+    } else {
+      split3(t, box.n[0], box.n[1], i, j, k);
+    }
     i += box.lo[0];
     j += box.lo[1];
     k += box.lo[2];
@@ -473,8 +459,8 @@ __global__ void __launch_bounds__(AFPB) k_adj_face(CVars Ph, const double* lf, L
 #pragma unroll
       for (int v = 0; v < NV; ++v) lct -= 0.5 * lam[v] * (UR[v] - UL[v]);
       double gl[9], gr[9];
-      side_grad<D>(PL, m, S.gam, lam, ct, +1.0, side_act == 1 ? (use_m ? 1 : -1) : 0, lct, gl);
-      side_grad<D>(PR, m, S.gam, lam, ct, -1.0, side_act == 2 ? (use_m ? 1 : -1) : 0, lct, gr);
+      side_grad_rev(PL, m, S.gam, lam, 0.5 * ct, D, side_act == 1 ? (use_m ? 1 : -1) : 0, lct, gl);
+      side_grad_rev(PR, m, S.gam, lam, -0.5 * ct, D, side_act == 2 ? (use_m ? 1 : -1) : 0, lct, gr);
       dg += gl[8] + gr[8];
       for (int v = 0; v < NV; ++v) {
         double* dst = lp + v * L.plane + c;
@@ -665,7 +651,8 @@ void reverse_stage(kh_ctx* x, const CVars& Ph, double coef, const double* seed, 
   const DevGeom G{x->geo, x->conn, x->flo};
   const long long nz = (long long)L.n1 * L.n2 * L.n3;
   cudaMemsetAsync(lp, 0, NV * L.plane * sizeof(double), s);
-  k_adj_src<<<nb(nz, ATPB), ATPB, 0, s>>>(lu, Ph, L, G, x->S, x->dscalar + 3, coef, gU_in, lp, x->adj_red);
+  k_adj_src<<<nb(nz, ATPB), ATPB, 0, s>>>(lu, Ph, L, G, x->S, x->dscalar + 3, coef, gU_in, lp, x->adj_red,
+                                          x->c.kind != KH_MINKOWSKI);
   cudaMemsetAsync(lf, 0, 3 * NV * L.plane * sizeof(double), s);
   cudaMemsetAsync(le, 0, 3 * L.plane * sizeof(double), s);
   launch_div_ct<1>(x, lu, lf, coef, seed, s);
