@@ -26,10 +26,11 @@ RECON = {"mc": 0, "weno5": 1}
 
 
 def build(force: bool = False) -> str:
-    """Compile liboracle.so in place (plain g++, OpenMP, no CPU-specific flags)."""
+    """Compile liboracle.so in place (plain g++, OpenMP, no CPU-specific flags;
+    no fused multiply-add contraction, so that it rounds alike on every host)."""
     newest = max(os.path.getmtime(p) for p in _SRC)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
-        cmd = ["g++", "-std=c++17", "-O3", "-fopenmp", "-fPIC", "-shared", "-o", _LIB_PATH,
+        cmd = ["g++", "-std=c++17", "-O3", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-o", _LIB_PATH,
                os.path.join(_HERE, "harm_oracle.cpp")]
         subprocess.run(cmd, check=True)
     return _LIB_PATH
@@ -104,6 +105,9 @@ def lib():
         L.or_cfl_dt.restype = C.c_double
         L.or_step.argtypes = [PP, _dp, _dp, C.c_double, C.c_void_p, C.c_void_p, C.POINTER(C.c_long)]
         L.or_step.restype = C.c_double
+        L.or_step_jvp.argtypes = [PP, _dp, _dp, _dp, _dp, C.c_double, C.c_double, C.c_void_p, C.c_void_p,
+                                  C.c_void_p, C.c_void_p, C.POINTER(C.c_long)]
+        L.or_step_jvp.restype = C.c_double
         L.or_evolve.argtypes = [PP, _dp, _dp, C.c_int, C.c_double, C.c_double, C.c_void_p, C.c_void_p,
                                 C.POINTER(C.c_long)]
         L.or_evolve.restype = C.c_double
@@ -219,6 +223,26 @@ def step(cfg: dict, U, P, dt: float, dirichlet=None):
     st = (C.c_long * 3)()
     dtn = lib().or_step(C.byref(params(cfg)), U, P, float(dt), _ptr(lo), _ptr(hi), st)
     return U, P, dtn, list(st)
+
+
+def step_jvp(cfg: dict, U, P, dU, dP, dgam: float, dt: float, dirichlet=None, flux: bool = False):
+    """One step and its directional derivative (dual numbers through the same
+    stages; dt fixed). Returns (U, P, dU, dP, dt_next, stats, zflag) -- zflag
+    per zone: 1 = an inversion failed (fixed up, frozen), 2 = a floor acted --
+    and, with flux=True, also the tangent of the stage-2 x1 fluxes (cell
+    layout)."""
+    U = np.array(U, dtype=np.float64, order="C", copy=True)
+    P = np.array(P, dtype=np.float64, order="C", copy=True)
+    dU = np.array(dU, dtype=np.float64, order="C", copy=True)
+    dP = np.array(dP, dtype=np.float64, order="C", copy=True)
+    dF1 = np.zeros_like(P) if flux else None
+    zflag = np.zeros(P.shape[1:], dtype=np.int32)
+    lo, hi = (dirichlet or (None, None))
+    st = (C.c_long * 3)()
+    dtn = lib().or_step_jvp(C.byref(params(cfg)), U, P, dU, dP, float(dgam), float(dt), _ptr(lo), _ptr(hi),
+                            _ptr(dF1), _ptr(zflag), st)
+    out = (U, P, dU, dP, dtn, list(st), zflag)
+    return out + (dF1,) if flux else out
 
 
 def evolve(cfg: dict, U, P, nsteps: int, dt: float, t_end: float = 0.0, dirichlet=None):

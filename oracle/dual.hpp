@@ -54,11 +54,16 @@ template <class T> inline bool operator<=(const Dual<T>& a, double b) { return v
 template <class T> inline bool operator>=(const Dual<T>& a, double b) { return val(a) >= b; }
 template <class T> inline bool operator<(double a, const Dual<T>& b) { return a < val(b); }
 template <class T> inline bool operator>(double a, const Dual<T>& b) { return a > val(b); }
+template <class T> inline bool operator==(const Dual<T>& a, double b) { return val(a) == b; }
+template <class T> inline bool operator!=(const Dual<T>& a, double b) { return val(a) != b; }
 
 // Elementary functions: chain rule on each.
+// At 0 the square root takes a zero derivative (the value of a clamped
+// argument, e.g. a discriminant held at 0, carries no tangent).
 template <class T> inline Dual<T> sqrt(const Dual<T>& a) {
   using std::sqrt;
   T s = sqrt(a.v);
+  if (val(s) == 0.0) return mk<T>(s, T(0.0));
   return mk<T>(s, a.d / (2.0 * s));
 }
 template <class T> inline Dual<T> sin(const Dual<T>& a) {

@@ -91,7 +91,8 @@ double radius_at(const Grid& gr, int j, int i) {
 //   polar:    reflect across the face, flipping the sign of u~2 and B2;
 //   dirichlet: copy caller-supplied ghost values (x1 faces only).
 // ---------------------------------------------------------------------------
-void apply_bc(const Grid& gr, double* P, const double* dir_lo, const double* dir_hi) {
+template <class R>
+void apply_bc(const Grid& gr, R* P, const double* dir_lo, const double* dir_hi) {
   const GridInfo& g = gr.g;
   const int ng = g.ng;
   // x1
@@ -103,27 +104,27 @@ void apply_bc(const Grid& gr, double* P, const double* dir_lo, const double* dir
           int bc = gr.c.bc[side];
           int ig = side == 0 ? ilo : ihi;
           for (int v = 0; v < NVAR; ++v) {
-            double val = 0.0;
+            R x(0.0);
             if (bc == BC_PERIODIC) {
               int src = side == 0 ? ig + g.n1 : ig - g.n1;
-              val = P[gr.idx(v, k, j, src)];
+              x = P[gr.idx(v, k, j, src)];
             } else if (bc == BC_OUTFLOW) {
               int src = side == 0 ? ng : ng + g.n1 - 1;
-              val = P[gr.idx(v, k, j, src)];
+              x = P[gr.idx(v, k, j, src)];
             } else if (bc == BC_DIRICHLET) {
               const double* D = side == 0 ? dir_lo : dir_hi;
               int ii = side == 0 ? ig : ig - (ng + g.n1);  // 0..ng-1
-              val = D[((static_cast<size_t>(v) * g.N3 + k) * g.N2 + j) * ng + ii];
+              x = R(D[((static_cast<size_t>(v) * g.N3 + k) * g.N2 + j) * ng + ii]);
             } else {  // polar reflection across an x1 face is not meaningful; copy
               int src = side == 0 ? 2 * ng - 1 - ig : 2 * (ng + g.n1) - 1 - ig;
-              val = P[gr.idx(v, k, j, src)];
+              x = P[gr.idx(v, k, j, src)];
             }
-            P[gr.idx(v, k, j, ig)] = val;
+            P[gr.idx(v, k, j, ig)] = x;
           }
           if (bc == BC_OUTFLOW) {
-            double& u1 = P[gr.idx(U1, k, j, ig)];
-            if (side == 0 && u1 > 0.0) u1 = 0.0;
-            if (side == 1 && u1 < 0.0) u1 = 0.0;
+            R& u1 = P[gr.idx(U1, k, j, ig)];
+            if (side == 0 && u1 > 0.0) u1 = R(0.0);
+            if (side == 1 && u1 < 0.0) u1 = R(0.0);
           }
         }
       }
@@ -143,9 +144,9 @@ void apply_bc(const Grid& gr, double* P, const double* dir_lo, const double* dir
           else  // polar
             src = side == 0 ? 2 * ng - 1 - jg : 2 * (ng + g.n2) - 1 - jg;
           for (int v = 0; v < NVAR; ++v) {
-            double val = P[gr.idx(v, k, src, i)];
-            if (bc == BC_POLAR && (v == U2 || v == B2)) val = -val;
-            P[gr.idx(v, k, jg, i)] = val;
+            R x = P[gr.idx(v, k, src, i)];
+            if (bc == BC_POLAR && (v == U2 || v == B2)) x = -x;
+            P[gr.idx(v, k, jg, i)] = x;
           }
         }
       }
@@ -175,10 +176,11 @@ void apply_bc(const Grid& gr, double* P, const double* dir_lo, const double* dir
 // F[d] has the cell layout; F[d] at (k,j,i) is the flux through the lower
 // x^d face of cell (k,j,i). ctop[d] likewise.
 // ---------------------------------------------------------------------------
-struct Fluxes {
-  std::vector<double> F[3];
-  std::vector<double> ctop[3];
+template <class R> struct FluxesT {
+  std::vector<R> F[3];
+  std::vector<double> ctop[3];  // signal speeds (values only: they set dt)
 };
+using Fluxes = FluxesT<double>;
 
 void face_range(const Grid& gr, int d, int lo[3], int hi[3]) {
   // inclusive ranges in (i, j, k) order
@@ -192,11 +194,12 @@ void face_range(const Grid& gr, int d, int lo[3], int hi[3]) {
   }
 }
 
-void compute_fluxes(const Grid& gr, const double* P, Fluxes& fx) {
+template <class R>
+void compute_fluxes(const Grid& gr, const R* P, FluxesT<R>& fx, const R& gam) {
   const GridInfo& g = gr.g;
   const size_t n = gr.cells();
   for (int d = 0; d < 3; ++d) {
-    fx.F[d].assign(NVAR * n, 0.0);
+    fx.F[d].assign(NVAR * n, R(0.0));
     fx.ctop[d].assign(n, 0.0);
   }
   for (int d = 0; d < g.ndim; ++d) {
@@ -207,26 +210,26 @@ void compute_fluxes(const Grid& gr, const double* P, Fluxes& fx) {
     for (int k = lo[2]; k <= hi[2]; ++k)
       for (int j = lo[1]; j <= hi[1]; ++j)
         for (int i = lo[0]; i <= hi[0]; ++i) {
-          double PL[NVAR], PR[NVAR];
+          R PL[NVAR], PR[NVAR];
           for (int v = 0; v < NVAR; ++v) {
             // stencil of the cell below the face (c = -1) and above it (c = 0)
-            double qm[5], qp[5];
+            R qm[5], qp[5];
             for (int s = 0; s < 5; ++s) {
               int o1 = (d == 0) ? s - 3 : 0, o2 = (d == 1) ? s - 3 : 0, o3 = (d == 2) ? s - 3 : 0;
               qm[s] = P[gr.idx(v, k + o3, j + o2, i + o1)];
               int p1 = (d == 0) ? s - 2 : 0, p2 = (d == 1) ? s - 2 : 0, p3 = (d == 2) ? s - 2 : 0;
               qp[s] = P[gr.idx(v, k + p3, j + p2, i + p1)];
             }
-            double lo_m, hi_m, lo_p, hi_p;
+            R lo_m, hi_m, lo_p, hi_p;
             recon_cell(gr.c.recon, qm, lo_m, hi_m);
             recon_cell(gr.c.recon, qp, lo_p, hi_p);
             PL[v] = hi_m;
             PR[v] = lo_p;
           }
-          double F[NVAR], ct;
-          llf_flux<double>(PL, PR, gr.G(loc, j, i), gr.c.gam, d + 1, F, ct);
+          R F[NVAR], ct;
+          llf_flux<R>(PL, PR, gr.G(loc, j, i), gam, d + 1, F, ct);
           for (int v = 0; v < NVAR; ++v) fx.F[d][gr.idx(v, k, j, i)] = F[v];
-          fx.ctop[d][gr.idx(0, k, j, i)] = ct;
+          fx.ctop[d][gr.idx(0, k, j, i)] = val(ct);
         }
   }
   // Polar axis: no flux of anything through an x2 face lying on the axis.
@@ -238,15 +241,15 @@ void compute_fluxes(const Grid& gr, const double* P, Fluxes& fx) {
       int j = side == 0 ? gr.s2() : gr.e2();
       for (int k = lo[2]; k <= hi[2]; ++k)
         for (int i = lo[0]; i <= hi[0]; ++i)
-          for (int v = 0; v < NVAR; ++v) fx.F[1][gr.idx(v, k, j, i)] = 0.0;
+          for (int v = 0; v < NVAR; ++v) fx.F[1][gr.idx(v, k, j, i)] = R(0.0);
     }
   }
   // Flux-CT (Toth 2000): corner EMFs as averages of the four adjacent face
   // fluxes of the field, then field fluxes as averages of the edge EMFs.
-  std::vector<double>& F1 = fx.F[0];
-  std::vector<double>& F2 = fx.F[1];
-  std::vector<double>& F3 = fx.F[2];
-  std::vector<double> e1(n, 0.0), e2(n, 0.0), e3(n, 0.0);
+  std::vector<R>& F1 = fx.F[0];
+  std::vector<R>& F2 = fx.F[1];
+  std::vector<R>& F3 = fx.F[2];
+  std::vector<R> e1(n, R(0.0)), e2(n, R(0.0)), e3(n, R(0.0));
   auto I = [&](int k, int j, int i) { return gr.idx(0, k, j, i); };
   auto V = [&](int v, int k, int j, int i) { return gr.idx(v, k, j, i); };
   if (g.ndim == 2) {
@@ -256,13 +259,13 @@ void compute_fluxes(const Grid& gr, const double* P, Fluxes& fx) {
         e3[I(k, j, i)] = 0.25 * (F1[V(B2, k, j, i)] + F1[V(B2, k, j - 1, i)] - F2[V(B1, k, j, i)] - F2[V(B1, k, j, i - 1)]);
     for (int j = gr.s2(); j < gr.e2(); ++j)
       for (int i = gr.s1(); i <= gr.e1(); ++i) {
-        F1[V(B1, k, j, i)] = 0.0;
+        F1[V(B1, k, j, i)] = R(0.0);
         F1[V(B2, k, j, i)] = 0.5 * (e3[I(k, j, i)] + e3[I(k, j + 1, i)]);
       }
     for (int j = gr.s2(); j <= gr.e2(); ++j)
       for (int i = gr.s1(); i < gr.e1(); ++i) {
         F2[V(B1, k, j, i)] = -0.5 * (e3[I(k, j, i)] + e3[I(k, j, i + 1)]);
-        F2[V(B2, k, j, i)] = 0.0;
+        F2[V(B2, k, j, i)] = R(0.0);
       }
     return;
   }
@@ -282,7 +285,7 @@ void compute_fluxes(const Grid& gr, const double* P, Fluxes& fx) {
   for (int k = gr.s3(); k < gr.e3(); ++k)
     for (int j = gr.s2(); j < gr.e2(); ++j)
       for (int i = gr.s1(); i <= gr.e1(); ++i) {
-        F1[V(B1, k, j, i)] = 0.0;
+        F1[V(B1, k, j, i)] = R(0.0);
         F1[V(B2, k, j, i)] = 0.5 * (e3[I(k, j, i)] + e3[I(k, j + 1, i)]);
         F1[V(B3, k, j, i)] = -0.5 * (e2[I(k, j, i)] + e2[I(k + 1, j, i)]);
       }
@@ -290,7 +293,7 @@ void compute_fluxes(const Grid& gr, const double* P, Fluxes& fx) {
     for (int j = gr.s2(); j <= gr.e2(); ++j)
       for (int i = gr.s1(); i < gr.e1(); ++i) {
         F2[V(B1, k, j, i)] = -0.5 * (e3[I(k, j, i)] + e3[I(k, j, i + 1)]);
-        F2[V(B2, k, j, i)] = 0.0;
+        F2[V(B2, k, j, i)] = R(0.0);
         F2[V(B3, k, j, i)] = 0.5 * (e1[I(k, j, i)] + e1[I(k + 1, j, i)]);
       }
   for (int k = gr.s3(); k <= gr.e3(); ++k)
@@ -298,7 +301,7 @@ void compute_fluxes(const Grid& gr, const double* P, Fluxes& fx) {
       for (int i = gr.s1(); i < gr.e1(); ++i) {
         F3[V(B1, k, j, i)] = 0.5 * (e2[I(k, j, i)] + e2[I(k, j, i + 1)]);
         F3[V(B2, k, j, i)] = -0.5 * (e1[I(k, j, i)] + e1[I(k, j + 1, i)]);
-        F3[V(B3, k, j, i)] = 0.0;
+        F3[V(B3, k, j, i)] = R(0.0);
       }
 }
 
@@ -333,10 +336,98 @@ int apply_floors(const Params& c, const Geo& G, double r, double P[NVAR]) {
   return flag;
 }
 
-void p2c_point(const Params& c, const Geo& G, const double P[NVAR], double U[NVAR]) {
-  FluidState<double> S;
+template <class R>
+void p2c_at(const Geo& G, const R P[NVAR], const R& gam, R U[NVAR]) {
+  FluidState<R> S;
   fluid_state(P, G, S);
-  prim_to_flux<double>(P, S, G, c.gam, 0, U);
+  prim_to_flux<R>(P, S, G, gam, 0, U);
+}
+
+void p2c_point(const Params& c, const Geo& G, const double P[NVAR], double U[NVAR]) { p2c_at<double>(G, P, c.gam, U); }
+
+// ---------------------------------------------------------------------------
+// Tangent (forward-mode) versions of the two non-smooth point operations, for
+// the step templated on Dual<double>. Values are always those of the plain
+// FP64 operations above; only the derivative rules are added here.
+// ---------------------------------------------------------------------------
+using Dd = Dual<double>;
+
+int invert_point(const double U[NVAR], const Geo& G, const double& gam, double P[NVAR]) {
+  return cons_to_prim_point(U, G, gam, P);
+}
+
+// Solve A x = b (n x n, row-major) by Gaussian elimination with partial
+// pivoting. Returns false on a zero pivot.
+bool solve_dense(int n, double* A, double* b) {
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(A[r * n + c]) > std::fabs(A[piv * n + c])) piv = r;
+    if (A[piv * n + c] == 0.0) return false;
+    if (piv != c) {
+      for (int q = 0; q < n; ++q) std::swap(A[c * n + q], A[piv * n + q]);
+      std::swap(b[c], b[piv]);
+    }
+    for (int r = c + 1; r < n; ++r) {
+      const double f = A[r * n + c] / A[c * n + c];
+      for (int q = c; q < n; ++q) A[r * n + q] -= f * A[c * n + q];
+      b[r] -= f * b[c];
+    }
+  }
+  for (int c = n - 1; c >= 0; --c) {
+    double acc = b[c];
+    for (int q = c + 1; q < n; ++q) acc -= A[c * n + q] * b[q];
+    b[c] = acc / A[c * n + c];
+  }
+  return true;
+}
+
+// Inversion of a dual U: the value from the FP64 bracketed inversion; the
+// tangent of the root from the implicit-function theorem on p2c(P) = U. With
+// J = d(U fluid slots)/d(P fluid slots) at the root (dual numbers, one column
+// per primitive) and r = the response of the same slots to the tangents of B
+// and of the adiabatic index at fixed fluid primitives,
+//   J dP_fluid = dU_fluid - r;   B = U_B / sqrt(-g) directly.
+int invert_point(const Dd U[NVAR], const Geo& G, const Dd& gam, Dd P[NVAR]) {
+  double u[NVAR], p[NVAR];
+  for (int v = 0; v < NVAR; ++v) {
+    u[v] = U[v].v;
+    p[v] = P[v].v;
+  }
+  const int flag = cons_to_prim_point(u, G, gam.v, p);
+  for (int b = 0; b < 3; ++b) P[B1 + b] = U[B1 + b] / G.gdet;
+  if (flag) {
+    for (int v = 0; v < 5; ++v) P[v] = Dd(p[v]);
+    return flag;
+  }
+  double J[25];
+  Dd Pd[NVAR], Ud[NVAR];
+  for (int q = 0; q < 5; ++q) {
+    for (int v = 0; v < NVAR; ++v) Pd[v] = mk<double>(p[v], v == q ? 1.0 : 0.0);
+    p2c_at<Dd>(G, Pd, Dd(gam.v), Ud);
+    for (int f = 0; f < 5; ++f) J[f * 5 + q] = Ud[f].d;
+  }
+  for (int v = 0; v < NVAR; ++v) Pd[v] = mk<double>(p[v], v >= B1 ? P[v].d : 0.0);
+  p2c_at<Dd>(G, Pd, gam, Ud);
+  double x[5];
+  for (int f = 0; f < 5; ++f) x[f] = U[f].d - Ud[f].d;
+  if (!solve_dense(5, J, x))
+    for (int f = 0; f < 5; ++f) x[f] = 0.0;
+  for (int f = 0; f < 5; ++f) P[f] = mk<double>(p[f], x[f]);
+  return 0;
+}
+
+int floors_point(const Params& c, const Geo& G, double r, double P[NVAR]) { return apply_floors(c, G, r, P); }
+
+// Floors on a dual state: values as apply_floors; a component that a floor or
+// ceiling changed is frozen (it keeps the new value with a zero tangent).
+int floors_point(const Params& c, const Geo& G, double r, Dd P[NVAR]) {
+  double p[NVAR];
+  for (int v = 0; v < NVAR; ++v) p[v] = P[v].v;
+  const int flag = apply_floors(c, G, r, p);
+  for (int v = 0; v < 5; ++v)
+    if (p[v] != P[v].v) P[v] = Dd(p[v]);
+  return flag;
 }
 
 struct StageStats {
@@ -346,10 +437,13 @@ struct StageStats {
 // One stage: Pin (ghosts filled) -> fluxes -> Uout = U0 + cdt (-div F + S(Pin))
 // -> inversion (guess Pin) -> floors -> fixup. Writes Pout (interior) and Uout
 // (interior; consistent with Pout wherever floors or fixups changed Pout).
-void stage(const Grid& gr, const double* U0, const double* Pin, double cdt, double* Uout, double* Pout,
-           Fluxes& fx, StageStats& st, std::vector<int>* pflag_out) {
+// R = Dual<double> carries a tangent through the same operations; a zone that
+// failed its inversion and was fixed up is frozen (zero tangent).
+template <class R>
+void stage(const Grid& gr, const R* U0, const R* Pin, const R& gam, double cdt, R* Uout, R* Pout,
+           FluxesT<R>& fx, StageStats& st, std::vector<int>* pflag_out, std::vector<int>* fflag_out = nullptr) {
   const GridInfo& g = gr.g;
-  compute_fluxes(gr, Pin, fx);
+  compute_fluxes(gr, Pin, fx, gam);
   std::vector<int> pflag(gr.cells(), 0), fflag(gr.cells(), 0);
   const double dx[3] = {g.dx1, g.dx2, g.dx3};
 #pragma omp parallel for collapse(2) schedule(static)
@@ -357,11 +451,11 @@ void stage(const Grid& gr, const double* U0, const double* Pin, double cdt, doub
     for (int j = gr.s2(); j < gr.e2(); ++j)
       for (int i = gr.s1(); i < gr.e1(); ++i) {
         const Geo& G = gr.G(LOC_CENT, j, i);
-        double P[NVAR], S[NVAR], U[NVAR];
+        R P[NVAR], S[NVAR], U[NVAR];
         for (int v = 0; v < NVAR; ++v) P[v] = Pin[gr.idx(v, k, j, i)];
-        source_terms<double>(P, G, gr.C(j, i), gr.c.gam, S);
+        source_terms<R>(P, G, gr.C(j, i), gam, S);
         for (int v = 0; v < NVAR; ++v) {
-          double div = 0.0;
+          R div(0.0);
           for (int d = 0; d < g.ndim; ++d) {
             int o1 = d == 0, o2 = d == 1, o3 = d == 2;
             div += (fx.F[d][gr.idx(v, k + o3, j + o2, i + o1)] - fx.F[d][gr.idx(v, k, j, i)]) / dx[d];
@@ -369,12 +463,12 @@ void stage(const Grid& gr, const double* U0, const double* Pin, double cdt, doub
           U[v] = U0[gr.idx(v, k, j, i)] + cdt * (-div + S[v]);
         }
         // guess = stage input
-        int flag = cons_to_prim_point(U, G, gr.c.gam, P);
+        int flag = invert_point(U, G, gam, P);
         size_t c = gr.idx(0, k, j, i);
         pflag[c] = flag;
         if (flag == 0) {
-          fflag[c] = apply_floors(gr.c, G, radius_at(gr, j, i), P);
-          if (fflag[c]) p2c_point(gr.c, G, P, U);
+          fflag[c] = floors_point(gr.c, G, radius_at(gr, j, i), P);
+          if (fflag[c]) p2c_at<R>(G, P, gam, U);
         } else {
           for (int v = 0; v < 5; ++v) P[v] = Pin[gr.idx(v, k, j, i)];  // provisional, replaced by fixup
         }
@@ -405,11 +499,11 @@ void stage(const Grid& gr, const double* U0, const double* Pin, double cdt, doub
               if (kk < gr.s3() || kk >= gr.e3() || jj < gr.s2() || jj >= gr.e2() || ii < gr.s1() || ii >= gr.e1())
                 continue;
               if (pflag[gr.idx(0, kk, jj, ii)] != 0) continue;
-              for (int v = 0; v < 5; ++v) sum[v] += Pout[gr.idx(v, kk, jj, ii)];
+              for (int v = 0; v < 5; ++v) sum[v] += val(Pout[gr.idx(v, kk, jj, ii)]);
               ++cnt;
             }
         double P[NVAR];
-        for (int v = 0; v < NVAR; ++v) P[v] = Pout[gr.idx(v, k, j, i)];
+        for (int v = 0; v < NVAR; ++v) P[v] = val(Pout[gr.idx(v, k, j, i)]);
         if (cnt > 0)
           for (int v = 0; v < 5; ++v) P[v] = sum[v] / cnt;
         else
@@ -427,18 +521,20 @@ void stage(const Grid& gr, const double* U0, const double* Pin, double cdt, doub
   for (size_t w = 0; w < where.size(); ++w) {
     size_t c = where[w];
     for (int v = 0; v < NVAR; ++v) {
-      Pout[c + static_cast<size_t>(v) * gr.cells()] = fixed[w * 16 + 2 * v];
-      Uout[c + static_cast<size_t>(v) * gr.cells()] = fixed[w * 16 + 2 * v + 1];
+      Pout[c + static_cast<size_t>(v) * gr.cells()] = R(fixed[w * 16 + 2 * v]);
+      Uout[c + static_cast<size_t>(v) * gr.cells()] = R(fixed[w * 16 + 2 * v + 1]);
     }
   }
   for (size_t c = 0; c < gr.cells(); ++c)
     if (fflag[c]) st.nfloor++;
   if (pflag_out) *pflag_out = pflag;
+  if (fflag_out) *fflag_out = fflag;
 }
 
 // CFL time step from the stage fluxes' signal speeds:
 // dt = cfl * min_zones 1 / sum_d (ctop_d / dx_d), ctop_d = max over the zone's two x^d faces.
-double cfl_dt(const Grid& gr, const Fluxes& fx) {
+template <class R>
+double cfl_dt(const Grid& gr, const FluxesT<R>& fx) {
   const GridInfo& g = gr.g;
   const double dx[3] = {g.dx1, g.dx2, g.dx3};
   double best = std::numeric_limits<double>::infinity();
@@ -576,7 +672,7 @@ void or_fluxes(const or_params* c, const double* P, double* F1, double* F2, doub
   Grid gr;
   build_grid(*c, gr);
   Fluxes fx;
-  compute_fluxes(gr, P, fx);
+  compute_fluxes(gr, P, fx, c->gam);
   double* Fo[3] = {F1, F2, F3};
   double* Co[3] = {ct1, ct2, ct3};
   for (int d = 0; d < 3; ++d) {
@@ -593,7 +689,7 @@ double or_cfl_dt(const or_params* c, const double* P, const double* dir_lo, cons
   std::vector<double> Pc(P, P + gr.cells() * NVAR);
   apply_bc(gr, Pc.data(), dir_lo, dir_hi);
   Fluxes fx;
-  compute_fluxes(gr, Pc.data(), fx);
+  compute_fluxes(gr, Pc.data(), fx, c->gam);
   return cfl_dt(gr, fx);
 }
 
@@ -608,7 +704,7 @@ void or_stage(const or_params* c, const double* U0, const double* Pin, double cd
   build_grid(*c, gr);
   Fluxes fx;
   StageStats st;
-  stage(gr, U0, Pin, cdt, Uout, Pout, fx, st, nullptr);
+  stage<double>(gr, U0, Pin, c->gam, cdt, Uout, Pout, fx, st, nullptr);
   double* Co[3] = {ct1, ct2, ct3};
   for (int d = 0; d < 3; ++d)
     if (Co[d]) std::memcpy(Co[d], fx.ctop[d].data(), fx.ctop[d].size() * sizeof(double));
@@ -632,12 +728,12 @@ double or_step(const or_params* c, double* U, double* P, double dt, const double
   Fluxes fx;
   StageStats st;
   apply_bc(gr, Pn.data(), dir_lo, dir_hi);
-  stage(gr, U0.data(), Pn.data(), 0.5 * dt, Us.data(), Ps.data(), fx, st, nullptr);
+  stage<double>(gr, U0.data(), Pn.data(), c->gam, 0.5 * dt, Us.data(), Ps.data(), fx, st, nullptr);
   // ghosts of P* start from those of P^n, then get refilled
   apply_bc(gr, Ps.data(), dir_lo, dir_hi);
   Pnew = Ps;
   Unew = U0;
-  stage(gr, U0.data(), Ps.data(), dt, Unew.data(), Pnew.data(), fx, st, nullptr);
+  stage<double>(gr, U0.data(), Ps.data(), c->gam, dt, Unew.data(), Pnew.data(), fx, st, nullptr);
   double dtn = cfl_dt(gr, fx);
   const GridInfo& g = gr.g;
   for (int v = 0; v < NVAR; ++v)
@@ -649,6 +745,64 @@ double or_step(const or_params* c, double* U, double* P, double dt, const double
           P[q] = Pnew[q];
         }
   (void)g;
+  if (stats) {
+    stats[0] = st.nfail;
+    stats[1] = st.nfloor;
+    stats[2] = st.nunfixed;
+  }
+  return dtn;
+}
+
+// Tangent of one step (forward-mode dual numbers through the same stages):
+// U, P advance exactly as in or_step (same values); dU, dP (same layouts)
+// and dgam carry a direction on entry, and on exit dU, dP hold the
+// directional derivative of U^{n+1}, P^{n+1} (interior; dt held fixed).
+// Derivative rules at the non-smooth points: the branch the values take
+// (MC: slope 0 when the one-sided differences do not agree in sign, the
+// first candidate on ties; ctop: the first of the maximal speeds), the
+// implicit-function derivative of the inversion, floored components and
+// fixed-up zones frozen, Dirichlet ghosts and clamped inflow constant.
+// dF1 (nullable): the tangent of the stage-2 x1 fluxes, cell layout.
+// zflag (nullable, [N3][N2][N1]): per zone, bit 1 = an inversion failed
+// (either stage; the zone was fixed up), bit 2 = a floor or ceiling acted.
+// stats as or_step. Returns the next CFL dt.
+double or_step_jvp(const or_params* c, double* U, double* P, double* dU, double* dP, double dgam, double dt,
+                   const double* dir_lo, const double* dir_hi, double* dF1, int* zflag, long* stats) {
+  Grid gr;
+  build_grid(*c, gr);
+  const size_t n = gr.cells() * NVAR;
+  std::vector<Dd> Pn(n), U0(n);
+  for (size_t q = 0; q < n; ++q) {
+    Pn[q] = mk<double>(P[q], dP[q]);
+    U0[q] = mk<double>(U[q], dU[q]);
+  }
+  const Dd gam = mk<double>(c->gam, dgam);
+  std::vector<Dd> Ps(Pn), Us(U0), Pnew, Unew;
+  FluxesT<Dd> fx;
+  StageStats st;
+  std::vector<int> pf[2], ff[2];
+  apply_bc(gr, Pn.data(), dir_lo, dir_hi);
+  stage<Dd>(gr, U0.data(), Pn.data(), gam, 0.5 * dt, Us.data(), Ps.data(), fx, st, &pf[0], &ff[0]);
+  apply_bc(gr, Ps.data(), dir_lo, dir_hi);
+  Pnew = Ps;
+  Unew = U0;
+  stage<Dd>(gr, U0.data(), Ps.data(), gam, dt, Unew.data(), Pnew.data(), fx, st, &pf[1], &ff[1]);
+  double dtn = cfl_dt(gr, fx);
+  if (zflag)
+    for (size_t q = 0; q < gr.cells(); ++q)
+      zflag[q] = ((pf[0][q] || pf[1][q]) ? 1 : 0) | ((ff[0][q] || ff[1][q]) ? 2 : 0);
+  for (int v = 0; v < NVAR; ++v)
+    for (int k = gr.s3(); k < gr.e3(); ++k)
+      for (int j = gr.s2(); j < gr.e2(); ++j)
+        for (int i = gr.s1(); i < gr.e1(); ++i) {
+          size_t q = gr.idx(v, k, j, i);
+          U[q] = Unew[q].v;
+          P[q] = Pnew[q].v;
+          dU[q] = Unew[q].d;
+          dP[q] = Pnew[q].d;
+        }
+  if (dF1)
+    for (size_t q = 0; q < n; ++q) dF1[q] = fx.F[0][q].d;
   if (stats) {
     stats[0] = st.nfail;
     stats[1] = st.nfloor;

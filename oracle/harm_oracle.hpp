@@ -317,8 +317,8 @@ void fluid_state(const R P[NVAR], const Geo& G, FluidState<R>& S) {
 
 // Mixed stress-energy tensor of ideal MHD ("Extended GRMHD" section):
 // T^mu_nu = (rho + u + p + b^2) u^mu u_nu + (p + b^2/2) delta^mu_nu - b^mu b_nu.
-template <class R>
-R t_mixed(const R P[NVAR], const FluidState<R>& S, double gam, int mu, int nu) {
+template <class R, class Gm>
+R t_mixed(const R P[NVAR], const FluidState<R>& S, const Gm& gam, int mu, int nu) {
   R p = (gam - 1.0) * P[UU];
   R w = P[RHO] + P[UU] + p;
   R out = (w + S.bsq) * S.ucon[mu] * S.ucov[nu] - S.bcon[mu] * S.bcov[nu];
@@ -329,8 +329,8 @@ R t_mixed(const R P[NVAR], const FluidState<R>& S, double gam, int mu, int nu) {
 // Conserved variables (dir == 0) or the flux through an x^dir face (dir = 1..3):
 //   sqrt(-g) (rho u^d, T^d_t + rho u^d, T^d_1, T^d_2, T^d_3, b^i u^d - b^d u^i).
 // For dir == 0 the induction entry equals sqrt(-g) B^i by definition.
-template <class R>
-void prim_to_flux(const R P[NVAR], const FluidState<R>& S, const Geo& G, double gam, int dir, R F[NVAR]) {
+template <class R, class Gm>
+void prim_to_flux(const R P[NVAR], const FluidState<R>& S, const Geo& G, const Gm& gam, int dir, R F[NVAR]) {
   R mflux = P[RHO] * S.ucon[dir];
   F[RHO] = G.gdet * mflux;
   F[UU] = G.gdet * (t_mixed(P, S, gam, dir, 0) + mflux);
@@ -348,8 +348,8 @@ void prim_to_flux(const R P[NVAR], const FluidState<R>& S, const Geo& G, double 
 // v_A^2 = b^2 / (b^2 + w), a wave vector k_mu = delta_mu^dir - v delta_mu^t obeys
 // (k.u)^2 = c_ms^2 (k.k + (k.u)^2), a quadratic in v. Its discriminant is
 // clamped at zero; c_ms^2 is clamped to [0, 1].
-template <class R>
-void signal_speeds(const R P[NVAR], const FluidState<R>& S, const Geo& G, double gam, int dir, R& cmax,
+template <class R, class Gm>
+void signal_speeds(const R P[NVAR], const FluidState<R>& S, const Geo& G, const Gm& gam, int dir, R& cmax,
                    R& cmin) {
   using std::sqrt;
   R p = (gam - 1.0) * P[UU];
@@ -377,8 +377,8 @@ void signal_speeds(const R P[NVAR], const FluidState<R>& S, const Geo& G, double
 
 // Local Lax-Friedrichs flux through an x^dir face from left/right states:
 // F = (F_L + F_R)/2 - c_top (U_R - U_L)/2, c_top = max(0, c+_L, c+_R, -c-_L, -c-_R).
-template <class R>
-void llf_flux(const R PL[NVAR], const R PR[NVAR], const Geo& G, double gam, int dir, R F[NVAR], R& ctop) {
+template <class R, class Gm>
+void llf_flux(const R PL[NVAR], const R PR[NVAR], const Geo& G, const Gm& gam, int dir, R F[NVAR], R& ctop) {
   FluidState<R> SL, SR;
   fluid_state(PL, G, SL);
   fluid_state(PR, G, SR);
@@ -401,8 +401,8 @@ void llf_flux(const R PL[NVAR], const R PR[NVAR], const Geo& G, double gam, int 
 
 // Connection source terms for the energy and momentum equations:
 // S_nu = sqrt(-g) T^k_l Gamma^l_{nu k}; zero for rho and B.
-template <class R>
-void source_terms(const R P[NVAR], const Geo& G, const double conn[4][4][4], double gam, R S[NVAR]) {
+template <class R, class Gm>
+void source_terms(const R P[NVAR], const Geo& G, const double conn[4][4][4], const Gm& gam, R S[NVAR]) {
   FluidState<R> st;
   fluid_state(P, G, st);
   R T[4][4];
@@ -424,49 +424,54 @@ void source_terms(const R P[NVAR], const Geo& G, const double conn[4][4][4], dou
 // Monotonized-central slope: 0 if the one-sided differences disagree in sign
 // (or one is zero), else the candidate of least magnitude among 2 d-, 2 d+ and
 // (d- + d+)/2 (ties go to the earlier candidate).
-inline double mc_slope(double qm, double q0, double qp) {
-  double dm = q0 - qm, dp = qp - q0;
-  if (dm * dp <= 0.0) return 0.0;
-  double cand[3] = {2.0 * dm, 2.0 * dp, 0.5 * (dm + dp)};
-  double s = cand[0];
+template <class R>
+R mc_slope(const R& qm, const R& q0, const R& qp) {
+  using std::fabs;
+  R dm = q0 - qm, dp = qp - q0;
+  if (dm * dp <= 0.0) return R(0.0);
+  R cand[3] = {2.0 * dm, 2.0 * dp, 0.5 * (dm + dp)};
+  R s = cand[0];
   for (int i = 1; i < 3; ++i)
-    if (std::fabs(cand[i]) < std::fabs(s)) s = cand[i];
+    if (fabs(cand[i]) < fabs(s)) s = cand[i];
   return s;
 }
 
 // WENO5 point value at the upper face of the centre cell of x[0..4]
 // (Jiang-Shu smoothness indicators, power 2, eps = 1e-26; candidate stencils
 // are the quadratic interpolants at x = +1/2, linear weights 1/16, 5/8, 5/16).
-inline double weno5_upper(const double x[5]) {
+template <class R>
+R weno5_upper(const R x[5]) {
+  using std::pow;
   const double eps = 1e-26;
-  double c[3];
+  R c[3];
   c[0] = (3.0 / 8.0) * x[0] - (5.0 / 4.0) * x[1] + (15.0 / 8.0) * x[2];
   c[1] = (-1.0 / 8.0) * x[1] + (3.0 / 4.0) * x[2] + (3.0 / 8.0) * x[3];
   c[2] = (3.0 / 8.0) * x[2] + (3.0 / 4.0) * x[3] - (1.0 / 8.0) * x[4];
-  double b[3];
-  b[0] = (13.0 / 12.0) * std::pow(x[0] - 2.0 * x[1] + x[2], 2) + 0.25 * std::pow(x[0] - 4.0 * x[1] + 3.0 * x[2], 2);
-  b[1] = (13.0 / 12.0) * std::pow(x[1] - 2.0 * x[2] + x[3], 2) + 0.25 * std::pow(x[1] - x[3], 2);
-  b[2] = (13.0 / 12.0) * std::pow(x[2] - 2.0 * x[3] + x[4], 2) + 0.25 * std::pow(3.0 * x[2] - 4.0 * x[3] + x[4], 2);
+  R b[3];
+  b[0] = (13.0 / 12.0) * pow(x[0] - 2.0 * x[1] + x[2], 2.0) + 0.25 * pow(x[0] - 4.0 * x[1] + 3.0 * x[2], 2.0);
+  b[1] = (13.0 / 12.0) * pow(x[1] - 2.0 * x[2] + x[3], 2.0) + 0.25 * pow(x[1] - x[3], 2.0);
+  b[2] = (13.0 / 12.0) * pow(x[2] - 2.0 * x[3] + x[4], 2.0) + 0.25 * pow(3.0 * x[2] - 4.0 * x[3] + x[4], 2.0);
   const double d[3] = {1.0 / 16.0, 5.0 / 8.0, 5.0 / 16.0};
-  double al[3], sum = 0.0;
+  R al[3], sum(0.0);
   for (int k = 0; k < 3; ++k) {
-    al[k] = d[k] / std::pow(eps + b[k], 2);
+    al[k] = d[k] / pow(eps + b[k], 2.0);
     sum += al[k];
   }
-  double out = 0.0;
+  R out(0.0);
   for (int k = 0; k < 3; ++k) out += (al[k] / sum) * c[k];
   return out;
 }
 
 // Face values of the centre cell of stencil q[0..4] (q[2] is the cell):
 // lo = value at its lower face, hi = value at its upper face.
-inline void recon_cell(int recon, const double q[5], double& lo, double& hi) {
+template <class R>
+void recon_cell(int recon, const R q[5], R& lo, R& hi) {
   if (recon == RECON_MC) {
-    double s = mc_slope(q[1], q[2], q[3]);
+    R s = mc_slope(q[1], q[2], q[3]);
     lo = q[2] - 0.5 * s;
     hi = q[2] + 0.5 * s;
   } else {
-    double rev[5] = {q[4], q[3], q[2], q[1], q[0]};
+    R rev[5] = {q[4], q[3], q[2], q[1], q[0]};
     hi = weno5_upper(q);
     lo = weno5_upper(rev);
   }

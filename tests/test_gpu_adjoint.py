@@ -364,3 +364,99 @@ def test_face_flux_seed_gradient(kh, torch):
     fd = (Jgpu(P0 + h * vP) - Jgpu(P0 - h * vP)) / (2 * h)
     assert abs(J - Jgpu(P0)) <= 1e-12 * abs(J)
     assert abs(adj - fd) <= 1e-6 * abs(fd), (adj, fd)
+
+
+def _dual_case(orc, case):
+    kind, recon = case.split("-")
+    if kind == "box":
+        cfg = inputs.linear_mode_cfg(8, ndim=3, recon=recon)
+        P0 = orc.apply_bc(cfg, _random_state(cfg, 8))
+        return cfg, P0, 0.3 / 8
+    cfg, P0 = _torus(48, 32, recon)
+    P0 = orc.apply_bc(cfg, P0)
+    return cfg, P0, 0.5 * orc.cfl_dt(cfg, P0)
+
+
+def _scaled_direction(cfg, P0, U0, seed):
+    vU, vP = _direction(cfg, P0, seed)
+    vU *= np.abs(U0).reshape(8, -1).max(axis=1)[:, None, None, None]
+    vP *= np.abs(P0).reshape(8, -1).max(axis=1)[:, None, None, None]
+    return vU, vP
+
+
+@pytest.mark.parametrize("case", ["box-mc", "box-weno5", "torus-mc", "torus-weno5"])
+def test_step_adjoint_equals_oracle_dual_tangent(kh, torch, orc, case):
+    """One step: <adjoint(w), v> of the CUDA reverse pass against
+    <w, tangent(v)> of the oracle's dual-number step (independent code), for
+    a direction v on every interior zone and on the adiabatic index. Both
+    are exact derivatives under the same rules (branch taken, implicit
+    function through the inversion, floored components and fixed-up zones
+    frozen), so they agree to round-off (1e-10 of the sum of magnitudes),
+    on the torus with its floors, fixups, polar and outflow ghosts."""
+    cfg, P0, dt = _dual_case(orc, case)
+    U0 = orc.prim_to_cons(cfg, P0)
+    wU, wP = _weights(cfg, 9)
+    gU, gP, gg = _adjoint_one_step(kh, torch, cfg, U0, P0, dt, wU, wP)
+    vU, vP = _scaled_direction(cfg, P0, U0, 10)
+    dgam = 0.37
+    T = orc.step_jvp(cfg, U0, P0, vU, vP, dgam, dt)
+    sl = (slice(None),) + inputs.interior(cfg)
+    terms = np.concatenate([(gU * vU).ravel(), (gP * vP).ravel(), [gg * dgam]])
+    lhs = terms.sum()
+    rhs_terms = np.concatenate([(wU[sl] * T[2][sl]).ravel(), (wP[sl] * T[3][sl]).ravel()])
+    rhs = rhs_terms.sum()
+    scale = max(np.abs(terms).sum(), np.abs(rhs_terms).sum())
+    assert abs(lhs - rhs) <= 1e-10 * scale, (lhs, rhs, scale, T[5])
+
+
+@pytest.mark.parametrize("case", ["box-weno5", "torus-mc"])
+def test_rollout_gradient_equals_oracle_dual_tangent(kh, torch, orc, case):
+    """Three steps through the torch.autograd wrappers (per-step
+    checkpoints), with an objective on U, P, B and on the last step's
+    stage-2 x1 face fluxes (a mass flux through the inner face plane on the
+    torus: the horizon accretion rate), against the oracle's dual-number
+    tangent chained over the same three steps; gradients in U0, P0, B0 and
+    the adiabatic index."""
+    from paper_2408_01361_gb300 import autograd as kga
+    cfg, P0, dt = _dual_case(orc, case)
+    U0 = orc.prim_to_cons(cfg, P0)
+    wU, wP = _weights(cfg, 19)
+    ng = 3
+    ksl, jsl, _ = inputs.interior(cfg)
+    i_f = ng if case.startswith("torus") else ng + cfg["n1"] // 2
+    wF = 0.0 if case.startswith("box") else 1.0
+    fscale = np.abs(wU).max()
+
+    ctx = kh.Context(cfg)
+    N1 = P0.shape[3]
+    Ut = ctx.to_device(U0).requires_grad_(True)
+    PB = ctx.to_device(P0)
+    Pt = PB[:5].clone().requires_grad_(True)
+    Bt = PB[5:].clone().requires_grad_(True)
+    gam = torch.tensor(cfg["gam"], dtype=torch.float64, device=ctx.device, requires_grad=True)
+    U, P, B = Ut, Pt, Bt
+    for q in range(3):
+        if q == 2:
+            U, P, B, F1 = kga.step(ctx, U, P, B, gam, dt, with_flux=True)
+        else:
+            U, P, B = kga.step(ctx, U, P, B, gam, dt)
+    tU, tP = ctx.to_device(wU), ctx.to_device(wP)
+    J = (tU * U).sum() + (tP[:5] * P).sum() + (tP[5:] * B).sum()
+    J = J - wF * fscale * F1[0, ksl, jsl, i_f].sum()
+    J.backward()
+    gUi = ctx.to_host(Ut.grad, N1)
+    gPi = np.concatenate([ctx.to_host(Pt.grad, N1), ctx.to_host(Bt.grad, N1)])
+
+    vU, vP = _scaled_direction(cfg, P0, U0, 20)
+    dgam = -0.21
+    Uo, Po, dUo, dPo = U0, P0, vU, vP
+    for q in range(3):
+        T = orc.step_jvp(cfg, Uo, Po, dUo, dPo, dgam, dt, flux=(q == 2))
+        Uo, Po, dUo, dPo = T[0], T[1], T[2], T[3]
+    dF1 = T[7]
+    sl = (slice(None),) + inputs.interior(cfg)
+    lhs_terms = np.concatenate([(gUi * vU).ravel(), (gPi * vP).ravel(), [float(gam.grad) * dgam]])
+    rhs_terms = np.concatenate([(wU[sl] * dUo[sl]).ravel(), (wP[sl] * dPo[sl]).ravel(),
+                                -wF * fscale * dF1[0, ksl, jsl, i_f].ravel()])
+    scale = max(np.abs(lhs_terms).sum(), np.abs(rhs_terms).sum())
+    assert abs(lhs_terms.sum() - rhs_terms.sum()) <= 1e-10 * scale, (lhs_terms.sum(), rhs_terms.sum(), scale)
