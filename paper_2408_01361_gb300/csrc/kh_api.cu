@@ -81,12 +81,12 @@ void free_all(kh_ctx* x) {
                   x->ctop[2], x->emf[0], x->emf[1], x->emf[2], x->pflag, x->partial, x->dscalar,
                   x->counters, x->dirichlet[0], x->dirichlet[1], x->geof, x->connf, x->pstarf, x->pnf, x->Ff[0],
                   x->Ff[1], x->Ff[2], x->ctopf[0], x->ctopf[1], x->ctopf[2], x->emff[0], x->emff[1],
-                  x->emff[2], x->dirichletf[0], x->dirichletf[1], x->adj, x->adj_i8, x->adj_red};
+                  x->emff[2], x->dirichletf[0], x->dirichletf[1], x->adj, x->adj_i8, x->adj_red, x->geodf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
 
-GeomT<float> geomf(const kh_ctx* x) { return GeomT<float>{x->geof, x->connf, x->flo}; }
+GeomT<float> geomf(const kh_ctx* x) { return GeomT<float>{x->geof, x->connf, x->flo, x->geodf}; }
 
 // One FP64 stage: ghost fill, fluxes per direction, Flux-CT, update, fixup.
 int run_stage(kh_ctx* x, int st, const double* U0, const Vars& Pin, const Vars& Pout, double* Uout, double coef) {
@@ -256,6 +256,7 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
   S.fl.ibsq_u_max = 1.0 / c->bsq_u_max;
   S.c2p.max_iter = c->newton_max_iter > 0 ? c->newton_max_iter : 30;
   S.c2p.tol = c->newton_tol > 0.0 ? c->newton_tol : 1e-14;
+  set_mixed(S);
 
   x->cp = CoordParams{c->kind, a, c->x1min, c->hslope, c->poly_xt, c->poly_alpha, c->mks_smooth};
 
@@ -287,6 +288,7 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
   } else {
     KH_ALLOC(x->geof, 3 * NGEO * gpf);
     KH_ALLOC(x->connf, NCONN * gpf);
+    KH_ALLOC(x->geodf, 2 * NDF * gpf);
     KH_ALLOC(x->pstarf, NV * plf);
     KH_ALLOC(x->pnf, NV * plf);
     for (int d = 0; d < L.ndim; ++d) {
@@ -327,6 +329,7 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
     if (mixed) {
       x->launches += launch_to_f32(x->geo, x->geof, 3LL * NGEO * L.gplane, 0);
       x->launches += launch_to_f32(x->conn, x->connf, (long long)NCONN * L.gplane, 0);
+      x->launches += launch_df_planes(x->geo, x->flo, x->geodf, L.gplane, 0);
     }
     rc = cuda_fail(cudaGetLastError());
     if (rc == KH_OK) rc = cuda_fail(cudaDeviceSynchronize());

@@ -27,6 +27,7 @@ struct kh_ctx {
   // FP32 stage-1 output and FP32 Dirichlet ghosts
   float* geof;
   float* connf;
+  float* geodf;    // [NDF][2] double-float planes of the cell-centre geometry and floors
   float* pstarf;   // 8 planes
   float* pnf;      // 8 planes: FP32 copy of the ghost-filled stage-1 input
   float* Ff[3];    // 8 planes each

@@ -4,7 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "kh_physics.cuh"
+#include "kh_mixed.cuh"  // kh_physics.cuh and the double-float update
 #include "kharma_gb300.h"
 
 namespace kh {
@@ -13,12 +13,6 @@ constexpr int NGHOST = 3;
 constexpr int NGEO = 22;  // per location: gcov (10 symmetric), gcon (10), gdet, alpha
 constexpr int NCONN = 40; // Gamma^l_{mn}: 4 x 10 symmetric pairs
 enum { LOC_CENT = 0, LOC_F1 = 1, LOC_F2 = 2 };
-
-// Symmetric-pair index of (m, n): 00 01 02 03 11 12 13 22 23 33.
-KH_HD int sym_index(int m, int n) {
-  if (m > n) { int t = m; m = n; n = t; }
-  return m == 0 ? n : (m == 1 ? 3 + n : (m == 2 ? 5 + n : 9));
-}
 
 struct Layout {
   int n1, n2, n3, ng, ng3, ndim;
@@ -47,6 +41,7 @@ template <class T> struct GeomT {
   const T* g;          // [3][NGEO][n2s][n1s]
   const T* conn;       // [NCONN][n2s][n1s]
   const double* flo;   // [3][n2s][n1s]: geometric floors of rho and u, and 1/sqrt(-g), at cell centres
+  const float* df;     // FP32 copy only: [NDF][2][n2s][n1s] double-float planes (above)
 };
 using DevGeom = GeomT<double>;
 
@@ -59,7 +54,11 @@ struct Scheme {
   int bc[6];
   FloorParams fl;
   C2POpts c2p;
+  MixedConsts mx;
 };
+
+// Host: fill S.mx from the FP64 fields.
+inline void set_mixed(Scheme& S) { S.mx = mixed_consts(S.gam, S.fl); }
 
 // Counters kept on the device for one step.
 enum { CNT_FAIL = 0, CNT_FLOOR = 1, CNT_UNFIXED = 2, CNT_TIMEOUT = 3, NCNT = 4 };
@@ -108,6 +107,8 @@ int launch_c2p(const double* U, const Vars& P, int8_t* pflag, const Layout& L, c
                unsigned long long* cnt, cudaStream_t s);
 // Element-wise FP64 -> FP32 copy of n values.
 int launch_to_f32(const double* src, float* dst, long long n, cudaStream_t s);
+// The double-float planes of one grid's cell-centre geometry and floors.
+int launch_df_planes(const double* geo, const double* flo, float* df, long long gplane, cudaStream_t s);
 // FP64 -> FP32 copy of the 8 primitive planes (every cell of the allocation).
 int launch_vars_to_f32(const CVars& src, const VarsT<float>& dst, const Layout& L, cudaStream_t s);
 

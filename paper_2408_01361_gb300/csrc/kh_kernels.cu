@@ -212,7 +212,8 @@ __global__ void __launch_bounds__(TPB_MAX) k_update_mixed(const double* U0, CVar
   if (t >= nzones(L)) return;
   int i, j, k;
   zone_ijk(L, t, i, j, k);
-  update_mixed_zone(U0, Pin, Pout64, Pout32, Uout, F1, F2, F3, L, G, Gf, S, coef * __ldg(dtp), pflag, cnt, i, j, k);
+  update_mixed_zone(U0, Pin, Pout64, Pout32, Uout, F1, F2, F3, L, G, Gf, S, df_of_f64(coef * __ldg(dtp)), pflag, cnt, i,
+                    j, k);
 }
 
 template <class T>
@@ -362,7 +363,7 @@ __global__ void k_vars_to_f32(CVars src, VarsT<float> dst, long long plane) {
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < plane;
        q += (long long)gridDim.x * blockDim.x) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) dst.v[v][q] = (float)src.v[v][q];
+    for (int v = 0; v < NV; ++v) dst.v[v][q] = f32_of_f64(src.v[v][q]);  // integer ops, not the FP64 pipe
   }
 }
 
@@ -486,6 +487,32 @@ int launch_vars_to_f32(const CVars& src, const VarsT<float>& dst, const Layout& 
   if (b > 152 * 16) b = 152 * 16;
   if (b < 1) b = 1;
   k_vars_to_f32<<<(int)b, 256, 0, s>>>(src, dst, L.plane);
+  return 1;
+}
+
+__global__ void k_df_planes(const double* geo, const double* flo, float* df, long long gplane) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < gplane;
+       p += (long long)gridDim.x * blockDim.x) {
+    auto put = [&](int q, double x) {
+      const df64 v = df_of_f64(x);
+      df[(2 * q) * gplane + p] = v.hi;
+      df[(2 * q + 1) * gplane + p] = v.lo;
+    };
+    // cell-centre planes: gcov pairs 0..9, gcon pairs 10..19, gdet 20, alpha 21
+    for (int q = 0; q < 10; ++q) put(DF_GCON + q, geo[(10 + q) * gplane + p]);
+    for (int q = 0; q < 6; ++q) put(DF_GCOV + q, geo[(4 + q) * gplane + p]);  // pairs 11 12 13 22 23 33
+    put(DF_ALPHA, geo[21 * gplane + p]);
+    put(DF_IG, flo[2 * gplane + p]);
+    put(DF_RHOFL, flo[p]);
+    put(DF_UFL, flo[gplane + p]);
+  }
+}
+
+int launch_df_planes(const double* geo, const double* flo, float* df, long long gplane, cudaStream_t s) {
+  long long b = nblocks(gplane, 256);
+  if (b > 152 * 4) b = 152 * 4;
+  if (b < 1) b = 1;
+  k_df_planes<<<(int)b, 256, 0, s>>>(geo, flo, df, gplane);
   return 1;
 }
 

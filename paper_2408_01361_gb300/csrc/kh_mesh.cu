@@ -98,12 +98,14 @@ struct GeoArena {
   const double* flo;
   const float* gf;
   const float* connf;
+  const float* df;
 };
 __device__ __forceinline__ DevGeom geo64(const GeoArena& A, const MBlock& m) {
   return DevGeom{A.g + 3LL * NGEO * m.goff, A.conn + (long long)NCONN * m.goff, A.flo + 3 * m.goff};
 }
 __device__ __forceinline__ GeomT<float> geo32(const GeoArena& A, const MBlock& m) {
-  return GeomT<float>{A.gf + 3LL * NGEO * m.goff, A.connf + (long long)NCONN * m.goff, A.flo + 3 * m.goff};
+  return GeomT<float>{A.gf + 3LL * NGEO * m.goff, A.connf + (long long)NCONN * m.goff, A.flo + 3 * m.goff,
+                      A.df ? A.df + 2LL * NDF * m.goff : nullptr};
 }
 
 // Largest b with pre[b] <= t (pre has nb + 1 entries, pre[0] = 0).
@@ -190,8 +192,8 @@ __global__ void __launch_bounds__(256) km_update_mixed(const MBlock* blk, const 
   if (Pout64.a) P64 = vars_at(Pout64, m); else for (int v = 0; v < NV; ++v) P64.v[v] = nullptr;
   if (Pout32.a) P32 = vars_at(Pout32, m); else for (int v = 0; v < NV; ++v) P32.v[v] = nullptr;
   update_mixed_zone(U0 + o8, cvars_at(Pin, m), P64, P32, Uout ? Uout + o8 : nullptr, F1 + o8, F2 + o8,
-                    m.L.ndim == 3 ? F3 + o8 : nullptr, m.L, geo64(GA, m), geo32(GA, m), S, coef * __ldg(dtp),
-                    pflag + m.off, cnt, i, j, k);
+                    m.L.ndim == 3 ? F3 + o8 : nullptr, m.L, geo64(GA, m), geo32(GA, m), S,
+                    df_of_f64(coef * __ldg(dtp)), pflag + m.off, cnt, i, j, k);
 }
 
 template <class T>
@@ -389,7 +391,7 @@ __global__ void km_to_f32(const MBlock* blk, const unsigned* pre, int nb, Arena<
   const CVars S = cvars_at(src, m);
   const VarsT<float> D = vars_at(dst, m);
 #pragma unroll
-  for (int v = 0; v < NV; ++v) D.v[v][c] = (float)S.v[v][c];
+  for (int v = 0; v < NV; ++v) D.v[v][c] = f32_of_f64(S.v[v][c]);  // integer ops, not the FP64 pipe
 }
 
 __global__ void km_p2c(const MBlock* blk, const unsigned* pre, int nb, Arena<double> P, double* U, GeoArena GA,
@@ -441,6 +443,7 @@ struct kh_mesh {
   long long nnbs;
   double *geo, *conn, *flo;
   float *geof, *connf;
+  float* geodf;  // [NDF][2] double-float planes per block (goff-based)
   double* pstar;
   float *pstarf, *pnf;
   double* F[3];
@@ -519,6 +522,7 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
                      c->u_rho_max,      c->gamma_max,       1.0 / c->bsq_rho_max,   1.0 / c->bsq_u_max};
   S.c2p.max_iter = c->newton_max_iter > 0 ? c->newton_max_iter : 30;
   S.c2p.tol = c->newton_tol > 0.0 ? c->newton_tol : 1e-14;
+  set_mixed(S);
   x->cp = CoordParams{c->kind, a, c->x1min, c->hslope, c->poly_xt, c->poly_alpha, c->mks_smooth};
 
   // ---- validate the blocks and rasterise ownership at the finest level ----
@@ -788,6 +792,7 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
   } else {
     KM_ALLOC(x->geof, 3 * NGEO * gpf);
     KM_ALLOC(x->connf, NCONN * gpf);
+    KM_ALLOC(x->geodf, 2 * NDF * gpf);
     KM_ALLOC(x->pstarf, NV * plf);
     KM_ALLOC(x->pnf, NV * plf);
     for (int d = 0; d < x->ndim; ++d) {
@@ -838,6 +843,11 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
   if (rc == KH_OK && mixed) {
     x->launches += launch_to_f32(x->geo, x->geof, 3LL * NGEO * gcells, 0);
     x->launches += launch_to_f32(x->conn, x->connf, (long long)NCONN * gcells, 0);
+    for (int b = 0; b < nblocks; ++b) {
+      const MBlock& m = x->hb[b];
+      x->launches += launch_df_planes(x->geo + 3LL * NGEO * m.goff, x->flo + 3 * m.goff, x->geodf + 2LL * NDF * m.goff,
+                                      m.L.gplane, 0);
+    }
     rc = cuda_rc(cudaGetLastError());
   }
   if (rc == KH_OK) rc = cuda_rc(cudaDeviceSynchronize());
@@ -853,7 +863,7 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
 
 namespace {
 
-GeoArena garena(const kh_mesh* x) { return GeoArena{x->geo, x->conn, x->flo, x->geof, x->connf}; }
+GeoArena garena(const kh_mesh* x) { return GeoArena{x->geo, x->conn, x->flo, x->geof, x->connf, x->geodf}; }
 
 template <class T> Arena<T> arena8(T* p) { return Arena<T>{p, nullptr, NV}; }
 Arena<double> arena_pb(double* P, double* B) { return Arena<double>{P, B, 5}; }
@@ -1225,7 +1235,7 @@ int kh_mesh_destroy(kh_mesh* x) {
   cudaStreamSynchronize(x->stream);
   drop_mesh_graph(x);
   if (x->cap_stream) cudaStreamDestroy(x->cap_stream);
-  void* ptrs[] = {x->dblk, x->dops, x->dnbs, x->geo, x->conn, x->flo, x->geof, x->connf, x->pstar, x->pstarf, x->pnf,
+  void* ptrs[] = {x->dblk, x->dops, x->dnbs, x->geo, x->conn, x->flo, x->geof, x->connf, x->geodf, x->pstar, x->pstarf, x->pnf,
                   x->pflag, x->partial, x->dscalar, x->counters, x->F[0], x->F[1], x->F[2], x->ctop[0],
                   x->ctop[1], x->ctop[2], x->emf[0], x->emf[1], x->emf[2], x->Ff[0], x->Ff[1], x->Ff[2],
                   x->ctopf[0], x->ctopf[1], x->ctopf[2], x->emff[0], x->emff[1], x->emff[2]};

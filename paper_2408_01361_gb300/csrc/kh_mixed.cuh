@@ -1,0 +1,175 @@
+// Mixed-precision inversion without the FP64 pipe: the Noble et al. (2006)
+// two-unknown (W, v^2) equations of noble2d, with
+//   * the invariants D, Q.n, Q~^2, B^2, (Q.B)^2 formed in double-float
+//     arithmetic from the double-float conserved variables and metric, on the
+//     problem scaled by S = 4^k ~ W (fluid conserved variables times 1/S, the
+//     field times 1/sqrt(S): every term of the momentum residual then scales
+//     as S^2 and of the energy residual as S, exactly);
+//   * Newton's iterations in FP32 on the scaled invariants (their hi parts),
+//     started from the stage input's (W, v^2);
+//   * one refinement with both residuals in double-float at the FP32 root and
+//     the FP32 Jacobian (its FP32 error multiplies a step of ~1e-7), accepted
+//     when the step is below 1e-5 -- the iterate then lies in Newton's
+//     quadratic regime, its error ~ the step squared;
+//   * the primitives recovered in double-float.
+// A zone whose FP32 phase or refinement does not meet these conditions is
+// reported (C2P_NEED_FP64) and the caller runs the FP64 inversion for it.
+#pragma once
+
+#include "kh_df64.cuh"
+#include "kh_physics.cuh"
+
+namespace kh {
+
+constexpr int C2P_NEED_FP64 = -1;
+
+// Double-float (hi, lo FP32 pair) copies of the cell-centre quantities the
+// mixed update's inversion and floors use, per (i, j): planes [NDF][2][n2s][n1s]
+// (hi plane, then lo plane, of each quantity). DF_GCON: g^{mn} in the
+// symmetric-pair order; DF_GCOV: g_ij (11 12 13 22 23 33).
+enum { DF_GCON = 0, DF_GCOV = 10, DF_ALPHA = 16, DF_IG = 17, DF_RHOFL = 18, DF_UFL = 19, NDF = 20 };
+
+// FP32 and double-float constants of the mixed update (host: set_mixed()).
+struct MixedConsts {
+  float gfac_hi, gfac_lo;  // (gam - 1) / gam as a double-float pair
+  float igam_hi, igam_lo;  // 1 / gam
+  float gam;
+  float ibsq_rho_max, ibsq_u_max, u_rho_max, g2max;  // floors: 1/(b^2/rho)max, 1/(b^2/u)max, (u/rho)max, gamma_max^2
+};
+
+// Host: the constants from the FP64 adiabatic index and floors (hi = the
+// nearest FP32, lo = the rest).
+inline MixedConsts mixed_consts(double gam, const FloorParams& fl) {
+  auto split = [](double x, float& hi, float& lo) {
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
+  };
+  MixedConsts k;
+  split((gam - 1.0) / gam, k.gfac_hi, k.gfac_lo);
+  split(1.0 / gam, k.igam_hi, k.igam_lo);
+  k.gam = (float)gam;
+  k.ibsq_rho_max = (float)fl.ibsq_rho_max;
+  k.ibsq_u_max = (float)fl.ibsq_u_max;
+  k.u_rho_max = (float)fl.u_rho_max;
+  const double g2 = fl.gamma_max * fl.gamma_max;
+  k.g2max = g2 < 3.0e38 ? (float)g2 : 3.0e38f;
+  return k;
+}
+
+struct MetDF {
+  df64 gcon[10];  // g^{mn}, symmetric-pair order
+  df64 gcov[6];   // g_ij: 11 12 13 22 23 33
+  df64 alpha, ig, rho_fl, u_fl;
+};
+
+#ifdef __CUDACC__
+__device__ __forceinline__ MetDF load_metdf(const float* df, long long gplane, long long p) {
+  auto ld = [&](int q) { return mkdf(__ldg(df + (2 * q) * gplane + p), __ldg(df + (2 * q + 1) * gplane + p)); };
+  MetDF m;
+#pragma unroll
+  for (int q = 0; q < 10; ++q) m.gcon[q] = ld(DF_GCON + q);
+#pragma unroll
+  for (int q = 0; q < 6; ++q) m.gcov[q] = ld(DF_GCOV + q);
+  m.alpha = ld(DF_ALPHA);
+  m.ig = ld(DF_IG);
+  m.rho_fl = ld(DF_RHOFL);
+  m.u_fl = ld(DF_UFL);
+  return m;
+}
+#endif
+
+// g_ij x^i x^j for a spatial vector (double-float)
+KH_HD df64 spatial_sq(const MetDF& m, df64 a, df64 b, df64 c) {
+  const df64 d = m.gcov[0] * (a * a) + m.gcov[3] * (b * b) + m.gcov[5] * (c * c);
+  const df64 o = m.gcov[1] * (a * b) + m.gcov[2] * (a * c) + m.gcov[4] * (b * c);
+  return d + scale2(o, 2.0f);
+}
+
+// U: conserved variables of the zone (double-float, densitised); W0, vsq0:
+// initial guess (FP32, unscaled). On success P[0..4] holds the fluid
+// primitives (B^i = U_B / sqrt(-g) is left to the caller). Returns 0, a
+// noble2d failure code (2 v^2 >= 1, 3 W <= 0, 4 rho <= 0, 5 u < 0) or
+// C2P_NEED_FP64.
+KH_HD int noble2d_df(const df64* U, const MetDF& m, const MixedConsts& k, float W0, float vsq0, df64* P) {
+  const uint32_t wb = f32_bits(W0);
+  const int ew = (int)((wb >> 23) & 0xffu);
+  if (!(W0 > 0.0f) || ew == 0 || ew == 255) return C2P_NEED_FP64;
+  const int e2 = (ew - 127) >> 1;                    // S = 4^e2 = 2^(2 e2)
+  const float S = f32_of_bits((uint32_t)(127 + 2 * e2) << 23);
+  const float iS = f32_of_bits((uint32_t)(127 - 2 * e2) << 23);
+  const float iSb = f32_of_bits((uint32_t)(127 - e2) << 23);  // 1 / sqrt(S)
+  const df64 aig = m.alpha * m.ig;
+  const df64 as = scale2(aig, iS), ab = scale2(aig, iSb);
+  const df64 D = as * U[V_RHO];
+  const df64 Qc[4] = {as * (U[V_U] - U[V_RHO]), as * U[V_U1], as * U[V_U2], as * U[V_U3]};
+  df64 Qu[4];
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu)
+    Qu[mu] = m.gcon[sym_index(mu, 0)] * Qc[0] + m.gcon[sym_index(mu, 1)] * Qc[1] + m.gcon[sym_index(mu, 2)] * Qc[2] +
+             m.gcon[sym_index(mu, 3)] * Qc[3];
+  const df64 Qdn = -(m.alpha * Qu[0]);  // n_mu = (-alpha, 0, 0, 0)
+  const df64 Qsq = Qc[0] * Qu[0] + Qc[1] * Qu[1] + Qc[2] * Qu[2] + Qc[3] * Qu[3];
+  const df64 Qtsq = dfmax(Qsq + Qdn * Qdn, mkdf(0.0f, 0.0f));
+  const df64 Bc[3] = {ab * U[V_B1], ab * U[V_B2], ab * U[V_B3]};
+  const df64 Bsq = spatial_sq(m, Bc[0], Bc[1], Bc[2]);
+  const df64 QdB = Qc[1] * Bc[0] + Qc[2] * Bc[1] + Qc[3] * Bc[2];
+  const df64 QdB2 = QdB * QdB;
+  const df64 gf = mkdf(k.gfac_hi, k.gfac_lo);
+
+  // FP32 phase on the scaled invariants
+  float Wf = W0 * iS, vf = vsq0, ef = 1.0f;
+  if (!(vf >= 0.0f)) vf = 0.0f;
+  if (vf > 1.0f - 1e-7f) vf = 1.0f - 1e-7f;
+  const float Df = D.hi, Bf = Bsq.hi, QBf = QdB2.hi, gff = k.gfac_hi;
+  const bool ok32 = newton_wv<float>(Df, Qdn.hi, Qtsq.hi, Bf, QBf, gff, 12, 3e-6f, Wf, vf, ef);
+  if (!ok32 || !(vf < 1.0f - 1e-6f)) return C2P_NEED_FP64;
+
+  // one refinement: double-float residuals, FP32 Jacobian
+  df64 W = mkdf(Wf, 0.0f), vsq = mkdf(vf, 0.0f);
+  {
+    const df64 x = 1.0f - vsq;
+    const df64 sg = dfsqrt(x);
+    const df64 iW = rcp(W);
+    const df64 iW2 = iW * iW;
+    const df64 BW = Bsq + W;
+    const df64 p = gf * (W * x - D * sg);
+    const df64 r1 = Qtsq - vsq * (BW * BW) + QdB2 * (Bsq + scale2(W, 2.0f)) * iW2;
+    const df64 r2 = Qdn + W - p + scale2(Bsq * (1.0f + vsq), 0.5f) - scale2(QdB2 * iW2, 0.5f);
+    const float xg = 1.0f - vf, sgf = sqrtf(xg), BWf = Bf + Wf, iWf = 1.0f / Wf, iW3f = iWf * iWf * iWf;
+    const float j11 = -2.0f * vf * BWf - 2.0f * QBf * BWf * iW3f;
+    const float j12 = -BWf * BWf;
+    const float j21 = 1.0f - gff * xg + QBf * iW3f;
+    const float j22 = 0.5f * Bf - gff * (-Wf + 0.5f * Df / sgf);
+    const float idet = 1.0f / (j11 * j22 - j12 * j21);
+    const float dW = (j22 * r1.hi - j12 * r2.hi) * idet;
+    const float dv = (-j21 * r1.hi + j11 * r2.hi) * idet;
+    const df64 Wn = W - dW, vn = vsq - dv;
+    if (!(Wn.hi > 0.0f && vn.hi >= 0.0f && vn.hi < 1.0f - 1e-7f)) return C2P_NEED_FP64;
+    if (!(fabsf(dW) * iWf + fabsf(dv) < 1e-5f)) return C2P_NEED_FP64;
+    W = Wn;
+    vsq = vn;
+  }
+
+  // primitives (scaled rho, u times S; u~ is scale free)
+  const df64 x = 1.0f - vsq;
+  const df64 sg = dfsqrt(x);  // 1 / Lorentz factor
+  const df64 gamma = rcp(sg);
+  const df64 rho = D * sg;
+  const df64 uint = (W * x - rho) * mkdf(k.igam_hi, k.igam_lo);
+  if (!(rho.hi > 0.0f)) return 4;
+  if (!(uint.hi >= 0.0f)) return 5;
+  P[V_RHO] = scale2(rho, S);
+  P[V_U] = scale2(uint, S);
+  const df64 BW = W + Bsq;
+  const df64 inv = rcp(W * BW);
+  const df64 f = gamma * W * inv;
+  const df64 iWb = BW * inv;
+#pragma unroll
+  for (int i = 1; i < 4; ++i) {
+    const df64 nu = -(m.alpha * m.gcon[sym_index(i, 0)]);  // n^i = -alpha g^{it}
+    P[V_U1 + i - 1] = f * (Qu[i] + nu * Qdn + QdB * Bc[i - 1] * iWb);
+  }
+  return 0;
+}
+
+}  // namespace kh

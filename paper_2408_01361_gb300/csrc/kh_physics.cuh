@@ -16,6 +16,12 @@ namespace kh {
 
 enum { V_RHO = 0, V_U = 1, V_U1 = 2, V_U2 = 3, V_U3 = 4, V_B1 = 5, V_B2 = 6, V_B3 = 7, NV = 8 };
 
+// Symmetric-pair index of (m, n): 00 01 02 03 11 12 13 22 23 33.
+KH_HD int sym_index(int m, int n) {
+  if (m > n) { int t = m; m = n; n = t; }
+  return m == 0 ? n : (m == 1 ? 3 + n : (m == 2 ? 5 + n : 9));
+}
+
 // 1/sqrt(x) (CUDA's rsqrt on the device; it gives sqrt(x) = x rsqrt(x) and its
 // reciprocal from one operation).
 KH_HD double krsqrt(double x) {

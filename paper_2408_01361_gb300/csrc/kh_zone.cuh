@@ -3,6 +3,7 @@
 #pragma once
 
 #include "kh_internal.h"
+#include "kh_mixed.cuh"
 
 namespace kh {
 
@@ -275,26 +276,30 @@ __device__ __forceinline__ void update_zone(const double* U0, const CVars& Pin, 
 }
 
 
-// Mixed-precision update of one interior zone: the divergence of the FP32
-// fluxes and the FP32 source terms (FP32 metric and connection) give dU in
-// FP32; U = U0 + cdt dU is accumulated in FP64; the Noble-2D inversion and the
-// floors run in FP64 on the FP64 metric. The stage input is read in FP32 only
-// (both stages' inputs exist as FP32 arrays): it gives the sources, the
-// inversion's initial guess, and the output of a zone whose inversion failed.
+// The mixed update of one zone, FP64 arithmetic only where the result is
+// FP64 storage. FP32: the stage input, the sources, the flux divergence, the
+// increment c dt (S - div F), the floors' decisions and b^2. Double-float
+// (kh_df64.cuh, on the FP32 pipe): the updated conserved variables entering
+// the inversion, the inversion (noble2d_df) and the primitives. FP64: the
+// stored conserved variables U^n + increment (an FP64 add per variable, the
+// conserved update exact to FP64 as in the FP64 path), the FP64 primitives
+// written at stage 2 (one add of the pair each) and the FP64 fallback
+// inversion of the zones noble2d_df hands back.
 __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT<float>& Pin, const Vars& Pout64,
                                                   const VarsT<float>& Pout32, double* Uout, const float* F1,
                                                   const float* F2, const float* F3, const Layout& L, const DevGeom& G,
-                                                  const GeomT<float>& Gf, const Scheme& S, double cdt, int8_t* pflag,
+                                                  const GeomT<float>& Gf, const Scheme& S, df64 cdt, int8_t* pflag,
                                                   unsigned long long* cnt, int i, int j, int k) {
   const long long c = L.at(k, j, i);
   const long long p = (long long)j * L.n1s + i;
   const long long sj = L.n1s, sk = (long long)L.n1s * L.n2s;
+  const MixedConsts& mx = S.mx;
   float Pf[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) Pf[v] = Pin.v[v][c];
   float Sv[NV] = {0, 0, 0, 0, 0, 0, 0, 0};
   const Met<float> mf = load_met(Gf, L.gplane, LOC_CENT, p);
-  source_terms(Pf, mf, Gf.conn, L.gplane, p, (float)S.gam, Sv);
+  source_terms(Pf, mf, Gf.conn, L.gplane, p, mx.gam, Sv);
   // initial guess of the inversion from the FP32 input: W = (rho + gam u) gamma^2, v^2 = q / gamma^2
   float W0, vsq0;
   {
@@ -302,79 +307,103 @@ __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT
     const float q = mf.gcov[1][1] * v1 * v1 + mf.gcov[2][2] * v2 * v2 + mf.gcov[3][3] * v3 * v3 +
                     2.0f * (mf.gcov[1][2] * v1 * v2 + mf.gcov[1][3] * v1 * v3 + mf.gcov[2][3] * v2 * v3);
     const float g2 = 1.0f + q;
-    W0 = (Pf[V_RHO] + (float)S.gam * Pf[V_U]) * g2;
+    W0 = (Pf[V_RHO] + mx.gam * Pf[V_U]) * g2;
     vsq0 = q / g2;
   }
   const float i1 = (float)L.idx[0], i2 = (float)L.idx[1], i3 = (float)L.idx[2];
-  double U[NV];
+  double U[NV];   // stored conserved variables (stage 2)
+  df64 Ud[NV];    // the same, double-float, for the inversion
+  float inc[NV];  // c dt (S - div F)
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     const long long o = v * L.plane + c;
     float div = (F1[o + 1] - F1[o]) * i1 + (F2[o + sj] - F2[o]) * i2;
     if (L.ndim == 3) div += (F3[o + sk] - F3[o]) * i3;
-    U[v] = U0[o] + cdt * (double)(Sv[v] - div);
+    inc[v] = (cdt * (Sv[v] - div)).hi;
+    const double u0 = U0[o];
+    if (Uout) U[v] = u0 + f64_of_f32(inc[v]);
+    Ud[v] = df_of_f64(u0) + inc[v];
   }
-  const Met<double> m = load_met(G, L.gplane, LOC_CENT, p);
-  const double ig = __ldg(G.flo + 2 * L.gplane + p);  // 1 / sqrt(-g)
-  double Pn[NV];
-  const int flag = noble2d_mixed(U, m, ig, S.gam, S.igam, S.gfac, S.c2p, W0, vsq0, Pn);
+  const MetDF md = load_metdf(Gf.df, L.gplane, p);
+  df64 Pn[NV];
+  int flag = noble2d_df(Ud, md, mx, W0, vsq0, Pn);
+  if (flag == C2P_NEED_FP64) {
+    // FP64 inversion of this zone from the stage input
+    double Uf[NV], Pd[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      Uf[v] = Uout ? U[v] : U0[v * L.plane + c] + f64_of_f32(inc[v]);
+      Pd[v] = f64_of_f32(Pf[v]);
+    }
+    const Met<double> m = load_met(G, L.gplane, LOC_CENT, p);
+    flag = noble2d(Uf, m, __ldg(G.flo + 2 * L.gplane + p), S.gam, S.igam, S.gfac, S.c2p, Pd);
+    if (flag == 0) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) Pn[v] = df_of_f64(Pd[v]);
+    }
+  }
   if (flag) {
 #pragma unroll
-    for (int v = 0; v < 5; ++v) Pn[v] = (double)Pf[v];
+    for (int v = 0; v < 5; ++v) Pn[v] = mkdf(Pf[v], 0.0f);
   }
-  Pn[V_B1] = U[V_B1] * ig;
-  Pn[V_B2] = U[V_B2] * ig;
-  Pn[V_B3] = U[V_B3] * ig;
+  Pn[V_B1] = Ud[V_B1] * md.ig;
+  Pn[V_B2] = Ud[V_B2] * md.ig;
+  Pn[V_B3] = Ud[V_B3] * md.ig;
   int fmask = 0;
   if (flag == 0) {
-    // FP32 fluid state for the magnetisation floors (a threshold) and for the
-    // conserved increment of a density/energy floor.
+    // floors: decisions on FP32 b^2 and Lorentz factor, values in double-float
     float q[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) q[v] = (float)Pn[v];
+    for (int v = 0; v < NV; ++v) q[v] = Pn[v].hi;
     FState<float> sf;
     fluid_state(q, mf, sf);
-    const double rho0 = Pn[V_RHO], u0 = Pn[V_U];
-    const float gq = mf.alpha * sf.ucon[0];  // Lorentz factor: the FP32 estimate of gamma^2 - 1 gates the ceiling
-    fmask = apply_floors(S.fl, m, __ldg(G.flo + p), __ldg(G.flo + L.gplane + p), (double)sf.bsq, Pn,
-                         (double)fmaxf(gq * gq - 1.0f, 0.0f));
+    const df64 rho0 = Pn[V_RHO], u0 = Pn[V_U];
+    const df64 rf = dfmax(md.rho_fl, mkdf(sf.bsq * mx.ibsq_rho_max, 0.0f));
+    const df64 uf = dfmax(md.u_fl, mkdf(sf.bsq * mx.ibsq_u_max, 0.0f));
+    if (Pn[V_RHO] < rf) { Pn[V_RHO] = rf; fmask |= 1; }
+    if (Pn[V_U] < uf) { Pn[V_U] = uf; fmask |= 1; }
+    const df64 umax = Pn[V_RHO] * mx.u_rho_max;
+    if (Pn[V_U] > umax) { Pn[V_U] = umax; fmask |= 2; }
+    const float gq = mf.alpha * sf.ucon[0];  // Lorentz factor (FP32 estimate gates the exact test)
+    if (gq * gq > 0.999f * mx.g2max) {
+      const df64 qq = spatial_sq(md, Pn[V_U1], Pn[V_U2], Pn[V_U3]);
+      if (qq.hi + 1.0f > mx.g2max) {
+        const df64 sc = dfsqrt(mkdf(mx.g2max - 1.0f, 0.0f) / qq);
+        Pn[V_U1] = Pn[V_U1] * sc;
+        Pn[V_U2] = Pn[V_U2] * sc;
+        Pn[V_U3] = Pn[V_U3] * sc;
+        fmask |= 4;
+      }
+    }
     if (fmask && Uout) {
       if (fmask & 4) {  // the Lorentz-factor ceiling changed u~: full FP64 recompute
+        double Pd[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Pd[v] = f64_of_df(Pn[v]);
+        const Met<double> m = load_met(G, L.gplane, LOC_CENT, p);
         FState<double> s;
-        fluid_state(Pn, m, s);
-        cons_only(Pn, s, m, S.gam, U);
+        fluid_state(Pd, m, s);
+        cons_only(Pd, s, m, S.gam, U);
       } else {
         // at fixed u~ and B, U is linear in (rho, u): add
         // drho dU/drho + du dU/du, formed in FP32, to the FP64 U
-        const float drho = (float)(Pn[V_RHO] - rho0), du = (float)(Pn[V_U] - u0);
-        const float gm = (float)S.gam, gd = mf.gdet, ut = sf.ucon[0];
-        U[V_RHO] += (double)(gd * ut * drho);
-        U[V_U] += (double)(gd * ((ut * sf.ucov[0] + ut) * drho + (gm * ut * sf.ucov[0] + gm - 1.0f) * du));
-        U[V_U1] += (double)(gd * ut * sf.ucov[1] * (drho + gm * du));
-        U[V_U2] += (double)(gd * ut * sf.ucov[2] * (drho + gm * du));
-        U[V_U3] += (double)(gd * ut * sf.ucov[3] * (drho + gm * du));
+        const float drho = (Pn[V_RHO] - rho0).hi, du = (Pn[V_U] - u0).hi;
+        const float gm = mx.gam, gd = mf.gdet, ut = sf.ucon[0];
+        U[V_RHO] += f64_of_f32(gd * ut * drho);
+        U[V_U] += f64_of_f32(gd * ((ut * sf.ucov[0] + ut) * drho + (gm * ut * sf.ucov[0] + gm - 1.0f) * du));
+        U[V_U1] += f64_of_f32(gd * ut * sf.ucov[1] * (drho + gm * du));
+        U[V_U2] += f64_of_f32(gd * ut * sf.ucov[2] * (drho + gm * du));
+        U[V_U3] += f64_of_f32(gd * ut * sf.ucov[3] * (drho + gm * du));
       }
     }
-    if (Pout32.v[0]) {
-      if (fmask) {
-        q[V_RHO] = (float)Pn[V_RHO];
-        q[V_U] = (float)Pn[V_U];
-        if (fmask & 4) {
-          q[V_U1] = (float)Pn[V_U1];
-          q[V_U2] = (float)Pn[V_U2];
-          q[V_U3] = (float)Pn[V_U3];
-        }
-      }
+  }
+  if (Pout32.v[0]) {
 #pragma unroll
-      for (int v = 0; v < NV; ++v) Pout32.v[v][c] = q[v];
-    }
-  } else if (Pout32.v[0]) {
-#pragma unroll
-    for (int v = 0; v < NV; ++v) Pout32.v[v][c] = v < 5 ? Pf[v] : (float)Pn[v];
+    for (int v = 0; v < NV; ++v) Pout32.v[v][c] = Pn[v].hi;
   }
   if (Pout64.v[0]) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) Pout64.v[v][c] = Pn[v];
+    for (int v = 0; v < NV; ++v) Pout64.v[v][c] = f64_of_df(Pn[v]);
   }
   if (Uout) {
 #pragma unroll
