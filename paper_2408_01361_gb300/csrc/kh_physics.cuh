@@ -362,11 +362,8 @@ struct FloorParams {
 
 // rho_geo, u_geo: the geometric floors max(rho_min r^-3/2, 1e-20) and
 // max(u_min r^-5/2, 1e-20) of the zone (cached per (i, j)); bsq: b^2 of P.
-// q_est >= 0: an estimate of g_ij u~^i u~^j (= gamma^2 - 1) that only decides
-// whether the Lorentz-factor ceiling applies (the exact FP64 value is then
-// formed for the rescaling); q_est < 0: formed in FP64 here.
 KH_HD int apply_floors(const FloorParams& f, const Met<double>& m, double rho_geo, double u_geo, double bsq,
-                       double* P, double q_est = -1.0) {
+                       double* P) {
   double rf = rho_geo, uf = u_geo;
   const double rb = bsq * f.ibsq_rho_max, ub = bsq * f.ibsq_u_max;
   rf = rf > rb ? rf : rb;
@@ -382,10 +379,8 @@ KH_HD int apply_floors(const FloorParams& f, const Met<double>& m, double rho_ge
     return m.gcov[1][1] * v1 * v1 + m.gcov[2][2] * v2 * v2 + m.gcov[3][3] * v3 * v3 +
            2.0 * (m.gcov[1][2] * v1 * v2 + m.gcov[1][3] * v1 * v3 + m.gcov[2][3] * v2 * v3);
   };
-  const double qt = q_est >= 0.0 ? q_est : qexact();
-  if (1.0 + qt > g2max * (q_est >= 0.0 ? 0.999 : 1.0)) {
-    const double q = q_est >= 0.0 ? qexact() : qt;
-    if (!(1.0 + q > g2max)) return mask;
+  const double q = qexact();
+  if (1.0 + q > g2max) {
     const double sc = sqrt((g2max - 1.0) / q);
     P[V_U1] *= sc;
     P[V_U2] *= sc;
@@ -396,15 +391,9 @@ KH_HD int apply_floors(const FloorParams& f, const Met<double>& m, double rho_ge
 }
 
 // ---------------------------------------------------------------------------
-// Mixed-precision inversion: the same (W, v^2) equations, with the Newton
-// iterations first run in FP32 on the problem scaled by a power of two
-// S ~ W (exact in either precision: every term of f1 scales as S^2, of f2 as
-// S), then finished in FP64. The FP64 phase stops once a step changes
-// |dW/W| + |dv^2| by less than a threshold (1e-5 after a converged FP32
-// phase, else 1e-6), i.e. the iterate it produced lies in Newton's quadratic
-// regime (its error ~ that step squared). Invariants D, Q.n, Q~^2, B^2,
-// (Q.B)^2 are formed in FP64 as in noble2d, from the cached 1/sqrt(-g). The
-// initial guess (W, v^2) comes from the FP32 stage input.
+// Newton's iterations on the (W, v^2) equations of noble2d in precision R
+// (the FP32 phase of the mixed update's inversion, on the problem scaled to
+// order unity): stops when a step changes |dW/W| + |dv^2| by less than stop.
 // ---------------------------------------------------------------------------
 template <class R>
 KH_HD bool newton_wv(R D, R Qdn, R Qtsq, R Bsq, R QdB2, R gf, int max_iter, R stop, R& W, R& vsq, R& err) {
@@ -438,124 +427,6 @@ KH_HD bool newton_wv(R D, R Qdn, R Qtsq, R Bsq, R QdB2, R gf, int max_iter, R st
     if (err < stop) return true;
   }
   return false;
-}
-
-// FP64 values refined from FP32 seeds by one Newton step each (Newton's
-// iteration for the square root, s <- s + (x - s^2) / (2 s), and for the
-// reciprocal, r <- r + r (1 - y r)): the seed's relative error e (~6e-8)
-// becomes ~e^2, well below the mixed path's FP32 flux error. x and y must lie
-// in FP32's normal range (the callers scale them by powers of two).
-KH_HD double sqrt_from_f32(double x) {
-  const float sf = sqrtf((float)x);
-  const double s = (double)sf;
-  return s + (x - s * s) * (0.5 * (double)(1.0f / sf));
-}
-KH_HD double rcp_from_f32(double y) {
-  const double r = (double)(1.0f / (float)y);
-  return r + r * (1.0 - y * r);
-}
-
-KH_HD int noble2d_mixed(const double* U, const Met<double>& m, double ig, double gam, double igam, double gf,
-                        const C2POpts& o, float W0, float vsq0, double* P) {
-  const double a = m.alpha;
-  const double aig = a * ig;
-  const double D = aig * U[V_RHO];
-  const double Qc[4] = {aig * (U[V_U] - U[V_RHO]), aig * U[V_U1], aig * U[V_U2], aig * U[V_U3]};
-  double Qu[4];
-#pragma unroll
-  for (int mu = 0; mu < 4; ++mu)
-    Qu[mu] = m.gcon[mu][0] * Qc[0] + m.gcon[mu][1] * Qc[1] + m.gcon[mu][2] * Qc[2] + m.gcon[mu][3] * Qc[3];
-  // n^mu = -alpha g^{mu t}, so Q.n = -alpha Q^t
-  const double nu[4] = {0.0, -a * m.gcon[1][0], -a * m.gcon[2][0], -a * m.gcon[3][0]};
-  const double Qdn = -a * Qu[0];
-  const double Qsq = Qc[0] * Qu[0] + Qc[1] * Qu[1] + Qc[2] * Qu[2] + Qc[3] * Qu[3];
-  const double Qtsq = fmax(Qsq + Qdn * Qdn, 0.0);
-  const double Bc1 = aig * U[V_B1], Bc2 = aig * U[V_B2], Bc3 = aig * U[V_B3];
-  const double Bsq = m.gcov[1][1] * Bc1 * Bc1 + m.gcov[2][2] * Bc2 * Bc2 + m.gcov[3][3] * Bc3 * Bc3 +
-                     2.0 * (m.gcov[1][2] * Bc1 * Bc2 + m.gcov[1][3] * Bc1 * Bc3 + m.gcov[2][3] * Bc2 * Bc3);
-  const double QdB = Qc[1] * Bc1 + Qc[2] * Bc2 + Qc[3] * Bc3;
-  const double QdB2 = QdB * QdB;
-
-  double W = (double)W0, vsq = (double)vsq0;
-  if (!(W > 0.0) || !isfinite(W)) W = fabs(Qdn) + 1e-300;
-  if (!(vsq >= 0.0)) vsq = 0.0;
-  if (vsq > 1.0 - 1e-16) vsq = 1.0 - 1e-16;
-
-  // FP32 phase on the problem scaled by S = 2^e ~ W
-  bool done = false;
-  double S = 1.0, iS = 1.0;
-  {
-    int e = 0;
-    frexp(W, &e);
-    S = ldexp(1.0, e);
-    iS = ldexp(1.0, -e);
-    const float Df = (float)(D * iS), Qnf = (float)(Qdn * iS), Qtf = (float)(Qtsq * iS * iS), Bf = (float)(Bsq * iS);
-    const float QBf = (float)(QdB2 * iS * iS * iS), gff = (float)gf;
-    float Wf = (float)(W * iS), vf = (float)vsq, ef = 1.0f;
-    const bool ok32 = newton_wv<float>(Df, Qnf, Qtf, Bf, QBf, gff, 12, 3e-6f, Wf, vf, ef);
-    if (ok32 || (isfinite(Wf) && isfinite(vf) && Wf > 0.0f && ef < 1e-3f)) {
-      W = (double)Wf * S;
-      vsq = (double)vf;
-    }
-    if (ok32 && vf < 1.0f - 1e-6f) {
-      // One refinement: the residuals (f1, f2) in FP64 at the FP32 root,
-      // the correction through the FP32 Jacobian of the scaled system (f1
-      // scales as S^2, f2 as S): the Jacobian's FP32 error multiplies a
-      // step of ~1e-7, so the refined iterate is as good as an FP64 Newton
-      // step's. Accepted when the step is below 1e-5; else the FP64 loop.
-      const double x = 1.0 - vsq;
-      const double sg = sqrt_from_f32(x);
-      const double iW = rcp_from_f32(W * iS) * iS;
-      const double p = gf * (W * x - D * sg);
-      const double BW = Bsq + W;
-      const double iW2 = iW * iW;
-      const double f1 = Qtsq - vsq * BW * BW + QdB2 * (Bsq + 2.0 * W) * iW2;
-      const double f2 = Qdn + W - p + 0.5 * Bsq * (1.0 + vsq) - 0.5 * QdB2 * iW2;
-      // scaled FP32 Jacobian at (Wf, vf)
-      const float xg = 1.0f - vf, sgf = sqrtf(xg), BWf = Bf + Wf, iWf = 1.0f / Wf, iW3f = iWf * iWf * iWf;
-      const float j11 = -2.0f * vf * BWf - 2.0f * QBf * BWf * iW3f;
-      const float j12 = -BWf * BWf;
-      const float j21 = 1.0f - gff * xg + QBf * iW3f;
-      const float j22 = 0.5f * Bf - gff * (-Wf + 0.5f * Df / sgf);
-      const float idet = 1.0f / (j11 * j22 - j12 * j21);
-      const float g1 = (float)(f1 * iS * iS), g2 = (float)(f2 * iS);
-      const double dW = (double)((j22 * g1 - j12 * g2) * idet) * S;
-      const double dv = (double)((-j21 * g1 + j11 * g2) * idet);
-      const double Wn = W - dW, vn = vsq - dv;
-      if (Wn > 0.0 && vn >= 0.0 && vn < 1.0 - 1e-16) {
-        const double err = fabs(dW) * iW + fabs(dv);
-        W = Wn;
-        vsq = vn;
-        done = err < 1e-5;
-      }
-    }
-  }
-  if (!done) {
-    double err = 1.0;
-    const bool conv = newton_wv<double>(D, Qdn, Qtsq, Bsq, QdB2, gf, o.max_iter, 1e-6, W, vsq, err);
-    if (!conv && !(err < 1e-9)) return 1;
-  }
-  if (!(W > 0.0)) return 3;
-  if (!(vsq < 1.0) || vsq < 0.0) return 2;
-  // primitives from (W, v^2); roots and reciprocals refined from FP32 seeds
-  // (1 - v^2 >= 1e-16 and the scaled W (W + B^2) are in FP32's normal range)
-  const double x = 1.0 - vsq;
-  const double sg = sqrt_from_f32(x);  // 1 / Lorentz factor
-  const double gamma = rcp_from_f32(sg);
-  const double rho = D * sg;
-  const double uint = (W * x - rho) * igam;
-  if (!(rho > 0.0)) return 4;
-  if (!(uint >= 0.0)) return 5;
-  P[V_RHO] = rho;
-  P[V_U] = uint;
-  const double BW = W + Bsq;
-  const double inv = rcp_from_f32(W * BW * iS * iS) * iS * iS;  // 1 / (W (W + B^2))
-  const double f = gamma * W * inv;
-  const double iW = BW * inv;
-  P[V_U1] = f * (Qu[1] + nu[1] * Qdn + QdB * Bc1 * iW);
-  P[V_U2] = f * (Qu[2] + nu[2] * Qdn + QdB * Bc2 * iW);
-  P[V_U3] = f * (Qu[3] + nu[3] * Qdn + QdB * Bc3 * iW);
-  return 0;
 }
 
 }  // namespace kh
