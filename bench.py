@@ -236,7 +236,8 @@ def measure(args, cfg, P0, ctx, dev, stream, dist, world, oracle_step):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     out = {"value": nz * args.steps * world / (ms * 1e-3), "ms": ms, "prof": prof, "launches": launches,
-           "clocks": clocks, "err": err, "nfail": nfail, "launch": {"tpb_flux": tuned[0], "tpb_update": tuned[1]}}
+           "clocks": clocks, "err": err, "nfail": nfail, "launch": {"tpb_flux": tuned[0], "tpb_update": tuned[1]},
+           "nfp64": int(ctx.stats().nfp64)}  # zones of the last timed step whose inversion fell back to FP64
     # the same K steps replayed as a CUDA graph (no per-kernel events)
     ctx.set_graph(True)
     dt, _ = ctx.step(U, P, B, 0.5 * dt)
@@ -386,9 +387,10 @@ def measure_adjoint(args, dev, stream, nsteps: int = 20):
 
 def roofline_of(prof, nz, precision):
     """Roofline of the kernel group with the largest share of the profiled
-    step time: FP64-ALU bound (the update on both paths, the FP64 flux) with
-    the executed FP64 flops per zone; the FP32 flux of the mixed path beside
-    it against the FP32 peak."""
+    step time, the others beside it: FP64 path -- FP64-ALU bound kernels with
+    their executed FP64 flops per zone; mixed path -- the face kernels and the
+    update (double-float inversion) with their executed FP32 flops per zone
+    against the FP32 peak."""
     hbm, hbm_kind, sm_max = peaks()
     groups = {k: v for k, v in prof.items() if v[1] > 0}
     top = max(groups, key=lambda k: groups[k][0])
@@ -485,7 +487,8 @@ def run_kh(args, world, rank, local):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": roof, "hbm_step": hbm_step, "kernel_share": share,
         "cpu_baseline": cpu, "err_vs_oracle": r["err"], "e2e": r.get("e2e"), "gpu_launches": r["launches"],
-        "clocks": r["clocks"], "nfail_timed": r["nfail"], "launch_config": r["launch"], "graph_replay": r["graph"],
+        "clocks": r["clocks"], "nfail_timed": r["nfail"], "nfp64_last_step": r["nfp64"], "launch_config": r["launch"],
+        "graph_replay": r["graph"],
     }
     for prec in args.precisions[1:]:
         q = results[prec]
@@ -511,15 +514,15 @@ def run_kh(args, world, rank, local):
 # counts 2, DADD/DMUL/FADD/FMUL 1), and DRAM bytes (read + write) per zone
 # per launch. Launch totals at the bench size scale by the zone count.
 FP64_FLOPS_PER_ZONE: dict = {
-    ("mixed", "update"): 215.0,  # stages 1 and 2 (214, 216)
     ("fp64", "update"): 947.0,
     ("fp64", "flux_x1"): 2102.3, ("fp64", "flux_x2"): 2091.0, ("fp64", "flux_x3"): 2083.5,
 }
 FP32_FLOPS_PER_ZONE: dict = {
     ("mixed", "flux_x1"): 1530.0, ("mixed", "flux_x2"): 1611.0, ("mixed", "flux_x3"): 1677.0,
+    ("mixed", "update"): 2261.0,  # stages 1 and 2 (2246, 2276); FP64: 6 and 26 flops per zone
 }
 DRAM_BYTES_PER_ZONE: dict = {
-    ("mixed", "update"): 282.6,  # mean of stage 1 (245.4) and stage 2 (319.5)
+    ("mixed", "update"): 303.4,  # mean of stage 1 (263.5) and stage 2 (343.2)
     ("mixed", "flux_x1"): 44.4, ("mixed", "flux_x2"): 46.0, ("mixed", "flux_x3"): 47.7,
     ("fp64", "update"): 419.1,  # stage 1
     ("fp64", "flux_x1"): 118.0, ("fp64", "flux_x2"): 126.1, ("fp64", "flux_x3"): 128.3,

@@ -74,6 +74,7 @@ typedef struct {
   int64_t nfloor;   /* zones where a floor or ceiling was applied */
   int64_t nunfixed; /* failed zones with no good neighbour (kept the stage input) */
   double dt_cfl;    /* CFL time step for the next step */
+  int64_t nfp64;    /* KH_MIXED: zones whose inversion fell back to the FP64 Newton iteration */
 } kh_stats;
 
 typedef struct kh_ctx kh_ctx;

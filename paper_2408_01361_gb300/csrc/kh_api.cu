@@ -234,7 +234,10 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
   L.dx[0] = (c->x1max - c->x1min) / c->n1;
   L.dx[1] = (c->x2max - c->x2min) / c->n2;
   L.dx[2] = (c->x3max - c->x3min) / c->n3;
-  for (int q = 0; q < 3; ++q) L.idx[q] = 1.0 / L.dx[q];
+  for (int q = 0; q < 3; ++q) {
+    L.idx[q] = 1.0 / L.dx[q];
+    L.idxf[q] = (float)L.idx[q];
+  }
   L.s[0] = L.ng; L.e[0] = L.ng + L.n1;
   L.s[1] = L.ng; L.e[1] = L.ng + L.n2;
   L.s[2] = L.ng3; L.e[2] = L.ng3 + L.n3;
@@ -666,6 +669,7 @@ int kh_get_stats(kh_ctx* x, kh_stats* out) {
   out->nfail = (int64_t)h[CNT_FAIL];
   out->nfloor = (int64_t)h[CNT_FLOOR];
   out->nunfixed = (int64_t)h[CNT_UNFIXED];
+  out->nfp64 = (int64_t)h[CNT_FP64];
   out->dt_cfl = dt;
   x->last = *out;
   return h[CNT_TIMEOUT] ? KH_ETIMEOUT : KH_OK;

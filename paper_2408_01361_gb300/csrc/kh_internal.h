@@ -22,6 +22,7 @@ struct Layout {
   long long gplane;   // n1s * n2s
   double dx[3];
   double idx[3];      // 1 / dx
+  float idxf[3];      // the same, FP32 (mixed update)
   int s[3], e[3];     // interior [s, e) per direction (i, j, k)
   KH_HD long long at(int k, int j, int i) const { return ((long long)k * n2s + j) * n1s + i; }
 };
@@ -61,7 +62,8 @@ struct Scheme {
 inline void set_mixed(Scheme& S) { S.mx = mixed_consts(S.gam, S.fl); }
 
 // Counters kept on the device for one step.
-enum { CNT_FAIL = 0, CNT_FLOOR = 1, CNT_UNFIXED = 2, CNT_TIMEOUT = 3, NCNT = 4 };
+// CNT_FP64: zones of the mixed update whose inversion fell back to FP64
+enum { CNT_FAIL = 0, CNT_FLOOR = 1, CNT_UNFIXED = 2, CNT_TIMEOUT = 3, CNT_FP64 = 4, NCNT = 5 };
 
 // ---- launchers (kh_kernels.cu); each returns the number of kernels launched ----
 // Geometry of a grid whose first interior cell starts at native (x1o, x2o);

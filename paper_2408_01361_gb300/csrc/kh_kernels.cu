@@ -203,7 +203,9 @@ __global__ void __launch_bounds__(TPB_MAX) k_update(const double* U0, CVars Pin,
   update_zone(U0, Pin, Pout, Uout, F1, F2, F3, L, G, S, coef * __ldg(dtp), pflag, cnt, i, j, k);
 }
 
-__global__ void __launch_bounds__(TPB_MAX) k_update_mixed(const double* U0, CVarsT<float> Pin, Vars Pout64,
+// three blocks of TPB_MAX per SM: ~80 registers (a few spill to L1); measured faster
+// than the unconstrained 128 registers at 16 warps per SM
+__global__ void __launch_bounds__(TPB_MAX, 3) k_update_mixed(const double* U0, CVarsT<float> Pin, Vars Pout64,
                                                          VarsT<float> Pout32, double* Uout, const float* F1,
                                                          const float* F2, const float* F3, Layout L, DevGeom G,
                                                          GeomT<float> Gf, Scheme S, const double* dtp, double coef,

@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(256) km_update(const MBlock* blk, const unsign
               k);
 }
 
-__global__ void __launch_bounds__(256) km_update_mixed(const MBlock* blk, const unsigned* pre, int nb,
+__global__ void __launch_bounds__(256, 2) km_update_mixed(const MBlock* blk, const unsigned* pre, int nb,
                                                       const double* U0, Arena<float> Pin, Arena<double> Pout64,
                                                       Arena<float> Pout32, double* Uout, const float* F1,
                                                       const float* F2, const float* F3, GeoArena GA, Scheme S,
@@ -577,6 +577,7 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
       const double rr = (double)(loc.ratio_pow(d, 0) / loc.ratio_pow(d, B.level));
       L.dx[d] = dx0[d] / rr;
       L.idx[d] = 1.0 / L.dx[d];
+      L.idxf[d] = (float)L.idx[d];
     }
     L.s[0] = L.ng; L.e[0] = L.ng + L.n1;
     L.s[1] = L.ng; L.e[1] = L.ng + L.n2;
@@ -1068,6 +1069,7 @@ int kh_mesh_get_stats(kh_mesh* x, kh_stats* out) {
   out->nfail = (int64_t)h[CNT_FAIL];
   out->nfloor = (int64_t)h[CNT_FLOOR];
   out->nunfixed = (int64_t)h[CNT_UNFIXED];
+  out->nfp64 = (int64_t)h[CNT_FP64];
   out->dt_cfl = dt;
   return KH_OK;
 }

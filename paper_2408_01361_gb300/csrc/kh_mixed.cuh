@@ -135,12 +135,12 @@ KH_HD int noble2d_df(const df64* U, const MetDF& m, const MixedConsts& k, float 
     const df64 p = gf * (W * x - D * sg);
     const df64 r1 = Qtsq - vsq * (BW * BW) + QdB2 * (Bsq + scale2(W, 2.0f)) * iW2;
     const df64 r2 = Qdn + W - p + scale2(Bsq * (1.0f + vsq), 0.5f) - scale2(QdB2 * iW2, 0.5f);
-    const float xg = 1.0f - vf, sgf = sqrtf(xg), BWf = Bf + Wf, iWf = 1.0f / Wf, iW3f = iWf * iWf * iWf;
+    const float xg = 1.0f - vf, BWf = Bf + Wf, iWf = kdiv(1.0f, Wf), iW3f = iWf * iWf * iWf;
     const float j11 = -2.0f * vf * BWf - 2.0f * QBf * BWf * iW3f;
     const float j12 = -BWf * BWf;
     const float j21 = 1.0f - gff * xg + QBf * iW3f;
-    const float j22 = 0.5f * Bf - gff * (-Wf + 0.5f * Df / sgf);
-    const float idet = 1.0f / (j11 * j22 - j12 * j21);
+    const float j22 = 0.5f * Bf - gff * (-Wf + 0.5f * Df * krsqrt(xg));
+    const float idet = kdiv(1.0f, j11 * j22 - j12 * j21);
     const float dW = (j22 * r1.hi - j12 * r2.hi) * idet;
     const float dv = (-j21 * r1.hi + j11 * r2.hi) * idet;
     const df64 Wn = W - dW, vn = vsq - dv;

@@ -404,7 +404,7 @@ KH_HD bool newton_wv(R D, R Qdn, R Qtsq, R Bsq, R QdB2, R gf, int max_iter, R st
     const R sg = g2i * rs;     // 1 / gamma
     const R p = gf * (W * g2i - D * sg);
     const R BW = Bsq + W;
-    const R iW = R(1) / W;
+    const R iW = kdiv(R(1), W);
     const R iW2 = iW * iW;
     const R f1 = Qtsq - vsq * BW * BW + QdB2 * (Bsq + R(2) * W) * iW2;
     const R f2 = Qdn + W - p + R(0.5) * Bsq * (R(1) + vsq) - R(0.5) * QdB2 * iW2;
@@ -414,7 +414,7 @@ KH_HD bool newton_wv(R D, R Qdn, R Qtsq, R Bsq, R QdB2, R gf, int max_iter, R st
     const R j12 = -BW * BW;
     const R j21 = R(1) - dpdW + QdB2 * iW2 * iW;
     const R j22 = R(0.5) * Bsq - dpdv;
-    const R idet = R(1) / (j11 * j22 - j12 * j21);
+    const R idet = kdiv(R(1), j11 * j22 - j12 * j21);
     R Wn = W - (j22 * f1 - j12 * f2) * idet;
     R vn = vsq - (-j21 * f1 + j11 * f2) * idet;
     if (!(Wn > R(0))) Wn = R(0.5) * W;

@@ -294,46 +294,50 @@ __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT
   const long long p = (long long)j * L.n1s + i;
   const long long sj = L.n1s, sk = (long long)L.n1s * L.n2s;
   const MixedConsts& mx = S.mx;
-  float Pf[NV];
-#pragma unroll
-  for (int v = 0; v < NV; ++v) Pf[v] = Pin.v[v][c];
-  float Sv[NV] = {0, 0, 0, 0, 0, 0, 0, 0};
-  const Met<float> mf = load_met(Gf, L.gplane, LOC_CENT, p);
-  source_terms(Pf, mf, Gf.conn, L.gplane, p, mx.gam, Sv);
-  // initial guess of the inversion from the FP32 input: W = (rho + gam u) gamma^2, v^2 = q / gamma^2
-  float W0, vsq0;
+  // the stored U (stage 2) is written here and touched again only by floors
+  df64 Ud[NV];    // U^n + increment, double-float, for the inversion
+  float W0, vsq0; // initial guess of the inversion from the FP32 input
   {
-    const float v1 = Pf[V_U1], v2 = Pf[V_U2], v3 = Pf[V_U3];
-    const float q = mf.gcov[1][1] * v1 * v1 + mf.gcov[2][2] * v2 * v2 + mf.gcov[3][3] * v3 * v3 +
-                    2.0f * (mf.gcov[1][2] * v1 * v2 + mf.gcov[1][3] * v1 * v3 + mf.gcov[2][3] * v2 * v3);
-    const float g2 = 1.0f + q;
-    W0 = (Pf[V_RHO] + mx.gam * Pf[V_U]) * g2;
-    vsq0 = q / g2;
-  }
-  const float i1 = (float)L.idx[0], i2 = (float)L.idx[1], i3 = (float)L.idx[2];
-  double U[NV];   // stored conserved variables (stage 2)
-  df64 Ud[NV];    // the same, double-float, for the inversion
-  float inc[NV];  // c dt (S - div F)
+    float Pf[NV];
 #pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    const long long o = v * L.plane + c;
-    float div = (F1[o + 1] - F1[o]) * i1 + (F2[o + sj] - F2[o]) * i2;
-    if (L.ndim == 3) div += (F3[o + sk] - F3[o]) * i3;
-    inc[v] = (cdt * (Sv[v] - div)).hi;
-    const double u0 = U0[o];
-    if (Uout) U[v] = u0 + f64_of_f32(inc[v]);
-    Ud[v] = df_of_f64(u0) + inc[v];
+    for (int v = 0; v < NV; ++v) Pf[v] = Pin.v[v][c];
+    float Sv[NV] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const Met<float> mf = load_met(Gf, L.gplane, LOC_CENT, p);
+    source_terms(Pf, mf, Gf.conn, L.gplane, p, mx.gam, Sv);
+    {  // W = (rho + gam u) gamma^2, v^2 = q / gamma^2
+      const float v1 = Pf[V_U1], v2 = Pf[V_U2], v3 = Pf[V_U3];
+      const float q = mf.gcov[1][1] * v1 * v1 + mf.gcov[2][2] * v2 * v2 + mf.gcov[3][3] * v3 * v3 +
+                      2.0f * (mf.gcov[1][2] * v1 * v2 + mf.gcov[1][3] * v1 * v3 + mf.gcov[2][3] * v2 * v3);
+      const float g2 = 1.0f + q;
+      W0 = (Pf[V_RHO] + mx.gam * Pf[V_U]) * g2;
+      vsq0 = kdiv(q, g2);
+    }
+    const float i1 = L.idxf[0], i2 = L.idxf[1], i3 = L.idxf[2];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const long long o = v * L.plane + c;
+      float div = (F1[o + 1] - F1[o]) * i1 + (F2[o + sj] - F2[o]) * i2;
+      if (L.ndim == 3) div += (F3[o + sk] - F3[o]) * i3;
+      const float inc = (cdt * (Sv[v] - div)).hi;  // c dt (S - div F)
+      const double u0 = U0[o];
+      if (Uout) Uout[o] = u0 + f64_of_f32(inc);    // the conserved update, FP64
+      Ud[v] = df_of_f64(u0) + inc;
+    }
   }
   const MetDF md = load_metdf(Gf.df, L.gplane, p);
   df64 Pn[NV];
+  Pn[V_B1] = Ud[V_B1] * md.ig;
+  Pn[V_B2] = Ud[V_B2] * md.ig;
+  Pn[V_B3] = Ud[V_B3] * md.ig;
   int flag = noble2d_df(Ud, md, mx, W0, vsq0, Pn);
   if (flag == C2P_NEED_FP64) {
     // FP64 inversion of this zone from the stage input
+    atomicAdd(cnt + CNT_FP64, 1ULL);
     double Uf[NV], Pd[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      Uf[v] = Uout ? U[v] : U0[v * L.plane + c] + f64_of_f32(inc[v]);
-      Pd[v] = f64_of_f32(Pf[v]);
+      Uf[v] = f64_of_df(Ud[v]);
+      Pd[v] = f64_of_f32(Pin.v[v][c]);
     }
     const Met<double> m = load_met(G, L.gplane, LOC_CENT, p);
     flag = noble2d(Uf, m, __ldg(G.flo + 2 * L.gplane + p), S.gam, S.igam, S.gfac, S.c2p, Pd);
@@ -344,14 +348,12 @@ __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT
   }
   if (flag) {
 #pragma unroll
-    for (int v = 0; v < 5; ++v) Pn[v] = mkdf(Pf[v], 0.0f);
+    for (int v = 0; v < 5; ++v) Pn[v] = mkdf(Pin.v[v][c], 0.0f);
   }
-  Pn[V_B1] = Ud[V_B1] * md.ig;
-  Pn[V_B2] = Ud[V_B2] * md.ig;
-  Pn[V_B3] = Ud[V_B3] * md.ig;
   int fmask = 0;
   if (flag == 0) {
     // floors: decisions on FP32 b^2 and Lorentz factor, values in double-float
+    const Met<float> mf = load_met(Gf, L.gplane, LOC_CENT, p);
     float q[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) q[v] = Pn[v].hi;
@@ -376,24 +378,27 @@ __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT
       }
     }
     if (fmask && Uout) {
+      double* Uc = Uout + c;
       if (fmask & 4) {  // the Lorentz-factor ceiling changed u~: full FP64 recompute
-        double Pd[NV];
+        double Pd[NV], U[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) Pd[v] = f64_of_df(Pn[v]);
         const Met<double> m = load_met(G, L.gplane, LOC_CENT, p);
         FState<double> s;
         fluid_state(Pd, m, s);
         cons_only(Pd, s, m, S.gam, U);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Uc[v * L.plane] = U[v];
       } else {
         // at fixed u~ and B, U is linear in (rho, u): add
         // drho dU/drho + du dU/du, formed in FP32, to the FP64 U
         const float drho = (Pn[V_RHO] - rho0).hi, du = (Pn[V_U] - u0).hi;
         const float gm = mx.gam, gd = mf.gdet, ut = sf.ucon[0];
-        U[V_RHO] += f64_of_f32(gd * ut * drho);
-        U[V_U] += f64_of_f32(gd * ((ut * sf.ucov[0] + ut) * drho + (gm * ut * sf.ucov[0] + gm - 1.0f) * du));
-        U[V_U1] += f64_of_f32(gd * ut * sf.ucov[1] * (drho + gm * du));
-        U[V_U2] += f64_of_f32(gd * ut * sf.ucov[2] * (drho + gm * du));
-        U[V_U3] += f64_of_f32(gd * ut * sf.ucov[3] * (drho + gm * du));
+        Uc[V_RHO * L.plane] += f64_of_f32(gd * ut * drho);
+        Uc[V_U * L.plane] += f64_of_f32(gd * ((ut * sf.ucov[0] + ut) * drho + (gm * ut * sf.ucov[0] + gm - 1.0f) * du));
+        Uc[V_U1 * L.plane] += f64_of_f32(gd * ut * sf.ucov[1] * (drho + gm * du));
+        Uc[V_U2 * L.plane] += f64_of_f32(gd * ut * sf.ucov[2] * (drho + gm * du));
+        Uc[V_U3 * L.plane] += f64_of_f32(gd * ut * sf.ucov[3] * (drho + gm * du));
       }
     }
   }
@@ -404,10 +409,6 @@ __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT
   if (Pout64.v[0]) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) Pout64.v[v][c] = f64_of_df(Pn[v]);
-  }
-  if (Uout) {
-#pragma unroll
-    for (int v = 0; v < NV; ++v) Uout[v * L.plane + c] = U[v];
   }
   pflag[c] = (int8_t)flag;
   if (flag) atomicAdd(cnt + CNT_FAIL, 1ULL);

@@ -46,7 +46,8 @@ class Coords(C.Structure):
 
 
 class Stats(C.Structure):
-    _fields_ = [("nfail", C.c_int64), ("nfloor", C.c_int64), ("nunfixed", C.c_int64), ("dt_cfl", C.c_double)]
+    _fields_ = [("nfail", C.c_int64), ("nfloor", C.c_int64), ("nunfixed", C.c_int64), ("dt_cfl", C.c_double),
+                ("nfp64", C.c_int64)]
 
 
 class Block(C.Structure):
