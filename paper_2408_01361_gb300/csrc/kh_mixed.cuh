@@ -7,10 +7,11 @@
 //     as S^2 and of the energy residual as S, exactly);
 //   * Newton's iterations in FP32 on the scaled invariants (their hi parts),
 //     started from the stage input's (W, v^2);
-//   * one refinement with both residuals in double-float at the FP32 root and
-//     the FP32 Jacobian (its FP32 error multiplies a step of ~1e-7), accepted
-//     when the step is below 1e-5 -- the iterate then lies in Newton's
-//     quadratic regime, its error ~ the step squared;
+//   * refinement steps with both residuals in double-float and the FP32
+//     Jacobian (its FP32 error multiplies a step of ~1e-7), until a step is
+//     below 1e-5 (at most three) -- the iterate then lies in Newton's
+//     quadratic regime, its error ~ the step squared (one step from a
+//     converged FP32 root; more where FP32 rounding stalled the FP32 phase);
 //   * the primitives recovered in double-float.
 // A zone whose FP32 phase or refinement does not meet these conditions is
 // reported (C2P_NEED_FP64) and the caller runs the FP64 inversion for it.
@@ -121,12 +122,16 @@ KH_HD int noble2d_df(const df64* U, const MetDF& m, const MixedConsts& k, float 
   if (!(vf >= 0.0f)) vf = 0.0f;
   if (vf > 1.0f - 1e-7f) vf = 1.0f - 1e-7f;
   const float Df = D.hi, Bf = Bsq.hi, QBf = QdB2.hi, gff = k.gfac_hi;
-  const bool ok32 = newton_wv<float>(Df, Qdn.hi, Qtsq.hi, Bf, QBf, gff, 12, 3e-6f, Wf, vf, ef);
-  if (!ok32 || !(vf < 1.0f - 1e-6f)) return C2P_NEED_FP64;
+  newton_wv<float>(Df, Qdn.hi, Qtsq.hi, Bf, QBf, gff, 10, 3e-6f, Wf, vf, ef);
+  // an FP32 phase that stalled on FP32 rounding still hands over a close root
+  if (!(Wf > 0.0f) || !kfinite(Wf) || !(vf >= 0.0f && vf < 1.0f - 1e-6f) || !(ef < 1e-2f)) return C2P_NEED_FP64;
 
-  // one refinement: double-float residuals, FP32 Jacobian
+  // refinement: double-float residuals, FP32 Jacobian at the current iterate;
+  // done after a step below 1e-5 (at most three steps)
   df64 W = mkdf(Wf, 0.0f), vsq = mkdf(vf, 0.0f);
-  {
+  bool done = false;
+  for (int r = 0; r < 3 && !done; ++r) {
+    const float wf = W.hi, vv = vsq.hi;
     const df64 x = 1.0f - vsq;
     const df64 sg = dfsqrt(x);
     const df64 iW = rcp(W);
@@ -135,20 +140,23 @@ KH_HD int noble2d_df(const df64* U, const MetDF& m, const MixedConsts& k, float 
     const df64 p = gf * (W * x - D * sg);
     const df64 r1 = Qtsq - vsq * (BW * BW) + QdB2 * (Bsq + scale2(W, 2.0f)) * iW2;
     const df64 r2 = Qdn + W - p + scale2(Bsq * (1.0f + vsq), 0.5f) - scale2(QdB2 * iW2, 0.5f);
-    const float xg = 1.0f - vf, BWf = Bf + Wf, iWf = kdiv(1.0f, Wf), iW3f = iWf * iWf * iWf;
-    const float j11 = -2.0f * vf * BWf - 2.0f * QBf * BWf * iW3f;
+    const float xg = 1.0f - vv, BWf = Bf + wf, iWf = kdiv(1.0f, wf), iW3f = iWf * iWf * iWf;
+    const float j11 = -2.0f * vv * BWf - 2.0f * QBf * BWf * iW3f;
     const float j12 = -BWf * BWf;
     const float j21 = 1.0f - gff * xg + QBf * iW3f;
-    const float j22 = 0.5f * Bf - gff * (-Wf + 0.5f * Df * krsqrt(xg));
+    const float j22 = 0.5f * Bf - gff * (-wf + 0.5f * Df * krsqrt(xg));
     const float idet = kdiv(1.0f, j11 * j22 - j12 * j21);
     const float dW = (j22 * r1.hi - j12 * r2.hi) * idet;
     const float dv = (-j21 * r1.hi + j11 * r2.hi) * idet;
-    const df64 Wn = W - dW, vn = vsq - dv;
-    if (!(Wn.hi > 0.0f && vn.hi >= 0.0f && vn.hi < 1.0f - 1e-7f)) return C2P_NEED_FP64;
-    if (!(fabsf(dW) * iWf + fabsf(dv) < 1e-5f)) return C2P_NEED_FP64;
+    const df64 Wn = W - dW;
+    df64 vn = vsq - dv;
+    if (vn.hi < 0.0f) vn = mkdf(0.0f, 0.0f);  // a fluid at rest in the normal frame: v^2 = 0 up to rounding
+    if (!(Wn.hi > 0.0f && vn.hi < 1.0f - 1e-7f)) return C2P_NEED_FP64;
+    done = fabsf(dW) * iWf + fabsf(dv) < 1e-5f;
     W = Wn;
     vsq = vn;
   }
+  if (!done) return C2P_NEED_FP64;
 
   // primitives (scaled rho, u times S; u~ is scale free)
   const df64 x = 1.0f - vsq;

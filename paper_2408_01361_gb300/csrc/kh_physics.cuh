@@ -38,6 +38,14 @@ KH_HD float krsqrt(float x) {
   return 1.0f / sqrtf(x);
 #endif
 }
+// |x| and finiteness without promotion to FP64 for FP32 arguments (an FP64
+// operation issues at 1/64 of the FP32 rate on GB300): x - x is 0 exactly
+// when x is finite.
+KH_HD float kabs(float x) { return fabsf(x); }
+KH_HD double kabs(double x) { return fabs(x); }
+KH_HD bool kfinite(float x) { return x - x == 0.0f; }
+KH_HD bool kfinite(double x) { return isfinite(x); }
+template <class R> KH_HD R kabs(const R& x) { return fabs(x); }  // other number types (duals)
 // a / b: IEEE division in FP64; in FP32 (the mixed path's stencil physics)
 // CUDA's fast division, for divisors of modest magnitude (|b| < 2^126).
 KH_HD double kdiv(double a, double b) { return a / b; }
@@ -177,8 +185,8 @@ template <class R> KH_HD void recon_mc(R qm, R q0, R qp, R& lo, R& hi) {
   if (dl * dr > R(0)) {
     const R a = R(2) * dl, b = R(2) * dr, c = R(0.5) * (dl + dr);
     s = a;
-    if (fabs(b) < fabs(s)) s = b;
-    if (fabs(c) < fabs(s)) s = c;
+    if (kabs(b) < kabs(s)) s = b;
+    if (kabs(c) < kabs(s)) s = c;
   }
   lo = q0 - R(0.5) * s;
   hi = q0 + R(0.5) * s;
@@ -420,10 +428,10 @@ KH_HD bool newton_wv(R D, R Qdn, R Qtsq, R Bsq, R QdB2, R gf, int max_iter, R st
     if (!(Wn > R(0))) Wn = R(0.5) * W;
     if (vn < R(0)) vn = R(0);
     if (vn > vmax) vn = vmax;
-    err = fabs(Wn - W) * iW + fabs(vn - vsq);  // step relative to the previous iterate
+    err = kabs(Wn - W) * iW + kabs(vn - vsq);  // step relative to the previous iterate
     W = Wn;
     vsq = vn;
-    if (!isfinite(W) || !isfinite(vsq)) return false;
+    if (!kfinite(W) || !kfinite(vsq)) return false;
     if (err < stop) return true;
   }
   return false;

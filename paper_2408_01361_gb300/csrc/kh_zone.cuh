@@ -38,8 +38,8 @@ template <class R> __device__ __forceinline__ R mc_slope(R qm, R q0, R qp) {
   const R dl = q0 - qm, dr = qp - q0;
   if (!(dl * dr > R(0))) return R(0);
   R s = R(2) * dl;
-  if (fabs(R(2) * dr) < fabs(s)) s = R(2) * dr;
-  if (fabs(R(0.5) * (dl + dr)) < fabs(s)) s = R(0.5) * (dl + dr);
+  if (kabs(R(2) * dr) < kabs(s)) s = R(2) * dr;
+  if (kabs(R(0.5) * (dl + dr)) < kabs(s)) s = R(0.5) * (dl + dr);
   return s;
 }
 
