@@ -81,7 +81,7 @@ void free_all(kh_ctx* x) {
                   x->ctop[2], x->emf[0], x->emf[1], x->emf[2], x->pflag, x->partial, x->dscalar,
                   x->counters, x->dirichlet[0], x->dirichlet[1], x->geof, x->connf, x->pstarf, x->pnf, x->Ff[0],
                   x->Ff[1], x->Ff[2], x->ctopf[0], x->ctopf[1], x->ctopf[2], x->emff[0], x->emff[1],
-                  x->emff[2], x->dirichletf[0], x->dirichletf[1], x->adj, x->adj_i8, x->adj_red, x->geodf};
+                  x->emff[2], x->dirichletf[0], x->dirichletf[1], x->adj, x->adj_i8, x->adj_red, x->geodf, x->flist};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -106,24 +106,21 @@ int run_stage(kh_ctx* x, int st, const double* U0, const Vars& Pin, const Vars& 
   n += launch_ct<double>(x->F, x->emf, L, s);
   mark(x, KH_T_CT, st, 1);
   mark(x, KH_T_UPDATE, st, 0);
+  const FailList fl{x->flist, x->counters + CNT_LIST0 + st};
   n += launch_update(U0, cview(Pin), Pout, Uout, x->F, L, G, x->S, x->dscalar + 3, coef, x->pflag, x->counters,
-                     x->tpb_update, s);
+                     x->tpb_update, s, fl);
   mark(x, KH_T_UPDATE, st, 1);
   mark(x, KH_T_FIXUP, st, 0);
-  n += launch_fixup<double>(Pout, Uout, x->pflag, L, G, x->S, x->counters, s);
+  n += launch_fixup<double>(Pout, Uout, x->pflag, L, G, x->S, x->counters, s, fl);
   mark(x, KH_T_FIXUP, st, 1);
   return n;
 }
 
-template <class T> CVarsT<T> cviewT(const VarsT<T>& v) {
-  CVarsT<T> c;
-  for (int q = 0; q < NV; ++q) c.v[q] = v.v[q];
-  return c;
-}
 
-// One mixed stage. Stage 1 (st = 0): FP64 input (ghost-filled in FP64) read
-// by the FP32 flux pass, output to the FP32 shadow P*. Stage 2 (st = 1): the
-// FP32 shadow (ghost-filled in FP32) as input, FP64 output and U.
+// One mixed stage. Stage 1 (st = 0): FP64 input, converted to FP32 with its
+// ghost cells filled in FP32, read by the FP32 flux pass, output to the FP32
+// shadow P*. Stage 2 (st = 1): the FP32 shadow (ghost-filled in FP32) as
+// input, FP64 output and U.
 template <class TIN>
 int run_stage_mixed(kh_ctx* x, int st, const double* U0, const VarsT<TIN>& Pin, const TIN* dlo, const TIN* dhi,
                     const Vars& Pout64, const VarsT<float>& Pout32, double* Uout, double coef) {
@@ -133,15 +130,17 @@ int run_stage_mixed(kh_ctx* x, int st, const double* U0, const VarsT<TIN>& Pin, 
   cudaStream_t s = x->stream;
   int n = 0;
   mark(x, KH_T_BC, st, 0);
-  n += launch_bc<TIN>(Pin, L, x->S, dlo, dhi, s);
   // The stencil pass reads FP32: an FP64 input is converted once per cell
-  // here (on GB300 a double->float conversion issues on the FP64 pipe, so
-  // converting inside the 6-point stencils would cost 6x more of it).
+  // (by integer operations; GB300 issues FP64 conversions at 1/64 the FP32
+  // rate), then its ghost cells are filled from the FP64 interior straight
+  // into the FP32 copy (the caller's FP64 ghosts are not needed).
   VarsT<float> Pf;
   if constexpr (sizeof(TIN) == sizeof(double)) {
     for (int q = 0; q < NV; ++q) Pf.v[q] = x->pnf + q * L.plane;
     n += launch_vars_to_f32(cviewT(Pin), Pf, L, s);
+    n += launch_bc_fill<double, float>(cviewT(Pin), Pf, L, x->S, dlo, dhi, s);
   } else {
+    n += launch_bc<TIN>(Pin, L, x->S, dlo, dhi, s);
     Pf = Pin;
   }
   mark(x, KH_T_BC, st, 1);
@@ -159,14 +158,15 @@ int run_stage_mixed(kh_ctx* x, int st, const double* U0, const VarsT<TIN>& Pin, 
   n += launch_ct<float>(x->Ff, x->emff, L, s);
   mark(x, KH_T_CT, st, 1);
   mark(x, KH_T_UPDATE, st, 0);
+  const FailList fl{x->flist, x->counters + CNT_LIST0 + st};
   n += launch_update_mixed(U0, cviewT(Pf), Pout64, Pout32, Uout, x->Ff, L, G, Gf, x->S, x->dscalar + 3, coef,
-                           x->pflag, x->counters, x->tpb_update, s);
+                           x->pflag, x->counters, x->tpb_update, s, fl);
   mark(x, KH_T_UPDATE, st, 1);
   mark(x, KH_T_FIXUP, st, 0);
   if (Pout64.v[0])
-    n += launch_fixup<double>(Pout64, Uout, x->pflag, L, G, x->S, x->counters, s);
+    n += launch_fixup<double>(Pout64, Uout, x->pflag, L, G, x->S, x->counters, s, fl);
   else
-    n += launch_fixup<float>(Pout32, Uout, x->pflag, L, G, x->S, x->counters, s);
+    n += launch_fixup<float>(Pout32, Uout, x->pflag, L, G, x->S, x->counters, s, fl);
   mark(x, KH_T_FIXUP, st, 1);
   return n;
 }
@@ -308,6 +308,7 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
         KH_ALLOC(x->dirichletf[f], (size_t)NV * L.n3s * L.n2s * L.ng * sizeof(float));
   }
   KH_ALLOC(x->pflag, (size_t)L.plane);
+  KH_ALLOC(x->flist, (size_t)L.n1 * L.n2 * L.n3 * sizeof(unsigned));
   KH_ALLOC(x->partial, 2 * (size_t)x->npartial * sizeof(double));
   KH_ALLOC(x->dscalar, 4 * sizeof(double));
   KH_ALLOC(x->counters, NCNT * sizeof(unsigned long long));

@@ -28,6 +28,7 @@ struct kh_ctx {
   float* geof;
   float* connf;
   float* geodf;    // [NDF][2] double-float planes of the cell-centre geometry and floors
+  unsigned* flist; // failed-zone list of the current stage (one entry per zone at most)
   float* pstarf;   // 8 planes
   float* pnf;      // 8 planes: FP32 copy of the ghost-filled stage-1 input
   float* Ff[3];    // 8 planes each

@@ -62,16 +62,37 @@ struct Scheme {
 inline void set_mixed(Scheme& S) { S.mx = mixed_consts(S.gam, S.fl); }
 
 // Counters kept on the device for one step.
-// CNT_FP64: zones of the mixed update whose inversion fell back to FP64
-enum { CNT_FAIL = 0, CNT_FLOOR = 1, CNT_UNFIXED = 2, CNT_TIMEOUT = 3, CNT_FP64 = 4, NCNT = 5 };
+// CNT_FP64: zones of the mixed update whose inversion fell back to FP64;
+// CNT_LIST0/1: lengths of the failed-zone lists of stages 1 and 2
+enum { CNT_FAIL = 0, CNT_FLOOR = 1, CNT_UNFIXED = 2, CNT_TIMEOUT = 3, CNT_FP64 = 4, CNT_LIST0 = 5, CNT_LIST1 = 6,
+       NCNT = 7 };
+
+// Cells (L.at index) whose inversion failed in one stage, appended by the
+// update (idx == nullptr: not recorded); the fixup then visits these only.
+struct FailList {
+  unsigned* idx;
+  unsigned long long* n;
+};
 
 // ---- launchers (kh_kernels.cu); each returns the number of kernels launched ----
 // Geometry of a grid whose first interior cell starts at native (x1o, x2o);
 // cp.x1min is the FMKS blending reference (the x1 start of the whole domain).
 int launch_geometry(const CoordParams& cp, double x1o, double x2o, const FloorParams& fl, const Layout& L, double* geo,
                     double* conn, double* flo, cudaStream_t s);
+template <class T> inline CVarsT<T> cviewT(const VarsT<T>& v) {
+  CVarsT<T> c;
+  for (int q = 0; q < NV; ++q) c.v[q] = v.v[q];
+  return c;
+}
+
+// Ghost fill in place (one kernel: the x1, x2, x3 rules composed per cell).
 template <class T>
 int launch_bc(const VarsT<T>& P, const Layout& L, const Scheme& S, const T* dlo, const T* dhi, cudaStream_t s);
+// The same map reading interior cells of src and writing the ghost cells of
+// dst (FP64 -> FP32 for the mixed path's stage-1 input).
+template <class TS, class TD>
+int launch_bc_fill(const CVarsT<TS>& src, const VarsT<TD>& dst, const Layout& L, const Scheme& S, const TS* dlo,
+                   const TS* dhi, cudaStream_t s);
 // Reconstruction + LLF through x^D faces: stencil read in TIN, arithmetic and
 // outputs in R (FP64 path: double/double; mixed: double or float in, float out).
 // FP32 face fluxes from TMA-staged shared-memory tiles (kh_flux_tma.cu): P8
@@ -87,7 +108,7 @@ template <class R> int launch_ct(R* const F[3], R* const emf[3], const Layout& L
 // captured step keeps working when dt changes.
 int launch_update(const double* U0, const CVars& Pin, const Vars& Pout, double* Uout, double* const F[3],
                   const Layout& L, const DevGeom& G, const Scheme& S, const double* dtp, double coef, int8_t* pflag,
-                  unsigned long long* cnt, int tpb, cudaStream_t s);
+                  unsigned long long* cnt, int tpb, cudaStream_t s, FailList fl = FailList{nullptr, nullptr});
 // Mixed update: FP32 fluxes and sources, FP64 accumulation of U and FP64
 // inversion; the stage input (sources, inversion guess) is read in FP32.
 // Writes the FP64 output (Pout64.v[0] may be null) and/or its FP32 shadow
@@ -95,10 +116,11 @@ int launch_update(const double* U0, const CVars& Pin, const Vars& Pout, double* 
 int launch_update_mixed(const double* U0, const CVarsT<float>& Pin, const Vars& Pout64, const VarsT<float>& Pout32,
                         double* Uout, float* const F[3], const Layout& L, const DevGeom& G, const GeomT<float>& Gf,
                         const Scheme& S, const double* dtp, double coef, int8_t* pflag, unsigned long long* cnt,
-                        int tpb, cudaStream_t s);
+                        int tpb, cudaStream_t s, FailList fl = FailList{nullptr, nullptr});
+// Fixup over every zone, or (fl.idx != nullptr) over the stage's failed-zone list.
 template <class T>
 int launch_fixup(const VarsT<T>& P, double* Uout, const int8_t* pflag, const Layout& L, const DevGeom& G,
-                 const Scheme& S, unsigned long long* cnt, cudaStream_t s);
+                 const Scheme& S, unsigned long long* cnt, cudaStream_t s, FailList fl = FailList{nullptr, nullptr});
 template <class T>
 int launch_cfl(T* const ctop[3], const Layout& L, double cfl, double* partial, int npartial, double* dt_out,
                cudaStream_t s);

@@ -65,89 +65,84 @@ __global__ void k_geometry(CoordParams cp, double x1o, double x2o, FloorParams f
 // ghosts over all i and interior k; x3 ghosts over all (i, j): edges and
 // corners are compositions of the face rules (three launches, in order).
 // ---------------------------------------------------------------------------
-template <class T>
-__global__ void k_bc_x1(VarsT<T> P, Layout L, Scheme S, const T* dlo, const T* dhi) {
-  const int nj = L.e[1] - L.s[1], nk = L.e[2] - L.s[2];
-  const long long tot = (long long)nj * nk * L.ng * 2;
+// One pass over every ghost cell: the x1 rule, then the x2 rule, then the x3
+// rule (the order of the per-direction passes, in which a later direction's
+// ghosts copy cells that an earlier direction filled) composed into one map
+// from the ghost cell to an interior cell (or to the x1 Dirichlet data at the
+// mapped (j, k)), with the per-component operations of the rules crossed on
+// the way: u~1 clamped by an x1 outflow face (no inflow), u~2 and B2 negated
+// by a polar x2 face. The two act on different components, so their order
+// does not matter. Reads interior cells of src only and writes ghost cells of
+// dst, so src == dst is allowed. Ghost cells are enumerated in three slabs:
+// x1 ghosts of interior (j, k), x2 ghosts of interior k, x3 ghosts.
+template <class TS, class TD>
+__global__ void k_bc_fill(CVarsT<TS> src, VarsT<TD> dst, Layout L, Scheme S, const TS* dlo, const TS* dhi) {
+  const long long nj = L.e[1] - L.s[1], nk = L.e[2] - L.s[2];
+  const long long T1 = nj * nk * L.ng * 2, T2 = (long long)L.N1 * nk * L.ng * 2;
+  const long long T3 = L.ndim == 3 ? (long long)L.N1 * L.N2 * L.ng3 * 2 : 0;
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= tot) return;
-  const int side = (int)(t % 2);
-  const int m = (int)((t / 2) % L.ng);
-  const int j = L.s[1] + (int)((t / (2 * L.ng)) % nj);
-  const int k = L.s[2] + (int)(t / (2LL * L.ng * nj));
-  const int ig = side == 0 ? L.ng - 1 - m : L.ng + L.n1 + m;
-  const int bc = S.bc[side];
-  const long long dst = L.at(k, j, ig);
-  if (bc == KH_BC_DIRICHLET) {
-    const T* D = side == 0 ? dlo : dhi;
-    const int ii = side == 0 ? ig : ig - (L.ng + L.n1);
-#pragma unroll
-    for (int v = 0; v < NV; ++v) P.v[v][dst] = D[(((long long)v * L.n3s + k) * L.n2s + j) * L.ng + ii];
-    return;
+  if (t >= T1 + T2 + T3) return;
+  int i, j, k;
+  if (t < T1) {
+    const int side = (int)(t % 2), m = (int)((t / 2) % L.ng);
+    j = L.s[1] + (int)((t / (2 * L.ng)) % nj);
+    k = L.s[2] + (int)(t / (2LL * L.ng * nj));
+    i = side == 0 ? L.ng - 1 - m : L.ng + L.n1 + m;
+  } else if (t < T1 + T2) {
+    const long long u = t - T1;
+    i = (int)(u % L.N1);
+    const int side = (int)((u / L.N1) % 2), m = (int)((u / (2LL * L.N1)) % L.ng);
+    k = L.s[2] + (int)(u / (2LL * L.N1 * L.ng));
+    j = side == 0 ? L.ng - 1 - m : L.ng + L.n2 + m;
+  } else {
+    const long long u = t - T1 - T2;
+    i = (int)(u % L.N1);
+    j = (int)((u / L.N1) % L.N2);
+    const int side = (int)((u / ((long long)L.N1 * L.N2)) % 2), m = (int)(u / (2LL * L.N1 * L.N2));
+    k = side == 0 ? L.ng3 - 1 - m : L.ng3 + L.n3 + m;
   }
-  int src;
-  if (bc == KH_BC_PERIODIC)
-    src = side == 0 ? ig + L.n1 : ig - L.n1;
-  else if (bc == KH_BC_OUTFLOW)
-    src = side == 0 ? L.ng : L.ng + L.n1 - 1;
-  else  // reflection (not used on x1 faces by the supported problems)
-    src = side == 0 ? 2 * L.ng - 1 - ig : 2 * (L.ng + L.n1) - 1 - ig;
-  const long long s = L.at(k, j, src);
-#pragma unroll
-  for (int v = 0; v < NV; ++v) P.v[v][dst] = P.v[v][s];
-  if (bc == KH_BC_OUTFLOW) {
-    T u1 = P.v[V_U1][dst];
-    if (side == 0 && u1 > T(0)) u1 = T(0);
-    if (side == 1 && u1 < T(0)) u1 = T(0);
-    P.v[V_U1][dst] = u1;
+  // x3, x2, x1 maps to the source cell
+  int ks = k, js = j, is = i;
+  if (L.ndim == 3 && (k < L.s[2] || k >= L.e[2])) {
+    const int side = k < L.s[2] ? 0 : 1;
+    if (S.bc[4 + side] == KH_BC_PERIODIC) ks = side == 0 ? k + L.n3 : k - L.n3;
+    else ks = side == 0 ? L.s[2] : L.e[2] - 1;
   }
-}
-
-template <class T>
-__global__ void k_bc_x2(VarsT<T> P, Layout L, Scheme S) {
-  const int nk = L.e[2] - L.s[2];
-  const long long tot = (long long)L.N1 * nk * L.ng * 2;
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= tot) return;
-  const int i = (int)(t % L.N1);
-  const int side = (int)((t / L.N1) % 2);
-  const int m = (int)((t / (2LL * L.N1)) % L.ng);
-  const int k = L.s[2] + (int)(t / (2LL * L.N1 * L.ng));
-  const int jg = side == 0 ? L.ng - 1 - m : L.ng + L.n2 + m;
-  const int bc = S.bc[2 + side];
-  int src;
-  if (bc == KH_BC_PERIODIC)
-    src = side == 0 ? jg + L.n2 : jg - L.n2;
-  else if (bc == KH_BC_OUTFLOW)
-    src = side == 0 ? L.ng : L.ng + L.n2 - 1;
-  else
-    src = side == 0 ? 2 * L.ng - 1 - jg : 2 * (L.ng + L.n2) - 1 - jg;
-  const long long s = L.at(k, src, i), d = L.at(k, jg, i);
-  const bool flip = (bc == KH_BC_POLAR);
+  bool flip = false;
+  if (j < L.s[1] || j >= L.e[1]) {
+    const int side = j < L.s[1] ? 0 : 1, bc = S.bc[2 + side];
+    if (bc == KH_BC_PERIODIC) js = side == 0 ? j + L.n2 : j - L.n2;
+    else if (bc == KH_BC_OUTFLOW) js = side == 0 ? L.ng : L.ng + L.n2 - 1;
+    else js = side == 0 ? 2 * L.ng - 1 - j : 2 * (L.ng + L.n2) - 1 - j;
+    flip = bc == KH_BC_POLAR;
+  }
+  int clamp = 0;  // 1: u~1 <= 0 (inner x1 outflow), 2: u~1 >= 0 (outer)
+  const TS* D = nullptr;
+  if (i < L.s[0] || i >= L.e[0]) {
+    const int side = i < L.s[0] ? 0 : 1, bc = S.bc[side];
+    if (bc == KH_BC_DIRICHLET) {
+      D = side == 0 ? dlo : dhi;
+      is = side == 0 ? i : i - (L.ng + L.n1);  // index into the ghost data
+    } else if (bc == KH_BC_PERIODIC) {
+      is = side == 0 ? i + L.n1 : i - L.n1;
+    } else if (bc == KH_BC_OUTFLOW) {
+      is = side == 0 ? L.ng : L.ng + L.n1 - 1;
+      clamp = side + 1;
+    } else {
+      is = side == 0 ? 2 * L.ng - 1 - i : 2 * (L.ng + L.n1) - 1 - i;
+    }
+  }
+  const long long d = L.at(k, j, i), sc = D ? 0 : L.at(ks, js, is);
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    const T x = P.v[v][s];
-    P.v[v][d] = (flip && (v == V_U2 || v == V_B2)) ? -x : x;
+    TS x = D ? D[(((long long)v * L.n3s + ks) * L.n2s + js) * L.ng + is] : src.v[v][sc];
+    if (v == V_U1 && ((clamp == 1 && x > TS(0)) || (clamp == 2 && x < TS(0)))) x = TS(0);
+    if (flip && (v == V_U2 || v == V_B2)) x = -x;
+    if constexpr (sizeof(TS) == sizeof(TD)) dst.v[v][d] = x;
+    else dst.v[v][d] = f32_of_f64(x);  // integer operations, not the FP64 pipe
   }
 }
 
-template <class T>
-__global__ void k_bc_x3(VarsT<T> P, Layout L, Scheme S) {
-  const long long tot = (long long)L.N1 * L.N2 * L.ng3 * 2;
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= tot) return;
-  const int i = (int)(t % L.N1);
-  const int j = (int)((t / L.N1) % L.N2);
-  const int side = (int)((t / ((long long)L.N1 * L.N2)) % 2);
-  const int m = (int)(t / (2LL * L.N1 * L.N2));
-  const int kg = side == 0 ? L.ng3 - 1 - m : L.ng3 + L.n3 + m;
-  const int bc = S.bc[4 + side];
-  const int src = (bc == KH_BC_PERIODIC) ? (side == 0 ? kg + L.n3 : kg - L.n3)
-                                          : (side == 0 ? L.ng3 : L.ng3 + L.n3 - 1);
-  const long long s = L.at(src, j, i), d = L.at(kg, j, i);
-#pragma unroll
-  for (int v = 0; v < NV; ++v) P.v[v][d] = P.v[v][s];
-}
 
 // ---------------------------------------------------------------------------
 // Reconstruction + LLF flux through the lower x^D face of cell (k, j, i),
@@ -195,12 +190,12 @@ __global__ void k_apply_ct(R* F1, R* F2, R* F3, const R* e1, const R* e2, const 
 __global__ void __launch_bounds__(TPB_MAX) k_update(const double* U0, CVars Pin, Vars Pout, double* Uout,
                                                    const double* F1, const double* F2, const double* F3, Layout L,
                                                    DevGeom G, Scheme S, const double* dtp, double coef, int8_t* pflag,
-                                                   unsigned long long* cnt) {
+                                                   unsigned long long* cnt, FailList fl) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nzones(L)) return;
   int i, j, k;
   zone_ijk(L, t, i, j, k);
-  update_zone(U0, Pin, Pout, Uout, F1, F2, F3, L, G, S, coef * __ldg(dtp), pflag, cnt, i, j, k);
+  update_zone(U0, Pin, Pout, Uout, F1, F2, F3, L, G, S, coef * __ldg(dtp), pflag, cnt, i, j, k, nullptr, fl);
 }
 
 // three blocks of TPB_MAX per SM: ~80 registers (a few spill to L1); measured faster
@@ -209,13 +204,13 @@ __global__ void __launch_bounds__(TPB_MAX, 3) k_update_mixed(const double* U0, C
                                                          VarsT<float> Pout32, double* Uout, const float* F1,
                                                          const float* F2, const float* F3, Layout L, DevGeom G,
                                                          GeomT<float> Gf, Scheme S, const double* dtp, double coef,
-                                                         int8_t* pflag, unsigned long long* cnt) {
+                                                         int8_t* pflag, unsigned long long* cnt, FailList fl) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nzones(L)) return;
   int i, j, k;
   zone_ijk(L, t, i, j, k);
   update_mixed_zone(U0, Pin, Pout64, Pout32, Uout, F1, F2, F3, L, G, Gf, S, df_of_f64(coef * __ldg(dtp)), pflag, cnt, i,
-                    j, k);
+                    j, k, fl);
 }
 
 template <class T>
@@ -226,6 +221,20 @@ __global__ void __launch_bounds__(TPB) k_fixup(VarsT<T> P, double* Uout, const i
   int i, j, k;
   zone_ijk(L, t, i, j, k);
   fixup_zone<T>(P, Uout, pflag, L, G, S, cnt, i, j, k);
+}
+
+// The same over the stage's failed-zone list (its length read on the device).
+template <class T>
+__global__ void __launch_bounds__(TPB) k_fixup_list(VarsT<T> P, double* Uout, const int8_t* pflag, Layout L,
+                                                   DevGeom G, Scheme S, unsigned long long* cnt, FailList fl) {
+  const unsigned long long n = *fl.n;
+  const long long gs = L.gplane;
+  for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < n;
+       q += (unsigned long long)gridDim.x * blockDim.x) {
+    const long long c = fl.idx[q];
+    const int k = (int)(c / gs), j = (int)((c % gs) / L.n1s), i = (int)(c % L.n1s);
+    fixup_zone<T>(P, Uout, pflag, L, G, S, cnt, i, j, k);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -264,12 +273,14 @@ template <class T>
 __global__ void __launch_bounds__(RED_THREADS) k_cfl(const T* c1, const T* c2, const T* c3, Layout L,
                                                     double* partial) {
   const unsigned nz = nzones(L);
-  double mx = 0.0, dummy = 0.0;
+  T m = T(0);  // per-thread maximum in the speeds' precision
   for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < nz; t += gridDim.x * blockDim.x) {
     int i, j, k;
     zone_ijk(L, t, i, j, k);
-    mx = fmax(mx, cfl_inv_zone(c1, c2, c3, L, i, j, k));
+    const T v = cfl_inv_zone(c1, c2, c3, L, i, j, k);
+    m = v > m ? v : m;
   }
+  double mx = (double)m, dummy = 0.0;
   block_max_sum(mx, dummy);
   if (threadIdx.x == 0) {
     partial[2 * blockIdx.x] = mx;
@@ -389,20 +400,20 @@ int launch_geometry(const CoordParams& cp, double x1o, double x2o, const FloorPa
 
 template <class T>
 int launch_bc(const VarsT<T>& P, const Layout& L, const Scheme& S, const T* dlo, const T* dhi, cudaStream_t s) {
-  int n = 0;
-  long long t1 = (long long)(L.e[1] - L.s[1]) * (L.e[2] - L.s[2]) * L.ng * 2;
-  k_bc_x1<T><<<nblocks(t1, TPB), TPB, 0, s>>>(P, L, S, dlo, dhi);
-  ++n;
-  long long t2 = (long long)L.N1 * (L.e[2] - L.s[2]) * L.ng * 2;
-  k_bc_x2<T><<<nblocks(t2, TPB), TPB, 0, s>>>(P, L, S);
-  ++n;
-  if (L.ndim == 3) {
-    long long t3 = (long long)L.N1 * L.N2 * L.ng3 * 2;
-    k_bc_x3<T><<<nblocks(t3, TPB), TPB, 0, s>>>(P, L, S);
-    ++n;
-  }
-  return n;
+  return launch_bc_fill<T, T>(cviewT(P), P, L, S, dlo, dhi, s);
 }
+
+template <class TS, class TD>
+int launch_bc_fill(const CVarsT<TS>& src, const VarsT<TD>& dst, const Layout& L, const Scheme& S, const TS* dlo,
+                   const TS* dhi, cudaStream_t s) {
+  const long long nj = L.e[1] - L.s[1], nk = L.e[2] - L.s[2];
+  const long long tot = nj * nk * L.ng * 2 + (long long)L.N1 * nk * L.ng * 2 +
+                        (L.ndim == 3 ? (long long)L.N1 * L.N2 * L.ng3 * 2 : 0);
+  k_bc_fill<TS, TD><<<nblocks(tot, TPB), TPB, 0, s>>>(src, dst, L, S, dlo, dhi);
+  return 1;
+}
+template int launch_bc_fill<double, float>(const CVarsT<double>&, const VarsT<float>&, const Layout&, const Scheme&,
+                                           const double*, const double*, cudaStream_t);
 template int launch_bc<double>(const VarsT<double>&, const Layout&, const Scheme&, const double*, const double*,
                                cudaStream_t);
 template int launch_bc<float>(const VarsT<float>&, const Layout&, const Scheme&, const float*, const float*,
@@ -446,33 +457,41 @@ template int launch_ct<float>(float* const[3], float* const[3], const Layout&, c
 
 int launch_update(const double* U0, const CVars& Pin, const Vars& Pout, double* Uout, double* const F[3],
                   const Layout& L, const DevGeom& G, const Scheme& S, const double* dtp, double coef, int8_t* pflag,
-                  unsigned long long* cnt, int tpb, cudaStream_t s) {
+                  unsigned long long* cnt, int tpb, cudaStream_t s, FailList fl) {
   const long long nz = (long long)L.n1 * L.n2 * L.n3;
-  k_update<<<nblocks(nz, tpb), tpb, 0, s>>>(U0, Pin, Pout, Uout, F[0], F[1], F[2], L, G, S, dtp, coef, pflag, cnt);
+  k_update<<<nblocks(nz, tpb), tpb, 0, s>>>(U0, Pin, Pout, Uout, F[0], F[1], F[2], L, G, S, dtp, coef, pflag, cnt,
+                                            fl);
   return 1;
 }
 
 int launch_update_mixed(const double* U0, const CVarsT<float>& Pin, const Vars& Pout64, const VarsT<float>& Pout32,
                         double* Uout, float* const F[3], const Layout& L, const DevGeom& G, const GeomT<float>& Gf,
                         const Scheme& S, const double* dtp, double coef, int8_t* pflag, unsigned long long* cnt,
-                        int tpb, cudaStream_t s) {
+                        int tpb, cudaStream_t s, FailList fl) {
   const long long nz = (long long)L.n1 * L.n2 * L.n3;
   k_update_mixed<<<nblocks(nz, tpb), tpb, 0, s>>>(U0, Pin, Pout64, Pout32, Uout, F[0], F[1], F[2], L, G, Gf, S, dtp,
-                                                  coef, pflag, cnt);
+                                                  coef, pflag, cnt, fl);
   return 1;
 }
 
 template <class T>
 int launch_fixup(const VarsT<T>& P, double* Uout, const int8_t* pflag, const Layout& L, const DevGeom& G,
-                 const Scheme& S, unsigned long long* cnt, cudaStream_t s) {
+                 const Scheme& S, unsigned long long* cnt, cudaStream_t s, FailList fl) {
   const long long nz = (long long)L.n1 * L.n2 * L.n3;
-  k_fixup<T><<<nblocks(nz, TPB), TPB, 0, s>>>(P, Uout, pflag, L, G, S, cnt);
+  if (fl.idx) {
+    // the list is short in practice; its length is known only on the device
+    long long b = nblocks(nz, TPB);
+    if (b > 152) b = 152;
+    k_fixup_list<T><<<(int)b, TPB, 0, s>>>(P, Uout, pflag, L, G, S, cnt, fl);
+  } else {
+    k_fixup<T><<<nblocks(nz, TPB), TPB, 0, s>>>(P, Uout, pflag, L, G, S, cnt);
+  }
   return 1;
 }
 template int launch_fixup<double>(const VarsT<double>&, double*, const int8_t*, const Layout&, const DevGeom&,
-                                  const Scheme&, unsigned long long*, cudaStream_t);
+                                  const Scheme&, unsigned long long*, cudaStream_t, FailList);
 template int launch_fixup<float>(const VarsT<float>&, double*, const int8_t*, const Layout&, const DevGeom&,
-                                 const Scheme&, unsigned long long*, cudaStream_t);
+                                 const Scheme&, unsigned long long*, cudaStream_t, FailList);
 
 template <class T>
 int launch_cfl(T* const ctop[3], const Layout& L, double cfl, double* partial, int npartial, double* dt_out,

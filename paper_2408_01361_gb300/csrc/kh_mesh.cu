@@ -219,15 +219,17 @@ __device__ __forceinline__ double wmax(double x) {
 template <class T>
 __global__ void __launch_bounds__(RED_THREADS) km_cfl(const MBlock* blk, const unsigned* pre, int nb, const T* c1,
                                                      const T* c2, const T* c3, double cfl, double* partial) {
-  double mx = 0.0;
+  T mt = T(0);  // per-thread maximum in the speeds' precision
   const unsigned nz = __ldg(pre + nb);
   for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < nz; t += gridDim.x * blockDim.x) {
     const int b = find_block(pre, nb, t);
     const MBlock& m = blk[b];
     int i, j, k;
     zone_ijk(m.L, t - __ldg(pre + b), i, j, k);
-    mx = fmax(mx, cfl_inv_zone(c1 + m.off, c2 + m.off, m.L.ndim == 3 ? c3 + m.off : c3, m.L, i, j, k));
+    const T v = cfl_inv_zone(c1 + m.off, c2 + m.off, m.L.ndim == 3 ? c3 + m.off : c3, m.L, i, j, k);
+    mt = v > mt ? v : mt;
   }
+  double mx = (double)mt;
   __shared__ double sm[RED_THREADS / 32];
   mx = wmax(mx);
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = mx;

@@ -224,7 +224,8 @@ __device__ __forceinline__ void source_terms(const R* P, const Met<M>& m, const 
 __device__ __forceinline__ void update_zone(const double* U0, const CVars& Pin, const Vars& Pout, double* Uout,
                                             const double* F1, const double* F2, const double* F3, const Layout& L,
                                             const DevGeom& G, const Scheme& S, double cdt, int8_t* pflag,
-                                            unsigned long long* cnt, int i, int j, int k, double* Praw = nullptr) {
+                                            unsigned long long* cnt, int i, int j, int k, double* Praw = nullptr,
+                                            FailList fl = FailList{nullptr, nullptr}) {
   const long long c = L.at(k, j, i);
   const long long p = (long long)j * L.n1s + i;
   const long long sj = L.n1s, sk = (long long)L.n1s * L.n2s;
@@ -271,7 +272,10 @@ __device__ __forceinline__ void update_zone(const double* U0, const CVars& Pin, 
     for (int v = 0; v < NV; ++v) Uout[v * L.plane + c] = U[v];
   }
   pflag[c] = (int8_t)flag;
-  if (flag) atomicAdd(cnt + CNT_FAIL, 1ULL);
+  if (flag) {
+    atomicAdd(cnt + CNT_FAIL, 1ULL);
+    if (fl.idx) fl.idx[atomicAdd(fl.n, 1ULL)] = (unsigned)c;
+  }
   if (fmask) atomicAdd(cnt + CNT_FLOOR, 1ULL);
 }
 
@@ -289,7 +293,8 @@ __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT
                                                   const VarsT<float>& Pout32, double* Uout, const float* F1,
                                                   const float* F2, const float* F3, const Layout& L, const DevGeom& G,
                                                   const GeomT<float>& Gf, const Scheme& S, df64 cdt, int8_t* pflag,
-                                                  unsigned long long* cnt, int i, int j, int k) {
+                                                  unsigned long long* cnt, int i, int j, int k,
+                                                  FailList fl = FailList{nullptr, nullptr}) {
   const long long c = L.at(k, j, i);
   const long long p = (long long)j * L.n1s + i;
   const long long sj = L.n1s, sk = (long long)L.n1s * L.n2s;
@@ -411,7 +416,10 @@ __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT
     for (int v = 0; v < NV; ++v) Pout64.v[v][c] = f64_of_df(Pn[v]);
   }
   pflag[c] = (int8_t)flag;
-  if (flag) atomicAdd(cnt + CNT_FAIL, 1ULL);
+  if (flag) {
+    atomicAdd(cnt + CNT_FAIL, 1ULL);
+    if (fl.idx) fl.idx[atomicAdd(fl.n, 1ULL)] = (unsigned)c;
+  }
   if (fmask) atomicAdd(cnt + CNT_FLOOR, 1ULL);
 }
 
@@ -463,14 +471,22 @@ __device__ __forceinline__ void fixup_zone(const VarsT<T>& P, double* Uout, cons
 }
 
 
-// sum_d max(ctop_d(lower face), ctop_d(upper face)) / dx_d of zone (k, j, i).
-template <class T>
-__device__ __forceinline__ double cfl_inv_zone(const T* c1, const T* c2, const T* c3, const Layout& L, int i, int j,
-                                               int k) {
+// sum_d max(ctop_d(lower face), ctop_d(upper face)) / dx_d of zone (k, j, i),
+// in the precision of the signal speeds (FP32 on the mixed path).
+__device__ __forceinline__ double cfl_inv_zone(const double* c1, const double* c2, const double* c3, const Layout& L,
+                                               int i, int j, int k) {
   const long long c = L.at(k, j, i);
   const long long sj = L.n1s, sk = (long long)L.n1s * L.n2s;
-  double inv = fmax((double)c1[c], (double)c1[c + 1]) * L.idx[0] + fmax((double)c2[c], (double)c2[c + sj]) * L.idx[1];
-  if (L.ndim == 3) inv += fmax((double)c3[c], (double)c3[c + sk]) * L.idx[2];
+  double inv = fmax(c1[c], c1[c + 1]) * L.idx[0] + fmax(c2[c], c2[c + sj]) * L.idx[1];
+  if (L.ndim == 3) inv += fmax(c3[c], c3[c + sk]) * L.idx[2];
+  return inv;
+}
+__device__ __forceinline__ float cfl_inv_zone(const float* c1, const float* c2, const float* c3, const Layout& L,
+                                              int i, int j, int k) {
+  const long long c = L.at(k, j, i);
+  const long long sj = L.n1s, sk = (long long)L.n1s * L.n2s;
+  float inv = fmaxf(c1[c], c1[c + 1]) * L.idxf[0] + fmaxf(c2[c], c2[c + sj]) * L.idxf[1];
+  if (L.ndim == 3) inv += fmaxf(c3[c], c3[c + sk]) * L.idxf[2];
   return inv;
 }
 
