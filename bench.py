@@ -519,10 +519,10 @@ FP64_FLOPS_PER_ZONE: dict = {
 }
 FP32_FLOPS_PER_ZONE: dict = {
     ("mixed", "flux_x1"): 1530.0, ("mixed", "flux_x2"): 1611.0, ("mixed", "flux_x3"): 1677.0,
-    ("mixed", "update"): 2261.0,  # stages 1 and 2 (2246, 2276); FP64: 6 and 26 flops per zone
+    ("mixed", "update"): 2271.0,  # stages 1 and 2 (2254, 2288); FP64: 1 and 21 flops per zone
 }
 DRAM_BYTES_PER_ZONE: dict = {
-    ("mixed", "update"): 303.4,  # mean of stage 1 (263.5) and stage 2 (343.2)
+    ("mixed", "update"): 294.4,  # mean of stage 1 (252.1) and stage 2 (336.7)
     ("mixed", "flux_x1"): 44.4, ("mixed", "flux_x2"): 46.0, ("mixed", "flux_x3"): 47.7,
     ("fp64", "update"): 419.1,  # stage 1
     ("fp64", "flux_x1"): 118.0, ("fp64", "flux_x2"): 126.1, ("fp64", "flux_x3"): 128.3,
