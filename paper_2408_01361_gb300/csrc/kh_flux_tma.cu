@@ -16,6 +16,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include "kh_pair.cuh"
 #include "kh_zone.cuh"
 
 namespace kh {
@@ -67,6 +68,38 @@ __device__ __forceinline__ void weno5_lohi(float a, float b, float c, float d, f
     const float p2 = 0.375f * c + 0.75f * b - 0.125f * a;
     const float w0 = 0.0625f * q2, w1 = 0.625f * q1, w2 = 0.3125f * q0;
     lo = __fdividef(w0 * p0 + w1 * p1 + w2 * p2, w0 + w1 + w2);
+  }
+}
+
+// The same for two variables at once (paired FP32 instructions).
+__device__ __forceinline__ void weno5_lohi(P2 a, P2 b, P2 c, P2 d, P2 e, P2& lo, P2& hi) {
+  const P2 k(13.0f / 12.0f), q4(0.25f);
+  const P2 t0 = P2(-2.0f) * b + (a + c), u0 = P2(3.0f) * c + (a - P2(4.0f) * b);
+  const P2 t1 = P2(-2.0f) * c + (b + d), u1 = b - d;
+  const P2 t2 = P2(-2.0f) * d + (c + e), u2 = P2(3.0f) * c + (e - P2(4.0f) * d);
+  const P2 b0 = (k * t0) * t0 + (q4 * u0) * u0;
+  const P2 b1 = (k * t1) * t1 + (q4 * u1) * u1;
+  const P2 b2 = (k * t2) * t2 + (q4 * u2) * u2;
+  const P2 sum = b0 + b1 + b2 + 1e-37f;
+  const P2 in(__frcp_rn(sum.v.x), __frcp_rn(sum.v.y));
+  const P2 eps(1e-12f);
+  const P2 s0 = b0 * in + eps, s1 = b1 * in + eps, s2 = b2 * in + eps;
+  const P2 sm(fminf(s0.v.x, fminf(s1.v.x, s2.v.x)), fminf(s0.v.y, fminf(s1.v.y, s2.v.y)));
+  const P2 r0 = kdiv(sm, s0), r1 = kdiv(sm, s1), r2 = kdiv(sm, s2);
+  const P2 q0 = r0 * r0, q1 = r1 * r1, q2 = r2 * r2;
+  {  // upper face
+    const P2 p0 = P2(0.375f) * a + (P2(-1.25f) * b + P2(1.875f) * c);
+    const P2 p1 = P2(-0.125f) * b + (P2(0.75f) * c + P2(0.375f) * d);
+    const P2 p2 = P2(0.375f) * c + (P2(0.75f) * d + P2(-0.125f) * e);
+    const P2 w0 = P2(0.0625f) * q0, w1 = P2(0.625f) * q1, w2 = P2(0.3125f) * q2;
+    hi = kdiv(w0 * p0 + (w1 * p1 + w2 * p2), w0 + w1 + w2);
+  }
+  {  // lower face: mirrored stencils, indicators' roles swapped
+    const P2 p0 = P2(0.375f) * e + (P2(-1.25f) * d + P2(1.875f) * c);
+    const P2 p1 = P2(-0.125f) * d + (P2(0.75f) * c + P2(0.375f) * b);
+    const P2 p2 = P2(0.375f) * c + (P2(0.75f) * b + P2(-0.125f) * a);
+    const P2 w0 = P2(0.0625f) * q2, w1 = P2(0.625f) * q1, w2 = P2(0.3125f) * q0;
+    lo = kdiv(w0 * p0 + (w1 * p1 + w2 * p2), w0 + w1 + w2);
   }
 }
 
@@ -158,30 +191,39 @@ __global__ void __launch_bounds__(NT) k_flux_tma(const __grid_constant__ CUtenso
   auto at = [&](int v, int x, int y, int z) { return tile[((v * Sh::BZ + z) * Sh::BY + y) * Sh::BX + x]; };
   {
     const int cl = D == 1 ? lx : ly, row = D == 1 ? ly : lx;
-    for (int v = 0; v < NV; ++v) {
-      float s[5];
-#pragma unroll
-      for (int o = 0; o < 5; ++o) {
-        // stencil of the cell: D = 1 at box x dx + cl .. dx + cl + 4 (the box
-        // holds the tile's cells from f0 - 3 on); D = 2, 3 at cl .. cl + 4 along
-        // the direction (the box starts 3 below the first face)
-        if (D == 1) s[o] = at(v, dx + cl + o, row, 0);
-        else if (D == 2) s[o] = at(v, row, cl + o, 0);
-        else s[o] = at(v, row, 0, cl + o);
-      }
-      float lo, hi;
-      if (RECON == KH_RECON_MC) {
-        recon_mc(s[1], s[2], s[3], lo, hi);
-      } else {
-        weno5_lohi(s[0], s[1], s[2], s[3], s[4], lo, hi);
-      }
-      // hi is the left state of the face above the cell, lo the right state of the face at its bottom
+    // stencil of the cell: D = 1 at box x dx + cl .. dx + cl + 4 (the box
+    // holds the tile's cells from f0 - 3 on); D = 2, 3 at cl .. cl + 4 along
+    // the direction (the box starts 3 below the first face)
+    auto sten = [&](int v, int o) {
+      if (D == 1) return at(v, dx + cl + o, row, 0);
+      else if (D == 2) return at(v, row, cl + o, 0);
+      else return at(v, row, 0, cl + o);
+    };
+    // hi is the left state of the face above the cell, lo the right state of the face at its bottom
+    auto put = [&](int v, float lo, float hi) {
       if (D == 1) {
         if (cl < Sh::FX) sL[v][row * CW + cl] = hi;
         if (cl >= 1) sR[v][row * CW + cl - 1] = lo;
       } else {
         if (cl < Sh::FY) sL[v][cl * CW + row] = hi;
         if (cl >= 1) sR[v][(cl - 1) * CW + row] = lo;
+      }
+    };
+    if (RECON == KH_RECON_MC) {
+      for (int v = 0; v < NV; ++v) {
+        float lo, hi;
+        recon_mc(sten(v, 1), sten(v, 2), sten(v, 3), lo, hi);
+        put(v, lo, hi);
+      }
+    } else {
+      for (int v = 0; v < NV; v += 2) {  // two variables per pass
+        P2 q[5];
+#pragma unroll
+        for (int o = 0; o < 5; ++o) q[o] = P2(sten(v, o), sten(v + 1, o));
+        P2 lo, hi;
+        weno5_lohi(q[0], q[1], q[2], q[3], q[4], lo, hi);
+        put(v, lo.v.x, hi.v.x);
+        put(v + 1, lo.v.y, hi.v.y);
       }
     }
   }
@@ -200,23 +242,24 @@ __global__ void __launch_bounds__(NT) k_flux_tma(const __grid_constant__ CUtenso
   }
   const long long c = L.at(k, j, i);
   const Met<float> m = load_met(G, L.gplane, D == 3 ? LOC_CENT : D, (long long)j * L.n1s + i);
-  const float gam = (float)S.gam;
-  FState<float> sLs, sRs;
-  fluid_state(PL, m, sLs);
-  fluid_state(PR, m, sRs);
-  float FL[NV], UL[NV], FR[NV], UR[NV];
-  flux_cons(PL, sLs, m, gam, D, FL, UL);
-  flux_cons(PR, sRs, m, gam, D, FR, UR);
-  float cmaxL, cminL, cmaxR, cminR;
-  signal_speeds(PL, sLs, m, gam, D, cmaxL, cminL);
-  signal_speeds(PR, sRs, m, gam, D, cmaxR, cminR);
-  const float cm = fmaxf(0.0f, fmaxf(cmaxL, cmaxR));
-  const float cn = fmaxf(0.0f, fmaxf(-cminL, -cminR));
+  // both states at once: (left, right) pairs through paired FP32 instructions
+  const P2 gam((float)S.mx.gam);
+  P2 Pp[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Pp[v] = P2(PL[v], PR[v]);
+  FState<P2> st;
+  fluid_state(Pp, m, st);
+  P2 Fp[NV], Up[NV];
+  flux_cons(Pp, st, m, gam, D, Fp, Up);
+  P2 cmax, cmin;
+  signal_speeds(Pp, st, m, gam, D, cmax, cmin);
+  const float cm = fmaxf(0.0f, fmaxf(cmax.v.x, cmax.v.y));
+  const float cn = fmaxf(0.0f, fmaxf(-cmin.v.x, -cmin.v.y));
   const float ct = fmaxf(cm, cn);
   const bool axis = (D == 2) && ((polar_lo && j == L.s[1]) || (polar_hi && j == L.e[1]));
 #pragma unroll
   for (int v = 0; v < NV; ++v)
-    F[v * L.plane + c] = axis ? 0.0f : 0.5f * (FL[v] + FR[v]) - 0.5f * ct * (UR[v] - UL[v]);
+    F[v * L.plane + c] = axis ? 0.0f : 0.5f * (Fp[v].v.x + Fp[v].v.y) - 0.5f * ct * (Up[v].v.y - Up[v].v.x);
   ctop[c] = ct;
 }
 

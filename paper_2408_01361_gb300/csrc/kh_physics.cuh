@@ -46,6 +46,14 @@ KH_HD double kabs(double x) { return fabs(x); }
 KH_HD bool kfinite(float x) { return x - x == 0.0f; }
 KH_HD bool kfinite(double x) { return isfinite(x); }
 template <class R> KH_HD R kabs(const R& x) { return fabs(x); }  // other number types (duals)
+// x clamped to [0, 1]; x clamped below at 0; the larger and smaller of a, b
+// (a NaN passes through the clamps; other number types overload these)
+template <class R> KH_HD R kclamp01(const R& x) { return x < R(0) ? R(0) : (x > R(1) ? R(1) : x); }
+template <class R> KH_HD R kmax0(const R& x) { return x < R(0) ? R(0) : x; }
+template <class R> KH_HD void kminmax(const R& a, const R& b, R& mx, R& mn) {
+  mx = a > b ? a : b;
+  mn = a > b ? b : a;
+}
 // a / b: IEEE division in FP64; in FP32 (the mixed path's stencil physics)
 // CUDA's fast division, for divisors of modest magnitude (|b| < 2^126).
 KH_HD double kdiv(double a, double b) { return a / b; }
@@ -158,20 +166,17 @@ template <class R, class M>
 KH_HD void signal_speeds(const R* P, const FState<R>& s, const Met<M>& m, R gam, int d, R& cmax, R& cmin) {
   const R p = (gam - R(1)) * P[V_U];
   const R w = P[V_RHO] + P[V_U] + p;
-  R cms2 = kdiv(gam * p + s.bsq, w + s.bsq);
-  cms2 = cms2 < R(0) ? R(0) : (cms2 > R(1) ? R(1) : cms2);
+  const R cms2 = kclamp01(R(kdiv(gam * p + s.bsq, w + s.bsq)));
   const R Au = s.ucon[d], Bu = s.ucon[0];
   const R A = Bu * Bu - (m.gcon[0][0] + Bu * Bu) * cms2;
   const R Bq = R(2) * (Au * Bu - (m.gcon[0][d] + Au * Bu) * cms2);
   const R C = Au * Au - (m.gcon[d][d] + Au * Au) * cms2;
-  R disc = Bq * Bq - R(4) * A * C;
-  disc = disc < R(0) ? R(0) : disc;
+  const R disc = kmax0(R(Bq * Bq - R(4) * A * C));
   const R sd = sqrt(disc);
   const R i2a = kdiv(R(1), R(2) * A);
   const R vp = (Bq + sd) * i2a;
   const R vm = (Bq - sd) * i2a;
-  cmax = vp > vm ? vp : vm;
-  cmin = vp > vm ? vm : vp;
+  kminmax(vp, vm, cmax, cmin);
 }
 
 // ---------------------------------------------------------------------------
