@@ -243,7 +243,8 @@ int kh_get_stage_flux(kh_ctx* ctx, int dir, double* F);
  * be at most one level apart. Boundaries: periodic, outflow, polar.
  *
  * Arrays are arenas of all blocks in order: block b's U occupies
- * U + 8 * off_b with 8 planes of its own padded shape (kh_mesh_block_shape),
+ * U + 8 * off_b with 8 planes of its own padded shape (kh_mesh_block_shape;
+ * rows padded to a multiple of 8 elements),
  * its P (5 planes) P + 5 * off_b, its B (3 planes) B + 3 * off_b, where off_b
  * is the block's cell offset. Ghost cells are filled from other blocks: a
  * same-level copy, an MC-limited linear prolongation from a coarser block,

@@ -108,14 +108,16 @@ __device__ __forceinline__ GeomT<float> geo32(const GeoArena& A, const MBlock& m
                       A.df ? A.df + 2LL * NDF * m.goff : nullptr};
 }
 
-// Largest b with pre[b] <= t (pre has nb + 1 entries, pre[0] = 0).
+// Largest b with pre[b] <= t (pre has nb + 1 entries, pre[0] = 0, non-
+// decreasing). After the prefix the array holds a granule table: entry g is
+// that block for t = g * 2^GRAN_SHIFT; from there a forward scan (over at most
+// the few block ends inside one granule -- every block holds far more than
+// 2^GRAN_SHIFT items) replaces a binary search's chain of dependent loads.
+constexpr int GRAN_SHIFT = 8;
 __device__ __forceinline__ int find_block(const unsigned* pre, int nb, unsigned t) {
-  int lo = 0, hi = nb;
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (__ldg(pre + mid) <= t) lo = mid; else hi = mid;
-  }
-  return lo;
+  int b = (int)__ldg(pre + nb + 1 + (t >> GRAN_SHIFT));
+  while (b + 1 < nb && __ldg(pre + b + 1) <= t) ++b;
+  return b;
 }
 
 template <int D, int RECON, class TIN, class R>
@@ -258,16 +260,17 @@ __global__ void km_cfl_finish(const double* partial, int n, double cfl, double* 
 // Mean of variable v over the 2x2(x2) cells of block m starting at cell c
 // (a restriction to the next coarser level), summed i fastest, then j, k.
 template <class T>
-__device__ __forceinline__ double restrict_at(const Arena<T>& P, const MBlock& m, int v, long long c) {
+__device__ __forceinline__ T restrict_at(const Arena<T>& P, const MBlock& m, int v, long long c) {
+  // in the arena's precision (FP32 on the mixed path)
   const Layout& L = m.L;
   const T* q = vars_at(P, m).v[v];
   const long long sj = L.n1s, sk = (long long)L.n1s * L.n2s;
   const int nk = L.ndim == 3 ? 2 : 1;
-  double acc = 0.0;
+  T acc = T(0);
   for (int dk = 0; dk < nk; ++dk)
     for (int dj = 0; dj < 2; ++dj)
-      for (int di = 0; di < 2; ++di) acc += (double)q[c + di + dj * sj + dk * sk];
-  return (L.ndim == 3 ? 0.125 : 0.25) * acc;
+      for (int di = 0; di < 2; ++di) acc += q[c + di + dj * sj + dk * sk];
+  return T(L.ndim == 3 ? 0.125 : 0.25) * acc;
 }
 
 __device__ __forceinline__ double wsum(double x) {
@@ -352,25 +355,27 @@ __global__ void km_ghost(const MBlock* blk, const GhostOp* ops, long long nops, 
     for (int v = 0; v < NV; ++v) val[v] = Sv.v[v][c];
   } else if (op.mode == G_RESTRICT) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) val[v] = (T)restrict_at(P, ms, v, c);
+    for (int v = 0; v < NV; ++v) val[v] = restrict_at(P, ms, v, c);
   } else {  // prolongation from the coarse cell c with MC slopes over coarse-level neighbours
+    // (in the arena's precision: FP64 arithmetic on FP32 data would run on
+    // GB300's 1/64-rate FP64 pipe)
     const ProlongNb& nb = nbs[op.nbi];
     const int nd = ms.L.ndim;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      const double q0 = (double)Sv.v[v][c];
-      double out = q0;
+      const T q0 = Sv.v[v][c];
+      T out = q0;
       for (int d = 0; d < nd; ++d) {
         if (op.off[d] == 0 || nb.mode[d][0] == NB_NONE || nb.mode[d][1] == NB_NONE) continue;
-        double q[2];
+        T q[2];
         for (int side = 0; side < 2; ++side) {
           const MBlock& mn = blk[nb.block[d][side]];
           const long long cn = nb.cell[d][side];
-          q[side] = nb.mode[d][side] == G_COPY ? (double)vars_at(P, mn).v[v][cn] : restrict_at(P, mn, v, cn);
+          q[side] = nb.mode[d][side] == G_COPY ? vars_at(P, mn).v[v][cn] : restrict_at(P, mn, v, cn);
         }
-        out += 0.25 * op.off[d] * mc_slope(q[0], q0, q[1]);
+        out += T(0.25) * T(op.off[d]) * mc_slope(q[0], q0, q[1]);
       }
-      val[v] = (T)out;
+      val[v] = out;
     }
   }
   if (op.flags & G_FLIP2) {
@@ -570,7 +575,7 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
     L.N1 = L.n1 + 2 * L.ng;
     L.N2 = L.n2 + 2 * L.ng;
     L.N3 = L.n3 + 2 * L.ng3;
-    L.n1s = (L.N1 + 15) / 16 * 16;
+    L.n1s = (L.N1 + 7) / 8 * 8;  // small blocks: 8-element rows waste less than 16 (22 -> 24, not 32)
     L.n2s = L.N2;
     L.n3s = L.N3;
     L.gplane = (long long)L.n1s * L.n2s;
@@ -774,7 +779,23 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
   const size_t pl = (size_t)cells * sizeof(double), plf = (size_t)cells * sizeof(float);
   const size_t gp = (size_t)gcells * sizeof(double), gpf = (size_t)gcells * sizeof(float);
   KM_ALLOC(x->dblk, sizeof(MBlock) * nblocks);
-  for (int q = 0; q < 8; ++q) KM_ALLOC(x->dpre[q], sizeof(unsigned) * (nblocks + 1));
+  // prefix sums, each followed by its granule table (see find_block)
+  const std::vector<unsigned>* pres[8] = {&x->pre_face[0], &x->pre_face[1], &x->pre_face[2], &x->pre_zone,
+                                          &x->pre_ct,      &x->pre_alloc,   &x->pre_all,     &x->pre_corner};
+  std::vector<unsigned> pretab[8];
+  for (int q = 0; q < 8; ++q) {
+    const std::vector<unsigned>& pr = *pres[q];
+    const unsigned tot = pr.back();
+    const size_t ngran = ((size_t)tot >> GRAN_SHIFT) + 1;
+    pretab[q] = pr;
+    int b = 0;
+    for (size_t g = 0; g < ngran; ++g) {
+      const unsigned t = (unsigned)(g << GRAN_SHIFT);
+      while (b + 1 < nblocks && pr[b + 1] <= t) ++b;
+      pretab[q].push_back((unsigned)b);
+    }
+    KM_ALLOC(x->dpre[q], sizeof(unsigned) * pretab[q].size());
+  }
   KM_ALLOC(x->dops, sizeof(GhostOp) * std::max<long long>(x->nops, 1));
   KM_ALLOC(x->dnbs, sizeof(ProlongNb) * std::max<long long>(x->nnbs, 1));
   KM_ALLOC(x->geo, 3 * NGEO * gp);
@@ -814,10 +835,9 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
   KM_ALLOC(x->counters, NCNT * sizeof(unsigned long long));
 #undef KM_ALLOC
   if (rc == KH_OK) rc = cuda_rc(cudaMemcpy(x->dblk, x->hb.data(), sizeof(MBlock) * nblocks, cudaMemcpyHostToDevice));
-  const std::vector<unsigned>* pres[8] = {&x->pre_face[0], &x->pre_face[1], &x->pre_face[2], &x->pre_zone,
-                                          &x->pre_ct,      &x->pre_alloc,   &x->pre_all,     &x->pre_corner};
   for (int q = 0; q < 8 && rc == KH_OK; ++q)
-    rc = cuda_rc(cudaMemcpy(x->dpre[q], pres[q]->data(), sizeof(unsigned) * (nblocks + 1), cudaMemcpyHostToDevice));
+    rc = cuda_rc(
+        cudaMemcpy(x->dpre[q], pretab[q].data(), sizeof(unsigned) * pretab[q].size(), cudaMemcpyHostToDevice));
   if (rc == KH_OK && x->nops)
     rc = cuda_rc(cudaMemcpy(x->dops, ops.data(), sizeof(GhostOp) * x->nops, cudaMemcpyHostToDevice));
   if (rc == KH_OK && x->nnbs)
@@ -942,10 +962,10 @@ int issue_mesh_step(kh_mesh* x, double* U, double* P, double* B) {
     const Arena<float> Psf = arena8(x->pstarf), Pnf = arena8(x->pnf);
     const Arena<double> none64{nullptr, nullptr, NV};
     const Arena<float> none32{nullptr, nullptr, NV};
-    // stage 1: FP64 P^n (ghost-filled in FP64, converted once) -> FP32 P*
-    n += fill_ghosts(x, Pn);
+    // stage 1: FP64 P^n (converted once, then ghost-filled in FP32) -> FP32 P*
     km_to_f32<<<nblk(x->pre_alloc.back(), 256), 256, 0, s>>>(x->dblk, x->dpre[5], x->nb, Pn, Pnf);
     ++n;
+    n += fill_ghosts(x, Pnf);
     n += flux_pass<float, float>(x, Pnf, x->Ff, x->ctopf, x->emff);
     km_update_mixed<<<gu, tu, 0, s>>>(x->dblk, x->dpre[3], x->nb, U, Pnf, none64, Psf, nullptr, x->Ff[0],
                                         x->Ff[1], x->Ff[2], GA, x->S, x->dscalar + 3, 0.5, x->pflag, x->counters);

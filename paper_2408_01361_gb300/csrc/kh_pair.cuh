@@ -14,6 +14,8 @@
 
 namespace kh {
 
+using ::sqrt;  // keep the scalar overloads visible beside the pair one
+
 struct P2 {
   float2 v;
   KH_HD P2() {}
@@ -92,6 +94,33 @@ KH_HD P2 kdiv(P2Prod a, P2 b) { return kdiv(P2(a), b); }
 KH_HD P2 kdiv(P2 a, P2Prod b) { return kdiv(a, P2(b)); }
 KH_HD P2 kclamp01(P2 a) { return P2(kclamp01(a.v.x), kclamp01(a.v.y)); }
 KH_HD P2 kmax0(P2 a) { return P2(kmax0(a.v.x), kmax0(a.v.y)); }
+// the FP32 scale-free WENO5 value at x = +1/2 (weno5_plus(float...)) of two
+// stencils at once
+KH_HD P2 weno5_plus(P2 a, P2 b, P2 c, P2 d, P2 e) {
+  const P2 p0 = P2(0.375f) * a + (P2(-1.25f) * b + P2(1.875f) * c);
+  const P2 p1 = P2(-0.125f) * b + (P2(0.75f) * c + P2(0.375f) * d);
+  const P2 p2 = P2(0.375f) * c + (P2(0.75f) * d + P2(-0.125f) * e);
+  const P2 k(13.0f / 12.0f), q4(0.25f);
+  const P2 t0 = P2(-2.0f) * b + (a + c), u0 = P2(3.0f) * c + (a - P2(4.0f) * b);
+  const P2 t1 = P2(-2.0f) * c + (b + d), u1 = b - d;
+  const P2 t2 = P2(-2.0f) * d + (c + e), u2 = P2(3.0f) * c + (e - P2(4.0f) * d);
+  const P2 b0 = (k * t0) * t0 + (q4 * u0) * u0;
+  const P2 b1 = (k * t1) * t1 + (q4 * u1) * u1;
+  const P2 b2 = (k * t2) * t2 + (q4 * u2) * u2;
+  const P2 sum = b0 + b1 + b2 + 1e-37f;
+#ifdef __CUDA_ARCH__
+  const P2 in(__frcp_rn(sum.v.x), __frcp_rn(sum.v.y));
+#else
+  const P2 in(1.0f / sum.v.x, 1.0f / sum.v.y);
+#endif
+  const P2 eps(1e-12f);
+  const P2 s0 = b0 * in + eps, s1 = b1 * in + eps, s2 = b2 * in + eps;
+  const P2 sm(fminf(s0.v.x, fminf(s1.v.x, s2.v.x)), fminf(s0.v.y, fminf(s1.v.y, s2.v.y)));
+  const P2 r0 = kdiv(sm, s0), r1 = kdiv(sm, s1), r2 = kdiv(sm, s2);
+  const P2 w0 = (P2(0.0625f) * r0) * r0, w1 = (P2(0.625f) * r1) * r1, w2 = (P2(0.3125f) * r2) * r2;
+  return kdiv(w0 * p0 + (w1 * p1 + w2 * p2), w0 + w1 + w2);
+}
+
 KH_HD void kminmax(P2 a, P2 b, P2& mx, P2& mn) {
   kminmax(a.v.x, b.v.x, mx.v.x, mn.v.x);
   kminmax(a.v.y, b.v.y, mx.v.y, mn.v.y);

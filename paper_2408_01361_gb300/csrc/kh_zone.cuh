@@ -4,6 +4,7 @@
 
 #include "kh_internal.h"
 #include "kh_mixed.cuh"
+#include "kh_pair.cuh"
 
 namespace kh {
 
@@ -88,9 +89,53 @@ __device__ __forceinline__ unsigned nzones(const Layout& L) {
 }
 
 // Reconstruction + LLF flux through the lower x^D face of cell (k, j, i).
+// FP32 (mixed path): the left and right states as packed pairs.
+template <int D, int RECON>
+__device__ __forceinline__ void flux_face_pair(const CVarsT<float>& P, const Layout& L, const GeomT<float>& G,
+                                               const Scheme& S, int i, int j, int k, float* F, float* ctop,
+                                               int polar_lo, int polar_hi) {
+  const long long c = L.at(k, j, i);
+  const long long st = (D == 1) ? 1 : (D == 2 ? (long long)L.n1s : (long long)L.n1s * L.n2s);
+  P2 Pp[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const float* q = P.v[v] + c;
+    if (RECON == KH_RECON_MC) {
+      const float qm2 = __ldg(q - 2 * st), qm1 = __ldg(q - st), q0 = __ldg(q), qp1 = __ldg(q + st);
+      float lo, hi, l2, h2;
+      recon_mc(qm2, qm1, q0, lo, hi);
+      recon_mc(qm1, q0, qp1, l2, h2);
+      Pp[v] = P2(hi, l2);
+    } else {
+      const float qm3 = __ldg(q - 3 * st), qm2 = __ldg(q - 2 * st), qm1 = __ldg(q - st), q0 = __ldg(q);
+      const float qp1 = __ldg(q + st), qp2 = __ldg(q + 2 * st);
+      // left: upper face of the cell below; right: lower face of the cell above (mirrored stencil)
+      Pp[v] = weno5_plus(P2(qm3, qp2), P2(qm2, qp1), P2(qm1, q0), P2(q0, qm1), P2(qp1, qm2));
+    }
+  }
+  const Met<float> m = load_met(G, L.gplane, D == 3 ? LOC_CENT : D, (long long)j * L.n1s + i);
+  const P2 gam(S.mx.gam);
+  FState<P2> sp;
+  fluid_state(Pp, m, sp);
+  P2 Fp[NV], Up[NV];
+  flux_cons(Pp, sp, m, gam, D, Fp, Up);
+  P2 cmax, cmin;
+  signal_speeds(Pp, sp, m, gam, D, cmax, cmin);
+  const float ct = fmaxf(fmaxf(0.0f, fmaxf(cmax.v.x, cmax.v.y)), fmaxf(0.0f, fmaxf(-cmin.v.x, -cmin.v.y)));
+  const bool axis = (D == 2) && ((polar_lo && j == L.s[1]) || (polar_hi && j == L.e[1]));
+#pragma unroll
+  for (int v = 0; v < NV; ++v)
+    F[v * L.plane + c] = axis ? 0.0f : 0.5f * (Fp[v].v.x + Fp[v].v.y) - 0.5f * ct * (Up[v].v.y - Up[v].v.x);
+  ctop[c] = ct;
+}
+
 template <int D, int RECON, class TIN, class R>
 __device__ __forceinline__ void flux_face(const CVarsT<TIN>& P, const Layout& L, const GeomT<R>& G, const Scheme& S,
                                           int i, int j, int k, R* F, R* ctop, int polar_lo, int polar_hi) {
+  if constexpr (sizeof(R) == 4 && sizeof(TIN) == 4) {
+    flux_face_pair<D, RECON>(P, L, G, S, i, j, k, F, ctop, polar_lo, polar_hi);
+    return;
+  }
   const long long c = L.at(k, j, i);
   const long long st = (D == 1) ? 1 : (D == 2 ? (long long)L.n1s : (long long)L.n1s * L.n2s);
   R PL[NV], PR[NV];
