@@ -18,7 +18,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
-_SRC = [os.path.join(_HERE, f) for f in ("harm_oracle.cpp", "harm_oracle.hpp", "dual.hpp")]
+_SRC = [os.path.join(_HERE, f) for f in ("harm_oracle.cpp", "harm_oracle.hpp", "dual.hpp", "opcount.hpp")]
 
 KIND = {"minkowski": 0, "ks": 1, "mks": 2, "fmks": 3}
 BC = {"periodic": 0, "outflow": 1, "polar": 2, "dirichlet": 3}
@@ -124,6 +124,7 @@ def lib():
         L.or_point_jacobians.argtypes = [C.c_double, _dp, _dp, C.c_int, _dp, _dp]
         L.or_point_source.argtypes = [PP, C.c_double, C.c_double, _dp, _dp]
         L.or_recon.argtypes = [C.c_int, C.c_int, _dp, _dp, _dp]
+        L.or_count_ops.argtypes = [PP, C.c_double, C.c_double, _dp, _dp]
     return _lib
 
 
@@ -329,3 +330,13 @@ def stage(cfg: dict, U0, Pin, cdt: float, Uout, Pout):
     st = (C.c_long * 3)()
     lib().or_stage(C.byref(params(cfg)), U0, Pin, float(cdt), Uout, Pout, *[_ptr(c) for c in ct], st)
     return ct, list(st)
+
+
+def count_ops(cfg: dict, x1: float, x2: float, P):
+    """Floating-point operations of the method's per-item formulas (oracle
+    point physics on the counting type): dict with weno5 (one face value),
+    mc (one cell), llf (one face from its two states), sources (one zone),
+    p2c (one zone)."""
+    out = np.zeros(5)
+    lib().or_count_ops(C.byref(params(cfg)), float(x1), float(x2), np.ascontiguousarray(P, dtype=np.float64), out)
+    return dict(zip(("weno5", "mc", "llf", "sources", "p2c"), out.tolist()))

@@ -954,6 +954,47 @@ void or_point_jacobians(double gam, const double* gcov16, const double* P, int d
   }
 }
 
+// Floating-point operations of the method's per-item formulas, counted by
+// running the oracle's own templated point physics on the counting type at
+// one state (the counts do not depend on the values except through the
+// clamps and branches the state takes): out[0] one WENO5 face value, out[1]
+// one MC reconstruction of a cell (slope and both face values), out[2] the
+// LLF flux of one face from its two states (two fluid states, four flux and
+// conserved vectors, two speed pairs, the LLF combination), out[3] the
+// connection source terms of one zone, out[4] the conserved variables of
+// one zone from its primitives. P: 8 primitives; the metric is that of the
+// cell centre at native (x1, x2).
+void or_count_ops(const or_params* c, double x1, double x2, const double* P, double* out) {
+  Geo G = geo_at(*c, x1, x2);
+  double cn[4][4][4];
+  connection_at(*c, x1, x2, cn);
+  OpCounts& k = op_counts();
+  // a monotone stencil: MC takes its full path (a nonzero slope)
+  Cnt q[5] = {Cnt(P[0]), Cnt(1.1 * P[0]), Cnt(1.25 * P[0]), Cnt(1.3 * P[0]), Cnt(1.5 * P[0])};
+  k = OpCounts();
+  (void)weno5_upper<Cnt>(q);
+  out[0] = (double)k.total();
+  k = OpCounts();
+  Cnt lo, hi;
+  recon_cell<Cnt>(RECON_MC, q, lo, hi);
+  out[1] = (double)k.total();
+  Cnt Pc[NVAR], Pr[NVAR], F[NVAR], S[NVAR], U[NVAR], ct;
+  for (int v = 0; v < NVAR; ++v) {
+    Pc[v] = Cnt(P[v]);
+    Pr[v] = Cnt(P[v] * (1.0 + 0.01 * (v + 1)));
+  }
+  const Cnt gam(c->gam);
+  k = OpCounts();
+  llf_flux<Cnt, Cnt>(Pc, Pr, G, gam, 1, F, ct);
+  out[2] = (double)k.total();
+  k = OpCounts();
+  source_terms<Cnt, Cnt>(Pc, G, cn, gam, S);
+  out[3] = (double)k.total();
+  k = OpCounts();
+  p2c_at<Cnt>(G, Pc, gam, U);
+  out[4] = (double)k.total();
+}
+
 // Source terms of one state at a cell centre of the grid (j, i).
 void or_point_source(const or_params* c, double x1, double x2, const double* P, double* S) {
   Geo G = geo_at(*c, x1, x2);

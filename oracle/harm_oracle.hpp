@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "dual.hpp"
+#include "opcount.hpp"
 
 namespace oracle {
 
