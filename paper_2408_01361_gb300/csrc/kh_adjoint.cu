@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(ATPB) k_adj_src(const double* lu, CVars Ph, La
         Sd[v] = D9(0.0);
       }
       const Met<double> m = load_met(G, L.gplane, LOC_CENT, p);
-      source_terms(Pd, m, G.conn, L.gplane, p, D9::var(S.gam, 8), Sd);
+      source_terms(Pd, m, G.dgm, L.gplane, p, D9::var(S.gam, 8), Sd);
       for (int q = 0; q < 9; ++q) {
         double acc = 0.0;
         for (int v = V_U; v <= V_U3; ++v) acc += ls[v] * Sd[v].d[q];
@@ -615,7 +615,7 @@ void launch_face_adj(const kh_ctx* x, const CVars& Ph, const double* lf, double*
   const FaceBox b = face_box(L, D);
   const long long tot = (long long)b.n[0] * b.n[1] * b.n[2];
   const int plo = x->S.bc[2] == KH_BC_POLAR, phi = x->S.bc[3] == KH_BC_POLAR;
-  const DevGeom G{x->geo, x->conn, x->flo};
+  const DevGeom G{x->geo, x->dgm, x->flo};
   if (x->S.recon == KH_RECON_MC)
     k_adj_face<D, KH_RECON_MC><<<nb(tot, AFPB), AFPB, 0, s>>>(Ph, lf, L, G, x->S, b, plo, phi, lp, gsum);
   else
@@ -648,7 +648,7 @@ void reverse_stage(kh_ctx* x, const CVars& Ph, double coef, const double* seed, 
   double* lp = x->adj + ADJ_LP * L.plane;
   double* lf = x->adj + ADJ_LF * L.plane;
   double* le = x->adj + ADJ_LE * L.plane;
-  const DevGeom G{x->geo, x->conn, x->flo};
+  const DevGeom G{x->geo, x->dgm, x->flo};
   const long long nz = (long long)L.n1 * L.n2 * L.n3;
   cudaMemsetAsync(lp, 0, NV * L.plane * sizeof(double), s);
   k_adj_src<<<nb(nz, ATPB), ATPB, 0, s>>>(lu, Ph, L, G, x->S, x->dscalar + 3, coef, gU_in, lp, x->adj_red,
@@ -704,7 +704,7 @@ int kh_step_adjoint(kh_ctx* x, const double* U, const double* P, const double* B
   double* raw2 = x->adj + ADJ_RAW2 * L.plane;
   double* un1 = x->adj + ADJ_UN1 * L.plane;
   int8_t* pflag1 = x->adj_i8;
-  const DevGeom G{x->geo, x->conn, x->flo};
+  const DevGeom G{x->geo, x->dgm, x->flo};
   const long long nz = (long long)L.n1 * L.n2 * L.n3;
 
   // ---- forward record from the checkpoint (the kernels of kh_step) ----
@@ -767,7 +767,7 @@ int kh_prim_to_cons_adjoint(kh_ctx* x, const double* P, const double* B, const d
   for (int q = 0; q < 5; ++q) Pv.v[q] = P + q * L.plane;
   for (int q = 0; q < 3; ++q) Pv.v[5 + q] = B + q * L.plane;
   cudaMemsetAsync(x->adj_red, 0, sizeof(double), s);
-  k_p2c_adj<<<nb(L.plane, ATPB), ATPB, 0, s>>>(Pv, gU, L, DevGeom{x->geo, x->conn, x->flo}, x->S, gP, gB,
+  k_p2c_adj<<<nb(L.plane, ATPB), ATPB, 0, s>>>(Pv, gU, L, DevGeom{x->geo, x->dgm, x->flo}, x->S, gP, gB,
                                                x->adj_red);
   double gg = 0.0;
   int rc = adj_rc(cudaGetLastError());

@@ -28,7 +28,7 @@ int cuda_fail(cudaError_t e) {
     if (_rc != KH_OK) return _rc;         \
   } while (0)
 
-DevGeom devgeom(const kh_ctx* x) { return DevGeom{x->geo, x->conn, x->flo}; }
+DevGeom devgeom(const kh_ctx* x) { return DevGeom{x->geo, x->dgm, x->flo}; }
 
 Vars vars_of(const kh_ctx* x, double* P, double* B) {
   Vars v;
@@ -77,16 +77,16 @@ int check_launch(kh_ctx* x, int n) {
 }
 
 void free_all(kh_ctx* x) {
-  void* ptrs[] = {x->geo, x->conn, x->flo, x->pstar, x->F[0], x->F[1], x->F[2], x->ctop[0], x->ctop[1],
+  void* ptrs[] = {x->geo, x->dgm, x->flo, x->pstar, x->F[0], x->F[1], x->F[2], x->ctop[0], x->ctop[1],
                   x->ctop[2], x->emf[0], x->emf[1], x->emf[2], x->pflag, x->partial, x->dscalar,
-                  x->counters, x->dirichlet[0], x->dirichlet[1], x->geof, x->connf, x->pstarf, x->pnf, x->Ff[0],
+                  x->counters, x->dirichlet[0], x->dirichlet[1], x->geof, x->dgmf, x->pstarf, x->pnf, x->Ff[0],
                   x->Ff[1], x->Ff[2], x->ctopf[0], x->ctopf[1], x->ctopf[2], x->emff[0], x->emff[1],
                   x->emff[2], x->dirichletf[0], x->dirichletf[1], x->adj, x->adj_i8, x->adj_red, x->geodf, x->flist};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
 
-GeomT<float> geomf(const kh_ctx* x) { return GeomT<float>{x->geof, x->connf, x->flo, x->geodf}; }
+GeomT<float> geomf(const kh_ctx* x) { return GeomT<float>{x->geof, x->dgmf, x->flo, x->geodf}; }
 
 // One FP64 stage: ghost fill, fluxes per direction, Flux-CT, update, fixup.
 int run_stage(kh_ctx* x, int st, const double* U0, const Vars& Pin, const Vars& Pout, double* Uout, double coef) {
@@ -272,7 +272,7 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
     rc = cuda_fail(cudaMalloc((void**)&(ptr), (bytes)));              \
   }
   KH_ALLOC(x->geo, 3 * NGEO * gp);
-  KH_ALLOC(x->conn, NCONN * gp);
+  KH_ALLOC(x->dgm, NDG * gp);
   KH_ALLOC(x->flo, 3 * gp);
   const bool mixed = c->precision == KH_MIXED;
   const size_t plf = (size_t)L.plane * sizeof(float);
@@ -290,7 +290,7 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
     }
   } else {
     KH_ALLOC(x->geof, 3 * NGEO * gpf);
-    KH_ALLOC(x->connf, NCONN * gpf);
+    KH_ALLOC(x->dgmf, NDG * gpf);
     KH_ALLOC(x->geodf, 2 * NDF * gpf);
     KH_ALLOC(x->pstarf, NV * plf);
     KH_ALLOC(x->pnf, NV * plf);
@@ -329,10 +329,10 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
     if (rc == KH_OK && x->pstarf) rc = cuda_fail(cudaMemset(x->pstarf, 0, NV * plf));
   }
   if (rc == KH_OK) {
-    x->launches += launch_geometry(x->cp, c->x1min, c->x2min, S.fl, L, x->geo, x->conn, x->flo, 0);
+    x->launches += launch_geometry(x->cp, c->x1min, c->x2min, S.fl, L, x->geo, x->dgm, x->flo, 0);
     if (mixed) {
       x->launches += launch_to_f32(x->geo, x->geof, 3LL * NGEO * L.gplane, 0);
-      x->launches += launch_to_f32(x->conn, x->connf, (long long)NCONN * L.gplane, 0);
+      x->launches += launch_to_f32(x->dgm, x->dgmf, (long long)NDG * L.gplane, 0);
       x->launches += launch_df_planes(x->geo, x->flo, x->geodf, L.gplane, 0);
     }
     rc = cuda_fail(cudaGetLastError());

@@ -11,7 +11,7 @@ struct kh_ctx {
   kh::CoordParams cp;
   cudaStream_t stream;
   double* geo;
-  double* conn;
+  double* dgm;
   double* flo;     // geometric floors of rho and u per (i, j)
   double* pstar;   // 8 planes: stage-1 output
   double* F[3];    // 8 planes each
@@ -26,7 +26,7 @@ struct kh_ctx {
   // mixed precision (KH_MIXED): FP32 geometry copy, FP32 flux pass buffers,
   // FP32 stage-1 output and FP32 Dirichlet ghosts
   float* geof;
-  float* connf;
+  float* dgmf;
   float* geodf;    // [NDF][2] double-float planes of the cell-centre geometry and floors
   unsigned* flist; // failed-zone list of the current stage (one entry per zone at most)
   float* pstarf;   // 8 planes

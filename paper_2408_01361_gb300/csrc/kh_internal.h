@@ -11,7 +11,7 @@ namespace kh {
 
 constexpr int NGHOST = 3;
 constexpr int NGEO = 22;  // per location: gcov (10 symmetric), gcon (10), gdet, alpha
-constexpr int NCONN = 40; // Gamma^l_{mn}: 4 x 10 symmetric pairs
+constexpr int NDG = 20;  // d_1 g_{mn}, d_2 g_{mn}: 2 x 10 symmetric pairs (cell centres)
 enum { LOC_CENT = 0, LOC_F1 = 1, LOC_F2 = 2 };
 
 struct Layout {
@@ -40,7 +40,7 @@ using CVars = CVarsT<double>;
 // Geometry cache in precision T (the FP64 cache and its FP32 copy).
 template <class T> struct GeomT {
   const T* g;          // [3][NGEO][n2s][n1s]
-  const T* conn;       // [NCONN][n2s][n1s]
+  const T* dgm;        // [NDG][n2s][n1s]: metric derivatives in x1 and x2 at cell centres
   const double* flo;   // [3][n2s][n1s]: geometric floors of rho and u, and 1/sqrt(-g), at cell centres
   const float* df;     // FP32 copy only: [NDF][2][n2s][n1s] double-float planes (above)
 };
@@ -78,7 +78,7 @@ struct FailList {
 // Geometry of a grid whose first interior cell starts at native (x1o, x2o);
 // cp.x1min is the FMKS blending reference (the x1 start of the whole domain).
 int launch_geometry(const CoordParams& cp, double x1o, double x2o, const FloorParams& fl, const Layout& L, double* geo,
-                    double* conn, double* flo, cudaStream_t s);
+                    double* dgm, double* flo, cudaStream_t s);
 template <class T> inline CVarsT<T> cviewT(const VarsT<T>& v) {
   CVarsT<T> c;
   for (int q = 0; q < NV; ++q) c.v[q] = v.v[q];

@@ -24,7 +24,7 @@ inline int nblocks(long long n, int tpb) { return (int)((n + tpb - 1) / tpb); }
 // sqrt(-g), lapse at CENT, x1 face and x2 face; connection and r at CENT.
 // ---------------------------------------------------------------------------
 __global__ void k_geometry(CoordParams cp, double x1o, double x2o, FloorParams fl, Layout L, double* geo,
-                           double* conn, double* flo) {
+                           double* dgm, double* flo) {
   const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= L.gplane) return;
   const int i = (int)(p % L.n1s), j = (int)(p / L.n1s);
@@ -47,11 +47,10 @@ __global__ void k_geometry(CoordParams cp, double x1o, double x2o, FloorParams f
     b[20 * L.gplane] = sqrt(fabs(det));
     b[21 * L.gplane] = 1.0 / sqrt(-gi[0][0]);
     if (loc == LOC_CENT) {
-      double G[4][4][4];
-      connection_from(gi, dg, G);
-      for (int l = 0; l < 4; ++l)
+      // d_1 g_{mn}, d_2 g_{mn} (the metric does not depend on t or phi)
+      for (int a = 1; a <= 2; ++a)
         for (int m = 0; m < 4; ++m)
-          for (int n = m; n < 4; ++n) conn[(l * 10 + sym_index(m, n)) * L.gplane + p] = G[l][m][n];
+          for (int n = m; n < 4; ++n) dgm[((a - 1) * 10 + sym_index(m, n)) * L.gplane + p] = dg[a][m][n];
       const double r = (cp.kind == COORD_MINKOWSKI) ? 1.0 : coord_map(cp, x1c, x2c).r;
       flo[p] = fmax(fl.rho_min * pow(r, -1.5), 1e-20);
       flo[L.gplane + p] = fmax(fl.u_min * pow(r, -2.5), 1e-20);
@@ -393,8 +392,8 @@ int reduction_blocks(const Layout& L) {
 }
 
 int launch_geometry(const CoordParams& cp, double x1o, double x2o, const FloorParams& fl, const Layout& L, double* geo,
-                    double* conn, double* flo, cudaStream_t s) {
-  k_geometry<<<nblocks(L.gplane, TPB), TPB, 0, s>>>(cp, x1o, x2o, fl, L, geo, conn, flo);
+                    double* dgm, double* flo, cudaStream_t s) {
+  k_geometry<<<nblocks(L.gplane, TPB), TPB, 0, s>>>(cp, x1o, x2o, fl, L, geo, dgm, flo);
   return 1;
 }
 

@@ -94,17 +94,17 @@ template <class T> __device__ __forceinline__ CVarsT<T> cvars_at(const Arena<T>&
 
 struct GeoArena {
   const double* g;
-  const double* conn;
+  const double* dgm;
   const double* flo;
   const float* gf;
-  const float* connf;
+  const float* dgmf;
   const float* df;
 };
 __device__ __forceinline__ DevGeom geo64(const GeoArena& A, const MBlock& m) {
-  return DevGeom{A.g + 3LL * NGEO * m.goff, A.conn + (long long)NCONN * m.goff, A.flo + 3 * m.goff};
+  return DevGeom{A.g + 3LL * NGEO * m.goff, A.dgm + (long long)NDG * m.goff, A.flo + 3 * m.goff};
 }
 __device__ __forceinline__ GeomT<float> geo32(const GeoArena& A, const MBlock& m) {
-  return GeomT<float>{A.gf + 3LL * NGEO * m.goff, A.connf + (long long)NCONN * m.goff, A.flo + 3 * m.goff,
+  return GeomT<float>{A.gf + 3LL * NGEO * m.goff, A.dgmf + (long long)NDG * m.goff, A.flo + 3 * m.goff,
                       A.df ? A.df + 2LL * NDF * m.goff : nullptr};
 }
 
@@ -448,8 +448,8 @@ struct kh_mesh {
   long long nops;
   ProlongNb* dnbs;
   long long nnbs;
-  double *geo, *conn, *flo;
-  float *geof, *connf;
+  double *geo, *dgm, *flo;
+  float *geof, *dgmf;
   float* geodf;  // [NDF][2] double-float planes per block (goff-based)
   double* pstar;
   float *pstarf, *pnf;
@@ -799,7 +799,7 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
   KM_ALLOC(x->dops, sizeof(GhostOp) * std::max<long long>(x->nops, 1));
   KM_ALLOC(x->dnbs, sizeof(ProlongNb) * std::max<long long>(x->nnbs, 1));
   KM_ALLOC(x->geo, 3 * NGEO * gp);
-  KM_ALLOC(x->conn, NCONN * gp);
+  KM_ALLOC(x->dgm, NDG * gp);
   KM_ALLOC(x->flo, 3 * gp);
   KM_ALLOC(x->pstar, NV * pl);
   KM_ALLOC(x->pflag, (size_t)cells);
@@ -815,7 +815,7 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
     }
   } else {
     KM_ALLOC(x->geof, 3 * NGEO * gpf);
-    KM_ALLOC(x->connf, NCONN * gpf);
+    KM_ALLOC(x->dgmf, NDG * gpf);
     KM_ALLOC(x->geodf, 2 * NDF * gpf);
     KM_ALLOC(x->pstarf, NV * plf);
     KM_ALLOC(x->pnf, NV * plf);
@@ -860,12 +860,12 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
     const double x1o = c->x1min + m.i0 * m.L.dx[0];
     const double x2o = c->x2min + m.j0 * m.L.dx[1];
     x->launches += launch_geometry(x->cp, x1o, x2o, S.fl, m.L, x->geo + 3LL * NGEO * m.goff,
-                                   x->conn + (long long)NCONN * m.goff, x->flo + 3 * m.goff, 0);
+                                   x->dgm + (long long)NDG * m.goff, x->flo + 3 * m.goff, 0);
     rc = cuda_rc(cudaGetLastError());
   }
   if (rc == KH_OK && mixed) {
     x->launches += launch_to_f32(x->geo, x->geof, 3LL * NGEO * gcells, 0);
-    x->launches += launch_to_f32(x->conn, x->connf, (long long)NCONN * gcells, 0);
+    x->launches += launch_to_f32(x->dgm, x->dgmf, (long long)NDG * gcells, 0);
     for (int b = 0; b < nblocks; ++b) {
       const MBlock& m = x->hb[b];
       x->launches += launch_df_planes(x->geo + 3LL * NGEO * m.goff, x->flo + 3 * m.goff, x->geodf + 2LL * NDF * m.goff,
@@ -886,7 +886,7 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
 
 namespace {
 
-GeoArena garena(const kh_mesh* x) { return GeoArena{x->geo, x->conn, x->flo, x->geof, x->connf, x->geodf}; }
+GeoArena garena(const kh_mesh* x) { return GeoArena{x->geo, x->dgm, x->flo, x->geof, x->dgmf, x->geodf}; }
 
 template <class T> Arena<T> arena8(T* p) { return Arena<T>{p, nullptr, NV}; }
 Arena<double> arena_pb(double* P, double* B) { return Arena<double>{P, B, 5}; }
@@ -1259,7 +1259,7 @@ int kh_mesh_destroy(kh_mesh* x) {
   cudaStreamSynchronize(x->stream);
   drop_mesh_graph(x);
   if (x->cap_stream) cudaStreamDestroy(x->cap_stream);
-  void* ptrs[] = {x->dblk, x->dops, x->dnbs, x->geo, x->conn, x->flo, x->geof, x->connf, x->geodf, x->pstar, x->pstarf, x->pnf,
+  void* ptrs[] = {x->dblk, x->dops, x->dnbs, x->geo, x->dgm, x->flo, x->geof, x->dgmf, x->geodf, x->pstar, x->pstarf, x->pnf,
                   x->pflag, x->partial, x->dscalar, x->counters, x->F[0], x->F[1], x->F[2], x->ctop[0],
                   x->ctop[1], x->ctop[2], x->emf[0], x->emf[1], x->emf[2], x->Ff[0], x->Ff[1], x->Ff[2],
                   x->ctopf[0], x->ctopf[1], x->ctopf[2], x->emff[0], x->emff[1], x->emff[2]};

@@ -235,31 +235,35 @@ __device__ __forceinline__ void apply_ct_at(R* F1, R* F2, R* F3, const R* e1, co
   }
 }
 
-
-// S_nu = sqrt(-g) T^k_l Gamma^l_{nu k} for nu = t, 1, 2, 3 (energy and
-// momentum slots); zero for rho and B.
+// Connection source terms of the energy and momentum equations,
+// S_nu = sqrt(-g) T^k_l Gamma^l_{nu k} (0 for rho and B), evaluated as
+// (1/2) sqrt(-g) T^{kl} d_nu g_{kl}: with T^{kl} symmetric, the two terms of
+// Gamma_{l nu k} = (d_nu g_{lk} + d_k g_{l nu} - d_l g_{nu k}) / 2 other than
+// the first cancel in the contraction. The metric depends on x1 and x2 only,
+// so S_t = S_phi = 0 and the sum needs the 2 x 10 derivatives d_1 g, d_2 g.
 template <class R, class M>
-__device__ __forceinline__ void source_terms(const R* P, const Met<M>& m, const M* conn, long long gplane, long long p,
+__device__ __forceinline__ void source_terms(const R* P, const Met<M>& m, const M* dgm, long long gplane, long long p,
                                              R gam, R* S) {
   FState<R> s;
   fluid_state(P, m, s);
   const R pg = (gam - R(1)) * P[V_U];
   const R eta = P[V_RHO] + P[V_U] + pg + s.bsq;
   const R ptot = pg + R(0.5) * s.bsq;
-  R T[4][4];
+  R acc1 = R(0), acc2 = R(0);
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) T[a][b] = eta * s.ucon[a] * s.ucov[b] - s.bcon[a] * s.bcov[b] + (a == b ? ptot : R(0));
-#pragma unroll
-  for (int nu = 0; nu < 4; ++nu) {
-    R acc = R(0);
-#pragma unroll
-    for (int l = 0; l < 4; ++l)
-#pragma unroll
-      for (int kk = 0; kk < 4; ++kk) acc += T[kk][l] * __ldg(conn + (l * 10 + sym_index(nu, kk)) * gplane + p);
-    S[V_U + nu] = m.gdet * acc;
-  }
+    for (int b = a; b < 4; ++b) {
+      const int q = sym_index(a, b);
+      R t = eta * s.ucon[a] * s.ucon[b] - s.bcon[a] * s.bcon[b] + ptot * m.gcon[a][b];  // T^{ab}
+      if (a != b) t = R(2) * t;
+      acc1 += t * __ldg(dgm + q * gplane + p);
+      acc2 += t * __ldg(dgm + (10 + q) * gplane + p);
+    }
+  S[V_U] = R(0);
+  S[V_U1] = R(0.5) * m.gdet * acc1;
+  S[V_U2] = R(0.5) * m.gdet * acc2;
+  S[V_U3] = R(0);
 }
 
 
@@ -279,7 +283,7 @@ __device__ __forceinline__ void update_zone(const double* U0, const CVars& Pin, 
 #pragma unroll
   for (int v = 0; v < NV; ++v) P[v] = Pin.v[v][c];
   double Sv[NV] = {0, 0, 0, 0, 0, 0, 0, 0};
-  source_terms(P, m, G.conn, L.gplane, p, S.gam, Sv);
+  source_terms(P, m, G.dgm, L.gplane, p, S.gam, Sv);
   double U[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
@@ -353,7 +357,7 @@ __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT
     for (int v = 0; v < NV; ++v) Pf[v] = Pin.v[v][c];
     float Sv[NV] = {0, 0, 0, 0, 0, 0, 0, 0};
     const Met<float> mf = load_met(Gf, L.gplane, LOC_CENT, p);
-    source_terms(Pf, mf, Gf.conn, L.gplane, p, mx.gam, Sv);
+    source_terms(Pf, mf, Gf.dgm, L.gplane, p, mx.gam, Sv);
     {  // W = (rho + gam u) gamma^2, v^2 = q / gamma^2
       const float v1 = Pf[V_U1], v2 = Pf[V_U2], v3 = Pf[V_U3];
       const float q = mf.gcov[1][1] * v1 * v1 + mf.gcov[2][2] * v2 * v2 + mf.gcov[3][3] * v3 * v3 +
