@@ -22,7 +22,7 @@ _SRC = [os.path.join(_HERE, f) for f in ("harm_oracle.cpp", "harm_oracle.hpp", "
 
 KIND = {"minkowski": 0, "ks": 1, "mks": 2, "fmks": 3}
 BC = {"periodic": 0, "outflow": 1, "polar": 2, "dirichlet": 3}
-RECON = {"mc": 0, "weno5": 1}
+RECON = {"mc": 0, "weno5": 1, "donor": 2}
 
 
 def build(force: bool = False) -> str:
@@ -47,7 +47,7 @@ class Params(C.Structure):
         ("mks_smooth", C.c_double), ("cfl", C.c_double),
         ("rho_min", C.c_double), ("u_min", C.c_double), ("bsq_rho_max", C.c_double),
         ("bsq_u_max", C.c_double), ("u_rho_max", C.c_double), ("gamma_max", C.c_double),
-        ("x1ref", C.c_double),
+        ("x1ref", C.c_double), ("fofc", C.c_int),
     ]
 
 
@@ -76,6 +76,7 @@ def params(cfg: dict) -> Params:
     p.u_rho_max = fl.get("u_rho_max", 1e300)
     p.gamma_max = fl.get("gamma_max", 1e300)
     p.x1ref = cfg.get("x1ref", cfg["x1"][0])
+    p.fofc = int(bool(cfg.get("fofc", False)))
     return p
 
 
@@ -125,7 +126,18 @@ def lib():
         L.or_point_source.argtypes = [PP, C.c_double, C.c_double, _dp, _dp]
         L.or_recon.argtypes = [C.c_int, C.c_int, _dp, _dp, _dp]
         L.or_count_ops.argtypes = [PP, C.c_double, C.c_double, _dp, _dp]
+        L.or_fofc_flags.argtypes = [PP, _dp, _dp, C.c_double, _ip]
+        L.or_fofc_flags.restype = C.c_long
     return _lib
+
+
+# zones flagged by the first-order flux correction in the last step/stage call
+last_nfofc = 0
+
+
+def _note(st):
+    global last_nfofc
+    last_nfofc = int(st[3])
 
 
 def set_threads(n: int) -> None:
@@ -221,9 +233,10 @@ def step(cfg: dict, U, P, dt: float, dirichlet=None):
     U = np.array(U, dtype=np.float64, order="C", copy=True)
     P = np.array(P, dtype=np.float64, order="C", copy=True)
     lo, hi = (dirichlet or (None, None))
-    st = (C.c_long * 3)()
+    st = (C.c_long * 4)()
     dtn = lib().or_step(C.byref(params(cfg)), U, P, float(dt), _ptr(lo), _ptr(hi), st)
-    return U, P, dtn, list(st)
+    _note(st)
+    return U, P, dtn, list(st)[:3]
 
 
 def step_jvp(cfg: dict, U, P, dU, dP, dgam: float, dt: float, dirichlet=None, flux: bool = False):
@@ -239,10 +252,11 @@ def step_jvp(cfg: dict, U, P, dU, dP, dgam: float, dt: float, dirichlet=None, fl
     dF1 = np.zeros_like(P) if flux else None
     zflag = np.zeros(P.shape[1:], dtype=np.int32)
     lo, hi = (dirichlet or (None, None))
-    st = (C.c_long * 3)()
+    st = (C.c_long * 4)()
     dtn = lib().or_step_jvp(C.byref(params(cfg)), U, P, dU, dP, float(dgam), float(dt), _ptr(lo), _ptr(hi),
                             _ptr(dF1), _ptr(zflag), st)
-    out = (U, P, dU, dP, dtn, list(st), zflag)
+    _note(st)
+    out = (U, P, dU, dP, dtn, list(st)[:3], zflag)
     return out + (dF1,) if flux else out
 
 
@@ -252,9 +266,10 @@ def evolve(cfg: dict, U, P, nsteps: int, dt: float, t_end: float = 0.0, dirichle
     U = np.array(U, dtype=np.float64, order="C", copy=True)
     P = np.array(P, dtype=np.float64, order="C", copy=True)
     lo, hi = (dirichlet or (None, None))
-    st = (C.c_long * 3)()
+    st = (C.c_long * 4)()
     t = lib().or_evolve(C.byref(params(cfg)), U, P, int(nsteps), float(dt), float(t_end), _ptr(lo), _ptr(hi), st)
-    return U, P, t, list(st)
+    _note(st)
+    return U, P, t, list(st)[:3]
 
 
 def divb(cfg: dict, P, field: bool = False):
@@ -327,9 +342,10 @@ def stage(cfg: dict, U0, Pin, cdt: float, Uout, Pout):
     U0 = np.ascontiguousarray(U0, dtype=np.float64)
     Pin = np.ascontiguousarray(Pin, dtype=np.float64)
     ct = [np.zeros(Pin.shape[1:]) for _ in range(3)]
-    st = (C.c_long * 3)()
+    st = (C.c_long * 4)()
     lib().or_stage(C.byref(params(cfg)), U0, Pin, float(cdt), Uout, Pout, *[_ptr(c) for c in ct], st)
-    return ct, list(st)
+    _note(st)
+    return ct, list(st)[:3]
 
 
 def count_ops(cfg: dict, x1: float, x2: float, P):
@@ -340,3 +356,13 @@ def count_ops(cfg: dict, x1: float, x2: float, P):
     out = np.zeros(5)
     lib().or_count_ops(C.byref(params(cfg)), float(x1), float(x2), np.ascontiguousarray(P, dtype=np.float64), out)
     return dict(zip(("weno5", "mc", "llf", "sources", "p2c"), out.tolist()))
+
+
+def fofc_flags(cfg: dict, U0, Pin, cdt: float):
+    """Zones the first-order flux correction flags in one stage (Pin with its
+    ghosts filled): int array over the cells, 1 = flagged."""
+    U0 = np.ascontiguousarray(U0, dtype=np.float64)
+    Pin = np.ascontiguousarray(Pin, dtype=np.float64)
+    flags = np.zeros(Pin.shape[1:], dtype=np.int32)
+    lib().or_fofc_flags(C.byref(params(cfg)), U0, Pin, float(cdt), flags)
+    return flags

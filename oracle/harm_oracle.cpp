@@ -195,7 +195,11 @@ void face_range(const Grid& gr, int d, int lo[3], int hi[3]) {
 }
 
 template <class R>
-void compute_fluxes(const Grid& gr, const R* P, FluxesT<R>& fx, const R& gam) {
+void finish_fluxes(const Grid& gr, FluxesT<R>& fx);
+
+// Raw LLF face fluxes (before polar zeroing and Flux-CT).
+template <class R>
+void compute_raw(const Grid& gr, const R* P, FluxesT<R>& fx, const R& gam) {
   const GridInfo& g = gr.g;
   const size_t n = gr.cells();
   for (int d = 0; d < 3; ++d) {
@@ -232,6 +236,19 @@ void compute_fluxes(const Grid& gr, const R* P, FluxesT<R>& fx, const R& gam) {
           fx.ctop[d][gr.idx(0, k, j, i)] = val(ct);
         }
   }
+}
+
+template <class R>
+void compute_fluxes(const Grid& gr, const R* P, FluxesT<R>& fx, const R& gam) {
+  compute_raw(gr, P, fx, gam);
+  finish_fluxes(gr, fx);
+}
+
+// Polar-axis zeroing and Flux-CT applied to the raw face fluxes of fx.
+template <class R>
+void finish_fluxes(const Grid& gr, FluxesT<R>& fx) {
+  const GridInfo& g = gr.g;
+  const size_t n = gr.cells();
   // Polar axis: no flux of anything through an x2 face lying on the axis.
   {
     int lo[3], hi[3];
@@ -431,8 +448,125 @@ int floors_point(const Params& c, const Geo& G, double r, Dd P[NVAR]) {
 }
 
 struct StageStats {
-  long nfail = 0, nfloor = 0, nunfixed = 0;
+  long nfail = 0, nfloor = 0, nunfixed = 0, nfofc = 0;
 };
+
+// First-order flux correction (the paper's "Algorithm" section, after
+// Beckwith & Stone 2011), in two parts.
+// The trial: the stage's update of every interior zone with the high-order
+// fluxes fx, then its inversion and floors; a zone whose trial inversion fails
+// or whose trial result a floor or ceiling would change is flagged
+// (flag[cell] = 1). Returns the number flagged.
+template <class R>
+long fofc_trial(const Grid& gr, const R* U0, const R* Pin, const R& gam, double cdt, const FluxesT<R>& fx,
+                char* flag) {
+  const GridInfo& g = gr.g;
+  const double dx[3] = {g.dx1, g.dx2, g.dx3};
+  long nflag = 0;
+#pragma omp parallel for collapse(2) schedule(static) reduction(+ : nflag)
+  for (int k = gr.s3(); k < gr.e3(); ++k)
+    for (int j = gr.s2(); j < gr.e2(); ++j)
+      for (int i = gr.s1(); i < gr.e1(); ++i) {
+        const Geo& G = gr.G(LOC_CENT, j, i);
+        R P[NVAR], S[NVAR], U[NVAR];
+        for (int v = 0; v < NVAR; ++v) P[v] = Pin[gr.idx(v, k, j, i)];
+        source_terms<R>(P, G, gr.C(j, i), gam, S);
+        for (int v = 0; v < NVAR; ++v) {
+          R div(0.0);
+          for (int d = 0; d < g.ndim; ++d) {
+            int o1 = d == 0, o2 = d == 1, o3 = d == 2;
+            div += (fx.F[d][gr.idx(v, k + o3, j + o2, i + o1)] - fx.F[d][gr.idx(v, k, j, i)]) / dx[d];
+          }
+          U[v] = U0[gr.idx(v, k, j, i)] + cdt * (-div + S[v]);
+        }
+        int f = invert_point(U, G, gam, P);
+        if (f == 0) f = floors_point(gr.c, G, radius_at(gr, j, i), P);
+        if (f) {
+          flag[gr.idx(0, k, j, i)] = 1;
+          ++nflag;
+        }
+      }
+  return nflag;
+}
+
+// The flags' ghost zones follow the ghost map of the state: periodic images
+// and outflow and polar copies carry the flag of the interior zone they copy
+// (so a face and its periodic image, or an edge's transverse ghost faces, are
+// corrected alike); Dirichlet ghosts are not evolved and stay unflagged.
+void fill_flag_ghosts(const Grid& gr, char* flag) {
+  const GridInfo& g = gr.g;
+  const int ng = g.ng;
+  auto src_of = [&](int bc, int side, int ig, int n) {
+    if (bc == BC_PERIODIC) return side == 0 ? ig + n : ig - n;
+    if (bc == BC_OUTFLOW) return side == 0 ? ng : ng + n - 1;
+    if (bc == BC_DIRICHLET) return -1;
+    return side == 0 ? 2 * ng - 1 - ig : 2 * (ng + n) - 1 - ig;  // polar mirror
+  };
+  for (int k = gr.s3(); k < gr.e3(); ++k)
+    for (int j = gr.s2(); j < gr.e2(); ++j)
+      for (int m = 0; m < ng; ++m)
+        for (int side = 0; side < 2; ++side) {
+          const int ig = side == 0 ? ng - 1 - m : ng + g.n1 + m;
+          const int src = src_of(gr.c.bc[side], side, ig, g.n1);
+          flag[gr.idx(0, k, j, ig)] = src < 0 ? 0 : flag[gr.idx(0, k, j, src)];
+        }
+  for (int k = gr.s3(); k < gr.e3(); ++k)
+    for (int i = 0; i < g.N1; ++i)
+      for (int m = 0; m < ng; ++m)
+        for (int side = 0; side < 2; ++side) {
+          const int jg = side == 0 ? ng - 1 - m : ng + g.n2 + m;
+          const int src = src_of(gr.c.bc[2 + side], side, jg, g.n2);
+          flag[gr.idx(0, k, jg, i)] = src < 0 ? 0 : flag[gr.idx(0, k, src, i)];
+        }
+  if (g.ndim == 3)
+    for (int j = 0; j < g.N2; ++j)
+      for (int i = 0; i < g.N1; ++i)
+        for (int m = 0; m < ng; ++m)
+          for (int side = 0; side < 2; ++side) {
+            const int kg = side == 0 ? ng - 1 - m : ng + g.n3 + m;
+            const int src = src_of(gr.c.bc[4 + side], side, kg, g.n3);
+            flag[gr.idx(0, kg, j, i)] = src < 0 ? 0 : flag[gr.idx(0, src, j, i)];
+          }
+}
+
+// The correction: every face of a flagged zone takes the LLF flux of the
+// donor-cell (piecewise constant) states of its two cells in place of the raw
+// high-order flux, and polar zeroing and Flux-CT are applied again to the
+// corrected raw fluxes (so divB stays as Flux-CT keeps it). raw: the
+// high-order raw fluxes; on return fx holds the corrected fluxes. Returns the
+// number of flagged zones.
+template <class R>
+long fofc_correct(const Grid& gr, const R* U0, const R* Pin, const R& gam, double cdt, FluxesT<R>& raw,
+                  FluxesT<R>& fx) {
+  const GridInfo& g = gr.g;
+  std::vector<char> flag(gr.cells(), 0);
+  const long nflag = fofc_trial(gr, U0, Pin, gam, cdt, fx, flag.data());
+  if (nflag == 0) return 0;
+  fill_flag_ghosts(gr, flag.data());
+  for (int d = 0; d < g.ndim; ++d) {
+    int lo[3], hi[3];
+    face_range(gr, d, lo, hi);
+    const int loc = LOC_FACE1 + d;
+    const int o1 = d == 0, o2 = d == 1, o3 = d == 2;
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int k = lo[2]; k <= hi[2]; ++k)
+      for (int j = lo[1]; j <= hi[1]; ++j)
+        for (int i = lo[0]; i <= hi[0]; ++i) {
+          if (!flag[gr.idx(0, k, j, i)] && !flag[gr.idx(0, k - o3, j - o2, i - o1)]) continue;
+          R PL[NVAR], PR[NVAR], F[NVAR], ct;
+          for (int v = 0; v < NVAR; ++v) {
+            PL[v] = Pin[gr.idx(v, k - o3, j - o2, i - o1)];
+            PR[v] = Pin[gr.idx(v, k, j, i)];
+          }
+          llf_flux<R>(PL, PR, gr.G(loc, j, i), gam, d + 1, F, ct);
+          for (int v = 0; v < NVAR; ++v) raw.F[d][gr.idx(v, k, j, i)] = F[v];
+          raw.ctop[d][gr.idx(0, k, j, i)] = val(ct);
+        }
+  }
+  fx = raw;
+  finish_fluxes(gr, fx);
+  return nflag;
+}
 
 // One stage: Pin (ghosts filled) -> fluxes -> Uout = U0 + cdt (-div F + S(Pin))
 // -> inversion (guess Pin) -> floors -> fixup. Writes Pout (interior) and Uout
@@ -443,7 +577,15 @@ template <class R>
 void stage(const Grid& gr, const R* U0, const R* Pin, const R& gam, double cdt, R* Uout, R* Pout,
            FluxesT<R>& fx, StageStats& st, std::vector<int>* pflag_out, std::vector<int>* fflag_out = nullptr) {
   const GridInfo& g = gr.g;
-  compute_fluxes(gr, Pin, fx, gam);
+  if (gr.c.fofc) {
+    FluxesT<R> raw;
+    compute_raw(gr, Pin, raw, gam);
+    fx = raw;
+    finish_fluxes(gr, fx);
+    st.nfofc += fofc_correct(gr, U0, Pin, gam, cdt, raw, fx);
+  } else {
+    compute_fluxes(gr, Pin, fx, gam);
+  }
   std::vector<int> pflag(gr.cells(), 0), fflag(gr.cells(), 0);
   const double dx[3] = {g.dx1, g.dx2, g.dx3};
 #pragma omp parallel for collapse(2) schedule(static)
@@ -712,13 +854,15 @@ void or_stage(const or_params* c, const double* U0, const double* Pin, double cd
     stats[0] = st.nfail;
     stats[1] = st.nfloor;
     stats[2] = st.nunfixed;
+    stats[3] = st.nfofc;
   }
 }
 
 // One full two-stage step (conserved-synchronised). U (interior) is advanced in
 // place; P holds P^n on entry (the stage-1 input and inversion guess) and
-// P^{n+1} in the interior on exit. stats[0..2] = failed inversions, floored
-// zones, unfixed zones (summed over both stages). Returns the next CFL dt.
+// P^{n+1} in the interior on exit. stats[0..3] = failed inversions, floored
+// zones, unfixed zones, zones flagged by the first-order flux correction
+// (summed over both stages). Returns the next CFL dt.
 double or_step(const or_params* c, double* U, double* P, double dt, const double* dir_lo, const double* dir_hi,
                long* stats) {
   Grid gr;
@@ -749,8 +893,23 @@ double or_step(const or_params* c, double* U, double* P, double dt, const double
     stats[0] = st.nfail;
     stats[1] = st.nfloor;
     stats[2] = st.nunfixed;
+    stats[3] = st.nfofc;
   }
   return dtn;
+}
+
+// The zones the first-order flux correction flags in one stage from the
+// ghost-filled stage input Pin and U0 (cdt = c dt): flags [N3][N2][N1], 1 for
+// a flagged interior zone. Returns their number.
+long or_fofc_flags(const or_params* c, const double* U0, const double* Pin, double cdt, int* flags) {
+  Grid gr;
+  build_grid(*c, gr);
+  Fluxes fx;
+  compute_fluxes(gr, Pin, fx, c->gam);
+  std::vector<char> flag(gr.cells(), 0);
+  const long n = fofc_trial(gr, U0, Pin, c->gam, cdt, fx, flag.data());
+  for (size_t q = 0; q < gr.cells(); ++q) flags[q] = flag[q];
+  return n;
 }
 
 // Tangent of one step (forward-mode dual numbers through the same stages):
@@ -807,6 +966,7 @@ double or_step_jvp(const or_params* c, double* U, double* P, double* dU, double*
     stats[0] = st.nfail;
     stats[1] = st.nfloor;
     stats[2] = st.nunfixed;
+    stats[3] = st.nfofc;
   }
   return dtn;
 }
@@ -819,21 +979,21 @@ double or_evolve(const or_params* c, double* U, double* P, int nsteps, double dt
                  const double* dir_hi, long* stats) {
   double t = 0.0;
   double dtc = dt > 0.0 ? dt : -dt;
-  long acc[3] = {0, 0, 0};
+  long acc[4] = {0, 0, 0, 0};
   for (int s = 0; s < nsteps || (t_end > 0.0 && nsteps <= 0); ++s) {
     double step_dt = dtc;
     if (t_end > 0.0) {
       if (t >= t_end * (1.0 - 1e-14)) break;
       if (t + step_dt > t_end) step_dt = t_end - t;
     }
-    long st[3];
+    long st[4];
     double next = or_step(c, U, P, step_dt, dir_lo, dir_hi, st);
-    for (int q = 0; q < 3; ++q) acc[q] += st[q];
+    for (int q = 0; q < 4; ++q) acc[q] += st[q];
     t += step_dt;
     if (dt <= 0.0) dtc = next;
   }
   if (stats)
-    for (int q = 0; q < 3; ++q) stats[q] = acc[q];
+    for (int q = 0; q < 4; ++q) stats[q] = acc[q];
   return t;
 }
 

@@ -32,7 +32,7 @@ namespace oracle {
 enum { RHO = 0, UU = 1, U1 = 2, U2 = 3, U3 = 4, B1 = 5, B2 = 6, B3 = 7, NVAR = 8 };
 enum { MINKOWSKI = 0, KS = 1, MKS = 2, FMKS = 3 };
 enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_POLAR = 2, BC_DIRICHLET = 3 };
-enum { RECON_MC = 0, RECON_WENO5 = 1 };
+enum { RECON_MC = 0, RECON_WENO5 = 1, RECON_DONOR = 2 };
 enum { LOC_CENT = 0, LOC_FACE1 = 1, LOC_FACE2 = 2, LOC_FACE3 = 3, LOC_CORN = 4 };
 
 // Problem parameters (plain C layout, filled from Python through ctypes).
@@ -40,7 +40,7 @@ struct Params {
   int kind;            // MINKOWSKI | KS | MKS | FMKS
   int n1, n2, n3;      // interior zones; n3 == 1 means a 2-D (x1,x2) problem
   int ng;              // ghost zones in each active direction
-  int recon;           // RECON_MC | RECON_WENO5
+  int recon;           // RECON_MC | RECON_WENO5 | RECON_DONOR (first order)
   int bc[6];           // x1 inner, x1 outer, x2 inner, x2 outer, x3 inner, x3 outer
   double a;            // black-hole spin (M = 1)
   double gam;          // adiabatic index of the ideal-gas EOS p = (gam-1) u
@@ -53,6 +53,7 @@ struct Params {
   double u_rho_max;               // temperature ceiling u/rho
   double gamma_max;               // Lorentz-factor ceiling
   double x1ref;                   // FMKS blending reference: the x1 start of the whole domain
+  int fofc;                       // first-order flux correction (see stage())
 };
 
 // Geometry of one point.
@@ -467,7 +468,10 @@ R weno5_upper(const R x[5]) {
 // lo = value at its lower face, hi = value at its upper face.
 template <class R>
 void recon_cell(int recon, const R q[5], R& lo, R& hi) {
-  if (recon == RECON_MC) {
+  if (recon == RECON_DONOR) {  // piecewise constant
+    lo = q[2];
+    hi = q[2];
+  } else if (recon == RECON_MC) {
     R s = mc_slope(q[1], q[2], q[3]);
     lo = q[2] - 0.5 * s;
     hi = q[2] + 0.5 * s;
