@@ -66,6 +66,14 @@ typedef struct {
   double gamma_max;       /* Lorentz-factor ceiling */
   int newton_max_iter;    /* inversion iteration cap (<= 0: 30) */
   double newton_tol;      /* inversion tolerance on |dW/W| + |dv^2| (<= 0: 1e-14) */
+  int fofc;               /* 1: first-order flux correction ("Algorithm" section, after
+                             Beckwith & Stone 2011): each stage first runs a trial
+                             update with its high-order fluxes; every face of a zone
+                             whose trial inversion fails or whose floors act takes the
+                             donor-cell (first-order) LLF flux, and polar zeroing and
+                             Flux-CT are applied again before the stage's update. The
+                             flags' ghost zones follow the state's ghost map (Dirichlet
+                             ghosts unflagged). 0: off. Single-grid contexts only. */
 } kh_coords;
 
 /* Counters of the last kh_step (both stages summed). */
@@ -75,6 +83,7 @@ typedef struct {
   int64_t nunfixed; /* failed zones with no good neighbour (kept the stage input) */
   double dt_cfl;    /* CFL time step for the next step */
   int64_t nfp64;    /* KH_MIXED: zones whose inversion fell back to the FP64 Newton iteration */
+  int64_t nfofc;    /* zones flagged by the first-order flux correction's trials */
 } kh_stats;
 
 typedef struct kh_ctx kh_ctx;
@@ -140,7 +149,8 @@ int kh_divb(kh_ctx* ctx, const double* B, double* max_abs, double* l1);
 /* Diagnostics: the fluxes kh_step uses, from (P, B) with ghosts filled by the
  * caller: F1, F2, F3 (device, [8][n3s][n2s][n1s], the flux through the lower
  * face of each cell, after polar zeroing and Flux-CT; F3 unused when
- * n3 == 1). Entries outside the computed face ranges are left untouched. */
+ * n3 == 1; the first-order flux correction, which needs a trial update, is
+ * not applied). Entries outside the computed face ranges are left untouched. */
 int kh_fluxes(kh_ctx* ctx, const double* P, const double* B, double* F1, double* F2, double* F3);
 
 /* Ghost fill of (P, B) in place with the context's boundary rules. */
@@ -181,7 +191,9 @@ enum {
   KH_T_UPDATE = 5, /* sources + update + inversion + floors */
   KH_T_FIXUP = 6,  /* neighbour-average repair of failed zones */
   KH_T_CFL = 7,    /* CFL reduction (2 kernels) */
-  KH_NTIMERS = 8
+  KH_T_FOFC = 8,   /* first-order flux correction: trial, flag ghosts, donor-cell
+                      faces and the second Flux-CT (kh_coords.fofc) */
+  KH_NTIMERS = 9
 };
 /* enable != 0: record CUDA events on the context stream around each group of
  * every later kh_step (each step then synchronises its stream) and reset the
@@ -207,8 +219,8 @@ int64_t kh_launch_count(const kh_ctx* ctx);
  * stage states, then reversed (see the reverse rules below). All arrays are
  * device pointers in the kh_shape layout; the call synchronises the context
  * stream. Scratch (~83 planes of doubles) is allocated on the first call and
- * kept until kh_destroy. KH_EINVAL for a mixed-precision context or bad
- * arguments.
+ * kept until kh_destroy. KH_EINVAL for a mixed-precision context, a
+ * context with the first-order flux correction on, or bad arguments.
  *
  * Reverse rules (NS pattern 3): limiter and max branches as taken by the
  * forward (ties: the first argument), LLF with ctop differentiated through

@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libkharma_gb300.so")
 SOURCES = ["kh_kernels.cu", "kh_api.cu", "kh_noalloc.cu", "kh_mesh.cu", "kh_adjoint.cu", "kh_flux_tma.cu"]
 HEADERS = ["kh_internal.h", "kh_physics.cuh", "kh_geom_math.h", "kh_zone.cuh", "kh_ctx.h", "kh_dual.cuh", "kh_df64.cuh",
-           "kh_mixed.cuh", "kh_face_vjp.cuh"]
+           "kh_mixed.cuh", "kh_face_vjp.cuh", "kh_pair.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -81,7 +81,8 @@ void free_all(kh_ctx* x) {
                   x->ctop[2], x->emf[0], x->emf[1], x->emf[2], x->pflag, x->partial, x->dscalar,
                   x->counters, x->dirichlet[0], x->dirichlet[1], x->geof, x->dgmf, x->pstarf, x->pnf, x->Ff[0],
                   x->Ff[1], x->Ff[2], x->ctopf[0], x->ctopf[1], x->ctopf[2], x->emff[0], x->emff[1],
-                  x->emff[2], x->dirichletf[0], x->dirichletf[1], x->adj, x->adj_i8, x->adj_red, x->geodf, x->flist};
+                  x->emff[2], x->dirichletf[0], x->dirichletf[1], x->adj, x->adj_i8, x->adj_red, x->geodf, x->flist,
+                  x->fflag, x->fsave};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -102,9 +103,30 @@ int run_stage(kh_ctx* x, int st, const double* U0, const Vars& Pin, const Vars& 
     n += launch_flux_dir<double, double>(d, cview(Pin), L, G, x->S, x->F[d - 1], x->ctop[d - 1], x->tpb_flux, s);
     mark(x, KH_T_FLUX1 + d - 1, st, 1);
   }
+  const size_t b3 = 3 * (size_t)L.plane * sizeof(double);
+  if (x->S.fofc) {
+    // Flux-CT overwrites the raw field fluxes; the correction needs them again
+    for (int d = 0; d < L.ndim; ++d)
+      cudaMemcpyAsync(x->fsave + 3 * d * L.plane, x->F[d] + V_B1 * L.plane, b3, cudaMemcpyDeviceToDevice, s);
+  }
   mark(x, KH_T_CT, st, 0);
   n += launch_ct<double>(x->F, x->emf, L, s);
   mark(x, KH_T_CT, st, 1);
+  if (x->S.fofc) {
+    // first-order flux correction: trial update with the high-order fluxes,
+    // donor-cell fluxes on the faces of the flagged zones, Flux-CT again
+    mark(x, KH_T_FOFC, st, 0);
+    n += launch_fofc_trial(U0, cview(Pin), x->F, L, G, x->S, x->dscalar + 3, coef, x->fflag, x->counters,
+                           x->tpb_update, s);
+    n += launch_flag_ghosts(x->fflag, L, x->S, s);
+    for (int d = 0; d < L.ndim; ++d)
+      cudaMemcpyAsync(x->F[d] + V_B1 * L.plane, x->fsave + 3 * d * L.plane, b3, cudaMemcpyDeviceToDevice, s);
+    for (int d = 1; d <= L.ndim; ++d)
+      n += launch_fofc_faces<double, double>(d, cview(Pin), L, G, x->S, x->fflag, x->F[d - 1], x->ctop[d - 1],
+                                             x->tpb_flux, s);
+    n += launch_ct<double>(x->F, x->emf, L, s);
+    mark(x, KH_T_FOFC, st, 1);
+  }
   mark(x, KH_T_UPDATE, st, 0);
   const FailList fl{x->flist, x->counters + CNT_LIST0 + st};
   n += launch_update(U0, cview(Pin), Pout, Uout, x->F, L, G, x->S, x->dscalar + 3, coef, x->pflag, x->counters,
@@ -193,6 +215,8 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
   if (c->n1 < 4 || c->n2 < 4 || c->n3 < 1) return KH_EINVAL;
   if (c->recon != KH_RECON_MC && c->recon != KH_RECON_WENO5) return KH_EINVAL;
   if (c->precision != KH_FP64 && c->precision != KH_MIXED) return KH_EINVAL;
+  if (c->fofc != 0 && c->fofc != 1) return KH_EINVAL;
+  if (c->fofc && c->precision != KH_FP64) return KH_EINVAL;
   if (!(gamma > 1.0) || !(c->cfl > 0.0) || !(fabs(a) < 1.0)) return KH_EINVAL;
   if (!(c->x1max > c->x1min) || !(c->x2max > c->x2min) || !(c->x3max > c->x3min)) return KH_EINVAL;
   for (int q = 0; q < 6; ++q) {
@@ -248,6 +272,7 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
   S.gfac = (gamma - 1.0) / gamma;
   S.cfl = c->cfl;
   S.recon = c->recon;
+  S.fofc = c->fofc;
   for (int q = 0; q < 6; ++q) S.bc[q] = c->bc[q];
   S.fl.rho_min = c->rho_min;
   S.fl.u_min = c->u_min;
@@ -308,6 +333,10 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
         KH_ALLOC(x->dirichletf[f], (size_t)NV * L.n3s * L.n2s * L.ng * sizeof(float));
   }
   KH_ALLOC(x->pflag, (size_t)L.plane);
+  if (c->fofc) {
+    KH_ALLOC(x->fflag, (size_t)L.plane);
+    KH_ALLOC(x->fsave, 3 * (size_t)L.ndim * pl);
+  }
   KH_ALLOC(x->flist, (size_t)L.n1 * L.n2 * L.n3 * sizeof(unsigned));
   KH_ALLOC(x->partial, 2 * (size_t)x->npartial * sizeof(double));
   KH_ALLOC(x->dscalar, 4 * sizeof(double));
@@ -671,6 +700,7 @@ int kh_get_stats(kh_ctx* x, kh_stats* out) {
   out->nfloor = (int64_t)h[CNT_FLOOR];
   out->nunfixed = (int64_t)h[CNT_UNFIXED];
   out->nfp64 = (int64_t)h[CNT_FP64];
+  out->nfofc = (int64_t)h[CNT_FOFC];
   out->dt_cfl = dt;
   x->last = *out;
   return h[CNT_TIMEOUT] ? KH_ETIMEOUT : KH_OK;

@@ -10,6 +10,9 @@
 namespace kh {
 
 constexpr int NGHOST = 3;
+// Piecewise-constant (donor-cell) reconstruction: the first-order fluxes of
+// the flux correction (not a user-selectable scheme)
+constexpr int RECON_DONOR = 2;
 constexpr int NGEO = 22;  // per location: gcov (10 symmetric), gcon (10), gdet, alpha
 constexpr int NDG = 20;  // d_1 g_{mn}, d_2 g_{mn}: 2 x 10 symmetric pairs (cell centres)
 enum { LOC_CENT = 0, LOC_F1 = 1, LOC_F2 = 2 };
@@ -52,6 +55,7 @@ struct Scheme {
   double gfac;  // (gam - 1) / gam
   double cfl;
   int recon;
+  int fofc;  // first-order flux correction on
   int bc[6];
   FloorParams fl;
   C2POpts c2p;
@@ -64,8 +68,9 @@ inline void set_mixed(Scheme& S) { S.mx = mixed_consts(S.gam, S.fl); }
 // Counters kept on the device for one step.
 // CNT_FP64: zones of the mixed update whose inversion fell back to FP64;
 // CNT_LIST0/1: lengths of the failed-zone lists of stages 1 and 2
+// CNT_FOFC: zones flagged by the first-order flux correction's trials
 enum { CNT_FAIL = 0, CNT_FLOOR = 1, CNT_UNFIXED = 2, CNT_TIMEOUT = 3, CNT_FP64 = 4, CNT_LIST0 = 5, CNT_LIST1 = 6,
-       NCNT = 7 };
+       CNT_FOFC = 7, NCNT = 8 };
 
 // Cells (L.at index) whose inversion failed in one stage, appended by the
 // update (idx == nullptr: not recorded); the fixup then visits these only.
@@ -104,6 +109,19 @@ template <class TIN, class R>
 int launch_flux_dir(int D, const CVarsT<TIN>& P, const Layout& L, const GeomT<R>& G, const Scheme& S, R* F, R* ctop,
                     int tpb, cudaStream_t s);
 template <class R> int launch_ct(R* const F[3], R* const emf[3], const Layout& L, cudaStream_t s);
+// First-order flux correction (after Beckwith & Stone 2011). The trial: the
+// FP64 update of every interior zone with the post-CT fluxes, writing only
+// flag[c] (1: inversion failed or a floor acted); then the flags' ghost
+// cells by the ghost map of the state (Dirichlet ghosts 0).
+int launch_fofc_trial(const double* U0, const CVars& Pin, double* const F[3], const Layout& L, const DevGeom& G,
+                      const Scheme& S, const double* dtp, double coef, int8_t* flag, unsigned long long* cnt,
+                      int tpb, cudaStream_t s);
+int launch_flag_ghosts(int8_t* flag, const Layout& L, const Scheme& S, cudaStream_t s);
+// Donor-cell LLF fluxes (with polar zeroing) through every x^D face of the
+// flux pass's face box that borders a flagged cell, over the raw fluxes.
+template <class TIN, class R>
+int launch_fofc_faces(int D, const CVarsT<TIN>& P, const Layout& L, const GeomT<R>& G, const Scheme& S,
+                      const int8_t* flag, R* F, R* ctop, int tpb, cudaStream_t s);
 // The update reads its time increment as coef * dtp[0] (device memory), so a
 // captured step keeps working when dt changes.
 int launch_update(const double* U0, const CVars& Pin, const Vars& Pout, double* Uout, double* const F[3],

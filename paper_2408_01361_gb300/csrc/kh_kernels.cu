@@ -74,14 +74,19 @@ __global__ void k_geometry(CoordParams cp, double x1o, double x2o, FloorParams f
 // does not matter. Reads interior cells of src only and writes ghost cells of
 // dst, so src == dst is allowed. Ghost cells are enumerated in three slabs:
 // x1 ghosts of interior (j, k), x2 ghosts of interior k, x3 ghosts.
-template <class TS, class TD>
-__global__ void k_bc_fill(CVarsT<TS> src, VarsT<TD> dst, Layout L, Scheme S, const TS* dlo, const TS* dhi) {
+
+// Number of ghost cells in the three slabs.
+__device__ __forceinline__ long long ghost_total(const Layout& L) {
   const long long nj = L.e[1] - L.s[1], nk = L.e[2] - L.s[2];
   const long long T1 = nj * nk * L.ng * 2, T2 = (long long)L.N1 * nk * L.ng * 2;
   const long long T3 = L.ndim == 3 ? (long long)L.N1 * L.N2 * L.ng3 * 2 : 0;
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= T1 + T2 + T3) return;
-  int i, j, k;
+  return T1 + T2 + T3;
+}
+
+// Ghost cell number t (< ghost_total) -> (i, j, k).
+__device__ __forceinline__ void ghost_cell(const Layout& L, long long t, int& i, int& j, int& k) {
+  const long long nj = L.e[1] - L.s[1], nk = L.e[2] - L.s[2];
+  const long long T1 = nj * nk * L.ng * 2, T2 = (long long)L.N1 * nk * L.ng * 2;
   if (t < T1) {
     const int side = (int)(t % 2), m = (int)((t / 2) % L.ng);
     j = L.s[1] + (int)((t / (2 * L.ng)) % nj);
@@ -100,37 +105,59 @@ __global__ void k_bc_fill(CVarsT<TS> src, VarsT<TD> dst, Layout L, Scheme S, con
     const int side = (int)((u / ((long long)L.N1 * L.N2)) % 2), m = (int)(u / (2LL * L.N1 * L.N2));
     k = side == 0 ? L.ng3 - 1 - m : L.ng3 + L.n3 + m;
   }
-  // x3, x2, x1 maps to the source cell
-  int ks = k, js = j, is = i;
+}
+
+// The composed ghost map of cell (i, j, k): its source cell (is, js, ks), or
+// for dir != 0 (1: inner, 2: outer x1 Dirichlet face) the index (ks, js, is)
+// into that face's ghost data; flip: u~2 and B2 change sign (polar x2 face);
+// clamp 1: u~1 <= 0 (inner x1 outflow), 2: u~1 >= 0 (outer).
+struct GhostSrc {
+  int i, j, k;
+  int dir, clamp;
+  bool flip;
+};
+
+__device__ __forceinline__ GhostSrc ghost_source(const Layout& L, const Scheme& S, int i, int j, int k) {
+  GhostSrc g{i, j, k, 0, 0, false};
   if (L.ndim == 3 && (k < L.s[2] || k >= L.e[2])) {
     const int side = k < L.s[2] ? 0 : 1;
-    if (S.bc[4 + side] == KH_BC_PERIODIC) ks = side == 0 ? k + L.n3 : k - L.n3;
-    else ks = side == 0 ? L.s[2] : L.e[2] - 1;
+    if (S.bc[4 + side] == KH_BC_PERIODIC) g.k = side == 0 ? k + L.n3 : k - L.n3;
+    else g.k = side == 0 ? L.s[2] : L.e[2] - 1;
   }
-  bool flip = false;
   if (j < L.s[1] || j >= L.e[1]) {
     const int side = j < L.s[1] ? 0 : 1, bc = S.bc[2 + side];
-    if (bc == KH_BC_PERIODIC) js = side == 0 ? j + L.n2 : j - L.n2;
-    else if (bc == KH_BC_OUTFLOW) js = side == 0 ? L.ng : L.ng + L.n2 - 1;
-    else js = side == 0 ? 2 * L.ng - 1 - j : 2 * (L.ng + L.n2) - 1 - j;
-    flip = bc == KH_BC_POLAR;
+    if (bc == KH_BC_PERIODIC) g.j = side == 0 ? j + L.n2 : j - L.n2;
+    else if (bc == KH_BC_OUTFLOW) g.j = side == 0 ? L.ng : L.ng + L.n2 - 1;
+    else g.j = side == 0 ? 2 * L.ng - 1 - j : 2 * (L.ng + L.n2) - 1 - j;
+    g.flip = bc == KH_BC_POLAR;
   }
-  int clamp = 0;  // 1: u~1 <= 0 (inner x1 outflow), 2: u~1 >= 0 (outer)
-  const TS* D = nullptr;
   if (i < L.s[0] || i >= L.e[0]) {
     const int side = i < L.s[0] ? 0 : 1, bc = S.bc[side];
     if (bc == KH_BC_DIRICHLET) {
-      D = side == 0 ? dlo : dhi;
-      is = side == 0 ? i : i - (L.ng + L.n1);  // index into the ghost data
+      g.dir = side + 1;
+      g.i = side == 0 ? i : i - (L.ng + L.n1);  // index into the ghost data
     } else if (bc == KH_BC_PERIODIC) {
-      is = side == 0 ? i + L.n1 : i - L.n1;
+      g.i = side == 0 ? i + L.n1 : i - L.n1;
     } else if (bc == KH_BC_OUTFLOW) {
-      is = side == 0 ? L.ng : L.ng + L.n1 - 1;
-      clamp = side + 1;
+      g.i = side == 0 ? L.ng : L.ng + L.n1 - 1;
+      g.clamp = side + 1;
     } else {
-      is = side == 0 ? 2 * L.ng - 1 - i : 2 * (L.ng + L.n1) - 1 - i;
+      g.i = side == 0 ? 2 * L.ng - 1 - i : 2 * (L.ng + L.n1) - 1 - i;
     }
   }
+  return g;
+}
+
+template <class TS, class TD>
+__global__ void k_bc_fill(CVarsT<TS> src, VarsT<TD> dst, Layout L, Scheme S, const TS* dlo, const TS* dhi) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= ghost_total(L)) return;
+  int i, j, k;
+  ghost_cell(L, t, i, j, k);
+  const GhostSrc g = ghost_source(L, S, i, j, k);
+  const int ks = g.k, js = g.j, is = g.i, clamp = g.clamp;
+  const bool flip = g.flip;
+  const TS* D = g.dir == 1 ? dlo : (g.dir == 2 ? dhi : nullptr);
   const long long d = L.at(k, j, i), sc = D ? 0 : L.at(ks, js, is);
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
@@ -234,6 +261,52 @@ __global__ void __launch_bounds__(TPB) k_fixup_list(VarsT<T> P, double* Uout, co
     const int k = (int)(c / gs), j = (int)((c % gs) / L.n1s), i = (int)(c % L.n1s);
     fixup_zone<T>(P, Uout, pflag, L, G, S, cnt, i, j, k);
   }
+}
+
+// ---------------------------------------------------------------------------
+// First-order flux correction (the paper's "Algorithm" section, after
+// Beckwith & Stone 2011): trial flags, their ghosts, donor-cell face fluxes.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(TPB_MAX) k_fofc_trial(const double* U0, CVars Pin, const double* F1,
+                                                       const double* F2, const double* F3, Layout L, DevGeom G,
+                                                       Scheme S, const double* dtp, double coef, int8_t* flag,
+                                                       unsigned long long* cnt) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nzones(L)) return;
+  int i, j, k;
+  zone_ijk(L, t, i, j, k);
+  update_zone<true>(U0, Pin, Vars{}, nullptr, F1, F2, F3, L, G, S, coef * __ldg(dtp), flag, cnt, i, j, k);
+}
+
+// Ghost flags follow the state's ghost map: a periodic image or an outflow or
+// polar copy carries its source zone's flag; Dirichlet ghosts are not evolved.
+__global__ void k_flag_ghosts(int8_t* flag, Layout L, Scheme S) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= ghost_total(L)) return;
+  int i, j, k;
+  ghost_cell(L, t, i, j, k);
+  const GhostSrc g = ghost_source(L, S, i, j, k);
+  flag[L.at(k, j, i)] = g.dir ? 0 : flag[L.at(g.k, g.j, g.i)];
+}
+
+// The raw flux of every face of the box that borders a flagged cell becomes
+// the LLF flux of the two cells' own (donor-cell) states.
+template <int D, class TIN, class R>
+__global__ void __launch_bounds__(TPB_MAX) k_fofc_faces(CVarsT<TIN> P, Layout L, GeomT<R> G, Scheme S, FaceBox box,
+                                                       const int8_t* flag, R* F, R* ctop, int polar_lo,
+                                                       int polar_hi) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned tot = (unsigned)box.n[0] * box.n[1] * box.n[2];
+  if (t >= tot) return;
+  int i, j, k;
+  split3(t, box.n[0], box.n[1], i, j, k);
+  i += box.lo[0];
+  j += box.lo[1];
+  k += box.lo[2];
+  const long long c = L.at(k, j, i);
+  const long long st = (D == 1) ? 1 : (D == 2 ? (long long)L.n1s : (long long)L.n1s * L.n2s);
+  if (!(flag[c] | flag[c - st])) return;
+  flux_face<D, RECON_DONOR, TIN, R>(P, L, G, S, i, j, k, F, ctop, polar_lo, polar_hi);
 }
 
 // ---------------------------------------------------------------------------
@@ -444,6 +517,44 @@ template int launch_flux_dir<double, float>(int, const CVarsT<double>&, const La
                                             const Scheme&, float*, float*, int, cudaStream_t);
 template int launch_flux_dir<float, float>(int, const CVarsT<float>&, const Layout&, const GeomT<float>&,
                                            const Scheme&, float*, float*, int, cudaStream_t);
+
+int launch_fofc_trial(const double* U0, const CVars& Pin, double* const F[3], const Layout& L, const DevGeom& G,
+                      const Scheme& S, const double* dtp, double coef, int8_t* flag, unsigned long long* cnt,
+                      int tpb, cudaStream_t s) {
+  const long long nz = (long long)L.n1 * L.n2 * L.n3;
+  k_fofc_trial<<<nblocks(nz, tpb), tpb, 0, s>>>(U0, Pin, F[0], F[1], F[2], L, G, S, dtp, coef, flag, cnt);
+  return 1;
+}
+
+int launch_flag_ghosts(int8_t* flag, const Layout& L, const Scheme& S, cudaStream_t s) {
+  const long long nj = L.e[1] - L.s[1], nk = L.e[2] - L.s[2];
+  const long long tot = nj * nk * L.ng * 2 + (long long)L.N1 * nk * L.ng * 2 +
+                        (L.ndim == 3 ? (long long)L.N1 * L.N2 * L.ng3 * 2 : 0);
+  k_flag_ghosts<<<nblocks(tot, TPB), TPB, 0, s>>>(flag, L, S);
+  return 1;
+}
+
+template <int D, class TIN, class R>
+static int launch_fofc_d(const CVarsT<TIN>& P, const Layout& L, const GeomT<R>& G, const Scheme& S,
+                         const int8_t* flag, R* F, R* ctop, int tpb, cudaStream_t s) {
+  const FaceBox b = face_box(L, D);
+  const long long tot = (long long)b.n[0] * b.n[1] * b.n[2];
+  const int plo = S.bc[2] == KH_BC_POLAR, phi = S.bc[3] == KH_BC_POLAR;
+  k_fofc_faces<D, TIN, R><<<nblocks(tot, tpb), tpb, 0, s>>>(P, L, G, S, b, flag, F, ctop, plo, phi);
+  return 1;
+}
+
+template <class TIN, class R>
+int launch_fofc_faces(int D, const CVarsT<TIN>& P, const Layout& L, const GeomT<R>& G, const Scheme& S,
+                      const int8_t* flag, R* F, R* ctop, int tpb, cudaStream_t s) {
+  if (D == 1) return launch_fofc_d<1>(P, L, G, S, flag, F, ctop, tpb, s);
+  if (D == 2) return launch_fofc_d<2>(P, L, G, S, flag, F, ctop, tpb, s);
+  return launch_fofc_d<3>(P, L, G, S, flag, F, ctop, tpb, s);
+}
+template int launch_fofc_faces<double, double>(int, const CVarsT<double>&, const Layout&, const GeomT<double>&,
+                                               const Scheme&, const int8_t*, double*, double*, int, cudaStream_t);
+template int launch_fofc_faces<float, float>(int, const CVarsT<float>&, const Layout&, const GeomT<float>&,
+                                             const Scheme&, const int8_t*, float*, float*, int, cudaStream_t);
 
 template <class R> int launch_ct(R* const F[3], R* const emf[3], const Layout& L, cudaStream_t s) {
   const long long tot = (long long)(L.e[0] - L.s[0] + 1) * (L.e[1] - L.s[1] + 1) * (L.ndim == 3 ? L.e[2] - L.s[2] + 1 : 1);

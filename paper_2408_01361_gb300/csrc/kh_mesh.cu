@@ -503,6 +503,7 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
   if (c->kind < KH_MINKOWSKI || c->kind > KH_FMKS || c->n1 < 2 || c->n2 < 2 || c->n3 < 1) return KH_EINVAL;
   if (c->precision != KH_FP64 && c->precision != KH_MIXED) return KH_EINVAL;
   if (c->recon != KH_RECON_MC && c->recon != KH_RECON_WENO5) return KH_EINVAL;
+  if (c->fofc) return KH_EINVAL;  // the flux correction runs on single grids
   if (!(gamma > 1.0) || !(c->cfl > 0.0) || !(fabs(a) < 1.0)) return KH_EINVAL;
   for (int q = 0; q < 6; ++q) {
     const int b = c->bc[q];
@@ -1092,6 +1093,7 @@ int kh_mesh_get_stats(kh_mesh* x, kh_stats* out) {
   out->nfloor = (int64_t)h[CNT_FLOOR];
   out->nunfixed = (int64_t)h[CNT_UNFIXED];
   out->nfp64 = (int64_t)h[CNT_FP64];
+  out->nfofc = 0;
   out->dt_cfl = dt;
   return KH_OK;
 }

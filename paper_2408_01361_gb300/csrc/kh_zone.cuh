@@ -100,7 +100,9 @@ __device__ __forceinline__ void flux_face_pair(const CVarsT<float>& P, const Lay
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     const float* q = P.v[v] + c;
-    if (RECON == KH_RECON_MC) {
+    if (RECON == RECON_DONOR) {
+      Pp[v] = P2(__ldg(q - st), __ldg(q));
+    } else if (RECON == KH_RECON_MC) {
       const float qm2 = __ldg(q - 2 * st), qm1 = __ldg(q - st), q0 = __ldg(q), qp1 = __ldg(q + st);
       float lo, hi, l2, h2;
       recon_mc(qm2, qm1, q0, lo, hi);
@@ -142,7 +144,10 @@ __device__ __forceinline__ void flux_face(const CVarsT<TIN>& P, const Layout& L,
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     const TIN* q = P.v[v] + c;
-    if (RECON == KH_RECON_MC) {
+    if (RECON == RECON_DONOR) {  // piecewise constant: the two cells' own values
+      PL[v] = (R)__ldg(q - st);
+      PR[v] = (R)__ldg(q);
+    } else if (RECON == KH_RECON_MC) {
       const R qm2 = (R)__ldg(q - 2 * st), qm1 = (R)__ldg(q - st), q0 = (R)__ldg(q), qp1 = (R)__ldg(q + st);
       R lo, hi;
       recon_mc(qm2, qm1, q0, lo, hi);
@@ -270,6 +275,11 @@ __device__ __forceinline__ void source_terms(const R* P, const Met<M>& m, const 
 // FP64 update of interior zone (k, j, i): U = U0 + cdt (-div F + S(Pin)),
 // Noble-2D inversion with Pin as the guess, floors; writes Pout, pflag and
 // (stage 2) U.
+// TRIAL (first-order flux correction): the same update, inversion and floors,
+// but only the zone's flag is written: pflag[c] = 1 if the inversion failed or
+// a floor acted, else 0 (flagged zones counted in CNT_FOFC); Pout, Uout and
+// the failure counters are not touched.
+template <bool TRIAL = false>
 __device__ __forceinline__ void update_zone(const double* U0, const CVars& Pin, const Vars& Pout, double* Uout,
                                             const double* F1, const double* F2, const double* F3, const Layout& L,
                                             const DevGeom& G, const Scheme& S, double cdt, int8_t* pflag,
@@ -297,6 +307,11 @@ __device__ __forceinline__ void update_zone(const double* U0, const CVars& Pin, 
   for (int v = 0; v < NV; ++v) Pn[v] = P[v];
   const double ig = __ldg(G.flo + 2 * L.gplane + p);  // 1 / sqrt(-g)
   const int flag = noble2d(U, m, ig, S.gam, S.igam, S.gfac, S.c2p, Pn);
+  if (TRIAL && flag) {
+    pflag[c] = 1;
+    atomicAdd(cnt + CNT_FOFC, 1ULL);
+    return;
+  }
   Pn[V_B1] = U[V_B1] * ig;
   Pn[V_B2] = U[V_B2] * ig;
   Pn[V_B3] = U[V_B3] * ig;
@@ -309,6 +324,11 @@ __device__ __forceinline__ void update_zone(const double* U0, const CVars& Pin, 
     FState<double> s;
     fluid_state(Pn, m, s);
     fmask = apply_floors(S.fl, m, __ldg(G.flo + p), __ldg(G.flo + L.gplane + p), s.bsq, Pn);
+    if (TRIAL) {
+      pflag[c] = fmask ? 1 : 0;
+      if (fmask) atomicAdd(cnt + CNT_FOFC, 1ULL);
+      return;
+    }
     if (fmask && Uout) {
       fluid_state(Pn, m, s);
       cons_only(Pn, s, m, S.gam, U);

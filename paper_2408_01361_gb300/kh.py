@@ -41,13 +41,13 @@ class Coords(C.Structure):
         ("hslope", C.c_double), ("poly_xt", C.c_double), ("poly_alpha", C.c_double), ("mks_smooth", C.c_double),
         ("cfl", C.c_double), ("rho_min", C.c_double), ("u_min", C.c_double), ("bsq_rho_max", C.c_double),
         ("bsq_u_max", C.c_double), ("u_rho_max", C.c_double), ("gamma_max", C.c_double),
-        ("newton_max_iter", C.c_int), ("newton_tol", C.c_double),
+        ("newton_max_iter", C.c_int), ("newton_tol", C.c_double), ("fofc", C.c_int),
     ]
 
 
 class Stats(C.Structure):
     _fields_ = [("nfail", C.c_int64), ("nfloor", C.c_int64), ("nunfixed", C.c_int64), ("dt_cfl", C.c_double),
-                ("nfp64", C.c_int64)]
+                ("nfp64", C.c_int64), ("nfofc", C.c_int64)]
 
 
 class Block(C.Structure):
@@ -143,6 +143,7 @@ def coords_from_cfg(cfg: dict) -> Coords:
     c.gamma_max = fl.get("gamma_max", 1e300)
     c.newton_max_iter = cfg.get("newton_max_iter", 30)
     c.newton_tol = cfg.get("newton_tol", 1e-14)
+    c.fofc = 1 if cfg.get("fofc") else 0
     return c
 
 
@@ -294,14 +295,14 @@ class Context:
         _check(lib().kh_get_stage_flux(self._h, int(d), _ptr(F)), "kh_get_stage_flux")
         return F
 
-    TIMERS = ("bc", "flux_x1", "flux_x2", "flux_x3", "flux_ct", "update", "fixup", "cfl")
+    TIMERS = ("bc", "flux_x1", "flux_x2", "flux_x3", "flux_ct", "update", "fixup", "cfl", "fofc")
 
     def profile(self, enable: bool):
         _check(lib().kh_profile(self._h, 1 if enable else 0), "kh_profile")
 
     def profile_read(self) -> dict:
-        ms = (C.c_double * 8)()
-        n = (C.c_int64 * 8)()
+        ms = (C.c_double * len(self.TIMERS))()
+        n = (C.c_int64 * len(self.TIMERS))()
         _check(lib().kh_profile_read(self._h, ms, n), "kh_profile_read")
         return {name: (ms[q], n[q]) for q, name in enumerate(self.TIMERS)}
 
