@@ -60,6 +60,7 @@ def parse():
     p.add_argument("--no-smr", action="store_true", help="skip the statically refined torus leg")
     p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-cost leg")
     p.add_argument("--no-cube", action="store_true", help="skip the 128^3 MKS torus leg")
+    p.add_argument("--no-fofc", action="store_true", help="skip the first-order flux correction leg")
     p.add_argument("--smr-only", action="store_true", help="run only the statically refined torus leg")
     p.add_argument("--precisions", default="mixed,fp64",
                    help="comma list; the first is the headline, the others are reported beside it")
@@ -328,6 +329,49 @@ def measure_cube(args, dev, stream, precision, n=128):
     return out
 
 
+def measure_fofc(args, cfg64, P0, dev, stream, precision):
+    """The workload torus with the first-order flux correction on (trial
+    update, flag ghosts, donor-cell faces, second Flux-CT per stage): timed
+    steps with CUDA events, eager and as a CUDA graph, and the zones flagged
+    per step."""
+    import torch
+
+    from paper_2408_01361_gb300 import kh
+
+    cfg = dict(cfg64, precision=precision, fofc=True)
+    nz = cfg["n1"] * cfg["n2"] * cfg["n3"]
+    ctx = kh.Context(cfg, device=dev)
+    PB = ctx.to_device(P0)
+    P, B = ctx.split(PB)
+    U = ctx.empty(8)
+    ctx.prim_to_cons(P, B, U)
+    dt = ctx.cfl_dt(P, B)
+    ctx.autotune(U, P, B, 0.5 * dt)  # the plain step's choice (process-wide cache)
+    for _ in range(max(args.warmup, 3)):
+        dt, _ = ctx.step(U, P, B, 0.5 * dt)
+    steps = max(args.steps, 5)
+    out = {"precision": precision, "zones": nz}
+    for graph in (False, True):
+        ctx.set_graph(graph)
+        if graph:
+            dt, _ = ctx.step(U, P, B, 0.5 * dt)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(steps):
+            dt, _ = ctx.step(U, P, B, 0.5 * dt)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+        out["graph" if graph else "eager"] = {"value": nz / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms}
+    ctx.set_graph(False)
+    st = ctx.stats()
+    out["nfofc_last_step"] = int(st.nfofc)
+    out["nfloor_last_step"] = int(st.nfloor)
+    ctx.close()
+    return out
+
+
 def measure_smr(args, dev, stream, precision):
     """The statically refined torus (3 levels, 592 uneven blocks, 5.57 M zones)
     stepped as one mesh: every kernel covers all blocks, ghost zones of every
@@ -577,6 +621,12 @@ def run_kh(args, world, rank, local):
     if not args.no_cube and world == 1:
         line["torus_128cubed"] = {p: measure_cube(args, dev, stream, p) for p in args.precisions}
         line["torus_128cubed"]["context"] = "paper: ~35 M zone-cycles/s per A100 GPU on 128^3 production problems"
+    if not args.no_fofc and world == 1:
+        fo = {}
+        for p in args.precisions:
+            fo[p] = measure_fofc(args, cfg64, P0, dev, stream, p)
+            fo[p]["cost_vs_plain_graph"] = results[p]["graph"]["value"] / fo[p]["graph"]["value"]
+        line["fofc"] = fo
     if not args.no_adjoint and world == 1:
         line["adjoint"] = measure_adjoint(args, dev, stream)
     print(json.dumps(line), flush=True)

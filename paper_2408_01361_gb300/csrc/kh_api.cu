@@ -82,7 +82,7 @@ void free_all(kh_ctx* x) {
                   x->counters, x->dirichlet[0], x->dirichlet[1], x->geof, x->dgmf, x->pstarf, x->pnf, x->Ff[0],
                   x->Ff[1], x->Ff[2], x->ctopf[0], x->ctopf[1], x->ctopf[2], x->emff[0], x->emff[1],
                   x->emff[2], x->dirichletf[0], x->dirichletf[1], x->adj, x->adj_i8, x->adj_red, x->geodf, x->flist,
-                  x->fflag, x->fsave};
+                  x->fflag, x->fsave, x->fsavef};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -176,9 +176,29 @@ int run_stage_mixed(kh_ctx* x, int st, const double* U0, const VarsT<TIN>& Pin, 
     n += r;
     mark(x, KH_T_FLUX1 + d - 1, st, 1);
   }
+  const size_t b3 = 3 * (size_t)L.plane * sizeof(float);
+  if (x->S.fofc) {
+    // Flux-CT overwrites the raw field fluxes; the correction needs them again
+    for (int d = 0; d < L.ndim; ++d)
+      cudaMemcpyAsync(x->fsavef + 3 * d * L.plane, x->Ff[d] + V_B1 * L.plane, b3, cudaMemcpyDeviceToDevice, s);
+  }
   mark(x, KH_T_CT, st, 0);
   n += launch_ct<float>(x->Ff, x->emff, L, s);
   mark(x, KH_T_CT, st, 1);
+  if (x->S.fofc) {
+    // first-order flux correction (as in run_stage), FP32 fluxes
+    mark(x, KH_T_FOFC, st, 0);
+    n += launch_fofc_trial_mixed(U0, cviewT(Pf), x->Ff, L, G, Gf, x->S, x->dscalar + 3, coef, x->fflag,
+                                 x->counters, x->tpb_update, s);
+    n += launch_flag_ghosts(x->fflag, L, x->S, s);
+    for (int d = 0; d < L.ndim; ++d)
+      cudaMemcpyAsync(x->Ff[d] + V_B1 * L.plane, x->fsavef + 3 * d * L.plane, b3, cudaMemcpyDeviceToDevice, s);
+    for (int d = 1; d <= L.ndim; ++d)
+      n += launch_fofc_faces<float, float>(d, cviewT(Pf), L, Gf, x->S, x->fflag, x->Ff[d - 1], x->ctopf[d - 1],
+                                           x->tpb_flux, s);
+    n += launch_ct<float>(x->Ff, x->emff, L, s);
+    mark(x, KH_T_FOFC, st, 1);
+  }
   mark(x, KH_T_UPDATE, st, 0);
   const FailList fl{x->flist, x->counters + CNT_LIST0 + st};
   n += launch_update_mixed(U0, cviewT(Pf), Pout64, Pout32, Uout, x->Ff, L, G, Gf, x->S, x->dscalar + 3, coef,
@@ -216,7 +236,6 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
   if (c->recon != KH_RECON_MC && c->recon != KH_RECON_WENO5) return KH_EINVAL;
   if (c->precision != KH_FP64 && c->precision != KH_MIXED) return KH_EINVAL;
   if (c->fofc != 0 && c->fofc != 1) return KH_EINVAL;
-  if (c->fofc && c->precision != KH_FP64) return KH_EINVAL;
   if (!(gamma > 1.0) || !(c->cfl > 0.0) || !(fabs(a) < 1.0)) return KH_EINVAL;
   if (!(c->x1max > c->x1min) || !(c->x2max > c->x2min) || !(c->x3max > c->x3min)) return KH_EINVAL;
   for (int q = 0; q < 6; ++q) {
@@ -335,7 +354,11 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
   KH_ALLOC(x->pflag, (size_t)L.plane);
   if (c->fofc) {
     KH_ALLOC(x->fflag, (size_t)L.plane);
-    KH_ALLOC(x->fsave, 3 * (size_t)L.ndim * pl);
+    if (mixed) {
+      KH_ALLOC(x->fsavef, 3 * (size_t)L.ndim * plf);
+    } else {
+      KH_ALLOC(x->fsave, 3 * (size_t)L.ndim * pl);
+    }
   }
   KH_ALLOC(x->flist, (size_t)L.n1 * L.n2 * L.n3 * sizeof(unsigned));
   KH_ALLOC(x->partial, 2 * (size_t)x->npartial * sizeof(double));

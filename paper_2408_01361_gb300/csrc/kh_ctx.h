@@ -20,6 +20,7 @@ struct kh_ctx {
   int8_t* pflag;
   int8_t* fflag;   // first-order flux correction: flags of the current stage (one plane)
   double* fsave;   // ... and the raw field fluxes kept across the trial (3 planes per direction)
+  float* fsavef;   // the same for the FP32 fluxes of KH_MIXED
   double* partial;
   int npartial;
   double* dscalar;              // [0] dt_cfl out, [1..2] divb max/sum, [3] dt in

@@ -116,6 +116,10 @@ template <class R> int launch_ct(R* const F[3], R* const emf[3], const Layout& L
 int launch_fofc_trial(const double* U0, const CVars& Pin, double* const F[3], const Layout& L, const DevGeom& G,
                       const Scheme& S, const double* dtp, double coef, int8_t* flag, unsigned long long* cnt,
                       int tpb, cudaStream_t s);
+// The same trial with the mixed update (FP32 fluxes; Gf the FP32 geometry).
+int launch_fofc_trial_mixed(const double* U0, const CVarsT<float>& Pin, float* const F[3], const Layout& L,
+                            const DevGeom& G, const GeomT<float>& Gf, const Scheme& S, const double* dtp, double coef,
+                            int8_t* flag, unsigned long long* cnt, int tpb, cudaStream_t s);
 int launch_flag_ghosts(int8_t* flag, const Layout& L, const Scheme& S, cudaStream_t s);
 // Donor-cell LLF fluxes (with polar zeroing) through every x^D face of the
 // flux pass's face box that borders a flagged cell, over the raw fluxes.

@@ -278,6 +278,19 @@ __global__ void __launch_bounds__(TPB_MAX) k_fofc_trial(const double* U0, CVars 
   update_zone<true>(U0, Pin, Vars{}, nullptr, F1, F2, F3, L, G, S, coef * __ldg(dtp), flag, cnt, i, j, k);
 }
 
+__global__ void __launch_bounds__(TPB_MAX, 3) k_fofc_trial_mixed(const double* U0, CVarsT<float> Pin,
+                                                                const float* F1, const float* F2, const float* F3,
+                                                                Layout L, DevGeom G, GeomT<float> Gf, Scheme S,
+                                                                const double* dtp, double coef, int8_t* flag,
+                                                                unsigned long long* cnt) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nzones(L)) return;
+  int i, j, k;
+  zone_ijk(L, t, i, j, k);
+  update_mixed_zone<true>(U0, Pin, Vars{}, VarsT<float>{}, nullptr, F1, F2, F3, L, G, Gf, S,
+                          df_of_f64(coef * __ldg(dtp)), flag, cnt, i, j, k);
+}
+
 // Ghost flags follow the state's ghost map: a periodic image or an outflow or
 // polar copy carries its source zone's flag; Dirichlet ghosts are not evolved.
 __global__ void k_flag_ghosts(int8_t* flag, Layout L, Scheme S) {
@@ -523,6 +536,14 @@ int launch_fofc_trial(const double* U0, const CVars& Pin, double* const F[3], co
                       int tpb, cudaStream_t s) {
   const long long nz = (long long)L.n1 * L.n2 * L.n3;
   k_fofc_trial<<<nblocks(nz, tpb), tpb, 0, s>>>(U0, Pin, F[0], F[1], F[2], L, G, S, dtp, coef, flag, cnt);
+  return 1;
+}
+
+int launch_fofc_trial_mixed(const double* U0, const CVarsT<float>& Pin, float* const F[3], const Layout& L,
+                            const DevGeom& G, const GeomT<float>& Gf, const Scheme& S, const double* dtp, double coef,
+                            int8_t* flag, unsigned long long* cnt, int tpb, cudaStream_t s) {
+  const long long nz = (long long)L.n1 * L.n2 * L.n3;
+  k_fofc_trial_mixed<<<nblocks(nz, tpb), tpb, 0, s>>>(U0, Pin, F[0], F[1], F[2], L, G, Gf, S, dtp, coef, flag, cnt);
   return 1;
 }
 

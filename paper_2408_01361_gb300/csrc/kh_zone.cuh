@@ -357,7 +357,9 @@ __device__ __forceinline__ void update_zone(const double* U0, const CVars& Pin, 
 // stored conserved variables U^n + increment (an FP64 add per variable, the
 // conserved update exact to FP64 as in the FP64 path), the FP64 primitives
 // written at stage 2 (one add of the pair each) and the FP64 fallback
-// inversion of the zones noble2d_df hands back.
+// inversion of the zones noble2d_df hands back. TRIAL: the first-order flux
+// correction's trial, as update_zone<true> (Uout must be null).
+template <bool TRIAL = false>
 __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT<float>& Pin, const Vars& Pout64,
                                                   const VarsT<float>& Pout32, double* Uout, const float* F1,
                                                   const float* F2, const float* F3, const Layout& L, const DevGeom& G,
@@ -406,7 +408,7 @@ __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT
   int flag = noble2d_df(Ud, md, mx, W0, vsq0, Pn);
   if (flag == C2P_NEED_FP64) {
     // FP64 inversion of this zone from the stage input
-    atomicAdd(cnt + CNT_FP64, 1ULL);
+    if (!TRIAL) atomicAdd(cnt + CNT_FP64, 1ULL);
     double Uf[NV], Pd[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
@@ -419,6 +421,11 @@ __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT
 #pragma unroll
       for (int v = 0; v < 5; ++v) Pn[v] = df_of_f64(Pd[v]);
     }
+  }
+  if (TRIAL && flag) {
+    pflag[c] = 1;
+    atomicAdd(cnt + CNT_FOFC, 1ULL);
+    return;
   }
   if (flag) {
 #pragma unroll
@@ -450,6 +457,11 @@ __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT
         Pn[V_U3] = Pn[V_U3] * sc;
         fmask |= 4;
       }
+    }
+    if (TRIAL) {
+      pflag[c] = fmask ? 1 : 0;
+      if (fmask) atomicAdd(cnt + CNT_FOFC, 1ULL);
+      return;
     }
     if (fmask && Uout) {
       double* Uc = Uout + c;
