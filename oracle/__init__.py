@@ -47,8 +47,12 @@ class Params(C.Structure):
         ("mks_smooth", C.c_double), ("cfl", C.c_double),
         ("rho_min", C.c_double), ("u_min", C.c_double), ("bsq_rho_max", C.c_double),
         ("bsq_u_max", C.c_double), ("u_rho_max", C.c_double), ("gamma_max", C.c_double),
-        ("x1ref", C.c_double), ("fofc", C.c_int),
+        ("x1ref", C.c_double), ("fofc", C.c_int), ("bfield", C.c_int), ("emf", C.c_int),
     ]
+
+
+BFIELD = {"fluxct": 0, "face": 1}
+EMF = {"average": 0, "gs05": 1}
 
 
 def params(cfg: dict) -> Params:
@@ -77,6 +81,8 @@ def params(cfg: dict) -> Params:
     p.gamma_max = fl.get("gamma_max", 1e300)
     p.x1ref = cfg.get("x1ref", cfg["x1"][0])
     p.fofc = int(bool(cfg.get("fofc", False)))
+    p.bfield = BFIELD[cfg.get("bfield", "fluxct")]
+    p.emf = EMF[cfg.get("emf", "gs05")]
     return p
 
 
@@ -127,6 +133,10 @@ def lib():
         L.or_recon.argtypes = [C.c_int, C.c_int, _dp, _dp, _dp]
         L.or_count_ops.argtypes = [PP, C.c_double, C.c_double, _dp, _dp]
         L.or_fofc_flags.argtypes = [PP, _dp, _dp, C.c_double, _ip]
+        L.or_step_face.argtypes = [PP, _dp, _dp, _dp, C.c_double, C.c_void_p, C.c_void_p, C.POINTER(C.c_long)]
+        L.or_step_face.restype = C.c_double
+        L.or_face_divb.argtypes = [PP, _dp, _dp, C.c_void_p]
+        L.or_face_to_cell.argtypes = [PP, _dp, _dp]
         L.or_fofc_flags.restype = C.c_long
     return _lib
 
@@ -366,3 +376,35 @@ def fofc_flags(cfg: dict, U0, Pin, cdt: float):
     flags = np.zeros(Pin.shape[1:], dtype=np.int32)
     lib().or_fofc_flags(C.byref(params(cfg)), U0, Pin, float(cdt), flags)
     return flags
+
+
+def step_face(cfg: dict, U, P, fB, dt: float, dirichlet=None):
+    """One two-stage step with face-centred constrained transport (cfg
+    "bfield": "face"). fB: [3][N3][N2][N1], sqrt(-g) B^(a+1) on the lower
+    x^(a+1) face of each cell. Returns (U, P, fB, dt_next, stats[3])."""
+    U = np.array(U, dtype=np.float64, order="C", copy=True)
+    P = np.array(P, dtype=np.float64, order="C", copy=True)
+    fB = np.array(fB, dtype=np.float64, order="C", copy=True)
+    lo, hi = (dirichlet or (None, None))
+    st = (C.c_long * 4)()
+    dtn = lib().or_step_face(C.byref(params(cfg)), U, P, fB, float(dt), _ptr(lo), _ptr(hi), st)
+    if dtn < 0:
+        raise ValueError("or_step_face: needs bfield 'face' and no flux correction")
+    _note(st)
+    return U, P, fB, dtn, list(st)[:3]
+
+
+def face_divb(cfg: dict, fB, field: bool = False):
+    """Face divergence of a face field: (max |div|, mean |div|[, per cell])."""
+    fB = np.ascontiguousarray(fB, dtype=np.float64)
+    out = np.zeros(2)
+    div = np.zeros(fB.shape[1:]) if field else None
+    lib().or_face_divb(C.byref(params(cfg)), fB, out, _ptr(div))
+    return (out[0], out[1], div) if field else (out[0], out[1])
+
+
+def face_to_cell(cfg: dict, fB, P):
+    """P with the interior cells' B^i replaced by the face means / sqrt(-g)."""
+    P = np.array(P, dtype=np.float64, order="C", copy=True)
+    lib().or_face_to_cell(C.byref(params(cfg)), np.ascontiguousarray(fB, dtype=np.float64), P)
+    return P

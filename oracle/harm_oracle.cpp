@@ -244,23 +244,26 @@ void compute_fluxes(const Grid& gr, const R* P, FluxesT<R>& fx, const R& gam) {
   finish_fluxes(gr, fx);
 }
 
+// Polar axis: no flux of anything through an x2 face lying on the axis.
+template <class R>
+void polar_zero(const Grid& gr, FluxesT<R>& fx) {
+  int lo[3], hi[3];
+  face_range(gr, 1, lo, hi);
+  for (int side = 0; side < 2; ++side) {
+    if (gr.c.bc[2 + side] != BC_POLAR) continue;
+    int j = side == 0 ? gr.s2() : gr.e2();
+    for (int k = lo[2]; k <= hi[2]; ++k)
+      for (int i = lo[0]; i <= hi[0]; ++i)
+        for (int v = 0; v < NVAR; ++v) fx.F[1][gr.idx(v, k, j, i)] = R(0.0);
+  }
+}
+
 // Polar-axis zeroing and Flux-CT applied to the raw face fluxes of fx.
 template <class R>
 void finish_fluxes(const Grid& gr, FluxesT<R>& fx) {
   const GridInfo& g = gr.g;
   const size_t n = gr.cells();
-  // Polar axis: no flux of anything through an x2 face lying on the axis.
-  {
-    int lo[3], hi[3];
-    face_range(gr, 1, lo, hi);
-    for (int side = 0; side < 2; ++side) {
-      if (gr.c.bc[2 + side] != BC_POLAR) continue;
-      int j = side == 0 ? gr.s2() : gr.e2();
-      for (int k = lo[2]; k <= hi[2]; ++k)
-        for (int i = lo[0]; i <= hi[0]; ++i)
-          for (int v = 0; v < NVAR; ++v) fx.F[1][gr.idx(v, k, j, i)] = R(0.0);
-    }
-  }
+  polar_zero(gr, fx);
   // Flux-CT (Toth 2000): corner EMFs as averages of the four adjacent face
   // fluxes of the field, then field fluxes as averages of the edge EMFs.
   std::vector<R>& F1 = fx.F[0];
@@ -320,6 +323,167 @@ void finish_fluxes(const Grid& gr, FluxesT<R>& fx) {
         F3[V(B2, k, j, i)] = -0.5 * (e1[I(k, j, i)] + e1[I(k, j + 1, i)]);
         F3[V(B3, k, j, i)] = R(0.0);
       }
+}
+
+// ---------------------------------------------------------------------------
+// Face-centred constrained transport (the paper's "Algorithm" section: the
+// scheme of Stone & Gardiner 2009, edge EMFs after Gardiner & Stone 2005).
+// The field lives on faces: fB[a][k][j][i] = sqrt(-g) B^(a+1) at the lower
+// x^(a+1) face of cell (k, j, i) (a 2-D grid keeps sqrt(-g) B^3 per cell).
+// With v = (a, b, c) cyclic, the edge EMF along x^c is
+//   E_c = sqrt(-g) (b^b u^a - b^a u^b) = F^a(B^b) = -F^b(B^a)
+// (F^d the x^d flux of sqrt(-g) B), stored at the cell whose lower x^a and
+// x^b faces bound the edge, and the induction equation is
+//   d/dt (sqrt(-g) B^a) = d_b E_c - d_c E_b,
+// whose discrete form keeps the face divergence of every cell unchanged.
+// ---------------------------------------------------------------------------
+
+// Cell-centred EMFs from the cell's primitives: E[c] along x^(c+1).
+template <class R>
+void cell_emfs(const R P[NVAR], const Geo& G, R E[3]) {
+  FluidState<R> S;
+  fluid_state(P, G, S);
+  for (int c = 0; c < 3; ++c) {
+    const int a = (c + 1) % 3 + 1, b = (c + 2) % 3 + 1;  // 4-vector indices of x^a, x^b
+    E[c] = G.gdet * (S.bcon[b] * S.ucon[a] - S.bcon[a] * S.ucon[b]);
+  }
+}
+
+// Edge EMFs from the raw face fluxes fx (after polar zeroing) and the stage
+// input P (ghosts filled). EMF_AVERAGE: the mean of the four face values
+// around the edge. EMF_GS05: that mean plus, along each of the two face
+// directions, the difference of the half-zone derivatives of E between the
+// faces and the edge, each taken from the cell upwind of the mass flux
+// through the face it is attached to (the mean of both cells when that flux
+// is zero). EMFs on edges lying on a polar axis are zero (the axis faces
+// carry no flux). E[c] covers the edges the interior faces need.
+template <class R>
+void face_emfs(const Grid& gr, const R* P, const FluxesT<R>& fx, std::vector<R> E[3]) {
+  const GridInfo& g = gr.g;
+  const size_t n = gr.cells();
+  for (int c = 0; c < 3; ++c) E[c].assign(n, R(0.0));
+  // cell-centred EMFs on every cell (ghosts included)
+  std::vector<R> Ec[3];
+  for (int c = 0; c < 3; ++c) Ec[c].assign(n, R(0.0));
+  if (gr.c.emf == EMF_GS05)
+    for (int k = 0; k < g.N3; ++k)
+      for (int j = 0; j < g.N2; ++j)
+        for (int i = 0; i < g.N1; ++i) {
+          R Pc[NVAR], e[3];
+          for (int v = 0; v < NVAR; ++v) Pc[v] = P[gr.idx(v, k, j, i)];
+          cell_emfs<R>(Pc, gr.G(LOC_CENT, j, i), e);
+          for (int c = 0; c < 3; ++c) Ec[c][gr.idx(0, k, j, i)] = e[c];
+        }
+  const int nd = g.ndim;
+  const int s[3] = {gr.s1(), gr.s2(), gr.s3()}, e[3] = {gr.e1(), gr.e2(), gr.e3()};
+  auto at = [&](const int x[3]) { return gr.idx(0, x[2], x[1], x[0]); };
+  auto flux = [&](int d, int v, const int x[3]) { return fx.F[d][gr.idx(v, x[2], x[1], x[0])]; };
+  for (int c = 0; c < 3; ++c) {
+    const int a = (c + 1) % 3, b = (c + 2) % 3;  // edge along x^c between faces normal to x^a and x^b
+    if (nd == 2 && c != 2) {
+      // no x3 variation: E1 is the x2-face value F^2(B^3), E2 minus the x1-face value F^1(B^3)
+      const int d = c == 0 ? 1 : 0;
+      const double sg = c == 0 ? 1.0 : -1.0;
+      for (int j = s[1]; j <= e[1] - (d == 0 ? 1 : 0); ++j)
+        for (int i = s[0]; i <= e[0] - (d == 1 ? 1 : 0); ++i) {
+          const int x[3] = {i, j, 0};
+          E[c][at(x)] = sg * flux(d, B3, x);
+        }
+      continue;
+    }
+    if (nd == 2 && (a == 2 || b == 2)) continue;
+    int lo[3], hi[3];
+    for (int q = 0; q < 3; ++q) {
+      const bool active = q < nd;
+      lo[q] = active ? s[q] : 0;
+      hi[q] = active ? (q == c ? e[q] - 1 : e[q]) : 0;  // edges: both ends along a and b
+    }
+    for (int k = lo[2]; k <= hi[2]; ++k)
+      for (int j = lo[1]; j <= hi[1]; ++j)
+        for (int i = lo[0]; i <= hi[0]; ++i) {
+          const int x[3] = {i, j, k};
+          int xb[3] = {i, j, k}, xa[3] = {i, j, k}, xab[3] = {i, j, k};
+          xb[b] -= 1;   // the cell below in x^b
+          xa[a] -= 1;   // the cell below in x^a
+          xab[a] -= 1;
+          xab[b] -= 1;  // the cell below in both
+          // face values of E_c: on x^a faces F^a(B^b), on x^b faces -F^b(B^a)
+          const R Ea_hi = flux(a, B1 + b, x), Ea_lo = flux(a, B1 + b, xb);     // x^a faces at b, b-1
+          const R Eb_hi = -flux(b, B1 + a, x), Eb_lo = -flux(b, B1 + a, xa);   // x^b faces at a, a-1
+          R emf = 0.25 * (Ea_hi + Ea_lo + Eb_hi + Eb_lo);
+          if (gr.c.emf == EMF_GS05) {
+            const std::vector<R>& C = Ec[c];
+            // along x^b, on the x^a faces: upwind across x^a by the mass flux there
+            auto up_a = [&](const R& mflux, const R& lowcell, const R& highcell) {
+              if (mflux > 0.0) return lowcell;
+              if (mflux < 0.0) return highcell;
+              return R(0.5 * (lowcell + highcell));
+            };
+            // (half-zone derivative x half width) above the edge in x^b: centre(b) - face(b-1/2)
+            const R db_hi = up_a(flux(a, RHO, x), C[at(xa)] - Eb_lo, C[at(x)] - Eb_hi);
+            // below the edge in x^b: face(b-1/2) - centre(b-1)
+            const R db_lo = up_a(flux(a, RHO, xb), Eb_lo - C[at(xab)], Eb_hi - C[at(xb)]);
+            // along x^a, on the x^b faces: upwind across x^b
+            const R da_hi = up_a(flux(b, RHO, x), C[at(xb)] - Ea_lo, C[at(x)] - Ea_hi);
+            const R da_lo = up_a(flux(b, RHO, xa), Ea_lo - C[at(xab)], Ea_hi - C[at(xa)]);
+            emf += 0.25 * ((db_lo - db_hi) + (da_lo - da_hi));
+          }
+          E[c][at(x)] = emf;
+        }
+  }
+  // polar axis: edges along x1 and x3 lying on an axis carry no EMF
+  for (int side = 0; side < 2; ++side) {
+    if (gr.c.bc[2 + side] != BC_POLAR) continue;
+    const int j = side == 0 ? s[1] : e[1];
+    for (int k = 0; k < g.N3; ++k)
+      for (int i = 0; i < g.N1; ++i) {
+        E[0][gr.idx(0, k, j, i)] = R(0.0);
+        E[2][gr.idx(0, k, j, i)] = R(0.0);
+      }
+  }
+}
+
+// Face update of one stage over every face of the interior cells (both
+// bounding faces along the normal): fBout = fB0 + cdt (d_b E_c - d_c E_b).
+// fB0 and fBout may be the same array.
+template <class R>
+void face_update(const Grid& gr, const R* fB0, const std::vector<R> E[3], double cdt, R* fBout) {
+  const GridInfo& g = gr.g;
+  const int nd = g.ndim;
+  const double dx[3] = {g.dx1, g.dx2, g.dx3};
+  const int s[3] = {gr.s1(), gr.s2(), gr.s3()}, e[3] = {gr.e1(), gr.e2(), gr.e3()};
+  for (int a = 0; a < 3; ++a) {
+    const int b = (a + 1) % 3, c = (a + 2) % 3;
+    int lo[3], hi[3];
+    for (int q = 0; q < 3; ++q) {
+      lo[q] = s[q];
+      hi[q] = (q == a && q < nd) ? e[q] : e[q] - 1;
+    }
+    for (int k = lo[2]; k <= hi[2]; ++k)
+      for (int j = lo[1]; j <= hi[1]; ++j)
+        for (int i = lo[0]; i <= hi[0]; ++i) {
+          const int x[3] = {i, j, k};
+          int xb[3] = {i, j, k}, xc[3] = {i, j, k};
+          xb[b] += 1;
+          xc[c] += 1;
+          const size_t f = gr.idx(a, k, j, i), o = gr.idx(0, k, j, i);
+          R rhs(0.0);
+          if (b < nd) rhs += (E[c][gr.idx(0, xb[2], xb[1], xb[0])] - E[c][o]) / dx[b];
+          if (c < nd) rhs -= (E[b][gr.idx(0, xc[2], xc[1], xc[0])] - E[b][o]) / dx[c];
+          (void)x;
+          fBout[f] = fB0[f] + cdt * rhs;
+        }
+  }
+}
+
+// sqrt(-g) B at cell centres: the mean of the two faces along each direction
+// (the face value itself along x3 on a 2-D grid).
+template <class R>
+void face_to_cell_u(const Grid& gr, const R* fB, int k, int j, int i, R UB[3]) {
+  const int nd = gr.g.ndim;
+  UB[0] = 0.5 * (fB[gr.idx(0, k, j, i)] + fB[gr.idx(0, k, j, i + 1)]);
+  UB[1] = 0.5 * (fB[gr.idx(1, k, j, i)] + fB[gr.idx(1, k, j + 1, i)]);
+  UB[2] = nd == 3 ? R(0.5 * (fB[gr.idx(2, k, j, i)] + fB[gr.idx(2, k + 1, j, i)])) : fB[gr.idx(2, k, j, i)];
 }
 
 // ---------------------------------------------------------------------------
@@ -575,9 +739,19 @@ long fofc_correct(const Grid& gr, const R* U0, const R* Pin, const R& gam, doubl
 // failed its inversion and was fixed up is frozen (zero tangent).
 template <class R>
 void stage(const Grid& gr, const R* U0, const R* Pin, const R& gam, double cdt, R* Uout, R* Pout,
-           FluxesT<R>& fx, StageStats& st, std::vector<int>* pflag_out, std::vector<int>* fflag_out = nullptr) {
+           FluxesT<R>& fx, StageStats& st, std::vector<int>* pflag_out, std::vector<int>* fflag_out = nullptr,
+           const R* fB0 = nullptr, R* fBout = nullptr) {
   const GridInfo& g = gr.g;
-  if (gr.c.fofc) {
+  const bool face = gr.c.bfield == BFIELD_FACE;
+  if (face) {
+    // face-centred CT: the raw fluxes move the fluid; the edge EMFs move the
+    // face field, whose cell means become the zones' sqrt(-g) B
+    compute_raw(gr, Pin, fx, gam);
+    polar_zero(gr, fx);
+    std::vector<R> E[3];
+    face_emfs(gr, Pin, fx, E);
+    face_update(gr, fB0, E, cdt, fBout);
+  } else if (gr.c.fofc) {
     FluxesT<R> raw;
     compute_raw(gr, Pin, raw, gam);
     fx = raw;
@@ -604,6 +778,7 @@ void stage(const Grid& gr, const R* U0, const R* Pin, const R& gam, double cdt, 
           }
           U[v] = U0[gr.idx(v, k, j, i)] + cdt * (-div + S[v]);
         }
+        if (face) face_to_cell_u(gr, (const R*)fBout, k, j, i, U + B1);
         // guess = stage input
         int flag = invert_point(U, G, gam, P);
         size_t c = gr.idx(0, k, j, i);
@@ -865,6 +1040,7 @@ void or_stage(const or_params* c, const double* U0, const double* Pin, double cd
 // (summed over both stages). Returns the next CFL dt.
 double or_step(const or_params* c, double* U, double* P, double dt, const double* dir_lo, const double* dir_hi,
                long* stats) {
+  if (c->bfield != BFIELD_FLUXCT) return -1.0;  // the face field is state: or_step_face
   Grid gr;
   build_grid(*c, gr);
   const size_t n = gr.cells() * NVAR;
@@ -896,6 +1072,89 @@ double or_step(const or_params* c, double* U, double* P, double dt, const double
     stats[3] = st.nfofc;
   }
   return dtn;
+}
+
+// One step with face-centred constrained transport: as or_step, with the
+// face field fB ([3][N3][N2][N1], sqrt(-g) B^(a+1) on the lower x^(a+1) face
+// of each cell) advanced by the edge EMFs of each stage and the zones'
+// sqrt(-g) B taken as its cell means. Faces of the interior cells are
+// updated; other entries are kept. Returns the next dt, or -1 for a
+// configuration it does not run (Flux-CT, or with the flux correction).
+double or_step_face(const or_params* c, double* U, double* P, double* fB, double dt, const double* dir_lo,
+                    const double* dir_hi, long* stats) {
+  if (c->bfield != BFIELD_FACE || c->fofc) return -1.0;
+  Grid gr;
+  build_grid(*c, gr);
+  const size_t n = gr.cells() * NVAR;
+  std::vector<double> Pn(P, P + n), U0(U, U + n), Ps(Pn), Us(U0), Pnew, Unew;
+  std::vector<double> fB0(fB, fB + 3 * gr.cells()), fBs(fB0), fBn(fB0);
+  Fluxes fx;
+  StageStats st;
+  apply_bc(gr, Pn.data(), dir_lo, dir_hi);
+  stage<double>(gr, U0.data(), Pn.data(), c->gam, 0.5 * dt, Us.data(), Ps.data(), fx, st, nullptr, nullptr,
+                fB0.data(), fBs.data());
+  apply_bc(gr, Ps.data(), dir_lo, dir_hi);
+  Pnew = Ps;
+  Unew = U0;
+  stage<double>(gr, U0.data(), Ps.data(), c->gam, dt, Unew.data(), Pnew.data(), fx, st, nullptr, nullptr,
+                fB0.data(), fBn.data());
+  const double dtn = cfl_dt(gr, fx);
+  for (int v = 0; v < NVAR; ++v)
+    for (int k = gr.s3(); k < gr.e3(); ++k)
+      for (int j = gr.s2(); j < gr.e2(); ++j)
+        for (int i = gr.s1(); i < gr.e1(); ++i) {
+          size_t q = gr.idx(v, k, j, i);
+          U[q] = Unew[q];
+          P[q] = Pnew[q];
+        }
+  std::memcpy(fB, fBn.data(), fBn.size() * sizeof(double));
+  if (stats) {
+    stats[0] = st.nfail;
+    stats[1] = st.nfloor;
+    stats[2] = st.nunfixed;
+    stats[3] = st.nfofc;
+  }
+  return dtn;
+}
+
+// Face divergence of a face field: per interior cell sum_a (fB_a(upper) -
+// fB_a(lower)) / dx_a (x1, x2 only on a 2-D grid); out = {max |div|, mean
+// |div|}; div (nullable) gets the per-cell values.
+void or_face_divb(const or_params* c, const double* fB, double* out, double* div) {
+  Grid gr;
+  build_grid(*c, gr);
+  const GridInfo& g = gr.g;
+  const double dx[3] = {g.dx1, g.dx2, g.dx3};
+  double mx = 0.0, sum = 0.0;
+  long cnt = 0;
+  for (int k = gr.s3(); k < gr.e3(); ++k)
+    for (int j = gr.s2(); j < gr.e2(); ++j)
+      for (int i = gr.s1(); i < gr.e1(); ++i) {
+        double d = (fB[gr.idx(0, k, j, i + 1)] - fB[gr.idx(0, k, j, i)]) / dx[0] +
+                   (fB[gr.idx(1, k, j + 1, i)] - fB[gr.idx(1, k, j, i)]) / dx[1];
+        if (g.ndim == 3) d += (fB[gr.idx(2, k + 1, j, i)] - fB[gr.idx(2, k, j, i)]) / dx[2];
+        if (div) div[gr.idx(0, k, j, i)] = d;
+        mx = std::max(mx, std::fabs(d));
+        sum += std::fabs(d);
+        ++cnt;
+      }
+  out[0] = mx;
+  out[1] = cnt ? sum / cnt : 0.0;
+}
+
+// Cell-centred B^i of the interior cells from a face field (the face means
+// over sqrt(-g) at the cell centre), written into P's field slots.
+void or_face_to_cell(const or_params* c, const double* fB, double* P) {
+  Grid gr;
+  build_grid(*c, gr);
+  for (int k = gr.s3(); k < gr.e3(); ++k)
+    for (int j = gr.s2(); j < gr.e2(); ++j)
+      for (int i = gr.s1(); i < gr.e1(); ++i) {
+        double UB[3];
+        face_to_cell_u<double>(gr, fB, k, j, i, UB);
+        const double gd = gr.G(LOC_CENT, j, i).gdet;
+        for (int b = 0; b < 3; ++b) P[gr.idx(B1 + b, k, j, i)] = UB[b] / gd;
+      }
 }
 
 // The zones the first-order flux correction flags in one stage from the

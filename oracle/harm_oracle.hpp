@@ -54,7 +54,12 @@ struct Params {
   double gamma_max;               // Lorentz-factor ceiling
   double x1ref;                   // FMKS blending reference: the x1 start of the whole domain
   int fofc;                       // first-order flux correction (see stage())
+  int bfield;                     // BFIELD_FLUXCT | BFIELD_FACE (face-centred constrained transport)
+  int emf;                        // face CT edge EMFs: EMF_AVERAGE | EMF_GS05 (contact-upwinded)
 };
+
+enum { BFIELD_FLUXCT = 0, BFIELD_FACE = 1 };
+enum { EMF_AVERAGE = 0, EMF_GS05 = 1 };
 
 // Geometry of one point.
 struct Geo {

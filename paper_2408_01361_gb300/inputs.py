@@ -193,11 +193,14 @@ def utilde_from_ks(cfg: dict, x1, x2, ut, ur, uth, uph):
 
 
 def gdet_native(cfg: dict, x1, x2):
-    """sqrt(-g) of Kerr in native MKS-family coordinates: Sigma |sin theta| r dtheta/dx2."""
+    """sqrt(-g) in native coordinates: 1 for Minkowski (Cartesian); for Kerr
+    Sigma |sin theta| (dr/dx1) (dtheta/dx2), dr/dx1 = r in the MKS family."""
+    if cfg["coords"] == "minkowski":
+        return np.ones(np.broadcast(np.asarray(x1), np.asarray(x2)).shape)
     a = cfg.get("a", 0.0)
     r, th, th1, th2 = embed(cfg, x1, x2)
     sig = r * r + a * a * np.cos(th) ** 2
-    return sig * np.abs(np.sin(th)) * r * th2
+    return sig * np.abs(np.sin(th)) * (r if cfg["coords"] != "ks" else 1.0) * th2
 
 
 # ---------------------------------------------------------------------------
@@ -484,6 +487,96 @@ def torus_state(cfg: dict, seed: int = 2, noise: float = 4e-2, kappa: float = 1e
     if return_norms:
         return P, (rho_max, norm if field else 0.0)
     return P
+
+
+# ---------------------------------------------------------------------------
+# Face-centred fields (for face-centred constrained transport): arrays
+# (3, N3, N2, N1), entry a = sqrt(-g) B^(a+1) on the lower x^(a+1) face of
+# each cell (a 2-D grid keeps sqrt(-g) B^3 per cell).
+# ---------------------------------------------------------------------------
+def _fwd(A, axis: int, d: float):
+    """Forward difference along an array axis / d; the last entry (no upper
+    neighbour) is 0."""
+    out = np.zeros_like(A)
+    sl_hi = [slice(None)] * 3
+    sl_lo = [slice(None)] * 3
+    sl_hi[axis] = slice(1, None)
+    sl_lo[axis] = slice(None, -1)
+    out[tuple(sl_lo)] = (A[tuple(sl_hi)] - A[tuple(sl_lo)]) / d
+    return out
+
+
+def face_field_from_potential(cfg: dict, A1=None, A2=None, A3=None) -> np.ndarray:
+    """The discrete curl of an edge vector potential: A1 on x1-edges
+    (i, j-1/2, k-1/2), A2 on x2-edges (i-1/2, j, k-1/2), A3 on x3-edges
+    (i-1/2, j-1/2, k), each (N3, N2, N1) or None (= 0); on a 2-D grid A1 sits on
+    x2 faces and A2 on x1 faces. sqrt(-g) B^a = eps^{abc} d_b A_c, so the face
+    divergence is zero up to rounding."""
+    N = shape(cfg)[1:]
+    z = np.zeros(N)
+    A1 = z if A1 is None else np.asarray(A1, dtype=np.float64)
+    A2 = z if A2 is None else np.asarray(A2, dtype=np.float64)
+    A3 = z if A3 is None else np.asarray(A3, dtype=np.float64)
+    dx = [(cfg[k][1] - cfg[k][0]) / cfg[n] for k, n in (("x1", "n1"), ("x2", "n2"), ("x3", "n3"))]
+    three = cfg["n3"] > 1
+    # array axes: 0 = x3, 1 = x2, 2 = x1
+    fB = np.zeros((3,) + N)
+    fB[0] = _fwd(A3, 1, dx[1]) - (_fwd(A2, 0, dx[2]) if three else 0.0)
+    fB[1] = (_fwd(A1, 0, dx[2]) if three else 0.0) - _fwd(A3, 2, dx[0])
+    fB[2] = _fwd(A2, 2, dx[0]) - _fwd(A1, 1, dx[1])
+    return fB
+
+
+def random_face_field(cfg: dict, seed: int, scale: float = 1.0) -> np.ndarray:
+    """A divergence-free face field of magnitude ~scale with grid-scale
+    structure: the curl of seeded uniform edge potentials, drawn per interior
+    edge and repeated periodically into the ghost rows (so that on a periodic
+    grid a face and its periodic image carry the same value)."""
+    N = shape(cfg)[1:]
+    ng = cfg.get("ng", NG)
+    g3 = ng if cfg["n3"] > 1 else 0
+    dx = min((cfg[k][1] - cfg[k][0]) / cfg[n] for k, n in (("x1", "n1"), ("x2", "n2"), ("x3", "n3")))
+    k, j, i = np.meshgrid((np.arange(N[0]) - g3) % cfg["n3"], (np.arange(N[1]) - ng) % cfg["n2"],
+                          (np.arange(N[2]) - ng) % cfg["n1"], indexing="ij")
+    idx = (k * cfg["n2"] + j) * cfg["n1"] + i
+    A = [scale * dx * (uniform01(seed + 101 * q, idx) - 0.5) for q in range(3)]
+    return face_field_from_potential(cfg, *A)
+
+
+def cell_field_from_faces(cfg: dict, fB: np.ndarray, P: np.ndarray) -> np.ndarray:
+    """P with the B^i of every cell that has both faces (all but the last
+    row along each axis) set to the face means over sqrt(-g)."""
+    P = np.array(P, dtype=np.float64, copy=True)
+    X2, X1 = np.meshgrid(centers(cfg, 1), centers(cfg, 0), indexing="ij")
+    gd = gdet_native(cfg, X1, X2)[None, :, :]
+    m1 = np.zeros_like(fB[0])
+    m2 = np.zeros_like(fB[1])
+    m1[:, :, :-1] = 0.5 * (fB[0][:, :, :-1] + fB[0][:, :, 1:])
+    m2[:, :-1, :] = 0.5 * (fB[1][:, :-1, :] + fB[1][:, 1:, :])
+    if cfg["n3"] > 1:
+        m3 = np.zeros_like(fB[2])
+        m3[:-1] = 0.5 * (fB[2][:-1] + fB[2][1:])
+    else:
+        m3 = fB[2].copy()
+    P[5], P[6], P[7] = m1 / gd, m2 / gd, m3 / gd
+    return P
+
+
+def torus_face_field(cfg: dict, kappa: float = 1e-3, norms=None) -> np.ndarray:
+    """The FM torus's poloidal loop as a face field: A_phi at cell corners as in
+    torus_state (the same normalisation), curled onto the faces. Its face means
+    over sqrt(-g) are torus_state's cell-centred B^1, B^2."""
+    if norms is None:
+        _, norms = torus_state(cfg, noise=0.0, kappa=kappa, return_norms=True)
+    rho_max, norm = norms
+    x1f = centers(cfg, 0, face=True)
+    x2f = centers(cfg, 1, face=True)
+    Y2, Y1 = np.meshgrid(x2f, x1f, indexing="ij")
+    rc, thc, _, _ = embed(cfg, Y1, Y2)
+    rhoc, _, insc = fm_density(cfg, rc, thc, kappa)
+    Aphi = np.maximum(np.where(insc, rhoc / rho_max, 0.0) - 0.2, 0.0) * norm
+    A3 = np.broadcast_to(Aphi[None, :, :], shape(cfg)[1:])
+    return face_field_from_potential(cfg, None, None, A3)
 
 
 # ---------------------------------------------------------------------------
