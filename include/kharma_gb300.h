@@ -40,6 +40,8 @@ enum { KH_MINKOWSKI = 0, KH_KS = 1, KH_MKS = 2, KH_FMKS = 3 };
 enum { KH_BC_PERIODIC = 0, KH_BC_OUTFLOW = 1, KH_BC_POLAR = 2, KH_BC_DIRICHLET = 3 };
 enum { KH_RECON_MC = 0, KH_RECON_WENO5 = 1 };
 enum { KH_FP64 = 0, KH_MIXED = 1 };
+enum { KH_B_FLUXCT = 0, KH_B_FACE = 1 };
+enum { KH_EMF_AVERAGE = 0, KH_EMF_GS05 = 1 };
 enum {
   KH_OK = 0,
   KH_EINVAL = -1,   /* bad argument or unsupported combination */
@@ -74,6 +76,20 @@ typedef struct {
                              Flux-CT are applied again before the stage's update. The
                              flags' ghost zones follow the state's ghost map (Dirichlet
                              ghosts unflagged). 0: off. Single-grid contexts only. */
+  int bfield;             /* KH_B_FLUXCT: cell-centred field, Flux-CT (Toth 2000);
+                             KH_B_FACE: face-centred constrained transport
+                             ("Algorithm" section: Stone & Gardiner 2009). The face
+                             field sqrt(-g) B^a lives on the lower x^a face of each
+                             cell (kh_set_face_field); the edge EMFs advance it by
+                             d_b E_c - d_c E_b, which keeps every cell's face
+                             divergence; B of a zone is the mean of its two faces
+                             over sqrt(-g). Edge EMFs on a polar axis are zero.
+                             Single-grid FP64 contexts; no flux correction. */
+  int emf;                /* KH_B_FACE edge EMFs: KH_EMF_AVERAGE (mean of the four
+                             face values; with face means as the zone field this is
+                             Flux-CT) or KH_EMF_GS05 (Gardiner & Stone 2005: plus the
+                             half-zone derivative terms, each taken from the cell
+                             upwind of the mass flux through its face) */
 } kh_coords;
 
 /* Counters of the last kh_step (both stages summed). */
@@ -152,6 +168,24 @@ int kh_divb(kh_ctx* ctx, const double* B, double* max_abs, double* l1);
  * n3 == 1; the first-order flux correction, which needs a trial update, is
  * not applied). Entries outside the computed face ranges are left untouched. */
 int kh_fluxes(kh_ctx* ctx, const double* P, const double* B, double* F1, double* F2, double* F3);
+
+/* KH_B_FACE contexts: register the face field fB (device, caller-owned,
+ * [3][n3s][n2s][n1s], plane a = sqrt(-g) B^(a+1) on the lower x^(a+1) face of
+ * each cell; on a 2-D grid plane 2 holds the cell's sqrt(-g) B^3) that every
+ * later kh_step advances together with (U, P, B). kh_step updates the faces
+ * of the interior cells (both bounding faces along the normal) and leaves
+ * other entries alone. The zone field B must be the face means over sqrt(-g)
+ * (kh_face_to_cell) when stepping starts. KH_EINVAL for other contexts. */
+int kh_set_face_field(kh_ctx* ctx, double* fB);
+
+/* B (3 planes) of the interior cells = the face means of fB over sqrt(-g)
+ * (ghost cells untouched). Any context. */
+int kh_face_to_cell(kh_ctx* ctx, const double* fB, double* B);
+
+/* Face divergence sum_a (fB_a(upper) - fB_a(lower)) / dx_a of the interior
+ * cells (x1, x2 only on a 2-D grid): *max_abs = max |div|, *l1 = mean |div|
+ * (host pointers; synchronises). Any context. */
+int kh_face_divb(kh_ctx* ctx, const double* fB, double* max_abs, double* l1);
 
 /* Ghost fill of (P, B) in place with the context's boundary rules. */
 int kh_fill_ghosts(kh_ctx* ctx, double* P, double* B);

@@ -82,7 +82,7 @@ void free_all(kh_ctx* x) {
                   x->counters, x->dirichlet[0], x->dirichlet[1], x->geof, x->dgmf, x->pstarf, x->pnf, x->Ff[0],
                   x->Ff[1], x->Ff[2], x->ctopf[0], x->ctopf[1], x->ctopf[2], x->emff[0], x->emff[1],
                   x->emff[2], x->dirichletf[0], x->dirichletf[1], x->adj, x->adj_i8, x->adj_red, x->geodf, x->flist,
-                  x->fflag, x->fsave, x->fsavef};
+                  x->fflag, x->fsave, x->fsavef, x->fBstar, x->ecc};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -109,9 +109,19 @@ int run_stage(kh_ctx* x, int st, const double* U0, const Vars& Pin, const Vars& 
     for (int d = 0; d < L.ndim; ++d)
       cudaMemcpyAsync(x->fsave + 3 * d * L.plane, x->F[d] + V_B1 * L.plane, b3, cudaMemcpyDeviceToDevice, s);
   }
-  mark(x, KH_T_CT, st, 0);
-  n += launch_ct<double>(x->F, x->emf, L, s);
-  mark(x, KH_T_CT, st, 1);
+  double* fBn = nullptr;
+  if (x->S.bfield == KH_B_FACE) {
+    // face-centred CT: edge EMFs from the raw fluxes move the face field;
+    // the update takes the zones' field from the new faces
+    fBn = st == 0 ? x->fBstar : x->fB;
+    mark(x, KH_T_CT, st, 0);
+    n += launch_face_ct(cview(Pin), x->F, x->ecc, x->emf, x->fB, fBn, L, G, x->S, x->dscalar + 3, coef, s);
+    mark(x, KH_T_CT, st, 1);
+  } else {
+    mark(x, KH_T_CT, st, 0);
+    n += launch_ct<double>(x->F, x->emf, L, s);
+    mark(x, KH_T_CT, st, 1);
+  }
   if (x->S.fofc) {
     // first-order flux correction: trial update with the high-order fluxes,
     // donor-cell fluxes on the faces of the flagged zones, Flux-CT again
@@ -130,7 +140,7 @@ int run_stage(kh_ctx* x, int st, const double* U0, const Vars& Pin, const Vars& 
   mark(x, KH_T_UPDATE, st, 0);
   const FailList fl{x->flist, x->counters + CNT_LIST0 + st};
   n += launch_update(U0, cview(Pin), Pout, Uout, x->F, L, G, x->S, x->dscalar + 3, coef, x->pflag, x->counters,
-                     x->tpb_update, s, fl);
+                     x->tpb_update, s, fl, fBn);
   mark(x, KH_T_UPDATE, st, 1);
   mark(x, KH_T_FIXUP, st, 0);
   n += launch_fixup<double>(Pout, Uout, x->pflag, L, G, x->S, x->counters, s, fl);
@@ -236,6 +246,9 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
   if (c->recon != KH_RECON_MC && c->recon != KH_RECON_WENO5) return KH_EINVAL;
   if (c->precision != KH_FP64 && c->precision != KH_MIXED) return KH_EINVAL;
   if (c->fofc != 0 && c->fofc != 1) return KH_EINVAL;
+  if (c->bfield != KH_B_FLUXCT && c->bfield != KH_B_FACE) return KH_EINVAL;
+  if (c->emf != KH_EMF_AVERAGE && c->emf != KH_EMF_GS05) return KH_EINVAL;
+  if (c->bfield == KH_B_FACE && (c->precision != KH_FP64 || c->fofc)) return KH_EINVAL;
   if (!(gamma > 1.0) || !(c->cfl > 0.0) || !(fabs(a) < 1.0)) return KH_EINVAL;
   if (!(c->x1max > c->x1min) || !(c->x2max > c->x2min) || !(c->x3max > c->x3min)) return KH_EINVAL;
   for (int q = 0; q < 6; ++q) {
@@ -292,6 +305,8 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
   S.cfl = c->cfl;
   S.recon = c->recon;
   S.fofc = c->fofc;
+  S.bfield = c->bfield;
+  S.emf = c->emf;
   for (int q = 0; q < 6; ++q) S.bc[q] = c->bc[q];
   S.fl.rho_min = c->rho_min;
   S.fl.u_min = c->u_min;
@@ -328,7 +343,7 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
       KH_ALLOC(x->ctop[d], pl);
     }
     KH_ALLOC(x->emf[2], pl);
-    if (L.ndim == 3) {
+    if (L.ndim == 3 || c->bfield == KH_B_FACE) {
       KH_ALLOC(x->emf[0], pl);
       KH_ALLOC(x->emf[1], pl);
     }
@@ -352,6 +367,10 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
         KH_ALLOC(x->dirichletf[f], (size_t)NV * L.n3s * L.n2s * L.ng * sizeof(float));
   }
   KH_ALLOC(x->pflag, (size_t)L.plane);
+  if (c->bfield == KH_B_FACE) {
+    KH_ALLOC(x->fBstar, 3 * pl);
+    if (c->emf == KH_EMF_GS05) KH_ALLOC(x->ecc, 3 * pl);
+  }
   if (c->fofc) {
     KH_ALLOC(x->fflag, (size_t)L.plane);
     if (mixed) {
@@ -550,6 +569,7 @@ extern "C" {
 
 int kh_step(kh_ctx* x, double* U, double* P, double* B, double dt, double* dt_cfl) {
   if (!x || !U || !P || !B || !(dt > 0.0) || !isfinite(dt)) return KH_EINVAL;
+  if (x->S.bfield == KH_B_FACE && !x->fB) return KH_EINVAL;  // no face field registered
   // dt enters through device memory (a pageable copy: the host value may be
   // reused as soon as the call returns)
   KH_TRY(cudaMemcpyAsync(x->dscalar + 3, &dt, sizeof(double), cudaMemcpyHostToDevice, x->stream));
@@ -573,6 +593,34 @@ int kh_step(kh_ctx* x, double* U, double* P, double* B, double dt, double* dt_cf
   *dt_cfl = st.dt_cfl;
   if (!isfinite(st.dt_cfl)) return KH_ENAN;
   return (int)(st.nfail > 0x7fffffffLL ? 0x7fffffff : st.nfail);
+}
+
+int kh_set_face_field(kh_ctx* x, double* fB) {
+  if (!x || !fB || x->S.bfield != KH_B_FACE) return KH_EINVAL;
+  if (x->fB != fB) drop_graph(x);  // a captured step holds the old pointer
+  x->fB = fB;
+  if (cudaMemsetAsync(x->fBstar, 0, 3 * (size_t)x->L.plane * sizeof(double), x->stream) != cudaSuccess)
+    return KH_ECUDA;
+  return KH_OK;
+}
+
+int kh_face_to_cell(kh_ctx* x, const double* fB, double* B) {
+  if (!x || !fB || !B) return KH_EINVAL;
+  return check_launch(x, launch_face_to_cell(fB, B, x->L, devgeom(x), x->stream));
+}
+
+int kh_face_divb(kh_ctx* x, const double* fB, double* max_abs, double* l1) {
+  if (!x || !fB) return KH_EINVAL;
+  const Layout& L = x->L;
+  int rc = check_launch(x, launch_face_divb(fB, L, x->partial, x->npartial, x->dscalar + 1, x->stream));
+  if (rc != KH_OK) return rc;
+  double h[2];
+  KH_TRY(cudaMemcpyAsync(h, x->dscalar + 1, sizeof(h), cudaMemcpyDeviceToHost, x->stream));
+  KH_TRY(cudaStreamSynchronize(x->stream));
+  const double nz = (double)L.n1 * L.n2 * L.n3;
+  if (max_abs) *max_abs = h[0];
+  if (l1) *l1 = h[1] / nz;
+  return KH_OK;
 }
 
 int kh_set_graph(kh_ctx* x, int enable) {

@@ -21,6 +21,11 @@ struct kh_ctx {
   int8_t* fflag;   // first-order flux correction: flags of the current stage (one plane)
   double* fsave;   // ... and the raw field fluxes kept across the trial (3 planes per direction)
   float* fsavef;   // the same for the FP32 fluxes of KH_MIXED
+  // face-centred CT (KH_B_FACE): the caller's face field (kh_set_face_field),
+  // the stage-1 face field and the cell-centred EMFs (3 planes each)
+  double* fB;
+  double* fBstar;
+  double* ecc;
   double* partial;
   int npartial;
   double* dscalar;              // [0] dt_cfl out, [1..2] divb max/sum, [3] dt in

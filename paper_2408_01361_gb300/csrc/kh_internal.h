@@ -56,6 +56,8 @@ struct Scheme {
   double cfl;
   int recon;
   int fofc;  // first-order flux correction on
+  int bfield; // KH_B_FLUXCT | KH_B_FACE
+  int emf;    // KH_EMF_AVERAGE | KH_EMF_GS05 (face CT)
   int bc[6];
   FloorParams fl;
   C2POpts c2p;
@@ -130,7 +132,16 @@ int launch_fofc_faces(int D, const CVarsT<TIN>& P, const Layout& L, const GeomT<
 // captured step keeps working when dt changes.
 int launch_update(const double* U0, const CVars& Pin, const Vars& Pout, double* Uout, double* const F[3],
                   const Layout& L, const DevGeom& G, const Scheme& S, const double* dtp, double coef, int8_t* pflag,
-                  unsigned long long* cnt, int tpb, cudaStream_t s, FailList fl = FailList{nullptr, nullptr});
+                  unsigned long long* cnt, int tpb, cudaStream_t s, FailList fl = FailList{nullptr, nullptr},
+                  const double* fBn = nullptr);
+// Face-centred CT of one stage (S.emf: KH_EMF_AVERAGE | KH_EMF_GS05): cell
+// EMFs into ecc (GS05 only), edge EMFs from the raw fluxes F into emf[3],
+// then fBout = fB0 + coef dtp[0] curl E on the interior cells' faces.
+int launch_face_ct(const CVars& P, double* const F[3], double* ecc, double* const emf[3], const double* fB0,
+                   double* fBout, const Layout& L, const DevGeom& G, const Scheme& S, const double* dtp, double coef,
+                   cudaStream_t s);
+int launch_face_divb(const double* fB, const Layout& L, double* partial, int npartial, double* out2, cudaStream_t s);
+int launch_face_to_cell(const double* fB, double* B, const Layout& L, const DevGeom& G, cudaStream_t s);
 // Mixed update: FP32 fluxes and sources, FP64 accumulation of U and FP64
 // inversion; the stage input (sources, inversion guess) is read in FP32.
 // Writes the FP64 output (Pout64.v[0] may be null) and/or its FP32 shadow

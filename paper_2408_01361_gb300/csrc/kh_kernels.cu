@@ -216,12 +216,12 @@ __global__ void k_apply_ct(R* F1, R* F2, R* F3, const R* e1, const R* e2, const 
 __global__ void __launch_bounds__(TPB_MAX) k_update(const double* U0, CVars Pin, Vars Pout, double* Uout,
                                                    const double* F1, const double* F2, const double* F3, Layout L,
                                                    DevGeom G, Scheme S, const double* dtp, double coef, int8_t* pflag,
-                                                   unsigned long long* cnt, FailList fl) {
+                                                   unsigned long long* cnt, FailList fl, const double* fBn) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nzones(L)) return;
   int i, j, k;
   zone_ijk(L, t, i, j, k);
-  update_zone(U0, Pin, Pout, Uout, F1, F2, F3, L, G, S, coef * __ldg(dtp), pflag, cnt, i, j, k, nullptr, fl);
+  update_zone(U0, Pin, Pout, Uout, F1, F2, F3, L, G, S, coef * __ldg(dtp), pflag, cnt, i, j, k, nullptr, fl, fBn);
 }
 
 // three blocks of TPB_MAX per SM: ~80 registers (a few spill to L1); measured faster
@@ -323,6 +323,116 @@ __global__ void __launch_bounds__(TPB_MAX) k_fofc_faces(CVarsT<TIN> P, Layout L,
 }
 
 // ---------------------------------------------------------------------------
+// Face-centred constrained transport: cell EMFs, edge EMFs, face update.
+// ---------------------------------------------------------------------------
+// Active-direction extents of the box [s - lo_pad, e] (inactive x3: one cell).
+__device__ __forceinline__ void box_dims(const Layout& L, int pad, int n[3], int lo[3]) {
+  for (int q = 0; q < 3; ++q) {
+    const bool active = q < 2 || L.ndim == 3;
+    lo[q] = active ? L.s[q] - pad : 0;
+    n[q] = active ? L.e[q] - L.s[q] + 1 + pad : 1;
+  }
+}
+
+// Cell-centred EMFs of the cells [s-1, e] along every active direction.
+__global__ void __launch_bounds__(TPB) k_cell_emf(CVars P, Layout L, DevGeom G, double* ecc) {
+  int n[3], lo[3];
+  box_dims(L, 1, n, lo);
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (unsigned)n[0] * n[1] * n[2]) return;
+  int i, j, k;
+  split3(t, n[0], n[1], i, j, k);
+  i += lo[0];
+  j += lo[1];
+  k += lo[2];
+  const long long c = L.at(k, j, i);
+  double Pc[NV], E[3];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Pc[v] = P.v[v][c];
+  const Met<double> m = load_met(G, L.gplane, LOC_CENT, (long long)j * L.n1s + i);
+  cell_emfs(Pc, m, E);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) ecc[q * L.plane + c] = E[q];
+}
+
+// Edge EMFs of the edges the interior faces need (box [s, e]; along its own
+// direction an edge stays inside [s, e)); zero on a polar axis.
+__global__ void __launch_bounds__(TPB) k_face_emf(const double* F1, const double* F2, const double* F3,
+                                                 const double* ecc, double* e1, double* e2, double* e3, Layout L,
+                                                 Scheme S, int emf) {
+  int n[3], lo[3];
+  box_dims(L, 0, n, lo);
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (unsigned)n[0] * n[1] * n[2]) return;
+  int i, j, k;
+  split3(t, n[0], n[1], i, j, k);
+  i += lo[0];
+  j += lo[1];
+  k += lo[2];
+  const long long c = L.at(k, j, i);
+  const double* F[3] = {F1, F2, F3};
+  const bool axis = (S.bc[2] == KH_BC_POLAR && j == L.s[1]) || (S.bc[3] == KH_BC_POLAR && j == L.e[1]);
+  if (L.ndim == 3) {
+    if (k < L.e[2]) e3[c] = axis ? 0.0 : edge_emf<double>(2, F, ecc, L, emf, i, j, k);
+    if (i < L.e[0]) e1[c] = axis ? 0.0 : edge_emf<double>(0, F, ecc, L, emf, i, j, k);
+    if (j < L.e[1]) e2[c] = edge_emf<double>(1, F, ecc, L, emf, i, j, k);
+  } else {
+    // no x3 variation: E1 is the x2-face value F^2(B^3), E2 minus the x1-face value F^1(B^3)
+    e3[c] = axis ? 0.0 : edge_emf<double>(2, F, ecc, L, emf, i, j, k);
+    if (i < L.e[0]) e1[c] = axis ? 0.0 : F2[V_B3 * L.plane + c];
+    if (j < L.e[1]) e2[c] = -F1[V_B3 * L.plane + c];
+  }
+}
+
+// fBout = fB0 + c dt (d_b E_c - d_c E_b) on every face of the interior cells
+// (box [s, e]: a face family keeps index e only along its normal).
+__global__ void __launch_bounds__(TPB) k_face_update(const double* fB0, double* fBout, const double* e1,
+                                                    const double* e2, const double* e3, Layout L, const double* dtp,
+                                                    double coef) {
+  int n[3], lo[3];
+  box_dims(L, 0, n, lo);
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (unsigned)n[0] * n[1] * n[2]) return;
+  int x[3];
+  split3(t, n[0], n[1], x[0], x[1], x[2]);
+  for (int q = 0; q < 3; ++q) x[q] += lo[q];
+  const long long c = L.at(x[2], x[1], x[0]);
+  const long long st[3] = {1, (long long)L.n1s, (long long)L.n1s * L.n2s};
+  const double* E[3] = {e1, e2, e3};
+  const double cdt = coef * __ldg(dtp);
+  const int nd = L.ndim;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int b = (a + 1) % 3, cc = (a + 2) % 3;
+    bool in = true;
+    for (int q = 0; q < nd; ++q)
+      if (q != a && x[q] >= L.e[q]) in = false;
+    if (!in) continue;
+    double rhs = 0.0;
+    if (b < nd) rhs += (E[cc][c + st[b]] - E[cc][c]) * L.idx[b];
+    if (cc < nd) rhs -= (E[b][c + st[cc]] - E[b][c]) * L.idx[cc];
+    fBout[a * L.plane + c] = fB0[a * L.plane + c] + cdt * rhs;
+  }
+}
+
+// Face divergence of the interior cells (max |div|, sum |div|) per block.
+__global__ void __launch_bounds__(RED_THREADS) k_face_divb(const double* fB, Layout L, double* partial);
+
+// B of the interior cells = face means / sqrt(-g).
+__global__ void __launch_bounds__(TPB) k_face_to_cell(const double* fB, double* B, Layout L, DevGeom G) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nzones(L)) return;
+  int i, j, k;
+  zone_ijk(L, t, i, j, k);
+  const long long c = L.at(k, j, i);
+  double UB[3];
+  face_means(fB, L, c, UB);
+  const double gd = __ldg(G.g + (long long)LOC_CENT * NGEO * L.gplane + 20 * L.gplane + (long long)j * L.n1s + i);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) B[q * L.plane + c] = UB[q] / gd;
+}
+
+// ---------------------------------------------------------------------------
 // Reductions: warp shuffles, then shared memory, then one block over partials.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double warp_max(double x) {
@@ -405,6 +515,26 @@ __global__ void __launch_bounds__(RED_THREADS) k_divb(const double* B1, const do
     const double dv = divb_corner(B1, B2, B3, L, gd, i, j, k);
     mx = fmax(mx, fabs(dv));
     sm += fabs(dv);
+  }
+  block_max_sum(mx, sm);
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = mx;
+    partial[2 * blockIdx.x + 1] = sm;
+  }
+}
+
+__global__ void __launch_bounds__(RED_THREADS) k_face_divb(const double* fB, Layout L, double* partial) {
+  const long long tot = nzones(L);
+  const long long P = L.plane, sj = L.n1s, sk = (long long)L.n1s * L.n2s;
+  double mx = 0.0, sm = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    zone_ijk(L, (unsigned)t, i, j, k);
+    const long long c = L.at(k, j, i);
+    double d = (fB[c + 1] - fB[c]) * L.idx[0] + (fB[P + c + sj] - fB[P + c]) * L.idx[1];
+    if (L.ndim == 3) d += (fB[2 * P + c + sk] - fB[2 * P + c]) * L.idx[2];
+    mx = fmax(mx, fabs(d));
+    sm += fabs(d);
   }
   block_max_sum(mx, sm);
   if (threadIdx.x == 0) {
@@ -588,10 +718,10 @@ template int launch_ct<float>(float* const[3], float* const[3], const Layout&, c
 
 int launch_update(const double* U0, const CVars& Pin, const Vars& Pout, double* Uout, double* const F[3],
                   const Layout& L, const DevGeom& G, const Scheme& S, const double* dtp, double coef, int8_t* pflag,
-                  unsigned long long* cnt, int tpb, cudaStream_t s, FailList fl) {
+                  unsigned long long* cnt, int tpb, cudaStream_t s, FailList fl, const double* fBn) {
   const long long nz = (long long)L.n1 * L.n2 * L.n3;
   k_update<<<nblocks(nz, tpb), tpb, 0, s>>>(U0, Pin, Pout, Uout, F[0], F[1], F[2], L, G, S, dtp, coef, pflag, cnt,
-                                            fl);
+                                            fl, fBn);
   return 1;
 }
 
@@ -681,6 +811,38 @@ int launch_divb(const double* const B[3], const Layout& L, const DevGeom& G, dou
   k_divb<<<npartial, RED_THREADS, 0, s>>>(B[0], B[1], B[2], L, G, partial);
   k_finish<<<1, RED_THREADS, 0, s>>>(partial, npartial, 0.0, 1, out2);
   return 2;
+}
+
+static long long box_count(const Layout& L, int pad) {
+  long long t = 1;
+  for (int q = 0; q < 3; ++q) t *= (q < 2 || L.ndim == 3) ? (long long)(L.e[q] - L.s[q] + 1 + pad) : 1LL;
+  return t;
+}
+
+int launch_face_ct(const CVars& P, double* const F[3], double* ecc, double* const emf[3], const double* fB0,
+                   double* fBout, const Layout& L, const DevGeom& G, const Scheme& S, const double* dtp, double coef,
+                   cudaStream_t s) {
+  int n = 0;
+  if (S.emf == KH_EMF_GS05) {
+    k_cell_emf<<<nblocks(box_count(L, 1), TPB), TPB, 0, s>>>(P, L, G, ecc);
+    ++n;
+  }
+  const long long tot = box_count(L, 0);
+  k_face_emf<<<nblocks(tot, TPB), TPB, 0, s>>>(F[0], F[1], F[2], ecc, emf[0], emf[1], emf[2], L, S, S.emf);
+  k_face_update<<<nblocks(tot, TPB), TPB, 0, s>>>(fB0, fBout, emf[0], emf[1], emf[2], L, dtp, coef);
+  return n + 2;
+}
+
+int launch_face_divb(const double* fB, const Layout& L, double* partial, int npartial, double* out2, cudaStream_t s) {
+  k_face_divb<<<npartial, RED_THREADS, 0, s>>>(fB, L, partial);
+  k_finish<<<1, RED_THREADS, 0, s>>>(partial, npartial, 0.0, 1, out2);
+  return 2;
+}
+
+int launch_face_to_cell(const double* fB, double* B, const Layout& L, const DevGeom& G, cudaStream_t s) {
+  const long long nz = (long long)L.n1 * L.n2 * L.n3;
+  k_face_to_cell<<<nblocks(nz, TPB), TPB, 0, s>>>(fB, B, L, G);
+  return 1;
 }
 
 int launch_p2c(const CVars& P, double* U, const Layout& L, const DevGeom& G, const Scheme& S, cudaStream_t s) {

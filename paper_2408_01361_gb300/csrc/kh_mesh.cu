@@ -504,6 +504,7 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
   if (c->precision != KH_FP64 && c->precision != KH_MIXED) return KH_EINVAL;
   if (c->recon != KH_RECON_MC && c->recon != KH_RECON_WENO5) return KH_EINVAL;
   if (c->fofc) return KH_EINVAL;  // the flux correction runs on single grids
+  if (c->bfield != KH_B_FLUXCT) return KH_EINVAL;  // face-centred CT: single grids
   if (!(gamma > 1.0) || !(c->cfl > 0.0) || !(fabs(a) < 1.0)) return KH_EINVAL;
   for (int q = 0; q < 6; ++q) {
     const int b = c->bc[q];

@@ -275,6 +275,68 @@ __device__ __forceinline__ void source_terms(const R* P, const Met<M>& m, const 
 // FP64 update of interior zone (k, j, i): U = U0 + cdt (-div F + S(Pin)),
 // Noble-2D inversion with Pin as the guess, floors; writes Pout, pflag and
 // (stage 2) U.
+// ---------------------------------------------------------------------------
+// Face-centred constrained transport (Stone & Gardiner 2009; edge EMFs after
+// Gardiner & Stone 2005). Face field fB: planes [3][n3s][n2s][n1s], plane a =
+// sqrt(-g) B^(a+1) on the lower x^(a+1) face of each cell (a 2-D grid keeps
+// sqrt(-g) B^3 per cell). Edge EMF along x^c, with (a, b, c) cyclic:
+// E_c = F^a(B^b) = -F^b(B^a), stored at the cell whose lower x^a and x^b
+// faces bound the edge; d/dt (sqrt(-g) B^a) = d_b E_c - d_c E_b.
+// ---------------------------------------------------------------------------
+
+// sqrt(-g) B of cell c: the mean of its two faces per direction.
+template <class T>
+__device__ __forceinline__ void face_means(const T* fB, const Layout& L, long long c, T* UB) {
+  const long long P = L.plane, sj = L.n1s, sk = (long long)L.n1s * L.n2s;
+  UB[0] = T(0.5) * (fB[c] + fB[c + 1]);
+  UB[1] = T(0.5) * (fB[P + c] + fB[P + c + sj]);
+  UB[2] = L.ndim == 3 ? T(0.5) * (fB[2 * P + c] + fB[2 * P + c + sk]) : fB[2 * P + c];
+}
+
+// Cell-centred EMFs of one cell: E[c] = sqrt(-g) (b^b u^a - b^a u^b).
+template <class R, class M>
+__device__ __forceinline__ void cell_emfs(const R* P, const Met<M>& m, R* E) {
+  FState<R> s;
+  fluid_state(P, m, s);
+  E[0] = R(m.gdet) * (s.bcon[3] * s.ucon[2] - s.bcon[2] * s.ucon[3]);
+  E[1] = R(m.gdet) * (s.bcon[1] * s.ucon[3] - s.bcon[3] * s.ucon[1]);
+  E[2] = R(m.gdet) * (s.bcon[2] * s.ucon[1] - s.bcon[1] * s.ucon[2]);
+}
+
+// Upwind choice across a face: the lower cell's value for a positive mass
+// flux, the upper's for a negative one, their mean for zero.
+template <class R> __device__ __forceinline__ R upwind(R mflux, R lower, R upper) {
+  return mflux > R(0) ? lower : (mflux < R(0) ? upper : R(0.5) * (lower + upper));
+}
+
+// E_c at the edge of cell (k, j, i) from the raw face fluxes F (8 planes per
+// direction) and, for GS05, the cell-centred EMFs ecc (3 planes): the mean of
+// the four face values, plus (GS05) the differences of the half-zone
+// derivatives of E towards the edge, each from the cell upwind of the mass
+// flux through the face it belongs to.
+template <class R>
+__device__ __forceinline__ R edge_emf(int c, const R* const F[3], const R* ecc, const Layout& L, int emf, int i,
+                                      int j, int k) {
+  const int a = (c + 1) % 3, b = (c + 2) % 3;
+  const long long st[3] = {1, (long long)L.n1s, (long long)L.n1s * L.n2s};
+  const long long P = L.plane;
+  const long long x = L.at(k, j, i), xa = x - st[a], xb = x - st[b], xab = xa - st[b];
+  const R* Fa = F[a];
+  const R* Fb = F[b];
+  const R Ea_hi = Fa[(V_B1 + b) * P + x], Ea_lo = Fa[(V_B1 + b) * P + xb];
+  const R Eb_hi = -Fb[(V_B1 + a) * P + x], Eb_lo = -Fb[(V_B1 + a) * P + xa];
+  R e = R(0.25) * ((Ea_hi + Ea_lo) + (Eb_hi + Eb_lo));
+  if (emf == KH_EMF_GS05) {
+    const R* C = ecc + c * P;
+    const R db_hi = upwind(Fa[x], C[xa] - Eb_lo, C[x] - Eb_hi);
+    const R db_lo = upwind(Fa[xb], Eb_lo - C[xab], Eb_hi - C[xb]);
+    const R da_hi = upwind(Fb[x], C[xb] - Ea_lo, C[x] - Ea_hi);
+    const R da_lo = upwind(Fb[xa], Ea_lo - C[xab], Ea_hi - C[xa]);
+    e += R(0.25) * ((db_lo - db_hi) + (da_lo - da_hi));
+  }
+  return e;
+}
+
 // TRIAL (first-order flux correction): the same update, inversion and floors,
 // but only the zone's flag is written: pflag[c] = 1 if the inversion failed or
 // a floor acted, else 0 (flagged zones counted in CNT_FOFC); Pout, Uout and
@@ -284,7 +346,7 @@ __device__ __forceinline__ void update_zone(const double* U0, const CVars& Pin, 
                                             const double* F1, const double* F2, const double* F3, const Layout& L,
                                             const DevGeom& G, const Scheme& S, double cdt, int8_t* pflag,
                                             unsigned long long* cnt, int i, int j, int k, double* Praw = nullptr,
-                                            FailList fl = FailList{nullptr, nullptr}) {
+                                            FailList fl = FailList{nullptr, nullptr}, const double* fBn = nullptr) {
   const long long c = L.at(k, j, i);
   const long long p = (long long)j * L.n1s + i;
   const long long sj = L.n1s, sk = (long long)L.n1s * L.n2s;
@@ -302,6 +364,7 @@ __device__ __forceinline__ void update_zone(const double* U0, const CVars& Pin, 
     if (L.ndim == 3) div += (F3[o + sk] - F3[o]) * L.idx[2];
     U[v] = U0[o] + cdt * (-div + Sv[v]);
   }
+  if (fBn) face_means(fBn, L, c, U + V_B1);  // face-centred CT: sqrt(-g) B from the updated faces
   double Pn[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) Pn[v] = P[v];

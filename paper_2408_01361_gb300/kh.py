@@ -25,6 +25,8 @@ KIND = {"minkowski": MINKOWSKI, "ks": KS, "mks": MKS, "fmks": FMKS}
 BC = {"periodic": 0, "outflow": 1, "polar": 2, "dirichlet": 3}
 RECON = {"mc": 0, "weno5": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
+BFIELD = {"fluxct": 0, "face": 1}
+EMF = {"average": 0, "gs05": 1}
 ERRORS = {0: "KH_OK", -1: "KH_EINVAL", -2: "KH_ECUDA", -3: "KH_ENOMEM", -4: "KH_ETIMEOUT", -5: "KH_ENAN"}
 
 
@@ -42,6 +44,7 @@ class Coords(C.Structure):
         ("cfl", C.c_double), ("rho_min", C.c_double), ("u_min", C.c_double), ("bsq_rho_max", C.c_double),
         ("bsq_u_max", C.c_double), ("u_rho_max", C.c_double), ("gamma_max", C.c_double),
         ("newton_max_iter", C.c_int), ("newton_tol", C.c_double), ("fofc", C.c_int),
+        ("bfield", C.c_int), ("emf", C.c_int),
     ]
 
 
@@ -75,6 +78,9 @@ def lib():
         L.kh_step.argtypes = [vp, vp, vp, vp, C.c_double, dp]
         L.kh_cfl_dt.argtypes = [vp, vp, vp, dp]
         L.kh_divb.argtypes = [vp, vp, dp, dp]
+        L.kh_set_face_field.argtypes = [vp, vp]
+        L.kh_face_to_cell.argtypes = [vp, vp, vp]
+        L.kh_face_divb.argtypes = [vp, vp, dp, dp]
         L.kh_fluxes.argtypes = [vp, vp, vp, vp, vp, vp]
         L.kh_fill_ghosts.argtypes = [vp, vp, vp]
         L.kh_get_stats.argtypes = [vp, C.POINTER(Stats)]
@@ -144,6 +150,8 @@ def coords_from_cfg(cfg: dict) -> Coords:
     c.newton_max_iter = cfg.get("newton_max_iter", 30)
     c.newton_tol = cfg.get("newton_tol", 1e-14)
     c.fofc = 1 if cfg.get("fofc") else 0
+    c.bfield = BFIELD[cfg.get("bfield", "fluxct")]
+    c.emf = EMF[cfg.get("emf", "gs05")]
     return c
 
 
@@ -241,6 +249,21 @@ class Context:
     def divb(self, B):
         mx, l1 = C.c_double(), C.c_double()
         _check(lib().kh_divb(self._h, _ptr(B), C.byref(mx), C.byref(l1)), "kh_divb")
+        return mx.value, l1.value
+
+    # ---- face-centred constrained transport ----
+    def set_face_field(self, fB):
+        """Register the face field (3 planes, kept by the caller) that kh_step
+        advances (bfield "face")."""
+        self._fB = fB
+        _check(lib().kh_set_face_field(self._h, _ptr(fB)), "kh_set_face_field")
+
+    def face_to_cell(self, fB, B):
+        _check(lib().kh_face_to_cell(self._h, _ptr(fB), _ptr(B)), "kh_face_to_cell")
+
+    def face_divb(self, fB):
+        mx, l1 = C.c_double(), C.c_double()
+        _check(lib().kh_face_divb(self._h, _ptr(fB), C.byref(mx), C.byref(l1)), "kh_face_divb")
         return mx.value, l1.value
 
     def fluxes(self, P, B, F1, F2, F3=None):

@@ -52,3 +52,22 @@ def test_argument_validation_without_gpu():
     c = kh.coords_from_cfg(dict(cfg, fofc=True))
     assert kh.lib().kh_mesh_init(0.0, ctypes.byref(c), float(cfg["gam"]), 1, ctypes.byref(blk),
                                  ctypes.byref(h)) == -1
+
+
+def test_face_ct_validation_without_gpu():
+    """Face-centred CT is refused with mixed precision, with the flux
+    correction, on a mesh, and with unknown scheme values."""
+    from paper_2408_01361_gb300 import inputs, kh
+    cfg = dict(inputs.linear_mode_cfg(8, ndim=3), bfield="face")
+    h = ctypes.c_void_p()
+    for over in (dict(precision="mixed"), dict(fofc=True)):
+        c = kh.coords_from_cfg(dict(cfg, **over))
+        assert kh.lib().kh_geometry_init(0.0, ctypes.byref(c), float(cfg["gam"]), ctypes.byref(h)) == -1
+    for field, value in (("bfield", 2), ("emf", 2)):
+        c = kh.coords_from_cfg(cfg)
+        setattr(c, field, value)
+        assert kh.lib().kh_geometry_init(0.0, ctypes.byref(c), float(cfg["gam"]), ctypes.byref(h)) == -1
+    blk = kh.Block(0, 0, 0, 0, 8, 8, 8)
+    c = kh.coords_from_cfg(cfg)
+    assert kh.lib().kh_mesh_init(0.0, ctypes.byref(c), float(cfg["gam"]), 1, ctypes.byref(blk),
+                                 ctypes.byref(h)) == -1
