@@ -84,7 +84,9 @@ typedef struct {
                              d_b E_c - d_c E_b, which keeps every cell's face
                              divergence; B of a zone is the mean of its two faces
                              over sqrt(-g). Edge EMFs on a polar axis are zero.
-                             Single-grid FP64 contexts; no flux correction. */
+                             Single-grid contexts (KH_MIXED: FP32 EMFs, the face
+                             field and its increments accumulated in FP64); no flux
+                             correction. */
   int emf;                /* KH_B_FACE edge EMFs: KH_EMF_AVERAGE (mean of the four
                              face values; with face means as the zone field this is
                              Flux-CT) or KH_EMF_GS05 (Gardiner & Stone 2005: plus the

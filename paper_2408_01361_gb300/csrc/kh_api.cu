@@ -82,7 +82,7 @@ void free_all(kh_ctx* x) {
                   x->counters, x->dirichlet[0], x->dirichlet[1], x->geof, x->dgmf, x->pstarf, x->pnf, x->Ff[0],
                   x->Ff[1], x->Ff[2], x->ctopf[0], x->ctopf[1], x->ctopf[2], x->emff[0], x->emff[1],
                   x->emff[2], x->dirichletf[0], x->dirichletf[1], x->adj, x->adj_i8, x->adj_red, x->geodf, x->flist,
-                  x->fflag, x->fsave, x->fsavef, x->fBstar, x->ecc};
+                  x->fflag, x->fsave, x->fsavef, x->fBstar, x->ecc, x->eccf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -115,7 +115,7 @@ int run_stage(kh_ctx* x, int st, const double* U0, const Vars& Pin, const Vars& 
     // the update takes the zones' field from the new faces
     fBn = st == 0 ? x->fBstar : x->fB;
     mark(x, KH_T_CT, st, 0);
-    n += launch_face_ct(cview(Pin), x->F, x->ecc, x->emf, x->fB, fBn, L, G, x->S, x->dscalar + 3, coef, s);
+    n += launch_face_ct<double>(cview(Pin), x->F, x->ecc, x->emf, x->fB, fBn, L, G, x->S, x->dscalar + 3, coef, s);
     mark(x, KH_T_CT, st, 1);
   } else {
     mark(x, KH_T_CT, st, 0);
@@ -192,8 +192,16 @@ int run_stage_mixed(kh_ctx* x, int st, const double* U0, const VarsT<TIN>& Pin, 
     for (int d = 0; d < L.ndim; ++d)
       cudaMemcpyAsync(x->fsavef + 3 * d * L.plane, x->Ff[d] + V_B1 * L.plane, b3, cudaMemcpyDeviceToDevice, s);
   }
+  double* fBn = nullptr;
   mark(x, KH_T_CT, st, 0);
-  n += launch_ct<float>(x->Ff, x->emff, L, s);
+  if (x->S.bfield == KH_B_FACE) {
+    // face-centred CT: FP32 EMFs, FP64 face field
+    fBn = st == 0 ? x->fBstar : x->fB;
+    n += launch_face_ct<float>(cviewT(Pf), x->Ff, x->eccf, x->emff, x->fB, fBn, L, Gf, x->S, x->dscalar + 3, coef,
+                               s);
+  } else {
+    n += launch_ct<float>(x->Ff, x->emff, L, s);
+  }
   mark(x, KH_T_CT, st, 1);
   if (x->S.fofc) {
     // first-order flux correction (as in run_stage), FP32 fluxes
@@ -212,7 +220,7 @@ int run_stage_mixed(kh_ctx* x, int st, const double* U0, const VarsT<TIN>& Pin, 
   mark(x, KH_T_UPDATE, st, 0);
   const FailList fl{x->flist, x->counters + CNT_LIST0 + st};
   n += launch_update_mixed(U0, cviewT(Pf), Pout64, Pout32, Uout, x->Ff, L, G, Gf, x->S, x->dscalar + 3, coef,
-                           x->pflag, x->counters, x->tpb_update, s, fl);
+                           x->pflag, x->counters, x->tpb_update, s, fl, fBn);
   mark(x, KH_T_UPDATE, st, 1);
   mark(x, KH_T_FIXUP, st, 0);
   if (Pout64.v[0])
@@ -248,7 +256,7 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
   if (c->fofc != 0 && c->fofc != 1) return KH_EINVAL;
   if (c->bfield != KH_B_FLUXCT && c->bfield != KH_B_FACE) return KH_EINVAL;
   if (c->emf != KH_EMF_AVERAGE && c->emf != KH_EMF_GS05) return KH_EINVAL;
-  if (c->bfield == KH_B_FACE && (c->precision != KH_FP64 || c->fofc)) return KH_EINVAL;
+  if (c->bfield == KH_B_FACE && c->fofc) return KH_EINVAL;
   if (!(gamma > 1.0) || !(c->cfl > 0.0) || !(fabs(a) < 1.0)) return KH_EINVAL;
   if (!(c->x1max > c->x1min) || !(c->x2max > c->x2min) || !(c->x3max > c->x3min)) return KH_EINVAL;
   for (int q = 0; q < 6; ++q) {
@@ -358,7 +366,7 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
       KH_ALLOC(x->ctopf[d], plf);
     }
     KH_ALLOC(x->emff[2], plf);
-    if (L.ndim == 3) {
+    if (L.ndim == 3 || c->bfield == KH_B_FACE) {
       KH_ALLOC(x->emff[0], plf);
       KH_ALLOC(x->emff[1], plf);
     }
@@ -369,7 +377,13 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
   KH_ALLOC(x->pflag, (size_t)L.plane);
   if (c->bfield == KH_B_FACE) {
     KH_ALLOC(x->fBstar, 3 * pl);
-    if (c->emf == KH_EMF_GS05) KH_ALLOC(x->ecc, 3 * pl);
+    if (c->emf == KH_EMF_GS05) {
+      if (mixed) {
+        KH_ALLOC(x->eccf, 3 * plf);
+      } else {
+        KH_ALLOC(x->ecc, 3 * pl);
+      }
+    }
   }
   if (c->fofc) {
     KH_ALLOC(x->fflag, (size_t)L.plane);

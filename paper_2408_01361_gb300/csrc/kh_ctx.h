@@ -26,6 +26,7 @@ struct kh_ctx {
   double* fB;
   double* fBstar;
   double* ecc;
+  float* eccf;     // the cell-centred EMFs of KH_MIXED (FP32)
   double* partial;
   int npartial;
   double* dscalar;              // [0] dt_cfl out, [1..2] divb max/sum, [3] dt in

@@ -137,8 +137,10 @@ int launch_update(const double* U0, const CVars& Pin, const Vars& Pout, double* 
 // Face-centred CT of one stage (S.emf: KH_EMF_AVERAGE | KH_EMF_GS05): cell
 // EMFs into ecc (GS05 only), edge EMFs from the raw fluxes F into emf[3],
 // then fBout = fB0 + coef dtp[0] curl E on the interior cells' faces.
-int launch_face_ct(const CVars& P, double* const F[3], double* ecc, double* const emf[3], const double* fB0,
-                   double* fBout, const Layout& L, const DevGeom& G, const Scheme& S, const double* dtp, double coef,
+// R = float (mixed): FP32 stage input, fluxes and EMFs, FP64 face field.
+template <class R>
+int launch_face_ct(const CVarsT<R>& P, R* const F[3], R* ecc, R* const emf[3], const double* fB0, double* fBout,
+                   const Layout& L, const GeomT<R>& G, const Scheme& S, const double* dtp, double coef,
                    cudaStream_t s);
 int launch_face_divb(const double* fB, const Layout& L, double* partial, int npartial, double* out2, cudaStream_t s);
 int launch_face_to_cell(const double* fB, double* B, const Layout& L, const DevGeom& G, cudaStream_t s);
@@ -149,7 +151,8 @@ int launch_face_to_cell(const double* fB, double* B, const Layout& L, const DevG
 int launch_update_mixed(const double* U0, const CVarsT<float>& Pin, const Vars& Pout64, const VarsT<float>& Pout32,
                         double* Uout, float* const F[3], const Layout& L, const DevGeom& G, const GeomT<float>& Gf,
                         const Scheme& S, const double* dtp, double coef, int8_t* pflag, unsigned long long* cnt,
-                        int tpb, cudaStream_t s, FailList fl = FailList{nullptr, nullptr});
+                        int tpb, cudaStream_t s, FailList fl = FailList{nullptr, nullptr},
+                        const double* fBn = nullptr);
 // Fixup over every zone, or (fl.idx != nullptr) over the stage's failed-zone list.
 template <class T>
 int launch_fixup(const VarsT<T>& P, double* Uout, const int8_t* pflag, const Layout& L, const DevGeom& G,

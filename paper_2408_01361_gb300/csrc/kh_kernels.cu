@@ -230,13 +230,14 @@ __global__ void __launch_bounds__(TPB_MAX, 3) k_update_mixed(const double* U0, C
                                                          VarsT<float> Pout32, double* Uout, const float* F1,
                                                          const float* F2, const float* F3, Layout L, DevGeom G,
                                                          GeomT<float> Gf, Scheme S, const double* dtp, double coef,
-                                                         int8_t* pflag, unsigned long long* cnt, FailList fl) {
+                                                         int8_t* pflag, unsigned long long* cnt, FailList fl,
+                                                         const double* fBn) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nzones(L)) return;
   int i, j, k;
   zone_ijk(L, t, i, j, k);
   update_mixed_zone(U0, Pin, Pout64, Pout32, Uout, F1, F2, F3, L, G, Gf, S, df_of_f64(coef * __ldg(dtp)), pflag, cnt, i,
-                    j, k, fl);
+                    j, k, fl, fBn);
 }
 
 template <class T>
@@ -335,7 +336,8 @@ __device__ __forceinline__ void box_dims(const Layout& L, int pad, int n[3], int
 }
 
 // Cell-centred EMFs of the cells [s-1, e] along every active direction.
-__global__ void __launch_bounds__(TPB) k_cell_emf(CVars P, Layout L, DevGeom G, double* ecc) {
+template <class R>
+__global__ void __launch_bounds__(TPB) k_cell_emf(CVarsT<R> P, Layout L, GeomT<R> G, R* ecc) {
   int n[3], lo[3];
   box_dims(L, 1, n, lo);
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -346,10 +348,10 @@ __global__ void __launch_bounds__(TPB) k_cell_emf(CVars P, Layout L, DevGeom G, 
   j += lo[1];
   k += lo[2];
   const long long c = L.at(k, j, i);
-  double Pc[NV], E[3];
+  R Pc[NV], E[3];
 #pragma unroll
   for (int v = 0; v < NV; ++v) Pc[v] = P.v[v][c];
-  const Met<double> m = load_met(G, L.gplane, LOC_CENT, (long long)j * L.n1s + i);
+  const Met<R> m = load_met(G, L.gplane, LOC_CENT, (long long)j * L.n1s + i);
   cell_emfs(Pc, m, E);
 #pragma unroll
   for (int q = 0; q < 3; ++q) ecc[q * L.plane + c] = E[q];
@@ -357,9 +359,9 @@ __global__ void __launch_bounds__(TPB) k_cell_emf(CVars P, Layout L, DevGeom G, 
 
 // Edge EMFs of the edges the interior faces need (box [s, e]; along its own
 // direction an edge stays inside [s, e)); zero on a polar axis.
-__global__ void __launch_bounds__(TPB) k_face_emf(const double* F1, const double* F2, const double* F3,
-                                                 const double* ecc, double* e1, double* e2, double* e3, Layout L,
-                                                 Scheme S, int emf) {
+template <class R>
+__global__ void __launch_bounds__(TPB) k_face_emf(const R* F1, const R* F2, const R* F3, const R* ecc, R* e1, R* e2,
+                                                 R* e3, Layout L, Scheme S, int emf) {
   int n[3], lo[3];
   box_dims(L, 0, n, lo);
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -370,25 +372,29 @@ __global__ void __launch_bounds__(TPB) k_face_emf(const double* F1, const double
   j += lo[1];
   k += lo[2];
   const long long c = L.at(k, j, i);
-  const double* F[3] = {F1, F2, F3};
+  const R* F[3] = {F1, F2, F3};
   const bool axis = (S.bc[2] == KH_BC_POLAR && j == L.s[1]) || (S.bc[3] == KH_BC_POLAR && j == L.e[1]);
   if (L.ndim == 3) {
-    if (k < L.e[2]) e3[c] = axis ? 0.0 : edge_emf<double>(2, F, ecc, L, emf, i, j, k);
-    if (i < L.e[0]) e1[c] = axis ? 0.0 : edge_emf<double>(0, F, ecc, L, emf, i, j, k);
-    if (j < L.e[1]) e2[c] = edge_emf<double>(1, F, ecc, L, emf, i, j, k);
+    if (k < L.e[2]) e3[c] = axis ? R(0) : edge_emf<R>(2, F, ecc, L, emf, i, j, k);
+    if (i < L.e[0]) e1[c] = axis ? R(0) : edge_emf<R>(0, F, ecc, L, emf, i, j, k);
+    if (j < L.e[1]) e2[c] = edge_emf<R>(1, F, ecc, L, emf, i, j, k);
   } else {
     // no x3 variation: E1 is the x2-face value F^2(B^3), E2 minus the x1-face value F^1(B^3)
-    e3[c] = axis ? 0.0 : edge_emf<double>(2, F, ecc, L, emf, i, j, k);
-    if (i < L.e[0]) e1[c] = axis ? 0.0 : F2[V_B3 * L.plane + c];
+    e3[c] = axis ? R(0) : edge_emf<R>(2, F, ecc, L, emf, i, j, k);
+    if (i < L.e[0]) e1[c] = axis ? R(0) : F2[V_B3 * L.plane + c];
     if (j < L.e[1]) e2[c] = -F1[V_B3 * L.plane + c];
   }
 }
 
 // fBout = fB0 + c dt (d_b E_c - d_c E_b) on every face of the interior cells
-// (box [s, e]: a face family keeps index e only along its normal).
-__global__ void __launch_bounds__(TPB) k_face_update(const double* fB0, double* fBout, const double* e1,
-                                                    const double* e2, const double* e3, Layout L, const double* dtp,
-                                                    double coef) {
+// (box [s, e]: a face family keeps index e only along its normal). The curl
+// is formed in FP64 also from FP32 EMFs (converted exactly, by integer
+// operations): the face divergence of the increments then cancels to FP64
+// rounding, as on the FP64 path (an FP32 curl would leave FP32-sized
+// divergence each step). A few FP64 operations per face.
+template <class R>
+__global__ void __launch_bounds__(TPB) k_face_update(const double* fB0, double* fBout, const R* e1, const R* e2,
+                                                    const R* e3, Layout L, const double* dtp, double coef) {
   int n[3], lo[3];
   box_dims(L, 0, n, lo);
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -398,7 +404,7 @@ __global__ void __launch_bounds__(TPB) k_face_update(const double* fB0, double* 
   for (int q = 0; q < 3; ++q) x[q] += lo[q];
   const long long c = L.at(x[2], x[1], x[0]);
   const long long st[3] = {1, (long long)L.n1s, (long long)L.n1s * L.n2s};
-  const double* E[3] = {e1, e2, e3};
+  const R* E[3] = {e1, e2, e3};
   const double cdt = coef * __ldg(dtp);
   const int nd = L.ndim;
 #pragma unroll
@@ -408,9 +414,13 @@ __global__ void __launch_bounds__(TPB) k_face_update(const double* fB0, double* 
     for (int q = 0; q < nd; ++q)
       if (q != a && x[q] >= L.e[q]) in = false;
     if (!in) continue;
+    auto f64 = [](R v) -> double {
+      if constexpr (sizeof(R) == sizeof(double)) return v;
+      else return f64_of_f32(v);
+    };
     double rhs = 0.0;
-    if (b < nd) rhs += (E[cc][c + st[b]] - E[cc][c]) * L.idx[b];
-    if (cc < nd) rhs -= (E[b][c + st[cc]] - E[b][c]) * L.idx[cc];
+    if (b < nd) rhs += (f64(E[cc][c + st[b]]) - f64(E[cc][c])) * L.idx[b];
+    if (cc < nd) rhs -= (f64(E[b][c + st[cc]]) - f64(E[b][c])) * L.idx[cc];
     fBout[a * L.plane + c] = fB0[a * L.plane + c] + cdt * rhs;
   }
 }
@@ -728,10 +738,10 @@ int launch_update(const double* U0, const CVars& Pin, const Vars& Pout, double* 
 int launch_update_mixed(const double* U0, const CVarsT<float>& Pin, const Vars& Pout64, const VarsT<float>& Pout32,
                         double* Uout, float* const F[3], const Layout& L, const DevGeom& G, const GeomT<float>& Gf,
                         const Scheme& S, const double* dtp, double coef, int8_t* pflag, unsigned long long* cnt,
-                        int tpb, cudaStream_t s, FailList fl) {
+                        int tpb, cudaStream_t s, FailList fl, const double* fBn) {
   const long long nz = (long long)L.n1 * L.n2 * L.n3;
   k_update_mixed<<<nblocks(nz, tpb), tpb, 0, s>>>(U0, Pin, Pout64, Pout32, Uout, F[0], F[1], F[2], L, G, Gf, S, dtp,
-                                                  coef, pflag, cnt, fl);
+                                                  coef, pflag, cnt, fl, fBn);
   return 1;
 }
 
@@ -819,19 +829,26 @@ static long long box_count(const Layout& L, int pad) {
   return t;
 }
 
-int launch_face_ct(const CVars& P, double* const F[3], double* ecc, double* const emf[3], const double* fB0,
-                   double* fBout, const Layout& L, const DevGeom& G, const Scheme& S, const double* dtp, double coef,
+template <class R>
+int launch_face_ct(const CVarsT<R>& P, R* const F[3], R* ecc, R* const emf[3], const double* fB0, double* fBout,
+                   const Layout& L, const GeomT<R>& G, const Scheme& S, const double* dtp, double coef,
                    cudaStream_t s) {
   int n = 0;
   if (S.emf == KH_EMF_GS05) {
-    k_cell_emf<<<nblocks(box_count(L, 1), TPB), TPB, 0, s>>>(P, L, G, ecc);
+    k_cell_emf<R><<<nblocks(box_count(L, 1), TPB), TPB, 0, s>>>(P, L, G, ecc);
     ++n;
   }
   const long long tot = box_count(L, 0);
-  k_face_emf<<<nblocks(tot, TPB), TPB, 0, s>>>(F[0], F[1], F[2], ecc, emf[0], emf[1], emf[2], L, S, S.emf);
-  k_face_update<<<nblocks(tot, TPB), TPB, 0, s>>>(fB0, fBout, emf[0], emf[1], emf[2], L, dtp, coef);
+  k_face_emf<R><<<nblocks(tot, TPB), TPB, 0, s>>>(F[0], F[1], F[2], ecc, emf[0], emf[1], emf[2], L, S, S.emf);
+  k_face_update<R><<<nblocks(tot, TPB), TPB, 0, s>>>(fB0, fBout, emf[0], emf[1], emf[2], L, dtp, coef);
   return n + 2;
 }
+template int launch_face_ct<double>(const CVarsT<double>&, double* const[3], double*, double* const[3],
+                                    const double*, double*, const Layout&, const GeomT<double>&, const Scheme&,
+                                    const double*, double, cudaStream_t);
+template int launch_face_ct<float>(const CVarsT<float>&, float* const[3], float*, float* const[3], const double*,
+                                   double*, const Layout&, const GeomT<float>&, const Scheme&, const double*, double,
+                                   cudaStream_t);
 
 int launch_face_divb(const double* fB, const Layout& L, double* partial, int npartial, double* out2, cudaStream_t s) {
   k_face_divb<<<npartial, RED_THREADS, 0, s>>>(fB, L, partial);

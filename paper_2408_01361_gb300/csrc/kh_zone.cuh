@@ -428,7 +428,8 @@ __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT
                                                   const float* F2, const float* F3, const Layout& L, const DevGeom& G,
                                                   const GeomT<float>& Gf, const Scheme& S, df64 cdt, int8_t* pflag,
                                                   unsigned long long* cnt, int i, int j, int k,
-                                                  FailList fl = FailList{nullptr, nullptr}) {
+                                                  FailList fl = FailList{nullptr, nullptr},
+                                                  const double* fBn = nullptr) {
   const long long c = L.at(k, j, i);
   const long long p = (long long)j * L.n1s + i;
   const long long sj = L.n1s, sk = (long long)L.n1s * L.n2s;
@@ -461,6 +462,15 @@ __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT
       const double u0 = U0[o];
       if (Uout) Uout[o] = u0 + f64_of_f32(inc);    // the conserved update, FP64
       Ud[v] = df_of_f64(u0) + inc;
+    }
+  }
+  if (fBn) {  // face-centred CT: sqrt(-g) B from the updated faces (FP64 means)
+    double UB[3];
+    face_means(fBn, L, c, UB);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      if (Uout) Uout[(V_B1 + q) * L.plane + c] = UB[q];
+      Ud[V_B1 + q] = df_of_f64(UB[q]);
     }
   }
   const MetDF md = load_metdf(Gf.df, L.gplane, p);

@@ -55,12 +55,12 @@ def test_argument_validation_without_gpu():
 
 
 def test_face_ct_validation_without_gpu():
-    """Face-centred CT is refused with mixed precision, with the flux
-    correction, on a mesh, and with unknown scheme values."""
+    """Face-centred CT is refused with the flux correction, on a mesh, and
+    with unknown scheme values."""
     from paper_2408_01361_gb300 import inputs, kh
     cfg = dict(inputs.linear_mode_cfg(8, ndim=3), bfield="face")
     h = ctypes.c_void_p()
-    for over in (dict(precision="mixed"), dict(fofc=True)):
+    for over in (dict(fofc=True),):
         c = kh.coords_from_cfg(dict(cfg, **over))
         assert kh.lib().kh_geometry_init(0.0, ctypes.byref(c), float(cfg["gam"]), ctypes.byref(h)) == -1
     for field, value in (("bfield", 2), ("emf", 2)):

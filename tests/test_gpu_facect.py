@@ -128,3 +128,44 @@ def test_face_ct_needs_a_face_field(kh):
     g = GpuRun(ctx, cfg, P)
     with pytest.raises(kh.KHError):
         ctx.step(g.U, g.P, g.B, 1e-3)
+
+
+# ---- mixed precision: FP32 EMFs, FP64 face field (curl formed in FP64) ----
+
+@pytest.mark.parametrize("which", ["torus3d-gs05", "box3d-gs05", "torus2d-average"])
+def test_mixed_face_ct_vs_oracle(kh, orc, which):
+    cfg, P, fB = _case(which)
+    cfg = dict(cfg, precision="mixed")
+    P = orc.apply_bc(cfg, P)
+    U = orc.prim_to_cons(cfg, P)
+    dt = 0.5 * orc.cfl_dt(cfg, P)
+    Uo, Po, fo, _, _ = orc.step_face(cfg, U, P, fB, dt)
+    ctx = kh.Context(cfg)
+    g = GpuRun(ctx, cfg, P, U=U)
+    fBd = ctx.to_device(fB)
+    ctx.set_face_field(fBd)
+    ctx.step(g.U, g.P, g.B, dt)
+    Ug, Pg = g.host()
+    a, b = interior(cfg, Ug), interior(cfg, Uo)
+    pa, pb = interior(cfg, Pg), interior(cfg, Po)
+    # the mixed path's FP32 flux level (as for Flux-CT; momenta and velocities
+    # against the mass scale near equilibrium)
+    mass = np.abs(b[0]).sum()
+    nz = b[0].size
+    for v in range(8):
+        tol = 2e-3 if v in (2, 3, 4) else 1e-4
+        den = max(np.abs(b[v]).sum(), 1e-3 * mass)
+        assert np.abs(a[v] - b[v]).sum() / den < tol, ("U", v, np.abs(a[v] - b[v]).sum() / den)
+        pden = max(np.abs(pb[v]).sum(), 1e-2 * nz if v in (2, 3, 4) else 0.0)
+        assert np.abs(pa[v] - pb[v]).sum() / pden < tol, ("P", v, np.abs(pa[v] - pb[v]).sum() / pden)
+    fg = ctx.to_host(fBd, P.shape[3])
+    for x, y in zip(_faces_interior(cfg, fg), _faces_interior(cfg, fo)):
+        den = np.abs(y).sum()
+        if den > 0:
+            assert np.abs(x - y).sum() / den < 1e-4
+    # the face divergence stays at FP64 rounding
+    dx = min((cfg[k][1] - cfg[k][0]) / cfg[n] for k, n in (("x1", "n1"), ("x2", "n2"), ("x3", "n3")))
+    for _ in range(4):
+        ctx.step(g.U, g.P, g.B, dt)
+    mx, _ = ctx.face_divb(fBd)
+    assert mx < 1e-12 * np.abs(fB).max() / dx
