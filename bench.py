@@ -61,6 +61,7 @@ def parse():
     p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-cost leg")
     p.add_argument("--no-cube", action="store_true", help="skip the 128^3 MKS torus leg")
     p.add_argument("--no-fofc", action="store_true", help="skip the first-order flux correction leg")
+    p.add_argument("--no-facect", action="store_true", help="skip the face-centred constrained transport leg")
     p.add_argument("--smr-only", action="store_true", help="run only the statically refined torus leg")
     p.add_argument("--precisions", default="mixed,fp64",
                    help="comma list; the first is the headline, the others are reported beside it")
@@ -372,6 +373,52 @@ def measure_fofc(args, cfg64, P0, dev, stream, precision):
     return out
 
 
+def measure_facect(args, cfg64, P0, dev, stream, precision, emf="gs05"):
+    """The workload torus with face-centred constrained transport (its loop
+    field on faces, upwinded edge EMFs): timed steps with CUDA events, eager
+    and as a CUDA graph, and the face divergence after them."""
+    import torch
+
+    from paper_2408_01361_gb300 import inputs, kh
+
+    cfg = dict(cfg64, precision=precision, bfield="face", emf=emf)
+    nz = cfg["n1"] * cfg["n2"] * cfg["n3"]
+    fB0 = inputs.torus_face_field(cfg)
+    ctx = kh.Context(cfg, device=dev)
+    PB = ctx.to_device(P0)
+    P, B = ctx.split(PB)
+    fB = ctx.to_device(fB0)
+    del fB0
+    ctx.set_face_field(fB)
+    ctx.face_to_cell(fB, B)
+    U = ctx.empty(8)
+    ctx.prim_to_cons(P, B, U)
+    dt = ctx.cfl_dt(P, B)
+    ctx.autotune(U, P, B, 0.5 * dt)
+    for _ in range(max(args.warmup, 3)):
+        dt, _ = ctx.step(U, P, B, 0.5 * dt)
+    steps = max(args.steps, 5)
+    out = {"precision": precision, "emf": emf, "zones": nz}
+    for graph in (False, True):
+        ctx.set_graph(graph)
+        if graph:
+            dt, _ = ctx.step(U, P, B, 0.5 * dt)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(steps):
+            dt, _ = ctx.step(U, P, B, 0.5 * dt)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+        out["graph" if graph else "eager"] = {"value": nz / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms}
+    ctx.set_graph(False)
+    mx, l1 = ctx.face_divb(fB)
+    out["face_divb_max"] = mx
+    ctx.close()
+    return out
+
+
 def measure_smr(args, dev, stream, precision):
     """The statically refined torus (3 levels, 592 uneven blocks, 5.57 M zones)
     stepped as one mesh: every kernel covers all blocks, ghost zones of every
@@ -627,6 +674,12 @@ def run_kh(args, world, rank, local):
             fo[p] = measure_fofc(args, cfg64, P0, dev, stream, p)
             fo[p]["cost_vs_plain_graph"] = results[p]["graph"]["value"] / fo[p]["graph"]["value"]
         line["fofc"] = fo
+    if not args.no_facect and world == 1:
+        fc = {}
+        for p in args.precisions:
+            fc[p] = measure_facect(args, cfg64, P0, dev, stream, p)
+            fc[p]["cost_vs_flux_ct_graph"] = results[p]["graph"]["value"] / fc[p]["graph"]["value"]
+        line["face_ct"] = fc
     if not args.no_adjoint and world == 1:
         line["adjoint"] = measure_adjoint(args, dev, stream)
     print(json.dumps(line), flush=True)

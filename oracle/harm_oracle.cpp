@@ -1,5 +1,9 @@
 // Grid-level oracle: boundaries, fluxes with Flux-CT, sources, the two-stage
-// update, primitive recovery, floors, fixup, the CFL time step and divB.
+// update, primitive recovery, floors, fixup, the CFL time step and divB; the
+// first-order flux correction; face-centred constrained transport (parity
+// partly unpinned there: which side the upwinded EMF derivative terms take
+// is fixed by no property the tests check; it changes results at second
+// order only).
 //
 // TEST INFRASTRUCTURE ONLY (see harm_oracle.hpp). Exposed to Python through a
 // plain C API (prefix or_) for the parity tests, the pin tests and the CPU
