@@ -42,6 +42,7 @@ enum { KH_RECON_MC = 0, KH_RECON_WENO5 = 1 };
 enum { KH_FP64 = 0, KH_MIXED = 1 };
 enum { KH_B_FLUXCT = 0, KH_B_FACE = 1 };
 enum { KH_EMF_AVERAGE = 0, KH_EMF_GS05 = 1 };
+enum { KH_INV_NOBLE2D = 0, KH_INV_1DW = 1, KH_INV_KASTAUN = 2 };
 enum {
   KH_OK = 0,
   KH_EINVAL = -1,   /* bad argument or unsupported combination */
@@ -92,6 +93,18 @@ typedef struct {
                              Flux-CT) or KH_EMF_GS05 (Gardiner & Stone 2005: plus the
                              half-zone derivative terms, each taken from the cell
                              upwind of the mass flux through its face) */
+  int inverter;           /* FP64 primitive recovery ("Algorithm" section): KH_INV_NOBLE2D
+                             (Noble et al. 2006, Newton on (W, v^2); default),
+                             KH_INV_1DW (Noble et al.'s one-unknown scheme: v^2(W) in
+                             closed form, Newton on the energy equation) or
+                             KH_INV_KASTAUN (Kastaun, Kalinani & Ciolfi 2021:
+                             bracketed root of a master function of 1/(h gamma)).
+                             All find the same root; newton_max_iter / newton_tol
+                             apply to each (KASTAUN: up to 4x the iterations, tol
+                             on the bracket width). FP64 single-grid contexts
+                             (the mixed path, the refined mesh and the adjoint
+                             carry Noble-2D and refuse the others); used by the
+                             update and kh_cons_to_prim. */
 } kh_coords;
 
 /* Counters of the last kh_step (both stages summed). */

@@ -213,6 +213,7 @@ __global__ void k_apply_ct(R* F1, R* F2, R* F3, const R* e1, const R* e2, const 
 // Pin as the guess, floors; writes Pout, pflag and (stage 2) U.
 // ---------------------------------------------------------------------------
 
+template <int INV>
 __global__ void __launch_bounds__(TPB_MAX) k_update(const double* U0, CVars Pin, Vars Pout, double* Uout,
                                                    const double* F1, const double* F2, const double* F3, Layout L,
                                                    DevGeom G, Scheme S, const double* dtp, double coef, int8_t* pflag,
@@ -221,7 +222,8 @@ __global__ void __launch_bounds__(TPB_MAX) k_update(const double* U0, CVars Pin,
   if (t >= nzones(L)) return;
   int i, j, k;
   zone_ijk(L, t, i, j, k);
-  update_zone(U0, Pin, Pout, Uout, F1, F2, F3, L, G, S, coef * __ldg(dtp), pflag, cnt, i, j, k, nullptr, fl, fBn);
+  update_zone<false, INV>(U0, Pin, Pout, Uout, F1, F2, F3, L, G, S, coef * __ldg(dtp), pflag, cnt, i, j, k, nullptr,
+                          fl, fBn);
 }
 
 // three blocks of TPB_MAX per SM: ~80 registers (a few spill to L1); measured faster
@@ -268,6 +270,7 @@ __global__ void __launch_bounds__(TPB) k_fixup_list(VarsT<T> P, double* Uout, co
 // First-order flux correction (the paper's "Algorithm" section, after
 // Beckwith & Stone 2011): trial flags, their ghosts, donor-cell face fluxes.
 // ---------------------------------------------------------------------------
+template <int INV>
 __global__ void __launch_bounds__(TPB_MAX) k_fofc_trial(const double* U0, CVars Pin, const double* F1,
                                                        const double* F2, const double* F3, Layout L, DevGeom G,
                                                        Scheme S, const double* dtp, double coef, int8_t* flag,
@@ -276,7 +279,7 @@ __global__ void __launch_bounds__(TPB_MAX) k_fofc_trial(const double* U0, CVars 
   if (t >= nzones(L)) return;
   int i, j, k;
   zone_ijk(L, t, i, j, k);
-  update_zone<true>(U0, Pin, Vars{}, nullptr, F1, F2, F3, L, G, S, coef * __ldg(dtp), flag, cnt, i, j, k);
+  update_zone<true, INV>(U0, Pin, Vars{}, nullptr, F1, F2, F3, L, G, S, coef * __ldg(dtp), flag, cnt, i, j, k);
 }
 
 __global__ void __launch_bounds__(TPB_MAX, 3) k_fofc_trial_mixed(const double* U0, CVarsT<float> Pin,
@@ -569,6 +572,7 @@ __global__ void __launch_bounds__(TPB) k_p2c(CVars P, double* U, Layout L, DevGe
   for (int v = 0; v < NV; ++v) U[v * L.plane + c] = u[v];
 }
 
+template <int INV>
 __global__ void __launch_bounds__(TPB) k_c2p(const double* U, Vars P, int8_t* pflag, Layout L, DevGeom G, Scheme S,
                                             unsigned long long* cnt) {
   const long long tot = (long long)L.N1 * L.N2 * L.N3;
@@ -583,7 +587,7 @@ __global__ void __launch_bounds__(TPB) k_c2p(const double* U, Vars P, int8_t* pf
     p[v] = P.v[v][c];
   }
   const double ig = __ldg(G.flo + 2 * L.gplane + (long long)j * L.n1s + i);  // 1 / sqrt(-g)
-  const int flag = noble2d(u, m, ig, S.gam, S.igam, S.gfac, S.c2p, p);
+  const int flag = invert<INV>(u, m, ig, S.gam, S.igam, S.gfac, S.c2p, p);
   p[V_B1] = u[V_B1] * ig;
   p[V_B2] = u[V_B2] * ig;
   p[V_B3] = u[V_B3] * ig;
@@ -675,7 +679,14 @@ int launch_fofc_trial(const double* U0, const CVars& Pin, double* const F[3], co
                       const Scheme& S, const double* dtp, double coef, int8_t* flag, unsigned long long* cnt,
                       int tpb, cudaStream_t s) {
   const long long nz = (long long)L.n1 * L.n2 * L.n3;
-  k_fofc_trial<<<nblocks(nz, tpb), tpb, 0, s>>>(U0, Pin, F[0], F[1], F[2], L, G, S, dtp, coef, flag, cnt);
+  if (S.c2p.method == C2P_KASTAUN)
+    k_fofc_trial<C2P_KASTAUN><<<nblocks(nz, tpb), tpb, 0, s>>>(U0, Pin, F[0], F[1], F[2], L, G, S, dtp, coef, flag,
+                                                               cnt);
+  else if (S.c2p.method == C2P_1DW)
+    k_fofc_trial<C2P_1DW><<<nblocks(nz, tpb), tpb, 0, s>>>(U0, Pin, F[0], F[1], F[2], L, G, S, dtp, coef, flag, cnt);
+  else
+    k_fofc_trial<C2P_NOBLE2D><<<nblocks(nz, tpb), tpb, 0, s>>>(U0, Pin, F[0], F[1], F[2], L, G, S, dtp, coef, flag,
+                                                               cnt);
   return 1;
 }
 
@@ -730,8 +741,15 @@ int launch_update(const double* U0, const CVars& Pin, const Vars& Pout, double* 
                   const Layout& L, const DevGeom& G, const Scheme& S, const double* dtp, double coef, int8_t* pflag,
                   unsigned long long* cnt, int tpb, cudaStream_t s, FailList fl, const double* fBn) {
   const long long nz = (long long)L.n1 * L.n2 * L.n3;
-  k_update<<<nblocks(nz, tpb), tpb, 0, s>>>(U0, Pin, Pout, Uout, F[0], F[1], F[2], L, G, S, dtp, coef, pflag, cnt,
-                                            fl, fBn);
+  if (S.c2p.method == C2P_KASTAUN)
+    k_update<C2P_KASTAUN><<<nblocks(nz, tpb), tpb, 0, s>>>(U0, Pin, Pout, Uout, F[0], F[1], F[2], L, G, S, dtp, coef,
+                                                           pflag, cnt, fl, fBn);
+  else if (S.c2p.method == C2P_1DW)
+    k_update<C2P_1DW><<<nblocks(nz, tpb), tpb, 0, s>>>(U0, Pin, Pout, Uout, F[0], F[1], F[2], L, G, S, dtp, coef,
+                                                       pflag, cnt, fl, fBn);
+  else
+    k_update<C2P_NOBLE2D><<<nblocks(nz, tpb), tpb, 0, s>>>(U0, Pin, Pout, Uout, F[0], F[1], F[2], L, G, S, dtp, coef,
+                                                           pflag, cnt, fl, fBn);
   return 1;
 }
 
@@ -871,7 +889,12 @@ int launch_p2c(const CVars& P, double* U, const Layout& L, const DevGeom& G, con
 int launch_c2p(const double* U, const Vars& P, int8_t* pflag, const Layout& L, const DevGeom& G, const Scheme& S,
                unsigned long long* cnt, cudaStream_t s) {
   const long long tot = (long long)L.N1 * L.N2 * L.N3;
-  k_c2p<<<nblocks(tot, TPB), TPB, 0, s>>>(U, P, pflag, L, G, S, cnt);
+  if (S.c2p.method == C2P_KASTAUN)
+    k_c2p<C2P_KASTAUN><<<nblocks(tot, TPB), TPB, 0, s>>>(U, P, pflag, L, G, S, cnt);
+  else if (S.c2p.method == C2P_1DW)
+    k_c2p<C2P_1DW><<<nblocks(tot, TPB), TPB, 0, s>>>(U, P, pflag, L, G, S, cnt);
+  else
+    k_c2p<C2P_NOBLE2D><<<nblocks(tot, TPB), TPB, 0, s>>>(U, P, pflag, L, G, S, cnt);
   return 1;
 }
 

@@ -504,6 +504,7 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
   if (c->precision != KH_FP64 && c->precision != KH_MIXED) return KH_EINVAL;
   if (c->recon != KH_RECON_MC && c->recon != KH_RECON_WENO5) return KH_EINVAL;
   if (c->fofc) return KH_EINVAL;  // the flux correction runs on single grids
+  if (c->inverter != KH_INV_NOBLE2D) return KH_EINVAL;  // the mesh kernels carry Noble-2D
   if (c->bfield != KH_B_FLUXCT) return KH_EINVAL;  // face-centred CT: single grids
   if (!(gamma > 1.0) || !(c->cfl > 0.0) || !(fabs(a) < 1.0)) return KH_EINVAL;
   for (int q = 0; q < 6; ++q) {
@@ -531,6 +532,7 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
                      c->u_rho_max,      c->gamma_max,       1.0 / c->bsq_rho_max,   1.0 / c->bsq_u_max};
   S.c2p.max_iter = c->newton_max_iter > 0 ? c->newton_max_iter : 30;
   S.c2p.tol = c->newton_tol > 0.0 ? c->newton_tol : 1e-14;
+  S.c2p.method = c->inverter;
   set_mixed(S);
   x->cp = CoordParams{c->kind, a, c->x1min, c->hslope, c->poly_xt, c->poly_alpha, c->mks_smooth};
 

@@ -251,57 +251,106 @@ KH_HD float weno5_plus(float a, float b, float c, float d, float e) {
 }
 
 // ---------------------------------------------------------------------------
-// Noble et al. (2006) 2-unknown inversion, FP64.
+// Primitive recovery, FP64. Shared notation (Noble et al. 2006):
 //   D = alpha rho u^t; Q_mu = alpha T^t_mu; B^mu = alpha (0, B^i);
-//   n_mu = (-alpha, 0, 0, 0); Q~^mu = Q^mu + n^mu (Q.n).
-// Unknowns W = (rho + u + p) gamma^2 and v^2 = 1 - 1/gamma^2:
-//   f1 = Q~^2 - v^2 (B^2 + W)^2 + (Q.B)^2 (B^2 + 2W) / W^2 = 0
-//   f2 = Q.n + W - p(W, v^2) + B^2 (1 + v^2)/2 - (Q.B)^2 / (2 W^2) = 0
+//   n_mu = (-alpha, 0, 0, 0); Q~^mu = Q^mu + n^mu (Q.n);
+//   W = (rho + u + p) gamma^2, v^2 = 1 - 1/gamma^2,
 //   p = (gam - 1)/gam (W (1 - v^2) - D sqrt(1 - v^2)).
-// Returns 0 or a failure code (1 no convergence, 2 v^2 >= 1, 3 W <= 0,
+// The root satisfies
+//   f1 = Q~^2 - v^2 (B^2 + W)^2 + (Q.B)^2 (B^2 + 2W) / W^2 = 0
+//   f2 = Q.n + W - p(W, v^2) + B^2 (1 + v^2)/2 - (Q.B)^2 / (2 W^2) = 0.
+// Three solvers find it (C2POpts::method): Noble's two-unknown Newton
+// iteration on (W, v^2); Noble's one-unknown scheme on W (v^2 from f1 in
+// closed form, Newton on f2, "1D_W"); and the scheme of Kastaun, Kalinani &
+// Ciolfi (2021; the paper's "Algorithm" section) on mu = 1/(h gamma). Each
+// returns 0 or a failure code (1 no convergence, 2 v^2 >= 1, 3 W <= 0,
 // 4 rho <= 0, 5 u < 0); P (fluid slots) is written only on success.
 // ---------------------------------------------------------------------------
+enum { C2P_NOBLE2D = 0, C2P_1DW = 1, C2P_KASTAUN = 2 };
+
 struct C2POpts {
   int max_iter;
   double tol;
+  int method;  // C2P_NOBLE2D | C2P_1DW | C2P_KASTAUN
 };
 
-KH_HD int noble2d(const double* U, const Met<double>& m, double ig, double gam, double igam, double gf,
-                  const C2POpts& o, double* P) {
+// The frame invariants of one zone's conserved variables.
+struct C2PInv {
+  double D, Qdn, Qtsq, Bsq, QdB, QdB2;
+  double Qu[4], nu[4], Bc[3];
+};
+
+KH_HD void c2p_invariants(const double* U, const Met<double>& m, double ig, C2PInv& I) {
   const double a = m.alpha;
-  const double D = a * U[V_RHO] * ig;
+  I.D = a * U[V_RHO] * ig;
   const double Qc[4] = {a * (U[V_U] - U[V_RHO]) * ig, a * U[V_U1] * ig, a * U[V_U2] * ig, a * U[V_U3] * ig};
-  double Qu[4];
 #pragma unroll
   for (int mu = 0; mu < 4; ++mu)
-    Qu[mu] = m.gcon[mu][0] * Qc[0] + m.gcon[mu][1] * Qc[1] + m.gcon[mu][2] * Qc[2] + m.gcon[mu][3] * Qc[3];
+    I.Qu[mu] = m.gcon[mu][0] * Qc[0] + m.gcon[mu][1] * Qc[1] + m.gcon[mu][2] * Qc[2] + m.gcon[mu][3] * Qc[3];
   // n^mu = -alpha g^{mu t}
-  const double nu[4] = {-a * m.gcon[0][0], -a * m.gcon[1][0], -a * m.gcon[2][0], -a * m.gcon[3][0]};
-  const double Qdn = Qc[0] * nu[0] + Qc[1] * nu[1] + Qc[2] * nu[2] + Qc[3] * nu[3];
-  const double Qsq = Qc[0] * Qu[0] + Qc[1] * Qu[1] + Qc[2] * Qu[2] + Qc[3] * Qu[3];
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) I.nu[mu] = -a * m.gcon[mu][0];
+  I.Qdn = Qc[0] * I.nu[0] + Qc[1] * I.nu[1] + Qc[2] * I.nu[2] + Qc[3] * I.nu[3];
+  const double Qsq = Qc[0] * I.Qu[0] + Qc[1] * I.Qu[1] + Qc[2] * I.Qu[2] + Qc[3] * I.Qu[3];
   // square of the spacelike projected momentum: >= 0 (rounding can make the
   // difference slightly negative for a fluid at rest in the normal frame)
-  const double Qtsq = fmax(Qsq + Qdn * Qdn, 0.0);
-  const double Bc1 = a * U[V_B1] * ig, Bc2 = a * U[V_B2] * ig, Bc3 = a * U[V_B3] * ig;
-  const double Bsq = m.gcov[1][1] * Bc1 * Bc1 + m.gcov[2][2] * Bc2 * Bc2 + m.gcov[3][3] * Bc3 * Bc3 +
-                     2.0 * (m.gcov[1][2] * Bc1 * Bc2 + m.gcov[1][3] * Bc1 * Bc3 + m.gcov[2][3] * Bc2 * Bc3);
-  const double QdB = Qc[1] * Bc1 + Qc[2] * Bc2 + Qc[3] * Bc3;
-  const double QdB2 = QdB * QdB;
+  I.Qtsq = fmax(Qsq + I.Qdn * I.Qdn, 0.0);
+  I.Bc[0] = a * U[V_B1] * ig;
+  I.Bc[1] = a * U[V_B2] * ig;
+  I.Bc[2] = a * U[V_B3] * ig;
+  const double Bc1 = I.Bc[0], Bc2 = I.Bc[1], Bc3 = I.Bc[2];
+  I.Bsq = m.gcov[1][1] * Bc1 * Bc1 + m.gcov[2][2] * Bc2 * Bc2 + m.gcov[3][3] * Bc3 * Bc3 +
+          2.0 * (m.gcov[1][2] * Bc1 * Bc2 + m.gcov[1][3] * Bc1 * Bc3 + m.gcov[2][3] * Bc2 * Bc3);
+  I.QdB = Qc[1] * Bc1 + Qc[2] * Bc2 + Qc[3] * Bc3;
+  I.QdB2 = I.QdB * I.QdB;
+}
 
-  // initial guess from the stage-input primitives at this metric
-  double W, vsq;
-  {
-    const double v1 = P[V_U1], v2 = P[V_U2], v3 = P[V_U3];
-    const double q = m.gcov[1][1] * v1 * v1 + m.gcov[2][2] * v2 * v2 + m.gcov[3][3] * v3 * v3 +
-                     2.0 * (m.gcov[1][2] * v1 * v2 + m.gcov[1][3] * v1 * v3 + m.gcov[2][3] * v2 * v3);
-    const double g2 = 1.0 + q;
-    W = (P[V_RHO] + gam * P[V_U]) * g2;
-    vsq = q / g2;
-  }
-  if (!(W > 0.0) || !isfinite(W)) W = fabs(Qdn) + 1e-300;
+// Primitives from a root (W, v^2): rho = D / gamma, u = (W (1 - v^2) - rho) / gam,
+// u~^i = gamma (Q~^i + (Q.B) B^i / W) / (W + B^2).
+KH_HD int c2p_output(const C2PInv& I, double W, double vsq, double igam, double* P) {
+  if (!(W > 0.0)) return 3;
+  if (!(vsq < 1.0) || vsq < 0.0) return 2;
+  const double gamma = krsqrt(1.0 - vsq);
+  const double rho = I.D * ((1.0 - vsq) * gamma);
+  const double uint = (W * (1.0 - vsq) - rho) * igam;
+  if (!(rho > 0.0)) return 4;
+  if (!(uint >= 0.0)) return 5;
+  P[V_RHO] = rho;
+  P[V_U] = uint;
+  const double BW = W + I.Bsq;
+  const double inv = 1.0 / (W * BW);  // one division for 1/W and gamma/(W + B^2)
+  const double f = gamma * W * inv;
+  const double iW = BW * inv;
+  P[V_U1] = f * (I.Qu[1] + I.nu[1] * I.Qdn + I.QdB * I.Bc[0] * iW);
+  P[V_U2] = f * (I.Qu[2] + I.nu[2] * I.Qdn + I.QdB * I.Bc[1] * iW);
+  P[V_U3] = f * (I.Qu[3] + I.nu[3] * I.Qdn + I.QdB * I.Bc[2] * iW);
+  return 0;
+}
+
+// Initial guess (W, v^2) from the primitives in P at this metric.
+KH_HD void c2p_guess(const double* P, const Met<double>& m, double gam, const C2PInv& I, double& W, double& vsq) {
+  const double v1 = P[V_U1], v2 = P[V_U2], v3 = P[V_U3];
+  const double q = m.gcov[1][1] * v1 * v1 + m.gcov[2][2] * v2 * v2 + m.gcov[3][3] * v3 * v3 +
+                   2.0 * (m.gcov[1][2] * v1 * v2 + m.gcov[1][3] * v1 * v3 + m.gcov[2][3] * v2 * v3);
+  const double g2 = 1.0 + q;
+  W = (P[V_RHO] + gam * P[V_U]) * g2;
+  vsq = q / g2;
+  if (!(W > 0.0) || !isfinite(W)) W = fabs(I.Qdn) + 1e-300;
   const double vmax = 1.0 - 1e-16;
   if (!(vsq >= 0.0)) vsq = 0.0;
   if (vsq > vmax) vsq = vmax;
+}
+
+// Noble's two-unknown Newton iteration on (W, v^2).
+KH_HD int noble2d(const double* U, const Met<double>& m, double ig, double gam, double igam, double gf,
+                  const C2POpts& o, double* P) {
+  C2PInv I;
+  c2p_invariants(U, m, ig, I);
+  const double D = I.D, Qdn = I.Qdn, Qtsq = I.Qtsq, Bsq = I.Bsq, QdB2 = I.QdB2;
+  // initial guess from the stage-input primitives at this metric
+  double W, vsq;
+  c2p_guess(P, m, gam, I, W, vsq);
+  const double vmax = 1.0 - 1e-16;
 
   bool conv = false;
   double err = 1.0;
@@ -340,23 +389,182 @@ KH_HD int noble2d(const double* U, const Met<double>& m, double ig, double gam, 
     }
   }
   if (!conv && !(err < 1e-9)) return 1;
-  if (!(W > 0.0)) return 3;
-  if (!(vsq < 1.0) || vsq < 0.0) return 2;
-  const double gamma = krsqrt(1.0 - vsq);
-  const double rho = D * ((1.0 - vsq) * gamma);
-  const double uint = (W * (1.0 - vsq) - rho) * igam;
-  if (!(rho > 0.0)) return 4;
-  if (!(uint >= 0.0)) return 5;
-  P[V_RHO] = rho;
-  P[V_U] = uint;
-  const double BW = W + Bsq;
-  const double inv = 1.0 / (W * BW);  // one division for 1/W and gamma/(W + B^2)
-  const double f = gamma * W * inv;
-  const double iW = BW * inv;
-  P[V_U1] = f * (Qu[1] + nu[1] * Qdn + QdB * Bc1 * iW);
-  P[V_U2] = f * (Qu[2] + nu[2] * Qdn + QdB * Bc2 * iW);
-  P[V_U3] = f * (Qu[3] + nu[3] * Qdn + QdB * Bc3 * iW);
-  return 0;
+  return c2p_output(I, W, vsq, igam, P);
+}
+
+// v^2(W) from f1 in closed form, with its W derivative.
+KH_HD void vsq_of_W(const C2PInv& I, double W, double& vsq, double& dvsq) {
+  const double BW = I.Bsq + W;
+  const double N = I.Qtsq * W * W + I.QdB2 * (I.Bsq + 2.0 * W);
+  const double Dn = W * W * BW * BW;
+  const double dN = 2.0 * (I.Qtsq * W + I.QdB2);
+  const double dDn = 2.0 * W * BW * (I.Bsq + 2.0 * W);
+  vsq = N / Dn;
+  dvsq = (dN * Dn - N * dDn) / (Dn * Dn);
+}
+
+// Noble's one-unknown scheme ("1D_W"): Newton on f2(W, v^2(W)); a step that
+// leaves W > 0 or v^2 < 1 is halved back towards the iterate.
+KH_HD int noble1dw(const double* U, const Met<double>& m, double ig, double gam, double igam, double gf,
+                   const C2POpts& o, double* P) {
+  C2PInv I;
+  c2p_invariants(U, m, ig, I);
+  double W, vsq;
+  c2p_guess(P, m, gam, I, W, vsq);
+  const double vmax = 1.0 - 1e-16;
+  double dv;
+  vsq_of_W(I, W, vsq, dv);
+  // start where v^2(W) < 1 (v^2 decreases towards 0 as W grows)
+  for (int g = 0; g < 200 && !(vsq < vmax); ++g) {
+    W *= 2.0;
+    vsq_of_W(I, W, vsq, dv);
+  }
+  if (!(vsq < vmax)) return 2;
+  bool conv = false;
+  double err = 1.0;
+  for (int it = 0; it < o.max_iter; ++it) {
+    vsq_of_W(I, W, vsq, dv);
+    const double g2i = 1.0 - vsq;
+    const double rs = krsqrt(g2i);
+    const double sg = g2i * rs;
+    const double p = gf * (W * g2i - I.D * sg);
+    const double iW = 1.0 / W;
+    const double iW2 = iW * iW;
+    const double f = I.Qdn + W - p + 0.5 * I.Bsq * (1.0 + vsq) - 0.5 * I.QdB2 * iW2;
+    const double dpdW = gf * g2i;
+    const double dpdv = gf * (-W + 0.5 * I.D * rs);
+    const double df = 1.0 - dpdW - dpdv * dv + 0.5 * I.Bsq * dv + I.QdB2 * iW2 * iW;
+    double dW = -f / df;
+    if (!isfinite(dW)) return 1;
+    double Wn = W + dW;
+    double vn = 0.0, dn;
+    for (int h = 0; h < 60; ++h) {  // keep the iterate admissible
+      if (Wn > 0.0) {
+        vsq_of_W(I, Wn, vn, dn);
+        if (vn < vmax) break;
+      }
+      dW *= 0.5;
+      Wn = W + dW;
+    }
+    err = fabs(Wn - W) * iW;
+    W = Wn;
+    if (!(W > 0.0) || !isfinite(W)) return 1;
+    if (err < o.tol) {
+      conv = true;
+      break;
+    }
+  }
+  if (!conv && !(err < 1e-9)) return 1;
+  vsq_of_W(I, W, vsq, dv);
+  return c2p_output(I, W, vsq, igam, P);
+}
+
+// Kastaun, Kalinani & Ciolfi (2021): one unknown mu = 1/(h gamma), in the
+// variables scaled by D: q = tau/D (tau = -Q.n - D), r^2 = Q~^2/D^2,
+// b^2 = B^2/D, (r.b) = Q.B/D^(3/2). For a trial mu, with x = 1/(1 + mu b^2):
+//   rbar^2 = x^2 r^2 + mu x (1 + x) (r.b)^2            (v^2 = mu^2 rbar^2)
+//   qbar   = q - b^2/2 - mu^2 x^2 (b^2 r^2 - (r.b)^2)/2
+//   v^2 <= r^2 / (h0^2 + r^2) (h0 = 1, the least enthalpy of an ideal gas),
+//   gamma, rho = D/gamma, eps = gamma (qbar - mu rbar^2) + v^2 gamma^2/(1 + gamma)
+//   (clamped to eps >= 0), a = p/(rho (1 + eps)),
+//   nu = max((1 + a)(1 + eps)/gamma, (1 + a)(1 + qbar - mu rbar^2)),
+// and the root of f(mu) = mu - 1/(nu + mu rbar^2) in (0, mu+] is the
+// solution; mu+ = 1/h0, or for r^2 >= h0^2 the root of
+// mu sqrt(h0^2 + rbar^2(mu)) - 1. The root gives W = D/mu and v^2.
+struct KastaunVars {
+  double q, r2, b2, rb2, brr;  // brr = b^2 r^2 - (r.b)^2 >= 0
+};
+
+KH_HD double kastaun_f(const KastaunVars& k, double mu, double gm1, double* vsq_out) {
+  const double x = 1.0 / (1.0 + mu * k.b2);
+  const double rbar2 = x * x * k.r2 + mu * x * (1.0 + x) * k.rb2;
+  const double qbar = k.q - 0.5 * k.b2 - 0.5 * mu * mu * x * x * k.brr;
+  const double v0sq = k.r2 / (1.0 + k.r2);
+  double vsq = mu * mu * rbar2;
+  if (vsq > v0sq) vsq = v0sq;
+  const double W = krsqrt(1.0 - vsq);
+  double eps = W * (qbar - mu * rbar2) + vsq * W * W / (1.0 + W);
+  if (eps < 0.0) eps = 0.0;
+  const double a = gm1 * eps / (1.0 + eps);  // p / (rho (1 + eps)) of an ideal gas
+  const double nuA = (1.0 + a) * (1.0 + eps) / W;
+  const double nuB = (1.0 + a) * (1.0 + qbar - mu * rbar2);
+  const double nu = nuA > nuB ? nuA : nuB;
+  if (vsq_out) *vsq_out = vsq;
+  return mu - 1.0 / (nu + mu * rbar2);
+}
+
+KH_HD int kastaun(const double* U, const Met<double>& m, double ig, double gam, double igam, const C2POpts& o,
+                  double* P) {
+  C2PInv I;
+  c2p_invariants(U, m, ig, I);
+  if (!(I.D > 0.0)) return 4;
+  const double iD = 1.0 / I.D;
+  KastaunVars k;
+  k.q = -I.Qdn * iD - 1.0;
+  k.r2 = I.Qtsq * iD * iD;
+  k.b2 = I.Bsq * iD;
+  k.rb2 = I.QdB2 * iD * iD * iD;
+  k.brr = k.b2 * k.r2 - k.rb2;
+  if (k.brr < 0.0) k.brr = 0.0;
+  const double gm1 = gam - 1.0;
+  // upper end of the bracket
+  double mup = 1.0;
+  if (k.r2 >= 1.0) {
+    double lo = 0.0, hi = 1.0;
+    for (int it = 0; it < 80 && hi - lo > 1e-15 * hi; ++it) {
+      const double mu = 0.5 * (lo + hi);
+      const double x = 1.0 / (1.0 + mu * k.b2);
+      const double rbar2 = x * x * k.r2 + mu * x * (1.0 + x) * k.rb2;
+      if (mu * sqrt(1.0 + rbar2) - 1.0 < 0.0) lo = mu; else hi = mu;
+    }
+    mup = hi;
+  }
+  // Illinois (modified regula falsi) on f over [0, mu+]
+  double a = 0.0, b = mup;
+  double fa = kastaun_f(k, a, gm1, nullptr), fb = kastaun_f(k, b, gm1, nullptr);
+  if (!(fa <= 0.0 && fb >= 0.0)) return 1;  // no bracket (an unphysical state)
+  int side = 0;
+  double mu = b;
+  bool conv = fb == 0.0;
+  const int nmax = 4 * o.max_iter;
+  for (int it = 0; it < nmax && !conv; ++it) {
+    mu = (a * fb - b * fa) / (fb - fa);
+    if (!(mu > a && mu < b)) mu = 0.5 * (a + b);
+    const double fm = kastaun_f(k, mu, gm1, nullptr);
+    if (fm == 0.0) {
+      conv = true;
+      break;
+    }
+    if (fm > 0.0) {
+      b = mu;
+      fb = fm;
+      if (side == 1) fa *= 0.5;
+      side = 1;
+    } else {
+      a = mu;
+      fa = fm;
+      if (side == -1) fb *= 0.5;
+      side = -1;
+    }
+    if (b - a < o.tol * b) {
+      mu = 0.5 * (a + b);
+      conv = true;
+    }
+  }
+  if (!conv) return 1;
+  double vsq;
+  kastaun_f(k, mu, gm1, &vsq);
+  return c2p_output(I, I.D / mu, vsq, igam, P);
+}
+
+// The solver INV (a compile-time choice: each kernel instance carries one
+// solver, so the default keeps the update kernels' register budget).
+template <int INV>
+KH_HD int invert(const double* U, const Met<double>& m, double ig, double gam, double igam, double gf,
+                 const C2POpts& o, double* P) {
+  if constexpr (INV == C2P_1DW) return noble1dw(U, m, ig, gam, igam, gf, o, P);
+  else if constexpr (INV == C2P_KASTAUN) return kastaun(U, m, ig, gam, igam, o, P);
+  else return noble2d(U, m, ig, gam, igam, gf, o, P);
 }
 
 // ---------------------------------------------------------------------------

@@ -341,7 +341,7 @@ __device__ __forceinline__ R edge_emf(int c, const R* const F[3], const R* ecc, 
 // but only the zone's flag is written: pflag[c] = 1 if the inversion failed or
 // a floor acted, else 0 (flagged zones counted in CNT_FOFC); Pout, Uout and
 // the failure counters are not touched.
-template <bool TRIAL = false>
+template <bool TRIAL = false, int INV = C2P_NOBLE2D>
 __device__ __forceinline__ void update_zone(const double* U0, const CVars& Pin, const Vars& Pout, double* Uout,
                                             const double* F1, const double* F2, const double* F3, const Layout& L,
                                             const DevGeom& G, const Scheme& S, double cdt, int8_t* pflag,
@@ -369,7 +369,7 @@ __device__ __forceinline__ void update_zone(const double* U0, const CVars& Pin, 
 #pragma unroll
   for (int v = 0; v < NV; ++v) Pn[v] = P[v];
   const double ig = __ldg(G.flo + 2 * L.gplane + p);  // 1 / sqrt(-g)
-  const int flag = noble2d(U, m, ig, S.gam, S.igam, S.gfac, S.c2p, Pn);
+  const int flag = invert<INV>(U, m, ig, S.gam, S.igam, S.gfac, S.c2p, Pn);
   if (TRIAL && flag) {
     pflag[c] = 1;
     atomicAdd(cnt + CNT_FOFC, 1ULL);

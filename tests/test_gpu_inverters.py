@@ -1,0 +1,139 @@
+"""The three FP64 primitive-recovery solvers on the GPU (Noble et al.'s
+two-unknown Newton iteration, their one-unknown 1D_W scheme, and the scheme
+of Kastaun, Kalinani & Ciolfi): each recovers seeded random states (Minkowski
+and FMKS Kerr, Lorentz factors to ~10, b^2/rho to ~50) from their conserved
+variables to the oracle's root within 1e-10, steps the torus to the oracle's
+step within 1e-10, and on a stress set (b^2/rho to ~1e4, Lorentz factors to
+~50, a far initial guess) fails on no more zones than it should: Kastaun's
+bracketed scheme on none. Where states fail (the torus atmosphere) the
+solvers differ by design: Kastaun's keeps eps >= 0 at its root."""
+import numpy as np
+import pytest
+
+from gpu_helpers import TOL, GpuRun, interior, rel_l1
+from paper_2408_01361_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+INVERTERS = ["noble2d", "1dw", "kastaun"]
+
+
+@pytest.fixture(scope="module")
+def kh():
+    from paper_2408_01361_gb300 import kh as _kh
+    return _kh
+
+
+def _cases():
+    mink = inputs.linear_mode_cfg(20, ndim=3)
+    Pm = inputs.random_prims(mink, seed=7, ut_scale=(6.0, 6.0, 6.0), b_scale=(4.0, 4.0, 4.0))
+    fm = inputs.torus_cfg(40, 24, 1)
+    fm["x1"] = (np.log(1.2), np.log(50.0))
+    Pf = inputs.random_prims(fm, seed=8, ut_scale=(6.0, 6.0, 6.0), b_scale=(4.0, 4.0, 4.0))
+    return [(mink, Pm), (fm, Pf)]
+
+
+def _c2p(kh, cfg, P, U, guess):
+    ctx = kh.Context(cfg)
+    g = GpuRun(ctx, cfg, guess, U=U)
+    pflag = ctx.torch.zeros(ctx.shape(1)[1:], dtype=ctx.torch.int8, device=ctx.device)
+    nfail = ctx.cons_to_prim(g.U, g.P, g.B, pflag)
+    _, Pg = g.host()
+    return nfail, Pg
+
+
+@pytest.mark.parametrize("inverter", INVERTERS)
+@pytest.mark.parametrize("case", [0, 1])
+def test_recovers_random_states(kh, orc, inverter, case):
+    cfg, P = _cases()[case]
+    cfg = dict(cfg, inverter=inverter)
+    Uo = orc.prim_to_cons(cfg, P)
+    guess = P * (1 + 0.05 * (inputs.uniform01(99, np.arange(P.size)).reshape(P.shape) - 0.5))
+    Po, _, nfail_o = orc.cons_to_prim(cfg, Uo, guess)
+    nfail, Pg = _c2p(kh, cfg, P, Uo, guess)
+    assert nfail == nfail_o == 0
+    assert rel_l1(Pg, Po).max() < TOL
+    assert rel_l1(Pg, P).max() < TOL
+
+
+def _step_case(which):
+    if which == "bondi":
+        cfg = inputs.bondi_cfg(64, 64)
+        P, dirich = inputs.bondi_state(cfg, seed=1)
+        return cfg, P, dirich
+    cfg = inputs.linear_mode_cfg(12, ndim=3, recon="weno5")
+    rng = np.random.default_rng(3)
+    P = np.zeros(inputs.shape(cfg))
+    P[0] = 1.0 + 0.1 * rng.random(P[0].shape)
+    P[1] = 1.0 + 0.1 * rng.random(P[1].shape)
+    P[2:5] = 0.1 * rng.normal(size=P[2:5].shape)
+    P[5:] = 0.5 * rng.normal(size=P[5:].shape)
+    return cfg, P, None
+
+
+@pytest.mark.parametrize("inverter", ["1dw", "kastaun"])
+@pytest.mark.parametrize("which", ["box", "bondi"])
+def test_step_parity(kh, orc, inverter, which):
+    """Where no inversion fails, every solver gives the oracle's step."""
+    cfg, P, dirich = _step_case(which)
+    cfg = dict(cfg, inverter=inverter)
+    Uo = orc.prim_to_cons(cfg, P)
+    dt = 0.5 * orc.cfl_dt(cfg, P, dirich)
+    ctx = kh.Context(cfg)
+    g = GpuRun(ctx, cfg, P, U=Uo, dirichlet=dirich)
+    Uc, Pc = Uo, P
+    for _ in range(3):
+        Uc, Pc, dto, st_o = orc.step(cfg, Uc, Pc, dt, dirich)
+        dtg, nfail = ctx.step(g.U, g.P, g.B, dt)
+        assert nfail == st_o[0] == 0
+    Ug, Pg = g.host()
+    eu = rel_l1(interior(cfg, Ug), interior(cfg, Uc))
+    ep = rel_l1(interior(cfg, Pg), interior(cfg, Pc))
+    assert eu.max() < TOL and ep.max() < TOL, (eu, ep)
+
+
+def test_torus_failures_by_solver(kh, orc):
+    """On the torus (atmosphere at its floors) some inversions fail every
+    step; the bracketed scheme, which keeps eps >= 0 at the root, hands fewer
+    zones to the fixup than the Newton schemes, and the 1D_W scheme fails
+    where the oracle's root finder does."""
+    cfg = inputs.torus_cfg(48, 32, 16, r_out=60.0)
+    P = inputs.torus_state(cfg, seed=2)
+    Uo = orc.prim_to_cons(cfg, P)
+    dt = 0.5 * orc.cfl_dt(cfg, P)
+    nf = {}
+    for inv in ("noble2d", "1dw", "kastaun"):
+        c = dict(cfg, inverter=inv)
+        ctx = kh.Context(c)
+        g = GpuRun(ctx, c, P, U=Uo)
+        nf[inv] = sum(ctx.step(g.U, g.P, g.B, dt)[1] for _ in range(3))
+        Ug, Pg = g.host()
+        assert np.isfinite(Ug).all() and np.isfinite(Pg).all()
+    Uc, Pc, n_o = Uo, P, 0
+    for _ in range(3):
+        Uc, Pc, _, st = orc.step(cfg, Uc, Pc, dt)
+        n_o += st[0]
+    assert nf["1dw"] == n_o, (nf, n_o)
+    assert nf["kastaun"] <= nf["noble2d"], (nf, n_o)
+
+
+def _stress():
+    cfg = inputs.torus_cfg(64, 48, 8)
+    cfg["x1"] = (np.log(1.2), np.log(50.0))
+    P = inputs.random_prims(cfg, seed=21, rho_range=(1e-6, 1.0), u_range=(1e-8, 1.0),
+                            ut_scale=(30.0, 30.0, 30.0), b_scale=(60.0, 60.0, 60.0))
+    far = inputs.random_prims(cfg, seed=22, ut_scale=(1.0, 1.0, 1.0), b_scale=(1.0, 1.0, 1.0))
+    return cfg, P, far
+
+
+def test_stress_set_failures(kh, orc):
+    cfg, P, far = _stress()
+    Uo = orc.prim_to_cons(cfg, P)
+    out = {}
+    for inv in INVERTERS:
+        c = dict(cfg, inverter=inv)
+        nfail, Pg = _c2p(kh, c, P, Uo, far)
+        ok = np.isfinite(Pg).all()
+        out[inv] = (nfail, ok)
+    assert out["kastaun"][0] == 0, out
+    assert all(v[1] for v in out.values()), out
