@@ -62,6 +62,7 @@ def parse():
     p.add_argument("--no-cube", action="store_true", help="skip the 128^3 MKS torus leg")
     p.add_argument("--no-fofc", action="store_true", help="skip the first-order flux correction leg")
     p.add_argument("--no-facect", action="store_true", help="skip the face-centred constrained transport leg")
+    p.add_argument("--no-inverters", action="store_true", help="skip the primitive-recovery solver leg")
     p.add_argument("--smr-only", action="store_true", help="run only the statically refined torus leg")
     p.add_argument("--precisions", default="mixed,fp64",
                    help="comma list; the first is the headline, the others are reported beside it")
@@ -419,6 +420,74 @@ def measure_facect(args, cfg64, P0, dev, stream, precision, emf="gs05"):
     return out
 
 
+def measure_inverters(args, cfg64, P0, dev, stream):
+    """FP64 primitive recovery by solver: the workload torus stepped with each
+    (zone-cycles/s, graph; zones handed to the fixup per step), and a stress
+    set of random states (sigma to 1e4, |u~| to 50, an unrelated guess)
+    recovered by kh_cons_to_prim (states/s, failures)."""
+    import numpy as np
+    import torch
+
+    from paper_2408_01361_gb300 import inputs, kh
+
+    nz = cfg64["n1"] * cfg64["n2"] * cfg64["n3"]
+    out = {}
+    scfg = inputs.torus_cfg(256, 128, 64)
+    scfg["x1"] = (np.log(1.2), np.log(50.0))
+    Ps = inputs.random_prims(scfg, seed=21, rho_range=(1e-6, 1.0), u_range=(1e-8, 1.0),
+                             ut_scale=(30.0, 30.0, 30.0), b_scale=(60.0, 60.0, 60.0))
+    far = inputs.random_prims(scfg, seed=22)
+    far[5:] = Ps[5:]
+    for inv in ("noble2d", "1dw", "kastaun"):
+        cfg = dict(cfg64, precision="fp64", inverter=inv)
+        ctx = kh.Context(cfg, device=dev)
+        PB = ctx.to_device(P0)
+        P, B = ctx.split(PB)
+        U = ctx.empty(8)
+        ctx.prim_to_cons(P, B, U)
+        dt = ctx.cfl_dt(P, B)
+        ctx.autotune(U, P, B, 0.5 * dt)
+        for _ in range(max(args.warmup, 3)):
+            dt, _ = ctx.step(U, P, B, 0.5 * dt)
+        ctx.set_graph(True)
+        dt, _ = ctx.step(U, P, B, 0.5 * dt)
+        steps = max(min(args.steps, 5), 3)
+        nfail = 0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(steps):
+            dt, nf = ctx.step(U, P, B, 0.5 * dt)
+            nfail += nf
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+        ctx.close()
+        r = {"torus_graph": {"value": nz / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms},
+             "torus_fixup_zones_per_step": nfail / steps}
+        # stress set: every cell of a 262x134x70 grid, recovered from an unrelated guess
+        c2 = dict(scfg, inverter=inv)
+        ctx = kh.Context(c2, device=dev)
+        PBs = ctx.to_device(Ps)
+        Pd, Bd = ctx.split(PBs)
+        Ud = ctx.empty(8)
+        ctx.prim_to_cons(Pd, Bd, Ud)
+        G = ctx.to_device(far)
+        Pg, Bg = ctx.split(G)
+        fails = ctx.cons_to_prim(Ud, Pg, Bg, None)  # warm-up and failure count
+        G.copy_(ctx.to_device(far))
+        e0.record(stream)
+        ctx.cons_to_prim(Ud, Pg, Bg, None)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        cells = Ps[0].size
+        r["stress_c2p"] = {"states": cells, "failures": int(fails), "failure_rate": fails / cells,
+                           "states_per_s": cells / (e0.elapsed_time(e1) * 1e-3)}
+        ctx.close()
+        out[inv] = r
+    return out
+
+
 def measure_smr(args, dev, stream, precision):
     """The statically refined torus (3 levels, 592 uneven blocks, 5.57 M zones)
     stepped as one mesh: every kernel covers all blocks, ghost zones of every
@@ -680,6 +749,8 @@ def run_kh(args, world, rank, local):
             fc[p] = measure_facect(args, cfg64, P0, dev, stream, p)
             fc[p]["cost_vs_flux_ct_graph"] = results[p]["graph"]["value"] / fc[p]["graph"]["value"]
         line["face_ct"] = fc
+    if not args.no_inverters and world == 1:
+        line["inverters"] = measure_inverters(args, cfg64, P0, dev, stream)
     if not args.no_adjoint and world == 1:
         line["adjoint"] = measure_adjoint(args, dev, stream)
     print(json.dumps(line), flush=True)
