@@ -48,11 +48,13 @@ class Params(C.Structure):
         ("rho_min", C.c_double), ("u_min", C.c_double), ("bsq_rho_max", C.c_double),
         ("bsq_u_max", C.c_double), ("u_rho_max", C.c_double), ("gamma_max", C.c_double),
         ("x1ref", C.c_double), ("fofc", C.c_int), ("bfield", C.c_int), ("emf", C.c_int),
+        ("integrator", C.c_int),
     ]
 
 
 BFIELD = {"fluxct": 0, "face": 1}
 EMF = {"average": 0, "gs05": 1}
+INTEGRATOR = {"vl2": 0, "rk1": 1, "rk2": 2, "ssprk54": 3}
 
 
 def params(cfg: dict) -> Params:
@@ -83,6 +85,7 @@ def params(cfg: dict) -> Params:
     p.fofc = int(bool(cfg.get("fofc", False)))
     p.bfield = BFIELD[cfg.get("bfield", "fluxct")]
     p.emf = EMF[cfg.get("emf", "gs05")]
+    p.integrator = INTEGRATOR[cfg.get("integrator", "vl2")]
     return p
 
 

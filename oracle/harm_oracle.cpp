@@ -744,7 +744,7 @@ long fofc_correct(const Grid& gr, const R* U0, const R* Pin, const R& gam, doubl
 template <class R>
 void stage(const Grid& gr, const R* U0, const R* Pin, const R& gam, double cdt, R* Uout, R* Pout,
            FluxesT<R>& fx, StageStats& st, std::vector<int>* pflag_out, std::vector<int>* fflag_out = nullptr,
-           const R* fB0 = nullptr, R* fBout = nullptr) {
+           const R* fB0 = nullptr, R* fBout = nullptr, R* dU_out = nullptr) {
   const GridInfo& g = gr.g;
   const bool face = gr.c.bfield == BFIELD_FACE;
   if (face) {
@@ -780,7 +780,9 @@ void stage(const Grid& gr, const R* U0, const R* Pin, const R& gam, double cdt, 
             int o1 = d == 0, o2 = d == 1, o3 = d == 2;
             div += (fx.F[d][gr.idx(v, k + o3, j + o2, i + o1)] - fx.F[d][gr.idx(v, k, j, i)]) / dx[d];
           }
-          U[v] = U0[gr.idx(v, k, j, i)] + cdt * (-div + S[v]);
+          const R inc = cdt * (-div + S[v]);
+          U[v] = U0[gr.idx(v, k, j, i)] + inc;
+          if (dU_out) dU_out[gr.idx(v, k, j, i)] = inc;  // the stage's raw increment (Runge-Kutta)
         }
         if (face) face_to_cell_u(gr, (const R*)fBout, k, j, i, U + B1);
         // guess = stage input
@@ -1042,9 +1044,13 @@ void or_stage(const or_params* c, const double* U0, const double* Pin, double cd
 // P^{n+1} in the interior on exit. stats[0..3] = failed inversions, floored
 // zones, unfixed zones, zones flagged by the first-order flux correction
 // (summed over both stages). Returns the next CFL dt.
+double or_step_rk(const or_params* c, double* U, double* P, double dt, const double* dir_lo, const double* dir_hi,
+                  long* stats);
+
 double or_step(const or_params* c, double* U, double* P, double dt, const double* dir_lo, const double* dir_hi,
                long* stats) {
   if (c->bfield != BFIELD_FLUXCT) return -1.0;  // the face field is state: or_step_face
+  if (c->integrator != INT_VL2) return or_step_rk(c, U, P, dt, dir_lo, dir_hi, stats);
   Grid gr;
   build_grid(*c, gr);
   const size_t n = gr.cells() * NVAR;
@@ -1069,6 +1075,85 @@ double or_step(const or_params* c, double* U, double* P, double dt, const double
           P[q] = Pnew[q];
         }
   (void)g;
+  if (stats) {
+    stats[0] = st.nfail;
+    stats[1] = st.nfloor;
+    stats[2] = st.nunfixed;
+    stats[3] = st.nfofc;
+  }
+  return dtn;
+}
+
+// One step of a Runge-Kutta integrator in Shu-Osher form (the paper's
+// "Algorithm" section lists RK1, RK2 and SSPRK(5)4 beside the predictor-
+// corrector): stage s forms U_s = sum_j a_sj U_j + c_s dt L(P_{s-1}) from the
+// stored stage states, where L(P) is the stage operator (fluxes of the
+// ghost-filled primitives, Flux-CT, sources) and P_s the inversion of U_s
+// (floors, fixup), exactly as a predictor-corrector stage computes them.
+//   RK1: U1 = U0 + dt L(P0).
+//   RK2 (Heun): U1 = U0 + dt L(P0); U2 = U0/2 + U1/2 + dt/2 L(P1).
+//   SSPRK(5,4) of Spiteri & Ruuth (2002): the five stages with their
+//   published coefficients; the last stage's dt L(P3) term reuses the raw
+//   increment of stage 4, c4 dt L(P3).
+double or_step_rk(const or_params* c, double* U, double* P, double dt, const double* dir_lo, const double* dir_hi,
+                  long* stats) {
+  struct RKStage {
+    int n;
+    int src[3];
+    double a[3];
+    double cdt;   // c_s
+    double dU4;   // weight of stage 4's raw increment (SSPRK(5,4) stage 5)
+  };
+  std::vector<RKStage> S;
+  if (c->integrator == INT_RK1) {
+    S = {{1, {0}, {1.0}, 1.0, 0.0}};
+  } else if (c->integrator == INT_RK2) {
+    S = {{1, {0}, {1.0}, 1.0, 0.0}, {2, {0, 1}, {0.5, 0.5}, 0.5, 0.0}};
+  } else if (c->integrator == INT_SSPRK54) {
+    const double c4 = 0.544974750228521, c53 = 0.063692468666290;
+    S = {{1, {0}, {1.0}, 0.391752226571890, 0.0},
+         {2, {0, 1}, {0.444370493651235, 0.555629506348765}, 0.368410593050371, 0.0},
+         {2, {0, 2}, {0.620101851488403, 0.379898148511597}, 0.251891774271694, 0.0},
+         {2, {0, 3}, {0.178079954393132, 0.821920045606868}, c4, 0.0},
+         {3, {2, 3, 4}, {0.517231671970585, 0.096059710526147, 0.386708617503269}, 0.226007483236906, c53 / c4}};
+  } else {
+    return -1.0;
+  }
+  Grid gr;
+  build_grid(*c, gr);
+  const size_t n = gr.cells() * NVAR;
+  std::vector<std::vector<double>> Us(S.size() + 1), Ps(S.size() + 1);
+  Us[0].assign(U, U + n);
+  Ps[0].assign(P, P + n);
+  std::vector<double> base(n), dU4(n, 0.0), dUs(n, 0.0);
+  Fluxes fx;
+  StageStats st;
+  for (size_t s = 0; s < S.size(); ++s) {
+    const RKStage& q = S[s];
+    apply_bc(gr, Ps[s].data(), dir_lo, dir_hi);
+    for (size_t e = 0; e < n; ++e) {
+      double b = 0.0;
+      for (int t = 0; t < q.n; ++t) b += q.a[t] * Us[q.src[t]][e];
+      if (q.dU4 != 0.0) b += q.dU4 * dU4[e];
+      base[e] = b;
+    }
+    Us[s + 1] = base;
+    Ps[s + 1] = Ps[s];
+    const bool keep = c->integrator == INT_SSPRK54 && s == 3;
+    stage<double>(gr, base.data(), Ps[s].data(), c->gam, q.cdt * dt, Us[s + 1].data(), Ps[s + 1].data(), fx, st,
+                  nullptr, nullptr, nullptr, nullptr, keep ? dU4.data() : nullptr);
+  }
+  const double dtn = cfl_dt(gr, fx);
+  const size_t last = S.size();
+  for (int v = 0; v < NVAR; ++v)
+    for (int k = gr.s3(); k < gr.e3(); ++k)
+      for (int j = gr.s2(); j < gr.e2(); ++j)
+        for (int i = gr.s1(); i < gr.e1(); ++i) {
+          const size_t e = gr.idx(v, k, j, i);
+          U[e] = Us[last][e];
+          P[e] = Ps[last][e];
+        }
+  (void)dUs;
   if (stats) {
     stats[0] = st.nfail;
     stats[1] = st.nfloor;

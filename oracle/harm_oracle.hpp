@@ -56,7 +56,10 @@ struct Params {
   int fofc;                       // first-order flux correction (see stage())
   int bfield;                     // BFIELD_FLUXCT | BFIELD_FACE (face-centred constrained transport)
   int emf;                        // face CT edge EMFs: EMF_AVERAGE | EMF_GS05 (contact-upwinded)
+  int integrator;                 // INT_VL2 (predictor-corrector) | INT_RK1 | INT_RK2 | INT_SSPRK54
 };
+
+enum { INT_VL2 = 0, INT_RK1 = 1, INT_RK2 = 2, INT_SSPRK54 = 3 };
 
 enum { BFIELD_FLUXCT = 0, BFIELD_FACE = 1 };
 enum { EMF_AVERAGE = 0, EMF_GS05 = 1 };

@@ -225,6 +225,33 @@ def linear_mode_state(cfg: dict, dP: np.ndarray, omega: float, t: float = 0.0, a
     return P
 
 
+def linear_mode_face_field(cfg: dict, dP: np.ndarray, omega: float, t: float = 0.0, amp: float = 1e-4):
+    """The mode's field on faces (Minkowski: sqrt(-g) = 1): the uniform
+    background plus the curl of the edge potential A = amp (dB x k)/|k|^2
+    sin(k.x - omega t), periodic and discretely divergence-free (k.dB = 0)."""
+    k = np.array(LINEAR_K)
+    dB = np.asarray(dP[5:8], dtype=np.float64)
+    Ahat = amp * np.cross(dB, k) / (k @ k)
+    c = [centers(cfg, q) for q in range(3)]
+    f = [centers(cfg, q, face=True) for q in range(3)]
+
+    def phase(x1, x2, x3):
+        X3, X2, X1 = np.meshgrid(x3, x2, x1, indexing="ij")
+        return np.sin(k[0] * X1 + k[1] * X2 + k[2] * X3 - omega * t)
+
+    three = cfg["n3"] > 1
+    # A1 on x1-edges (i, j-1/2, k-1/2), A2 on x2-edges (i-1/2, j, k-1/2),
+    # A3 on x3-edges (i-1/2, j-1/2, k); on a 2-D grid x3 sits at the centre
+    z = f[2] if three else c[2]
+    A1 = Ahat[0] * phase(c[0], f[1], z)
+    A2 = Ahat[1] * phase(f[0], c[1], z)
+    A3 = Ahat[2] * phase(f[0], f[1], c[2])
+    fB = face_field_from_potential(cfg, A1, A2, A3)
+    for q in range(3):
+        fB[q] += LINEAR_BACKGROUND[5 + q]
+    return fB
+
+
 def load_eigvec(path: str):
     """(dP[8], omega) from a fixture written by tests/golden/make_linear_mode.py."""
     vals = {}

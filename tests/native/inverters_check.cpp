@@ -18,7 +18,7 @@ struct orp {
   int kind, n1, n2, n3, ng, recon, bc[6];
   double a, gam, x1min, x1max, x2min, x2max, x3min, x3max, hslope, poly_xt, poly_alpha, mks_smooth, cfl, rho_min,
       u_min, bsq_rho_max, bsq_u_max, u_rho_max, gamma_max, x1ref;
-  int fofc, bfield, emf;
+  int fofc, bfield, emf, integrator;
 };
 void or_metric_points(const orp*, int, const double*, const double*, double*, double*, double*, double*);
 }
