@@ -43,6 +43,7 @@ enum { KH_FP64 = 0, KH_MIXED = 1 };
 enum { KH_B_FLUXCT = 0, KH_B_FACE = 1 };
 enum { KH_EMF_AVERAGE = 0, KH_EMF_GS05 = 1 };
 enum { KH_INV_NOBLE2D = 0, KH_INV_1DW = 1, KH_INV_KASTAUN = 2 };
+enum { KH_INT_VL2 = 0, KH_INT_RK1 = 1, KH_INT_RK2 = 2, KH_INT_SSPRK54 = 3 };
 enum {
   KH_OK = 0,
   KH_EINVAL = -1,   /* bad argument or unsupported combination */
@@ -105,6 +106,14 @@ typedef struct {
                              (the mixed path, the refined mesh and the adjoint
                              carry Noble-2D and refuse the others); used by the
                              update and kh_cons_to_prim. */
+  int integrator;         /* time integrator ("Algorithm" section): KH_INT_VL2 (the
+                             predictor-corrector, default), KH_INT_RK1, KH_INT_RK2
+                             (Heun) or KH_INT_SSPRK54 (Spiteri & Ruuth's five-stage
+                             fourth-order SSP scheme), in Shu-Osher form: each stage
+                             U_s = sum_j a_sj U_j + c_s dt L(P_{s-1}) with the
+                             stage operator, inversion, floors and fixup of a
+                             predictor-corrector stage. FP64 single-grid contexts
+                             with Flux-CT (8 to 48 extra planes of scratch). */
 } kh_coords;
 
 /* Counters of the last kh_step (both stages summed). */

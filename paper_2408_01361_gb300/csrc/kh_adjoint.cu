@@ -686,7 +686,8 @@ int kh_step_adjoint(kh_ctx* x, const double* U, const double* P, const double* B
                     const double* gP, const double* gB, const double* gF1, double* gU_in, double* gP_in,
                     double* gB_in, double* g_gamma) {
   if (!x || !U || !P || !B || !gU_in || !gP_in || !gB_in || !(dt > 0.0) || !isfinite(dt)) return KH_EINVAL;
-  if (x->c.precision != KH_FP64 || x->S.fofc || x->S.bfield != KH_B_FLUXCT || x->S.c2p.method != C2P_NOBLE2D)
+  if (x->c.precision != KH_FP64 || x->S.fofc || x->S.bfield != KH_B_FLUXCT || x->S.c2p.method != C2P_NOBLE2D ||
+      x->S.integrator != KH_INT_VL2)
     return KH_EINVAL;
   const Layout& L = x->L;
   cudaStream_t s = x->stream;

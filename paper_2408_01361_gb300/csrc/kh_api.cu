@@ -82,7 +82,7 @@ void free_all(kh_ctx* x) {
                   x->counters, x->dirichlet[0], x->dirichlet[1], x->geof, x->dgmf, x->pstarf, x->pnf, x->Ff[0],
                   x->Ff[1], x->Ff[2], x->ctopf[0], x->ctopf[1], x->ctopf[2], x->emff[0], x->emff[1],
                   x->emff[2], x->dirichletf[0], x->dirichletf[1], x->adj, x->adj_i8, x->adj_red, x->geodf, x->flist,
-                  x->fflag, x->fsave, x->fsavef, x->fBstar, x->ecc, x->eccf};
+                  x->fflag, x->fsave, x->fsavef, x->fBstar, x->ecc, x->eccf, x->rk};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -90,7 +90,8 @@ void free_all(kh_ctx* x) {
 GeomT<float> geomf(const kh_ctx* x) { return GeomT<float>{x->geof, x->dgmf, x->flo, x->geodf}; }
 
 // One FP64 stage: ghost fill, fluxes per direction, Flux-CT, update, fixup.
-int run_stage(kh_ctx* x, int st, const double* U0, const Vars& Pin, const Vars& Pout, double* Uout, double coef) {
+int run_stage(kh_ctx* x, int st, const double* U0, const Vars& Pin, const Vars& Pout, double* Uout, double coef,
+              double* dUout = nullptr) {
   const Layout& L = x->L;
   const DevGeom G = devgeom(x);
   cudaStream_t s = x->stream;
@@ -140,7 +141,7 @@ int run_stage(kh_ctx* x, int st, const double* U0, const Vars& Pin, const Vars& 
   mark(x, KH_T_UPDATE, st, 0);
   const FailList fl{x->flist, x->counters + CNT_LIST0 + st};
   n += launch_update(U0, cview(Pin), Pout, Uout, x->F, L, G, x->S, x->dscalar + 3, coef, x->pflag, x->counters,
-                     x->tpb_update, s, fl, fBn);
+                     x->tpb_update, s, fl, fBn, dUout);
   mark(x, KH_T_UPDATE, st, 1);
   mark(x, KH_T_FIXUP, st, 0);
   n += launch_fixup<double>(Pout, Uout, x->pflag, L, G, x->S, x->counters, s, fl);
@@ -256,6 +257,8 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
   if (c->fofc != 0 && c->fofc != 1) return KH_EINVAL;
   if (c->inverter < KH_INV_NOBLE2D || c->inverter > KH_INV_KASTAUN) return KH_EINVAL;
   if (c->inverter != KH_INV_NOBLE2D && c->precision != KH_FP64) return KH_EINVAL;
+  if (c->integrator < KH_INT_VL2 || c->integrator > KH_INT_SSPRK54) return KH_EINVAL;
+  if (c->integrator != KH_INT_VL2 && (c->precision != KH_FP64 || c->bfield != KH_B_FLUXCT)) return KH_EINVAL;
   if (c->bfield != KH_B_FLUXCT && c->bfield != KH_B_FACE) return KH_EINVAL;
   if (c->emf != KH_EMF_AVERAGE && c->emf != KH_EMF_GS05) return KH_EINVAL;
   if (c->bfield == KH_B_FACE && c->fofc) return KH_EINVAL;
@@ -315,6 +318,7 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
   S.cfl = c->cfl;
   S.recon = c->recon;
   S.fofc = c->fofc;
+  S.integrator = c->integrator;
   S.bfield = c->bfield;
   S.emf = c->emf;
   for (int q = 0; q < 6; ++q) S.bc[q] = c->bc[q];
@@ -378,6 +382,11 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
         KH_ALLOC(x->dirichletf[f], (size_t)NV * L.n3s * L.n2s * L.ng * sizeof(float));
   }
   KH_ALLOC(x->pflag, (size_t)L.plane);
+  if (c->integrator != KH_INT_VL2) {
+    // stage states, the stage base and SSPRK(5,4)'s stage-4 increment
+    const int nrk = c->integrator == KH_INT_SSPRK54 ? 6 : (c->integrator == KH_INT_RK2 ? 2 : 0);
+    if (nrk) KH_ALLOC(x->rk, (size_t)nrk * NV * pl);
+  }
   if (c->bfield == KH_B_FACE) {
     KH_ALLOC(x->fBstar, 3 * pl);
     if (c->emf == KH_EMF_GS05) {
@@ -503,6 +512,71 @@ int kh_fluxes(kh_ctx* x, const double* P, const double* B, double* F1, double* F
 
 namespace {
 
+// One Runge-Kutta step (FP64, Flux-CT) in Shu-Osher form: stage s forms its
+// base sum_j a_sj U_j (k_lincomb) and runs the predictor-corrector's stage
+// with coefficient c_s (run_stage: U_s = base + c_s dt L(P), inversion in
+// place on P -- every kernel that reads the stage input runs before the
+// update overwrites it). Stage states live in x->rk (8 planes each), then
+// the base (8 planes) and SSPRK(5,4)'s stage-4 increment (8 planes).
+//   RK1: U1 = U0 + dt L.  RK2: U1 = U0 + dt L; U2 = (U0 + U1)/2 + dt/2 L.
+//   SSPRK(5,4) (Spiteri & Ruuth 2002): the published five-stage table, the
+//   fifth stage reusing stage 4's raw increment c4 dt L(P3).
+int issue_rk(kh_ctx* x, double* U, const Vars& Pn) {
+  const Layout& L = x->L;
+  cudaStream_t s = x->stream;
+  const long long n8 = (long long)NV * L.plane;
+  double* st[5] = {U, x->rk, x->rk + n8, x->rk + 2 * n8, x->rk + 3 * n8};
+  const int nst = x->S.integrator == KH_INT_SSPRK54 ? 4 : (x->S.integrator == KH_INT_RK2 ? 1 : 0);
+  double* base = x->rk + nst * n8;
+  double* dU4 = base + n8;
+  int n = 0;
+  auto stage = [&](int q, const double* U0, double* Uout, double c, double* dUout) {
+    // each stage appends to the failed-zone list of slot q % 2: start it empty
+    cudaMemsetAsync(x->counters + CNT_LIST0 + (q % 2), 0, sizeof(unsigned long long), s);
+    n += run_stage(x, q % 2, U0, Pn, Pn, Uout, c, dUout);
+  };
+  auto comb = [&](int nt, const double* const* in, const double* a) {
+    n += launch_lincomb(base, nt, in, a, n8, s);
+  };
+  if (x->S.integrator == KH_INT_RK1) {
+    stage(0, U, U, 1.0, nullptr);
+  } else if (x->S.integrator == KH_INT_RK2) {
+    stage(0, U, st[1], 1.0, nullptr);
+    const double* in[2] = {U, st[1]};
+    const double a[2] = {0.5, 0.5};
+    comb(2, in, a);
+    stage(1, base, U, 0.5, nullptr);
+  } else {
+    const double c4 = 0.544974750228521, c53 = 0.063692468666290;
+    stage(0, U, st[1], 0.391752226571890, nullptr);
+    {
+      const double* in[2] = {U, st[1]};
+      const double a[2] = {0.444370493651235, 0.555629506348765};
+      comb(2, in, a);
+      stage(1, base, st[2], 0.368410593050371, nullptr);
+    }
+    {
+      const double* in[2] = {U, st[2]};
+      const double a[2] = {0.620101851488403, 0.379898148511597};
+      comb(2, in, a);
+      stage(2, base, st[3], 0.251891774271694, nullptr);
+    }
+    {
+      const double* in[2] = {U, st[3]};
+      const double a[2] = {0.178079954393132, 0.821920045606868};
+      comb(2, in, a);
+      stage(3, base, st[4], c4, dU4);
+    }
+    {
+      const double* in[4] = {st[2], st[3], st[4], dU4};
+      const double a[4] = {0.517231671970585, 0.096059710526147, 0.386708617503269, c53 / c4};
+      comb(4, in, a);
+      stage(4, base, U, 0.226007483236906, nullptr);
+    }
+  }
+  return n;
+}
+
 // Issue the launches of one full step on x->stream (dt is read from
 // x->dscalar[3] by the update kernels).
 int issue_step(kh_ctx* x, double* U, double* P, double* B) {
@@ -515,8 +589,14 @@ int issue_step(kh_ctx* x, double* U, double* P, double* B) {
   int n = 0;
   if (x->c.precision == KH_FP64) {
     // stage 1: P^n -> P* (U* is not stored); stage 2: P* -> P^{n+1}, U^{n+1} in place
-    n += run_stage(x, 0, U, Pn, Ps, nullptr, 0.5);
-    n += run_stage(x, 1, U, Ps, Pn, U, 1.0);
+    if (x->S.integrator != KH_INT_VL2) {
+      const int r = issue_rk(x, U, Pn);
+      if (r < 0) return r;
+      n += r;
+    } else {
+      n += run_stage(x, 0, U, Pn, Ps, nullptr, 0.5);
+      n += run_stage(x, 1, U, Ps, Pn, U, 1.0);
+    }
     mark(x, KH_T_CFL, 1, 0);
     n += launch_cfl<double>(x->ctop, L, x->S.cfl, x->partial, x->npartial, x->dscalar, s);
     mark(x, KH_T_CFL, 1, 1);

@@ -27,6 +27,7 @@ struct kh_ctx {
   double* fBstar;
   double* ecc;
   float* eccf;     // the cell-centred EMFs of KH_MIXED (FP32)
+  double* rk;      // Runge-Kutta integrators: stage states, base, stage-4 increment (8 planes each)
   double* partial;
   int npartial;
   double* dscalar;              // [0] dt_cfl out, [1..2] divb max/sum, [3] dt in

@@ -57,6 +57,7 @@ struct Scheme {
   int recon;
   int fofc;  // first-order flux correction on
   int bfield; // KH_B_FLUXCT | KH_B_FACE
+  int integrator;  // KH_INT_*
   int emf;    // KH_EMF_AVERAGE | KH_EMF_GS05 (face CT)
   int bc[6];
   FloorParams fl;
@@ -133,7 +134,9 @@ int launch_fofc_faces(int D, const CVarsT<TIN>& P, const Layout& L, const GeomT<
 int launch_update(const double* U0, const CVars& Pin, const Vars& Pout, double* Uout, double* const F[3],
                   const Layout& L, const DevGeom& G, const Scheme& S, const double* dtp, double coef, int8_t* pflag,
                   unsigned long long* cnt, int tpb, cudaStream_t s, FailList fl = FailList{nullptr, nullptr},
-                  const double* fBn = nullptr);
+                  const double* fBn = nullptr, double* dUout = nullptr);
+// out = sum_t a[t] in[t] over n values (nterm <= 4).
+int launch_lincomb(double* out, int nterm, const double* const* in, const double* a, long long n, cudaStream_t s);
 // Face-centred CT of one stage (S.emf: KH_EMF_AVERAGE | KH_EMF_GS05): cell
 // EMFs into ecc (GS05 only), edge EMFs from the raw fluxes F into emf[3],
 // then fBout = fB0 + coef dtp[0] curl E on the interior cells' faces.

@@ -217,13 +217,28 @@ template <int INV>
 __global__ void __launch_bounds__(TPB_MAX) k_update(const double* U0, CVars Pin, Vars Pout, double* Uout,
                                                    const double* F1, const double* F2, const double* F3, Layout L,
                                                    DevGeom G, Scheme S, const double* dtp, double coef, int8_t* pflag,
-                                                   unsigned long long* cnt, FailList fl, const double* fBn) {
+                                                   unsigned long long* cnt, FailList fl, const double* fBn,
+                                                   double* dUout) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nzones(L)) return;
   int i, j, k;
   zone_ijk(L, t, i, j, k);
   update_zone<false, INV>(U0, Pin, Pout, Uout, F1, F2, F3, L, G, S, coef * __ldg(dtp), pflag, cnt, i, j, k, nullptr,
-                          fl, fBn);
+                          fl, fBn, dUout);
+}
+
+// out = sum_t a_t in_t over n values (Runge-Kutta stage bases; up to 4 terms).
+struct LinComb {
+  const double* in[4];
+  double a[4];
+  int n;
+};
+__global__ void k_lincomb(double* out, LinComb lc, long long n) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    double s = lc.a[0] * lc.in[0][q];
+    for (int t = 1; t < lc.n; ++t) s += lc.a[t] * lc.in[t][q];
+    out[q] = s;
+  }
 }
 
 // three blocks of TPB_MAX per SM: ~80 registers (a few spill to L1); measured faster
@@ -739,17 +754,18 @@ template int launch_ct<float>(float* const[3], float* const[3], const Layout&, c
 
 int launch_update(const double* U0, const CVars& Pin, const Vars& Pout, double* Uout, double* const F[3],
                   const Layout& L, const DevGeom& G, const Scheme& S, const double* dtp, double coef, int8_t* pflag,
-                  unsigned long long* cnt, int tpb, cudaStream_t s, FailList fl, const double* fBn) {
+                  unsigned long long* cnt, int tpb, cudaStream_t s, FailList fl, const double* fBn,
+                  double* dUout) {
   const long long nz = (long long)L.n1 * L.n2 * L.n3;
   if (S.c2p.method == C2P_KASTAUN)
     k_update<C2P_KASTAUN><<<nblocks(nz, tpb), tpb, 0, s>>>(U0, Pin, Pout, Uout, F[0], F[1], F[2], L, G, S, dtp, coef,
-                                                           pflag, cnt, fl, fBn);
+                                                           pflag, cnt, fl, fBn, dUout);
   else if (S.c2p.method == C2P_1DW)
     k_update<C2P_1DW><<<nblocks(nz, tpb), tpb, 0, s>>>(U0, Pin, Pout, Uout, F[0], F[1], F[2], L, G, S, dtp, coef,
-                                                       pflag, cnt, fl, fBn);
+                                                       pflag, cnt, fl, fBn, dUout);
   else
     k_update<C2P_NOBLE2D><<<nblocks(nz, tpb), tpb, 0, s>>>(U0, Pin, Pout, Uout, F[0], F[1], F[2], L, G, S, dtp, coef,
-                                                           pflag, cnt, fl, fBn);
+                                                           pflag, cnt, fl, fBn, dUout);
   return 1;
 }
 
@@ -867,6 +883,19 @@ template int launch_face_ct<double>(const CVarsT<double>&, double* const[3], dou
 template int launch_face_ct<float>(const CVarsT<float>&, float* const[3], float*, float* const[3], const double*,
                                    double*, const Layout&, const GeomT<float>&, const Scheme&, const double*, double,
                                    cudaStream_t);
+
+int launch_lincomb(double* out, int nterm, const double* const* in, const double* a, long long n, cudaStream_t s) {
+  LinComb lc{};
+  for (int t = 0; t < nterm; ++t) {
+    lc.in[t] = in[t];
+    lc.a[t] = a[t];
+  }
+  lc.n = nterm;
+  long long b = nblocks(n, TPB);
+  if (b > 152 * 16) b = 152 * 16;
+  k_lincomb<<<(int)b, TPB, 0, s>>>(out, lc, n);
+  return 1;
+}
 
 int launch_face_divb(const double* fB, const Layout& L, double* partial, int npartial, double* out2, cudaStream_t s) {
   k_face_divb<<<npartial, RED_THREADS, 0, s>>>(fB, L, partial);

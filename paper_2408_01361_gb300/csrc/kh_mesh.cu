@@ -505,6 +505,7 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
   if (c->recon != KH_RECON_MC && c->recon != KH_RECON_WENO5) return KH_EINVAL;
   if (c->fofc) return KH_EINVAL;  // the flux correction runs on single grids
   if (c->inverter != KH_INV_NOBLE2D) return KH_EINVAL;  // the mesh kernels carry Noble-2D
+  if (c->integrator != KH_INT_VL2) return KH_EINVAL;    // the mesh steps with the predictor-corrector
   if (c->bfield != KH_B_FLUXCT) return KH_EINVAL;  // face-centred CT: single grids
   if (!(gamma > 1.0) || !(c->cfl > 0.0) || !(fabs(a) < 1.0)) return KH_EINVAL;
   for (int q = 0; q < 6; ++q) {

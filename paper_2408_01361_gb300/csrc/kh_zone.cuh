@@ -346,7 +346,8 @@ __device__ __forceinline__ void update_zone(const double* U0, const CVars& Pin, 
                                             const double* F1, const double* F2, const double* F3, const Layout& L,
                                             const DevGeom& G, const Scheme& S, double cdt, int8_t* pflag,
                                             unsigned long long* cnt, int i, int j, int k, double* Praw = nullptr,
-                                            FailList fl = FailList{nullptr, nullptr}, const double* fBn = nullptr) {
+                                            FailList fl = FailList{nullptr, nullptr}, const double* fBn = nullptr,
+                                            double* dUout = nullptr) {
   const long long c = L.at(k, j, i);
   const long long p = (long long)j * L.n1s + i;
   const long long sj = L.n1s, sk = (long long)L.n1s * L.n2s;
@@ -363,6 +364,7 @@ __device__ __forceinline__ void update_zone(const double* U0, const CVars& Pin, 
     double div = (F1[o + 1] - F1[o]) * L.idx[0] + (F2[o + sj] - F2[o]) * L.idx[1];
     if (L.ndim == 3) div += (F3[o + sk] - F3[o]) * L.idx[2];
     U[v] = U0[o] + cdt * (-div + Sv[v]);
+    if (dUout) dUout[o] = cdt * (-div + Sv[v]);  // the raw increment (Runge-Kutta stages)
   }
   if (fBn) face_means(fBn, L, c, U + V_B1);  // face-centred CT: sqrt(-g) B from the updated faces
   double Pn[NV];

