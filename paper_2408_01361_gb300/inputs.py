@@ -517,6 +517,63 @@ def torus_state(cfg: dict, seed: int = 2, noise: float = 4e-2, kappa: float = 1e
 
 
 # ---------------------------------------------------------------------------
+# Minkowski test problems the paper cites beside the linear modes ("Readiness
+# and Testing" section): the Orszag-Tang vortex and Komissarov's (1999)
+# magnetised cylindrical explosion, in the relativistic setting below (the
+# paper names the problems, not their parameters).
+# ---------------------------------------------------------------------------
+def orszag_tang_cfg(n: int = 256, recon: str = "mc") -> dict:
+    """[0, 2 pi)^2 periodic, gamma = 5/3, CFL 0.9."""
+    return dict(
+        name=f"orszag-tang {n}^2", coords="minkowski", n1=n, n2=n, n3=1, recon=recon, bc=["periodic"] * 6,
+        a=0.0, gam=5.0 / 3.0, x1=(0.0, 2 * math.pi), x2=(0.0, 2 * math.pi), x3=(0.0, 1.0), cfl=0.9,
+        floors=dict(rho_min=1e-6, u_min=1e-8),
+    )
+
+
+def orszag_tang_state(cfg: dict, v0: float = 0.5, B0: float = 1.0) -> np.ndarray:
+    """rho = 25/9, p = 5/3, 3-velocity v = v0 (-sin y, sin x), B = B0 (-sin y,
+    sin 2x); u~ = W v. The state is odd under the half-turn about the
+    centre ((x, y) -> (2 pi - x, 2 pi - y), v -> -v, B -> -B)."""
+    X2, X1 = np.meshgrid(centers(cfg, 1), centers(cfg, 0), indexing="ij")
+    v1, v2 = -v0 * np.sin(X2), v0 * np.sin(X1)
+    W = 1.0 / np.sqrt(1.0 - v1 * v1 - v2 * v2)
+    P = np.zeros(shape(cfg))
+    P[0] = 25.0 / 9.0
+    P[1] = (5.0 / 3.0) / (cfg["gam"] - 1.0)
+    P[2], P[3] = W * v1, W * v2
+    P[5], P[6] = -B0 * np.sin(X2), B0 * np.sin(2.0 * X1)
+    return P
+
+
+def explosion_cfg(n: int = 256, recon: str = "mc", B0: float = 0.1) -> dict:
+    """[-6, 6]^2, outflow boundaries, gamma = 4/3, CFL 0.5."""
+    return dict(
+        name=f"cylindrical explosion {n}^2", coords="minkowski", n1=n, n2=n, n3=1, recon=recon,
+        bc=["outflow", "outflow", "outflow", "outflow", "periodic", "periodic"], a=0.0, gam=4.0 / 3.0,
+        x1=(-6.0, 6.0), x2=(-6.0, 6.0), x3=(0.0, 1.0), cfl=0.5, B0=B0,
+        floors=dict(rho_min=1e-8, u_min=1e-10, bsq_rho_max=1e4, bsq_u_max=1e6),
+    )
+
+
+def explosion_state(cfg: dict) -> np.ndarray:
+    """Komissarov (1999): rho = 1e-2, p = 1 for r < 0.8; rho = 1e-4, p = 5e-4
+    for r > 1; log-linear in r between; at rest; uniform B = (B0, 0, 0).
+    Mirror-symmetric about both axes (x -> -x with u~1, B2, B3 odd; y -> -y
+    with u~2, B2 odd)."""
+    X2, X1 = np.meshgrid(centers(cfg, 1), centers(cfg, 0), indexing="ij")
+    r = np.sqrt(X1 * X1 + X2 * X2)
+    w = np.clip((r - 0.8) / 0.2, 0.0, 1.0)
+    rho = np.exp((1 - w) * np.log(1e-2) + w * np.log(1e-4))
+    p = np.exp((1 - w) * np.log(1.0) + w * np.log(5e-4))
+    P = np.zeros(shape(cfg))
+    P[0] = rho
+    P[1] = p / (cfg["gam"] - 1.0)
+    P[5] = cfg.get("B0", 0.1)
+    return P
+
+
+# ---------------------------------------------------------------------------
 # Face-centred fields (for face-centred constrained transport): arrays
 # (3, N3, N2, N1), entry a = sqrt(-g) B^(a+1) on the lower x^(a+1) face of
 # each cell (a 2-D grid keeps sqrt(-g) B^3 per cell).
