@@ -63,6 +63,7 @@ def parse():
     p.add_argument("--no-fofc", action="store_true", help="skip the first-order flux correction leg")
     p.add_argument("--no-facect", action="store_true", help="skip the face-centred constrained transport leg")
     p.add_argument("--no-inverters", action="store_true", help="skip the primitive-recovery solver leg")
+    p.add_argument("--no-workloads", action="store_true", help="skip the Orszag-Tang / explosion leg")
     p.add_argument("--smr-only", action="store_true", help="run only the statically refined torus leg")
     p.add_argument("--precisions", default="mixed,fp64",
                    help="comma list; the first is the headline, the others are reported beside it")
@@ -488,6 +489,46 @@ def measure_inverters(args, cfg64, P0, dev, stream):
     return out
 
 
+def measure_workloads(args, dev, stream, n=2048):
+    """The Minkowski test problems as throughput workloads: the Orszag-Tang
+    vortex and the cylindrical explosion on n^2 grids, mixed and FP64, timed
+    as CUDA graphs after a warm-up."""
+    import torch
+
+    from paper_2408_01361_gb300 import inputs, kh
+
+    out = {}
+    for name, mk, st in (("orszag_tang", inputs.orszag_tang_cfg, inputs.orszag_tang_state),
+                         ("explosion", inputs.explosion_cfg, inputs.explosion_state)):
+        res = {"zones": n * n}
+        for prec in args.precisions:
+            cfg = dict(mk(n), precision=prec)
+            ctx = kh.Context(cfg, device=dev)
+            PB = ctx.to_device(st(cfg))
+            P, B = ctx.split(PB)
+            U = ctx.empty(8)
+            ctx.prim_to_cons(P, B, U)
+            dt = ctx.cfl_dt(P, B)
+            ctx.autotune(U, P, B, dt)
+            for _ in range(max(args.warmup, 3)):
+                dt, _ = ctx.step(U, P, B, dt)
+            ctx.set_graph(True)
+            dt, _ = ctx.step(U, P, B, dt)
+            steps = max(args.steps, 5)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            for _ in range(steps):
+                dt, _ = ctx.step(U, P, B, dt)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1) / steps
+            res[prec] = {"value": n * n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms}
+            ctx.close()
+        out[name] = res
+    return out
+
+
 def measure_smr(args, dev, stream, precision):
     """The statically refined torus (3 levels, 592 uneven blocks, 5.57 M zones)
     stepped as one mesh: every kernel covers all blocks, ghost zones of every
@@ -749,6 +790,8 @@ def run_kh(args, world, rank, local):
             fc[p] = measure_facect(args, cfg64, P0, dev, stream, p)
             fc[p]["cost_vs_flux_ct_graph"] = results[p]["graph"]["value"] / fc[p]["graph"]["value"]
         line["face_ct"] = fc
+    if not args.no_workloads and world == 1:
+        line["workloads_2d"] = measure_workloads(args, dev, stream)
     if not args.no_inverters and world == 1:
         line["inverters"] = measure_inverters(args, cfg64, P0, dev, stream)
     if not args.no_adjoint and world == 1:
