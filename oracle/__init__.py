@@ -140,6 +140,9 @@ def lib():
         L.or_step_face.restype = C.c_double
         L.or_face_divb.argtypes = [PP, _dp, _dp, C.c_void_p]
         L.or_face_to_cell.argtypes = [PP, _dp, _dp]
+        L.or_face_emfs.argtypes = [PP, _dp, _dp]
+        L.or_stage_face.argtypes = [PP, _dp, _dp, C.c_double, _dp, _dp, _dp, _dp, _dp, C.c_void_p, C.c_void_p,
+                                    C.c_void_p, C.POINTER(C.c_long)]
         L.or_fofc_flags.restype = C.c_long
     return _lib
 
@@ -411,3 +414,24 @@ def face_to_cell(cfg: dict, fB, P):
     P = np.array(P, dtype=np.float64, order="C", copy=True)
     lib().or_face_to_cell(C.byref(params(cfg)), np.ascontiguousarray(fB, dtype=np.float64), P)
     return P
+
+
+def face_emfs(cfg: dict, Pin):
+    """Edge EMFs of face-centred CT from a ghost-filled state: (3, N3, N2, N1)."""
+    Pin = np.ascontiguousarray(Pin, dtype=np.float64)
+    E = np.zeros((3,) + Pin.shape[1:])
+    lib().or_face_emfs(C.byref(params(cfg)), Pin, E)
+    return E
+
+
+def stage_face(cfg: dict, U0, Pin, cdt: float, E, fB0, fBout, Uout, Pout):
+    """One face-CT stage with caller-supplied edge EMFs; fBout, Uout, Pout
+    updated in place. Returns (ctop[3] arrays, stats)."""
+    U0 = np.ascontiguousarray(U0, dtype=np.float64)
+    Pin = np.ascontiguousarray(Pin, dtype=np.float64)
+    ct = [np.zeros(Pin.shape[1:]) for _ in range(3)]
+    st = (C.c_long * 4)()
+    lib().or_stage_face(C.byref(params(cfg)), U0, Pin, float(cdt), np.ascontiguousarray(E, dtype=np.float64),
+                        np.ascontiguousarray(fB0, dtype=np.float64), fBout, Uout, Pout, *[_ptr(c) for c in ct], st)
+    _note(st)
+    return ct, list(st)[:3]

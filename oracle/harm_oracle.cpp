@@ -744,16 +744,22 @@ long fofc_correct(const Grid& gr, const R* U0, const R* Pin, const R& gam, doubl
 template <class R>
 void stage(const Grid& gr, const R* U0, const R* Pin, const R& gam, double cdt, R* Uout, R* Pout,
            FluxesT<R>& fx, StageStats& st, std::vector<int>* pflag_out, std::vector<int>* fflag_out = nullptr,
-           const R* fB0 = nullptr, R* fBout = nullptr, R* dU_out = nullptr) {
+           const R* fB0 = nullptr, R* fBout = nullptr, R* dU_out = nullptr, const R* Egiven = nullptr) {
   const GridInfo& g = gr.g;
   const bool face = gr.c.bfield == BFIELD_FACE;
   if (face) {
     // face-centred CT: the raw fluxes move the fluid; the edge EMFs move the
-    // face field, whose cell means become the zones' sqrt(-g) B
+    // face field, whose cell means become the zones' sqrt(-g) B (Egiven: the
+    // edge EMFs supplied by the caller, [3][cells], as a refined mesh
+    // corrects them at level interfaces)
     compute_raw(gr, Pin, fx, gam);
     polar_zero(gr, fx);
     std::vector<R> E[3];
-    face_emfs(gr, Pin, fx, E);
+    if (Egiven) {
+      for (int c = 0; c < 3; ++c) E[c].assign(Egiven + c * gr.cells(), Egiven + (c + 1) * gr.cells());
+    } else {
+      face_emfs(gr, Pin, fx, E);
+    }
     face_update(gr, fB0, E, cdt, fBout);
   } else if (gr.c.fofc) {
     FluxesT<R> raw;
@@ -1204,6 +1210,42 @@ double or_step_face(const or_params* c, double* U, double* P, double* fB, double
     stats[3] = st.nfofc;
   }
   return dtn;
+}
+
+// The edge EMFs of face-centred CT from a ghost-filled state ([3][cells],
+// entries the interior faces need; others 0).
+void or_face_emfs(const or_params* c, const double* Pin, double* E) {
+  Grid gr;
+  build_grid(*c, gr);
+  Fluxes fx;
+  compute_raw(gr, Pin, fx, c->gam);
+  polar_zero(gr, fx);
+  std::vector<double> Ev[3];
+  face_emfs(gr, Pin, fx, Ev);
+  for (int q = 0; q < 3; ++q) std::memcpy(E + q * gr.cells(), Ev[q].data(), gr.cells() * sizeof(double));
+}
+
+// One face-CT stage on a grid with caller-filled ghosts and caller-supplied
+// edge EMFs E ([3][cells]): fBout = fB0 + cdt curl E on the interior cells'
+// faces, then the zone update as or_stage with the zones' field from the new
+// faces. ctop as or_stage.
+void or_stage_face(const or_params* c, const double* U0, const double* Pin, double cdt, const double* E,
+                   const double* fB0, double* fBout, double* Uout, double* Pout, double* ct1, double* ct2, double* ct3,
+                   long* stats) {
+  Grid gr;
+  build_grid(*c, gr);
+  Fluxes fx;
+  StageStats st;
+  stage<double>(gr, U0, Pin, c->gam, cdt, Uout, Pout, fx, st, nullptr, nullptr, fB0, fBout, nullptr, E);
+  double* Co[3] = {ct1, ct2, ct3};
+  for (int d = 0; d < 3; ++d)
+    if (Co[d]) std::memcpy(Co[d], fx.ctop[d].data(), fx.ctop[d].size() * sizeof(double));
+  if (stats) {
+    stats[0] = st.nfail;
+    stats[1] = st.nfloor;
+    stats[2] = st.nunfixed;
+    stats[3] = st.nfofc;
+  }
 }
 
 // Face divergence of a face field: per interior cell sum_a (fB_a(upper) -

@@ -24,6 +24,15 @@ ghost cell's centre:
 Every block takes the same dt; there is no flux correction at level
 interfaces. Written from positions in floating point, independently of the
 CUDA library's integer map.
+
+With face-centred constrained transport (step_face) every block also
+carries its face field; after each block's edge EMFs are computed, an edge
+of a coarse block that lies on the surface of a block one level finer takes
+the fine block's EMF there (the mean of the two fine edges along it where
+the edge's own direction is refined), so that the coarse face on the
+interface moves exactly as the mean of the fine faces covering it and the
+face divergence stays zero on both sides. (Interfaces across a periodic
+domain edge are not matched; the layouts here have none.)
 """
 from __future__ import annotations
 
@@ -31,7 +40,7 @@ import math
 
 import numpy as np
 
-from . import stage
+from . import face_emfs, stage, stage_face
 
 NV = 8
 
@@ -250,3 +259,101 @@ class OracleMesh:
             cts.append(ct)
             tot = [a + c for a, c in zip(tot, st)]
         return Uout, Pout, self.cfl_dt(cts), tot
+
+    # ---- face-centred constrained transport ----
+    def _edge_ranges(self, b, c):
+        """Local index ranges (lo, hi inclusive) per direction of block b's
+        edges along x^(c+1) that its interior faces need."""
+        cfg = self.cfgs[b]
+        n = (cfg["n1"], cfg["n2"], cfg["n3"])
+        out = []
+        for q in range(3):
+            active = q < 2 or self.ndim == 3
+            if not active:
+                out.append((0, 0))
+                continue
+            g = self.ng
+            out.append((g, g + n[q] - 1) if q == c else (g, g + n[q]))
+        return out
+
+    def _global(self, b, q, i):
+        blk = self.blocks[b]
+        o = (blk["i0"], blk["j0"], blk["k0"])[q]
+        active = q < 2 or self.ndim == 3
+        return o + i - self.ng if active else 0
+
+    def _local(self, f, q, G):
+        blk = self.blocks[f]
+        o = (blk["i0"], blk["j0"], blk["k0"])[q]
+        active = q < 2 or self.ndim == 3
+        return G - o + self.ng if active else 0
+
+    def emf_matches(self):
+        """[(b, c, (k, j, i), f, [(k, j, i), ...])]: the coarse edges of block b
+        on the surface of a block f one level finer, with the fine edges whose
+        mean replaces them."""
+        out = []
+        for b, bb in enumerate(self.blocks):
+            for f, fb in enumerate(self.blocks):
+                if fb["level"] != bb["level"] + 1:
+                    continue
+                for c in range(3):
+                    rb = self._edge_ranges(b, c)
+                    rf = self._edge_ranges(f, c)
+                    for k in range(rb[2][0], rb[2][1] + 1):
+                        for j in range(rb[1][0], rb[1][1] + 1):
+                            for i in range(rb[0][0], rb[0][1] + 1):
+                                loc = (i, j, k)
+                                fine = []
+                                ok = True
+                                for q in range(3):
+                                    active = q < 2 or self.ndim == 3
+                                    G = self._global(b, q, loc[q])
+                                    if not active:
+                                        fine.append([0])
+                                    elif q == c:
+                                        fine.append([self._local(f, q, 2 * G), self._local(f, q, 2 * G + 1)])
+                                    else:
+                                        fine.append([self._local(f, q, 2 * G)])
+                                    for x in fine[-1]:
+                                        if not (rf[q][0] <= x <= rf[q][1]):
+                                            ok = False
+                                if not ok:
+                                    continue
+                                cells = [(kk, jj, ii) for kk in fine[2] for jj in fine[1] for ii in fine[0]]
+                                out.append((b, c, (k, j, i), f, cells))
+        return out
+
+    def _correct(self, Es, matches):
+        for b, c, (k, j, i), f, cells in matches:
+            Es[b][c][k, j, i] = sum(Es[f][c][kk, jj, ii] for kk, jj, ii in cells) / len(cells)
+
+    def step_face(self, Us, Ps, fBs, dt):
+        """One two-stage step with face-centred CT (every block's cfg has bfield
+        "face"): returns (Us, Ps, fBs, dt_cfl, stats)."""
+        matches = self.emf_matches()
+        Pn = [np.array(P, copy=True) for P in Ps]
+        U0 = [np.array(U, copy=True) for U in Us]
+        f0 = [np.array(f, copy=True) for f in fBs]
+        tot = [0, 0, 0]
+        self.fill_ghosts(Pn)
+        Ps_ = [np.array(P, copy=True) for P in Pn]
+        Us_ = [np.array(U, copy=True) for U in U0]
+        fs_ = [np.array(f, copy=True) for f in f0]
+        Es = [face_emfs(self.cfgs[b], Pn[b]) for b in range(len(Pn))]
+        self._correct(Es, matches)
+        for b in range(len(Pn)):
+            _, st = stage_face(self.cfgs[b], U0[b], Pn[b], 0.5 * dt, Es[b], f0[b], fs_[b], Us_[b], Ps_[b])
+            tot = [a + c for a, c in zip(tot, st)]
+        self.fill_ghosts(Ps_)
+        Pout = [np.array(P, copy=True) for P in Pn]
+        Uout = [np.array(U, copy=True) for U in U0]
+        fout = [np.array(f, copy=True) for f in f0]
+        Es = [face_emfs(self.cfgs[b], Ps_[b]) for b in range(len(Pn))]
+        self._correct(Es, matches)
+        cts = []
+        for b in range(len(Pn)):
+            ct, st = stage_face(self.cfgs[b], U0[b], Ps_[b], dt, Es[b], f0[b], fout[b], Uout[b], Pout[b])
+            cts.append(ct)
+            tot = [a + c for a, c in zip(tot, st)]
+        return Uout, Pout, fout, self.cfl_dt(cts), tot
