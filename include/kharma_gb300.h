@@ -324,7 +324,15 @@ int kh_get_stage_flux(kh_ctx* ctx, int dir, double* F);
  * zero where one is missing (past a non-periodic domain edge, or inside a
  * still coarser block). Every block takes the same dt (no sub-cycling);
  * fluxes at level interfaces are not corrected (no refluxing) and Flux-CT
- * keeps divB only inside blocks.
+ * keeps divB only inside blocks. With face-centred CT (kh_coords.bfield =
+ * KH_B_FACE) each block carries its face field in an arena like B's (3 planes
+ * per block at fB + 3 * off_b; kh_mesh_set_face_field); after the blocks'
+ * edge EMFs are computed, every coarse edge lying on the surface of a block
+ * one level finer takes the fine block's EMF there (the mean of the two fine
+ * edges along a refined edge direction), so each coarse face on a level
+ * interface moves exactly as the mean of the fine faces covering it and the
+ * face divergence stays zero in every block (interfaces across a periodic
+ * domain edge are not matched).
  *
  * kh_mesh_init returns KH_EINVAL for blocks that overlap, leave a hole, are
  * smaller than 4 cells a side (n3 == 1 in 2-D), are misaligned, meet a block
@@ -340,6 +348,10 @@ typedef struct kh_mesh kh_mesh;
 
 int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const kh_block* blocks, kh_mesh** out);
 int kh_mesh_block_shape(const kh_mesh* mesh, int b, int* n1s, int* n2s, int* n3s, int64_t* cell_offset);
+/* KH_B_FACE meshes: register the face-field arena (device, caller-owned,
+ * 3 planes per block as above) that every later kh_mesh_step advances. The
+ * zones' B must be the face means over sqrt(-g) when stepping starts. */
+int kh_mesh_set_face_field(kh_mesh* mesh, double* fB);
 int64_t kh_mesh_cells(const kh_mesh* mesh);       /* sum of the blocks' allocation planes */
 int64_t kh_mesh_zones(const kh_mesh* mesh);       /* interior zones of all blocks */
 int64_t kh_mesh_ghost_cells(const kh_mesh* mesh); /* entries of the ghost map */

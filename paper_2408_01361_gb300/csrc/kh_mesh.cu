@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(256) km_update(const MBlock* blk, const unsign
                                                 Arena<double> Pin, Arena<double> Pout, double* Uout,
                                                 const double* F1, const double* F2, const double* F3, GeoArena GA,
                                                 Scheme S, const double* dtp, double coef, int8_t* pflag,
-                                                unsigned long long* cnt) {
+                                                unsigned long long* cnt, const double* fBn) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= __ldg(pre + nb)) return;
   const int b = find_block(pre, nb, t);
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(256) km_update(const MBlock* blk, const unsign
   const long long o8 = NV * m.off;
   update_zone(U0 + o8, cvars_at(Pin, m), vars_at(Pout, m), Uout ? Uout + o8 : nullptr, F1 + o8, F2 + o8,
               m.L.ndim == 3 ? F3 + o8 : nullptr, m.L, geo64(GA, m), S, coef * __ldg(dtp), pflag + m.off, cnt, i, j,
-              k);
+              k, nullptr, FailList{nullptr, nullptr}, fBn ? fBn + 3 * m.off : nullptr);
 }
 
 __global__ void __launch_bounds__(256, 2) km_update_mixed(const MBlock* blk, const unsigned* pre, int nb,
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(256, 2) km_update_mixed(const MBlock* blk, con
                                                       Arena<float> Pout32, double* Uout, const float* F1,
                                                       const float* F2, const float* F3, GeoArena GA, Scheme S,
                                                       const double* dtp, double coef, int8_t* pflag,
-                                                      unsigned long long* cnt) {
+                                                      unsigned long long* cnt, const double* fBn) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= __ldg(pre + nb)) return;
   const int b = find_block(pre, nb, t);
@@ -195,7 +195,8 @@ __global__ void __launch_bounds__(256, 2) km_update_mixed(const MBlock* blk, con
   if (Pout32.a) P32 = vars_at(Pout32, m); else for (int v = 0; v < NV; ++v) P32.v[v] = nullptr;
   update_mixed_zone(U0 + o8, cvars_at(Pin, m), P64, P32, Uout ? Uout + o8 : nullptr, F1 + o8, F2 + o8,
                     m.L.ndim == 3 ? F3 + o8 : nullptr, m.L, geo64(GA, m), geo32(GA, m), S,
-                    df_of_f64(coef * __ldg(dtp)), pflag + m.off, cnt, i, j, k);
+                    df_of_f64(coef * __ldg(dtp)), pflag + m.off, cnt, i, j, k, FailList{nullptr, nullptr},
+                    fBn ? fBn + 3 * m.off : nullptr);
 }
 
 template <class T>
@@ -429,6 +430,117 @@ inline int nblk(long long n, int tpb) { return (int)((n + tpb - 1) / tpb); }
 // ---------------------------------------------------------------------------
 // The mesh context
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// Face-centred CT on the mesh: each block's face field lives in an arena of 3
+// planes per block (block b at 3 * off). Cell EMFs over every allocated cell
+// of every block (ghosts hold the filled state), edge EMFs over each block's
+// [s, e] box, then the interface matching (a coarse edge on the surface of a
+// finer block takes the fine EMF, the mean of the two fine edges along a
+// refined edge direction), then the face update.
+// ---------------------------------------------------------------------------
+template <class R>
+__global__ void km_cell_emf(const MBlock* blk, const unsigned* pre, int nb, Arena<R> Pin, GeoArena GA, R* ecc) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= __ldg(pre + nb)) return;
+  const int b = find_block(pre, nb, t);
+  const MBlock& m = blk[b];
+  const Layout& L = m.L;
+  int i, j, k;
+  split3(t - __ldg(pre + b), L.N1, L.N2, i, j, k);
+  const long long c = L.at(k, j, i);
+  const CVarsT<R> P = cvars_at(Pin, m);
+  R Pc[NV], E[3];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Pc[v] = P.v[v][c];
+  Met<R> mt;
+  if constexpr (sizeof(R) == sizeof(double)) mt = load_met(geo64(GA, m), L.gplane, LOC_CENT, (long long)j * L.n1s + i);
+  else mt = load_met(geo32(GA, m), L.gplane, LOC_CENT, (long long)j * L.n1s + i);
+  cell_emfs(Pc, mt, E);
+  R* out = ecc + 3 * m.off;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) out[q * L.plane + c] = E[q];
+}
+
+template <class R>
+__global__ void km_face_emf(const MBlock* blk, const unsigned* pre, int nb, const R* F1, const R* F2, const R* F3,
+                            const R* ecc, R* e1, R* e2, R* e3, int emf) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= __ldg(pre + nb)) return;
+  const int b = find_block(pre, nb, t);
+  const MBlock& m = blk[b];
+  const Layout& L = m.L;
+  int i, j, k;
+  split3(t - __ldg(pre + b), L.e[0] - L.s[0] + 1, L.e[1] - L.s[1] + 1, i, j, k);
+  i += L.s[0];
+  j += L.s[1];
+  k += (L.ndim == 3 ? L.s[2] : 0);
+  const long long o8 = NV * m.off, o1 = m.off, c = L.at(k, j, i);
+  const R* F[3] = {F1 + o8, F2 + o8, L.ndim == 3 ? F3 + o8 : nullptr};
+  const R* C = ecc ? ecc + 3 * m.off : nullptr;
+  const bool axis = (m.polar_lo && j == L.s[1]) || (m.polar_hi && j == L.e[1]);
+  if (L.ndim == 3) {
+    if (k < L.e[2]) e3[o1 + c] = axis ? R(0) : edge_emf<R>(2, F, C, L, emf, i, j, k);
+    if (i < L.e[0]) e1[o1 + c] = axis ? R(0) : edge_emf<R>(0, F, C, L, emf, i, j, k);
+    if (j < L.e[1]) e2[o1 + c] = edge_emf<R>(1, F, C, L, emf, i, j, k);
+  } else {
+    e3[o1 + c] = axis ? R(0) : edge_emf<R>(2, F, C, L, emf, i, j, k);
+    if (i < L.e[0]) e1[o1 + c] = axis ? R(0) : F[1][V_B3 * L.plane + c];
+    if (j < L.e[1]) e2[o1 + c] = -F[0][V_B3 * L.plane + c];
+  }
+}
+
+// One interface edge: E_c[dst] = mean of E_c[src[0..n)] (arena indices).
+struct EmfMatch {
+  long long dst, src[2];
+  int c, n;
+};
+template <class R>
+__global__ void km_emf_match(const EmfMatch* mt, long long nm, R* e1, R* e2, R* e3) {
+  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= nm) return;
+  const EmfMatch M = mt[q];
+  R* E = M.c == 0 ? e1 : (M.c == 1 ? e2 : e3);
+  E[M.dst] = M.n == 2 ? R(0.5) * (E[M.src[0]] + E[M.src[1]]) : E[M.src[0]];
+}
+
+template <class R>
+__global__ void km_face_update(const MBlock* blk, const unsigned* pre, int nb, const double* fB0, double* fBout,
+                               const R* e1, const R* e2, const R* e3, const double* dtp, double coef) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= __ldg(pre + nb)) return;
+  const int b = find_block(pre, nb, t);
+  const MBlock& m = blk[b];
+  const Layout& L = m.L;
+  int x[3];
+  split3(t - __ldg(pre + b), L.e[0] - L.s[0] + 1, L.e[1] - L.s[1] + 1, x[0], x[1], x[2]);
+  x[0] += L.s[0];
+  x[1] += L.s[1];
+  x[2] += (L.ndim == 3 ? L.s[2] : 0);
+  const long long c = L.at(x[2], x[1], x[0]);
+  const long long st[3] = {1, (long long)L.n1s, (long long)L.n1s * L.n2s};
+  const R* E[3] = {e1 + m.off, e2 + m.off, e3 + m.off};
+  const double cdt = coef * __ldg(dtp);
+  const double* f0 = fB0 + 3 * m.off;
+  double* f1 = fBout + 3 * m.off;
+  const int nd = L.ndim;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int bb = (a + 1) % 3, cc = (a + 2) % 3;
+    bool in = true;
+    for (int q = 0; q < nd; ++q)
+      if (q != a && x[q] >= L.e[q]) in = false;
+    if (!in) continue;
+    auto f64 = [](R v) -> double {
+      if constexpr (sizeof(R) == sizeof(double)) return v;
+      else return f64_of_f32(v);
+    };
+    double rhs = 0.0;
+    if (bb < nd) rhs += (f64(E[cc][c + st[bb]]) - f64(E[cc][c])) * L.idx[bb];
+    if (cc < nd) rhs -= (f64(E[bb][c + st[cc]]) - f64(E[bb][c])) * L.idx[cc];
+    f1[a * L.plane + c] = f0[a * L.plane + c] + cdt * rhs;
+  }
+}
+
 struct kh_mesh {
   kh_coords c;
   Scheme S;
@@ -471,6 +583,14 @@ struct kh_mesh {
   cudaGraphExec_t gexec;
   const void* gkey[3];
   int graph_launches;
+  // face-centred CT: the caller's face field, the stage-1 face field, cell
+  // EMFs (FP64 or FP32) and the interface EMF matches
+  double* fB;
+  double* fBstar;
+  double* ecc;
+  float* eccf;
+  EmfMatch* dmatch;
+  long long nmatch;
 };
 
 namespace {
@@ -506,7 +626,8 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
   if (c->fofc) return KH_EINVAL;  // the flux correction runs on single grids
   if (c->inverter != KH_INV_NOBLE2D) return KH_EINVAL;  // the mesh kernels carry Noble-2D
   if (c->integrator != KH_INT_VL2) return KH_EINVAL;    // the mesh steps with the predictor-corrector
-  if (c->bfield != KH_B_FLUXCT) return KH_EINVAL;  // face-centred CT: single grids
+  if (c->bfield != KH_B_FLUXCT && c->bfield != KH_B_FACE) return KH_EINVAL;
+  if (c->emf != KH_EMF_AVERAGE && c->emf != KH_EMF_GS05) return KH_EINVAL;
   if (!(gamma > 1.0) || !(c->cfl > 0.0) || !(fabs(a) < 1.0)) return KH_EINVAL;
   for (int q = 0; q < 6; ++q) {
     const int b = c->bc[q];
@@ -534,6 +655,8 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
   S.c2p.max_iter = c->newton_max_iter > 0 ? c->newton_max_iter : 30;
   S.c2p.tol = c->newton_tol > 0.0 ? c->newton_tol : 1e-14;
   S.c2p.method = c->inverter;
+  S.bfield = c->bfield;
+  S.emf = c->emf;
   set_mixed(S);
   x->cp = CoordParams{c->kind, a, c->x1min, c->hslope, c->poly_xt, c->poly_alpha, c->mks_smooth};
 
@@ -776,6 +899,68 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
   }
   x->corners = x->pre_corner.back();
 
+  // ---- face-centred CT: coarse edges on the surface of a finer block ----
+  std::vector<EmfMatch> matches;
+  if (c->bfield == KH_B_FACE) {
+    const int nd = x->ndim;
+    auto act = [&](int q) { return q < 2 || nd == 3; };
+    for (int b = 0; b < nblocks; ++b)
+      for (int f = 0; f < nblocks; ++f) {
+        const MBlock& mb = x->hb[b];
+        const MBlock& mf = x->hb[f];
+        if (mf.level != mb.level + 1) continue;
+        const int ob[3] = {mb.i0, mb.j0, mb.k0}, nb3[3] = {mb.L.n1, mb.L.n2, mb.L.n3};
+        const int of[3] = {mf.i0, mf.j0, mf.k0}, nf3[3] = {mf.L.n1, mf.L.n2, mf.L.n3};
+        bool touch = true;  // closed boxes in level-(l+1) indices
+        for (int q = 0; q < 3; ++q)
+          if (act(q) && (2 * (ob[q] + nb3[q]) < of[q] || of[q] + nf3[q] < 2 * ob[q])) touch = false;
+        if (!touch) continue;
+        for (int cdir = 0; cdir < 3; ++cdir) {
+          int lo[3], hi[3];
+          for (int q = 0; q < 3; ++q) {
+            lo[q] = act(q) ? mb.L.s[q] : 0;
+            hi[q] = act(q) ? (q == cdir ? mb.L.e[q] - 1 : mb.L.e[q]) : 0;
+          }
+          for (int k = lo[2]; k <= hi[2]; ++k)
+            for (int j = lo[1]; j <= hi[1]; ++j)
+              for (int i = lo[0]; i <= hi[0]; ++i) {
+                const int l[3] = {i, j, k};
+                bool edge_of_box = false;
+                for (int q = 0; q < 3; ++q)
+                  if (q != cdir && act(q) && (l[q] == mb.L.s[q] || l[q] == mb.L.e[q])) edge_of_box = true;
+                if (!edge_of_box) continue;
+                int fl[3][2], nfl[3];
+                bool ok = true;
+                for (int q = 0; q < 3; ++q) {
+                  if (!act(q)) {
+                    fl[q][0] = 0;
+                    nfl[q] = 1;
+                    continue;
+                  }
+                  const int G = ob[q] + (l[q] - mb.L.s[q]);
+                  const int flo = mf.L.s[q], fhi = q == cdir ? mf.L.e[q] - 1 : mf.L.e[q];
+                  nfl[q] = q == cdir ? 2 : 1;
+                  for (int r = 0; r < nfl[q]; ++r) {
+                    fl[q][r] = 2 * G + r - of[q] + mf.L.s[q];
+                    if (fl[q][r] < flo || fl[q][r] > fhi) ok = false;
+                  }
+                }
+                if (!ok) continue;
+                EmfMatch M{};
+                M.c = cdir;
+                M.dst = mb.off + mb.L.at(k, j, i);
+                M.n = 0;
+                for (int r2 = 0; r2 < nfl[2]; ++r2)
+                  for (int r1 = 0; r1 < nfl[1]; ++r1)
+                    for (int r0 = 0; r0 < nfl[0]; ++r0)
+                      M.src[M.n++] = mf.off + mf.L.at(fl[2][r2], fl[1][r1], fl[0][r0]);
+                matches.push_back(M);
+              }
+        }
+      }
+  }
+  x->nmatch = (long long)matches.size();
+
   // ---- device buffers ----
   int rc = KH_OK;
 #define KM_ALLOC(ptr, bytes) \
@@ -814,10 +999,11 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
       KM_ALLOC(x->ctop[d], pl);
     }
     KM_ALLOC(x->emf[2], pl);
-    if (x->ndim == 3) {
+    if (x->ndim == 3 || c->bfield == KH_B_FACE) {
       KM_ALLOC(x->emf[0], pl);
       KM_ALLOC(x->emf[1], pl);
     }
+    if (c->bfield == KH_B_FACE && c->emf == KH_EMF_GS05) KM_ALLOC(x->ecc, 3 * pl);
   } else {
     KM_ALLOC(x->geof, 3 * NGEO * gpf);
     KM_ALLOC(x->dgmf, NDG * gpf);
@@ -829,10 +1015,15 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
       KM_ALLOC(x->ctopf[d], plf);
     }
     KM_ALLOC(x->emff[2], plf);
-    if (x->ndim == 3) {
+    if (x->ndim == 3 || c->bfield == KH_B_FACE) {
       KM_ALLOC(x->emff[0], plf);
       KM_ALLOC(x->emff[1], plf);
     }
+    if (c->bfield == KH_B_FACE && c->emf == KH_EMF_GS05) KM_ALLOC(x->eccf, 3 * plf);
+  }
+  if (c->bfield == KH_B_FACE) {
+    KM_ALLOC(x->fBstar, 3 * pl);
+    KM_ALLOC(x->dmatch, sizeof(EmfMatch) * std::max<long long>(x->nmatch, 1));
   }
   x->npartial = 152 * 4;
   KM_ALLOC(x->partial, sizeof(double) * 2 * x->npartial);  // (max, sum) pairs for divB
@@ -847,6 +1038,9 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
     rc = cuda_rc(cudaMemcpy(x->dops, ops.data(), sizeof(GhostOp) * x->nops, cudaMemcpyHostToDevice));
   if (rc == KH_OK && x->nnbs)
     rc = cuda_rc(cudaMemcpy(x->dnbs, nbs.data(), sizeof(ProlongNb) * x->nnbs, cudaMemcpyHostToDevice));
+  if (rc == KH_OK && x->nmatch)
+    rc = cuda_rc(cudaMemcpy(x->dmatch, matches.data(), sizeof(EmfMatch) * x->nmatch, cudaMemcpyHostToDevice));
+  if (rc == KH_OK && x->fBstar) rc = cuda_rc(cudaMemset(x->fBstar, 0, 3 * pl));
   // zero scratch so never-written entries stay finite
   for (int d = 0; d < 3 && rc == KH_OK; ++d) {
     if (x->F[d]) rc = cuda_rc(cudaMemset(x->F[d], 0, NV * pl));
@@ -903,7 +1097,7 @@ template <class T> int fill_ghosts(kh_mesh* x, const Arena<T>& P) {
 }
 
 template <class TIN, class R>
-int flux_pass(kh_mesh* x, const Arena<TIN>& P, R* const F[3], R* const ct[3], R* const emf[3]) {
+int flux_pass(kh_mesh* x, const Arena<TIN>& P, R* const F[3], R* const ct[3], R* const emf[3], bool fluxct = true) {
   int n = 0;
   const GeoArena GA = garena(x);
   for (int d = 1; d <= x->ndim; ++d) {
@@ -922,12 +1116,37 @@ int flux_pass(kh_mesh* x, const Arena<TIN>& P, R* const F[3], R* const ct[3], R*
     ++n;
   }
   const unsigned tot = x->pre_ct.back();
-  for (int phase = 0; phase < 2; ++phase) {
+  for (int phase = 0; phase < 2 && fluxct; ++phase) {
     km_ct<R><<<nblk(tot, MTPB), MTPB, 0, x->stream>>>(x->dblk, x->dpre[4], x->nb, F[0], F[1], F[2], emf[0], emf[1],
                                                       emf[2], phase);
     ++n;
   }
   return n;
+}
+
+// Face-centred CT of one stage over all blocks (after the flux pass without
+// Flux-CT): cell EMFs (upwinded EMFs only), edge EMFs, interface matching,
+// face update fBout = fB0 + coef dt curl E.
+template <class R>
+int face_ct_pass(kh_mesh* x, const Arena<R>& P, R* const F[3], R* ecc, R* const emf[3], double* fBout, double coef) {
+  int n = 0;
+  cudaStream_t s = x->stream;
+  if (x->S.emf == KH_EMF_GS05) {
+    km_cell_emf<R><<<nblk(x->pre_all.back(), MTPB), MTPB, 0, s>>>(x->dblk, x->dpre[6], x->nb, P, garena(x), ecc);
+    ++n;
+  }
+  const unsigned tot = x->pre_ct.back();
+  km_face_emf<R><<<nblk(tot, MTPB), MTPB, 0, s>>>(x->dblk, x->dpre[4], x->nb, F[0], F[1], F[2],
+                                                  x->S.emf == KH_EMF_GS05 ? ecc : nullptr, emf[0], emf[1], emf[2],
+                                                  x->S.emf);
+  ++n;
+  if (x->nmatch) {
+    km_emf_match<R><<<nblk(x->nmatch, MTPB), MTPB, 0, s>>>(x->dmatch, x->nmatch, emf[0], emf[1], emf[2]);
+    ++n;
+  }
+  km_face_update<R><<<nblk(tot, MTPB), MTPB, 0, s>>>(x->dblk, x->dpre[4], x->nb, x->fB, fBout, emf[0], emf[1],
+                                                     emf[2], x->dscalar + 3, coef);
+  return n + 1;
 }
 
 template <class T> int cfl_pass(kh_mesh* x, T* const ct[3]) {
@@ -946,20 +1165,23 @@ int issue_mesh_step(kh_mesh* x, double* U, double* P, double* B) {
   const int tu = x->tpb_update, gu = nblk(nz, tu);
   const Arena<double> Pn = arena_pb(P, B);
   int n = 0;
+  const bool face = x->S.bfield == KH_B_FACE;
   if (x->c.precision == KH_FP64) {
     const Arena<double> Ps = arena8(x->pstar);
     // stage 1: P^n -> P*
     n += fill_ghosts(x, Pn);
-    n += flux_pass<double, double>(x, Pn, x->F, x->ctop, x->emf);
+    n += flux_pass<double, double>(x, Pn, x->F, x->ctop, x->emf, !face);
+    if (face) n += face_ct_pass<double>(x, Pn, x->F, x->ecc, x->emf, x->fBstar, 0.5);
     km_update<<<gu, tu, 0, s>>>(x->dblk, x->dpre[3], x->nb, U, Pn, Ps, nullptr, x->F[0], x->F[1], x->F[2], GA,
-                                  x->S, x->dscalar + 3, 0.5, x->pflag, x->counters);
+                                  x->S, x->dscalar + 3, 0.5, x->pflag, x->counters, face ? x->fBstar : nullptr);
     km_fixup<double><<<gz, MTPB, 0, s>>>(x->dblk, x->dpre[3], x->nb, Ps, nullptr, x->pflag, GA, x->S, x->counters);
     n += 2;
     // stage 2: P* -> P^{n+1}, U^{n+1}
     n += fill_ghosts(x, Ps);
-    n += flux_pass<double, double>(x, Ps, x->F, x->ctop, x->emf);
+    n += flux_pass<double, double>(x, Ps, x->F, x->ctop, x->emf, !face);
+    if (face) n += face_ct_pass<double>(x, Ps, x->F, x->ecc, x->emf, x->fB, 1.0);
     km_update<<<gu, tu, 0, s>>>(x->dblk, x->dpre[3], x->nb, U, Ps, Pn, U, x->F[0], x->F[1], x->F[2], GA, x->S,
-                                  x->dscalar + 3, 1.0, x->pflag, x->counters);
+                                  x->dscalar + 3, 1.0, x->pflag, x->counters, face ? x->fB : nullptr);
     km_fixup<double><<<gz, MTPB, 0, s>>>(x->dblk, x->dpre[3], x->nb, Pn, U, x->pflag, GA, x->S, x->counters);
     n += 2;
     n += cfl_pass<double>(x, x->ctop);
@@ -971,16 +1193,20 @@ int issue_mesh_step(kh_mesh* x, double* U, double* P, double* B) {
     km_to_f32<<<nblk(x->pre_alloc.back(), 256), 256, 0, s>>>(x->dblk, x->dpre[5], x->nb, Pn, Pnf);
     ++n;
     n += fill_ghosts(x, Pnf);
-    n += flux_pass<float, float>(x, Pnf, x->Ff, x->ctopf, x->emff);
+    n += flux_pass<float, float>(x, Pnf, x->Ff, x->ctopf, x->emff, !face);
+    if (face) n += face_ct_pass<float>(x, Pnf, x->Ff, x->eccf, x->emff, x->fBstar, 0.5);
     km_update_mixed<<<gu, tu, 0, s>>>(x->dblk, x->dpre[3], x->nb, U, Pnf, none64, Psf, nullptr, x->Ff[0],
-                                        x->Ff[1], x->Ff[2], GA, x->S, x->dscalar + 3, 0.5, x->pflag, x->counters);
+                                        x->Ff[1], x->Ff[2], GA, x->S, x->dscalar + 3, 0.5, x->pflag, x->counters,
+                                        face ? x->fBstar : nullptr);
     km_fixup<float><<<gz, MTPB, 0, s>>>(x->dblk, x->dpre[3], x->nb, Psf, nullptr, x->pflag, GA, x->S, x->counters);
     n += 2;
     // stage 2: FP32 P* -> FP64 P^{n+1}, U^{n+1}
     n += fill_ghosts(x, Psf);
-    n += flux_pass<float, float>(x, Psf, x->Ff, x->ctopf, x->emff);
+    n += flux_pass<float, float>(x, Psf, x->Ff, x->ctopf, x->emff, !face);
+    if (face) n += face_ct_pass<float>(x, Psf, x->Ff, x->eccf, x->emff, x->fB, 1.0);
     km_update_mixed<<<gu, tu, 0, s>>>(x->dblk, x->dpre[3], x->nb, U, Psf, Pn, none32, U, x->Ff[0], x->Ff[1],
-                                        x->Ff[2], GA, x->S, x->dscalar + 3, 1.0, x->pflag, x->counters);
+                                        x->Ff[2], GA, x->S, x->dscalar + 3, 1.0, x->pflag, x->counters,
+                                        face ? x->fB : nullptr);
     km_fixup<double><<<gz, MTPB, 0, s>>>(x->dblk, x->dpre[3], x->nb, Pn, U, x->pflag, GA, x->S, x->counters);
     n += 2;
     n += cfl_pass<float>(x, x->ctopf);
@@ -1102,8 +1328,16 @@ int kh_mesh_get_stats(kh_mesh* x, kh_stats* out) {
   return KH_OK;
 }
 
+int kh_mesh_set_face_field(kh_mesh* x, double* fB) {
+  if (!x || !fB || x->S.bfield != KH_B_FACE) return KH_EINVAL;
+  if (x->fB != fB) drop_mesh_graph(x);
+  x->fB = fB;
+  return KH_OK;
+}
+
 int kh_mesh_step(kh_mesh* x, double* U, double* P, double* B, double dt, double* dt_cfl) {
   if (!x || !U || !P || !B || !(dt > 0.0) || !isfinite(dt)) return KH_EINVAL;
+  if (x->S.bfield == KH_B_FACE && !x->fB) return KH_EINVAL;
   int rc = cuda_rc(cudaMemcpyAsync(x->dscalar + 3, &dt, sizeof(double), cudaMemcpyHostToDevice, x->stream));
   if (rc != KH_OK) return rc;
   if (x->graph_on) {
@@ -1268,7 +1502,8 @@ int kh_mesh_destroy(kh_mesh* x) {
   void* ptrs[] = {x->dblk, x->dops, x->dnbs, x->geo, x->dgm, x->flo, x->geof, x->dgmf, x->geodf, x->pstar, x->pstarf, x->pnf,
                   x->pflag, x->partial, x->dscalar, x->counters, x->F[0], x->F[1], x->F[2], x->ctop[0],
                   x->ctop[1], x->ctop[2], x->emf[0], x->emf[1], x->emf[2], x->Ff[0], x->Ff[1], x->Ff[2],
-                  x->ctopf[0], x->ctopf[1], x->ctopf[2], x->emff[0], x->emff[1], x->emff[2]};
+                  x->ctopf[0], x->ctopf[1], x->ctopf[2], x->emff[0], x->emff[1], x->emff[2],
+                  x->fBstar, x->ecc, x->eccf, x->dmatch};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int q = 0; q < 8; ++q)

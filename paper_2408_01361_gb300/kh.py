@@ -117,6 +117,7 @@ def lib():
         L.kh_mesh_get_launch.argtypes = [vp, ip, ip]
         L.kh_mesh_autotune.argtypes = [vp, vp, vp, vp, C.c_double, ip, ip]
         L.kh_mesh_get_stats.argtypes = [vp, C.POINTER(Stats)]
+        L.kh_mesh_set_face_field.argtypes = [vp, vp]
         L.kh_mesh_destroy.argtypes = [vp]
         _lib = L
     return _lib
@@ -470,6 +471,25 @@ class Mesh:
         mx, l1 = C.c_double(), C.c_double()
         _check(lib().kh_mesh_divb(self._h, _ptr(B), C.byref(mx), C.byref(l1)), "kh_mesh_divb")
         return mx.value, l1.value
+
+    def set_face_field(self, fB):
+        """Register the face-field arena (3 planes per block; bfield "face")."""
+        self._fB = fB
+        _check(lib().kh_mesh_set_face_field(self._h, _ptr(fB)), "kh_mesh_set_face_field")
+
+    def faces_to_device(self, fBs):
+        """List of per-block (3, N3, N2, N1) numpy face fields -> face arena."""
+        A = self.empty(3)
+        for f, v in zip(fBs, self.views(A, 3)):
+            v[:, :, :, : f.shape[3]].copy_(self.torch.from_numpy(np.ascontiguousarray(f)))
+        return A
+
+    def faces_to_host(self, A):
+        out = []
+        for blk, v in zip(self.blocks, self.views(A, 3)):
+            N1 = blk["n1"] + 2 * 3
+            out.append(v[:, :, :, :N1].cpu().numpy())
+        return out
 
     def set_launch(self, tpb_flux: int, tpb_update: int):
         _check(lib().kh_mesh_set_launch(self._h, int(tpb_flux), int(tpb_update)), "kh_mesh_set_launch")

@@ -55,8 +55,8 @@ def test_argument_validation_without_gpu():
 
 
 def test_face_ct_validation_without_gpu():
-    """Face-centred CT is refused with the flux correction, on a mesh, and
-    with unknown scheme values."""
+    """Face-centred CT is refused with the flux correction and with unknown
+    scheme values (single grid and mesh)."""
     from paper_2408_01361_gb300 import inputs, kh
     cfg = dict(inputs.linear_mode_cfg(8, ndim=3), bfield="face")
     h = ctypes.c_void_p()
@@ -69,5 +69,6 @@ def test_face_ct_validation_without_gpu():
         assert kh.lib().kh_geometry_init(0.0, ctypes.byref(c), float(cfg["gam"]), ctypes.byref(h)) == -1
     blk = kh.Block(0, 0, 0, 0, 8, 8, 8)
     c = kh.coords_from_cfg(cfg)
+    c.emf = 5
     assert kh.lib().kh_mesh_init(0.0, ctypes.byref(c), float(cfg["gam"]), 1, ctypes.byref(blk),
                                  ctypes.byref(h)) == -1
