@@ -112,8 +112,10 @@ typedef struct {
                              fourth-order SSP scheme), in Shu-Osher form: each stage
                              U_s = sum_j a_sj U_j + c_s dt L(P_{s-1}) with the
                              stage operator, inversion, floors and fixup of a
-                             predictor-corrector stage. FP64 single-grid contexts
-                             with Flux-CT (8 to 48 extra planes of scratch). */
+                             predictor-corrector stage. Single-grid Flux-CT contexts
+                             without the flux correction, FP64 or KH_MIXED (the
+                             FP32 shadow carries the intermediate stage states); 8 to
+                             48 extra planes of scratch. */
 } kh_coords;
 
 /* Counters of the last kh_step (both stages summed). */

@@ -156,7 +156,8 @@ int run_stage(kh_ctx* x, int st, const double* U0, const Vars& Pin, const Vars& 
 // input, FP64 output and U.
 template <class TIN>
 int run_stage_mixed(kh_ctx* x, int st, const double* U0, const VarsT<TIN>& Pin, const TIN* dlo, const TIN* dhi,
-                    const Vars& Pout64, const VarsT<float>& Pout32, double* Uout, double coef) {
+                    const Vars& Pout64, const VarsT<float>& Pout32, double* Uout, double coef,
+                    double* dUout = nullptr) {
   const Layout& L = x->L;
   const DevGeom G = devgeom(x);
   const GeomT<float> Gf = geomf(x);
@@ -221,7 +222,7 @@ int run_stage_mixed(kh_ctx* x, int st, const double* U0, const VarsT<TIN>& Pin, 
   mark(x, KH_T_UPDATE, st, 0);
   const FailList fl{x->flist, x->counters + CNT_LIST0 + st};
   n += launch_update_mixed(U0, cviewT(Pf), Pout64, Pout32, Uout, x->Ff, L, G, Gf, x->S, x->dscalar + 3, coef,
-                           x->pflag, x->counters, x->tpb_update, s, fl, fBn);
+                           x->pflag, x->counters, x->tpb_update, s, fl, fBn, dUout);
   mark(x, KH_T_UPDATE, st, 1);
   mark(x, KH_T_FIXUP, st, 0);
   if (Pout64.v[0])
@@ -258,7 +259,7 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
   if (c->inverter < KH_INV_NOBLE2D || c->inverter > KH_INV_KASTAUN) return KH_EINVAL;
   if (c->inverter != KH_INV_NOBLE2D && c->precision != KH_FP64) return KH_EINVAL;
   if (c->integrator < KH_INT_VL2 || c->integrator > KH_INT_SSPRK54) return KH_EINVAL;
-  if (c->integrator != KH_INT_VL2 && (c->precision != KH_FP64 || c->bfield != KH_B_FLUXCT)) return KH_EINVAL;
+  if (c->integrator != KH_INT_VL2 && (c->bfield != KH_B_FLUXCT || c->fofc)) return KH_EINVAL;
   if (c->bfield != KH_B_FLUXCT && c->bfield != KH_B_FACE) return KH_EINVAL;
   if (c->emf != KH_EMF_AVERAGE && c->emf != KH_EMF_GS05) return KH_EINVAL;
   if (c->bfield == KH_B_FACE && c->fofc) return KH_EINVAL;
@@ -530,10 +531,30 @@ int issue_rk(kh_ctx* x, double* U, const Vars& Pn) {
   double* base = x->rk + nst * n8;
   double* dU4 = base + n8;
   int n = 0;
+  const int nstage = x->S.integrator == KH_INT_SSPRK54 ? 5 : (x->S.integrator == KH_INT_RK2 ? 2 : 1);
   auto stage = [&](int q, const double* U0, double* Uout, double c, double* dUout) {
     // each stage appends to the failed-zone list of slot q % 2: start it empty
     cudaMemsetAsync(x->counters + CNT_LIST0 + (q % 2), 0, sizeof(unsigned long long), s);
-    n += run_stage(x, q % 2, U0, Pn, Pn, Uout, c, dUout);
+    if (x->c.precision == KH_FP64) {
+      n += run_stage(x, q % 2, U0, Pn, Pn, Uout, c, dUout);
+      return;
+    }
+    // mixed: the FP64 P^n enters the first stage, the FP32 shadow the later
+    // ones (in place); the last stage writes the FP64 P^{n+1}
+    VarsT<float> Psf, nof;
+    Vars no64;
+    for (int v = 0; v < NV; ++v) {
+      Psf.v[v] = x->pstarf + v * L.plane;
+      nof.v[v] = nullptr;
+      no64.v[v] = nullptr;
+    }
+    const bool last = q == nstage - 1;
+    if (q == 0)
+      n += run_stage_mixed<double>(x, 0, U0, Pn, x->dirichlet[0], x->dirichlet[1], last ? Pn : no64,
+                                   last ? nof : Psf, Uout, c, dUout);
+    else
+      n += run_stage_mixed<float>(x, q % 2, U0, Psf, x->dirichletf[0], x->dirichletf[1], last ? Pn : no64,
+                                  last ? nof : Psf, Uout, c, dUout);
   };
   auto comb = [&](int nt, const double* const* in, const double* a) {
     n += launch_lincomb(base, nt, in, a, n8, s);
@@ -609,8 +630,14 @@ int issue_step(kh_ctx* x, double* U, double* P, double* B) {
       nof.v[q] = nullptr;
       no64.v[q] = nullptr;
     }
-    n += run_stage_mixed<double>(x, 0, U, Pn, x->dirichlet[0], x->dirichlet[1], no64, Psf, nullptr, 0.5);
-    n += run_stage_mixed<float>(x, 1, U, Psf, x->dirichletf[0], x->dirichletf[1], Pn, nof, U, 1.0);
+    if (x->S.integrator != KH_INT_VL2) {
+      const int r = issue_rk(x, U, Pn);
+      if (r < 0) return r;
+      n += r;
+    } else {
+      n += run_stage_mixed<double>(x, 0, U, Pn, x->dirichlet[0], x->dirichlet[1], no64, Psf, nullptr, 0.5);
+      n += run_stage_mixed<float>(x, 1, U, Psf, x->dirichletf[0], x->dirichletf[1], Pn, nof, U, 1.0);
+    }
     mark(x, KH_T_CFL, 1, 0);
     n += launch_cfl<float>(x->ctopf, L, x->S.cfl, x->partial, x->npartial, x->dscalar, s);
     mark(x, KH_T_CFL, 1, 1);

@@ -155,7 +155,7 @@ int launch_update_mixed(const double* U0, const CVarsT<float>& Pin, const Vars& 
                         double* Uout, float* const F[3], const Layout& L, const DevGeom& G, const GeomT<float>& Gf,
                         const Scheme& S, const double* dtp, double coef, int8_t* pflag, unsigned long long* cnt,
                         int tpb, cudaStream_t s, FailList fl = FailList{nullptr, nullptr},
-                        const double* fBn = nullptr);
+                        const double* fBn = nullptr, double* dUout = nullptr);
 // Fixup over every zone, or (fl.idx != nullptr) over the stage's failed-zone list.
 template <class T>
 int launch_fixup(const VarsT<T>& P, double* Uout, const int8_t* pflag, const Layout& L, const DevGeom& G,

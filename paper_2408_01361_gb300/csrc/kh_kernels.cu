@@ -248,13 +248,13 @@ __global__ void __launch_bounds__(TPB_MAX, 3) k_update_mixed(const double* U0, C
                                                          const float* F2, const float* F3, Layout L, DevGeom G,
                                                          GeomT<float> Gf, Scheme S, const double* dtp, double coef,
                                                          int8_t* pflag, unsigned long long* cnt, FailList fl,
-                                                         const double* fBn) {
+                                                         const double* fBn, double* dUout) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nzones(L)) return;
   int i, j, k;
   zone_ijk(L, t, i, j, k);
   update_mixed_zone(U0, Pin, Pout64, Pout32, Uout, F1, F2, F3, L, G, Gf, S, df_of_f64(coef * __ldg(dtp)), pflag, cnt, i,
-                    j, k, fl, fBn);
+                    j, k, fl, fBn, dUout);
 }
 
 template <class T>
@@ -772,10 +772,10 @@ int launch_update(const double* U0, const CVars& Pin, const Vars& Pout, double* 
 int launch_update_mixed(const double* U0, const CVarsT<float>& Pin, const Vars& Pout64, const VarsT<float>& Pout32,
                         double* Uout, float* const F[3], const Layout& L, const DevGeom& G, const GeomT<float>& Gf,
                         const Scheme& S, const double* dtp, double coef, int8_t* pflag, unsigned long long* cnt,
-                        int tpb, cudaStream_t s, FailList fl, const double* fBn) {
+                        int tpb, cudaStream_t s, FailList fl, const double* fBn, double* dUout) {
   const long long nz = (long long)L.n1 * L.n2 * L.n3;
   k_update_mixed<<<nblocks(nz, tpb), tpb, 0, s>>>(U0, Pin, Pout64, Pout32, Uout, F[0], F[1], F[2], L, G, Gf, S, dtp,
-                                                  coef, pflag, cnt, fl, fBn);
+                                                  coef, pflag, cnt, fl, fBn, dUout);
   return 1;
 }
 

@@ -431,7 +431,7 @@ __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT
                                                   const GeomT<float>& Gf, const Scheme& S, df64 cdt, int8_t* pflag,
                                                   unsigned long long* cnt, int i, int j, int k,
                                                   FailList fl = FailList{nullptr, nullptr},
-                                                  const double* fBn = nullptr) {
+                                                  const double* fBn = nullptr, double* dUout = nullptr) {
   const long long c = L.at(k, j, i);
   const long long p = (long long)j * L.n1s + i;
   const long long sj = L.n1s, sk = (long long)L.n1s * L.n2s;
@@ -463,6 +463,7 @@ __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT
       const float inc = (cdt * (Sv[v] - div)).hi;  // c dt (S - div F)
       const double u0 = U0[o];
       if (Uout) Uout[o] = u0 + f64_of_f32(inc);    // the conserved update, FP64
+      if (dUout) dUout[o] = f64_of_f32(inc);       // the raw increment (Runge-Kutta stages)
       Ud[v] = df_of_f64(u0) + inc;
     }
   }

@@ -96,3 +96,30 @@ def test_ssprk54_graph_replay_matches_eager(kh, orc):
     a = _run(kh, orc, cfg, P, 2, graph=False, check_oracle=False)
     b = _run(kh, orc, cfg, P, 2, graph=True, check_oracle=False)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+@pytest.mark.parametrize("integ", ["rk2", "ssprk54"])
+def test_mixed_integrators_vs_oracle(kh, orc, integ):
+    """The mixed path's Runge-Kutta stages (FP32 shadow between stages, FP64
+    U and final P) against the oracle's FP64 integrator, at the mixed path's
+    FP32 level (momenta and velocities against the mass scale near the
+    torus's equilibrium, as for the predictor-corrector)."""
+    cfg, P = _case("torus")
+    cfg = dict(cfg, integrator=integ, precision="mixed")
+    Uo = orc.prim_to_cons(cfg, P)
+    dt = 0.5 * orc.cfl_dt(cfg, P)
+    Uo2, Po2, _, _ = orc.step(cfg, Uo, P, dt)
+    ctx = kh.Context(cfg)
+    g = GpuRun(ctx, cfg, P, U=Uo)
+    ctx.step(g.U, g.P, g.B, dt)
+    Ug, Pg = g.host()
+    a, b = interior(cfg, Ug), interior(cfg, Uo2)
+    pa, pb = interior(cfg, Pg), interior(cfg, Po2)
+    mass = np.abs(b[0]).sum()
+    nz = b[0].size
+    for v in range(8):
+        tol = 2e-3 if v in (2, 3, 4) else 1e-4
+        den = max(np.abs(b[v]).sum(), 1e-3 * mass)
+        assert np.abs(a[v] - b[v]).sum() / den < tol, ("U", v, np.abs(a[v] - b[v]).sum() / den)
+        pden = max(np.abs(pb[v]).sum(), 1e-2 * nz if v in (2, 3, 4) else 0.0)
+        assert np.abs(pa[v] - pb[v]).sum() / pden < tol, ("P", v, np.abs(pa[v] - pb[v]).sum() / pden)
