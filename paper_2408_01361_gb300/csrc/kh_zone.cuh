@@ -584,6 +584,36 @@ __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT
 // Fixup: a zone whose inversion failed takes the equal-weight mean of the
 // fluid primitives of its non-failed interior neighbours (3x3x3, or 3x3 in
 // 2-D); with none it keeps the stage input. Then floors; U recomputed.
+// The repair after the neighbour mean (sum[5] over n good neighbours):
+// floors, the primitives written, U recomputed.
+template <class T>
+__device__ __forceinline__ void fixup_finish(const VarsT<T>& P, double* Uout, const Layout& L, const DevGeom& G,
+                                             const Scheme& S, unsigned long long* cnt, int i, int j, int k,
+                                             const double* sum, int n) {
+  const long long c = L.at(k, j, i);
+  double Pn[NV];
+  for (int v = 0; v < NV; ++v) Pn[v] = (double)P.v[v][c];
+  if (n > 0) {
+    for (int v = 0; v < 5; ++v) Pn[v] = sum[v] / n;
+  } else {
+    atomicAdd(cnt + CNT_UNFIXED, 1ULL);
+  }
+  const long long p = (long long)j * L.n1s + i;
+  const Met<double> m = load_met(G, L.gplane, LOC_CENT, p);
+  FState<double> sb;
+  fluid_state(Pn, m, sb);
+  const int fmask = apply_floors(S.fl, m, __ldg(G.flo + p), __ldg(G.flo + L.gplane + p), sb.bsq, Pn);
+  if (fmask) atomicAdd(cnt + CNT_FLOOR, 1ULL);
+  for (int v = 0; v < 5; ++v) P.v[v][c] = (T)Pn[v];
+  if (Uout) {
+    FState<double> s;
+    fluid_state(Pn, m, s);
+    double U[NV];
+    cons_only(Pn, s, m, S.gam, U);
+    for (int v = 0; v < NV; ++v) Uout[v * L.plane + c] = U[v];
+  }
+}
+
 template <class T>
 __device__ __forceinline__ void fixup_zone(const VarsT<T>& P, double* Uout, const int8_t* pflag, const Layout& L,
                                            const DevGeom& G, const Scheme& S, unsigned long long* cnt, int i, int j,
