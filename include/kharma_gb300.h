@@ -77,7 +77,9 @@ typedef struct {
                              donor-cell (first-order) LLF flux, and polar zeroing and
                              Flux-CT are applied again before the stage's update. The
                              flags' ghost zones follow the state's ghost map (Dirichlet
-                             ghosts unflagged). 0: off. Single-grid contexts only. */
+                             ghosts unflagged). 0: off. Single-grid contexts with
+                             Flux-CT and the predictor-corrector (the mesh, face CT,
+                             the Runge-Kutta integrators and the adjoint refuse it). */
   int bfield;             /* KH_B_FLUXCT: cell-centred field, Flux-CT (Toth 2000);
                              KH_B_FACE: face-centred constrained transport
                              ("Algorithm" section: Stone & Gardiner 2009). The face
@@ -86,9 +88,11 @@ typedef struct {
                              d_b E_c - d_c E_b, which keeps every cell's face
                              divergence; B of a zone is the mean of its two faces
                              over sqrt(-g). Edge EMFs on a polar axis are zero.
-                             Single-grid contexts (KH_MIXED: FP32 EMFs, the face
-                             field and its increments accumulated in FP64); no flux
-                             correction. */
+                             Single grids and the refined mesh (kh_mesh_*: coarse
+                             edges on a level interface take the finer block's EMFs),
+                             FP64 and KH_MIXED (FP32 EMFs, the curl formed in FP64,
+                             the face field in FP64); no flux correction, the
+                             predictor-corrector only, no adjoint. */
   int emf;                /* KH_B_FACE edge EMFs: KH_EMF_AVERAGE (mean of the four
                              face values; with face means as the zone field this is
                              Flux-CT) or KH_EMF_GS05 (Gardiner & Stone 2005: plus the
