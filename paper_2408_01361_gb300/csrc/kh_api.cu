@@ -188,41 +188,37 @@ int run_stage_mixed(kh_ctx* x, int st, const double* U0, const VarsT<TIN>& Pin, 
     n += r;
     mark(x, KH_T_FLUX1 + d - 1, st, 1);
   }
-  const size_t b3 = 3 * (size_t)L.plane * sizeof(float);
-  if (x->S.fofc) {
-    // Flux-CT overwrites the raw field fluxes; the correction needs them again
-    for (int d = 0; d < L.ndim; ++d)
-      cudaMemcpyAsync(x->fsavef + 3 * d * L.plane, x->Ff[d] + V_B1 * L.plane, b3, cudaMemcpyDeviceToDevice, s);
-  }
+  // Flux-CT: the edge EMFs only; the update (and the correction's trial)
+  // form the field fluxes from them, so the raw field fluxes stay in Ff
+  const bool fct = x->S.bfield == KH_B_FLUXCT;
   double* fBn = nullptr;
   mark(x, KH_T_CT, st, 0);
-  if (x->S.bfield == KH_B_FACE) {
+  if (!fct) {
     // face-centred CT: FP32 EMFs, FP64 face field
     fBn = st == 0 ? x->fBstar : x->fB;
     n += launch_face_ct<float>(cviewT(Pf), x->Ff, x->eccf, x->emff, x->fB, fBn, L, Gf, x->S, x->dscalar + 3, coef,
                                s);
   } else {
-    n += launch_ct<float>(x->Ff, x->emff, L, s);
+    n += launch_emf<float>(x->Ff, x->emff, L, s);
   }
   mark(x, KH_T_CT, st, 1);
   if (x->S.fofc) {
-    // first-order flux correction (as in run_stage), FP32 fluxes
+    // first-order flux correction (as in run_stage), FP32 fluxes; the raw
+    // field fluxes were never overwritten, so the EMFs are simply redone
     mark(x, KH_T_FOFC, st, 0);
     n += launch_fofc_trial_mixed(U0, cviewT(Pf), x->Ff, L, G, Gf, x->S, x->dscalar + 3, coef, x->fflag,
-                                 x->counters, x->tpb_update, s);
+                                 x->counters, x->tpb_update, s, x->emff);
     n += launch_flag_ghosts(x->fflag, L, x->S, s);
-    for (int d = 0; d < L.ndim; ++d)
-      cudaMemcpyAsync(x->Ff[d] + V_B1 * L.plane, x->fsavef + 3 * d * L.plane, b3, cudaMemcpyDeviceToDevice, s);
     for (int d = 1; d <= L.ndim; ++d)
       n += launch_fofc_faces<float, float>(d, cviewT(Pf), L, Gf, x->S, x->fflag, x->Ff[d - 1], x->ctopf[d - 1],
                                            x->tpb_flux, s);
-    n += launch_ct<float>(x->Ff, x->emff, L, s);
+    n += launch_emf<float>(x->Ff, x->emff, L, s);
     mark(x, KH_T_FOFC, st, 1);
   }
   mark(x, KH_T_UPDATE, st, 0);
   const FailList fl{x->flist, x->counters + CNT_LIST0 + st};
   n += launch_update_mixed(U0, cviewT(Pf), Pout64, Pout32, Uout, x->Ff, L, G, Gf, x->S, x->dscalar + 3, coef,
-                           x->pflag, x->counters, x->tpb_update, s, fl, fBn, dUout);
+                           x->pflag, x->counters, x->tpb_update, s, fl, fBn, dUout, fct ? x->emff : nullptr);
   mark(x, KH_T_UPDATE, st, 1);
   mark(x, KH_T_FIXUP, st, 0);
   if (Pout64.v[0])
@@ -400,11 +396,7 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
   }
   if (c->fofc) {
     KH_ALLOC(x->fflag, (size_t)L.plane);
-    if (mixed) {
-      KH_ALLOC(x->fsavef, 3 * (size_t)L.ndim * plf);
-    } else {
-      KH_ALLOC(x->fsave, 3 * (size_t)L.ndim * pl);
-    }
+    if (!mixed) KH_ALLOC(x->fsave, 3 * (size_t)L.ndim * pl);  // the mixed path keeps its raw field fluxes
   }
   KH_ALLOC(x->flist, (size_t)L.n1 * L.n2 * L.n3 * sizeof(unsigned));
   KH_ALLOC(x->partial, 2 * (size_t)x->npartial * sizeof(double));

@@ -20,7 +20,7 @@ struct kh_ctx {
   int8_t* pflag;
   int8_t* fflag;   // first-order flux correction: flags of the current stage (one plane)
   double* fsave;   // ... and the raw field fluxes kept across the trial (3 planes per direction)
-  float* fsavef;   // the same for the FP32 fluxes of KH_MIXED
+  float* fsavef;   // (unused: the mixed path never overwrites its raw field fluxes)
   // face-centred CT (KH_B_FACE): the caller's face field (kh_set_face_field),
   // the stage-1 face field and the cell-centred EMFs (3 planes each)
   double* fB;

@@ -112,6 +112,9 @@ template <class TIN, class R>
 int launch_flux_dir(int D, const CVarsT<TIN>& P, const Layout& L, const GeomT<R>& G, const Scheme& S, R* F, R* ctop,
                     int tpb, cudaStream_t s);
 template <class R> int launch_ct(R* const F[3], R* const emf[3], const Layout& L, cudaStream_t s);
+// Flux-CT's edge EMFs only (the field fluxes left raw; the mixed update forms
+// its field fluxes from the EMFs).
+template <class R> int launch_emf(R* const F[3], R* const emf[3], const Layout& L, cudaStream_t s);
 // First-order flux correction (after Beckwith & Stone 2011). The trial: the
 // FP64 update of every interior zone with the post-CT fluxes, writing only
 // flag[c] (1: inversion failed or a floor acted); then the flags' ghost
@@ -122,7 +125,8 @@ int launch_fofc_trial(const double* U0, const CVars& Pin, double* const F[3], co
 // The same trial with the mixed update (FP32 fluxes; Gf the FP32 geometry).
 int launch_fofc_trial_mixed(const double* U0, const CVarsT<float>& Pin, float* const F[3], const Layout& L,
                             const DevGeom& G, const GeomT<float>& Gf, const Scheme& S, const double* dtp, double coef,
-                            int8_t* flag, unsigned long long* cnt, int tpb, cudaStream_t s);
+                            int8_t* flag, unsigned long long* cnt, int tpb, cudaStream_t s,
+                            float* const* emf = nullptr);
 int launch_flag_ghosts(int8_t* flag, const Layout& L, const Scheme& S, cudaStream_t s);
 // Donor-cell LLF fluxes (with polar zeroing) through every x^D face of the
 // flux pass's face box that borders a flagged cell, over the raw fluxes.
@@ -155,7 +159,7 @@ int launch_update_mixed(const double* U0, const CVarsT<float>& Pin, const Vars& 
                         double* Uout, float* const F[3], const Layout& L, const DevGeom& G, const GeomT<float>& Gf,
                         const Scheme& S, const double* dtp, double coef, int8_t* pflag, unsigned long long* cnt,
                         int tpb, cudaStream_t s, FailList fl = FailList{nullptr, nullptr},
-                        const double* fBn = nullptr, double* dUout = nullptr);
+                        const double* fBn = nullptr, double* dUout = nullptr, float* const* emf = nullptr);
 // Fixup over every zone, or (fl.idx != nullptr) over the stage's failed-zone list.
 template <class T>
 int launch_fixup(const VarsT<T>& P, double* Uout, const int8_t* pflag, const Layout& L, const DevGeom& G,

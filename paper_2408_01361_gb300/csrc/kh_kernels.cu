@@ -248,13 +248,13 @@ __global__ void __launch_bounds__(TPB_MAX, 3) k_update_mixed(const double* U0, C
                                                          const float* F2, const float* F3, Layout L, DevGeom G,
                                                          GeomT<float> Gf, Scheme S, const double* dtp, double coef,
                                                          int8_t* pflag, unsigned long long* cnt, FailList fl,
-                                                         const double* fBn, double* dUout) {
+                                                         const double* fBn, double* dUout, CtEmf ect) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nzones(L)) return;
   int i, j, k;
   zone_ijk(L, t, i, j, k);
   update_mixed_zone(U0, Pin, Pout64, Pout32, Uout, F1, F2, F3, L, G, Gf, S, df_of_f64(coef * __ldg(dtp)), pflag, cnt, i,
-                    j, k, fl, fBn, dUout);
+                    j, k, fl, fBn, dUout, ect);
 }
 
 template <class T>
@@ -332,13 +332,14 @@ __global__ void __launch_bounds__(TPB_MAX, 3) k_fofc_trial_mixed(const double* U
                                                                 const float* F1, const float* F2, const float* F3,
                                                                 Layout L, DevGeom G, GeomT<float> Gf, Scheme S,
                                                                 const double* dtp, double coef, int8_t* flag,
-                                                                unsigned long long* cnt) {
+                                                                unsigned long long* cnt, CtEmf ect) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nzones(L)) return;
   int i, j, k;
   zone_ijk(L, t, i, j, k);
   update_mixed_zone<true>(U0, Pin, Vars{}, VarsT<float>{}, nullptr, F1, F2, F3, L, G, Gf, S,
-                          df_of_f64(coef * __ldg(dtp)), flag, cnt, i, j, k);
+                          df_of_f64(coef * __ldg(dtp)), flag, cnt, i, j, k, FailList{nullptr, nullptr}, nullptr,
+                          nullptr, ect);
 }
 
 // Ghost flags follow the state's ghost map: a periodic image or an outflow or
@@ -738,9 +739,11 @@ int launch_fofc_trial(const double* U0, const CVars& Pin, double* const F[3], co
 
 int launch_fofc_trial_mixed(const double* U0, const CVarsT<float>& Pin, float* const F[3], const Layout& L,
                             const DevGeom& G, const GeomT<float>& Gf, const Scheme& S, const double* dtp, double coef,
-                            int8_t* flag, unsigned long long* cnt, int tpb, cudaStream_t s) {
+                            int8_t* flag, unsigned long long* cnt, int tpb, cudaStream_t s, float* const* emf) {
   const long long nz = (long long)L.n1 * L.n2 * L.n3;
-  k_fofc_trial_mixed<<<nblocks(nz, tpb), tpb, 0, s>>>(U0, Pin, F[0], F[1], F[2], L, G, Gf, S, dtp, coef, flag, cnt);
+  const CtEmf ect{{emf ? emf[0] : nullptr, emf ? emf[1] : nullptr, emf ? emf[2] : nullptr}};
+  k_fofc_trial_mixed<<<nblocks(nz, tpb), tpb, 0, s>>>(U0, Pin, F[0], F[1], F[2], L, G, Gf, S, dtp, coef, flag, cnt,
+                                                      ect);
   return 1;
 }
 
@@ -780,6 +783,12 @@ template <class R> int launch_ct(R* const F[3], R* const emf[3], const Layout& L
   k_apply_ct<R><<<nblocks(tot, TPB), TPB, 0, s>>>(F[0], F[1], F[2], emf[0], emf[1], emf[2], L);
   return 2;
 }
+template <class R> int launch_emf(R* const F[3], R* const emf[3], const Layout& L, cudaStream_t s) {
+  const long long tot = (long long)(L.e[0] - L.s[0] + 1) * (L.e[1] - L.s[1] + 1) * (L.ndim == 3 ? L.e[2] - L.s[2] + 1 : 1);
+  k_emf<R><<<nblocks(tot, TPB), TPB, 0, s>>>(F[0], F[1], F[2], emf[0], emf[1], emf[2], L);
+  return 1;
+}
+template int launch_emf<float>(float* const[3], float* const[3], const Layout&, cudaStream_t);
 template int launch_ct<double>(double* const[3], double* const[3], const Layout&, cudaStream_t);
 template int launch_ct<float>(float* const[3], float* const[3], const Layout&, cudaStream_t);
 
@@ -803,10 +812,12 @@ int launch_update(const double* U0, const CVars& Pin, const Vars& Pout, double* 
 int launch_update_mixed(const double* U0, const CVarsT<float>& Pin, const Vars& Pout64, const VarsT<float>& Pout32,
                         double* Uout, float* const F[3], const Layout& L, const DevGeom& G, const GeomT<float>& Gf,
                         const Scheme& S, const double* dtp, double coef, int8_t* pflag, unsigned long long* cnt,
-                        int tpb, cudaStream_t s, FailList fl, const double* fBn, double* dUout) {
+                        int tpb, cudaStream_t s, FailList fl, const double* fBn, double* dUout,
+                        float* const* emf) {
   const long long nz = (long long)L.n1 * L.n2 * L.n3;
+  const CtEmf ect{{emf ? emf[0] : nullptr, emf ? emf[1] : nullptr, emf ? emf[2] : nullptr}};
   k_update_mixed<<<nblocks(nz, tpb), tpb, 0, s>>>(U0, Pin, Pout64, Pout32, Uout, F[0], F[1], F[2], L, G, Gf, S, dtp,
-                                                  coef, pflag, cnt, fl, fBn, dUout);
+                                                  coef, pflag, cnt, fl, fBn, dUout, ect);
   return 1;
 }
 

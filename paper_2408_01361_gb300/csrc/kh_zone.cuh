@@ -414,6 +414,14 @@ __device__ __forceinline__ void update_zone(const double* U0, const CVars& Pin, 
 }
 
 
+// Edge EMFs of Flux-CT (k_emf's output). When given to the mixed update, the
+// field components' face fluxes are formed from them right there (the
+// values k_apply_ct would have stored: halved sums of two edge EMFs; a
+// halving is exact, so the divergence rounds as before) instead of read back.
+struct CtEmf {
+  const float* e[3];
+};
+
 // The mixed update of one zone, FP64 arithmetic only where the result is
 // FP64 storage. FP32: the stage input, the sources, the flux divergence, the
 // increment c dt (S - div F), the floors' decisions and b^2. Double-float
@@ -431,7 +439,8 @@ __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT
                                                   const GeomT<float>& Gf, const Scheme& S, df64 cdt, int8_t* pflag,
                                                   unsigned long long* cnt, int i, int j, int k,
                                                   FailList fl = FailList{nullptr, nullptr},
-                                                  const double* fBn = nullptr, double* dUout = nullptr) {
+                                                  const double* fBn = nullptr, double* dUout = nullptr,
+                                                  CtEmf ect = CtEmf{{nullptr, nullptr, nullptr}}) {
   const long long c = L.at(k, j, i);
   const long long p = (long long)j * L.n1s + i;
   const long long sj = L.n1s, sk = (long long)L.n1s * L.n2s;
@@ -458,8 +467,50 @@ __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const long long o = v * L.plane + c;
-      float div = (F1[o + 1] - F1[o]) * i1 + (F2[o + sj] - F2[o]) * i2;
-      if (L.ndim == 3) div += (F3[o + sk] - F3[o]) * i3;
+      // lower / upper face fluxes per direction
+      float a1, b1, a2, b2, a3 = 0.0f, b3 = 0.0f;
+      const bool three = L.ndim == 3;
+      if (ect.e[2] && v >= V_B1 && (three || v != V_B3)) {
+        const float* e1 = ect.e[0];
+        const float* e2 = ect.e[1];
+        const float* e3 = ect.e[2];
+        const float h = 0.5f;
+        if (v == V_B1) {
+          a1 = 0.0f;
+          b1 = 0.0f;
+          a2 = -h * (e3[c] + e3[c + 1]);
+          b2 = -h * (e3[c + sj] + e3[c + sj + 1]);
+          if (three) {
+            a3 = h * (e2[c] + e2[c + 1]);
+            b3 = h * (e2[c + sk] + e2[c + sk + 1]);
+          }
+        } else if (v == V_B2) {
+          a1 = h * (e3[c] + e3[c + sj]);
+          b1 = h * (e3[c + 1] + e3[c + 1 + sj]);
+          a2 = 0.0f;
+          b2 = 0.0f;
+          if (three) {
+            a3 = -h * (e1[c] + e1[c + sj]);
+            b3 = -h * (e1[c + sk] + e1[c + sk + sj]);
+          }
+        } else {  // B3, 3-D
+          a1 = -h * (e2[c] + e2[c + sk]);
+          b1 = -h * (e2[c + 1] + e2[c + 1 + sk]);
+          a2 = h * (e1[c] + e1[c + sk]);
+          b2 = h * (e1[c + sj] + e1[c + sj + sk]);
+        }
+      } else {
+        a1 = F1[o];
+        b1 = F1[o + 1];
+        a2 = F2[o];
+        b2 = F2[o + sj];
+        if (three) {
+          a3 = F3[o];
+          b3 = F3[o + sk];
+        }
+      }
+      float div = (b1 - a1) * i1 + (b2 - a2) * i2;
+      if (three) div += (b3 - a3) * i3;
       const float inc = (cdt * (Sv[v] - div)).hi;  // c dt (S - div F)
       const double u0 = U0[o];
       if (Uout) Uout[o] = u0 + f64_of_f32(inc);    // the conserved update, FP64
