@@ -171,8 +171,7 @@ int run_stage_mixed(kh_ctx* x, int st, const double* U0, const VarsT<TIN>& Pin, 
   VarsT<float> Pf;
   if constexpr (sizeof(TIN) == sizeof(double)) {
     for (int q = 0; q < NV; ++q) Pf.v[q] = x->pnf + q * L.plane;
-    n += launch_vars_to_f32(cviewT(Pin), Pf, L, s);
-    n += launch_bc_fill<double, float>(cviewT(Pin), Pf, L, x->S, dlo, dhi, s);
+    n += launch_fill_f32(cviewT(Pin), Pf, L, x->S, dlo, dhi, s);
   } else {
     n += launch_bc<TIN>(Pin, L, x->S, dlo, dhi, s);
     Pf = Pin;

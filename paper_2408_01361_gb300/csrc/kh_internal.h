@@ -178,6 +178,10 @@ int launch_to_f32(const double* src, float* dst, long long n, cudaStream_t s);
 int launch_df_planes(const double* geo, const double* flo, float* df, long long gplane, cudaStream_t s);
 // FP64 -> FP32 copy of the 8 primitive planes (every cell of the allocation).
 int launch_vars_to_f32(const CVars& src, const VarsT<float>& dst, const Layout& L, cudaStream_t s);
+// The FP32 copy of an FP64 state with its ghost cells filled, in one pass:
+// interior converted, ghosts by the ghost map from the FP64 interior.
+int launch_fill_f32(const CVars& src, const VarsT<float>& dst, const Layout& L, const Scheme& S, const double* dlo,
+                    const double* dhi, cudaStream_t s);
 
 // Blocks used by the reductions (partial buffers hold 2 doubles per block).
 constexpr int RED_THREADS = 256;

@@ -149,11 +149,8 @@ __device__ __forceinline__ GhostSrc ghost_source(const Layout& L, const Scheme& 
 }
 
 template <class TS, class TD>
-__global__ void k_bc_fill(CVarsT<TS> src, VarsT<TD> dst, Layout L, Scheme S, const TS* dlo, const TS* dhi) {
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= ghost_total(L)) return;
-  int i, j, k;
-  ghost_cell(L, t, i, j, k);
+__device__ __forceinline__ void bc_cell(const CVarsT<TS>& src, const VarsT<TD>& dst, const Layout& L, const Scheme& S,
+                                        const TS* dlo, const TS* dhi, int i, int j, int k) {
   const GhostSrc g = ghost_source(L, S, i, j, k);
   const int ks = g.k, js = g.j, is = g.i, clamp = g.clamp;
   const bool flip = g.flip;
@@ -166,6 +163,33 @@ __global__ void k_bc_fill(CVarsT<TS> src, VarsT<TD> dst, Layout L, Scheme S, con
     if (flip && (v == V_U2 || v == V_B2)) x = -x;
     if constexpr (sizeof(TS) == sizeof(TD)) dst.v[v][d] = x;
     else dst.v[v][d] = f32_of_f64(x);  // integer operations, not the FP64 pipe
+  }
+}
+
+template <class TS, class TD>
+__global__ void k_bc_fill(CVarsT<TS> src, VarsT<TD> dst, Layout L, Scheme S, const TS* dlo, const TS* dhi) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= ghost_total(L)) return;
+  int i, j, k;
+  ghost_cell(L, t, i, j, k);
+  bc_cell<TS, TD>(src, dst, L, S, dlo, dhi, i, j, k);
+}
+
+// The FP32 copy of an FP64 state in one pass over the ghosted box (row
+// padding skipped): interior cells converted, ghost cells by the ghost map
+// from the FP64 interior (the mixed path's stage-1 input).
+__global__ void k_fill_f32(CVarsT<double> src, VarsT<float> dst, Layout L, Scheme S, const double* dlo,
+                           const double* dhi) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (unsigned)L.N1 * L.N2 * L.N3) return;
+  int i, j, k;
+  split3(t, L.N1, L.N2, i, j, k);
+  if (i >= L.s[0] && i < L.e[0] && j >= L.s[1] && j < L.e[1] && k >= L.s[2] && k < L.e[2]) {
+    const long long c = L.at(k, j, i);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) dst.v[v][c] = f32_of_f64(src.v[v][c]);  // integer ops, not the FP64 pipe
+  } else {
+    bc_cell<double, float>(src, dst, L, S, dlo, dhi, i, j, k);
   }
 }
 
@@ -849,6 +873,13 @@ int launch_cfl(T* const ctop[3], const Layout& L, double cfl, double* partial, i
 }
 template int launch_cfl<double>(double* const[3], const Layout&, double, double*, int, double*, cudaStream_t);
 template int launch_cfl<float>(float* const[3], const Layout&, double, double*, int, double*, cudaStream_t);
+
+int launch_fill_f32(const CVars& src, const VarsT<float>& dst, const Layout& L, const Scheme& S, const double* dlo,
+                    const double* dhi, cudaStream_t s) {
+  const long long tot = (long long)L.N1 * L.N2 * L.N3;
+  k_fill_f32<<<nblocks(tot, TPB), TPB, 0, s>>>(src, dst, L, S, dlo, dhi);
+  return 1;
+}
 
 int launch_vars_to_f32(const CVars& src, const VarsT<float>& dst, const Layout& L, cudaStream_t s) {
   long long b = nblocks(L.plane, 256);
