@@ -828,10 +828,10 @@ FP64_FLOPS_PER_ZONE: dict = {
 FP32_FLOPS_PER_ZONE: dict = {
     # paired instructions count 2 lanes (an FFMA2 = 4 flops)
     ("mixed", "flux_x1"): 1565.0, ("mixed", "flux_x2"): 1645.0, ("mixed", "flux_x3"): 1714.0,
-    ("mixed", "update"): 2171.1,  # stages 1 and 2 (2154, 2188); FP64: 1 and 21 flops per zone
+    ("mixed", "update"): 2195.1,  # stages 1 and 2 (2178, 2212); FP64: 1 and 21 flops per zone
 }
 DRAM_BYTES_PER_ZONE: dict = {
-    ("mixed", "update"): 296.7,  # mean of stage 1 (252.4) and stage 2 (341.0)
+    ("mixed", "update"): 266.2,  # mean of stage 1 (223.4) and stage 2 (309.0)
     ("mixed", "flux_x1"): 44.4, ("mixed", "flux_x2"): 46.0, ("mixed", "flux_x3"): 47.7,
     ("fp64", "update"): 419.1,  # stage 1
     ("fp64", "flux_x1"): 118.0, ("fp64", "flux_x2"): 126.1, ("fp64", "flux_x3"): 128.3,
