@@ -181,7 +181,8 @@ __global__ void __launch_bounds__(256, 2) km_update_mixed(const MBlock* blk, con
                                                       Arena<float> Pout32, double* Uout, const float* F1,
                                                       const float* F2, const float* F3, GeoArena GA, Scheme S,
                                                       const double* dtp, double coef, int8_t* pflag,
-                                                      unsigned long long* cnt, const double* fBn) {
+                                                      unsigned long long* cnt, const double* fBn, const float* e1,
+                                                      const float* e2, const float* e3) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= __ldg(pre + nb)) return;
   const int b = find_block(pre, nb, t);
@@ -196,7 +197,8 @@ __global__ void __launch_bounds__(256, 2) km_update_mixed(const MBlock* blk, con
   update_mixed_zone(U0 + o8, cvars_at(Pin, m), P64, P32, Uout ? Uout + o8 : nullptr, F1 + o8, F2 + o8,
                     m.L.ndim == 3 ? F3 + o8 : nullptr, m.L, geo64(GA, m), geo32(GA, m), S,
                     df_of_f64(coef * __ldg(dtp)), pflag + m.off, cnt, i, j, k, FailList{nullptr, nullptr},
-                    fBn ? fBn + 3 * m.off : nullptr);
+                    fBn ? fBn + 3 * m.off : nullptr, nullptr,
+                    CtEmf{{e1 ? e1 + m.off : nullptr, e2 ? e2 + m.off : nullptr, e3 ? e3 + m.off : nullptr}});
 }
 
 template <class T>
@@ -1096,8 +1098,12 @@ template <class T> int fill_ghosts(kh_mesh* x, const Arena<T>& P) {
   return 1;
 }
 
+// fluxct: Flux-CT after the face fluxes (its EMF phase; the field-flux phase
+// too unless emf_only, for an update that forms the field fluxes from the
+// EMFs).
 template <class TIN, class R>
-int flux_pass(kh_mesh* x, const Arena<TIN>& P, R* const F[3], R* const ct[3], R* const emf[3], bool fluxct = true) {
+int flux_pass(kh_mesh* x, const Arena<TIN>& P, R* const F[3], R* const ct[3], R* const emf[3], bool fluxct = true,
+              bool emf_only = false) {
   int n = 0;
   const GeoArena GA = garena(x);
   for (int d = 1; d <= x->ndim; ++d) {
@@ -1116,7 +1122,7 @@ int flux_pass(kh_mesh* x, const Arena<TIN>& P, R* const F[3], R* const ct[3], R*
     ++n;
   }
   const unsigned tot = x->pre_ct.back();
-  for (int phase = 0; phase < 2 && fluxct; ++phase) {
+  for (int phase = 0; phase < (emf_only ? 1 : 2) && fluxct; ++phase) {
     km_ct<R><<<nblk(tot, MTPB), MTPB, 0, x->stream>>>(x->dblk, x->dpre[4], x->nb, F[0], F[1], F[2], emf[0], emf[1],
                                                       emf[2], phase);
     ++n;
@@ -1193,20 +1199,22 @@ int issue_mesh_step(kh_mesh* x, double* U, double* P, double* B) {
     km_to_f32<<<nblk(x->pre_alloc.back(), 256), 256, 0, s>>>(x->dblk, x->dpre[5], x->nb, Pn, Pnf);
     ++n;
     n += fill_ghosts(x, Pnf);
-    n += flux_pass<float, float>(x, Pnf, x->Ff, x->ctopf, x->emff, !face);
+    // Flux-CT: EMFs only, the update forms the field fluxes from them
+    const float* ce[3] = {face ? nullptr : x->emff[0], face ? nullptr : x->emff[1], face ? nullptr : x->emff[2]};
+    n += flux_pass<float, float>(x, Pnf, x->Ff, x->ctopf, x->emff, !face, true);
     if (face) n += face_ct_pass<float>(x, Pnf, x->Ff, x->eccf, x->emff, x->fBstar, 0.5);
     km_update_mixed<<<gu, tu, 0, s>>>(x->dblk, x->dpre[3], x->nb, U, Pnf, none64, Psf, nullptr, x->Ff[0],
                                         x->Ff[1], x->Ff[2], GA, x->S, x->dscalar + 3, 0.5, x->pflag, x->counters,
-                                        face ? x->fBstar : nullptr);
+                                        face ? x->fBstar : nullptr, ce[0], ce[1], ce[2]);
     km_fixup<float><<<gz, MTPB, 0, s>>>(x->dblk, x->dpre[3], x->nb, Psf, nullptr, x->pflag, GA, x->S, x->counters);
     n += 2;
     // stage 2: FP32 P* -> FP64 P^{n+1}, U^{n+1}
     n += fill_ghosts(x, Psf);
-    n += flux_pass<float, float>(x, Psf, x->Ff, x->ctopf, x->emff, !face);
+    n += flux_pass<float, float>(x, Psf, x->Ff, x->ctopf, x->emff, !face, true);
     if (face) n += face_ct_pass<float>(x, Psf, x->Ff, x->eccf, x->emff, x->fB, 1.0);
     km_update_mixed<<<gu, tu, 0, s>>>(x->dblk, x->dpre[3], x->nb, U, Psf, Pn, none32, U, x->Ff[0], x->Ff[1],
                                         x->Ff[2], GA, x->S, x->dscalar + 3, 1.0, x->pflag, x->counters,
-                                        face ? x->fB : nullptr);
+                                        face ? x->fB : nullptr, ce[0], ce[1], ce[2]);
     km_fixup<double><<<gz, MTPB, 0, s>>>(x->dblk, x->dpre[3], x->nb, Pn, U, x->pflag, GA, x->S, x->counters);
     n += 2;
     n += cfl_pass<float>(x, x->ctopf);
