@@ -264,21 +264,23 @@ def measure(args, cfg, P0, ctx, dev, stream, dist, world, oracle_step):
     ctx.set_graph(False)
     out["graph"] = {"value": nz * args.steps * world / (gms * 1e-3), "ms_per_step": gms / args.steps}
     if not args.no_e2e:
-        hU = torch.empty(U.shape, dtype=torch.float64, pin_memory=True)
-        hPB = torch.empty(PB.shape, dtype=torch.float64, pin_memory=True)
-        hU.copy_(U)
-        hPB.copy_(PB)
+        # the state crosses the host link in the library's compact interior
+        # order (kh_pack_state / kh_unpack_state: no ghost cells, no padding)
+        stage_d = torch.empty(16 * nz, dtype=torch.float64, device=dev)
+        host = torch.empty(16 * nz, dtype=torch.float64, pin_memory=True)
+        ctx.pack_state(U, P, B, stage_d)
+        host.copy_(stage_d)
         torch.cuda.synchronize(dev)
         if dist:
             dist.barrier()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)
         for _ in range(args.steps):
-            U.copy_(hU, non_blocking=True)
-            PB.copy_(hPB, non_blocking=True)
+            stage_d.copy_(host, non_blocking=True)
+            ctx.unpack_state(stage_d, U, P, B)
             dt, _ = ctx.step(U, P, B, 0.5 * dt)
-            hU.copy_(U, non_blocking=True)
-            hPB.copy_(PB, non_blocking=True)
+            ctx.pack_state(U, P, B, stage_d)
+            host.copy_(stage_d, non_blocking=True)
         f1.record(stream)
         torch.cuda.synchronize(dev)
         ems = f0.elapsed_time(f1)
@@ -286,7 +288,7 @@ def measure(args, cfg, P0, ctx, dev, stream, dist, world, oracle_step):
             t = torch.tensor([ems], device=dev, dtype=torch.float64)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ems = float(t.item())
-        nbytes = (U.numel() + PB.numel()) * 8
+        nbytes = host.numel() * 8
         out["e2e"] = {"value": nz * args.steps * world / (ems * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                       "d2h_bytes_per_step": nbytes}
     return out

@@ -217,6 +217,14 @@ int kh_face_to_cell(kh_ctx* ctx, const double* fB, double* B);
  * (host pointers; synchronises). Any context. */
 int kh_face_divb(kh_ctx* ctx, const double* fB, double* max_abs, double* l1);
 
+/* The interior state in a compact order, for moving it to and from the host
+ * with the ghost cells and row padding left out: kh_pack_state writes
+ * out[16][n3][n2][n1] (device) = U's 8 slots, then P's 5 and B's 3, of the
+ * interior zones; kh_unpack_state writes them back into the padded layout
+ * (interior cells only). Asynchronous on the context stream. */
+int kh_pack_state(kh_ctx* ctx, const double* U, const double* P, const double* B, double* out);
+int kh_unpack_state(kh_ctx* ctx, const double* in, double* U, double* P, double* B);
+
 /* Ghost fill of (P, B) in place with the context's boundary rules. */
 int kh_fill_ghosts(kh_ctx* ctx, double* P, double* B);
 

@@ -710,6 +710,16 @@ int kh_step(kh_ctx* x, double* U, double* P, double* B, double dt, double* dt_cf
   return (int)(st.nfail > 0x7fffffffLL ? 0x7fffffff : st.nfail);
 }
 
+int kh_pack_state(kh_ctx* x, const double* U, const double* P, const double* B, double* out) {
+  if (!x || !U || !P || !B || !out) return KH_EINVAL;
+  return check_launch(x, launch_pack(U, cvars_of(x, P, B), out, x->L, x->stream));
+}
+
+int kh_unpack_state(kh_ctx* x, const double* in, double* U, double* P, double* B) {
+  if (!x || !in || !U || !P || !B) return KH_EINVAL;
+  return check_launch(x, launch_unpack(in, U, vars_of(x, P, B), x->L, x->stream));
+}
+
 int kh_set_face_field(kh_ctx* x, double* fB) {
   if (!x || !fB || x->S.bfield != KH_B_FACE) return KH_EINVAL;
   if (x->fB != fB) drop_graph(x);  // a captured step holds the old pointer

@@ -178,6 +178,9 @@ int launch_to_f32(const double* src, float* dst, long long n, cudaStream_t s);
 int launch_df_planes(const double* geo, const double* flo, float* df, long long gplane, cudaStream_t s);
 // FP64 -> FP32 copy of the 8 primitive planes (every cell of the allocation).
 int launch_vars_to_f32(const CVars& src, const VarsT<float>& dst, const Layout& L, cudaStream_t s);
+// The interior state (U, then P and B) in the compact order [16][n3][n2][n1].
+int launch_pack(const double* U, const CVars& PB, double* out, const Layout& L, cudaStream_t s);
+int launch_unpack(const double* in, double* U, const Vars& PB, const Layout& L, cudaStream_t s);
 // The FP32 copy of an FP64 state with its ghost cells filled, in one pass:
 // interior converted, ghosts by the ghost map from the FP64 interior.
 int launch_fill_f32(const CVars& src, const VarsT<float>& dst, const Layout& L, const Scheme& S, const double* dlo,

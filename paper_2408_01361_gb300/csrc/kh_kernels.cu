@@ -874,6 +874,46 @@ int launch_cfl(T* const ctop[3], const Layout& L, double cfl, double* partial, i
 template int launch_cfl<double>(double* const[3], const Layout&, double, double*, int, double*, cudaStream_t);
 template int launch_cfl<float>(float* const[3], const Layout&, double, double*, int, double*, cudaStream_t);
 
+// The interior state in the compact order [16][n3][n2][n1] (U's 8 slots,
+// then P's 5 and B's 3) from / to the padded layout.
+__global__ void k_pack(const double* U, CVars PB, double* out, Layout L) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned nz = nzones(L);
+  if (t >= nz) return;
+  int i, j, k;
+  zone_ijk(L, t, i, j, k);
+  const long long c = L.at(k, j, i);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) out[(long long)v * nz + t] = U[v * L.plane + c];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) out[(long long)(NV + v) * nz + t] = PB.v[v][c];
+}
+
+__global__ void k_unpack(const double* in, double* U, Vars PB, Layout L) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned nz = nzones(L);
+  if (t >= nz) return;
+  int i, j, k;
+  zone_ijk(L, t, i, j, k);
+  const long long c = L.at(k, j, i);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) U[v * L.plane + c] = in[(long long)v * nz + t];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) PB.v[v][c] = in[(long long)(NV + v) * nz + t];
+}
+
+int launch_pack(const double* U, const CVars& PB, double* out, const Layout& L, cudaStream_t s) {
+  const long long nz = (long long)L.n1 * L.n2 * L.n3;
+  k_pack<<<nblocks(nz, TPB), TPB, 0, s>>>(U, PB, out, L);
+  return 1;
+}
+
+int launch_unpack(const double* in, double* U, const Vars& PB, const Layout& L, cudaStream_t s) {
+  const long long nz = (long long)L.n1 * L.n2 * L.n3;
+  k_unpack<<<nblocks(nz, TPB), TPB, 0, s>>>(in, U, PB, L);
+  return 1;
+}
+
 int launch_fill_f32(const CVars& src, const VarsT<float>& dst, const Layout& L, const Scheme& S, const double* dlo,
                     const double* dhi, cudaStream_t s) {
   const long long tot = (long long)L.N1 * L.N2 * L.N3;

@@ -81,6 +81,8 @@ def lib():
         L.kh_cfl_dt.argtypes = [vp, vp, vp, dp]
         L.kh_divb.argtypes = [vp, vp, dp, dp]
         L.kh_set_face_field.argtypes = [vp, vp]
+        L.kh_pack_state.argtypes = [vp, vp, vp, vp, vp]
+        L.kh_unpack_state.argtypes = [vp, vp, vp, vp, vp]
         L.kh_face_to_cell.argtypes = [vp, vp, vp]
         L.kh_face_divb.argtypes = [vp, vp, dp, dp]
         L.kh_fluxes.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -255,6 +257,14 @@ class Context:
         mx, l1 = C.c_double(), C.c_double()
         _check(lib().kh_divb(self._h, _ptr(B), C.byref(mx), C.byref(l1)), "kh_divb")
         return mx.value, l1.value
+
+    # ---- compact interior state ----
+    def pack_state(self, U, P, B, out):
+        """out (device, 16 x interior zones): U's 8 slots, then P's 5 and B's 3."""
+        _check(lib().kh_pack_state(self._h, _ptr(U), _ptr(P), _ptr(B), _ptr(out)), "kh_pack_state")
+
+    def unpack_state(self, inp, U, P, B):
+        _check(lib().kh_unpack_state(self._h, _ptr(inp), _ptr(U), _ptr(P), _ptr(B)), "kh_unpack_state")
 
     # ---- face-centred constrained transport ----
     def set_face_field(self, fB):

@@ -77,3 +77,30 @@ def test_graph_follows_new_pointers(kh):
     assert np.array_equal(ga[0], na[0]) and np.array_equal(gb[0], nb[0])
     assert np.array_equal(ga[1], na[1]) and np.array_equal(gb[1], nb[1])
     assert not np.array_equal(ga[0], gb[0])
+
+
+def test_pack_unpack_state_round_trip(kh):
+    """kh_pack_state writes the interior of U, P, B in the compact order
+    [16][n3][n2][n1]; kh_unpack_state puts it back (interior cells only);
+    a step from the unpacked state equals a step from the original."""
+    cfg = inputs.torus_cfg(40, 24, 10, r_out=60.0)
+    P = inputs.torus_state(cfg, seed=2)
+    ctx = kh.Context(cfg)
+    g = GpuRun(ctx, cfg, P)
+    nz = cfg["n1"] * cfg["n2"] * cfg["n3"]
+    buf = ctx.torch.empty(16 * nz, dtype=ctx.torch.float64, device=ctx.device)
+    ctx.pack_state(g.U, g.P, g.B, buf)
+    Uh, Ph = g.host()
+    sl = (slice(None),) + inputs.interior(cfg)
+    packed = buf.cpu().numpy().reshape(16, cfg["n3"], cfg["n2"], cfg["n1"])
+    assert np.array_equal(packed[:8], Uh[sl]) and np.array_equal(packed[8:], Ph[sl])
+    U2 = ctx.empty(8)
+    PB2 = ctx.empty(8)
+    P2, B2 = ctx.split(PB2)
+    ctx.unpack_state(buf, U2, P2, B2)
+    dt = 0.5 * ctx.cfl_dt(g.P, g.B)
+    ctx.step(g.U, g.P, g.B, dt)
+    ctx.step(U2, P2, B2, dt)
+    N1 = P.shape[3]
+    assert np.array_equal(ctx.to_host(U2, N1)[sl], ctx.to_host(g.U, N1)[sl])
+    assert np.array_equal(ctx.to_host(PB2, N1)[sl], ctx.to_host(g.PB, N1)[sl])
