@@ -78,8 +78,8 @@ typedef struct {
                              Flux-CT are applied again before the stage's update. The
                              flags' ghost zones follow the state's ghost map (Dirichlet
                              ghosts unflagged). 0: off. Single-grid contexts with
-                             Flux-CT and the predictor-corrector (the mesh, face CT,
-                             the Runge-Kutta integrators and the adjoint refuse it). */
+                             Flux-CT, with any integrator (the mesh, face CT and
+                             the adjoint refuse it). */
   int bfield;             /* KH_B_FLUXCT: cell-centred field, Flux-CT (Toth 2000);
                              KH_B_FACE: face-centred constrained transport
                              ("Algorithm" section: Stone & Gardiner 2009). The face
@@ -91,8 +91,10 @@ typedef struct {
                              Single grids and the refined mesh (kh_mesh_*: coarse
                              edges on a level interface take the finer block's EMFs),
                              FP64 and KH_MIXED (FP32 EMFs, the curl formed in FP64,
-                             the face field in FP64); no flux correction, the
-                             predictor-corrector only, no adjoint. */
+                             the face field in FP64); no flux correction, no
+                             adjoint. Single grids run it with any integrator (the
+                             face field is a stage state like U); the mesh with the
+                             predictor-corrector. */
   int emf;                /* KH_B_FACE edge EMFs: KH_EMF_AVERAGE (mean of the four
                              face values; with face means as the zone field this is
                              Flux-CT) or KH_EMF_GS05 (Gardiner & Stone 2005: plus the
@@ -116,10 +118,13 @@ typedef struct {
                              fourth-order SSP scheme), in Shu-Osher form: each stage
                              U_s = sum_j a_sj U_j + c_s dt L(P_{s-1}) with the
                              stage operator, inversion, floors and fixup of a
-                             predictor-corrector stage. Single-grid Flux-CT contexts
-                             without the flux correction, FP64 or KH_MIXED (the
-                             FP32 shadow carries the intermediate stage states); 8 to
-                             48 extra planes of scratch. */
+                             predictor-corrector stage. Single-grid contexts, FP64 or
+                             KH_MIXED (the FP32 shadow carries the intermediate stage
+                             primitives), with Flux-CT (and the flux correction in
+                             every stage) or face CT (the face field combined with
+                             the same weights; SSPRK(5,4)'s fifth stage takes stage
+                             4's face increment as its output minus its base); 8 to
+                             48 extra planes of scratch, plus 6 to 15 with face CT. */
 } kh_coords;
 
 /* Counters of the last kh_step (both stages summed). */

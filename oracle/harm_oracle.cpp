@@ -1052,6 +1052,8 @@ void or_stage(const or_params* c, const double* U0, const double* Pin, double cd
 // (summed over both stages). Returns the next CFL dt.
 double or_step_rk(const or_params* c, double* U, double* P, double dt, const double* dir_lo, const double* dir_hi,
                   long* stats);
+static double rk_step(const or_params* c, double* U, double* P, double* fB, double dt, const double* dir_lo,
+                      const double* dir_hi, long* stats);
 
 double or_step(const or_params* c, double* U, double* P, double dt, const double* dir_lo, const double* dir_hi,
                long* stats) {
@@ -1101,8 +1103,17 @@ double or_step(const or_params* c, double* U, double* P, double dt, const double
 //   SSPRK(5,4) of Spiteri & Ruuth (2002): the five stages with their
 //   published coefficients; the last stage's dt L(P3) term reuses the raw
 //   increment of stage 4, c4 dt L(P3).
+// With face-centred CT (fB non-null) the face field is state like U: stage s
+// forms its face base sum_j a_sj fB_j and adds c_s dt curl E(P_{s-1}); the
+// fifth SSPRK(5,4) stage's face increment is stage 4's output minus stage 4's
+// base (c4 dt curl E(P3) up to rounding).
 double or_step_rk(const or_params* c, double* U, double* P, double dt, const double* dir_lo, const double* dir_hi,
                   long* stats) {
+  return rk_step(c, U, P, nullptr, dt, dir_lo, dir_hi, stats);
+}
+
+static double rk_step(const or_params* c, double* U, double* P, double* fB, double dt, const double* dir_lo,
+                      const double* dir_hi, long* stats) {
   struct RKStage {
     int n;
     int src[3];
@@ -1132,6 +1143,11 @@ double or_step_rk(const or_params* c, double* U, double* P, double dt, const dou
   Us[0].assign(U, U + n);
   Ps[0].assign(P, P + n);
   std::vector<double> base(n), dU4(n, 0.0), dUs(n, 0.0);
+  const bool face = fB != nullptr;
+  const size_t nf = face ? 3 * gr.cells() : 0;
+  std::vector<std::vector<double>> Fs(S.size() + 1);
+  std::vector<double> fbase(nf), fbase4(nf, 0.0);
+  if (face) Fs[0].assign(fB, fB + nf);
   Fluxes fx;
   StageStats st;
   for (size_t s = 0; s < S.size(); ++s) {
@@ -1145,10 +1161,22 @@ double or_step_rk(const or_params* c, double* U, double* P, double dt, const dou
     }
     Us[s + 1] = base;
     Ps[s + 1] = Ps[s];
+    if (face) {
+      for (size_t e = 0; e < nf; ++e) {
+        double b = 0.0;
+        for (int t = 0; t < q.n; ++t) b += q.a[t] * Fs[q.src[t]][e];
+        if (q.dU4 != 0.0) b += q.dU4 * (Fs[4][e] - fbase4[e]);
+        fbase[e] = b;
+      }
+      Fs[s + 1] = fbase;
+    }
     const bool keep = c->integrator == INT_SSPRK54 && s == 3;
     stage<double>(gr, base.data(), Ps[s].data(), c->gam, q.cdt * dt, Us[s + 1].data(), Ps[s + 1].data(), fx, st,
-                  nullptr, nullptr, nullptr, nullptr, keep ? dU4.data() : nullptr);
+                  nullptr, nullptr, face ? fbase.data() : nullptr, face ? Fs[s + 1].data() : nullptr,
+                  keep ? dU4.data() : nullptr);
+    if (face && keep) fbase4 = fbase;
   }
+  if (face) std::memcpy(fB, Fs[S.size()].data(), nf * sizeof(double));
   const double dtn = cfl_dt(gr, fx);
   const size_t last = S.size();
   for (int v = 0; v < NVAR; ++v)
@@ -1178,6 +1206,7 @@ double or_step_rk(const or_params* c, double* U, double* P, double dt, const dou
 double or_step_face(const or_params* c, double* U, double* P, double* fB, double dt, const double* dir_lo,
                     const double* dir_hi, long* stats) {
   if (c->bfield != BFIELD_FACE || c->fofc) return -1.0;
+  if (c->integrator != INT_VL2) return rk_step(c, U, P, fB, dt, dir_lo, dir_hi, stats);
   Grid gr;
   build_grid(*c, gr);
   const size_t n = gr.cells() * NVAR;

@@ -82,7 +82,7 @@ void free_all(kh_ctx* x) {
                   x->counters, x->dirichlet[0], x->dirichlet[1], x->geof, x->dgmf, x->pstarf, x->pnf, x->Ff[0],
                   x->Ff[1], x->Ff[2], x->ctopf[0], x->ctopf[1], x->ctopf[2], x->emff[0], x->emff[1],
                   x->emff[2], x->dirichletf[0], x->dirichletf[1], x->adj, x->adj_i8, x->adj_red, x->geodf, x->flist,
-                  x->fflag, x->fsave, x->fsavef, x->fBstar, x->ecc, x->eccf, x->rk};
+                  x->fflag, x->fsave, x->fsavef, x->fBstar, x->ecc, x->eccf, x->rk, x->rkf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -114,9 +114,10 @@ int run_stage(kh_ctx* x, int st, const double* U0, const Vars& Pin, const Vars& 
   if (x->S.bfield == KH_B_FACE) {
     // face-centred CT: edge EMFs from the raw fluxes move the face field;
     // the update takes the zones' field from the new faces
-    fBn = st == 0 ? x->fBstar : x->fB;
+    fBn = x->fb_out ? x->fb_out : (st == 0 ? x->fBstar : x->fB);
+    const double* fB0 = x->fb_in ? x->fb_in : x->fB;
     mark(x, KH_T_CT, st, 0);
-    n += launch_face_ct<double>(cview(Pin), x->F, x->ecc, x->emf, x->fB, fBn, L, G, x->S, x->dscalar + 3, coef, s);
+    n += launch_face_ct<double>(cview(Pin), x->F, x->ecc, x->emf, fB0, fBn, L, G, x->S, x->dscalar + 3, coef, s);
     mark(x, KH_T_CT, st, 1);
   } else {
     mark(x, KH_T_CT, st, 0);
@@ -194,8 +195,9 @@ int run_stage_mixed(kh_ctx* x, int st, const double* U0, const VarsT<TIN>& Pin, 
   mark(x, KH_T_CT, st, 0);
   if (!fct) {
     // face-centred CT: FP32 EMFs, FP64 face field
-    fBn = st == 0 ? x->fBstar : x->fB;
-    n += launch_face_ct<float>(cviewT(Pf), x->Ff, x->eccf, x->emff, x->fB, fBn, L, Gf, x->S, x->dscalar + 3, coef,
+    fBn = x->fb_out ? x->fb_out : (st == 0 ? x->fBstar : x->fB);
+    const double* fB0 = x->fb_in ? x->fb_in : x->fB;
+    n += launch_face_ct<float>(cviewT(Pf), x->Ff, x->eccf, x->emff, fB0, fBn, L, Gf, x->S, x->dscalar + 3, coef,
                                s);
   } else {
     n += launch_emf<float>(x->Ff, x->emff, L, s);
@@ -254,7 +256,6 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
   if (c->inverter < KH_INV_NOBLE2D || c->inverter > KH_INV_KASTAUN) return KH_EINVAL;
   if (c->inverter != KH_INV_NOBLE2D && c->precision != KH_FP64) return KH_EINVAL;
   if (c->integrator < KH_INT_VL2 || c->integrator > KH_INT_SSPRK54) return KH_EINVAL;
-  if (c->integrator != KH_INT_VL2 && (c->bfield != KH_B_FLUXCT || c->fofc)) return KH_EINVAL;
   if (c->bfield != KH_B_FLUXCT && c->bfield != KH_B_FACE) return KH_EINVAL;
   if (c->emf != KH_EMF_AVERAGE && c->emf != KH_EMF_GS05) return KH_EINVAL;
   if (c->bfield == KH_B_FACE && c->fofc) return KH_EINVAL;
@@ -382,6 +383,8 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
     // stage states, the stage base and SSPRK(5,4)'s stage-4 increment
     const int nrk = c->integrator == KH_INT_SSPRK54 ? 6 : (c->integrator == KH_INT_RK2 ? 2 : 0);
     if (nrk) KH_ALLOC(x->rk, (size_t)nrk * NV * pl);
+    const int nrkf = c->integrator == KH_INT_SSPRK54 ? 5 : (c->integrator == KH_INT_RK2 ? 2 : 0);
+    if (nrkf && c->bfield == KH_B_FACE) KH_ALLOC(x->rkf, (size_t)nrkf * 3 * pl);
   }
   if (c->bfield == KH_B_FACE) {
     KH_ALLOC(x->fBstar, 3 * pl);
@@ -415,6 +418,10 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
       if (rc == KH_OK && x->emff[d]) rc = cuda_fail(cudaMemset(x->emff[d], 0, plf));
     }
     if (rc == KH_OK) rc = cuda_fail(cudaMemset(x->pstar, 0, NV * pl));
+    if (rc == KH_OK && x->rkf) {
+      const int nrkf = c->integrator == KH_INT_SSPRK54 ? 5 : 2;
+      rc = cuda_fail(cudaMemset(x->rkf, 0, (size_t)nrkf * 3 * pl));
+    }
     if (rc == KH_OK && x->pstarf) rc = cuda_fail(cudaMemset(x->pstarf, 0, NV * plf));
   }
   if (rc == KH_OK) {
@@ -550,42 +557,68 @@ int issue_rk(kh_ctx* x, double* U, const Vars& Pn) {
   auto comb = [&](int nt, const double* const* in, const double* a) {
     n += launch_lincomb(base, nt, in, a, n8, s);
   };
+  // face-centred CT: the face field's stage states (fs[0] = the caller's
+  // field, the last stage writes it) and base, combined with the same
+  // weights; SSPRK(5,4)'s fifth stage takes stage 4's face increment as
+  // stage 4's output minus its base
+  const bool face = x->S.bfield == KH_B_FACE;
+  const long long n3 = 3 * (long long)L.plane;
+  double* fs[5] = {x->fB, nullptr, nullptr, nullptr, nullptr};
+  double* fbase = nullptr;
+  if (face && x->rkf) {
+    for (int q = 1; q <= nst; ++q) fs[q] = x->rkf + (q - 1) * n3;
+    fbase = x->rkf + nst * n3;
+  }
+  auto fcomb = [&](int nt, const double* const* in, const double* a) {
+    if (face) n += launch_lincomb(fbase, nt, in, a, n3, s);
+  };
+  auto faces = [&](const double* in, double* out) {
+    x->fb_in = face ? in : nullptr;
+    x->fb_out = face ? out : nullptr;
+  };
   if (x->S.integrator == KH_INT_RK1) {
+    faces(x->fB, x->fB);
     stage(0, U, U, 1.0, nullptr);
   } else if (x->S.integrator == KH_INT_RK2) {
+    faces(x->fB, fs[1]);
     stage(0, U, st[1], 1.0, nullptr);
     const double* in[2] = {U, st[1]};
     const double a[2] = {0.5, 0.5};
     comb(2, in, a);
+    const double* fin[2] = {fs[0], fs[1]};
+    fcomb(2, fin, a);
+    faces(fbase, x->fB);
     stage(1, base, U, 0.5, nullptr);
   } else {
     const double c4 = 0.544974750228521, c53 = 0.063692468666290;
+    faces(x->fB, fs[1]);
     stage(0, U, st[1], 0.391752226571890, nullptr);
-    {
-      const double* in[2] = {U, st[1]};
-      const double a[2] = {0.444370493651235, 0.555629506348765};
-      comb(2, in, a);
-      stage(1, base, st[2], 0.368410593050371, nullptr);
+    // stages 2-4 combine U (and fB) with the previous stage's state
+    const double a2[3][2] = {{0.444370493651235, 0.555629506348765},
+                             {0.620101851488403, 0.379898148511597},
+                             {0.178079954393132, 0.821920045606868}};
+    const double cs[3] = {0.368410593050371, 0.251891774271694, c4};
+    for (int q = 1; q <= 3; ++q) {
+      const double* in[2] = {U, st[q]};
+      comb(2, in, a2[q - 1]);
+      const double* fin[2] = {fs[0], fs[q]};
+      fcomb(2, fin, a2[q - 1]);
+      faces(fbase, fs[q + 1]);
+      stage(q, base, st[q + 1], cs[q - 1], q == 3 ? dU4 : nullptr);
     }
     {
-      const double* in[2] = {U, st[2]};
-      const double a[2] = {0.620101851488403, 0.379898148511597};
-      comb(2, in, a);
-      stage(2, base, st[3], 0.251891774271694, nullptr);
-    }
-    {
-      const double* in[2] = {U, st[3]};
-      const double a[2] = {0.178079954393132, 0.821920045606868};
-      comb(2, in, a);
-      stage(3, base, st[4], c4, dU4);
-    }
-    {
-      const double* in[4] = {st[2], st[3], st[4], dU4};
       const double a[4] = {0.517231671970585, 0.096059710526147, 0.386708617503269, c53 / c4};
+      const double* in[4] = {st[2], st[3], st[4], dU4};
       comb(4, in, a);
+      // fbase still holds stage 4's base: fs4 - fbase is stage 4's increment
+      const double fa[4] = {a[0], a[1], a[2] + a[3], -a[3]};
+      const double* fin[4] = {fs[2], fs[3], fs[4], fbase};
+      fcomb(4, fin, fa);
+      faces(fbase, x->fB);
       stage(4, base, U, 0.226007483236906, nullptr);
     }
   }
+  faces(nullptr, nullptr);
   return n;
 }
 

@@ -28,6 +28,11 @@ struct kh_ctx {
   double* ecc;
   float* eccf;     // the cell-centred EMFs of KH_MIXED (FP32)
   double* rk;      // Runge-Kutta integrators: stage states, base, stage-4 increment (8 planes each)
+  double* rkf;     // with face-centred CT: the face field's stage states and base (3 planes each)
+  // the face field a stage reads and writes (set per Runge-Kutta stage;
+  // null: the predictor-corrector's fB -> fBstar, fB -> fB)
+  const double* fb_in;
+  double* fb_out;
   double* partial;
   int npartial;
   double* dscalar;              // [0] dt_cfl out, [1..2] divb max/sum, [3] dt in

@@ -1,7 +1,9 @@
 """GPU parity of the Runge-Kutta integrators (RK1, RK2, SSPRK(5,4); FP64,
 Flux-CT) with the oracle's on a periodic box and on the FMKS torus
 (floors, failed inversions and their fixup included), their temporal orders
-on a fixed grid, and graph replay equal to eager stepping."""
+on a fixed grid, and graph replay equal to eager stepping; the same parity
+with face-centred CT (the face field a stage state) and with the first-order
+flux correction in every stage, FP64 and mixed."""
 import os
 
 import numpy as np
@@ -123,3 +125,94 @@ def test_mixed_integrators_vs_oracle(kh, orc, integ):
         assert np.abs(a[v] - b[v]).sum() / den < tol, ("U", v, np.abs(a[v] - b[v]).sum() / den)
         pden = max(np.abs(pb[v]).sum(), 1e-2 * nz if v in (2, 3, 4) else 0.0)
         assert np.abs(pa[v] - pb[v]).sum() / pden < tol, ("P", v, np.abs(pa[v] - pb[v]).sum() / pden)
+
+
+# ---- the integrators with face-centred CT and with the flux correction ----
+
+@pytest.mark.parametrize("integ", INTEGRATORS)
+@pytest.mark.parametrize("which", ["box3d-gs05", "torus3d-gs05", "torus2d-average"])
+def test_face_ct_integrator_parity(kh, orc, integ, which):
+    from test_gpu_facect import _case as face_case, _faces_interior, _run as face_run
+    cfg, P, fB = face_case(which)
+    cfg = dict(cfg, integrator=integ)
+    ctx, fBd, Ug, Pg, fg, Uc, Pc, fc, dtg, dto = face_run(kh, orc, cfg, P, fB, 2)
+    eu = rel_l1(interior(cfg, Ug), interior(cfg, Uc))
+    ep = rel_l1(interior(cfg, Pg), interior(cfg, Pc))
+    assert eu.max() < TOL and ep.max() < TOL, (eu, ep)
+    for x, y in zip(_faces_interior(cfg, fg), _faces_interior(cfg, fc)):
+        den = np.abs(y).sum()
+        if den > 0:
+            assert np.abs(x - y).sum() / den < TOL
+    assert abs(dtg - dto) <= 1e-10 * dto
+    mx, _ = ctx.face_divb(fBd)
+    dx = min((cfg[k][1] - cfg[k][0]) / cfg[n] for k, n in (("x1", "n1"), ("x2", "n2"), ("x3", "n3")))
+    assert mx < 1e-12 * np.abs(fc).max() / dx
+
+
+@pytest.mark.parametrize("integ", INTEGRATORS)
+@pytest.mark.parametrize("which", ["box_some", "torus3d"])
+def test_fofc_integrator_parity(kh, orc, integ, which):
+    from test_gpu_fofc import _case as fofc_case, _run as fofc_run
+    cfg, P, dirich = fofc_case(which)
+    cfg = dict(cfg, integrator=integ)
+    cfg, Ug, Pg, Uc, Pc, counts, dtg, dto = fofc_run(kh, orc, cfg, P, dirich, 2)
+    for c in counts:
+        assert c[0] == c[1] and c[0] > 0 and c[2] == c[3] and c[4] == c[5], counts
+    eu = rel_l1(interior(cfg, Ug), interior(cfg, Uc))
+    ep = rel_l1(interior(cfg, Pg), interior(cfg, Pc))
+    assert eu.max() < TOL and ep.max() < TOL, (eu, ep)
+    assert abs(dtg - dto) <= 1e-10 * dto
+
+
+def test_ssprk54_face_ct_graph_replay_matches_eager(kh, orc):
+    from test_gpu_facect import _case as face_case, _run as face_run
+    cfg, P, fB = face_case("torus3d-gs05")
+    cfg = dict(cfg, integrator="ssprk54")
+    a = face_run(kh, orc, cfg, P, fB, 2, graph=False)
+    b = face_run(kh, orc, cfg, P, fB, 2, graph=True)
+    for x, y in zip(a[2:5], b[2:5]):
+        assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("opt", ["face", "fofc"])
+def test_mixed_ssprk54_with_options_vs_oracle(kh, orc, opt):
+    """The mixed path's SSPRK(5,4) with face CT / the flux correction against
+    the oracle's FP64 step at the mixed path's FP32 flux level."""
+    if opt == "face":
+        from test_gpu_facect import _case as face_case
+        cfg, P, fB = face_case("torus3d-gs05")
+        dirich = None
+    else:
+        from test_gpu_fofc import _case as fofc_case
+        cfg, P, dirich = fofc_case("torus3d")
+        cfg, fB = dict(cfg, fofc=True), None
+    cfg = dict(cfg, integrator="ssprk54")
+    P = orc.apply_bc(cfg, P, dirich) if dirich is not None else orc.apply_bc(cfg, P)
+    U = orc.prim_to_cons(cfg, P)
+    dt = 0.5 * orc.cfl_dt(cfg, P)
+    if fB is None:
+        Uo, Po, _, _ = orc.step(cfg, U, P, dt)
+    else:
+        Uo, Po, fo, _, _ = orc.step_face(cfg, U, P, fB, dt)
+    c = dict(cfg, precision="mixed")
+    ctx = kh.Context(c)
+    g = GpuRun(ctx, c, P, U=U)
+    if fB is not None:
+        fBd = ctx.to_device(fB)
+        ctx.set_face_field(fBd)
+    ctx.step(g.U, g.P, g.B, dt)
+    Ug, Pg = g.host()
+    a, b = interior(cfg, Ug), interior(cfg, Uo)
+    pa, pb = interior(cfg, Pg), interior(cfg, Po)
+    mass = np.abs(b[0]).sum()
+    nz = b[0].size
+    for v in range(8):
+        tol = 2e-3 if v in (2, 3, 4) else 1e-4
+        den = max(np.abs(b[v]).sum(), 1e-3 * mass)
+        assert np.abs(a[v] - b[v]).sum() / den < tol, ("U", v, np.abs(a[v] - b[v]).sum() / den)
+        pden = max(np.abs(pb[v]).sum(), 1e-2 * nz if v in (2, 3, 4) else 0.0)
+        assert np.abs(pa[v] - pb[v]).sum() / pden < tol, ("P", v, np.abs(pa[v] - pb[v]).sum() / pden)
+    if fB is not None:
+        dx = min((cfg[k][1] - cfg[k][0]) / cfg[n] for k, n in (("x1", "n1"), ("x2", "n2"), ("x3", "n3")))
+        mx, _ = ctx.face_divb(fBd)
+        assert mx < 1e-12 * np.abs(fB).max() / dx
