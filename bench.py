@@ -424,8 +424,9 @@ def measure_facect(args, cfg64, P0, dev, stream, precision, emf="gs05"):
 
 
 def measure_inverters(args, cfg64, P0, dev, stream):
-    """FP64 primitive recovery by solver: the workload torus stepped with each
-    (zone-cycles/s, graph; zones handed to the fixup per step), and a stress
+    """Primitive recovery by solver: the workload torus stepped with each, FP64
+    and mixed (zone-cycles/s, graph; zones handed to the fixup per step; the
+    mixed path runs Noble-2D in double-float, the others in FP64), and a stress
     set of random states (sigma to 1e4, |u~| to 50, an unrelated guess)
     recovered by kh_cons_to_prim (states/s, failures)."""
     import numpy as np
@@ -442,32 +443,35 @@ def measure_inverters(args, cfg64, P0, dev, stream):
     far = inputs.random_prims(scfg, seed=22)
     far[5:] = Ps[5:]
     for inv in ("noble2d", "1dw", "kastaun"):
-        cfg = dict(cfg64, precision="fp64", inverter=inv)
-        ctx = kh.Context(cfg, device=dev)
-        PB = ctx.to_device(P0)
-        P, B = ctx.split(PB)
-        U = ctx.empty(8)
-        ctx.prim_to_cons(P, B, U)
-        dt = ctx.cfl_dt(P, B)
-        ctx.autotune(U, P, B, 0.5 * dt)
-        for _ in range(max(args.warmup, 3)):
+        r = {}
+        for prec in ("fp64", "mixed"):
+            cfg = dict(cfg64, precision=prec, inverter=inv)
+            ctx = kh.Context(cfg, device=dev)
+            PB = ctx.to_device(P0)
+            P, B = ctx.split(PB)
+            U = ctx.empty(8)
+            ctx.prim_to_cons(P, B, U)
+            dt = ctx.cfl_dt(P, B)
+            ctx.autotune(U, P, B, 0.5 * dt)
+            for _ in range(max(args.warmup, 3)):
+                dt, _ = ctx.step(U, P, B, 0.5 * dt)
+            ctx.set_graph(True)
             dt, _ = ctx.step(U, P, B, 0.5 * dt)
-        ctx.set_graph(True)
-        dt, _ = ctx.step(U, P, B, 0.5 * dt)
-        steps = max(min(args.steps, 5), 3)
-        nfail = 0
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize(dev)
-        e0.record(stream)
-        for _ in range(steps):
-            dt, nf = ctx.step(U, P, B, 0.5 * dt)
-            nfail += nf
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        ms = e0.elapsed_time(e1) / steps
-        ctx.close()
-        r = {"torus_graph": {"value": nz / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms},
-             "torus_fixup_zones_per_step": nfail / steps}
+            steps = max(min(args.steps, 5), 3)
+            nfail = 0
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            for _ in range(steps):
+                dt, nf = ctx.step(U, P, B, 0.5 * dt)
+                nfail += nf
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1) / steps
+            ctx.close()
+            sfx = "" if prec == "fp64" else "_mixed"
+            r["torus_graph" + sfx] = {"value": nz / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms}
+            r["torus_fixup_zones_per_step" + sfx] = nfail / steps
         # stress set: every cell of a 262x134x70 grid, recovered from an unrelated guess
         c2 = dict(scfg, inverter=inv)
         ctx = kh.Context(c2, device=dev)

@@ -108,10 +108,11 @@ typedef struct {
                              bracketed root of a master function of 1/(h gamma)).
                              All find the same root; newton_max_iter / newton_tol
                              apply to each (KASTAUN: up to 4x the iterations, tol
-                             on the bracket width). FP64 single-grid contexts
-                             (the mixed path, the refined mesh and the adjoint
-                             carry Noble-2D and refuse the others); used by the
-                             update and kh_cons_to_prim. */
+                             on the bracket width). Single-grid contexts, FP64 and
+                             KH_MIXED (there Noble-2D runs in double-float with an
+                             FP64 fallback, the others in FP64); the refined mesh
+                             and the adjoint carry Noble-2D and refuse the others;
+                             used by the update and kh_cons_to_prim. */
   int integrator;         /* time integrator ("Algorithm" section): KH_INT_VL2 (the
                              predictor-corrector, default), KH_INT_RK1, KH_INT_RK2
                              (Heun) or KH_INT_SSPRK54 (Spiteri & Ruuth's five-stage

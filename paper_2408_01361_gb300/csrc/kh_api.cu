@@ -254,7 +254,6 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
   if (c->precision != KH_FP64 && c->precision != KH_MIXED) return KH_EINVAL;
   if (c->fofc != 0 && c->fofc != 1) return KH_EINVAL;
   if (c->inverter < KH_INV_NOBLE2D || c->inverter > KH_INV_KASTAUN) return KH_EINVAL;
-  if (c->inverter != KH_INV_NOBLE2D && c->precision != KH_FP64) return KH_EINVAL;
   if (c->integrator < KH_INT_VL2 || c->integrator > KH_INT_SSPRK54) return KH_EINVAL;
   if (c->bfield != KH_B_FLUXCT && c->bfield != KH_B_FACE) return KH_EINVAL;
   if (c->emf != KH_EMF_AVERAGE && c->emf != KH_EMF_GS05) return KH_EINVAL;

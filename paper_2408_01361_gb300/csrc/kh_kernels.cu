@@ -267,6 +267,7 @@ __global__ void k_lincomb(double* out, LinComb lc, long long n) {
 
 // three blocks of TPB_MAX per SM: ~80 registers (a few spill to L1); measured faster
 // than the unconstrained 128 registers at 16 warps per SM
+template <int INV>
 __global__ void __launch_bounds__(TPB_MAX, 3) k_update_mixed(const double* U0, CVarsT<float> Pin, Vars Pout64,
                                                          VarsT<float> Pout32, double* Uout, const float* F1,
                                                          const float* F2, const float* F3, Layout L, DevGeom G,
@@ -277,8 +278,8 @@ __global__ void __launch_bounds__(TPB_MAX, 3) k_update_mixed(const double* U0, C
   if (t >= nzones(L)) return;
   int i, j, k;
   zone_ijk(L, t, i, j, k);
-  update_mixed_zone(U0, Pin, Pout64, Pout32, Uout, F1, F2, F3, L, G, Gf, S, df_of_f64(coef * __ldg(dtp)), pflag, cnt, i,
-                    j, k, fl, fBn, dUout, ect);
+  update_mixed_zone<false, INV>(U0, Pin, Pout64, Pout32, Uout, F1, F2, F3, L, G, Gf, S, df_of_f64(coef * __ldg(dtp)),
+                                pflag, cnt, i, j, k, fl, fBn, dUout, ect);
 }
 
 template <class T>
@@ -352,6 +353,7 @@ __global__ void __launch_bounds__(TPB_MAX) k_fofc_trial(const double* U0, CVars 
   update_zone<true, INV>(U0, Pin, Vars{}, nullptr, F1, F2, F3, L, G, S, coef * __ldg(dtp), flag, cnt, i, j, k);
 }
 
+template <int INV>
 __global__ void __launch_bounds__(TPB_MAX, 3) k_fofc_trial_mixed(const double* U0, CVarsT<float> Pin,
                                                                 const float* F1, const float* F2, const float* F3,
                                                                 Layout L, DevGeom G, GeomT<float> Gf, Scheme S,
@@ -361,7 +363,7 @@ __global__ void __launch_bounds__(TPB_MAX, 3) k_fofc_trial_mixed(const double* U
   if (t >= nzones(L)) return;
   int i, j, k;
   zone_ijk(L, t, i, j, k);
-  update_mixed_zone<true>(U0, Pin, Vars{}, VarsT<float>{}, nullptr, F1, F2, F3, L, G, Gf, S,
+  update_mixed_zone<true, INV>(U0, Pin, Vars{}, VarsT<float>{}, nullptr, F1, F2, F3, L, G, Gf, S,
                           df_of_f64(coef * __ldg(dtp)), flag, cnt, i, j, k, FailList{nullptr, nullptr}, nullptr,
                           nullptr, ect);
 }
@@ -766,8 +768,12 @@ int launch_fofc_trial_mixed(const double* U0, const CVarsT<float>& Pin, float* c
                             int8_t* flag, unsigned long long* cnt, int tpb, cudaStream_t s, float* const* emf) {
   const long long nz = (long long)L.n1 * L.n2 * L.n3;
   const CtEmf ect{{emf ? emf[0] : nullptr, emf ? emf[1] : nullptr, emf ? emf[2] : nullptr}};
-  k_fofc_trial_mixed<<<nblocks(nz, tpb), tpb, 0, s>>>(U0, Pin, F[0], F[1], F[2], L, G, Gf, S, dtp, coef, flag, cnt,
-                                                      ect);
+  auto go = [&](auto kern) {
+    kern<<<nblocks(nz, tpb), tpb, 0, s>>>(U0, Pin, F[0], F[1], F[2], L, G, Gf, S, dtp, coef, flag, cnt, ect);
+  };
+  if (S.c2p.method == C2P_KASTAUN) go(k_fofc_trial_mixed<C2P_KASTAUN>);
+  else if (S.c2p.method == C2P_1DW) go(k_fofc_trial_mixed<C2P_1DW>);
+  else go(k_fofc_trial_mixed<C2P_NOBLE2D>);
   return 1;
 }
 
@@ -840,8 +846,13 @@ int launch_update_mixed(const double* U0, const CVarsT<float>& Pin, const Vars& 
                         float* const* emf) {
   const long long nz = (long long)L.n1 * L.n2 * L.n3;
   const CtEmf ect{{emf ? emf[0] : nullptr, emf ? emf[1] : nullptr, emf ? emf[2] : nullptr}};
-  k_update_mixed<<<nblocks(nz, tpb), tpb, 0, s>>>(U0, Pin, Pout64, Pout32, Uout, F[0], F[1], F[2], L, G, Gf, S, dtp,
-                                                  coef, pflag, cnt, fl, fBn, dUout, ect);
+  auto go = [&](auto kern) {
+    kern<<<nblocks(nz, tpb), tpb, 0, s>>>(U0, Pin, Pout64, Pout32, Uout, F[0], F[1], F[2], L, G, Gf, S, dtp, coef,
+                                          pflag, cnt, fl, fBn, dUout, ect);
+  };
+  if (S.c2p.method == C2P_KASTAUN) go(k_update_mixed<C2P_KASTAUN>);
+  else if (S.c2p.method == C2P_1DW) go(k_update_mixed<C2P_1DW>);
+  else go(k_update_mixed<C2P_NOBLE2D>);
   return 1;
 }
 

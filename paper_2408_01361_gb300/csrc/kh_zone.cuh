@@ -431,8 +431,10 @@ struct CtEmf {
 // conserved update exact to FP64 as in the FP64 path), the FP64 primitives
 // written at stage 2 (one add of the pair each) and the FP64 fallback
 // inversion of the zones noble2d_df hands back. TRIAL: the first-order flux
-// correction's trial, as update_zone<true> (Uout must be null).
-template <bool TRIAL = false>
+// correction's trial, as update_zone<true> (Uout must be null). INV: the
+// solver; Noble-2D runs in double-float with the FP64 fallback, the others
+// invert every zone in FP64 (from the double-float U rounded to FP64).
+template <bool TRIAL = false, int INV = C2P_NOBLE2D>
 __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT<float>& Pin, const Vars& Pout64,
                                                   const VarsT<float>& Pout32, double* Uout, const float* F1,
                                                   const float* F2, const float* F3, const Layout& L, const DevGeom& G,
@@ -532,10 +534,11 @@ __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT
   Pn[V_B1] = Ud[V_B1] * md.ig;
   Pn[V_B2] = Ud[V_B2] * md.ig;
   Pn[V_B3] = Ud[V_B3] * md.ig;
-  int flag = noble2d_df(Ud, md, mx, W0, vsq0, Pn);
+  int flag = C2P_NEED_FP64;
+  if constexpr (INV == C2P_NOBLE2D) flag = noble2d_df(Ud, md, mx, W0, vsq0, Pn);
   if (flag == C2P_NEED_FP64) {
     // FP64 inversion of this zone from the stage input
-    if (!TRIAL) atomicAdd(cnt + CNT_FP64, 1ULL);
+    if (!TRIAL && INV == C2P_NOBLE2D) atomicAdd(cnt + CNT_FP64, 1ULL);
     double Uf[NV], Pd[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
@@ -543,7 +546,7 @@ __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT
       Pd[v] = f64_of_f32(Pin.v[v][c]);
     }
     const Met<double> m = load_met(G, L.gplane, LOC_CENT, p);
-    flag = noble2d(Uf, m, __ldg(G.flo + 2 * L.gplane + p), S.gam, S.igam, S.gfac, S.c2p, Pd);
+    flag = invert<INV>(Uf, m, __ldg(G.flo + 2 * L.gplane + p), S.gam, S.igam, S.gfac, S.c2p, Pd);
     if (flag == 0) {
 #pragma unroll
       for (int v = 0; v < 5; ++v) Pn[v] = df_of_f64(Pd[v]);

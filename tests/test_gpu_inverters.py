@@ -6,7 +6,8 @@ variables to the oracle's root within 1e-10, steps the torus to the oracle's
 step within 1e-10, and on a stress set (b^2/rho to ~1e4, Lorentz factors to
 ~50, a far initial guess) fails on no more zones than it should: Kastaun's
 bracketed scheme on none. Where states fail (the torus atmosphere) the
-solvers differ by design: Kastaun's keeps eps >= 0 at its root."""
+solvers differ by design: Kastaun's keeps eps >= 0 at its root. The mixed
+path runs each solver too (Noble-2D in double-float, the others in FP64)."""
 import numpy as np
 import pytest
 
@@ -137,3 +138,69 @@ def test_stress_set_failures(kh, orc):
         out[inv] = (nfail, ok)
     assert out["kastaun"][0] == 0, out
     assert all(v[1] for v in out.values()), out
+
+
+# ---- the mixed path with each solver (FP32 fluxes, FP64 inversion) ----
+
+@pytest.mark.parametrize("inverter", ["1dw", "kastaun"])
+@pytest.mark.parametrize("which", ["box", "bondi"])
+def test_mixed_step_with_solver_vs_oracle(kh, orc, inverter, which):
+    """Where no inversion fails the mixed step with each solver is the
+    oracle's step at the mixed path's FP32 flux level, and equals the mixed
+    Noble-2D step (whose root is double-float) to 1e-7."""
+    cfg, P, dirich = _step_case(which)
+    Uo = orc.prim_to_cons(cfg, P)
+    dt = 0.5 * orc.cfl_dt(cfg, P, dirich)
+    Uc, Pc, _, st_o = orc.step(cfg, Uo, P, dt, dirich)
+    outs = {}
+    for inv in ("noble2d", inverter):
+        c = dict(cfg, inverter=inv, precision="mixed")
+        ctx = kh.Context(c)
+        g = GpuRun(ctx, c, P, U=Uo, dirichlet=dirich)
+        _, nfail = ctx.step(g.U, g.P, g.B, dt)
+        assert nfail == 0
+        outs[inv] = g.host()
+    Ug, Pg = outs[inverter]
+    # the mixed path's FP32 flux level (momenta and velocities against the
+    # mass scale: Bondi's x2 components are ~0)
+    a, b = interior(cfg, Ug), interior(cfg, Uc)
+    pa, pb = interior(cfg, Pg), interior(cfg, Pc)
+    mass = np.abs(b[0]).sum()
+    nz = b[0].size
+    for v in range(8):
+        tol = 2e-3 if v in (2, 3, 4) else 1e-4
+        den = max(np.abs(b[v]).sum(), 1e-3 * mass)
+        assert np.abs(a[v] - b[v]).sum() / den < tol, ("U", v, np.abs(a[v] - b[v]).sum() / den)
+        pden = max(np.abs(pb[v]).sum(), 1e-2 * nz if v in (2, 3, 4) else 0.0)
+        if pden == 0:  # an unmagnetised flow: the field stays exactly 0
+            assert np.abs(pa[v]).max() == 0
+            continue
+        assert np.abs(pa[v] - pb[v]).sum() / pden < tol, ("P", v, np.abs(pa[v] - pb[v]).sum() / pden)
+    # the double-float Noble-2D root agrees with the FP64 roots to ~1e-8
+    # (velocities against the whole velocity scale: Bondi's u~2 is ~0)
+    a, b = interior(cfg, Pg), interior(cfg, outs["noble2d"][1])
+    vscale = np.abs(b[2:5]).sum() / 3
+    for v in range(8):
+        den = max(np.abs(b[v]).sum(), vscale if v in (2, 3, 4) else 0.0)
+        if den > 0:
+            assert np.abs(a[v] - b[v]).sum() / den < 1e-7, (v, np.abs(a[v] - b[v]).sum() / den)
+
+
+def test_mixed_torus_with_each_solver(kh, orc):
+    """The mixed torus steps with every solver: finite, failures a small
+    fraction of the zones, the bracketed scheme failing on no more zones than
+    the FP64 Newton scheme."""
+    cfg = inputs.torus_cfg(48, 32, 16, r_out=60.0)
+    P = inputs.torus_state(cfg, seed=2)
+    Uo = orc.prim_to_cons(cfg, P)
+    dt = 0.5 * orc.cfl_dt(cfg, P)
+    nf = {}
+    for inv in INVERTERS:
+        c = dict(cfg, inverter=inv, precision="mixed")
+        ctx = kh.Context(c)
+        g = GpuRun(ctx, c, P, U=Uo)
+        nf[inv] = sum(ctx.step(g.U, g.P, g.B, dt)[1] for _ in range(3))
+        Ug, Pg = g.host()
+        assert np.isfinite(Ug).all() and np.isfinite(Pg).all()
+        assert nf[inv] < 0.02 * 48 * 32 * 16 * 3, nf  # < 2% of the zones per step
+    assert nf["kastaun"] <= 1.05 * nf["1dw"], nf
