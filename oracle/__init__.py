@@ -134,6 +134,8 @@ def lib():
         L.or_point_jacobians.argtypes = [C.c_double, _dp, _dp, C.c_int, _dp, _dp]
         L.or_point_source.argtypes = [PP, C.c_double, C.c_double, _dp, _dp]
         L.or_recon.argtypes = [C.c_int, C.c_int, _dp, _dp, _dp]
+        L.or_point_floors.argtypes = [PP, C.c_double, C.c_double, _dp]
+        L.or_point_floors.restype = C.c_int
         L.or_count_ops.argtypes = [PP, C.c_double, C.c_double, _dp, _dp]
         L.or_fofc_flags.argtypes = [PP, _dp, _dp, C.c_double, _ip]
         L.or_step_face.argtypes = [PP, _dp, _dp, _dp, C.c_double, C.c_void_p, C.c_void_p, C.POINTER(C.c_long)]
@@ -343,6 +345,14 @@ def point_source(cfg, x1, x2, P):
     S = np.zeros(8)
     lib().or_point_source(C.byref(params(cfg)), float(x1), float(x2), np.ascontiguousarray(P, dtype=np.float64), S)
     return S
+
+
+def point_floors(cfg, x1, x2, P):
+    """Floors of one state at native (x1, x2): (floored P, bit mask 1 density or
+    energy floor, 2 u/rho ceiling, 4 Lorentz-factor ceiling)."""
+    P = np.array(P, dtype=np.float64, copy=True)
+    flag = lib().or_point_floors(C.byref(params(cfg)), float(x1), float(x2), P)
+    return P, flag
 
 
 def recon(kind: str, q):

@@ -1582,6 +1582,16 @@ void or_point_source(const or_params* c, double x1, double x2, const double* P, 
   source_terms<double>(P, G, cn, c->gam, S);
 }
 
+// Floors of one state at native (x1, x2) (the radius as the grid's floors
+// take it: r of the Kerr-Schild family, 1 in Minkowski). P: 8 primitives,
+// floored in place; returns the floor bit mask of apply_floors.
+int or_point_floors(const or_params* c, double x1, double x2, double* P) {
+  Geo G = geo_at(*c, x1, x2);
+  double r = 1.0, th = 0.0;
+  if (c->kind != MINKOWSKI) native_to_ks<double>(*c, x1, x2, r, th);
+  return apply_floors(*c, G, r, P);
+}
+
 // 1-D reconstruction of q[0..n-1]: lo[i], hi[i] = lower/upper face values of
 // cell i for 2 <= i < n-2 (others untouched).
 void or_recon(int recon, int n, const double* q, double* lo, double* hi) {
