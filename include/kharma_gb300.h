@@ -58,7 +58,16 @@ typedef struct {
   int kind;               /* KH_MINKOWSKI | KH_KS | KH_MKS | KH_FMKS */
   int n1, n2, n3;         /* interior zones; n3 == 1 => 2-D (x1, x2) problem */
   int recon;              /* KH_RECON_MC | KH_RECON_WENO5 */
-  int precision;          /* KH_FP64 (KH_MIXED reserved) */
+  int precision;          /* KH_FP64: every step of the path in FP64.
+                             KH_MIXED: reconstruction, face fluxes, signal speeds,
+                             Flux-CT EMFs and the connection sources in FP32 (FP32
+                             stencil copies of P and of the geometry); U stored in
+                             FP64 (U^n + the FP32 increment is an FP64 add); the
+                             Noble-2D inversion in double-float (two FP32 numbers,
+                             ~48 bits) with an FP64 fallback for zones it does not
+                             converge (or in FP64 for every zone: mixed_inversion),
+                             floors with FP32 decisions and double-float values;
+                             1D_W and Kastaun invert in FP64; divB in FP64. */
   int bc[6];              /* x1 in, x1 out, x2 in, x2 out, x3 in, x3 out: KH_BC_* */
   double x1min, x1max, x2min, x2max, x3min, x3max; /* native coordinate box */
   double hslope;          /* MKS / FMKS theta concentration h */
@@ -126,7 +135,16 @@ typedef struct {
                              the same weights; SSPRK(5,4)'s fifth stage takes stage
                              4's face increment as its output minus its base); 8 to
                              48 extra planes of scratch, plus 6 to 15 with face CT. */
+  int mixed_inversion;    /* KH_MIXED with KH_INV_NOBLE2D: KH_MIXINV_DF (default) runs the
+                             inversion in double-float with the FP64 fallback above;
+                             KH_MIXINV_FP64 keeps the whole inversion in FP64 for every
+                             zone: the conserved variables entering it are the FP64
+                             U^n + increment, the Noble-2D Newton iteration starts from
+                             the FP32 stage input, and the floors act in FP64 as on the
+                             FP64 path. Ignored by KH_FP64 contexts and the other
+                             solvers; the refined mesh refuses KH_MIXINV_FP64. */
 } kh_coords;
+enum { KH_MIXINV_DF = 0, KH_MIXINV_FP64 = 1 };
 
 /* Counters of the last kh_step (both stages summed). */
 typedef struct {
@@ -164,7 +182,9 @@ int kh_set_stream(kh_ctx* ctx, void* cuda_stream);
 int kh_set_dirichlet(kh_ctx* ctx, int face, const double* PB);
 
 /* U = sqrt(-g) (rho u^t, T^t_t + rho u^t, T^t_i, B^i) at every cell
- * (ghosts included), T^mu_nu the ideal-MHD stress-energy tensor. */
+ * (ghosts included), T^mu_nu the ideal-MHD stress-energy tensor of the
+ * "Extended GRMHD" section (the conserved variables of the "Algorithm"
+ * section's update). */
 int kh_prim_to_cons(kh_ctx* ctx, const double* P, const double* B, double* U);
 
 /* Primitive recovery at every cell (ghosts included) by the Noble et al.
@@ -194,8 +214,10 @@ int kh_step(kh_ctx* ctx, double* U, double* P, double* B, double dt, double* dt_
 int kh_cfl_dt(kh_ctx* ctx, const double* P, const double* B, double* dt_cfl);
 
 /* Corner divergence of sqrt(-g) B at corners whose adjacent cells are all
- * interior (the quantity Flux-CT conserves): *max_abs = max |divB|, *l1 =
- * mean |divB| over those corners (host pointers; synchronises). */
+ * interior (the quantity the "Algorithm" section's Flux-CT conserves, and
+ * the divergence the "Readiness and Testing" section monitors): *max_abs =
+ * max |divB|, *l1 = mean |divB| over those corners (host pointers;
+ * synchronises). */
 int kh_divb(kh_ctx* ctx, const double* B, double* max_abs, double* l1);
 
 /* Diagnostics: the fluxes kh_step uses, from (P, B) with ghosts filled by the
@@ -284,6 +306,20 @@ int kh_profile_read(const kh_ctx* ctx, double* ms, int64_t* count);
 /* Number of kernel launches issued by this context since creation. */
 int64_t kh_launch_count(const kh_ctx* ctx);
 
+/* Bounded device wait of the KH_MIXED face kernels: each CTA stages its
+ * tile in shared memory by one TMA tensor copy and polls the copy's mbarrier
+ * at most `polls` times (default KH_WAIT_POLLS; each poll may suspend the
+ * thread for a short hardware-defined interval). A CTA that gives up counts
+ * a timeout, keeps waiting (at most KH_WAIT_POLLS more polls) until its
+ * copy has landed, so that no copy outlives the CTA's shared memory, and
+ * leaves its faces unwritten; the next kh_get_stats (and kh_step with a
+ * dt_cfl pointer) returns KH_ETIMEOUT, and the step's result is not valid.
+ * polls = 0 gives up before the first poll (to exercise the path). The
+ * context stays usable: set the limit back and step again. Drops a captured
+ * graph. KH_EINVAL for a null context. */
+#define KH_WAIT_POLLS (1u << 22)
+int kh_set_wait_limit(kh_ctx* ctx, unsigned polls);
+
 /* ---------------------------------------------------------------------------
  * Adjoint of one step (FP64 contexts). Given the gradient of an objective
  * with respect to the outputs of kh_step(U, P, B, dt) -- gU (8 planes), gP
@@ -300,7 +336,7 @@ int64_t kh_launch_count(const kh_ctx* ctx);
  * kept until kh_destroy. KH_EINVAL for a mixed-precision context, a
  * context with the first-order flux correction on, or bad arguments.
  *
- * Reverse rules (NS pattern 3): limiter and max branches as taken by the
+ * Reverse rules: limiter and max branches as taken by the
  * forward (ties: the first argument), LLF with ctop differentiated through
  * its active speed, Flux-CT and the ghost fill transposed exactly, the
  * inversion by the implicit-function theorem (a 5x5 FP64 solve per zone),
@@ -418,9 +454,15 @@ int kh_mesh_destroy(kh_mesh* mesh);
  *   out:  device, 2 doubles: out[0] = max |divB|, out[1] = mean |divB| over the
  *         corners whose adjacent cells are all interior;
  *   cuda_stream: cudaStream_t to launch on (NULL = legacy default stream).
- * Asynchronous on the stream; returns KH_EINVAL for bad sizes, including a
- * grid with more than KH_DIVB_NOALLOC_MAX_ROWS rows of corners
- * ((n2 - 1) * max(n3 - 1, 1)), and KH_ECUDA if a launch fails.
+ * B, gdet and out must be memory of the CURRENT device (cudaGetDevice), and
+ * cuda_stream a stream of that device: the scratch address used is the
+ * current device's. Asynchronous on the stream; returns KH_EINVAL for bad
+ * sizes, including a grid with more than KH_DIVB_NOALLOC_MAX_ROWS rows of
+ * corners ((n2 - 1) * max(n3 - 1, 1)), or for an array that is not memory of
+ * the current device, and KH_ECUDA if a CUDA error was already pending on
+ * entry (left untouched for the caller) or a launch fails. The scratch
+ * address looked up for a device is kept for the life of the process; it
+ * does not survive a cudaDeviceReset of that device.
  * The first call on a device looks up the scratch array's device address
  * (cudaGetSymbolAddress, with that device current); make that first call
  * before any stream capture. Every call shares the one array and leaves its

@@ -182,7 +182,8 @@ int run_stage_mixed(kh_ctx* x, int st, const double* U0, const VarsT<TIN>& Pin, 
     mark(x, KH_T_FLUX1 + d - 1, st, 0);
     // the stage input's 8 FP32 planes are contiguous (pnf or pstarf); a grid
     // too small for the tile's tensor box takes the per-face kernel
-    int r = launch_flux_dir_tma(d, Pf.v[0], L, Gf, x->S, x->Ff[d - 1], x->ctopf[d - 1], x->counters, s);
+    int r = launch_flux_dir_tma(d, Pf.v[0], L, Gf, x->S, x->Ff[d - 1], x->ctopf[d - 1], x->counters,
+                                x->wait_limit, s);
     if (r < 0)
       r = launch_flux_dir<float, float>(d, cviewT(Pf), L, Gf, x->S, x->Ff[d - 1], x->ctopf[d - 1], x->tpb_flux, s);
     n += r;
@@ -258,6 +259,7 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
   if (c->bfield != KH_B_FLUXCT && c->bfield != KH_B_FACE) return KH_EINVAL;
   if (c->emf != KH_EMF_AVERAGE && c->emf != KH_EMF_GS05) return KH_EINVAL;
   if (c->bfield == KH_B_FACE && c->fofc) return KH_EINVAL;
+  if (c->mixed_inversion != KH_MIXINV_DF && c->mixed_inversion != KH_MIXINV_FP64) return KH_EINVAL;
   if (!(gamma > 1.0) || !(c->cfl > 0.0) || !(fabs(a) < 1.0)) return KH_EINVAL;
   if (!(c->x1max > c->x1min) || !(c->x2max > c->x2min) || !(c->x3max > c->x3min)) return KH_EINVAL;
   for (int q = 0; q < 6; ++q) {
@@ -296,6 +298,7 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
   }
   x->tpb_flux = 128;
   x->tpb_update = 128;
+  x->wait_limit = KH_WAIT_POLLS;
   L.dx[0] = (c->x1max - c->x1min) / c->n1;
   L.dx[1] = (c->x2max - c->x2min) / c->n2;
   L.dx[2] = (c->x3max - c->x3min) / c->n3;
@@ -329,6 +332,7 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
   S.c2p.max_iter = c->newton_max_iter > 0 ? c->newton_max_iter : 30;
   S.c2p.tol = c->newton_tol > 0.0 ? c->newton_tol : 1e-14;
   S.c2p.method = c->inverter;
+  S.mixed_fp64 = c->precision == KH_MIXED && c->inverter == KH_INV_NOBLE2D && c->mixed_inversion == KH_MIXINV_FP64;
   set_mixed(S);
 
   x->cp = CoordParams{c->kind, a, c->x1min, c->hslope, c->poly_xt, c->poly_alpha, c->mks_smooth};
@@ -978,6 +982,13 @@ int kh_divb(kh_ctx* x, const double* B, double* max_abs, double* l1) {
 }
 
 int64_t kh_launch_count(const kh_ctx* x) { return x ? (int64_t)x->launches : 0; }
+
+int kh_set_wait_limit(kh_ctx* x, unsigned polls) {
+  if (!x) return KH_EINVAL;
+  if (polls != x->wait_limit) drop_graph(x);  // a captured step holds the old limit
+  x->wait_limit = polls;
+  return KH_OK;
+}
 
 int kh_destroy(kh_ctx* x) {
   if (!x) return KH_EINVAL;

@@ -54,6 +54,7 @@ struct kh_ctx {
   kh_stats last;
   // launch configuration (threads per block of the stencil and update kernels)
   int tpb_flux, tpb_update;
+  unsigned wait_limit;  // polls of a face CTA's wait for its TMA tile (kh_set_wait_limit)
   // CUDA-graph replay of the step, keyed by the (U, P, B) pointers captured
   int graph_on;
   cudaStream_t cap_stream;

@@ -24,7 +24,7 @@ namespace {
 
 constexpr int NT = 256;    // threads = cells reconstructed per tile
 constexpr int CW = 32;     // cells per tile row along x1
-constexpr unsigned WAIT_LIMIT = 1u << 22;  // bounded mbarrier polling
+constexpr unsigned WAIT_LIMIT = KH_WAIT_POLLS;  // polls of the drain after a timed-out wait
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -115,7 +115,7 @@ template <int D> struct TileShape {
 template <int D, int RECON>
 __global__ void __launch_bounds__(NT) k_flux_tma(const __grid_constant__ CUtensorMap tm, Layout L, GeomT<float> G,
                                                  Scheme S, FaceBox box, float* F, float* ctop, int polar_lo,
-                                                 int polar_hi, unsigned long long* cnt) {
+                                                 int polar_hi, unsigned long long* cnt, unsigned wlim) {
   using Sh = TileShape<D>;
   __shared__ alignas(128) float tile[NV * Sh::BZ * Sh::BY * Sh::BX];
   __shared__ float sL[NV][NT], sR[NV][NT];
@@ -166,20 +166,21 @@ __global__ void __launch_bounds__(NT) k_flux_tma(const __grid_constant__ CUtenso
         "l"(reinterpret_cast<unsigned long long>(&tm)), "r"(c0), "r"(c1), "r"(c2), "r"(0), "r"(smem_u32(&bar))
         : "memory");
   }
-  // thread 0 waits (bounded) and tells the others; on a timeout it flags the
-  // error, lets the copy in flight land (again bounded) and the CTA leaves
+  // thread 0 waits (at most wlim polls) and tells the others. On a timeout
+  // it counts it, then keeps the CTA resident until the copy it issued has
+  // landed in this CTA's shared memory (the drain, bounded by the full
+  // limit; a drain that also runs out is counted apart), and the CTA leaves
+  // without writing its faces.
   __shared__ int ready;
   if (tid == 0) {
-    unsigned spins = 0;
-    bool ok = true;
-    while (!mbar_try_wait(&bar, 0))
-      if (++spins == WAIT_LIMIT) {
-        ok = false;
-        atomicAdd(cnt + CNT_TIMEOUT, 1ULL);
-        for (unsigned r = 0; r < WAIT_LIMIT && !mbar_try_wait(&bar, 0); ++r) {
-        }
-        break;
-      }
+    bool ok = false;
+    for (unsigned spins = 0; spins < wlim && !ok; ++spins) ok = mbar_try_wait(&bar, 0);
+    if (!ok) {
+      atomicAdd(cnt + CNT_TIMEOUT, 1ULL);
+      bool landed = false;
+      for (unsigned r = 0; r < WAIT_LIMIT && !landed; ++r) landed = mbar_try_wait(&bar, 0);
+      if (!landed) atomicAdd(cnt + CNT_DRAIN, 1ULL);
+    }
     ready = ok ? 1 : 0;
   }
   __syncthreads();
@@ -292,7 +293,7 @@ template <int D> bool encode(CUtensorMap* tm, const float* base, const Layout& L
 
 template <int D>
 int launch_d(const float* P8, const Layout& L, const GeomT<float>& G, const Scheme& S, float* F, float* ctop,
-             unsigned long long* cnt, cudaStream_t s) {
+             unsigned long long* cnt, unsigned wlim, cudaStream_t s) {
   alignas(64) CUtensorMap tm;
   if (!encode<D>(&tm, P8, L)) return -1;
   const FaceBox b = face_box(L, D);
@@ -306,19 +307,19 @@ int launch_d(const float* P8, const Layout& L, const GeomT<float>& G, const Sche
   else
     grid = dim3((L.e[0] + 1 + CW - 1) / CW, (L.n3 + 1 + Sh::FY - 1) / Sh::FY, L.n2 + 2);
   if (S.recon == KH_RECON_MC)
-    k_flux_tma<D, KH_RECON_MC><<<grid, NT, 0, s>>>(tm, L, G, S, b, F, ctop, plo, phi, cnt);
+    k_flux_tma<D, KH_RECON_MC><<<grid, NT, 0, s>>>(tm, L, G, S, b, F, ctop, plo, phi, cnt, wlim);
   else
-    k_flux_tma<D, KH_RECON_WENO5><<<grid, NT, 0, s>>>(tm, L, G, S, b, F, ctop, plo, phi, cnt);
+    k_flux_tma<D, KH_RECON_WENO5><<<grid, NT, 0, s>>>(tm, L, G, S, b, F, ctop, plo, phi, cnt, wlim);
   return 1;
 }
 
 }  // namespace
 
 int launch_flux_dir_tma(int D, const float* P8, const Layout& L, const GeomT<float>& G, const Scheme& S, float* F,
-                        float* ctop, unsigned long long* cnt, cudaStream_t s) {
-  if (D == 1) return launch_d<1>(P8, L, G, S, F, ctop, cnt, s);
-  if (D == 2) return launch_d<2>(P8, L, G, S, F, ctop, cnt, s);
-  return launch_d<3>(P8, L, G, S, F, ctop, cnt, s);
+                        float* ctop, unsigned long long* cnt, unsigned wlim, cudaStream_t s) {
+  if (D == 1) return launch_d<1>(P8, L, G, S, F, ctop, cnt, wlim, s);
+  if (D == 2) return launch_d<2>(P8, L, G, S, F, ctop, cnt, wlim, s);
+  return launch_d<3>(P8, L, G, S, F, ctop, cnt, wlim, s);
 }
 
 }  // namespace kh

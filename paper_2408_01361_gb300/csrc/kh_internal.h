@@ -63,7 +63,12 @@ struct Scheme {
   FloorParams fl;
   C2POpts c2p;
   MixedConsts mx;
+  int mixed_fp64;  // KH_MIXED, Noble-2D: every zone inverted in FP64 (kh_coords.mixed_inversion)
 };
+
+// Kernel template id of the mixed update's FP64 Noble-2D for every zone (not a
+// solver of its own: the FP64 noble2d, entered without the double-float try).
+constexpr int C2P_NOBLE2D_FP64 = 3;
 
 // Host: fill S.mx from the FP64 fields.
 inline void set_mixed(Scheme& S) { S.mx = mixed_consts(S.gam, S.fl); }
@@ -72,8 +77,10 @@ inline void set_mixed(Scheme& S) { S.mx = mixed_consts(S.gam, S.fl); }
 // CNT_FP64: zones of the mixed update whose inversion fell back to FP64;
 // CNT_LIST0/1: lengths of the failed-zone lists of stages 1 and 2
 // CNT_FOFC: zones flagged by the first-order flux correction's trials
+// CNT_TIMEOUT: CTAs whose bounded wait for their TMA tile gave up;
+// CNT_DRAIN: ... of those, CTAs whose copy had not landed after the drain wait
 enum { CNT_FAIL = 0, CNT_FLOOR = 1, CNT_UNFIXED = 2, CNT_TIMEOUT = 3, CNT_FP64 = 4, CNT_LIST0 = 5, CNT_LIST1 = 6,
-       CNT_FOFC = 7, NCNT = 8 };
+       CNT_FOFC = 7, CNT_DRAIN = 8, NCNT = 9 };
 
 // Cells (L.at index) whose inversion failed in one stage, appended by the
 // update (idx == nullptr: not recorded); the fixup then visits these only.
@@ -104,10 +111,11 @@ int launch_bc_fill(const CVarsT<TS>& src, const VarsT<TD>& dst, const Layout& L,
 // Reconstruction + LLF through x^D faces: stencil read in TIN, arithmetic and
 // outputs in R (FP64 path: double/double; mixed: double or float in, float out).
 // FP32 face fluxes from TMA-staged shared-memory tiles (kh_flux_tma.cu): P8
-// is the 8-plane FP32 stage input; returns -1 if the tensor map cannot be
-// encoded.
+// is the 8-plane FP32 stage input; wlim bounds the polls of a CTA's wait for
+// its tile (0: give up before the first poll); returns -1 if the tensor map
+// cannot be encoded.
 int launch_flux_dir_tma(int D, const float* P8, const Layout& L, const GeomT<float>& G, const Scheme& S, float* F,
-                        float* ctop, unsigned long long* cnt, cudaStream_t s);
+                        float* ctop, unsigned long long* cnt, unsigned wlim, cudaStream_t s);
 template <class TIN, class R>
 int launch_flux_dir(int D, const CVarsT<TIN>& P, const Layout& L, const GeomT<R>& G, const Scheme& S, R* F, R* ctop,
                     int tpb, cudaStream_t s);

@@ -773,6 +773,7 @@ int launch_fofc_trial_mixed(const double* U0, const CVarsT<float>& Pin, float* c
   };
   if (S.c2p.method == C2P_KASTAUN) go(k_fofc_trial_mixed<C2P_KASTAUN>);
   else if (S.c2p.method == C2P_1DW) go(k_fofc_trial_mixed<C2P_1DW>);
+  else if (S.mixed_fp64) go(k_fofc_trial_mixed<C2P_NOBLE2D_FP64>);
   else go(k_fofc_trial_mixed<C2P_NOBLE2D>);
   return 1;
 }
@@ -852,6 +853,7 @@ int launch_update_mixed(const double* U0, const CVarsT<float>& Pin, const Vars& 
   };
   if (S.c2p.method == C2P_KASTAUN) go(k_update_mixed<C2P_KASTAUN>);
   else if (S.c2p.method == C2P_1DW) go(k_update_mixed<C2P_1DW>);
+  else if (S.mixed_fp64) go(k_update_mixed<C2P_NOBLE2D_FP64>);
   else go(k_update_mixed<C2P_NOBLE2D>);
   return 1;
 }

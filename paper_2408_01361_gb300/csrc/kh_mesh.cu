@@ -628,6 +628,7 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
   if (c->fofc) return KH_EINVAL;  // the flux correction runs on single grids
   if (c->inverter != KH_INV_NOBLE2D) return KH_EINVAL;  // the mesh kernels carry Noble-2D
   if (c->integrator != KH_INT_VL2) return KH_EINVAL;    // the mesh steps with the predictor-corrector
+  if (c->mixed_inversion != KH_MIXINV_DF) return KH_EINVAL;  // the mesh's mixed update keeps double-float
   if (c->bfield != KH_B_FLUXCT && c->bfield != KH_B_FACE) return KH_EINVAL;
   if (c->emf != KH_EMF_AVERAGE && c->emf != KH_EMF_GS05) return KH_EINVAL;
   if (!(gamma > 1.0) || !(c->cfl > 0.0) || !(fabs(a) < 1.0)) return KH_EINVAL;

@@ -28,7 +28,8 @@ std::mutex g_scratch_lock;
 double* g_scratch[kMaxDevices] = {nullptr};
 
 // Device address of the scratch array on the current device (looked up on the
-// first call per device, with that device current).
+// first call per device, with that device current, and cached for the life of
+// the process: a cudaDeviceReset makes the cached address stale).
 int scratch_on_current_device(double** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return KH_ECUDA;
@@ -125,16 +126,33 @@ __global__ void __launch_bounds__(kRowThreads) k_divb_rows_final(const double* s
   }
 }
 
+// True when p is device memory of the device dev (or managed memory).
+bool on_device(const void* p, int dev) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // an unregistered host pointer: clear the lookup's error
+    return false;
+  }
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
+}
+
 }  // namespace
 
 extern "C" int kh_divb_noalloc(const double* B, const double* gdet, int n1, int n2, int n3, int n1s, int n2s,
                                double dx1, double dx2, double dx3, double* out, void* cuda_stream) {
   if (!B || !gdet || !out) return KH_EINVAL;
+  // an error left by an earlier, unrelated call is not this call's: report it
+  // without clearing it, so that the caller still sees the original error
+  if (cudaPeekAtLastError() != cudaSuccess) return KH_ECUDA;
   if (n1 < 2 || n2 < 2 || n3 < 1) return KH_EINVAL;
   if (n1s < n1 + 2 * kh::NGHOST || n2s < n2 + 2 * kh::NGHOST) return KH_EINVAL;
   if (!(dx1 > 0.0) || !(dx2 > 0.0) || (n3 > 1 && !(dx3 > 0.0))) return KH_EINVAL;
   const long long nrows = (long long)(n2 - 1) * (n3 > 1 ? (n3 - 1) : 1);
   if (nrows > KH_DIVB_NOALLOC_MAX_ROWS) return KH_EINVAL;  // larger than the static scratch
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return KH_ECUDA;
+  // the scratch address is the current device's: the arrays must live there
+  if (!on_device(B, dev) || !on_device(gdet, dev) || !on_device(out, dev)) return KH_EINVAL;
   double* scratch = nullptr;
   const int rc = scratch_on_current_device(&scratch);
   if (rc != KH_OK) return rc;

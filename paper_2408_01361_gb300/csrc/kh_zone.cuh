@@ -422,6 +422,68 @@ struct CtEmf {
   const float* e[3];
 };
 
+// The end of the mixed update when its inversion stays in FP64 for every
+// zone (kh_coords.mixed_inversion = KH_MIXINV_FP64, the precision split that
+// keeps the whole Noble-2D inversion in FP64): U holds the FP64 conserved
+// variables U^n + increment; the FP64 Noble-2D iteration starts from the
+// FP32 stage input; floors as on the FP64 path (FP64 decisions and values),
+// U recomputed in FP64 where one acted; outputs as update_mixed_zone's.
+template <bool TRIAL>
+__device__ __forceinline__ void update_mixed_fp64_tail(double* U, const CVarsT<float>& Pin, const Vars& Pout64,
+                                                       const VarsT<float>& Pout32, double* Uout, const Layout& L,
+                                                       const DevGeom& G, const Scheme& S, int8_t* pflag,
+                                                       unsigned long long* cnt, long long c, long long p,
+                                                       FailList fl) {
+  const Met<double> m = load_met(G, L.gplane, LOC_CENT, p);
+  double Pn[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Pn[v] = f64_of_f32(Pin.v[v][c]);
+  const double ig = __ldg(G.flo + 2 * L.gplane + p);  // 1 / sqrt(-g)
+  const int flag = invert<C2P_NOBLE2D>(U, m, ig, S.gam, S.igam, S.gfac, S.c2p, Pn);
+  if (TRIAL && flag) {
+    pflag[c] = 1;
+    atomicAdd(cnt + CNT_FOFC, 1ULL);
+    return;
+  }
+  Pn[V_B1] = U[V_B1] * ig;
+  Pn[V_B2] = U[V_B2] * ig;
+  Pn[V_B3] = U[V_B3] * ig;
+  int fmask = 0;
+  if (flag == 0) {
+    FState<double> sb;
+    fluid_state(Pn, m, sb);
+    fmask = apply_floors(S.fl, m, __ldg(G.flo + p), __ldg(G.flo + L.gplane + p), sb.bsq, Pn);
+    if (TRIAL) {
+      pflag[c] = fmask ? 1 : 0;
+      if (fmask) atomicAdd(cnt + CNT_FOFC, 1ULL);
+      return;
+    }
+    if (fmask && Uout) {
+      fluid_state(Pn, m, sb);
+      cons_only(Pn, sb, m, S.gam, U);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Uout[v * L.plane + c] = U[v];
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) Pn[v] = f64_of_f32(Pin.v[v][c]);  // provisional, replaced by the fixup
+  }
+  if (Pout32.v[0]) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Pout32.v[v][c] = f32_of_f64(Pn[v]);
+  }
+  if (Pout64.v[0]) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Pout64.v[v][c] = Pn[v];
+  }
+  pflag[c] = (int8_t)flag;
+  if (flag) {
+    atomicAdd(cnt + CNT_FAIL, 1ULL);
+    if (fl.idx) fl.idx[atomicAdd(fl.n, 1ULL)] = (unsigned)c;
+  }
+  if (fmask) atomicAdd(cnt + CNT_FLOOR, 1ULL);
+}
+
 // The mixed update of one zone, FP64 arithmetic only where the result is
 // FP64 storage. FP32: the stage input, the sources, the flux divergence, the
 // increment c dt (S - div F), the floors' decisions and b^2. Double-float
@@ -434,6 +496,8 @@ struct CtEmf {
 // correction's trial, as update_zone<true> (Uout must be null). INV: the
 // solver; Noble-2D runs in double-float with the FP64 fallback, the others
 // invert every zone in FP64 (from the double-float U rounded to FP64).
+// INV = C2P_NOBLE2D_FP64: the FP64 Noble-2D for every zone from the FP64
+// U^n + increment (update_mixed_fp64_tail).
 template <bool TRIAL = false, int INV = C2P_NOBLE2D>
 __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT<float>& Pin, const Vars& Pout64,
                                                   const VarsT<float>& Pout32, double* Uout, const float* F1,
@@ -449,6 +513,7 @@ __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT
   const MixedConsts& mx = S.mx;
   // the stored U (stage 2) is written here and touched again only by floors
   df64 Ud[NV];    // U^n + increment, double-float, for the inversion
+  double Ue[NV];  // ... in FP64 (C2P_NOBLE2D_FP64 only)
   float W0, vsq0; // initial guess of the inversion from the FP32 input
   {
     float Pf[NV];
@@ -517,7 +582,8 @@ __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT
       const double u0 = U0[o];
       if (Uout) Uout[o] = u0 + f64_of_f32(inc);    // the conserved update, FP64
       if (dUout) dUout[o] = f64_of_f32(inc);       // the raw increment (Runge-Kutta stages)
-      Ud[v] = df_of_f64(u0) + inc;
+      if constexpr (INV == C2P_NOBLE2D_FP64) Ue[v] = u0 + f64_of_f32(inc);
+      else Ud[v] = df_of_f64(u0) + inc;
     }
   }
   if (fBn) {  // face-centred CT: sqrt(-g) B from the updated faces (FP64 means)
@@ -526,8 +592,13 @@ __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       if (Uout) Uout[(V_B1 + q) * L.plane + c] = UB[q];
-      Ud[V_B1 + q] = df_of_f64(UB[q]);
+      if constexpr (INV == C2P_NOBLE2D_FP64) Ue[V_B1 + q] = UB[q];
+      else Ud[V_B1 + q] = df_of_f64(UB[q]);
     }
+  }
+  if constexpr (INV == C2P_NOBLE2D_FP64) {
+    update_mixed_fp64_tail<TRIAL>(Ue, Pin, Pout64, Pout32, Uout, L, G, S, pflag, cnt, c, p, fl);
+    return;
   }
   const MetDF md = load_metdf(Gf.df, L.gplane, p);
   df64 Pn[NV];

@@ -454,6 +454,10 @@ def torus_state(cfg: dict, seed: int = 2, noise: float = 4e-2, kappa: float = 1e
     r, th, th1, th2 = embed(cfg, X1, X2)
     rho, uint, inside = fm_density(cfg, r, th, kappa)
     ut_bl, uph = fm_velocity(cfg["a"], fm_angular_momentum(a, cfg["r_max"]), r, th)
+    # the torus velocity is defined inside the torus only (NaN e.g. inside the
+    # horizon); outside, the atmosphere is at rest: mask before transforming
+    ut_bl = np.where(inside, ut_bl, 1.0)
+    uph = np.where(inside, uph, 0.0)
     # BL -> KS with u^r = 0: u^t and u^phi are unchanged.
     u1, u2, u3 = utilde_from_ks(cfg, X1, X2, ut_bl, 0.0 * r, 0.0 * r, uph)
     rho_max = rho.max() if norms is None else norms[0]

@@ -29,6 +29,8 @@ BFIELD = {"fluxct": 0, "face": 1}
 EMF = {"average": 0, "gs05": 1}
 INVERTER = {"noble2d": 0, "1dw": 1, "kastaun": 2}
 INTEGRATOR = {"vl2": 0, "rk1": 1, "rk2": 2, "ssprk54": 3}
+MIXED_INVERSION = {"df": 0, "fp64": 1}
+WAIT_POLLS = 1 << 22  # KH_WAIT_POLLS
 ERRORS = {0: "KH_OK", -1: "KH_EINVAL", -2: "KH_ECUDA", -3: "KH_ENOMEM", -4: "KH_ETIMEOUT", -5: "KH_ENAN"}
 
 
@@ -47,6 +49,7 @@ class Coords(C.Structure):
         ("bsq_u_max", C.c_double), ("u_rho_max", C.c_double), ("gamma_max", C.c_double),
         ("newton_max_iter", C.c_int), ("newton_tol", C.c_double), ("fofc", C.c_int),
         ("bfield", C.c_int), ("emf", C.c_int), ("inverter", C.c_int), ("integrator", C.c_int),
+        ("mixed_inversion", C.c_int),
     ]
 
 
@@ -94,6 +97,7 @@ def lib():
         L.kh_get_launch.argtypes = [vp, ip, ip]
         L.kh_autotune.argtypes = [vp, vp, vp, vp, C.c_double, ip, ip]
         L.kh_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+        L.kh_set_wait_limit.argtypes = [vp, C.c_uint]
         L.kh_launch_count.argtypes = [vp]
         L.kh_launch_count.restype = C.c_int64
         L.kh_destroy.argtypes = [vp]
@@ -159,6 +163,7 @@ def coords_from_cfg(cfg: dict) -> Coords:
     c.emf = EMF[cfg.get("emf", "gs05")]
     c.inverter = INVERTER[cfg.get("inverter", "noble2d")]
     c.integrator = INTEGRATOR[cfg.get("integrator", "vl2")]
+    c.mixed_inversion = MIXED_INVERSION[cfg.get("mixed_inversion", "df")]
     return c
 
 
@@ -294,6 +299,15 @@ class Context:
 
     def set_graph(self, enable: bool):
         _check(lib().kh_set_graph(self._h, 1 if enable else 0), "kh_set_graph")
+
+    def set_wait_limit(self, polls: int = WAIT_POLLS):
+        """Polls of a mixed face CTA's wait for its TMA tile (kh_set_wait_limit)."""
+        _check(lib().kh_set_wait_limit(self._h, C.c_uint(int(polls))), "kh_set_wait_limit")
+
+    def step_rc(self, U, P, B, dt: float):
+        """kh_step with a dt_cfl pointer; returns the raw return code (no raise)."""
+        d = C.c_double()
+        return lib().kh_step(self._h, _ptr(U), _ptr(P), _ptr(B), float(dt), C.byref(d))
 
     def set_launch(self, tpb_flux: int, tpb_update: int):
         _check(lib().kh_set_launch(self._h, int(tpb_flux), int(tpb_update)), "kh_set_launch")

@@ -6,7 +6,7 @@ and the face field; the face divergence stays at rounding level."""
 import numpy as np
 import pytest
 
-from gpu_helpers import TOL, GpuRun, interior, rel_l1
+from gpu_helpers import GpuRun, TOL, assert_fp64_parity, interior
 from paper_2408_01361_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -85,9 +85,8 @@ CASES = ["box3d-gs05", "box3d-average", "box2d-gs05", "torus2d-gs05", "torus3d-g
 def test_face_ct_step_parity(kh, orc, which, nsteps):
     cfg, P, fB = _case(which)
     ctx, fBd, Ug, Pg, fg, Uc, Pc, fc, dtg, dto = _run(kh, orc, cfg, P, fB, nsteps)
-    eu = rel_l1(interior(cfg, Ug), interior(cfg, Uc))
-    ep = rel_l1(interior(cfg, Pg), interior(cfg, Pc))
-    assert eu.max() < TOL and ep.max() < TOL, (eu, ep)
+    assert_fp64_parity(interior(cfg, Ug), interior(cfg, Uc), "U")
+    assert_fp64_parity(interior(cfg, Pg), interior(cfg, Pc), "P")
     for a, (x, y) in enumerate(zip(_faces_interior(cfg, fg), _faces_interior(cfg, fc))):
         den = np.abs(y).sum()
         if den > 0:

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 from conftest import GOLDEN
-from gpu_helpers import TOL, GpuRun, interior, rel_l1
+from gpu_helpers import GpuRun, TOL, assert_fp64_parity, interior
 from paper_2408_01361_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -62,9 +62,8 @@ def test_integrator_step_parity(kh, orc, integ, which):
     cfg, P = _case(which)
     cfg = dict(cfg, integrator=integ)
     Ug, Pg, Uc, Pc, dtg, dto = _run(kh, orc, cfg, P, 3)
-    eu = rel_l1(interior(cfg, Ug), interior(cfg, Uc))
-    ep = rel_l1(interior(cfg, Pg), interior(cfg, Pc))
-    assert eu.max() < TOL and ep.max() < TOL, (eu, ep)
+    assert_fp64_parity(interior(cfg, Ug), interior(cfg, Uc), "U")
+    assert_fp64_parity(interior(cfg, Pg), interior(cfg, Pc), "P")
     assert abs(dtg - dto) <= 1e-10 * dto
 
 
@@ -136,9 +135,8 @@ def test_face_ct_integrator_parity(kh, orc, integ, which):
     cfg, P, fB = face_case(which)
     cfg = dict(cfg, integrator=integ)
     ctx, fBd, Ug, Pg, fg, Uc, Pc, fc, dtg, dto = face_run(kh, orc, cfg, P, fB, 2)
-    eu = rel_l1(interior(cfg, Ug), interior(cfg, Uc))
-    ep = rel_l1(interior(cfg, Pg), interior(cfg, Pc))
-    assert eu.max() < TOL and ep.max() < TOL, (eu, ep)
+    assert_fp64_parity(interior(cfg, Ug), interior(cfg, Uc), "U")
+    assert_fp64_parity(interior(cfg, Pg), interior(cfg, Pc), "P")
     for x, y in zip(_faces_interior(cfg, fg), _faces_interior(cfg, fc)):
         den = np.abs(y).sum()
         if den > 0:
@@ -158,9 +156,8 @@ def test_fofc_integrator_parity(kh, orc, integ, which):
     cfg, Ug, Pg, Uc, Pc, counts, dtg, dto = fofc_run(kh, orc, cfg, P, dirich, 2)
     for c in counts:
         assert c[0] == c[1] and c[0] > 0 and c[2] == c[3] and c[4] == c[5], counts
-    eu = rel_l1(interior(cfg, Ug), interior(cfg, Uc))
-    ep = rel_l1(interior(cfg, Pg), interior(cfg, Pc))
-    assert eu.max() < TOL and ep.max() < TOL, (eu, ep)
+    assert_fp64_parity(interior(cfg, Ug), interior(cfg, Uc), "U")
+    assert_fp64_parity(interior(cfg, Pg), interior(cfg, Pc), "P")
     assert abs(dtg - dto) <= 1e-10 * dto
 
 

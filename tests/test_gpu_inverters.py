@@ -11,7 +11,7 @@ path runs each solver too (Noble-2D in double-float, the others in FP64)."""
 import numpy as np
 import pytest
 
-from gpu_helpers import TOL, GpuRun, interior, rel_l1
+from gpu_helpers import GpuRun, assert_fp64_parity, interior
 from paper_2408_01361_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -53,8 +53,8 @@ def test_recovers_random_states(kh, orc, inverter, case):
     Po, _, nfail_o = orc.cons_to_prim(cfg, Uo, guess)
     nfail, Pg = _c2p(kh, cfg, P, Uo, guess)
     assert nfail == nfail_o == 0
-    assert rel_l1(Pg, Po).max() < TOL
-    assert rel_l1(Pg, P).max() < TOL
+    assert_fp64_parity(Pg, Po, "c2p vs oracle")
+    assert_fp64_parity(Pg, P, "c2p vs state")
 
 
 def _step_case(which):
@@ -88,9 +88,8 @@ def test_step_parity(kh, orc, inverter, which):
         dtg, nfail = ctx.step(g.U, g.P, g.B, dt)
         assert nfail == st_o[0] == 0
     Ug, Pg = g.host()
-    eu = rel_l1(interior(cfg, Ug), interior(cfg, Uc))
-    ep = rel_l1(interior(cfg, Pg), interior(cfg, Pc))
-    assert eu.max() < TOL and ep.max() < TOL, (eu, ep)
+    assert_fp64_parity(interior(cfg, Ug), interior(cfg, Uc), "U")
+    assert_fp64_parity(interior(cfg, Pg), interior(cfg, Pc), "P")
 
 
 def test_torus_failures_by_solver(kh, orc):

@@ -1,17 +1,68 @@
 """Mixed-precision path (FP32 reconstruction, fluxes, EMFs and sources; FP64
-accumulation of U, FP64 Noble-2D inversion and floors): its error against the
-FP64 oracle is measured and bounded here (the paper fixes no precision; the
-FP64 path is the parity path)."""
+storage and accumulation of U; Noble-2D inversion in double-float with an
+FP64 fallback, or in FP64 for every zone): its error against the FP64 oracle
+is measured and bounded here (the paper fixes no precision; the FP64 path is
+the parity path).
+
+The bounds are five times the errors measured on a GB300 when they were set
+(and never below 1e-9, the FP64 round-off floor of these norms): a regression
+of the mixed path by more than 5x anywhere fails, where the earlier blanket
+bounds (2e-3 momenta, 1e-4 the rest) let 10-200x regressions pass."""
 import os
 
 import numpy as np
 import pytest
 
 from conftest import GOLDEN
-from gpu_helpers import GpuRun, interior, rel_l1
+from gpu_helpers import GpuRun, elem_err, interior, rel_l1
 from paper_2408_01361_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
+
+# Measured errors (U slots rho u^t, energy, 3 momenta, 3 field; P slots rho,
+# u, u~1..3, B1..3): the test's norm of each case, one step.
+#   "mixl1": L1 over the variable's own L1, momenta against the mass scale
+#            1e-3 sum|U_rho| and velocities against 1e-2 per zone where those
+#            are larger (near-equilibrium tori have momenta ~0; FP32
+#            cancellation leaves an absolute residual there);
+#   "l1":    plain relative L1 per variable (gpu_helpers.rel_l1);
+#   "elem":  the element-wise error of gpu_helpers.elem_err.
+MEASURED = {
+    "torus48_mc": dict(
+        mixl1U=[3.6e-10, 1.0e-8, 1.9e-9, 1.4e-7, 1.7e-9, 2.9e-11, 9.6e-12, 1.3e-10],
+        mixl1P=[5.0e-10, 4.2e-8, 1.6e-6, 2.9e-8, 2.3e-6, 5.4e-10, 3.0e-10, 7.4e-7],
+        elemU=[2e-6, 4e-6, 2e-6, 1e-5, 1e-6, 2e-7, 3e-7, 2e-4],
+        elemP=[1e-6, 3e-6, 7e-3, 8e-3, 6e-3, 1e-6, 5e-7, 2e-4]),
+    "torus48_weno5": dict(
+        mixl1U=[3.8e-8, 1.0e-6, 3.4e-7, 2.0e-4, 3.6e-7, 3.6e-11, 1.2e-11, 1.4e-10],
+        mixl1P=[5.8e-10, 4.3e-8, 4.7e-5, 8.7e-7, 1.2e-4, 6.5e-10, 3.7e-10, 7.3e-7],
+        elemU=[5e-4, 4e-3, 9e-3, 2e-2, 1e-2, 3e-7, 4e-7, 7e-5],
+        elemP=[2e-6, 8e-6, 2e-1, 2e-1, 2e-1, 1e-6, 6e-7, 7e-5]),
+    "torus37_mc": dict(
+        l1U=[2.6e-9, 3.9e-8, 1.1e-8, 2.2e-5, 1.4e-8, 2.3e-10, 1.8e-10, 1.1e-6],
+        l1P=[3.5e-9, 3.7e-8, 1.1e-5, 2.3e-6, 1.1e-5, 4.5e-10, 3.0e-10, 8.5e-7],
+        elemU=[7e-5, 2e-4, 3e-5, 6e-4, 3e-5, 2e-7, 3e-7, 7e-4],
+        elemP=[9e-5, 7e-5, 2e-2, 1e-2, 2e-2, 1e-6, 6e-7, 1e-3]),
+    "torus37_weno5": dict(
+        l1U=[2.8e-9, 3.7e-8, 1.9e-8, 3.3e-7, 1.2e-8, 2.6e-10, 2.1e-10, 6.5e-7],
+        l1P=[4.5e-9, 4.2e-8, 9.5e-5, 1.5e-5, 8.8e-5, 5.8e-10, 3.8e-10, 9.8e-7],
+        elemU=[5e-5, 1e-4, 5e-4, 7e-4, 3e-4, 3e-7, 3e-7, 1e-3],
+        elemP=[6e-5, 5e-5, 5e-2, 3e-3, 3e-2, 1e-6, 6e-7, 2e-3]),
+    # the benchmark workload: 192x96x96 FMKS torus, WENO5
+    "torus192": dict(
+        l1U=[6.4e-10, 1.8e-8, 9.4e-10, 1.1e-5, 9.2e-10, 6.2e-10, 4.7e-10, 1.9e-6],
+        l1P=[1.1e-9, 9.0e-8, 8.1e-7, 2.9e-6, 3.7e-7, 1.1e-9, 7.4e-10, 2.2e-6],
+        elemU=[1e-7, 2e-7, 1e-7, 9e-3, 1e-7, 7e-7, 1e-6, 4e-4],
+        elemP=[2e-7, 5e-6, 1e-4, 1e-3, 8e-5, 3e-6, 1e-6, 4e-4]),
+}
+# Ragged and minimum Minkowski grids of random states (one step, MC): every
+# variable's relative L1 was 5e-9 - 4e-8 and its element-wise error at most
+# 4e-5 on all of them.
+RAGGED_L1, RAGGED_ELEM = 2e-7, 2e-4
+
+
+def _bound(x):
+    return np.maximum(5.0 * np.asarray(x), 1e-9)
 
 
 @pytest.fixture(scope="module")
@@ -20,43 +71,117 @@ def kh():
     return _kh
 
 
-def _torus(n1=48, n2=32, n3=16):
+def _torus(n1=48, n2=32, n3=16, recon="weno5", **over):
     cfg = inputs.torus_cfg(n1, n2, n3, r_out=60.0)
-    cfg["precision"] = "mixed"
+    cfg.update(precision="mixed", recon=recon, **over)
     return cfg, inputs.torus_state(cfg, seed=2)
 
 
-@pytest.mark.parametrize("recon", ["mc", "weno5"])
-def test_mixed_one_step_error_vs_oracle(kh, orc, recon):
-    cfg, P = _torus()
-    cfg["recon"] = recon
+def _one_step(kh, orc, cfg, P, dtf=0.5):
     Uo = orc.prim_to_cons(cfg, P)
-    dt = 0.5 * orc.cfl_dt(cfg, P)
+    dt = dtf * orc.cfl_dt(cfg, P)
     Uo2, Po2, dto, st = orc.step(cfg, Uo, P, dt)
     ctx = kh.Context(cfg)
     g = GpuRun(ctx, cfg, P, U=Uo)
     dtg, nfail = ctx.step(g.U, g.P, g.B, dt)
+    assert nfail == st[0], (nfail, st)
     Ug, Pg = g.host()
-    a, b = interior(cfg, Ug), interior(cfg, Uo2)
-    pa, pb = interior(cfg, Pg), interior(cfg, Po2)
-    # L1 error per variable over its own L1 norm, except for quantities that
-    # are near zero everywhere in an equilibrium torus (momenta, velocities,
-    # B3): those are measured against the mass scale sum|U_rho| (momenta) or
-    # 1e-2 per zone (velocities), since FP32 flux/source cancellation near
-    # equilibrium leaves an absolute residual, not a relative one.
-    # Momenta and velocities carry the FP32 rounding of the large pressure
-    # flux p sqrt(-g) against its geometric source near hydrostatic balance
-    # (an absolute residual ~1e-7 p sqrt(-g) dt/dx per step): bound 2e-3; the
-    # other variables 1e-4.
+    return (interior(cfg, Ug), interior(cfg, Uo2), interior(cfg, Pg), interior(cfg, Po2), dtg, dto)
+
+
+def _mixl1(a, b, pa, pb):
+    """The near-equilibrium norm of MEASURED's "mixl1"."""
     mass = np.abs(b[0]).sum()
     nz = b[0].size
+    eu, ep = [], []
     for v in range(8):
-        tol = 2e-3 if v in (2, 3, 4) else 1e-4
-        den = max(np.abs(b[v]).sum(), 1e-3 * mass)
-        assert np.abs(a[v] - b[v]).sum() / den < tol, ("U", v, np.abs(a[v] - b[v]).sum() / den)
+        eu.append(np.abs(a[v] - b[v]).sum() / max(np.abs(b[v]).sum(), 1e-3 * mass))
         pden = max(np.abs(pb[v]).sum(), 1e-2 * nz if v in (2, 3, 4) else 0.0)
-        assert np.abs(pa[v] - pb[v]).sum() / pden < tol, ("P", v, np.abs(pa[v] - pb[v]).sum() / pden)
-    assert abs(dtg - dto) < 1e-5 * dto
+        ep.append(np.abs(pa[v] - pb[v]).sum() / pden)
+    return np.array(eu), np.array(ep)
+
+
+def _check(name, got, key):
+    want = _bound(MEASURED[name][key])
+    assert np.all(got <= want), (name, key, got, want)
+
+
+@pytest.mark.parametrize("recon", ["mc", "weno5"])
+def test_mixed_one_step_error_vs_oracle(kh, orc, recon):
+    a, b, pa, pb, dtg, dto = _one_step(kh, orc, *_torus(recon=recon))
+    name = "torus48_" + recon
+    eu, ep = _mixl1(a, b, pa, pb)
+    _check(name, eu, "mixl1U")
+    _check(name, ep, "mixl1P")
+    _check(name, elem_err(a, b), "elemU")
+    _check(name, elem_err(pa, pb), "elemP")
+    assert abs(dtg - dto) < 2e-6 * dto
+
+
+@pytest.mark.parametrize("recon", ["mc", "weno5"])
+def test_mixed_ragged_torus(kh, orc, recon):
+    """A torus whose sizes are multiples of nothing (37 x 23 x 11): the TMA
+    tiles' 16-byte-aligned boxes start below the stencil and read zero-filled
+    cells past the array edge, which only feed faces outside the face box."""
+    a, b, pa, pb, dtg, dto = _one_step(kh, orc, *_torus(37, 23, 11, recon=recon))
+    name = "torus37_" + recon
+    _check(name, rel_l1(a, b), "l1U")
+    _check(name, rel_l1(pa, pb), "l1P")
+    _check(name, elem_err(a, b), "elemU")
+    _check(name, elem_err(pa, pb), "elemP")
+    assert abs(dtg - dto) < 2e-6 * dto
+
+
+@pytest.mark.parametrize("n", [(37, 23, 11), (4, 4, 4), (5, 7, 1), (33, 17, 9), (64, 40, 24)])
+def test_mixed_ragged_and_minimum_sizes(kh, orc, n):
+    """Rows not a multiple of the padding, odd sizes, the minimum 4^3 grid and
+    a 2-D grid on the mixed path (TMA tiles where the grid holds the tensor
+    box, the per-face kernel where it does not)."""
+    cfg = inputs.linear_mode_cfg(8, ndim=3)
+    cfg.update(n1=n[0], n2=n[1], n3=n[2], precision="mixed")
+    P = inputs.random_prims(cfg, seed=3, rho_range=(0.5, 1.0), u_range=(0.3, 1.0), ut_scale=(0.3, 0.3, 0.3),
+                            b_scale=(0.3, 0.3, 0.3))
+    P = orc.apply_bc(cfg, P)
+    a, b, pa, pb, dtg, dto = _one_step(kh, orc, cfg, P, dtf=0.3)
+    for name, e, tol in (("U l1", rel_l1(a, b), RAGGED_L1), ("P l1", rel_l1(pa, pb), RAGGED_L1),
+                         ("U elem", elem_err(a, b), RAGGED_ELEM), ("P elem", elem_err(pa, pb), RAGGED_ELEM)):
+        assert e.max() < tol, (n, name, e)
+    assert abs(dtg - dto) < 2e-6 * dto
+
+
+def test_mixed_full_size_torus_one_step(kh, orc):
+    """The benchmark workload (192x96x96 FMKS torus, WENO5) on the mixed path,
+    in the launch configuration the benchmark times: one step against the
+    oracle, every variable within 5x its measured error."""
+    cfg = inputs.torus_cfg(192, 96, 96)
+    cfg["precision"] = "mixed"
+    P = inputs.torus_state(cfg, seed=2)
+    a, b, pa, pb, dtg, dto = _one_step(kh, orc, cfg, P)
+    _check("torus192", rel_l1(a, b), "l1U")
+    _check("torus192", rel_l1(pa, pb), "l1P")
+    _check("torus192", elem_err(a, b), "elemU")
+    _check("torus192", elem_err(pa, pb), "elemP")
+    assert abs(dtg - dto) < 2e-6 * dto
+
+
+@pytest.mark.parametrize("recon", ["mc", "weno5"])
+def test_mixed_fp64_inversion(kh, orc, recon):
+    """mixed_inversion "fp64" (FP32 stencil, the whole Noble-2D inversion and
+    the floors in FP64): within the double-float variant's bounds of the
+    oracle (the FP32 fluxes set the error), the same failed zones, and its
+    state within 1e-4 (element-wise, elem_err) of the double-float variant's:
+    the two inversions agree far below the FP32 level, and what remains is
+    the FP32 floor decisions and the FP32 rounding of the stage-1 output."""
+    cfg, P = _torus(recon=recon, mixed_inversion="fp64")
+    a, b, pa, pb, dtg, dto = _one_step(kh, orc, cfg, P)
+    name = "torus48_" + recon
+    eu, ep = _mixl1(a, b, pa, pb)
+    _check(name, eu, "mixl1U")
+    _check(name, ep, "mixl1P")
+    cfg_df = dict(cfg, mixed_inversion="df")
+    a2, _, pa2, _, _, _ = _one_step(kh, orc, cfg_df, P)
+    assert elem_err(pa, pa2).max() < 1e-4, elem_err(pa, pa2)
+    assert elem_err(a, a2).max() < 1e-4, elem_err(a, a2)
 
 
 def test_mixed_linear_mode_converges(kh):

@@ -1,12 +1,14 @@
 """GPU parity: the FP64 CUDA path (through the C ABI) against the FP64 CPU
-oracle on the same seeded inputs. Bar: relative L1 per variable <= 1e-10."""
+oracle on the same seeded inputs. Bar: relative L1 per variable <= 1e-10,
+and every cell within 5e-8 of max(|oracle|, 1e-3 x the variable's largest
+magnitude) (gpu_helpers.assert_fp64_parity)."""
 import os
 
 import numpy as np
 import pytest
 
 from conftest import GOLDEN
-from gpu_helpers import TOL, GpuRun, interior, rel_l1
+from gpu_helpers import GpuRun, assert_fp64_parity, interior, rel_l1
 from paper_2408_01361_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -58,7 +60,7 @@ def test_cons_to_prim(kh, orc, case):
     nfail = ctx.cons_to_prim(g.U, g.P, g.B, pflag)
     _, Pg = g.host()
     assert nfail == nfail_o == 0
-    assert rel_l1(Pg, Po).max() < TOL
+    assert_fp64_parity(Pg, Po, "c2p")
     assert int(pflag.abs().sum()) == 0
 
 
@@ -88,7 +90,7 @@ def test_fluxes(kh, orc, which):
         mask = np.abs(Fo[d]).sum(axis=0) > 0
         a = Fg[:, mask]
         b = Fo[d][:, mask]
-        assert rel_l1(a, b).max() < TOL, (d, rel_l1(a, b))
+        assert_fp64_parity(a, b, ("flux", d))
 
 
 def _step_case(which):
@@ -124,9 +126,8 @@ def test_step_parity(kh, orc, which, nsteps):
         dtn_g, nfail = ctx.step(g.U, g.P, g.B, dt)
         assert nfail == st_o[0]
     Ug, Pg = g.host()
-    eu = rel_l1(interior(cfg, Ug), interior(cfg, Uc))
-    ep = rel_l1(interior(cfg, Pg), interior(cfg, Pc))
-    assert eu.max() < TOL and ep.max() < TOL, (eu, ep)
+    assert_fp64_parity(interior(cfg, Ug), interior(cfg, Uc), "U")
+    assert_fp64_parity(interior(cfg, Pg), interior(cfg, Pc), "P")
     assert abs(dtn_g - dtn_o) <= 1e-10 * dtn_o
 
 
@@ -188,7 +189,7 @@ def test_linear_mode_one_period_gpu(kh, orc):
         t += h
     assert abs(t - to) < 1e-12
     _, Pg = g.host()
-    assert rel_l1(interior(cfg, Pg), interior(cfg, Po2)).max() < TOL
+    assert_fp64_parity(interior(cfg, Pg), interior(cfg, Po2), "P")
     Pex = inputs.linear_mode_state(cfg, dP, om, t=T)
     sl = inputs.interior(cfg)
     eg = np.array([np.abs(Pg[v][sl] - Pex[v][sl]).mean() for v in range(8)])
@@ -209,9 +210,8 @@ def test_full_size_torus_one_step(kh, orc):
     dtg, nfail = ctx.step(g.U, g.P, g.B, dt)
     assert nfail == st[0]
     Ug, Pg = g.host()
-    eu = rel_l1(interior(cfg, Ug), interior(cfg, Uo2))
-    ep = rel_l1(interior(cfg, Pg), interior(cfg, Po2))
-    assert eu.max() < TOL and ep.max() < TOL, (eu, ep)
+    assert_fp64_parity(interior(cfg, Ug), interior(cfg, Uo2), "U")
+    assert_fp64_parity(interior(cfg, Pg), interior(cfg, Po2), "P")
     assert abs(dtg - dto) <= 1e-10 * dto
 
 
@@ -230,9 +230,8 @@ def test_full_size_bondi_10_steps(kh, orc):
         dtg2, nfail = ctx.step(g.U, g.P, g.B, dtg)
         dtg = dtg2
     Ug, Pg = g.host()
-    eu = rel_l1(interior(cfg, Ug), interior(cfg, Uc))
-    ep = rel_l1(interior(cfg, Pg), interior(cfg, Pc))
-    assert eu.max() < TOL and ep.max() < TOL, (eu, ep)
+    assert_fp64_parity(interior(cfg, Ug), interior(cfg, Uc), "U")
+    assert_fp64_parity(interior(cfg, Pg), interior(cfg, Pc), "P")
 
 
 def test_ragged_and_minimum_sizes(kh, orc):
@@ -252,8 +251,8 @@ def test_ragged_and_minimum_sizes(kh, orc):
         _, nfail = ctx.step(g.U, g.P, g.B, dt)
         assert nfail == st[0]
         Ug, Pg = g.host()
-        assert rel_l1(interior(cfg, Ug), interior(cfg, Uo2)).max() < TOL
-        assert rel_l1(interior(cfg, Pg), interior(cfg, Po2)).max() < TOL
+        assert_fp64_parity(interior(cfg, Ug), interior(cfg, Uo2), ("U", n1, n2, n3))
+        assert_fp64_parity(interior(cfg, Pg), interior(cfg, Po2), ("P", n1, n2, n3))
 
 
 def test_failed_inversion_fixup_parity(kh, orc):
@@ -275,8 +274,8 @@ def test_failed_inversion_fixup_parity(kh, orc):
     _, nfail = ctx.step(g.U, g.P, g.B, dt)
     assert nfail == st[0]
     Ug, Pg = g.host()
-    assert rel_l1(interior(cfg, Ug), interior(cfg, Uo2)).max() < TOL
-    assert rel_l1(interior(cfg, Pg), interior(cfg, Po2)).max() < TOL
+    assert_fp64_parity(interior(cfg, Ug), interior(cfg, Uo2), "U")
+    assert_fp64_parity(interior(cfg, Pg), interior(cfg, Po2), "P")
 
 
 def test_inversion_failure_codes_match(kh, orc):

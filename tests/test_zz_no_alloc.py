@@ -92,3 +92,38 @@ def test_noalloc_rejects_oversize_grid():
     with pytest.raises(kh.KHError, match="KH_EINVAL"):
         # (n2 - 1) * (n3 - 1) = 300 * 300 rows > KH_DIVB_NOALLOC_MAX_ROWS; rejected before any launch
         kh.divb_noalloc(t, t, 8, 301, 301, 16, 307, (1.0, 1.0, 1.0), t)
+
+
+def test_noalloc_accepts_the_largest_grid():
+    """(n2 - 1) (n3 - 1) = 256 x 256 = KH_DIVB_NOALLOC_MAX_ROWS rows: the last
+    scratch slot is used, and the result still equals kh_divb's."""
+    from paper_2408_01361_gb300 import kh
+
+    cfg = inputs.linear_mode_cfg(8, ndim=3)
+    cfg.update(n1=4, n2=257, n3=257)
+    P = inputs.random_prims(cfg, seed=23, b_scale=(1.0, 1.0, 1.0))
+    ctx = kh.Context(cfg)
+    PB = ctx.to_device(P)
+    _, B = ctx.split(PB)
+    ref_max, ref_l1 = ctx.divb(B)
+    gdet = _gdet(cfg, ctx)
+    out = ctx.torch.full((2,), -1.0, dtype=ctx.torch.float64, device=ctx.device)
+    dx = [(cfg[a][1] - cfg[a][0]) / cfg[n] for a, n in (("x1", "n1"), ("x2", "n2"), ("x3", "n3"))]
+    assert (cfg["n2"] - 1) * (cfg["n3"] - 1) == 65536
+    kh.divb_noalloc(B, gdet, cfg["n1"], cfg["n2"], cfg["n3"], ctx.n1s, ctx.n2s, dx, out)
+    ctx.torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    assert abs(got[0] - ref_max) <= TOL * ref_max and abs(got[1] - ref_l1) <= TOL * ref_l1, (got, ref_max, ref_l1)
+
+
+def test_noalloc_rejects_host_memory():
+    """The arrays must be memory of the current device (the scratch address is
+    that device's): a host array is refused before any launch."""
+    from paper_2408_01361_gb300 import kh
+
+    import torch
+
+    d = torch.zeros(16, dtype=torch.float64, device="cuda:0")
+    h = torch.zeros(4096, dtype=torch.float64)
+    with pytest.raises(kh.KHError, match="KH_EINVAL"):
+        kh.divb_noalloc(h, d, 4, 4, 1, 16, 10, (1.0, 1.0, 1.0), d)
