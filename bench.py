@@ -64,6 +64,8 @@ def parse():
     p.add_argument("--no-facect", action="store_true", help="skip the face-centred constrained transport leg")
     p.add_argument("--no-inverters", action="store_true", help="skip the primitive-recovery solver leg")
     p.add_argument("--no-workloads", action="store_true", help="skip the Orszag-Tang / explosion leg")
+    p.add_argument("--no-fp64-inversion", action="store_true",
+                   help="skip the mixed leg with the whole inversion in FP64")
     p.add_argument("--smr-only", action="store_true", help="run only the statically refined torus leg")
     p.add_argument("--precisions", default="mixed,fp64",
                    help="comma list; the first is the headline, the others are reported beside it")
@@ -194,7 +196,7 @@ def run_reference(args, world, rank):
 # ---------------------------------------------------------------------------
 # the CUDA arm
 # ---------------------------------------------------------------------------
-def measure(args, cfg, P0, ctx, dev, stream, dist, world, oracle_step):
+def measure(args, cfg, P0, ctx, dev, stream, dist, world, oracle_step, e2e=True):
     """Warm-up + K timed steps (+ e2e) of one context; returns a dict."""
     import torch
 
@@ -263,7 +265,7 @@ def measure(args, cfg, P0, ctx, dev, stream, dist, world, oracle_step):
     gms = g0.elapsed_time(g1)
     ctx.set_graph(False)
     out["graph"] = {"value": nz * args.steps * world / (gms * 1e-3), "ms_per_step": gms / args.steps}
-    if not args.no_e2e:
+    if e2e and not args.no_e2e:
         # the state crosses the host link in the library's compact interior
         # order (kh_pack_state / kh_unpack_state: no ghost cells, no padding)
         stage_d = torch.empty(16 * nz, dtype=torch.float64, device=dev)
@@ -759,6 +761,14 @@ def run_kh(args, world, rank, local):
         ctx = kh.Context(cfg, device=dev)
         results[prec] = measure(args, cfg, P0, ctx, dev, stream, dist, world, oracle_step)
         ctx.close()
+    fp64inv = None
+    if "mixed" in args.precisions and not args.no_fp64_inversion:
+        # the precision split that keeps the whole Noble-2D inversion (and the
+        # floors) in FP64 for every zone, beside the double-float headline
+        cfg = dict(cfg64, precision="mixed", mixed_inversion="fp64")
+        ctx = kh.Context(cfg, device=dev)
+        fp64inv = measure(args, cfg, P0, ctx, dev, stream, dist, world, oracle_step, e2e=False)
+        ctx.close()
 
     if rank != 0:
         if dist:
@@ -792,6 +802,17 @@ def run_kh(args, world, rank, local):
                       "gpu_launches": q["launches"], "clocks": q["clocks"], "nfail_timed": q["nfail"],
                       "launch_config": q["launch"], "graph_replay": q["graph"]}
         line[f"speedup_{head}_vs_{prec}"] = r["value"] / q["value"]
+    if fp64inv is not None:
+        q = fp64inv
+        rf, sh = roofline_of(q["prof"], nz, "mixed")
+        line["mixed_fp64_inversion"] = {
+            "what": "mixed path with the whole Noble-2D inversion and the floors in FP64 for every zone "
+                    "(FP32 stencil; FP64 U^n + increment; kh_coords.mixed_inversion = KH_MIXINV_FP64)",
+            "value": q["value"], "ms_per_step": q["ms"] / args.steps, "dtype": "f32+f64",
+            "err_vs_oracle": q["err"], "roofline": rf, "kernel_share": sh, "gpu_launches": q["launches"],
+            "clocks": q["clocks"], "nfail_timed": q["nfail"], "launch_config": q["launch"],
+            "graph_replay": q["graph"],
+            "headline_over_this": r["value"] / q["value"] if head == "mixed" else None}
     if not args.no_smr and world == 1:
         line["smr"] = {p: measure_smr(args, dev, stream, p) for p in args.precisions}
         line["smr_face_ct"] = {p: measure_smr(args, dev, stream, p, face=True) for p in args.precisions}
@@ -848,21 +869,79 @@ def fp32_peak_tflops(sm_mhz: float) -> float:
     return 152 * 256 * sm_mhz * 1e6 / 1e12
 
 
+def host_cores() -> dict:
+    """The host's core count and this process's affinity (the cores the
+    oracle's OpenMP threads may run on)."""
+    n = os.cpu_count() or 1
+    try:
+        aff = sorted(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        aff = list(range(n))
+    return {"nproc": n, "affinity_count": len(aff),
+            "affinity": f"{aff[0]}-{aff[-1]}" if aff == list(range(aff[0], aff[-1] + 1)) else ",".join(map(str, aff))}
+
+
+def _oracle_rate(oracle, cfg, P, U, dt, steps, dirichlet=None):
+    """Zone-cycles/s of `steps` oracle steps from (U, P) with a fixed dt."""
+    nz = cfg["n1"] * cfg["n2"] * cfg["n3"]
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        U, P, _, _ = oracle.step(cfg, U, P, dt, dirichlet)
+    el = time.perf_counter() - t0
+    return nz * steps / el, el, U, P
+
+
 def cpu_leg(cfg, P0, dt):
-    """The oracle as it stands on the host cores: one full step of the same
-    workload from the same state (the bounded sample is one step)."""
+    """The oracle as it stands on the host cores. The headline figure is one
+    full step of the workload torus on all the cores this process may use
+    (also the state the GPU's error is measured against); beside it, the
+    survey's six legs: the 32^3 linear mode (C1), the 128x128 Bondi flow (C2)
+    and the workload torus (C3), each single-threaded and on all cores (C3 on
+    all cores for 10 steps, single-threaded for one)."""
+    import numpy as np
+
     import oracle
+    from paper_2408_01361_gb300 import inputs
 
     oracle.build()
-    cores = os.cpu_count() or 1
-    oracle.set_threads(cores)
+    hc = host_cores()
+    allc = hc["affinity_count"]
+    oracle.set_threads(allc)
     U0 = oracle.prim_to_cons(cfg, P0)
     t0 = time.perf_counter()
     Uo, Po, dto, st = oracle.step(cfg, U0, P0, dt)
     el = time.perf_counter() - t0
     nz = cfg["n1"] * cfg["n2"] * cfg["n3"]
     cpu = {"value": nz / el, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
-           "sample": f"1 two-stage step of the full {cfg['n1']}x{cfg['n2']}x{cfg['n3']} torus ({el:.1f} s)"}
+           "sample": f"1 two-stage step of the full {cfg['n1']}x{cfg['n2']}x{cfg['n3']} torus ({el:.1f} s)",
+           "host": hc}
+    # the six legs
+    dP = np.zeros(8)
+    dP[0] = 1.0
+    c1 = inputs.linear_mode_cfg(32, ndim=3)
+    P1 = inputs.linear_mode_state(c1, dP, 1.0, amp=1e-4)
+    U1 = oracle.prim_to_cons(c1, P1)
+    dt1 = oracle.cfl_dt(c1, P1)
+    c2 = inputs.bondi_cfg(128, 128)
+    P2, d2 = inputs.bondi_state(c2, seed=1)
+    U2 = oracle.prim_to_cons(c2, P2)
+    dt2 = oracle.cfl_dt(c2, P2, d2)
+    legs = {}
+    for threads, label in ((1, "1 thread"), (allc, f"{allc} threads")):
+        oracle.set_threads(threads)
+        v1, e1, _, _ = _oracle_rate(oracle, c1, P1, U1, dt1, 20 if threads == 1 else 100)
+        v2, e2, _, _ = _oracle_rate(oracle, c2, P2, U2, dt2, 20 if threads == 1 else 100, d2)
+        n3 = 1 if threads == 1 else 10
+        v3, e3, _, _ = _oracle_rate(oracle, cfg, Po, Uo, dto, n3)
+        legs[label] = {
+            "threads": oracle.get_threads(),
+            "C1 linear mode 32^3": {"value": v1, "unit": UNIT, "seconds": e1},
+            "C2 Bondi 128x128": {"value": v2, "unit": UNIT, "seconds": e2},
+            f"C3 torus {cfg['n1']}x{cfg['n2']}x{cfg['n3']} ({n3} step{'s' if n3 > 1 else ''})":
+                {"value": v3, "unit": UNIT, "seconds": e3},
+        }
+    oracle.set_threads(allc)
+    cpu["legs"] = legs
     return {"U": Uo, "P": Po, "dt": dt}, cpu
 
 

@@ -154,6 +154,9 @@ typedef struct {
   double dt_cfl;    /* CFL time step for the next step */
   int64_t nfp64;    /* KH_MIXED: zones whose inversion fell back to the FP64 Newton iteration */
   int64_t nfofc;    /* zones flagged by the first-order flux correction's trials */
+  int64_t nbounds;  /* a library built with -DKH_BOUNDS_CHECK: work items whose cells fell
+                       outside the allocation and were skipped, since the context was
+                       created (0 in release builds, which have no checks) */
 } kh_stats;
 
 typedef struct kh_ctx kh_ctx;

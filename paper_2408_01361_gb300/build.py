@@ -16,6 +16,11 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libkharma_gb300.so")
+# the bounds-checked variant (-DKH_BOUNDS_CHECK): every instrumented kernel
+# checks its work item's cells against the allocation and counts and skips a
+# violation instead of touching memory out of bounds
+BUILD_BOUNDS = os.path.join(HERE, "_build_bounds")
+LIB_BOUNDS = os.path.join(HERE, "libkharma_gb300_bounds.so")
 SOURCES = ["kh_kernels.cu", "kh_api.cu", "kh_noalloc.cu", "kh_mesh.cu", "kh_adjoint.cu", "kh_flux_tma.cu"]
 HEADERS = ["kh_internal.h", "kh_physics.cuh", "kh_geom_math.h", "kh_zone.cuh", "kh_ctx.h", "kh_dual.cuh", "kh_df64.cuh",
            "kh_mixed.cuh", "kh_face_vjp.cuh", "kh_pair.cuh"]
@@ -29,25 +34,28 @@ def nvcc() -> str:
     return "nvcc"
 
 
-def _flags(verbose: bool):
+def _flags(verbose: bool, bounds: bool = False):
     f = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", CSRC, "-I", os.path.join(ROOT, "include")]
     f += ARCH
     if verbose:
         f += ["-Xptxas", "-v"]
+    if bounds:
+        f += ["-DKH_BOUNDS_CHECK"]
     return f
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, bounds: bool = False) -> str:
+    lib_path, build_dir = (LIB_BOUNDS, BUILD_BOUNDS) if bounds else (LIB, BUILD)
     deps = [os.path.join(CSRC, s) for s in SOURCES + HEADERS] + [os.path.join(ROOT, "include", "kharma_gb300.h")]
     newest = max(os.path.getmtime(p) for p in deps)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest and not verbose:
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
-    objs = [os.path.join(BUILD, s.replace(".cu", ".o")) for s in SOURCES]
+    if not force and os.path.exists(lib_path) and os.path.getmtime(lib_path) >= newest and not verbose:
+        return lib_path
+    os.makedirs(build_dir, exist_ok=True)
+    objs = [os.path.join(build_dir, s.replace(".cu", ".o")) for s in SOURCES]
 
     def compile_one(pair):
         src, obj = pair
-        cmd = [nvcc(), "-c", os.path.join(CSRC, src), "-o", obj] + _flags(verbose)
+        cmd = [nvcc(), "-c", os.path.join(CSRC, src), "-o", obj] + _flags(verbose, bounds)
         r = subprocess.run(cmd, capture_output=True, text=True)
         return cmd, r
 
@@ -59,15 +67,15 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if r.returncode != 0:
             sys.stderr.write(r.stdout + r.stderr)
             raise RuntimeError("nvcc failed: " + " ".join(cmd))
-    tmp = LIB + ".tmp"
+    tmp = lib_path + ".tmp"
     link = [nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-lcudart"]
     r = subprocess.run(link, capture_output=True, text=True)
     if r.returncode != 0:
         sys.stderr.write(r.stdout + r.stderr)
         raise RuntimeError("link failed: " + " ".join(link))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":
-    print(build(force=True, verbose="-v" in sys.argv))
+    print(build(force=True, verbose="-v" in sys.argv, bounds="--bounds" in sys.argv))

@@ -8,6 +8,8 @@
 #include <mutex>
 #include <tuple>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "kh_ctx.h"
 
 using namespace kh;
@@ -50,7 +52,17 @@ CVars cview(const Vars& v) {
   return c;
 }
 
+// NVTX range names of the kernel groups (visible to Nsight tools; a no-op
+// when no tool is attached).
+const char* const kGroupName[KH_NTIMERS] = {"kh ghost fill", "kh faces x1", "kh faces x2", "kh faces x3",
+                                            "kh flux-CT",    "kh update",   "kh fixup",    "kh CFL",
+                                            "kh flux correction"};
+
 void mark(kh_ctx* x, int group, int stage, int which) {
+  if (which == 0)
+    nvtxRangePushA(kGroupName[group]);
+  else
+    nvtxRangePop();
   if (!x->profiling) return;
   cudaEventRecord(x->ev[group][stage][which], x->stream);
   if (which == 1) x->ev_used[group][stage] = 1;
@@ -406,7 +418,7 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
   KH_ALLOC(x->flist, (size_t)L.n1 * L.n2 * L.n3 * sizeof(unsigned));
   KH_ALLOC(x->partial, 2 * (size_t)x->npartial * sizeof(double));
   KH_ALLOC(x->dscalar, 4 * sizeof(double));
-  KH_ALLOC(x->counters, NCNT * sizeof(unsigned long long));
+  KH_ALLOC(x->counters, (NCNT + 1) * sizeof(unsigned long long));  // + the bounds-check count
   for (int f = 0; f < 2; ++f)
     if (c->bc[f] == KH_BC_DIRICHLET) KH_ALLOC(x->dirichlet[f], (size_t)NV * L.n3s * L.n2s * L.ng * sizeof(double));
 #undef KH_ALLOC
@@ -421,6 +433,8 @@ int kh_geometry_init(double a, const kh_coords* c, double gamma, kh_ctx** out) {
       if (rc == KH_OK && x->emff[d]) rc = cuda_fail(cudaMemset(x->emff[d], 0, plf));
     }
     if (rc == KH_OK) rc = cuda_fail(cudaMemset(x->pstar, 0, NV * pl));
+    if (rc == KH_OK) rc = cuda_fail(cudaMemset(x->counters, 0, (NCNT + 1) * sizeof(unsigned long long)));
+    L.oob = x->counters + NCNT;
     if (rc == KH_OK && x->rkf) {
       const int nrkf = c->integrator == KH_INT_SSPRK54 ? 5 : 2;
       rc = cuda_fail(cudaMemset(x->rkf, 0, (size_t)nrkf * 3 * pl));
@@ -923,7 +937,7 @@ int kh_profile_read(const kh_ctx* x, double* ms, int64_t* count) {
 
 int kh_get_stats(kh_ctx* x, kh_stats* out) {
   if (!x || !out) return KH_EINVAL;
-  unsigned long long h[NCNT];
+  unsigned long long h[NCNT + 1];
   double dt;
   KH_TRY(cudaMemcpyAsync(h, x->counters, sizeof(h), cudaMemcpyDeviceToHost, x->stream));
   KH_TRY(cudaMemcpyAsync(&dt, x->dscalar, sizeof(double), cudaMemcpyDeviceToHost, x->stream));
@@ -933,6 +947,7 @@ int kh_get_stats(kh_ctx* x, kh_stats* out) {
   out->nunfixed = (int64_t)h[CNT_UNFIXED];
   out->nfp64 = (int64_t)h[CNT_FP64];
   out->nfofc = (int64_t)h[CNT_FOFC];
+  out->nbounds = (int64_t)h[NCNT];
   out->dt_cfl = dt;
   x->last = *out;
   return h[CNT_TIMEOUT] ? KH_ETIMEOUT : KH_OK;

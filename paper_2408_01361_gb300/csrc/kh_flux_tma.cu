@@ -234,6 +234,7 @@ __global__ void __launch_bounds__(NT) k_flux_tma(const __grid_constant__ CUtenso
   const bool in_box = i >= box.lo[0] && i < box.lo[0] + box.n[0] && j >= box.lo[1] && j < box.lo[1] + box.n[1] &&
                       k >= box.lo[2] && k < box.lo[2] + box.n[2];
   if (!in_box) return;
+  if (KH_OOB(L, kh_in(L, i, j, k, 0))) return;
   float PL[NV], PR[NV];
   const int slot = ly * CW + lx;
 #pragma unroll

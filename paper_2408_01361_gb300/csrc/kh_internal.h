@@ -27,8 +27,38 @@ struct Layout {
   double idx[3];      // 1 / dx
   float idxf[3];      // the same, FP32 (mixed update)
   int s[3], e[3];     // interior [s, e) per direction (i, j, k)
+  // bounds-checked builds (KH_BOUNDS_CHECK): counter of refused accesses
+  unsigned long long* oob = nullptr;
   KH_HD long long at(int k, int j, int i) const { return ((long long)k * n2s + j) * n1s + i; }
 };
+
+// Bounds-checked builds (-DKH_BOUNDS_CHECK; the variant the tests build
+// beside the release library, standing in for a memory checker): before a
+// kernel touches the cells of its work item it checks them against the
+// allocation; on a violation it counts it in *L.oob (kh_stats.nbounds) and
+// skips the item instead of reading or writing out of bounds. Release builds
+// compile the checks away (KH_OOB is false).
+#ifdef KH_BOUNDS_CHECK
+#define KH_OOB(L, ok) (!(ok) ? (((L).oob ? atomicAdd((L).oob, 1ULL) : 0ULL), true) : false)
+#else
+#define KH_OOB(L, ok) false
+#endif
+
+// The box [i - r, i + r] x [j - r, j + r] x [k - r, k + r] (k only in 3-D)
+// lies inside the allocation.
+KH_HD bool kh_in(const Layout& L, int i, int j, int k, int r) {
+  const int r3 = L.ndim == 3 ? r : 0;
+  return i - r >= 0 && i + r < L.n1s && j - r >= 0 && j + r < L.n2s && k - r3 >= 0 && k + r3 < L.n3s;
+}
+
+// The stencil [lo, hi] cells along x^D of cell (i, j, k) lies inside the
+// allocation.
+KH_HD bool kh_in_dir(const Layout& L, int D, int i, int j, int k, int lo, int hi) {
+  const int a[3] = {D == 1 ? lo : 0, D == 2 ? lo : 0, D == 3 ? lo : 0};
+  const int b[3] = {D == 1 ? hi : 0, D == 2 ? hi : 0, D == 3 ? hi : 0};
+  return i + a[0] >= 0 && i + b[0] < L.n1s && j + a[1] >= 0 && j + b[1] < L.n2s && k + a[2] >= 0 &&
+         k + b[2] < L.n3s;
+}
 
 // Pointers to the 8 primitive planes (5 fluid + 3 field) of one state.
 template <class T> struct VarsT {
@@ -79,6 +109,8 @@ inline void set_mixed(Scheme& S) { S.mx = mixed_consts(S.gam, S.fl); }
 // CNT_FOFC: zones flagged by the first-order flux correction's trials
 // CNT_TIMEOUT: CTAs whose bounded wait for their TMA tile gave up;
 // CNT_DRAIN: ... of those, CTAs whose copy had not landed after the drain wait
+// (the slot after the NCNT per-step counters holds the bounds-checked
+// build's count of refused accesses, kept for the context's life)
 enum { CNT_FAIL = 0, CNT_FLOOR = 1, CNT_UNFIXED = 2, CNT_TIMEOUT = 3, CNT_FP64 = 4, CNT_LIST0 = 5, CNT_LIST1 = 6,
        CNT_FOFC = 7, CNT_DRAIN = 8, NCNT = 9 };
 

@@ -155,6 +155,7 @@ __device__ __forceinline__ void bc_cell(const CVarsT<TS>& src, const VarsT<TD>& 
   const int ks = g.k, js = g.j, is = g.i, clamp = g.clamp;
   const bool flip = g.flip;
   const TS* D = g.dir == 1 ? dlo : (g.dir == 2 ? dhi : nullptr);
+  if (KH_OOB(L, kh_in(L, i, j, k, 0) && (D != nullptr || kh_in(L, is, js, ks, 0)))) return;
   const long long d = L.at(k, j, i), sc = D ? 0 : L.at(ks, js, is);
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
@@ -184,6 +185,7 @@ __global__ void k_fill_f32(CVarsT<double> src, VarsT<float> dst, Layout L, Schem
   if (t >= (unsigned)L.N1 * L.N2 * L.N3) return;
   int i, j, k;
   split3(t, L.N1, L.N2, i, j, k);
+  if (KH_OOB(L, kh_in(L, i, j, k, 0))) return;
   if (i >= L.s[0] && i < L.e[0] && j >= L.s[1] && j < L.e[1] && k >= L.s[2] && k < L.e[2]) {
     const long long c = L.at(k, j, i);
 #pragma unroll
@@ -206,6 +208,7 @@ __global__ void __launch_bounds__(TPB_MAX) k_flux(CVarsT<TIN> P, Layout L, GeomT
   if (t >= tot) return;
   int i, j, k;
   split3(t, box.n[0], box.n[1], i, j, k);
+  if (KH_OOB(L, kh_in_dir(L, D, i + box.lo[0], j + box.lo[1], k + box.lo[2], -3, 2))) return;
   flux_face<D, RECON, TIN, R>(P, L, G, S, i + box.lo[0], j + box.lo[1], k + box.lo[2], F, ctop, polar_lo, polar_hi);
 }
 
@@ -219,6 +222,10 @@ __global__ void k_emf(const R* F1, const R* F2, const R* F3, R* e1, R* e2, R* e3
   if (t >= (unsigned)n0 * n1 * n2) return;
   int i, j, k;
   split3(t, n0, n1, i, j, k);
+  {
+    const int ii = i + L.s[0], jj = j + L.s[1], kk = k + (L.ndim == 3 ? L.s[2] : 0);
+    if (KH_OOB(L, kh_in(L, ii, jj, kk, 0) && kh_in(L, ii - 1, jj - 1, L.ndim == 3 ? kk - 1 : kk, 0))) return;
+  }
   emf_at<R>(F1, F2, F3, e1, e2, e3, L, i + L.s[0], j + L.s[1], k + (L.ndim == 3 ? L.s[2] : 0));
 }
 
@@ -247,6 +254,7 @@ __global__ void __launch_bounds__(TPB_MAX) k_update(const double* U0, CVars Pin,
   if (t >= nzones(L)) return;
   int i, j, k;
   zone_ijk(L, t, i, j, k);
+  if (KH_OOB(L, kh_in(L, i, j, k, 1))) return;
   update_zone<false, INV>(U0, Pin, Pout, Uout, F1, F2, F3, L, G, S, coef * __ldg(dtp), pflag, cnt, i, j, k, nullptr,
                           fl, fBn, dUout);
 }
@@ -274,10 +282,9 @@ __global__ void __launch_bounds__(TPB_MAX, 3) k_update_mixed(const double* U0, C
                                                          GeomT<float> Gf, Scheme S, const double* dtp, double coef,
                                                          int8_t* pflag, unsigned long long* cnt, FailList fl,
                                                          const double* fBn, double* dUout, CtEmf ect) {
-  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nzones(L)) return;
   int i, j, k;
-  zone_ijk(L, t, i, j, k);
+  if (!tile_zone(L, i, j, k)) return;
+  if (KH_OOB(L, kh_in(L, i, j, k, 1))) return;
   update_mixed_zone<false, INV>(U0, Pin, Pout64, Pout32, Uout, F1, F2, F3, L, G, Gf, S, df_of_f64(coef * __ldg(dtp)),
                                 pflag, cnt, i, j, k, fl, fBn, dUout, ect);
 }
@@ -289,6 +296,7 @@ __global__ void __launch_bounds__(TPB) k_fixup(VarsT<T> P, double* Uout, const i
   if (t >= nzones(L)) return;
   int i, j, k;
   zone_ijk(L, t, i, j, k);
+  if (KH_OOB(L, kh_in(L, i, j, k, 1))) return;
   fixup_zone<T>(P, Uout, pflag, L, G, S, cnt, i, j, k);
 }
 
@@ -309,6 +317,12 @@ __global__ void __launch_bounds__(TPB) k_fixup_list(VarsT<T> P, double* Uout, co
   for (unsigned long long q = warp; q < n; q += nwarps) {
     const long long c = fl.idx[q];
     const int k = (int)(c / gs), j = (int)((c % gs) / L.n1s), i = (int)(c % L.n1s);
+#ifdef KH_BOUNDS_CHECK
+    if (!kh_in(L, i, j, k, 1)) {  // c is the warp's: the whole warp skips it, lane 0 counts it
+      if (lane == 0 && L.oob) atomicAdd(L.oob, 1ULL);
+      continue;
+    }
+#endif
     double s[5] = {0, 0, 0, 0, 0};
     int good = 0;
     if (lane < nnb) {
@@ -558,6 +572,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_cfl(const T* c1, const T* c2, c
   for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < nz; t += gridDim.x * blockDim.x) {
     int i, j, k;
     zone_ijk(L, t, i, j, k);
+    if (KH_OOB(L, kh_in(L, i, j, k, 1))) continue;
     const T v = cfl_inv_zone(c1, c2, c3, L, i, j, k);
     m = v > m ? v : m;
   }
@@ -845,11 +860,10 @@ int launch_update_mixed(const double* U0, const CVarsT<float>& Pin, const Vars& 
                         const Scheme& S, const double* dtp, double coef, int8_t* pflag, unsigned long long* cnt,
                         int tpb, cudaStream_t s, FailList fl, const double* fBn, double* dUout,
                         float* const* emf) {
-  const long long nz = (long long)L.n1 * L.n2 * L.n3;
   const CtEmf ect{{emf ? emf[0] : nullptr, emf ? emf[1] : nullptr, emf ? emf[2] : nullptr}};
   auto go = [&](auto kern) {
-    kern<<<nblocks(nz, tpb), tpb, 0, s>>>(U0, Pin, Pout64, Pout32, Uout, F[0], F[1], F[2], L, G, Gf, S, dtp, coef,
-                                          pflag, cnt, fl, fBn, dUout, ect);
+    kern<<<(unsigned)tile_blocks(L, tpb), tpb, 0, s>>>(U0, Pin, Pout64, Pout32, Uout, F[0], F[1], F[2], L, G, Gf, S,
+                                                       dtp, coef, pflag, cnt, fl, fBn, dUout, ect);
   };
   if (S.c2p.method == C2P_KASTAUN) go(k_update_mixed<C2P_KASTAUN>);
   else if (S.c2p.method == C2P_1DW) go(k_update_mixed<C2P_1DW>);

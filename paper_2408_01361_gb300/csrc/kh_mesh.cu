@@ -1333,6 +1333,7 @@ int kh_mesh_get_stats(kh_mesh* x, kh_stats* out) {
   out->nunfixed = (int64_t)h[CNT_UNFIXED];
   out->nfp64 = (int64_t)h[CNT_FP64];
   out->nfofc = 0;
+  out->nbounds = 0;
   out->dt_cfl = dt;
   return KH_OK;
 }

@@ -88,6 +88,38 @@ __device__ __forceinline__ unsigned nzones(const Layout& L) {
   return (unsigned)(L.e[0] - L.s[0]) * (L.e[1] - L.s[1]) * (L.e[2] - L.s[2]);
 }
 
+// Tiled zone order of the per-zone kernels that read the axisymmetric
+// geometry: a block covers one warp-wide run of 32 zones along x1 on each of
+// blockDim.x / 32 consecutive planes of the outermost direction (x3 in 3-D,
+// x2 in 2-D). Its warps then read the same geometry columns (the first warp
+// brings them into L1 for the others) and each other's x3 (x2) face and edge
+// neighbours. Returns false for threads past the interior (ragged tiles).
+__device__ __forceinline__ bool tile_zone(const Layout& L, int& i, int& j, int& k) {
+  const int nw = (int)(blockDim.x >> 5);
+  const int ni = (L.e[0] - L.s[0] + 31) >> 5;
+  unsigned b = blockIdx.x;
+  const int it = (int)(b % (unsigned)ni);
+  b /= (unsigned)ni;
+  const int w = (int)(threadIdx.x >> 5);
+  i = L.s[0] + (it << 5) + (int)(threadIdx.x & 31u);
+  if (L.ndim == 3) {
+    const int nj = L.e[1] - L.s[1];
+    j = L.s[1] + (int)(b % (unsigned)nj);
+    k = L.s[2] + (int)(b / (unsigned)nj) * nw + w;
+  } else {
+    j = L.s[1] + (int)b * nw + w;
+    k = L.s[2];
+  }
+  return i < L.e[0] && j < L.e[1] && k < L.e[2];
+}
+
+// Blocks of tile_zone's order over the interior for tpb threads per block.
+KH_HD long long tile_blocks(const Layout& L, int tpb) {
+  const long long nw = tpb / 32, ni = (L.e[0] - L.s[0] + 31) / 32;
+  if (L.ndim == 3) return ni * (L.e[1] - L.s[1]) * ((L.e[2] - L.s[2] + nw - 1) / nw);
+  return ni * ((L.e[1] - L.s[1] + nw - 1) / nw);
+}
+
 // Reconstruction + LLF flux through the lower x^D face of cell (k, j, i).
 // FP32 (mixed path): the left and right states as packed pairs.
 template <int D, int RECON>

@@ -18,7 +18,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_LIB = os.path.join(_HERE, "libkharma_gb300.so")
+# KH_LIBRARY selects another in-tree build of the library (the bounds-checked
+# variant libkharma_gb300_bounds.so that build.build(bounds=True) makes)
+_LIB = os.environ.get("KH_LIBRARY") or os.path.join(_HERE, "libkharma_gb300.so")
 
 MINKOWSKI, KS, MKS, FMKS = 0, 1, 2, 3
 KIND = {"minkowski": MINKOWSKI, "ks": KS, "mks": MKS, "fmks": FMKS}
@@ -55,7 +57,7 @@ class Coords(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("nfail", C.c_int64), ("nfloor", C.c_int64), ("nunfixed", C.c_int64), ("dt_cfl", C.c_double),
-                ("nfp64", C.c_int64), ("nfofc", C.c_int64)]
+                ("nfp64", C.c_int64), ("nfofc", C.c_int64), ("nbounds", C.c_int64)]
 
 
 class Block(C.Structure):
