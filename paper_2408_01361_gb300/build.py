@@ -21,9 +21,10 @@ LIB = os.path.join(HERE, "libkharma_gb300.so")
 # violation instead of touching memory out of bounds
 BUILD_BOUNDS = os.path.join(HERE, "_build_bounds")
 LIB_BOUNDS = os.path.join(HERE, "libkharma_gb300_bounds.so")
-SOURCES = ["kh_kernels.cu", "kh_api.cu", "kh_noalloc.cu", "kh_mesh.cu", "kh_adjoint.cu", "kh_flux_tma.cu"]
+SOURCES = ["kh_kernels.cu", "kh_api.cu", "kh_noalloc.cu", "kh_mesh.cu", "kh_adjoint.cu", "kh_flux_tma.cu",
+           "kh_update_tma.cu"]
 HEADERS = ["kh_internal.h", "kh_physics.cuh", "kh_geom_math.h", "kh_zone.cuh", "kh_ctx.h", "kh_dual.cuh", "kh_df64.cuh",
-           "kh_mixed.cuh", "kh_face_vjp.cuh", "kh_pair.cuh"]
+           "kh_mixed.cuh", "kh_face_vjp.cuh", "kh_pair.cuh", "kh_tma.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

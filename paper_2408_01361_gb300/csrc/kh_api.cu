@@ -231,8 +231,16 @@ int run_stage_mixed(kh_ctx* x, int st, const double* U0, const VarsT<TIN>& Pin, 
   }
   mark(x, KH_T_UPDATE, st, 0);
   const FailList fl{x->flist, x->counters + CNT_LIST0 + st};
-  n += launch_update_mixed(U0, cviewT(Pf), Pout64, Pout32, Uout, x->Ff, L, G, Gf, x->S, x->dscalar + 3, coef,
-                           x->pflag, x->counters, x->tpb_update, s, fl, fBn, dUout, fct ? x->emff : nullptr);
+  // 3-D Flux-CT stages stage their inputs by TMA; otherwise (2-D, face CT,
+  // or no tensor map) the update reads them itself
+  int ru = -1;
+  if (fct && L.ndim == 3)
+    ru = launch_update_mixed_tma(U0, Pf.v[0], Pout64, Pout32, Uout, x->Ff, x->emff, L, G, Gf, x->S, x->dscalar + 3,
+                                 coef, x->pflag, x->counters, fl, dUout, x->wait_limit, s);
+  if (ru < 0)
+    ru = launch_update_mixed(U0, cviewT(Pf), Pout64, Pout32, Uout, x->Ff, L, G, Gf, x->S, x->dscalar + 3, coef,
+                             x->pflag, x->counters, x->tpb_update, s, fl, fBn, dUout, fct ? x->emff : nullptr);
+  n += ru;
   mark(x, KH_T_UPDATE, st, 1);
   mark(x, KH_T_FIXUP, st, 0);
   if (Pout64.v[0])

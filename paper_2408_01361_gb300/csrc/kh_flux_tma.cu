@@ -13,30 +13,38 @@
 // Tiles are aligned so that the innermost tensor coordinate is a multiple of
 // 4 floats (16 bytes); reads past the array edge are zero-filled by the copy
 // and only feed faces outside the face box, which are skipped.
-#include <cuda.h>
-#include <cudaTypedefs.h>
-
 #include "kh_pair.cuh"
+#include "kh_tma.cuh"
 #include "kh_zone.cuh"
 
 namespace kh {
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+bool encode_tiled(CUtensorMap* tm, CUtensorMapDataType type, int rank, const void* base, const cuuint64_t* dims,
+                  const cuuint64_t* strides, const cuuint32_t* box) {
+  auto fn = tensor_map_encoder();
+  if (!fn) return false;
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  return fn(tm, type, (cuuint32_t)rank, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 namespace {
 
 constexpr int NT = 256;    // threads = cells reconstructed per tile
 constexpr int CW = 32;     // cells per tile row along x1
-constexpr unsigned WAIT_LIMIT = KH_WAIT_POLLS;  // polls of the drain after a timed-out wait
-
-__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned phase) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(phase)
-      : "memory");
-  return ok != 0;
-}
 
 // Both face values of one cell from its 5-point stencil (a, b, c, d, e):
 // hi at x = +1/2 (as weno5_plus(a, b, c, d, e)), lo at x = -1/2 (as
@@ -150,43 +158,15 @@ __global__ void __launch_bounds__(NT) k_flux_tma(const __grid_constant__ CUtenso
     k = k0 + ly;
     c0 = x0, c1 = j, c2 = k0 - 3;
   }
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)));
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  }
+  if (tid == 0) mbar_init(&bar);
   __syncthreads();
   if (tid == 0) {
-    constexpr unsigned bytes = sizeof(float) * NV * Sh::BZ * Sh::BY * Sh::BX;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bar)), "r"(bytes)
-                 : "memory");
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
-        "[%6];" ::"r"(smem_u32(tile)),
-        "l"(reinterpret_cast<unsigned long long>(&tm)), "r"(c0), "r"(c1), "r"(c2), "r"(0), "r"(smem_u32(&bar))
-        : "memory");
+    mbar_expect_tx(&bar, sizeof(float) * NV * Sh::BZ * Sh::BY * Sh::BX);
+    tma_load_4d(tile, &tm, c0, c1, c2, 0, &bar);
   }
-  // thread 0 waits (at most wlim polls) and tells the others. On a timeout
-  // it counts it, then keeps the CTA resident until the copy it issued has
-  // landed in this CTA's shared memory (the drain, bounded by the full
-  // limit; a drain that also runs out is counted apart), and the CTA leaves
-  // without writing its faces.
-  __shared__ int ready;
-  if (tid == 0) {
-    bool ok = false;
-    for (unsigned spins = 0; spins < wlim && !ok; ++spins) ok = mbar_try_wait(&bar, 0);
-    if (!ok) {
-      atomicAdd(cnt + CNT_TIMEOUT, 1ULL);
-      bool landed = false;
-      for (unsigned r = 0; r < WAIT_LIMIT && !landed; ++r) landed = mbar_try_wait(&bar, 0);
-      if (!landed) atomicAdd(cnt + CNT_DRAIN, 1ULL);
-    }
-    ready = ok ? 1 : 0;
-  }
-  __syncthreads();
-  if (!ready) return;
-  for (unsigned r = 0; r < WAIT_LIMIT && !mbar_try_wait(&bar, 0); ++r) {  // completed: returns at once
-  }
+  // bounded wait; on a timeout the CTA leaves (after its copy has landed)
+  // without writing its faces
+  if (!cta_wait_tiles(&bar, wlim, cnt)) return;
   // ---- reconstruct this thread's cell once, for both of its x^D faces ----
   // cell cl along D (0 = the cell below the tile's first face), row across
   auto at = [&](int v, int x, int y, int z) { return tile[((v * Sh::BZ + z) * Sh::BY + y) * Sh::BX + x]; };
@@ -265,31 +245,14 @@ __global__ void __launch_bounds__(NT) k_flux_tma(const __grid_constant__ CUtenso
   ctop[c] = ct;
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
-  return fn;
-}
-
 // The 8 FP32 planes [v][k][j][i] as a 4-D tensor (i, j, k, v) with the box of
 // direction D.
 template <int D> bool encode(CUtensorMap* tm, const float* base, const Layout& L) {
   using Sh = TileShape<D>;
-  auto fn = encode_fn();
-  if (!fn) return false;
   const cuuint64_t dims[4] = {(cuuint64_t)L.n1s, (cuuint64_t)L.n2s, (cuuint64_t)L.n3s, (cuuint64_t)NV};
   const cuuint64_t strides[3] = {(cuuint64_t)L.n1s * 4, (cuuint64_t)L.n1s * L.n2s * 4, (cuuint64_t)L.plane * 4};
   const cuuint32_t boxd[4] = {(cuuint32_t)Sh::BX, (cuuint32_t)Sh::BY, (cuuint32_t)Sh::BZ, (cuuint32_t)NV};
-  const cuuint32_t estr[4] = {1, 1, 1, 1};
-  return fn(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(base), dims, strides, boxd, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  return encode_tiled(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, boxd);
 }
 
 template <int D>

@@ -200,6 +200,15 @@ int launch_update_mixed(const double* U0, const CVarsT<float>& Pin, const Vars& 
                         const Scheme& S, const double* dtp, double coef, int8_t* pflag, unsigned long long* cnt,
                         int tpb, cudaStream_t s, FailList fl = FailList{nullptr, nullptr},
                         const double* fBn = nullptr, double* dUout = nullptr, float* const* emf = nullptr);
+// The same update (3-D grids, Flux-CT EMFs, no face field) with its inputs --
+// P8 the 8-plane FP32 stage input, U0, the FP32 fluxes F and edge EMFs emf --
+// staged per tile in shared memory by TMA (kh_update_tma.cu); wlim bounds the
+// polls of a CTA's wait for its tiles. Returns -1 (nothing launched) where it
+// does not apply or the tensor maps cannot be encoded.
+int launch_update_mixed_tma(const double* U0, const float* P8, const Vars& Pout64, const VarsT<float>& Pout32,
+                            double* Uout, float* const F[3], float* const emf[3], const Layout& L, const DevGeom& G,
+                            const GeomT<float>& Gf, const Scheme& S, const double* dtp, double coef, int8_t* pflag,
+                            unsigned long long* cnt, FailList fl, double* dUout, unsigned wlim, cudaStream_t s);
 // Fixup over every zone, or (fl.idx != nullptr) over the stage's failed-zone list.
 template <class T>
 int launch_fixup(const VarsT<T>& P, double* Uout, const int8_t* pflag, const Layout& L, const DevGeom& G,

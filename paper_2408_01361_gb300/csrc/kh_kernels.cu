@@ -273,17 +273,20 @@ __global__ void k_lincomb(double* out, LinComb lc, long long n) {
   }
 }
 
-// three blocks of TPB_MAX per SM: ~80 registers (a few spill to L1); measured faster
-// than the unconstrained 128 registers at 16 warps per SM
+// four blocks of TPB_MAX per SM: 64 registers (the unconstrained kernel takes
+// ~220; the spills go to L1). Measured on GB300 (192x96x96 torus, per launch):
+// 300 us at 4 blocks, 308 us at 3 (80 registers), 334 us at 2 (128).
 template <int INV>
-__global__ void __launch_bounds__(TPB_MAX, 3) k_update_mixed(const double* U0, CVarsT<float> Pin, Vars Pout64,
+__global__ void __launch_bounds__(TPB_MAX, 4) k_update_mixed(const double* U0, CVarsT<float> Pin, Vars Pout64,
                                                          VarsT<float> Pout32, double* Uout, const float* F1,
                                                          const float* F2, const float* F3, Layout L, DevGeom G,
                                                          GeomT<float> Gf, Scheme S, const double* dtp, double coef,
                                                          int8_t* pflag, unsigned long long* cnt, FailList fl,
                                                          const double* fBn, double* dUout, CtEmf ect) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nzones(L)) return;
   int i, j, k;
-  if (!tile_zone(L, i, j, k)) return;
+  zone_ijk(L, t, i, j, k);
   if (KH_OOB(L, kh_in(L, i, j, k, 1))) return;
   update_mixed_zone<false, INV>(U0, Pin, Pout64, Pout32, Uout, F1, F2, F3, L, G, Gf, S, df_of_f64(coef * __ldg(dtp)),
                                 pflag, cnt, i, j, k, fl, fBn, dUout, ect);
@@ -862,8 +865,9 @@ int launch_update_mixed(const double* U0, const CVarsT<float>& Pin, const Vars& 
                         float* const* emf) {
   const CtEmf ect{{emf ? emf[0] : nullptr, emf ? emf[1] : nullptr, emf ? emf[2] : nullptr}};
   auto go = [&](auto kern) {
-    kern<<<(unsigned)tile_blocks(L, tpb), tpb, 0, s>>>(U0, Pin, Pout64, Pout32, Uout, F[0], F[1], F[2], L, G, Gf, S,
-                                                       dtp, coef, pflag, cnt, fl, fBn, dUout, ect);
+    kern<<<nblocks((long long)L.n1 * L.n2 * L.n3, tpb), tpb, 0, s>>>(U0, Pin, Pout64, Pout32, Uout, F[0], F[1], F[2],
+                                                                     L, G, Gf, S, dtp, coef, pflag, cnt, fl, fBn,
+                                                                     dUout, ect);
   };
   if (S.c2p.method == C2P_KASTAUN) go(k_update_mixed<C2P_KASTAUN>);
   else if (S.c2p.method == C2P_1DW) go(k_update_mixed<C2P_1DW>);

@@ -88,38 +88,6 @@ __device__ __forceinline__ unsigned nzones(const Layout& L) {
   return (unsigned)(L.e[0] - L.s[0]) * (L.e[1] - L.s[1]) * (L.e[2] - L.s[2]);
 }
 
-// Tiled zone order of the per-zone kernels that read the axisymmetric
-// geometry: a block covers one warp-wide run of 32 zones along x1 on each of
-// blockDim.x / 32 consecutive planes of the outermost direction (x3 in 3-D,
-// x2 in 2-D). Its warps then read the same geometry columns (the first warp
-// brings them into L1 for the others) and each other's x3 (x2) face and edge
-// neighbours. Returns false for threads past the interior (ragged tiles).
-__device__ __forceinline__ bool tile_zone(const Layout& L, int& i, int& j, int& k) {
-  const int nw = (int)(blockDim.x >> 5);
-  const int ni = (L.e[0] - L.s[0] + 31) >> 5;
-  unsigned b = blockIdx.x;
-  const int it = (int)(b % (unsigned)ni);
-  b /= (unsigned)ni;
-  const int w = (int)(threadIdx.x >> 5);
-  i = L.s[0] + (it << 5) + (int)(threadIdx.x & 31u);
-  if (L.ndim == 3) {
-    const int nj = L.e[1] - L.s[1];
-    j = L.s[1] + (int)(b % (unsigned)nj);
-    k = L.s[2] + (int)(b / (unsigned)nj) * nw + w;
-  } else {
-    j = L.s[1] + (int)b * nw + w;
-    k = L.s[2];
-  }
-  return i < L.e[0] && j < L.e[1] && k < L.e[2];
-}
-
-// Blocks of tile_zone's order over the interior for tpb threads per block.
-KH_HD long long tile_blocks(const Layout& L, int tpb) {
-  const long long nw = tpb / 32, ni = (L.e[0] - L.s[0] + 31) / 32;
-  if (L.ndim == 3) return ni * (L.e[1] - L.s[1]) * ((L.e[2] - L.s[2] + nw - 1) / nw);
-  return ni * ((L.e[1] - L.s[1] + nw - 1) / nw);
-}
-
 // Reconstruction + LLF flux through the lower x^D face of cell (k, j, i).
 // FP32 (mixed path): the left and right states as packed pairs.
 template <int D, int RECON>
@@ -454,14 +422,38 @@ struct CtEmf {
   const float* e[3];
 };
 
+// Where the mixed update of one zone reads its inputs -- the stage input P,
+// U^n, the face fluxes of the fluid variables and Flux-CT's edge EMFs -- as
+// values around the zone: f(d, v, up) is variable v's flux through the
+// zone's lower (up = 0) or upper (up = 1) x^(d+1) face, e(a, di, dj, dk) the
+// x^(a+1)-edge EMF at offset (di, dj, dk) from the zone's lower corner.
+// MixedInGlobal reads the arrays in global memory (the layout of L); the
+// TMA-staged update kernel reads shared-memory tiles through its own view.
+struct MixedInGlobal {
+  const double* U0;
+  CVarsT<float> Pin;
+  const float* F[3];
+  CtEmf ect;
+  long long c, sj, sk, plane;
+  __device__ __forceinline__ float pin(int v) const { return Pin.v[v][c]; }
+  __device__ __forceinline__ double u0(int v) const { return U0[v * plane + c]; }
+  __device__ __forceinline__ float f(int d, int v, int up) const {
+    return F[d][v * plane + c + (up ? (d == 0 ? 1 : (d == 1 ? sj : sk)) : 0)];
+  }
+  __device__ __forceinline__ float e(int a, int di, int dj, int dk) const {
+    return ect.e[a][c + di + dj * sj + dk * sk];
+  }
+  __device__ __forceinline__ bool has_emf() const { return ect.e[2] != nullptr; }
+};
+
 // The end of the mixed update when its inversion stays in FP64 for every
 // zone (kh_coords.mixed_inversion = KH_MIXINV_FP64, the precision split that
 // keeps the whole Noble-2D inversion in FP64): U holds the FP64 conserved
 // variables U^n + increment; the FP64 Noble-2D iteration starts from the
 // FP32 stage input; floors as on the FP64 path (FP64 decisions and values),
 // U recomputed in FP64 where one acted; outputs as update_mixed_zone's.
-template <bool TRIAL>
-__device__ __forceinline__ void update_mixed_fp64_tail(double* U, const CVarsT<float>& Pin, const Vars& Pout64,
+template <bool TRIAL, class IN>
+__device__ __forceinline__ void update_mixed_fp64_tail(double* U, const IN& in, const Vars& Pout64,
                                                        const VarsT<float>& Pout32, double* Uout, const Layout& L,
                                                        const DevGeom& G, const Scheme& S, int8_t* pflag,
                                                        unsigned long long* cnt, long long c, long long p,
@@ -469,7 +461,7 @@ __device__ __forceinline__ void update_mixed_fp64_tail(double* U, const CVarsT<f
   const Met<double> m = load_met(G, L.gplane, LOC_CENT, p);
   double Pn[NV];
 #pragma unroll
-  for (int v = 0; v < NV; ++v) Pn[v] = f64_of_f32(Pin.v[v][c]);
+  for (int v = 0; v < NV; ++v) Pn[v] = f64_of_f32(in.pin(v));
   const double ig = __ldg(G.flo + 2 * L.gplane + p);  // 1 / sqrt(-g)
   const int flag = invert<C2P_NOBLE2D>(U, m, ig, S.gam, S.igam, S.gfac, S.c2p, Pn);
   if (TRIAL && flag) {
@@ -498,7 +490,7 @@ __device__ __forceinline__ void update_mixed_fp64_tail(double* U, const CVarsT<f
     }
   } else {
 #pragma unroll
-    for (int v = 0; v < 5; ++v) Pn[v] = f64_of_f32(Pin.v[v][c]);  // provisional, replaced by the fixup
+    for (int v = 0; v < 5; ++v) Pn[v] = f64_of_f32(in.pin(v));  // provisional, replaced by the fixup
   }
   if (Pout32.v[0]) {
 #pragma unroll
@@ -530,18 +522,14 @@ __device__ __forceinline__ void update_mixed_fp64_tail(double* U, const CVarsT<f
 // invert every zone in FP64 (from the double-float U rounded to FP64).
 // INV = C2P_NOBLE2D_FP64: the FP64 Noble-2D for every zone from the FP64
 // U^n + increment (update_mixed_fp64_tail).
-template <bool TRIAL = false, int INV = C2P_NOBLE2D>
-__device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT<float>& Pin, const Vars& Pout64,
-                                                  const VarsT<float>& Pout32, double* Uout, const float* F1,
-                                                  const float* F2, const float* F3, const Layout& L, const DevGeom& G,
-                                                  const GeomT<float>& Gf, const Scheme& S, df64 cdt, int8_t* pflag,
-                                                  unsigned long long* cnt, int i, int j, int k,
-                                                  FailList fl = FailList{nullptr, nullptr},
-                                                  const double* fBn = nullptr, double* dUout = nullptr,
-                                                  CtEmf ect = CtEmf{{nullptr, nullptr, nullptr}}) {
+template <bool TRIAL, int INV, class IN>
+__device__ __forceinline__ void update_mixed_zone_in(const IN& in, const Vars& Pout64, const VarsT<float>& Pout32,
+                                                     double* Uout, const Layout& L, const DevGeom& G,
+                                                     const GeomT<float>& Gf, const Scheme& S, df64 cdt,
+                                                     int8_t* pflag, unsigned long long* cnt, int i, int j, int k,
+                                                     FailList fl, const double* fBn, double* dUout) {
   const long long c = L.at(k, j, i);
   const long long p = (long long)j * L.n1s + i;
-  const long long sj = L.n1s, sk = (long long)L.n1s * L.n2s;
   const MixedConsts& mx = S.mx;
   // the stored U (stage 2) is written here and touched again only by floors
   df64 Ud[NV];    // U^n + increment, double-float, for the inversion
@@ -550,7 +538,7 @@ __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT
   {
     float Pf[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) Pf[v] = Pin.v[v][c];
+    for (int v = 0; v < NV; ++v) Pf[v] = in.pin(v);
     float Sv[NV] = {0, 0, 0, 0, 0, 0, 0, 0};
     const Met<float> mf = load_met(Gf, L.gplane, LOC_CENT, p);
     source_terms(Pf, mf, Gf.dgm, L.gplane, p, mx.gam, Sv);
@@ -569,49 +557,46 @@ __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT
       // lower / upper face fluxes per direction
       float a1, b1, a2, b2, a3 = 0.0f, b3 = 0.0f;
       const bool three = L.ndim == 3;
-      if (ect.e[2] && v >= V_B1 && (three || v != V_B3)) {
-        const float* e1 = ect.e[0];
-        const float* e2 = ect.e[1];
-        const float* e3 = ect.e[2];
+      if (in.has_emf() && v >= V_B1 && (three || v != V_B3)) {
         const float h = 0.5f;
         if (v == V_B1) {
           a1 = 0.0f;
           b1 = 0.0f;
-          a2 = -h * (e3[c] + e3[c + 1]);
-          b2 = -h * (e3[c + sj] + e3[c + sj + 1]);
+          a2 = -h * (in.e(2, 0, 0, 0) + in.e(2, 1, 0, 0));
+          b2 = -h * (in.e(2, 0, 1, 0) + in.e(2, 1, 1, 0));
           if (three) {
-            a3 = h * (e2[c] + e2[c + 1]);
-            b3 = h * (e2[c + sk] + e2[c + sk + 1]);
+            a3 = h * (in.e(1, 0, 0, 0) + in.e(1, 1, 0, 0));
+            b3 = h * (in.e(1, 0, 0, 1) + in.e(1, 1, 0, 1));
           }
         } else if (v == V_B2) {
-          a1 = h * (e3[c] + e3[c + sj]);
-          b1 = h * (e3[c + 1] + e3[c + 1 + sj]);
+          a1 = h * (in.e(2, 0, 0, 0) + in.e(2, 0, 1, 0));
+          b1 = h * (in.e(2, 1, 0, 0) + in.e(2, 1, 1, 0));
           a2 = 0.0f;
           b2 = 0.0f;
           if (three) {
-            a3 = -h * (e1[c] + e1[c + sj]);
-            b3 = -h * (e1[c + sk] + e1[c + sk + sj]);
+            a3 = -h * (in.e(0, 0, 0, 0) + in.e(0, 0, 1, 0));
+            b3 = -h * (in.e(0, 0, 0, 1) + in.e(0, 0, 1, 1));
           }
         } else {  // B3, 3-D
-          a1 = -h * (e2[c] + e2[c + sk]);
-          b1 = -h * (e2[c + 1] + e2[c + 1 + sk]);
-          a2 = h * (e1[c] + e1[c + sk]);
-          b2 = h * (e1[c + sj] + e1[c + sj + sk]);
+          a1 = -h * (in.e(1, 0, 0, 0) + in.e(1, 0, 0, 1));
+          b1 = -h * (in.e(1, 1, 0, 0) + in.e(1, 1, 0, 1));
+          a2 = h * (in.e(0, 0, 0, 0) + in.e(0, 0, 0, 1));
+          b2 = h * (in.e(0, 0, 1, 0) + in.e(0, 0, 1, 1));
         }
       } else {
-        a1 = F1[o];
-        b1 = F1[o + 1];
-        a2 = F2[o];
-        b2 = F2[o + sj];
+        a1 = in.f(0, v, 0);
+        b1 = in.f(0, v, 1);
+        a2 = in.f(1, v, 0);
+        b2 = in.f(1, v, 1);
         if (three) {
-          a3 = F3[o];
-          b3 = F3[o + sk];
+          a3 = in.f(2, v, 0);
+          b3 = in.f(2, v, 1);
         }
       }
       float div = (b1 - a1) * i1 + (b2 - a2) * i2;
       if (three) div += (b3 - a3) * i3;
       const float inc = (cdt * (Sv[v] - div)).hi;  // c dt (S - div F)
-      const double u0 = U0[o];
+      const double u0 = in.u0(v);
       if (Uout) Uout[o] = u0 + f64_of_f32(inc);    // the conserved update, FP64
       if (dUout) dUout[o] = f64_of_f32(inc);       // the raw increment (Runge-Kutta stages)
       if constexpr (INV == C2P_NOBLE2D_FP64) Ue[v] = u0 + f64_of_f32(inc);
@@ -629,7 +614,7 @@ __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT
     }
   }
   if constexpr (INV == C2P_NOBLE2D_FP64) {
-    update_mixed_fp64_tail<TRIAL>(Ue, Pin, Pout64, Pout32, Uout, L, G, S, pflag, cnt, c, p, fl);
+    update_mixed_fp64_tail<TRIAL>(Ue, in, Pout64, Pout32, Uout, L, G, S, pflag, cnt, c, p, fl);
     return;
   }
   const MetDF md = load_metdf(Gf.df, L.gplane, p);
@@ -646,7 +631,7 @@ __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       Uf[v] = f64_of_df(Ud[v]);
-      Pd[v] = f64_of_f32(Pin.v[v][c]);
+      Pd[v] = f64_of_f32(in.pin(v));
     }
     const Met<double> m = load_met(G, L.gplane, LOC_CENT, p);
     flag = invert<INV>(Uf, m, __ldg(G.flo + 2 * L.gplane + p), S.gam, S.igam, S.gfac, S.c2p, Pd);
@@ -662,7 +647,7 @@ __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT
   }
   if (flag) {
 #pragma unroll
-    for (int v = 0; v < 5; ++v) Pn[v] = mkdf(Pin.v[v][c], 0.0f);
+    for (int v = 0; v < 5; ++v) Pn[v] = mkdf(in.pin(v), 0.0f);
   }
   int fmask = 0;
   if (flag == 0) {
@@ -737,6 +722,21 @@ __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT
   if (fmask) atomicAdd(cnt + CNT_FLOOR, 1ULL);
 }
 
+
+// The mixed update of zone (i, j, k) reading its inputs from global memory.
+template <bool TRIAL = false, int INV = C2P_NOBLE2D>
+__device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT<float>& Pin, const Vars& Pout64,
+                                                  const VarsT<float>& Pout32, double* Uout, const float* F1,
+                                                  const float* F2, const float* F3, const Layout& L, const DevGeom& G,
+                                                  const GeomT<float>& Gf, const Scheme& S, df64 cdt, int8_t* pflag,
+                                                  unsigned long long* cnt, int i, int j, int k,
+                                                  FailList fl = FailList{nullptr, nullptr},
+                                                  const double* fBn = nullptr, double* dUout = nullptr,
+                                                  CtEmf ect = CtEmf{{nullptr, nullptr, nullptr}}) {
+  const MixedInGlobal in{U0, Pin, {F1, F2, F3}, ect, L.at(k, j, i), (long long)L.n1s, (long long)L.n1s * L.n2s,
+                         L.plane};
+  update_mixed_zone_in<TRIAL, INV>(in, Pout64, Pout32, Uout, L, G, Gf, S, cdt, pflag, cnt, i, j, k, fl, fBn, dUout);
+}
 
 // Fixup: a zone whose inversion failed takes the equal-weight mean of the
 // fluid primitives of its non-failed interior neighbours (3x3x3, or 3x3 in
