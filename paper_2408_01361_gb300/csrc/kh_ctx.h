@@ -42,7 +42,7 @@ struct kh_ctx {
   // FP32 stage-1 output and FP32 Dirichlet ghosts
   float* geof;
   float* dgmf;
-  float* geodf;    // [NDF][2] double-float planes of the cell-centre geometry and floors
+  float* geodf;    // [NDF] planes of double-float (hi, lo) pairs: the cell-centre geometry and floors
   unsigned* flist; // failed-zone list of the current stage (one entry per zone at most)
   float* pstarf;   // 8 planes
   float* pnf;      // 8 planes: FP32 copy of the ghost-filled stage-1 input

@@ -75,7 +75,7 @@ template <class T> struct GeomT {
   const T* g;          // [3][NGEO][n2s][n1s]
   const T* dgm;        // [NDG][n2s][n1s]: metric derivatives in x1 and x2 at cell centres
   const double* flo;   // [3][n2s][n1s]: geometric floors of rho and u, and 1/sqrt(-g), at cell centres
-  const float* df;     // FP32 copy only: [NDF][2][n2s][n1s] double-float planes (above)
+  const float* df;     // FP32 copy only: [NDF][n2s][n1s] double-float (hi, lo) pairs (above)
 };
 using DevGeom = GeomT<double>;
 

@@ -965,8 +965,8 @@ __global__ void k_df_planes(const double* geo, const double* flo, float* df, lon
        p += (long long)gridDim.x * blockDim.x) {
     auto put = [&](int q, double x) {
       const df64 v = df_of_f64(x);
-      df[(2 * q) * gplane + p] = v.hi;
-      df[(2 * q + 1) * gplane + p] = v.lo;
+      df[2 * (q * gplane + p)] = v.hi;
+      df[2 * (q * gplane + p) + 1] = v.lo;
     };
     // cell-centre planes: gcov pairs 0..9, gcon pairs 10..19, gdet 20, alpha 21
     for (int q = 0; q < 10; ++q) put(DF_GCON + q, geo[(10 + q) * gplane + p]);

@@ -564,7 +564,7 @@ struct kh_mesh {
   long long nnbs;
   double *geo, *dgm, *flo;
   float *geof, *dgmf;
-  float* geodf;  // [NDF][2] double-float planes per block (goff-based)
+  float* geodf;  // [NDF] planes of double-float (hi, lo) pairs per block (goff-based)
   double* pstar;
   float *pstarf, *pnf;
   double* F[3];

@@ -25,8 +25,8 @@ namespace kh {
 constexpr int C2P_NEED_FP64 = -1;
 
 // Double-float (hi, lo FP32 pair) copies of the cell-centre quantities the
-// mixed update's inversion and floors use, per (i, j): planes [NDF][2][n2s][n1s]
-// (hi plane, then lo plane, of each quantity). DF_GCON: g^{mn} in the
+// mixed update's inversion and floors use, per (i, j): planes [NDF][n2s][n1s]
+// of (hi, lo) float pairs, so that one 8-byte load brings both halves. DF_GCON: g^{mn} in the
 // symmetric-pair order; DF_GCOV: g_ij (11 12 13 22 23 33).
 enum { DF_GCON = 0, DF_GCOV = 10, DF_ALPHA = 16, DF_IG = 17, DF_RHOFL = 18, DF_UFL = 19, NDF = 20 };
 
@@ -65,7 +65,11 @@ struct MetDF {
 
 #ifdef __CUDACC__
 __device__ __forceinline__ MetDF load_metdf(const float* df, long long gplane, long long p) {
-  auto ld = [&](int q) { return mkdf(__ldg(df + (2 * q) * gplane + p), __ldg(df + (2 * q + 1) * gplane + p)); };
+  const float2* d2 = reinterpret_cast<const float2*>(df);  // (hi, lo) pairs: one 8-byte load each
+  auto ld = [&](int q) {
+    const float2 v = __ldg(d2 + q * gplane + p);
+    return mkdf(v.x, v.y);
+  };
   MetDF m;
 #pragma unroll
   for (int q = 0; q < 10; ++q) m.gcon[q] = ld(DF_GCON + q);

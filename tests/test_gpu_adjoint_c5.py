@@ -11,15 +11,24 @@ Checks, per objective and direction v (on every interior zone, and on gamma):
     (independent code, the same derivative rules: branches as taken, the
     inversion by the implicit-function theorem, floored components and
     fixed-up zones frozen): within 1e-6 of the sum of the terms' magnitudes;
-  * against central differences (h = 1e-6 relative): of the FP64 oracle for
-    E, of the CUDA forward for the flux objective (the oracle does not expose
-    its stage-2 fluxes). Over 20 steps every direction meets kinks (limiter
-    and LLF-speed branches, floors and fixups decide differently at +h and
-    -h somewhere among ~1e6-1e7 branch evaluations), so a quotient carries
-    an error of its own, estimated by the difference of the quotients at h
-    and h/2. The adjoint must lie within that band (or 1e-6) of the h/2
-    quotient; a direction whose band exceeds 1e-3 of the quotient measures
-    nothing and is reported, not counted.
+  * against central differences of the CUDA forward for the flux objective
+    on the box. The step is piecewise smooth (MC's branches, the max in the
+    LLF speed): a perturbation of size h flips every branch decided within h
+    of a tie, and over 20 steps the perturbation reaches every zone, so a
+    difference quotient carries an error of its own that does not vanish
+    with h at a useful rate -- measured on the oracle alone (16^3 and 32^3
+    boxes, 20 steps), quotients of a direction on every zone stay 0.2-0.6%
+    from the exact (dual-number) derivative for h from 1e-5 to 1e-7; for a
+    direction on three zones the 16^3 box reaches 3e-8 at h = 1e-7, the 32^3
+    box (whole box reached) still 0.2%. The check therefore takes a direction
+    on three zones, h = 1e-7 relative and h/2, and a bound of 5e-3 of the
+    quotient (or twice the quotients' difference, if larger).
+    On the torus the adjoint's rules themselves differ from the function:
+    floored components and fixed-up zones are frozen (zero derivative), while
+    the floors there include the magnetisation ceilings rho >= b^2/100 that
+    do depend on the state -- near the horizon the accretion rate's
+    derivative through them is tens of percent. There the dual-number tangent
+    (the same rules) is the check, and central differences are not used.
   * the mixed-precision forward: the gradient of the FP64 step taken along
     the mixed trajectory (adj_ctx) against the FP64 trajectory's, within the
     distance of the two trajectories."""
@@ -135,13 +144,24 @@ def _dual(orc, cfg, U0, P0, dt, vU, vP, dgam, i_face):
     return {"energy": dE, "mdot": dM}
 
 
-def _direction(cfg, U0, P0, seed):
+def _direction(cfg, U0, P0, seed, zones=None):
+    """A random direction on every interior zone (zones=None) or on `zones`
+    random interior zones, each variable scaled by its largest magnitude,
+    and a random gamma component."""
     rng = np.random.default_rng(seed)
     sl = (slice(None),) + inputs.interior(cfg)
     vU = np.zeros(P0.shape)
     vP = np.zeros(P0.shape)
-    vU[sl] = rng.normal(size=vU[sl].shape)
-    vP[sl] = rng.normal(size=vP[sl].shape)
+    if zones is None:
+        vU[sl] = rng.normal(size=vU[sl].shape)
+        vP[sl] = rng.normal(size=vP[sl].shape)
+    else:
+        lo = [s.start for s in inputs.interior(cfg)]
+        hi = [s.stop for s in inputs.interior(cfg)]
+        for _ in range(zones):
+            z = tuple(int(rng.integers(lo[a], hi[a])) for a in range(3))
+            vU[(slice(None),) + z] = rng.normal(size=8)
+            vP[(slice(None),) + z] = rng.normal(size=8)
     vU *= np.abs(U0).reshape(8, -1).max(axis=1)[:, None, None, None]
     vP *= np.abs(P0).reshape(8, -1).max(axis=1)[:, None, None, None]
     return vU, vP, float(rng.normal())
@@ -152,15 +172,6 @@ def _pair(g, vU, vP, dgam):
     _, gU, gPB, gg = g
     terms = np.concatenate([(gU * vU).ravel(), (gPB * vP).ravel(), [gg * dgam]])
     return terms.sum(), np.abs(terms).sum()
-
-
-def _oracle_energy(orc, cfg, U0, P0, dt, gam):
-    c = dict(cfg, gam=gam)
-    U, P = U0, P0
-    for _ in range(NSTEPS):
-        U, P, _, _ = orc.step(c, U, P, dt)
-    ksl, jsl, isl = inputs.interior(cfg)
-    return -(U[1][ksl, jsl, isl] - U[0][ksl, jsl, isl]).sum() * _dV(cfg)
 
 
 def _cuda_mdot(kh, cfg, U0, P0, dt, gam, i_face):
@@ -175,7 +186,7 @@ def _cuda_mdot(kh, cfg, U0, P0, dt, gam, i_face):
     return -F1[0, ksl, jsl, i_face].sum() * _dA1(cfg)
 
 
-def _fd(f, U0, P0, gam, vU, vP, dgam, rel=1e-6):
+def _fd(f, U0, P0, gam, vU, vP, dgam, rel=1e-7):
     """Central differences of f(U, P, gam) along the direction at steps h and
     h/2 (h = rel, the direction already carries each variable's scale)."""
     out = []
@@ -185,10 +196,13 @@ def _fd(f, U0, P0, gam, vU, vP, dgam, rel=1e-6):
     return out
 
 
-def _check_case(kh, torch, orc, cfg, P0, dt, i_face, seeds, energy_fd):
+def _check_case(kh, torch, orc, cfg, P0, dt, i_face, seeds, fd):
+    """Adjoint vs the oracle's dual tangent for a direction on every zone
+    (both objectives), and (fd) vs central differences of the CUDA forward
+    for the flux objective along a direction on three zones."""
     U0 = orc.prim_to_cons(cfg, P0)
     grads = _rollout(kh, torch, cfg, U0, P0, dt, i_face)
-    report = {"flips": [], "checked": {"energy": 0, "mdot": 0}}
+    checked = 0
     for seed in seeds:
         vU, vP, dgam_unit = _direction(cfg, U0, P0, seed)
         dgam = dgam_unit * cfg["gam"]
@@ -196,20 +210,16 @@ def _check_case(kh, torch, orc, cfg, P0, dt, i_face, seeds, energy_fd):
         for name in ("energy", "mdot"):
             adj, scale = _pair(grads[name], vU, vP, dgam)
             assert abs(adj - tan[name]) <= 1e-6 * scale, (name, seed, adj, tan[name], scale)
-        fdsets = {"mdot": _fd(lambda U, P, g: _cuda_mdot(kh, cfg, U, P, dt, g, i_face), U0, P0, cfg["gam"],
-                              vU, vP, dgam_unit)}
-        if energy_fd:
-            fdsets["energy"] = _fd(lambda U, P, g: _oracle_energy(orc, cfg, U, P, dt, g), U0, P0, cfg["gam"],
-                                   vU, vP, dgam_unit)
-        for name, fds in fdsets.items():
-            adj, scale = _pair(grads[name], vU, vP, dgam)
-            band = abs(fds[0] - fds[1])
-            if band > 1e-3 * abs(fds[1]):
-                report["flips"].append((name, seed, fds))
-                continue
-            assert abs(adj - fds[1]) <= max(2.0 * band, 1e-6 * abs(fds[1])), (name, seed, adj, fds)
-            report["checked"][name] += 1
-    return grads, report
+        if not fd:
+            continue
+        vU, vP, dgam_unit = _direction(cfg, U0, P0, seed + 100, zones=3)
+        dgam = dgam_unit * cfg["gam"]
+        fds = _fd(lambda U, P, g: _cuda_mdot(kh, cfg, U, P, dt, g, i_face), U0, P0, cfg["gam"], vU, vP, dgam_unit)
+        adj, _ = _pair(grads["mdot"], vU, vP, dgam)
+        band = abs(fds[0] - fds[1])
+        assert abs(adj - fds[1]) <= max(2.0 * band, 5e-3 * abs(fds[1])), (seed, adj, fds)
+        checked += 1
+    return grads, checked
 
 
 def test_c5_box_64cubed_20_steps(kh, torch, orc):
@@ -217,22 +227,21 @@ def test_c5_box_64cubed_20_steps(kh, torch, orc):
     -dV (e_energy - e_rho) at every interior zone; the face-plane mass flux
     is a generic objective."""
     cfg, P0, dt, i_face = _box(orc)
-    grads, rep = _check_case(kh, torch, orc, cfg, P0, dt, i_face, seeds=(40, 41), energy_fd=False)
+    grads, checked = _check_case(kh, torch, orc, cfg, P0, dt, i_face, seeds=(40, 41), fd=True)
     _, gU, gPB, gg = grads["energy"]
     sl = (slice(None),) + inputs.interior(cfg)
     want = np.zeros(8)
     want[0], want[1] = _dV(cfg), -_dV(cfg)
     assert np.abs(gU[sl] - want[:, None, None, None]).max() <= 1e-9 * _dV(cfg)
     assert np.abs(gPB[sl]).max() <= 1e-9 * _dV(cfg) and abs(gg) <= 1e-9
-    assert rep["checked"]["mdot"] >= 1, rep
+    assert checked == 2
 
 
 def test_c5_torus_128x64_20_steps(kh, torch, orc):
     """The FMKS torus with its floors, fixups, polar axis and outflow
-    boundaries: E and the horizon mass flux."""
+    boundaries: E and the horizon mass flux against the dual tangent."""
     cfg, P0, dt, i_face = _torus(orc)
-    grads, rep = _check_case(kh, torch, orc, cfg, P0, dt, i_face, seeds=(50, 51, 52), energy_fd=True)
-    assert rep["checked"]["energy"] + rep["checked"]["mdot"] >= 2, rep
+    _check_case(kh, torch, orc, cfg, P0, dt, i_face, seeds=(50, 51, 52), fd=False)
 
 
 def test_c5_torus_mixed_forward(kh, torch, orc):
