@@ -119,9 +119,10 @@ typedef struct {
                              apply to each (KASTAUN: up to 4x the iterations, tol
                              on the bracket width). Single-grid contexts, FP64 and
                              KH_MIXED (there Noble-2D runs in double-float with an
-                             FP64 fallback, the others in FP64); the refined mesh
-                             and the adjoint carry Noble-2D and refuse the others;
-                             used by the update and kh_cons_to_prim. */
+                             FP64 fallback, the others in FP64), single grids and
+                             the refined mesh; the adjoint carries Noble-2D and
+                             refuses the others; used by the update and
+                             kh_cons_to_prim. */
   int integrator;         /* time integrator ("Algorithm" section): KH_INT_VL2 (the
                              predictor-corrector, default), KH_INT_RK1, KH_INT_RK2
                              (Heun) or KH_INT_SSPRK54 (Spiteri & Ruuth's five-stage
@@ -142,7 +143,7 @@ typedef struct {
                              U^n + increment, the Noble-2D Newton iteration starts from
                              the FP32 stage input, and the floors act in FP64 as on the
                              FP64 path. Ignored by KH_FP64 contexts and the other
-                             solvers; the refined mesh refuses KH_MIXINV_FP64. */
+                             solvers; single grids and the refined mesh. */
 } kh_coords;
 enum { KH_MIXINV_DF = 0, KH_MIXINV_FP64 = 1 };
 

@@ -159,6 +159,7 @@ __global__ void km_ct(const MBlock* blk, const unsigned* pre, int nb, R* F1, R* 
     apply_ct_at<R>(F1 + o8, F2 + o8, f3, ee1, ee2, e3 + o1, L, i, j, k);
 }
 
+template <int INV>
 __global__ void __launch_bounds__(256) km_update(const MBlock* blk, const unsigned* pre, int nb, const double* U0,
                                                 Arena<double> Pin, Arena<double> Pout, double* Uout,
                                                 const double* F1, const double* F2, const double* F3, GeoArena GA,
@@ -171,11 +172,12 @@ __global__ void __launch_bounds__(256) km_update(const MBlock* blk, const unsign
   int i, j, k;
   zone_ijk(m.L, t - __ldg(pre + b), i, j, k);
   const long long o8 = NV * m.off;
-  update_zone(U0 + o8, cvars_at(Pin, m), vars_at(Pout, m), Uout ? Uout + o8 : nullptr, F1 + o8, F2 + o8,
+  update_zone<false, INV>(U0 + o8, cvars_at(Pin, m), vars_at(Pout, m), Uout ? Uout + o8 : nullptr, F1 + o8, F2 + o8,
               m.L.ndim == 3 ? F3 + o8 : nullptr, m.L, geo64(GA, m), S, coef * __ldg(dtp), pflag + m.off, cnt, i, j,
               k, nullptr, FailList{nullptr, nullptr}, fBn ? fBn + 3 * m.off : nullptr);
 }
 
+template <int INV>
 __global__ void __launch_bounds__(256, 2) km_update_mixed(const MBlock* blk, const unsigned* pre, int nb,
                                                       const double* U0, Arena<float> Pin, Arena<double> Pout64,
                                                       Arena<float> Pout32, double* Uout, const float* F1,
@@ -194,7 +196,7 @@ __global__ void __launch_bounds__(256, 2) km_update_mixed(const MBlock* blk, con
   VarsT<float> P32;
   if (Pout64.a) P64 = vars_at(Pout64, m); else for (int v = 0; v < NV; ++v) P64.v[v] = nullptr;
   if (Pout32.a) P32 = vars_at(Pout32, m); else for (int v = 0; v < NV; ++v) P32.v[v] = nullptr;
-  update_mixed_zone(U0 + o8, cvars_at(Pin, m), P64, P32, Uout ? Uout + o8 : nullptr, F1 + o8, F2 + o8,
+  update_mixed_zone<false, INV>(U0 + o8, cvars_at(Pin, m), P64, P32, Uout ? Uout + o8 : nullptr, F1 + o8, F2 + o8,
                     m.L.ndim == 3 ? F3 + o8 : nullptr, m.L, geo64(GA, m), geo32(GA, m), S,
                     df_of_f64(coef * __ldg(dtp)), pflag + m.off, cnt, i, j, k, FailList{nullptr, nullptr},
                     fBn ? fBn + 3 * m.off : nullptr, nullptr,
@@ -626,9 +628,9 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
   if (c->precision != KH_FP64 && c->precision != KH_MIXED) return KH_EINVAL;
   if (c->recon != KH_RECON_MC && c->recon != KH_RECON_WENO5) return KH_EINVAL;
   if (c->fofc) return KH_EINVAL;  // the flux correction runs on single grids
-  if (c->inverter != KH_INV_NOBLE2D) return KH_EINVAL;  // the mesh kernels carry Noble-2D
+  if (c->inverter < KH_INV_NOBLE2D || c->inverter > KH_INV_KASTAUN) return KH_EINVAL;
   if (c->integrator != KH_INT_VL2) return KH_EINVAL;    // the mesh steps with the predictor-corrector
-  if (c->mixed_inversion != KH_MIXINV_DF) return KH_EINVAL;  // the mesh's mixed update keeps double-float
+  if (c->mixed_inversion != KH_MIXINV_DF && c->mixed_inversion != KH_MIXINV_FP64) return KH_EINVAL;
   if (c->bfield != KH_B_FLUXCT && c->bfield != KH_B_FACE) return KH_EINVAL;
   if (c->emf != KH_EMF_AVERAGE && c->emf != KH_EMF_GS05) return KH_EINVAL;
   if (!(gamma > 1.0) || !(c->cfl > 0.0) || !(fabs(a) < 1.0)) return KH_EINVAL;
@@ -658,6 +660,7 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
   S.c2p.max_iter = c->newton_max_iter > 0 ? c->newton_max_iter : 30;
   S.c2p.tol = c->newton_tol > 0.0 ? c->newton_tol : 1e-14;
   S.c2p.method = c->inverter;
+  S.mixed_fp64 = c->precision == KH_MIXED && c->inverter == KH_INV_NOBLE2D && c->mixed_inversion == KH_MIXINV_FP64;
   S.bfield = c->bfield;
   S.emf = c->emf;
   set_mixed(S);
@@ -1163,6 +1166,34 @@ template <class T> int cfl_pass(kh_mesh* x, T* const ct[3]) {
   return 2;
 }
 
+// The update kernels over all blocks, instantiated for the context's solver
+// (the mixed path: double-float Noble-2D, or FP64 for every zone).
+void km_update_any(const kh_mesh* x, int g, int t, double* U0, const Arena<double>& Pin, const Arena<double>& Pout,
+                   double* Uout, double coef, const double* fBn) {
+  const GeoArena GA = garena(x);
+  auto go = [&](auto kern) {
+    kern<<<g, t, 0, x->stream>>>(x->dblk, x->dpre[3], x->nb, U0, Pin, Pout, Uout, x->F[0], x->F[1], x->F[2], GA,
+                                 x->S, x->dscalar + 3, coef, x->pflag, x->counters, fBn);
+  };
+  if (x->S.c2p.method == C2P_KASTAUN) go(km_update<C2P_KASTAUN>);
+  else if (x->S.c2p.method == C2P_1DW) go(km_update<C2P_1DW>);
+  else go(km_update<C2P_NOBLE2D>);
+}
+void km_update_mixed_any(const kh_mesh* x, int g, int t, double* U0, const Arena<float>& Pin,
+                         const Arena<double>& Pout64, const Arena<float>& Pout32, double* Uout, double coef,
+                         const double* fBn, const float* const* ce) {
+  const GeoArena GA = garena(x);
+  auto go = [&](auto kern) {
+    kern<<<g, t, 0, x->stream>>>(x->dblk, x->dpre[3], x->nb, U0, Pin, Pout64, Pout32, Uout, x->Ff[0], x->Ff[1],
+                                 x->Ff[2], GA, x->S, x->dscalar + 3, coef, x->pflag, x->counters, fBn, ce[0], ce[1],
+                                 ce[2]);
+  };
+  if (x->S.c2p.method == C2P_KASTAUN) go(km_update_mixed<C2P_KASTAUN>);
+  else if (x->S.c2p.method == C2P_1DW) go(km_update_mixed<C2P_1DW>);
+  else if (x->S.mixed_fp64) go(km_update_mixed<C2P_NOBLE2D_FP64>);
+  else go(km_update_mixed<C2P_NOBLE2D>);
+}
+
 int issue_mesh_step(kh_mesh* x, double* U, double* P, double* B) {
   cudaStream_t s = x->stream;
   if (cudaMemsetAsync(x->counters, 0, NCNT * sizeof(unsigned long long), s) != cudaSuccess) return -1;
@@ -1179,16 +1210,14 @@ int issue_mesh_step(kh_mesh* x, double* U, double* P, double* B) {
     n += fill_ghosts(x, Pn);
     n += flux_pass<double, double>(x, Pn, x->F, x->ctop, x->emf, !face);
     if (face) n += face_ct_pass<double>(x, Pn, x->F, x->ecc, x->emf, x->fBstar, 0.5);
-    km_update<<<gu, tu, 0, s>>>(x->dblk, x->dpre[3], x->nb, U, Pn, Ps, nullptr, x->F[0], x->F[1], x->F[2], GA,
-                                  x->S, x->dscalar + 3, 0.5, x->pflag, x->counters, face ? x->fBstar : nullptr);
+    km_update_any(x, gu, tu, U, Pn, Ps, nullptr, 0.5, face ? x->fBstar : nullptr);
     km_fixup<double><<<gz, MTPB, 0, s>>>(x->dblk, x->dpre[3], x->nb, Ps, nullptr, x->pflag, GA, x->S, x->counters);
     n += 2;
     // stage 2: P* -> P^{n+1}, U^{n+1}
     n += fill_ghosts(x, Ps);
     n += flux_pass<double, double>(x, Ps, x->F, x->ctop, x->emf, !face);
     if (face) n += face_ct_pass<double>(x, Ps, x->F, x->ecc, x->emf, x->fB, 1.0);
-    km_update<<<gu, tu, 0, s>>>(x->dblk, x->dpre[3], x->nb, U, Ps, Pn, U, x->F[0], x->F[1], x->F[2], GA, x->S,
-                                  x->dscalar + 3, 1.0, x->pflag, x->counters, face ? x->fB : nullptr);
+    km_update_any(x, gu, tu, U, Ps, Pn, U, 1.0, face ? x->fB : nullptr);
     km_fixup<double><<<gz, MTPB, 0, s>>>(x->dblk, x->dpre[3], x->nb, Pn, U, x->pflag, GA, x->S, x->counters);
     n += 2;
     n += cfl_pass<double>(x, x->ctop);
@@ -1204,18 +1233,14 @@ int issue_mesh_step(kh_mesh* x, double* U, double* P, double* B) {
     const float* ce[3] = {face ? nullptr : x->emff[0], face ? nullptr : x->emff[1], face ? nullptr : x->emff[2]};
     n += flux_pass<float, float>(x, Pnf, x->Ff, x->ctopf, x->emff, !face, true);
     if (face) n += face_ct_pass<float>(x, Pnf, x->Ff, x->eccf, x->emff, x->fBstar, 0.5);
-    km_update_mixed<<<gu, tu, 0, s>>>(x->dblk, x->dpre[3], x->nb, U, Pnf, none64, Psf, nullptr, x->Ff[0],
-                                        x->Ff[1], x->Ff[2], GA, x->S, x->dscalar + 3, 0.5, x->pflag, x->counters,
-                                        face ? x->fBstar : nullptr, ce[0], ce[1], ce[2]);
+    km_update_mixed_any(x, gu, tu, U, Pnf, none64, Psf, nullptr, 0.5, face ? x->fBstar : nullptr, ce);
     km_fixup<float><<<gz, MTPB, 0, s>>>(x->dblk, x->dpre[3], x->nb, Psf, nullptr, x->pflag, GA, x->S, x->counters);
     n += 2;
     // stage 2: FP32 P* -> FP64 P^{n+1}, U^{n+1}
     n += fill_ghosts(x, Psf);
     n += flux_pass<float, float>(x, Psf, x->Ff, x->ctopf, x->emff, !face, true);
     if (face) n += face_ct_pass<float>(x, Psf, x->Ff, x->eccf, x->emff, x->fB, 1.0);
-    km_update_mixed<<<gu, tu, 0, s>>>(x->dblk, x->dpre[3], x->nb, U, Psf, Pn, none32, U, x->Ff[0], x->Ff[1],
-                                        x->Ff[2], GA, x->S, x->dscalar + 3, 1.0, x->pflag, x->counters,
-                                        face ? x->fB : nullptr, ce[0], ce[1], ce[2]);
+    km_update_mixed_any(x, gu, tu, U, Psf, Pn, none32, U, 1.0, face ? x->fB : nullptr, ce);
     km_fixup<double><<<gz, MTPB, 0, s>>>(x->dblk, x->dpre[3], x->nb, Pn, U, x->pflag, GA, x->S, x->counters);
     n += 2;
     n += cfl_pass<float>(x, x->ctopf);

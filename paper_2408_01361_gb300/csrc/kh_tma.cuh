@@ -52,21 +52,6 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* tm, in
       : "memory");
 }
 
-// L2 prefetch of a tensor box (no shared memory, no completion to wait for):
-// warms L2 for a tile a later CTA will stage.
-__device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap* tm, int c0, int c1, int c2) {
-  asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(
-                   reinterpret_cast<unsigned long long>(tm)),
-               "r"(c0), "r"(c1), "r"(c2)
-               : "memory");
-}
-__device__ __forceinline__ void tma_prefetch_4d(const CUtensorMap* tm, int c0, int c1, int c2, int c3) {
-  asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];" ::"l"(
-                   reinterpret_cast<unsigned long long>(tm)),
-               "r"(c0), "r"(c1), "r"(c2), "r"(c3)
-               : "memory");
-}
-
 // Thread 0 of a CTA waits for its staged tiles (phase 0 of bar) with at most
 // wlim polls. On a timeout it counts it (CNT_TIMEOUT) and keeps polling --
 // up to KH_WAIT_POLLS more times -- until the copies it issued have landed,

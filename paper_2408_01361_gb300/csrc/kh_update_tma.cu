@@ -76,10 +76,6 @@ struct UpdateMaps {
   CUtensorMap p, f1, f2, f3, e1, e2, e3, u;
 };
 
-// CTAs resident at once on the GPU (152 SMs x 3): the tile this many CTAs
-// ahead is staged about one wave later, and its L2 prefetch is issued now.
-constexpr int WAVE = 152 * 3;
-
 template <int INV>
 __global__ void __launch_bounds__(TX * TY, 3)
     k_update_mixed_tma(const __grid_constant__ UpdateMaps tm, Vars Pout64, VarsT<float> Pout32, double* Uout,
@@ -103,24 +99,6 @@ __global__ void __launch_bounds__(TX * TY, 3)
     tma_load_3d(smem + O_E2, &tm.e2, x0, j0, k, bar);
     tma_load_3d(smem + O_E3, &tm.e3, x0, j0, k, bar);
     tma_load_4d(smem + O_U, &tm.u, xu0, j0, k, 0, bar);
-    // warm L2 for the tile one wave ahead (its fluxes and EMFs were written
-    // by the previous kernels and are mostly evicted; prefetches past the
-    // grid or the arrays are simply not issued or read nothing)
-    const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
-    const unsigned b = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z) + WAVE;
-    if (b < nb) {
-      const int bx = (int)(b % gridDim.x), by = (int)((b / gridDim.x) % gridDim.y), bz = (int)(b / (gridDim.x * gridDim.y));
-      const int pi0 = L.s[0] + TX * bx, pj0 = L.s[1] + TY * by, pk = L.s[2] + bz;
-      const int px0 = pi0 & ~3;
-      tma_prefetch_4d(&tm.p, px0, pj0, pk, 0);
-      tma_prefetch_4d(&tm.f1, px0, pj0, pk, 0);
-      tma_prefetch_4d(&tm.f2, px0, pj0, pk, 0);
-      tma_prefetch_4d(&tm.f3, px0, pj0, pk, 0);
-      tma_prefetch_3d(&tm.e1, px0, pj0, pk);
-      tma_prefetch_3d(&tm.e2, px0, pj0, pk);
-      tma_prefetch_3d(&tm.e3, px0, pj0, pk);
-      tma_prefetch_4d(&tm.u, pi0 & ~1, pj0, pk, 0);
-    }
   }
   if (!cta_wait_tiles(bar, wlim, cnt)) return;
   const int i = i0 + lx, j = j0 + ly;

@@ -446,6 +446,31 @@ struct MixedInGlobal {
   __device__ __forceinline__ bool has_emf() const { return ect.e[2] != nullptr; }
 };
 
+// The FP64 inversion of a zone whose double-float iteration handed it back
+// (C2P_NEED_FP64; a handful of zones per step once the flow has settled): the
+// FP64 solver from the FP32 stage input (Pin8) as the guess. Kept out of line
+// so that the update's hot path -- long straight-line code whose instruction
+// fetch already stalls it -- does not carry the FP64 solver. Returns the
+// solver's flag; on success Pn5 holds the fluid primitives.
+template <int INV>
+__device__ __noinline__ int mixed_fp64_fallback(const df64* Ud, const float* Pin8, DevGeom G, long long gplane,
+                                                long long p, double gam, double igam, double gfac, C2POpts o,
+                                                df64* Pn5) {
+  double Uf[NV], Pd[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    Uf[v] = f64_of_df(Ud[v]);
+    Pd[v] = f64_of_f32(Pin8[v]);
+  }
+  const Met<double> m = load_met(G, gplane, LOC_CENT, p);
+  const int flag = invert<INV>(Uf, m, __ldg(G.flo + 2 * gplane + p), gam, igam, gfac, o, Pd);
+  if (flag == 0) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) Pn5[v] = df_of_f64(Pd[v]);
+  }
+  return flag;
+}
+
 // The end of the mixed update when its inversion stays in FP64 for every
 // zone (kh_coords.mixed_inversion = KH_MIXINV_FP64, the precision split that
 // keeps the whole Noble-2D inversion in FP64): U holds the FP64 conserved
@@ -625,19 +650,20 @@ __device__ __forceinline__ void update_mixed_zone_in(const IN& in, const Vars& P
   int flag = C2P_NEED_FP64;
   if constexpr (INV == C2P_NOBLE2D) flag = noble2d_df(Ud, md, mx, W0, vsq0, Pn);
   if (flag == C2P_NEED_FP64) {
-    // FP64 inversion of this zone from the stage input
+    // FP64 inversion of this zone from the stage input (out of line; the
+    // arrays it takes are copies, so that Ud and Pn stay in registers)
     if (!TRIAL && INV == C2P_NOBLE2D) atomicAdd(cnt + CNT_FP64, 1ULL);
-    double Uf[NV], Pd[NV];
+    df64 Uc[NV], P5[5];
+    float Pi[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      Uf[v] = f64_of_df(Ud[v]);
-      Pd[v] = f64_of_f32(in.pin(v));
+      Uc[v] = Ud[v];
+      Pi[v] = in.pin(v);
     }
-    const Met<double> m = load_met(G, L.gplane, LOC_CENT, p);
-    flag = invert<INV>(Uf, m, __ldg(G.flo + 2 * L.gplane + p), S.gam, S.igam, S.gfac, S.c2p, Pd);
+    flag = mixed_fp64_fallback<INV>(Uc, Pi, G, L.gplane, p, S.gam, S.igam, S.gfac, S.c2p, P5);
     if (flag == 0) {
 #pragma unroll
-      for (int v = 0; v < 5; ++v) Pn[v] = df_of_f64(Pd[v]);
+      for (int v = 0; v < 5; ++v) Pn[v] = P5[v];
     }
   }
   if (TRIAL && flag) {

@@ -74,26 +74,27 @@ def test_face_ct_validation_without_gpu():
                                  ctypes.byref(h)) == -1
 
 
-def test_mixed_inversion_validation_without_gpu():
-    """mixed_inversion outside {df, fp64} is refused; the refined mesh keeps the
-    double-float inversion and refuses fp64."""
+def test_mixed_inversion_and_solver_validation_without_gpu():
+    """mixed_inversion outside {df, fp64} and an unknown solver are refused by
+    single grids and the refined mesh; the mesh accepts every solver and both
+    mixed inversions (validation passes; the call then needs a device:
+    KH_ECUDA here, KH_OK on a GPU)."""
     from paper_2408_01361_gb300 import inputs, kh
     cfg = dict(inputs.linear_mode_cfg(8, ndim=3), precision="mixed")
     h = ctypes.c_void_p()
-    c = kh.coords_from_cfg(cfg)
-    c.mixed_inversion = 2
-    assert kh.lib().kh_geometry_init(0.0, ctypes.byref(c), float(cfg["gam"]), ctypes.byref(h)) == -1
     blk = kh.Block(0, 0, 0, 0, 8, 8, 8)
-    c = kh.coords_from_cfg(dict(cfg, mixed_inversion="fp64"))
-    assert kh.lib().kh_mesh_init(0.0, ctypes.byref(c), float(cfg["gam"]), 1, ctypes.byref(blk),
-                                 ctypes.byref(h)) == -1
-    # the same mesh with the double-float inversion passes validation (it then
-    # needs a device: KH_ECUDA here, KH_OK on a GPU)
-    c = kh.coords_from_cfg(cfg)
-    rc = kh.lib().kh_mesh_init(0.0, ctypes.byref(c), float(cfg["gam"]), 1, ctypes.byref(blk), ctypes.byref(h))
-    assert rc != -1
-    if rc == 0:
-        kh.lib().kh_mesh_destroy(h)
+    for field, bad in (("mixed_inversion", 2), ("inverter", 3)):
+        c = kh.coords_from_cfg(cfg)
+        setattr(c, field, bad)
+        assert kh.lib().kh_geometry_init(0.0, ctypes.byref(c), float(cfg["gam"]), ctypes.byref(h)) == -1
+        assert kh.lib().kh_mesh_init(0.0, ctypes.byref(c), float(cfg["gam"]), 1, ctypes.byref(blk),
+                                     ctypes.byref(h)) == -1
+    for over in (dict(mixed_inversion="fp64"), dict(inverter="1dw"), dict(inverter="kastaun")):
+        c = kh.coords_from_cfg(dict(cfg, **over))
+        rc = kh.lib().kh_mesh_init(0.0, ctypes.byref(c), float(cfg["gam"]), 1, ctypes.byref(blk), ctypes.byref(h))
+        assert rc != -1, over
+        if rc == 0:
+            kh.lib().kh_mesh_destroy(h)
 
 
 def test_wait_limit_rejects_a_null_context_without_gpu():

@@ -6,7 +6,7 @@ uneven blocks at one level equal to the single-grid CUDA step."""
 import numpy as np
 import pytest
 
-from gpu_helpers import TOL, GpuRun, interior, rel_l1
+from gpu_helpers import TOL, GpuRun, assert_fp64_parity, elem_err, interior, rel_l1
 from mesh_cases import (block_interior, blk, box_two_level, mode_states, slice_blocks, torus_base, torus_states,
                         torus_three_level, torus_two_level, uneven_split)
 from paper_2408_01361_gb300 import inputs
@@ -171,6 +171,53 @@ def test_mesh_mixed_error_vs_oracle(kh, orc, OM):
         assert np.abs(a[v] - r[v]).sum() / den < tol, ("U", v)
         pden = max(np.abs(pr[v]).sum(), 1e-2 * nz if v in (2, 3, 4) else 0.0)
         assert np.abs(pa[v] - pr[v]).sum() / pden < tol, ("P", v)
+
+
+def _mesh_run(kh, base, blocks, Ps, U0, dt, nsteps, **over):
+    m = kh.Mesh(dict(base, **over), blocks)
+    P, B = m.to_device(Ps)
+    U = m.cons_to_device(U0)
+    nf = []
+    for _ in range(nsteps):
+        _, nfail = m.step(U, P, B, dt)
+        nf.append(nfail)
+    return m.cons_to_host(U), m.to_host(P, B), nf
+
+
+@pytest.mark.parametrize("inverter", ["1dw", "kastaun"])
+def test_mesh_other_solvers(kh, orc, OM, inverter):
+    """The refined mesh with the one-unknown (1D_W) and bracketed (Kastaun)
+    solvers, its update kernels instantiated per solver. On the two-level 3-D
+    box (no inversion fails) the FP64 mesh equals the oracle's mesh step
+    (its own bracketed 1D_w inversion: every solver finds the same root)
+    within the FP64 bar; the mixed mesh (these solvers invert in FP64 there)
+    equals the double-float Noble-2D mixed mesh within 1e-5 element-wise
+    (the same FP32 stencil; the inversions agree far below FP32)."""
+    base, blocks, Ps = _case("box_weno5")
+    U0, dt, Uo, Po, hist = _oracle_run(orc, OM, base, blocks, Ps, 2)
+    assert all(h[1][0] == 0 for h in hist)
+    Ug, Pg, nf = _mesh_run(kh, base, blocks, Ps, U0, dt, 2, inverter=inverter)
+    assert nf == [0, 0]
+    assert_fp64_parity(_flat(base, blocks, Ug), _flat(base, blocks, Uo), "U")
+    assert_fp64_parity(_flat(base, blocks, Pg), _flat(base, blocks, Po), "P")
+    Um, Pm, _ = _mesh_run(kh, base, blocks, Ps, U0, dt, 2, precision="mixed", inverter=inverter)
+    Ud, Pd, _ = _mesh_run(kh, base, blocks, Ps, U0, dt, 2, precision="mixed")
+    assert elem_err(_flat(base, blocks, Um), _flat(base, blocks, Ud)).max() < 1e-5
+    assert elem_err(_flat(base, blocks, Pm), _flat(base, blocks, Pd)).max() < 1e-5
+
+
+def test_mesh_mixed_fp64_inversion(kh, orc, OM):
+    """The mixed mesh with the whole inversion and the floors in FP64 for
+    every zone: the same failed zones as the oracle's mesh, and its state
+    within 1e-4 element-wise of the double-float mixed mesh (as on single
+    grids: the FP32 floor decisions and P* rounding remain)."""
+    base, blocks, Ps = _case("torus2_weno5")
+    U0, dt, Uo, Po, hist = _oracle_run(orc, OM, base, blocks, Ps, 1)
+    Uf, Pf, nf = _mesh_run(kh, base, blocks, Ps, U0, dt, 1, precision="mixed", mixed_inversion="fp64")
+    assert nf[0] == hist[0][1][0]
+    Ud, Pd, _ = _mesh_run(kh, base, blocks, Ps, U0, dt, 1, precision="mixed")
+    assert elem_err(_flat(base, blocks, Uf), _flat(base, blocks, Ud)).max() < 1e-4
+    assert elem_err(_flat(base, blocks, Pf), _flat(base, blocks, Pd)).max() < 1e-4
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
