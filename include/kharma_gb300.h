@@ -251,9 +251,14 @@ int kh_face_divb(kh_ctx* ctx, const double* fB, double* max_abs, double* l1);
 
 /* The interior state in a compact order, for moving it to and from the host
  * with the ghost cells and row padding left out: kh_pack_state writes
- * out[16][n3][n2][n1] (device) = U's 8 slots, then P's 5 and B's 3, of the
- * interior zones; kh_unpack_state writes them back into the padded layout
- * (interior cells only). Asynchronous on the context stream. */
+ * out[16][n3][n2][n1] = U's 8 slots, then P's 5 and B's 3, of the interior
+ * zones; kh_unpack_state writes them back into the padded layout (interior
+ * cells only). out / in may be device memory or page-locked host memory
+ * (cudaHostAlloc, or cudaHostRegister'ed; under unified addressing it is
+ * mapped into the device address space at the same address): the kernels
+ * then read or write it over the host link directly, with no separate copy.
+ * Asynchronous on the context stream (synchronise before the host reads a
+ * packed host buffer, or reuses one being unpacked). */
 int kh_pack_state(kh_ctx* ctx, const double* U, const double* P, const double* B, double* out);
 int kh_unpack_state(kh_ctx* ctx, const double* in, double* U, double* P, double* B);
 

@@ -52,30 +52,44 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* tm, in
       : "memory");
 }
 
-// Thread 0 of a CTA waits for its staged tiles (phase 0 of bar) with at most
-// wlim polls. On a timeout it counts it (CNT_TIMEOUT) and keeps polling --
-// up to KH_WAIT_POLLS more times -- until the copies it issued have landed,
-// so that none outlives the CTA's shared memory (a drain that also runs out
-// is counted as CNT_DRAIN). Returns, to every thread of the CTA, whether the
-// tiles arrived in time; all threads then observe the completed phase.
-__device__ __forceinline__ bool cta_wait_tiles(unsigned long long* bar, unsigned wlim, unsigned long long* cnt) {
+// Thread 0 of a CTA waits for the phase of parity `phase` of bar (its staged
+// tiles) with at most wlim polls. On a timeout it counts it (CNT_TIMEOUT) and
+// keeps polling -- up to KH_WAIT_POLLS more times -- until the copies it
+// issued have landed: the one on bar and, if `other` is given, the one on
+// other (phase other_phase), so that none outlives the CTA's shared memory
+// (a drain that also runs out is counted as CNT_DRAIN). Returns, to every
+// thread of the CTA, whether the tiles arrived in time; all threads then
+// observe the completed phase.
+__device__ __forceinline__ bool cta_wait_tiles2(unsigned long long* bar, unsigned phase, unsigned wlim,
+                                                unsigned long long* cnt, unsigned long long* other,
+                                                unsigned other_phase) {
   __shared__ int ready;
   if (threadIdx.x == 0) {
     bool ok = false;
-    for (unsigned spins = 0; spins < wlim && !ok; ++spins) ok = mbar_try_wait(bar, 0);
+    for (unsigned spins = 0; spins < wlim && !ok; ++spins) ok = mbar_try_wait(bar, phase);
     if (!ok) {
       atomicAdd(cnt + CNT_TIMEOUT, 1ULL);
       bool landed = false;
-      for (unsigned r = 0; r < KH_WAIT_POLLS && !landed; ++r) landed = mbar_try_wait(bar, 0);
+      for (unsigned r = 0; r < KH_WAIT_POLLS && !landed; ++r) landed = mbar_try_wait(bar, phase);
+      if (other) {
+        bool landed2 = false;
+        for (unsigned r = 0; r < KH_WAIT_POLLS && !landed2; ++r) landed2 = mbar_try_wait(other, other_phase);
+        landed = landed && landed2;
+      }
       if (!landed) atomicAdd(cnt + CNT_DRAIN, 1ULL);
     }
     ready = ok ? 1 : 0;
   }
   __syncthreads();
   if (!ready) return false;
-  for (unsigned r = 0; r < KH_WAIT_POLLS && !mbar_try_wait(bar, 0); ++r) {  // completed: returns at once
+  for (unsigned r = 0; r < KH_WAIT_POLLS && !mbar_try_wait(bar, phase); ++r) {  // completed: returns at once
   }
   return true;
+}
+
+// The same for a CTA with one copy in flight, on the first phase of bar.
+__device__ __forceinline__ bool cta_wait_tiles(unsigned long long* bar, unsigned wlim, unsigned long long* cnt) {
+  return cta_wait_tiles2(bar, 0, wlim, cnt, nullptr, 0);
 }
 #endif
 

@@ -267,7 +267,8 @@ class Context:
 
     # ---- compact interior state ----
     def pack_state(self, U, P, B, out):
-        """out (device, 16 x interior zones): U's 8 slots, then P's 5 and B's 3."""
+        """out (16 x interior zones; device, or pinned host memory written over
+        the host link): U's 8 slots, then P's 5 and B's 3."""
         _check(lib().kh_pack_state(self._h, _ptr(U), _ptr(P), _ptr(B), _ptr(out)), "kh_pack_state")
 
     def unpack_state(self, inp, U, P, B):

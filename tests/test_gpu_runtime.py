@@ -104,3 +104,30 @@ def test_pack_unpack_state_round_trip(kh):
     N1 = P.shape[3]
     assert np.array_equal(ctx.to_host(U2, N1)[sl], ctx.to_host(g.U, N1)[sl])
     assert np.array_equal(ctx.to_host(PB2, N1)[sl], ctx.to_host(g.PB, N1)[sl])
+
+
+def test_pack_unpack_state_through_pinned_host_memory(kh):
+    """The compact state read and written straight from page-locked host
+    memory (the kernels address it over the host link; no separate copy):
+    identical to the device-buffer path."""
+    cfg = inputs.torus_cfg(40, 24, 10, r_out=60.0)
+    P = inputs.torus_state(cfg, seed=2)
+    ctx = kh.Context(cfg)
+    g = GpuRun(ctx, cfg, P)
+    torch = ctx.torch
+    nz = cfg["n1"] * cfg["n2"] * cfg["n3"]
+    dev = torch.empty(16 * nz, dtype=torch.float64, device=ctx.device)
+    host = torch.full((16 * nz,), -1.0, dtype=torch.float64, pin_memory=True)
+    ctx.pack_state(g.U, g.P, g.B, dev)
+    ctx.pack_state(g.U, g.P, g.B, host)
+    torch.cuda.synchronize()
+    assert np.array_equal(host.numpy(), dev.cpu().numpy())
+    host.mul_(1.0 + 1e-3)  # a different state, written by the host
+    U2, PB2 = ctx.empty(8), ctx.empty(8)
+    P2, B2 = ctx.split(PB2)
+    ctx.unpack_state(host, U2, P2, B2)
+    U3, PB3 = ctx.empty(8), ctx.empty(8)
+    P3, B3 = ctx.split(PB3)
+    ctx.unpack_state(host.to(ctx.device), U3, P3, B3)
+    torch.cuda.synchronize()
+    assert torch.equal(U2, U3) and torch.equal(PB2, PB3)

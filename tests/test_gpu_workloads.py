@@ -6,7 +6,7 @@ level), and the periodic vortex conserves its totals."""
 import numpy as np
 import pytest
 
-from gpu_helpers import TOL, GpuRun, interior, rel_l1
+from gpu_helpers import ELEM_TOL, TOL, GpuRun, elem_err, interior, rel_l1
 from paper_2408_01361_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -43,9 +43,12 @@ def test_workload_parity(kh, orc, which, recon):
     Ug, Pg = g.host()
     eu = rel_l1(interior(cfg, Ug), interior(cfg, Uc))
     ep = rel_l1(interior(cfg, Pg), interior(cfg, Pc))
+    xu = elem_err(interior(cfg, Ug), interior(cfg, Uc))
+    xp = elem_err(interior(cfg, Pg), interior(cfg, Pc))
     for v in range(8):
         if np.abs(interior(cfg, Pc)[v]).max() > 1e-10:
             assert eu[v] < TOL and ep[v] < TOL, (v, eu, ep)
+            assert xu[v] < ELEM_TOL and xp[v] < ELEM_TOL, (v, xu, xp)
 
 
 def _run_to(kh, cfg, P, t_end):
