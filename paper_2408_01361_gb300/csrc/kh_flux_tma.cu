@@ -45,7 +45,6 @@ namespace {
 
 constexpr int NT = 256;    // threads = cells reconstructed per tile
 constexpr int CW = 32;     // cells per tile row along x1
-constexpr int RESIDENT = 152 * 4;  // CTAs resident at once (4 per SM: 64 registers, 41 KB shared memory each)
 
 // Both face values of one cell from its 5-point stencil (a, b, c, d, e):
 // hi at x = +1/2 (as weno5_plus(a, b, c, d, e)), lo at x = -1/2 (as
@@ -121,95 +120,97 @@ template <int D> struct TileShape {
   static constexpr int BZ = D == 3 ? 12 : 1;
 };
 
-// Tile (bx, by, bz) of direction D: the thread's face (i, j, k) and the
-// tensor coordinates (c0, c1, c2) of the tile's box; for x1 the box starts at
-// the 16-byte boundary at or below the stencil's first cell, dx cells earlier.
-template <int D>
-__device__ __forceinline__ void tile_origin(const Layout& L, int bx, int by, int bz, int lx, int ly, int& i, int& j,
-                                            int& k, int& c0, int& c1, int& c2, int& dx) {
+template <int D, int RECON>
+__global__ void __launch_bounds__(NT) k_flux_tma(const __grid_constant__ CUtensorMap tm, Layout L, GeomT<float> G,
+                                                 Scheme S, FaceBox box, float* F, float* ctop, int polar_lo,
+                                                 int polar_hi, unsigned long long* cnt, unsigned wlim) {
   using Sh = TileShape<D>;
-  dx = 0;
+  __shared__ alignas(128) float tile[NV * Sh::BZ * Sh::BY * Sh::BX];
+  __shared__ float sL[NV][NT], sR[NV][NT];
+  __shared__ alignas(8) unsigned long long bar;
+  const int tid = threadIdx.x;
+  const int lx = tid % CW, ly = tid / CW;
+  // tile origin (cell coordinates) and the tensor coordinates of the box; for
+  // x1 the box starts at the 16-byte boundary at or below the stencil's first
+  // cell, dx cells earlier
+  int i, j, k, c0, c1, c2, dx = 0;
   if (D == 1) {
-    const int f0 = L.s[0] + Sh::FX * bx;  // first face of the tile
-    const int j0 = (L.s[1] - 1) + Sh::FY * by;
-    k = L.ndim == 3 ? (L.s[2] - 1) + bz : 0;
+    const int f0 = L.s[0] + Sh::FX * blockIdx.x;  // first face of the tile
+    const int j0 = (L.s[1] - 1) + Sh::FY * blockIdx.y;
+    k = L.ndim == 3 ? (L.s[2] - 1) + (int)blockIdx.z : 0;
     c0 = (f0 - 3) & ~3;
     dx = (f0 - 3) - c0;
     i = f0 + lx;
     j = j0 + ly;
     c1 = j0, c2 = k;
   } else if (D == 2) {
-    const int x0 = CW * bx;
-    const int j0 = L.s[1] + Sh::FY * by;
-    k = L.ndim == 3 ? (L.s[2] - 1) + bz : 0;
+    const int x0 = CW * blockIdx.x;
+    const int j0 = L.s[1] + Sh::FY * blockIdx.y;
+    k = L.ndim == 3 ? (L.s[2] - 1) + (int)blockIdx.z : 0;
     i = x0 + lx;
     j = j0 + ly;
     c0 = x0, c1 = j0 - 3, c2 = k;
   } else {
-    const int x0 = CW * bx;
-    const int k0 = L.s[2] + Sh::FY * by;
-    j = (L.s[1] - 1) + bz;
+    const int x0 = CW * blockIdx.x;
+    const int k0 = L.s[2] + Sh::FY * blockIdx.y;
+    j = (L.s[1] - 1) + (int)blockIdx.z;
     i = x0 + lx;
     k = k0 + ly;
     c0 = x0, c1 = j, c2 = k0 - 3;
   }
-}
-
-// Reconstruct this thread's cell of the staged tile once, for both of its x^D
-// faces: the upper face value is the left state of the face above the cell
-// (sL), the lower one the right state of the face at its bottom (sR).
-template <int D, int RECON>
-__device__ __forceinline__ void recon_tile(const float* tile, int dx, int lx, int ly, float (*sL)[NT],
-                                           float (*sR)[NT]) {
-  using Sh = TileShape<D>;
-  auto at = [&](int v, int x, int y, int z) { return tile[((v * Sh::BZ + z) * Sh::BY + y) * Sh::BX + x]; };
+  if (tid == 0) mbar_init(&bar);
+  __syncthreads();
+  if (tid == 0) {
+    mbar_expect_tx(&bar, sizeof(float) * NV * Sh::BZ * Sh::BY * Sh::BX);
+    tma_load_4d(tile, &tm, c0, c1, c2, 0, &bar);
+  }
+  // bounded wait; on a timeout the CTA leaves (after its copy has landed)
+  // without writing its faces
+  if (!cta_wait_tiles(&bar, wlim, cnt)) return;
+  // ---- reconstruct this thread's cell once, for both of its x^D faces ----
   // cell cl along D (0 = the cell below the tile's first face), row across
-  const int cl = D == 1 ? lx : ly, row = D == 1 ? ly : lx;
-  // stencil of the cell: D = 1 at box x dx + cl .. dx + cl + 4 (the box
-  // holds the tile's cells from f0 - 3 on); D = 2, 3 at cl .. cl + 4 along
-  // the direction (the box starts 3 below the first face)
-  auto sten = [&](int v, int o) {
-    if (D == 1) return at(v, dx + cl + o, row, 0);
-    else if (D == 2) return at(v, row, cl + o, 0);
-    else return at(v, row, 0, cl + o);
-  };
-  auto put = [&](int v, float lo, float hi) {
-    if (D == 1) {
-      if (cl < Sh::FX) sL[v][row * CW + cl] = hi;
-      if (cl >= 1) sR[v][row * CW + cl - 1] = lo;
+  auto at = [&](int v, int x, int y, int z) { return tile[((v * Sh::BZ + z) * Sh::BY + y) * Sh::BX + x]; };
+  {
+    const int cl = D == 1 ? lx : ly, row = D == 1 ? ly : lx;
+    // stencil of the cell: D = 1 at box x dx + cl .. dx + cl + 4 (the box
+    // holds the tile's cells from f0 - 3 on); D = 2, 3 at cl .. cl + 4 along
+    // the direction (the box starts 3 below the first face)
+    auto sten = [&](int v, int o) {
+      if (D == 1) return at(v, dx + cl + o, row, 0);
+      else if (D == 2) return at(v, row, cl + o, 0);
+      else return at(v, row, 0, cl + o);
+    };
+    // hi is the left state of the face above the cell, lo the right state of the face at its bottom
+    auto put = [&](int v, float lo, float hi) {
+      if (D == 1) {
+        if (cl < Sh::FX) sL[v][row * CW + cl] = hi;
+        if (cl >= 1) sR[v][row * CW + cl - 1] = lo;
+      } else {
+        if (cl < Sh::FY) sL[v][cl * CW + row] = hi;
+        if (cl >= 1) sR[v][(cl - 1) * CW + row] = lo;
+      }
+    };
+    if (RECON == KH_RECON_MC) {
+      for (int v = 0; v < NV; ++v) {
+        float lo, hi;
+        recon_mc(sten(v, 1), sten(v, 2), sten(v, 3), lo, hi);
+        put(v, lo, hi);
+      }
     } else {
-      if (cl < Sh::FY) sL[v][cl * CW + row] = hi;
-      if (cl >= 1) sR[v][(cl - 1) * CW + row] = lo;
-    }
-  };
-  if (RECON == KH_RECON_MC) {
-    for (int v = 0; v < NV; ++v) {
-      float lo, hi;
-      recon_mc(sten(v, 1), sten(v, 2), sten(v, 3), lo, hi);
-      put(v, lo, hi);
-    }
-  } else {
-    for (int v = 0; v < NV; v += 2) {  // two variables per pass
-      P2 q[5];
+      for (int v = 0; v < NV; v += 2) {  // two variables per pass
+        P2 q[5];
 #pragma unroll
-      for (int o = 0; o < 5; ++o) q[o] = P2(sten(v, o), sten(v + 1, o));
-      P2 lo, hi;
-      weno5_lohi(q[0], q[1], q[2], q[3], q[4], lo, hi);
-      put(v, lo.v.x, hi.v.x);
-      put(v + 1, lo.v.y, hi.v.y);
+        for (int o = 0; o < 5; ++o) q[o] = P2(sten(v, o), sten(v + 1, o));
+        P2 lo, hi;
+        weno5_lohi(q[0], q[1], q[2], q[3], q[4], lo, hi);
+        put(v, lo.v.x, hi.v.x);
+        put(v + 1, lo.v.y, hi.v.y);
+      }
     }
   }
-}
-
-// The LLF flux of this thread's face (i, j, k) from its reconstructed left
-// and right states, if the thread has a face inside the face box.
-template <int D>
-__device__ __forceinline__ void face_flux(const float (*sL)[NT], const float (*sR)[NT], const Layout& L,
-                                          const GeomT<float>& G, const Scheme& S, const FaceBox& box, float* F,
-                                          float* ctop, int polar_lo, int polar_hi, int lx, int ly, int i, int j,
-                                          int k) {
-  using Sh = TileShape<D>;
+  __syncthreads();
   if ((D == 1 && lx >= Sh::FX) || (D != 1 && ly >= Sh::FY)) return;  // cells without a face of their own
+  // ---- the LLF flux of this thread's face ----
   const bool in_box = i >= box.lo[0] && i < box.lo[0] + box.n[0] && j >= box.lo[1] && j < box.lo[1] + box.n[1] &&
                       k >= box.lo[2] && k < box.lo[2] + box.n[2];
   if (!in_box) return;
@@ -244,59 +245,6 @@ __device__ __forceinline__ void face_flux(const float (*sL)[NT], const float (*s
   ctop[c] = ct;
 }
 
-// A persistent CTA walks the tiles t = blockIdx.x, + gridDim.x, ... of the
-// face pass (tile t = (t % gx, (t / gx) % gy, t / (gx gy))) with two tile
-// buffers: while it reconstructs and fluxes tile t it has already issued the
-// tensor copy of its next tile into the other buffer, so the copy overlaps
-// the arithmetic instead of stalling the CTA at its start. Buffer b's mbarrier
-// completes once per use; its n-th use waits for phase parity n & 1.
-template <int D, int RECON>
-__global__ void __launch_bounds__(NT, 4) k_flux_tma(const __grid_constant__ CUtensorMap tm, Layout L, GeomT<float> G,
-                                                 Scheme S, FaceBox box, float* F, float* ctop, int polar_lo,
-                                                 int polar_hi, unsigned long long* cnt, unsigned wlim, int gx,
-                                                 int gy, int ntiles) {
-  using Sh = TileShape<D>;
-  constexpr int TSZ = NV * Sh::BZ * Sh::BY * Sh::BX;
-  __shared__ alignas(128) float tile[2][TSZ];
-  __shared__ float sL[NV][NT], sR[NV][NT];
-  __shared__ alignas(8) unsigned long long bar[2];
-  const int tid = threadIdx.x;
-  const int lx = tid % CW, ly = tid / CW;
-  auto issue = [&](int t, int b) {
-    int i, j, k, c0, c1, c2, dx;
-    tile_origin<D>(L, t % gx, (t / gx) % gy, t / (gx * gy), 0, 0, i, j, k, c0, c1, c2, dx);
-    mbar_expect_tx(&bar[b], sizeof(float) * TSZ);
-    tma_load_4d(tile[b], &tm, c0, c1, c2, 0, &bar[b]);
-  };
-  if (tid == 0) {
-    mbar_init(&bar[0]);
-    mbar_init(&bar[1]);
-  }
-  __syncthreads();
-  int t = blockIdx.x;
-  if (tid == 0 && t < ntiles) issue(t, 0);
-  unsigned uses0 = 0, uses1 = 0;
-  for (int it = 0; t < ntiles; ++it, t += gridDim.x) {
-    const int b = it & 1;
-    const int tn = t + gridDim.x;
-    // the other buffer was last read in the previous iteration, which every
-    // thread has left (its closing barrier)
-    if (tid == 0 && tn < ntiles) issue(tn, b ^ 1);
-    const unsigned ph = (b ? uses1 : uses0) & 1u;
-    // bounded wait; on a timeout the CTA leaves after both of its copies in
-    // flight have landed, without writing this or later tiles' faces
-    if (!cta_wait_tiles2(&bar[b], ph, wlim, cnt, tn < ntiles ? &bar[b ^ 1] : nullptr, (b ? uses0 : uses1) & 1u))
-      return;
-    if (b) ++uses1; else ++uses0;
-    int i, j, k, c0, c1, c2, dx;
-    tile_origin<D>(L, t % gx, (t / gx) % gy, t / (gx * gy), lx, ly, i, j, k, c0, c1, c2, dx);
-    recon_tile<D, RECON>(tile[b], dx, lx, ly, sL, sR);
-    __syncthreads();
-    face_flux<D>(sL, sR, L, G, S, box, F, ctop, polar_lo, polar_hi, lx, ly, i, j, k);
-    __syncthreads();  // sL, sR and tile[b] free for reuse
-  }
-}
-
 // The 8 FP32 planes [v][k][j][i] as a 4-D tensor (i, j, k, v) with the box of
 // direction D.
 template <int D> bool encode(CUtensorMap* tm, const float* base, const Layout& L) {
@@ -315,21 +263,17 @@ int launch_d(const float* P8, const Layout& L, const GeomT<float>& G, const Sche
   const FaceBox b = face_box(L, D);
   const int plo = S.bc[2] == KH_BC_POLAR, phi = S.bc[3] == KH_BC_POLAR;
   using Sh = TileShape<D>;
-  int gx, gy, gz;
-  if (D == 1) {
-    gx = (L.n1 + 1 + Sh::FX - 1) / Sh::FX, gy = (L.n2 + 2 + Sh::FY - 1) / Sh::FY, gz = L.ndim == 3 ? L.n3 + 2 : 1;
-  } else if (D == 2) {
-    gx = (L.e[0] + 1 + CW - 1) / CW, gy = (L.n2 + 1 + Sh::FY - 1) / Sh::FY, gz = L.ndim == 3 ? L.n3 + 2 : 1;
-  } else {
-    gx = (L.e[0] + 1 + CW - 1) / CW, gy = (L.n3 + 1 + Sh::FY - 1) / Sh::FY, gz = L.n2 + 2;
-  }
-  const int ntiles = gx * gy * gz;
-  const int grid = ntiles < RESIDENT ? ntiles : RESIDENT;  // persistent CTAs, all resident at once
-  if (S.recon == KH_RECON_MC)
-    k_flux_tma<D, KH_RECON_MC><<<grid, NT, 0, s>>>(tm, L, G, S, b, F, ctop, plo, phi, cnt, wlim, gx, gy, ntiles);
+  dim3 grid;
+  if (D == 1)
+    grid = dim3((L.n1 + 1 + Sh::FX - 1) / Sh::FX, (L.n2 + 2 + Sh::FY - 1) / Sh::FY, L.ndim == 3 ? L.n3 + 2 : 1);
+  else if (D == 2)
+    grid = dim3((L.e[0] + 1 + CW - 1) / CW, (L.n2 + 1 + Sh::FY - 1) / Sh::FY, L.ndim == 3 ? L.n3 + 2 : 1);
   else
-    k_flux_tma<D, KH_RECON_WENO5><<<grid, NT, 0, s>>>(tm, L, G, S, b, F, ctop, plo, phi, cnt, wlim, gx, gy,
-                                                      ntiles);
+    grid = dim3((L.e[0] + 1 + CW - 1) / CW, (L.n3 + 1 + Sh::FY - 1) / Sh::FY, L.n2 + 2);
+  if (S.recon == KH_RECON_MC)
+    k_flux_tma<D, KH_RECON_MC><<<grid, NT, 0, s>>>(tm, L, G, S, b, F, ctop, plo, phi, cnt, wlim);
+  else
+    k_flux_tma<D, KH_RECON_WENO5><<<grid, NT, 0, s>>>(tm, L, G, S, b, F, ctop, plo, phi, cnt, wlim);
   return 1;
 }
 

@@ -109,8 +109,9 @@ __global__ void __launch_bounds__(TX * TY, 3)
                        reinterpret_cast<const float*>(smem + O_E1), reinterpret_cast<const float*>(smem + O_E2),
                        reinterpret_cast<const float*>(smem + O_E3), reinterpret_cast<const double*>(smem + O_U),
                        (i0 - x0) + lx, (i0 - xu0) + lx, ly};
-  update_mixed_zone_in<false, INV>(in, Pout64, Pout32, Uout, L, G, Gf, S, df_of_f64(coef * __ldg(dtp)), pflag, cnt,
-                                   i, j, k, fl, nullptr, dUout);
+  update_mixed_zone_in<false, INV, MixedInTile, true>(in, Pout64, Pout32, Uout, L, G, Gf, S,
+                                                      df_of_f64(coef * __ldg(dtp)), pflag, cnt, i, j, k, fl, nullptr,
+                                                      dUout);
 }
 
 template <int INV> bool set_smem_once() {
