@@ -123,7 +123,9 @@ def lib():
         L.or_evolve.restype = C.c_double
         L.or_divb.argtypes = [PP, _dp, _dp, C.c_void_p]
         L.or_stage.argtypes = [PP, _dp, _dp, C.c_double, _dp, _dp, C.c_void_p, C.c_void_p, C.c_void_p,
-                               C.POINTER(C.c_long)]
+                               C.POINTER(C.c_long), C.c_void_p]
+        L.or_rk_table.argtypes = [C.c_int, _ip, _ip, _dp, _dp, _dp]
+        L.or_rk_table.restype = C.c_int
         L.or_point_flux.argtypes = [C.c_double, _dp, _dp, C.c_int, _dp]
         L.or_point_state.argtypes = [_dp, _dp, _dp]
         L.or_point_speeds.argtypes = [C.c_double, _dp, _dp, C.c_int, C.POINTER(C.c_double),
@@ -362,16 +364,29 @@ def recon(kind: str, q):
     return lo, hi
 
 
-def stage(cfg: dict, U0, Pin, cdt: float, Uout, Pout):
+def stage(cfg: dict, U0, Pin, cdt: float, Uout, Pout, dU=None):
     """One stage on a grid with caller-filled ghosts; Uout/Pout updated in place
-    (interior). Returns (ctop[3] arrays, stats)."""
+    (interior); dU (optional, full array) receives the raw increment
+    cdt (-div F + S) of every interior zone. Returns (ctop[3] arrays, stats)."""
     U0 = np.ascontiguousarray(U0, dtype=np.float64)
     Pin = np.ascontiguousarray(Pin, dtype=np.float64)
     ct = [np.zeros(Pin.shape[1:]) for _ in range(3)]
     st = (C.c_long * 4)()
-    lib().or_stage(C.byref(params(cfg)), U0, Pin, float(cdt), Uout, Pout, *[_ptr(c) for c in ct], st)
+    lib().or_stage(C.byref(params(cfg)), U0, Pin, float(cdt), Uout, Pout, *[_ptr(c) for c in ct], st, _ptr(dU))
     _note(st)
     return ct, list(st)[:3]
+
+
+def rk_table(integrator: str):
+    """The stages of a Runge-Kutta integrator ("rk1", "rk2", "ssprk54") in
+    Shu-Osher form: a list of (sources, weights, c_s, weight of stage 4's raw
+    increment); stage s forms sum_t w_t U_src_t (+ that increment term) and adds
+    c_s dt L(P_{s-1})."""
+    n = np.zeros(5, dtype=np.int32); src = np.zeros(15, dtype=np.int32)
+    a = np.zeros(15); cdt = np.zeros(5); du4 = np.zeros(5)
+    ns = lib().or_rk_table(INTEGRATOR[integrator], n, src, a, cdt, du4)
+    return [([int(src[3 * s + t]) for t in range(n[s])], [float(a[3 * s + t]) for t in range(n[s])],
+             float(cdt[s]), float(du4[s])) for s in range(ns)]
 
 
 def count_ops(cfg: dict, x1: float, x2: float, P):

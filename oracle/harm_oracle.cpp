@@ -1026,14 +1026,16 @@ double or_cfl_dt(const or_params* c, const double* P, const double* dir_lo, cons
 // multi-block mesh): fluxes from Pin, Uout = U0 + cdt (-div F + S(Pin)),
 // inversion, floors, fixup (interior neighbours only). Uout and Pout: full
 // arrays, interior written. ctop1..3 (nullable): signal speeds per face.
+// dU (nullable): the raw increment cdt (-div F + S(Pin)) of every interior
+// zone (a Runge-Kutta stage whose increment a later stage reuses).
 // stats[0..2] as or_step (this stage only).
 void or_stage(const or_params* c, const double* U0, const double* Pin, double cdt, double* Uout, double* Pout,
-              double* ct1, double* ct2, double* ct3, long* stats) {
+              double* ct1, double* ct2, double* ct3, long* stats, double* dU) {
   Grid gr;
   build_grid(*c, gr);
   Fluxes fx;
   StageStats st;
-  stage<double>(gr, U0, Pin, c->gam, cdt, Uout, Pout, fx, st, nullptr);
+  stage<double>(gr, U0, Pin, c->gam, cdt, Uout, Pout, fx, st, nullptr, nullptr, nullptr, nullptr, dU);
   double* Co[3] = {ct1, ct2, ct3};
   for (int d = 0; d < 3; ++d)
     if (Co[d]) std::memcpy(Co[d], fx.ctop[d].data(), fx.ctop[d].size() * sizeof(double));
@@ -1112,30 +1114,53 @@ double or_step_rk(const or_params* c, double* U, double* P, double dt, const dou
   return rk_step(c, U, P, nullptr, dt, dir_lo, dir_hi, stats);
 }
 
+// The stages of a Runge-Kutta integrator in Shu-Osher form: stage s forms
+// sum_t a[t] U_src[t] (+ dU4 times stage 4's raw increment) and adds
+// cdt dt L(P_{s-1}).
+struct RKStage {
+  int n;
+  int src[3];
+  double a[3];
+  double cdt;   // c_s
+  double dU4;   // weight of stage 4's raw increment (SSPRK(5,4) stage 5)
+};
+
+static std::vector<RKStage> rk_table(int integrator) {
+  if (integrator == INT_RK1) return {{1, {0}, {1.0}, 1.0, 0.0}};
+  if (integrator == INT_RK2) return {{1, {0}, {1.0}, 1.0, 0.0}, {2, {0, 1}, {0.5, 0.5}, 0.5, 0.0}};
+  if (integrator == INT_SSPRK54) {
+    const double c4 = 0.544974750228521, c53 = 0.063692468666290;
+    return {{1, {0}, {1.0}, 0.391752226571890, 0.0},
+            {2, {0, 1}, {0.444370493651235, 0.555629506348765}, 0.368410593050371, 0.0},
+            {2, {0, 2}, {0.620101851488403, 0.379898148511597}, 0.251891774271694, 0.0},
+            {2, {0, 3}, {0.178079954393132, 0.821920045606868}, c4, 0.0},
+            {3, {2, 3, 4}, {0.517231671970585, 0.096059710526147, 0.386708617503269}, 0.226007483236906, c53 / c4}};
+  }
+  return {};
+}
+
+// The table of an integrator for callers that run the stages themselves (a
+// refined mesh): per stage s (at most 5), n[s] sources src[3 s + t] with
+// weights a[3 s + t], cdt[s] and dU4[s]. Returns the number of stages (0 for
+// the predictor-corrector or an unknown integrator).
+int or_rk_table(int integrator, int* n, int* src, double* a, double* cdt, double* dU4) {
+  const std::vector<RKStage> S = rk_table(integrator);
+  for (size_t s = 0; s < S.size(); ++s) {
+    n[s] = S[s].n;
+    for (int t = 0; t < 3; ++t) {
+      src[3 * s + t] = t < S[s].n ? S[s].src[t] : 0;
+      a[3 * s + t] = t < S[s].n ? S[s].a[t] : 0.0;
+    }
+    cdt[s] = S[s].cdt;
+    dU4[s] = S[s].dU4;
+  }
+  return (int)S.size();
+}
+
 static double rk_step(const or_params* c, double* U, double* P, double* fB, double dt, const double* dir_lo,
                       const double* dir_hi, long* stats) {
-  struct RKStage {
-    int n;
-    int src[3];
-    double a[3];
-    double cdt;   // c_s
-    double dU4;   // weight of stage 4's raw increment (SSPRK(5,4) stage 5)
-  };
-  std::vector<RKStage> S;
-  if (c->integrator == INT_RK1) {
-    S = {{1, {0}, {1.0}, 1.0, 0.0}};
-  } else if (c->integrator == INT_RK2) {
-    S = {{1, {0}, {1.0}, 1.0, 0.0}, {2, {0, 1}, {0.5, 0.5}, 0.5, 0.0}};
-  } else if (c->integrator == INT_SSPRK54) {
-    const double c4 = 0.544974750228521, c53 = 0.063692468666290;
-    S = {{1, {0}, {1.0}, 0.391752226571890, 0.0},
-         {2, {0, 1}, {0.444370493651235, 0.555629506348765}, 0.368410593050371, 0.0},
-         {2, {0, 2}, {0.620101851488403, 0.379898148511597}, 0.251891774271694, 0.0},
-         {2, {0, 3}, {0.178079954393132, 0.821920045606868}, c4, 0.0},
-         {3, {2, 3, 4}, {0.517231671970585, 0.096059710526147, 0.386708617503269}, 0.226007483236906, c53 / c4}};
-  } else {
-    return -1.0;
-  }
+  const std::vector<RKStage> S = rk_table(c->integrator);
+  if (S.empty()) return -1.0;
   Grid gr;
   build_grid(*c, gr);
   const size_t n = gr.cells() * NVAR;

@@ -22,7 +22,9 @@ ghost cell's centre:
   edge of the domain or inside a still coarser block.
 
 Every block takes the same dt; there is no flux correction at level
-interfaces. Written from positions in floating point, independently of the
+interfaces. step advances every block with the predictor-corrector, step_rk
+with a Runge-Kutta integrator (each stage's input ghost-filled across blocks
+before the blocks' stages). Written from positions in floating point, independently of the
 CUDA library's integer map.
 
 With face-centred constrained transport (step_face) every block also
@@ -40,7 +42,7 @@ import math
 
 import numpy as np
 
-from . import face_emfs, stage, stage_face
+from . import face_emfs, rk_table, stage, stage_face
 
 NV = 8
 
@@ -259,6 +261,40 @@ class OracleMesh:
             cts.append(ct)
             tot = [a + c for a, c in zip(tot, st)]
         return Uout, Pout, self.cfl_dt(cts), tot
+
+    def step_rk(self, Us, Ps, dt, integrator):
+        """One Runge-Kutta step ("rk1", "rk2" or "ssprk54") of every block:
+        the stages of the oracle's single-grid Runge-Kutta step (its table,
+        rk_table), each stage input's ghost zones filled across blocks before
+        the blocks' stages; returns (Us, Ps, dt_cfl, stats)."""
+        table = rk_table(integrator)
+        nb = len(Us)
+        Ust = [[np.array(U, copy=True) for U in Us]]
+        Pst = [[np.array(P, copy=True) for P in Ps]]
+        dU4 = [np.zeros_like(U) for U in Us]
+        tot = [0, 0, 0]
+        cts = []
+        for s, (src, w, c, w4) in enumerate(table):
+            Pin = Pst[s]
+            self.fill_ghosts(Pin)
+            keep = integrator == "ssprk54" and s == 3
+            Uout, Pout, cts = [], [], []
+            for b in range(nb):
+                base = 0.0
+                for t, a in zip(src, w):
+                    base = base + a * Ust[t][b]
+                if w4 != 0.0:
+                    base = base + w4 * dU4[b]
+                Ub = np.array(base, copy=True)
+                Pb = np.array(Pin[b], copy=True)
+                ct, st = stage(self.cfgs[b], base, Pin[b], c * dt, Ub, Pb, dU=dU4[b] if keep else None)
+                cts.append(ct)
+                tot = [x + y for x, y in zip(tot, st)]
+                Uout.append(Ub)
+                Pout.append(Pb)
+            Ust.append(Uout)
+            Pst.append(Pout)
+        return Ust[-1], Pst[-1], self.cfl_dt(cts), tot
 
     # ---- face-centred constrained transport ----
     def _edge_ranges(self, b, c):
