@@ -563,17 +563,20 @@ def measure_workloads(args, dev, stream, n=2048):
     return out
 
 
-def measure_smr(args, dev, stream, precision, face=False):
+def measure_smr(args, dev, stream, precision, face=False, integrator="vl2"):
     """The statically refined torus (3 levels, 592 uneven blocks, 5.57 M zones)
     stepped as one mesh: every kernel covers all blocks, ghost zones of every
     block are filled by one gather, the step is replayed as a CUDA graph.
     face: face-centred CT with interface-matched upwinded EMFs (the loop
-    field curled onto every block's faces from the shared corner potential)."""
+    field curled onto every block's faces from the shared corner potential).
+    integrator: the time integrator ("vl2": the predictor-corrector; "rk1",
+    "rk2", "ssprk54": Runge-Kutta stages over the whole mesh)."""
     import torch
 
     from paper_2408_01361_gb300 import inputs, kh
 
     base, blocks = inputs.smr_torus_layout()
+    base = dict(base, integrator=integrator)
     if face:
         base = dict(base, bfield="face", emf="gs05")
     norms = inputs.torus_norms(base)
@@ -615,7 +618,8 @@ def measure_smr(args, dev, stream, precision, face=False):
     out = {
         "workload": "FM torus (as above) on 3 static refinement levels: level 2 over the disc, level 1 around "
                     f"it, level 0 at the poles and outer radii; base {base['n1']}x{base['n2']}x{base['n3']}"
-                    + ("; face-centred CT, interface-matched upwinded EMFs" if face else ""),
+                    + ("; face-centred CT, interface-matched upwinded EMFs" if face else "")
+                    + (f"; integrator {integrator}" if integrator != "vl2" else ""),
         "precision": precision, "dtype": DTYPE[precision], "blocks": len(blocks), "block_shapes": dict(shapes),
         "zones": m.zones, "ghost_cells": m.ghost_cells, "value": m.zones * args.steps / (ms * 1e-3), "unit": UNIT,
         "ms_per_step": ms / args.steps, "graph": True, "gpu_launches": m.launches() - l0, "clocks": clocks,
@@ -765,7 +769,8 @@ def run_kh(args, world, rank, local):
 
     if args.smr_only:
         out = {p: measure_smr(args, dev, stream, p) for p in args.precisions}
-        print(json.dumps({"smr": out}), flush=True)
+        rk = {"mixed": measure_smr(args, dev, stream, "mixed", integrator="ssprk54")}
+        print(json.dumps({"smr": out, "smr_ssprk54": rk}), flush=True)
         return 0
 
     cfg64 = workload_cfg(args.n3)
@@ -842,6 +847,7 @@ def run_kh(args, world, rank, local):
     if not args.no_smr and world == 1:
         line["smr"] = {p: measure_smr(args, dev, stream, p) for p in args.precisions}
         line["smr_face_ct"] = {p: measure_smr(args, dev, stream, p, face=True) for p in args.precisions}
+        line["smr_ssprk54"] = {"mixed": measure_smr(args, dev, stream, "mixed", integrator="ssprk54")}
     if not args.no_cube and world == 1:
         line["torus_128cubed"] = {p: measure_cube(args, dev, stream, p) for p in args.precisions}
         line["torus_128cubed"]["context"] = "paper: ~35 M zone-cycles/s per A100 GPU on 128^3 production problems"

@@ -441,6 +441,16 @@ int kh_mesh_set_graph(kh_mesh* mesh, int enable);
  * reconstruction, precision). Results are bitwise independent of the choice. */
 int kh_mesh_set_launch(kh_mesh* mesh, int tpb_flux, int tpb_update);
 int kh_mesh_get_launch(const kh_mesh* mesh, int* tpb_flux, int* tpb_update);
+/* The mixed mesh's update with its inputs staged in shared memory by TMA
+ * tensor copies (as kh_step's on 3-D grids), used when the mesh qualifies:
+ * KH_MIXED, 3-D, Flux-CT, Noble-2D, every block 16 or 32 zones wide along x1,
+ * and the U passed to kh_mesh_step 16-byte aligned (its tensor maps are
+ * rebuilt, and copied to the device on the mesh's stream, whenever the step
+ * is handed another U). enable = 0 selects the update that loads its inputs
+ * itself; results are bitwise the same. Returns 1 if the staged update is
+ * selected and the mesh qualifies (the U condition is checked per step), 0
+ * otherwise, KH_EINVAL for a null mesh. Enabled by default. */
+int kh_mesh_set_staged_update(kh_mesh* mesh, int enable);
 int kh_mesh_autotune(kh_mesh* mesh, const double* U, const double* P, const double* B, double dt, int* tpb_flux,
                      int* tpb_update);
 int kh_mesh_get_stats(kh_mesh* mesh, kh_stats* out);

@@ -24,7 +24,7 @@ LIB_BOUNDS = os.path.join(HERE, "libkharma_gb300_bounds.so")
 SOURCES = ["kh_kernels.cu", "kh_api.cu", "kh_noalloc.cu", "kh_mesh.cu", "kh_adjoint.cu", "kh_flux_tma.cu",
            "kh_update_tma.cu"]
 HEADERS = ["kh_internal.h", "kh_physics.cuh", "kh_geom_math.h", "kh_zone.cuh", "kh_ctx.h", "kh_dual.cuh", "kh_df64.cuh",
-           "kh_mixed.cuh", "kh_face_vjp.cuh", "kh_pair.cuh", "kh_tma.cuh"]
+           "kh_mixed.cuh", "kh_face_vjp.cuh", "kh_pair.cuh", "kh_tma.cuh", "kh_update_tile.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -615,24 +615,20 @@ int issue_rk(kh_ctx* x, double* U, const Vars& Pn) {
     faces(fbase, x->fB);
     stage(1, base, U, 0.5, nullptr);
   } else {
-    const double c4 = 0.544974750228521, c53 = 0.063692468666290;
+    using T = Ssprk54;
     faces(x->fB, fs[1]);
-    stage(0, U, st[1], 0.391752226571890, nullptr);
+    stage(0, U, st[1], T::c1, nullptr);
     // stages 2-4 combine U (and fB) with the previous stage's state
-    const double a2[3][2] = {{0.444370493651235, 0.555629506348765},
-                             {0.620101851488403, 0.379898148511597},
-                             {0.178079954393132, 0.821920045606868}};
-    const double cs[3] = {0.368410593050371, 0.251891774271694, c4};
     for (int q = 1; q <= 3; ++q) {
       const double* in[2] = {U, st[q]};
-      comb(2, in, a2[q - 1]);
+      comb(2, in, T::a[q - 1]);
       const double* fin[2] = {fs[0], fs[q]};
-      fcomb(2, fin, a2[q - 1]);
+      fcomb(2, fin, T::a[q - 1]);
       faces(fbase, fs[q + 1]);
-      stage(q, base, st[q + 1], cs[q - 1], q == 3 ? dU4 : nullptr);
+      stage(q, base, st[q + 1], T::c[q - 1], q == 3 ? dU4 : nullptr);
     }
     {
-      const double a[4] = {0.517231671970585, 0.096059710526147, 0.386708617503269, c53 / c4};
+      const double a[4] = {T::a5[0], T::a5[1], T::a5[2], T::c53 / T::c[2]};
       const double* in[4] = {st[2], st[3], st[4], dU4};
       comb(4, in, a);
       // fbase still holds stage 4's base: fs4 - fbase is stage 4's increment
@@ -640,7 +636,7 @@ int issue_rk(kh_ctx* x, double* U, const Vars& Pn) {
       const double* fin[4] = {fs[2], fs[3], fs[4], fbase};
       fcomb(4, fin, fa);
       faces(fbase, x->fB);
-      stage(4, base, U, 0.226007483236906, nullptr);
+      stage(4, base, U, T::c5, nullptr);
     }
   }
   faces(nullptr, nullptr);

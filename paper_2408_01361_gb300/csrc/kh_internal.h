@@ -121,6 +121,22 @@ struct FailList {
   unsigned long long* n;
 };
 
+// SSPRK(5,4) of Spiteri & Ruuth (2002) in Shu-Osher form (the paper's
+// "Algorithm" section lists it beside RK1, RK2 and the predictor-corrector):
+// U1 = U + c1 dt L(P); U_{q+1} = a[q-1][0] U + a[q-1][1] U_q + c[q-1] dt L(P_q)
+// for q = 1..3; U5 = a5[0] U2 + a5[1] U3 + a5[2] U4 + (c53 / c[2]) dU4 + c5 dt
+// L(P4), where dU4 = c[2] dt L(P3) is stage 4's raw increment.
+struct Ssprk54 {
+  static constexpr double c1 = 0.391752226571890;
+  static constexpr double a[3][2] = {{0.444370493651235, 0.555629506348765},
+                                     {0.620101851488403, 0.379898148511597},
+                                     {0.178079954393132, 0.821920045606868}};
+  static constexpr double c[3] = {0.368410593050371, 0.251891774271694, 0.544974750228521};
+  static constexpr double a5[3] = {0.517231671970585, 0.096059710526147, 0.386708617503269};
+  static constexpr double c53 = 0.063692468666290;
+  static constexpr double c5 = 0.226007483236906;
+};
+
 // ---- launchers (kh_kernels.cu); each returns the number of kernels launched ----
 // Geometry of a grid whose first interior cell starts at native (x1o, x2o);
 // cp.x1min is the FMKS blending reference (the x1 start of the whole domain).

@@ -27,6 +27,7 @@
 #include <tuple>
 #include <vector>
 
+#include "kh_update_tile.cuh"
 #include "kh_zone.cuh"
 
 using namespace kh;
@@ -164,7 +165,7 @@ __global__ void __launch_bounds__(256) km_update(const MBlock* blk, const unsign
                                                 Arena<double> Pin, Arena<double> Pout, double* Uout,
                                                 const double* F1, const double* F2, const double* F3, GeoArena GA,
                                                 Scheme S, const double* dtp, double coef, int8_t* pflag,
-                                                unsigned long long* cnt, const double* fBn) {
+                                                unsigned long long* cnt, const double* fBn, double* dUout) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= __ldg(pre + nb)) return;
   const int b = find_block(pre, nb, t);
@@ -174,7 +175,7 @@ __global__ void __launch_bounds__(256) km_update(const MBlock* blk, const unsign
   const long long o8 = NV * m.off;
   update_zone<false, INV>(U0 + o8, cvars_at(Pin, m), vars_at(Pout, m), Uout ? Uout + o8 : nullptr, F1 + o8, F2 + o8,
               m.L.ndim == 3 ? F3 + o8 : nullptr, m.L, geo64(GA, m), S, coef * __ldg(dtp), pflag + m.off, cnt, i, j,
-              k, nullptr, FailList{nullptr, nullptr}, fBn ? fBn + 3 * m.off : nullptr);
+              k, nullptr, FailList{nullptr, nullptr}, fBn ? fBn + 3 * m.off : nullptr, dUout ? dUout + o8 : nullptr);
 }
 
 template <int INV>
@@ -184,7 +185,7 @@ __global__ void __launch_bounds__(256, 2) km_update_mixed(const MBlock* blk, con
                                                       const float* F2, const float* F3, GeoArena GA, Scheme S,
                                                       const double* dtp, double coef, int8_t* pflag,
                                                       unsigned long long* cnt, const double* fBn, const float* e1,
-                                                      const float* e2, const float* e3) {
+                                                      const float* e2, const float* e3, double* dUout) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= __ldg(pre + nb)) return;
   const int b = find_block(pre, nb, t);
@@ -199,8 +200,70 @@ __global__ void __launch_bounds__(256, 2) km_update_mixed(const MBlock* blk, con
   update_mixed_zone<false, INV>(U0 + o8, cvars_at(Pin, m), P64, P32, Uout ? Uout + o8 : nullptr, F1 + o8, F2 + o8,
                     m.L.ndim == 3 ? F3 + o8 : nullptr, m.L, geo64(GA, m), geo32(GA, m), S,
                     df_of_f64(coef * __ldg(dtp)), pflag + m.off, cnt, i, j, k, FailList{nullptr, nullptr},
-                    fBn ? fBn + 3 * m.off : nullptr, nullptr,
+                    fBn ? fBn + 3 * m.off : nullptr, dUout ? dUout + o8 : nullptr,
                     CtEmf{{e1 ? e1 + m.off : nullptr, e2 ? e2 + m.off : nullptr, e3 ? e3 + m.off : nullptr}});
+}
+
+// ---- the mixed update with TMA-staged tiles (3-D Flux-CT stages) ----
+// As on the single grid (kh_update_tile.cuh): one CTA of 256 threads per tile
+// of TX zones along x1 -- a block's whole interior row, TX = 16 or 32 -- by
+// 256 / TX rows along x2 of one x3 plane, its inputs staged by eight tensor
+// copies. The tensor maps sit in a device table, two or three sets per block
+// over the block's own allocation (set 0: the first stage's input and the
+// caller's U^n; set 1: the FP32 shadow of later stages and U^n; set 2, with
+// a Runge-Kutta integrator: the shadow and the stage base): built at set-up
+// for the internal arrays, and rebuilt for U^n (the caller's array) whenever
+// the step is handed another one. Blocks start their rows at cell 0, a 16-byte
+// boundary at or below the first interior cell (3) for floats and doubles
+// alike; the U^n box starts at cell 2.
+struct MTile {
+  int b, j0, k;  // block, first row (x2 cell index), plane (x3 cell index)
+};
+constexpr int TMA_N1[2] = {16, 32};  // block widths the staged update serves (one kernel each)
+
+template <int TX, int INV>
+__global__ void __launch_bounds__(256, 3)
+    km_update_mixed_tma(const MBlock* blk, const MTile* tiles, const UpdateMaps* maps, int nsets, int set,
+                        Arena<double> Pout64, Arena<float> Pout32, double* Uout, GeoArena GA, Scheme S,
+                        const double* dtp, double coef, int8_t* pflag, unsigned long long* cnt, unsigned wlim,
+                        double* dUout) {
+  using T = UpdTile<TX, 256 / TX>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* smem = aligned_smem(smem_raw);
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + T::O_BAR);
+  const MTile t = tiles[blockIdx.x];
+  const MBlock& m = blk[t.b];
+  const UpdateMaps& tm = maps[nsets * t.b + set];
+  const int lx = threadIdx.x & (TX - 1), ly = threadIdx.x / TX;
+  const int i0 = m.L.s[0], x0 = i0 & ~3, xu0 = i0 & ~1;
+  if (threadIdx.x == 0) {
+    mbar_init(bar);
+    // the maps were written through the generic proxy (a host copy)
+    tensormap_acquire(&tm.p);
+    tensormap_acquire(&tm.f1);
+    tensormap_acquire(&tm.f2);
+    tensormap_acquire(&tm.f3);
+    tensormap_acquire(&tm.e1);
+    tensormap_acquire(&tm.e2);
+    tensormap_acquire(&tm.e3);
+    tensormap_acquire(&tm.u);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) issue_update_tile<T>(smem, tm, x0, xu0, t.j0, t.k, bar);
+  if (!cta_wait_tiles(bar, wlim, cnt)) return;
+  const Layout& L = m.L;
+  const int i = i0 + lx, j = t.j0 + ly, k = t.k;
+  if (i >= L.e[0] || j >= L.e[1]) return;  // ragged tile
+  if (KH_OOB(L, kh_in(L, i, j, k, 1))) return;
+  Vars P64;
+  VarsT<float> P32;
+  if (Pout64.a) P64 = vars_at(Pout64, m); else for (int v = 0; v < NV; ++v) P64.v[v] = nullptr;
+  if (Pout32.a) P32 = vars_at(Pout32, m); else for (int v = 0; v < NV; ++v) P32.v[v] = nullptr;
+  const typename T::In in{smem, (i0 - x0) + lx, (i0 - xu0) + lx, ly};
+  update_mixed_zone_in<false, INV, typename T::In, true>(
+      in, P64, P32, Uout ? Uout + NV * m.off : nullptr, L, geo64(GA, m), geo32(GA, m), S,
+      df_of_f64(coef * __ldg(dtp)), pflag + m.off, cnt, i, j, k, FailList{nullptr, nullptr}, nullptr,
+      dUout ? dUout + NV * m.off : nullptr);
 }
 
 template <class T>
@@ -595,11 +658,30 @@ struct kh_mesh {
   float* eccf;
   EmfMatch* dmatch;
   long long nmatch;
+  // Runge-Kutta integrators: the stage states after U (SSPRK(5,4): 4, RK2: 1,
+  // RK1: 0), the stage base and (SSPRK(5,4)) stage 4's raw increment, each
+  // 8 planes of every block's cells
+  double* rk;
+  // TMA-staged mixed update (3-D Flux-CT, Noble-2D, every block 16 or 32
+  // zones wide): tiles of the 16-wide blocks, then of the 32-wide ones; two
+  // map sets per block (stage 1 and 2 inputs), host copy and device table
+  int tma_upd;        // the mesh qualifies
+  int tma_off;        // disabled by the caller (kh_mesh_set_staged_update)
+  int tma_now;        // the maps hold the U^n of the current step
+  MTile* dtiles;
+  long long ntile[2];
+  int nsets;          // map sets per block (see km_update_mixed_tma)
+  UpdateMaps* dmaps;
+  std::vector<UpdateMaps> hmaps;
+  const double* umap_key;  // the U^n the maps point at
 };
 
 namespace {
 
 int cuda_rc(cudaError_t e) { return e == cudaSuccess ? KH_OK : (e == cudaErrorMemoryAllocation ? KH_ENOMEM : KH_ECUDA); }
+
+// Stored stage states of a Runge-Kutta integrator besides U (the stage base follows them).
+int rk_states(int integrator) { return integrator == KH_INT_SSPRK54 ? 4 : (integrator == KH_INT_RK2 ? 1 : 0); }
 
 // Doubled finest-level index coordinates of cell centres (exact integers):
 // the centre of level-l cell g along a direction refined by ratio r is
@@ -629,7 +711,9 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
   if (c->recon != KH_RECON_MC && c->recon != KH_RECON_WENO5) return KH_EINVAL;
   if (c->fofc) return KH_EINVAL;  // the flux correction runs on single grids
   if (c->inverter < KH_INV_NOBLE2D || c->inverter > KH_INV_KASTAUN) return KH_EINVAL;
-  if (c->integrator != KH_INT_VL2) return KH_EINVAL;    // the mesh steps with the predictor-corrector
+  if (c->integrator < KH_INT_VL2 || c->integrator > KH_INT_SSPRK54) return KH_EINVAL;
+  // Runge-Kutta stages carry U (and P) only: with face-centred CT the face field would be stage state too
+  if (c->integrator != KH_INT_VL2 && c->bfield == KH_B_FACE) return KH_EINVAL;
   if (c->mixed_inversion != KH_MIXINV_DF && c->mixed_inversion != KH_MIXINV_FP64) return KH_EINVAL;
   if (c->bfield != KH_B_FLUXCT && c->bfield != KH_B_FACE) return KH_EINVAL;
   if (c->emf != KH_EMF_AVERAGE && c->emf != KH_EMF_GS05) return KH_EINVAL;
@@ -663,6 +747,7 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
   S.mixed_fp64 = c->precision == KH_MIXED && c->inverter == KH_INV_NOBLE2D && c->mixed_inversion == KH_MIXINV_FP64;
   S.bfield = c->bfield;
   S.emf = c->emf;
+  S.integrator = c->integrator;
   set_mixed(S);
   x->cp = CoordParams{c->kind, a, c->x1min, c->hslope, c->poly_xt, c->poly_alpha, c->mks_smooth};
 
@@ -1031,6 +1116,8 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
     KM_ALLOC(x->fBstar, 3 * pl);
     KM_ALLOC(x->dmatch, sizeof(EmfMatch) * std::max<long long>(x->nmatch, 1));
   }
+  if (c->integrator != KH_INT_VL2)
+    KM_ALLOC(x->rk, (size_t)(rk_states(c->integrator) + (c->integrator == KH_INT_SSPRK54 ? 2 : 1)) * NV * pl);
   x->npartial = 152 * 4;
   KM_ALLOC(x->partial, sizeof(double) * 2 * x->npartial);  // (max, sum) pairs for divB
   KM_ALLOC(x->dscalar, 4 * sizeof(double));
@@ -1047,6 +1134,50 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
   if (rc == KH_OK && x->nmatch)
     rc = cuda_rc(cudaMemcpy(x->dmatch, matches.data(), sizeof(EmfMatch) * x->nmatch, cudaMemcpyHostToDevice));
   if (rc == KH_OK && x->fBstar) rc = cuda_rc(cudaMemset(x->fBstar, 0, 3 * pl));
+  // the TMA-staged update: its tiles and the maps of the internal arrays (U^n's are made per step)
+  x->tma_upd = mixed && x->ndim == 3 && c->bfield == KH_B_FLUXCT && c->inverter == KH_INV_NOBLE2D &&
+               tensor_map_encoder() != nullptr;
+  for (int b = 0; b < nblocks && x->tma_upd; ++b)
+    if (x->hb[b].L.n1 != TMA_N1[0] && x->hb[b].L.n1 != TMA_N1[1]) x->tma_upd = 0;
+  if (rc == KH_OK && x->tma_upd) {
+    std::vector<MTile> tl;
+    for (int cls = 0; cls < 2; ++cls) {
+      const size_t t0 = tl.size();
+      for (int b = 0; b < nblocks; ++b) {
+        const Layout& L = x->hb[b].L;
+        if (L.n1 != TMA_N1[cls]) continue;
+        const int ty = 256 / L.n1;
+        for (int k = L.s[2]; k < L.e[2]; ++k)
+          for (int j0 = L.s[1]; j0 < L.e[1]; j0 += ty) tl.push_back(MTile{b, j0, k});
+      }
+      x->ntile[cls] = (long long)(tl.size() - t0);
+    }
+    x->nsets = c->integrator == KH_INT_VL2 ? 2 : 3;
+    x->hmaps.resize((size_t)x->nsets * nblocks);
+    const double* rkbase = x->rk ? x->rk + (size_t)rk_states(c->integrator) * NV * cells : nullptr;
+    for (int b = 0; b < nblocks && x->tma_upd; ++b) {
+      const MBlock& m = x->hb[b];
+      const float* F[3] = {x->Ff[0] + NV * m.off, x->Ff[1] + NV * m.off, x->Ff[2] + NV * m.off};
+      const float* E[3] = {x->emff[0] + m.off, x->emff[1] + m.off, x->emff[2] + m.off};
+      const float* Pst[3] = {x->pnf + NV * m.off, x->pstarf + NV * m.off, x->pstarf + NV * m.off};
+      for (int st = 0; st < x->nsets && x->tma_upd; ++st) {
+        UpdateMaps& tm = x->hmaps[(size_t)x->nsets * b + st];
+        // the caller's U^n (sets 0, 1) is encoded per step (refresh_umaps); set 2 reads the stage base
+        const double* Ub = st == 2 ? rkbase + NV * m.off : nullptr;
+        const bool ok = m.L.n1 == 16 ? encode_update_maps<UpdTile<16, 16>>(&tm, Pst[st], Ub, F, E, m.L.n1s,
+                                                                             m.L.n2s, m.L.n3s)
+                                     : encode_update_maps<UpdTile<32, 8>>(&tm, Pst[st], Ub, F, E, m.L.n1s,
+                                                                            m.L.n2s, m.L.n3s);
+        if (!ok) x->tma_upd = 0;
+      }
+    }
+    if (x->tma_upd) {
+      rc = cuda_rc(cudaMalloc((void**)&x->dtiles, sizeof(MTile) * std::max<size_t>(tl.size(), 1)));
+      if (rc == KH_OK) rc = cuda_rc(cudaMalloc((void**)&x->dmaps, sizeof(UpdateMaps) * x->hmaps.size()));
+      if (rc == KH_OK)
+        rc = cuda_rc(cudaMemcpy(x->dtiles, tl.data(), sizeof(MTile) * tl.size(), cudaMemcpyHostToDevice));
+    }
+  }
   // zero scratch so never-written entries stay finite
   for (int d = 0; d < 3 && rc == KH_OK; ++d) {
     if (x->F[d]) rc = cuda_rc(cudaMemset(x->F[d], 0, NV * pl));
@@ -1168,25 +1299,25 @@ template <class T> int cfl_pass(kh_mesh* x, T* const ct[3]) {
 
 // The update kernels over all blocks, instantiated for the context's solver
 // (the mixed path: double-float Noble-2D, or FP64 for every zone).
-void km_update_any(const kh_mesh* x, int g, int t, double* U0, const Arena<double>& Pin, const Arena<double>& Pout,
-                   double* Uout, double coef, const double* fBn) {
+void km_update_any(const kh_mesh* x, int g, int t, const double* U0, const Arena<double>& Pin,
+                   const Arena<double>& Pout, double* Uout, double coef, const double* fBn, double* dUout) {
   const GeoArena GA = garena(x);
   auto go = [&](auto kern) {
     kern<<<g, t, 0, x->stream>>>(x->dblk, x->dpre[3], x->nb, U0, Pin, Pout, Uout, x->F[0], x->F[1], x->F[2], GA,
-                                 x->S, x->dscalar + 3, coef, x->pflag, x->counters, fBn);
+                                 x->S, x->dscalar + 3, coef, x->pflag, x->counters, fBn, dUout);
   };
   if (x->S.c2p.method == C2P_KASTAUN) go(km_update<C2P_KASTAUN>);
   else if (x->S.c2p.method == C2P_1DW) go(km_update<C2P_1DW>);
   else go(km_update<C2P_NOBLE2D>);
 }
-void km_update_mixed_any(const kh_mesh* x, int g, int t, double* U0, const Arena<float>& Pin,
+void km_update_mixed_any(const kh_mesh* x, int g, int t, const double* U0, const Arena<float>& Pin,
                          const Arena<double>& Pout64, const Arena<float>& Pout32, double* Uout, double coef,
-                         const double* fBn, const float* const* ce) {
+                         const double* fBn, const float* const* ce, double* dUout) {
   const GeoArena GA = garena(x);
   auto go = [&](auto kern) {
     kern<<<g, t, 0, x->stream>>>(x->dblk, x->dpre[3], x->nb, U0, Pin, Pout64, Pout32, Uout, x->Ff[0], x->Ff[1],
                                  x->Ff[2], GA, x->S, x->dscalar + 3, coef, x->pflag, x->counters, fBn, ce[0], ce[1],
-                                 ce[2]);
+                                 ce[2], dUout);
   };
   if (x->S.c2p.method == C2P_KASTAUN) go(km_update_mixed<C2P_KASTAUN>);
   else if (x->S.c2p.method == C2P_1DW) go(km_update_mixed<C2P_1DW>);
@@ -1194,57 +1325,215 @@ void km_update_mixed_any(const kh_mesh* x, int g, int t, double* U0, const Arena
   else go(km_update_mixed<C2P_NOBLE2D>);
 }
 
-int issue_mesh_step(kh_mesh* x, double* U, double* P, double* B) {
-  cudaStream_t s = x->stream;
-  if (cudaMemsetAsync(x->counters, 0, NCNT * sizeof(unsigned long long), s) != cudaSuccess) return -1;
-  const GeoArena GA = garena(x);
-  const unsigned nz = x->pre_zone.back();
-  const int gz = nblk(nz, MTPB);
-  const int tu = x->tpb_update, gu = nblk(nz, tu);
-  const Arena<double> Pn = arena_pb(P, B);
+// Points the U^n maps of the staged update at U (the caller's conserved
+// array) and copies the table to the device, ordered on the mesh's stream.
+// Leaves the staged update off for this U if a map cannot be encoded (U not
+// 16-byte aligned).
+int refresh_umaps(kh_mesh* x, const double* U) {
+  x->tma_now = 0;
+  x->umap_key = U;
+  for (int b = 0; b < x->nb; ++b) {
+    const MBlock& m = x->hb[b];
+    const double* Ub = U + NV * m.off;
+    for (int st = 0; st < 2; ++st) {
+      CUtensorMap* tm = &x->hmaps[(size_t)x->nsets * b + st].u;
+      const bool ok = m.L.n1 == 16 ? encode_update_umap<UpdTile<16, 16>>(tm, Ub, m.L.n1s, m.L.n2s, m.L.n3s)
+                                   : encode_update_umap<UpdTile<32, 8>>(tm, Ub, m.L.n1s, m.L.n2s, m.L.n3s);
+      if (!ok) return KH_OK;
+    }
+  }
+  const int rc = cuda_rc(cudaMemcpyAsync(x->dmaps, x->hmaps.data(), sizeof(UpdateMaps) * x->hmaps.size(),
+                                         cudaMemcpyHostToDevice, x->stream));
+  x->tma_now = rc == KH_OK;
+  return rc;
+}
+
+template <int TX, int INV> bool mesh_tma_smem_once() {
+  static bool done = false;
+  if (!done)
+    done = cudaFuncSetAttribute(km_update_mixed_tma<TX, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                UpdTile<TX, 256 / TX>::SMEM) == cudaSuccess;
+  return done;
+}
+
+// The staged update of one stage over all blocks (one launch per block
+// width); the number of launches, or -1.
+int km_update_mixed_tma_all(const kh_mesh* x, int set, const Arena<double>& Pout64, const Arena<float>& Pout32,
+                            double* Uout, double coef, double* dUout) {
   int n = 0;
+  long long t0 = 0;
+  for (int cls = 0; cls < 2; ++cls) {
+    const long long nt = x->ntile[cls];
+    if (!nt) continue;
+    auto go = [&](auto kern, bool ok, int smem) {
+      if (!ok) return false;
+      kern<<<(unsigned)nt, 256, smem, x->stream>>>(x->dblk, x->dtiles + t0, x->dmaps, x->nsets, set, Pout64,
+                                                   Pout32, Uout, garena(x), x->S, x->dscalar + 3, coef, x->pflag,
+                                                   x->counters, (unsigned)KH_WAIT_POLLS, dUout);
+      return true;
+    };
+    bool ok;
+    if (cls == 0) {
+      ok = x->S.mixed_fp64
+               ? go(km_update_mixed_tma<16, C2P_NOBLE2D_FP64>, mesh_tma_smem_once<16, C2P_NOBLE2D_FP64>(),
+                    UpdTile<16, 16>::SMEM)
+               : go(km_update_mixed_tma<16, C2P_NOBLE2D>, mesh_tma_smem_once<16, C2P_NOBLE2D>(), UpdTile<16, 16>::SMEM);
+    } else {
+      ok = x->S.mixed_fp64
+               ? go(km_update_mixed_tma<32, C2P_NOBLE2D_FP64>, mesh_tma_smem_once<32, C2P_NOBLE2D_FP64>(),
+                    UpdTile<32, 8>::SMEM)
+               : go(km_update_mixed_tma<32, C2P_NOBLE2D>, mesh_tma_smem_once<32, C2P_NOBLE2D>(), UpdTile<32, 8>::SMEM);
+    }
+    if (!ok) return -1;
+    ++n;
+    t0 += nt;
+  }
+  return n;
+}
+
+// One FP64 stage over all blocks: Pin's ghost cells, the fluxes (with
+// Flux-CT, or face-centred CT moving the face field into fBst), the update
+// U0 + coef dt (S - div F) -> Pout (Uout and dUout when given; Pin = Pout is
+// allowed: every zone reads only its own input), the fixup.
+int mesh_stage64(kh_mesh* x, const double* U0, const Arena<double>& Pin, const Arena<double>& Pout, double* Uout,
+                 double coef, double* dUout, double* fBst) {
   const bool face = x->S.bfield == KH_B_FACE;
-  if (x->c.precision == KH_FP64) {
-    const Arena<double> Ps = arena8(x->pstar);
-    // stage 1: P^n -> P*
-    n += fill_ghosts(x, Pn);
-    n += flux_pass<double, double>(x, Pn, x->F, x->ctop, x->emf, !face);
-    if (face) n += face_ct_pass<double>(x, Pn, x->F, x->ecc, x->emf, x->fBstar, 0.5);
-    km_update_any(x, gu, tu, U, Pn, Ps, nullptr, 0.5, face ? x->fBstar : nullptr);
-    km_fixup<double><<<gz, MTPB, 0, s>>>(x->dblk, x->dpre[3], x->nb, Ps, nullptr, x->pflag, GA, x->S, x->counters);
-    n += 2;
-    // stage 2: P* -> P^{n+1}, U^{n+1}
-    n += fill_ghosts(x, Ps);
-    n += flux_pass<double, double>(x, Ps, x->F, x->ctop, x->emf, !face);
-    if (face) n += face_ct_pass<double>(x, Ps, x->F, x->ecc, x->emf, x->fB, 1.0);
-    km_update_any(x, gu, tu, U, Ps, Pn, U, 1.0, face ? x->fB : nullptr);
-    km_fixup<double><<<gz, MTPB, 0, s>>>(x->dblk, x->dpre[3], x->nb, Pn, U, x->pflag, GA, x->S, x->counters);
-    n += 2;
-    n += cfl_pass<double>(x, x->ctop);
+  const unsigned nz = x->pre_zone.back();
+  int n = fill_ghosts(x, Pin);
+  n += flux_pass<double, double>(x, Pin, x->F, x->ctop, x->emf, !face);
+  if (face) n += face_ct_pass<double>(x, Pin, x->F, x->ecc, x->emf, fBst, coef);
+  km_update_any(x, nblk(nz, x->tpb_update), x->tpb_update, U0, Pin, Pout, Uout, coef, face ? fBst : nullptr, dUout);
+  km_fixup<double><<<nblk(nz, MTPB), MTPB, 0, x->stream>>>(x->dblk, x->dpre[3], x->nb, Pout, Uout, x->pflag,
+                                                           garena(x), x->S, x->counters);
+  return n + 2;
+}
+
+// One mixed stage over all blocks. first: the caller's FP64 P^n (Pn64)
+// converted to FP32 (pnf) and ghost-filled there; otherwise the FP32 shadow
+// (pstarf) ghost-filled in place. Outputs: the FP64 primitives (Pout64, the
+// last stage) or the FP32 shadow (Pout32), Uout and dUout when given; set:
+// the staged update's map set for this stage's input and U0 (-1: U0 has
+// none).
+int mesh_stage_mixed(kh_mesh* x, bool first, const double* U, const double* U0, const Arena<double>& Pn64,
+                     const Arena<double>& Pout64, const Arena<float>& Pout32, double* Uout, double coef,
+                     double* dUout, double* fBst, int set) {
+  cudaStream_t s = x->stream;
+  const bool face = x->S.bfield == KH_B_FACE;
+  const unsigned nz = x->pre_zone.back();
+  const Arena<float> Pin = first ? arena8(x->pnf) : arena8(x->pstarf);
+  int n = 0;
+  if (first) {
+    km_to_f32<<<nblk(x->pre_alloc.back(), 256), 256, 0, s>>>(x->dblk, x->dpre[5], x->nb, Pn64, Pin);
+    ++n;
+  }
+  n += fill_ghosts(x, Pin);
+  // Flux-CT: EMFs only, the update forms the field fluxes from them
+  const float* ce[3] = {face ? nullptr : x->emff[0], face ? nullptr : x->emff[1], face ? nullptr : x->emff[2]};
+  n += flux_pass<float, float>(x, Pin, x->Ff, x->ctopf, x->emff, !face, true);
+  if (face) n += face_ct_pass<float>(x, Pin, x->Ff, x->eccf, x->emff, fBst, coef);
+  const bool staged = set >= 0 && x->tma_upd && !x->tma_off && x->tma_now && x->umap_key == U && !face;
+  if (staged) {
+    const int r = km_update_mixed_tma_all(x, set, Pout64, Pout32, Uout, coef, dUout);
+    if (r < 0) return -1;
+    n += r;
   } else {
-    const Arena<float> Psf = arena8(x->pstarf), Pnf = arena8(x->pnf);
+    km_update_mixed_any(x, nblk(nz, x->tpb_update), x->tpb_update, U0, Pin, Pout64, Pout32, Uout, coef,
+                        face ? fBst : nullptr, ce, dUout);
+    ++n;
+  }
+  if (Pout64.a)
+    km_fixup<double><<<nblk(nz, MTPB), MTPB, 0, s>>>(x->dblk, x->dpre[3], x->nb, Pout64, Uout, x->pflag, garena(x),
+                                                     x->S, x->counters);
+  else
+    km_fixup<float><<<nblk(nz, MTPB), MTPB, 0, s>>>(x->dblk, x->dpre[3], x->nb, Pout32, Uout, x->pflag, garena(x),
+                                                    x->S, x->counters);
+  return n + 1;
+}
+
+// A Runge-Kutta step (RK1, RK2, SSPRK(5,4); Flux-CT) over all blocks: the
+// stages of the single grid's Runge-Kutta step, each stage's input
+// ghost-filled across blocks; stage bases formed over the whole arena. The
+// FP64 path updates P in place; the mixed path enters with the caller's FP64
+// P^n, carries the FP32 shadow between stages and writes the FP64 P^{n+1} at
+// the last stage.
+int issue_mesh_rk(kh_mesh* x, double* U, const Arena<double>& Pn) {
+  cudaStream_t s = x->stream;
+  const long long n8 = (long long)NV * x->cells;
+  const int nst = rk_states(x->S.integrator);
+  double* st[5] = {U, x->rk, x->rk + n8, x->rk + 2 * n8, x->rk + 3 * n8};
+  double* base = x->rk + nst * n8;
+  double* dU4 = base + n8;
+  const int nstage = x->S.integrator == KH_INT_SSPRK54 ? 5 : (x->S.integrator == KH_INT_RK2 ? 2 : 1);
+  const Arena<double> none64{nullptr, nullptr, NV};
+  const Arena<float> none32{nullptr, nullptr, NV};
+  int n = 0;
+  bool ok = true;
+  auto stage = [&](int q, const double* U0, double* Uout, double c, double* dUout) {
+    if (x->c.precision == KH_FP64) {
+      n += mesh_stage64(x, U0, Pn, Pn, Uout, c, dUout, nullptr);
+      return;
+    }
+    const bool last = q == nstage - 1;
+    // map sets: the first stage reads P^n and the caller's U, later ones the shadow and the base
+    const int set = q == 0 ? 0 : (U0 == base ? 2 : -1);
+    const int r = mesh_stage_mixed(x, q == 0, U, U0, Pn, last ? Pn : none64, last ? none32 : arena8(x->pstarf), Uout,
+                                   c, dUout, nullptr, set);
+    if (r < 0) ok = false;
+    n += r;
+  };
+  auto comb = [&](int nt, const double* const* in, const double* a) { n += launch_lincomb(base, nt, in, a, n8, s); };
+  if (x->S.integrator == KH_INT_RK1) {
+    stage(0, U, U, 1.0, nullptr);
+  } else if (x->S.integrator == KH_INT_RK2) {
+    stage(0, U, st[1], 1.0, nullptr);
+    const double* in[2] = {U, st[1]};
+    const double a[2] = {0.5, 0.5};
+    comb(2, in, a);
+    stage(1, base, U, 0.5, nullptr);
+  } else {
+    using T = Ssprk54;
+    stage(0, U, st[1], T::c1, nullptr);
+    for (int q = 1; q <= 3; ++q) {
+      const double* in[2] = {U, st[q]};
+      comb(2, in, T::a[q - 1]);
+      stage(q, base, st[q + 1], T::c[q - 1], q == 3 ? dU4 : nullptr);
+    }
+    const double a[4] = {T::a5[0], T::a5[1], T::a5[2], T::c53 / T::c[2]};
+    const double* in[4] = {st[2], st[3], st[4], dU4};
+    comb(4, in, a);
+    stage(4, base, U, T::c5, nullptr);
+  }
+  return ok ? n : -1;
+}
+
+int issue_mesh_step(kh_mesh* x, double* U, double* P, double* B) {
+  if (cudaMemsetAsync(x->counters, 0, NCNT * sizeof(unsigned long long), x->stream) != cudaSuccess) return -1;
+  const Arena<double> Pn = arena_pb(P, B);
+  const bool face = x->S.bfield == KH_B_FACE;
+  const bool fp64 = x->c.precision == KH_FP64;
+  int n = 0;
+  if (x->S.integrator != KH_INT_VL2) {
+    const int r = issue_mesh_rk(x, U, Pn);
+    if (r < 0) return -1;
+    n += r;
+  } else if (fp64) {
+    // stage 1: P^n -> P* (U* is not stored); stage 2: P* -> P^{n+1}, U^{n+1}
+    const Arena<double> Ps = arena8(x->pstar);
+    n += mesh_stage64(x, U, Pn, Ps, nullptr, 0.5, nullptr, face ? x->fBstar : nullptr);
+    n += mesh_stage64(x, U, Ps, Pn, U, 1.0, nullptr, face ? x->fB : nullptr);
+  } else {
+    // stage 1: FP64 P^n (converted once, then ghost-filled in FP32) -> FP32 P*; stage 2: FP32 P* -> FP64 P^{n+1}, U^{n+1}
     const Arena<double> none64{nullptr, nullptr, NV};
     const Arena<float> none32{nullptr, nullptr, NV};
-    // stage 1: FP64 P^n (converted once, then ghost-filled in FP32) -> FP32 P*
-    km_to_f32<<<nblk(x->pre_alloc.back(), 256), 256, 0, s>>>(x->dblk, x->dpre[5], x->nb, Pn, Pnf);
-    ++n;
-    n += fill_ghosts(x, Pnf);
-    // Flux-CT: EMFs only, the update forms the field fluxes from them
-    const float* ce[3] = {face ? nullptr : x->emff[0], face ? nullptr : x->emff[1], face ? nullptr : x->emff[2]};
-    n += flux_pass<float, float>(x, Pnf, x->Ff, x->ctopf, x->emff, !face, true);
-    if (face) n += face_ct_pass<float>(x, Pnf, x->Ff, x->eccf, x->emff, x->fBstar, 0.5);
-    km_update_mixed_any(x, gu, tu, U, Pnf, none64, Psf, nullptr, 0.5, face ? x->fBstar : nullptr, ce);
-    km_fixup<float><<<gz, MTPB, 0, s>>>(x->dblk, x->dpre[3], x->nb, Psf, nullptr, x->pflag, GA, x->S, x->counters);
-    n += 2;
-    // stage 2: FP32 P* -> FP64 P^{n+1}, U^{n+1}
-    n += fill_ghosts(x, Psf);
-    n += flux_pass<float, float>(x, Psf, x->Ff, x->ctopf, x->emff, !face, true);
-    if (face) n += face_ct_pass<float>(x, Psf, x->Ff, x->eccf, x->emff, x->fB, 1.0);
-    km_update_mixed_any(x, gu, tu, U, Psf, Pn, none32, U, 1.0, face ? x->fB : nullptr, ce);
-    km_fixup<double><<<gz, MTPB, 0, s>>>(x->dblk, x->dpre[3], x->nb, Pn, U, x->pflag, GA, x->S, x->counters);
-    n += 2;
-    n += cfl_pass<float>(x, x->ctopf);
+    int r = mesh_stage_mixed(x, true, U, U, Pn, none64, arena8(x->pstarf), nullptr, 0.5, nullptr,
+                             face ? x->fBstar : nullptr, 0);
+    if (r < 0) return -1;
+    n += r;
+    r = mesh_stage_mixed(x, false, U, U, Pn, Pn, none32, U, 1.0, nullptr, face ? x->fB : nullptr, 1);
+    if (r < 0) return -1;
+    n += r;
   }
+  n += fp64 ? cfl_pass<double>(x, x->ctop) : cfl_pass<float>(x, x->ctopf);
   return n;
 }
 
@@ -1375,6 +1664,10 @@ int kh_mesh_step(kh_mesh* x, double* U, double* P, double* B, double dt, double*
   if (x->S.bfield == KH_B_FACE && !x->fB) return KH_EINVAL;
   int rc = cuda_rc(cudaMemcpyAsync(x->dscalar + 3, &dt, sizeof(double), cudaMemcpyHostToDevice, x->stream));
   if (rc != KH_OK) return rc;
+  if (x->tma_upd && x->umap_key != U) {
+    rc = refresh_umaps(x, U);
+    if (rc != KH_OK) return rc;
+  }
   if (x->graph_on) {
     if (!(x->gexec && x->gkey[0] == U && x->gkey[1] == P && x->gkey[2] == B)) {
       drop_mesh_graph(x);
@@ -1522,6 +1815,13 @@ int kh_mesh_autotune(kh_mesh* x, const double* U, const double* P, const double*
   return KH_OK;
 }
 
+int kh_mesh_set_staged_update(kh_mesh* x, int enable) {
+  if (!x) return KH_EINVAL;
+  if (x->tma_off != !enable) drop_mesh_graph(x);
+  x->tma_off = !enable;
+  return x->tma_upd && !x->tma_off ? 1 : 0;
+}
+
 int kh_mesh_set_graph(kh_mesh* x, int enable) {
   if (!x) return KH_EINVAL;
   if (!enable) drop_mesh_graph(x);
@@ -1538,7 +1838,7 @@ int kh_mesh_destroy(kh_mesh* x) {
                   x->pflag, x->partial, x->dscalar, x->counters, x->F[0], x->F[1], x->F[2], x->ctop[0],
                   x->ctop[1], x->ctop[2], x->emf[0], x->emf[1], x->emf[2], x->Ff[0], x->Ff[1], x->Ff[2],
                   x->ctopf[0], x->ctopf[1], x->ctopf[2], x->emff[0], x->emff[1], x->emff[2],
-                  x->fBstar, x->ecc, x->eccf, x->dmatch};
+                  x->fBstar, x->ecc, x->eccf, x->dmatch, x->dtiles, x->dmaps, x->rk};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int q = 0; q < 8; ++q)

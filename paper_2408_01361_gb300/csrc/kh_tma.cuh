@@ -52,6 +52,13 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* tm, in
       : "memory");
 }
 
+// Makes a tensor map in global memory, written through the generic proxy (a
+// host-to-device copy), visible to the tensor copies that read it.
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap* tm) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<unsigned long long>(tm))
+               : "memory");
+}
+
 // Thread 0 of a CTA waits for the phase of parity `phase` of bar (its staged
 // tiles) with at most wlim polls. On a timeout it counts it (CNT_TIMEOUT) and
 // keeps polling -- up to KH_WAIT_POLLS more times -- until the copies it

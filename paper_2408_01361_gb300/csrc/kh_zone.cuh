@@ -448,30 +448,10 @@ struct MixedInGlobal {
 
 // The FP64 inversion of a zone whose double-float iteration handed it back
 // (C2P_NEED_FP64; a handful of zones per step once the flow has settled): the
-// FP64 solver from the FP32 stage input (Pin8) as the guess. Kept out of line
-// so that the update's hot path -- long straight-line code whose instruction
-// fetch already stalls it -- does not carry the FP64 solver. Returns the
-// solver's flag; on success Pn5 holds the fluid primitives.
-template <int INV>
-__device__ __noinline__ int mixed_fp64_fallback(const df64* Ud, const float* Pin8, DevGeom G, long long gplane,
-                                                long long p, double gam, double igam, double gfac, C2POpts o,
-                                                df64* Pn5) {
-  double Uf[NV], Pd[NV];
-#pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    Uf[v] = f64_of_df(Ud[v]);
-    Pd[v] = f64_of_f32(Pin8[v]);
-  }
-  const Met<double> m = load_met(G, gplane, LOC_CENT, p);
-  const int flag = invert<INV>(Uf, m, __ldg(G.flo + 2 * gplane + p), gam, igam, gfac, o, Pd);
-  if (flag == 0) {
-#pragma unroll
-    for (int v = 0; v < 5; ++v) Pn5[v] = df_of_f64(Pd[v]);
-  }
-  return flag;
-}
-
-// The same, inlined.
+// FP64 solver from the FP32 stage input (Pin8) as the guess. Returns the
+// solver's flag; on success Pn5 holds the fluid primitives. The out-of-line
+// form (mixed_fp64_fallback) keeps the FP64 solver off the hot path of an
+// update whose long straight-line code already stalls on instruction fetch.
 template <int INV>
 __device__ __forceinline__ int mixed_fp64_fallback_inl(const df64* Ud, const float* Pin8, DevGeom G, long long gplane,
                                                 long long p, double gam, double igam, double gfac, C2POpts o,
@@ -489,6 +469,30 @@ __device__ __forceinline__ int mixed_fp64_fallback_inl(const df64* Ud, const flo
     for (int v = 0; v < 5; ++v) Pn5[v] = df_of_f64(Pd[v]);
   }
   return flag;
+}
+
+// The same, out of line.
+template <int INV>
+__device__ __noinline__ int mixed_fp64_fallback(const df64* Ud, const float* Pin8, DevGeom G, long long gplane,
+                                                long long p, double gam, double igam, double gfac, C2POpts o,
+                                                df64* Pn5) {
+  return mixed_fp64_fallback_inl<INV>(Ud, Pin8, G, gplane, p, gam, igam, gfac, o, Pn5);
+}
+
+// A zone whose Lorentz-factor ceiling changed u~ (rare): its conserved
+// variables recomputed in FP64 from the floored primitives Pn and written to
+// Uc (stride plane). Inlined: out of line it cost the TMA-staged update 2%.
+__device__ __forceinline__ void recompute_u_fp64(const df64* Pn, const DevGeom& G, long long gplane, long long p,
+                                                 double gam, double* Uc, long long plane) {
+  double Pd[NV], U[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Pd[v] = f64_of_df(Pn[v]);
+  const Met<double> m = load_met(G, gplane, LOC_CENT, p);
+  FState<double> s;
+  fluid_state(Pd, m, s);
+  cons_only(Pd, s, m, gam, U);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Uc[v * plane] = U[v];
 }
 
 // The end of the mixed update when its inversion stays in FP64 for every
@@ -568,8 +572,8 @@ __device__ __forceinline__ void update_mixed_fp64_tail(double* U, const IN& in, 
 // INV = C2P_NOBLE2D_FP64: the FP64 Noble-2D for every zone from the FP64
 // U^n + increment (update_mixed_fp64_tail).
 // COLD: the FP64 fallback inversion is called out of line (the TMA-staged
-// kernel, whose instruction fetch stalls it: 1% faster so) or inlined (the
-// mesh's update at 128 registers: 5% faster so).
+// kernels, whose instruction fetch stalls them: 1% faster so) or inlined (the
+// mesh's own-loads update at 128 registers: 5% faster so).
 template <bool TRIAL, int INV, class IN, bool COLD = false>
 __device__ __forceinline__ void update_mixed_zone_in(const IN& in, const Vars& Pout64, const VarsT<float>& Pout32,
                                                      double* Uout, const Layout& L, const DevGeom& G,
@@ -606,30 +610,33 @@ __device__ __forceinline__ void update_mixed_zone_in(const IN& in, const Vars& P
       float a1, b1, a2, b2, a3 = 0.0f, b3 = 0.0f;
       const bool three = L.ndim == 3;
       if (in.has_emf() && v >= V_B1 && (three || v != V_B3)) {
+        // the field's face fluxes from the edge EMFs, each product rounded
+        // on its own (no fusing with the difference below)
         const float h = 0.5f;
+        auto em = [](float w, float e0, float e1) { return __fmul_rn(w, __fadd_rn(e0, e1)); };
         if (v == V_B1) {
           a1 = 0.0f;
           b1 = 0.0f;
-          a2 = -h * (in.e(2, 0, 0, 0) + in.e(2, 1, 0, 0));
-          b2 = -h * (in.e(2, 0, 1, 0) + in.e(2, 1, 1, 0));
+          a2 = em(-h, in.e(2, 0, 0, 0), in.e(2, 1, 0, 0));
+          b2 = em(-h, in.e(2, 0, 1, 0), in.e(2, 1, 1, 0));
           if (three) {
-            a3 = h * (in.e(1, 0, 0, 0) + in.e(1, 1, 0, 0));
-            b3 = h * (in.e(1, 0, 0, 1) + in.e(1, 1, 0, 1));
+            a3 = em(h, in.e(1, 0, 0, 0), in.e(1, 1, 0, 0));
+            b3 = em(h, in.e(1, 0, 0, 1), in.e(1, 1, 0, 1));
           }
         } else if (v == V_B2) {
-          a1 = h * (in.e(2, 0, 0, 0) + in.e(2, 0, 1, 0));
-          b1 = h * (in.e(2, 1, 0, 0) + in.e(2, 1, 1, 0));
+          a1 = em(h, in.e(2, 0, 0, 0), in.e(2, 0, 1, 0));
+          b1 = em(h, in.e(2, 1, 0, 0), in.e(2, 1, 1, 0));
           a2 = 0.0f;
           b2 = 0.0f;
           if (three) {
-            a3 = -h * (in.e(0, 0, 0, 0) + in.e(0, 0, 1, 0));
-            b3 = -h * (in.e(0, 0, 0, 1) + in.e(0, 0, 1, 1));
+            a3 = em(-h, in.e(0, 0, 0, 0), in.e(0, 0, 1, 0));
+            b3 = em(-h, in.e(0, 0, 0, 1), in.e(0, 0, 1, 1));
           }
         } else {  // B3, 3-D
-          a1 = -h * (in.e(1, 0, 0, 0) + in.e(1, 0, 0, 1));
-          b1 = -h * (in.e(1, 1, 0, 0) + in.e(1, 1, 0, 1));
-          a2 = h * (in.e(0, 0, 0, 0) + in.e(0, 0, 0, 1));
-          b2 = h * (in.e(0, 0, 1, 0) + in.e(0, 0, 1, 1));
+          a1 = em(-h, in.e(1, 0, 0, 0), in.e(1, 0, 0, 1));
+          b1 = em(-h, in.e(1, 1, 0, 0), in.e(1, 1, 0, 1));
+          a2 = em(h, in.e(0, 0, 0, 0), in.e(0, 0, 0, 1));
+          b2 = em(h, in.e(0, 0, 1, 0), in.e(0, 0, 1, 1));
         }
       } else {
         a1 = in.f(0, v, 0);
@@ -641,9 +648,10 @@ __device__ __forceinline__ void update_mixed_zone_in(const IN& in, const Vars& P
           b3 = in.f(2, v, 1);
         }
       }
-      float div = (b1 - a1) * i1 + (b2 - a2) * i2;
-      if (three) div += (b3 - a3) * i3;
-      const float inc = (cdt * (Sv[v] - div)).hi;  // c dt (S - div F)
+      // fused as written, so that every kernel inlining this rounds alike
+      float div = __fmaf_rn(b2 - a2, i2, __fmul_rn(b1 - a1, i1));
+      if (three) div = __fmaf_rn(b3 - a3, i3, div);
+      const float inc = (cdt * __fsub_rn(Sv[v], div)).hi;  // c dt (S - div F)
       const double u0 = in.u0(v);
       if (Uout) Uout[o] = u0 + f64_of_f32(inc);    // the conserved update, FP64
       if (dUout) dUout[o] = f64_of_f32(inc);       // the raw increment (Runge-Kutta stages)
@@ -734,15 +742,7 @@ __device__ __forceinline__ void update_mixed_zone_in(const IN& in, const Vars& P
     if (fmask && Uout) {
       double* Uc = Uout + c;
       if (fmask & 4) {  // the Lorentz-factor ceiling changed u~: full FP64 recompute
-        double Pd[NV], U[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) Pd[v] = f64_of_df(Pn[v]);
-        const Met<double> m = load_met(G, L.gplane, LOC_CENT, p);
-        FState<double> s;
-        fluid_state(Pd, m, s);
-        cons_only(Pd, s, m, S.gam, U);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) Uc[v * L.plane] = U[v];
+        recompute_u_fp64(Pn, G, L.gplane, p, S.gam, Uc, L.plane);
       } else {
         // at fixed u~ and B, U is linear in (rho, u): add
         // drho dU/drho + du dU/du, formed in FP32, to the FP64 U

@@ -120,6 +120,7 @@ def lib():
         L.kh_mesh_cfl_dt.argtypes = [vp, vp, vp, dp]
         L.kh_mesh_step.argtypes = [vp, vp, vp, vp, C.c_double, dp]
         L.kh_mesh_set_graph.argtypes = [vp, C.c_int]
+        L.kh_mesh_set_staged_update.argtypes = [vp, C.c_int]
         L.kh_mesh_divb.argtypes = [vp, vp, dp, dp]
         L.kh_mesh_set_launch.argtypes = [vp, C.c_int, C.c_int]
         L.kh_mesh_get_launch.argtypes = [vp, ip, ip]
@@ -534,6 +535,11 @@ class Mesh:
 
     def set_graph(self, enable: bool):
         _check(lib().kh_mesh_set_graph(self._h, 1 if enable else 0), "kh_mesh_set_graph")
+
+    def set_staged_update(self, enable: bool) -> bool:
+        """Select the TMA-staged mixed update (kh_mesh_set_staged_update);
+        True if it is selected and the mesh qualifies."""
+        return _check(lib().kh_mesh_set_staged_update(self._h, 1 if enable else 0), "kh_mesh_set_staged_update") == 1
 
     def stats(self) -> Stats:
         s = Stats()
