@@ -74,7 +74,7 @@ MIXED_MEAS = {
 }
 
 
-@pytest.mark.parametrize("integrator", ["ssprk54"])
+@pytest.mark.parametrize("integrator", ["rk2", "ssprk54"])
 def test_mesh_rk_mixed_staged(kh, orc, OM, integrator):
     base, blocks = _layout()
     base = dict(base, integrator=integrator)
@@ -87,8 +87,23 @@ def test_mesh_rk_mixed_staged(kh, orc, OM, integrator):
     Ug, Pg, _ = _gpu_rk(kh, base, blocks, Ps, U0, dt, 1, True, precision="mixed")
     a, r = _flat(base, blocks, Ug), _flat(base, blocks, Uo)
     pa, pr = _flat(base, blocks, Pg), _flat(base, blocks, Po)
+    mass, nz = np.abs(r[0]).sum(), r[0].size
+    # the single-grid mixed integrators' bars: relative L1 per variable,
+    # momenta and velocities against the mass scale near the equilibrium
+    for v in range(8):
+        tol = 2e-3 if v in (2, 3, 4) else 1e-4
+        assert np.abs(a[v] - r[v]).sum() / max(np.abs(r[v]).sum(), 1e-3 * mass) < tol, ("U", v)
+        assert np.abs(pa[v] - pr[v]).sum() / max(np.abs(pr[v]).sum(), 1e-2 * nz if v in (2, 3, 4) else 0.0) < tol, v
     eu, ep = elem_err(a, r), elem_err(pa, pr)
     print(integrator, "mixed RK mesh vs oracle: eU", eu, "eP", ep)
-    meas = MIXED_MEAS[integrator]
-    for v in range(8):  # within 5x of the measured error (floor 1e-9)
-        assert eu[v] < max(5.0 * meas["eU"][v], 1e-9) and ep[v] < max(5.0 * meas["eP"][v], 1e-9), v
+    if integrator in MIXED_MEAS:
+        meas = MIXED_MEAS[integrator]
+        for v in range(8):  # within 5x of the measured error (floor 1e-9)
+            assert eu[v] < max(5.0 * meas["eU"][v], 1e-9) and ep[v] < max(5.0 * meas["eP"][v], 1e-9), v
+    else:
+        # RK2's first stage is a full forward-Euler step: at the polar cap one
+        # zone more fails its inversion than in FP64 (242 against 241), and
+        # the zones its fixup and the second stage touch differ by O(1) of
+        # their small components; measured 19 zones of 27,648 above 1e-3
+        eb = np.abs(a - r) / np.maximum(np.abs(r), 1e-3 * np.abs(r).max(axis=1, keepdims=True))
+        assert int((eb.max(axis=0) > 1e-3).sum()) <= 5 * 19
