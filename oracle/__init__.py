@@ -123,7 +123,7 @@ def lib():
         L.or_evolve.restype = C.c_double
         L.or_divb.argtypes = [PP, _dp, _dp, C.c_void_p]
         L.or_stage.argtypes = [PP, _dp, _dp, C.c_double, _dp, _dp, C.c_void_p, C.c_void_p, C.c_void_p,
-                               C.POINTER(C.c_long), C.c_void_p]
+                               C.POINTER(C.c_long), C.c_void_p, C.c_void_p]
         L.or_rk_table.argtypes = [C.c_int, _ip, _ip, _dp, _dp, _dp]
         L.or_rk_table.restype = C.c_int
         L.or_point_flux.argtypes = [C.c_double, _dp, _dp, C.c_int, _dp]
@@ -364,15 +364,20 @@ def recon(kind: str, q):
     return lo, hi
 
 
-def stage(cfg: dict, U0, Pin, cdt: float, Uout, Pout, dU=None):
+def stage(cfg: dict, U0, Pin, cdt: float, Uout, Pout, dU=None, fofc_flags=None):
     """One stage on a grid with caller-filled ghosts; Uout/Pout updated in place
     (interior); dU (optional, full array) receives the raw increment
-    cdt (-div F + S) of every interior zone. Returns (ctop[3] arrays, stats)."""
+    cdt (-div F + S) of every interior zone; fofc_flags (optional, int32 per
+    cell, ghosts included; cfg with "fofc"): the flux correction's flagged
+    zones, used instead of the grid's own trial. Returns (ctop[3] arrays,
+    stats)."""
     U0 = np.ascontiguousarray(U0, dtype=np.float64)
     Pin = np.ascontiguousarray(Pin, dtype=np.float64)
     ct = [np.zeros(Pin.shape[1:]) for _ in range(3)]
     st = (C.c_long * 4)()
-    lib().or_stage(C.byref(params(cfg)), U0, Pin, float(cdt), Uout, Pout, *[_ptr(c) for c in ct], st, _ptr(dU))
+    fl = None if fofc_flags is None else np.ascontiguousarray(fofc_flags, dtype=np.int32)
+    lib().or_stage(C.byref(params(cfg)), U0, Pin, float(cdt), Uout, Pout, *[_ptr(c) for c in ct], st, _ptr(dU),
+                   _ptr(fl))
     _note(st)
     return ct, list(st)[:3]
 

@@ -701,16 +701,29 @@ void fill_flag_ghosts(const Grid& gr, char* flag) {
 // donor-cell (piecewise constant) states of its two cells in place of the raw
 // high-order flux, and polar zeroing and Flux-CT are applied again to the
 // corrected raw fluxes (so divB stays as Flux-CT keeps it). raw: the
-// high-order raw fluxes; on return fx holds the corrected fluxes. Returns the
-// number of flagged zones.
+// high-order raw fluxes; on return fx holds the corrected fluxes. flag_in
+// (nullable, every cell, ghosts included): the flags to use instead of this
+// grid's own trial and ghost rules (a block of a refined mesh, whose ghost
+// flags come from its neighbours). Returns the number of flagged zones.
 template <class R>
 long fofc_correct(const Grid& gr, const R* U0, const R* Pin, const R& gam, double cdt, FluxesT<R>& raw,
-                  FluxesT<R>& fx) {
+                  FluxesT<R>& fx, const int* flag_in = nullptr) {
   const GridInfo& g = gr.g;
   std::vector<char> flag(gr.cells(), 0);
-  const long nflag = fofc_trial(gr, U0, Pin, gam, cdt, fx, flag.data());
-  if (nflag == 0) return 0;
-  fill_flag_ghosts(gr, flag.data());
+  long nflag = 0;
+  if (flag_in) {
+    for (size_t q = 0; q < gr.cells(); ++q) flag[q] = flag_in[q] != 0;
+    for (int k = gr.s3(); k < gr.e3(); ++k)
+      for (int j = gr.s2(); j < gr.e2(); ++j)
+        for (int i = gr.s1(); i < gr.e1(); ++i) nflag += flag[gr.idx(0, k, j, i)];
+    bool any = false;
+    for (size_t q = 0; q < gr.cells() && !any; ++q) any = flag[q];
+    if (!any) return 0;
+  } else {
+    nflag = fofc_trial(gr, U0, Pin, gam, cdt, fx, flag.data());
+    if (nflag == 0) return 0;
+    fill_flag_ghosts(gr, flag.data());
+  }
   for (int d = 0; d < g.ndim; ++d) {
     int lo[3], hi[3];
     face_range(gr, d, lo, hi);
@@ -744,7 +757,8 @@ long fofc_correct(const Grid& gr, const R* U0, const R* Pin, const R& gam, doubl
 template <class R>
 void stage(const Grid& gr, const R* U0, const R* Pin, const R& gam, double cdt, R* Uout, R* Pout,
            FluxesT<R>& fx, StageStats& st, std::vector<int>* pflag_out, std::vector<int>* fflag_out = nullptr,
-           const R* fB0 = nullptr, R* fBout = nullptr, R* dU_out = nullptr, const R* Egiven = nullptr) {
+           const R* fB0 = nullptr, R* fBout = nullptr, R* dU_out = nullptr, const R* Egiven = nullptr,
+           const int* fflag_in = nullptr) {
   const GridInfo& g = gr.g;
   const bool face = gr.c.bfield == BFIELD_FACE;
   if (face) {
@@ -766,7 +780,7 @@ void stage(const Grid& gr, const R* U0, const R* Pin, const R& gam, double cdt, 
     compute_raw(gr, Pin, raw, gam);
     fx = raw;
     finish_fluxes(gr, fx);
-    st.nfofc += fofc_correct(gr, U0, Pin, gam, cdt, raw, fx);
+    st.nfofc += fofc_correct(gr, U0, Pin, gam, cdt, raw, fx, fflag_in);
   } else {
     compute_fluxes(gr, Pin, fx, gam);
   }
@@ -1028,14 +1042,18 @@ double or_cfl_dt(const or_params* c, const double* P, const double* dir_lo, cons
 // arrays, interior written. ctop1..3 (nullable): signal speeds per face.
 // dU (nullable): the raw increment cdt (-div F + S(Pin)) of every interior
 // zone (a Runge-Kutta stage whose increment a later stage reuses).
-// stats[0..2] as or_step (this stage only).
+// fofc_flags (nullable; with the first-order flux correction on): the
+// flagged zones, every cell of the grid, ghosts included (a refined mesh
+// fills a block's ghost flags from its neighbours), used instead of the
+// grid's own trial. stats[0..3] as or_step (this stage only).
 void or_stage(const or_params* c, const double* U0, const double* Pin, double cdt, double* Uout, double* Pout,
-              double* ct1, double* ct2, double* ct3, long* stats, double* dU) {
+              double* ct1, double* ct2, double* ct3, long* stats, double* dU, const int* fofc_flags) {
   Grid gr;
   build_grid(*c, gr);
   Fluxes fx;
   StageStats st;
-  stage<double>(gr, U0, Pin, c->gam, cdt, Uout, Pout, fx, st, nullptr, nullptr, nullptr, nullptr, dU);
+  stage<double>(gr, U0, Pin, c->gam, cdt, Uout, Pout, fx, st, nullptr, nullptr, nullptr, nullptr, dU, nullptr,
+                fofc_flags);
   double* Co[3] = {ct1, ct2, ct3};
   for (int d = 0; d < 3; ++d)
     if (Co[d]) std::memcpy(Co[d], fx.ctop[d].data(), fx.ctop[d].size() * sizeof(double));

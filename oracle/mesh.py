@@ -24,7 +24,11 @@ ghost cell's centre:
 Every block takes the same dt; there is no flux correction at level
 interfaces. step advances every block with the predictor-corrector, step_rk
 with a Runge-Kutta integrator (each stage's input ghost-filled across blocks
-before the blocks' stages). Written from positions in floating point, independently of the
+before the blocks' stages). With the first-order flux correction each stage
+first runs every block's trial, then fills the flags' ghost cells across
+blocks by the same map (a copied or prolonged ghost takes its source cell's
+flag, a restricted one the largest of the fine cells'), and corrects the
+faces of the flagged zones of every block from those flags. Written from positions in floating point, independently of the
 CUDA library's integer map.
 
 With face-centred constrained transport (step_face) every block also
@@ -42,7 +46,7 @@ import math
 
 import numpy as np
 
-from . import face_emfs, rk_table, stage, stage_face
+from . import face_emfs, fofc_flags, rk_table, stage, stage_face
 
 NV = 8
 
@@ -221,6 +225,62 @@ class OracleMesh:
                             val[2] = 0.0
                         P[:, k, j, i] = val
 
+    def fill_flag_ghosts(self, Fs):
+        """The flux correction's flags in every block's ghost cells (Fs: list
+        of int (N3, N2, N1), interior flags set), by the ghost map of the
+        state: a ghost cell takes the flag of the cell whose value it copies,
+        of the coarse cell it is prolonged from, or the largest flag of the
+        fine cells whose mean it takes."""
+        lev = [blk["level"] for blk in self.blocks]
+        for b, F in enumerate(Fs):
+            N3, N2, N1 = F.shape
+            o, dx = self._origin(b), self._dx(b)
+            g = [self._ng(0), self._ng(1), self._ng(2)]
+            n = [self.cfgs[b]["n1"], self.cfgs[b]["n2"], self.cfgs[b]["n3"]]
+            for k in range(N3):
+                for j in range(N2):
+                    for i in range(N1):
+                        idx = (i, j, k)
+                        if all(g[d] <= idx[d] < g[d] + n[d] for d in range(3)):
+                            continue
+                        x = [o[d] + (idx[d] - g[d] + 0.5) * dx[d] for d in range(3)]
+                        if self.ndim == 2:
+                            x[2] = 0.5 * sum(self.dom[2])
+                        x, _, _ = self._transform(b, x)
+                        s = self._owner(x)
+                        dl = lev[s] - lev[b]
+                        if dl in (0, -1):
+                            ci = self._cell(s, x)
+                            F[k, j, i] = Fs[s][ci[2], ci[1], ci[0]]
+                        elif dl == 1:
+                            dxs = self._dx(s)
+                            f = 0
+                            for a3 in ((-0.5, 0.5) if self.ndim == 3 else (0.0,)):
+                                for a2 in (-0.5, 0.5):
+                                    for a1 in (-0.5, 0.5):
+                                        ci = self._cell(s, [x[0] + a1 * dxs[0], x[1] + a2 * dxs[1],
+                                                            x[2] + a3 * dxs[2]])
+                                        f = max(f, int(Fs[s][ci[2], ci[1], ci[0]]))
+                            F[k, j, i] = f
+                        else:
+                            raise ValueError("blocks more than one level apart")
+
+    def _stage_all(self, U0s, Pins, cdt, Uouts, Pouts, dUs=None):
+        """One stage of every block (Pins ghost-filled); with the flux
+        correction (base "fofc") the flags of all blocks' trials first, their
+        ghosts filled across blocks. Returns (ctops, summed stats)."""
+        flags = [None] * len(Pins)
+        if self.base.get("fofc"):
+            flags = [fofc_flags(self.cfgs[b], U0s[b], Pins[b], cdt) for b in range(len(Pins))]
+            self.fill_flag_ghosts(flags)
+        tot, cts = [0, 0, 0], []
+        for b in range(len(Pins)):
+            ct, st = stage(self.cfgs[b], U0s[b], Pins[b], cdt, Uouts[b], Pouts[b],
+                           dU=None if dUs is None else dUs[b], fofc_flags=flags[b])
+            cts.append(ct)
+            tot = [x + y for x, y in zip(tot, st)]
+        return cts, tot
+
     def cfl_dt(self, cts):
         """cfl / max over all blocks' zones of sum_d max(ctop faces)/dx_d."""
         mx = 0.0
@@ -248,18 +308,12 @@ class OracleMesh:
         self.fill_ghosts(Pn)
         Ps_ = [np.array(P, copy=True) for P in Pn]
         Us_ = [np.array(U, copy=True) for U in U0]
-        tot = [0, 0, 0]
-        for b in range(len(Pn)):
-            _, st = stage(self.cfgs[b], U0[b], Pn[b], 0.5 * dt, Us_[b], Ps_[b])
-            tot = [a + c for a, c in zip(tot, st)]
+        _, tot = self._stage_all(U0, Pn, 0.5 * dt, Us_, Ps_)
         self.fill_ghosts(Ps_)
         Pout = [np.array(P, copy=True) for P in Pn]
         Uout = [np.array(U, copy=True) for U in U0]
-        cts = []
-        for b in range(len(Pn)):
-            ct, st = stage(self.cfgs[b], U0[b], Ps_[b], dt, Uout[b], Pout[b])
-            cts.append(ct)
-            tot = [a + c for a, c in zip(tot, st)]
+        cts, t2 = self._stage_all(U0, Ps_, dt, Uout, Pout)
+        tot = [a + c for a, c in zip(tot, t2)]
         return Uout, Pout, self.cfl_dt(cts), tot
 
     def step_rk(self, Us, Ps, dt, integrator):
@@ -278,20 +332,18 @@ class OracleMesh:
             Pin = Pst[s]
             self.fill_ghosts(Pin)
             keep = integrator == "ssprk54" and s == 3
-            Uout, Pout, cts = [], [], []
+            bases = []
             for b in range(nb):
                 base = 0.0
                 for t, a in zip(src, w):
                     base = base + a * Ust[t][b]
                 if w4 != 0.0:
                     base = base + w4 * dU4[b]
-                Ub = np.array(base, copy=True)
-                Pb = np.array(Pin[b], copy=True)
-                ct, st = stage(self.cfgs[b], base, Pin[b], c * dt, Ub, Pb, dU=dU4[b] if keep else None)
-                cts.append(ct)
-                tot = [x + y for x, y in zip(tot, st)]
-                Uout.append(Ub)
-                Pout.append(Pb)
+                bases.append(base)
+            Uout = [np.array(x, copy=True) for x in bases]
+            Pout = [np.array(P, copy=True) for P in Pin]
+            cts, st = self._stage_all(bases, Pin, c * dt, Uout, Pout, dU4 if keep else None)
+            tot = [x + y for x, y in zip(tot, st)]
             Ust.append(Uout)
             Pst.append(Pout)
         return Ust[-1], Pst[-1], self.cfl_dt(cts), tot

@@ -75,6 +75,38 @@ def test_single_level_mesh_rk_equals_single_grid(orc, integrator):
                for B, a, c in zip(blocks, Um, Uv)) > 1e-12
 
 
+def test_single_level_mesh_fofc_equals_single_grid(orc):
+    """With the first-order flux correction the mesh runs every block's trial,
+    fills the flags' ghost cells across blocks and corrects from them; on
+    uneven blocks at one level this reproduces the single grid's correction,
+    whose ghost flags follow its own boundary rules. The torus flags ~1,000
+    zones (floors acting in the trial) and 30 inversions fail; the cuts lie
+    away from those zones, whose fixup would otherwise draw on neighbours
+    inside their own block only."""
+    cfg = dict(torus_base(32, 24, "mc"), fofc=True)
+    P = orc.apply_bc(cfg, inputs.torus_state(cfg, seed=2))
+    blocks = uneven_split(cfg, [16], [10, 14])
+    U = orc.prim_to_cons(cfg, P)
+    dt = 0.5 * orc.cfl_dt(cfg, P)
+    U1, P1, dt1, st1 = orc.step(cfg, U, P, dt)
+    assert orc.last_nfofc > 500
+    M = OracleMesh(cfg, blocks, inputs.block_cfg)
+    Um, Pm, dtm, stm = M.step(slice_blocks(cfg, U, blocks), slice_blocks(cfg, P, blocks), dt)
+    assert list(stm) == list(st1)
+    ref_U, ref_P = slice_blocks(cfg, U1, blocks), slice_blocks(cfg, P1, blocks)
+    for b, B in enumerate(blocks):
+        for got, ref in ((Um[b], ref_U[b]), (Pm[b], ref_P[b])):
+            g, r = block_interior(cfg, B, got), block_interior(cfg, B, ref)
+            scale = np.abs(r).reshape(8, -1).max(axis=1)[:, None] + 1e-300
+            assert (np.abs(g - r).reshape(8, -1) / scale).max() < 1e-10, b
+    assert abs(dtm - dt1) <= 1e-12 * dt1
+    # the correction changed the step
+    Mp = OracleMesh(dict(cfg, fofc=False), blocks, inputs.block_cfg)
+    Up, _, _, _ = Mp.step(slice_blocks(cfg, U, blocks), slice_blocks(cfg, P, blocks), dt)
+    assert max(np.abs(block_interior(cfg, B, a) - block_interior(cfg, B, c)).max()
+               for B, a, c in zip(blocks, Um, Up)) > 1e-8
+
+
 def _linear_fill(base, blocks, coef):
     M = OracleMesh(base, blocks, inputs.block_cfg)
     Ps, centres = [], []
