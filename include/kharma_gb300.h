@@ -86,9 +86,11 @@ typedef struct {
                              donor-cell (first-order) LLF flux, and polar zeroing and
                              Flux-CT are applied again before the stage's update. The
                              flags' ghost zones follow the state's ghost map (Dirichlet
-                             ghosts unflagged). 0: off. Single-grid contexts with
-                             Flux-CT, with any integrator (the mesh, face CT and
-                             the adjoint refuse it). */
+                             ghosts unflagged; on a refined mesh a ghost takes the
+                             flag of the cell it copies or is prolonged from, or the
+                             largest flag of the fine cells it restricts). 0: off.
+                             With Flux-CT, any integrator, single grids and meshes
+                             (face CT and the adjoint refuse it). */
   int bfield;             /* KH_B_FLUXCT: cell-centred field, Flux-CT (Toth 2000);
                              KH_B_FACE: face-centred constrained transport
                              ("Algorithm" section: Stone & Gardiner 2009). The face
@@ -399,10 +401,14 @@ int kh_get_stage_flux(kh_ctx* ctx, int dir, double* F);
  * face divergence stays zero in every block (interfaces across a periodic
  * domain edge are not matched).
  *
+ * The mesh takes every kh_coords option of a single grid except face-centred
+ * CT together with a Runge-Kutta integrator or with the flux correction.
+ *
  * kh_mesh_init returns KH_EINVAL for blocks that overlap, leave a hole, are
  * smaller than 4 cells a side (n3 == 1 in 2-D), are misaligned, meet a block
- * more than one level away, or for more than 5 levels or 2^31 cells; it
- * copies the block list, so the caller may free it on return. */
+ * more than one level away, or for more than 5 levels or 2^31 cells, and for
+ * the option combinations above; it copies the block list, so the caller may
+ * free it on return. */
 typedef struct {
   int level;
   int i0, j0, k0;  /* first interior cell in level-l indices */

@@ -266,6 +266,94 @@ __global__ void __launch_bounds__(256, 3)
       dUout ? dUout + NV * m.off : nullptr);
 }
 
+// ---- first-order flux correction over all blocks (as the single grid's
+// k_fofc_trial / k_flag_ghosts / k_fofc_faces) ----
+// The trial update of every interior zone from the corrected-so-far fluxes:
+// flag = 1 where the inversion fails or a floor or ceiling would act.
+template <int INV>
+__global__ void __launch_bounds__(256) km_fofc_trial(const MBlock* blk, const unsigned* pre, int nb, const double* U0,
+                                                    Arena<double> Pin, const double* F1, const double* F2,
+                                                    const double* F3, GeoArena GA, Scheme S, const double* dtp,
+                                                    double coef, int8_t* flag, unsigned long long* cnt) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= __ldg(pre + nb)) return;
+  const int b = find_block(pre, nb, t);
+  const MBlock& m = blk[b];
+  int i, j, k;
+  zone_ijk(m.L, t - __ldg(pre + b), i, j, k);
+  const long long o8 = NV * m.off;
+  update_zone<true, INV>(U0 + o8, cvars_at(Pin, m), Vars{}, nullptr, F1 + o8, F2 + o8,
+                         m.L.ndim == 3 ? F3 + o8 : nullptr, m.L, geo64(GA, m), S, coef * __ldg(dtp), flag + m.off,
+                         cnt, i, j, k);
+}
+
+template <int INV>
+__global__ void __launch_bounds__(256, 2) km_fofc_trial_mixed(const MBlock* blk, const unsigned* pre, int nb,
+                                                          const double* U0, Arena<float> Pin, const float* F1,
+                                                          const float* F2, const float* F3, GeoArena GA, Scheme S,
+                                                          const double* dtp, double coef, int8_t* flag,
+                                                          unsigned long long* cnt, const float* e1, const float* e2,
+                                                          const float* e3) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= __ldg(pre + nb)) return;
+  const int b = find_block(pre, nb, t);
+  const MBlock& m = blk[b];
+  int i, j, k;
+  zone_ijk(m.L, t - __ldg(pre + b), i, j, k);
+  const long long o8 = NV * m.off;
+  update_mixed_zone<true, INV>(U0 + o8, cvars_at(Pin, m), Vars{}, VarsT<float>{}, nullptr, F1 + o8, F2 + o8,
+                               m.L.ndim == 3 ? F3 + o8 : nullptr, m.L, geo64(GA, m), geo32(GA, m), S,
+                               df_of_f64(coef * __ldg(dtp)), flag + m.off, cnt, i, j, k, FailList{nullptr, nullptr},
+                               nullptr, nullptr,
+                               CtEmf{{e1 ? e1 + m.off : nullptr, e2 ? e2 + m.off : nullptr, e3 + m.off}});
+}
+
+// The flags' ghost cells by the state's ghost map: a copied or prolonged
+// ghost takes its source cell's flag, a restricted one the largest flag of
+// the 2x2(x2) fine cells whose mean it takes.
+__global__ void km_flag_ghost(const MBlock* blk, const GhostOp* ops, long long nops, int8_t* flag) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= nops) return;
+  const GhostOp op = ops[t];
+  const MBlock& ms = blk[op.src_block];
+  const int8_t* fs = flag + ms.off;
+  int8_t f = fs[op.src_cell];
+  if (op.mode == G_RESTRICT) {
+    const Layout& L = ms.L;
+    const long long sj = L.n1s, sk = (long long)L.n1s * L.n2s;
+    for (int dk = 0; dk < (L.ndim == 3 ? 2 : 1); ++dk)
+      for (int dj = 0; dj < 2; ++dj)
+        for (int di = 0; di < 2; ++di) f = max(f, fs[op.src_cell + di + dj * sj + dk * sk]);
+  }
+  flag[blk[op.dst_block].off + op.dst_cell] = f;
+}
+
+// Every face of every block's face box that borders a flagged cell takes the
+// LLF flux of its two cells' own (donor-cell) states.
+template <int D, class TIN, class R>
+__global__ void __launch_bounds__(256) km_fofc_faces(const MBlock* blk, const unsigned* pre, int nb, Arena<TIN> P,
+                                                    GeoArena GA, Scheme S, const int8_t* flag, R* F, R* ctop) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= __ldg(pre + nb)) return;
+  const int b = find_block(pre, nb, t);
+  const MBlock& m = blk[b];
+  int i, j, k;
+  const FaceBox& fb = m.fb[D - 1];
+  split3(t - __ldg(pre + b), fb.n[0], fb.n[1], i, j, k);
+  i += fb.lo[0];
+  j += fb.lo[1];
+  k += fb.lo[2];
+  const Layout& L = m.L;
+  const long long c = L.at(k, j, i);
+  const long long st = D == 1 ? 1 : (D == 2 ? (long long)L.n1s : (long long)L.n1s * L.n2s);
+  const int8_t* fl = flag + m.off;
+  if (!(fl[c] | fl[c - st])) return;
+  GeomT<R> G;
+  if constexpr (sizeof(R) == sizeof(double)) G = geo64(GA, m); else G = geo32(GA, m);
+  flux_face<D, RECON_DONOR, TIN, R>(cvars_at(P, m), L, G, S, i, j, k, F + NV * m.off, ctop + m.off, m.polar_lo,
+                                    m.polar_hi);
+}
+
 template <class T>
 __global__ void km_fixup(const MBlock* blk, const unsigned* pre, int nb, Arena<T> P, double* Uout,
                          const int8_t* pflag, GeoArena GA, Scheme S, unsigned long long* cnt) {
@@ -662,6 +750,10 @@ struct kh_mesh {
   // RK1: 0), the stage base and (SSPRK(5,4)) stage 4's raw increment, each
   // 8 planes of every block's cells
   double* rk;
+  // first-order flux correction: the flags (every cell) and, FP64, the raw
+  // fluxes saved before Flux-CT (8 planes of every block's cells per direction)
+  int8_t* fflag;
+  double* fsave;
   // TMA-staged mixed update (3-D Flux-CT, Noble-2D, every block 16 or 32
   // zones wide): tiles of the 16-wide blocks, then of the 32-wide ones; two
   // map sets per block (stage 1 and 2 inputs), host copy and device table
@@ -709,7 +801,8 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
   if (c->kind < KH_MINKOWSKI || c->kind > KH_FMKS || c->n1 < 2 || c->n2 < 2 || c->n3 < 1) return KH_EINVAL;
   if (c->precision != KH_FP64 && c->precision != KH_MIXED) return KH_EINVAL;
   if (c->recon != KH_RECON_MC && c->recon != KH_RECON_WENO5) return KH_EINVAL;
-  if (c->fofc) return KH_EINVAL;  // the flux correction runs on single grids
+  if (c->fofc != 0 && c->fofc != 1) return KH_EINVAL;
+  if (c->fofc && c->bfield == KH_B_FACE) return KH_EINVAL;  // the correction runs with Flux-CT
   if (c->inverter < KH_INV_NOBLE2D || c->inverter > KH_INV_KASTAUN) return KH_EINVAL;
   if (c->integrator < KH_INT_VL2 || c->integrator > KH_INT_SSPRK54) return KH_EINVAL;
   // Runge-Kutta stages carry U (and P) only: with face-centred CT the face field would be stage state too
@@ -748,6 +841,7 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
   S.bfield = c->bfield;
   S.emf = c->emf;
   S.integrator = c->integrator;
+  S.fofc = c->fofc;
   set_mixed(S);
   x->cp = CoordParams{c->kind, a, c->x1min, c->hslope, c->poly_xt, c->poly_alpha, c->mks_smooth};
 
@@ -1116,6 +1210,10 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
     KM_ALLOC(x->fBstar, 3 * pl);
     KM_ALLOC(x->dmatch, sizeof(EmfMatch) * std::max<long long>(x->nmatch, 1));
   }
+  if (c->fofc) {
+    KM_ALLOC(x->fflag, (size_t)cells);
+    if (!mixed) KM_ALLOC(x->fsave, (size_t)x->ndim * NV * pl);
+  }
   if (c->integrator != KH_INT_VL2)
     KM_ALLOC(x->rk, (size_t)(rk_states(c->integrator) + (c->integrator == KH_INT_SSPRK54 ? 2 : 1)) * NV * pl);
   x->npartial = 152 * 4;
@@ -1188,6 +1286,7 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
     if (rc == KH_OK && x->emff[d]) rc = cuda_rc(cudaMemset(x->emff[d], 0, plf));
   }
   if (rc == KH_OK) rc = cuda_rc(cudaMemset(x->pstar, 0, NV * pl));
+  if (rc == KH_OK && x->fflag) rc = cuda_rc(cudaMemset(x->fflag, 0, (size_t)cells));
   if (rc == KH_OK && x->pstarf) rc = cuda_rc(cudaMemset(x->pstarf, 0, NV * plf));
   if (rc == KH_OK && x->pnf) rc = cuda_rc(cudaMemset(x->pnf, 0, NV * plf));
   // geometry of every block
@@ -1236,6 +1335,19 @@ template <class T> int fill_ghosts(kh_mesh* x, const Arena<T>& P) {
 // fluxct: Flux-CT after the face fluxes (its EMF phase; the field-flux phase
 // too unless emf_only, for an update that forms the field fluxes from the
 // EMFs).
+// Flux-CT over all blocks: the edge EMFs, then (unless emf_only) the field
+// fluxes rewritten from them.
+template <class R> int ct_pass(kh_mesh* x, R* const F[3], R* const emf[3], bool emf_only) {
+  const unsigned tot = x->pre_ct.back();
+  int n = 0;
+  for (int phase = 0; phase < (emf_only ? 1 : 2); ++phase) {
+    km_ct<R><<<nblk(tot, MTPB), MTPB, 0, x->stream>>>(x->dblk, x->dpre[4], x->nb, F[0], F[1], F[2], emf[0], emf[1],
+                                                      emf[2], phase);
+    ++n;
+  }
+  return n;
+}
+
 template <class TIN, class R>
 int flux_pass(kh_mesh* x, const Arena<TIN>& P, R* const F[3], R* const ct[3], R* const emf[3], bool fluxct = true,
               bool emf_only = false) {
@@ -1256,13 +1368,65 @@ int flux_pass(kh_mesh* x, const Arena<TIN>& P, R* const F[3], R* const ct[3], R*
 #undef KM_FLUX
     ++n;
   }
-  const unsigned tot = x->pre_ct.back();
-  for (int phase = 0; phase < (emf_only ? 1 : 2) && fluxct; ++phase) {
-    km_ct<R><<<nblk(tot, MTPB), MTPB, 0, x->stream>>>(x->dblk, x->dpre[4], x->nb, F[0], F[1], F[2], emf[0], emf[1],
-                                                      emf[2], phase);
+  if (fluxct) n += ct_pass(x, F, emf, emf_only);
+  return n;
+}
+
+// The first-order flux correction of one stage over all blocks (Flux-CT),
+// after the flux pass: the trial update of every zone from U0 with the
+// fluxes so far, the flags' ghost cells, donor-cell fluxes on the faces of
+// the flagged zones (FP64: on the raw fluxes saved before Flux-CT, restored
+// first), Flux-CT again (mixed: the EMFs only; its raw field fluxes were
+// never overwritten).
+template <class TIN, class R>
+int fofc_pass(kh_mesh* x, const double* U0, const Arena<TIN>& P, R* const F[3], R* const ct[3], R* const emf[3],
+              double coef) {
+  cudaStream_t s = x->stream;
+  const GeoArena GA = garena(x);
+  const unsigned nz = x->pre_zone.back();
+  const int g = nblk(nz, 256);
+  constexpr bool mixed = sizeof(R) == sizeof(float);
+  auto go = [&](auto kern) {
+    if constexpr (mixed)
+      kern<<<g, 256, 0, s>>>(x->dblk, x->dpre[3], x->nb, U0, P, F[0], F[1], F[2], GA, x->S, x->dscalar + 3, coef,
+                             x->fflag, x->counters, x->ndim == 3 ? emf[0] : nullptr,
+                             x->ndim == 3 ? emf[1] : nullptr, emf[2]);
+    else
+      kern<<<g, 256, 0, s>>>(x->dblk, x->dpre[3], x->nb, U0, P, F[0], F[1], F[2], GA, x->S, x->dscalar + 3, coef,
+                             x->fflag, x->counters);
+  };
+  if constexpr (mixed) {
+    if (x->S.c2p.method == C2P_KASTAUN) go(km_fofc_trial_mixed<C2P_KASTAUN>);
+    else if (x->S.c2p.method == C2P_1DW) go(km_fofc_trial_mixed<C2P_1DW>);
+    else if (x->S.mixed_fp64) go(km_fofc_trial_mixed<C2P_NOBLE2D_FP64>);
+    else go(km_fofc_trial_mixed<C2P_NOBLE2D>);
+  } else {
+    if (x->S.c2p.method == C2P_KASTAUN) go(km_fofc_trial<C2P_KASTAUN>);
+    else if (x->S.c2p.method == C2P_1DW) go(km_fofc_trial<C2P_1DW>);
+    else go(km_fofc_trial<C2P_NOBLE2D>);
+  }
+  int n = 1;
+  if (x->nops) {
+    km_flag_ghost<<<nblk(x->nops, MTPB), MTPB, 0, s>>>(x->dblk, x->dops, x->nops, x->fflag);
     ++n;
   }
-  return n;
+  if constexpr (!mixed) {
+    const size_t bytes = (size_t)NV * x->cells * sizeof(double);
+    for (int d = 0; d < x->ndim; ++d)
+      cudaMemcpyAsync(F[d], x->fsave + (size_t)d * NV * x->cells, bytes, cudaMemcpyDeviceToDevice, s);
+  }
+  for (int d = 1; d <= x->ndim; ++d) {
+    const unsigned tot = x->pre_face[d - 1].back();
+    auto faces = [&](auto kern) {
+      kern<<<nblk(tot, 256), 256, 0, s>>>(x->dblk, x->dpre[d - 1], x->nb, P, GA, x->S, x->fflag, F[d - 1],
+                                          ct[d - 1]);
+    };
+    if (d == 1) faces(km_fofc_faces<1, TIN, R>);
+    else if (d == 2) faces(km_fofc_faces<2, TIN, R>);
+    else faces(km_fofc_faces<3, TIN, R>);
+    ++n;
+  }
+  return n + ct_pass(x, F, emf, mixed);
 }
 
 // Face-centred CT of one stage over all blocks (after the flux pass without
@@ -1400,7 +1564,17 @@ int mesh_stage64(kh_mesh* x, const double* U0, const Arena<double>& Pin, const A
   const bool face = x->S.bfield == KH_B_FACE;
   const unsigned nz = x->pre_zone.back();
   int n = fill_ghosts(x, Pin);
-  n += flux_pass<double, double>(x, Pin, x->F, x->ctop, x->emf, !face);
+  if (x->S.fofc) {
+    // Flux-CT overwrites the raw field fluxes; the correction needs them again
+    n += flux_pass<double, double>(x, Pin, x->F, x->ctop, x->emf, false);
+    const size_t bytes = (size_t)NV * x->cells * sizeof(double);
+    for (int d = 0; d < x->ndim; ++d)
+      cudaMemcpyAsync(x->fsave + (size_t)d * NV * x->cells, x->F[d], bytes, cudaMemcpyDeviceToDevice, x->stream);
+    n += ct_pass<double>(x, x->F, x->emf, false);
+    n += fofc_pass<double, double>(x, U0, Pin, x->F, x->ctop, x->emf, coef);
+  } else {
+    n += flux_pass<double, double>(x, Pin, x->F, x->ctop, x->emf, !face);
+  }
   if (face) n += face_ct_pass<double>(x, Pin, x->F, x->ecc, x->emf, fBst, coef);
   km_update_any(x, nblk(nz, x->tpb_update), x->tpb_update, U0, Pin, Pout, Uout, coef, face ? fBst : nullptr, dUout);
   km_fixup<double><<<nblk(nz, MTPB), MTPB, 0, x->stream>>>(x->dblk, x->dpre[3], x->nb, Pout, Uout, x->pflag,
@@ -1430,6 +1604,7 @@ int mesh_stage_mixed(kh_mesh* x, bool first, const double* U, const double* U0, 
   // Flux-CT: EMFs only, the update forms the field fluxes from them
   const float* ce[3] = {face ? nullptr : x->emff[0], face ? nullptr : x->emff[1], face ? nullptr : x->emff[2]};
   n += flux_pass<float, float>(x, Pin, x->Ff, x->ctopf, x->emff, !face, true);
+  if (x->S.fofc) n += fofc_pass<float, float>(x, U0, Pin, x->Ff, x->ctopf, x->emff, coef);
   if (face) n += face_ct_pass<float>(x, Pin, x->Ff, x->eccf, x->emff, fBst, coef);
   const bool staged = set >= 0 && x->tma_upd && !x->tma_off && x->tma_now && x->umap_key == U && !face;
   if (staged) {
@@ -1646,7 +1821,7 @@ int kh_mesh_get_stats(kh_mesh* x, kh_stats* out) {
   out->nfloor = (int64_t)h[CNT_FLOOR];
   out->nunfixed = (int64_t)h[CNT_UNFIXED];
   out->nfp64 = (int64_t)h[CNT_FP64];
-  out->nfofc = 0;
+  out->nfofc = (int64_t)h[CNT_FOFC];
   out->nbounds = 0;
   out->dt_cfl = dt;
   return KH_OK;
@@ -1838,7 +2013,7 @@ int kh_mesh_destroy(kh_mesh* x) {
                   x->pflag, x->partial, x->dscalar, x->counters, x->F[0], x->F[1], x->F[2], x->ctop[0],
                   x->ctop[1], x->ctop[2], x->emf[0], x->emf[1], x->emf[2], x->Ff[0], x->Ff[1], x->Ff[2],
                   x->ctopf[0], x->ctopf[1], x->ctopf[2], x->emff[0], x->emff[1], x->emff[2],
-                  x->fBstar, x->ecc, x->eccf, x->dmatch, x->dtiles, x->dmaps, x->rk};
+                  x->fBstar, x->ecc, x->eccf, x->dmatch, x->dtiles, x->dmaps, x->rk, x->fflag, x->fsave};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int q = 0; q < 8; ++q)

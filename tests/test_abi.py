@@ -49,9 +49,21 @@ def test_argument_validation_without_gpu():
     c.precision = 2
     assert kh.lib().kh_geometry_init(0.0, ctypes.byref(c), float(cfg["gam"]), ctypes.byref(h)) == -1
     blk = kh.Block(0, 0, 0, 0, 8, 8, 8)
-    c = kh.coords_from_cfg(dict(cfg, fofc=True))
+    c = kh.coords_from_cfg(cfg)
+    c.fofc = 2
     assert kh.lib().kh_mesh_init(0.0, ctypes.byref(c), float(cfg["gam"]), 1, ctypes.byref(blk),
                                  ctypes.byref(h)) == -1
+    # the mesh takes the flux correction and the Runge-Kutta integrators with
+    # Flux-CT (validation passes; the call then needs a device), not with face CT
+    for over in (dict(fofc=True), dict(integrator="rk2"), dict(integrator="ssprk54", fofc=True)):
+        c = kh.coords_from_cfg(dict(cfg, **over))
+        rc = kh.lib().kh_mesh_init(0.0, ctypes.byref(c), float(cfg["gam"]), 1, ctypes.byref(blk), ctypes.byref(h))
+        assert rc != -1, over
+        if rc == 0:
+            kh.lib().kh_mesh_destroy(h)
+        c = kh.coords_from_cfg(dict(cfg, bfield="face", **over))
+        assert kh.lib().kh_mesh_init(0.0, ctypes.byref(c), float(cfg["gam"]), 1, ctypes.byref(blk),
+                                     ctypes.byref(h)) == -1, over
 
 
 def test_face_ct_validation_without_gpu():
