@@ -10,7 +10,12 @@ coordinates, zone-cycles per second).
 Prints ONE JSON line (rank 0). The timed region holds exactly K full steps
 (both stages, ghost fills, Flux-CT, inversions, fixups and the CFL reduction)
 bracketed by a barrier and device synchronisation on both sides, timed with
-CUDA events on the stream the library launches on; max over ranks. Inputs
+CUDA events on the stream the library launches on; max over ranks. Each
+step is one kh_step call replaying the step's captured CUDA graph
+(kh_set_graph; captured by an untimed step first). The per-kernel timings
+(roofline, kernel_share) come from the same K steps replayed once more with
+the library's group events recorded inside the graph (`profiled_graph`);
+the steps launched kernel by kernel are reported as `eager`. Inputs
 (~1 GB resident) are larger than the 129 MB L2, so no flush is needed.
 
 Beside the headline (mixed path) the line carries the FP64 path, the
@@ -51,7 +56,7 @@ DTYPE = {"fp64": "f64", "mixed": "f32+f64"}
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=50)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["kh", "reference"], default="kh")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -90,7 +95,7 @@ def fp64_peak_tflops(sm_mhz: float) -> float:
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 20 ms."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -105,7 +110,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=self.tmp, stderr=subprocess.DEVNULL)
+                 "-lms", "20"], stdout=self.tmp, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
 
@@ -221,50 +226,65 @@ def measure(args, cfg, P0, ctx, dev, stream, dist, world, oracle_step, e2e=True)
     dt = dt0
     for _ in range(args.warmup):
         dt, _ = ctx.step(U, P, B, 0.5 * dt)
-    ctx.profile(True)
-    sampler = ClockSampler(dev.index or 0)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    sampler.start()
-    l0 = ctx.launches()
-    nfail = 0
-    e0.record(stream)
-    for _ in range(args.steps):
-        dt, nf = ctx.step(U, P, B, 0.5 * dt)
-        nfail += nf
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    if dist:
-        dist.barrier()
-    clocks = sampler.stop()
-    launches = ctx.launches() - l0
-    ms = e0.elapsed_time(e1)
-    prof = ctx.profile_read()
-    ctx.profile(False)
-    if dist:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    out = {"value": nz * args.steps * world / (ms * 1e-3), "ms": ms, "prof": prof, "launches": launches,
+
+    def timed(graph, profile):
+        """K steps between CUDA events on the library's stream (barrier and
+        device synchronisation on both sides); graph: the step replayed as
+        the captured CUDA graph (captured by an untimed step first);
+        profile: the library's per-group events (inside the graph as
+        event record nodes)."""
+        nonlocal dt
+        ctx.set_graph(graph)
+        ctx.profile(profile)
+        if graph:
+            dt, _ = ctx.step(U, P, B, 0.5 * dt)  # capture
+        sampler = ClockSampler(dev.index or 0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        sampler.start()
+        l0 = ctx.launches()
+        nfail = 0
+        e0.record(stream)
+        for _ in range(args.steps):
+            dt, nf = ctx.step(U, P, B, 0.5 * dt)
+            nfail += nf
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+        clocks = sampler.stop()
+        launches = ctx.launches() - l0
+        ms = e0.elapsed_time(e1)
+        prof = ctx.profile_read() if profile else None
+        ctx.profile(False)
+        if dist:
+            t = torch.tensor([ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, prof, launches, clocks, nfail
+
+    # headline: the step as a CUDA graph (kh_set_graph)
+    ms, _, launches, clocks, nfail = timed(True, False)
+    out = {"value": nz * args.steps * world / (ms * 1e-3), "ms": ms, "launches": launches,
            "clocks": clocks, "err": err, "nfail": nfail, "launch": {"tpb_flux": tuned[0], "tpb_update": tuned[1]},
-           "nfp64": int(ctx.stats().nfp64)}  # zones of the last timed step whose inversion fell back to FP64
-    # the same K steps replayed as a CUDA graph (no per-kernel events)
+           "nfp64": int(ctx.stats().nfp64),  # zones of the last timed step whose inversion fell back to FP64
+           "mode": "CUDA graph replay of kh_step (kh_set_graph)"}
+    out["graph"] = {"value": out["value"], "ms_per_step": ms / args.steps}
+    # kernel timings: the same K steps replayed with the library's group
+    # events inside the captured graph (event record nodes between the
+    # groups; they lengthen the step, not the kernels they bracket)
+    pms, prof, _, _, _ = timed(True, True)
+    out["prof"] = prof
+    out["profiled_graph"] = {"value": nz * args.steps * world / (pms * 1e-3), "ms_per_step": pms / args.steps,
+                             "how": "the captured step with the per-group CUDA events recorded inside every "
+                                    "replay; source of the kernel timings (roofline, kernel_share)"}
+    # the same launched kernel by kernel (eager)
+    ems_, _, _, _, _ = timed(False, False)
+    out["eager"] = {"value": nz * args.steps * world / (ems_ * 1e-3), "ms_per_step": ems_ / args.steps}
     ctx.set_graph(True)
-    dt, _ = ctx.step(U, P, B, 0.5 * dt)
-    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    g0.record(stream)
-    for _ in range(args.steps):
-        dt, _ = ctx.step(U, P, B, 0.5 * dt)
-    g1.record(stream)
-    torch.cuda.synchronize(dev)
-    gms = g0.elapsed_time(g1)
-    ctx.set_graph(False)
-    out["graph"] = {"value": nz * args.steps * world / (gms * 1e-3), "ms_per_step": gms / args.steps}
+    dt, _ = ctx.step(U, P, B, 0.5 * dt)  # capture (untimed) for the end-to-end leg
     if e2e and not args.no_e2e:
         # the state crosses the host link in the library's compact interior
         # order (kh_pack_state / kh_unpack_state: no ghost cells, no padding)
@@ -563,20 +583,22 @@ def measure_workloads(args, dev, stream, n=2048):
     return out
 
 
-def measure_smr(args, dev, stream, precision, face=False, integrator="vl2"):
+def measure_smr(args, dev, stream, precision, face=False, integrator="vl2", fofc=False):
     """The statically refined torus (3 levels, 592 uneven blocks, 5.57 M zones)
     stepped as one mesh: every kernel covers all blocks, ghost zones of every
     block are filled by one gather, the step is replayed as a CUDA graph.
     face: face-centred CT with interface-matched upwinded EMFs (the loop
     field curled onto every block's faces from the shared corner potential).
     integrator: the time integrator ("vl2": the predictor-corrector; "rk1",
-    "rk2", "ssprk54": Runge-Kutta stages over the whole mesh)."""
+    "rk2", "ssprk54": Runge-Kutta stages over the whole mesh). fofc: the
+    first-order flux correction in every stage (trial over all blocks, flags
+    carried across block boundaries by the ghost map)."""
     import torch
 
     from paper_2408_01361_gb300 import inputs, kh
 
     base, blocks = inputs.smr_torus_layout()
-    base = dict(base, integrator=integrator)
+    base = dict(base, integrator=integrator, fofc=1 if fofc else 0)
     if face:
         base = dict(base, bfield="face", emf="gs05")
     norms = inputs.torus_norms(base)
@@ -619,12 +641,15 @@ def measure_smr(args, dev, stream, precision, face=False, integrator="vl2"):
         "workload": "FM torus (as above) on 3 static refinement levels: level 2 over the disc, level 1 around "
                     f"it, level 0 at the poles and outer radii; base {base['n1']}x{base['n2']}x{base['n3']}"
                     + ("; face-centred CT, interface-matched upwinded EMFs" if face else "")
-                    + (f"; integrator {integrator}" if integrator != "vl2" else ""),
+                    + (f"; integrator {integrator}" if integrator != "vl2" else "")
+                    + ("; first-order flux correction" if fofc else ""),
         "precision": precision, "dtype": DTYPE[precision], "blocks": len(blocks), "block_shapes": dict(shapes),
         "zones": m.zones, "ghost_cells": m.ghost_cells, "value": m.zones * args.steps / (ms * 1e-3), "unit": UNIT,
         "ms_per_step": ms / args.steps, "graph": True, "gpu_launches": m.launches() - l0, "clocks": clocks,
         "nfail_timed": nfail, "launch_config": {"tpb_flux": tuned[0], "tpb_update": tuned[1]},
     }
+    if fofc:
+        out["nfofc_last_step"] = int(m.stats().nfofc)  # zone-stages flagged by the last step's trials
     m.close()
     return out
 
@@ -808,6 +833,8 @@ def run_kh(args, world, rank, local):
     head = args.precisions[0]
     r = results[head]
     roof, share = roofline_of(r["prof"], nz, head)
+    roof["timing"] = ("average launch duration from CUDA events around the kernel group inside the profiled "
+                      "graph replay of the same K steps (profiled_graph)")
     hbm, hbm_kind, _ = peaks()
     alg = ALG_BYTES_PER_ZONE_CYCLE[head]
     hbm_step = {"algorithmic_bytes_per_zone_cycle": alg, "achieved_gbs": alg * r["value"] / world / 1e9,
@@ -823,7 +850,7 @@ def run_kh(args, world, rank, local):
         "roofline": roof, "hbm_step": hbm_step, "kernel_share": share,
         "cpu_baseline": cpu, "err_vs_oracle": r["err"], "e2e": r.get("e2e"), "gpu_launches": r["launches"],
         "clocks": r["clocks"], "nfail_timed": r["nfail"], "nfp64_last_step": r["nfp64"], "launch_config": r["launch"],
-        "graph_replay": r["graph"],
+        "mode": r["mode"], "profiled_graph": r["profiled_graph"], "eager": r["eager"],
     }
     for prec in args.precisions[1:]:
         q = results[prec]
@@ -831,7 +858,8 @@ def run_kh(args, world, rank, local):
         line[prec] = {"value": q["value"], "ms_per_step": q["ms"] / args.steps, "dtype": DTYPE[prec],
                       "err_vs_oracle": q["err"], "e2e": q.get("e2e"), "roofline": rf, "kernel_share": sh,
                       "gpu_launches": q["launches"], "clocks": q["clocks"], "nfail_timed": q["nfail"],
-                      "launch_config": q["launch"], "graph_replay": q["graph"]}
+                      "launch_config": q["launch"], "mode": q["mode"], "profiled_graph": q["profiled_graph"],
+                      "eager": q["eager"]}
         line[f"speedup_{head}_vs_{prec}"] = r["value"] / q["value"]
     if fp64inv is not None:
         q = fp64inv
@@ -841,13 +869,14 @@ def run_kh(args, world, rank, local):
                     "(FP32 stencil; FP64 U^n + increment; kh_coords.mixed_inversion = KH_MIXINV_FP64)",
             "value": q["value"], "ms_per_step": q["ms"] / args.steps, "dtype": "f32+f64",
             "err_vs_oracle": q["err"], "roofline": rf, "kernel_share": sh, "gpu_launches": q["launches"],
-            "clocks": q["clocks"], "nfail_timed": q["nfail"], "launch_config": q["launch"],
-            "graph_replay": q["graph"],
+            "clocks": q["clocks"], "nfail_timed": q["nfail"], "launch_config": q["launch"], "mode": q["mode"],
+            "eager": q["eager"],
             "headline_over_this": r["value"] / q["value"] if head == "mixed" else None}
     if not args.no_smr and world == 1:
         line["smr"] = {p: measure_smr(args, dev, stream, p) for p in args.precisions}
         line["smr_face_ct"] = {p: measure_smr(args, dev, stream, p, face=True) for p in args.precisions}
         line["smr_ssprk54"] = {"mixed": measure_smr(args, dev, stream, "mixed", integrator="ssprk54")}
+        line["smr_fofc"] = {"mixed": measure_smr(args, dev, stream, "mixed", fofc=True)}
     if not args.no_cube and world == 1:
         line["torus_128cubed"] = {p: measure_cube(args, dev, stream, p) for p in args.precisions}
         line["torus_128cubed"]["context"] = "paper: ~35 M zone-cycles/s per A100 GPU on 128^3 production problems"

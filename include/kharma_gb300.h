@@ -275,7 +275,9 @@ int kh_get_stats(kh_ctx* ctx, kh_stats* out);
  * given (U, P, B) triple and replays it on the context stream afterwards;
  * dt reaches the captured update kernels through device memory, so every
  * call may use a new dt. New pointers or launch settings re-capture.
- * Profiling (kh_profile) bypasses the graph. enable == 0 frees it. */
+ * With profiling on (kh_profile) the captured step holds the group events
+ * as external event record nodes, recorded on every replay; switching
+ * profiling re-captures. enable == 0 frees the graph. */
 int kh_set_graph(kh_ctx* ctx, int enable);
 
 /* Threads per block of the stencil (reconstruction + LLF) kernels and of the
@@ -307,8 +309,10 @@ enum {
   KH_NTIMERS = 9
 };
 /* enable != 0: record CUDA events on the context stream around each group of
- * every later kh_step (each step then synchronises its stream) and reset the
- * accumulators; enable == 0 stops and resets. */
+ * every later kh_step (each step then synchronises its stream; with a CUDA
+ * graph, kh_set_graph, the events are nodes of the captured step and are
+ * recorded by every replay) and reset the accumulators; enable == 0 stops
+ * and resets. */
 int kh_profile(kh_ctx* ctx, int enable);
 /* Accumulated milliseconds and timed intervals per group (host arrays of
  * KH_NTIMERS entries; either may be NULL). One interval per stage. */

@@ -64,7 +64,10 @@ void mark(kh_ctx* x, int group, int stage, int which) {
   else
     nvtxRangePop();
   if (!x->profiling) return;
-  cudaEventRecord(x->ev[group][stage][which], x->stream);
+  // inside a stream capture the event becomes an external event record node:
+  // every replay of the graph records it
+  cudaEventRecordWithFlags(x->ev[group][stage][which], x->stream,
+                           x->capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
   if (which == 1) x->ev_used[group][stage] = 1;
 }
 
@@ -696,9 +699,11 @@ void drop_graph(kh_ctx* x) {
   x->gkey[0] = x->gkey[1] = x->gkey[2] = nullptr;
 }
 
-// Capture the step for these pointers (once) and replay it.
+// Capture the step for these pointers (once) and replay it. A step captured
+// while profiling records the group events on every replay (their set is
+// handed to harvest after each launch).
 int step_graph(kh_ctx* x, double* U, double* P, double* B) {
-  if (!(x->gexec && x->gkey[0] == U && x->gkey[1] == P && x->gkey[2] == B)) {
+  if (!(x->gexec && x->gkey[0] == U && x->gkey[1] == P && x->gkey[2] == B && x->gprof == x->profiling)) {
     drop_graph(x);
     if (!x->cap_stream && cudaStreamCreateWithFlags(&x->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
       return KH_ECUDA;
@@ -708,10 +713,17 @@ int step_graph(kh_ctx* x, double* U, double* P, double* B) {
       x->stream = user;
       return KH_ECUDA;
     }
+    x->capturing = 1;
     const int n = issue_step(x, U, P, B);
+    x->capturing = 0;
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(x->cap_stream, &g);
     x->stream = user;
+    for (int q = 0; q < KH_NTIMERS; ++q)
+      for (int st = 0; st < 2; ++st) {
+        x->gev_used[q][st] = x->ev_used[q][st];
+        x->ev_used[q][st] = 0;
+      }
     if (n < 0 || e != cudaSuccess || !g) {
       if (g) cudaGraphDestroy(g);
       return KH_ECUDA;
@@ -725,10 +737,14 @@ int step_graph(kh_ctx* x, double* U, double* P, double* B) {
     x->gkey[0] = U;
     x->gkey[1] = P;
     x->gkey[2] = B;
+    x->gprof = x->profiling;
     x->graph_launches = n;
   }
   if (cudaGraphLaunch(x->gexec, x->stream) != cudaSuccess) return KH_ECUDA;
   x->launches += x->graph_launches;
+  if (x->profiling)
+    for (int q = 0; q < KH_NTIMERS; ++q)
+      for (int st = 0; st < 2; ++st) x->ev_used[q][st] = x->gev_used[q][st];
   return KH_OK;
 }
 
@@ -743,7 +759,7 @@ int kh_step(kh_ctx* x, double* U, double* P, double* B, double dt, double* dt_cf
   // reused as soon as the call returns)
   KH_TRY(cudaMemcpyAsync(x->dscalar + 3, &dt, sizeof(double), cudaMemcpyHostToDevice, x->stream));
   int rc;
-  if (x->graph_on && !x->profiling) {
+  if (x->graph_on) {
     rc = step_graph(x, U, P, B);
     if (rc != KH_OK) return rc;
     rc = cuda_fail(cudaGetLastError());
@@ -911,6 +927,7 @@ int kh_autotune(kh_ctx* x, const double* U, const double* P, const double* B, do
 
 int kh_profile(kh_ctx* x, int enable) {
   if (!x) return KH_EINVAL;
+  if ((enable ? 1 : 0) != x->profiling) drop_graph(x);  // a captured step holds the events (or none)
   if (enable && !x->profiling) {
     for (int g = 0; g < KH_NTIMERS; ++g)
       for (int st = 0; st < 2; ++st)

@@ -65,6 +65,10 @@ struct kh_ctx {
   int profiling;
   cudaEvent_t ev[KH_NTIMERS][2][2];  // [group][stage][start, stop]
   int ev_used[KH_NTIMERS][2];
+  // a step captured while profiling holds its group events as external event
+  // record nodes; gev_used is the set it records on every replay
+  int capturing, gprof;
+  int gev_used[KH_NTIMERS][2];
   double prof_ms[KH_NTIMERS];
   long long prof_n[KH_NTIMERS];
   // adjoint step (kh_step_adjoint): recorded forward states and adjoint

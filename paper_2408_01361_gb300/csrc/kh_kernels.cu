@@ -969,7 +969,13 @@ __global__ void k_df_planes(const double* geo, const double* flo, float* df, lon
       df[2 * (q * gplane + p) + 1] = v.lo;
     };
     // cell-centre planes: gcov pairs 0..9, gcon pairs 10..19, gdet 20, alpha 21
-    for (int q = 0; q < 10; ++q) put(DF_GCON + q, geo[(10 + q) * gplane + p]);
+    const double* gc = geo + 10 * gplane + p;
+    for (int q = 0; q < 4; ++q) put(DF_GCON0 + q, gc[q * gplane]);  // g^{0m}: pairs 00 01 02 03
+    const int sp[6][2] = {{1, 1}, {1, 2}, {1, 3}, {2, 2}, {2, 3}, {3, 3}};
+    for (int q = 0; q < 6; ++q) {  // gamma^{ij} = g^{ij} - g^{0i} g^{0j} / g^{00}, in FP64
+      const int a = sp[q][0], b = sp[q][1];
+      put(DF_GSP + q, gc[(4 + q) * gplane] - gc[a * gplane] * gc[b * gplane] / gc[0]);
+    }
     for (int q = 0; q < 6; ++q) put(DF_GCOV + q, geo[(4 + q) * gplane + p]);  // pairs 11 12 13 22 23 33
     put(DF_ALPHA, geo[21 * gplane + p]);
     put(DF_IG, flo[2 * gplane + p]);

@@ -197,7 +197,9 @@ __global__ void __launch_bounds__(256, 2) km_update_mixed(const MBlock* blk, con
   VarsT<float> P32;
   if (Pout64.a) P64 = vars_at(Pout64, m); else for (int v = 0; v < NV; ++v) P64.v[v] = nullptr;
   if (Pout32.a) P32 = vars_at(Pout32, m); else for (int v = 0; v < NV; ++v) P32.v[v] = nullptr;
-  update_mixed_zone<false, INV>(U0 + o8, cvars_at(Pin, m), P64, P32, Uout ? Uout + o8 : nullptr, F1 + o8, F2 + o8,
+  // the FP64 fallback inversion out of line, as in the staged update: both
+  // then run the one compiled copy and round alike
+  update_mixed_zone<false, INV, true>(U0 + o8, cvars_at(Pin, m), P64, P32, Uout ? Uout + o8 : nullptr, F1 + o8, F2 + o8,
                     m.L.ndim == 3 ? F3 + o8 : nullptr, m.L, geo64(GA, m), geo32(GA, m), S,
                     df_of_f64(coef * __ldg(dtp)), pflag + m.off, cnt, i, j, k, FailList{nullptr, nullptr},
                     fBn ? fBn + 3 * m.off : nullptr, dUout ? dUout + o8 : nullptr,
@@ -551,6 +553,25 @@ __global__ void km_to_f32(const MBlock* blk, const unsigned* pre, int nb, Arena<
   const int b = find_block(pre, nb, t);
   const MBlock& m = blk[b];
   const long long c = t - __ldg(pre + b);
+  const CVars S = cvars_at(src, m);
+  const VarsT<float> D = vars_at(dst, m);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) D.v[v][c] = f32_of_f64(S.v[v][c]);  // integer ops, not the FP64 pipe
+}
+
+// FP64 -> FP32 copy of the 8 slots of the interior cells of every block (the
+// first mixed stage: its ghost cells are filled in FP32 by the gather right
+// after, from interior cells only, so converting them as well is wasted work
+// -- 2.4x the interior on a 16x16x32 block).
+__global__ void km_to_f32_interior(const MBlock* blk, const unsigned* pre, int nb, Arena<double> src,
+                                   Arena<float> dst) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= __ldg(pre + nb)) return;
+  const int b = find_block(pre, nb, t);
+  const MBlock& m = blk[b];
+  int i, j, k;
+  zone_ijk(m.L, t - __ldg(pre + b), i, j, k);
+  const long long c = m.L.at(k, j, i);
   const CVars S = cvars_at(src, m);
   const VarsT<float> D = vars_at(dst, m);
 #pragma unroll
@@ -1597,7 +1618,7 @@ int mesh_stage_mixed(kh_mesh* x, bool first, const double* U, const double* U0, 
   const Arena<float> Pin = first ? arena8(x->pnf) : arena8(x->pstarf);
   int n = 0;
   if (first) {
-    km_to_f32<<<nblk(x->pre_alloc.back(), 256), 256, 0, s>>>(x->dblk, x->dpre[5], x->nb, Pn64, Pin);
+    km_to_f32_interior<<<nblk(nz, 256), 256, 0, s>>>(x->dblk, x->dpre[3], x->nb, Pn64, Pin);
     ++n;
   }
   n += fill_ghosts(x, Pin);

@@ -26,9 +26,11 @@ constexpr int C2P_NEED_FP64 = -1;
 
 // Double-float (hi, lo FP32 pair) copies of the cell-centre quantities the
 // mixed update's inversion and floors use, per (i, j): planes [NDF][n2s][n1s]
-// of (hi, lo) float pairs, so that one 8-byte load brings both halves. DF_GCON: g^{mn} in the
-// symmetric-pair order; DF_GCOV: g_ij (11 12 13 22 23 33).
-enum { DF_GCON = 0, DF_GCOV = 10, DF_ALPHA = 16, DF_IG = 17, DF_RHOFL = 18, DF_UFL = 19, NDF = 20 };
+// of (hi, lo) float pairs, so that one 8-byte load brings both halves.
+// DF_GCON0: g^{0m} (m = 0..3); DF_GSP: gamma^{ij} = g^{ij} - g^{0i} g^{0j} / g^{00},
+// the inverse of the spatial metric (11 12 13 22 23 33), formed in FP64 at
+// setup; DF_GCOV: g_ij (same order).
+enum { DF_GCON0 = 0, DF_GSP = 4, DF_GCOV = 10, DF_ALPHA = 16, DF_IG = 17, DF_RHOFL = 18, DF_UFL = 19, NDF = 20 };
 
 // FP32 and double-float constants of the mixed update (host: set_mixed()).
 struct MixedConsts {
@@ -58,7 +60,8 @@ inline MixedConsts mixed_consts(double gam, const FloorParams& fl) {
 }
 
 struct MetDF {
-  df64 gcon[10];  // g^{mn}, symmetric-pair order
+  df64 gcon0[4];  // g^{0m}
+  df64 gsp[6];    // gamma^{ij}: 11 12 13 22 23 33
   df64 gcov[6];   // g_ij: 11 12 13 22 23 33
   df64 alpha, ig, rho_fl, u_fl;
 };
@@ -72,7 +75,9 @@ __device__ __forceinline__ MetDF load_metdf(const float* df, long long gplane, l
   };
   MetDF m;
 #pragma unroll
-  for (int q = 0; q < 10; ++q) m.gcon[q] = ld(DF_GCON + q);
+  for (int q = 0; q < 4; ++q) m.gcon0[q] = ld(DF_GCON0 + q);
+#pragma unroll
+  for (int q = 0; q < 6; ++q) m.gsp[q] = ld(DF_GSP + q);
 #pragma unroll
   for (int q = 0; q < 6; ++q) m.gcov[q] = ld(DF_GCOV + q);
   m.alpha = ld(DF_ALPHA);
@@ -88,6 +93,46 @@ KH_HD df64 spatial_sq(const MetDF& m, df64 a, df64 b, df64 c) {
   const df64 d = m.gcov[0] * (a * a) + m.gcov[3] * (b * b) + m.gcov[5] * (c * c);
   const df64 o = m.gcov[1] * (a * b) + m.gcov[2] * (a * c) + m.gcov[4] * (b * c);
   return d + scale2(o, 2.0f);
+}
+
+// FP32 quantities the floors decide on, from the leading parts of the
+// primitives P (double-float) and of the metric: u_i = g_ij u~^j (the spatial
+// part of u_mu), the Lorentz factor squared gamma^2 = 1 + u~^i u_i, and
+// b^2 = alpha^2 (g_ij B^i B^j + (b^t)^2) / gamma^2 with b^t = B^i u_i (that is
+// (B^i B_i + (b^t)^2) / (u^t)^2, u^t = gamma / alpha).
+struct FloorF32 {
+  float ucov[3];  // u_1, u_2, u_3
+  float g2, bsq;
+};
+// a0 b0 + a1 b1 + a2 b2 with every rounding explicit (a product, then two
+// fused multiply-adds), so that every kernel inlining this rounds alike
+KH_HD float dot3f(float a0, float b0, float a1, float b1, float a2, float b2) {
+  return fmaf(a2, b2, fmaf(a1, b1, fmul(a0, b0)));
+}
+KH_HD FloorF32 floor_f32(const MetDF& m, const df64* P) {
+  const float g11 = m.gcov[0].hi, g12 = m.gcov[1].hi, g13 = m.gcov[2].hi;
+  const float g22 = m.gcov[3].hi, g23 = m.gcov[4].hi, g33 = m.gcov[5].hi;
+  const float v1 = P[V_U1].hi, v2 = P[V_U2].hi, v3 = P[V_U3].hi;
+  const float B1 = P[V_B1].hi, B2 = P[V_B2].hi, B3 = P[V_B3].hi;
+  FloorF32 f;
+  f.ucov[0] = dot3f(g11, v1, g12, v2, g13, v3);
+  f.ucov[1] = dot3f(g12, v1, g22, v2, g23, v3);
+  f.ucov[2] = dot3f(g13, v1, g23, v2, g33, v3);
+  f.g2 = fadd(1.0f, dot3f(f.ucov[0], v1, f.ucov[1], v2, f.ucov[2], v3));
+  const float bt = dot3f(f.ucov[0], B1, f.ucov[1], B2, f.ucov[2], B3);
+  const float BB = dot3f(dot3f(g11, B1, g12, B2, g13, B3), B1, dot3f(g12, B1, g22, B2, g23, B3), B2,
+                         dot3f(g13, B1, g23, B2, g33, B3), B3);
+  const float a = m.alpha.hi;
+  f.bsq = kdiv(fmul(fmul(a, a), fmaf(bt, bt, BB)), f.g2);
+  return f;
+}
+
+// u^t and u_t of the same state: u^t = gamma / alpha, u_t = -alpha gamma +
+// beta_i u~^i with the shift beta_i = alpha^2 g_ij g^{0j}, i.e. alpha^2 g^{0j} u_j.
+KH_HD void floor_ut(const MetDF& m, const FloorF32& f, float& ut, float& u_t) {
+  const float a = m.alpha.hi, gl = sqrtf(f.g2);
+  ut = kdiv(gl, a);
+  u_t = fmul(a, fsub(fmul(a, dot3f(m.gcon0[1].hi, f.ucov[0], m.gcon0[2].hi, f.ucov[1], m.gcon0[3].hi, f.ucov[2])), gl));
 }
 
 // U: conserved variables of the zone (double-float, densitised); W0, vsq0:
@@ -107,14 +152,15 @@ KH_HD int noble2d_df(const df64* U, const MetDF& m, const MixedConsts& k, float 
   const df64 as = scale2(aig, iS), ab = scale2(aig, iSb);
   const df64 D = as * U[V_RHO];
   const df64 Qc[4] = {as * (U[V_U] - U[V_RHO]), as * U[V_U1], as * U[V_U2], as * U[V_U3]};
-  df64 Qu[4];
-#pragma unroll
-  for (int mu = 0; mu < 4; ++mu)
-    Qu[mu] = m.gcon[sym_index(mu, 0)] * Qc[0] + m.gcon[sym_index(mu, 1)] * Qc[1] + m.gcon[sym_index(mu, 2)] * Qc[2] +
-             m.gcon[sym_index(mu, 3)] * Qc[3];
-  const df64 Qdn = -(m.alpha * Qu[0]);  // n_mu = (-alpha, 0, 0, 0)
-  const df64 Qsq = Qc[0] * Qu[0] + Qc[1] * Qu[1] + Qc[2] * Qu[2] + Qc[3] * Qu[3];
-  const df64 Qtsq = dfmax(Qsq + Qdn * Qdn, mkdf(0.0f, 0.0f));
+  // Q.n = -alpha Q^t (n_mu = (-alpha, 0, 0, 0))
+  const df64 Qdn = -(m.alpha * (m.gcon0[0] * Qc[0] + m.gcon0[1] * Qc[1] + m.gcon0[2] * Qc[2] + m.gcon0[3] * Qc[3]));
+  // Q~^i = gamma^{ij} Q_j: the part of Q^mu orthogonal to n (its time component
+  // vanishes, since gamma^{i0} = g^{i0} + n^i n^0 = 0), and Q~^2 = Q~^i Q_i =
+  // Q^mu Q_mu + (Q.n)^2
+  const df64 Qt[3] = {m.gsp[0] * Qc[1] + m.gsp[1] * Qc[2] + m.gsp[2] * Qc[3],
+                      m.gsp[1] * Qc[1] + m.gsp[3] * Qc[2] + m.gsp[4] * Qc[3],
+                      m.gsp[2] * Qc[1] + m.gsp[4] * Qc[2] + m.gsp[5] * Qc[3]};
+  const df64 Qtsq = dfmax(Qt[0] * Qc[1] + Qt[1] * Qc[2] + Qt[2] * Qc[3], mkdf(0.0f, 0.0f));
   const df64 Bc[3] = {ab * U[V_B1], ab * U[V_B2], ab * U[V_B3]};
   const df64 Bsq = spatial_sq(m, Bc[0], Bc[1], Bc[2]);
   const df64 QdB = Qc[1] * Bc[0] + Qc[2] * Bc[1] + Qc[3] * Bc[2];
@@ -177,10 +223,7 @@ KH_HD int noble2d_df(const df64* U, const MetDF& m, const MixedConsts& k, float 
   const df64 f = gamma * W * inv;
   const df64 iWb = BW * inv;
 #pragma unroll
-  for (int i = 1; i < 4; ++i) {
-    const df64 nu = -(m.alpha * m.gcon[sym_index(i, 0)]);  // n^i = -alpha g^{it}
-    P[V_U1 + i - 1] = f * (Qu[i] + nu * Qdn + QdB * Bc[i - 1] * iWb);
-  }
+  for (int i = 0; i < 3; ++i) P[V_U1 + i] = f * (Qt[i] + QdB * Bc[i] * iWb);
   return 0;
 }
 

@@ -2,6 +2,8 @@
 // block), shared by the single-grid kernels and the multi-block kernels.
 #pragma once
 
+#include <type_traits>
+
 #include "kh_internal.h"
 #include "kh_mixed.cuh"
 #include "kh_pair.cuh"
@@ -255,16 +257,33 @@ __device__ __forceinline__ void source_terms(const R* P, const Met<M>& m, const 
   const R eta = P[V_RHO] + P[V_U] + pg + s.bsq;
   const R ptot = pg + R(0.5) * s.bsq;
   R acc1 = R(0), acc2 = R(0);
+  if constexpr (std::is_same<R, float>::value) {
+    // FP32: the two sums as one pair (paired FP32 fused multiply-adds)
+    P2 acc(0.0f);
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = a; b < 4; ++b) {
-      const int q = sym_index(a, b);
-      R t = eta * s.ucon[a] * s.ucon[b] - s.bcon[a] * s.bcon[b] + ptot * m.gcon[a][b];  // T^{ab}
-      if (a != b) t = R(2) * t;
-      acc1 += t * __ldg(dgm + q * gplane + p);
-      acc2 += t * __ldg(dgm + (10 + q) * gplane + p);
-    }
+      for (int b = a; b < 4; ++b) {
+        const int q = sym_index(a, b);
+        // T^{ab}, every rounding explicit (so that every kernel inlining this rounds alike)
+        R t = fmaf(ptot, m.gcon[a][b], fmaf(-s.bcon[a], s.bcon[b], __fmul_rn(__fmul_rn(eta, s.ucon[a]), s.ucon[b])));
+        if (a != b) t = R(2) * t;
+        acc = pfma(P2(t), P2(__ldg(dgm + q * gplane + p), __ldg(dgm + (10 + q) * gplane + p)), acc);
+      }
+    acc1 = acc.v.x;
+    acc2 = acc.v.y;
+  } else {
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = a; b < 4; ++b) {
+        const int q = sym_index(a, b);
+        R t = eta * s.ucon[a] * s.ucon[b] - s.bcon[a] * s.bcon[b] + ptot * m.gcon[a][b];  // T^{ab}
+        if (a != b) t = R(2) * t;
+        acc1 += t * __ldg(dgm + q * gplane + p);
+        acc2 += t * __ldg(dgm + (10 + q) * gplane + p);
+      }
+  }
   S[V_U] = R(0);
   S[V_U1] = R(0.5) * m.gdet * acc1;
   S[V_U2] = R(0.5) * m.gdet * acc2;
@@ -572,8 +591,10 @@ __device__ __forceinline__ void update_mixed_fp64_tail(double* U, const IN& in, 
 // INV = C2P_NOBLE2D_FP64: the FP64 Noble-2D for every zone from the FP64
 // U^n + increment (update_mixed_fp64_tail).
 // COLD: the FP64 fallback inversion is called out of line (the TMA-staged
-// kernels, whose instruction fetch stalls them: 1% faster so) or inlined (the
-// mesh's own-loads update at 128 registers: 5% faster so).
+// kernels, whose instruction fetch stalls them: 1% faster so; and the mesh's
+// own-loads update, so that it runs the same compiled copy as the mesh's
+// staged update and the two round alike) or inlined (the trial and the
+// single grid's own-loads update).
 template <bool TRIAL, int INV, class IN, bool COLD = false>
 __device__ __forceinline__ void update_mixed_zone_in(const IN& in, const Vars& Pout64, const VarsT<float>& Pout32,
                                                      double* Uout, const Layout& L, const DevGeom& G,
@@ -653,10 +674,16 @@ __device__ __forceinline__ void update_mixed_zone_in(const IN& in, const Vars& P
       if (three) div = __fmaf_rn(b3 - a3, i3, div);
       const float inc = (cdt * __fsub_rn(Sv[v], div)).hi;  // c dt (S - div F)
       const double u0 = in.u0(v);
-      if (Uout) Uout[o] = u0 + f64_of_f32(inc);    // the conserved update, FP64
-      if (dUout) dUout[o] = f64_of_f32(inc);       // the raw increment (Runge-Kutta stages)
-      if constexpr (INV == C2P_NOBLE2D_FP64) Ue[v] = u0 + f64_of_f32(inc);
-      else Ud[v] = df_of_f64(u0) + inc;
+      if (dUout) dUout[o] = f64_of_f32(inc);  // the raw increment (Runge-Kutta stages)
+      if (Uout) {
+        const double un = u0 + f64_of_f32(inc);  // the conserved update, FP64
+        Uout[o] = un;
+        if constexpr (INV == C2P_NOBLE2D_FP64) Ue[v] = un;
+        else Ud[v] = df_of_f64(un);  // the stored sum split, in place of a second (double-float) sum
+      } else {
+        if constexpr (INV == C2P_NOBLE2D_FP64) Ue[v] = u0 + f64_of_f32(inc);
+        else Ud[v] = df_of_f64(u0) + inc;
+      }
     }
   }
   if (fBn) {  // face-centred CT: sqrt(-g) B from the updated faces (FP64 means)
@@ -709,13 +736,9 @@ __device__ __forceinline__ void update_mixed_zone_in(const IN& in, const Vars& P
   }
   int fmask = 0;
   if (flag == 0) {
-    // floors: decisions on FP32 b^2 and Lorentz factor, values in double-float
-    const Met<float> mf = load_met(Gf, L.gplane, LOC_CENT, p);
-    float q[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) q[v] = Pn[v].hi;
-    FState<float> sf;
-    fluid_state(q, mf, sf);
+    // floors: decisions on FP32 b^2 and Lorentz factor (from the double-float
+    // metric's leading parts, no further loads), values in double-float
+    const FloorF32 sf = floor_f32(md, Pn);
     const df64 rho0 = Pn[V_RHO], u0 = Pn[V_U];
     const df64 rf = dfmax(md.rho_fl, mkdf(sf.bsq * mx.ibsq_rho_max, 0.0f));
     const df64 uf = dfmax(md.u_fl, mkdf(sf.bsq * mx.ibsq_u_max, 0.0f));
@@ -723,8 +746,7 @@ __device__ __forceinline__ void update_mixed_zone_in(const IN& in, const Vars& P
     if (Pn[V_U] < uf) { Pn[V_U] = uf; fmask |= 1; }
     const df64 umax = Pn[V_RHO] * mx.u_rho_max;
     if (Pn[V_U] > umax) { Pn[V_U] = umax; fmask |= 2; }
-    const float gq = mf.alpha * sf.ucon[0];  // Lorentz factor (FP32 estimate gates the exact test)
-    if (gq * gq > 0.999f * mx.g2max) {
+    if (sf.g2 > 0.999f * mx.g2max) {  // the FP32 Lorentz factor gates the exact test
       const df64 qq = spatial_sq(md, Pn[V_U1], Pn[V_U2], Pn[V_U3]);
       if (qq.hi + 1.0f > mx.g2max) {
         const df64 sc = dfsqrt(mkdf(mx.g2max - 1.0f, 0.0f) / qq);
@@ -747,12 +769,17 @@ __device__ __forceinline__ void update_mixed_zone_in(const IN& in, const Vars& P
         // at fixed u~ and B, U is linear in (rho, u): add
         // drho dU/drho + du dU/du, formed in FP32, to the FP64 U
         const float drho = (Pn[V_RHO] - rho0).hi, du = (Pn[V_U] - u0).hi;
-        const float gm = mx.gam, gd = mf.gdet, ut = sf.ucon[0];
-        Uc[V_RHO * L.plane] += f64_of_f32(gd * ut * drho);
-        Uc[V_U * L.plane] += f64_of_f32(gd * ((ut * sf.ucov[0] + ut) * drho + (gm * ut * sf.ucov[0] + gm - 1.0f) * du));
-        Uc[V_U1 * L.plane] += f64_of_f32(gd * ut * sf.ucov[1] * (drho + gm * du));
-        Uc[V_U2 * L.plane] += f64_of_f32(gd * ut * sf.ucov[2] * (drho + gm * du));
-        Uc[V_U3 * L.plane] += f64_of_f32(gd * ut * sf.ucov[3] * (drho + gm * du));
+        float ut, u_t;
+        floor_ut(md, sf, ut, u_t);
+        const float gm = mx.gam, gd = kdiv(1.0f, md.ig.hi);
+        // (every rounding explicit, so that every kernel inlining this rounds alike)
+        const float gu = fmul(gd, ut), dm = fmaf(gm, du, drho);
+        Uc[V_RHO * L.plane] += f64_of_f32(fmul(gu, drho));
+        Uc[V_U * L.plane] +=
+            f64_of_f32(fmul(gd, fmaf(fmaf(ut, u_t, ut), drho, fmul(fsub(fmaf(fmul(gm, ut), u_t, gm), 1.0f), du))));
+        Uc[V_U1 * L.plane] += f64_of_f32(fmul(fmul(gu, sf.ucov[0]), dm));
+        Uc[V_U2 * L.plane] += f64_of_f32(fmul(fmul(gu, sf.ucov[1]), dm));
+        Uc[V_U3 * L.plane] += f64_of_f32(fmul(fmul(gu, sf.ucov[2]), dm));
       }
     }
   }
@@ -773,8 +800,9 @@ __device__ __forceinline__ void update_mixed_zone_in(const IN& in, const Vars& P
 }
 
 
-// The mixed update of zone (i, j, k) reading its inputs from global memory.
-template <bool TRIAL = false, int INV = C2P_NOBLE2D>
+// The mixed update of zone (i, j, k) reading its inputs from global memory
+// (COLD as for update_mixed_zone_in).
+template <bool TRIAL = false, int INV = C2P_NOBLE2D, bool COLD = false>
 __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT<float>& Pin, const Vars& Pout64,
                                                   const VarsT<float>& Pout32, double* Uout, const float* F1,
                                                   const float* F2, const float* F3, const Layout& L, const DevGeom& G,
@@ -785,7 +813,8 @@ __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT
                                                   CtEmf ect = CtEmf{{nullptr, nullptr, nullptr}}) {
   const MixedInGlobal in{U0, Pin, {F1, F2, F3}, ect, L.at(k, j, i), (long long)L.n1s, (long long)L.n1s * L.n2s,
                          L.plane};
-  update_mixed_zone_in<TRIAL, INV>(in, Pout64, Pout32, Uout, L, G, Gf, S, cdt, pflag, cnt, i, j, k, fl, fBn, dUout);
+  update_mixed_zone_in<TRIAL, INV, MixedInGlobal, COLD>(in, Pout64, Pout32, Uout, L, G, Gf, S, cdt, pflag, cnt, i, j,
+                                                        k, fl, fBn, dUout);
 }
 
 // Fixup: a zone whose inversion failed takes the equal-weight mean of the

@@ -6,7 +6,9 @@
 // (fluid primitives, normalised per zone by max(|P|) over rho, u and by the
 // Lorentz-factor scale for u~), the same for the FP64 inversion, the largest
 // difference between the two, the number of zones handed back to FP64, the
-// number of other failures and the number of states.
+// number of other failures, the number of states, and the largest relative
+// error of the floors' FP32 b^2, Lorentz factor and u_mu (floor_f32) against
+// the FP64 fluid state.
 #include <cmath>
 #include <cstdio>
 #include <random>
@@ -44,7 +46,7 @@ int main() {
   fl.ibsq_u_max = 1.0 / 5000.0;
   const MixedConsts mx = mixed_consts(gam, fl);
   C2POpts o{30, 1e-14};
-  double worst_df = 0.0, worst_64 = 0.0, worst_d = 0.0;
+  double worst_df = 0.0, worst_64 = 0.0, worst_d = 0.0, worst_fl = 0.0;
   long need = 0, fails = 0, n = 0;
   for (int t = 0; t < 200000; ++t) {
     Met<double> m;
@@ -87,10 +89,13 @@ int main() {
     const double ig = 1.0 / m.gdet;
     const int f64 = noble2d(U, m, ig, gam, 1.0 / gam, (gam - 1.0) / gam, o, P64);
     MetDF md;
-    for (int a = 0; a < 4; ++a)
-      for (int b = a; b < 4; ++b) md.gcon[sym_index(a, b)] = df_of_f64(m.gcon[a][b]);
+    for (int a = 0; a < 4; ++a) md.gcon0[a] = df_of_f64(m.gcon[0][a]);
     const int gs[6][2] = {{1, 1}, {1, 2}, {1, 3}, {2, 2}, {2, 3}, {3, 3}};
-    for (int q = 0; q < 6; ++q) md.gcov[q] = df_of_f64(m.gcov[gs[q][0]][gs[q][1]]);
+    for (int q = 0; q < 6; ++q) {
+      const int a = gs[q][0], b = gs[q][1];
+      md.gsp[q] = df_of_f64(m.gcon[a][b] - m.gcon[0][a] * m.gcon[0][b] / m.gcon[0][0]);
+      md.gcov[q] = df_of_f64(m.gcov[a][b]);
+    }
     md.alpha = df_of_f64(m.alpha);
     md.ig = df_of_f64(ig);
     df64 Ud[8], Pd[8];
@@ -110,6 +115,22 @@ int main() {
     double sc_u = 0.0;
     for (int q = 0; q < 3; ++q) sc_u = std::fmax(sc_u, std::fabs(P[2 + q]) * std::sqrt(std::fabs(m.gcov[1 + q][1 + q])));
     sc_u = std::fmax(sc_u, 1e-300);
+    {  // the floors' FP32 b^2, Lorentz factor and u_mu against the FP64 fluid state
+      df64 Pf[8];
+      for (int v = 0; v < 8; ++v) Pf[v] = df_of_f64(P[v]);
+      const FloorF32 ff = floor_f32(md, Pf);
+      const double g2 = (m.alpha * s.ucon[0]) * (m.alpha * s.ucon[0]);
+      worst_fl = std::fmax(worst_fl, std::fabs(ff.bsq - s.bsq) / s.bsq);
+      worst_fl = std::fmax(worst_fl, std::fabs(ff.g2 - g2) / g2);
+      const float a = md.alpha.hi, gl = std::sqrt(ff.g2);
+      const float u_t = a * (a * (md.gcon0[1].hi * ff.ucov[0] + md.gcon0[2].hi * ff.ucov[1] +
+                                  md.gcon0[3].hi * ff.ucov[2]) - gl);
+      const double usc = std::sqrt(g2) * std::fmax(1.0, m.alpha);
+      worst_fl = std::fmax(worst_fl, std::fabs(u_t - s.ucov[0]) / usc);
+      for (int q = 0; q < 3; ++q)  // u_i on the scale sqrt(g_ii) gamma
+        worst_fl = std::fmax(worst_fl, std::fabs(ff.ucov[q] - s.ucov[1 + q]) /
+                                           (std::sqrt(std::fabs(m.gcov[1 + q][1 + q]) * g2)));
+    }
     for (int v = 0; v < 5; ++v) {
       const double sc = v < 2 ? sc_th : sc_u / std::sqrt(std::fabs(m.gcov[v - 1][v - 1]));
       const double dv = (double)Pd[v].hi + (double)Pd[v].lo;
@@ -118,6 +139,6 @@ int main() {
       worst_d = std::fmax(worst_d, std::fabs(dv - P64[v]) / sc);
     }
   }
-  std::printf("%.3e %.3e %.3e %ld %ld %ld\n", worst_df, worst_64, worst_d, need, fails, n);
+  std::printf("%.3e %.3e %.3e %ld %ld %ld %.3e\n", worst_df, worst_64, worst_d, need, fails, n, worst_fl);
   return 0;
 }

@@ -131,3 +131,34 @@ def test_pack_unpack_state_through_pinned_host_memory(kh):
     ctx.unpack_state(host.to(ctx.device), U3, P3, B3)
     torch.cuda.synchronize()
     assert torch.equal(U2, U3) and torch.equal(PB2, PB3)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_profiled_graph_replay(kh, precision):
+    """kh_profile with kh_set_graph: the captured step holds the group events,
+    so every replay times every group of both stages; the arithmetic is the
+    unprofiled step's, bit for bit, and switching profiling off again
+    re-captures a step without the events."""
+    cfg = inputs.torus_cfg(40, 24, 12, r_out=60.0)
+    cfg["precision"] = precision
+    P = inputs.torus_state(cfg, seed=2)
+    (U0, P0), d0 = _run(kh, cfg, P, 4)
+    ctx = kh.Context(cfg)
+    g = GpuRun(ctx, cfg, P)
+    dt = 0.5 * ctx.cfl_dt(g.P, g.B)
+    ctx.set_graph(True)
+    ctx.profile(True)
+    dts = []
+    for q in range(4):
+        if q == 2:
+            ctx.profile(False)  # the events go, the graph is captured again
+        d, _ = ctx.step(g.U, g.P, g.B, dt)
+        if q == 1:
+            prof = ctx.profile_read()
+        dts.append(d)
+        dt = 0.5 * d
+    U1, P1 = g.host()
+    assert np.array_equal(U0, U1) and np.array_equal(P0, P1) and d0 == dts
+    for name in ("flux_x1", "flux_x2", "flux_x3", "update", "cfl"):
+        ms, n = prof[name]
+        assert n == (2 if name == "cfl" else 4) and ms > 0.0, (name, prof[name])
