@@ -72,6 +72,9 @@ def parse():
     p.add_argument("--no-fp64-inversion", action="store_true",
                    help="skip the mixed leg with the whole inversion in FP64")
     p.add_argument("--smr-only", action="store_true", help="run only the statically refined torus leg")
+    p.add_argument("--smr-n3", type=int, default=64,
+                   help="azimuthal zones of the refined torus's level-0 grid (64 = the named workload; 32 = "
+                        "a half-size case of the same blocks, for profiler captures)")
     p.add_argument("--precisions", default="mixed,fp64",
                    help="comma list; the first is the headline, the others are reported beside it")
     a = p.parse_args()
@@ -597,7 +600,7 @@ def measure_smr(args, dev, stream, precision, face=False, integrator="vl2", fofc
 
     from paper_2408_01361_gb300 import inputs, kh
 
-    base, blocks = inputs.smr_torus_layout()
+    base, blocks = inputs.smr_torus_layout(n3=args.smr_n3)
     base = dict(base, integrator=integrator, fofc=1 if fofc else 0)
     if face:
         base = dict(base, bfield="face", emf="gs05")

@@ -8,7 +8,8 @@
 // search over a per-kernel prefix sum of item counts, then runs the same
 // per-item device function as the single-grid kernels with that block's
 // layout, geometry and arena offsets. Ghost cells of every block are filled
-// by ONE gather kernel from a map built on the host at set-up: each ghost
+// by one gather (two launches: same-level copies, then the interpolating
+// ops) from a map built on the host at set-up: each ghost
 // cell's centre is carried through the physical boundary rules (outflow
 // clamps to the first interior cell, polar reflection, periodic wrap), the
 // leaf block owning that point is found, and the ghost cell copies the
@@ -496,10 +497,43 @@ __global__ void km_max_sum_finish(const double* partial, int n, double* out) {
   }
 }
 
-// The ghost-fill gather: one thread per ghost cell of any block.
+// The physical boundary rules a ghost cell's op carries: polar reflection of
+// the x2 components, no inflow through the x1 boundaries.
+template <class T> __device__ __forceinline__ void ghost_flags(unsigned char flags, T* val) {
+  if (flags & G_FLIP2) {
+    val[V_U2] = -val[V_U2];
+    val[V_B2] = -val[V_B2];
+  }
+  if ((flags & G_CLAMP_IN) && val[V_U1] > T(0)) val[V_U1] = T(0);
+  if ((flags & G_CLAMP_OUT) && val[V_U1] < T(0)) val[V_U1] = T(0);
+}
+
+// The ghost-fill gather, part 1: the ghost cells whose owner is at the same
+// level (the op list holds them first), one thread per ghost cell. They are
+// most ghost cells (~88% on the refined torus); on their own they run without
+// the registers and branches of the interpolating ops below.
 template <class T>
-__global__ void km_ghost(const MBlock* blk, const GhostOp* ops, long long nops, const ProlongNb* nbs, Arena<T> P) {
+__global__ void __launch_bounds__(MTPB) km_ghost_copy(const MBlock* blk, const GhostOp* ops, long long n,
+                                                      Arena<T> P) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const GhostOp op = ops[t];
+  const VarsT<T> D = vars_at(P, blk[op.dst_block]);
+  const VarsT<T> Sv = vars_at(P, blk[op.src_block]);
+  T val[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) val[v] = Sv.v[v][op.src_cell];
+  ghost_flags(op.flags, val);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) D.v[v][op.dst_cell] = val[v];
+}
+
+// Part 2: the ops from index `first` on, restriction (finer owner) or
+// prolongation (coarser owner), one thread per ghost cell.
+template <class T>
+__global__ void km_ghost(const MBlock* blk, const GhostOp* ops, long long first, long long nops, const ProlongNb* nbs,
+                         Arena<T> P) {
+  const long long t = first + blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= nops) return;
   const GhostOp op = ops[t];
   const MBlock& md = blk[op.dst_block];
@@ -516,32 +550,35 @@ __global__ void km_ghost(const MBlock* blk, const GhostOp* ops, long long nops, 
     for (int v = 0; v < NV; ++v) val[v] = restrict_at(P, ms, v, c);
   } else {  // prolongation from the coarse cell c with MC slopes over coarse-level neighbours
     // (in the arena's precision: FP64 arithmetic on FP32 data would run on
-    // GB300's 1/64-rate FP64 pipe)
+    // GB300's 1/64-rate FP64 pipe); each neighbour's block is looked up once
+    // for all 8 variables
     const ProlongNb& nb = nbs[op.nbi];
     const int nd = ms.L.ndim;
+    T q0[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const T q0 = Sv.v[v][c];
-      T out = q0;
-      for (int d = 0; d < nd; ++d) {
-        if (op.off[d] == 0 || nb.mode[d][0] == NB_NONE || nb.mode[d][1] == NB_NONE) continue;
-        T q[2];
-        for (int side = 0; side < 2; ++side) {
-          const MBlock& mn = blk[nb.block[d][side]];
-          const long long cn = nb.cell[d][side];
-          q[side] = nb.mode[d][side] == G_COPY ? vars_at(P, mn).v[v][cn] : restrict_at(P, mn, v, cn);
+    for (int v = 0; v < NV; ++v) val[v] = q0[v] = Sv.v[v][c];
+    for (int d = 0; d < nd; ++d) {
+      if (op.off[d] == 0 || nb.mode[d][0] == NB_NONE || nb.mode[d][1] == NB_NONE) continue;
+      T q[2][NV];
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        const MBlock& mn = blk[nb.block[d][side]];
+        const long long cn = nb.cell[d][side];
+        if (nb.mode[d][side] == G_COPY) {
+          const VarsT<T> V = vars_at(P, mn);
+#pragma unroll
+          for (int v = 0; v < NV; ++v) q[side][v] = V.v[v][cn];
+        } else {
+#pragma unroll
+          for (int v = 0; v < NV; ++v) q[side][v] = restrict_at(P, mn, v, cn);
         }
-        out += T(0.25) * T(op.off[d]) * mc_slope(q[0], q0, q[1]);
       }
-      val[v] = out;
+      const T w = T(0.25) * T(op.off[d]);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) val[v] += w * mc_slope(q[0][v], q0[v], q[1][v]);
     }
   }
-  if (op.flags & G_FLIP2) {
-    val[V_U2] = -val[V_U2];
-    val[V_B2] = -val[V_B2];
-  }
-  if ((op.flags & G_CLAMP_IN) && val[V_U1] > T(0)) val[V_U1] = T(0);
-  if ((op.flags & G_CLAMP_OUT) && val[V_U1] < T(0)) val[V_U1] = T(0);
+  ghost_flags(op.flags, val);
 #pragma unroll
   for (int v = 0; v < NV; ++v) D.v[v][op.dst_cell] = val[v];
 }
@@ -734,6 +771,7 @@ struct kh_mesh {
   unsigned* dpre[8];   // face1..3, zone, ct, alloc cells (km_to_f32), all-cells (p2c), divB corners
   GhostOp* dops;
   long long nops;
+  long long ncopy;  // ops [0, ncopy) are same-level copies
   ProlongNb* dnbs;
   long long nnbs;
   double *geo, *dgm, *flo;
@@ -1078,7 +1116,11 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
           ops.push_back(op);
         }
   }
+  // same-level copies first (km_ghost_copy), the interpolating ops after
+  // (km_ghost); the fill has no ordering, every source being an interior cell
+  std::stable_partition(ops.begin(), ops.end(), [](const GhostOp& o) { return o.mode == G_COPY; });
   x->nops = (long long)ops.size();
+  x->ncopy = (long long)std::count_if(ops.begin(), ops.end(), [](const GhostOp& o) { return o.mode == G_COPY; });
   x->nnbs = (long long)nbs.size();
 
   // ---- prefix sums per kernel ----
@@ -1349,8 +1391,17 @@ Arena<double> arena_pb(double* P, double* B) { return Arena<double>{P, B, 5}; }
 
 template <class T> int fill_ghosts(kh_mesh* x, const Arena<T>& P) {
   if (!x->nops) return 0;
-  km_ghost<T><<<nblk(x->nops, MTPB), MTPB, 0, x->stream>>>(x->dblk, x->dops, x->nops, x->dnbs, P);
-  return 1;
+  int n = 0;
+  if (x->ncopy) {
+    km_ghost_copy<T><<<nblk(x->ncopy, MTPB), MTPB, 0, x->stream>>>(x->dblk, x->dops, x->ncopy, P);
+    ++n;
+  }
+  if (x->nops > x->ncopy) {
+    km_ghost<T><<<nblk(x->nops - x->ncopy, MTPB), MTPB, 0, x->stream>>>(x->dblk, x->dops, x->ncopy, x->nops,
+                                                                         x->dnbs, P);
+    ++n;
+  }
+  return n;
 }
 
 // fluxct: Flux-CT after the face fluxes (its EMF phase; the field-flux phase
