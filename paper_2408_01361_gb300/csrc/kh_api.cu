@@ -155,7 +155,7 @@ int run_stage(kh_ctx* x, int st, const double* U0, const Vars& Pin, const Vars& 
     mark(x, KH_T_FOFC, st, 1);
   }
   mark(x, KH_T_UPDATE, st, 0);
-  const FailList fl{x->flist, x->counters + CNT_LIST0 + st};
+  const FailList fl{x->flist, x->counters + CNT_LIST0 + st, 0u};
   n += launch_update(U0, cview(Pin), Pout, Uout, x->F, L, G, x->S, x->dscalar + 3, coef, x->pflag, x->counters,
                      x->tpb_update, s, fl, fBn, dUout);
   mark(x, KH_T_UPDATE, st, 1);
@@ -233,7 +233,7 @@ int run_stage_mixed(kh_ctx* x, int st, const double* U0, const VarsT<TIN>& Pin, 
     mark(x, KH_T_FOFC, st, 1);
   }
   mark(x, KH_T_UPDATE, st, 0);
-  const FailList fl{x->flist, x->counters + CNT_LIST0 + st};
+  const FailList fl{x->flist, x->counters + CNT_LIST0 + st, 0u};
   // 3-D Flux-CT stages stage their inputs by TMA; otherwise (2-D, face CT,
   // or no tensor map) the update reads them itself
   int ru = -1;

@@ -115,10 +115,13 @@ enum { CNT_FAIL = 0, CNT_FLOOR = 1, CNT_UNFIXED = 2, CNT_TIMEOUT = 3, CNT_FP64 =
        CNT_FOFC = 7, CNT_DRAIN = 8, NCNT = 9 };
 
 // Cells (L.at index) whose inversion failed in one stage, appended by the
-// update (idx == nullptr: not recorded); the fixup then visits these only.
+// update (idx == nullptr: not recorded) as tag | cell; the fixup then visits
+// these only. The single grid's tag is 0; the refined mesh's carries the
+// block (block << 20, every block's allocation holding fewer than 2^20 cells).
 struct FailList {
   unsigned* idx;
   unsigned long long* n;
+  unsigned tag;
 };
 
 // SSPRK(5,4) of Spiteri & Ruuth (2002) in Shu-Osher form (the paper's

@@ -304,10 +304,7 @@ __global__ void __launch_bounds__(TPB) k_fixup(VarsT<T> P, double* Uout, const i
 }
 
 // The same over the stage's failed-zone list (its length read on the
-// device), one warp per failed zone: lane l examines neighbour l of the
-// 3x3(x3) block (26 or 8 of them) at once, the sums meet by shuffles, and
-// lane 0 finishes the repair (the serial walk over the neighbours was a
-// chain of dependent loads).
+// device), one warp per failed zone (fixup_warp).
 template <class T>
 __global__ void __launch_bounds__(TPB) k_fixup_list(VarsT<T> P, double* Uout, const int8_t* pflag, Layout L,
                                                    DevGeom G, Scheme S, unsigned long long* cnt, FailList fl) {
@@ -316,7 +313,6 @@ __global__ void __launch_bounds__(TPB) k_fixup_list(VarsT<T> P, double* Uout, co
   const int lane = threadIdx.x & 31;
   const unsigned long long warp = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
   const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
-  const int nnb = L.ndim == 3 ? 26 : 8;
   for (unsigned long long q = warp; q < n; q += nwarps) {
     const long long c = fl.idx[q];
     const int k = (int)(c / gs), j = (int)((c % gs) / L.n1s), i = (int)(c % L.n1s);
@@ -326,31 +322,7 @@ __global__ void __launch_bounds__(TPB) k_fixup_list(VarsT<T> P, double* Uout, co
       continue;
     }
 #endif
-    double s[5] = {0, 0, 0, 0, 0};
-    int good = 0;
-    if (lane < nnb) {
-      // neighbour offsets in (dk, dj, di) order, the centre skipped
-      const int side = L.ndim == 3 ? 3 : 1;
-      const int idx = lane < (side * 9) / 2 ? lane : lane + 1;
-      const int dk = L.ndim == 3 ? idx / 9 - 1 : 0, dj = (idx / 3) % 3 - 1, di = idx % 3 - 1;
-      const int ii = i + di, jj = j + dj, kk = k + dk;
-      if (ii >= L.s[0] && ii < L.e[0] && jj >= L.s[1] && jj < L.e[1] && kk >= L.s[2] && kk < L.e[2]) {
-        const long long qn = L.at(kk, jj, ii);
-        if (pflag[qn] == 0) {
-          good = 1;
-#pragma unroll
-          for (int v = 0; v < 5; ++v) s[v] = (double)P.v[v][qn];
-        }
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-      for (int v = 0; v < 5; ++v) s[v] += __shfl_xor_sync(0xffffffffu, s[v], o);
-      good += __shfl_xor_sync(0xffffffffu, good, o);
-    }
-    if (lane == 0) fixup_finish<T>(P, Uout, L, G, S, cnt, i, j, k, s, good);
-    __syncwarp();
+    fixup_warp<T>(P, Uout, pflag, L, G, S, cnt, i, j, k, lane);
   }
 }
 
@@ -381,7 +353,7 @@ __global__ void __launch_bounds__(TPB_MAX, 3) k_fofc_trial_mixed(const double* U
   int i, j, k;
   zone_ijk(L, t, i, j, k);
   update_mixed_zone<true, INV>(U0, Pin, Vars{}, VarsT<float>{}, nullptr, F1, F2, F3, L, G, Gf, S,
-                          df_of_f64(coef * __ldg(dtp)), flag, cnt, i, j, k, FailList{nullptr, nullptr}, nullptr,
+                          df_of_f64(coef * __ldg(dtp)), flag, cnt, i, j, k, FailList{nullptr, nullptr, 0u}, nullptr,
                           nullptr, ect);
 }
 

@@ -161,12 +161,19 @@ __global__ void km_ct(const MBlock* blk, const unsigned* pre, int nb, R* F1, R* 
     apply_ct_at<R>(F1 + o8, F2 + o8, f3, ee1, ee2, e3 + o1, L, i, j, k);
 }
 
+// The stage's failed-zone list as block b's update appends to it (entries
+// b << 20 | cell; the list is off when idx is null).
+__device__ __forceinline__ FailList block_list(const FailList& fl, int b) {
+  return FailList{fl.idx, fl.n, fl.idx ? (unsigned)b << 20 : 0u};
+}
+
 template <int INV>
 __global__ void __launch_bounds__(256) km_update(const MBlock* blk, const unsigned* pre, int nb, const double* U0,
                                                 Arena<double> Pin, Arena<double> Pout, double* Uout,
                                                 const double* F1, const double* F2, const double* F3, GeoArena GA,
                                                 Scheme S, const double* dtp, double coef, int8_t* pflag,
-                                                unsigned long long* cnt, const double* fBn, double* dUout) {
+                                                unsigned long long* cnt, const double* fBn, double* dUout,
+                                                FailList fl) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= __ldg(pre + nb)) return;
   const int b = find_block(pre, nb, t);
@@ -176,7 +183,7 @@ __global__ void __launch_bounds__(256) km_update(const MBlock* blk, const unsign
   const long long o8 = NV * m.off;
   update_zone<false, INV>(U0 + o8, cvars_at(Pin, m), vars_at(Pout, m), Uout ? Uout + o8 : nullptr, F1 + o8, F2 + o8,
               m.L.ndim == 3 ? F3 + o8 : nullptr, m.L, geo64(GA, m), S, coef * __ldg(dtp), pflag + m.off, cnt, i, j,
-              k, nullptr, FailList{nullptr, nullptr}, fBn ? fBn + 3 * m.off : nullptr, dUout ? dUout + o8 : nullptr);
+              k, nullptr, block_list(fl, b), fBn ? fBn + 3 * m.off : nullptr, dUout ? dUout + o8 : nullptr);
 }
 
 template <int INV>
@@ -186,7 +193,7 @@ __global__ void __launch_bounds__(256, 2) km_update_mixed(const MBlock* blk, con
                                                       const float* F2, const float* F3, GeoArena GA, Scheme S,
                                                       const double* dtp, double coef, int8_t* pflag,
                                                       unsigned long long* cnt, const double* fBn, const float* e1,
-                                                      const float* e2, const float* e3, double* dUout) {
+                                                      const float* e2, const float* e3, double* dUout, FailList fl) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= __ldg(pre + nb)) return;
   const int b = find_block(pre, nb, t);
@@ -202,7 +209,7 @@ __global__ void __launch_bounds__(256, 2) km_update_mixed(const MBlock* blk, con
   // then run the one compiled copy and round alike
   update_mixed_zone<false, INV, true>(U0 + o8, cvars_at(Pin, m), P64, P32, Uout ? Uout + o8 : nullptr, F1 + o8, F2 + o8,
                     m.L.ndim == 3 ? F3 + o8 : nullptr, m.L, geo64(GA, m), geo32(GA, m), S,
-                    df_of_f64(coef * __ldg(dtp)), pflag + m.off, cnt, i, j, k, FailList{nullptr, nullptr},
+                    df_of_f64(coef * __ldg(dtp)), pflag + m.off, cnt, i, j, k, block_list(fl, b),
                     fBn ? fBn + 3 * m.off : nullptr, dUout ? dUout + o8 : nullptr,
                     CtEmf{{e1 ? e1 + m.off : nullptr, e2 ? e2 + m.off : nullptr, e3 ? e3 + m.off : nullptr}});
 }
@@ -229,7 +236,7 @@ __global__ void __launch_bounds__(256, 3)
     km_update_mixed_tma(const MBlock* blk, const MTile* tiles, const UpdateMaps* maps, int nsets, int set,
                         Arena<double> Pout64, Arena<float> Pout32, double* Uout, GeoArena GA, Scheme S,
                         const double* dtp, double coef, int8_t* pflag, unsigned long long* cnt, unsigned wlim,
-                        double* dUout) {
+                        double* dUout, FailList fl) {
   using T = UpdTile<TX, 256 / TX>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* smem = aligned_smem(smem_raw);
@@ -265,7 +272,7 @@ __global__ void __launch_bounds__(256, 3)
   const typename T::In in{smem, (i0 - x0) + lx, (i0 - xu0) + lx, ly};
   update_mixed_zone_in<false, INV, typename T::In, true>(
       in, P64, P32, Uout ? Uout + NV * m.off : nullptr, L, geo64(GA, m), geo32(GA, m), S,
-      df_of_f64(coef * __ldg(dtp)), pflag + m.off, cnt, i, j, k, FailList{nullptr, nullptr}, nullptr,
+      df_of_f64(coef * __ldg(dtp)), pflag + m.off, cnt, i, j, k, block_list(fl, t.b), nullptr,
       dUout ? dUout + NV * m.off : nullptr);
 }
 
@@ -306,7 +313,7 @@ __global__ void __launch_bounds__(256, 2) km_fofc_trial_mixed(const MBlock* blk,
   const long long o8 = NV * m.off;
   update_mixed_zone<true, INV>(U0 + o8, cvars_at(Pin, m), Vars{}, VarsT<float>{}, nullptr, F1 + o8, F2 + o8,
                                m.L.ndim == 3 ? F3 + o8 : nullptr, m.L, geo64(GA, m), geo32(GA, m), S,
-                               df_of_f64(coef * __ldg(dtp)), flag + m.off, cnt, i, j, k, FailList{nullptr, nullptr},
+                               df_of_f64(coef * __ldg(dtp)), flag + m.off, cnt, i, j, k, FailList{nullptr, nullptr, 0u},
                                nullptr, nullptr,
                                CtEmf{{e1 ? e1 + m.off : nullptr, e2 ? e2 + m.off : nullptr, e3 + m.off}});
 }
@@ -355,6 +362,26 @@ __global__ void __launch_bounds__(256) km_fofc_faces(const MBlock* blk, const un
   if constexpr (sizeof(R) == sizeof(double)) G = geo64(GA, m); else G = geo32(GA, m);
   flux_face<D, RECON_DONOR, TIN, R>(cvars_at(P, m), L, G, S, i, j, k, F + NV * m.off, ctop + m.off, m.polar_lo,
                                     m.polar_hi);
+}
+
+// The fixup over the stage's failed-zone list (its length read on the
+// device), one warp per failed zone, as the single grid's k_fixup_list.
+template <class T>
+__global__ void __launch_bounds__(256) km_fixup_list(const MBlock* blk, Arena<T> P, double* Uout, const int8_t* pflag,
+                                                     GeoArena GA, Scheme S, unsigned long long* cnt, FailList fl) {
+  const unsigned long long n = *fl.n;
+  const int lane = threadIdx.x & 31;
+  const unsigned long long warp = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
+  const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+  for (unsigned long long q = warp; q < n; q += nwarps) {
+    const unsigned e = fl.idx[q];
+    const MBlock& m = blk[e >> 20];
+    const Layout& L = m.L;
+    const long long c = e & 0xFFFFFu;
+    const int k = (int)(c / L.gplane), j = (int)((c % L.gplane) / L.n1s), i = (int)(c % L.n1s);
+    fixup_warp<T>(vars_at(P, m), Uout ? Uout + NV * m.off : nullptr, pflag + m.off, L, geo64(GA, m), S, cnt, i, j, k,
+                  lane);
+  }
 }
 
 template <class T>
@@ -786,6 +813,7 @@ struct kh_mesh {
   float* ctopf[3];
   float* emff[3];
   int8_t* pflag;
+  unsigned* flist = nullptr;  // a stage's failed zones, b << 20 | cell (null: the fixup scans every zone)
   double* partial;
   int npartial;
   double* dscalar;  // [0] dt out, [1..2] divB max and sum, [3] dt in
@@ -1241,6 +1269,11 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
   KM_ALLOC(x->flo, 3 * gp);
   KM_ALLOC(x->pstar, NV * pl);
   KM_ALLOC(x->pflag, (size_t)cells);
+  {
+    bool list_ok = nblocks <= 4096;
+    for (int b = 0; b < nblocks; ++b) list_ok = list_ok && x->hb[b].L.plane < (1LL << 20);
+    if (list_ok) KM_ALLOC(x->flist, sizeof(unsigned) * (size_t)std::max<long long>(zones, 1));
+  }
   if (!mixed) {
     for (int d = 0; d < x->ndim; ++d) {
       KM_ALLOC(x->F[d], NV * pl);
@@ -1533,6 +1566,30 @@ template <class T> int cfl_pass(kh_mesh* x, T* const ct[3]) {
   return 2;
 }
 
+// The stage's failed-zone list (off when the mesh has none: more than 4096
+// blocks, or a block allocation of 2^20 cells or more).
+FailList mesh_list(const kh_mesh* x) {
+  return x->flist ? FailList{x->flist, x->counters + CNT_LIST0, 0u} : FailList{nullptr, nullptr, 0u};
+}
+// Before a stage's update: its failed-zone list starts empty.
+void start_list(kh_mesh* x) {
+  if (x->flist) cudaMemsetAsync(x->counters + CNT_LIST0, 0, sizeof(unsigned long long), x->stream);
+}
+// The stage's fixup: over the failed-zone list (one warp per zone; the list
+// is short in practice and its length known only on the device), else over
+// every zone.
+template <class T> void mesh_fixup(kh_mesh* x, const Arena<T>& P, double* Uout) {
+  const unsigned nz = x->pre_zone.back();
+  if (x->flist) {
+    const long long b = std::min<long long>(nblk(nz, 256), 152);
+    km_fixup_list<T><<<(unsigned)b, 256, 0, x->stream>>>(x->dblk, P, Uout, x->pflag, garena(x), x->S, x->counters,
+                                                         mesh_list(x));
+  } else {
+    km_fixup<T><<<nblk(nz, MTPB), MTPB, 0, x->stream>>>(x->dblk, x->dpre[3], x->nb, P, Uout, x->pflag, garena(x), x->S,
+                                                       x->counters);
+  }
+}
+
 // The update kernels over all blocks, instantiated for the context's solver
 // (the mixed path: double-float Noble-2D, or FP64 for every zone).
 void km_update_any(const kh_mesh* x, int g, int t, const double* U0, const Arena<double>& Pin,
@@ -1540,7 +1597,7 @@ void km_update_any(const kh_mesh* x, int g, int t, const double* U0, const Arena
   const GeoArena GA = garena(x);
   auto go = [&](auto kern) {
     kern<<<g, t, 0, x->stream>>>(x->dblk, x->dpre[3], x->nb, U0, Pin, Pout, Uout, x->F[0], x->F[1], x->F[2], GA,
-                                 x->S, x->dscalar + 3, coef, x->pflag, x->counters, fBn, dUout);
+                                 x->S, x->dscalar + 3, coef, x->pflag, x->counters, fBn, dUout, mesh_list(x));
   };
   if (x->S.c2p.method == C2P_KASTAUN) go(km_update<C2P_KASTAUN>);
   else if (x->S.c2p.method == C2P_1DW) go(km_update<C2P_1DW>);
@@ -1553,7 +1610,7 @@ void km_update_mixed_any(const kh_mesh* x, int g, int t, const double* U0, const
   auto go = [&](auto kern) {
     kern<<<g, t, 0, x->stream>>>(x->dblk, x->dpre[3], x->nb, U0, Pin, Pout64, Pout32, Uout, x->Ff[0], x->Ff[1],
                                  x->Ff[2], GA, x->S, x->dscalar + 3, coef, x->pflag, x->counters, fBn, ce[0], ce[1],
-                                 ce[2], dUout);
+                                 ce[2], dUout, mesh_list(x));
   };
   if (x->S.c2p.method == C2P_KASTAUN) go(km_update_mixed<C2P_KASTAUN>);
   else if (x->S.c2p.method == C2P_1DW) go(km_update_mixed<C2P_1DW>);
@@ -1605,7 +1662,7 @@ int km_update_mixed_tma_all(const kh_mesh* x, int set, const Arena<double>& Pout
       if (!ok) return false;
       kern<<<(unsigned)nt, 256, smem, x->stream>>>(x->dblk, x->dtiles + t0, x->dmaps, x->nsets, set, Pout64,
                                                    Pout32, Uout, garena(x), x->S, x->dscalar + 3, coef, x->pflag,
-                                                   x->counters, (unsigned)KH_WAIT_POLLS, dUout);
+                                                   x->counters, (unsigned)KH_WAIT_POLLS, dUout, mesh_list(x));
       return true;
     };
     bool ok;
@@ -1648,9 +1705,9 @@ int mesh_stage64(kh_mesh* x, const double* U0, const Arena<double>& Pin, const A
     n += flux_pass<double, double>(x, Pin, x->F, x->ctop, x->emf, !face);
   }
   if (face) n += face_ct_pass<double>(x, Pin, x->F, x->ecc, x->emf, fBst, coef);
+  start_list(x);
   km_update_any(x, nblk(nz, x->tpb_update), x->tpb_update, U0, Pin, Pout, Uout, coef, face ? fBst : nullptr, dUout);
-  km_fixup<double><<<nblk(nz, MTPB), MTPB, 0, x->stream>>>(x->dblk, x->dpre[3], x->nb, Pout, Uout, x->pflag,
-                                                           garena(x), x->S, x->counters);
+  mesh_fixup(x, Pout, Uout);
   return n + 2;
 }
 
@@ -1679,6 +1736,7 @@ int mesh_stage_mixed(kh_mesh* x, bool first, const double* U, const double* U0, 
   if (x->S.fofc) n += fofc_pass<float, float>(x, U0, Pin, x->Ff, x->ctopf, x->emff, coef);
   if (face) n += face_ct_pass<float>(x, Pin, x->Ff, x->eccf, x->emff, fBst, coef);
   const bool staged = set >= 0 && x->tma_upd && !x->tma_off && x->tma_now && x->umap_key == U && !face;
+  start_list(x);
   if (staged) {
     const int r = km_update_mixed_tma_all(x, set, Pout64, Pout32, Uout, coef, dUout);
     if (r < 0) return -1;
@@ -1688,12 +1746,8 @@ int mesh_stage_mixed(kh_mesh* x, bool first, const double* U, const double* U0, 
                         face ? fBst : nullptr, ce, dUout);
     ++n;
   }
-  if (Pout64.a)
-    km_fixup<double><<<nblk(nz, MTPB), MTPB, 0, s>>>(x->dblk, x->dpre[3], x->nb, Pout64, Uout, x->pflag, garena(x),
-                                                     x->S, x->counters);
-  else
-    km_fixup<float><<<nblk(nz, MTPB), MTPB, 0, s>>>(x->dblk, x->dpre[3], x->nb, Pout32, Uout, x->pflag, garena(x),
-                                                    x->S, x->counters);
+  if (Pout64.a) mesh_fixup(x, Pout64, Uout);
+  else mesh_fixup(x, Pout32, Uout);
   return n + 1;
 }
 
@@ -2082,7 +2136,7 @@ int kh_mesh_destroy(kh_mesh* x) {
   drop_mesh_graph(x);
   if (x->cap_stream) cudaStreamDestroy(x->cap_stream);
   void* ptrs[] = {x->dblk, x->dops, x->dnbs, x->geo, x->dgm, x->flo, x->geof, x->dgmf, x->geodf, x->pstar, x->pstarf, x->pnf,
-                  x->pflag, x->partial, x->dscalar, x->counters, x->F[0], x->F[1], x->F[2], x->ctop[0],
+                  x->pflag, x->flist, x->partial, x->dscalar, x->counters, x->F[0], x->F[1], x->F[2], x->ctop[0],
                   x->ctop[1], x->ctop[2], x->emf[0], x->emf[1], x->emf[2], x->Ff[0], x->Ff[1], x->Ff[2],
                   x->ctopf[0], x->ctopf[1], x->ctopf[2], x->emff[0], x->emff[1], x->emff[2],
                   x->fBstar, x->ecc, x->eccf, x->dmatch, x->dtiles, x->dmaps, x->rk, x->fflag, x->fsave};

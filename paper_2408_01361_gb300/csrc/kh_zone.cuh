@@ -365,7 +365,7 @@ __device__ __forceinline__ void update_zone(const double* U0, const CVars& Pin, 
                                             const double* F1, const double* F2, const double* F3, const Layout& L,
                                             const DevGeom& G, const Scheme& S, double cdt, int8_t* pflag,
                                             unsigned long long* cnt, int i, int j, int k, double* Praw = nullptr,
-                                            FailList fl = FailList{nullptr, nullptr}, const double* fBn = nullptr,
+                                            FailList fl = FailList{nullptr, nullptr, 0u}, const double* fBn = nullptr,
                                             double* dUout = nullptr) {
   const long long c = L.at(k, j, i);
   const long long p = (long long)j * L.n1s + i;
@@ -427,7 +427,7 @@ __device__ __forceinline__ void update_zone(const double* U0, const CVars& Pin, 
   pflag[c] = (int8_t)flag;
   if (flag) {
     atomicAdd(cnt + CNT_FAIL, 1ULL);
-    if (fl.idx) fl.idx[atomicAdd(fl.n, 1ULL)] = (unsigned)c;
+    if (fl.idx) fl.idx[atomicAdd(fl.n, 1ULL)] = fl.tag | (unsigned)c;
   }
   if (fmask) atomicAdd(cnt + CNT_FLOOR, 1ULL);
 }
@@ -571,7 +571,7 @@ __device__ __forceinline__ void update_mixed_fp64_tail(double* U, const IN& in, 
   pflag[c] = (int8_t)flag;
   if (flag) {
     atomicAdd(cnt + CNT_FAIL, 1ULL);
-    if (fl.idx) fl.idx[atomicAdd(fl.n, 1ULL)] = (unsigned)c;
+    if (fl.idx) fl.idx[atomicAdd(fl.n, 1ULL)] = fl.tag | (unsigned)c;
   }
   if (fmask) atomicAdd(cnt + CNT_FLOOR, 1ULL);
 }
@@ -794,7 +794,7 @@ __device__ __forceinline__ void update_mixed_zone_in(const IN& in, const Vars& P
   pflag[c] = (int8_t)flag;
   if (flag) {
     atomicAdd(cnt + CNT_FAIL, 1ULL);
-    if (fl.idx) fl.idx[atomicAdd(fl.n, 1ULL)] = (unsigned)c;
+    if (fl.idx) fl.idx[atomicAdd(fl.n, 1ULL)] = fl.tag | (unsigned)c;
   }
   if (fmask) atomicAdd(cnt + CNT_FLOOR, 1ULL);
 }
@@ -808,7 +808,7 @@ __device__ __forceinline__ void update_mixed_zone(const double* U0, const CVarsT
                                                   const float* F2, const float* F3, const Layout& L, const DevGeom& G,
                                                   const GeomT<float>& Gf, const Scheme& S, df64 cdt, int8_t* pflag,
                                                   unsigned long long* cnt, int i, int j, int k,
-                                                  FailList fl = FailList{nullptr, nullptr},
+                                                  FailList fl = FailList{nullptr, nullptr, 0u},
                                                   const double* fBn = nullptr, double* dUout = nullptr,
                                                   CtEmf ect = CtEmf{{nullptr, nullptr, nullptr}}) {
   const MixedInGlobal in{U0, Pin, {F1, F2, F3}, ect, L.at(k, j, i), (long long)L.n1s, (long long)L.n1s * L.n2s,
@@ -848,6 +848,42 @@ __device__ __forceinline__ void fixup_finish(const VarsT<T>& P, double* Uout, co
     cons_only(Pn, s, m, S.gam, U);
     for (int v = 0; v < NV; ++v) Uout[v * L.plane + c] = U[v];
   }
+}
+
+// The fixup of failed zone (i, j, k) by one warp: lane l examines neighbour
+// l of the 3x3(x3) block (26 or 8 of them) at once, the sums meet by
+// shuffles, and lane 0 finishes the repair (a serial walk over the
+// neighbours is a chain of dependent loads). Every lane of the warp calls it.
+template <class T>
+__device__ __forceinline__ void fixup_warp(const VarsT<T>& P, double* Uout, const int8_t* pflag, const Layout& L,
+                                           const DevGeom& G, const Scheme& S, unsigned long long* cnt, int i, int j,
+                                           int k, int lane) {
+  const int nnb = L.ndim == 3 ? 26 : 8;
+  double s[5] = {0, 0, 0, 0, 0};
+  int good = 0;
+  if (lane < nnb) {
+    // neighbour offsets in (dk, dj, di) order, the centre skipped
+    const int side = L.ndim == 3 ? 3 : 1;
+    const int idx = lane < (side * 9) / 2 ? lane : lane + 1;
+    const int dk = L.ndim == 3 ? idx / 9 - 1 : 0, dj = (idx / 3) % 3 - 1, di = idx % 3 - 1;
+    const int ii = i + di, jj = j + dj, kk = k + dk;
+    if (ii >= L.s[0] && ii < L.e[0] && jj >= L.s[1] && jj < L.e[1] && kk >= L.s[2] && kk < L.e[2]) {
+      const long long qn = L.at(kk, jj, ii);
+      if (pflag[qn] == 0) {
+        good = 1;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) s[v] = (double)P.v[v][qn];
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) s[v] += __shfl_xor_sync(0xffffffffu, s[v], o);
+    good += __shfl_xor_sync(0xffffffffu, good, o);
+  }
+  if (lane == 0) fixup_finish<T>(P, Uout, L, G, S, cnt, i, j, k, s, good);
+  __syncwarp();
 }
 
 template <class T>
