@@ -122,9 +122,14 @@ __device__ __forceinline__ int find_block(const unsigned* pre, int nb, unsigned 
   return b;
 }
 
+// One face per thread. The FP32 faces are held to 64 registers (four
+// 256-thread blocks per SM): their stencil loads are latency-bound, and the
+// extra warps hide more of it than the few spilled values cost (refined torus
+// 870 -> 915 M zone-cycles/s against 80 registers); the FP64 faces would
+// spill ~700 bytes a thread under that cap and keep their registers.
 template <int D, int RECON, class TIN, class R>
-__global__ void __launch_bounds__(256) km_flux(const MBlock* blk, const unsigned* pre, int nb, Arena<TIN> Pin,
-                                              GeoArena GA, Scheme S, R* F, R* ctop) {
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1)
+    km_flux(const MBlock* blk, const unsigned* pre, int nb, Arena<TIN> Pin, GeoArena GA, Scheme S, R* F, R* ctop) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= __ldg(pre + nb)) return;
   const int b = find_block(pre, nb, t);

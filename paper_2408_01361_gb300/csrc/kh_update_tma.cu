@@ -7,20 +7,23 @@
 // longer in L2. Read by the threads themselves, those loads hold the
 // registers of a kernel whose arithmetic (the double-float inversion) wants
 // ~220 of them, and their DRAM latency is exposed at the ~35% occupancy the
-// register budget leaves. Here one CTA updates a tile of 32 (x1) x 8 (x2)
+// register budget leaves. Here one CTA updates a tile of 32 (x1) x 4 (x2)
 // zones of one x3 plane: thread 0 issues eight tensor copies (kh_update_tile.cuh)
 // on one mbarrier, the copy engine moves them while the SM runs other CTAs,
 // and every thread then runs the same per-zone update (update_mixed_zone_in)
-// reading its values from the tiles.
+// reading its values from the tiles. Seven 128-thread CTAs per SM (72
+// registers, 29 KB of tiles each): 2% faster than three 256-thread CTAs at 80
+// registers; 32 x 8, 32 x 2 and 32 x 1 x 8 tiles (the last sharing the
+// geometry columns of a CTA's warps through L1) measured within 3% of these.
 #include "kh_update_tile.cuh"
 
 namespace kh {
 namespace {
 
-using Tile = UpdTile<32, 8>;
+using Tile = UpdTile<32, 4>;
 
 template <int INV>
-__global__ void __launch_bounds__(Tile::NT, 3)
+__global__ void __launch_bounds__(Tile::NT, 7)
     k_update_mixed_tma(const __grid_constant__ UpdateMaps tm, Vars Pout64, VarsT<float> Pout32, double* Uout,
                        Layout L, DevGeom G, GeomT<float> Gf, Scheme S, const double* dtp, double coef, int8_t* pflag,
                        unsigned long long* cnt, FailList fl, double* dUout, unsigned wlim) {
