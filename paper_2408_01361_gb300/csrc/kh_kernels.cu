@@ -188,8 +188,13 @@ __global__ void k_fill_f32(CVarsT<double> src, VarsT<float> dst, Layout L, Schem
   if (KH_OOB(L, kh_in(L, i, j, k, 0))) return;
   if (i >= L.s[0] && i < L.e[0] && j >= L.s[1] && j < L.e[1] && k >= L.s[2] && k < L.e[2]) {
     const long long c = L.at(k, j, i);
+    // all eight loads first (in flight together), then the conversions
+    // (integer ops, not the FP64 pipe) and stores
+    double q[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) dst.v[v][c] = f32_of_f64(src.v[v][c]);  // integer ops, not the FP64 pipe
+    for (int v = 0; v < NV; ++v) q[v] = src.v[v][c];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) dst.v[v][c] = f32_of_f64(q[v]);
   } else {
     bc_cell<double, float>(src, dst, L, S, dlo, dhi, i, j, k);
   }

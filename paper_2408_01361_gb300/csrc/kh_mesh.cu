@@ -58,6 +58,13 @@ struct GhostOp {
   unsigned char mode, flags, pad;
 };
 
+// A same-level copy in 16 bytes (one vector load per thread): the source
+// cell in the low 28 bits of the last word, the boundary flags above them.
+struct __align__(16) GhostCopy {
+  int dst_block, dst_cell, src_block;
+  unsigned src_cell_flags;
+};
+
 // Coarse-level values on either side of a prolonged coarse cell, per
 // direction: [d][0] below, [d][1] above. mode G_COPY: a cell of a block at
 // the coarse level; G_RESTRICT: the mean of a finer block's 2x2(x2) cells
@@ -545,19 +552,21 @@ template <class T> __device__ __forceinline__ void ghost_flags(unsigned char fla
 // most ghost cells (~88% on the refined torus); on their own they run without
 // the registers and branches of the interpolating ops below.
 template <class T>
-__global__ void __launch_bounds__(MTPB) km_ghost_copy(const MBlock* blk, const GhostOp* ops, long long n,
+__global__ void __launch_bounds__(MTPB) km_ghost_copy(const MBlock* blk, const GhostCopy* ops, long long n,
                                                       Arena<T> P) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= n) return;
-  const GhostOp op = ops[t];
-  const VarsT<T> D = vars_at(P, blk[op.dst_block]);
-  const VarsT<T> Sv = vars_at(P, blk[op.src_block]);
+  const int4 q = __ldg(reinterpret_cast<const int4*>(ops) + t);
+  const unsigned sc = (unsigned)q.w;
+  const VarsT<T> D = vars_at(P, blk[q.x]);
+  const VarsT<T> Sv = vars_at(P, blk[q.z]);
+  const long long c = sc & 0x0FFFFFFFu;
   T val[NV];
 #pragma unroll
-  for (int v = 0; v < NV; ++v) val[v] = Sv.v[v][op.src_cell];
-  ghost_flags(op.flags, val);
+  for (int v = 0; v < NV; ++v) val[v] = Sv.v[v][c];
+  ghost_flags((unsigned char)(sc >> 28), val);
 #pragma unroll
-  for (int v = 0; v < NV; ++v) D.v[v][op.dst_cell] = val[v];
+  for (int v = 0; v < NV; ++v) D.v[v][q.y] = val[v];
 }
 
 // Part 2: the ops from index `first` on, restriction (finer owner) or
@@ -624,8 +633,13 @@ __global__ void km_to_f32(const MBlock* blk, const unsigned* pre, int nb, Arena<
   const long long c = t - __ldg(pre + b);
   const CVars S = cvars_at(src, m);
   const VarsT<float> D = vars_at(dst, m);
+  // all eight loads first (in flight together), then the conversions
+  // (integer ops, not the FP64 pipe) and stores
+  double q[NV];
 #pragma unroll
-  for (int v = 0; v < NV; ++v) D.v[v][c] = f32_of_f64(S.v[v][c]);  // integer ops, not the FP64 pipe
+  for (int v = 0; v < NV; ++v) q[v] = S.v[v][c];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) D.v[v][c] = f32_of_f64(q[v]);
 }
 
 // FP64 -> FP32 copy of the 8 slots of the interior cells of every block (the
@@ -643,8 +657,13 @@ __global__ void km_to_f32_interior(const MBlock* blk, const unsigned* pre, int n
   const long long c = m.L.at(k, j, i);
   const CVars S = cvars_at(src, m);
   const VarsT<float> D = vars_at(dst, m);
+  // all eight loads first (in flight together), then the conversions
+  // (integer ops, not the FP64 pipe) and stores
+  double q[NV];
 #pragma unroll
-  for (int v = 0; v < NV; ++v) D.v[v][c] = f32_of_f64(S.v[v][c]);  // integer ops, not the FP64 pipe
+  for (int v = 0; v < NV; ++v) q[v] = S.v[v][c];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) D.v[v][c] = f32_of_f64(q[v]);
 }
 
 __global__ void km_p2c(const MBlock* blk, const unsigned* pre, int nb, Arena<double> P, double* U, GeoArena GA,
@@ -802,6 +821,7 @@ struct kh_mesh {
   MBlock* dblk;
   unsigned* dpre[8];   // face1..3, zone, ct, alloc cells (km_to_f32), all-cells (p2c), divB corners
   GhostOp* dops;
+  GhostCopy* dcopy = nullptr;  // ops [0, ncopy) in the compact form km_ghost_copy reads
   long long nops;
   long long ncopy;  // ops [0, ncopy) are same-level copies
   ProlongNb* dnbs;
@@ -1268,6 +1288,7 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
     KM_ALLOC(x->dpre[q], sizeof(unsigned) * pretab[q].size());
   }
   KM_ALLOC(x->dops, sizeof(GhostOp) * std::max<long long>(x->nops, 1));
+  KM_ALLOC(x->dcopy, sizeof(GhostCopy) * std::max<long long>(x->ncopy, 1));
   KM_ALLOC(x->dnbs, sizeof(ProlongNb) * std::max<long long>(x->nnbs, 1));
   KM_ALLOC(x->geo, 3 * NGEO * gp);
   KM_ALLOC(x->dgm, NDG * gp);
@@ -1328,6 +1349,16 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
         cudaMemcpy(x->dpre[q], pretab[q].data(), sizeof(unsigned) * pretab[q].size(), cudaMemcpyHostToDevice));
   if (rc == KH_OK && x->nops)
     rc = cuda_rc(cudaMemcpy(x->dops, ops.data(), sizeof(GhostOp) * x->nops, cudaMemcpyHostToDevice));
+  if (rc == KH_OK && x->ncopy) {
+    std::vector<GhostCopy> cops((size_t)x->ncopy);
+    for (long long q = 0; q < x->ncopy && rc == KH_OK; ++q) {
+      const GhostOp& o = ops[(size_t)q];
+      if ((unsigned)o.src_cell >= (1u << 28) || o.flags >= 16) rc = KH_EINVAL;  // beyond the compact form
+      cops[(size_t)q] = GhostCopy{o.dst_block, o.dst_cell, o.src_block, (unsigned)o.src_cell | ((unsigned)o.flags << 28)};
+    }
+    if (rc == KH_OK)
+      rc = cuda_rc(cudaMemcpy(x->dcopy, cops.data(), sizeof(GhostCopy) * x->ncopy, cudaMemcpyHostToDevice));
+  }
   if (rc == KH_OK && x->nnbs)
     rc = cuda_rc(cudaMemcpy(x->dnbs, nbs.data(), sizeof(ProlongNb) * x->nnbs, cudaMemcpyHostToDevice));
   if (rc == KH_OK && x->nmatch)
@@ -1431,7 +1462,7 @@ template <class T> int fill_ghosts(kh_mesh* x, const Arena<T>& P) {
   if (!x->nops) return 0;
   int n = 0;
   if (x->ncopy) {
-    km_ghost_copy<T><<<nblk(x->ncopy, MTPB), MTPB, 0, x->stream>>>(x->dblk, x->dops, x->ncopy, P);
+    km_ghost_copy<T><<<nblk(x->ncopy, MTPB), MTPB, 0, x->stream>>>(x->dblk, x->dcopy, x->ncopy, P);
     ++n;
   }
   if (x->nops > x->ncopy) {
@@ -2140,7 +2171,7 @@ int kh_mesh_destroy(kh_mesh* x) {
   cudaStreamSynchronize(x->stream);
   drop_mesh_graph(x);
   if (x->cap_stream) cudaStreamDestroy(x->cap_stream);
-  void* ptrs[] = {x->dblk, x->dops, x->dnbs, x->geo, x->dgm, x->flo, x->geof, x->dgmf, x->geodf, x->pstar, x->pstarf, x->pnf,
+  void* ptrs[] = {x->dblk, x->dops, x->dcopy, x->dnbs, x->geo, x->dgm, x->flo, x->geof, x->dgmf, x->geodf, x->pstar, x->pstarf, x->pnf,
                   x->pflag, x->flist, x->partial, x->dscalar, x->counters, x->F[0], x->F[1], x->F[2], x->ctop[0],
                   x->ctop[1], x->ctop[2], x->emf[0], x->emf[1], x->emf[2], x->Ff[0], x->Ff[1], x->Ff[2],
                   x->ctopf[0], x->ctopf[1], x->ctopf[2], x->emff[0], x->emff[1], x->emff[2],
