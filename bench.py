@@ -919,10 +919,10 @@ FP64_FLOPS_PER_ZONE: dict = {
 FP32_FLOPS_PER_ZONE: dict = {
     # paired instructions count 2 lanes (an FFMA2 = 4 flops)
     ("mixed", "flux_x1"): 1565.0, ("mixed", "flux_x2"): 1645.0, ("mixed", "flux_x3"): 1714.0,
-    ("mixed", "update"): 2192.1,  # stages 1 and 2 (2175, 2209); FP64: 1 and 21 flops per zone
+    ("mixed", "update"): 1903.3,  # stages 1 and 2 (1919.3, 1887.3); FP64: 1 and 21 flops per zone
 }
 DRAM_BYTES_PER_ZONE: dict = {
-    ("mixed", "update"): 256.8,  # the TMA-staged update: mean of stage 1 (217.6) and stage 2 (296.0)
+    ("mixed", "update"): 279.8,  # the TMA-staged update (32x4 tiles): mean of stage 1 (232.0) and stage 2 (327.6)
     ("mixed", "flux_x1"): 44.4, ("mixed", "flux_x2"): 46.0, ("mixed", "flux_x3"): 47.7,
     ("fp64", "update"): 419.1,  # stage 1
     ("fp64", "flux_x1"): 118.0, ("fp64", "flux_x2"): 126.1, ("fp64", "flux_x3"): 128.3,

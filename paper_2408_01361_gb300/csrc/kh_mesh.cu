@@ -1044,6 +1044,7 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
   // ---- ghost map ----
   std::vector<GhostOp> ops;
   std::vector<ProlongNb> nbs;
+  std::map<std::pair<int, long long>, int> nb_of;  // (source block, coarse cell) -> its record
   const long long two_nf[3] = {2 * loc.nf[0], 2 * loc.nf[1], 2 * loc.nf[2]};
   for (int b = 0; b < nblocks && true; ++b) {
     const MBlock& m = x->hb[b];
@@ -1150,8 +1151,16 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
                   nb.block[d][side] = w;
                   nb.cell[d][side] = (int)mw.L.at(lw[2], lw[1], lw[0]);
                 }
-              op.nbi = (int)nbs.size();
-              nbs.push_back(nb);
+              // one record per coarse cell, shared by the fine ghost cells prolonged from it
+              const auto key = std::make_pair(s, (long long)Ls.at(li[2], li[1], li[0]));
+              const auto it = nb_of.find(key);
+              if (it != nb_of.end()) {
+                op.nbi = it->second;
+              } else {
+                op.nbi = (int)nbs.size();
+                nbs.push_back(nb);
+                nb_of.emplace(key, op.nbi);
+              }
             }
           } else if (dl == 1) {
             // the owner's 2x2(x2) fine cells covering this coarse cell
@@ -1174,6 +1183,12 @@ int kh_mesh_init(double a, const kh_coords* c, double gamma, int nblocks, const 
   std::stable_partition(ops.begin(), ops.end(), [](const GhostOp& o) { return o.mode == G_COPY; });
   x->nops = (long long)ops.size();
   x->ncopy = (long long)std::count_if(ops.begin(), ops.end(), [](const GhostOp& o) { return o.mode == G_COPY; });
+  // the interpolating ops grouped by source cell: the fine ghost cells
+  // prolonged from one coarse cell (up to 8) sit in neighbouring lanes and
+  // their identical loads of the coarse cell and its neighbours merge
+  std::stable_sort(ops.begin() + x->ncopy, ops.end(), [](const GhostOp& a, const GhostOp& b) {
+    return a.src_block != b.src_block ? a.src_block < b.src_block : a.src_cell < b.src_cell;
+  });
   x->nnbs = (long long)nbs.size();
 
   // ---- prefix sums per kernel ----
