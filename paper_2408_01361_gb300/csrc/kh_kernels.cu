@@ -891,10 +891,15 @@ __global__ void k_pack(const double* U, CVars PB, double* out, Layout L) {
   int i, j, k;
   zone_ijk(L, t, i, j, k);
   const long long c = L.at(k, j, i);
+  // all sixteen loads first (in flight together), then the stores
+  double q[2 * NV];
 #pragma unroll
-  for (int v = 0; v < NV; ++v) out[(long long)v * nz + t] = U[v * L.plane + c];
+  for (int v = 0; v < NV; ++v) {
+    q[v] = U[v * L.plane + c];
+    q[NV + v] = PB.v[v][c];
+  }
 #pragma unroll
-  for (int v = 0; v < NV; ++v) out[(long long)(NV + v) * nz + t] = PB.v[v][c];
+  for (int v = 0; v < 2 * NV; ++v) out[(long long)v * nz + t] = q[v];
 }
 
 __global__ void k_unpack(const double* in, double* U, Vars PB, Layout L) {
@@ -904,10 +909,16 @@ __global__ void k_unpack(const double* in, double* U, Vars PB, Layout L) {
   int i, j, k;
   zone_ijk(L, t, i, j, k);
   const long long c = L.at(k, j, i);
+  // all sixteen loads first (over the host link when `in` is pinned host
+  // memory: their latencies overlap), then the stores
+  double q[2 * NV];
 #pragma unroll
-  for (int v = 0; v < NV; ++v) U[v * L.plane + c] = in[(long long)v * nz + t];
+  for (int v = 0; v < 2 * NV; ++v) q[v] = in[(long long)v * nz + t];
 #pragma unroll
-  for (int v = 0; v < NV; ++v) PB.v[v][c] = in[(long long)(NV + v) * nz + t];
+  for (int v = 0; v < NV; ++v) {
+    U[v * L.plane + c] = q[v];
+    PB.v[v][c] = q[NV + v];
+  }
 }
 
 int launch_pack(const double* U, const CVars& PB, double* out, const Layout& L, cudaStream_t s) {

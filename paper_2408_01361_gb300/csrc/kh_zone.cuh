@@ -200,17 +200,25 @@ __device__ __forceinline__ void emf_at(const R* F1, const R* F2, const R* F3, R*
     e3[c] = q * (F1B2[c] + F1B2[c - sj] - F2B1[c] - F2B1[c - 1]);
     return;
   }
-  if (k < L.e[2]) e3[c] = q * (F1B2[c] + F1B2[c - sj] - F2B1[c] - F2B1[c - 1]);
-  if (i < L.e[0]) {
-    const R* F2B3 = F2 + V_B3 * P;
-    const R* F3B2 = F3 + V_B2 * P;
-    e1[c] = q * (F2B3[c] + F2B3[c - sk] - F3B2[c] - F3B2[c - sj]);
+  // the three edges' loads first (in flight together), then the sums and stores
+  const bool d3 = k < L.e[2], d1 = i < L.e[0], d2 = j < L.e[1];
+  const R* F2B3 = F2 + V_B3 * P;
+  const R* F3B2 = F3 + V_B2 * P;
+  const R* F3B1 = F3 + V_B1 * P;
+  const R* F1B3 = F1 + V_B3 * P;
+  R a[4] = {R(0), R(0), R(0), R(0)}, b[4] = {R(0), R(0), R(0), R(0)}, g[4] = {R(0), R(0), R(0), R(0)};
+  if (d3) {
+    a[0] = F1B2[c], a[1] = F1B2[c - sj], a[2] = F2B1[c], a[3] = F2B1[c - 1];
   }
-  if (j < L.e[1]) {
-    const R* F3B1 = F3 + V_B1 * P;
-    const R* F1B3 = F1 + V_B3 * P;
-    e2[c] = q * (F3B1[c] + F3B1[c - 1] - F1B3[c] - F1B3[c - sk]);
+  if (d1) {
+    b[0] = F2B3[c], b[1] = F2B3[c - sk], b[2] = F3B2[c], b[3] = F3B2[c - sj];
   }
+  if (d2) {
+    g[0] = F3B1[c], g[1] = F3B1[c - 1], g[2] = F1B3[c], g[3] = F1B3[c - sk];
+  }
+  if (d3) e3[c] = q * (a[0] + a[1] - a[2] - a[3]);
+  if (d1) e1[c] = q * (b[0] + b[1] - b[2] - b[3]);
+  if (d2) e2[c] = q * (g[0] + g[1] - g[2] - g[3]);
 }
 
 
