@@ -258,7 +258,7 @@ def _rollout_grad(kh, torch, cfg, P0, nsteps, dt, objective):
     J.backward()
     N1 = P0.shape[3]
     gPB = np.concatenate([ctx.to_host(P.grad, N1), ctx.to_host(B.grad, N1)])
-    return float(J), gPB, float(gam.grad)
+    return float(J.detach()), gPB, float(gam.grad)
 
 
 def _energy(cfg, torch):

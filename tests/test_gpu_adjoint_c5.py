@@ -126,7 +126,7 @@ def _rollout(kh, torch, cfg, U0, P0, dt, i_face, precision=None):
         else:
             J = -F1[0, ksl, jsl, i_face].sum() * _dA1(cfg)
         J.backward()
-        out[name] = (float(J), ctx.to_host(Ut.grad, N1),
+        out[name] = (float(J.detach()), ctx.to_host(Ut.grad, N1),
                      np.concatenate([ctx.to_host(Pt.grad, N1), ctx.to_host(Bt.grad, N1)]), float(gam.grad))
     return out
 
