@@ -124,6 +124,7 @@ template <int D, int RECON>
 __global__ void __launch_bounds__(NT) k_flux_tma(const __grid_constant__ CUtensorMap tm, Layout L, GeomT<float> G,
                                                  Scheme S, FaceBox box, float* F, float* ctop, int polar_lo,
                                                  int polar_hi, unsigned long long* cnt, unsigned wlim) {
+  pdl_wait();
   using Sh = TileShape<D>;
   __shared__ alignas(128) float tile[NV * Sh::BZ * Sh::BY * Sh::BX];
   __shared__ float sL[NV][NT], sR[NV][NT];
@@ -271,9 +272,9 @@ int launch_d(const float* P8, const Layout& L, const GeomT<float>& G, const Sche
   else
     grid = dim3((L.e[0] + 1 + CW - 1) / CW, (L.n3 + 1 + Sh::FY - 1) / Sh::FY, L.n2 + 2);
   if (S.recon == KH_RECON_MC)
-    k_flux_tma<D, KH_RECON_MC><<<grid, NT, 0, s>>>(tm, L, G, S, b, F, ctop, plo, phi, cnt, wlim);
+    launch_pdl(k_flux_tma<D, KH_RECON_MC>, grid, dim3(NT), 0, s, tm, L, G, S, b, F, ctop, plo, phi, cnt, wlim);
   else
-    k_flux_tma<D, KH_RECON_WENO5><<<grid, NT, 0, s>>>(tm, L, G, S, b, F, ctop, plo, phi, cnt, wlim);
+    launch_pdl(k_flux_tma<D, KH_RECON_WENO5>, grid, dim3(NT), 0, s, tm, L, G, S, b, F, ctop, plo, phi, cnt, wlim);
   return 1;
 }
 

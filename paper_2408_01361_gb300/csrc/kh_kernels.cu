@@ -169,6 +169,7 @@ __device__ __forceinline__ void bc_cell(const CVarsT<TS>& src, const VarsT<TD>& 
 
 template <class TS, class TD>
 __global__ void k_bc_fill(CVarsT<TS> src, VarsT<TD> dst, Layout L, Scheme S, const TS* dlo, const TS* dhi) {
+  pdl_wait();
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= ghost_total(L)) return;
   int i, j, k;
@@ -181,6 +182,7 @@ __global__ void k_bc_fill(CVarsT<TS> src, VarsT<TD> dst, Layout L, Scheme S, con
 // from the FP64 interior (the mixed path's stage-1 input).
 __global__ void k_fill_f32(CVarsT<double> src, VarsT<float> dst, Layout L, Scheme S, const double* dlo,
                            const double* dhi) {
+  pdl_wait();
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (unsigned)L.N1 * L.N2 * L.N3) return;
   int i, j, k;
@@ -222,6 +224,7 @@ __global__ void __launch_bounds__(TPB_MAX) k_flux(CVarsT<TIN> P, Layout L, GeomT
 //   cyclic e1 (x1-edges), e2 (x2-edges) in 3-D.
 template <class R>
 __global__ void k_emf(const R* F1, const R* F2, const R* F3, R* e1, R* e2, R* e3, Layout L) {
+  pdl_wait();
   const int n0 = L.e[0] - L.s[0] + 1, n1 = L.e[1] - L.s[1] + 1, n2 = (L.ndim == 3) ? L.e[2] - L.s[2] + 1 : 1;
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (unsigned)n0 * n1 * n2) return;
@@ -313,6 +316,7 @@ __global__ void __launch_bounds__(TPB) k_fixup(VarsT<T> P, double* Uout, const i
 template <class T>
 __global__ void __launch_bounds__(TPB) k_fixup_list(VarsT<T> P, double* Uout, const int8_t* pflag, Layout L,
                                                    DevGeom G, Scheme S, unsigned long long* cnt, FailList fl) {
+  pdl_wait();
   const unsigned long long n = *fl.n;
   const long long gs = L.gplane;
   const int lane = threadIdx.x & 31;
@@ -547,6 +551,7 @@ __device__ __forceinline__ void block_max_sum(double& a, double& b) {
 template <class T>
 __global__ void __launch_bounds__(RED_THREADS) k_cfl(const T* c1, const T* c2, const T* c3, Layout L,
                                                     double* partial) {
+  pdl_wait();
   const unsigned nz = nzones(L);
   T m = T(0);  // per-thread maximum in the speeds' precision
   for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < nz; t += gridDim.x * blockDim.x) {
@@ -565,6 +570,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_cfl(const T* c1, const T* c2, c
 }
 
 __global__ void k_finish(const double* partial, int n, double cfl, int mode, double* out) {
+  pdl_wait();
   double a = 0.0, b = 0.0;
   for (int q = threadIdx.x; q < n; q += blockDim.x) {
     a = fmax(a, partial[2 * q]);
@@ -706,7 +712,7 @@ int launch_bc_fill(const CVarsT<TS>& src, const VarsT<TD>& dst, const Layout& L,
   const long long nj = L.e[1] - L.s[1], nk = L.e[2] - L.s[2];
   const long long tot = nj * nk * L.ng * 2 + (long long)L.N1 * nk * L.ng * 2 +
                         (L.ndim == 3 ? (long long)L.N1 * L.N2 * L.ng3 * 2 : 0);
-  k_bc_fill<TS, TD><<<nblocks(tot, TPB), TPB, 0, s>>>(src, dst, L, S, dlo, dhi);
+  launch_pdl(k_bc_fill<TS, TD>, dim3((unsigned)nblocks(tot, TPB)), dim3(TPB), 0, s, src, dst, L, S, dlo, dhi);
   return 1;
 }
 template int launch_bc_fill<double, float>(const CVarsT<double>&, const VarsT<float>&, const Layout&, const Scheme&,
@@ -811,7 +817,7 @@ template <class R> int launch_ct(R* const F[3], R* const emf[3], const Layout& L
 }
 template <class R> int launch_emf(R* const F[3], R* const emf[3], const Layout& L, cudaStream_t s) {
   const long long tot = (long long)(L.e[0] - L.s[0] + 1) * (L.e[1] - L.s[1] + 1) * (L.ndim == 3 ? L.e[2] - L.s[2] + 1 : 1);
-  k_emf<R><<<nblocks(tot, TPB), TPB, 0, s>>>(F[0], F[1], F[2], emf[0], emf[1], emf[2], L);
+  launch_pdl(k_emf<R>, dim3((unsigned)nblocks(tot, TPB)), dim3(TPB), 0, s, F[0], F[1], F[2], emf[0], emf[1], emf[2], L);
   return 1;
 }
 template int launch_emf<float>(float* const[3], float* const[3], const Layout&, cudaStream_t);
@@ -861,7 +867,7 @@ int launch_fixup(const VarsT<T>& P, double* Uout, const int8_t* pflag, const Lay
     // the list is short in practice; its length is known only on the device
     long long b = nblocks(nz, TPB);
     if (b > 152) b = 152;
-    k_fixup_list<T><<<(int)b, TPB, 0, s>>>(P, Uout, pflag, L, G, S, cnt, fl);
+    launch_pdl(k_fixup_list<T>, dim3((unsigned)b), dim3(TPB), 0, s, P, Uout, pflag, L, G, S, cnt, fl);
   } else {
     k_fixup<T><<<nblocks(nz, TPB), TPB, 0, s>>>(P, Uout, pflag, L, G, S, cnt);
   }
@@ -875,8 +881,8 @@ template int launch_fixup<float>(const VarsT<float>&, double*, const int8_t*, co
 template <class T>
 int launch_cfl(T* const ctop[3], const Layout& L, double cfl, double* partial, int npartial, double* dt_out,
                cudaStream_t s) {
-  k_cfl<T><<<npartial, RED_THREADS, 0, s>>>(ctop[0], ctop[1], ctop[2], L, partial);
-  k_finish<<<1, RED_THREADS, 0, s>>>(partial, npartial, cfl, 0, dt_out);
+  launch_pdl(k_cfl<T>, dim3(npartial), dim3(RED_THREADS), 0, s, ctop[0], ctop[1], ctop[2], L, partial);
+  launch_pdl(k_finish, dim3(1), dim3(RED_THREADS), 0, s, partial, npartial, cfl, 0, dt_out);
   return 2;
 }
 template int launch_cfl<double>(double* const[3], const Layout&, double, double*, int, double*, cudaStream_t);
@@ -936,7 +942,7 @@ int launch_unpack(const double* in, double* U, const Vars& PB, const Layout& L, 
 int launch_fill_f32(const CVars& src, const VarsT<float>& dst, const Layout& L, const Scheme& S, const double* dlo,
                     const double* dhi, cudaStream_t s) {
   const long long tot = (long long)L.N1 * L.N2 * L.N3;
-  k_fill_f32<<<nblocks(tot, TPB), TPB, 0, s>>>(src, dst, L, S, dlo, dhi);
+  launch_pdl(k_fill_f32, dim3((unsigned)nblocks(tot, TPB)), dim3(TPB), 0, s, src, dst, L, S, dlo, dhi);
   return 1;
 }
 

@@ -27,6 +27,7 @@ __global__ void __launch_bounds__(Tile::NT, 7)
     k_update_mixed_tma(const __grid_constant__ UpdateMaps tm, Vars Pout64, VarsT<float> Pout32, double* Uout,
                        Layout L, DevGeom G, GeomT<float> Gf, Scheme S, const double* dtp, double coef, int8_t* pflag,
                        unsigned long long* cnt, FailList fl, double* dUout, unsigned wlim) {
+  pdl_wait();
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* smem = aligned_smem(smem_raw);
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + Tile::O_BAR);
@@ -69,8 +70,8 @@ int launch_update_mixed_tma(const double* U0, const float* P8, const Vars& Pout6
   const dim3 grid((L.n1 + Tile::TX - 1) / Tile::TX, (L.n2 + Tile::TY - 1) / Tile::TY, L.n3);
   auto go = [&](auto kern, bool ok) {
     if (!ok) return false;
-    kern<<<grid, Tile::NT, Tile::SMEM, s>>>(tm, Pout64, Pout32, Uout, L, G, Gf, S, dtp, coef, pflag, cnt, fl, dUout,
-                                            wlim);
+    launch_pdl(kern, grid, dim3(Tile::NT), Tile::SMEM, s, tm, Pout64, Pout32, Uout, L, G, Gf, S, dtp, coef, pflag, cnt,
+               fl, dUout, wlim);
     return true;
   };
   bool ok;
