@@ -57,6 +57,25 @@ int main() {
     const kh::df64 Z = kh::dfabs(X);
     e_sqrt = std::fmax(e_sqrt, std::fabs(val(kh::dfsqrt(Z)) - std::sqrt(std::fabs(vx))) / std::sqrt(std::fabs(vx)) / ulp48);
   }
+  // FP32 -> FP64 at the edges of every branch: signed zeros, the smallest and
+  // largest subnormals and normals, exponent boundaries, infinities (bit for
+  // bit) and NaN
+  {
+    const uint32_t edge[] = {0x00000000u, 0x00000001u, 0x007fffffu, 0x00800000u, 0x00800001u, 0x3f7fffffu,
+                             0x3f800000u, 0x3f800001u, 0x7effffffu, 0x7f000000u, 0x7f7fffffu, 0x7f800000u};
+    for (uint32_t e : edge)
+      for (uint32_t sg : {0u, 0x80000000u}) {
+        const float f = kh::f32_of_bits(e | sg);
+        if (kh::f64_bits(kh::f64_of_f32(f)) != kh::f64_bits((double)f)) ++bad_f32;
+      }
+    if (!std::isnan(kh::f64_of_f32(kh::f32_of_bits(0x7fc00000u)))) ++bad_f32;
+    for (uint32_t q = 0; q < 4000000u; ++q) {  // every exponent, random significands
+      const uint32_t bits = (uint32_t)(rng() & 0xffffffffu);
+      const float f = kh::f32_of_bits(bits);
+      if (std::isnan(f)) continue;
+      if (kh::f64_bits(kh::f64_of_f32(f)) != kh::f64_bits((double)f)) ++bad_f32;
+    }
+  }
   std::printf("%.3Le %.3Le %.3Le %.3Le %.3Le %.3Le %.3Le %.3Le %.3Le %.3Le %.3Le %ld %ld\n", e_sum, e_prod, e_conv, e_back,
               e_add, e_addf, e_mul, e_mulf, e_div, e_rcp, e_sqrt, bad_norm, bad_f32);
   return 0;
