@@ -156,6 +156,25 @@ def workload_name(cfg) -> str:
             f"2-stage Noble-2D, floors bsq/rho<100, 4e-2 u noise (seed 2)")
 
 
+def max_over_ranks(ms: float, dist, dev) -> float:
+    """The largest of every rank's elapsed time (the job's time: each rank's
+    units count in the throughput only once the slowest rank is done); ms
+    itself on a single process (dist None)."""
+    if not dist:
+        return ms
+    import torch
+
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def throughput(zones_per_rank: int, steps: int, world: int, ms: float) -> float:
+    """Whole-job zone-cycles/s: the zones every rank stepped, over the
+    slowest rank's time."""
+    return zones_per_rank * steps * world / (ms * 1e-3)
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -264,10 +283,7 @@ def measure(args, cfg, P0, ctx, dev, stream, dist, world, oracle_step, e2e=True)
         ms = e0.elapsed_time(e1)
         prof = ctx.profile_read() if profile else None
         ctx.profile(False)
-        if dist:
-            t = torch.tensor([ms], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, dist, dev)
         return ms, prof, launches, clocks, nfail
 
     # the step as a CUDA graph (kh_set_graph) and launched kernel by kernel
@@ -284,18 +300,18 @@ def measure(args, cfg, P0, ctx, dev, stream, dist, world, oracle_step, e2e=True)
     use_graph = gms <= ems_
     ms, launches, clocks, nfail, nfp64 = ((gms, glaunches, gclocks, gnfail, gnfp64) if use_graph
                                           else (ems_, elaunches, eclocks, enfail, enfp64))
-    out = {"value": nz * args.steps * world / (ms * 1e-3), "ms": ms, "launches": launches,
+    out = {"value": throughput(nz, args.steps, world, ms), "ms": ms, "launches": launches,
            "clocks": clocks, "err": err, "nfail": nfail, "launch": {"tpb_flux": tuned[0], "tpb_update": tuned[1]},
            "nfp64": nfp64,
            "mode": ("CUDA graph replay of kh_step (kh_set_graph)" if use_graph else
                     "kh_step launched kernel by kernel (eager), the mixed step's kernels chained by "
                     "programmatic dependent launch; the faster of eager and graph replay")}
-    out["graph"] = {"value": nz * args.steps * world / (gms * 1e-3), "ms_per_step": gms / args.steps}
+    out["graph"] = {"value": throughput(nz, args.steps, world, gms), "ms_per_step": gms / args.steps}
     out["prof"] = prof
-    out["profiled_graph"] = {"value": nz * args.steps * world / (pms * 1e-3), "ms_per_step": pms / args.steps,
+    out["profiled_graph"] = {"value": throughput(nz, args.steps, world, pms), "ms_per_step": pms / args.steps,
                              "how": "the captured step with the per-group CUDA events recorded inside every "
                                     "replay; source of the kernel timings (roofline, kernel_share)"}
-    out["eager"] = {"value": nz * args.steps * world / (ems_ * 1e-3), "ms_per_step": ems_ / args.steps}
+    out["eager"] = {"value": throughput(nz, args.steps, world, ems_), "ms_per_step": ems_ / args.steps}
     ctx.set_graph(use_graph)
     if use_graph:
         dt, _ = ctx.step(U, P, B, 0.5 * dt)  # capture (untimed) for the end-to-end leg
@@ -319,13 +335,9 @@ def measure(args, cfg, P0, ctx, dev, stream, dist, world, oracle_step, e2e=True)
             host.copy_(stage_d, non_blocking=True)
         f1.record(stream)
         torch.cuda.synchronize(dev)
-        ems = f0.elapsed_time(f1)
-        if dist:
-            t = torch.tensor([ems], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
+        ems = max_over_ranks(f0.elapsed_time(f1), dist, dev)
         nbytes = host.numel() * 8
-        copy_engine = {"value": nz * args.steps * world / (ems * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+        copy_engine = {"value": throughput(nz, args.steps, world, ems), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                        "d2h_bytes_per_step": nbytes,
                        "how": "pinned host buffer -> device buffer (copy engine) -> kh_unpack_state; kh_step; "
                               "kh_pack_state -> device buffer -> pinned host buffer"}
@@ -342,12 +354,8 @@ def measure(args, cfg, P0, ctx, dev, stream, dist, world, oracle_step, e2e=True)
             ctx.pack_state(U, P, B, host)
         z1.record(stream)
         torch.cuda.synchronize(dev)
-        zms = z0.elapsed_time(z1)
-        if dist:
-            t = torch.tensor([zms], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            zms = float(t.item())
-        direct = {"value": nz * args.steps * world / (zms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+        zms = max_over_ranks(z0.elapsed_time(z1), dist, dev)
+        direct = {"value": throughput(nz, args.steps, world, zms), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                   "d2h_bytes_per_step": nbytes,
                   "how": "kh_unpack_state reading the pinned host buffer and kh_pack_state writing it, over the "
                          "host link (no staging copy); kh_step between"}
